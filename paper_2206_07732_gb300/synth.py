@@ -1,0 +1,164 @@
+"""Seeded synthetic inputs for the wave-tank workloads.
+
+This module only draws random numbers and holds the workload definitions
+(grid sizes, fluid constants, wave and body parameters).  It contains none of
+the method's arithmetic: wave spectra, dispersion, materials, the time step and
+the pressure solve live in the CUDA library (and, independently, in the CPU
+oracle used by the tests).  Both sides receive the dictionaries built here.
+
+Fluid constants and tank geometry follow the paper's numerical wave tank
+(Section "Numerical wave tank", water/air properties of the test cases); the
+sizes are the workloads this library is benchmarked on.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+WATER = dict(rho_w=1025.0, mu_w=1.0e-3)
+AIR = dict(rho_a=1.225, mu_a=1.8e-5)
+GRAVITY = 9.81
+
+
+def _base(nx, ny, lx, ly, depth):
+    d = dict(nx=nx, ny=ny, lx=lx, ly=ly, depth=depth, g=GRAVITY)
+    d.update(WATER)
+    d.update(AIR)
+    return d
+
+
+def _solver(rtol=1e-8, precision=0):
+    return dict(rtol=rtol, max_iters=400, restart=20, n_reinit=4, n_jacobi=3,
+                mg_pre=2, mg_post=2, precision=precision)
+
+
+def box_body(xc, width, height, draft, depth, rho_w, pto_damping=0.0,
+             kappa_p=1e-8, extra_sink=0.0):
+    """Heaving box whose mass floats it at ``draft`` (per unit span).
+
+    The mass is the workload's definition of the body ("mass giving a draft"),
+    i.e. the displaced water mass per unit span; ``extra_sink`` shifts the
+    initial position downward from that equilibrium.
+    """
+    mass = rho_w * width * draft
+    yc = depth - draft + 0.5 * height - extra_sink
+    # Artificial added mass of the stabilised heave update: the water mass that
+    # would fill the box's rectangle (an upper scale of the 2D heave added mass).
+    added_mass = rho_w * width * height
+    return dict(xc=xc, yc=yc, width=width, height=height, mass=mass,
+                added_mass=added_mass, kappa_p=kappa_p, pto_damping=pto_damping)
+
+
+def regular_wave(H, T, rng):
+    """One Airy component: height H, period T, phase drawn from ``rng``."""
+    return dict(kind="regular", H=H, T=T, phase=float(rng.uniform(0.0, 2.0 * math.pi)))
+
+
+def irregular_wave(Hs, Tp, gamma, ncomp, rng):
+    """JONSWAP sea state; only the random phases are drawn here."""
+    return dict(kind="jonswap", Hs=Hs, Tp=Tp, gamma=gamma, ncomp=ncomp,
+                phases=rng.uniform(0.0, 2.0 * math.pi, size=ncomp).tolist())
+
+
+def tank_small(seed=0, nx=128, ny=64, **solver_kw):
+    """4 m x 2 m tank, 128x64, depth 1 m, regular wave H=0.05 T=1.0, box at x=2 m."""
+    rng = np.random.default_rng(seed)
+    c = _base(nx, ny, 4.0, 2.0, 1.0)
+    c["wave"] = regular_wave(0.05, 1.0, rng)
+    c["damp_x0"], c["damp_len"], c["probe_x"] = 3.0, 1.0, 0.5
+    c["body"] = box_body(2.0, 0.5, 0.4, 0.2, 1.0, c["rho_w"], pto_damping=50.0)
+    c["solver"] = _solver(**solver_kw)
+    c["dt"], c["steps"] = 1e-3, 100
+    c["name"] = f"tank {nx}x{ny} 4mx2m regular-wave box"
+    return c
+
+
+def tank_large(seed=0, nx=1024, ny=256, **solver_kw):
+    """16 m x 4 m tank, 1024x256, depth 2.5 m, JONSWAP Hs=0.15 Tp=1.6 gamma=3.3, 64 comps."""
+    rng = np.random.default_rng(seed)
+    c = _base(nx, ny, 16.0, 4.0, 2.5)
+    c["wave"] = irregular_wave(0.15, 1.6, 3.3, 64, rng)
+    # Damping zone: 1.5 peak wavelengths (deep-water estimate g Tp^2 / 2pi).
+    lam_p = GRAVITY * 1.6 ** 2 / (2.0 * math.pi)
+    c["damp_len"] = 1.5 * lam_p
+    c["damp_x0"] = 16.0 - c["damp_len"]
+    c["probe_x"] = 1.0
+    # Device placed one wavelength plus five half-widths from the inlet.
+    c["body"] = box_body(lam_p + 2.5, 1.0, 0.8, 0.4, 2.5, c["rho_w"], pto_damping=0.0)
+    c["solver"] = _solver(**solver_kw)
+    c["dt"], c["steps"] = 5e-4, 2000
+    c["pto_limit"] = 2000.0
+    c["name"] = f"tank {nx}x{ny} 16mx4m JONSWAP box"
+    return c
+
+
+def still_water(nx=64, ny=32, body=False, seed=0, **solver_kw):
+    """Still water (H=0) in a 4 m x 2 m tank; optional box at its floating draft."""
+    rng = np.random.default_rng(seed)
+    c = _base(nx, ny, 4.0, 2.0, 1.0)
+    w = regular_wave(0.0, 1.0, rng)
+    c["wave"] = w
+    c["damp_x0"], c["damp_len"], c["probe_x"] = 4.0, 0.0, 0.5
+    c["body"] = box_body(2.0, 0.5, 0.4, 0.2, 1.0, c["rho_w"], pto_damping=0.0) if body else None
+    c["solver"] = _solver(**solver_kw)
+    c["dt"], c["steps"] = 1e-3, 50
+    c["name"] = f"still water {nx}x{ny}"
+    return c
+
+
+def batch_tanks(ntanks=64, seed=0):
+    """Uneven tanks: h = 1/64 m, nx in 256..768, ny in 128..256 (multiples of 64)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(ntanks):
+        nx = int(rng.integers(4, 13)) * 64
+        ny = int(rng.integers(2, 5)) * 64
+        ny = min(ny, nx // 2)
+        h = 1.0 / 64.0
+        lx, ly = nx * h, ny * h
+        depth = 0.5 * ly
+        c = _base(nx, ny, lx, ly, depth)
+        H = float(rng.uniform(0.02, 0.1))
+        T = float(rng.uniform(0.8, 2.0))
+        c["wave"] = regular_wave(H, T, rng)
+        lam = GRAVITY * T * T / (2.0 * math.pi)
+        c["damp_len"] = min(1.5 * lam, 0.25 * lx)
+        c["damp_x0"] = lx - c["damp_len"]
+        c["probe_x"] = 0.25
+        bw = float(rng.uniform(0.25, 1.0))
+        bh = float(rng.uniform(0.2, 0.6))
+        c["body"] = box_body(0.5 * lx, bw, bh, 0.5 * bh, depth, c["rho_w"])
+        c["solver"] = _solver(precision=1)
+        c["dt"], c["steps"] = 5e-4, 500
+        c["name"] = f"batch tank {k} {nx}x{ny}"
+        out.append(c)
+    return out
+
+
+def random_fields(nx, ny, seed, scale=1.0):
+    """Seeded random cell/face arrays (used to perturb states in parity tests)."""
+    rng = np.random.default_rng(seed)
+    return dict(
+        cell=scale * rng.standard_normal((ny, nx)),
+        u=scale * rng.standard_normal((ny, nx + 1)),
+        v=scale * rng.standard_normal((ny + 1, nx)),
+    )
+
+
+def random_coefficients(nx, ny, seed, contrast=1.0):
+    """Seeded positive face coefficients for Poisson tests.
+
+    Faces on the left, right and bottom walls are zero (Neumann walls); the top
+    faces are kept (Dirichlet p=0 above the top row).  ``contrast`` > 1 draws a
+    log-uniform spread over that ratio.
+    """
+    rng = np.random.default_rng(seed)
+    lo = math.log(1.0)
+    hi = math.log(max(contrast, 1.0))
+    bu = np.exp(rng.uniform(lo, hi, size=(ny, nx + 1))) if contrast > 1 else 0.5 + rng.uniform(size=(ny, nx + 1))
+    bv = np.exp(rng.uniform(lo, hi, size=(ny + 1, nx))) if contrast > 1 else 0.5 + rng.uniform(size=(ny + 1, nx))
+    bu[:, 0] = 0.0
+    bu[:, nx] = 0.0
+    bv[0, :] = 0.0
+    return bu, bv
