@@ -1,0 +1,381 @@
+#!/usr/bin/env python
+"""Benchmark: cell-steps/s of the wave-tank step at a 1e-8 FP64 pressure residual.
+
+Workload: the 16 m x 4 m tank on a 1024 x 256 grid (depth 2.5 m, JONSWAP Hs 0.15 m,
+Tp 1.6 s, gamma 3.3, 64 seeded components, heaving 1 m x 0.8 m box, dt 5e-4 s).
+A step is one wec_step: force, heave, level set, momentum, pressure solve,
+projection.  Our arm runs the mixed-precision path (FP32 multigrid V-cycles
+inside FP64 FGMRES) and, beside it, the plain FP64 path on the same GPU.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (under torchrun): independent replicas, one tank per rank (the single
+tank is not partitioned), value = all ranks' cell-steps / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-steps/s at 1e-8 pressure residual: mixed+learned vs plain FP64, same GB300"
+UNIT = "cell-steps/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU-baseline sample budget")
+    return ap.parse_args()
+
+
+def workload(seed):
+    from paper_2206_07732_gb300 import synth
+    return synth.tank_large(seed=seed)
+
+
+def config_dict(cfg, precision, l2_note):
+    return {"workload": cfg["name"], "grid": f"{cfg['nx']}x{cfg['ny']}", "cells": cfg["nx"] * cfg["ny"],
+            "dt": cfg["dt"], "rtol": cfg["solver"]["rtol"], "precision": precision,
+            "wave": "JONSWAP Hs=0.15 Tp=1.6 gamma=3.3 N=64", "body": "box 1.0x0.8 m, heave",
+            "l2": l2_note, "seed": 0}
+
+
+# ----------------------------------------------------------------- oracle --
+def run_oracle(cfg, steps, budget_s=None):
+    """Time the CPU oracle on the same workload; returns (cell-steps/s, steps run)."""
+    from oracle.tank import OracleTank
+    T = OracleTank(cfg)
+    n = cfg["nx"] * cfg["ny"]
+    done = 0
+    t0 = time.perf_counter()
+    while done < steps:
+        T.step(cfg["dt"])
+        done += 1
+        if budget_s is not None and time.perf_counter() - t0 > budget_s:
+            break
+    el = time.perf_counter() - t0
+    return n * done / el, done, el
+
+
+# ------------------------------------------------------------------ clocks --
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- roofline --
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def source_sha():
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2206_07732_gb300", "csrc", "*"))):
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_key):
+    """dram bytes per launch of `kernel_key` from a committed ncu summary, if it
+    was captured on the current kernel sources (else None)."""
+    sha = source_sha()
+    for f in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
+        with open(f) as fh:
+            text = fh.read()
+        m_k = re.search(r"^roofline_kernel:\s*(\S+)", text, re.M)
+        m_s = re.search(r"^source_sha:\s*(\S+)", text, re.M)
+        m_t = re.search(r"^traffic_bytes_per_launch:\s*([0-9.eE+]+)", text, re.M)
+        if m_k and m_s and m_t and m_k.group(1) == kernel_key and m_s.group(1) == sha:
+            return float(m_t.group(1))
+    return None
+
+
+def read_profile(L):
+    import ctypes as C
+    mx, stride = 256, 64
+    names = C.create_string_buffer(mx * stride)
+    lv = (C.c_int * mx)()
+    la = (C.c_longlong * mx)()
+    ms = (C.c_double * mx)()
+    by = (C.c_double * mx)()
+    cnt = C.c_int(0)
+    L.wec_profile_read(mx, names, stride, lv, la, ms, by, C.byref(cnt))
+    out = []
+    for k in range(min(cnt.value, mx)):
+        nm = names.raw[k * stride:(k + 1) * stride].split(b"\0")[0].decode()
+        out.append(dict(name=nm, level=lv[k], launches=la[k], ms=ms[k], bytes=by[k]))
+    return out
+
+
+def setup_lib():
+    import ctypes as C
+    from paper_2206_07732_gb300 import build as B
+    from paper_2206_07732_gb300 import wec
+    B.build()
+    L = wec.load()
+    L.wec_launch_count.restype = C.c_longlong
+    L.wec_profile_enable.argtypes = [C.c_int, C.c_char_p]
+    L.wec_profile_read.argtypes = [C.c_int, C.c_char_p, C.c_size_t, C.POINTER(C.c_int), C.POINTER(C.c_longlong),
+                                   C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int)]
+    return L, wec
+
+
+# ---------------------------------------------------------------- our arm --
+def time_path(L, wec, torch, cfg, precision, steps, warmup, flush, profile_kernel=None):
+    """Time K steps (CUDA events per step on the tank's stream, L2 flushed in between)."""
+    tank = wec.Tank(cfg, precision=precision)
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        tank.step(cfg["dt"])
+    torch.cuda.synchronize()
+    if profile_kernel:
+        L.wec_profile_read(0, None, 0, None, None, None, None, (__import__("ctypes").c_int * 1)())
+        L.wec_profile_enable(2, profile_kernel.encode())
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    its, res = [], []
+    n0 = L.wec_launch_count()
+    if torch.distributed.is_initialized():
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for k in range(steps):
+        flush.zero_()  # evict the working set from L2 (outside the timed events)
+        ev[k][0].record(stream)
+        r = tank.step(cfg["dt"])
+        ev[k][1].record(stream)
+        its.append(r["iters"])
+        res.append(r["residual"])
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if torch.distributed.is_initialized():
+        torch.distributed.barrier()
+    launches = L.wec_launch_count() - n0
+    prof = None
+    if profile_kernel:
+        L.wec_profile_enable(0, None)
+        prof = read_profile(L)
+    ms = [a.elapsed_time(b) for a, b in ev]
+    tank.close()
+    return dict(ms=ms, iters=its, residual=max(res), launches=launches, wall=wall, prof=prof)
+
+
+def profile_all(L, wec, torch, cfg, precision, steps=2):
+    tank = wec.Tank(cfg, precision=precision)
+    for _ in range(3):
+        tank.step(cfg["dt"])
+    torch.cuda.synchronize()
+    read_profile(L)
+    L.wec_profile_enable(1, None)
+    for _ in range(steps):
+        tank.step(cfg["dt"])
+    L.wec_profile_enable(0, None)
+    p = read_profile(L)
+    tank.close()
+    return p
+
+
+def e2e_path(wec, torch, cfg, precision, steps, warmup, flush):
+    """Through the public call with host buffers: wec_step takes the host PTO
+    force and returns the host step record (synchronous D2H) every step."""
+    tank = wec.Tank(cfg, precision=precision)
+    for _ in range(warmup):
+        tank.step(cfg["dt"])
+    torch.cuda.synchronize()
+    t = []
+    for _ in range(steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tank.step(cfg["dt"], 0.0)  # result record read back to the host inside the call
+        t.append(time.perf_counter() - t0)
+    tank.close()
+    return t
+
+
+def main_ours(args):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    L, wec = setup_lib()
+    cfg = workload(args.seed)
+    n = cfg["nx"] * cfg["ny"]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 256 MiB > L2
+    steps, warmup = args.steps, max(args.warmup, 3)
+
+    # which kernel dominates the mixed path (untimed profiling pass)
+    prof_all = profile_all(L, wec, torch, cfg, wec.PREC_MIXED)
+    by_name = {}
+    for p in prof_all:
+        d = by_name.setdefault(p["name"], dict(ms=0.0, bytes=0.0, launches=0))
+        d["ms"] += p["ms"]; d["bytes"] += p["bytes"]; d["launches"] += p["launches"]
+    top = max(by_name, key=lambda k: by_name[k]["ms"])
+
+    clocks = Clocks(local)
+    clocks.start()
+    mixed = time_path(L, wec, torch, cfg, wec.PREC_MIXED, steps, warmup, flush, profile_kernel=top)
+    ck = clocks.stop()
+    fp64 = time_path(L, wec, torch, cfg, wec.PREC_FP64, steps, warmup, flush)
+    e2e = e2e_path(wec, torch, cfg, wec.PREC_MIXED, max(steps // 2, 5), warmup, flush)
+
+    def reduce_max(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    t_mixed = reduce_max(sum(mixed["ms"]) / 1e3)
+    t_fp64 = reduce_max(sum(fp64["ms"]) / 1e3)
+    t_e2e = reduce_max(sum(e2e))
+    value = world * n * steps / t_mixed
+    fp64_value = world * n * steps / t_fp64
+    e2e_value = world * n * len(e2e) / t_e2e
+
+    # roofline of the dominant kernel, live over the timed region
+    peak, peak_kind = peaks()
+    pk = [p for p in (mixed["prof"] or []) if p["name"] == top]
+    tot_ms = sum(p["ms"] for p in pk)
+    tot_b = sum(p["bytes"] for p in pk)
+    nl = sum(p["launches"] for p in pk)
+    achieved = (tot_b / nl) / (tot_ms / nl / 1e3) / 1e9 if nl and tot_ms > 0 else None
+    share = by_name[top]["ms"] / sum(d["ms"] for d in by_name.values())
+    roofline = {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None,
+                "traffic": ncu_traffic(top), "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
+                "algorithmic_bytes_per_launch": (tot_b / nl) if nl else None,
+                "launches_timed": nl, "avg_launch_us": (tot_ms / nl * 1e3) if nl else None,
+                "share_of_step_gpu_time": share}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, k, el = run_oracle(cfg, 1000, budget_s=args.cpu_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{k} oracle steps of the 1024x256 tank from its initial state ({el:.1f} s, 1 thread)"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": warmup,
+        "ms_per_step": t_mixed / steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64+f32(multigrid)", "data": "synthetic (seeded JONSWAP phases)",
+        "config": config_dict(cfg, "mixed: FP32 V-cycles in FP64 FGMRES", "flushed between timed steps (256 MiB write)"),
+        "fp64_value": fp64_value, "fp64_ms_per_step": t_fp64 / steps * 1e3,
+        "speedup_mixed_vs_fp64": value / fp64_value,
+        "learned_warm_start": "not built",
+        "fgmres_iters_per_step": {"mixed": statistics.mean(mixed["iters"]), "fp64": statistics.mean(fp64["iters"])},
+        "max_relative_residual": {"mixed": mixed["residual"], "fp64": fp64["residual"]},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8, "d2h_bytes_per_step": 72,
+                "note": "wec_step wall clock: host PTO force in, host step record out, per step"},
+        "gpu_launches": mixed["launches"],
+        "clocks": ck,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import build as ob
+    ob.build()
+    cfg = workload(args.seed)
+    n = cfg["nx"] * cfg["ny"]
+    from oracle.tank import OracleTank
+    T = OracleTank(cfg)
+    for _ in range(max(args.warmup, 0)):
+        T.step(cfg["dt"])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        T.step(cfg["dt"])
+    el = time.perf_counter() - t0
+    v = n * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded JONSWAP phases)",
+            "config": config_dict(cfg, "fp64 (CPU oracle)", "n/a (CPU)"),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} timed oracle steps after {args.warmup} warm-up steps, 1 thread"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        main_reference(a)
+    else:
+        main_ours(a)

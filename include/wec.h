@@ -1,0 +1,238 @@
+/*
+ * wec.h -- C ABI of the GB300 wave-tank library (libwec.so).
+ *
+ * One time step of the two-phase (water/air) incompressible Navier-Stokes
+ * equations on a uniform staggered MAC grid with a Brinkman-penalised heaving
+ * body (arxiv 2206.07732, Sections "Continuous equations of motion" through
+ * "Fluid-structure coupling"), run as CUDA kernels on one sm_103a GPU.
+ *
+ * Conventions (all entry points):
+ *   - Return value: WEC_OK (0) or one of the WEC_ERR_* codes below; the message
+ *     of the last failure on the calling thread is returned by wec_last_error().
+ *   - The library owns every device buffer it allocates; host arrays passed in
+ *     are copied before the call returns and stay owned by the caller.
+ *   - Pointers documented as "device" are caller-owned device memory of the
+ *     current CUDA device (e.g. a torch tensor's data_ptr()), used on the
+ *     object's stream; the caller keeps them alive until the call returns.
+ *   - Units are SI; in 2D, forces, masses and PTO forces are per unit span.
+ *   - Layouts are row-major with x fastest:
+ *       cell arrays (sigma, p):  [ny][nx]        cell (i, j) centre ((i+1/2)h, (j+1/2)h)
+ *       u on x-faces:            [ny][nx+1]      face (i, j) at (i h, (j+1/2)h)
+ *       v on y-faces:            [ny+1][nx]      face (i, j) at ((i+1/2)h, j h)
+ *     (Section "Spatial discretization": cell-centred scalars, face velocities.)
+ *   - No entry point falls back to the CPU.  A missing or unusable GPU is an
+ *     error (WEC_ERR_CUDA).
+ */
+#ifndef WEC_H
+#define WEC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    WEC_OK = 0,
+    WEC_ERR_INVALID = 1,       /* bad sizes or parameters; nothing was changed      */
+    WEC_ERR_CUDA = 2,          /* a CUDA call failed (message names it)             */
+    WEC_ERR_NOT_CONVERGED = 3, /* solver hit max_iters; results are still written   */
+    WEC_ERR_NONFINITE = 4,     /* a NaN/Inf reached the step's scalars or residual  */
+    WEC_ERR_NOMEM = 5          /* device allocation failed                          */
+};
+
+/* Uniform 2D grid (Section "Spatial discretization"): h = lx / nx must equal
+ * ly / ny.  nx, ny >= 8 and even.  depth = still-water depth d above the bed. */
+typedef struct {
+    int nx, ny;
+    double lx, ly, depth;
+} wec_grid;
+
+/* Water (liquid) and air (gas) properties and gravity g = (0, -g)
+ * (Eq. momentum; Eqs. ls_flow with l = water, g = air). */
+typedef struct {
+    double rho_w, rho_a, mu_w, mu_a, g;
+} wec_fluids;
+
+/* Incident wave as ncomp Airy components eta = sum a_i cos(k_i x - w_i t + th_i)
+ * (Eqs. first_order_wave_elev, irregular_elevation).  k_i is computed by the
+ * library from w_i and depth (Eq. dispersion_relation).  Host arrays, copied.
+ * damp_x0 / damp_len: wave damping zone [damp_x0, damp_x0 + damp_len] at the
+ * outlet (Section "Numerical wave tank"; damp_len = 0 disables it).
+ * probe_x: x of the surface-elevation probe reported each step. */
+typedef struct {
+    int ncomp;
+    const double *amp, *omega, *phase;
+    double damp_x0, damp_len, probe_x;
+} wec_waves;
+
+/* Heaving rectangular body (2D box), SDF by CSG max of half-planes (Section
+ * "Interface tracking").  present = 0: no body.  mass per unit span; the solid
+ * density is mass / (width height).  kappa_p: Brinkman permeability (Eq.
+ * bp_discrete, O(1e-8)).  pto_damping: linear PTO damper c, F_PTO = f_pto - c zdot.
+ * added_mass: artificial added mass m_a of the stabilised heave update
+ *   (m + m_a)(zdot^{n+1} - zdot^n) = dt (F_hydro - m g + F_PTO) + m_a (zdot^n - zdot^{n-1});
+ *   m_a = 0 is Eq. newton_u exactly. */
+typedef struct {
+    int present;
+    double xc, yc, width, height, mass, added_mass, kappa_p, pto_damping;
+} wec_body;
+
+enum { WEC_PREC_FP64 = 0, WEC_PREC_MIXED = 1 };
+
+/* Pressure solver and step options.  precision: WEC_PREC_FP64 (everything FP64)
+ * or WEC_PREC_MIXED (multigrid V-cycles in FP32 inside the FP64 FGMRES; the
+ * residual, orthogonalisation and all step arithmetic stay FP64).
+ * rtol: relative FP64 residual ||b - A x||_2 <= rtol ||b||_2 of each solve.
+ * restart: FGMRES restart length m (1..32).  n_reinit: Sussman pseudo-steps per
+ * step.  n_jacobi: Jacobi sweeps of the Crank-Nicolson momentum system.
+ * mg_pre / mg_post: red-black Gauss-Seidel sweeps before / after coarse correction. */
+typedef struct {
+    int precision;
+    double rtol;
+    int max_iters, restart, n_reinit, n_jacobi, mg_pre, mg_post;
+} wec_solver_opts;
+
+/* Record of one step.  z: heave displacement from the initial position;
+ * f_hydro: heave force of Eq. int_fh (from the step's initial p, u); f_pto: the
+ * PTO force used; eta_probe: surface elevation at probe_x (NaN if no crossing);
+ * residual: final relative FP64 residual of the pressure solve; div_norm:
+ * ||h div u^{n+1}||_2; iters: FGMRES iterations (V-cycles); status: WEC_* code. */
+typedef struct {
+    double t, z, zdot, f_hydro, f_pto, eta_probe, residual, div_norm;
+    int iters, status;
+} wec_step_result;
+
+typedef struct wec_tank wec_tank;
+typedef struct wec_poisson wec_poisson;
+
+/* Field ids for wec_get_field / wec_set_field. */
+enum {
+    WEC_F_SIGMA = 0,   /* level set sigma^n (cells; < 0 water)                 */
+    WEC_F_U = 1,       /* u^n (x-faces)                                         */
+    WEC_F_V = 2,       /* v^n (y-faces)                                         */
+    WEC_F_P = 3,       /* p^{n-1/2} (cells)                                     */
+    WEC_F_USTAR = 4,   /* last step's predicted u* (x-faces), read only         */
+    WEC_F_VSTAR = 5,   /* last step's predicted v* (y-faces), read only         */
+    WEC_F_BETA_U = 6,  /* last step's pressure coefficient 1/D on x-faces, r/o  */
+    WEC_F_BETA_V = 7,  /* last step's pressure coefficient 1/D on y-faces, r/o  */
+    WEC_F_RHS = 8,     /* last step's pressure right-hand side -h div u*, r/o   */
+    WEC_F_SIGMA_ADV = 9 /* last step's advected sigma before reinit, r/o        */
+};
+
+/* Create a tank and its initial state: sigma = y - (d + eta(x, 0)), Airy
+ * velocities (Wheeler-stretched, zero in air), p = discrete hydrostatic pressure
+ * of the flow density.  stream: a cudaStream_t (NULL = legacy default stream)
+ * on which every later call on this tank is enqueued.  *out receives the tank.
+ * Errors: WEC_ERR_INVALID (non-uniform h, odd or too small sizes, non-positive
+ * densities or kappa_p, ncomp < 0, restart out of range), WEC_ERR_NOMEM,
+ * WEC_ERR_CUDA.  On error *out is NULL and nothing leaks. */
+int wec_tank_create(const wec_grid *grid, const wec_fluids *fluids, const wec_waves *waves,
+                    const wec_body *body, const wec_solver_opts *opts, void *cuda_stream,
+                    wec_tank **out);
+
+/* Free a tank (NULL is ignored).  Synchronises its stream first. */
+void wec_tank_destroy(wec_tank *tank);
+
+/* Advance one step of size dt > 0 (Sections "Solution methodology" and "Time
+ * stepping scheme", n_cycles = 1): hydrodynamic force from p^{n-1/2}, u^n (Eq.
+ * int_fh) -> heave update (Eq. newton_u, stabilised as in wec_body) -> psi at the
+ * new position -> sigma advection (PPM) and damping-zone relaxation -> Sussman
+ * reinitialisation -> materials (Eqs. ls_flow, ls_solid) -> consistent transport
+ * and Crank-Nicolson momentum with implicit Brinkman term (Eqs.
+ * c_discrete_momentum, bp_discrete) -> pressure increment by FGMRES + multigrid ->
+ * projection (Eq. c_discrete_continuity).  pto_force is added to -c zdot^n.
+ * out (host, may be NULL) receives the step record; the call synchronises the
+ * tank's stream when out != NULL.  Returns the step's status.  A solve that does
+ * not converge still completes the step (WEC_ERR_NOT_CONVERGED). */
+int wec_step(wec_tank *tank, double dt, double pto_force, wec_step_result *out);
+
+/* nsteps steps; pto_forces (host, nsteps values, or NULL = zeros); out_n (host,
+ * nsteps records, or NULL).  Stops at the first step whose status is not WEC_OK
+ * and returns it. */
+int wec_step_n(wec_tank *tank, int nsteps, double dt, const double *pto_forces,
+               wec_step_result *out_n);
+
+/* Solve A p = rhs with the tank's pressure operator of its last step (face
+ * coefficients 1/D; Neumann walls, p = 0 above the top row).  rhs, p: device,
+ * nx*ny doubles; p holds the initial guess on entry and the solution on exit.
+ * rtol > 0; iters / final_rel_residual (host, may be NULL).  Errors:
+ * WEC_ERR_INVALID before the first step (no operator yet), WEC_ERR_NOT_CONVERGED. */
+int wec_pressure_solve(wec_tank *tank, const double *rhs, double *p, double rtol, int *iters,
+                       double *final_rel_residual);
+
+/* Copy a field (ids above) to / from host memory; n must equal the field's size.
+ * Setting a read-only field is WEC_ERR_INVALID.  Synchronous. */
+int wec_get_field(const wec_tank *tank, int field_id, double *host_dst, size_t n);
+int wec_set_field(wec_tank *tank, int field_id, const double *host_src, size_t n);
+
+/* Body/time state: out[0..4] = t, yc (body centre y), zdot, zdot^{n-1}, yc at creation. */
+int wec_get_state(const wec_tank *tank, double *out5);
+int wec_set_state(wec_tank *tank, double t, double yc, double zdot, double zdot_prev);
+
+/* Checkpoint: *n receives the byte size when buf is NULL; otherwise buf (host,
+ * *n bytes) receives (sigma, u, v, p, t, yc, zdot, zdot_prev).  wec_load restores
+ * it into a tank of the same size; resuming reproduces the same steps bit for bit. */
+int wec_save(const wec_tank *tank, void *buf, size_t *n);
+int wec_load(wec_tank *tank, const void *buf, size_t n);
+
+/* ---- standalone pressure solver on caller coefficients ------------------ */
+/* The operator of the pressure equation on an nx x ny grid: (A p)_c = sum over
+ * the cell's faces of beta_f (p_c - p_nb), with the left, right and bottom walls
+ * Neumann whatever beta holds there and the top face Dirichlet p = 0 (ghost -p_c,
+ * i.e. 2 beta_top p_c).  Preconditioner: one multigrid V(mg_pre, mg_post) cycle
+ * (red-black Gauss-Seidel, 2x2 sum restriction, piecewise-constant prolongation,
+ * coarse faces = mean of the two fine faces, dense LU on the coarsest level).
+ * nx, ny >= 2. */
+int wec_poisson_create(int nx, int ny, const wec_solver_opts *opts, void *cuda_stream,
+                       wec_poisson **out);
+void wec_poisson_destroy(wec_poisson *P);
+/* beta_u: device, (nx+1)*ny; beta_v: device, nx*(ny+1).  Copied; builds the hierarchy. */
+int wec_poisson_set_coefficients(wec_poisson *P, const double *beta_u, const double *beta_v);
+/* y = A x (device, nx*ny each). */
+int wec_poisson_apply(wec_poisson *P, const double *x, double *y);
+/* x = M^{-1} b: one V-cycle from a zero guess (device, nx*ny each), in the
+ * object's precision (FP32 arithmetic for WEC_PREC_MIXED, FP64 values in/out). */
+int wec_poisson_vcycle(wec_poisson *P, const double *b, double *x);
+/* FGMRES(restart) right-preconditioned by the V-cycle; x: device, guess in,
+ * solution out.  Converged when ||b - A x||_2 <= rtol ||b||_2 (true residual). */
+int wec_poisson_solve(wec_poisson *P, const double *b, double *x, double rtol, int max_iters,
+                      int *iters, double *final_rel_residual);
+
+/* ---- host wave utilities (no device work) ------------------------------- */
+/* k solving omega^2 = g k tanh(k d) (Eq. dispersion_relation), |residual| <= 1e-14 omega^2. */
+double wec_wave_number(double omega, double depth, double g);
+/* Fenton's explicit k d (Eq. explicit_dispersion_relation). */
+double wec_wave_number_fenton_kd(double omega, double depth, double g);
+/* JONSWAP sea state as ncomp Airy components (Eq. wave_spectrum_amplitude with the
+ * Bretschneider shape of Eq. Bretshneider_wave_spec, its period taken so that the
+ * spectrum peaks at 2 pi / Tp, times the peak enhancement gamma^r, r =
+ * exp(-(w - wp)^2 / (2 s^2 wp^2)), s = 0.07 / 0.09); equal bins over
+ * [1.6 / 3.5955, 20 / 3.5955] wp at their mid-points; amplitudes rescaled so that
+ * 4 sqrt(sum a^2 / 2) = Hs.  amp, omega: host, ncomp each (outputs). */
+int wec_jonswap(double Hs, double Tp, double gamma, int ncomp, double *amp, double *omega);
+
+/* ---- launch accounting and profiling ------------------------------------ */
+/* Number of kernels this library has launched in the process so far. */
+long long wec_launch_count(void);
+/* mode 0: off; 1: time every kernel launch with a CUDA event pair on its stream;
+ * 2: time only kernels whose name equals `only`.  Names are the kernel names
+ * reported by wec_profile_read (e.g. "mg_rbgs"). */
+int wec_profile_enable(int mode, const char *only);
+/* Aggregate the timed launches since the last read, per (kernel name, multigrid
+ * level; -1 = not a multigrid kernel), and forget them.  Synchronises on the
+ * recorded events.  *count receives the number of aggregates; at most max are
+ * written: names (max rows of name_stride chars), levels, launches, total ms and
+ * total algorithmic bytes (the bytes the operation must read and write at least
+ * once, as counted by the launch site). */
+int wec_profile_read(int max, char *names, size_t name_stride, int *levels, long long *launches, double *ms,
+                     double *bytes, int *count);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *wec_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WEC_H */

@@ -1,0 +1,931 @@
+// One time step of the two-phase wave tank on the GPU (2D, FP64).
+//
+// Paper (arxiv 2206.07732) passages implemented here:
+//   Eq. int_fh ............ heave force as a sum over the faces where the body SDF
+//                           changes sign (k_force_partial, k_heave)
+//   Eq. newton_u .......... heave update, with an artificial added mass that keeps
+//                           the n_cycles = 1 coupling stable (k_heave)
+//   Section "Interface tracking" and "Level set advection" .. PPM advection of
+//                           sigma (k_advect), Sussman reinitialisation (k_reinit),
+//                           analytic body SDF psi by CSG max (psi_box)
+//   Eqs. ls_flow, ls_solid, Hflow, Hbody .. materials (k_materials)
+//   Eq. c_discrete_momentum .. consistent mass/momentum transport, Crank-Nicolson
+//                           viscosity, flow-density gravity, implicit Brinkman term
+//                           (Eq. bp_discrete) (k_mom_u, k_mom_v, k_jacobi)
+//   Eq. spongelayer ....... vorticity damping over the top four cells
+//   Section "Numerical wave tank" .. Airy inflow at x = 0, wave damping zone
+//   Eq. c_discrete_continuity .. incremental projection (k_proj_rhs, solver, k_project)
+// Layouts: cells [ny][nx], u [ny][nx+1], v [ny+1][nx]; one thread per cell/face,
+// consecutive threads along x (coalesced rows).
+#include <algorithm>
+#include <cmath>
+#include <utility>
+
+#include "tank.cuh"
+
+namespace wec {
+namespace {
+
+constexpr int TB = 256;
+
+__device__ __forceinline__ int clampi(int a, int lo, int hi) { return a < lo ? lo : (a > hi ? hi : a); }
+__device__ __forceinline__ double sq(double a) { return a * a; }
+
+// Smoothed Heaviside of Eqs. Hflow / Hbody, half-width eps = n_cells h (n_cells = 1).
+__device__ __forceinline__ double heav(double phi, double eps)
+{
+    if (phi < -eps) return 0.0;
+    if (phi > eps) return 1.0;
+    return 0.5 * (1.0 + phi / eps + sin(kPi * phi / eps) / kPi);
+}
+
+// Box SDF as the CSG intersection (max) of four half-planes.
+__device__ __forceinline__ double psi_box(const TankP &P, double x, double y, double yc)
+{
+    if (!P.has_body) return 1.0e3;
+    return fmax(fabs(x - P.bxc) - 0.5 * P.bw, fabs(y - yc) - 0.5 * P.bh);
+}
+
+__device__ double eta_at(const TankP &P, double x, double t)
+{
+    double e = 0.0;
+    for (int c = 0; c < P.ncomp; ++c) e += P.amp[c] * cos(P.kw[c] * x - P.omega[c] * t + P.phase[c]);
+    return e;
+}
+
+// Linear Airy velocity with Wheeler stretching y' = d y / (d + eta) up to the
+// surface, blended to zero in the air by 1 - H(y - d - eta).
+__device__ void airy_uv(const TankP &P, double x, double y, double t, double *uo, double *vo)
+{
+    double d = P.depth;
+    double e = eta_at(P, x, t);
+    double ys = y < d + e ? y : d + e;
+    double yp = d * ys / (d + e);
+    double blend = 1.0 - heav(y - d - e, P.h);
+    double su = 0.0, sv = 0.0;
+    for (int c = 0; c < P.ncomp; ++c) {
+        double k = P.kw[c], w = P.omega[c];
+        double ph = k * x - w * t + P.phase[c];
+        double sk = sinh(k * d);
+        su += P.amp[c] * w * cosh(k * yp) / sk * cos(ph);
+        sv += P.amp[c] * w * sinh(k * yp) / sk * sin(ph);
+    }
+    *uo = blend * su;
+    *vo = blend * sv;
+}
+
+// -------------------------------------------------------- ghost values ----
+// sigma: left = incident wave y - d - eta(x, t) (eta precomputed per ghost column),
+// right = zero gradient, bottom/top = linear extrapolation.
+__device__ __forceinline__ double sig_at(const TankP &P, const double *__restrict__ s,
+                                         const double *__restrict__ etag, int i, int j)
+{
+    if (i < 0) return (j + 0.5) * P.h - P.depth - etag[-1 - i];
+    if (i > P.nx - 1) i = P.nx - 1;
+    if (j < 0) return s[i] + j * (s[P.nx + i] - s[i]);
+    if (j > P.ny - 1) {
+        int m = j - (P.ny - 1);
+        double a = s[(P.ny - 1) * P.nx + i], b = s[(P.ny - 2) * P.nx + i];
+        return a + m * (a - b);
+    }
+    return s[j * P.nx + i];
+}
+
+__device__ __forceinline__ double u_at(const TankP &P, const double *__restrict__ u, int i, int j)
+{
+    return u[clampi(j, 0, P.ny - 1) * (P.nx + 1) + clampi(i, 0, P.nx)];
+}
+
+// v: clamp rows; right wall free slip; left: odd reflection about v_in(y_j, t).
+__device__ __forceinline__ double v_at(const TankP &P, const double *__restrict__ v,
+                                       const double *__restrict__ vin, int i, int j)
+{
+    j = clampi(j, 0, P.ny);
+    if (i > P.nx - 1) i = P.nx - 1;
+    if (i < 0) return 2.0 * vin[j] - v[j * P.nx + (-1 - i)];
+    return v[j * P.nx + i];
+}
+
+__device__ __forceinline__ double cell_at(const TankP &P, const double *__restrict__ a, int i, int j)
+{
+    return a[clampi(j, 0, P.ny - 1) * P.nx + clampi(i, 0, P.nx - 1)];
+}
+
+// ----------------------------------------------------------------- PPM ----
+__device__ __forceinline__ double vl_slope(double am, double a0, double ap)
+{
+    double dl = a0 - am, dr = ap - a0;
+    if (dl * dr <= 0.0) return 0.0;
+    double dc = 0.5 * (ap - am);
+    double m = fmin(fabs(dc), fmin(2.0 * fabs(dl), 2.0 * fabs(dr)));
+    return dc > 0.0 ? m : -m;
+}
+
+// Limited Colella-Woodward edge values of the middle cell of a[0..4].
+__device__ __forceinline__ void ppm_edges(const double *a, double &L, double &R)
+{
+    double dm = vl_slope(a[0], a[1], a[2]);
+    double d0 = vl_slope(a[1], a[2], a[3]);
+    double dp = vl_slope(a[2], a[3], a[4]);
+    L = a[1] + 0.5 * (a[2] - a[1]) - (d0 - dm) / 6.0;
+    R = a[2] + 0.5 * (a[3] - a[2]) - (dp - d0) / 6.0;
+    double c = a[2];
+    if ((R - c) * (c - L) <= 0.0) {
+        L = c;
+        R = c;
+    } else {
+        double dA = R - L;
+        double m6 = dA * (c - 0.5 * (L + R));
+        double q = dA * dA / 6.0;
+        if (m6 > q)
+            L = 3.0 * c - 2.0 * R;
+        else if (-q > m6)
+            R = 3.0 * c - 2.0 * L;
+    }
+}
+
+// Time-centred upwind face state; a[0..5] = cells f-3..f+2 around face f.
+__device__ __forceinline__ double ppm_face(const double *a, double vel, double dt, double h)
+{
+    double L, R;
+    if (vel >= 0.0) {
+        ppm_edges(a, L, R);
+        double C = vel * dt / h, dA = R - L, a6 = 6.0 * (a[2] - 0.5 * (L + R));
+        return R - 0.5 * C * (dA - (1.0 - 2.0 * C / 3.0) * a6);
+    }
+    ppm_edges(a + 1, L, R);
+    double C = -vel * dt / h, dA = R - L, a6 = 6.0 * (a[3] - 0.5 * (L + R));
+    return L + 0.5 * C * (dA + (1.0 - 2.0 * C / 3.0) * a6);
+}
+
+__device__ __forceinline__ double damp_alpha(const TankP &P, double x)
+{
+    if (P.damp_len <= 0.0 || x <= P.damp_x0) return 0.0;
+    double xi = (x - P.damp_x0) / P.damp_len;
+    if (xi > 1.0) xi = 1.0;
+    return (exp(pow(xi, 3.5)) - 1.0) / (exp(1.0) - 1.0);
+}
+
+__device__ __forceinline__ double vort_damp(const TankP &P, double y, double dt)
+{
+    double w = 4.0 * P.h;
+    if (y < P.ly - w) return 0.0;
+    double zt = (y - P.ly) / w;
+    return P.rho_a * (cos(kPi * zt) + 1.0) / (4.0 * dt);
+}
+
+__device__ __forceinline__ double minmod(double a, double b)
+{
+    if (a * b <= 0.0) return 0.0;
+    return fabs(a) < fabs(b) ? a : b;
+}
+
+__device__ __forceinline__ double koren(double quu, double qu, double qd)
+{
+    double d1 = qu - quu, d2 = qd - qu;
+    if (d1 * d2 <= 0.0) return qu;
+    double m = fmin(2.0 * fabs(d2), fmin((fabs(d1) + 2.0 * fabs(d2)) / 3.0, 2.0 * fabs(d1)));
+    return d1 > 0.0 ? qu + 0.5 * m : qu - 0.5 * m;
+}
+
+__device__ __forceinline__ double upwind(double q0, double q1, double q2, double q3, double vel)
+{
+    return vel >= 0.0 ? koren(q0, q1, q2) : koren(q3, q2, q1);
+}
+
+// ------------------------------------------------------------- kernels ----
+__global__ void k_bc(TankP P, const StepScalars *S, double dt, Bc bc)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j > P.ny) return;
+    double t0 = S->t, t1 = S->t + dt, uu, vv;
+    if (j < P.ny) {
+        airy_uv(P, 0.0, (j + 0.5) * P.h, t1, &uu, &vv);
+        bc.uin1[j] = uu;
+    }
+    airy_uv(P, 0.0, j * P.h, t0, &uu, &vv);
+    bc.vin0[j] = vv;
+    airy_uv(P, 0.0, j * P.h, t1, &uu, &vv);
+    bc.vin1[j] = vv;
+    if (j < 3) {
+        double x = (-1 - j + 0.5) * P.h;
+        bc.eta0[j] = eta_at(P, x, t0);
+        bc.eta1[j] = eta_at(P, x, t1);
+    }
+}
+
+// Cell materials from sigma and the body at yc (which = 0: y_c^n, 1: y_c^{n+1}).
+__global__ void k_materials(TankP P, const StepScalars *S, int which, const double *__restrict__ sig,
+                            double *rho, double *mu, double *rhof, double *chi)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= P.nx * P.ny) return;
+    int i = c % P.nx, j = c / P.nx;
+    double yc = which ? S->yc1 : S->yc;
+    double ps = psi_box(P, (i + 0.5) * P.h, (j + 0.5) * P.h, yc);
+    double hf = heav(sig[c], P.h), hb = heav(ps, P.h);
+    double rf = P.rho_w + (P.rho_a - P.rho_w) * hf;
+    double mf = P.mu_w + (P.mu_a - P.mu_w) * hf;
+    if (rho) rho[c] = P.rho_s + (rf - P.rho_s) * hb;
+    if (mu) mu[c] = P.mu_s + (mf - P.mu_s) * hb;
+    if (rhof) rhof[c] = rf;
+    if (chi) chi[c] = 1.0 - hb;
+}
+
+__device__ double block_sum(double v, double *sh)
+{
+    int t = threadIdx.x;
+    sh[t] = v;
+    __syncthreads();
+    for (int s = blockDim.x >> 1; s > 0; s >>= 1) {
+        if (t < s) sh[t] += sh[t + s];
+        __syncthreads();
+    }
+    double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+// Eq. int_fh, heave component: faces whose two cells have opposite psi sign;
+// pressure linearly interpolated to the psi = 0 crossing with |psi| weights;
+// n_f out of the body; viscous traction by central differences at the face.
+__global__ void k_force_partial(TankP P, const StepScalars *S, const double *__restrict__ p,
+                                const double *__restrict__ u, const double *__restrict__ v,
+                                const double *__restrict__ mu, const double *__restrict__ vin0,
+                                double *__restrict__ part)
+{
+    __shared__ double sh[TB];
+    const int nx = P.nx, ny = P.ny;
+    const double h = P.h, yc = S->yc;
+    long long ny_faces = (long long)(ny - 1) * nx, nx_faces = (long long)ny * (nx - 1);
+    double acc = 0.0;
+    if (P.has_body) {
+        for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < ny_faces + nx_faces;
+             k += (long long)gridDim.x * blockDim.x) {
+            if (k < ny_faces) {
+                int i = (int)(k % nx), j = (int)(k / nx) + 1;
+                double x = (i + 0.5) * h;
+                double pl = psi_box(P, x, (j - 0.5) * h, yc), pr = psi_box(P, x, (j + 0.5) * h, yc);
+                if (!(pl * pr < 0.0)) continue;
+                double nrm = pl < 0.0 ? 1.0 : -1.0;
+                double wl = fabs(pl), wr = fabs(pr);
+                double pf = (p[(j - 1) * nx + i] * wr + p[j * nx + i] * wl) / (wl + wr);
+                double muf = 0.5 * (mu[(j - 1) * nx + i] + mu[j * nx + i]);
+                double dvdy = (v_at(P, v, vin0, i, j + 1) - v_at(P, v, vin0, i, j - 1)) / (2.0 * h);
+                acc += (-pf * nrm + muf * 2.0 * dvdy * nrm) * h;
+            } else {
+                long long q = k - ny_faces;
+                int i = (int)(q % (nx - 1)) + 1, j = (int)(q / (nx - 1));
+                double y = (j + 0.5) * h;
+                double pl = psi_box(P, (i - 0.5) * h, y, yc), pr = psi_box(P, (i + 0.5) * h, y, yc);
+                if (!(pl * pr < 0.0)) continue;
+                double nrm = pl < 0.0 ? 1.0 : -1.0;
+                double muf = 0.5 * (mu[j * nx + i - 1] + mu[j * nx + i]);
+                double dvdx = 0.5 * ((v_at(P, v, vin0, i, j) - v_at(P, v, vin0, i - 1, j)) +
+                                     (v_at(P, v, vin0, i, j + 1) - v_at(P, v, vin0, i - 1, j + 1))) / h;
+                double dudy = (u_at(P, u, i, j + 1) - u_at(P, u, i, j - 1)) / (2.0 * h);
+                acc += muf * (dvdx + dudy) * nrm * h;
+            }
+        }
+    }
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+// Sum of the force partials (fixed order), then the stabilised heave update:
+// (m + m_a)(zdot^{n+1} - zdot^n) = dt (F - m g + F_PTO) + m_a (zdot^n - zdot^{n-1}).
+__global__ void k_heave(TankP P, StepScalars *S, const double *__restrict__ part, double dt, double fpto_in)
+{
+    __shared__ double sh[TB];
+    double s = 0.0;
+    for (int b = threadIdx.x; b < kRedBlocks; b += blockDim.x) s += part[b];
+    double F = block_sum(s, sh);
+    if (threadIdx.x != 0) return;
+    double fpto = fpto_in - P.pto_c * S->zdot;
+    double zd1 = S->zdot, yc1 = S->yc;
+    if (P.has_body) {
+        double m = P.mass, ma = P.added_mass;
+        zd1 = S->zdot + (dt * (F - m * P.g + fpto) + ma * (S->zdot - S->zdot_prev)) / (m + ma);
+        yc1 = S->yc + 0.5 * dt * (S->zdot + zd1);
+    }
+    S->F = F;
+    S->fpto = fpto;
+    S->zdot1 = zd1;
+    S->yc1 = yc1;
+}
+
+// sigma* = sigma^n - dt Q(u^n, sigma^n), then damping-zone relaxation.
+__global__ void k_advect(TankP P, const double *__restrict__ s, const double *__restrict__ u,
+                         const double *__restrict__ v, const double *__restrict__ eta0, double dt,
+                         double *__restrict__ out)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= P.nx * P.ny) return;
+    const int nx = P.nx, i = c % nx, j = c / nx;
+    const double h = P.h;
+    double a[6], fx[2], fy[2];
+    for (int f = 0; f < 2; ++f) {
+        int fi = i + f;
+        for (int q = 0; q < 6; ++q) a[q] = sig_at(P, s, eta0, fi - 3 + q, j);
+        fx[f] = ppm_face(a, u[j * (nx + 1) + fi], dt, h);
+        int fj = j + f;
+        for (int q = 0; q < 6; ++q) a[q] = sig_at(P, s, eta0, i, fj - 3 + q);
+        fy[f] = ppm_face(a, v[fj * nx + i], dt, h);
+    }
+    double ub = 0.5 * (u[j * (nx + 1) + i] + u[j * (nx + 1) + i + 1]);
+    double vb = 0.5 * (v[j * nx + i] + v[(j + 1) * nx + i]);
+    double Q = ub * (fx[1] - fx[0]) / h + vb * (fy[1] - fy[0]) / h;
+    double sa = s[c] - dt * Q;
+    double al = damp_alpha(P, (i + 0.5) * h);
+    out[c] = (1.0 - al) * sa + al * ((j + 0.5) * h - P.depth);
+}
+
+// Sussman relaxation right-hand side S(sigma0)(|grad f| - 1), Godunov
+// Hamiltonian on ENO-2 (minmod) one-sided differences.
+__device__ double reinit_rhs(const TankP &P, const double *__restrict__ f, const double *__restrict__ s0,
+                             const double *__restrict__ eta1, int i, int j)
+{
+    const double h = P.h;
+    double c = f[j * P.nx + i];
+    double xm2 = sig_at(P, f, eta1, i - 2, j), xm1 = sig_at(P, f, eta1, i - 1, j);
+    double xp1 = sig_at(P, f, eta1, i + 1, j), xp2 = sig_at(P, f, eta1, i + 2, j);
+    double ym2 = sig_at(P, f, eta1, i, j - 2), ym1 = sig_at(P, f, eta1, i, j - 1);
+    double yp1 = sig_at(P, f, eta1, i, j + 1), yp2 = sig_at(P, f, eta1, i, j + 2);
+    double dxm = xm2 - 2.0 * xm1 + c, dx0 = xm1 - 2.0 * c + xp1, dxp = c - 2.0 * xp1 + xp2;
+    double dym = ym2 - 2.0 * ym1 + c, dy0 = ym1 - 2.0 * c + yp1, dyp = c - 2.0 * yp1 + yp2;
+    double a = (c - xm1) / h + minmod(dxm, dx0) / (2.0 * h);
+    double b = (xp1 - c) / h - minmod(dx0, dxp) / (2.0 * h);
+    double cc = (c - ym1) / h + minmod(dym, dy0) / (2.0 * h);
+    double d = (yp1 - c) / h - minmod(dy0, dyp) / (2.0 * h);
+    double g0 = s0[j * P.nx + i];
+    double S = g0 / sqrt(g0 * g0 + h * h);
+    double gx, gy;
+    if (S > 0.0) {
+        gx = fmax(sq(fmax(a, 0.0)), sq(fmin(b, 0.0)));
+        gy = fmax(sq(fmax(cc, 0.0)), sq(fmin(d, 0.0)));
+    } else {
+        gx = fmax(sq(fmin(a, 0.0)), sq(fmax(b, 0.0)));
+        gy = fmax(sq(fmin(cc, 0.0)), sq(fmax(d, 0.0)));
+    }
+    return S * (sqrt(gx + gy) - 1.0);
+}
+
+// TVD-RK2 stage: stage 1 out = f - dtau L(f); stage 2 out = (fprev + (f - dtau L(f))) / 2.
+__global__ void k_reinit(TankP P, const double *__restrict__ f, const double *__restrict__ s0,
+                         const double *__restrict__ fprev, const double *__restrict__ eta1, double dtau,
+                         double *__restrict__ out)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= P.nx * P.ny) return;
+    int i = c % P.nx, j = c / P.nx;
+    double s1 = f[c] - dtau * reinit_rhs(P, f, s0, eta1, i, j);
+    out[c] = fprev ? 0.5 * (fprev[c] + s1) : s1;
+}
+
+// ---------------------------------------------------- momentum helpers ----
+struct Fields {
+    const double *rc;         // cell density rho^n (transport)
+    const double *u, *v;      // velocities
+    const double *vin;        // left tangential inflow for v ghosts
+};
+
+__device__ __forceinline__ double ru_at(const TankP &P, const double *rc, int i, int j)
+{
+    i = clampi(i, 0, P.nx);
+    j = clampi(j, 0, P.ny - 1);
+    return 0.5 * (cell_at(P, rc, i - 1, j) + cell_at(P, rc, i, j));
+}
+
+__device__ __forceinline__ double rv_at(const TankP &P, const double *rc, int i, int j)
+{
+    i = clampi(i, 0, P.nx - 1);
+    j = clampi(j, 0, P.ny);
+    return 0.5 * (cell_at(P, rc, i, j - 1) + cell_at(P, rc, i, j));
+}
+
+// Consistent transport on the u-face (i, j): rho-breve and C share the mass flux.
+__device__ void transport_u(const TankP &P, const Fields &X, int i, int j, double dt, double &rb, double &C)
+{
+    double m[4], f[4];
+    for (int s = 0; s < 2; ++s) {
+        int a = i - 1 + s;
+        double U = 0.5 * (u_at(P, X.u, a, j) + u_at(P, X.u, a + 1, j));
+        double r = upwind(ru_at(P, X.rc, a - 1, j), ru_at(P, X.rc, a, j), ru_at(P, X.rc, a + 1, j),
+                          ru_at(P, X.rc, a + 2, j), U);
+        double q = upwind(u_at(P, X.u, a - 1, j), u_at(P, X.u, a, j), u_at(P, X.u, a + 1, j),
+                          u_at(P, X.u, a + 2, j), U);
+        m[s] = U * r;
+        f[s] = m[s] * q;
+    }
+    for (int s = 0; s < 2; ++s) {
+        int b = j - 1 + s;
+        double V = 0.5 * (v_at(P, X.v, X.vin, i - 1, b + 1) + v_at(P, X.v, X.vin, i, b + 1));
+        double r = upwind(ru_at(P, X.rc, i, b - 1), ru_at(P, X.rc, i, b), ru_at(P, X.rc, i, b + 1),
+                          ru_at(P, X.rc, i, b + 2), V);
+        double q = upwind(u_at(P, X.u, i, b - 1), u_at(P, X.u, i, b), u_at(P, X.u, i, b + 1),
+                          u_at(P, X.u, i, b + 2), V);
+        m[2 + s] = V * r;
+        f[2 + s] = m[2 + s] * q;
+    }
+    rb = ru_at(P, X.rc, i, j) - dt / P.h * ((m[1] - m[0]) + (m[3] - m[2]));
+    C = ((f[1] - f[0]) + (f[3] - f[2])) / P.h;
+}
+
+__device__ void transport_v(const TankP &P, const Fields &X, int i, int j, double dt, double &rb, double &C)
+{
+    double m[4], f[4];
+    for (int s = 0; s < 2; ++s) {
+        int a = i - 1 + s;
+        double U = 0.5 * (u_at(P, X.u, a + 1, j - 1) + u_at(P, X.u, a + 1, j));
+        double r = upwind(rv_at(P, X.rc, a - 1, j), rv_at(P, X.rc, a, j), rv_at(P, X.rc, a + 1, j),
+                          rv_at(P, X.rc, a + 2, j), U);
+        double q = upwind(v_at(P, X.v, X.vin, a - 1, j), v_at(P, X.v, X.vin, a, j),
+                          v_at(P, X.v, X.vin, a + 1, j), v_at(P, X.v, X.vin, a + 2, j), U);
+        m[s] = U * r;
+        f[s] = m[s] * q;
+    }
+    for (int s = 0; s < 2; ++s) {
+        int b = j - 1 + s;
+        double V = 0.5 * (v_at(P, X.v, X.vin, i, b) + v_at(P, X.v, X.vin, i, b + 1));
+        double r = upwind(rv_at(P, X.rc, i, b - 1), rv_at(P, X.rc, i, b), rv_at(P, X.rc, i, b + 1),
+                          rv_at(P, X.rc, i, b + 2), V);
+        double q = upwind(v_at(P, X.v, X.vin, i, b - 1), v_at(P, X.v, X.vin, i, b),
+                          v_at(P, X.v, X.vin, i, b + 1), v_at(P, X.v, X.vin, i, b + 2), V);
+        m[2 + s] = V * r;
+        f[2 + s] = m[2 + s] * q;
+    }
+    rb = rv_at(P, X.rc, i, j) - dt / P.h * ((m[1] - m[0]) + (m[3] - m[2]));
+    C = ((f[1] - f[0]) + (f[3] - f[2])) / P.h;
+}
+
+// L_mu u = div[mu (grad u + grad u^T)]: tau_xx / tau_yy at cells, tau_xy at
+// nodes with the four-cell mean viscosity.
+struct Visc {
+    const double *mu, *u, *v, *vin;
+};
+
+__device__ __forceinline__ double mnode(const TankP &P, const Visc &X, int i, int j)
+{
+    return 0.25 * (cell_at(P, X.mu, i - 1, j - 1) + cell_at(P, X.mu, i, j - 1) + cell_at(P, X.mu, i - 1, j) +
+                   cell_at(P, X.mu, i, j));
+}
+
+__device__ __forceinline__ double txx(const TankP &P, const Visc &X, int i, int j)
+{
+    return 2.0 * cell_at(P, X.mu, i, j) * (u_at(P, X.u, i + 1, j) - u_at(P, X.u, i, j)) / P.h;
+}
+
+__device__ __forceinline__ double tyy(const TankP &P, const Visc &X, int i, int j)
+{
+    return 2.0 * cell_at(P, X.mu, i, j) * (v_at(P, X.v, X.vin, i, j + 1) - v_at(P, X.v, X.vin, i, j)) / P.h;
+}
+
+__device__ __forceinline__ double txy(const TankP &P, const Visc &X, int i, int j)
+{
+    return mnode(P, X, i, j) * ((u_at(P, X.u, i, j) - u_at(P, X.u, i, j - 1)) / P.h +
+                                (v_at(P, X.v, X.vin, i, j) - v_at(P, X.v, X.vin, i - 1, j)) / P.h);
+}
+
+__device__ __forceinline__ double visc_x(const TankP &P, const Visc &X, int i, int j)
+{
+    return (txx(P, X, i, j) - txx(P, X, i - 1, j)) / P.h + (txy(P, X, i, j + 1) - txy(P, X, i, j)) / P.h;
+}
+
+__device__ __forceinline__ double visc_y(const TankP &P, const Visc &X, int i, int j)
+{
+    return (tyy(P, X, i, j) - tyy(P, X, i, j - 1)) / P.h + (txy(P, X, i + 1, j) - txy(P, X, i, j)) / P.h;
+}
+
+__device__ __forceinline__ double visc_diag_x(const TankP &P, const Visc &X, int i, int j)
+{
+    return -(2.0 * cell_at(P, X.mu, i, j) + 2.0 * cell_at(P, X.mu, i - 1, j) + mnode(P, X, i, j + 1) +
+             mnode(P, X, i, j)) / (P.h * P.h);
+}
+
+__device__ __forceinline__ double visc_diag_y(const TankP &P, const Visc &X, int i, int j)
+{
+    return -(2.0 * cell_at(P, X.mu, i, j) + 2.0 * cell_at(P, X.mu, i, j - 1) + mnode(P, X, i + 1, j) +
+             mnode(P, X, i, j)) / (P.h * P.h);
+}
+
+// Right-hand side R and diagonal D of the u-momentum system; also the first
+// Jacobi iterate (u^n with the Dirichlet faces at t^{n+1}).
+__global__ void k_mom_u(TankP P, const StepScalars *S, double dt, const double *__restrict__ rho_n,
+                        const double *__restrict__ mu_n, const double *__restrict__ chi_1,
+                        const double *__restrict__ u, const double *__restrict__ v, const double *__restrict__ p,
+                        Bc bc, double *Ru, double *Du, double *rbu, double *ua)
+{
+    int f = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nx = P.nx;
+    if (f >= (nx + 1) * P.ny) return;
+    int i = f % (nx + 1), j = f / (nx + 1);
+    if (i == 0) {
+        ua[f] = bc.uin1[j];
+        return;
+    }
+    if (i == nx) {
+        ua[f] = 0.0;
+        return;
+    }
+    ua[f] = u[f];
+    Fields X{rho_n, u, v, bc.vin0};
+    Visc Vn{mu_n, u, v, bc.vin0};
+    double rb, C;
+    transport_u(P, X, i, j, dt, rb, C);
+    double x = i * P.h, y = (j + 0.5) * P.h;
+    double chi = 0.5 * (cell_at(P, chi_1, i - 1, j) + cell_at(P, chi_1, i, j));
+    rbu[f] = rb;
+    Du[f] = rb / dt + chi / P.kappa_p + damp_alpha(P, x) * rb / dt + vort_damp(P, y, dt);
+    Ru[f] = ru_at(P, rho_n, i, j) * u[f] / dt - C + 0.5 * visc_x(P, Vn, i, j) -
+            (p[j * nx + i] - p[j * nx + i - 1]) / P.h;
+}
+
+__global__ void k_mom_v(TankP P, const StepScalars *S, double dt, const double *__restrict__ rho_n,
+                        const double *__restrict__ mu_n, const double *__restrict__ chi_1,
+                        const double *__restrict__ rf_1, const double *__restrict__ u,
+                        const double *__restrict__ v, const double *__restrict__ p, Bc bc, double *Rv,
+                        double *Dv, double *rbv, double *va)
+{
+    int f = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nx = P.nx, ny = P.ny;
+    if (f >= nx * (ny + 1)) return;
+    int i = f % nx, j = f / nx;
+    if (j == 0) {
+        va[f] = 0.0;
+        return;
+    }
+    va[f] = v[f];
+    Fields X{rho_n, u, v, bc.vin0};
+    Visc Vn{mu_n, u, v, bc.vin0};
+    double rb, C;
+    transport_v(P, X, i, j, dt, rb, C);
+    double x = (i + 0.5) * P.h, y = j * P.h;
+    double chi = 0.5 * (cell_at(P, chi_1, i, j - 1) + cell_at(P, chi_1, i, j));
+    double rf = 0.5 * (cell_at(P, rf_1, i, j - 1) + cell_at(P, rf_1, i, j));
+    rbv[f] = rb;
+    Dv[f] = rb / dt + chi / P.kappa_p + damp_alpha(P, x) * rb / dt + vort_damp(P, y, dt);
+    double gp = j < ny ? (p[j * nx + i] - p[(j - 1) * nx + i]) / P.h : -2.0 * p[(ny - 1) * nx + i] / P.h;
+    Rv[f] = rv_at(P, rho_n, i, j) * v[f] / dt - C + 0.5 * visc_y(P, Vn, i, j) - rf * P.g +
+            chi * S->zdot1 / P.kappa_p - gp;
+}
+
+// One Jacobi sweep of (D - L_mu / 2) u* = R (Crank-Nicolson implicit half),
+// splitting on the interior diagonal of L_mu; Dirichlet faces are copied.
+__global__ void k_jacobi(TankP P, const double *__restrict__ mu_1, const double *__restrict__ vin1,
+                         const double *__restrict__ Ru, const double *__restrict__ Du,
+                         const double *__restrict__ Rv, const double *__restrict__ Dv,
+                         const double *__restrict__ ua, const double *__restrict__ va, double *__restrict__ ub,
+                         double *__restrict__ vb)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nx = P.nx, ny = P.ny;
+    const int nu = (nx + 1) * ny, nv = nx * (ny + 1);
+    Visc Vk{mu_1, ua, va, vin1};
+    if (k < nu) {
+        int i = k % (nx + 1), j = k / (nx + 1);
+        if (i == 0 || i == nx) {
+            ub[k] = ua[k];
+            return;
+        }
+        double ld = visc_diag_x(P, Vk, i, j);
+        ub[k] = (Ru[k] + 0.5 * (visc_x(P, Vk, i, j) - ld * ua[k])) / (Du[k] - 0.5 * ld);
+    } else if (k < nu + nv) {
+        int f = k - nu;
+        int i = f % nx, j = f / nx;
+        if (j == 0) {
+            vb[f] = va[f];
+            return;
+        }
+        double ld = visc_diag_y(P, Vk, i, j);
+        vb[f] = (Rv[f] + 0.5 * (visc_y(P, Vk, i, j) - ld * va[f])) / (Dv[f] - 0.5 * ld);
+    }
+}
+
+// b = -h div u*, face coefficients beta = 1 / D (zero on Neumann walls).
+__global__ void k_proj_rhs(TankP P, const double *__restrict__ us, const double *__restrict__ vs,
+                           const double *__restrict__ Du, const double *__restrict__ Dv, double *rhs,
+                           double *bu, double *bv)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nx = P.nx, ny = P.ny;
+    const int nc = nx * ny, nu = (nx + 1) * ny, nv = nx * (ny + 1);
+    if (k < nc) {
+        int i = k % nx, j = k / nx;
+        rhs[k] = -P.h * (us[j * (nx + 1) + i + 1] - us[j * (nx + 1) + i] + vs[(j + 1) * nx + i] - vs[j * nx + i]);
+    } else if (k < nc + nu) {
+        int f = k - nc, i = f % (nx + 1);
+        bu[f] = (i == 0 || i == nx) ? 0.0 : 1.0 / Du[f];
+    } else if (k < nc + nu + nv) {
+        int f = k - nc - nu, j = f / nx;
+        bv[f] = j == 0 ? 0.0 : 1.0 / Dv[f];
+    }
+}
+
+// u^{n+1} = u* - beta grad phi; p^{n+1/2} = p^{n-1/2} + phi.
+__global__ void k_project(TankP P, const double *__restrict__ us, const double *__restrict__ vs,
+                          const double *__restrict__ bu, const double *__restrict__ bv,
+                          const double *__restrict__ phi, double *u, double *v, double *p)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nx = P.nx, ny = P.ny;
+    const int nc = nx * ny, nu = (nx + 1) * ny, nv = nx * (ny + 1);
+    const double h = P.h;
+    if (k < nu) {
+        int i = k % (nx + 1), j = k / (nx + 1);
+        double uu = us[k];
+        if (i > 0 && i < nx) uu -= bu[k] * (phi[j * nx + i] - phi[j * nx + i - 1]) / h;
+        u[k] = uu;
+    } else if (k < nu + nv) {
+        int f = k - nu, i = f % nx, j = f / nx;
+        double vv = vs[f];
+        if (j > 0 && j < ny) vv -= bv[f] * (phi[j * nx + i] - phi[(j - 1) * nx + i]) / h;
+        if (j == ny) vv += 2.0 * bv[f] * phi[(ny - 1) * nx + i] / h;
+        v[f] = vv;
+    } else if (k < nu + nv + nc) {
+        int c = k - nu - nv;
+        p[c] += phi[c];
+    }
+}
+
+__global__ void k_div_partial(TankP P, const double *__restrict__ u, const double *__restrict__ v,
+                              double *__restrict__ part)
+{
+    __shared__ double sh[TB];
+    const int nx = P.nx;
+    double acc = 0.0;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nx * P.ny; c += gridDim.x * blockDim.x) {
+        int i = c % nx, j = c / nx;
+        acc += sq(P.h * (u[j * (nx + 1) + i + 1] - u[j * (nx + 1) + i] + v[(j + 1) * nx + i] - v[j * nx + i]));
+    }
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+// Close the step: divergence norm, probe elevation, advance time and body state.
+__global__ void k_finalize(TankP P, StepScalars *S, const double *__restrict__ part,
+                           const double *__restrict__ sig, double dt)
+{
+    __shared__ double sh[TB];
+    double s = 0.0;
+    for (int b = threadIdx.x; b < kRedBlocks; b += blockDim.x) s += part[b];
+    double d2 = block_sum(s, sh);
+    if (threadIdx.x != 0) return;
+    int ip = clampi((int)floor(P.probe_x / P.h), 0, P.nx - 1);
+    double eta = nan("");
+    for (int j = 0; j + 1 < P.ny; ++j) {
+        double a = sig[j * P.nx + ip], b = sig[(j + 1) * P.nx + ip];
+        if (a < 0.0 && b >= 0.0) {
+            eta = (j + 0.5) * P.h + P.h * a / (a - b) - P.depth;
+            break;
+        }
+    }
+    S->div2 = d2;
+    S->eta = eta;
+    S->t = S->t + dt;
+    S->yc = S->yc1;
+    S->zdot_prev = S->zdot;
+    S->zdot = S->zdot1;
+}
+
+// Initial state: sigma = y - (d + eta(x, 0)); Airy velocities (u = 0 on the
+// right wall, v = 0 on the bed).
+__global__ void k_init_fields(TankP P, double *sig, double *u, double *v)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nx = P.nx, ny = P.ny;
+    const int nc = nx * ny, nu = (nx + 1) * ny, nv = nx * (ny + 1);
+    const double h = P.h;
+    double uu, vv;
+    if (k < nc) {
+        int i = k % nx, j = k / nx;
+        sig[k] = (j + 0.5) * h - P.depth - eta_at(P, (i + 0.5) * h, 0.0);
+    } else if (k < nc + nu) {
+        int f = k - nc, i = f % (nx + 1), j = f / (nx + 1);
+        airy_uv(P, i * h, (j + 0.5) * h, 0.0, &uu, &vv);
+        u[f] = i == nx ? 0.0 : uu;
+    } else if (k < nc + nu + nv) {
+        int f = k - nc - nu, i = f % nx, j = f / nx;
+        airy_uv(P, (i + 0.5) * h, j * h, 0.0, &uu, &vv);
+        v[f] = j == 0 ? 0.0 : vv;
+    }
+}
+
+// p^{-1/2}: discrete hydrostatic pressure of the flow density (p = 0 at the top
+// face): p_{ny-1} = rho_f g h / 2, p_{j-1} = p_j + (face mean rho_f) g h.
+__global__ void k_init_pressure(TankP P, const double *__restrict__ rf, double *p)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nx = P.nx, ny = P.ny;
+    if (i >= nx) return;
+    double pj = 0.5 * rf[(ny - 1) * nx + i] * P.g * P.h;
+    p[(ny - 1) * nx + i] = pj;
+    for (int j = ny - 1; j >= 1; --j) {
+        pj += 0.5 * (rf[(j - 1) * nx + i] + rf[j * nx + i]) * P.g * P.h;
+        p[(j - 1) * nx + i] = pj;
+    }
+}
+
+}  // namespace
+
+int tank_alloc_and_init(wec_tank *T)
+{
+    const TankP &P = T->P;
+    T->nc = (size_t)P.nx * P.ny;
+    T->nu = (size_t)(P.nx + 1) * P.ny;
+    T->nv = (size_t)P.nx * (P.ny + 1);
+    size_t nc = T->nc, nu = T->nu, nv = T->nv;
+    double **cells[] = {&T->sig, &T->sa, &T->r0, &T->r1, &T->rt, &T->p, &T->phi, &T->rhs,
+                        &T->rho_n, &T->mu_n, &T->mu_1, &T->rf_1, &T->chi_1};
+    for (double **q : cells) WEC_CK(cudaMalloc(q, nc * 8));
+    double **ufaces[] = {&T->u, &T->us, &T->ua, &T->ub, &T->uc, &T->Ru, &T->Du, &T->rbu};
+    for (double **q : ufaces) {
+        WEC_CK(cudaMalloc(q, nu * 8));
+        WEC_CK(cudaMemset(*q, 0, nu * 8));
+    }
+    double **vfaces[] = {&T->v, &T->vs, &T->va, &T->vb, &T->vc, &T->Rv, &T->Dv, &T->rbv};
+    for (double **q : vfaces) {
+        WEC_CK(cudaMalloc(q, nv * 8));
+        WEC_CK(cudaMemset(*q, 0, nv * 8));
+    }
+    for (double **q : cells) WEC_CK(cudaMemset(*q, 0, nc * 8));
+    size_t nbc = (size_t)P.ny + 2 * (P.ny + 1) + 6;
+    WEC_CK(cudaMalloc(&T->bcbuf, nbc * 8));
+    T->bc.uin1 = T->bcbuf;
+    T->bc.vin0 = T->bc.uin1 + P.ny;
+    T->bc.vin1 = T->bc.vin0 + P.ny + 1;
+    T->bc.eta0 = T->bc.vin1 + P.ny + 1;
+    T->bc.eta1 = T->bc.eta0 + 3;
+    WEC_CK(cudaMalloc(&T->part, kRedBlocks * 8));
+    WEC_CK(cudaMalloc(&T->S, sizeof(StepScalars)));
+    WEC_CK(cudaMallocHost(&T->Sh, sizeof(StepScalars)));
+    *T->Sh = StepScalars{};
+    if (int e = poisson_init(&T->solver, P.nx, P.ny, T->opts.precision, T->opts.restart, T->opts.mg_pre,
+                             T->opts.mg_post, T->st))
+        return e;
+    long long ninit = (long long)nc + nu + nv;
+    WEC_PROF("init", -1, 8.0 * ninit, T->st);
+    k_init_fields<<<nblk(ninit, TB), TB, 0, T->st>>>(P, T->sig, T->u, T->v);
+    WEC_CK(cudaGetLastError());
+    return WEC_OK;
+}
+
+// Called after the host sets Sh (initial yc): hydrostatic p from the initial sigma.
+int tank_init_pressure(wec_tank *T)
+{
+    WEC_CK(cudaMemcpyAsync(T->S, T->Sh, sizeof(StepScalars), cudaMemcpyHostToDevice, T->st));
+    const TankP &P = T->P;
+    {
+        WEC_PROF("materials", -1, 16.0 * T->nc, T->st);
+        k_materials<<<nblk(T->nc, TB), TB, 0, T->st>>>(P, T->S, 0, T->sig, nullptr, nullptr, T->rf_1, nullptr);
+    }
+    {
+        WEC_PROF("init", -1, 16.0 * T->nc, T->st);
+        k_init_pressure<<<nblk(P.nx, 128), 128, 0, T->st>>>(P, T->rf_1, T->p);
+    }
+    WEC_CK(cudaGetLastError());
+    WEC_CK(cudaStreamSynchronize(T->st));
+    return WEC_OK;
+}
+
+int tank_step(wec_tank *T, double dt, double fpto, wec_step_result *out)
+{
+    const TankP &P = T->P;
+    cudaStream_t st = T->st;
+    const long long nc = T->nc, nu = T->nu, nv = T->nv;
+    const double fb = 8.0;  // FP64 bytes
+    // (1) inflow / ghost data at t^n and t^{n+1}
+    {
+        WEC_PROF("bc", -1, fb * (3.0 * P.ny + 6), st);
+        k_bc<<<nblk(P.ny + 1, 128), 128, 0, st>>>(P, T->S, dt, T->bc);
+    }
+    // (2) materials at n, force from p^{n-1/2}, u^n (Eq. int_fh), heave (Eq. newton_u)
+    {
+        WEC_PROF("materials", -1, fb * 3.0 * nc, st);
+        k_materials<<<nblk(nc, TB), TB, 0, st>>>(P, T->S, 0, T->sig, T->rho_n, T->mu_n, nullptr, nullptr);
+    }
+    {
+        WEC_PROF("force", -1, fb * kRedBlocks, st);
+        k_force_partial<<<kRedBlocks, TB, 0, st>>>(P, T->S, T->p, T->u, T->v, T->mu_n, T->bc.vin0, T->part);
+    }
+    {
+        WEC_PROF("scalar", -1, fb * kRedBlocks, st);
+        k_heave<<<1, TB, 0, st>>>(P, T->S, T->part, dt, fpto);
+    }
+    // (3) sigma advection + damping-zone relaxation, then reinitialisation
+    {
+        WEC_PROF("advect", -1, fb * (2.0 * nc + nu + nv), st);
+        k_advect<<<nblk(nc, TB), TB, 0, st>>>(P, T->sig, T->u, T->v, T->bc.eta0, dt, T->sa);
+    }
+    const double dtau = 0.3 * P.h;
+    const double *f = T->sa;
+    double *bufs[2] = {T->r0, T->r1};
+    for (int it = 0; it < T->opts.n_reinit; ++it) {
+        double *dst = bufs[it & 1];
+        {
+            WEC_PROF("reinit", -1, fb * 3.0 * nc, st);
+            k_reinit<<<nblk(nc, TB), TB, 0, st>>>(P, f, T->sa, nullptr, T->bc.eta1, dtau, T->rt);
+        }
+        {
+            WEC_PROF("reinit", -1, fb * 4.0 * nc, st);
+            k_reinit<<<nblk(nc, TB), TB, 0, st>>>(P, T->rt, T->sa, f, T->bc.eta1, dtau, dst);
+        }
+        f = dst;
+    }
+    if (T->opts.n_reinit == 0) WEC_CK(cudaMemcpyAsync(T->r0, T->sa, nc * 8, cudaMemcpyDeviceToDevice, st));
+    double *sig1 = T->opts.n_reinit == 0 ? T->r0 : (double *)f;
+    // (4) materials at n+1 (psi at the new body position)
+    {
+        WEC_PROF("materials", -1, fb * 4.0 * nc, st);
+        k_materials<<<nblk(nc, TB), TB, 0, st>>>(P, T->S, 1, sig1, nullptr, T->mu_1, T->rf_1, T->chi_1);
+    }
+    // (5) momentum right-hand side and diagonal, (6) Crank-Nicolson Jacobi sweeps
+    {
+        WEC_PROF("mom_u", -1, fb * (4.0 * nc + nu + nv + 4.0 * nu), st);
+        k_mom_u<<<nblk(nu, TB), TB, 0, st>>>(P, T->S, dt, T->rho_n, T->mu_n, T->chi_1, T->u, T->v, T->p, T->bc,
+                                             T->Ru, T->Du, T->rbu, T->ua);
+    }
+    {
+        WEC_PROF("mom_v", -1, fb * (5.0 * nc + nu + nv + 4.0 * nv), st);
+        k_mom_v<<<nblk(nv, TB), TB, 0, st>>>(P, T->S, dt, T->rho_n, T->mu_n, T->chi_1, T->rf_1, T->u, T->v,
+                                             T->p, T->bc, T->Rv, T->Dv, T->rbv, T->va);
+    }
+    const double *ju = T->ua, *jv = T->va;
+    double *tu[2] = {T->ub, T->uc}, *tv[2] = {T->vb, T->vc};
+    for (int it = 0; it < T->opts.n_jacobi; ++it) {
+        double *du = it == T->opts.n_jacobi - 1 ? T->us : tu[it & 1];
+        double *dv = it == T->opts.n_jacobi - 1 ? T->vs : tv[it & 1];
+        {
+            WEC_PROF("jacobi", -1, fb * (nc + 4.0 * (nu + nv)), st);
+            k_jacobi<<<nblk(nu + nv, TB), TB, 0, st>>>(P, T->mu_1, T->bc.vin1, T->Ru, T->Du, T->Rv, T->Dv, ju,
+                                                       jv, du, dv);
+        }
+        ju = du;
+        jv = dv;
+    }
+    // (7) pressure increment: A phi = -h div u*, beta = 1/D
+    wec_poisson *S = &T->solver;
+    {
+        WEC_PROF("proj_rhs", -1, fb * (nc + 3.0 * (nu + nv)), st);
+        k_proj_rhs<<<nblk(nc + nu + nv, TB), TB, 0, st>>>(P, T->us, T->vs, T->Du, T->Dv, T->rhs, S->L64[0].bu,
+                                                          S->L64[0].bv);
+    }
+    WEC_CK(cudaGetLastError());
+    if (int e = poisson_build(S)) return e;
+    WEC_CK(cudaMemsetAsync(T->phi, 0, nc * 8, st));
+    int iters = 0;
+    double relres = 0.0;
+    int status = poisson_solve(S, T->rhs, T->phi, T->opts.rtol, T->opts.max_iters, &iters, &relres);
+    if (status != WEC_OK && status != WEC_ERR_NOT_CONVERGED) return status;
+    // (8) projection (Eq. c_discrete_continuity)
+    {
+        WEC_PROF("project", -1, fb * (3.0 * nc + 3.0 * (nu + nv)), st);
+        k_project<<<nblk(nu + nv + nc, TB), TB, 0, st>>>(P, T->us, T->vs, S->L64[0].bu, S->L64[0].bv, T->phi,
+                                                         T->u, T->v, T->p);
+    }
+    {
+        WEC_PROF("divergence", -1, fb * (nu + nv), st);
+        k_div_partial<<<kRedBlocks, TB, 0, st>>>(P, T->u, T->v, T->part);
+    }
+    {
+        WEC_PROF("scalar", -1, fb * (kRedBlocks + P.ny), st);
+        k_finalize<<<1, TB, 0, st>>>(P, T->S, T->part, sig1, dt);
+    }
+    WEC_CK(cudaGetLastError());
+    // sigma^{n+1} becomes the state; the old buffer joins the scratch set
+    if (sig1 == T->r0) std::swap(T->sig, T->r0);
+    else std::swap(T->sig, T->r1);
+    T->stepped = true;
+    T->last_iters = iters;
+    T->last_relres = relres;
+    if (out) {
+        WEC_CK(cudaMemcpyAsync(T->Sh, T->S, sizeof(StepScalars), cudaMemcpyDeviceToHost, st));
+        WEC_CK(cudaStreamSynchronize(st));
+        const StepScalars &s = *T->Sh;
+        out->t = s.t;
+        out->z = s.yc - s.yc0;
+        out->zdot = s.zdot;
+        out->f_hydro = s.F;
+        out->f_pto = s.fpto;
+        out->eta_probe = s.eta;
+        out->residual = relres;
+        out->div_norm = sqrt(s.div2);
+        out->iters = iters;
+        if (status == WEC_OK && !(std::isfinite(s.zdot) && std::isfinite(s.F) && std::isfinite(relres)))
+            status = fail(WEC_ERR_NONFINITE, "step: non-finite body state or residual");
+        out->status = status;
+    }
+    return status;
+}
+
+void tank_free(wec_tank *T)
+{
+    double *all[] = {T->sig, T->sa, T->r0, T->r1, T->rt, T->p, T->phi, T->rhs, T->rho_n, T->mu_n, T->mu_1,
+                     T->rf_1, T->chi_1, T->u, T->us, T->ua, T->ub, T->uc, T->Ru, T->Du, T->rbu, T->v, T->vs,
+                     T->va, T->vb, T->vc, T->Rv, T->Dv, T->rbv, T->bcbuf, T->part, T->waves};
+    for (double *q : all) cudaFree(q);
+    cudaFree(T->S);
+    if (T->Sh) cudaFreeHost(T->Sh);
+    poisson_free(&T->solver);
+}
+
+}  // namespace wec

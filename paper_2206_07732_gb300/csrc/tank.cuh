@@ -1,0 +1,65 @@
+// Tank state and device helpers shared by the step kernels and the C ABI.
+#pragma once
+
+#include "internal.cuh"
+
+namespace wec {
+
+// Per-tank constants, passed to kernels by value.
+struct TankP {
+    int nx, ny;
+    double h, lx, ly, depth;
+    double rho_w, rho_a, rho_s, mu_w, mu_a, mu_s, g;
+    double damp_x0, damp_len, probe_x;
+    int has_body;
+    double bxc, bw, bh, mass, added_mass, kappa_p, pto_c;
+    int ncomp;
+    const double *amp, *omega, *kw, *phase;  // device
+};
+
+// Device-resident scalars of the step (keeps the step free of host round trips).
+struct StepScalars {
+    double t, yc, zdot, zdot_prev, yc0;  // state at step n
+    double yc1, zdot1;                   // body after the heave update
+    double F, fpto;                      // force and PTO force of this step
+    double div2, eta;                    // diagnostics of the finished step
+};
+
+// Boundary data of one step: inflow at x = 0 and eta at the three ghost columns.
+struct Bc {
+    double *uin1;  // [ny]   u_in(y_j+1/2, t^{n+1})
+    double *vin0;  // [ny+1] v_in(y_j, t^n)
+    double *vin1;  // [ny+1] v_in(y_j, t^{n+1})
+    double *eta0;  // [3]    eta(-(g+1/2) h, t^n)
+    double *eta1;  // [3]    eta(-(g+1/2) h, t^{n+1})
+};
+
+}  // namespace wec
+
+struct wec_tank {
+    wec::TankP P{};
+    wec_solver_opts opts{};
+    cudaStream_t st = nullptr;
+    size_t nc = 0, nu = 0, nv = 0;
+    double *sig = nullptr, *sa = nullptr, *r0 = nullptr, *r1 = nullptr, *rt = nullptr;
+    double *u = nullptr, *v = nullptr, *us = nullptr, *vs = nullptr;
+    double *ua = nullptr, *va = nullptr, *ub = nullptr, *vb = nullptr, *uc = nullptr, *vc = nullptr;
+    double *Ru = nullptr, *Rv = nullptr, *Du = nullptr, *Dv = nullptr, *rbu = nullptr, *rbv = nullptr;
+    double *p = nullptr, *phi = nullptr, *rhs = nullptr;
+    double *rho_n = nullptr, *mu_n = nullptr, *mu_1 = nullptr, *rf_1 = nullptr, *chi_1 = nullptr;
+    double *bcbuf = nullptr, *part = nullptr, *waves = nullptr;
+    wec::Bc bc{};
+    wec::StepScalars *S = nullptr;   // device
+    wec::StepScalars *Sh = nullptr;  // pinned host mirror
+    wec_poisson solver;
+    bool stepped = false;
+    int last_iters = 0;
+    double last_relres = 0.0;
+};
+
+namespace wec {
+int tank_alloc_and_init(wec_tank *T);
+int tank_init_pressure(wec_tank *T);  // after the host filled T->Sh (initial body state)
+int tank_step(wec_tank *T, double dt, double fpto, wec_step_result *out);
+void tank_free(wec_tank *T);
+}  // namespace wec

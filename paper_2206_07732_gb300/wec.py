@@ -1,0 +1,291 @@
+"""ctypes binding of libwec (include/wec.h): argument marshalling only.
+
+Every step of the wave-tank path runs in the CUDA library; there is no CPU
+fallback.  Loading fails loudly if libwec.so has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libwec.so")
+
+WEC_OK, WEC_ERR_INVALID, WEC_ERR_CUDA, WEC_ERR_NOT_CONVERGED, WEC_ERR_NONFINITE, WEC_ERR_NOMEM = range(6)
+PREC_FP64, PREC_MIXED = 0, 1
+(F_SIGMA, F_U, F_V, F_P, F_USTAR, F_VSTAR, F_BETA_U, F_BETA_V, F_RHS, F_SIGMA_ADV) = range(10)
+FIELD_NAMES = {"sigma": F_SIGMA, "u": F_U, "v": F_V, "p": F_P, "ustar": F_USTAR, "vstar": F_VSTAR,
+               "beta_u": F_BETA_U, "beta_v": F_BETA_V, "rhs": F_RHS, "sigma_adv": F_SIGMA_ADV}
+
+_dp = C.POINTER(C.c_double)
+
+
+class Grid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("lx", C.c_double), ("ly", C.c_double), ("depth", C.c_double)]
+
+
+class Fluids(C.Structure):
+    _fields_ = [(k, C.c_double) for k in ("rho_w", "rho_a", "mu_w", "mu_a", "g")]
+
+
+class Waves(C.Structure):
+    _fields_ = [("ncomp", C.c_int), ("amp", _dp), ("omega", _dp), ("phase", _dp),
+                ("damp_x0", C.c_double), ("damp_len", C.c_double), ("probe_x", C.c_double)]
+
+
+class Body(C.Structure):
+    _fields_ = [("present", C.c_int)] + [(k, C.c_double) for k in
+                                         ("xc", "yc", "width", "height", "mass", "added_mass", "kappa_p",
+                                          "pto_damping")]
+
+
+class SolverOpts(C.Structure):
+    _fields_ = [("precision", C.c_int), ("rtol", C.c_double), ("max_iters", C.c_int), ("restart", C.c_int),
+                ("n_reinit", C.c_int), ("n_jacobi", C.c_int), ("mg_pre", C.c_int), ("mg_post", C.c_int)]
+
+
+class StepResult(C.Structure):
+    _fields_ = [(k, C.c_double) for k in
+                ("t", "z", "zdot", "f_hydro", "f_pto", "eta_probe", "residual", "div_norm")] + \
+               [("iters", C.c_int), ("status", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class WecError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libwec error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load():
+    """Load libwec.so (built by paper_2206_07732_gb300.build).  Raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2206_07732_gb300.build.build() "
+                           "(there is no CPU fallback)")
+    L = C.CDLL(LIB_PATH)
+    vp = C.c_void_p
+    L.wec_last_error.restype = C.c_char_p
+    L.wec_tank_create.argtypes = [C.POINTER(Grid), C.POINTER(Fluids), C.POINTER(Waves), C.POINTER(Body),
+                                  C.POINTER(SolverOpts), vp, C.POINTER(vp)]
+    L.wec_tank_destroy.argtypes = [vp]
+    L.wec_tank_destroy.restype = None
+    L.wec_step.argtypes = [vp, C.c_double, C.c_double, C.POINTER(StepResult)]
+    L.wec_step_n.argtypes = [vp, C.c_int, C.c_double, _dp, C.POINTER(StepResult)]
+    L.wec_pressure_solve.argtypes = [vp, vp, vp, C.c_double, C.POINTER(C.c_int), _dp]
+    L.wec_get_field.argtypes = [vp, C.c_int, _dp, C.c_size_t]
+    L.wec_set_field.argtypes = [vp, C.c_int, _dp, C.c_size_t]
+    L.wec_get_state.argtypes = [vp, _dp]
+    L.wec_set_state.argtypes = [vp, C.c_double, C.c_double, C.c_double, C.c_double]
+    L.wec_save.argtypes = [vp, vp, C.POINTER(C.c_size_t)]
+    L.wec_load.argtypes = [vp, vp, C.c_size_t]
+    L.wec_poisson_create.argtypes = [C.c_int, C.c_int, C.POINTER(SolverOpts), vp, C.POINTER(vp)]
+    L.wec_poisson_destroy.argtypes = [vp]
+    L.wec_poisson_destroy.restype = None
+    L.wec_poisson_set_coefficients.argtypes = [vp, vp, vp]
+    L.wec_poisson_apply.argtypes = [vp, vp, vp]
+    L.wec_poisson_vcycle.argtypes = [vp, vp, vp]
+    L.wec_poisson_solve.argtypes = [vp, vp, vp, C.c_double, C.c_int, C.POINTER(C.c_int), _dp]
+    L.wec_wave_number.restype = C.c_double
+    L.wec_wave_number.argtypes = [C.c_double, C.c_double, C.c_double]
+    L.wec_wave_number_fenton_kd.restype = C.c_double
+    L.wec_wave_number_fenton_kd.argtypes = [C.c_double, C.c_double, C.c_double]
+    L.wec_jonswap.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int, _dp, _dp]
+    _lib = L
+    return L
+
+
+def _check(code, ok=(WEC_OK,)):
+    if code not in ok:
+        raise WecError(code, load().wec_last_error().decode())
+    return code
+
+
+def _ptr(a):
+    return a.ctypes.data_as(_dp)
+
+
+def _dev(t):
+    """Device pointer of a contiguous float64 CUDA tensor."""
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is not None:
+        return C.c_void_p(int(stream))
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return C.c_void_p(0)
+
+
+def wave_number(omega, depth, g):
+    return load().wec_wave_number(omega, depth, g)
+
+
+def wave_number_fenton_kd(omega, depth, g):
+    return load().wec_wave_number_fenton_kd(omega, depth, g)
+
+
+def jonswap(Hs, Tp, gamma, ncomp):
+    amp = np.zeros(ncomp)
+    om = np.zeros(ncomp)
+    _check(load().wec_jonswap(Hs, Tp, gamma, ncomp, _ptr(amp), _ptr(om)))
+    return amp, om
+
+
+def wave_components(wave):
+    """(amp, omega, phase) of a workload's wave dict (JONSWAP built by the library)."""
+    if wave["kind"] == "regular":
+        return (np.array([0.5 * wave["H"]]), np.array([2.0 * math.pi / wave["T"]]),
+                np.array([wave["phase"]], dtype=np.float64))
+    if wave["kind"] == "jonswap":
+        amp, om = jonswap(wave["Hs"], wave["Tp"], wave["gamma"], wave["ncomp"])
+        return amp, om, np.asarray(wave["phases"], dtype=np.float64)
+    raise ValueError(wave["kind"])
+
+
+def solver_opts(s, precision=None):
+    o = SolverOpts()
+    o.precision = s.get("precision", 0) if precision is None else precision
+    o.rtol = s["rtol"]
+    o.max_iters, o.restart = s["max_iters"], s["restart"]
+    o.n_reinit, o.n_jacobi, o.mg_pre, o.mg_post = s["n_reinit"], s["n_jacobi"], s["mg_pre"], s["mg_post"]
+    return o
+
+
+class Tank:
+    """A 2D wave tank on the GPU (wec_tank_create ... wec_tank_destroy)."""
+
+    def __init__(self, cfg, precision=None, stream=None):
+        L = load()
+        self.cfg = cfg
+        self.nx, self.ny = cfg["nx"], cfg["ny"]
+        g = Grid(cfg["nx"], cfg["ny"], cfg["lx"], cfg["ly"], cfg["depth"])
+        f = Fluids(cfg["rho_w"], cfg["rho_a"], cfg["mu_w"], cfg["mu_a"], cfg["g"])
+        amp, om, ph = wave_components(cfg["wave"])
+        self._w = [np.ascontiguousarray(a, dtype=np.float64) for a in (amp, om, ph)]
+        w = Waves(len(amp), _ptr(self._w[0]), _ptr(self._w[1]), _ptr(self._w[2]),
+                  cfg["damp_x0"], cfg["damp_len"], cfg["probe_x"])
+        b = cfg.get("body")
+        body = Body(1, b["xc"], b["yc"], b["width"], b["height"], b["mass"], b["added_mass"], b["kappa_p"],
+                    b["pto_damping"]) if b else Body(0)
+        o = solver_opts(cfg["solver"], precision)
+        h = C.c_void_p()
+        _check(L.wec_tank_create(C.byref(g), C.byref(f), C.byref(w), C.byref(body), C.byref(o),
+                                 _stream(stream), C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().wec_tank_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def shape(self, f):
+        f = FIELD_NAMES.get(f, f)
+        if f in (F_U, F_USTAR, F_BETA_U):
+            return (self.ny, self.nx + 1)
+        if f in (F_V, F_VSTAR, F_BETA_V):
+            return (self.ny + 1, self.nx)
+        return (self.ny, self.nx)
+
+    def get(self, f):
+        f = FIELD_NAMES.get(f, f)
+        a = np.zeros(self.shape(f))
+        _check(load().wec_get_field(self.h, f, _ptr(a), a.size))
+        return a
+
+    def set(self, f, a):
+        f = FIELD_NAMES.get(f, f)
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        if a.shape != self.shape(f):
+            raise ValueError(f"shape {a.shape} != {self.shape(f)}")
+        _check(load().wec_set_field(self.h, f, _ptr(a), a.size))
+
+    def state(self):
+        a = np.zeros(5)
+        _check(load().wec_get_state(self.h, _ptr(a)))
+        return dict(t=a[0], yc=a[1], zdot=a[2], zdot_prev=a[3], yc0=a[4])
+
+    def set_state(self, t, yc, zdot, zdot_prev=None):
+        _check(load().wec_set_state(self.h, t, yc, zdot, zdot if zdot_prev is None else zdot_prev))
+
+    def step(self, dt, f_pto=0.0, allow=(WEC_OK, WEC_ERR_NOT_CONVERGED)):
+        r = StepResult()
+        _check(load().wec_step(self.h, dt, f_pto, C.byref(r)), ok=allow)
+        return r.as_dict()
+
+    def step_n(self, n, dt, pto=None, records=True):
+        out = (StepResult * n)() if records else None
+        p = None if pto is None else _ptr(np.ascontiguousarray(pto, dtype=np.float64))
+        _check(load().wec_step_n(self.h, n, dt, p, out))
+        return [r.as_dict() for r in out] if records else None
+
+    def pressure_solve(self, rhs, p, rtol):
+        it = C.c_int(0)
+        rr = C.c_double(0)
+        code = _check(load().wec_pressure_solve(self.h, _dev(rhs), _dev(p), rtol, C.byref(it), C.byref(rr)),
+                      ok=(WEC_OK, WEC_ERR_NOT_CONVERGED))
+        return dict(iters=it.value, relres=rr.value, status=code)
+
+    def save(self):
+        n = C.c_size_t(0)
+        _check(load().wec_save(self.h, None, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        _check(load().wec_save(self.h, buf, C.byref(n)))
+        return buf.raw
+
+    def load_state(self, data):
+        buf = C.create_string_buffer(data, len(data))
+        _check(load().wec_load(self.h, buf, len(data)))
+
+
+class Poisson:
+    """Standalone pressure operator and solver on caller coefficients (torch CUDA tensors)."""
+
+    def __init__(self, nx, ny, precision=PREC_FP64, restart=20, mg_pre=2, mg_post=2, stream=None):
+        o = SolverOpts(precision, 1e-8, 1000, restart, 0, 1, mg_pre, mg_post)
+        h = C.c_void_p()
+        _check(load().wec_poisson_create(nx, ny, C.byref(o), _stream(stream), C.byref(h)))
+        self.h, self.nx, self.ny = h, nx, ny
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().wec_poisson_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def set_coefficients(self, bu, bv):
+        _check(load().wec_poisson_set_coefficients(self.h, _dev(bu), _dev(bv)))
+
+    def apply(self, x, y):
+        _check(load().wec_poisson_apply(self.h, _dev(x), _dev(y)))
+
+    def vcycle(self, b, x):
+        _check(load().wec_poisson_vcycle(self.h, _dev(b), _dev(x)))
+
+    def solve(self, b, x, rtol=1e-10, max_iters=500):
+        it = C.c_int(0)
+        rr = C.c_double(0)
+        code = _check(load().wec_poisson_solve(self.h, _dev(b), _dev(x), rtol, max_iters, C.byref(it),
+                                               C.byref(rr)), ok=(WEC_OK, WEC_ERR_NOT_CONVERGED))
+        return dict(iters=it.value, relres=rr.value, status=code)
