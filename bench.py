@@ -37,12 +37,14 @@ UNIT = "cell-steps/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU-baseline sample budget")
+    ap.add_argument("--ncu-steps", type=int, default=0,
+                    help="profiling helper: run warm-up + this many mixed-path steps only, print nothing")
     return ap.parse_args()
 
 
@@ -89,7 +91,7 @@ class Clocks:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except (FileNotFoundError, OSError):
             self.proc = None
@@ -156,50 +158,30 @@ def ncu_traffic(kernel_key):
     return None
 
 
-def read_profile(L):
-    import ctypes as C
-    mx, stride = 256, 64
-    names = C.create_string_buffer(mx * stride)
-    lv = (C.c_int * mx)()
-    la = (C.c_longlong * mx)()
-    ms = (C.c_double * mx)()
-    by = (C.c_double * mx)()
-    cnt = C.c_int(0)
-    L.wec_profile_read(mx, names, stride, lv, la, ms, by, C.byref(cnt))
-    out = []
-    for k in range(min(cnt.value, mx)):
-        nm = names.raw[k * stride:(k + 1) * stride].split(b"\0")[0].decode()
-        out.append(dict(name=nm, level=lv[k], launches=la[k], ms=ms[k], bytes=by[k]))
-    return out
-
-
 def setup_lib():
-    import ctypes as C
     from paper_2206_07732_gb300 import build as B
     from paper_2206_07732_gb300 import wec
     B.build()
-    L = wec.load()
-    L.wec_launch_count.restype = C.c_longlong
-    L.wec_profile_enable.argtypes = [C.c_int, C.c_char_p]
-    L.wec_profile_read.argtypes = [C.c_int, C.c_char_p, C.c_size_t, C.POINTER(C.c_int), C.POINTER(C.c_longlong),
-                                   C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int)]
-    return L, wec
+    return wec.load(), wec
 
 
 # ---------------------------------------------------------------- our arm --
-def time_path(L, wec, torch, cfg, precision, steps, warmup, flush, profile_kernel=None):
-    """Time K steps (CUDA events per step on the tank's stream, L2 flushed in between)."""
+def time_path(L, wec, torch, cfg, precision, steps, warmup, flush, graph=True, profile_kernel=None):
+    """Time K steps (CUDA events per step on the caller's stream, L2 flushed in
+    between).  graph=False with profile_kernel: the eager pass that times one
+    kernel's launches with event pairs (graph bodies cannot hold events)."""
     tank = wec.Tank(cfg, precision=precision)
+    tank.use_graph(graph)
     stream = torch.cuda.current_stream()
     for _ in range(warmup):
         tank.step(cfg["dt"])
     torch.cuda.synchronize()
     if profile_kernel:
-        L.wec_profile_read(0, None, 0, None, None, None, None, (__import__("ctypes").c_int * 1)())
-        L.wec_profile_enable(2, profile_kernel.encode())
+        wec.profile_read()
+        wec.profile_enable(2, profile_kernel)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     its, res = [], []
-    n0 = L.wec_launch_count()
+    n0 = wec.launch_count()
     if torch.distributed.is_initialized():
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -215,27 +197,29 @@ def time_path(L, wec, torch, cfg, precision, steps, warmup, flush, profile_kerne
     wall = time.perf_counter() - wall0
     if torch.distributed.is_initialized():
         torch.distributed.barrier()
-    launches = L.wec_launch_count() - n0
+    launches = wec.launch_count() - n0
     prof = None
     if profile_kernel:
-        L.wec_profile_enable(0, None)
-        prof = read_profile(L)
+        wec.profile_enable(0)
+        prof = wec.profile_read()
     ms = [a.elapsed_time(b) for a, b in ev]
     tank.close()
     return dict(ms=ms, iters=its, residual=max(res), launches=launches, wall=wall, prof=prof)
 
 
-def profile_all(L, wec, torch, cfg, precision, steps=2):
+def profile_all(wec, torch, cfg, precision, steps=2):
+    """Untimed eager pass with every launch timed: which kernel dominates."""
     tank = wec.Tank(cfg, precision=precision)
+    tank.use_graph(False)
     for _ in range(3):
         tank.step(cfg["dt"])
     torch.cuda.synchronize()
-    read_profile(L)
-    L.wec_profile_enable(1, None)
+    wec.profile_read()
+    wec.profile_enable(1)
     for _ in range(steps):
         tank.step(cfg["dt"])
-    L.wec_profile_enable(0, None)
-    p = read_profile(L)
+    wec.profile_enable(0)
+    p = wec.profile_read()
     tank.close()
     return p
 
@@ -269,11 +253,17 @@ def main_ours(args):
     L, wec = setup_lib()
     cfg = workload(args.seed)
     n = cfg["nx"] * cfg["ny"]
+    if args.ncu_steps:
+        tank = wec.Tank(cfg, precision=wec.PREC_MIXED)
+        for _ in range(max(args.warmup, 1) + args.ncu_steps):
+            tank.step(cfg["dt"])
+        torch.cuda.synchronize()
+        return
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 256 MiB > L2
     steps, warmup = args.steps, max(args.warmup, 3)
 
-    # which kernel dominates the mixed path (untimed profiling pass)
-    prof_all = profile_all(L, wec, torch, cfg, wec.PREC_MIXED)
+    # which kernel dominates the mixed path (untimed, eager, every launch timed)
+    prof_all = profile_all(wec, torch, cfg, wec.PREC_MIXED)
     by_name = {}
     for p in prof_all:
         d = by_name.setdefault(p["name"], dict(ms=0.0, bytes=0.0, launches=0))
@@ -282,9 +272,11 @@ def main_ours(args):
 
     clocks = Clocks(local)
     clocks.start()
-    mixed = time_path(L, wec, torch, cfg, wec.PREC_MIXED, steps, warmup, flush, profile_kernel=top)
+    mixed = time_path(L, wec, torch, cfg, wec.PREC_MIXED, steps, warmup, flush)
     ck = clocks.stop()
     fp64 = time_path(L, wec, torch, cfg, wec.PREC_FP64, steps, warmup, flush)
+    kpass = time_path(L, wec, torch, cfg, wec.PREC_MIXED, max(steps // 4, 5), warmup, flush, graph=False,
+                      profile_kernel=top)
     e2e = e2e_path(wec, torch, cfg, wec.PREC_MIXED, max(steps // 2, 5), warmup, flush)
 
     def reduce_max(x):
@@ -301,20 +293,25 @@ def main_ours(args):
     fp64_value = world * n * steps / t_fp64
     e2e_value = world * n * len(e2e) / t_e2e
 
-    # roofline of the dominant kernel, live over the timed region
+    # roofline of the dominant kernel: event pairs around each of its launches
     peak, peak_kind = peaks()
-    pk = [p for p in (mixed["prof"] or []) if p["name"] == top]
+    pk = [p for p in (kpass["prof"] or []) if p["name"] == top]
     tot_ms = sum(p["ms"] for p in pk)
     tot_b = sum(p["bytes"] for p in pk)
     nl = sum(p["launches"] for p in pk)
     achieved = (tot_b / nl) / (tot_ms / nl / 1e3) / 1e9 if nl and tot_ms > 0 else None
     share = by_name[top]["ms"] / sum(d["ms"] for d in by_name.values())
+    lvl = {}
+    for p in pk:
+        lvl[str(p["level"])] = {"launches": p["launches"], "avg_us": p["ms"] / p["launches"] * 1e3,
+                                "GBps": p["bytes"] / (p["ms"] / 1e3) / 1e9 if p["ms"] > 0 else None}
     roofline = {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None,
                 "traffic": ncu_traffic(top), "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
                 "algorithmic_bytes_per_launch": (tot_b / nl) if nl else None,
                 "launches_timed": nl, "avg_launch_us": (tot_ms / nl * 1e3) if nl else None,
-                "share_of_step_gpu_time": share}
+                "share_of_step_gpu_time": share, "per_level": lvl,
+                "timing": "event pair per launch of this kernel over an eager pass of the same steps"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -330,10 +327,11 @@ def main_ours(args):
         "fp64_value": fp64_value, "fp64_ms_per_step": t_fp64 / steps * 1e3,
         "speedup_mixed_vs_fp64": value / fp64_value,
         "learned_warm_start": "not built",
+        "execution": "one CUDA graph per step (conditional WHILE/IF nodes steer FGMRES on the GPU)",
         "fgmres_iters_per_step": {"mixed": statistics.mean(mixed["iters"]), "fp64": statistics.mean(fp64["iters"])},
         "max_relative_residual": {"mixed": mixed["residual"], "fp64": fp64["residual"]},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8, "d2h_bytes_per_step": 72,
-                "note": "wec_step wall clock: host PTO force in, host step record out, per step"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 16, "d2h_bytes_per_step": 72,
+                "note": "wec_step wall clock: host dt and PTO force in, host step record out, per step"},
         "gpu_launches": mixed["launches"],
         "clocks": ck,
         "roofline": roofline,

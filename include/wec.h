@@ -153,6 +153,14 @@ int wec_step(wec_tank *tank, double dt, double pto_force, wec_step_result *out);
 int wec_step_n(wec_tank *tank, int nsteps, double dt, const double *pto_forces,
                wec_step_result *out_n);
 
+/* Execution mode.  enable = 1 (default): the whole step -- including the
+ * pressure solve's iteration, steered on the GPU by conditional WHILE / IF graph
+ * nodes -- runs as one CUDA graph, captured at the first step and replayed.
+ * enable = 0: kernels are launched one by one and the solver's progress is read
+ * by the host once per iteration.  Both run the same kernels in the same order
+ * (identical results).  Event profiling (wec_profile_enable) uses mode 0. */
+int wec_tank_use_graph(wec_tank *tank, int enable);
+
 /* Solve A p = rhs with the tank's pressure operator of its last step (face
  * coefficients 1/D; Neumann walls, p = 0 above the top row).  rhs, p: device,
  * nx*ny doubles; p holds the initial guess on entry and the solution on exit.
@@ -211,6 +219,15 @@ double wec_wave_number_fenton_kd(double omega, double depth, double g);
  * [1.6 / 3.5955, 20 / 3.5955] wp at their mid-points; amplitudes rescaled so that
  * 4 sqrt(sum a^2 / 2) = Hs.  amp, omega: host, ncomp each (outputs). */
 int wec_jonswap(double Hs, double Tp, double gamma, int ncomp, double *amp, double *omega);
+
+/* ---- process-wide options ------------------------------------------------ */
+/* "mg_fused" (default 1): the multigrid V-cycle runs as one shared-memory tile
+ * kernel per fine level for pre-smoothing + residual + restriction, one for
+ * prolongation + post-smoothing, and one single-CTA kernel for every level of at
+ * most 16384 cells; 0 launches one kernel per colour pass, restriction and
+ * prolongation.  Both compute the same values bit for bit.  Applies to graphs
+ * captured and solves started after the call.  Unknown name: WEC_ERR_INVALID. */
+int wec_set_option(const char *name, int value);
 
 /* ---- launch accounting and profiling ------------------------------------ */
 /* Number of kernels this library has launched in the process so far. */

@@ -41,9 +41,17 @@ static int check_opts(const wec_solver_opts *o)
         return fail(WEC_ERR_INVALID, "precision must be WEC_PREC_FP64 or WEC_PREC_MIXED");
     if (!(o->rtol > 0.0) || o->max_iters < 1) return fail(WEC_ERR_INVALID, "rtol must be > 0 and max_iters >= 1");
     if (o->restart < 1 || o->restart > kMaxRestart) return fail(WEC_ERR_INVALID, "restart must be in 1..32");
-    if (o->n_reinit < 0 || o->n_jacobi < 1 || o->mg_pre < 0 || o->mg_post < 0 || o->mg_pre + o->mg_post < 1)
-        return fail(WEC_ERR_INVALID, "need n_reinit >= 0, n_jacobi >= 1 and at least one smoothing sweep");
+    if (o->n_reinit < 0 || o->n_jacobi < 1 || o->mg_pre < 1 || o->mg_post < 0 || o->mg_pre > 4 || o->mg_post > 4)
+        return fail(WEC_ERR_INVALID, "need n_reinit >= 0, n_jacobi >= 1, 1 <= mg_pre <= 4, 0 <= mg_post <= 4");
     return WEC_OK;
+}
+
+// Wait for the caller's stream and the tank's own stream.
+static cudaError_t sync_tank(const wec_tank *T)
+{
+    cudaError_t e = cudaStreamSynchronize(T->st);
+    if (e == cudaSuccess && T->gst) e = cudaStreamSynchronize(T->gst);
+    return e;
 }
 
 static double *field_ptr(const wec_tank *T, int id, size_t *n, bool *writable)
@@ -158,6 +166,7 @@ void wec_tank_destroy(wec_tank *T)
 {
     if (!T) return;
     cudaStreamSynchronize(T->st);
+    if (T->gst) cudaStreamSynchronize(T->gst);
     tank_free(T);
     delete T;
 }
@@ -180,12 +189,36 @@ int wec_step_n(wec_tank *T, int nsteps, double dt, const double *pto, wec_step_r
     return WEC_OK;
 }
 
+int wec_set_option(const char *name, int value)
+{
+    if (!name) return fail(WEC_ERR_INVALID, "option name is NULL");
+    if (std::string(name) == "mg_fused") {
+        set_mg_fused(value != 0);
+        return WEC_OK;
+    }
+    return fail(WEC_ERR_INVALID, std::string("unknown option: ") + name);
+}
+
+int wec_tank_use_graph(wec_tank *T, int enable)
+{
+    if (!T) return fail(WEC_ERR_INVALID, "tank is NULL");
+    T->use_graph = enable != 0;
+    return WEC_OK;
+}
+
 int wec_pressure_solve(wec_tank *T, const double *rhs, double *p, double rtol, int *iters, double *relres)
 {
     if (!T || !rhs || !p) return fail(WEC_ERR_INVALID, "NULL argument");
     if (!T->stepped) return fail(WEC_ERR_INVALID, "no pressure operator yet: take a step first");
     if (!(rtol > 0.0)) return fail(WEC_ERR_INVALID, "rtol must be > 0");
-    return poisson_solve(&T->solver, rhs, p, rtol, T->opts.max_iters, iters, relres);
+    // the caller's device buffers are ordered on the caller's stream
+    WEC_CK(cudaEventRecord(T->ev_in, T->st));
+    WEC_CK(cudaStreamWaitEvent(T->gst, T->ev_in, 0));
+    T->solver.st = T->gst;
+    int rc = poisson_solve(&T->solver, rhs, p, rtol, T->opts.max_iters, iters, relres);
+    WEC_CK(cudaEventRecord(T->ev_out, T->gst));
+    WEC_CK(cudaStreamWaitEvent(T->st, T->ev_out, 0));
+    return rc;
 }
 
 int wec_get_field(const wec_tank *T, int id, double *dst, size_t n)
@@ -196,7 +229,7 @@ int wec_get_field(const wec_tank *T, int id, double *dst, size_t n)
     double *src = field_ptr(T, id, &m, &w);
     if (!src) return fail(WEC_ERR_INVALID, "unknown field id");
     if (n != m) return fail(WEC_ERR_INVALID, "field size mismatch: expected " + std::to_string(m));
-    WEC_CK(cudaStreamSynchronize(T->st));
+    WEC_CK(sync_tank(T));
     WEC_CK(cudaMemcpy(dst, src, n * 8, cudaMemcpyDeviceToHost));
     return WEC_OK;
 }
@@ -210,7 +243,7 @@ int wec_set_field(wec_tank *T, int id, const double *src, size_t n)
     if (!dst) return fail(WEC_ERR_INVALID, "unknown field id");
     if (!w) return fail(WEC_ERR_INVALID, "field is read-only");
     if (n != m) return fail(WEC_ERR_INVALID, "field size mismatch: expected " + std::to_string(m));
-    WEC_CK(cudaStreamSynchronize(T->st));
+    WEC_CK(sync_tank(T));
     WEC_CK(cudaMemcpy(dst, src, n * 8, cudaMemcpyHostToDevice));
     return WEC_OK;
 }
@@ -218,7 +251,7 @@ int wec_set_field(wec_tank *T, int id, const double *src, size_t n)
 int wec_get_state(const wec_tank *T, double *out5)
 {
     if (!T || !out5) return fail(WEC_ERR_INVALID, "NULL argument");
-    WEC_CK(cudaStreamSynchronize(T->st));
+    WEC_CK(sync_tank(T));
     StepScalars s;
     WEC_CK(cudaMemcpy(&s, T->S, sizeof(s), cudaMemcpyDeviceToHost));
     out5[0] = s.t; out5[1] = s.yc; out5[2] = s.zdot; out5[3] = s.zdot_prev; out5[4] = s.yc0;
@@ -228,7 +261,7 @@ int wec_get_state(const wec_tank *T, double *out5)
 int wec_set_state(wec_tank *T, double t, double yc, double zdot, double zdot_prev)
 {
     if (!T) return fail(WEC_ERR_INVALID, "tank is NULL");
-    WEC_CK(cudaStreamSynchronize(T->st));
+    WEC_CK(sync_tank(T));
     StepScalars s;
     WEC_CK(cudaMemcpy(&s, T->S, sizeof(s), cudaMemcpyDeviceToHost));
     s.t = t; s.yc = yc; s.zdot = zdot; s.zdot_prev = zdot_prev;
@@ -247,7 +280,7 @@ int wec_save(const wec_tank *T, void *buf, size_t *n)
         return WEC_OK;
     }
     if (*n < need) return fail(WEC_ERR_INVALID, "checkpoint buffer too small");
-    WEC_CK(cudaStreamSynchronize(T->st));
+    WEC_CK(sync_tank(T));
     char *q = (char *)buf;
     uint64_t hdr[2] = {kMagic, ((uint64_t)T->P.nx << 32) | (uint32_t)T->P.ny};
     memcpy(q, hdr, 16);
@@ -275,7 +308,7 @@ int wec_load(wec_tank *T, const void *buf, size_t n)
     if (hdr[0] != kMagic || hdr[1] != (((uint64_t)T->P.nx << 32) | (uint32_t)T->P.ny))
         return fail(WEC_ERR_INVALID, "checkpoint header does not match this tank");
     q += 16;
-    WEC_CK(cudaStreamSynchronize(T->st));
+    WEC_CK(sync_tank(T));
     WEC_CK(cudaMemcpy(T->sig, q, T->nc * 8, cudaMemcpyHostToDevice)); q += T->nc * 8;
     WEC_CK(cudaMemcpy(T->u, q, T->nu * 8, cudaMemcpyHostToDevice)); q += T->nu * 8;
     WEC_CK(cudaMemcpy(T->v, q, T->nv * 8, cudaMemcpyHostToDevice)); q += T->nv * 8;
@@ -320,7 +353,7 @@ int wec_poisson_set_coefficients(wec_poisson *P, const double *bu, const double 
     size_t nu = (size_t)(P->nx + 1) * P->ny, nv = (size_t)P->nx * (P->ny + 1);
     WEC_CK(cudaMemcpyAsync(P->L64[0].bu, bu, nu * 8, cudaMemcpyDeviceToDevice, P->st));
     WEC_CK(cudaMemcpyAsync(P->L64[0].bv, bv, nv * 8, cudaMemcpyDeviceToDevice, P->st));
-    int e = poisson_build(P);
+    int e = poisson_build(P, P->st);
     if (e) return e;
     WEC_CK(cudaStreamSynchronize(P->st));
     return WEC_OK;

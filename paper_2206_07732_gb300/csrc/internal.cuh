@@ -15,8 +15,9 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr int kMaxLevels = 24;
 constexpr int kMaxRestart = 32;
 constexpr int kMaxCoarse = 512;      // cells on the coarsest multigrid level
-constexpr int kRedBlocks = 304;      // partial-sum blocks of every reduction (2 x 152 SMs)
+constexpr int kRedBlocks = 304;      // partial-sum blocks of the step's reductions (2 x 152 SMs)
 constexpr int kRedThreads = 256;
+constexpr int kKrylovBlocks = 1216;  // max blocks of the fused Krylov kernels (8 x 152 SMs)
 
 void set_error(const std::string &msg);
 int fail(int code, const std::string &msg);
@@ -41,6 +42,11 @@ class Scope {
     int slot_;
     cudaStream_t st_;
 };
+void begin_capture();          // launch scopes on this thread are being recorded into a graph
+long long captured();          // scopes opened since begin_capture()
+void end_capture();
+void add_launches(long long n);  // kernels a graph replay executed
+bool enabled();                // event profiling on (graphs are then not used)
 }  // namespace prof
 
 #define WEC_PROF(NAME, LEVEL, BYTES, ST) ::wec::prof::Scope wec_prof_scope_((NAME), (LEVEL), (double)(BYTES), (ST))
@@ -50,6 +56,13 @@ template <typename T>
 struct Level {
     int nx = 0, ny = 0;
     T *bu = nullptr, *bv = nullptr, *x = nullptr, *b = nullptr;
+};
+
+// FGMRES state on the device (read by the kernels that steer the iteration).
+struct KState {
+    int j, its, jd, cycle_end, done, status, maxit, m, ncycles, pad_;
+    unsigned int cnt[4];  // last-block counters of the fused reductions
+    double bn, tol, beta, hn, rtol;
 };
 
 }  // namespace wec
@@ -67,11 +80,12 @@ struct wec_poisson {
     double *V = nullptr;        // (m+1) x n
     void *Z = nullptr;          // m x n, double (FP64) or float (mixed)
     double *w = nullptr;        // n
-    double *part = nullptr;     // kMaxRestart+1 x kRedBlocks partial sums
-    double *dots = nullptr;     // kMaxRestart+1 results
-    double *hess = nullptr;     // (m+1) x m Hessenberg, then cs, sn, g, y, scalars
-    double *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr, *scal = nullptr;
-    double *host = nullptr;     // pinned mirror of a few scalars
+    double *part = nullptr;     // (kMaxRestart+2) x kKrylovBlocks partial sums
+    double *dots = nullptr;     // h1, h2 of the two Gram-Schmidt passes
+    double *hess = nullptr;     // (m+1) x m Hessenberg, then cs, sn, g, y
+    double *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr;
+    wec::KState *ks = nullptr;  // device
+    wec::KState *ksh = nullptr; // pinned host mirror
     size_t bytes = 0;
 };
 
@@ -82,15 +96,21 @@ int poisson_init(wec_poisson *P, int nx, int ny, int prec, int restart, int nu1,
                  cudaStream_t st);
 void poisson_free(wec_poisson *P);
 // Level-0 coefficients already in P->L64[0].bu / bv (device): build coarse levels,
-// FP32 copies and the coarse LU.
-int poisson_build(wec_poisson *P);
+// FP32 copies and the coarse LU (enqueued on st).
+int poisson_build(wec_poisson *P, cudaStream_t st);
+// Host-polled FGMRES solve on P->st.
 int poisson_solve(wec_poisson *P, const double *b, double *x, double rtol, int maxit, int *iters,
                   double *relres);
+// Record the same solve into the graph being captured on st (conditional nodes).
+int poisson_capture_solve(wec_poisson *P, const double *b, double *x, double rtol, int maxit, cudaStream_t st,
+                          cudaStream_t h1, cudaStream_t h2);
+int poisson_state_to_host(wec_poisson *P, cudaStream_t st);
+int poisson_count_kernels(wec_poisson *P, cudaStream_t s, int *n_begin, int *n_body, int *n_close);
+// Status / iterations / relative residual from the host mirror of the state.
+int solve_result(wec_poisson *P, int *iters, double *relres);
 int poisson_apply(wec_poisson *P, const double *x, double *y);
+void set_mg_fused(bool on);
 int poisson_vcycle(wec_poisson *P, const double *b, double *x);
-
-// Deterministic reductions: partial sums per block, then one block per result.
-void launch_norm2(const double *a, int n, double *part, double *out, cudaStream_t st);
 
 // waves.cpp
 double wave_number(double omega, double depth, double g);

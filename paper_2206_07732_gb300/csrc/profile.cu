@@ -23,6 +23,8 @@ struct Rec {
 
 std::mutex g_mu;
 long long g_launches = 0;
+thread_local int t_capturing = 0;
+thread_local long long t_captured = 0;
 int g_mode = 0;
 std::string g_only;
 std::vector<Rec> g_recs;
@@ -44,6 +46,10 @@ cudaEvent_t take_event()
 
 Scope::Scope(const char *name, int level, double bytes, cudaStream_t st) : slot_(-1), st_(st)
 {
+    if (t_capturing) {  // recorded into a graph: counted when the graph runs
+        ++t_captured;
+        return;
+    }
     std::lock_guard<std::mutex> lk(g_mu);
     ++g_launches;
     if (g_mode == 0 || (g_mode == 2 && g_only != name)) return;
@@ -58,6 +64,34 @@ Scope::~Scope()
     if (slot_ < 0) return;
     std::lock_guard<std::mutex> lk(g_mu);
     cudaEventRecord(g_recs[slot_].b, st_);
+}
+
+void begin_capture()
+{
+    t_capturing = 1;
+    t_captured = 0;
+}
+
+long long captured()
+{
+    return t_captured;
+}
+
+void end_capture()
+{
+    t_capturing = 0;
+}
+
+void add_launches(long long n)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_launches += n;
+}
+
+bool enabled()
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    return g_mode != 0;
 }
 
 }  // namespace prof

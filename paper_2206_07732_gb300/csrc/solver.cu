@@ -10,6 +10,7 @@
 // fine faces it covers, dense LU on the coarsest level (<= 512 cells).
 // Mixed precision: the V-cycle runs in FP32 on FP32 copies of the hierarchy;
 // the Krylov basis, Hessenberg, residuals and the solution stay FP64.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -18,6 +19,14 @@
 
 namespace wec {
 namespace {
+
+// Level-0 vectors of the V-cycle are FGMRES basis columns: base + j * n with j
+// read on the device (so a captured graph serves every Arnoldi index).
+template <typename T>
+__device__ __forceinline__ T *at_sel(T *p, const int *sel, long long stride)
+{
+    return sel ? p + (long long)(*sel) * stride : p;
+}
 
 // ------------------------------------------------------------ stencil ----
 template <typename T>
@@ -73,11 +82,14 @@ __global__ void k_residual(int nx, int ny, const double *__restrict__ bu, const 
 // x = 0, so the red pass writes b / d and zeroes the black cells.
 template <typename T>
 __global__ void k_rbgs(int nx, int ny, const T *__restrict__ bu, const T *__restrict__ bv, T *x,
-                       const T *__restrict__ b, int color, int first)
+                       const T *__restrict__ b, int color, int first, const int *bsel, const int *xsel)
 {
     int half = nx >> 1;
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= half * ny) return;
+    const long long n = (long long)nx * ny;
+    x = at_sel(x, xsel, n);
+    b = at_sel(b, bsel, n);
     int j = k / half;
     int i = 2 * (k - j * half) + ((j & 1) ^ color);
     int c = j * nx + i;
@@ -93,11 +105,15 @@ __global__ void k_rbgs(int nx, int ny, const T *__restrict__ bu, const T *__rest
 // Coarse right-hand side = sum of the residuals of the four children.
 template <typename T>
 __global__ void k_resid_restrict(int nx, int ny, const T *__restrict__ bu, const T *__restrict__ bv,
-                                 const T *__restrict__ x, const T *__restrict__ b, T *__restrict__ bc)
+                                 const T *__restrict__ x, const T *__restrict__ b, T *__restrict__ bc,
+                                 const int *bsel, const int *xsel)
 {
     int ncx = nx >> 1, ncy = ny >> 1;
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= ncx * ncy) return;
+    const long long n = (long long)nx * ny;
+    x = at_sel(x, xsel, n);
+    b = at_sel(b, bsel, n);
     int I = k % ncx, J = k / ncx;
     T r[4];
     int q = 0;
@@ -112,10 +128,11 @@ __global__ void k_resid_restrict(int nx, int ny, const T *__restrict__ bu, const
 }
 
 template <typename T>
-__global__ void k_prolong(int nx, int ny, T *__restrict__ x, const T *__restrict__ xc)
+__global__ void k_prolong(int nx, int ny, T *__restrict__ x, const T *__restrict__ xc, const int *sel)
 {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= nx * ny) return;
+    x = at_sel(x, sel, (long long)nx * ny);
     int i = c % nx, j = c / nx;
     x[c] += xc[(j >> 1) * (nx >> 1) + (i >> 1)];
 }
@@ -138,10 +155,12 @@ __global__ void k_coarsen(int nx, int ny, const T *__restrict__ fu, const T *__r
 }
 
 template <typename TO, typename TI>
-__global__ void k_convert(long long n, const TI *__restrict__ in, TO *__restrict__ out)
+__global__ void k_convert(long long n, const TI *__restrict__ in, TO *__restrict__ out, const int *insel)
 {
     long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (c < n) out[c] = TO(in[c]);
+    if (c >= n) return;
+    in = at_sel(in, insel, n);
+    out[c] = TO(in[c]);
 }
 
 // Dense LU of the coarsest operator (no pivoting: A is a symmetric M-matrix).
@@ -174,9 +193,12 @@ __global__ void k_lu_factor(int nx, int ny, const T *__restrict__ bu, const T *_
 
 // x = U^{-1} L^{-1} b, one warp.
 template <typename T>
-__global__ void k_lu_solve(int n, const T *__restrict__ A, const T *__restrict__ b, T *__restrict__ x)
+__global__ void k_lu_solve(int n, const T *__restrict__ A, const T *__restrict__ b, T *__restrict__ x,
+                           const int *bsel, const int *xsel)
 {
     int lane = threadIdx.x;
+    b = at_sel(b, bsel, n);
+    x = at_sel(x, xsel, n);
     for (int r = 0; r < n; ++r) {
         T s = T(0);
         for (int c = lane; c < r; c += 32) s += A[(long long)r * n + c] * x[c];
@@ -193,99 +215,301 @@ __global__ void k_lu_solve(int n, const T *__restrict__ A, const T *__restrict__
     }
 }
 
-// ---------------------------------------------------------- reductions ----
-__device__ __forceinline__ double block_sum(double v, double *sh)
+}  // namespace
+}  // namespace wec
+
+#include "mg_fused.cuh"
+
+namespace wec {
+namespace {
+
+bool g_mg_fused = true;  // fused V-cycle kernels (wec_set_option "mg_fused")
+
+// --------------------------------------------------- Krylov (FP64 outer) ----
+// Device-resident FGMRES state: the iteration is steered by the GPU, so the
+// same kernels run host-polled (one status read per iteration) or inside one
+// CUDA graph whose WHILE / IF conditional nodes read the state.
+constexpr int KT = 256;  // threads of every fused Krylov kernel (8 warps)
+
+__device__ __forceinline__ double warp_sum(double v)
 {
-    int t = threadIdx.x;
-    sh[t] = v;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum over the block's 256 threads in a fixed tree; valid in thread 0.
+__device__ double block_sum(double v, double *sh8)
+{
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0) sh8[threadIdx.x >> 5] = v;
     __syncthreads();
-    for (int s = blockDim.x >> 1; s > 0; s >>= 1) {
-        if (t < s) sh[t] += sh[t + s];
-        __syncthreads();
-    }
-    double r = sh[0];
+    double r = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < KT / 32; ++w) r += sh8[w];
     __syncthreads();
     return r;
 }
 
-// part[k * kRedBlocks + b] = partial sum of V_k . w over block b's elements
-__global__ void k_dots_partial(int n, const double *__restrict__ V, const double *__restrict__ w,
-                               double *__restrict__ part)
+// True in the block that finishes last (all other blocks' partials are visible).
+__device__ bool last_block(unsigned int *cnt)
 {
-    __shared__ double sh[kRedThreads];
-    int k = blockIdx.y;
-    const double *vk = V + (long long)k * n;
+    __shared__ int s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(cnt, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    return s_last != 0;
+}
+
+// Deterministic total of the G partials of one quantity.
+__device__ double final_sum(const double *part, int G, double *sh8)
+{
     double s = 0.0;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) s += vk[c] * w[c];
-    s = block_sum(s, sh);
-    if (threadIdx.x == 0) part[k * kRedBlocks + blockIdx.x] = s;
+    for (int b = threadIdx.x; b < G; b += KT) s += __ldcg(part + b);
+    return block_sum(s, sh8);
 }
 
-__global__ void k_dots_final(const double *__restrict__ part, double *__restrict__ out)
+__device__ __forceinline__ void set_cond(unsigned long long h, int use, unsigned int v)
 {
-    __shared__ double sh[kRedThreads];
-    int k = blockIdx.x;
-    double s = 0.0;
-    for (int b = threadIdx.x; b < kRedBlocks; b += blockDim.x) s += part[k * kRedBlocks + b];
-    s = block_sum(s, sh);
-    if (threadIdx.x == 0) out[k] = s;
+    if (use) cudaGraphSetConditional((cudaGraphConditionalHandle)h, v);
 }
 
-// w -= sum_k h[k] V_k
-__global__ void k_axpy_multi(int n, int nvec, const double *__restrict__ V, const double *__restrict__ hcoef,
-                             double *__restrict__ w)
+__global__ void k_ks_init(KState *ks, double rtol, int maxit, int m)
 {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= n) return;
-    double a = w[c];
-    for (int k = 0; k < nvec; ++k) a -= hcoef[k] * V[(long long)k * n + c];
-    w[c] = a;
+    ks->rtol = rtol;
+    ks->maxit = maxit;
+    ks->m = m;
+    ks->its = 0;
+    ks->status = 0;
+    ks->done = 0;
+    ks->j = 0;
+    ks->jd = 0;
+    ks->cycle_end = 0;
+    ks->ncycles = 0;
 }
 
-__global__ void k_scale_div(int n, const double *__restrict__ w, const double *__restrict__ s,
-                            double *__restrict__ out)
+// bn = ||b||_2, tol = rtol bn.
+__global__ void __launch_bounds__(KT) k_bnorm(long long n, const double *__restrict__ b, double *part,
+                                                KState *ks)
 {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < n) out[c] = w[c] / s[0];
+    __shared__ double sh[KT / 32];
+    double a = 0.0;
+    for (long long c = blockIdx.x * (long long)KT + threadIdx.x; c < n; c += (long long)gridDim.x * KT)
+        a += b[c] * b[c];
+    a = block_sum(a, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = a;
+    if (!last_block(&ks->cnt[0])) return;
+    double t = final_sum(part, gridDim.x, sh);
+    if (threadIdx.x == 0) {
+        double bn = sqrt(t);
+        ks->bn = bn;
+        ks->tol = ks->rtol * bn;
+        ks->cnt[0] = 0;
+    }
 }
 
-__global__ void k_sqrt(double *a) { a[0] = sqrt(a[0]); }
-
-// Column j of the Hessenberg matrix from the two Gram-Schmidt passes, Givens
-// rotations, residual estimate.  scal[2] = |g_{j+1}|, scal[3] = h_{j+1,j}.
-__global__ void k_givens(int j, int m, const double *__restrict__ h1, const double *__restrict__ h2,
-                         const double *__restrict__ hn2, double *H, double *cs, double *sn, double *g,
-                         double *scal)
+// w = b - A x and beta = ||w||.  mode 0 (start): converged if beta <= tol.
+// mode 1 (end of a cycle): converged, out of iterations, or restart.
+// A zero right-hand side gives x = 0.  Opens a new Arnoldi cycle unless done and
+// sets the WHILE condition to !done.
+__global__ void __launch_bounds__(KT) k_residual_norm(int nx, int ny, const double *__restrict__ bu,
+                                                        const double *__restrict__ bv, const double *__restrict__ b,
+                                                        double *x, double *__restrict__ w, double *part,
+                                                        KState *ks, double *g, int mode,
+                                                        unsigned long long hwhile, int use)
 {
+    __shared__ double sh[KT / 32];
+    const long long n = (long long)nx * ny;
+    const bool zero = ks->bn == 0.0;
+    double a = 0.0;
+    for (long long c = blockIdx.x * (long long)KT + threadIdx.x; c < n; c += (long long)gridDim.x * KT) {
+        if (zero) {
+            x[c] = 0.0;
+            w[c] = 0.0;
+            continue;
+        }
+        int i = (int)(c % nx), j = (int)(c / nx);
+        double d = diag_at(bu, bv, nx, ny, i, j);
+        double r = b[c] - (d * x[c] - offsum_at(bu, bv, x, nx, ny, i, j));
+        w[c] = r;
+        a += r * r;
+    }
+    a = block_sum(a, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = a;
+    if (!last_block(&ks->cnt[1])) return;
+    double t = final_sum(part, gridDim.x, sh);
+    if (threadIdx.x == 0) {
+        double beta = sqrt(t);
+        ks->beta = beta;
+        if (mode == 1) ks->ncycles += 1;
+        int done;
+        if (zero) {
+            done = 1;
+        } else if (!isfinite(beta)) {
+            done = 1;
+            ks->status = WEC_ERR_NONFINITE;
+        } else if (beta <= ks->tol) {
+            done = 1;
+        } else if (mode == 1 && ks->its >= ks->maxit) {
+            done = 1;
+            ks->status = WEC_ERR_NOT_CONVERGED;
+        } else {
+            done = 0;
+        }
+        ks->done = done;
+        if (!done) {
+            g[0] = beta;
+            for (int k = 1; k <= ks->m; ++k) g[k] = 0.0;
+            ks->j = 0;
+            ks->cycle_end = 0;
+        }
+        ks->cnt[1] = 0;
+        set_cond(hwhile, use, done ? 0u : 1u);
+    }
+}
+
+// V_0 = w / beta for a new cycle.
+__global__ void k_scale0(long long n, const double *__restrict__ w, double *__restrict__ V, const KState *ks)
+{
+    if (ks->done) return;
+    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c < n) V[c] = w[c] / ks->beta;
+}
+
+// w = A z_j and the first Gram-Schmidt dot products h1_k = V_k . w (k <= j).
+template <typename TZ>
+__global__ void __launch_bounds__(KT) k_matvec_dots(int nx, int ny, const double *__restrict__ bu,
+                                                      const double *__restrict__ bv, const TZ *__restrict__ Z,
+                                                      const double *__restrict__ V, double *__restrict__ w,
+                                                      double *part, double *h1, KState *ks)
+{
+    __shared__ double sh[KT / 32];
+    const long long n = (long long)nx * ny;
+    const int j = ks->j, G = gridDim.x;
+    const TZ *z = Z + (long long)j * n;
+    for (long long c = blockIdx.x * (long long)KT + threadIdx.x; c < n; c += (long long)G * KT) {
+        int i = (int)(c % nx), jj = (int)(c / nx);
+        double d = diag_at(bu, bv, nx, ny, i, jj);
+        w[c] = d * double(z[c]) - offsum_at(bu, bv, z, nx, ny, i, jj);
+    }
+    for (int k = 0; k <= j; ++k) {
+        const double *vk = V + (long long)k * n;
+        double a = 0.0;
+        for (long long c = blockIdx.x * (long long)KT + threadIdx.x; c < n; c += (long long)G * KT)
+            a += vk[c] * w[c];
+        a = block_sum(a, sh);
+        if (threadIdx.x == 0) part[k * G + blockIdx.x] = a;
+    }
+    if (!last_block(&ks->cnt[2])) return;
+    for (int k = 0; k <= j; ++k) {
+        double t = final_sum(part + k * G, G, sh);
+        if (threadIdx.x == 0) h1[k] = t;
+    }
+    if (threadIdx.x == 0) ks->cnt[2] = 0;
+}
+
+// First Gram-Schmidt update w -= sum_k h1_k V_k, then h2_k = V_k . w.
+__global__ void __launch_bounds__(KT) k_orth_dots(long long n, const double *__restrict__ V, double *__restrict__ w,
+                                                    const double *__restrict__ h1, double *part, double *h2,
+                                                    KState *ks)
+{
+    __shared__ double sh[KT / 32];
+    const int j = ks->j, G = gridDim.x;
+    for (long long c = blockIdx.x * (long long)KT + threadIdx.x; c < n; c += (long long)G * KT) {
+        double a = w[c];
+        for (int k = 0; k <= j; ++k) a -= h1[k] * V[(long long)k * n + c];
+        w[c] = a;
+    }
+    for (int k = 0; k <= j; ++k) {
+        const double *vk = V + (long long)k * n;
+        double a = 0.0;
+        for (long long c = blockIdx.x * (long long)KT + threadIdx.x; c < n; c += (long long)G * KT)
+            a += vk[c] * w[c];
+        a = block_sum(a, sh);
+        if (threadIdx.x == 0) part[k * G + blockIdx.x] = a;
+    }
+    if (!last_block(&ks->cnt[2])) return;
+    for (int k = 0; k <= j; ++k) {
+        double t = final_sum(part + k * G, G, sh);
+        if (threadIdx.x == 0) h2[k] = t;
+    }
+    if (threadIdx.x == 0) ks->cnt[2] = 0;
+}
+
+// Second update w -= sum_k h2_k V_k and h_{j+1,j} = ||w||; the last block applies
+// the Givens rotations to column j, counts the iteration, decides whether the
+// cycle ends (converged estimate, iteration cap, breakdown, or full basis) and
+// sets the IF condition.
+__global__ void __launch_bounds__(KT) k_orth_norm(long long n, const double *__restrict__ V, double *__restrict__ w,
+                                                    const double *__restrict__ h1, const double *__restrict__ h2,
+                                                    double *part, KState *ks, double *H, double *cs, double *sn,
+                                                    double *g, unsigned long long hif, int use)
+{
+    __shared__ double sh[KT / 32];
+    const int j = ks->j, G = gridDim.x;
+    double a2 = 0.0;
+    for (long long c = blockIdx.x * (long long)KT + threadIdx.x; c < n; c += (long long)G * KT) {
+        double a = w[c];
+        for (int k = 0; k <= j; ++k) a -= h2[k] * V[(long long)k * n + c];
+        w[c] = a;
+        a2 += a * a;
+    }
+    a2 = block_sum(a2, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = a2;
+    if (!last_block(&ks->cnt[2])) return;
+    double t = final_sum(part, G, sh);
+    if (threadIdx.x != 0) return;
+    const int m = ks->m;
     for (int k = 0; k <= j; ++k) H[k * m + j] = (0.0 + h1[k]) + h2[k];
-    double hn = sqrt(hn2[0]);
+    double hn = sqrt(t);
     H[(j + 1) * m + j] = hn;
     for (int k = 0; k < j; ++k) {
-        double a = H[k * m + j], b = H[(k + 1) * m + j];
-        H[k * m + j] = cs[k] * a + sn[k] * b;
-        H[(k + 1) * m + j] = -sn[k] * a + cs[k] * b;
+        double p = H[k * m + j], q = H[(k + 1) * m + j];
+        H[k * m + j] = cs[k] * p + sn[k] * q;
+        H[(k + 1) * m + j] = -sn[k] * p + cs[k] * q;
     }
-    double a = H[j * m + j], b = H[(j + 1) * m + j];
-    double den = sqrt(a * a + b * b);
-    cs[j] = a / den;
-    sn[j] = b / den;
+    double p = H[j * m + j], q = H[(j + 1) * m + j];
+    double den = sqrt(p * p + q * q);
+    cs[j] = p / den;
+    sn[j] = q / den;
     H[j * m + j] = den;
     H[(j + 1) * m + j] = 0.0;
     g[j + 1] = -sn[j] * g[j];
     g[j] = cs[j] * g[j];
-    scal[2] = fabs(g[j + 1]);
-    scal[3] = hn;
+    ks->its += 1;
+    ks->jd = j + 1;
+    ks->hn = hn;
+    double est = fabs(g[j + 1]);
+    int ce = est <= ks->tol || ks->its >= ks->maxit || hn == 0.0 || j + 1 == m || !isfinite(est);
+    if (!isfinite(est)) ks->status = WEC_ERR_NONFINITE;
+    ks->cycle_end = ce;
+    ks->cnt[2] = 0;
+    set_cond(hif, use, (unsigned)ce);
 }
 
-__global__ void k_cycle_init(int m, const double *beta, double *g)
+// V_{j+1} = w / h_{j+1,j}, then j += 1 (unless the cycle ends).
+__global__ void __launch_bounds__(KT) k_next_basis(long long n, const double *__restrict__ w, double *V, KState *ks)
 {
-    for (int k = 0; k <= m; ++k) g[k] = 0.0;
-    g[0] = beta[0];
+    const int j = ks->j;
+    if (!ks->cycle_end) {
+        double *vn = V + (long long)(j + 1) * n;
+        const double hn = ks->hn;
+        for (long long c = blockIdx.x * (long long)KT + threadIdx.x; c < n; c += (long long)gridDim.x * KT)
+            vn[c] = w[c] / hn;
+    }
+    if (!last_block(&ks->cnt[3])) return;
+    if (threadIdx.x == 0) {
+        if (!ks->cycle_end) ks->j = j + 1;
+        ks->cnt[3] = 0;
+    }
 }
 
-__global__ void k_backsolve(int jd, int m, const double *__restrict__ H, const double *__restrict__ g,
-                            double *__restrict__ y)
+__global__ void k_backsolve(int m, const double *__restrict__ H, const double *__restrict__ g, double *__restrict__ y,
+                            const KState *ks)
 {
+    const int jd = ks->jd;
     for (int k = jd - 1; k >= 0; --k) {
         double s = g[k];
         for (int l = k + 1; l < jd; ++l) s -= H[k * m + l] * y[l];
@@ -294,133 +518,262 @@ __global__ void k_backsolve(int jd, int m, const double *__restrict__ H, const d
 }
 
 template <typename TZ>
-__global__ void k_update_x(int n, int jd, const double *__restrict__ y, const TZ *__restrict__ Z,
-                           double *__restrict__ x)
+__global__ void k_update_x(long long n, const double *__restrict__ y, const TZ *__restrict__ Z, double *__restrict__ x,
+                           const KState *ks)
 {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (c >= n) return;
+    const int jd = ks->jd;
     double a = x[c];
     for (int k = 0; k < jd; ++k) a += y[k] * double(Z[(long long)k * n + c]);
     x[c] = a;
 }
 
 // ------------------------------------------------------------ V-cycle ----
+// bsel / xsel: device index of the level-0 right-hand side / solution column
+// (nullptr: the pointer is used as is).
 template <typename T>
-void vcycle_t(wec_poisson *P, Level<T> *L, const T *b0, T *x0)
+void vcycle_unfused(wec_poisson *P, Level<T> *L, const T *b0, T *x0, const int *bsel, const int *xsel,
+                    cudaStream_t st)
 {
-    cudaStream_t st = P->st;
     const int TB = 256;
     const double ts = sizeof(T);
     for (int l = 0; l < P->nlev; ++l) {
         Level<T> &A = L[l];
         const T *b = l == 0 ? b0 : A.b;
         T *x = l == 0 ? x0 : A.x;
+        const int *bs = l == 0 ? bsel : nullptr, *xs = l == 0 ? xsel : nullptr;
         const double n = (double)A.nx * A.ny, nf = (double)(A.nx + 1) * A.ny + (double)A.nx * (A.ny + 1);
         if (l == P->nlev - 1) {
             T *lu = nullptr;
             if constexpr (sizeof(T) == 8) lu = (T *)P->lu64; else lu = (T *)P->lu32;
             WEC_PROF("mg_lu_solve", l, (n * n + 2 * n) * ts, st);
-            k_lu_solve<T><<<1, 32, 0, st>>>(A.nx * A.ny, lu, b, x);
+            k_lu_solve<T><<<1, 32, 0, st>>>(A.nx * A.ny, lu, b, x, bs, xs);
             break;
         }
         int nh = (A.nx >> 1) * A.ny;
-        for (int s = 0; s < P->nu1; ++s) {
+        for (int q = 0; q < P->nu1; ++q) {
             {
                 WEC_PROF("mg_rbgs", l, (1.5 * n + nf) * ts, st);
-                k_rbgs<T><<<nblk(nh, TB), TB, 0, st>>>(A.nx, A.ny, A.bu, A.bv, x, b, 0, s == 0);
+                k_rbgs<T><<<nblk(nh, TB), TB, 0, st>>>(A.nx, A.ny, A.bu, A.bv, x, b, 0, q == 0, bs, xs);
             }
             {
                 WEC_PROF("mg_rbgs", l, (1.5 * n + nf) * ts, st);
-                k_rbgs<T><<<nblk(nh, TB), TB, 0, st>>>(A.nx, A.ny, A.bu, A.bv, x, b, 1, 0);
+                k_rbgs<T><<<nblk(nh, TB), TB, 0, st>>>(A.nx, A.ny, A.bu, A.bv, x, b, 1, 0, bs, xs);
             }
         }
-        if (P->nu1 == 0) cudaMemsetAsync(x, 0, sizeof(T) * A.nx * A.ny, st);
         Level<T> &C = L[l + 1];
         WEC_PROF("mg_resid_restrict", l, (2.25 * n + nf) * ts, st);
-        k_resid_restrict<T><<<nblk(C.nx * C.ny, TB), TB, 0, st>>>(A.nx, A.ny, A.bu, A.bv, x, b, C.b);
+        k_resid_restrict<T><<<nblk(C.nx * C.ny, TB), TB, 0, st>>>(A.nx, A.ny, A.bu, A.bv, x, b, C.b, bs, xs);
     }
     for (int l = P->nlev - 2; l >= 0; --l) {
         Level<T> &A = L[l];
         const T *b = l == 0 ? b0 : A.b;
         T *x = l == 0 ? x0 : A.x;
+        const int *bs = l == 0 ? bsel : nullptr, *xs = l == 0 ? xsel : nullptr;
         const double n = (double)A.nx * A.ny, nf = (double)(A.nx + 1) * A.ny + (double)A.nx * (A.ny + 1);
         int nh = (A.nx >> 1) * A.ny;
         {
             WEC_PROF("mg_prolong", l, 2.25 * n * ts, st);
-            k_prolong<T><<<nblk(A.nx * A.ny, TB), TB, 0, st>>>(A.nx, A.ny, x, L[l + 1].x);
+            k_prolong<T><<<nblk(A.nx * A.ny, TB), TB, 0, st>>>(A.nx, A.ny, x, L[l + 1].x, xs);
         }
-        for (int s = 0; s < P->nu2; ++s) {
+        for (int q = 0; q < P->nu2; ++q) {
             {
                 WEC_PROF("mg_rbgs", l, (1.5 * n + nf) * ts, st);
-                k_rbgs<T><<<nblk(nh, TB), TB, 0, st>>>(A.nx, A.ny, A.bu, A.bv, x, b, 0, 0);
+                k_rbgs<T><<<nblk(nh, TB), TB, 0, st>>>(A.nx, A.ny, A.bu, A.bv, x, b, 0, 0, bs, xs);
             }
             {
                 WEC_PROF("mg_rbgs", l, (1.5 * n + nf) * ts, st);
-                k_rbgs<T><<<nblk(nh, TB), TB, 0, st>>>(A.nx, A.ny, A.bu, A.bv, x, b, 1, 0);
+                k_rbgs<T><<<nblk(nh, TB), TB, 0, st>>>(A.nx, A.ny, A.bu, A.bv, x, b, 1, 0, bs, xs);
             }
         }
     }
 }
 
-// z = M^{-1} v for the FGMRES basis vector v (FP64); z in the object's precision.
-void precond(wec_poisson *P, const double *v, void *z)
+// Fused V-cycle: per fine level one pre and one post kernel, one CTA for the
+// levels of at most kBottomCells cells.
+template <typename T>
+void vcycle_fused(wec_poisson *P, Level<T> *L, const T *b0, T *x0, const int *bsel, const int *xsel,
+                  cudaStream_t st)
 {
-    int n = P->nx * P->ny;
+    const double ts = sizeof(T);
+    const int H = 2 * std::max(P->nu1, P->nu2);
+    const size_t smem = tile_smem<T>(H);
+    int lb = 0;
+    while (lb < P->nlev - 1 && (long long)L[lb].nx * L[lb].ny > kBottomCells) ++lb;
+    for (int l = 0; l < lb; ++l) {
+        Level<T> &A = L[l];
+        const double n = (double)A.nx * A.ny, nf = (double)(A.nx + 1) * A.ny + (double)A.nx * (A.ny + 1);
+        dim3 grid((A.nx + kTX - 1) / kTX, (A.ny + kTY - 1) / kTY);
+        WEC_PROF("mg_pre", l, (2.25 * n + nf) * ts, st);
+        k_mg_pre<T><<<grid, 256, smem, st>>>(A.nx, A.ny, A.bu, A.bv, l == 0 ? b0 : A.b, l == 0 ? x0 : A.x,
+                                             L[l + 1].b, P->nu1, H, l == 0 ? bsel : nullptr,
+                                             l == 0 ? xsel : nullptr);
+    }
+    {
+        BottomLevels<T> B;
+        B.lb = lb;
+        B.nlev = P->nlev;
+        B.nu1 = P->nu1;
+        B.nu2 = P->nu2;
+        double bytes = 0.0;
+        for (int l = 0; l < P->nlev; ++l) {
+            B.nx[l] = L[l].nx;
+            B.ny[l] = L[l].ny;
+            B.bu[l] = L[l].bu;
+            B.bv[l] = L[l].bv;
+            B.x[l] = l == 0 ? x0 : L[l].x;
+            B.b[l] = l == 0 ? (T *)b0 : L[l].b;
+            if (l >= lb) {
+                const double n = (double)L[l].nx * L[l].ny, nf = (L[l].nx + 1.0) * L[l].ny + L[l].nx * (L[l].ny + 1.0);
+                bytes += (l == P->nlev - 1) ? (n * n + 2 * n) * ts : (2.25 * n + nf + 3.25 * n + nf) * ts;
+            }
+        }
+        if constexpr (sizeof(T) == 8) B.lu = (const T *)P->lu64; else B.lu = (const T *)P->lu32;
+        WEC_PROF("mg_bottom", lb, bytes, st);
+        k_mg_bottom<T><<<1, kBottomThreads, 0, st>>>(B, bsel, xsel);
+    }
+    for (int l = lb - 1; l >= 0; --l) {
+        Level<T> &A = L[l];
+        const double n = (double)A.nx * A.ny, nf = (double)(A.nx + 1) * A.ny + (double)A.nx * (A.ny + 1);
+        dim3 grid((A.nx + kTX - 1) / kTX, (A.ny + kTY - 1) / kTY);
+        WEC_PROF("mg_post", l, (3.25 * n + nf) * ts, st);
+        k_mg_post<T><<<grid, 256, smem, st>>>(A.nx, A.ny, A.bu, A.bv, l == 0 ? b0 : A.b, l == 0 ? x0 : A.x,
+                                              L[l + 1].x, P->nu2, H, l == 0 ? bsel : nullptr,
+                                              l == 0 ? xsel : nullptr);
+    }
+}
+
+template <typename T>
+void vcycle_t(wec_poisson *P, Level<T> *L, const T *b0, T *x0, const int *bsel, const int *xsel, cudaStream_t st)
+{
+    if (g_mg_fused)
+        vcycle_fused<T>(P, L, b0, x0, bsel, xsel, st);
+    else
+        vcycle_unfused<T>(P, L, b0, x0, bsel, xsel, st);
+}
+
+int kgrid(long long n) { return (int)std::min<long long>(nblk(n, KT), kKrylovBlocks); }
+
+// ---------------------------------------------------------- FGMRES parts ----
+void enqueue_begin(wec_poisson *P, const double *b, double *x, double rtol, int maxit, unsigned long long hw,
+                   int use, cudaStream_t st)
+{
+    const long long n = (long long)P->nx * P->ny;
+    const double nf = (P->nx + 1.0) * P->ny + P->nx * (P->ny + 1.0);
+    const int G = kgrid(n);
+    {
+        WEC_PROF("scalar", -1, 64.0, st);
+        k_ks_init<<<1, 1, 0, st>>>(P->ks, rtol, maxit, P->restart);
+    }
+    {
+        WEC_PROF("krylov_norm", -1, 8.0 * n, st);
+        k_bnorm<<<G, KT, 0, st>>>(n, b, P->part, P->ks);
+    }
+    {
+        WEC_PROF("krylov_residual", -1, 8.0 * (3.0 * n + nf), st);
+        k_residual_norm<<<G, KT, 0, st>>>(P->nx, P->ny, P->L64[0].bu, P->L64[0].bv, b, x, P->w, P->part, P->ks,
+                                          P->g, 0, hw, use);
+    }
+    WEC_PROF("krylov_scale", -1, 16.0 * n, st);
+    k_scale0<<<nblk(n, 256), 256, 0, st>>>(n, P->w, P->V, P->ks);
+}
+
+// One Arnoldi step j (preconditioner, matvec, CGS2, Givens, next basis vector).
+// Algorithmic bytes of the Krylov kernels are counted at the largest j (m - 1).
+void enqueue_body(wec_poisson *P, unsigned long long hif, int use, cudaStream_t st)
+{
+    const long long n = (long long)P->nx * P->ny;
+    const double nf = (P->nx + 1.0) * P->ny + P->nx * (P->ny + 1.0);
+    const int G = kgrid(n), m = P->restart;
+    const size_t zsz = P->prec == WEC_PREC_FP64 ? 8 : 4;
+    double *h1 = P->dots, *h2 = P->dots + (kMaxRestart + 2);
     if (P->prec == WEC_PREC_FP64) {
-        vcycle_t<double>(P, P->L64, v, (double *)z);
+        vcycle_t<double>(P, P->L64, P->V, (double *)P->Z, &P->ks->j, &P->ks->j, st);
     } else {
         {
-            WEC_PROF("convert", -1, 12.0 * n, P->st);
-            k_convert<float, double><<<nblk(n, 256), 256, 0, P->st>>>(n, v, P->L32[0].b);
+            WEC_PROF("convert", -1, 12.0 * n, st);
+            k_convert<float, double><<<nblk(n, 256), 256, 0, st>>>(n, P->V, P->L32[0].b, &P->ks->j);
         }
-        vcycle_t<float>(P, P->L32, P->L32[0].b, (float *)z);
+        vcycle_t<float>(P, P->L32, P->L32[0].b, (float *)P->Z, nullptr, &P->ks->j, st);
     }
-}
-
-int read_scal(wec_poisson *P, int count)
-{
-    WEC_CK(cudaMemcpyAsync(P->host, P->scal, sizeof(double) * count, cudaMemcpyDeviceToHost, P->st));
-    WEC_CK(cudaStreamSynchronize(P->st));
-    return WEC_OK;
-}
-
-void dots(wec_poisson *P, const double *V, int nvec, const double *w, double *out)
-{
-    int n = P->nx * P->ny;
-    dim3 grid(kRedBlocks, nvec);
     {
-        WEC_PROF("krylov_dots", -1, 8.0 * n * (nvec + 1), P->st);
-        k_dots_partial<<<grid, kRedThreads, 0, P->st>>>(n, V, w, P->part);
+        WEC_PROF("krylov_matvec_dots", -1, 8.0 * (n + nf) + (double)zsz * n + 8.0 * n * m, st);
+        if (P->prec == WEC_PREC_FP64)
+            k_matvec_dots<double><<<G, KT, 0, st>>>(P->nx, P->ny, P->L64[0].bu, P->L64[0].bv, (const double *)P->Z,
+                                                    P->V, P->w, P->part, h1, P->ks);
+        else
+            k_matvec_dots<float><<<G, KT, 0, st>>>(P->nx, P->ny, P->L64[0].bu, P->L64[0].bv, (const float *)P->Z,
+                                                   P->V, P->w, P->part, h1, P->ks);
     }
-    WEC_PROF("reduce_final", -1, 8.0 * nvec * (kRedBlocks + 1), P->st);
-    k_dots_final<<<nvec, kRedThreads, 0, P->st>>>(P->part, out);
+    {
+        WEC_PROF("krylov_orth_dots", -1, 8.0 * n * (m + 2), st);
+        k_orth_dots<<<G, KT, 0, st>>>(n, P->V, P->w, h1, P->part, h2, P->ks);
+    }
+    {
+        WEC_PROF("krylov_orth_norm", -1, 8.0 * n * (m + 2), st);
+        k_orth_norm<<<G, KT, 0, st>>>(n, P->V, P->w, h1, h2, P->part, P->ks, P->hess, P->cs, P->sn, P->g, hif, use);
+    }
+    WEC_PROF("krylov_next_basis", -1, 16.0 * n, st);
+    k_next_basis<<<G, KT, 0, st>>>(n, P->w, P->V, P->ks);
+}
+
+// End of a cycle: y from the triangular system, x += Z y, true residual, then
+// converge / stop / restart.
+void enqueue_close(wec_poisson *P, const double *b, double *x, unsigned long long hw, int use, cudaStream_t st)
+{
+    const long long n = (long long)P->nx * P->ny;
+    const double nf = (P->nx + 1.0) * P->ny + P->nx * (P->ny + 1.0);
+    const int G = kgrid(n), m = P->restart;
+    const size_t zsz = P->prec == WEC_PREC_FP64 ? 8 : 4;
+    {
+        WEC_PROF("scalar", -1, 8.0 * m * m, st);
+        k_backsolve<<<1, 1, 0, st>>>(m, P->hess, P->g, P->y, P->ks);
+    }
+    {
+        WEC_PROF("krylov_update_x", -1, 16.0 * n + (double)zsz * n * m, st);
+        if (P->prec == WEC_PREC_FP64)
+            k_update_x<double><<<nblk(n, 256), 256, 0, st>>>(n, P->y, (const double *)P->Z, x, P->ks);
+        else
+            k_update_x<float><<<nblk(n, 256), 256, 0, st>>>(n, P->y, (const float *)P->Z, x, P->ks);
+    }
+    {
+        WEC_PROF("krylov_residual", -1, 8.0 * (3.0 * n + nf), st);
+        k_residual_norm<<<G, KT, 0, st>>>(P->nx, P->ny, P->L64[0].bu, P->L64[0].bv, b, x, P->w, P->part, P->ks,
+                                          P->g, 1, hw, use);
+    }
+    WEC_PROF("krylov_scale", -1, 16.0 * n, st);
+    k_scale0<<<nblk(n, 256), 256, 0, st>>>(n, P->w, P->V, P->ks);
+}
+
+int read_state(wec_poisson *P, cudaStream_t st)
+{
+    WEC_CK(cudaMemcpyAsync(P->ksh, P->ks, sizeof(KState), cudaMemcpyDeviceToHost, st));
+    WEC_CK(cudaStreamSynchronize(st));
+    return WEC_OK;
 }
 
 }  // namespace
 
-void launch_norm2(const double *a, int n, double *part, double *out, cudaStream_t st)
-{
-    dim3 grid(kRedBlocks, 1);
-    {
-        WEC_PROF("krylov_dots", -1, 8.0 * n, st);
-        k_dots_partial<<<grid, kRedThreads, 0, st>>>(n, a, a, part);
-    }
-    {
-        WEC_PROF("reduce_final", -1, 8.0 * (kRedBlocks + 1), st);
-        k_dots_final<<<1, kRedThreads, 0, st>>>(part, out);
-    }
-    WEC_PROF("scalar", -1, 16.0, st);
-    k_sqrt<<<1, 1, 0, st>>>(out);
-}
+void set_mg_fused(bool on) { g_mg_fused = on; }
 
 int poisson_init(wec_poisson *P, int nx, int ny, int prec, int restart, int nu1, int nu2, cudaStream_t st)
 {
+    static bool attrs_done = false;
+    if (!attrs_done) {
+        // shared-memory tiles of the fused level kernels exceed the 48 KB default (H <= 8)
+        WEC_CK(cudaFuncSetAttribute(k_mg_pre<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem<double>(8)));
+        WEC_CK(cudaFuncSetAttribute(k_mg_post<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem<double>(8)));
+        WEC_CK(cudaFuncSetAttribute(k_mg_pre<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem<float>(8)));
+        WEC_CK(cudaFuncSetAttribute(k_mg_post<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem<float>(8)));
+        attrs_done = true;
+    }
     if (nx < 2 || ny < 2) return fail(WEC_ERR_INVALID, "poisson: nx, ny must be >= 2");
     if (restart < 1 || restart > kMaxRestart) return fail(WEC_ERR_INVALID, "poisson: restart must be in 1..32");
-    if (nu1 < 0 || nu2 < 0 || nu1 + nu2 == 0) return fail(WEC_ERR_INVALID, "poisson: need at least one smoothing sweep");
+    if (nu1 < 1 || nu2 < 0 || nu1 > 4 || nu2 > 4)
+        return fail(WEC_ERR_INVALID, "poisson: need 1 <= mg_pre <= 4 and 0 <= mg_post <= 4");
     if (prec != WEC_PREC_FP64 && prec != WEC_PREC_MIXED) return fail(WEC_ERR_INVALID, "poisson: unknown precision");
     P->nx = nx; P->ny = ny; P->prec = prec; P->restart = restart; P->nu1 = nu1; P->nu2 = nu2; P->st = st;
-    // levels: coarsen while both sizes are even and >= 4
     int lx = nx, ly = ny, nl = 0;
     for (;;) {
         P->L64[nl].nx = lx; P->L64[nl].ny = ly;
@@ -461,8 +814,8 @@ int poisson_init(wec_poisson *P, int nx, int ny, int prec, int restart, int nu1,
     WEC_CK(cudaMalloc(&P->V, (m + 1) * n * 8));
     WEC_CK(cudaMalloc(&P->Z, m * n * (prec == WEC_PREC_FP64 ? 8 : 4)));
     WEC_CK(cudaMalloc(&P->w, n * 8));
-    WEC_CK(cudaMalloc(&P->part, (size_t)(kMaxRestart + 1) * kRedBlocks * 8));
-    WEC_CK(cudaMalloc(&P->dots, 3 * (kMaxRestart + 2) * 8));
+    WEC_CK(cudaMalloc(&P->part, (size_t)(kMaxRestart + 2) * kKrylovBlocks * 8));
+    WEC_CK(cudaMalloc(&P->dots, 2 * (kMaxRestart + 2) * 8));
     size_t nh = (size_t)(m + 1) * m + 3 * (m + 1) + m + 8;
     WEC_CK(cudaMalloc(&P->hess, nh * 8));
     WEC_CK(cudaMemset(P->hess, 0, nh * 8));
@@ -470,8 +823,9 @@ int poisson_init(wec_poisson *P, int nx, int ny, int prec, int restart, int nu1,
     P->sn = P->cs + (m + 1);
     P->g = P->sn + (m + 1);
     P->y = P->g + (m + 1);
-    P->scal = P->y + m;
-    WEC_CK(cudaMallocHost(&P->host, 8 * 8));
+    WEC_CK(cudaMalloc(&P->ks, sizeof(KState)));
+    WEC_CK(cudaMemset(P->ks, 0, sizeof(KState)));
+    WEC_CK(cudaMallocHost(&P->ksh, sizeof(KState)));
     P->bytes += ((m + 1) * n + n) * 8 + m * n * (prec == WEC_PREC_FP64 ? 8 : 4);
     return WEC_OK;
 }
@@ -484,13 +838,13 @@ void poisson_free(wec_poisson *P)
     }
     cudaFree(P->lu64); cudaFree(P->lu32);
     cudaFree(P->V); cudaFree(P->Z); cudaFree(P->w); cudaFree(P->part); cudaFree(P->dots); cudaFree(P->hess);
-    if (P->host) cudaFreeHost(P->host);
+    cudaFree(P->ks);
+    if (P->ksh) cudaFreeHost(P->ksh);
     *P = wec_poisson();
 }
 
-int poisson_build(wec_poisson *P)
+int poisson_build(wec_poisson *P, cudaStream_t st)
 {
-    cudaStream_t st = P->st;
     for (int l = 0; l + 1 < P->nlev; ++l) {
         Level<double> &F = P->L64[l], &C = P->L64[l + 1];
         int cnt = (C.nx + 1) * C.ny + C.nx * (C.ny + 1);
@@ -508,10 +862,10 @@ int poisson_build(wec_poisson *P)
             long long nu = (long long)(P->L64[l].nx + 1) * P->L64[l].ny, nv = (long long)P->L64[l].nx * (P->L64[l].ny + 1);
             {
                 WEC_PROF("convert", l, 12.0 * nu, st);
-                k_convert<float, double><<<nblk(nu, 256), 256, 0, st>>>(nu, P->L64[l].bu, P->L32[l].bu);
+                k_convert<float, double><<<nblk(nu, 256), 256, 0, st>>>(nu, P->L64[l].bu, P->L32[l].bu, nullptr);
             }
             WEC_PROF("convert", l, 12.0 * nv, st);
-            k_convert<float, double><<<nblk(nv, 256), 256, 0, st>>>(nv, P->L64[l].bv, P->L32[l].bv);
+            k_convert<float, double><<<nblk(nv, 256), 256, 0, st>>>(nv, P->L64[l].bv, P->L32[l].bv, nullptr);
         }
         Level<float> &Lf = P->L32[P->nlev - 1];
         const double nn = (double)Lf.nx * Lf.ny;
@@ -535,120 +889,129 @@ int poisson_apply(wec_poisson *P, const double *x, double *y)
 int poisson_vcycle(wec_poisson *P, const double *b, double *x)
 {
     int n = P->nx * P->ny;
+    cudaStream_t st = P->st;
     if (P->prec == WEC_PREC_FP64) {
-        vcycle_t<double>(P, P->L64, b, x);
+        vcycle_t<double>(P, P->L64, b, x, nullptr, nullptr, st);
     } else {
         {
-            WEC_PROF("convert", -1, 12.0 * n, P->st);
-            k_convert<float, double><<<nblk(n, 256), 256, 0, P->st>>>(n, b, P->L32[0].b);
+            WEC_PROF("convert", -1, 12.0 * n, st);
+            k_convert<float, double><<<nblk(n, 256), 256, 0, st>>>(n, b, P->L32[0].b, nullptr);
         }
-        vcycle_t<float>(P, P->L32, P->L32[0].b, P->L32[0].x);
-        WEC_PROF("convert", -1, 12.0 * n, P->st);
-        k_convert<double, float><<<nblk(n, 256), 256, 0, P->st>>>(n, P->L32[0].x, x);
+        vcycle_t<float>(P, P->L32, P->L32[0].b, P->L32[0].x, nullptr, nullptr, st);
+        WEC_PROF("convert", -1, 12.0 * n, st);
+        k_convert<double, float><<<nblk(n, 256), 256, 0, st>>>(n, P->L32[0].x, x, nullptr);
     }
     WEC_CK(cudaGetLastError());
     return WEC_OK;
 }
 
+// Host-polled solve: one state read per Arnoldi step.
 int poisson_solve(wec_poisson *P, const double *b, double *x, double rtol, int maxit, int *iters, double *relres)
 {
     cudaStream_t st = P->st;
-    const int n = P->nx * P->ny, m = P->restart, TB = 256;
-    const size_t zsz = P->prec == WEC_PREC_FP64 ? 8 : 4;
-    double *bn_d = P->scal + 0, *beta_d = P->scal + 1;
-    const double *bu = P->L64[0].bu, *bv = P->L64[0].bv;
-    if (iters) *iters = 0;
-    if (relres) *relres = 0.0;
-    launch_norm2(b, n, P->part, bn_d, st);
-    if (int e = read_scal(P, 1)) return e;
-    double bn = P->host[0];
-    if (!std::isfinite(bn)) return fail(WEC_ERR_NONFINITE, "pressure solve: right-hand side is not finite");
-    if (bn == 0.0) {
-        WEC_CK(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
-        return WEC_OK;
-    }
-    double tol = rtol * bn;
-    const double nf = (P->nx + 1.0) * P->ny + P->nx * (P->ny + 1.0);
-    {
-        WEC_PROF("krylov_residual", -1, 8.0 * (3.0 * n + nf), st);
-        k_residual<<<nblk(n, TB), TB, 0, st>>>(P->nx, P->ny, bu, bv, x, b, P->w);
-    }
-    launch_norm2(P->w, n, P->part, beta_d, st);
-    if (int e = read_scal(P, 2)) return e;
-    double beta = P->host[1];
-    int its = 0;
-    bool conv = beta <= tol;
-    double *h1 = P->dots, *h2 = P->dots + (kMaxRestart + 2), *hn2 = P->dots + 2 * (kMaxRestart + 2);
-    while (!conv && its < maxit) {
-        {
-            WEC_PROF("krylov_scale", -1, 16.0 * n, st);
-            k_scale_div<<<nblk(n, TB), TB, 0, st>>>(n, P->w, beta_d, P->V);
-        }
-        {
-            WEC_PROF("scalar", -1, 8.0 * (m + 2), st);
-            k_cycle_init<<<1, 1, 0, st>>>(m, beta_d, P->g);
-        }
-        int jd = 0;
-        for (int j = 0; j < m; ++j) {
-            double *vj = P->V + (size_t)j * n;
-            void *zj = (char *)P->Z + (size_t)j * n * zsz;
-            precond(P, vj, zj);
-            {
-                WEC_PROF("krylov_matvec", -1, 8.0 * (n + nf) + (double)zsz * n, st);
-                if (P->prec == WEC_PREC_FP64)
-                    k_apply<double><<<nblk(n, TB), TB, 0, st>>>(P->nx, P->ny, bu, bv, (const double *)zj, P->w);
-                else
-                    k_apply<float><<<nblk(n, TB), TB, 0, st>>>(P->nx, P->ny, bu, bv, (const float *)zj, P->w);
-            }
-            its++;
-            dots(P, P->V, j + 1, P->w, h1);
-            {
-                WEC_PROF("krylov_axpy", -1, 8.0 * n * (j + 3), st);
-                k_axpy_multi<<<nblk(n, TB), TB, 0, st>>>(n, j + 1, P->V, h1, P->w);
-            }
-            dots(P, P->V, j + 1, P->w, h2);
-            {
-                WEC_PROF("krylov_axpy", -1, 8.0 * n * (j + 3), st);
-                k_axpy_multi<<<nblk(n, TB), TB, 0, st>>>(n, j + 1, P->V, h2, P->w);
-            }
-            dots(P, P->w, 1, P->w, hn2);
-            {
-                WEC_PROF("scalar", -1, 8.0 * (3 * (j + 2) + 4), st);
-                k_givens<<<1, 1, 0, st>>>(j, m, h1, h2, hn2, P->hess, P->cs, P->sn, P->g, P->scal);
-            }
-            if (int e = read_scal(P, 4)) return e;
-            double est = P->host[2], hn = P->host[3];
-            jd = j + 1;
-            if (!std::isfinite(est)) return fail(WEC_ERR_NONFINITE, "pressure solve: residual estimate is not finite");
-            if (est <= tol || its >= maxit || hn == 0.0) break;
-            WEC_PROF("krylov_scale", -1, 16.0 * n, st);
-            k_scale_div<<<nblk(n, TB), TB, 0, st>>>(n, P->w, P->scal + 3, P->V + (size_t)(j + 1) * n);
-        }
-        {
-            WEC_PROF("scalar", -1, 8.0 * (jd * jd + 2 * jd), st);
-            k_backsolve<<<1, 1, 0, st>>>(jd, m, P->hess, P->g, P->y);
-        }
-        {
-            WEC_PROF("krylov_update_x", -1, 16.0 * n + (double)zsz * n * jd, st);
-            if (P->prec == WEC_PREC_FP64)
-                k_update_x<double><<<nblk(n, TB), TB, 0, st>>>(n, jd, P->y, (const double *)P->Z, x);
-            else
-                k_update_x<float><<<nblk(n, TB), TB, 0, st>>>(n, jd, P->y, (const float *)P->Z, x);
-        }
-        {
-            WEC_PROF("krylov_residual", -1, 8.0 * (3.0 * n + nf), st);
-            k_residual<<<nblk(n, TB), TB, 0, st>>>(P->nx, P->ny, bu, bv, x, b, P->w);
-        }
-        launch_norm2(P->w, n, P->part, beta_d, st);
-        if (int e = read_scal(P, 2)) return e;
-        beta = P->host[1];
-        if (!std::isfinite(beta)) return fail(WEC_ERR_NONFINITE, "pressure solve: residual is not finite");
-        conv = beta <= tol;
-    }
+    enqueue_begin(P, b, x, rtol, maxit, 0ull, 0, st);
     WEC_CK(cudaGetLastError());
-    if (iters) *iters = its;
-    if (relres) *relres = beta / bn;
-    if (!conv) return fail(WEC_ERR_NOT_CONVERGED, "pressure solve: not converged within max_iters");
+    if (int e = read_state(P, st)) return e;
+    while (!P->ksh->done) {
+        enqueue_body(P, 0ull, 0, st);
+        WEC_CK(cudaGetLastError());
+        if (int e = read_state(P, st)) return e;
+        if (P->ksh->cycle_end) {
+            enqueue_close(P, b, x, 0ull, 0, st);
+            WEC_CK(cudaGetLastError());
+            if (int e = read_state(P, st)) return e;
+        }
+    }
+    return solve_result(P, iters, relres);
+}
+
+int solve_result(wec_poisson *P, int *iters, double *relres)
+{
+    const KState &k = *P->ksh;
+    if (iters) *iters = k.its;
+    if (relres) *relres = k.bn > 0.0 ? k.beta / k.bn : 0.0;
+    if (k.status == WEC_ERR_NONFINITE) return fail(WEC_ERR_NONFINITE, "pressure solve: residual is not finite");
+    if (k.status == WEC_ERR_NOT_CONVERGED) return fail(WEC_ERR_NOT_CONVERGED, "pressure solve: not converged within max_iters");
+    return WEC_OK;
+}
+
+// Record the whole solve into the graph being captured on st: WHILE(not done)
+// { Arnoldi step; IF(cycle ends) { close cycle } }.  h1, h2: idle streams used to
+// capture the two conditional bodies.
+int poisson_capture_solve(wec_poisson *P, const double *b, double *x, double rtol, int maxit, cudaStream_t st,
+                          cudaStream_t h1, cudaStream_t h2)
+{
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    WEC_CK(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, nullptr, &nd));
+    if (cs != cudaStreamCaptureStatusActive) return fail(WEC_ERR_CUDA, "capture_solve: stream is not capturing");
+    cudaGraphConditionalHandle hw, hi;
+    WEC_CK(cudaGraphConditionalHandleCreate(&hw, g, 1, cudaGraphCondAssignDefault));
+    WEC_CK(cudaGraphConditionalHandleCreate(&hi, g, 0, cudaGraphCondAssignDefault));
+    enqueue_begin(P, b, x, rtol, maxit, (unsigned long long)hw, 1, st);
+    WEC_CK(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, nullptr, &nd));
+    cudaGraphNodeParams wp = {};
+    wp.type = cudaGraphNodeTypeConditional;
+    wp.conditional.handle = hw;
+    wp.conditional.type = cudaGraphCondTypeWhile;
+    wp.conditional.size = 1;
+    cudaGraphNode_t wnode;
+    WEC_CK(cudaGraphAddNode(&wnode, g, deps, nullptr, nd, &wp));
+    cudaGraph_t wbody = wp.conditional.phGraph_out[0];
+    WEC_CK(cudaStreamUpdateCaptureDependencies(st, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+
+    WEC_CK(cudaStreamBeginCaptureToGraph(h1, wbody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    enqueue_body(P, (unsigned long long)hi, 1, h1);
+    cudaGraph_t g1 = nullptr;
+    const cudaGraphNode_t *d1 = nullptr;
+    size_t n1 = 0;
+    WEC_CK(cudaStreamGetCaptureInfo(h1, &cs, nullptr, &g1, &d1, nullptr, &n1));
+    cudaGraphNodeParams ip = {};
+    ip.type = cudaGraphNodeTypeConditional;
+    ip.conditional.handle = hi;
+    ip.conditional.type = cudaGraphCondTypeIf;
+    ip.conditional.size = 1;
+    cudaGraphNode_t inode;
+    WEC_CK(cudaGraphAddNode(&inode, g1, d1, nullptr, n1, &ip));
+    cudaGraph_t ibody = ip.conditional.phGraph_out[0];
+    WEC_CK(cudaStreamUpdateCaptureDependencies(h1, &inode, nullptr, 1, cudaStreamSetCaptureDependencies));
+    WEC_CK(cudaStreamBeginCaptureToGraph(h2, ibody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    enqueue_close(P, b, x, (unsigned long long)hw, 1, h2);
+    cudaGraph_t tmp;
+    WEC_CK(cudaStreamEndCapture(h2, &tmp));
+    WEC_CK(cudaStreamEndCapture(h1, &tmp));
+    WEC_CK(cudaGetLastError());
+    return WEC_OK;
+}
+
+// Kernels enqueued by the solve's opening, by one Arnoldi step and by one cycle
+// close (counted on a throwaway capture of the same enqueue code).
+int poisson_count_kernels(wec_poisson *P, cudaStream_t s, int *n_begin, int *n_body, int *n_close)
+{
+    cudaGraph_t tmp = nullptr;
+    WEC_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    prof::begin_capture();
+    enqueue_begin(P, P->w, P->w, 1.0, 1, 0ull, 0, s);
+    long long a = prof::captured();
+    enqueue_body(P, 0ull, 0, s);
+    long long b = prof::captured();
+    enqueue_close(P, P->w, P->w, 0ull, 0, s);
+    long long c = prof::captured();
+    prof::end_capture();
+    WEC_CK(cudaStreamEndCapture(s, &tmp));
+    if (tmp) cudaGraphDestroy(tmp);
+    *n_begin = (int)a;
+    *n_body = (int)(b - a);
+    *n_close = (int)(c - b);
+    return WEC_OK;
+}
+
+// After a captured solve ran: state -> host (enqueued on st; caller synchronises).
+int poisson_state_to_host(wec_poisson *P, cudaStream_t st)
+{
+    WEC_CK(cudaMemcpyAsync(P->ksh, P->ks, sizeof(KState), cudaMemcpyDeviceToHost, st));
     return WEC_OK;
 }
 

@@ -194,10 +194,11 @@ __device__ __forceinline__ double upwind(double q0, double q1, double q2, double
 }
 
 // ------------------------------------------------------------- kernels ----
-__global__ void k_bc(TankP P, const StepScalars *S, double dt, Bc bc)
+__global__ void k_bc(TankP P, const StepScalars *S, const double *__restrict__ inp, Bc bc)
 {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j > P.ny) return;
+    const double dt = inp[0];
     double t0 = S->t, t1 = S->t + dt, uu, vv;
     if (j < P.ny) {
         airy_uv(P, 0.0, (j + 0.5) * P.h, t1, &uu, &vv);
@@ -294,8 +295,9 @@ __global__ void k_force_partial(TankP P, const StepScalars *S, const double *__r
 
 // Sum of the force partials (fixed order), then the stabilised heave update:
 // (m + m_a)(zdot^{n+1} - zdot^n) = dt (F - m g + F_PTO) + m_a (zdot^n - zdot^{n-1}).
-__global__ void k_heave(TankP P, StepScalars *S, const double *__restrict__ part, double dt, double fpto_in)
+__global__ void k_heave(TankP P, StepScalars *S, const double *__restrict__ part, const double *__restrict__ inp)
 {
+    const double dt = inp[0], fpto_in = inp[1];
     __shared__ double sh[TB];
     double s = 0.0;
     for (int b = threadIdx.x; b < kRedBlocks; b += blockDim.x) s += part[b];
@@ -316,11 +318,12 @@ __global__ void k_heave(TankP P, StepScalars *S, const double *__restrict__ part
 
 // sigma* = sigma^n - dt Q(u^n, sigma^n), then damping-zone relaxation.
 __global__ void k_advect(TankP P, const double *__restrict__ s, const double *__restrict__ u,
-                         const double *__restrict__ v, const double *__restrict__ eta0, double dt,
-                         double *__restrict__ out)
+                         const double *__restrict__ v, const double *__restrict__ eta0,
+                         const double *__restrict__ inp, double *__restrict__ out)
 {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= P.nx * P.ny) return;
+    const double dt = inp[0];
     const int nx = P.nx, i = c % nx, j = c / nx;
     const double h = P.h;
     double a[6], fx[2], fy[2];
@@ -510,7 +513,7 @@ __device__ __forceinline__ double visc_diag_y(const TankP &P, const Visc &X, int
 
 // Right-hand side R and diagonal D of the u-momentum system; also the first
 // Jacobi iterate (u^n with the Dirichlet faces at t^{n+1}).
-__global__ void k_mom_u(TankP P, const StepScalars *S, double dt, const double *__restrict__ rho_n,
+__global__ void k_mom_u(TankP P, const StepScalars *S, const double *__restrict__ inp, const double *__restrict__ rho_n,
                         const double *__restrict__ mu_n, const double *__restrict__ chi_1,
                         const double *__restrict__ u, const double *__restrict__ v, const double *__restrict__ p,
                         Bc bc, double *Ru, double *Du, double *rbu, double *ua)
@@ -518,6 +521,7 @@ __global__ void k_mom_u(TankP P, const StepScalars *S, double dt, const double *
     int f = blockIdx.x * blockDim.x + threadIdx.x;
     const int nx = P.nx;
     if (f >= (nx + 1) * P.ny) return;
+    const double dt = inp[0];
     int i = f % (nx + 1), j = f / (nx + 1);
     if (i == 0) {
         ua[f] = bc.uin1[j];
@@ -540,7 +544,7 @@ __global__ void k_mom_u(TankP P, const StepScalars *S, double dt, const double *
             (p[j * nx + i] - p[j * nx + i - 1]) / P.h;
 }
 
-__global__ void k_mom_v(TankP P, const StepScalars *S, double dt, const double *__restrict__ rho_n,
+__global__ void k_mom_v(TankP P, const StepScalars *S, const double *__restrict__ inp, const double *__restrict__ rho_n,
                         const double *__restrict__ mu_n, const double *__restrict__ chi_1,
                         const double *__restrict__ rf_1, const double *__restrict__ u,
                         const double *__restrict__ v, const double *__restrict__ p, Bc bc, double *Rv,
@@ -549,6 +553,7 @@ __global__ void k_mom_v(TankP P, const StepScalars *S, double dt, const double *
     int f = blockIdx.x * blockDim.x + threadIdx.x;
     const int nx = P.nx, ny = P.ny;
     if (f >= nx * (ny + 1)) return;
+    const double dt = inp[0];
     int i = f % nx, j = f / nx;
     if (j == 0) {
         va[f] = 0.0;
@@ -661,9 +666,12 @@ __global__ void k_div_partial(TankP P, const double *__restrict__ u, const doubl
     if (threadIdx.x == 0) part[blockIdx.x] = acc;
 }
 
-// Close the step: divergence norm, probe elevation, advance time and body state.
+// Close the step: divergence norm, probe elevation, advance time and body state,
+// and account the kernels a graph replay executed (fixed part + per-iteration
+// and per-cycle parts of the solve).
 __global__ void k_finalize(TankP P, StepScalars *S, const double *__restrict__ part,
-                           const double *__restrict__ sig, double dt)
+                           const double *__restrict__ sig, const double *__restrict__ inp, const KState *ks,
+                           int n_fixed, int n_body, int n_close)
 {
     __shared__ double sh[TB];
     double s = 0.0;
@@ -681,10 +689,11 @@ __global__ void k_finalize(TankP P, StepScalars *S, const double *__restrict__ p
     }
     S->div2 = d2;
     S->eta = eta;
-    S->t = S->t + dt;
+    S->t = S->t + inp[0];
     S->yc = S->yc1;
     S->zdot_prev = S->zdot;
     S->zdot = S->zdot1;
+    S->launches = (long long)n_fixed + (long long)ks->its * n_body + (long long)ks->ncycles * n_close;
 }
 
 // Initial state: sigma = y - (d + eta(x, 0)); Airy velocities (u = 0 on the
@@ -734,9 +743,17 @@ int tank_alloc_and_init(wec_tank *T)
     T->nu = (size_t)(P.nx + 1) * P.ny;
     T->nv = (size_t)P.nx * (P.ny + 1);
     size_t nc = T->nc, nu = T->nu, nv = T->nv;
+    WEC_CK(cudaStreamCreateWithFlags(&T->gst, cudaStreamNonBlocking));
+    WEC_CK(cudaStreamCreateWithFlags(&T->h1, cudaStreamNonBlocking));
+    WEC_CK(cudaStreamCreateWithFlags(&T->h2, cudaStreamNonBlocking));
+    WEC_CK(cudaEventCreateWithFlags(&T->ev_in, cudaEventDisableTiming));
+    WEC_CK(cudaEventCreateWithFlags(&T->ev_out, cudaEventDisableTiming));
     double **cells[] = {&T->sig, &T->sa, &T->r0, &T->r1, &T->rt, &T->p, &T->phi, &T->rhs,
                         &T->rho_n, &T->mu_n, &T->mu_1, &T->rf_1, &T->chi_1};
-    for (double **q : cells) WEC_CK(cudaMalloc(q, nc * 8));
+    for (double **q : cells) {
+        WEC_CK(cudaMalloc(q, nc * 8));
+        WEC_CK(cudaMemset(*q, 0, nc * 8));
+    }
     double **ufaces[] = {&T->u, &T->us, &T->ua, &T->ub, &T->uc, &T->Ru, &T->Du, &T->rbu};
     for (double **q : ufaces) {
         WEC_CK(cudaMalloc(q, nu * 8));
@@ -747,7 +764,6 @@ int tank_alloc_and_init(wec_tank *T)
         WEC_CK(cudaMalloc(q, nv * 8));
         WEC_CK(cudaMemset(*q, 0, nv * 8));
     }
-    for (double **q : cells) WEC_CK(cudaMemset(*q, 0, nc * 8));
     size_t nbc = (size_t)P.ny + 2 * (P.ny + 1) + 6;
     WEC_CK(cudaMalloc(&T->bcbuf, nbc * 8));
     T->bc.uin1 = T->bcbuf;
@@ -756,47 +772,51 @@ int tank_alloc_and_init(wec_tank *T)
     T->bc.eta0 = T->bc.vin1 + P.ny + 1;
     T->bc.eta1 = T->bc.eta0 + 3;
     WEC_CK(cudaMalloc(&T->part, kRedBlocks * 8));
+    WEC_CK(cudaMalloc(&T->inp, 2 * 8));
+    WEC_CK(cudaMemset(T->inp, 0, 2 * 8));
     WEC_CK(cudaMalloc(&T->S, sizeof(StepScalars)));
     WEC_CK(cudaMallocHost(&T->Sh, sizeof(StepScalars)));
     *T->Sh = StepScalars{};
     if (int e = poisson_init(&T->solver, P.nx, P.ny, T->opts.precision, T->opts.restart, T->opts.mg_pre,
-                             T->opts.mg_post, T->st))
+                             T->opts.mg_post, T->gst))
         return e;
     long long ninit = (long long)nc + nu + nv;
-    WEC_PROF("init", -1, 8.0 * ninit, T->st);
-    k_init_fields<<<nblk(ninit, TB), TB, 0, T->st>>>(P, T->sig, T->u, T->v);
+    WEC_PROF("init", -1, 8.0 * ninit, T->gst);
+    k_init_fields<<<nblk(ninit, TB), TB, 0, T->gst>>>(P, T->sig, T->u, T->v);
     WEC_CK(cudaGetLastError());
     return WEC_OK;
 }
 
-// Called after the host sets Sh (initial yc): hydrostatic p from the initial sigma.
+// Called after the host filled Sh (initial body state): hydrostatic p from the initial sigma.
 int tank_init_pressure(wec_tank *T)
 {
-    WEC_CK(cudaMemcpyAsync(T->S, T->Sh, sizeof(StepScalars), cudaMemcpyHostToDevice, T->st));
+    WEC_CK(cudaMemcpyAsync(T->S, T->Sh, sizeof(StepScalars), cudaMemcpyHostToDevice, T->gst));
     const TankP &P = T->P;
     {
-        WEC_PROF("materials", -1, 16.0 * T->nc, T->st);
-        k_materials<<<nblk(T->nc, TB), TB, 0, T->st>>>(P, T->S, 0, T->sig, nullptr, nullptr, T->rf_1, nullptr);
+        WEC_PROF("materials", -1, 16.0 * T->nc, T->gst);
+        k_materials<<<nblk(T->nc, TB), TB, 0, T->gst>>>(P, T->S, 0, T->sig, nullptr, nullptr, T->rf_1, nullptr);
     }
     {
-        WEC_PROF("init", -1, 16.0 * T->nc, T->st);
-        k_init_pressure<<<nblk(P.nx, 128), 128, 0, T->st>>>(P, T->rf_1, T->p);
+        WEC_PROF("init", -1, 16.0 * T->nc, T->gst);
+        k_init_pressure<<<nblk(P.nx, 128), 128, 0, T->gst>>>(P, T->rf_1, T->p);
     }
     WEC_CK(cudaGetLastError());
-    WEC_CK(cudaStreamSynchronize(T->st));
+    WEC_CK(cudaStreamSynchronize(T->gst));
     return WEC_OK;
 }
 
-int tank_step(wec_tank *T, double dt, double fpto, wec_step_result *out)
+namespace {
+
+// Everything before the pressure solve: steps (1)-(7) of the step.
+void enqueue_front(wec_tank *T, cudaStream_t st)
 {
     const TankP &P = T->P;
-    cudaStream_t st = T->st;
     const long long nc = T->nc, nu = T->nu, nv = T->nv;
     const double fb = 8.0;  // FP64 bytes
     // (1) inflow / ghost data at t^n and t^{n+1}
     {
         WEC_PROF("bc", -1, fb * (3.0 * P.ny + 6), st);
-        k_bc<<<nblk(P.ny + 1, 128), 128, 0, st>>>(P, T->S, dt, T->bc);
+        k_bc<<<nblk(P.ny + 1, 128), 128, 0, st>>>(P, T->S, T->inp, T->bc);
     }
     // (2) materials at n, force from p^{n-1/2}, u^n (Eq. int_fh), heave (Eq. newton_u)
     {
@@ -809,18 +829,20 @@ int tank_step(wec_tank *T, double dt, double fpto, wec_step_result *out)
     }
     {
         WEC_PROF("scalar", -1, fb * kRedBlocks, st);
-        k_heave<<<1, TB, 0, st>>>(P, T->S, T->part, dt, fpto);
+        k_heave<<<1, TB, 0, st>>>(P, T->S, T->part, T->inp);
     }
-    // (3) sigma advection + damping-zone relaxation, then reinitialisation
+    // (3) sigma advection + damping-zone relaxation, then reinitialisation; the
+    // last pseudo-step writes sigma^{n+1} over sigma^n (no longer needed).
     {
         WEC_PROF("advect", -1, fb * (2.0 * nc + nu + nv), st);
-        k_advect<<<nblk(nc, TB), TB, 0, st>>>(P, T->sig, T->u, T->v, T->bc.eta0, dt, T->sa);
+        k_advect<<<nblk(nc, TB), TB, 0, st>>>(P, T->sig, T->u, T->v, T->bc.eta0, T->inp, T->sa);
     }
     const double dtau = 0.3 * P.h;
     const double *f = T->sa;
     double *bufs[2] = {T->r0, T->r1};
-    for (int it = 0; it < T->opts.n_reinit; ++it) {
-        double *dst = bufs[it & 1];
+    const int nr = T->opts.n_reinit;
+    for (int it = 0; it < nr; ++it) {
+        double *dst = it == nr - 1 ? T->sig : bufs[it & 1];
         {
             WEC_PROF("reinit", -1, fb * 3.0 * nc, st);
             k_reinit<<<nblk(nc, TB), TB, 0, st>>>(P, f, T->sa, nullptr, T->bc.eta1, dtau, T->rt);
@@ -831,22 +853,21 @@ int tank_step(wec_tank *T, double dt, double fpto, wec_step_result *out)
         }
         f = dst;
     }
-    if (T->opts.n_reinit == 0) WEC_CK(cudaMemcpyAsync(T->r0, T->sa, nc * 8, cudaMemcpyDeviceToDevice, st));
-    double *sig1 = T->opts.n_reinit == 0 ? T->r0 : (double *)f;
+    if (nr == 0) cudaMemcpyAsync(T->sig, T->sa, nc * 8, cudaMemcpyDeviceToDevice, st);
     // (4) materials at n+1 (psi at the new body position)
     {
         WEC_PROF("materials", -1, fb * 4.0 * nc, st);
-        k_materials<<<nblk(nc, TB), TB, 0, st>>>(P, T->S, 1, sig1, nullptr, T->mu_1, T->rf_1, T->chi_1);
+        k_materials<<<nblk(nc, TB), TB, 0, st>>>(P, T->S, 1, T->sig, nullptr, T->mu_1, T->rf_1, T->chi_1);
     }
     // (5) momentum right-hand side and diagonal, (6) Crank-Nicolson Jacobi sweeps
     {
         WEC_PROF("mom_u", -1, fb * (4.0 * nc + nu + nv + 4.0 * nu), st);
-        k_mom_u<<<nblk(nu, TB), TB, 0, st>>>(P, T->S, dt, T->rho_n, T->mu_n, T->chi_1, T->u, T->v, T->p, T->bc,
-                                             T->Ru, T->Du, T->rbu, T->ua);
+        k_mom_u<<<nblk(nu, TB), TB, 0, st>>>(P, T->S, T->inp, T->rho_n, T->mu_n, T->chi_1, T->u, T->v, T->p,
+                                             T->bc, T->Ru, T->Du, T->rbu, T->ua);
     }
     {
         WEC_PROF("mom_v", -1, fb * (5.0 * nc + nu + nv + 4.0 * nv), st);
-        k_mom_v<<<nblk(nv, TB), TB, 0, st>>>(P, T->S, dt, T->rho_n, T->mu_n, T->chi_1, T->rf_1, T->u, T->v,
+        k_mom_v<<<nblk(nv, TB), TB, 0, st>>>(P, T->S, T->inp, T->rho_n, T->mu_n, T->chi_1, T->rf_1, T->u, T->v,
                                              T->p, T->bc, T->Rv, T->Dv, T->rbv, T->va);
     }
     const double *ju = T->ua, *jv = T->va;
@@ -862,21 +883,24 @@ int tank_step(wec_tank *T, double dt, double fpto, wec_step_result *out)
         ju = du;
         jv = dv;
     }
-    // (7) pressure increment: A phi = -h div u*, beta = 1/D
+    // (7) pressure increment: A phi = -h div u*, beta = 1/D; phi from zero
     wec_poisson *S = &T->solver;
     {
         WEC_PROF("proj_rhs", -1, fb * (nc + 3.0 * (nu + nv)), st);
         k_proj_rhs<<<nblk(nc + nu + nv, TB), TB, 0, st>>>(P, T->us, T->vs, T->Du, T->Dv, T->rhs, S->L64[0].bu,
                                                           S->L64[0].bv);
     }
-    WEC_CK(cudaGetLastError());
-    if (int e = poisson_build(S)) return e;
-    WEC_CK(cudaMemsetAsync(T->phi, 0, nc * 8, st));
-    int iters = 0;
-    double relres = 0.0;
-    int status = poisson_solve(S, T->rhs, T->phi, T->opts.rtol, T->opts.max_iters, &iters, &relres);
-    if (status != WEC_OK && status != WEC_ERR_NOT_CONVERGED) return status;
-    // (8) projection (Eq. c_discrete_continuity)
+    poisson_build(S, st);
+    cudaMemsetAsync(T->phi, 0, nc * 8, st);
+}
+
+// (8) projection and the close of the step.
+void enqueue_back(wec_tank *T, cudaStream_t st)
+{
+    const TankP &P = T->P;
+    const long long nc = T->nc, nu = T->nu, nv = T->nv;
+    const double fb = 8.0;
+    wec_poisson *S = &T->solver;
     {
         WEC_PROF("project", -1, fb * (3.0 * nc + 3.0 * (nu + nv)), st);
         k_project<<<nblk(nu + nv + nc, TB), TB, 0, st>>>(P, T->us, T->vs, S->L64[0].bu, S->L64[0].bv, T->phi,
@@ -886,21 +910,65 @@ int tank_step(wec_tank *T, double dt, double fpto, wec_step_result *out)
         WEC_PROF("divergence", -1, fb * (nu + nv), st);
         k_div_partial<<<kRedBlocks, TB, 0, st>>>(P, T->u, T->v, T->part);
     }
+    WEC_PROF("scalar", -1, fb * (kRedBlocks + P.ny), st);
+    k_finalize<<<1, TB, 0, st>>>(P, T->S, T->part, T->sig, T->inp, S->ks, T->n_fixed, T->n_body, T->n_close);
+}
+
+int build_graph(wec_tank *T)
+{
+    wec_poisson *S = &T->solver;
+    S->st = T->gst;
+    // kernels per replay: front + the solve's opening + back once, then the
+    // Arnoldi-step kernels per iteration and the cycle-closing kernels per cycle
     {
-        WEC_PROF("scalar", -1, fb * (kRedBlocks + P.ny), st);
-        k_finalize<<<1, TB, 0, st>>>(P, T->S, T->part, sig1, dt);
+        cudaGraph_t tmp = nullptr;
+        WEC_CK(cudaStreamBeginCapture(T->h1, cudaStreamCaptureModeThreadLocal));
+        prof::begin_capture();
+        enqueue_front(T, T->h1);
+        enqueue_back(T, T->h1);
+        long long nfb = prof::captured();
+        prof::end_capture();
+        WEC_CK(cudaStreamEndCapture(T->h1, &tmp));
+        if (tmp) cudaGraphDestroy(tmp);
+        int nbeg = 0, nb = 0, ncl = 0;
+        if (int e = poisson_count_kernels(S, T->h1, &nbeg, &nb, &ncl)) return e;
+        T->n_fixed = (int)nfb + nbeg;
+        T->n_body = nb;
+        T->n_close = ncl;
     }
-    WEC_CK(cudaGetLastError());
-    // sigma^{n+1} becomes the state; the old buffer joins the scratch set
-    if (sig1 == T->r0) std::swap(T->sig, T->r0);
-    else std::swap(T->sig, T->r1);
+    WEC_CK(cudaStreamBeginCapture(T->gst, cudaStreamCaptureModeThreadLocal));
+    prof::begin_capture();
+    enqueue_front(T, T->gst);
+    int e = poisson_capture_solve(S, T->rhs, T->phi, T->opts.rtol, T->opts.max_iters, T->gst, T->h1, T->h2);
+    enqueue_back(T, T->gst);
+    cudaMemcpyAsync(T->Sh, T->S, sizeof(StepScalars), cudaMemcpyDeviceToHost, T->gst);
+    poisson_state_to_host(S, T->gst);
+    prof::end_capture();
+    cudaGraph_t g = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(T->gst, &g);
+    if (e) {
+        if (g) cudaGraphDestroy(g);
+        return e;
+    }
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture (step graph)");
+    T->graph = g;
+    WEC_CK(cudaGraphInstantiate(&T->exec, g, 0));
+    return WEC_OK;
+}
+
+int finish_step(wec_tank *T, int status, wec_step_result *out)
+{
+    const StepScalars &s = *T->Sh;
+    int iters = 0;
+    double relres = 0.0;
+    int st = solve_result(&T->solver, &iters, &relres);
+    if (status == WEC_OK) status = st;
     T->stepped = true;
     T->last_iters = iters;
     T->last_relres = relres;
+    if (status == WEC_OK && !(std::isfinite(s.zdot) && std::isfinite(s.F) && std::isfinite(relres)))
+        status = fail(WEC_ERR_NONFINITE, "step: non-finite body state or residual");
     if (out) {
-        WEC_CK(cudaMemcpyAsync(T->Sh, T->S, sizeof(StepScalars), cudaMemcpyDeviceToHost, st));
-        WEC_CK(cudaStreamSynchronize(st));
-        const StepScalars &s = *T->Sh;
         out->t = s.t;
         out->z = s.yc - s.yc0;
         out->zdot = s.zdot;
@@ -910,22 +978,65 @@ int tank_step(wec_tank *T, double dt, double fpto, wec_step_result *out)
         out->residual = relres;
         out->div_norm = sqrt(s.div2);
         out->iters = iters;
-        if (status == WEC_OK && !(std::isfinite(s.zdot) && std::isfinite(s.F) && std::isfinite(relres)))
-            status = fail(WEC_ERR_NONFINITE, "step: non-finite body state or residual");
         out->status = status;
     }
     return status;
 }
 
+}  // namespace
+
+int tank_step(wec_tank *T, double dt, double fpto, wec_step_result *out)
+{
+    cudaStream_t st = T->gst;
+    // order after the caller's stream, and the caller's stream after this step
+    WEC_CK(cudaEventRecord(T->ev_in, T->st));
+    WEC_CK(cudaStreamWaitEvent(st, T->ev_in, 0));
+    double in[2] = {dt, fpto};
+    WEC_CK(cudaMemcpyAsync(T->inp, in, sizeof(in), cudaMemcpyHostToDevice, st));  // pageable: staged before return
+    const bool graph = T->use_graph && !prof::enabled();
+    int status = WEC_OK;
+    if (graph) {
+        if (!T->exec)
+            if (int e = build_graph(T)) return e;
+        WEC_CK(cudaGraphLaunch(T->exec, st));
+        WEC_CK(cudaStreamSynchronize(st));
+        prof::add_launches(T->Sh->launches);
+    } else {
+        wec_poisson *S = &T->solver;
+        S->st = st;
+        enqueue_front(T, st);
+        WEC_CK(cudaGetLastError());
+        int iters = 0;
+        double relres = 0.0;
+        status = poisson_solve(S, T->rhs, T->phi, T->opts.rtol, T->opts.max_iters, &iters, &relres);
+        if (status != WEC_OK && status != WEC_ERR_NOT_CONVERGED) return status;
+        enqueue_back(T, st);
+        WEC_CK(cudaGetLastError());
+        WEC_CK(cudaMemcpyAsync(T->Sh, T->S, sizeof(StepScalars), cudaMemcpyDeviceToHost, st));
+        WEC_CK(cudaStreamSynchronize(st));
+        status = WEC_OK;
+    }
+    WEC_CK(cudaEventRecord(T->ev_out, st));
+    WEC_CK(cudaStreamWaitEvent(T->st, T->ev_out, 0));
+    return finish_step(T, status, out);
+}
+
 void tank_free(wec_tank *T)
 {
+    if (T->exec) cudaGraphExecDestroy(T->exec);
+    if (T->graph) cudaGraphDestroy(T->graph);
     double *all[] = {T->sig, T->sa, T->r0, T->r1, T->rt, T->p, T->phi, T->rhs, T->rho_n, T->mu_n, T->mu_1,
                      T->rf_1, T->chi_1, T->u, T->us, T->ua, T->ub, T->uc, T->Ru, T->Du, T->rbu, T->v, T->vs,
-                     T->va, T->vb, T->vc, T->Rv, T->Dv, T->rbv, T->bcbuf, T->part, T->waves};
+                     T->va, T->vb, T->vc, T->Rv, T->Dv, T->rbv, T->bcbuf, T->part, T->waves, T->inp};
     for (double *q : all) cudaFree(q);
     cudaFree(T->S);
     if (T->Sh) cudaFreeHost(T->Sh);
     poisson_free(&T->solver);
+    if (T->ev_in) cudaEventDestroy(T->ev_in);
+    if (T->ev_out) cudaEventDestroy(T->ev_out);
+    if (T->h1) cudaStreamDestroy(T->h1);
+    if (T->h2) cudaStreamDestroy(T->h2);
+    if (T->gst) cudaStreamDestroy(T->gst);
 }
 
 }  // namespace wec

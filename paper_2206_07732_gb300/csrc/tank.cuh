@@ -23,6 +23,7 @@ struct StepScalars {
     double yc1, zdot1;                   // body after the heave update
     double F, fpto;                      // force and PTO force of this step
     double div2, eta;                    // diagnostics of the finished step
+    long long launches;                  // kernels executed by the last graph replay
 };
 
 // Boundary data of one step: inflow at x = 0 and eta at the three ghost columns.
@@ -39,7 +40,15 @@ struct Bc {
 struct wec_tank {
     wec::TankP P{};
     wec_solver_opts opts{};
-    cudaStream_t st = nullptr;
+    cudaStream_t st = nullptr;        // caller's stream (ordering only)
+    cudaStream_t gst = nullptr;       // the tank's own stream: every kernel runs here
+    cudaStream_t h1 = nullptr, h2 = nullptr;  // capture helpers for the solver's conditional bodies
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool use_graph = true;
+    int n_fixed = 0, n_body = 0, n_close = 0;  // kernels per replay: fixed, per iteration, per cycle
+    double *inp = nullptr;            // device: dt, f_pto of the current step
     size_t nc = 0, nu = 0, nv = 0;
     double *sig = nullptr, *sa = nullptr, *r0 = nullptr, *r1 = nullptr, *rt = nullptr;
     double *u = nullptr, *v = nullptr, *us = nullptr, *vs = nullptr;

@@ -83,6 +83,12 @@ def load():
     L.wec_step.argtypes = [vp, C.c_double, C.c_double, C.POINTER(StepResult)]
     L.wec_step_n.argtypes = [vp, C.c_int, C.c_double, _dp, C.POINTER(StepResult)]
     L.wec_pressure_solve.argtypes = [vp, vp, vp, C.c_double, C.POINTER(C.c_int), _dp]
+    L.wec_tank_use_graph.argtypes = [vp, C.c_int]
+    L.wec_set_option.argtypes = [C.c_char_p, C.c_int]
+    L.wec_launch_count.restype = C.c_longlong
+    L.wec_profile_enable.argtypes = [C.c_int, C.c_char_p]
+    L.wec_profile_read.argtypes = [C.c_int, C.c_char_p, C.c_size_t, C.POINTER(C.c_int), C.POINTER(C.c_longlong),
+                                   C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int)]
     L.wec_get_field.argtypes = [vp, C.c_int, _dp, C.c_size_t]
     L.wec_set_field.argtypes = [vp, C.c_int, _dp, C.c_size_t]
     L.wec_get_state.argtypes = [vp, _dp]
@@ -199,6 +205,9 @@ class Tank:
 
     __del__ = close
 
+    def use_graph(self, enable=True):
+        _check(load().wec_tank_use_graph(self.h, 1 if enable else 0))
+
     def shape(self, f):
         f = FIELD_NAMES.get(f, f)
         if f in (F_U, F_USTAR, F_BETA_U):
@@ -256,6 +265,35 @@ class Tank:
     def load_state(self, data):
         buf = C.create_string_buffer(data, len(data))
         _check(load().wec_load(self.h, buf, len(data)))
+
+
+def set_option(name, value):
+    _check(load().wec_set_option(name.encode(), int(value)))
+
+
+def launch_count():
+    return load().wec_launch_count()
+
+
+def profile_enable(mode, only=None):
+    _check(load().wec_profile_enable(mode, only.encode() if only else None))
+
+
+def profile_read():
+    """Aggregated per-(kernel, level) timings since the last read."""
+    mx, stride = 256, 64
+    names = C.create_string_buffer(mx * stride)
+    lv = (C.c_int * mx)()
+    la = (C.c_longlong * mx)()
+    ms = (C.c_double * mx)()
+    by = (C.c_double * mx)()
+    cnt = C.c_int(0)
+    _check(load().wec_profile_read(mx, names, stride, lv, la, ms, by, C.byref(cnt)))
+    out = []
+    for k in range(min(cnt.value, mx)):
+        nm = names.raw[k * stride:(k + 1) * stride].split(b"\0")[0].decode()
+        out.append(dict(name=nm, level=lv[k], launches=la[k], ms=ms[k], bytes=by[k]))
+    return out
 
 
 class Poisson:
