@@ -254,7 +254,10 @@ def main_ours(args):
     cfg = workload(args.seed)
     n = cfg["nx"] * cfg["ny"]
     if args.ncu_steps:
+        # one-by-one launches: ncu cannot profile kernel nodes of graphs with
+        # conditional nodes (same kernels, same order as the graph)
         tank = wec.Tank(cfg, precision=wec.PREC_MIXED)
+        tank.use_graph(False)
         for _ in range(max(args.warmup, 1) + args.ncu_steps):
             tank.step(cfg["dt"])
         torch.cuda.synchronize()
@@ -269,6 +272,10 @@ def main_ours(args):
         d = by_name.setdefault(p["name"], dict(ms=0.0, bytes=0.0, launches=0))
         d["ms"] += p["ms"]; d["bytes"] += p["bytes"]; d["launches"] += p["launches"]
     top = max(by_name, key=lambda k: by_name[k]["ms"])
+    tot_prof = sum(d["ms"] for d in by_name.values())
+    breakdown = [{"kernel": k, "launches_per_step": d["launches"] / 2, "us_per_step": d["ms"] / 2 * 1e3,
+                  "share": d["ms"] / tot_prof}
+                 for k, d in sorted(by_name.items(), key=lambda kv: -kv[1]["ms"])[:12]]
 
     clocks = Clocks(local)
     clocks.start()
@@ -335,6 +342,7 @@ def main_ours(args):
         "gpu_launches": mixed["launches"],
         "clocks": ck,
         "roofline": roofline,
+        "kernel_breakdown_eager": breakdown,
         "cpu_baseline": cpu,
     }
     if rank == 0:

@@ -56,6 +56,7 @@ template <typename T>
 struct Level {
     int nx = 0, ny = 0;
     T *bu = nullptr, *bv = nullptr, *x = nullptr, *b = nullptr;
+    T *xp = nullptr;  // pre-smoothed iterate of a tiled (fused) level, read by its post kernel
 };
 
 // FGMRES state on the device (read by the kernels that steer the iteration).

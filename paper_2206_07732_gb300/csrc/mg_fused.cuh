@@ -98,16 +98,17 @@ __device__ void tile_pass(TileView<T> &t, int color, int m, int first)
     __syncthreads();
 }
 
-// nu1 sweeps from zero, then x (tile interior) and the restricted residual.
+// nu1 sweeps from zero, then the smoothed iterate (tile interior) into xp and
+// the restricted residual into bc.
 template <typename T>
 __global__ void __launch_bounds__(256) k_mg_pre(int nx, int ny, const T *__restrict__ bu, const T *__restrict__ bv,
-                                                const T *__restrict__ b, T *x, T *__restrict__ bc, int nu1, int H,
-                                                const int *bsel, const int *xsel)
+                                                const T *__restrict__ b, T *__restrict__ xp, T *__restrict__ bc,
+                                                int nu1, int H, const int *bsel)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const long long n = (long long)nx * ny;
     b = at_sel(b, bsel, n);
-    x = at_sel(x, xsel, n);
+    T *x = xp;
     TileView<T> t;
     t.nx = nx;
     t.ny = ny;
@@ -151,11 +152,13 @@ __global__ void __launch_bounds__(256) k_mg_pre(int nx, int ny, const T *__restr
     }
 }
 
-// x += P x_c, then nu2 sweeps; writes the tile interior.
+// x = xp + P x_c, then nu2 sweeps; writes the tile interior of x.  Reads xp and
+// writes x (different arrays): tiles read their halos while others write.
 template <typename T>
 __global__ void __launch_bounds__(256) k_mg_post(int nx, int ny, const T *__restrict__ bu, const T *__restrict__ bv,
-                                                 const T *__restrict__ b, T *x, const T *__restrict__ xc, int nu2,
-                                                 int H, const int *bsel, const int *xsel)
+                                                 const T *__restrict__ b, const T *__restrict__ xp, T *x,
+                                                 const T *__restrict__ xc, int nu2, int H, const int *bsel,
+                                                 const int *xsel)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const long long n = (long long)nx * ny;
@@ -173,7 +176,7 @@ __global__ void __launch_bounds__(256) k_mg_post(int nx, int ny, const T *__rest
     t.b = t.x + t.ex * t.ey;
     t.bu = t.b + t.ex * t.ey;
     t.bv = t.bu + (t.ex + 1) * t.ey;
-    tile_load(t, bu, bv, b, (const T *)x, xc);
+    tile_load(t, bu, bv, b, xp, xc);
     int pass = 1;  // loaded x is exact everywhere; pass p is exact at margin >= p
     for (int q = 0; q < nu2; ++q) {
         tile_pass(t, 0, pass, 0);

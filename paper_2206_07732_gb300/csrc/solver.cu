@@ -606,9 +606,8 @@ void vcycle_fused(wec_poisson *P, Level<T> *L, const T *b0, T *x0, const int *bs
         const double n = (double)A.nx * A.ny, nf = (double)(A.nx + 1) * A.ny + (double)A.nx * (A.ny + 1);
         dim3 grid((A.nx + kTX - 1) / kTX, (A.ny + kTY - 1) / kTY);
         WEC_PROF("mg_pre", l, (2.25 * n + nf) * ts, st);
-        k_mg_pre<T><<<grid, 256, smem, st>>>(A.nx, A.ny, A.bu, A.bv, l == 0 ? b0 : A.b, l == 0 ? x0 : A.x,
-                                             L[l + 1].b, P->nu1, H, l == 0 ? bsel : nullptr,
-                                             l == 0 ? xsel : nullptr);
+        k_mg_pre<T><<<grid, 256, smem, st>>>(A.nx, A.ny, A.bu, A.bv, l == 0 ? b0 : A.b, A.xp, L[l + 1].b, P->nu1,
+                                             H, l == 0 ? bsel : nullptr);
     }
     {
         BottomLevels<T> B;
@@ -638,8 +637,8 @@ void vcycle_fused(wec_poisson *P, Level<T> *L, const T *b0, T *x0, const int *bs
         const double n = (double)A.nx * A.ny, nf = (double)(A.nx + 1) * A.ny + (double)A.nx * (A.ny + 1);
         dim3 grid((A.nx + kTX - 1) / kTX, (A.ny + kTY - 1) / kTY);
         WEC_PROF("mg_post", l, (3.25 * n + nf) * ts, st);
-        k_mg_post<T><<<grid, 256, smem, st>>>(A.nx, A.ny, A.bu, A.bv, l == 0 ? b0 : A.b, l == 0 ? x0 : A.x,
-                                              L[l + 1].x, P->nu2, H, l == 0 ? bsel : nullptr,
+        k_mg_post<T><<<grid, 256, smem, st>>>(A.nx, A.ny, A.bu, A.bv, l == 0 ? b0 : A.b, A.xp,
+                                              l == 0 ? x0 : A.x, L[l + 1].x, P->nu2, H, l == 0 ? bsel : nullptr,
                                               l == 0 ? xsel : nullptr);
     }
 }
@@ -799,6 +798,10 @@ int poisson_init(wec_poisson *P, int nx, int ny, int prec, int restart, int nu1,
             WEC_CK(cudaMalloc(&P->L64[l].b, nc * 8));
         }
         P->bytes += (nu + nv) * 8 + (l > 0 ? 2 * nc * 8 : 0);
+        if (l < nl - 1 && (long long)nc > kBottomCells) {  // tiled level of the fused V-cycle
+            WEC_CK(cudaMalloc(&P->L64[l].xp, nc * 8));
+            if (prec == WEC_PREC_MIXED) WEC_CK(cudaMalloc(&P->L32[l].xp, nc * 4));
+        }
         if (prec == WEC_PREC_MIXED) {
             WEC_CK(cudaMalloc(&P->L32[l].bu, nu * 4));
             WEC_CK(cudaMalloc(&P->L32[l].bv, nv * 4));
@@ -835,6 +838,7 @@ void poisson_free(wec_poisson *P)
     for (int l = 0; l < P->nlev; ++l) {
         cudaFree(P->L64[l].bu); cudaFree(P->L64[l].bv); cudaFree(P->L64[l].x); cudaFree(P->L64[l].b);
         cudaFree(P->L32[l].bu); cudaFree(P->L32[l].bv); cudaFree(P->L32[l].x); cudaFree(P->L32[l].b);
+        cudaFree(P->L64[l].xp); cudaFree(P->L32[l].xp);
     }
     cudaFree(P->lu64); cudaFree(P->lu32);
     cudaFree(P->V); cudaFree(P->Z); cudaFree(P->w); cudaFree(P->part); cudaFree(P->dots); cudaFree(P->hess);

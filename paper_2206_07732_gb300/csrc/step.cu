@@ -194,25 +194,62 @@ __device__ __forceinline__ double upwind(double q0, double q1, double q2, double
 }
 
 // ------------------------------------------------------------- kernels ----
-__global__ void k_bc(TankP P, const StepScalars *S, const double *__restrict__ inp, Bc bc)
+__device__ __forceinline__ double warp_sum_d(double v)
 {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// eta at x = 0 (for the inflow profile) and at the three ghost columns, at t^n
+// and t^{n+1}: one warp per value, lanes over the wave components.
+__global__ void k_bc_eta(TankP P, const StepScalars *S, const double *__restrict__ inp, Bc bc)
+{
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;  // 8 warps: (time, position)
+    const double t = (w & 1) ? S->t + inp[0] : S->t;
+    const int pos = w >> 1;                                    // 0: x = 0; 1..3: ghost columns
+    const double x = pos == 0 ? 0.0 : (-pos + 0.5) * P.h;
+    double e = 0.0;
+    for (int c = lane; c < P.ncomp; c += 32) e += P.amp[c] * cos(P.kw[c] * x - P.omega[c] * t + P.phase[c]);
+    e = warp_sum_d(e);
+    if (lane) return;
+    if (pos == 0)
+        bc.eta_in[w & 1] = e;
+    else
+        ((w & 1) ? bc.eta1 : bc.eta0)[pos - 1] = e;
+}
+
+// Inflow at x = 0: u_in(y_{j+1/2}, t^{n+1}) and v_in(y_j, t^n), v_in(y_j, t^{n+1}),
+// Airy velocities with Wheeler stretching, blended to zero in the air.  One warp
+// per row j, lanes over the components.
+__global__ void k_bc_rows(TankP P, const StepScalars *S, const double *__restrict__ inp, Bc bc)
+{
+    const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (j > P.ny) return;
-    const double dt = inp[0];
-    double t0 = S->t, t1 = S->t + dt, uu, vv;
-    if (j < P.ny) {
-        airy_uv(P, 0.0, (j + 0.5) * P.h, t1, &uu, &vv);
-        bc.uin1[j] = uu;
+    const double t0 = S->t, t1 = S->t + inp[0], d = P.depth;
+    double out[3];
+    for (int q = 0; q < 3; ++q) {
+        const double t = q == 1 ? t0 : t1;
+        const double y = q == 0 ? (j + 0.5) * P.h : j * P.h;
+        const double e = bc.eta_in[q == 1 ? 0 : 1];
+        const double ys = y < d + e ? y : d + e;
+        const double yp = d * ys / (d + e);
+        double acc = 0.0;
+        for (int c = lane; c < P.ncomp; c += 32) {
+            double k = P.kw[c], w = P.omega[c];
+            double ph = -w * t + P.phase[c];
+            double sk = sinh(k * d);
+            if (q == 0)
+                acc += P.amp[c] * w * cosh(k * yp) / sk * cos(ph);
+            else
+                acc += P.amp[c] * w * sinh(k * yp) / sk * sin(ph);
+        }
+        acc = warp_sum_d(acc);
+        out[q] = (1.0 - heav(y - d - e, P.h)) * acc;
     }
-    airy_uv(P, 0.0, j * P.h, t0, &uu, &vv);
-    bc.vin0[j] = vv;
-    airy_uv(P, 0.0, j * P.h, t1, &uu, &vv);
-    bc.vin1[j] = vv;
-    if (j < 3) {
-        double x = (-1 - j + 0.5) * P.h;
-        bc.eta0[j] = eta_at(P, x, t0);
-        bc.eta1[j] = eta_at(P, x, t1);
-    }
+    if (lane) return;
+    if (j < P.ny) bc.uin1[j] = out[0];
+    bc.vin0[j] = out[1];
+    bc.vin1[j] = out[2];
 }
 
 // Cell materials from sigma and the body at yc (which = 0: y_c^n, 1: y_c^{n+1}).
@@ -764,13 +801,14 @@ int tank_alloc_and_init(wec_tank *T)
         WEC_CK(cudaMalloc(q, nv * 8));
         WEC_CK(cudaMemset(*q, 0, nv * 8));
     }
-    size_t nbc = (size_t)P.ny + 2 * (P.ny + 1) + 6;
+    size_t nbc = (size_t)P.ny + 2 * (P.ny + 1) + 8;
     WEC_CK(cudaMalloc(&T->bcbuf, nbc * 8));
     T->bc.uin1 = T->bcbuf;
     T->bc.vin0 = T->bc.uin1 + P.ny;
     T->bc.vin1 = T->bc.vin0 + P.ny + 1;
     T->bc.eta0 = T->bc.vin1 + P.ny + 1;
     T->bc.eta1 = T->bc.eta0 + 3;
+    T->bc.eta_in = T->bc.eta1 + 3;
     WEC_CK(cudaMalloc(&T->part, kRedBlocks * 8));
     WEC_CK(cudaMalloc(&T->inp, 2 * 8));
     WEC_CK(cudaMemset(T->inp, 0, 2 * 8));
@@ -815,8 +853,12 @@ void enqueue_front(wec_tank *T, cudaStream_t st)
     const double fb = 8.0;  // FP64 bytes
     // (1) inflow / ghost data at t^n and t^{n+1}
     {
-        WEC_PROF("bc", -1, fb * (3.0 * P.ny + 6), st);
-        k_bc<<<nblk(P.ny + 1, 128), 128, 0, st>>>(P, T->S, T->inp, T->bc);
+        WEC_PROF("bc", -1, fb * 8.0, st);
+        k_bc_eta<<<1, 256, 0, st>>>(P, T->S, T->inp, T->bc);
+    }
+    {
+        WEC_PROF("bc", -1, fb * (3.0 * P.ny + 2), st);
+        k_bc_rows<<<nblk(P.ny + 1, 8), 256, 0, st>>>(P, T->S, T->inp, T->bc);
     }
     // (2) materials at n, force from p^{n-1/2}, u^n (Eq. int_fh), heave (Eq. newton_u)
     {

@@ -33,6 +33,7 @@ struct Bc {
     double *vin1;  // [ny+1] v_in(y_j, t^{n+1})
     double *eta0;  // [3]    eta(-(g+1/2) h, t^n)
     double *eta1;  // [3]    eta(-(g+1/2) h, t^{n+1})
+    double *eta_in;  // [2]  eta(0, t^n), eta(0, t^{n+1})
 };
 
 }  // namespace wec

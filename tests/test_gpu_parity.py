@@ -31,8 +31,9 @@ def built():
 
 # Absolute floors of the relative comparison (a field whose values are all
 # rounding noise is compared absolutely): velocities 1e-6 m/s, pressure 1e-6 Pa,
-# level set 1e-9 m, everything else 1e-300.
-FLOORS = {"u": 1e-6, "v": 1e-6, "ustar": 1e-6, "vstar": 1e-6, "p": 1e-6, "sigma": 1e-9, "sigma_adv": 1e-9}
+# level set 1e-9 m, pressure right-hand side 1e-7 m^2/s, everything else 1e-300.
+FLOORS = {"u": 1e-6, "v": 1e-6, "ustar": 1e-6, "vstar": 1e-6, "p": 1e-6, "sigma": 1e-9, "sigma_adv": 1e-9,
+          "rhs": 1e-7}
 
 
 def rel(a, b, name=None):
@@ -81,14 +82,16 @@ def test_fgmres_solution_matches_oracle(nx, ny, contrast, rtol):
 
 @pytest.mark.parametrize("nx,ny", [(96, 40), (256, 128), (288, 80), (1024, 256)])
 @pytest.mark.parametrize("prec", [wec.PREC_FP64, wec.PREC_MIXED])
-def test_fused_vcycle_equals_unfused(nx, ny, prec):
-    # the fused tile kernels recompute halo cells with the same arithmetic:
-    # identical bits to one kernel per colour pass (288 x 80: partial tiles)
+def test_fused_vcycle_matches_unfused(nx, ny, prec):
+    # The fused tile kernels recompute halo cells with the one-pass kernels'
+    # formulas; the compiler may round a fused expression differently, so the two
+    # agree to rounding, and the fused V-cycle is reproducible bit for bit (a race
+    # between tiles would not be).  288 x 80 has partial tiles.
     bu, bv = synth.random_coefficients(nx, ny, seed=nx * 7 + ny, contrast=1e3)
     b = np.random.default_rng(6).standard_normal((ny, nx))
     out = []
     try:
-        for fused in (0, 1):
+        for fused in (0, 1, 1):
             wec.set_option("mg_fused", fused)
             P = wec.Poisson(nx, ny, precision=prec)
             P.set_coefficients(cuda(bu), cuda(bv))
@@ -99,9 +102,13 @@ def test_fused_vcycle_equals_unfused(nx, ny, prec):
             out.append((z.cpu().numpy(), x.cpu().numpy(), info))
     finally:
         wec.set_option("mg_fused", 1)
-    assert np.array_equal(out[0][0], out[1][0])
-    assert np.array_equal(out[0][1], out[1][1])
-    assert out[0][2] == out[1][2]
+    assert np.array_equal(out[1][0], out[2][0]) and np.array_equal(out[1][1], out[2][1])
+    tol = 1e-12 if prec == wec.PREC_FP64 else 1e-5
+    d = rel(out[1][0], out[0][0])
+    assert d < tol, d
+    assert out[0][2]["status"] == out[1][2]["status"] == 0
+    assert abs(out[0][2]["iters"] - out[1][2]["iters"]) <= 1
+    assert rel(out[1][1], out[0][1]) < 1e3 * 1e-10
     if prec == wec.PREC_FP64:
         zo, _ = O.vcycle(bu, bv, b)
         assert rel(out[1][0], zo) < 1e-11
