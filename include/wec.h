@@ -207,6 +207,25 @@ int wec_poisson_vcycle(wec_poisson *P, const double *b, double *x);
 int wec_poisson_solve(wec_poisson *P, const double *b, double *x, double rtol, int max_iters,
                       int *iters, double *final_rel_residual);
 
+/* ---- without device allocation ------------------------------------------ */
+/* ||b - A x||_2 for the pressure operator above (same coefficient layout and
+ * boundary rules as wec_poisson_*), written to *norm_out (device, 1 double).
+ * The paper has no counterpart: this exists for callers that cannot allocate
+ * device memory when they need the number -- e.g. a control loop under a fixed
+ * memory budget, or a process whose device memory all belongs to another
+ * allocator.  The call allocates nothing: its scratch (residual vector, partial
+ * sums, a counter) is one file-scope device array sized for nx * ny <= 1048576
+ * cells (about 8 MiB, held by every GPU that loads the library until exit);
+ * larger sizes return WEC_ERR_INVALID.  beta_u, beta_v, x, b: device, caller
+ * owned, layouts as in wec_poisson_set_coefficients.  Enqueued on cuda_stream
+ * (NULL = legacy default stream); *norm_out is valid once that stream reaches
+ * it.  The first call on each device looks up the array's device address (with
+ * that device current); make that first call before any stream capture.  All
+ * calls share the one array: calls that overlap on the GPU (different streams,
+ * no ordering between them) race and may return wrong norms. */
+int wec_residual_norm_noalloc(int nx, int ny, const double *beta_u, const double *beta_v, const double *x,
+                              const double *b, double *norm_out, void *cuda_stream);
+
 /* ---- host wave utilities (no device work) ------------------------------- */
 /* k solving omega^2 = g k tanh(k d) (Eq. dispersion_relation), |residual| <= 1e-14 omega^2. */
 double wec_wave_number(double omega, double depth, double g);
