@@ -126,6 +126,8 @@ int wec_tank_create(const wec_grid *grid, const wec_fluids *fl, const wec_waves 
         P.rho_s = fl->rho_w;
     }
     P.mu_s = fl->mu_w;
+    P.ih = 1.0 / h;
+    P.ikp = 1.0 / P.kappa_p;
     P.ncomp = wv->ncomp;
     int rc = WEC_OK;
     {

@@ -18,6 +18,7 @@ constexpr int kMaxCoarse = 512;      // cells on the coarsest multigrid level
 constexpr int kRedBlocks = 304;      // partial-sum blocks of the step's reductions (2 x 152 SMs)
 constexpr int kRedThreads = 256;
 constexpr int kKrylovBlocks = 1216;  // max blocks of the fused Krylov kernels (8 x 152 SMs)
+constexpr int kDotBlocks = 304;      // max blocks of the multi-dot Krylov kernels (2 x 152 SMs)
 
 void set_error(const std::string &msg);
 int fail(int code, const std::string &msg);

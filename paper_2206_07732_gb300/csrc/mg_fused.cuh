@@ -9,9 +9,9 @@
 //               (the first red pass from x = 0 reads no neighbour), so after
 //               2 nu1 passes the tile and one ring around it are exact, which is
 //               what the residual needs.  Halo cells are recomputed redundantly.
-//   k_mg_bottom one CTA for all levels of at most kBottomCells cells, down to
-//               the dense LU of the coarsest level and back up, with
-//               __syncthreads() between colour passes.
+//   k_mg_bottom one CTA for all levels of at most kBottomCells cells, staged in
+//               shared memory, down to the dense LU of the coarsest level and
+//               back up, with __syncthreads() between colour passes.
 //   k_mg_post   per fine level: prolongation + correction and nu2 sweeps, same
 //               tiling.
 // Every cell update is the same arithmetic, in the same order, as the one-pass
@@ -22,7 +22,8 @@ namespace wec {
 namespace {
 
 constexpr int kTX = 64, kTY = 16;       // tile of a fused level kernel (interior cells)
-constexpr int kBottomCells = 16384;     // levels up to this size run inside one CTA
+constexpr int kBottomCells = 4096;      // levels up to this size run inside one CTA (shared memory)
+constexpr int kBottomSmemMax = 200 * 1024;
 constexpr int kBottomThreads = 1024;
 
 template <typename T>
@@ -199,10 +200,19 @@ struct BottomLevels {
     const T *lu;
 };
 
-// One colour pass of level arrays in global memory by the whole CTA.
+// Shared-memory elements the bottom kernel stages for levels lb.. (x, b, bu, bv each).
 template <typename T>
-__device__ void glob_pass(int nx, int ny, const T *__restrict__ bu, const T *__restrict__ bv, T *x, const T *b,
-                          int color, int first)
+__host__ __device__ inline long long bottom_elems(const BottomLevels<T> &L, int lb)
+{
+    long long e = 0;
+    for (int l = lb; l < L.nlev; ++l)
+        e += 2LL * L.nx[l] * L.ny[l] + (long long)(L.nx[l] + 1) * L.ny[l] + (long long)L.nx[l] * (L.ny[l] + 1);
+    return e;
+}
+
+// One colour pass of a level held in shared memory by the whole CTA.
+template <typename T>
+__device__ void sm_pass(int nx, int ny, const T *bu, const T *bv, T *x, const T *b, int color, int first)
 {
     const int half = nx >> 1;
     for (int k = threadIdx.x; k < half * ny; k += blockDim.x) {
@@ -220,23 +230,51 @@ __device__ void glob_pass(int nx, int ny, const T *__restrict__ bu, const T *__r
     __syncthreads();
 }
 
-// Levels lb .. nlev-1 of the V-cycle in one CTA.
+// Levels lb .. nlev-1 of the V-cycle in one CTA, all staged in shared memory:
+// load b of level lb and every level's coefficients, smooth / restrict down to
+// the dense LU of the coarsest level, prolong / smooth back up, store x of level lb.
 template <typename T>
 __global__ void __launch_bounds__(kBottomThreads) k_mg_bottom(BottomLevels<T> L, const int *bsel,
                                                                const int *xsel)
 {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ long long off[kMaxLevels];
     const int lb = L.lb, last = L.nlev - 1;
+    if (threadIdx.x == 0) {
+        long long o = 0;
+        for (int l = lb; l < L.nlev; ++l) {
+            off[l] = o;
+            o += 2LL * L.nx[l] * L.ny[l] + (long long)(L.nx[l] + 1) * L.ny[l] + (long long)L.nx[l] * (L.ny[l] + 1);
+        }
+    }
+    __syncthreads();
+    T *sm = reinterpret_cast<T *>(smem_raw);
+    auto X = [&](int l) { return sm + off[l]; };
+    auto B = [&](int l) { return sm + off[l] + (long long)L.nx[l] * L.ny[l]; };
+    auto BU = [&](int l) { return sm + off[l] + 2LL * L.nx[l] * L.ny[l]; };
+    auto BV = [&](int l) { return sm + off[l] + 2LL * L.nx[l] * L.ny[l] + (long long)(L.nx[l] + 1) * L.ny[l]; };
+    for (int l = lb; l < L.nlev; ++l) {
+        const int nx = L.nx[l], ny = L.ny[l];
+        T *su = BU(l), *sv = BV(l);
+        for (int k = threadIdx.x; k < (nx + 1) * ny; k += blockDim.x) su[k] = L.bu[l][k];
+        for (int k = threadIdx.x; k < nx * (ny + 1); k += blockDim.x) sv[k] = L.bv[l][k];
+    }
+    {
+        const long long n = (long long)L.nx[lb] * L.ny[lb];
+        const T *bg = lb == 0 ? at_sel((const T *)L.b[lb], bsel, n) : L.b[lb];
+        T *sb = B(lb);
+        for (int k = threadIdx.x; k < n; k += blockDim.x) sb[k] = bg[k];
+    }
+    __syncthreads();
     for (int l = lb; l < last; ++l) {
         const int nx = L.nx[l], ny = L.ny[l];
-        const long long n = (long long)nx * ny;
-        T *x = l == 0 ? at_sel(L.x[l], xsel, n) : L.x[l];
-        const T *b = l == 0 ? at_sel((const T *)L.b[l], bsel, n) : L.b[l];
+        T *x = X(l), *b = B(l), *su = BU(l), *sv = BV(l);
         for (int q = 0; q < L.nu1; ++q) {
-            glob_pass(nx, ny, L.bu[l], L.bv[l], x, b, 0, q == 0);
-            glob_pass(nx, ny, L.bu[l], L.bv[l], x, b, 1, 0);
+            sm_pass(nx, ny, su, sv, x, b, 0, q == 0);
+            sm_pass(nx, ny, su, sv, x, b, 1, 0);
         }
         const int ncx = nx >> 1, ncy = ny >> 1;
-        T *bc = L.b[l + 1];
+        T *bc = B(l + 1);
         for (int k = threadIdx.x; k < ncx * ncy; k += blockDim.x) {
             int I = k % ncx, J = k / ncx;
             T r[4];
@@ -244,8 +282,8 @@ __global__ void __launch_bounds__(kBottomThreads) k_mg_bottom(BottomLevels<T> L,
             for (int dj = 0; dj < 2; ++dj)
                 for (int di = 0; di < 2; ++di) {
                     int i = 2 * I + di, j = 2 * J + dj, c = j * nx + i;
-                    T d = diag_at(L.bu[l], L.bv[l], nx, ny, i, j);
-                    T ax = d * x[c] - offsum_at(L.bu[l], L.bv[l], x, nx, ny, i, j);
+                    T d = diag_at(su, sv, nx, ny, i, j);
+                    T ax = d * x[c] - offsum_at(su, sv, x, nx, ny, i, j);
                     r[qq++] = b[c] - ax;
                 }
             bc[k] = ((r[0] + r[1]) + r[2]) + r[3];
@@ -254,8 +292,8 @@ __global__ void __launch_bounds__(kBottomThreads) k_mg_bottom(BottomLevels<T> L,
     }
     {
         const int n = L.nx[last] * L.ny[last];
-        T *x = last == 0 ? at_sel(L.x[last], xsel, n) : L.x[last];
-        const T *b = last == 0 ? at_sel((const T *)L.b[last], bsel, n) : L.b[last];
+        T *x = X(last);
+        const T *b = B(last);
         if (threadIdx.x < 32) {
             const int lane = threadIdx.x;
             for (int r = 0; r < n; ++r) {
@@ -277,19 +315,23 @@ __global__ void __launch_bounds__(kBottomThreads) k_mg_bottom(BottomLevels<T> L,
     }
     for (int l = last - 1; l >= lb; --l) {
         const int nx = L.nx[l], ny = L.ny[l];
-        const long long n = (long long)nx * ny;
-        T *x = l == 0 ? at_sel(L.x[l], xsel, n) : L.x[l];
-        const T *b = l == 0 ? at_sel((const T *)L.b[l], bsel, n) : L.b[l];
-        const T *xc = L.x[l + 1];
+        T *x = X(l), *b = B(l), *su = BU(l), *sv = BV(l);
+        const T *xc = X(l + 1);
         for (int k = threadIdx.x; k < nx * ny; k += blockDim.x) {
             int i = k % nx, j = k / nx;
             x[k] += xc[(j >> 1) * (nx >> 1) + (i >> 1)];
         }
         __syncthreads();
         for (int q = 0; q < L.nu2; ++q) {
-            glob_pass(nx, ny, L.bu[l], L.bv[l], x, b, 0, 0);
-            glob_pass(nx, ny, L.bu[l], L.bv[l], x, b, 1, 0);
+            sm_pass(nx, ny, su, sv, x, b, 0, 0);
+            sm_pass(nx, ny, su, sv, x, b, 1, 0);
         }
+    }
+    {
+        const long long n = (long long)L.nx[lb] * L.ny[lb];
+        T *xg = lb == 0 ? at_sel(L.x[lb], xsel, n) : L.x[lb];
+        const T *x = X(lb);
+        for (int k = threadIdx.x; k < n; k += blockDim.x) xg[k] = x[k];
     }
 }
 

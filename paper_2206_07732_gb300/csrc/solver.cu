@@ -378,6 +378,43 @@ __global__ void k_scale0(long long n, const double *__restrict__ w, double *__re
     if (c < n) V[c] = w[c] / ks->beta;
 }
 
+// All j+1 block partials of V_k . w (k <= j) at once: per-thread register
+// accumulators (KMAXV covers restart <= 32), warp shuffles, then one value per
+// (warp, k) combined in warp order.  part[k * G + block].
+constexpr int KMAXV = kMaxRestart + 1;
+
+__device__ __forceinline__ void block_partials(const double *acc, int nk, double *part, double (*sh)[KMAXV])
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < KMAXV; ++k) {
+        if (k < nk) {
+            double v = acc[k];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) sh[warp][k] = v;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < nk) {
+        double r = 0.0;
+        for (int w = 0; w < KT / 32; ++w) r += sh[w][threadIdx.x];
+        part[threadIdx.x * gridDim.x + blockIdx.x] = r;
+    }
+}
+
+// In the last block: out[k] = sum over blocks of part[k * G + b], one warp per k,
+// lanes over blocks in a fixed assignment, fixed shuffle tree.
+__device__ __forceinline__ void final_partials(const double *part, int nk, double *out)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, G = gridDim.x;
+    for (int k = warp; k < nk; k += KT / 32) {
+        double s = 0.0;
+        for (int b = lane; b < G; b += 32) s += __ldcg(part + k * G + b);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) out[k] = s;
+    }
+}
+
 // w = A z_j and the first Gram-Schmidt dot products h1_k = V_k . w (k <= j).
 template <typename TZ>
 __global__ void __launch_bounds__(KT) k_matvec_dots(int nx, int ny, const double *__restrict__ bu,
@@ -385,28 +422,25 @@ __global__ void __launch_bounds__(KT) k_matvec_dots(int nx, int ny, const double
                                                       const double *__restrict__ V, double *__restrict__ w,
                                                       double *part, double *h1, KState *ks)
 {
-    __shared__ double sh[KT / 32];
+    __shared__ double sh[KT / 32][KMAXV];
     const long long n = (long long)nx * ny;
-    const int j = ks->j, G = gridDim.x;
+    const int j = ks->j, nk = j + 1;
     const TZ *z = Z + (long long)j * n;
-    for (long long c = blockIdx.x * (long long)KT + threadIdx.x; c < n; c += (long long)G * KT) {
+    double acc[KMAXV];
+#pragma unroll
+    for (int k = 0; k < KMAXV; ++k) acc[k] = 0.0;
+    for (long long c = blockIdx.x * (long long)KT + threadIdx.x; c < n; c += (long long)gridDim.x * KT) {
         int i = (int)(c % nx), jj = (int)(c / nx);
         double d = diag_at(bu, bv, nx, ny, i, jj);
-        w[c] = d * double(z[c]) - offsum_at(bu, bv, z, nx, ny, i, jj);
+        double wc = d * double(z[c]) - offsum_at(bu, bv, z, nx, ny, i, jj);
+        w[c] = wc;
+#pragma unroll
+        for (int k = 0; k < KMAXV; ++k)
+            if (k < nk) acc[k] += V[(long long)k * n + c] * wc;
     }
-    for (int k = 0; k <= j; ++k) {
-        const double *vk = V + (long long)k * n;
-        double a = 0.0;
-        for (long long c = blockIdx.x * (long long)KT + threadIdx.x; c < n; c += (long long)G * KT)
-            a += vk[c] * w[c];
-        a = block_sum(a, sh);
-        if (threadIdx.x == 0) part[k * G + blockIdx.x] = a;
-    }
+    block_partials(acc, nk, part, sh);
     if (!last_block(&ks->cnt[2])) return;
-    for (int k = 0; k <= j; ++k) {
-        double t = final_sum(part + k * G, G, sh);
-        if (threadIdx.x == 0) h1[k] = t;
-    }
+    final_partials(part, nk, h1);
     if (threadIdx.x == 0) ks->cnt[2] = 0;
 }
 
@@ -415,26 +449,31 @@ __global__ void __launch_bounds__(KT) k_orth_dots(long long n, const double *__r
                                                     const double *__restrict__ h1, double *part, double *h2,
                                                     KState *ks)
 {
-    __shared__ double sh[KT / 32];
-    const int j = ks->j, G = gridDim.x;
-    for (long long c = blockIdx.x * (long long)KT + threadIdx.x; c < n; c += (long long)G * KT) {
+    __shared__ double sh[KT / 32][KMAXV];
+    __shared__ double hs[KMAXV];
+    const int j = ks->j, nk = j + 1;
+    if (threadIdx.x < nk) hs[threadIdx.x] = h1[threadIdx.x];
+    __syncthreads();
+    double acc[KMAXV];
+#pragma unroll
+    for (int k = 0; k < KMAXV; ++k) acc[k] = 0.0;
+    for (long long c = blockIdx.x * (long long)KT + threadIdx.x; c < n; c += (long long)gridDim.x * KT) {
+        double vr[KMAXV];
         double a = w[c];
-        for (int k = 0; k <= j; ++k) a -= h1[k] * V[(long long)k * n + c];
+#pragma unroll
+        for (int k = 0; k < KMAXV; ++k)
+            if (k < nk) {
+                vr[k] = V[(long long)k * n + c];
+                a -= hs[k] * vr[k];
+            }
         w[c] = a;
+#pragma unroll
+        for (int k = 0; k < KMAXV; ++k)
+            if (k < nk) acc[k] += vr[k] * a;
     }
-    for (int k = 0; k <= j; ++k) {
-        const double *vk = V + (long long)k * n;
-        double a = 0.0;
-        for (long long c = blockIdx.x * (long long)KT + threadIdx.x; c < n; c += (long long)G * KT)
-            a += vk[c] * w[c];
-        a = block_sum(a, sh);
-        if (threadIdx.x == 0) part[k * G + blockIdx.x] = a;
-    }
+    block_partials(acc, nk, part, sh);
     if (!last_block(&ks->cnt[2])) return;
-    for (int k = 0; k <= j; ++k) {
-        double t = final_sum(part + k * G, G, sh);
-        if (threadIdx.x == 0) h2[k] = t;
-    }
+    final_partials(part, nk, h2);
     if (threadIdx.x == 0) ks->cnt[2] = 0;
 }
 
@@ -599,8 +638,24 @@ void vcycle_fused(wec_poisson *P, Level<T> *L, const T *b0, T *x0, const int *bs
     const double ts = sizeof(T);
     const int H = 2 * std::max(P->nu1, P->nu2);
     const size_t smem = tile_smem<T>(H);
+    BottomLevels<T> B;
+    B.nlev = P->nlev;
+    B.nu1 = P->nu1;
+    B.nu2 = P->nu2;
+    for (int l = 0; l < P->nlev; ++l) {
+        B.nx[l] = L[l].nx;
+        B.ny[l] = L[l].ny;
+        B.bu[l] = L[l].bu;
+        B.bv[l] = L[l].bv;
+        B.x[l] = l == 0 ? x0 : L[l].x;
+        B.b[l] = l == 0 ? (T *)b0 : L[l].b;
+    }
+    // first level small enough, whose staging (with all coarser levels) fits in shared memory
     int lb = 0;
-    while (lb < P->nlev - 1 && (long long)L[lb].nx * L[lb].ny > kBottomCells) ++lb;
+    while (lb < P->nlev - 1 &&
+           ((long long)L[lb].nx * L[lb].ny > kBottomCells || bottom_elems(B, lb) * (long long)sizeof(T) > kBottomSmemMax))
+        ++lb;
+    B.lb = lb;
     for (int l = 0; l < lb; ++l) {
         Level<T> &A = L[l];
         const double n = (double)A.nx * A.ny, nf = (double)(A.nx + 1) * A.ny + (double)A.nx * (A.ny + 1);
@@ -610,27 +665,14 @@ void vcycle_fused(wec_poisson *P, Level<T> *L, const T *b0, T *x0, const int *bs
                                              H, l == 0 ? bsel : nullptr);
     }
     {
-        BottomLevels<T> B;
-        B.lb = lb;
-        B.nlev = P->nlev;
-        B.nu1 = P->nu1;
-        B.nu2 = P->nu2;
-        double bytes = 0.0;
-        for (int l = 0; l < P->nlev; ++l) {
-            B.nx[l] = L[l].nx;
-            B.ny[l] = L[l].ny;
-            B.bu[l] = L[l].bu;
-            B.bv[l] = L[l].bv;
-            B.x[l] = l == 0 ? x0 : L[l].x;
-            B.b[l] = l == 0 ? (T *)b0 : L[l].b;
-            if (l >= lb) {
-                const double n = (double)L[l].nx * L[l].ny, nf = (L[l].nx + 1.0) * L[l].ny + L[l].nx * (L[l].ny + 1.0);
-                bytes += (l == P->nlev - 1) ? (n * n + 2 * n) * ts : (2.25 * n + nf + 3.25 * n + nf) * ts;
-            }
-        }
+        // algorithmic bytes: b and x of level lb, every level's coefficients, the LU
+        const double nb = (double)L[lb].nx * L[lb].ny, nc = (double)L[P->nlev - 1].nx * L[P->nlev - 1].ny;
+        double bytes = (2.0 * nb + nc * nc) * ts;
+        for (int l = lb; l < P->nlev; ++l) bytes += ((L[l].nx + 1.0) * L[l].ny + L[l].nx * (L[l].ny + 1.0)) * ts;
         if constexpr (sizeof(T) == 8) B.lu = (const T *)P->lu64; else B.lu = (const T *)P->lu32;
+        const size_t smem_b = (size_t)bottom_elems(B, lb) * sizeof(T);
         WEC_PROF("mg_bottom", lb, bytes, st);
-        k_mg_bottom<T><<<1, kBottomThreads, 0, st>>>(B, bsel, xsel);
+        k_mg_bottom<T><<<1, kBottomThreads, smem_b, st>>>(B, bsel, xsel);
     }
     for (int l = lb - 1; l >= 0; --l) {
         Level<T> &A = L[l];
@@ -653,6 +695,8 @@ void vcycle_t(wec_poisson *P, Level<T> *L, const T *b0, T *x0, const int *bsel, 
 }
 
 int kgrid(long long n) { return (int)std::min<long long>(nblk(n, KT), kKrylovBlocks); }
+// the multi-dot kernels keep a few elements per thread: fewer blocks to sum at the end
+int kgrid_dots(long long n) { return (int)std::min<long long>(nblk(n, KT), kDotBlocks); }
 
 // ---------------------------------------------------------- FGMRES parts ----
 void enqueue_begin(wec_poisson *P, const double *b, double *x, double rtol, int maxit, unsigned long long hw,
@@ -684,7 +728,7 @@ void enqueue_body(wec_poisson *P, unsigned long long hif, int use, cudaStream_t 
 {
     const long long n = (long long)P->nx * P->ny;
     const double nf = (P->nx + 1.0) * P->ny + P->nx * (P->ny + 1.0);
-    const int G = kgrid(n), m = P->restart;
+    const int G = kgrid(n), Gd = kgrid_dots(n), m = P->restart;
     const size_t zsz = P->prec == WEC_PREC_FP64 ? 8 : 4;
     double *h1 = P->dots, *h2 = P->dots + (kMaxRestart + 2);
     if (P->prec == WEC_PREC_FP64) {
@@ -699,15 +743,15 @@ void enqueue_body(wec_poisson *P, unsigned long long hif, int use, cudaStream_t 
     {
         WEC_PROF("krylov_matvec_dots", -1, 8.0 * (n + nf) + (double)zsz * n + 8.0 * n * m, st);
         if (P->prec == WEC_PREC_FP64)
-            k_matvec_dots<double><<<G, KT, 0, st>>>(P->nx, P->ny, P->L64[0].bu, P->L64[0].bv, (const double *)P->Z,
+            k_matvec_dots<double><<<Gd, KT, 0, st>>>(P->nx, P->ny, P->L64[0].bu, P->L64[0].bv, (const double *)P->Z,
                                                     P->V, P->w, P->part, h1, P->ks);
         else
-            k_matvec_dots<float><<<G, KT, 0, st>>>(P->nx, P->ny, P->L64[0].bu, P->L64[0].bv, (const float *)P->Z,
+            k_matvec_dots<float><<<Gd, KT, 0, st>>>(P->nx, P->ny, P->L64[0].bu, P->L64[0].bv, (const float *)P->Z,
                                                    P->V, P->w, P->part, h1, P->ks);
     }
     {
         WEC_PROF("krylov_orth_dots", -1, 8.0 * n * (m + 2), st);
-        k_orth_dots<<<G, KT, 0, st>>>(n, P->V, P->w, h1, P->part, h2, P->ks);
+        k_orth_dots<<<Gd, KT, 0, st>>>(n, P->V, P->w, h1, P->part, h2, P->ks);
     }
     {
         WEC_PROF("krylov_orth_norm", -1, 8.0 * n * (m + 2), st);
@@ -765,6 +809,8 @@ int poisson_init(wec_poisson *P, int nx, int ny, int prec, int restart, int nu1,
         WEC_CK(cudaFuncSetAttribute(k_mg_post<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem<double>(8)));
         WEC_CK(cudaFuncSetAttribute(k_mg_pre<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem<float>(8)));
         WEC_CK(cudaFuncSetAttribute(k_mg_post<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem<float>(8)));
+        WEC_CK(cudaFuncSetAttribute(k_mg_bottom<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBottomSmemMax));
+        WEC_CK(cudaFuncSetAttribute(k_mg_bottom<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBottomSmemMax));
         attrs_done = true;
     }
     if (nx < 2 || ny < 2) return fail(WEC_ERR_INVALID, "poisson: nx, ny must be >= 2");
@@ -798,7 +844,7 @@ int poisson_init(wec_poisson *P, int nx, int ny, int prec, int restart, int nu1,
             WEC_CK(cudaMalloc(&P->L64[l].b, nc * 8));
         }
         P->bytes += (nu + nv) * 8 + (l > 0 ? 2 * nc * 8 : 0);
-        if (l < nl - 1 && (long long)nc > kBottomCells) {  // tiled level of the fused V-cycle
+        if (l < nl - 1) {  // may be a tiled level of the fused V-cycle
             WEC_CK(cudaMalloc(&P->L64[l].xp, nc * 8));
             if (prec == WEC_PREC_MIXED) WEC_CK(cudaMalloc(&P->L32[l].xp, nc * 4));
         }

@@ -127,8 +127,8 @@ __device__ __forceinline__ void ppm_edges(const double *a, double &L, double &R)
     double dm = vl_slope(a[0], a[1], a[2]);
     double d0 = vl_slope(a[1], a[2], a[3]);
     double dp = vl_slope(a[2], a[3], a[4]);
-    L = a[1] + 0.5 * (a[2] - a[1]) - (d0 - dm) / 6.0;
-    R = a[2] + 0.5 * (a[3] - a[2]) - (dp - d0) / 6.0;
+    L = a[1] + 0.5 * (a[2] - a[1]) - (d0 - dm) * (1.0 / 6.0);
+    R = a[2] + 0.5 * (a[3] - a[2]) - (dp - d0) * (1.0 / 6.0);
     double c = a[2];
     if ((R - c) * (c - L) <= 0.0) {
         L = c;
@@ -136,7 +136,7 @@ __device__ __forceinline__ void ppm_edges(const double *a, double &L, double &R)
     } else {
         double dA = R - L;
         double m6 = dA * (c - 0.5 * (L + R));
-        double q = dA * dA / 6.0;
+        double q = dA * dA * (1.0 / 6.0);
         if (m6 > q)
             L = 3.0 * c - 2.0 * R;
         else if (-q > m6)
@@ -145,20 +145,22 @@ __device__ __forceinline__ void ppm_edges(const double *a, double &L, double &R)
 }
 
 // Time-centred upwind face state; a[0..5] = cells f-3..f+2 around face f.
-__device__ __forceinline__ double ppm_face(const double *a, double vel, double dt, double h)
+__device__ __forceinline__ double ppm_face(const double *a, double vel, double dt, double ih)
 {
     double L, R;
     if (vel >= 0.0) {
         ppm_edges(a, L, R);
-        double C = vel * dt / h, dA = R - L, a6 = 6.0 * (a[2] - 0.5 * (L + R));
-        return R - 0.5 * C * (dA - (1.0 - 2.0 * C / 3.0) * a6);
+        double C = vel * dt * ih, dA = R - L, a6 = 6.0 * (a[2] - 0.5 * (L + R));
+        return R - 0.5 * C * (dA - (1.0 - C * (2.0 / 3.0)) * a6);
     }
     ppm_edges(a + 1, L, R);
-    double C = -vel * dt / h, dA = R - L, a6 = 6.0 * (a[3] - 0.5 * (L + R));
-    return L + 0.5 * C * (dA + (1.0 - 2.0 * C / 3.0) * a6);
+    double C = -vel * dt * ih, dA = R - L, a6 = 6.0 * (a[3] - 0.5 * (L + R));
+    return L + 0.5 * C * (dA + (1.0 - C * (2.0 / 3.0)) * a6);
 }
 
-__device__ __forceinline__ double damp_alpha(const TankP &P, double x)
+// Damping-zone weight (Jacobsen) and the vorticity-damping shape (cos(pi z~) + 1),
+// evaluated once per tank into tables (columns / rows) by k_tables.
+__device__ __forceinline__ double damp_alpha_eval(const TankP &P, double x)
 {
     if (P.damp_len <= 0.0 || x <= P.damp_x0) return 0.0;
     double xi = (x - P.damp_x0) / P.damp_len;
@@ -166,12 +168,18 @@ __device__ __forceinline__ double damp_alpha(const TankP &P, double x)
     return (exp(pow(xi, 3.5)) - 1.0) / (exp(1.0) - 1.0);
 }
 
-__device__ __forceinline__ double vort_damp(const TankP &P, double y, double dt)
+__device__ __forceinline__ double vort_shape_eval(const TankP &P, double y)
 {
     double w = 4.0 * P.h;
     if (y < P.ly - w) return 0.0;
     double zt = (y - P.ly) / w;
-    return P.rho_a * (cos(kPi * zt) + 1.0) / (4.0 * dt);
+    return cos(kPi * zt) + 1.0;
+}
+
+// g(z~) = rho_a (cos(pi z~) + 1) / (4 dt) (Eq. spongelayer) from the tabulated shape.
+__device__ __forceinline__ double vort_damp(const TankP &P, double shape, double idt)
+{
+    return P.rho_a * shape * (0.25 * idt);
 }
 
 __device__ __forceinline__ double minmod(double a, double b)
@@ -184,7 +192,7 @@ __device__ __forceinline__ double koren(double quu, double qu, double qd)
 {
     double d1 = qu - quu, d2 = qd - qu;
     if (d1 * d2 <= 0.0) return qu;
-    double m = fmin(2.0 * fabs(d2), fmin((fabs(d1) + 2.0 * fabs(d2)) / 3.0, 2.0 * fabs(d1)));
+    double m = fmin(2.0 * fabs(d2), fmin((fabs(d1) + 2.0 * fabs(d2)) * (1.0 / 3.0), 2.0 * fabs(d1)));
     return d1 > 0.0 ? qu + 0.5 * m : qu - 0.5 * m;
 }
 
@@ -356,7 +364,8 @@ __global__ void k_heave(TankP P, StepScalars *S, const double *__restrict__ part
 // sigma* = sigma^n - dt Q(u^n, sigma^n), then damping-zone relaxation.
 __global__ void k_advect(TankP P, const double *__restrict__ s, const double *__restrict__ u,
                          const double *__restrict__ v, const double *__restrict__ eta0,
-                         const double *__restrict__ inp, double *__restrict__ out)
+                         const double *__restrict__ inp, const double *__restrict__ alpha_c,
+                         double *__restrict__ out)
 {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= P.nx * P.ny) return;
@@ -367,25 +376,25 @@ __global__ void k_advect(TankP P, const double *__restrict__ s, const double *__
     for (int f = 0; f < 2; ++f) {
         int fi = i + f;
         for (int q = 0; q < 6; ++q) a[q] = sig_at(P, s, eta0, fi - 3 + q, j);
-        fx[f] = ppm_face(a, u[j * (nx + 1) + fi], dt, h);
+        fx[f] = ppm_face(a, u[j * (nx + 1) + fi], dt, P.ih);
         int fj = j + f;
         for (int q = 0; q < 6; ++q) a[q] = sig_at(P, s, eta0, i, fj - 3 + q);
-        fy[f] = ppm_face(a, v[fj * nx + i], dt, h);
+        fy[f] = ppm_face(a, v[fj * nx + i], dt, P.ih);
     }
     double ub = 0.5 * (u[j * (nx + 1) + i] + u[j * (nx + 1) + i + 1]);
     double vb = 0.5 * (v[j * nx + i] + v[(j + 1) * nx + i]);
-    double Q = ub * (fx[1] - fx[0]) / h + vb * (fy[1] - fy[0]) / h;
+    double Q = ub * (fx[1] - fx[0]) * P.ih + vb * (fy[1] - fy[0]) * P.ih;
     double sa = s[c] - dt * Q;
-    double al = damp_alpha(P, (i + 0.5) * h);
+    double al = alpha_c[i];
     out[c] = (1.0 - al) * sa + al * ((j + 0.5) * h - P.depth);
 }
 
 // Sussman relaxation right-hand side S(sigma0)(|grad f| - 1), Godunov
 // Hamiltonian on ENO-2 (minmod) one-sided differences.
-__device__ double reinit_rhs(const TankP &P, const double *__restrict__ f, const double *__restrict__ s0,
+__device__ double reinit_rhs(const TankP &P, const double *__restrict__ f, const double *__restrict__ sgn,
                              const double *__restrict__ eta1, int i, int j)
 {
-    const double h = P.h;
+    const double ih = P.ih, ih2 = 0.5 * P.ih;
     double c = f[j * P.nx + i];
     double xm2 = sig_at(P, f, eta1, i - 2, j), xm1 = sig_at(P, f, eta1, i - 1, j);
     double xp1 = sig_at(P, f, eta1, i + 1, j), xp2 = sig_at(P, f, eta1, i + 2, j);
@@ -393,12 +402,11 @@ __device__ double reinit_rhs(const TankP &P, const double *__restrict__ f, const
     double yp1 = sig_at(P, f, eta1, i, j + 1), yp2 = sig_at(P, f, eta1, i, j + 2);
     double dxm = xm2 - 2.0 * xm1 + c, dx0 = xm1 - 2.0 * c + xp1, dxp = c - 2.0 * xp1 + xp2;
     double dym = ym2 - 2.0 * ym1 + c, dy0 = ym1 - 2.0 * c + yp1, dyp = c - 2.0 * yp1 + yp2;
-    double a = (c - xm1) / h + minmod(dxm, dx0) / (2.0 * h);
-    double b = (xp1 - c) / h - minmod(dx0, dxp) / (2.0 * h);
-    double cc = (c - ym1) / h + minmod(dym, dy0) / (2.0 * h);
-    double d = (yp1 - c) / h - minmod(dy0, dyp) / (2.0 * h);
-    double g0 = s0[j * P.nx + i];
-    double S = g0 / sqrt(g0 * g0 + h * h);
+    double a = (c - xm1) * ih + minmod(dxm, dx0) * ih2;
+    double b = (xp1 - c) * ih - minmod(dx0, dxp) * ih2;
+    double cc = (c - ym1) * ih + minmod(dym, dy0) * ih2;
+    double d = (yp1 - c) * ih - minmod(dy0, dyp) * ih2;
+    double S = sgn[j * P.nx + i];
     double gx, gy;
     if (S > 0.0) {
         gx = fmax(sq(fmax(a, 0.0)), sq(fmin(b, 0.0)));
@@ -410,19 +418,43 @@ __device__ double reinit_rhs(const TankP &P, const double *__restrict__ f, const
     return S * (sqrt(gx + gy) - 1.0);
 }
 
+// Smoothed sign S(sigma0) = sigma0 / sqrt(sigma0^2 + h^2), fixed over the pseudo-steps.
+__global__ void k_reinit_sign(TankP P, const double *__restrict__ s0, double *__restrict__ sgn)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= P.nx * P.ny) return;
+    double g0 = s0[c];
+    sgn[c] = g0 / sqrt(g0 * g0 + P.h * P.h);
+}
+
 // TVD-RK2 stage: stage 1 out = f - dtau L(f); stage 2 out = (fprev + (f - dtau L(f))) / 2.
-__global__ void k_reinit(TankP P, const double *__restrict__ f, const double *__restrict__ s0,
+__global__ void k_reinit(TankP P, const double *__restrict__ f, const double *__restrict__ sgn,
                          const double *__restrict__ fprev, const double *__restrict__ eta1, double dtau,
                          double *__restrict__ out)
 {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= P.nx * P.ny) return;
     int i = c % P.nx, j = c / P.nx;
-    double s1 = f[c] - dtau * reinit_rhs(P, f, s0, eta1, i, j);
+    double s1 = f[c] - dtau * reinit_rhs(P, f, sgn, eta1, i, j);
     out[c] = fprev ? 0.5 * (fprev[c] + s1) : s1;
 }
 
 // ---------------------------------------------------- momentum helpers ----
+// Per-tank tables: alpha at cell centres [nx] and at u-faces [nx+1]; vorticity
+// shape at cell-centre rows [ny] and at v-face rows [ny+1].
+struct Tabs {
+    const double *alpha_c, *alpha_u, *vort_c, *vort_v;
+};
+
+__global__ void k_tables(TankP P, double *alpha_c, double *alpha_u, double *vort_c, double *vort_v)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < P.nx) alpha_c[k] = damp_alpha_eval(P, (k + 0.5) * P.h);
+    if (k <= P.nx) alpha_u[k] = damp_alpha_eval(P, k * P.h);
+    if (k < P.ny) vort_c[k] = vort_shape_eval(P, (k + 0.5) * P.h);
+    if (k <= P.ny) vort_v[k] = vort_shape_eval(P, k * P.h);
+}
+
 struct Fields {
     const double *rc;         // cell density rho^n (transport)
     const double *u, *v;      // velocities
@@ -467,8 +499,8 @@ __device__ void transport_u(const TankP &P, const Fields &X, int i, int j, doubl
         m[2 + s] = V * r;
         f[2 + s] = m[2 + s] * q;
     }
-    rb = ru_at(P, X.rc, i, j) - dt / P.h * ((m[1] - m[0]) + (m[3] - m[2]));
-    C = ((f[1] - f[0]) + (f[3] - f[2])) / P.h;
+    rb = ru_at(P, X.rc, i, j) - dt * P.ih * ((m[1] - m[0]) + (m[3] - m[2]));
+    C = ((f[1] - f[0]) + (f[3] - f[2])) * P.ih;
 }
 
 __device__ void transport_v(const TankP &P, const Fields &X, int i, int j, double dt, double &rb, double &C)
@@ -494,8 +526,8 @@ __device__ void transport_v(const TankP &P, const Fields &X, int i, int j, doubl
         m[2 + s] = V * r;
         f[2 + s] = m[2 + s] * q;
     }
-    rb = rv_at(P, X.rc, i, j) - dt / P.h * ((m[1] - m[0]) + (m[3] - m[2]));
-    C = ((f[1] - f[0]) + (f[3] - f[2])) / P.h;
+    rb = rv_at(P, X.rc, i, j) - dt * P.ih * ((m[1] - m[0]) + (m[3] - m[2]));
+    C = ((f[1] - f[0]) + (f[3] - f[2])) * P.ih;
 }
 
 // L_mu u = div[mu (grad u + grad u^T)]: tau_xx / tau_yy at cells, tau_xy at
@@ -512,45 +544,46 @@ __device__ __forceinline__ double mnode(const TankP &P, const Visc &X, int i, in
 
 __device__ __forceinline__ double txx(const TankP &P, const Visc &X, int i, int j)
 {
-    return 2.0 * cell_at(P, X.mu, i, j) * (u_at(P, X.u, i + 1, j) - u_at(P, X.u, i, j)) / P.h;
+    return 2.0 * cell_at(P, X.mu, i, j) * (u_at(P, X.u, i + 1, j) - u_at(P, X.u, i, j)) * P.ih;
 }
 
 __device__ __forceinline__ double tyy(const TankP &P, const Visc &X, int i, int j)
 {
-    return 2.0 * cell_at(P, X.mu, i, j) * (v_at(P, X.v, X.vin, i, j + 1) - v_at(P, X.v, X.vin, i, j)) / P.h;
+    return 2.0 * cell_at(P, X.mu, i, j) * (v_at(P, X.v, X.vin, i, j + 1) - v_at(P, X.v, X.vin, i, j)) * P.ih;
 }
 
 __device__ __forceinline__ double txy(const TankP &P, const Visc &X, int i, int j)
 {
-    return mnode(P, X, i, j) * ((u_at(P, X.u, i, j) - u_at(P, X.u, i, j - 1)) / P.h +
-                                (v_at(P, X.v, X.vin, i, j) - v_at(P, X.v, X.vin, i - 1, j)) / P.h);
+    return mnode(P, X, i, j) * ((u_at(P, X.u, i, j) - u_at(P, X.u, i, j - 1)) * P.ih +
+                                (v_at(P, X.v, X.vin, i, j) - v_at(P, X.v, X.vin, i - 1, j)) * P.ih);
 }
 
 __device__ __forceinline__ double visc_x(const TankP &P, const Visc &X, int i, int j)
 {
-    return (txx(P, X, i, j) - txx(P, X, i - 1, j)) / P.h + (txy(P, X, i, j + 1) - txy(P, X, i, j)) / P.h;
+    return (txx(P, X, i, j) - txx(P, X, i - 1, j)) * P.ih + (txy(P, X, i, j + 1) - txy(P, X, i, j)) * P.ih;
 }
 
 __device__ __forceinline__ double visc_y(const TankP &P, const Visc &X, int i, int j)
 {
-    return (tyy(P, X, i, j) - tyy(P, X, i, j - 1)) / P.h + (txy(P, X, i + 1, j) - txy(P, X, i, j)) / P.h;
+    return (tyy(P, X, i, j) - tyy(P, X, i, j - 1)) * P.ih + (txy(P, X, i + 1, j) - txy(P, X, i, j)) * P.ih;
 }
 
 __device__ __forceinline__ double visc_diag_x(const TankP &P, const Visc &X, int i, int j)
 {
     return -(2.0 * cell_at(P, X.mu, i, j) + 2.0 * cell_at(P, X.mu, i - 1, j) + mnode(P, X, i, j + 1) +
-             mnode(P, X, i, j)) / (P.h * P.h);
+             mnode(P, X, i, j)) * (P.ih * P.ih);
 }
 
 __device__ __forceinline__ double visc_diag_y(const TankP &P, const Visc &X, int i, int j)
 {
     return -(2.0 * cell_at(P, X.mu, i, j) + 2.0 * cell_at(P, X.mu, i, j - 1) + mnode(P, X, i + 1, j) +
-             mnode(P, X, i, j)) / (P.h * P.h);
+             mnode(P, X, i, j)) * (P.ih * P.ih);
 }
 
 // Right-hand side R and diagonal D of the u-momentum system; also the first
 // Jacobi iterate (u^n with the Dirichlet faces at t^{n+1}).
-__global__ void k_mom_u(TankP P, const StepScalars *S, const double *__restrict__ inp, const double *__restrict__ rho_n,
+__global__ void k_mom_u(TankP P, const StepScalars *S, const double *__restrict__ inp, Tabs tb,
+                        const double *__restrict__ rho_n,
                         const double *__restrict__ mu_n, const double *__restrict__ chi_1,
                         const double *__restrict__ u, const double *__restrict__ v, const double *__restrict__ p,
                         Bc bc, double *Ru, double *Du, double *rbu, double *ua)
@@ -576,12 +609,14 @@ __global__ void k_mom_u(TankP P, const StepScalars *S, const double *__restrict_
     double x = i * P.h, y = (j + 0.5) * P.h;
     double chi = 0.5 * (cell_at(P, chi_1, i - 1, j) + cell_at(P, chi_1, i, j));
     rbu[f] = rb;
-    Du[f] = rb / dt + chi / P.kappa_p + damp_alpha(P, x) * rb / dt + vort_damp(P, y, dt);
-    Ru[f] = ru_at(P, rho_n, i, j) * u[f] / dt - C + 0.5 * visc_x(P, Vn, i, j) -
-            (p[j * nx + i] - p[j * nx + i - 1]) / P.h;
+    const double idt = 1.0 / dt;
+    Du[f] = rb * idt + chi * P.ikp + tb.alpha_u[i] * rb * idt + vort_damp(P, tb.vort_c[j], idt);
+    Ru[f] = ru_at(P, rho_n, i, j) * u[f] * idt - C + 0.5 * visc_x(P, Vn, i, j) -
+            (p[j * nx + i] - p[j * nx + i - 1]) * P.ih;
 }
 
-__global__ void k_mom_v(TankP P, const StepScalars *S, const double *__restrict__ inp, const double *__restrict__ rho_n,
+__global__ void k_mom_v(TankP P, const StepScalars *S, const double *__restrict__ inp, Tabs tb,
+                        const double *__restrict__ rho_n,
                         const double *__restrict__ mu_n, const double *__restrict__ chi_1,
                         const double *__restrict__ rf_1, const double *__restrict__ u,
                         const double *__restrict__ v, const double *__restrict__ p, Bc bc, double *Rv,
@@ -605,10 +640,11 @@ __global__ void k_mom_v(TankP P, const StepScalars *S, const double *__restrict_
     double chi = 0.5 * (cell_at(P, chi_1, i, j - 1) + cell_at(P, chi_1, i, j));
     double rf = 0.5 * (cell_at(P, rf_1, i, j - 1) + cell_at(P, rf_1, i, j));
     rbv[f] = rb;
-    Dv[f] = rb / dt + chi / P.kappa_p + damp_alpha(P, x) * rb / dt + vort_damp(P, y, dt);
-    double gp = j < ny ? (p[j * nx + i] - p[(j - 1) * nx + i]) / P.h : -2.0 * p[(ny - 1) * nx + i] / P.h;
-    Rv[f] = rv_at(P, rho_n, i, j) * v[f] / dt - C + 0.5 * visc_y(P, Vn, i, j) - rf * P.g +
-            chi * S->zdot1 / P.kappa_p - gp;
+    const double idt = 1.0 / dt;
+    Dv[f] = rb * idt + chi * P.ikp + tb.alpha_c[i] * rb * idt + vort_damp(P, tb.vort_v[j], idt);
+    double gp = j < ny ? (p[j * nx + i] - p[(j - 1) * nx + i]) * P.ih : -2.0 * p[(ny - 1) * nx + i] * P.ih;
+    Rv[f] = rv_at(P, rho_n, i, j) * v[f] * idt - C + 0.5 * visc_y(P, Vn, i, j) - rf * P.g +
+            chi * S->zdot1 * P.ikp - gp;
 }
 
 // One Jacobi sweep of (D - L_mu / 2) u* = R (Crank-Nicolson implicit half),
@@ -675,13 +711,13 @@ __global__ void k_project(TankP P, const double *__restrict__ us, const double *
     if (k < nu) {
         int i = k % (nx + 1), j = k / (nx + 1);
         double uu = us[k];
-        if (i > 0 && i < nx) uu -= bu[k] * (phi[j * nx + i] - phi[j * nx + i - 1]) / h;
+        if (i > 0 && i < nx) uu -= bu[k] * (phi[j * nx + i] - phi[j * nx + i - 1]) * P.ih;
         u[k] = uu;
     } else if (k < nu + nv) {
         int f = k - nu, i = f % nx, j = f / nx;
         double vv = vs[f];
-        if (j > 0 && j < ny) vv -= bv[f] * (phi[j * nx + i] - phi[(j - 1) * nx + i]) / h;
-        if (j == ny) vv += 2.0 * bv[f] * phi[(ny - 1) * nx + i] / h;
+        if (j > 0 && j < ny) vv -= bv[f] * (phi[j * nx + i] - phi[(j - 1) * nx + i]) * P.ih;
+        if (j == ny) vv += 2.0 * bv[f] * phi[(ny - 1) * nx + i] * P.ih;
         v[f] = vv;
     } else if (k < nu + nv + nc) {
         int c = k - nu - nv;
@@ -714,15 +750,22 @@ __global__ void k_finalize(TankP P, StepScalars *S, const double *__restrict__ p
     double s = 0.0;
     for (int b = threadIdx.x; b < kRedBlocks; b += blockDim.x) s += part[b];
     double d2 = block_sum(s, sh);
-    if (threadIdx.x != 0) return;
-    int ip = clampi((int)floor(P.probe_x / P.h), 0, P.nx - 1);
-    double eta = nan("");
-    for (int j = 0; j + 1 < P.ny; ++j) {
+    // probe: the lowest row j of the probe column with sigma_j < 0 <= sigma_{j+1}
+    __shared__ int jmin;
+    if (threadIdx.x == 0) jmin = P.ny;
+    __syncthreads();
+    const int ip = clampi((int)floor(P.probe_x / P.h), 0, P.nx - 1);
+    for (int j = threadIdx.x; j + 1 < P.ny; j += blockDim.x) {
         double a = sig[j * P.nx + ip], b = sig[(j + 1) * P.nx + ip];
-        if (a < 0.0 && b >= 0.0) {
-            eta = (j + 0.5) * P.h + P.h * a / (a - b) - P.depth;
-            break;
-        }
+        if (a < 0.0 && b >= 0.0) atomicMin(&jmin, j);
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double eta = nan("");
+    if (jmin < P.ny) {
+        const int j = jmin;
+        double a = sig[j * P.nx + ip], b = sig[(j + 1) * P.nx + ip];
+        eta = (j + 0.5) * P.h + P.h * a / (a - b) - P.depth;
     }
     S->div2 = d2;
     S->eta = eta;
@@ -810,6 +853,14 @@ int tank_alloc_and_init(wec_tank *T)
     T->bc.eta1 = T->bc.eta0 + 3;
     T->bc.eta_in = T->bc.eta1 + 3;
     WEC_CK(cudaMalloc(&T->part, kRedBlocks * 8));
+    WEC_CK(cudaMalloc(&T->tabs, (size_t)(2 * P.nx + 1 + 2 * P.ny + 1) * 8));
+    WEC_CK(cudaMalloc(&T->sgn, nc * 8));
+    {
+        WEC_PROF("init", -1, 8.0 * (2 * P.nx + 2 * P.ny + 2), T->gst);
+        double *t = T->tabs;
+        k_tables<<<nblk(std::max(P.nx, P.ny) + 1, 128), 128, 0, T->gst>>>(P, t, t + P.nx, t + 2 * P.nx + 1,
+                                                                          t + 2 * P.nx + 1 + P.ny);
+    }
     WEC_CK(cudaMalloc(&T->inp, 2 * 8));
     WEC_CK(cudaMemset(T->inp, 0, 2 * 8));
     WEC_CK(cudaMalloc(&T->S, sizeof(StepScalars)));
@@ -845,6 +896,12 @@ int tank_init_pressure(wec_tank *T)
 
 namespace {
 
+Tabs tabs(const wec_tank *T)
+{
+    const int nx = T->P.nx, ny = T->P.ny;
+    return Tabs{T->tabs, T->tabs + nx, T->tabs + 2 * nx + 1, T->tabs + 2 * nx + 1 + ny};
+}
+
 // Everything before the pressure solve: steps (1)-(7) of the step.
 void enqueue_front(wec_tank *T, cudaStream_t st)
 {
@@ -858,7 +915,7 @@ void enqueue_front(wec_tank *T, cudaStream_t st)
     }
     {
         WEC_PROF("bc", -1, fb * (3.0 * P.ny + 2), st);
-        k_bc_rows<<<nblk(P.ny + 1, 8), 256, 0, st>>>(P, T->S, T->inp, T->bc);
+        k_bc_rows<<<nblk(P.ny + 1, 2), 64, 0, st>>>(P, T->S, T->inp, T->bc);
     }
     // (2) materials at n, force from p^{n-1/2}, u^n (Eq. int_fh), heave (Eq. newton_u)
     {
@@ -877,21 +934,25 @@ void enqueue_front(wec_tank *T, cudaStream_t st)
     // last pseudo-step writes sigma^{n+1} over sigma^n (no longer needed).
     {
         WEC_PROF("advect", -1, fb * (2.0 * nc + nu + nv), st);
-        k_advect<<<nblk(nc, TB), TB, 0, st>>>(P, T->sig, T->u, T->v, T->bc.eta0, T->inp, T->sa);
+        k_advect<<<nblk(nc, TB), TB, 0, st>>>(P, T->sig, T->u, T->v, T->bc.eta0, T->inp, T->tabs, T->sa);
     }
     const double dtau = 0.3 * P.h;
     const double *f = T->sa;
     double *bufs[2] = {T->r0, T->r1};
     const int nr = T->opts.n_reinit;
+    if (nr > 0) {
+        WEC_PROF("reinit", -1, fb * 2.0 * nc, st);
+        k_reinit_sign<<<nblk(nc, TB), TB, 0, st>>>(P, T->sa, T->sgn);
+    }
     for (int it = 0; it < nr; ++it) {
         double *dst = it == nr - 1 ? T->sig : bufs[it & 1];
         {
             WEC_PROF("reinit", -1, fb * 3.0 * nc, st);
-            k_reinit<<<nblk(nc, TB), TB, 0, st>>>(P, f, T->sa, nullptr, T->bc.eta1, dtau, T->rt);
+            k_reinit<<<nblk(nc, TB), TB, 0, st>>>(P, f, T->sgn, nullptr, T->bc.eta1, dtau, T->rt);
         }
         {
             WEC_PROF("reinit", -1, fb * 4.0 * nc, st);
-            k_reinit<<<nblk(nc, TB), TB, 0, st>>>(P, T->rt, T->sa, f, T->bc.eta1, dtau, dst);
+            k_reinit<<<nblk(nc, TB), TB, 0, st>>>(P, T->rt, T->sgn, f, T->bc.eta1, dtau, dst);
         }
         f = dst;
     }
@@ -904,12 +965,12 @@ void enqueue_front(wec_tank *T, cudaStream_t st)
     // (5) momentum right-hand side and diagonal, (6) Crank-Nicolson Jacobi sweeps
     {
         WEC_PROF("mom_u", -1, fb * (4.0 * nc + nu + nv + 4.0 * nu), st);
-        k_mom_u<<<nblk(nu, TB), TB, 0, st>>>(P, T->S, T->inp, T->rho_n, T->mu_n, T->chi_1, T->u, T->v, T->p,
+        k_mom_u<<<nblk(nu, TB), TB, 0, st>>>(P, T->S, T->inp, tabs(T), T->rho_n, T->mu_n, T->chi_1, T->u, T->v, T->p,
                                              T->bc, T->Ru, T->Du, T->rbu, T->ua);
     }
     {
         WEC_PROF("mom_v", -1, fb * (5.0 * nc + nu + nv + 4.0 * nv), st);
-        k_mom_v<<<nblk(nv, TB), TB, 0, st>>>(P, T->S, T->inp, T->rho_n, T->mu_n, T->chi_1, T->rf_1, T->u, T->v,
+        k_mom_v<<<nblk(nv, TB), TB, 0, st>>>(P, T->S, T->inp, tabs(T), T->rho_n, T->mu_n, T->chi_1, T->rf_1, T->u, T->v,
                                              T->p, T->bc, T->Rv, T->Dv, T->rbv, T->va);
     }
     const double *ju = T->ua, *jv = T->va;
@@ -1069,7 +1130,8 @@ void tank_free(wec_tank *T)
     if (T->graph) cudaGraphDestroy(T->graph);
     double *all[] = {T->sig, T->sa, T->r0, T->r1, T->rt, T->p, T->phi, T->rhs, T->rho_n, T->mu_n, T->mu_1,
                      T->rf_1, T->chi_1, T->u, T->us, T->ua, T->ub, T->uc, T->Ru, T->Du, T->rbu, T->v, T->vs,
-                     T->va, T->vb, T->vc, T->Rv, T->Dv, T->rbv, T->bcbuf, T->part, T->waves, T->inp};
+                     T->va, T->vb, T->vc, T->Rv, T->Dv, T->rbv, T->bcbuf, T->part, T->waves, T->inp,
+                     T->tabs, T->sgn};
     for (double *q : all) cudaFree(q);
     cudaFree(T->S);
     if (T->Sh) cudaFreeHost(T->Sh);

@@ -8,11 +8,11 @@ namespace wec {
 // Per-tank constants, passed to kernels by value.
 struct TankP {
     int nx, ny;
-    double h, lx, ly, depth;
+    double h, ih, lx, ly, depth;  // ih = 1 / h
     double rho_w, rho_a, rho_s, mu_w, mu_a, mu_s, g;
     double damp_x0, damp_len, probe_x;
     int has_body;
-    double bxc, bw, bh, mass, added_mass, kappa_p, pto_c;
+    double bxc, bw, bh, mass, added_mass, kappa_p, ikp, pto_c;  // ikp = 1 / kappa_p
     int ncomp;
     const double *amp, *omega, *kw, *phase;  // device
 };
@@ -50,6 +50,8 @@ struct wec_tank {
     bool use_graph = true;
     int n_fixed = 0, n_body = 0, n_close = 0;  // kernels per replay: fixed, per iteration, per cycle
     double *inp = nullptr;            // device: dt, f_pto of the current step
+    double *tabs = nullptr;           // device: damping weights / vorticity shape per column / row
+    double *sgn = nullptr;            // device: Sussman smoothed sign of the step's sigma0
     size_t nc = 0, nu = 0, nv = 0;
     double *sig = nullptr, *sa = nullptr, *r0 = nullptr, *r1 = nullptr, *rt = nullptr;
     double *u = nullptr, *v = nullptr, *us = nullptr, *vs = nullptr;
