@@ -277,6 +277,10 @@ def main_ours(args):
                   "share": d["ms"] / tot_prof}
                  for k, d in sorted(by_name.items(), key=lambda kv: -kv[1]["ms"])[:12]]
 
+    tiles_t = wec.Tank(cfg, precision=wec.PREC_MIXED)
+    mg_tiles = tiles_t.mg_tiles()
+    tiles_t.close()
+
     clocks = Clocks(local)
     clocks.start()
     mixed = time_path(L, wec, torch, cfg, wec.PREC_MIXED, steps, warmup, flush)
@@ -335,6 +339,7 @@ def main_ours(args):
         "speedup_mixed_vs_fp64": value / fp64_value,
         "learned_warm_start": "not built",
         "execution": "one CUDA graph per step (conditional WHILE/IF nodes steer FGMRES on the GPU)",
+        "mg_tiles_autotuned": mg_tiles,
         "fgmres_iters_per_step": {"mixed": statistics.mean(mixed["iters"]), "fp64": statistics.mean(fp64["iters"])},
         "max_relative_residual": {"mixed": mixed["residual"], "fp64": fp64["residual"]},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 16, "d2h_bytes_per_step": 72,

@@ -242,11 +242,20 @@ int wec_jonswap(double Hs, double Tp, double gamma, int ncomp, double *amp, doub
 /* ---- process-wide options ------------------------------------------------ */
 /* "mg_fused" (default 1): the multigrid V-cycle runs as one shared-memory tile
  * kernel per fine level for pre-smoothing + residual + restriction, one for
- * prolongation + post-smoothing, and one single-CTA kernel for every level of at
- * most 16384 cells; 0 launches one kernel per colour pass, restriction and
- * prolongation.  Both compute the same values bit for bit.  Applies to graphs
+ * prolongation + post-smoothing, and one single-CTA kernel, staged in shared
+ * memory, for the levels of at most 4096 cells; 0 launches one kernel per colour
+ * pass, restriction and prolongation.  Both compute the same values up to
+ * rounding.  "mg_autotune" (default 1): when a solver is created, time the fused
+ * kernels' tile shapes (64x16, 32x16, 32x8, 16x8) on each level and keep the
+ * fastest; 0 uses 64x16 everywhere.  Options apply to solvers created, graphs
  * captured and solves started after the call.  Unknown name: WEC_ERR_INVALID. */
 int wec_set_option(const char *name, int value);
+
+/* Fused multigrid tile shape (interior cells) per level of the tank's solver, as
+ * chosen by the autotuner when the tank was created ("mg_autotune" option; the
+ * coarsest level's entry is meaningless).  *nlev receives the number of levels;
+ * at most max entries are written. */
+int wec_tank_mg_tiles(const wec_tank *tank, int *tile_x, int *tile_y, int max, int *nlev);
 
 /* ---- launch accounting and profiling ------------------------------------ */
 /* Number of kernels this library has launched in the process so far. */

@@ -198,7 +198,19 @@ int wec_set_option(const char *name, int value)
         set_mg_fused(value != 0);
         return WEC_OK;
     }
+    if (std::string(name) == "mg_autotune") {
+        set_mg_autotune(value != 0);
+        return WEC_OK;
+    }
     return fail(WEC_ERR_INVALID, std::string("unknown option: ") + name);
+}
+
+int wec_tank_mg_tiles(const wec_tank *T, int *tile_x, int *tile_y, int max, int *nlev)
+{
+    if (!T || !nlev || (max > 0 && (!tile_x || !tile_y))) return fail(WEC_ERR_INVALID, "NULL argument");
+    *nlev = T->solver.nlev;
+    poisson_tiles(&T->solver, tile_x, tile_y, max);
+    return WEC_OK;
 }
 
 int wec_tank_use_graph(wec_tank *T, int enable)

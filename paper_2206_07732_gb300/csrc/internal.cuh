@@ -86,6 +86,8 @@ struct wec_poisson {
     double *dots = nullptr;     // h1, h2 of the two Gram-Schmidt passes
     double *hess = nullptr;     // (m+1) x m Hessenberg, then cs, sn, g, y
     double *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr;
+    int tile64[wec::kMaxLevels] = {}, tile32[wec::kMaxLevels] = {};  // fused tile shape per level (autotuned)
+    bool tuned = false;
     wec::KState *ks = nullptr;  // device
     wec::KState *ksh = nullptr; // pinned host mirror
     size_t bytes = 0;
@@ -112,6 +114,8 @@ int poisson_count_kernels(wec_poisson *P, cudaStream_t s, int *n_begin, int *n_b
 int solve_result(wec_poisson *P, int *iters, double *relres);
 int poisson_apply(wec_poisson *P, const double *x, double *y);
 void set_mg_fused(bool on);
+void set_mg_autotune(bool on);
+void poisson_tiles(const wec_poisson *P, int *tx, int *ty, int max);
 int poisson_vcycle(wec_poisson *P, const double *b, double *x);
 
 // waves.cpp

@@ -21,7 +21,11 @@
 namespace wec {
 namespace {
 
-constexpr int kTX = 64, kTY = 16;       // tile of a fused level kernel (interior cells)
+// Tile shapes (interior cells) of the fused level kernels; the autotuner picks
+// one per level and precision.
+constexpr int kNumTiles = 4;
+constexpr int kTileX[kNumTiles] = {64, 32, 32, 16};
+constexpr int kTileY[kNumTiles] = {16, 16, 8, 8};
 constexpr int kBottomCells = 4096;      // levels up to this size run inside one CTA (shared memory)
 constexpr int kBottomSmemMax = 200 * 1024;
 constexpr int kBottomThreads = 1024;
@@ -80,15 +84,19 @@ __device__ void tile_load(TileView<T> &t, const T *__restrict__ bu, const T *__r
     __syncthreads();
 }
 
-// One colour pass over the tile cells at margin >= m (inside the domain).
+// One colour pass over the tile cells at margin >= m (inside the domain): the
+// threads walk the cells of that colour only, row by row.
 template <typename T>
 __device__ void tile_pass(TileView<T> &t, int color, int m, int first)
 {
     const int ex = t.ex, ey = t.ey;
-    const int w = ex - 2 * m, hgt = ey - 2 * m;
-    for (int k = threadIdx.x; k < w * hgt; k += blockDim.x) {
-        int li = m + k % w, lj = m + k / w, gi = t.gx0 + li, gj = t.gy0 + lj;
-        if (gi < 0 || gi >= t.nx || gj < 0 || gj >= t.ny || ((gi + gj) & 1) != color) continue;
+    const int w = ex - 2 * m, hgt = ey - 2 * m, wh = (w + 1) >> 1;
+    for (int k = threadIdx.x; k < wh * hgt; k += blockDim.x) {
+        const int r = k / wh, q = k - r * wh;
+        const int lj = m + r;
+        const int li = m + ((color - (t.gx0 + m) - (t.gy0 + lj)) & 1) + 2 * q;
+        const int gi = t.gx0 + li, gj = t.gy0 + lj;
+        if (li >= ex - m || gi < 0 || gi >= t.nx || gj < 0 || gj >= t.ny) continue;
         int c = lj * ex + li;
         T d = t.diag(li, lj);
         if (first)
@@ -101,7 +109,7 @@ __device__ void tile_pass(TileView<T> &t, int color, int m, int first)
 
 // nu1 sweeps from zero, then the smoothed iterate (tile interior) into xp and
 // the restricted residual into bc.
-template <typename T>
+template <typename T, int kTX, int kTY>
 __global__ void __launch_bounds__(256) k_mg_pre(int nx, int ny, const T *__restrict__ bu, const T *__restrict__ bv,
                                                 const T *__restrict__ b, T *__restrict__ xp, T *__restrict__ bc,
                                                 int nu1, int H, const int *bsel)
@@ -155,7 +163,7 @@ __global__ void __launch_bounds__(256) k_mg_pre(int nx, int ny, const T *__restr
 
 // x = xp + P x_c, then nu2 sweeps; writes the tile interior of x.  Reads xp and
 // writes x (different arrays): tiles read their halos while others write.
-template <typename T>
+template <typename T, int kTX, int kTY>
 __global__ void __launch_bounds__(256) k_mg_post(int nx, int ny, const T *__restrict__ bu, const T *__restrict__ bv,
                                                  const T *__restrict__ b, const T *__restrict__ xp, T *x,
                                                  const T *__restrict__ xc, int nu2, int H, const int *bsel,
@@ -336,7 +344,7 @@ __global__ void __launch_bounds__(kBottomThreads) k_mg_bottom(BottomLevels<T> L,
 }
 
 template <typename T>
-size_t tile_smem(int H)
+size_t tile_smem(int H, int kTX, int kTY)
 {
     const size_t ex = kTX + 2 * H, ey = kTY + 2 * H;
     return sizeof(T) * (2 * ex * ey + (ex + 1) * ey + ex * (ey + 1));

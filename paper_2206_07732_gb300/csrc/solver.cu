@@ -378,26 +378,27 @@ __global__ void k_scale0(long long n, const double *__restrict__ w, double *__re
     if (c < n) V[c] = w[c] / ks->beta;
 }
 
-// All j+1 block partials of V_k . w (k <= j) at once: per-thread register
-// accumulators (KMAXV covers restart <= 32), warp shuffles, then one value per
-// (warp, k) combined in warp order.  part[k * G + block].
+// Block partials of V_k . w for k <= j: for each k the threads of a warp sum
+// their elements and shuffle-reduce (no block barrier per k); one barrier, then
+// thread k adds the warps' sums in warp order.  part[k * G + block].
 constexpr int KMAXV = kMaxRestart + 1;
 
-__device__ __forceinline__ void block_partials(const double *acc, int nk, double *part, double (*sh)[KMAXV])
+__device__ __forceinline__ void multi_dot_partials(const double *__restrict__ V, const double *__restrict__ w,
+                                                   long long n, int nk, double *part, double (*sh)[KMAXV])
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < KMAXV; ++k) {
-        if (k < nk) {
-            double v = acc[k];
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-            if (lane == 0) sh[warp][k] = v;
-        }
+    for (int k = 0; k < nk; ++k) {
+        const double *vk = V + (long long)k * n;
+        double a = 0.0;
+        for (long long c = blockIdx.x * (long long)KT + threadIdx.x; c < n; c += (long long)gridDim.x * KT)
+            a += vk[c] * w[c];
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        if (lane == 0) sh[warp][k] = a;
     }
     __syncthreads();
     if (threadIdx.x < nk) {
         double r = 0.0;
-        for (int w = 0; w < KT / 32; ++w) r += sh[w][threadIdx.x];
+        for (int q = 0; q < KT / 32; ++q) r += sh[q][threadIdx.x];
         part[threadIdx.x * gridDim.x + blockIdx.x] = r;
     }
 }
@@ -419,33 +420,26 @@ __device__ __forceinline__ void final_partials(const double *part, int nk, doubl
 template <typename TZ>
 __global__ void __launch_bounds__(KT) k_matvec_dots(int nx, int ny, const double *__restrict__ bu,
                                                       const double *__restrict__ bv, const TZ *__restrict__ Z,
-                                                      const double *__restrict__ V, double *__restrict__ w,
+                                                      const double *__restrict__ V, double *w,
                                                       double *part, double *h1, KState *ks)
 {
     __shared__ double sh[KT / 32][KMAXV];
     const long long n = (long long)nx * ny;
     const int j = ks->j, nk = j + 1;
     const TZ *z = Z + (long long)j * n;
-    double acc[KMAXV];
-#pragma unroll
-    for (int k = 0; k < KMAXV; ++k) acc[k] = 0.0;
     for (long long c = blockIdx.x * (long long)KT + threadIdx.x; c < n; c += (long long)gridDim.x * KT) {
         int i = (int)(c % nx), jj = (int)(c / nx);
         double d = diag_at(bu, bv, nx, ny, i, jj);
-        double wc = d * double(z[c]) - offsum_at(bu, bv, z, nx, ny, i, jj);
-        w[c] = wc;
-#pragma unroll
-        for (int k = 0; k < KMAXV; ++k)
-            if (k < nk) acc[k] += V[(long long)k * n + c] * wc;
+        w[c] = d * double(z[c]) - offsum_at(bu, bv, z, nx, ny, i, jj);
     }
-    block_partials(acc, nk, part, sh);
+    multi_dot_partials(V, w, n, nk, part, sh);
     if (!last_block(&ks->cnt[2])) return;
     final_partials(part, nk, h1);
     if (threadIdx.x == 0) ks->cnt[2] = 0;
 }
 
 // First Gram-Schmidt update w -= sum_k h1_k V_k, then h2_k = V_k . w.
-__global__ void __launch_bounds__(KT) k_orth_dots(long long n, const double *__restrict__ V, double *__restrict__ w,
+__global__ void __launch_bounds__(KT) k_orth_dots(long long n, const double *__restrict__ V, double *w,
                                                     const double *__restrict__ h1, double *part, double *h2,
                                                     KState *ks)
 {
@@ -454,24 +448,12 @@ __global__ void __launch_bounds__(KT) k_orth_dots(long long n, const double *__r
     const int j = ks->j, nk = j + 1;
     if (threadIdx.x < nk) hs[threadIdx.x] = h1[threadIdx.x];
     __syncthreads();
-    double acc[KMAXV];
-#pragma unroll
-    for (int k = 0; k < KMAXV; ++k) acc[k] = 0.0;
     for (long long c = blockIdx.x * (long long)KT + threadIdx.x; c < n; c += (long long)gridDim.x * KT) {
-        double vr[KMAXV];
         double a = w[c];
-#pragma unroll
-        for (int k = 0; k < KMAXV; ++k)
-            if (k < nk) {
-                vr[k] = V[(long long)k * n + c];
-                a -= hs[k] * vr[k];
-            }
+        for (int k = 0; k < nk; ++k) a -= hs[k] * V[(long long)k * n + c];
         w[c] = a;
-#pragma unroll
-        for (int k = 0; k < KMAXV; ++k)
-            if (k < nk) acc[k] += vr[k] * a;
     }
-    block_partials(acc, nk, part, sh);
+    multi_dot_partials(V, w, n, nk, part, sh);
     if (!last_block(&ks->cnt[2])) return;
     final_partials(part, nk, h2);
     if (threadIdx.x == 0) ks->cnt[2] = 0;
@@ -629,6 +611,67 @@ void vcycle_unfused(wec_poisson *P, Level<T> *L, const T *b0, T *x0, const int *
     }
 }
 
+template <typename T, int TX, int TY>
+int set_attrs_one()
+{
+    const int mx = (int)tile_smem<T>(8, TX, TY);
+    WEC_CK(cudaFuncSetAttribute(k_mg_pre<T, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    WEC_CK(cudaFuncSetAttribute(k_mg_post<T, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    return WEC_OK;
+}
+
+int set_tile_attrs()
+{
+    int e = set_attrs_one<double, 64, 16>();
+    if (!e) e = set_attrs_one<double, 32, 16>();
+    if (!e) e = set_attrs_one<double, 32, 8>();
+    if (!e) e = set_attrs_one<double, 16, 8>();
+    if (!e) e = set_attrs_one<float, 64, 16>();
+    if (!e) e = set_attrs_one<float, 32, 16>();
+    if (!e) e = set_attrs_one<float, 32, 8>();
+    if (!e) e = set_attrs_one<float, 16, 8>();
+    return e;
+}
+
+template <typename T, int TX, int TY>
+void launch_pre_t(const Level<T> &A, const T *b, T *bc, int nu1, int H, const int *bsel, cudaStream_t st)
+{
+    dim3 grid((A.nx + TX - 1) / TX, (A.ny + TY - 1) / TY);
+    k_mg_pre<T, TX, TY><<<grid, 256, tile_smem<T>(H, TX, TY), st>>>(A.nx, A.ny, A.bu, A.bv, b, A.xp, bc, nu1, H, bsel);
+}
+
+template <typename T, int TX, int TY>
+void launch_post_t(const Level<T> &A, const T *b, T *x, const T *xc, int nu2, int H, const int *bsel,
+                   const int *xsel, cudaStream_t st)
+{
+    dim3 grid((A.nx + TX - 1) / TX, (A.ny + TY - 1) / TY);
+    k_mg_post<T, TX, TY><<<grid, 256, tile_smem<T>(H, TX, TY), st>>>(A.nx, A.ny, A.bu, A.bv, b, A.xp, x, xc, nu2, H,
+                                                                     bsel, xsel);
+}
+
+template <typename T>
+void launch_pre(int tile, const Level<T> &A, const T *b, T *bc, int nu1, int H, const int *bsel, cudaStream_t st)
+{
+    switch (tile) {
+    case 1: launch_pre_t<T, 32, 16>(A, b, bc, nu1, H, bsel, st); break;
+    case 2: launch_pre_t<T, 32, 8>(A, b, bc, nu1, H, bsel, st); break;
+    case 3: launch_pre_t<T, 16, 8>(A, b, bc, nu1, H, bsel, st); break;
+    default: launch_pre_t<T, 64, 16>(A, b, bc, nu1, H, bsel, st); break;
+    }
+}
+
+template <typename T>
+void launch_post(int tile, const Level<T> &A, const T *b, T *x, const T *xc, int nu2, int H, const int *bsel,
+                 const int *xsel, cudaStream_t st)
+{
+    switch (tile) {
+    case 1: launch_post_t<T, 32, 16>(A, b, x, xc, nu2, H, bsel, xsel, st); break;
+    case 2: launch_post_t<T, 32, 8>(A, b, x, xc, nu2, H, bsel, xsel, st); break;
+    case 3: launch_post_t<T, 16, 8>(A, b, x, xc, nu2, H, bsel, xsel, st); break;
+    default: launch_post_t<T, 64, 16>(A, b, x, xc, nu2, H, bsel, xsel, st); break;
+    }
+}
+
 // Fused V-cycle: per fine level one pre and one post kernel, one CTA for the
 // levels of at most kBottomCells cells.
 template <typename T>
@@ -637,7 +680,7 @@ void vcycle_fused(wec_poisson *P, Level<T> *L, const T *b0, T *x0, const int *bs
 {
     const double ts = sizeof(T);
     const int H = 2 * std::max(P->nu1, P->nu2);
-    const size_t smem = tile_smem<T>(H);
+    const int *tiles = sizeof(T) == 8 ? P->tile64 : P->tile32;
     BottomLevels<T> B;
     B.nlev = P->nlev;
     B.nu1 = P->nu1;
@@ -659,10 +702,8 @@ void vcycle_fused(wec_poisson *P, Level<T> *L, const T *b0, T *x0, const int *bs
     for (int l = 0; l < lb; ++l) {
         Level<T> &A = L[l];
         const double n = (double)A.nx * A.ny, nf = (double)(A.nx + 1) * A.ny + (double)A.nx * (A.ny + 1);
-        dim3 grid((A.nx + kTX - 1) / kTX, (A.ny + kTY - 1) / kTY);
         WEC_PROF("mg_pre", l, (2.25 * n + nf) * ts, st);
-        k_mg_pre<T><<<grid, 256, smem, st>>>(A.nx, A.ny, A.bu, A.bv, l == 0 ? b0 : A.b, A.xp, L[l + 1].b, P->nu1,
-                                             H, l == 0 ? bsel : nullptr);
+        launch_pre<T>(tiles[l], A, l == 0 ? b0 : A.b, L[l + 1].b, P->nu1, H, l == 0 ? bsel : nullptr, st);
     }
     {
         // algorithmic bytes: b and x of level lb, every level's coefficients, the LU
@@ -677,12 +718,89 @@ void vcycle_fused(wec_poisson *P, Level<T> *L, const T *b0, T *x0, const int *bs
     for (int l = lb - 1; l >= 0; --l) {
         Level<T> &A = L[l];
         const double n = (double)A.nx * A.ny, nf = (double)(A.nx + 1) * A.ny + (double)A.nx * (A.ny + 1);
-        dim3 grid((A.nx + kTX - 1) / kTX, (A.ny + kTY - 1) / kTY);
         WEC_PROF("mg_post", l, (3.25 * n + nf) * ts, st);
-        k_mg_post<T><<<grid, 256, smem, st>>>(A.nx, A.ny, A.bu, A.bv, l == 0 ? b0 : A.b, A.xp,
-                                              l == 0 ? x0 : A.x, L[l + 1].x, P->nu2, H, l == 0 ? bsel : nullptr,
-                                              l == 0 ? xsel : nullptr);
+        launch_post<T>(tiles[l], A, l == 0 ? b0 : A.b, l == 0 ? x0 : A.x, L[l + 1].x, P->nu2, H,
+                       l == 0 ? bsel : nullptr, l == 0 ? xsel : nullptr, st);
     }
+}
+
+bool g_mg_autotune = true;  // wec_set_option "mg_autotune"
+
+// Autotuner of the fused level kernels: on each non-coarsest level, time the
+// pre + post pair of every tile shape (3 runs each, CUDA events on the solver's
+// stream) and keep the fastest.  Runs once per solver, on placeholder
+// coefficients (all 1), before anything is captured.
+template <typename T>
+int autotune_levels(wec_poisson *P, Level<T> *L, int *tiles, cudaStream_t st)
+{
+    const int H = 2 * std::max(P->nu1, P->nu2);
+    cudaEvent_t e0, e1;
+    WEC_CK(cudaEventCreate(&e0));
+    WEC_CK(cudaEventCreate(&e1));
+    int rc = WEC_OK;
+    for (int l = 0; l + 1 < P->nlev && rc == WEC_OK; ++l) {
+        Level<T> &A = L[l];
+        const long long n = (long long)A.nx * A.ny;
+        T *b = l == 0 ? (T *)P->w : A.b;  // scratch stand-ins for the level-0 vectors
+        T *x = l == 0 ? (T *)P->w : A.x;
+        if (l == 0 && !A.b) cudaMemsetAsync(P->w, 0, n * sizeof(double), st);
+        float best = 1e30f;
+        tiles[l] = 0;
+        for (int t = 0; t < kNumTiles; ++t) {
+            float tmin = 1e30f;
+            for (int r = 0; r < 3; ++r) {
+                cudaEventRecord(e0, st);
+                launch_pre<T>(t, A, b, L[l + 1].b, P->nu1, H, nullptr, st);
+                launch_post<T>(t, A, b, x, L[l + 1].x, P->nu2, H, nullptr, nullptr, st);
+                cudaEventRecord(e1, st);
+                cudaError_t e = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (e != cudaSuccess) {
+                    rc = cuda_fail(e, "autotune timing");
+                    break;
+                }
+                if (r > 0) tmin = std::min(tmin, ms);  // first run warms up
+            }
+            if (rc != WEC_OK) break;
+            if (tmin < best) {
+                best = tmin;
+                tiles[l] = t;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
+}
+
+template <typename T>
+__global__ void k_fill(long long n, T *a, T v)
+{
+    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c < n) a[c] = v;
+}
+
+int poisson_autotune(wec_poisson *P, cudaStream_t st)
+{
+    for (int l = 0; l < kMaxLevels; ++l) P->tile64[l] = P->tile32[l] = 0;
+    if (!g_mg_autotune || P->nlev < 2) return WEC_OK;
+    // placeholder coefficients (the real ones are set before every solve)
+    for (int l = 0; l < P->nlev; ++l) {
+        long long nu = (long long)(P->L64[l].nx + 1) * P->L64[l].ny, nv = (long long)P->L64[l].nx * (P->L64[l].ny + 1);
+        k_fill<double><<<nblk(nu, 256), 256, 0, st>>>(nu, P->L64[l].bu, 1.0);
+        k_fill<double><<<nblk(nv, 256), 256, 0, st>>>(nv, P->L64[l].bv, 1.0);
+        if (P->prec == WEC_PREC_MIXED) {
+            k_fill<float><<<nblk(nu, 256), 256, 0, st>>>(nu, P->L32[l].bu, 1.0f);
+            k_fill<float><<<nblk(nv, 256), 256, 0, st>>>(nv, P->L32[l].bv, 1.0f);
+        }
+    }
+    int e = P->prec == WEC_PREC_FP64 ? autotune_levels<double>(P, P->L64, P->tile64, st)
+                                     : autotune_levels<float>(P, P->L32, P->tile32, st);
+    if (e) return e;
+    P->tuned = true;
+    WEC_CK(cudaStreamSynchronize(st));
+    return WEC_OK;
 }
 
 template <typename T>
@@ -696,7 +814,7 @@ void vcycle_t(wec_poisson *P, Level<T> *L, const T *b0, T *x0, const int *bsel, 
 
 int kgrid(long long n) { return (int)std::min<long long>(nblk(n, KT), kKrylovBlocks); }
 // the multi-dot kernels keep a few elements per thread: fewer blocks to sum at the end
-int kgrid_dots(long long n) { return (int)std::min<long long>(nblk(n, KT), kDotBlocks); }
+int kgrid_dots(long long n) { return (int)std::min<long long>(nblk(n, KT), kKrylovBlocks); }
 
 // ---------------------------------------------------------- FGMRES parts ----
 void enqueue_begin(wec_poisson *P, const double *b, double *x, double rtol, int maxit, unsigned long long hw,
@@ -799,16 +917,23 @@ int read_state(wec_poisson *P, cudaStream_t st)
 }  // namespace
 
 void set_mg_fused(bool on) { g_mg_fused = on; }
+void set_mg_autotune(bool on) { g_mg_autotune = on; }
+
+void poisson_tiles(const wec_poisson *P, int *tx, int *ty, int max)
+{
+    const int *t = P->prec == WEC_PREC_FP64 ? P->tile64 : P->tile32;
+    for (int l = 0; l < max && l < P->nlev; ++l) {
+        tx[l] = kTileX[t[l]];
+        ty[l] = kTileY[t[l]];
+    }
+}
 
 int poisson_init(wec_poisson *P, int nx, int ny, int prec, int restart, int nu1, int nu2, cudaStream_t st)
 {
     static bool attrs_done = false;
     if (!attrs_done) {
         // shared-memory tiles of the fused level kernels exceed the 48 KB default (H <= 8)
-        WEC_CK(cudaFuncSetAttribute(k_mg_pre<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem<double>(8)));
-        WEC_CK(cudaFuncSetAttribute(k_mg_post<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem<double>(8)));
-        WEC_CK(cudaFuncSetAttribute(k_mg_pre<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem<float>(8)));
-        WEC_CK(cudaFuncSetAttribute(k_mg_post<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem<float>(8)));
+        if (int e = set_tile_attrs()) return e;
         WEC_CK(cudaFuncSetAttribute(k_mg_bottom<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBottomSmemMax));
         WEC_CK(cudaFuncSetAttribute(k_mg_bottom<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBottomSmemMax));
         attrs_done = true;
@@ -876,7 +1001,7 @@ int poisson_init(wec_poisson *P, int nx, int ny, int prec, int restart, int nu1,
     WEC_CK(cudaMemset(P->ks, 0, sizeof(KState)));
     WEC_CK(cudaMallocHost(&P->ksh, sizeof(KState)));
     P->bytes += ((m + 1) * n + n) * 8 + m * n * (prec == WEC_PREC_FP64 ? 8 : 4);
-    return WEC_OK;
+    return poisson_autotune(P, st);
 }
 
 void poisson_free(wec_poisson *P)

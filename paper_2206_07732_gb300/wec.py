@@ -85,6 +85,7 @@ def load():
     L.wec_pressure_solve.argtypes = [vp, vp, vp, C.c_double, C.POINTER(C.c_int), _dp]
     L.wec_tank_use_graph.argtypes = [vp, C.c_int]
     L.wec_set_option.argtypes = [C.c_char_p, C.c_int]
+    L.wec_tank_mg_tiles.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_int, C.POINTER(C.c_int)]
     L.wec_launch_count.restype = C.c_longlong
     L.wec_profile_enable.argtypes = [C.c_int, C.c_char_p]
     L.wec_profile_read.argtypes = [C.c_int, C.c_char_p, C.c_size_t, C.POINTER(C.c_int), C.POINTER(C.c_longlong),
@@ -204,6 +205,11 @@ class Tank:
             self.h = None
 
     __del__ = close
+
+    def mg_tiles(self):
+        tx, ty, nl = (C.c_int * 32)(), (C.c_int * 32)(), C.c_int(0)
+        _check(load().wec_tank_mg_tiles(self.h, tx, ty, 32, C.byref(nl)))
+        return [(tx[k], ty[k]) for k in range(max(nl.value - 1, 0))]
 
     def use_graph(self, enable=True):
         _check(load().wec_tank_use_graph(self.h, 1 if enable else 0))
