@@ -128,6 +128,11 @@ int wec_tank_create(const wec_grid *grid, const wec_fluids *fl, const wec_waves 
     P.mu_s = fl->mu_w;
     P.ih = 1.0 / h;
     P.ikp = 1.0 / P.kappa_p;
+    P.cd = TankC<double>{P.h, P.ih, P.depth, P.g, P.rho_w, P.rho_a, P.rho_s, P.mu_w, P.mu_a, P.mu_s, P.ikp,
+                         P.bxc, P.bw, P.bh};
+    P.cf = TankC<float>{(float)P.h, (float)P.ih, (float)P.depth, (float)P.g, (float)P.rho_w, (float)P.rho_a,
+                        (float)P.rho_s, (float)P.mu_w, (float)P.mu_a, (float)P.mu_s, (float)P.ikp, (float)P.bxc,
+                        (float)P.bw, (float)P.bh};
     P.ncomp = wv->ncomp;
     int rc = WEC_OK;
     {

@@ -266,9 +266,14 @@ __device__ bool last_block(unsigned int *cnt)
 // Deterministic total of the G partials of one quantity.
 __device__ double final_sum(const double *part, int G, double *sh8)
 {
-    double s = 0.0;
-    for (int b = threadIdx.x; b < G; b += KT) s += __ldcg(part + b);
-    return block_sum(s, sh8);
+    double s0 = 0.0, s1 = 0.0;
+    int b = threadIdx.x;
+    for (; b + KT < G; b += 2 * KT) {
+        s0 += __ldcg(part + b);
+        s1 += __ldcg(part + b + KT);
+    }
+    for (; b < G; b += KT) s0 += __ldcg(part + b);
+    return block_sum(s0 + s1, sh8);
 }
 
 __device__ __forceinline__ void set_cond(unsigned long long h, int use, unsigned int v)
@@ -409,8 +414,18 @@ __device__ __forceinline__ void final_partials(const double *part, int nk, doubl
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, G = gridDim.x;
     for (int k = warp; k < nk; k += KT / 32) {
-        double s = 0.0;
-        for (int b = lane; b < G; b += 32) s += __ldcg(part + k * G + b);
+        // four independent chains so the loads overlap
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        const double *pk = part + k * G;
+        int b = lane;
+        for (; b + 96 < G; b += 128) {
+            s0 += __ldcg(pk + b);
+            s1 += __ldcg(pk + b + 32);
+            s2 += __ldcg(pk + b + 64);
+            s3 += __ldcg(pk + b + 96);
+        }
+        for (; b < G; b += 32) s0 += __ldcg(pk + b);
+        double s = (s0 + s1) + (s2 + s3);
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
         if (lane == 0) out[k] = s;
     }
@@ -812,9 +827,9 @@ void vcycle_t(wec_poisson *P, Level<T> *L, const T *b0, T *x0, const int *bsel, 
         vcycle_unfused<T>(P, L, b0, x0, bsel, xsel, st);
 }
 
-int kgrid(long long n) { return (int)std::min<long long>(nblk(n, KT), kKrylovBlocks); }
+int kgrid(long long n) { return (int)std::min<long long>(nblk(n, KT), kDotBlocks); }
 // the multi-dot kernels keep a few elements per thread: fewer blocks to sum at the end
-int kgrid_dots(long long n) { return (int)std::min<long long>(nblk(n, KT), kKrylovBlocks); }
+int kgrid_dots(long long n) { return (int)std::min<long long>(nblk(n, KT), kDotBlocks); }
 
 // ---------------------------------------------------------- FGMRES parts ----
 void enqueue_begin(wec_poisson *P, const double *b, double *x, double rtol, int maxit, unsigned long long hw,
@@ -1020,32 +1035,41 @@ void poisson_free(wec_poisson *P)
 
 int poisson_build(wec_poisson *P, cudaStream_t st)
 {
-    for (int l = 0; l + 1 < P->nlev; ++l) {
-        Level<double> &F = P->L64[l], &C = P->L64[l + 1];
-        int cnt = (C.nx + 1) * C.ny + C.nx * (C.ny + 1);
-        WEC_PROF("mg_coarsen", l, 24.0 * cnt, st);
-        k_coarsen<double><<<nblk(cnt, 256), 256, 0, st>>>(F.nx, F.ny, F.bu, F.bv, C.bu, C.bv);
-    }
-    Level<double> &Lc = P->L64[P->nlev - 1];
-    {
-        const double nn = (double)Lc.nx * Lc.ny;
-        WEC_PROF("mg_lu_factor", P->nlev - 1, 8.0 * nn * nn, st);
-        k_lu_factor<double><<<1, 256, 0, st>>>(Lc.nx, Lc.ny, Lc.bu, Lc.bv, P->lu64);
-    }
     if (P->prec == WEC_PREC_MIXED) {
-        for (int l = 0; l < P->nlev; ++l) {
-            long long nu = (long long)(P->L64[l].nx + 1) * P->L64[l].ny, nv = (long long)P->L64[l].nx * (P->L64[l].ny + 1);
-            {
-                WEC_PROF("convert", l, 12.0 * nu, st);
-                k_convert<float, double><<<nblk(nu, 256), 256, 0, st>>>(nu, P->L64[l].bu, P->L32[l].bu, nullptr);
-            }
-            WEC_PROF("convert", l, 12.0 * nv, st);
-            k_convert<float, double><<<nblk(nv, 256), 256, 0, st>>>(nv, P->L64[l].bv, P->L32[l].bv, nullptr);
+        // the V-cycle is FP32 throughout: level 0 converted once, coarse levels
+        // and the coarsest LU formed in FP32 (the FP64 operator is level 0 only)
+        Level<double> &A = P->L64[0];
+        Level<float> &F = P->L32[0];
+        const long long nu = (long long)(A.nx + 1) * A.ny, nv = (long long)A.nx * (A.ny + 1);
+        {
+            WEC_PROF("convert", 0, 12.0 * nu, st);
+            k_convert<float, double><<<nblk(nu, 256), 256, 0, st>>>(nu, A.bu, F.bu, nullptr);
+        }
+        {
+            WEC_PROF("convert", 0, 12.0 * nv, st);
+            k_convert<float, double><<<nblk(nv, 256), 256, 0, st>>>(nv, A.bv, F.bv, nullptr);
+        }
+        for (int l = 0; l + 1 < P->nlev; ++l) {
+            Level<float> &Fl = P->L32[l], &C = P->L32[l + 1];
+            int cnt = (C.nx + 1) * C.ny + C.nx * (C.ny + 1);
+            WEC_PROF("mg_coarsen", l, 12.0 * cnt, st);
+            k_coarsen<float><<<nblk(cnt, 256), 256, 0, st>>>(Fl.nx, Fl.ny, Fl.bu, Fl.bv, C.bu, C.bv);
         }
         Level<float> &Lf = P->L32[P->nlev - 1];
         const double nn = (double)Lf.nx * Lf.ny;
         WEC_PROF("mg_lu_factor", P->nlev - 1, 4.0 * nn * nn, st);
         k_lu_factor<float><<<1, 256, 0, st>>>(Lf.nx, Lf.ny, Lf.bu, Lf.bv, P->lu32);
+    } else {
+        for (int l = 0; l + 1 < P->nlev; ++l) {
+            Level<double> &F = P->L64[l], &C = P->L64[l + 1];
+            int cnt = (C.nx + 1) * C.ny + C.nx * (C.ny + 1);
+            WEC_PROF("mg_coarsen", l, 24.0 * cnt, st);
+            k_coarsen<double><<<nblk(cnt, 256), 256, 0, st>>>(F.nx, F.ny, F.bu, F.bv, C.bu, C.bv);
+        }
+        Level<double> &Lc = P->L64[P->nlev - 1];
+        const double nn = (double)Lc.nx * Lc.ny;
+        WEC_PROF("mg_lu_factor", P->nlev - 1, 8.0 * nn * nn, st);
+        k_lu_factor<double><<<1, 256, 0, st>>>(Lc.nx, Lc.ny, Lc.bu, Lc.bv, P->lu64);
     }
     WEC_CK(cudaGetLastError());
     P->have_coef = true;

@@ -28,22 +28,34 @@ namespace {
 
 constexpr int TB = 256;
 
+template <typename R>
+__device__ __forceinline__ const TankC<R> &cst(const TankP &P)
+{
+    if constexpr (sizeof(R) == 4)
+        return P.cf;
+    else
+        return P.cd;
+}
+
 __device__ __forceinline__ int clampi(int a, int lo, int hi) { return a < lo ? lo : (a > hi ? hi : a); }
-__device__ __forceinline__ double sq(double a) { return a * a; }
+template <typename R>
+__device__ __forceinline__ R sq(R a) { return a * a; }
 
 // Smoothed Heaviside of Eqs. Hflow / Hbody, half-width eps = n_cells h (n_cells = 1).
-__device__ __forceinline__ double heav(double phi, double eps)
+template <typename R>
+__device__ __forceinline__ R heav(R phi, R eps)
 {
-    if (phi < -eps) return 0.0;
-    if (phi > eps) return 1.0;
-    return 0.5 * (1.0 + phi / eps + sin(kPi * phi / eps) / kPi);
+    if (phi < -eps) return R(0.0);
+    if (phi > eps) return R(1.0);
+    return R(0.5) * (R(1.0) + phi / eps + sin(R(kPi) * phi / eps) / R(kPi));
 }
 
 // Box SDF as the CSG intersection (max) of four half-planes.
-__device__ __forceinline__ double psi_box(const TankP &P, double x, double y, double yc)
+template <typename R>
+__device__ __forceinline__ R psi_box(const TankP &P, R x, R y, R yc)
 {
-    if (!P.has_body) return 1.0e3;
-    return fmax(fabs(x - P.bxc) - 0.5 * P.bw, fabs(y - yc) - 0.5 * P.bh);
+    if (!P.has_body) return R(1.0e3);
+    return fmax(fabs(x - cst<R>(P).bxc) - R(0.5) * cst<R>(P).bw, fabs(y - yc) - R(0.5) * cst<R>(P).bh);
 }
 
 __device__ double eta_at(const TankP &P, double x, double t)
@@ -77,85 +89,92 @@ __device__ void airy_uv(const TankP &P, double x, double y, double t, double *uo
 // -------------------------------------------------------- ghost values ----
 // sigma: left = incident wave y - d - eta(x, t) (eta precomputed per ghost column),
 // right = zero gradient, bottom/top = linear extrapolation.
-__device__ __forceinline__ double sig_at(const TankP &P, const double *__restrict__ s,
+template <typename R, typename S>
+__device__ __forceinline__ R sig_at(const TankP &P, const S *__restrict__ s,
                                          const double *__restrict__ etag, int i, int j)
 {
-    if (i < 0) return (j + 0.5) * P.h - P.depth - etag[-1 - i];
+    if (i < 0) return (j + R(0.5)) * cst<R>(P).h - cst<R>(P).depth - R(etag[-1 - i]);
     if (i > P.nx - 1) i = P.nx - 1;
-    if (j < 0) return s[i] + j * (s[P.nx + i] - s[i]);
+    if (j < 0) return R(s[i]) + j * (R(s[P.nx + i]) - R(s[i]));
     if (j > P.ny - 1) {
         int m = j - (P.ny - 1);
-        double a = s[(P.ny - 1) * P.nx + i], b = s[(P.ny - 2) * P.nx + i];
+        R a = R(s[(P.ny - 1) * P.nx + i]), b = R(s[(P.ny - 2) * P.nx + i]);
         return a + m * (a - b);
     }
-    return s[j * P.nx + i];
+    return R(s[j * P.nx + i]);
 }
 
-__device__ __forceinline__ double u_at(const TankP &P, const double *__restrict__ u, int i, int j)
+template <typename R, typename S>
+__device__ __forceinline__ R u_at(const TankP &P, const S *__restrict__ u, int i, int j)
 {
-    return u[clampi(j, 0, P.ny - 1) * (P.nx + 1) + clampi(i, 0, P.nx)];
+    return R(u[clampi(j, 0, P.ny - 1) * (P.nx + 1) + clampi(i, 0, P.nx)]);
 }
 
 // v: clamp rows; right wall free slip; left: odd reflection about v_in(y_j, t).
-__device__ __forceinline__ double v_at(const TankP &P, const double *__restrict__ v,
+template <typename R, typename S>
+__device__ __forceinline__ R v_at(const TankP &P, const S *__restrict__ v,
                                        const double *__restrict__ vin, int i, int j)
 {
     j = clampi(j, 0, P.ny);
     if (i > P.nx - 1) i = P.nx - 1;
-    if (i < 0) return 2.0 * vin[j] - v[j * P.nx + (-1 - i)];
-    return v[j * P.nx + i];
+    if (i < 0) return R(2.0) * R(vin[j]) - R(v[j * P.nx + (-1 - i)]);
+    return R(v[j * P.nx + i]);
 }
 
-__device__ __forceinline__ double cell_at(const TankP &P, const double *__restrict__ a, int i, int j)
+template <typename R, typename S>
+__device__ __forceinline__ R cell_at(const TankP &P, const S *__restrict__ a, int i, int j)
 {
-    return a[clampi(j, 0, P.ny - 1) * P.nx + clampi(i, 0, P.nx - 1)];
+    return R(a[clampi(j, 0, P.ny - 1) * P.nx + clampi(i, 0, P.nx - 1)]);
 }
 
 // ----------------------------------------------------------------- PPM ----
-__device__ __forceinline__ double vl_slope(double am, double a0, double ap)
+template <typename R>
+__device__ __forceinline__ R vl_slope(R am, R a0, R ap)
 {
-    double dl = a0 - am, dr = ap - a0;
-    if (dl * dr <= 0.0) return 0.0;
-    double dc = 0.5 * (ap - am);
-    double m = fmin(fabs(dc), fmin(2.0 * fabs(dl), 2.0 * fabs(dr)));
-    return dc > 0.0 ? m : -m;
+    R dl = a0 - am, dr = ap - a0;
+    if (dl * dr <= R(0.0)) return R(0.0);
+    R dc = R(0.5) * (ap - am);
+    R m = fmin(fabs(dc), fmin(R(2.0) * fabs(dl), R(2.0) * fabs(dr)));
+    return dc > R(0.0) ? m : -m;
 }
 
-// Limited Colella-Woodward edge values of the middle cell of a[0..4].
-__device__ __forceinline__ void ppm_edges(const double *a, double &L, double &R)
+// Limited Colella-Woodward edge values (left eL, right eR) of the middle cell of a[0..4].
+template <typename R>
+__device__ __forceinline__ void ppm_edges(const R *a, R &eL, R &eR)
 {
-    double dm = vl_slope(a[0], a[1], a[2]);
-    double d0 = vl_slope(a[1], a[2], a[3]);
-    double dp = vl_slope(a[2], a[3], a[4]);
-    L = a[1] + 0.5 * (a[2] - a[1]) - (d0 - dm) * (1.0 / 6.0);
-    R = a[2] + 0.5 * (a[3] - a[2]) - (dp - d0) * (1.0 / 6.0);
-    double c = a[2];
-    if ((R - c) * (c - L) <= 0.0) {
-        L = c;
-        R = c;
+    R dm = vl_slope<R>(a[0], a[1], a[2]);
+    R d0 = vl_slope<R>(a[1], a[2], a[3]);
+    R dp = vl_slope<R>(a[2], a[3], a[4]);
+    eL = a[1] + R(0.5) * (a[2] - a[1]) - (d0 - dm) * (R(1.0) / R(6.0));
+    eR = a[2] + R(0.5) * (a[3] - a[2]) - (dp - d0) * (R(1.0) / R(6.0));
+    R c = a[2];
+    if ((eR - c) * (c - eL) <= R(0.0)) {
+        eL = c;
+        eR = c;
     } else {
-        double dA = R - L;
-        double m6 = dA * (c - 0.5 * (L + R));
-        double q = dA * dA * (1.0 / 6.0);
+        R dA = eR - eL;
+        R m6 = dA * (c - R(0.5) * (eL + eR));
+        R q = dA * dA * (R(1.0) / R(6.0));
         if (m6 > q)
-            L = 3.0 * c - 2.0 * R;
+            eL = R(3.0) * c - R(2.0) * eR;
         else if (-q > m6)
-            R = 3.0 * c - 2.0 * L;
+            eR = R(3.0) * c - R(2.0) * eL;
     }
 }
 
 // Time-centred upwind face state; a[0..5] = cells f-3..f+2 around face f.
-__device__ __forceinline__ double ppm_face(const double *a, double vel, double dt, double ih)
+template <typename R>
+__device__ __forceinline__ R ppm_face(const R *a, R vel, R dt, R ih)
 {
-    double L, R;
-    if (vel >= 0.0) {
-        ppm_edges(a, L, R);
-        double C = vel * dt * ih, dA = R - L, a6 = 6.0 * (a[2] - 0.5 * (L + R));
-        return R - 0.5 * C * (dA - (1.0 - C * (2.0 / 3.0)) * a6);
+    R eL, eR;
+    if (vel >= R(0.0)) {
+        ppm_edges<R>(a, eL, eR);
+        R C = vel * dt * ih, dA = eR - eL, a6 = R(6.0) * (a[2] - R(0.5) * (eL + eR));
+        return eR - R(0.5) * C * (dA - (R(1.0) - C * (R(2.0) / R(3.0))) * a6);
     }
-    ppm_edges(a + 1, L, R);
-    double C = -vel * dt * ih, dA = R - L, a6 = 6.0 * (a[3] - 0.5 * (L + R));
-    return L + 0.5 * C * (dA + (1.0 - C * (2.0 / 3.0)) * a6);
+    ppm_edges<R>(a + 1, eL, eR);
+    R C = -vel * dt * ih, dA = eR - eL, a6 = R(6.0) * (a[3] - R(0.5) * (eL + eR));
+    return eL + R(0.5) * C * (dA + (R(1.0) - C * (R(2.0) / R(3.0))) * a6);
 }
 
 // Damping-zone weight (Jacobsen) and the vorticity-damping shape (cos(pi z~) + 1),
@@ -177,32 +196,37 @@ __device__ __forceinline__ double vort_shape_eval(const TankP &P, double y)
 }
 
 // g(z~) = rho_a (cos(pi z~) + 1) / (4 dt) (Eq. spongelayer) from the tabulated shape.
-__device__ __forceinline__ double vort_damp(const TankP &P, double shape, double idt)
+template <typename R>
+__device__ __forceinline__ R vort_damp(const TankP &P, R shape, R idt)
 {
-    return P.rho_a * shape * (0.25 * idt);
+    return cst<R>(P).rho_a * shape * (R(0.25) * idt);
 }
 
-__device__ __forceinline__ double minmod(double a, double b)
+template <typename R>
+__device__ __forceinline__ R minmod(R a, R b)
 {
-    if (a * b <= 0.0) return 0.0;
+    if (a * b <= R(0.0)) return R(0.0);
     return fabs(a) < fabs(b) ? a : b;
 }
 
-__device__ __forceinline__ double koren(double quu, double qu, double qd)
+template <typename R>
+__device__ __forceinline__ R koren(R quu, R qu, R qd)
 {
-    double d1 = qu - quu, d2 = qd - qu;
-    if (d1 * d2 <= 0.0) return qu;
-    double m = fmin(2.0 * fabs(d2), fmin((fabs(d1) + 2.0 * fabs(d2)) * (1.0 / 3.0), 2.0 * fabs(d1)));
-    return d1 > 0.0 ? qu + 0.5 * m : qu - 0.5 * m;
+    R d1 = qu - quu, d2 = qd - qu;
+    if (d1 * d2 <= R(0.0)) return qu;
+    R m = fmin(R(2.0) * fabs(d2), fmin((fabs(d1) + R(2.0) * fabs(d2)) * (R(1.0) / R(3.0)), R(2.0) * fabs(d1)));
+    return d1 > R(0.0) ? qu + R(0.5) * m : qu - R(0.5) * m;
 }
 
-__device__ __forceinline__ double upwind(double q0, double q1, double q2, double q3, double vel)
+template <typename R>
+__device__ __forceinline__ R upwind(R q0, R q1, R q2, R q3, R vel)
 {
-    return vel >= 0.0 ? koren(q0, q1, q2) : koren(q3, q2, q1);
+    return vel >= R(0.0) ? koren<R>(q0, q1, q2) : koren<R>(q3, q2, q1);
 }
 
 // ------------------------------------------------------------- kernels ----
-__device__ __forceinline__ double warp_sum_d(double v)
+template <typename R>
+__device__ __forceinline__ R warp_sum_d(R v)
 {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
@@ -229,30 +253,41 @@ __global__ void k_bc_eta(TankP P, const StepScalars *S, const double *__restrict
 // Inflow at x = 0: u_in(y_{j+1/2}, t^{n+1}) and v_in(y_j, t^n), v_in(y_j, t^{n+1}),
 // Airy velocities with Wheeler stretching, blended to zero in the air.  One warp
 // per row j, lanes over the components.
+template <typename R>
 __global__ void k_bc_rows(TankP P, const StepScalars *S, const double *__restrict__ inp, Bc bc)
 {
     const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (j > P.ny) return;
-    const double t0 = S->t, t1 = S->t + inp[0], d = P.depth;
-    double out[3];
+    const R t0 = R(S->t), t1 = R(S->t) + R(inp[0]), d = cst<R>(P).depth;
+    R out[3];
     for (int q = 0; q < 3; ++q) {
-        const double t = q == 1 ? t0 : t1;
-        const double y = q == 0 ? (j + 0.5) * P.h : j * P.h;
-        const double e = bc.eta_in[q == 1 ? 0 : 1];
-        const double ys = y < d + e ? y : d + e;
-        const double yp = d * ys / (d + e);
-        double acc = 0.0;
+        const R t = q == 1 ? t0 : t1;
+        const R y = q == 0 ? (j + R(0.5)) * cst<R>(P).h : j * cst<R>(P).h;
+        const R e = R(bc.eta_in[q == 1 ? 0 : 1]);
+        const R ys = y < d + e ? y : d + e;
+        const R yp = d * ys / (d + e);
+        R acc = R(0.0);
         for (int c = lane; c < P.ncomp; c += 32) {
-            double k = P.kw[c], w = P.omega[c];
-            double ph = -w * t + P.phase[c];
-            double sk = sinh(k * d);
+            R k = R(P.kw[c]), w = R(P.omega[c]);
+            R ph = -w * t + R(P.phase[c]);
+            R ch, sh;  // cosh(k y') / sinh(k d) and sinh(k y') / sinh(k d)
+            if constexpr (sizeof(R) == 4) {
+                // overflow-free in FP32 (k d reaches ~120 for short components)
+                R e1 = exp(k * (yp - d)), e2 = exp(-k * (yp + d)), den = R(1.0) - exp(R(-2.0) * k * d);
+                ch = (e1 + e2) / den;
+                sh = (e1 - e2) / den;
+            } else {
+                R sk = sinh(k * d);
+                ch = cosh(k * yp) / sk;
+                sh = sinh(k * yp) / sk;
+            }
             if (q == 0)
-                acc += P.amp[c] * w * cosh(k * yp) / sk * cos(ph);
+                acc += R(P.amp[c]) * w * ch * cos(ph);
             else
-                acc += P.amp[c] * w * sinh(k * yp) / sk * sin(ph);
+                acc += R(P.amp[c]) * w * sh * sin(ph);
         }
-        acc = warp_sum_d(acc);
-        out[q] = (1.0 - heav(y - d - e, P.h)) * acc;
+        acc = warp_sum_d<R>(acc);
+        out[q] = (R(1.0) - heav<R>(y - d - e, cst<R>(P).h)) * acc;
     }
     if (lane) return;
     if (j < P.ny) bc.uin1[j] = out[0];
@@ -261,21 +296,22 @@ __global__ void k_bc_rows(TankP P, const StepScalars *S, const double *__restric
 }
 
 // Cell materials from sigma and the body at yc (which = 0: y_c^n, 1: y_c^{n+1}).
+template <typename R>
 __global__ void k_materials(TankP P, const StepScalars *S, int which, const double *__restrict__ sig,
-                            double *rho, double *mu, double *rhof, double *chi)
+                            R *rho, R *mu, R *rhof, R *chi)
 {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= P.nx * P.ny) return;
     int i = c % P.nx, j = c / P.nx;
-    double yc = which ? S->yc1 : S->yc;
-    double ps = psi_box(P, (i + 0.5) * P.h, (j + 0.5) * P.h, yc);
-    double hf = heav(sig[c], P.h), hb = heav(ps, P.h);
-    double rf = P.rho_w + (P.rho_a - P.rho_w) * hf;
-    double mf = P.mu_w + (P.mu_a - P.mu_w) * hf;
-    if (rho) rho[c] = P.rho_s + (rf - P.rho_s) * hb;
-    if (mu) mu[c] = P.mu_s + (mf - P.mu_s) * hb;
+    R yc = which ? R(S->yc1) : R(S->yc);
+    R ps = psi_box<R>(P, (i + R(0.5)) * cst<R>(P).h, (j + R(0.5)) * cst<R>(P).h, yc);
+    R hf = heav<R>(R(sig[c]), cst<R>(P).h), hb = heav<R>(ps, cst<R>(P).h);
+    R rf = cst<R>(P).rho_w + (cst<R>(P).rho_a - cst<R>(P).rho_w) * hf;
+    R mf = cst<R>(P).mu_w + (cst<R>(P).mu_a - cst<R>(P).mu_w) * hf;
+    if (rho) rho[c] = cst<R>(P).rho_s + (rf - cst<R>(P).rho_s) * hb;
+    if (mu) mu[c] = cst<R>(P).mu_s + (mf - cst<R>(P).mu_s) * hb;
     if (rhof) rhof[c] = rf;
-    if (chi) chi[c] = 1.0 - hb;
+    if (chi) chi[c] = R(1.0) - hb;
 }
 
 __device__ double block_sum(double v, double *sh)
@@ -295,41 +331,52 @@ __device__ double block_sum(double v, double *sh)
 // Eq. int_fh, heave component: faces whose two cells have opposite psi sign;
 // pressure linearly interpolated to the psi = 0 crossing with |psi| weights;
 // n_f out of the body; viscous traction by central differences at the face.
+template <typename M>
 __global__ void k_force_partial(TankP P, const StepScalars *S, const double *__restrict__ p,
                                 const double *__restrict__ u, const double *__restrict__ v,
-                                const double *__restrict__ mu, const double *__restrict__ vin0,
+                                const M *__restrict__ mu, const double *__restrict__ vin0,
                                 double *__restrict__ part)
 {
     __shared__ double sh[TB];
     const int nx = P.nx, ny = P.ny;
     const double h = P.h, yc = S->yc;
-    long long ny_faces = (long long)(ny - 1) * nx, nx_faces = (long long)ny * (nx - 1);
+    // Only faces whose two cells straddle the box boundary contribute, and those
+    // cells lie within one cell of it: walk cells i0..i1 x j0..j1, two cells
+    // around the box (the same nonzero terms as a walk over every face).
+    const int i0 = max(0, (int)floor((P.bxc - 0.5 * P.bw) / h) - 2);
+    const int i1 = min(nx - 1, (int)ceil((P.bxc + 0.5 * P.bw) / h) + 2);
+    const int j0 = max(0, (int)floor((yc - 0.5 * P.bh) / h) - 2);
+    const int j1 = min(ny - 1, (int)ceil((yc + 0.5 * P.bh) / h) + 2);
+    const int bi = i1 - i0 + 1, bj = j1 - j0 + 1;
+    // y-faces: j in j0+1..j1, i in i0..i1; x-faces: i in i0+1..i1, j in j0..j1
+    const long long ny_faces = bi > 0 && bj > 1 ? (long long)bi * (bj - 1) : 0;
+    const long long nx_faces = bi > 1 && bj > 0 ? (long long)(bi - 1) * bj : 0;
     double acc = 0.0;
     if (P.has_body) {
         for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < ny_faces + nx_faces;
              k += (long long)gridDim.x * blockDim.x) {
             if (k < ny_faces) {
-                int i = (int)(k % nx), j = (int)(k / nx) + 1;
+                int i = i0 + (int)(k % bi), j = j0 + 1 + (int)(k / bi);
                 double x = (i + 0.5) * h;
                 double pl = psi_box(P, x, (j - 0.5) * h, yc), pr = psi_box(P, x, (j + 0.5) * h, yc);
                 if (!(pl * pr < 0.0)) continue;
                 double nrm = pl < 0.0 ? 1.0 : -1.0;
                 double wl = fabs(pl), wr = fabs(pr);
                 double pf = (p[(j - 1) * nx + i] * wr + p[j * nx + i] * wl) / (wl + wr);
-                double muf = 0.5 * (mu[(j - 1) * nx + i] + mu[j * nx + i]);
-                double dvdy = (v_at(P, v, vin0, i, j + 1) - v_at(P, v, vin0, i, j - 1)) / (2.0 * h);
+                double muf = 0.5 * (double(mu[(j - 1) * nx + i]) + double(mu[j * nx + i]));
+                double dvdy = (v_at<double>(P, v, vin0, i, j + 1) - v_at<double>(P, v, vin0, i, j - 1)) / (2.0 * h);
                 acc += (-pf * nrm + muf * 2.0 * dvdy * nrm) * h;
             } else {
                 long long q = k - ny_faces;
-                int i = (int)(q % (nx - 1)) + 1, j = (int)(q / (nx - 1));
+                int i = i0 + 1 + (int)(q % (bi - 1)), j = j0 + (int)(q / (bi - 1));
                 double y = (j + 0.5) * h;
                 double pl = psi_box(P, (i - 0.5) * h, y, yc), pr = psi_box(P, (i + 0.5) * h, y, yc);
                 if (!(pl * pr < 0.0)) continue;
                 double nrm = pl < 0.0 ? 1.0 : -1.0;
-                double muf = 0.5 * (mu[j * nx + i - 1] + mu[j * nx + i]);
-                double dvdx = 0.5 * ((v_at(P, v, vin0, i, j) - v_at(P, v, vin0, i - 1, j)) +
-                                     (v_at(P, v, vin0, i, j + 1) - v_at(P, v, vin0, i - 1, j + 1))) / h;
-                double dudy = (u_at(P, u, i, j + 1) - u_at(P, u, i, j - 1)) / (2.0 * h);
+                double muf = 0.5 * (double(mu[j * nx + i - 1]) + double(mu[j * nx + i]));
+                double dvdx = 0.5 * ((v_at<double>(P, v, vin0, i, j) - v_at<double>(P, v, vin0, i - 1, j)) +
+                                     (v_at<double>(P, v, vin0, i, j + 1) - v_at<double>(P, v, vin0, i - 1, j + 1))) / h;
+                double dudy = (u_at<double>(P, u, i, j + 1) - u_at<double>(P, u, i, j - 1)) / (2.0 * h);
                 acc += muf * (dvdx + dudy) * nrm * h;
             }
         }
@@ -362,326 +409,376 @@ __global__ void k_heave(TankP P, StepScalars *S, const double *__restrict__ part
 }
 
 // sigma* = sigma^n - dt Q(u^n, sigma^n), then damping-zone relaxation.
-__global__ void k_advect(TankP P, const double *__restrict__ s, const double *__restrict__ u,
-                         const double *__restrict__ v, const double *__restrict__ eta0,
-                         const double *__restrict__ inp, const double *__restrict__ alpha_c,
-                         double *__restrict__ out)
+template <typename R>
+__global__ void k_advect(TankP P, const R *__restrict__ s, const R *__restrict__ u,
+                         const R *__restrict__ v, const double *__restrict__ eta0,
+                         const double *__restrict__ inp, const R *__restrict__ alpha_c,
+                         double *__restrict__ out, R *__restrict__ out_w)
 {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= P.nx * P.ny) return;
-    const double dt = inp[0];
+    const R dt = R(inp[0]);
     const int nx = P.nx, i = c % nx, j = c / nx;
-    const double h = P.h;
-    double a[6], fx[2], fy[2];
+    const R h = cst<R>(P).h;
+    R a[6], fx[2], fy[2];
     for (int f = 0; f < 2; ++f) {
         int fi = i + f;
-        for (int q = 0; q < 6; ++q) a[q] = sig_at(P, s, eta0, fi - 3 + q, j);
-        fx[f] = ppm_face(a, u[j * (nx + 1) + fi], dt, P.ih);
+        for (int q = 0; q < 6; ++q) a[q] = sig_at<R>(P, s, eta0, fi - 3 + q, j);
+        fx[f] = ppm_face<R>(a, R(u[j * (nx + 1) + fi]), dt, cst<R>(P).ih);
         int fj = j + f;
-        for (int q = 0; q < 6; ++q) a[q] = sig_at(P, s, eta0, i, fj - 3 + q);
-        fy[f] = ppm_face(a, v[fj * nx + i], dt, P.ih);
+        for (int q = 0; q < 6; ++q) a[q] = sig_at<R>(P, s, eta0, i, fj - 3 + q);
+        fy[f] = ppm_face<R>(a, R(v[fj * nx + i]), dt, cst<R>(P).ih);
     }
-    double ub = 0.5 * (u[j * (nx + 1) + i] + u[j * (nx + 1) + i + 1]);
-    double vb = 0.5 * (v[j * nx + i] + v[(j + 1) * nx + i]);
-    double Q = ub * (fx[1] - fx[0]) * P.ih + vb * (fy[1] - fy[0]) * P.ih;
-    double sa = s[c] - dt * Q;
-    double al = alpha_c[i];
-    out[c] = (1.0 - al) * sa + al * ((j + 0.5) * h - P.depth);
+    R ub = R(0.5) * (R(u[j * (nx + 1) + i]) + R(u[j * (nx + 1) + i + 1]));
+    R vb = R(0.5) * (R(v[j * nx + i]) + R(v[(j + 1) * nx + i]));
+    R Q = ub * (fx[1] - fx[0]) * cst<R>(P).ih + vb * (fy[1] - fy[0]) * cst<R>(P).ih;
+    R sa = R(s[c]) - dt * Q;
+    R al = alpha_c[i];
+    const R r = (R(1.0) - al) * sa + al * ((j + R(0.5)) * h - cst<R>(P).depth);
+    out[c] = r;
+    if (out_w) out_w[c] = r;
 }
 
 // Sussman relaxation right-hand side S(sigma0)(|grad f| - 1), Godunov
 // Hamiltonian on ENO-2 (minmod) one-sided differences.
-__device__ double reinit_rhs(const TankP &P, const double *__restrict__ f, const double *__restrict__ sgn,
+template <typename R>
+__device__ R reinit_rhs(const TankP &P, const R *__restrict__ f, const R *__restrict__ sgn,
                              const double *__restrict__ eta1, int i, int j)
 {
-    const double ih = P.ih, ih2 = 0.5 * P.ih;
-    double c = f[j * P.nx + i];
-    double xm2 = sig_at(P, f, eta1, i - 2, j), xm1 = sig_at(P, f, eta1, i - 1, j);
-    double xp1 = sig_at(P, f, eta1, i + 1, j), xp2 = sig_at(P, f, eta1, i + 2, j);
-    double ym2 = sig_at(P, f, eta1, i, j - 2), ym1 = sig_at(P, f, eta1, i, j - 1);
-    double yp1 = sig_at(P, f, eta1, i, j + 1), yp2 = sig_at(P, f, eta1, i, j + 2);
-    double dxm = xm2 - 2.0 * xm1 + c, dx0 = xm1 - 2.0 * c + xp1, dxp = c - 2.0 * xp1 + xp2;
-    double dym = ym2 - 2.0 * ym1 + c, dy0 = ym1 - 2.0 * c + yp1, dyp = c - 2.0 * yp1 + yp2;
-    double a = (c - xm1) * ih + minmod(dxm, dx0) * ih2;
-    double b = (xp1 - c) * ih - minmod(dx0, dxp) * ih2;
-    double cc = (c - ym1) * ih + minmod(dym, dy0) * ih2;
-    double d = (yp1 - c) * ih - minmod(dy0, dyp) * ih2;
-    double S = sgn[j * P.nx + i];
-    double gx, gy;
-    if (S > 0.0) {
-        gx = fmax(sq(fmax(a, 0.0)), sq(fmin(b, 0.0)));
-        gy = fmax(sq(fmax(cc, 0.0)), sq(fmin(d, 0.0)));
+    const R ih = cst<R>(P).ih, ih2 = R(0.5) * cst<R>(P).ih;
+    R c = R(f[j * P.nx + i]);
+    R xm2 = sig_at<R>(P, f, eta1, i - 2, j), xm1 = sig_at<R>(P, f, eta1, i - 1, j);
+    R xp1 = sig_at<R>(P, f, eta1, i + 1, j), xp2 = sig_at<R>(P, f, eta1, i + 2, j);
+    R ym2 = sig_at<R>(P, f, eta1, i, j - 2), ym1 = sig_at<R>(P, f, eta1, i, j - 1);
+    R yp1 = sig_at<R>(P, f, eta1, i, j + 1), yp2 = sig_at<R>(P, f, eta1, i, j + 2);
+    R dxm = xm2 - R(2.0) * xm1 + c, dx0 = xm1 - R(2.0) * c + xp1, dxp = c - R(2.0) * xp1 + xp2;
+    R dym = ym2 - R(2.0) * ym1 + c, dy0 = ym1 - R(2.0) * c + yp1, dyp = c - R(2.0) * yp1 + yp2;
+    R a = (c - xm1) * ih + minmod<R>(dxm, dx0) * ih2;
+    R b = (xp1 - c) * ih - minmod<R>(dx0, dxp) * ih2;
+    R cc = (c - ym1) * ih + minmod<R>(dym, dy0) * ih2;
+    R d = (yp1 - c) * ih - minmod<R>(dy0, dyp) * ih2;
+    R S = R(sgn[j * P.nx + i]);
+    R gx, gy;
+    if (S > R(0.0)) {
+        gx = fmax(sq<R>(fmax(a, R(0.0))), sq<R>(fmin(b, R(0.0))));
+        gy = fmax(sq<R>(fmax(cc, R(0.0))), sq<R>(fmin(d, R(0.0))));
     } else {
-        gx = fmax(sq(fmin(a, 0.0)), sq(fmax(b, 0.0)));
-        gy = fmax(sq(fmin(cc, 0.0)), sq(fmax(d, 0.0)));
+        gx = fmax(sq<R>(fmin(a, R(0.0))), sq<R>(fmax(b, R(0.0))));
+        gy = fmax(sq<R>(fmin(cc, R(0.0))), sq<R>(fmax(d, R(0.0))));
     }
-    return S * (sqrt(gx + gy) - 1.0);
+    return S * (sqrt(gx + gy) - R(1.0));
 }
 
 // Smoothed sign S(sigma0) = sigma0 / sqrt(sigma0^2 + h^2), fixed over the pseudo-steps.
-__global__ void k_reinit_sign(TankP P, const double *__restrict__ s0, double *__restrict__ sgn)
+template <typename R>
+__global__ void k_reinit_sign(TankP P, const R *__restrict__ s0, R *__restrict__ sgn)
 {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= P.nx * P.ny) return;
-    double g0 = s0[c];
-    sgn[c] = g0 / sqrt(g0 * g0 + P.h * P.h);
+    R g0 = s0[c];
+    sgn[c] = g0 / sqrt(g0 * g0 + cst<R>(P).h * cst<R>(P).h);
 }
 
 // TVD-RK2 stage: stage 1 out = f - dtau L(f); stage 2 out = (fprev + (f - dtau L(f))) / 2.
-__global__ void k_reinit(TankP P, const double *__restrict__ f, const double *__restrict__ sgn,
-                         const double *__restrict__ fprev, const double *__restrict__ eta1, double dtau,
-                         double *__restrict__ out)
+template <typename R, typename TO>
+__global__ void k_reinit(TankP P, const R *__restrict__ f, const R *__restrict__ sgn,
+                         const R *__restrict__ fprev, const double *__restrict__ eta1, R dtau,
+                         TO *__restrict__ out)
 {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= P.nx * P.ny) return;
     int i = c % P.nx, j = c / P.nx;
-    double s1 = f[c] - dtau * reinit_rhs(P, f, sgn, eta1, i, j);
-    out[c] = fprev ? 0.5 * (fprev[c] + s1) : s1;
+    R s1 = R(f[c]) - dtau * reinit_rhs<R>(P, f, sgn, eta1, i, j);
+    out[c] = fprev ? R(0.5) * (R(fprev[c]) + s1) : s1;
 }
 
 // ---------------------------------------------------- momentum helpers ----
 // Per-tank tables: alpha at cell centres [nx] and at u-faces [nx+1]; vorticity
 // shape at cell-centre rows [ny] and at v-face rows [ny+1].
+template <typename R>
 struct Tabs {
-    const double *alpha_c, *alpha_u, *vort_c, *vort_v;
+    const R *alpha_c, *alpha_u, *vort_c, *vort_v;
 };
 
-__global__ void k_tables(TankP P, double *alpha_c, double *alpha_u, double *vort_c, double *vort_v)
+// Layout of one table set: alpha_c [nx], alpha_u [nx+1], vort_c [ny], vort_v [ny+1].
+// t32 (optional) receives the same tables in FP32.
+__global__ void k_tables(TankP P, double *t, float *t32)
 {
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < P.nx) alpha_c[k] = damp_alpha_eval(P, (k + 0.5) * P.h);
-    if (k <= P.nx) alpha_u[k] = damp_alpha_eval(P, k * P.h);
-    if (k < P.ny) vort_c[k] = vort_shape_eval(P, (k + 0.5) * P.h);
-    if (k <= P.ny) vort_v[k] = vort_shape_eval(P, k * P.h);
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nx = P.nx, ny = P.ny, o1 = nx, o2 = 2 * nx + 1, o3 = 2 * nx + 1 + ny;
+    auto put = [&](int o, double val) {
+        t[o] = val;
+        if (t32) t32[o] = (float)val;
+    };
+    if (k < nx) put(k, damp_alpha_eval(P, (k + 0.5) * P.h));
+    if (k <= nx) put(o1 + k, damp_alpha_eval(P, k * P.h));
+    if (k < ny) put(o2 + k, vort_shape_eval(P, (k + 0.5) * P.h));
+    if (k <= ny) put(o3 + k, vort_shape_eval(P, k * P.h));
 }
 
+template <typename R>
 struct Fields {
-    const double *rc;         // cell density rho^n (transport)
-    const double *u, *v;      // velocities
+    const R *rc;              // cell density rho^n (transport)
+    const R *u, *v;           // velocities
     const double *vin;        // left tangential inflow for v ghosts
 };
 
-__device__ __forceinline__ double ru_at(const TankP &P, const double *rc, int i, int j)
+template <typename R>
+__device__ __forceinline__ R ru_at(const TankP &P, const R *rc, int i, int j)
 {
     i = clampi(i, 0, P.nx);
     j = clampi(j, 0, P.ny - 1);
-    return 0.5 * (cell_at(P, rc, i - 1, j) + cell_at(P, rc, i, j));
+    return R(0.5) * (cell_at<R>(P, rc, i - 1, j) + cell_at<R>(P, rc, i, j));
 }
 
-__device__ __forceinline__ double rv_at(const TankP &P, const double *rc, int i, int j)
+template <typename R>
+__device__ __forceinline__ R rv_at(const TankP &P, const R *rc, int i, int j)
 {
     i = clampi(i, 0, P.nx - 1);
     j = clampi(j, 0, P.ny);
-    return 0.5 * (cell_at(P, rc, i, j - 1) + cell_at(P, rc, i, j));
+    return R(0.5) * (cell_at<R>(P, rc, i, j - 1) + cell_at<R>(P, rc, i, j));
 }
 
 // Consistent transport on the u-face (i, j): rho-breve and C share the mass flux.
-__device__ void transport_u(const TankP &P, const Fields &X, int i, int j, double dt, double &rb, double &C)
+template <typename R>
+__device__ void transport_u(const TankP &P, const Fields<R> &X, int i, int j, R dt, R &rb, R &C)
 {
-    double m[4], f[4];
+    R m[4], f[4];
     for (int s = 0; s < 2; ++s) {
         int a = i - 1 + s;
-        double U = 0.5 * (u_at(P, X.u, a, j) + u_at(P, X.u, a + 1, j));
-        double r = upwind(ru_at(P, X.rc, a - 1, j), ru_at(P, X.rc, a, j), ru_at(P, X.rc, a + 1, j),
-                          ru_at(P, X.rc, a + 2, j), U);
-        double q = upwind(u_at(P, X.u, a - 1, j), u_at(P, X.u, a, j), u_at(P, X.u, a + 1, j),
-                          u_at(P, X.u, a + 2, j), U);
+        R U = R(0.5) * (u_at<R>(P, X.u, a, j) + u_at<R>(P, X.u, a + 1, j));
+        R r = upwind<R>(ru_at<R>(P, X.rc, a - 1, j), ru_at<R>(P, X.rc, a, j), ru_at<R>(P, X.rc, a + 1, j),
+                          ru_at<R>(P, X.rc, a + 2, j), U);
+        R q = upwind<R>(u_at<R>(P, X.u, a - 1, j), u_at<R>(P, X.u, a, j), u_at<R>(P, X.u, a + 1, j),
+                          u_at<R>(P, X.u, a + 2, j), U);
         m[s] = U * r;
         f[s] = m[s] * q;
     }
     for (int s = 0; s < 2; ++s) {
         int b = j - 1 + s;
-        double V = 0.5 * (v_at(P, X.v, X.vin, i - 1, b + 1) + v_at(P, X.v, X.vin, i, b + 1));
-        double r = upwind(ru_at(P, X.rc, i, b - 1), ru_at(P, X.rc, i, b), ru_at(P, X.rc, i, b + 1),
-                          ru_at(P, X.rc, i, b + 2), V);
-        double q = upwind(u_at(P, X.u, i, b - 1), u_at(P, X.u, i, b), u_at(P, X.u, i, b + 1),
-                          u_at(P, X.u, i, b + 2), V);
+        R V = R(0.5) * (v_at<R>(P, X.v, X.vin, i - 1, b + 1) + v_at<R>(P, X.v, X.vin, i, b + 1));
+        R r = upwind<R>(ru_at<R>(P, X.rc, i, b - 1), ru_at<R>(P, X.rc, i, b), ru_at<R>(P, X.rc, i, b + 1),
+                          ru_at<R>(P, X.rc, i, b + 2), V);
+        R q = upwind<R>(u_at<R>(P, X.u, i, b - 1), u_at<R>(P, X.u, i, b), u_at<R>(P, X.u, i, b + 1),
+                          u_at<R>(P, X.u, i, b + 2), V);
         m[2 + s] = V * r;
         f[2 + s] = m[2 + s] * q;
     }
-    rb = ru_at(P, X.rc, i, j) - dt * P.ih * ((m[1] - m[0]) + (m[3] - m[2]));
-    C = ((f[1] - f[0]) + (f[3] - f[2])) * P.ih;
+    rb = ru_at<R>(P, X.rc, i, j) - dt * cst<R>(P).ih * ((m[1] - m[0]) + (m[3] - m[2]));
+    C = ((R(f[1]) - R(f[0])) + (R(f[3]) - R(f[2]))) * cst<R>(P).ih;
 }
 
-__device__ void transport_v(const TankP &P, const Fields &X, int i, int j, double dt, double &rb, double &C)
+template <typename R>
+__device__ void transport_v(const TankP &P, const Fields<R> &X, int i, int j, R dt, R &rb, R &C)
 {
-    double m[4], f[4];
+    R m[4], f[4];
     for (int s = 0; s < 2; ++s) {
         int a = i - 1 + s;
-        double U = 0.5 * (u_at(P, X.u, a + 1, j - 1) + u_at(P, X.u, a + 1, j));
-        double r = upwind(rv_at(P, X.rc, a - 1, j), rv_at(P, X.rc, a, j), rv_at(P, X.rc, a + 1, j),
-                          rv_at(P, X.rc, a + 2, j), U);
-        double q = upwind(v_at(P, X.v, X.vin, a - 1, j), v_at(P, X.v, X.vin, a, j),
-                          v_at(P, X.v, X.vin, a + 1, j), v_at(P, X.v, X.vin, a + 2, j), U);
+        R U = R(0.5) * (u_at<R>(P, X.u, a + 1, j - 1) + u_at<R>(P, X.u, a + 1, j));
+        R r = upwind<R>(rv_at<R>(P, X.rc, a - 1, j), rv_at<R>(P, X.rc, a, j), rv_at<R>(P, X.rc, a + 1, j),
+                          rv_at<R>(P, X.rc, a + 2, j), U);
+        R q = upwind<R>(v_at<R>(P, X.v, X.vin, a - 1, j), v_at<R>(P, X.v, X.vin, a, j),
+                          v_at<R>(P, X.v, X.vin, a + 1, j), v_at<R>(P, X.v, X.vin, a + 2, j), U);
         m[s] = U * r;
         f[s] = m[s] * q;
     }
     for (int s = 0; s < 2; ++s) {
         int b = j - 1 + s;
-        double V = 0.5 * (v_at(P, X.v, X.vin, i, b) + v_at(P, X.v, X.vin, i, b + 1));
-        double r = upwind(rv_at(P, X.rc, i, b - 1), rv_at(P, X.rc, i, b), rv_at(P, X.rc, i, b + 1),
-                          rv_at(P, X.rc, i, b + 2), V);
-        double q = upwind(v_at(P, X.v, X.vin, i, b - 1), v_at(P, X.v, X.vin, i, b),
-                          v_at(P, X.v, X.vin, i, b + 1), v_at(P, X.v, X.vin, i, b + 2), V);
+        R V = R(0.5) * (v_at<R>(P, X.v, X.vin, i, b) + v_at<R>(P, X.v, X.vin, i, b + 1));
+        R r = upwind<R>(rv_at<R>(P, X.rc, i, b - 1), rv_at<R>(P, X.rc, i, b), rv_at<R>(P, X.rc, i, b + 1),
+                          rv_at<R>(P, X.rc, i, b + 2), V);
+        R q = upwind<R>(v_at<R>(P, X.v, X.vin, i, b - 1), v_at<R>(P, X.v, X.vin, i, b),
+                          v_at<R>(P, X.v, X.vin, i, b + 1), v_at<R>(P, X.v, X.vin, i, b + 2), V);
         m[2 + s] = V * r;
         f[2 + s] = m[2 + s] * q;
     }
-    rb = rv_at(P, X.rc, i, j) - dt * P.ih * ((m[1] - m[0]) + (m[3] - m[2]));
-    C = ((f[1] - f[0]) + (f[3] - f[2])) * P.ih;
+    rb = rv_at<R>(P, X.rc, i, j) - dt * cst<R>(P).ih * ((m[1] - m[0]) + (m[3] - m[2]));
+    C = ((R(f[1]) - R(f[0])) + (R(f[3]) - R(f[2]))) * cst<R>(P).ih;
 }
 
 // L_mu u = div[mu (grad u + grad u^T)]: tau_xx / tau_yy at cells, tau_xy at
 // nodes with the four-cell mean viscosity.
+template <typename R>
 struct Visc {
-    const double *mu, *u, *v, *vin;
+    const R *mu, *u, *v;
+    const double *vin;
 };
 
-__device__ __forceinline__ double mnode(const TankP &P, const Visc &X, int i, int j)
+template <typename R>
+__device__ __forceinline__ R mnode(const TankP &P, const Visc<R> &X, int i, int j)
 {
-    return 0.25 * (cell_at(P, X.mu, i - 1, j - 1) + cell_at(P, X.mu, i, j - 1) + cell_at(P, X.mu, i - 1, j) +
-                   cell_at(P, X.mu, i, j));
+    return R(0.25) * (cell_at<R>(P, X.mu, i - 1, j - 1) + cell_at<R>(P, X.mu, i, j - 1) + cell_at<R>(P, X.mu, i - 1, j) +
+                   cell_at<R>(P, X.mu, i, j));
 }
 
-__device__ __forceinline__ double txx(const TankP &P, const Visc &X, int i, int j)
+template <typename R>
+__device__ __forceinline__ R txx(const TankP &P, const Visc<R> &X, int i, int j)
 {
-    return 2.0 * cell_at(P, X.mu, i, j) * (u_at(P, X.u, i + 1, j) - u_at(P, X.u, i, j)) * P.ih;
+    return R(2.0) * cell_at<R>(P, X.mu, i, j) * (u_at<R>(P, X.u, i + 1, j) - u_at<R>(P, X.u, i, j)) * cst<R>(P).ih;
 }
 
-__device__ __forceinline__ double tyy(const TankP &P, const Visc &X, int i, int j)
+template <typename R>
+__device__ __forceinline__ R tyy(const TankP &P, const Visc<R> &X, int i, int j)
 {
-    return 2.0 * cell_at(P, X.mu, i, j) * (v_at(P, X.v, X.vin, i, j + 1) - v_at(P, X.v, X.vin, i, j)) * P.ih;
+    return R(2.0) * cell_at<R>(P, X.mu, i, j) * (v_at<R>(P, X.v, X.vin, i, j + 1) - v_at<R>(P, X.v, X.vin, i, j)) * cst<R>(P).ih;
 }
 
-__device__ __forceinline__ double txy(const TankP &P, const Visc &X, int i, int j)
+template <typename R>
+__device__ __forceinline__ R txy(const TankP &P, const Visc<R> &X, int i, int j)
 {
-    return mnode(P, X, i, j) * ((u_at(P, X.u, i, j) - u_at(P, X.u, i, j - 1)) * P.ih +
-                                (v_at(P, X.v, X.vin, i, j) - v_at(P, X.v, X.vin, i - 1, j)) * P.ih);
+    return mnode<R>(P, X, i, j) * ((u_at<R>(P, X.u, i, j) - u_at<R>(P, X.u, i, j - 1)) * cst<R>(P).ih +
+                                (v_at<R>(P, X.v, X.vin, i, j) - v_at<R>(P, X.v, X.vin, i - 1, j)) * cst<R>(P).ih);
 }
 
-__device__ __forceinline__ double visc_x(const TankP &P, const Visc &X, int i, int j)
+template <typename R>
+__device__ __forceinline__ R visc_x(const TankP &P, const Visc<R> &X, int i, int j)
 {
-    return (txx(P, X, i, j) - txx(P, X, i - 1, j)) * P.ih + (txy(P, X, i, j + 1) - txy(P, X, i, j)) * P.ih;
+    return (txx<R>(P, X, i, j) - txx<R>(P, X, i - 1, j)) * cst<R>(P).ih + (txy<R>(P, X, i, j + 1) - txy<R>(P, X, i, j)) * cst<R>(P).ih;
 }
 
-__device__ __forceinline__ double visc_y(const TankP &P, const Visc &X, int i, int j)
+template <typename R>
+__device__ __forceinline__ R visc_y(const TankP &P, const Visc<R> &X, int i, int j)
 {
-    return (tyy(P, X, i, j) - tyy(P, X, i, j - 1)) * P.ih + (txy(P, X, i + 1, j) - txy(P, X, i, j)) * P.ih;
+    return (tyy<R>(P, X, i, j) - tyy<R>(P, X, i, j - 1)) * cst<R>(P).ih + (txy<R>(P, X, i + 1, j) - txy<R>(P, X, i, j)) * cst<R>(P).ih;
 }
 
-__device__ __forceinline__ double visc_diag_x(const TankP &P, const Visc &X, int i, int j)
+template <typename R>
+__device__ __forceinline__ R visc_diag_x(const TankP &P, const Visc<R> &X, int i, int j)
 {
-    return -(2.0 * cell_at(P, X.mu, i, j) + 2.0 * cell_at(P, X.mu, i - 1, j) + mnode(P, X, i, j + 1) +
-             mnode(P, X, i, j)) * (P.ih * P.ih);
+    return -(R(2.0) * cell_at<R>(P, X.mu, i, j) + R(2.0) * cell_at<R>(P, X.mu, i - 1, j) + mnode<R>(P, X, i, j + 1) +
+             mnode<R>(P, X, i, j)) * (cst<R>(P).ih * cst<R>(P).ih);
 }
 
-__device__ __forceinline__ double visc_diag_y(const TankP &P, const Visc &X, int i, int j)
+template <typename R>
+__device__ __forceinline__ R visc_diag_y(const TankP &P, const Visc<R> &X, int i, int j)
 {
-    return -(2.0 * cell_at(P, X.mu, i, j) + 2.0 * cell_at(P, X.mu, i, j - 1) + mnode(P, X, i + 1, j) +
-             mnode(P, X, i, j)) * (P.ih * P.ih);
+    return -(R(2.0) * cell_at<R>(P, X.mu, i, j) + R(2.0) * cell_at<R>(P, X.mu, i, j - 1) + mnode<R>(P, X, i + 1, j) +
+             mnode<R>(P, X, i, j)) * (cst<R>(P).ih * cst<R>(P).ih);
 }
 
 // Right-hand side R and diagonal D of the u-momentum system; also the first
 // Jacobi iterate (u^n with the Dirichlet faces at t^{n+1}).
-__global__ void k_mom_u(TankP P, const StepScalars *S, const double *__restrict__ inp, Tabs tb,
-                        const double *__restrict__ rho_n,
-                        const double *__restrict__ mu_n, const double *__restrict__ chi_1,
-                        const double *__restrict__ u, const double *__restrict__ v, const double *__restrict__ p,
-                        Bc bc, double *Ru, double *Du, double *rbu, double *ua)
+template <typename R>
+__global__ void k_mom_u(TankP P, const StepScalars *S, const double *__restrict__ inp, Tabs<R> tb,
+                        const R *__restrict__ rho_n, const R *__restrict__ mu_n, const R *__restrict__ chi_1,
+                        const R *__restrict__ u, const R *__restrict__ v, const double *__restrict__ p,
+                        Bc bc, R *Ru, R *Du, R *ua)
 {
     int f = blockIdx.x * blockDim.x + threadIdx.x;
     const int nx = P.nx;
     if (f >= (nx + 1) * P.ny) return;
-    const double dt = inp[0];
+    const R dt = R(inp[0]);
     int i = f % (nx + 1), j = f / (nx + 1);
     if (i == 0) {
         ua[f] = bc.uin1[j];
         return;
     }
     if (i == nx) {
-        ua[f] = 0.0;
+        ua[f] = R(0.0);
         return;
     }
-    ua[f] = u[f];
-    Fields X{rho_n, u, v, bc.vin0};
-    Visc Vn{mu_n, u, v, bc.vin0};
-    double rb, C;
-    transport_u(P, X, i, j, dt, rb, C);
-    double x = i * P.h, y = (j + 0.5) * P.h;
-    double chi = 0.5 * (cell_at(P, chi_1, i - 1, j) + cell_at(P, chi_1, i, j));
-    rbu[f] = rb;
-    const double idt = 1.0 / dt;
-    Du[f] = rb * idt + chi * P.ikp + tb.alpha_u[i] * rb * idt + vort_damp(P, tb.vort_c[j], idt);
-    Ru[f] = ru_at(P, rho_n, i, j) * u[f] * idt - C + 0.5 * visc_x(P, Vn, i, j) -
-            (p[j * nx + i] - p[j * nx + i - 1]) * P.ih;
+    ua[f] = R(u[f]);
+    Fields<R> X{rho_n, u, v, bc.vin0};
+    Visc<R> Vn{mu_n, u, v, bc.vin0};
+    R rb, C;
+    transport_u<R>(P, X, i, j, dt, rb, C);
+    R chi = R(0.5) * (cell_at<R>(P, chi_1, i - 1, j) + cell_at<R>(P, chi_1, i, j));
+    const R idt = R(1.0) / dt;
+    Du[f] = rb * idt + chi * cst<R>(P).ikp + tb.alpha_u[i] * rb * idt + vort_damp<R>(P, tb.vort_c[j], idt);
+    Ru[f] = ru_at<R>(P, rho_n, i, j) * R(u[f]) * idt - C + R(0.5) * visc_x<R>(P, Vn, i, j) -
+            R(p[j * nx + i] - p[j * nx + i - 1]) * cst<R>(P).ih;
 }
 
-__global__ void k_mom_v(TankP P, const StepScalars *S, const double *__restrict__ inp, Tabs tb,
-                        const double *__restrict__ rho_n,
-                        const double *__restrict__ mu_n, const double *__restrict__ chi_1,
-                        const double *__restrict__ rf_1, const double *__restrict__ u,
-                        const double *__restrict__ v, const double *__restrict__ p, Bc bc, double *Rv,
-                        double *Dv, double *rbv, double *va)
+template <typename R>
+__global__ void k_mom_v(TankP P, const StepScalars *S, const double *__restrict__ inp, Tabs<R> tb,
+                        const R *__restrict__ rho_n, const R *__restrict__ mu_n, const R *__restrict__ chi_1,
+                        const R *__restrict__ rf_1, const R *__restrict__ u, const R *__restrict__ v,
+                        const double *__restrict__ p, Bc bc, R *Rv, R *Dv, R *va)
 {
     int f = blockIdx.x * blockDim.x + threadIdx.x;
     const int nx = P.nx, ny = P.ny;
     if (f >= nx * (ny + 1)) return;
-    const double dt = inp[0];
+    const R dt = R(inp[0]);
     int i = f % nx, j = f / nx;
     if (j == 0) {
-        va[f] = 0.0;
+        va[f] = R(0.0);
         return;
     }
-    va[f] = v[f];
-    Fields X{rho_n, u, v, bc.vin0};
-    Visc Vn{mu_n, u, v, bc.vin0};
-    double rb, C;
-    transport_v(P, X, i, j, dt, rb, C);
-    double x = (i + 0.5) * P.h, y = j * P.h;
-    double chi = 0.5 * (cell_at(P, chi_1, i, j - 1) + cell_at(P, chi_1, i, j));
-    double rf = 0.5 * (cell_at(P, rf_1, i, j - 1) + cell_at(P, rf_1, i, j));
-    rbv[f] = rb;
-    const double idt = 1.0 / dt;
-    Dv[f] = rb * idt + chi * P.ikp + tb.alpha_c[i] * rb * idt + vort_damp(P, tb.vort_v[j], idt);
-    double gp = j < ny ? (p[j * nx + i] - p[(j - 1) * nx + i]) * P.ih : -2.0 * p[(ny - 1) * nx + i] * P.ih;
-    Rv[f] = rv_at(P, rho_n, i, j) * v[f] * idt - C + 0.5 * visc_y(P, Vn, i, j) - rf * P.g +
-            chi * S->zdot1 * P.ikp - gp;
+    va[f] = R(v[f]);
+    Fields<R> X{rho_n, u, v, bc.vin0};
+    Visc<R> Vn{mu_n, u, v, bc.vin0};
+    R rb, C;
+    transport_v<R>(P, X, i, j, dt, rb, C);
+    R chi = R(0.5) * (cell_at<R>(P, chi_1, i, j - 1) + cell_at<R>(P, chi_1, i, j));
+    R rf = R(0.5) * (cell_at<R>(P, rf_1, i, j - 1) + cell_at<R>(P, rf_1, i, j));
+    const R idt = R(1.0) / dt;
+    Dv[f] = rb * idt + chi * cst<R>(P).ikp + tb.alpha_c[i] * rb * idt + vort_damp<R>(P, tb.vort_v[j], idt);
+    R gp = j < ny ? R(p[j * nx + i] - p[(j - 1) * nx + i]) * cst<R>(P).ih : -R(2.0) * R(p[(ny - 1) * nx + i]) * cst<R>(P).ih;
+    Rv[f] = rv_at<R>(P, rho_n, i, j) * R(v[f]) * idt - C + R(0.5) * visc_y<R>(P, Vn, i, j) - rf * cst<R>(P).g +
+            chi * R(S->zdot1) * cst<R>(P).ikp - gp;
+}
+
+// Working buffers the stencil kernels read, in the compute type R.  An FP64 tank
+// points them at its FP64 buffers (sig, u, v are the state itself); a mixed tank
+// points them into its FP32 slab, where sig, u, v are mirrors refreshed at the
+// start of each step.  Loading FP32 directly keeps the FP32 kernels off the FP64
+// pipe, which a per-load FP64 -> FP32 conversion would otherwise saturate.
+template <typename R>
+struct Work {
+    R *sig, *u, *v;                           // state (or its FP32 mirror)
+    R *sa, *sgn, *r0, *r1, *rt;               // advected sigma, reinitialisation
+    R *rho_n, *mu_n, *mu_1, *rf_1, *chi_1;    // materials
+    R *Ru, *Du, *ua, *ub, *uc, *Rv, *Dv, *va, *vb, *vc;  // momentum systems, Jacobi iterates
+};
+
+// sig, u, v -> FP32 mirrors (one thread per cell / face of the largest set).
+__global__ void k_mirror(long long nc, long long nu, long long nv, const double *__restrict__ sig,
+                         const double *__restrict__ u, const double *__restrict__ v, float *__restrict__ sig32,
+                         float *__restrict__ u32, float *__restrict__ v32)
+{
+    long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k < nc) sig32[k] = float(sig[k]);
+    if (k < nu) u32[k] = float(u[k]);
+    if (k < nv) v32[k] = float(v[k]);
 }
 
 // One Jacobi sweep of (D - L_mu / 2) u* = R (Crank-Nicolson implicit half),
 // splitting on the interior diagonal of L_mu; Dirichlet faces are copied.
-__global__ void k_jacobi(TankP P, const double *__restrict__ mu_1, const double *__restrict__ vin1,
-                         const double *__restrict__ Ru, const double *__restrict__ Du,
-                         const double *__restrict__ Rv, const double *__restrict__ Dv,
-                         const double *__restrict__ ua, const double *__restrict__ va, double *__restrict__ ub,
-                         double *__restrict__ vb)
+template <typename R, typename TO>
+__global__ void k_jacobi(TankP P, const R *__restrict__ mu_1, const double *__restrict__ vin1,
+                         const R *__restrict__ Ru, const R *__restrict__ Du,
+                         const R *__restrict__ Rv, const R *__restrict__ Dv,
+                         const R *__restrict__ ua, const R *__restrict__ va, TO *__restrict__ ub,
+                         TO *__restrict__ vb)
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int nx = P.nx, ny = P.ny;
     const int nu = (nx + 1) * ny, nv = nx * (ny + 1);
-    Visc Vk{mu_1, ua, va, vin1};
+    Visc<R> Vk{mu_1, ua, va, vin1};
     if (k < nu) {
         int i = k % (nx + 1), j = k / (nx + 1);
         if (i == 0 || i == nx) {
-            ub[k] = ua[k];
+            ub[k] = R(ua[k]);
             return;
         }
-        double ld = visc_diag_x(P, Vk, i, j);
-        ub[k] = (Ru[k] + 0.5 * (visc_x(P, Vk, i, j) - ld * ua[k])) / (Du[k] - 0.5 * ld);
+        R ld = visc_diag_x<R>(P, Vk, i, j);
+        ub[k] = (R(Ru[k]) + R(0.5) * (visc_x<R>(P, Vk, i, j) - ld * R(ua[k]))) / (R(Du[k]) - R(0.5) * ld);
     } else if (k < nu + nv) {
         int f = k - nu;
         int i = f % nx, j = f / nx;
         if (j == 0) {
-            vb[f] = va[f];
+            vb[f] = R(va[f]);
             return;
         }
-        double ld = visc_diag_y(P, Vk, i, j);
-        vb[f] = (Rv[f] + 0.5 * (visc_y(P, Vk, i, j) - ld * va[f])) / (Dv[f] - 0.5 * ld);
+        R ld = visc_diag_y<R>(P, Vk, i, j);
+        vb[f] = (R(Rv[f]) + R(0.5) * (visc_y<R>(P, Vk, i, j) - ld * R(va[f]))) / (R(Dv[f]) - R(0.5) * ld);
     }
 }
 
 // b = -h div u*, face coefficients beta = 1 / D (zero on Neumann walls).
+template <typename TD>
 __global__ void k_proj_rhs(TankP P, const double *__restrict__ us, const double *__restrict__ vs,
-                           const double *__restrict__ Du, const double *__restrict__ Dv, double *rhs,
+                           const TD *__restrict__ Du, const TD *__restrict__ Dv, double *rhs,
                            double *bu, double *bv)
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -692,10 +789,10 @@ __global__ void k_proj_rhs(TankP P, const double *__restrict__ us, const double 
         rhs[k] = -P.h * (us[j * (nx + 1) + i + 1] - us[j * (nx + 1) + i] + vs[(j + 1) * nx + i] - vs[j * nx + i]);
     } else if (k < nc + nu) {
         int f = k - nc, i = f % (nx + 1);
-        bu[f] = (i == 0 || i == nx) ? 0.0 : 1.0 / Du[f];
+        bu[f] = (i == 0 || i == nx) ? 0.0 : 1.0 / double(Du[f]);
     } else if (k < nc + nu + nv) {
         int f = k - nc - nu, j = f / nx;
-        bv[f] = j == 0 ? 0.0 : 1.0 / Dv[f];
+        bv[f] = j == 0 ? 0.0 : 1.0 / double(Dv[f]);
     }
 }
 
@@ -814,6 +911,33 @@ __global__ void k_init_pressure(TankP P, const double *__restrict__ rf, double *
     }
 }
 
+inline size_t pad64(size_t n) { return (n + 63) & ~size_t(63); }
+
+// FP32 slab of a mixed tank: 11 cell arrays, 6 u-face and 6 v-face arrays, each
+// starting on a 256-byte boundary.
+size_t work_floats(size_t nc, size_t nu, size_t nv) { return 11 * pad64(nc) + 6 * pad64(nu) + 6 * pad64(nv); }
+
+Work<double> work64(wec_tank *T)
+{
+    return Work<double>{T->sig, T->u, T->v, T->sa, T->sgn, T->r0, T->r1, T->rt, T->rho_n, T->mu_n, T->mu_1,
+                        T->rf_1, T->chi_1, T->Ru, T->Du, T->ua, T->ub, T->uc, T->Rv, T->Dv, T->va, T->vb,
+                        T->vc};
+}
+
+Work<float> work32(wec_tank *T)
+{
+    float *q = T->w32;
+    auto take = [&q](size_t n) { float *r = q; q += pad64(n); return r; };
+    Work<float> W;
+    float **cells[] = {&W.sig, &W.sa, &W.sgn, &W.r0, &W.r1, &W.rt, &W.rho_n, &W.mu_n, &W.mu_1, &W.rf_1, &W.chi_1};
+    for (float **c : cells) *c = take(T->nc);
+    float **uf[] = {&W.u, &W.Ru, &W.Du, &W.ua, &W.ub, &W.uc};
+    for (float **c : uf) *c = take(T->nu);
+    float **vf[] = {&W.v, &W.Rv, &W.Dv, &W.va, &W.vb, &W.vc};
+    for (float **c : vf) *c = take(T->nv);
+    return W;
+}
+
 }  // namespace
 
 int tank_alloc_and_init(wec_tank *T)
@@ -834,12 +958,17 @@ int tank_alloc_and_init(wec_tank *T)
         WEC_CK(cudaMalloc(q, nc * 8));
         WEC_CK(cudaMemset(*q, 0, nc * 8));
     }
-    double **ufaces[] = {&T->u, &T->us, &T->ua, &T->ub, &T->uc, &T->Ru, &T->Du, &T->rbu};
+    double **ufaces[] = {&T->u, &T->us, &T->ua, &T->ub, &T->uc, &T->Ru, &T->Du};
     for (double **q : ufaces) {
         WEC_CK(cudaMalloc(q, nu * 8));
         WEC_CK(cudaMemset(*q, 0, nu * 8));
     }
-    double **vfaces[] = {&T->v, &T->vs, &T->va, &T->vb, &T->vc, &T->Rv, &T->Dv, &T->rbv};
+    double **vfaces[] = {&T->v, &T->vs, &T->va, &T->vb, &T->vc, &T->Rv, &T->Dv};
+    if (T->opts.precision == WEC_PREC_MIXED) {
+        const size_t e = work_floats(nc, nu, nv);
+        WEC_CK(cudaMalloc(&T->w32, e * 4));
+        WEC_CK(cudaMemset(T->w32, 0, e * 4));
+    }
     for (double **q : vfaces) {
         WEC_CK(cudaMalloc(q, nv * 8));
         WEC_CK(cudaMemset(*q, 0, nv * 8));
@@ -854,12 +983,11 @@ int tank_alloc_and_init(wec_tank *T)
     T->bc.eta_in = T->bc.eta1 + 3;
     WEC_CK(cudaMalloc(&T->part, kRedBlocks * 8));
     WEC_CK(cudaMalloc(&T->tabs, (size_t)(2 * P.nx + 1 + 2 * P.ny + 1) * 8));
+    if (T->opts.precision == WEC_PREC_MIXED) WEC_CK(cudaMalloc(&T->tabs32, (size_t)(2 * P.nx + 1 + 2 * P.ny + 1) * 4));
     WEC_CK(cudaMalloc(&T->sgn, nc * 8));
     {
         WEC_PROF("init", -1, 8.0 * (2 * P.nx + 2 * P.ny + 2), T->gst);
-        double *t = T->tabs;
-        k_tables<<<nblk(std::max(P.nx, P.ny) + 1, 128), 128, 0, T->gst>>>(P, t, t + P.nx, t + 2 * P.nx + 1,
-                                                                          t + 2 * P.nx + 1 + P.ny);
+        k_tables<<<nblk(std::max(P.nx, P.ny) + 1, 128), 128, 0, T->gst>>>(P, T->tabs, T->tabs32);
     }
     WEC_CK(cudaMalloc(&T->inp, 2 * 8));
     WEC_CK(cudaMemset(T->inp, 0, 2 * 8));
@@ -883,7 +1011,7 @@ int tank_init_pressure(wec_tank *T)
     const TankP &P = T->P;
     {
         WEC_PROF("materials", -1, 16.0 * T->nc, T->gst);
-        k_materials<<<nblk(T->nc, TB), TB, 0, T->gst>>>(P, T->S, 0, T->sig, nullptr, nullptr, T->rf_1, nullptr);
+        k_materials<double><<<nblk(T->nc, TB), TB, 0, T->gst>>>(P, T->S, 0, T->sig, nullptr, nullptr, T->rf_1, nullptr);
     }
     {
         WEC_PROF("init", -1, 16.0 * T->nc, T->gst);
@@ -896,18 +1024,32 @@ int tank_init_pressure(wec_tank *T)
 
 namespace {
 
-Tabs tabs(const wec_tank *T)
+template <typename R>
+Tabs<R> tabs(const wec_tank *T)
 {
     const int nx = T->P.nx, ny = T->P.ny;
-    return Tabs{T->tabs, T->tabs + nx, T->tabs + 2 * nx + 1, T->tabs + 2 * nx + 1 + ny};
+    const R *t;
+    if constexpr (sizeof(R) == 4)
+        t = T->tabs32;
+    else
+        t = T->tabs;
+    return Tabs<R>{t, t + nx, t + 2 * nx + 1, t + 2 * nx + 1 + ny};
 }
 
-// Everything before the pressure solve: steps (1)-(7) of the step.
-void enqueue_front(wec_tank *T, cudaStream_t st)
+// Everything before the pressure solve: steps (1)-(7) of the step, stencils in
+// the compute type R over the working set W.
+template <typename R>
+void enqueue_front_t(wec_tank *T, const Work<R> &W, cudaStream_t st)
 {
     const TankP &P = T->P;
     const long long nc = T->nc, nu = T->nu, nv = T->nv;
-    const double fb = 8.0;  // FP64 bytes
+    const double fb = 8.0, rb = sizeof(R);  // bytes of FP64 storage / of the working type
+    constexpr bool f32 = sizeof(R) == 4;
+    if constexpr (f32) {
+        WEC_PROF("mirror", -1, (fb + rb) * (nc + nu + nv), st);
+        k_mirror<<<nblk(std::max(nc, std::max(nu, nv)), TB), TB, 0, st>>>(nc, nu, nv, T->sig, T->u, T->v, W.sig,
+                                                                            W.u, W.v);
+    }
     // (1) inflow / ghost data at t^n and t^{n+1}
     {
         WEC_PROF("bc", -1, fb * 8.0, st);
@@ -915,16 +1057,16 @@ void enqueue_front(wec_tank *T, cudaStream_t st)
     }
     {
         WEC_PROF("bc", -1, fb * (3.0 * P.ny + 2), st);
-        k_bc_rows<<<nblk(P.ny + 1, 2), 64, 0, st>>>(P, T->S, T->inp, T->bc);
+        k_bc_rows<R><<<nblk(P.ny + 1, 2), 64, 0, st>>>(P, T->S, T->inp, T->bc);
     }
     // (2) materials at n, force from p^{n-1/2}, u^n (Eq. int_fh), heave (Eq. newton_u)
     {
-        WEC_PROF("materials", -1, fb * 3.0 * nc, st);
-        k_materials<<<nblk(nc, TB), TB, 0, st>>>(P, T->S, 0, T->sig, T->rho_n, T->mu_n, nullptr, nullptr);
+        WEC_PROF("materials", -1, (fb + 2.0 * rb) * nc, st);
+        k_materials<R><<<nblk(nc, TB), TB, 0, st>>>(P, T->S, 0, T->sig, W.rho_n, W.mu_n, nullptr, nullptr);
     }
     {
         WEC_PROF("force", -1, fb * kRedBlocks, st);
-        k_force_partial<<<kRedBlocks, TB, 0, st>>>(P, T->S, T->p, T->u, T->v, T->mu_n, T->bc.vin0, T->part);
+        k_force_partial<R><<<kRedBlocks, TB, 0, st>>>(P, T->S, T->p, T->u, T->v, W.mu_n, T->bc.vin0, T->part);
     }
     {
         WEC_PROF("scalar", -1, fb * kRedBlocks, st);
@@ -933,68 +1075,83 @@ void enqueue_front(wec_tank *T, cudaStream_t st)
     // (3) sigma advection + damping-zone relaxation, then reinitialisation; the
     // last pseudo-step writes sigma^{n+1} over sigma^n (no longer needed).
     {
-        WEC_PROF("advect", -1, fb * (2.0 * nc + nu + nv), st);
-        k_advect<<<nblk(nc, TB), TB, 0, st>>>(P, T->sig, T->u, T->v, T->bc.eta0, T->inp, T->tabs, T->sa);
+        WEC_PROF("advect", -1, rb * (nc + nu + nv) + (fb + (f32 ? rb : 0.0)) * nc, st);
+        k_advect<R><<<nblk(nc, TB), TB, 0, st>>>(P, W.sig, W.u, W.v, T->bc.eta0, T->inp, tabs<R>(T).alpha_c, T->sa,
+                                                 f32 ? W.sa : nullptr);
     }
-    const double dtau = 0.3 * P.h;
-    const double *f = T->sa;
-    double *bufs[2] = {T->r0, T->r1};
+    const R dtau = R(0.3 * P.h);
+    const R *f = W.sa;
+    R *bufs[2] = {W.r0, W.r1};
     const int nr = T->opts.n_reinit;
     if (nr > 0) {
-        WEC_PROF("reinit", -1, fb * 2.0 * nc, st);
-        k_reinit_sign<<<nblk(nc, TB), TB, 0, st>>>(P, T->sa, T->sgn);
+        WEC_PROF("reinit", -1, rb * 2.0 * nc, st);
+        k_reinit_sign<R><<<nblk(nc, TB), TB, 0, st>>>(P, W.sa, W.sgn);
     }
     for (int it = 0; it < nr; ++it) {
-        double *dst = it == nr - 1 ? T->sig : bufs[it & 1];
         {
-            WEC_PROF("reinit", -1, fb * 3.0 * nc, st);
-            k_reinit<<<nblk(nc, TB), TB, 0, st>>>(P, f, T->sgn, nullptr, T->bc.eta1, dtau, T->rt);
+            WEC_PROF("reinit", -1, rb * 3.0 * nc, st);
+            k_reinit<R, R><<<nblk(nc, TB), TB, 0, st>>>(P, f, W.sgn, nullptr, T->bc.eta1, dtau, W.rt);
         }
-        {
-            WEC_PROF("reinit", -1, fb * 4.0 * nc, st);
-            k_reinit<<<nblk(nc, TB), TB, 0, st>>>(P, T->rt, T->sgn, f, T->bc.eta1, dtau, dst);
+        WEC_PROF("reinit", -1, rb * 3.0 * nc + (it == nr - 1 ? fb : rb) * nc, st);
+        if (it == nr - 1) {
+            k_reinit<R, double><<<nblk(nc, TB), TB, 0, st>>>(P, W.rt, W.sgn, f, T->bc.eta1, dtau, T->sig);
+        } else {
+            R *dst = bufs[it & 1];
+            k_reinit<R, R><<<nblk(nc, TB), TB, 0, st>>>(P, W.rt, W.sgn, f, T->bc.eta1, dtau, dst);
+            f = dst;
         }
-        f = dst;
     }
     if (nr == 0) cudaMemcpyAsync(T->sig, T->sa, nc * 8, cudaMemcpyDeviceToDevice, st);
     // (4) materials at n+1 (psi at the new body position)
     {
-        WEC_PROF("materials", -1, fb * 4.0 * nc, st);
-        k_materials<<<nblk(nc, TB), TB, 0, st>>>(P, T->S, 1, T->sig, nullptr, T->mu_1, T->rf_1, T->chi_1);
+        WEC_PROF("materials", -1, (fb + 3.0 * rb) * nc, st);
+        k_materials<R><<<nblk(nc, TB), TB, 0, st>>>(P, T->S, 1, T->sig, nullptr, W.mu_1, W.rf_1, W.chi_1);
     }
     // (5) momentum right-hand side and diagonal, (6) Crank-Nicolson Jacobi sweeps
     {
-        WEC_PROF("mom_u", -1, fb * (4.0 * nc + nu + nv + 4.0 * nu), st);
-        k_mom_u<<<nblk(nu, TB), TB, 0, st>>>(P, T->S, T->inp, tabs(T), T->rho_n, T->mu_n, T->chi_1, T->u, T->v, T->p,
-                                             T->bc, T->Ru, T->Du, T->rbu, T->ua);
+        WEC_PROF("mom_u", -1, rb * (3.0 * nc + nu + nv + 2.0 * nu) + fb * (nc + nu), st);
+        k_mom_u<R><<<nblk(nu, TB), TB, 0, st>>>(P, T->S, T->inp, tabs<R>(T), W.rho_n, W.mu_n, W.chi_1, W.u, W.v, T->p,
+                                                T->bc, W.Ru, W.Du, W.ua);
     }
     {
-        WEC_PROF("mom_v", -1, fb * (5.0 * nc + nu + nv + 4.0 * nv), st);
-        k_mom_v<<<nblk(nv, TB), TB, 0, st>>>(P, T->S, T->inp, tabs(T), T->rho_n, T->mu_n, T->chi_1, T->rf_1, T->u, T->v,
-                                             T->p, T->bc, T->Rv, T->Dv, T->rbv, T->va);
+        WEC_PROF("mom_v", -1, rb * (4.0 * nc + nu + nv + 2.0 * nv) + fb * (nc + nv), st);
+        k_mom_v<R><<<nblk(nv, TB), TB, 0, st>>>(P, T->S, T->inp, tabs<R>(T), W.rho_n, W.mu_n, W.chi_1, W.rf_1, W.u,
+                                                W.v, T->p, T->bc, W.Rv, W.Dv, W.va);
     }
-    const double *ju = T->ua, *jv = T->va;
-    double *tu[2] = {T->ub, T->uc}, *tv[2] = {T->vb, T->vc};
-    for (int it = 0; it < T->opts.n_jacobi; ++it) {
-        double *du = it == T->opts.n_jacobi - 1 ? T->us : tu[it & 1];
-        double *dv = it == T->opts.n_jacobi - 1 ? T->vs : tv[it & 1];
-        {
-            WEC_PROF("jacobi", -1, fb * (nc + 4.0 * (nu + nv)), st);
-            k_jacobi<<<nblk(nu + nv, TB), TB, 0, st>>>(P, T->mu_1, T->bc.vin1, T->Ru, T->Du, T->Rv, T->Dv, ju,
-                                                       jv, du, dv);
+    const R *ju = W.ua, *jv = W.va;
+    R *tu[2] = {W.ub, W.uc}, *tv[2] = {W.vb, W.vc};
+    const int nj = T->opts.n_jacobi;
+    for (int it = 0; it < nj; ++it) {
+        const bool last = it == nj - 1;
+        WEC_PROF("jacobi", -1, rb * (nc + 4.0 * (nu + nv)) + fb * (nu + nv) + (last ? fb - rb : 0.0) * (nu + nv),
+                 st);
+        if (last) {
+            k_jacobi<R, double><<<nblk(nu + nv, TB), TB, 0, st>>>(P, W.mu_1, T->bc.vin1, W.Ru, W.Du, W.Rv, W.Dv,
+                                                                  ju, jv, T->us, T->vs);
+        } else {
+            k_jacobi<R, R><<<nblk(nu + nv, TB), TB, 0, st>>>(P, W.mu_1, T->bc.vin1, W.Ru, W.Du, W.Rv, W.Dv, ju,
+                                                             jv, tu[it & 1], tv[it & 1]);
+            ju = tu[it & 1];
+            jv = tv[it & 1];
         }
-        ju = du;
-        jv = dv;
     }
     // (7) pressure increment: A phi = -h div u*, beta = 1/D; phi from zero
     wec_poisson *S = &T->solver;
     {
         WEC_PROF("proj_rhs", -1, fb * (nc + 3.0 * (nu + nv)), st);
-        k_proj_rhs<<<nblk(nc + nu + nv, TB), TB, 0, st>>>(P, T->us, T->vs, T->Du, T->Dv, T->rhs, S->L64[0].bu,
+        k_proj_rhs<R><<<nblk(nc + nu + nv, TB), TB, 0, st>>>(P, T->us, T->vs, W.Du, W.Dv, T->rhs, S->L64[0].bu,
                                                           S->L64[0].bv);
     }
     poisson_build(S, st);
     cudaMemsetAsync(T->phi, 0, nc * 8, st);
+}
+
+void enqueue_front(wec_tank *T, cudaStream_t st)
+{
+    if (T->opts.precision == WEC_PREC_MIXED)
+        enqueue_front_t<float>(T, work32(T), st);
+    else
+        enqueue_front_t<double>(T, work64(T), st);
 }
 
 // (8) projection and the close of the step.
@@ -1129,10 +1286,12 @@ void tank_free(wec_tank *T)
     if (T->exec) cudaGraphExecDestroy(T->exec);
     if (T->graph) cudaGraphDestroy(T->graph);
     double *all[] = {T->sig, T->sa, T->r0, T->r1, T->rt, T->p, T->phi, T->rhs, T->rho_n, T->mu_n, T->mu_1,
-                     T->rf_1, T->chi_1, T->u, T->us, T->ua, T->ub, T->uc, T->Ru, T->Du, T->rbu, T->v, T->vs,
-                     T->va, T->vb, T->vc, T->Rv, T->Dv, T->rbv, T->bcbuf, T->part, T->waves, T->inp,
+                     T->rf_1, T->chi_1, T->u, T->us, T->ua, T->ub, T->uc, T->Ru, T->Du, T->v, T->vs,
+                     T->va, T->vb, T->vc, T->Rv, T->Dv, T->bcbuf, T->part, T->waves, T->inp,
                      T->tabs, T->sgn};
     for (double *q : all) cudaFree(q);
+    cudaFree(T->w32);
+    cudaFree(T->tabs32);
     cudaFree(T->S);
     if (T->Sh) cudaFreeHost(T->Sh);
     poisson_free(&T->solver);

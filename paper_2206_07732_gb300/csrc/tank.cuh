@@ -6,6 +6,13 @@
 namespace wec {
 
 // Per-tank constants, passed to kernels by value.
+// Tank constants the stencil kernels read, in their compute type (an FP32
+// kernel reading FP64 constants would convert them on the FP64 pipe).
+template <typename R>
+struct TankC {
+    R h, ih, depth, g, rho_w, rho_a, rho_s, mu_w, mu_a, mu_s, ikp, bxc, bw, bh;
+};
+
 struct TankP {
     int nx, ny;
     double h, ih, lx, ly, depth;  // ih = 1 / h
@@ -15,6 +22,8 @@ struct TankP {
     double bxc, bw, bh, mass, added_mass, kappa_p, ikp, pto_c;  // ikp = 1 / kappa_p
     int ncomp;
     const double *amp, *omega, *kw, *phase;  // device
+    TankC<float> cf;                          // the constants above, FP32
+    TankC<double> cd;                         // and FP64
 };
 
 // Device-resident scalars of the step (keeps the step free of host round trips).
@@ -51,15 +60,20 @@ struct wec_tank {
     int n_fixed = 0, n_body = 0, n_close = 0;  // kernels per replay: fixed, per iteration, per cycle
     double *inp = nullptr;            // device: dt, f_pto of the current step
     double *tabs = nullptr;           // device: damping weights / vorticity shape per column / row
+    float *tabs32 = nullptr;          // device: the same tables in FP32 (mixed precision)
     double *sgn = nullptr;            // device: Sussman smoothed sign of the step's sigma0
     size_t nc = 0, nu = 0, nv = 0;
     double *sig = nullptr, *sa = nullptr, *r0 = nullptr, *r1 = nullptr, *rt = nullptr;
     double *u = nullptr, *v = nullptr, *us = nullptr, *vs = nullptr;
     double *ua = nullptr, *va = nullptr, *ub = nullptr, *vb = nullptr, *uc = nullptr, *vc = nullptr;
-    double *Ru = nullptr, *Rv = nullptr, *Du = nullptr, *Dv = nullptr, *rbu = nullptr, *rbv = nullptr;
+    double *Ru = nullptr, *Rv = nullptr, *Du = nullptr, *Dv = nullptr;
     double *p = nullptr, *phi = nullptr, *rhs = nullptr;
     double *rho_n = nullptr, *mu_n = nullptr, *mu_1 = nullptr, *rf_1 = nullptr, *chi_1 = nullptr;
     double *bcbuf = nullptr, *part = nullptr, *waves = nullptr;
+    // Mixed precision: FP32 working copies that the step's stencils read (state
+    // mirrors, materials, reinitialisation stages, momentum right-hand sides,
+    // Jacobi iterates), one allocation.  nullptr for an FP64 tank.
+    float *w32 = nullptr;
     wec::Bc bc{};
     wec::StepScalars *S = nullptr;   // device
     wec::StepScalars *Sh = nullptr;  // pinned host mirror

@@ -235,6 +235,11 @@ def test_full_size_tank_one_step():
 
 
 def test_mixed_precision_step_reaches_tolerance():
+    # The mixed tank computes its stencils and its multigrid preconditioner in
+    # FP32 (storage, residual, Krylov basis, force and heave stay FP64).  A
+    # stencil evaluation takes a few dozen FP32 operations (unit roundoff
+    # 6e-8), so one step perturbs a field by ~1e-6 of its scale; 20 steps stay
+    # below 1e-4.  The projection is solved to the FP64 tolerance every step.
     cfg = synth.tank_small(seed=0)
     g = wec.Tank(cfg, precision=wec.PREC_MIXED)
     o = O.OracleTank(cfg)
@@ -242,8 +247,12 @@ def test_mixed_precision_step_reaches_tolerance():
         rg = g.step(cfg["dt"])
         ro = o.step(cfg["dt"])
         assert rg["status"] == 0 and rg["residual"] <= cfg["solver"]["rtol"]
+    errs = {name: rel(g.get(name), o.get(fo)) for name, fo in FIELDS[:4]}
+    print("mixed vs oracle after 20 steps:", errs, "z", rg["z"], ro["z"])
     assert rg["z"] == pytest.approx(ro["z"], rel=1e-4, abs=1e-9)
-    assert rel(g.get("p"), o.get(O.F_P)) < 1e-6
+    for name in ("sigma", "u", "v"):
+        assert errs[name] < 1e-4, name
+    assert errs["p"] < 1e-5
 
 
 def test_checkpoint_resume_is_bit_identical():
