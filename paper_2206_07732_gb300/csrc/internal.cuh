@@ -17,8 +17,7 @@ constexpr int kMaxRestart = 32;
 constexpr int kMaxCoarse = 512;      // cells on the coarsest multigrid level
 constexpr int kRedBlocks = 304;      // partial-sum blocks of the step's reductions (2 x 152 SMs)
 constexpr int kRedThreads = 256;
-constexpr int kKrylovBlocks = 1216;  // max blocks of the fused Krylov kernels (8 x 152 SMs)
-constexpr int kDotBlocks = 304;      // max blocks of the multi-dot Krylov kernels (2 x 152 SMs)
+constexpr int kKrylovBlocks = 304;   // max CTAs of the Krylov reduction kernels (2 x 152 SMs)
 
 void set_error(const std::string &msg);
 int fail(int code, const std::string &msg);
@@ -65,6 +64,7 @@ struct KState {
     int j, its, jd, cycle_end, done, status, maxit, m, ncycles, pad_;
     unsigned int cnt[4];  // last-block counters of the fused reductions
     double bn, tol, beta, hn, rtol;
+    double ibeta, ihn;    // 1 / beta, 1 / hn (set with them)
 };
 
 }  // namespace wec
@@ -80,9 +80,10 @@ struct wec_poisson {
     float *lu32 = nullptr;
     // FGMRES workspace (FP64 outer iteration)
     double *V = nullptr;        // (m+1) x n
-    void *Z = nullptr;          // m x n, double (FP64) or float (mixed)
+    double *Z = nullptr;        // m x n preconditioned vectors (FP64 in both precisions)
     double *w = nullptr;        // n
-    double *part = nullptr;     // (kMaxRestart+2) x kKrylovBlocks partial sums
+    double *d0 = nullptr;       // n: diagonal of the FP64 level-0 operator
+    double *part = nullptr;     // (kMaxRestart+2) x (kKrylovBlocks / 8) cluster partial sums
     double *dots = nullptr;     // h1, h2 of the two Gram-Schmidt passes
     double *hess = nullptr;     // (m+1) x m Hessenberg, then cs, sn, g, y
     double *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr;

@@ -197,11 +197,12 @@ __global__ void __launch_bounds__(256) k_mg_pre(int nx, int ny, const T *__restr
     }
 }
 
-// x = xp + P x_c, then nu2 sweeps; writes the tile interior of x.  Reads xp and
+// x = xp + P x_c, then nu2 sweeps; writes the tile interior of x (in TO: the
+// level-0 result of an FP32 V-cycle is stored widened to FP64).  Reads xp and
 // writes x (different arrays): tiles read their halos while others write.
-template <typename T, int kTX, int kTY>
+template <typename T, int kTX, int kTY, typename TO>
 __global__ void __launch_bounds__(256) k_mg_post(int nx, int ny, const T *__restrict__ bu, const T *__restrict__ bv,
-                                                 const T *__restrict__ b, const T *__restrict__ xp, T *x,
+                                                 const T *__restrict__ b, const T *__restrict__ xp, TO *x,
                                                  const T *__restrict__ xc, int nu2, int H, const int *bsel,
                                                  const int *xsel)
 {
@@ -219,7 +220,7 @@ __global__ void __launch_bounds__(256) k_mg_post(int nx, int ny, const T *__rest
     }
     for (int k = threadIdx.x; k < kTX * kTY; k += blockDim.x) {
         int li = H + k % kTX, lj = H + k / kTX, gi = t.gx0 + li, gj = t.gy0 + lj;
-        if (gi < nx && gj < ny) x[gj * nx + gi] = t.x[lj * t.ex + li];
+        if (gi < nx && gj < ny) x[gj * nx + gi] = TO(t.x[lj * t.ex + li]);
     }
 }
 
@@ -230,6 +231,7 @@ struct BottomLevels {
     const T *bu[kMaxLevels], *bv[kMaxLevels];
     T *x[kMaxLevels], *b[kMaxLevels];
     const T *lu;
+    double *x0d;  // when set (lb = 0, FP32 levels): level-0 result stored widened here instead of x[0]
 };
 
 // The LU of the coarsest level is staged in shared memory when it takes at most
@@ -404,9 +406,14 @@ __global__ void __launch_bounds__(kBottomThreads) k_mg_bottom(BottomLevels<T> L,
     }
     {
         const long long n = (long long)L.nx[lb] * L.ny[lb];
-        T *xg = lb == 0 ? at_sel(L.x[lb], xsel, n) : L.x[lb];
         const T *x = X(lb);
-        for (int k = threadIdx.x; k < n; k += blockDim.x) xg[k] = x[k];
+        if (lb == 0 && L.x0d) {
+            double *xg = at_sel(L.x0d, xsel, n);
+            for (int k = threadIdx.x; k < n; k += blockDim.x) xg[k] = double(x[k]);
+        } else {
+            T *xg = lb == 0 ? at_sel(L.x[lb], xsel, n) : L.x[lb];
+            for (int k = threadIdx.x; k < n; k += blockDim.x) xg[k] = x[k];
+        }
     }
 }
 

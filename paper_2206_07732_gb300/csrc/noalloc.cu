@@ -9,7 +9,7 @@
 // a completion counter) lives in one file-scope device array instead of memory
 // the caller or the library allocates.
 //
-// The array is sized for at most kNoAllocMaxCells cells (8 MiB + 10 KiB); every
+// The array is sized for at most kNoAllocMaxCells cells (a little over 8 MiB); every
 // GPU that loads the library holds it until the process exits.
 #include <algorithm>
 #include <cmath>

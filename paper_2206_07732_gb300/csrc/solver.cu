@@ -11,11 +11,16 @@
 // Mixed precision: the V-cycle runs in FP32 on FP32 copies of the hierarchy;
 // the Krylov basis, Hessenberg, residuals and the solution stay FP64.
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 
+#include <cooperative_groups.h>
+
 #include "internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace wec {
 namespace {
@@ -154,6 +159,15 @@ __global__ void k_coarsen(int nx, int ny, const T *__restrict__ fu, const T *__r
     }
 }
 
+// out (column outsel, if given) = in widened to FP64
+__global__ void k_widen(long long n, const float *__restrict__ in, double *out, const int *outsel)
+{
+    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    out = at_sel(out, outsel, n);
+    out[c] = double(in[c]);
+}
+
 template <typename TO, typename TI>
 __global__ void k_convert(long long n, const TI *__restrict__ in, TO *__restrict__ out, const int *insel)
 {
@@ -229,7 +243,17 @@ bool g_mg_fused = true;  // fused V-cycle kernels (wec_set_option "mg_fused")
 // Device-resident FGMRES state: the iteration is steered by the GPU, so the
 // same kernels run host-polled (one status read per iteration) or inside one
 // CUDA graph whose WHILE / IF conditional nodes read the state.
-constexpr int KT = 256;  // threads of every fused Krylov kernel (8 warps)
+//
+// Reductions run in three fixed-order stages, so every result is reproducible
+// bit for bit: a shuffle tree per warp and the warps in order within a CTA; the
+// 8 CTAs of a thread-block cluster in rank order through distributed shared
+// memory; then the cluster partials, in the rank-0 CTA of the cluster that
+// finishes last.  Grids are multiples of the cluster size and fit one wave: 2
+// CTAs per SM, about 3.4 elements per thread on the 1024 x 256 grid, so the
+// warp reductions (FP64 adds) are spread over several elements.
+constexpr int KT = 256;   // threads of every fused Krylov kernel (8 warps)
+constexpr int kCl = 8;    // CTAs per cluster of the reduction kernels
+constexpr int KMAXV = kMaxRestart + 1;
 
 __device__ __forceinline__ double warp_sum(double v)
 {
@@ -250,7 +274,38 @@ __device__ double block_sum(double v, double *sh8)
     return r;
 }
 
-// True in the block that finishes last (all other blocks' partials are visible).
+// bsm[k] (k < nk, one per CTA, in shared memory) -> the cluster's sum over its 8
+// CTAs in rank order, written by the rank-0 CTA to part[k * NC + cluster].
+// Every CTA of the cluster calls it (two cluster barriers: the second keeps each
+// CTA's shared memory alive until rank 0 has read it).
+__device__ void cluster_partials(double *bsm, int nk, double *part)
+{
+    cg::cluster_group cl = cg::this_cluster();
+    const int NC = gridDim.x / kCl;
+    cl.sync();
+    if (cl.block_rank() == 0 && threadIdx.x < nk) {
+        double s = 0.0;
+        for (int r = 0; r < kCl; ++r) s += cl.map_shared_rank(bsm, r)[threadIdx.x];
+        part[threadIdx.x * NC + blockIdx.x / kCl] = s;
+    }
+    cl.sync();
+}
+
+// Called by every CTA after cluster_partials: true in the rank-0 CTA of the
+// cluster that finishes last (all cluster partials are then visible).
+__device__ bool last_cluster(unsigned int *cnt)
+{
+    __shared__ int s_last;
+    if (cg::this_cluster().block_rank() != 0) return false;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(cnt, 1u) == gridDim.x / kCl - 1;
+    }
+    __syncthreads();
+    return s_last != 0;
+}
+
+// True in the block that finishes last (all other blocks' writes are visible).
 __device__ bool last_block(unsigned int *cnt)
 {
     __shared__ int s_last;
@@ -263,7 +318,7 @@ __device__ bool last_block(unsigned int *cnt)
     return s_last != 0;
 }
 
-// Deterministic total of the G partials of one quantity.
+// Deterministic total of the G partials of one quantity (one CTA).
 __device__ double final_sum(const double *part, int G, double *sh8)
 {
     double s0 = 0.0, s1 = 0.0;
@@ -274,6 +329,103 @@ __device__ double final_sum(const double *part, int G, double *sh8)
     }
     for (; b < G; b += KT) s0 += __ldcg(part + b);
     return block_sum(s0 + s1, sh8);
+}
+
+// out[k] = sum over the G partials part[k * G + c] (k < nk), one warp per k,
+// lanes over c in a fixed assignment, fixed shuffle tree.
+__device__ __forceinline__ void final_partials(const double *part, int nk, int G, double *out)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = warp; k < nk; k += KT / 32) {
+        double s0 = 0.0, s1 = 0.0;
+        const double *pk = part + k * G;
+        int b = lane;
+        for (; b + 32 < G; b += 64) {
+            s0 += __ldcg(pk + b);
+            s1 += __ldcg(pk + b + 32);
+        }
+        for (; b < G; b += 32) s0 += __ldcg(pk + b);
+        double s = warp_sum(s0 + s1);
+        if (lane == 0) out[k] = s;
+    }
+}
+
+// Warp reduce-scatter of K values per lane (K a power of two, at most 32): each
+// exchange halves the values a lane holds, so the warp spends K - 1 + 5 - log2 K
+// adds per lane instead of 5 K (FP64 adds are as scarce as FP64 FMAs on this
+// GPU).  Afterwards a[0] of lane l is the warp total of value l >> (5 - log2 K).
+// The exchange pattern is fixed: results are reproducible bit for bit.
+template <int M, int O, int K>
+__device__ __forceinline__ void wrs_stage(double (&a)[K], int lane)
+{
+    if constexpr (O > 0) {
+        if constexpr (M > 1) {
+            constexpr int H = M / 2;
+            const bool up = (lane & O) != 0;
+#pragma unroll
+            for (int q = 0; q < H; ++q) {
+                const double send = up ? a[q] : a[H + q];
+                const double keep = up ? a[H + q] : a[q];
+                a[q] = keep + __shfl_xor_sync(0xffffffffu, send, O);
+            }
+            wrs_stage<H, O / 2, K>(a, lane);
+        } else {
+            a[0] += __shfl_xor_sync(0xffffffffu, a[0], O);
+            wrs_stage<1, O / 2, K>(a, lane);
+        }
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void warp_reduce_scatter(double (&a)[K], int lane)
+{
+    wrs_stage<K, 16, K>(a, lane);
+}
+
+template <int K>
+__device__ void block_dots_k(const double *__restrict__ V, const double *__restrict__ w, long long n, int nk,
+                             double (*sh)[KMAXV], double *bsm)
+{
+    constexpr int P2 = K >= 32 ? 5 : K >= 16 ? 4 : K >= 8 ? 3 : K >= 4 ? 2 : K >= 2 ? 1 : 0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double a[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q) a[q] = 0.0;
+    for (long long c = blockIdx.x * (long long)KT + threadIdx.x; c < n; c += (long long)gridDim.x * KT) {
+        const double wc = w[c];
+#pragma unroll
+        for (int q = 0; q < K; ++q)
+            if (q < nk) a[q] += V[(long long)q * n + c] * wc;
+    }
+    warp_reduce_scatter<K>(a, lane);
+    if ((lane & ((32 >> P2) - 1)) == 0) {
+        const int k = lane >> (5 - P2);
+        if (k < nk) sh[warp][k] = a[0];
+    }
+    __syncthreads();
+    if (threadIdx.x < nk) {
+        double r = 0.0;
+        for (int q = 0; q < KT / 32; ++q) r += sh[q][threadIdx.x];
+        bsm[threadIdx.x] = r;
+    }
+}
+
+// The CTA's partials of V_k . w (k < nk <= 32) into bsm[k], in fixed order.
+__device__ void block_dots(const double *__restrict__ V, const double *__restrict__ w, long long n, int nk,
+                           double (*sh)[KMAXV], double *bsm)
+{
+    if (nk <= 1)
+        block_dots_k<1>(V, w, n, nk, sh, bsm);
+    else if (nk <= 2)
+        block_dots_k<2>(V, w, n, nk, sh, bsm);
+    else if (nk <= 4)
+        block_dots_k<4>(V, w, n, nk, sh, bsm);
+    else if (nk <= 8)
+        block_dots_k<8>(V, w, n, nk, sh, bsm);
+    else if (nk <= 16)
+        block_dots_k<16>(V, w, n, nk, sh, bsm);
+    else
+        block_dots_k<32>(V, w, n, nk, sh, bsm);
 }
 
 __device__ __forceinline__ void set_cond(unsigned long long h, int use, unsigned int v)
@@ -295,18 +447,30 @@ __global__ void k_ks_init(KState *ks, double rtol, int maxit, int m)
     ks->ncycles = 0;
 }
 
+// d = diag(A) of level 0 (FP64), once per set of coefficients.
+__global__ void k_diag0(int nx, int ny, const double *__restrict__ bu, const double *__restrict__ bv,
+                        double *__restrict__ d)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nx * ny) return;
+    const int j = c / nx, i = c - j * nx;
+    d[c] = diag_at(bu, bv, nx, ny, i, j);
+}
+
 // bn = ||b||_2, tol = rtol bn.
-__global__ void __launch_bounds__(KT) k_bnorm(long long n, const double *__restrict__ b, double *part,
-                                                KState *ks)
+__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 2)
+    k_bnorm(long long n, const double *__restrict__ b, double *part, KState *ks)
 {
     __shared__ double sh[KT / 32];
+    __shared__ double bsm[1];
     double a = 0.0;
     for (long long c = blockIdx.x * (long long)KT + threadIdx.x; c < n; c += (long long)gridDim.x * KT)
         a += b[c] * b[c];
     a = block_sum(a, sh);
-    if (threadIdx.x == 0) part[blockIdx.x] = a;
-    if (!last_block(&ks->cnt[0])) return;
-    double t = final_sum(part, gridDim.x, sh);
+    if (threadIdx.x == 0) bsm[0] = a;
+    cluster_partials(bsm, 1, part);
+    if (!last_cluster(&ks->cnt[0])) return;
+    double t = final_sum(part, gridDim.x / kCl, sh);
     if (threadIdx.x == 0) {
         double bn = sqrt(t);
         ks->bn = bn;
@@ -319,13 +483,13 @@ __global__ void __launch_bounds__(KT) k_bnorm(long long n, const double *__restr
 // mode 1 (end of a cycle): converged, out of iterations, or restart.
 // A zero right-hand side gives x = 0.  Opens a new Arnoldi cycle unless done and
 // sets the WHILE condition to !done.
-__global__ void __launch_bounds__(KT) k_residual_norm(int nx, int ny, const double *__restrict__ bu,
-                                                        const double *__restrict__ bv, const double *__restrict__ b,
-                                                        double *x, double *__restrict__ w, double *part,
-                                                        KState *ks, double *g, int mode,
-                                                        unsigned long long hwhile, int use)
+__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 2)
+    k_residual_norm(int nx, int ny, const double *__restrict__ bu, const double *__restrict__ bv,
+                    const double *__restrict__ d0, const double *__restrict__ b, double *x, double *__restrict__ w,
+                    double *part, KState *ks, double *g, int mode, unsigned long long hwhile, int use)
 {
     __shared__ double sh[KT / 32];
+    __shared__ double bsm[1];
     const long long n = (long long)nx * ny;
     const bool zero = ks->bn == 0.0;
     double a = 0.0;
@@ -335,19 +499,20 @@ __global__ void __launch_bounds__(KT) k_residual_norm(int nx, int ny, const doub
             w[c] = 0.0;
             continue;
         }
-        int i = (int)(c % nx), j = (int)(c / nx);
-        double d = diag_at(bu, bv, nx, ny, i, j);
-        double r = b[c] - (d * x[c] - offsum_at(bu, bv, x, nx, ny, i, j));
+        const int j = (int)(c / nx), i = (int)(c - (long long)j * nx);
+        double r = b[c] - (d0[c] * x[c] - offsum_at(bu, bv, x, nx, ny, i, j));
         w[c] = r;
         a += r * r;
     }
     a = block_sum(a, sh);
-    if (threadIdx.x == 0) part[blockIdx.x] = a;
-    if (!last_block(&ks->cnt[1])) return;
-    double t = final_sum(part, gridDim.x, sh);
+    if (threadIdx.x == 0) bsm[0] = a;
+    cluster_partials(bsm, 1, part);
+    if (!last_cluster(&ks->cnt[1])) return;
+    double t = final_sum(part, gridDim.x / kCl, sh);
     if (threadIdx.x == 0) {
         double beta = sqrt(t);
         ks->beta = beta;
+        ks->ibeta = beta != 0.0 ? 1.0 / beta : 0.0;
         if (mode == 1) ks->ncycles += 1;
         int done;
         if (zero) {
@@ -375,127 +540,92 @@ __global__ void __launch_bounds__(KT) k_residual_norm(int nx, int ny, const doub
     }
 }
 
-// V_0 = w / beta for a new cycle.
-__global__ void k_scale0(long long n, const double *__restrict__ w, double *__restrict__ V, const KState *ks)
+// V_0 = w / beta for a new cycle (and its FP32 copy b32 for a mixed V-cycle).
+__global__ void k_scale0(long long n, const double *__restrict__ w, double *__restrict__ V, float *__restrict__ b32,
+                         const KState *ks)
 {
     if (ks->done) return;
-    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (c < n) V[c] = w[c] / ks->beta;
-}
-
-// Block partials of V_k . w for k <= j: for each k the threads of a warp sum
-// their elements and shuffle-reduce (no block barrier per k); one barrier, then
-// thread k adds the warps' sums in warp order.  part[k * G + block].
-constexpr int KMAXV = kMaxRestart + 1;
-
-__device__ __forceinline__ void multi_dot_partials(const double *__restrict__ V, const double *__restrict__ w,
-                                                   long long n, int nk, double *part, double (*sh)[KMAXV])
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int k = 0; k < nk; ++k) {
-        const double *vk = V + (long long)k * n;
-        double a = 0.0;
-        for (long long c = blockIdx.x * (long long)KT + threadIdx.x; c < n; c += (long long)gridDim.x * KT)
-            a += vk[c] * w[c];
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-        if (lane == 0) sh[warp][k] = a;
-    }
-    __syncthreads();
-    if (threadIdx.x < nk) {
-        double r = 0.0;
-        for (int q = 0; q < KT / 32; ++q) r += sh[q][threadIdx.x];
-        part[threadIdx.x * gridDim.x + blockIdx.x] = r;
-    }
-}
-
-// In the last block: out[k] = sum over blocks of part[k * G + b], one warp per k,
-// lanes over blocks in a fixed assignment, fixed shuffle tree.
-__device__ __forceinline__ void final_partials(const double *part, int nk, double *out)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, G = gridDim.x;
-    for (int k = warp; k < nk; k += KT / 32) {
-        // four independent chains so the loads overlap
-        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-        const double *pk = part + k * G;
-        int b = lane;
-        for (; b + 96 < G; b += 128) {
-            s0 += __ldcg(pk + b);
-            s1 += __ldcg(pk + b + 32);
-            s2 += __ldcg(pk + b + 64);
-            s3 += __ldcg(pk + b + 96);
-        }
-        for (; b < G; b += 32) s0 += __ldcg(pk + b);
-        double s = (s0 + s1) + (s2 + s3);
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        if (lane == 0) out[k] = s;
-    }
+    const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    const double v = w[c] * ks->ibeta;
+    V[c] = v;
+    if (b32) b32[c] = (float)v;
 }
 
 // w = A z_j and the first Gram-Schmidt dot products h1_k = V_k . w (k <= j).
-template <typename TZ>
-__global__ void __launch_bounds__(KT) k_matvec_dots(int nx, int ny, const double *__restrict__ bu,
-                                                      const double *__restrict__ bv, const TZ *__restrict__ Z,
-                                                      const double *__restrict__ V, double *w,
-                                                      double *part, double *h1, KState *ks)
+__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 2)
+    k_matvec_dots(int nx, int ny, const double *__restrict__ bu, const double *__restrict__ bv,
+                  const double *__restrict__ d0, const double *__restrict__ Z, const double *__restrict__ V, double *w,
+                  double *part, double *h1, KState *ks)
 {
     __shared__ double sh[KT / 32][KMAXV];
+    __shared__ double bsm[KMAXV];
     const long long n = (long long)nx * ny;
     const int j = ks->j, nk = j + 1;
-    const TZ *z = Z + (long long)j * n;
+    const double *z = Z + (long long)j * n;
     for (long long c = blockIdx.x * (long long)KT + threadIdx.x; c < n; c += (long long)gridDim.x * KT) {
-        int i = (int)(c % nx), jj = (int)(c / nx);
-        double d = diag_at(bu, bv, nx, ny, i, jj);
-        w[c] = d * double(z[c]) - offsum_at(bu, bv, z, nx, ny, i, jj);
+        const int jj = (int)(c / nx), i = (int)(c - (long long)jj * nx);
+        w[c] = d0[c] * z[c] - offsum_at(bu, bv, z, nx, ny, i, jj);
     }
-    multi_dot_partials(V, w, n, nk, part, sh);
-    if (!last_block(&ks->cnt[2])) return;
-    final_partials(part, nk, h1);
+    block_dots(V, w, n, nk, sh, bsm);
+    cluster_partials(bsm, nk, part);
+    if (!last_cluster(&ks->cnt[2])) return;
+    final_partials(part, nk, gridDim.x / kCl, h1);
     if (threadIdx.x == 0) ks->cnt[2] = 0;
 }
 
 // First Gram-Schmidt update w -= sum_k h1_k V_k, then h2_k = V_k . w.
-__global__ void __launch_bounds__(KT) k_orth_dots(long long n, const double *__restrict__ V, double *w,
-                                                    const double *__restrict__ h1, double *part, double *h2,
-                                                    KState *ks)
+__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 2)
+    k_orth_dots(long long n, const double *__restrict__ V, double *w, const double *__restrict__ h1, double *part,
+                double *h2, KState *ks)
 {
     __shared__ double sh[KT / 32][KMAXV];
+    __shared__ double bsm[KMAXV];
     __shared__ double hs[KMAXV];
     const int j = ks->j, nk = j + 1;
     if (threadIdx.x < nk) hs[threadIdx.x] = h1[threadIdx.x];
     __syncthreads();
     for (long long c = blockIdx.x * (long long)KT + threadIdx.x; c < n; c += (long long)gridDim.x * KT) {
         double a = w[c];
+#pragma unroll 4
         for (int k = 0; k < nk; ++k) a -= hs[k] * V[(long long)k * n + c];
         w[c] = a;
     }
-    multi_dot_partials(V, w, n, nk, part, sh);
-    if (!last_block(&ks->cnt[2])) return;
-    final_partials(part, nk, h2);
+    block_dots(V, w, n, nk, sh, bsm);
+    cluster_partials(bsm, nk, part);
+    if (!last_cluster(&ks->cnt[2])) return;
+    final_partials(part, nk, gridDim.x / kCl, h2);
     if (threadIdx.x == 0) ks->cnt[2] = 0;
 }
 
-// Second update w -= sum_k h2_k V_k and h_{j+1,j} = ||w||; the last block applies
-// the Givens rotations to column j, counts the iteration, decides whether the
-// cycle ends (converged estimate, iteration cap, breakdown, or full basis) and
-// sets the IF condition.
-__global__ void __launch_bounds__(KT) k_orth_norm(long long n, const double *__restrict__ V, double *__restrict__ w,
-                                                    const double *__restrict__ h1, const double *__restrict__ h2,
-                                                    double *part, KState *ks, double *H, double *cs, double *sn,
-                                                    double *g, unsigned long long hif, int use)
+// Second update w -= sum_k h2_k V_k and h_{j+1,j} = ||w||; the last cluster
+// applies the Givens rotations to column j, counts the iteration, decides whether
+// the cycle ends (converged estimate, iteration cap, breakdown, or full basis)
+// and sets the IF condition.
+__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 2)
+    k_orth_norm(long long n, const double *__restrict__ V, double *__restrict__ w, const double *__restrict__ h1,
+                const double *__restrict__ h2, double *part, KState *ks, double *H, double *cs, double *sn,
+                double *g, unsigned long long hif, int use)
 {
     __shared__ double sh[KT / 32];
-    const int j = ks->j, G = gridDim.x;
+    __shared__ double bsm[1];
+    __shared__ double hs[KMAXV];
+    const int j = ks->j;
+    if (threadIdx.x <= j) hs[threadIdx.x] = h2[threadIdx.x];
+    __syncthreads();
     double a2 = 0.0;
-    for (long long c = blockIdx.x * (long long)KT + threadIdx.x; c < n; c += (long long)G * KT) {
+    for (long long c = blockIdx.x * (long long)KT + threadIdx.x; c < n; c += (long long)gridDim.x * KT) {
         double a = w[c];
-        for (int k = 0; k <= j; ++k) a -= h2[k] * V[(long long)k * n + c];
+#pragma unroll 4
+        for (int k = 0; k <= j; ++k) a -= hs[k] * V[(long long)k * n + c];
         w[c] = a;
         a2 += a * a;
     }
     a2 = block_sum(a2, sh);
-    if (threadIdx.x == 0) part[blockIdx.x] = a2;
-    if (!last_block(&ks->cnt[2])) return;
-    double t = final_sum(part, G, sh);
+    if (threadIdx.x == 0) bsm[0] = a2;
+    cluster_partials(bsm, 1, part);
+    if (!last_cluster(&ks->cnt[2])) return;
+    double t = final_sum(part, gridDim.x / kCl, sh);
     if (threadIdx.x != 0) return;
     const int m = ks->m;
     for (int k = 0; k <= j; ++k) H[k * m + j] = (0.0 + h1[k]) + h2[k];
@@ -517,6 +647,7 @@ __global__ void __launch_bounds__(KT) k_orth_norm(long long n, const double *__r
     ks->its += 1;
     ks->jd = j + 1;
     ks->hn = hn;
+    ks->ihn = hn != 0.0 ? 1.0 / hn : 0.0;
     double est = fabs(g[j + 1]);
     int ce = est <= ks->tol || ks->its >= ks->maxit || hn == 0.0 || j + 1 == m || !isfinite(est);
     if (!isfinite(est)) ks->status = WEC_ERR_NONFINITE;
@@ -525,15 +656,20 @@ __global__ void __launch_bounds__(KT) k_orth_norm(long long n, const double *__r
     set_cond(hif, use, (unsigned)ce);
 }
 
-// V_{j+1} = w / h_{j+1,j}, then j += 1 (unless the cycle ends).
-__global__ void __launch_bounds__(KT) k_next_basis(long long n, const double *__restrict__ w, double *V, KState *ks)
+// V_{j+1} = w / h_{j+1,j} (and its FP32 copy b32 for a mixed V-cycle), then
+// j += 1 (unless the cycle ends).
+__global__ void __launch_bounds__(KT) k_next_basis(long long n, const double *__restrict__ w, double *V,
+                                                     float *__restrict__ b32, KState *ks)
 {
     const int j = ks->j;
     if (!ks->cycle_end) {
         double *vn = V + (long long)(j + 1) * n;
-        const double hn = ks->hn;
-        for (long long c = blockIdx.x * (long long)KT + threadIdx.x; c < n; c += (long long)gridDim.x * KT)
-            vn[c] = w[c] / hn;
+        const double ih = ks->ihn;
+        for (long long c = blockIdx.x * (long long)KT + threadIdx.x; c < n; c += (long long)gridDim.x * KT) {
+            const double v = w[c] * ih;
+            vn[c] = v;
+            if (b32) b32[c] = (float)v;
+        }
     }
     if (!last_block(&ks->cnt[3])) return;
     if (threadIdx.x == 0) {
@@ -553,15 +689,15 @@ __global__ void k_backsolve(int m, const double *__restrict__ H, const double *_
     }
 }
 
-template <typename TZ>
-__global__ void k_update_x(long long n, const double *__restrict__ y, const TZ *__restrict__ Z, double *__restrict__ x,
+__global__ void k_update_x(long long n, const double *__restrict__ y, const double *__restrict__ Z, double *__restrict__ x,
                            const KState *ks)
 {
     long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (c >= n) return;
     const int jd = ks->jd;
     double a = x[c];
-    for (int k = 0; k < jd; ++k) a += y[k] * double(Z[(long long)k * n + c]);
+#pragma unroll 4
+    for (int k = 0; k < jd; ++k) a += y[k] * Z[(long long)k * n + c];
     x[c] = a;
 }
 
@@ -631,7 +767,9 @@ int set_attrs_one()
 {
     const int mx = (int)tile_smem<T>(8, TX, TY);
     WEC_CK(cudaFuncSetAttribute(k_mg_pre<T, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-    WEC_CK(cudaFuncSetAttribute(k_mg_post<T, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    WEC_CK(cudaFuncSetAttribute(k_mg_post<T, TX, TY, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    if constexpr (sizeof(T) == 4)
+        WEC_CK(cudaFuncSetAttribute(k_mg_post<T, TX, TY, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
     return WEC_OK;
 }
 
@@ -655,13 +793,13 @@ void launch_pre_t(const Level<T> &A, const T *b, T *bc, int nu1, int H, const in
     k_mg_pre<T, TX, TY><<<grid, 256, tile_smem<T>(H, TX, TY), st>>>(A.nx, A.ny, A.bu, A.bv, b, A.xp, bc, nu1, H, bsel);
 }
 
-template <typename T, int TX, int TY>
-void launch_post_t(const Level<T> &A, const T *b, T *x, const T *xc, int nu2, int H, const int *bsel,
+template <typename T, int TX, int TY, typename TO>
+void launch_post_t(const Level<T> &A, const T *b, TO *x, const T *xc, int nu2, int H, const int *bsel,
                    const int *xsel, cudaStream_t st)
 {
     dim3 grid((A.nx + TX - 1) / TX, (A.ny + TY - 1) / TY);
-    k_mg_post<T, TX, TY><<<grid, 256, tile_smem<T>(H, TX, TY), st>>>(A.nx, A.ny, A.bu, A.bv, b, A.xp, x, xc, nu2, H,
-                                                                     bsel, xsel);
+    k_mg_post<T, TX, TY, TO><<<grid, 256, tile_smem<T>(H, TX, TY), st>>>(A.nx, A.ny, A.bu, A.bv, b, A.xp, x, xc, nu2,
+                                                                         H, bsel, xsel);
 }
 
 template <typename T>
@@ -675,22 +813,22 @@ void launch_pre(int tile, const Level<T> &A, const T *b, T *bc, int nu1, int H, 
     }
 }
 
-template <typename T>
-void launch_post(int tile, const Level<T> &A, const T *b, T *x, const T *xc, int nu2, int H, const int *bsel,
+template <typename T, typename TO>
+void launch_post(int tile, const Level<T> &A, const T *b, TO *x, const T *xc, int nu2, int H, const int *bsel,
                  const int *xsel, cudaStream_t st)
 {
     switch (tile) {
-    case 1: launch_post_t<T, 32, 16>(A, b, x, xc, nu2, H, bsel, xsel, st); break;
-    case 2: launch_post_t<T, 32, 8>(A, b, x, xc, nu2, H, bsel, xsel, st); break;
-    case 3: launch_post_t<T, 16, 8>(A, b, x, xc, nu2, H, bsel, xsel, st); break;
-    default: launch_post_t<T, 64, 16>(A, b, x, xc, nu2, H, bsel, xsel, st); break;
+    case 1: launch_post_t<T, 32, 16, TO>(A, b, x, xc, nu2, H, bsel, xsel, st); break;
+    case 2: launch_post_t<T, 32, 8, TO>(A, b, x, xc, nu2, H, bsel, xsel, st); break;
+    case 3: launch_post_t<T, 16, 8, TO>(A, b, x, xc, nu2, H, bsel, xsel, st); break;
+    default: launch_post_t<T, 64, 16, TO>(A, b, x, xc, nu2, H, bsel, xsel, st); break;
     }
 }
 
 // Fused V-cycle: per fine level one pre and one post kernel, one CTA for the
-// levels of at most kBottomCells cells.
-template <typename T>
-void vcycle_fused(wec_poisson *P, Level<T> *L, const T *b0, T *x0, const int *bsel, const int *xsel,
+// levels of at most kBottomCells cells.  The level-0 result x0 is stored in TO.
+template <typename T, typename TO>
+void vcycle_fused(wec_poisson *P, Level<T> *L, const T *b0, TO *x0, const int *bsel, const int *xsel,
                   cudaStream_t st)
 {
     const double ts = sizeof(T);
@@ -705,8 +843,14 @@ void vcycle_fused(wec_poisson *P, Level<T> *L, const T *b0, T *x0, const int *bs
         B.ny[l] = L[l].ny;
         B.bu[l] = L[l].bu;
         B.bv[l] = L[l].bv;
-        B.x[l] = l == 0 ? x0 : L[l].x;
+        B.x[l] = l == 0 ? nullptr : L[l].x;
         B.b[l] = l == 0 ? (T *)b0 : L[l].b;
+    }
+    if constexpr (std::is_same<T, TO>::value) {
+        B.x[0] = x0;
+        B.x0d = nullptr;
+    } else {
+        B.x0d = x0;  // FP32 levels, FP64 level-0 result
     }
     // first level small enough, whose staging (with all coarser levels) fits in shared memory
     int lb = 0;
@@ -734,8 +878,10 @@ void vcycle_fused(wec_poisson *P, Level<T> *L, const T *b0, T *x0, const int *bs
         Level<T> &A = L[l];
         const double n = (double)A.nx * A.ny, nf = (double)(A.nx + 1) * A.ny + (double)A.nx * (A.ny + 1);
         WEC_PROF("mg_post", l, (3.25 * n + nf) * ts, st);
-        launch_post<T>(tiles[l], A, l == 0 ? b0 : A.b, l == 0 ? x0 : A.x, L[l + 1].x, P->nu2, H,
-                       l == 0 ? bsel : nullptr, l == 0 ? xsel : nullptr, st);
+        if (l == 0)
+            launch_post<T, TO>(tiles[0], A, b0, x0, L[1].x, P->nu2, H, bsel, xsel, st);
+        else
+            launch_post<T, T>(tiles[l], A, A.b, A.x, L[l + 1].x, P->nu2, H, nullptr, nullptr, st);
     }
 }
 
@@ -766,7 +912,7 @@ int autotune_levels(wec_poisson *P, Level<T> *L, int *tiles, cudaStream_t st)
             for (int r = 0; r < 3; ++r) {
                 cudaEventRecord(e0, st);
                 launch_pre<T>(t, A, b, L[l + 1].b, P->nu1, H, nullptr, st);
-                launch_post<T>(t, A, b, x, L[l + 1].x, P->nu2, H, nullptr, nullptr, st);
+                launch_post<T, T>(t, A, b, x, L[l + 1].x, P->nu2, H, nullptr, nullptr, st);
                 cudaEventRecord(e1, st);
                 cudaError_t e = cudaEventSynchronize(e1);
                 float ms = 0.f;
@@ -818,18 +964,67 @@ int poisson_autotune(wec_poisson *P, cudaStream_t st)
     return WEC_OK;
 }
 
-template <typename T>
-void vcycle_t(wec_poisson *P, Level<T> *L, const T *b0, T *x0, const int *bsel, const int *xsel, cudaStream_t st)
+// x0 = M^{-1} b0 by one V-cycle over the levels L (precision T); the level-0
+// result is stored in TO (an FP32 V-cycle may deliver FP64).
+template <typename T, typename TO>
+void vcycle_t(wec_poisson *P, Level<T> *L, const T *b0, TO *x0, const int *bsel, const int *xsel, cudaStream_t st)
 {
-    if (g_mg_fused)
-        vcycle_fused<T>(P, L, b0, x0, bsel, xsel, st);
-    else
+    if (g_mg_fused) {
+        vcycle_fused<T, TO>(P, L, b0, x0, bsel, xsel, st);
+    } else if constexpr (std::is_same<T, TO>::value) {
         vcycle_unfused<T>(P, L, b0, x0, bsel, xsel, st);
+    } else {
+        // one-pass kernels smooth in place: run on the FP32 level-0 scratch, then widen
+        const long long n = (long long)L[0].nx * L[0].ny;
+        vcycle_unfused<T>(P, L, b0, L[0].x, bsel, nullptr, st);
+        WEC_PROF("convert", 0, 12.0 * n, st);
+        k_widen<<<nblk(n, 256), 256, 0, st>>>(n, L[0].x, x0, xsel);
+    }
 }
 
-int kgrid(long long n) { return (int)std::min<long long>(nblk(n, KT), kDotBlocks); }
-// the multi-dot kernels keep a few elements per thread: fewer blocks to sum at the end
-int kgrid_dots(long long n) { return (int)std::min<long long>(nblk(n, KT), kDotBlocks); }
+// CTAs of the cluster reduction kernels that run as one wave on this GPU: the
+// scheduler places whole clusters inside a GPC, so the count comes from the
+// occupancy query, not from SMs x CTAs per SM.  Set once by poisson_init.
+int g_kgrid_max = kKrylovBlocks;
+
+template <typename K>
+int clusters_resident(K kern, int *out)
+{
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = kCl;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(kKrylovBlocks);
+    cfg.blockDim = dim3(KT);
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    WEC_CK(cudaOccupancyMaxActiveClusters(out, (void *)kern, &cfg));
+    return WEC_OK;
+}
+
+int set_kgrid_max()
+{
+    int c[6];
+    int e = clusters_resident(k_bnorm, &c[0]);
+    if (!e) e = clusters_resident(k_residual_norm, &c[1]);
+    if (!e) e = clusters_resident(k_matvec_dots, &c[2]);
+    if (!e) e = clusters_resident(k_matvec_dots, &c[3]);
+    if (!e) e = clusters_resident(k_orth_dots, &c[4]);
+    if (!e) e = clusters_resident(k_orth_norm, &c[5]);
+    if (e) return e;
+    int m = *std::min_element(c, c + 6);
+    g_kgrid_max = std::max(1, std::min(m, kKrylovBlocks / kCl)) * kCl;
+    return WEC_OK;
+}
+
+// Reduction kernels: a multiple of the cluster size, at most one wave.
+int kgrid(long long n)
+{
+    const long long g = std::min<long long>(nblk(n, KT), g_kgrid_max);
+    return (int)((g + kCl - 1) / kCl * kCl);
+}
 
 // ---------------------------------------------------------- FGMRES parts ----
 void enqueue_begin(wec_poisson *P, const double *b, double *x, double rtol, int maxit, unsigned long long hw,
@@ -838,6 +1033,7 @@ void enqueue_begin(wec_poisson *P, const double *b, double *x, double rtol, int 
     const long long n = (long long)P->nx * P->ny;
     const double nf = (P->nx + 1.0) * P->ny + P->nx * (P->ny + 1.0);
     const int G = kgrid(n);
+    float *b32 = P->prec == WEC_PREC_MIXED ? P->L32[0].b : nullptr;
     {
         WEC_PROF("scalar", -1, 64.0, st);
         k_ks_init<<<1, 1, 0, st>>>(P->ks, rtol, maxit, P->restart);
@@ -847,12 +1043,12 @@ void enqueue_begin(wec_poisson *P, const double *b, double *x, double rtol, int 
         k_bnorm<<<G, KT, 0, st>>>(n, b, P->part, P->ks);
     }
     {
-        WEC_PROF("krylov_residual", -1, 8.0 * (3.0 * n + nf), st);
-        k_residual_norm<<<G, KT, 0, st>>>(P->nx, P->ny, P->L64[0].bu, P->L64[0].bv, b, x, P->w, P->part, P->ks,
-                                          P->g, 0, hw, use);
+        WEC_PROF("krylov_residual", -1, 8.0 * (4.0 * n + nf), st);
+        k_residual_norm<<<G, KT, 0, st>>>(P->nx, P->ny, P->L64[0].bu, P->L64[0].bv, P->d0, b, x, P->w, P->part,
+                                          P->ks, P->g, 0, hw, use);
     }
-    WEC_PROF("krylov_scale", -1, 16.0 * n, st);
-    k_scale0<<<nblk(n, 256), 256, 0, st>>>(n, P->w, P->V, P->ks);
+    WEC_PROF("krylov_scale", -1, (16.0 + (b32 ? 4.0 : 0.0)) * n, st);
+    k_scale0<<<nblk(n, 256), 256, 0, st>>>(n, P->w, P->V, b32, P->ks);
 }
 
 // One Arnoldi step j (preconditioner, matvec, CGS2, Givens, next basis vector).
@@ -861,37 +1057,29 @@ void enqueue_body(wec_poisson *P, unsigned long long hif, int use, cudaStream_t 
 {
     const long long n = (long long)P->nx * P->ny;
     const double nf = (P->nx + 1.0) * P->ny + P->nx * (P->ny + 1.0);
-    const int G = kgrid(n), Gd = kgrid_dots(n), m = P->restart;
-    const size_t zsz = P->prec == WEC_PREC_FP64 ? 8 : 4;
+    const int G = kgrid(n), m = P->restart;
+    const bool mixed = P->prec == WEC_PREC_MIXED;
     double *h1 = P->dots, *h2 = P->dots + (kMaxRestart + 2);
-    if (P->prec == WEC_PREC_FP64) {
-        vcycle_t<double>(P, P->L64, P->V, (double *)P->Z, &P->ks->j, &P->ks->j, st);
-    } else {
-        {
-            WEC_PROF("convert", -1, 12.0 * n, st);
-            k_convert<float, double><<<nblk(n, 256), 256, 0, st>>>(n, P->V, P->L32[0].b, &P->ks->j);
-        }
-        vcycle_t<float>(P, P->L32, P->L32[0].b, (float *)P->Z, nullptr, &P->ks->j, st);
-    }
+    // the mixed V-cycle reads b = V_j in FP32, written beside V_j by k_scale0 / k_next_basis
+    if (!mixed)
+        vcycle_t<double, double>(P, P->L64, P->V, P->Z, &P->ks->j, &P->ks->j, st);
+    else
+        vcycle_t<float, double>(P, P->L32, P->L32[0].b, P->Z, nullptr, &P->ks->j, st);
     {
-        WEC_PROF("krylov_matvec_dots", -1, 8.0 * (n + nf) + (double)zsz * n + 8.0 * n * m, st);
-        if (P->prec == WEC_PREC_FP64)
-            k_matvec_dots<double><<<Gd, KT, 0, st>>>(P->nx, P->ny, P->L64[0].bu, P->L64[0].bv, (const double *)P->Z,
-                                                    P->V, P->w, P->part, h1, P->ks);
-        else
-            k_matvec_dots<float><<<Gd, KT, 0, st>>>(P->nx, P->ny, P->L64[0].bu, P->L64[0].bv, (const float *)P->Z,
-                                                   P->V, P->w, P->part, h1, P->ks);
+        WEC_PROF("krylov_matvec_dots", -1, 8.0 * (3.0 * n + nf) + 8.0 * n * m, st);
+        k_matvec_dots<<<G, KT, 0, st>>>(P->nx, P->ny, P->L64[0].bu, P->L64[0].bv, P->d0, P->Z, P->V, P->w, P->part,
+                                        h1, P->ks);
     }
     {
         WEC_PROF("krylov_orth_dots", -1, 8.0 * n * (m + 2), st);
-        k_orth_dots<<<Gd, KT, 0, st>>>(n, P->V, P->w, h1, P->part, h2, P->ks);
+        k_orth_dots<<<G, KT, 0, st>>>(n, P->V, P->w, h1, P->part, h2, P->ks);
     }
     {
         WEC_PROF("krylov_orth_norm", -1, 8.0 * n * (m + 2), st);
         k_orth_norm<<<G, KT, 0, st>>>(n, P->V, P->w, h1, h2, P->part, P->ks, P->hess, P->cs, P->sn, P->g, hif, use);
     }
-    WEC_PROF("krylov_next_basis", -1, 16.0 * n, st);
-    k_next_basis<<<G, KT, 0, st>>>(n, P->w, P->V, P->ks);
+    WEC_PROF("krylov_next_basis", -1, (16.0 + (mixed ? 4.0 : 0.0)) * n, st);
+    k_next_basis<<<nblk(n, KT), KT, 0, st>>>(n, P->w, P->V, mixed ? P->L32[0].b : nullptr, P->ks);
 }
 
 // End of a cycle: y from the triangular system, x += Z y, true residual, then
@@ -901,25 +1089,22 @@ void enqueue_close(wec_poisson *P, const double *b, double *x, unsigned long lon
     const long long n = (long long)P->nx * P->ny;
     const double nf = (P->nx + 1.0) * P->ny + P->nx * (P->ny + 1.0);
     const int G = kgrid(n), m = P->restart;
-    const size_t zsz = P->prec == WEC_PREC_FP64 ? 8 : 4;
+    const bool mixed = P->prec == WEC_PREC_MIXED;
     {
         WEC_PROF("scalar", -1, 8.0 * m * m, st);
         k_backsolve<<<1, 1, 0, st>>>(m, P->hess, P->g, P->y, P->ks);
     }
     {
-        WEC_PROF("krylov_update_x", -1, 16.0 * n + (double)zsz * n * m, st);
-        if (P->prec == WEC_PREC_FP64)
-            k_update_x<double><<<nblk(n, 256), 256, 0, st>>>(n, P->y, (const double *)P->Z, x, P->ks);
-        else
-            k_update_x<float><<<nblk(n, 256), 256, 0, st>>>(n, P->y, (const float *)P->Z, x, P->ks);
+        WEC_PROF("krylov_update_x", -1, 16.0 * n + 8.0 * n * m, st);
+        k_update_x<<<nblk(n, 256), 256, 0, st>>>(n, P->y, P->Z, x, P->ks);
     }
     {
-        WEC_PROF("krylov_residual", -1, 8.0 * (3.0 * n + nf), st);
-        k_residual_norm<<<G, KT, 0, st>>>(P->nx, P->ny, P->L64[0].bu, P->L64[0].bv, b, x, P->w, P->part, P->ks,
-                                          P->g, 1, hw, use);
+        WEC_PROF("krylov_residual", -1, 8.0 * (4.0 * n + nf), st);
+        k_residual_norm<<<G, KT, 0, st>>>(P->nx, P->ny, P->L64[0].bu, P->L64[0].bv, P->d0, b, x, P->w, P->part,
+                                          P->ks, P->g, 1, hw, use);
     }
-    WEC_PROF("krylov_scale", -1, 16.0 * n, st);
-    k_scale0<<<nblk(n, 256), 256, 0, st>>>(n, P->w, P->V, P->ks);
+    WEC_PROF("krylov_scale", -1, (16.0 + (mixed ? 4.0 : 0.0)) * n, st);
+    k_scale0<<<nblk(n, 256), 256, 0, st>>>(n, P->w, P->V, mixed ? P->L32[0].b : nullptr, P->ks);
 }
 
 int read_state(wec_poisson *P, cudaStream_t st)
@@ -951,6 +1136,7 @@ int poisson_init(wec_poisson *P, int nx, int ny, int prec, int restart, int nu1,
         if (int e = set_tile_attrs()) return e;
         WEC_CK(cudaFuncSetAttribute(k_mg_bottom<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBottomSmemMax));
         WEC_CK(cudaFuncSetAttribute(k_mg_bottom<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBottomSmemMax));
+        if (int e = set_kgrid_max()) return e;
         attrs_done = true;
     }
     if (nx < 2 || ny < 2) return fail(WEC_ERR_INVALID, "poisson: nx, ny must be >= 2");
@@ -1001,9 +1187,11 @@ int poisson_init(wec_poisson *P, int nx, int ny, int prec, int restart, int nu1,
     size_t n = (size_t)nx * ny;
     int m = restart;
     WEC_CK(cudaMalloc(&P->V, (m + 1) * n * 8));
-    WEC_CK(cudaMalloc(&P->Z, m * n * (prec == WEC_PREC_FP64 ? 8 : 4)));
+    WEC_CK(cudaMalloc(&P->Z, m * n * 8));
     WEC_CK(cudaMalloc(&P->w, n * 8));
-    WEC_CK(cudaMalloc(&P->part, (size_t)(kMaxRestart + 2) * kKrylovBlocks * 8));
+    WEC_CK(cudaMalloc(&P->d0, n * 8));
+    // reduction partials: one per cluster and quantity (k_next_basis counts blocks only)
+    WEC_CK(cudaMalloc(&P->part, (size_t)(kMaxRestart + 2) * (kKrylovBlocks / kCl) * 8));
     WEC_CK(cudaMalloc(&P->dots, 2 * (kMaxRestart + 2) * 8));
     size_t nh = (size_t)(m + 1) * m + 3 * (m + 1) + m + 8;
     WEC_CK(cudaMalloc(&P->hess, nh * 8));
@@ -1015,7 +1203,7 @@ int poisson_init(wec_poisson *P, int nx, int ny, int prec, int restart, int nu1,
     WEC_CK(cudaMalloc(&P->ks, sizeof(KState)));
     WEC_CK(cudaMemset(P->ks, 0, sizeof(KState)));
     WEC_CK(cudaMallocHost(&P->ksh, sizeof(KState)));
-    P->bytes += ((m + 1) * n + n) * 8 + m * n * (prec == WEC_PREC_FP64 ? 8 : 4);
+    P->bytes += ((m + 1) * n + n) * 8 + m * n * 8;
     return poisson_autotune(P, st);
 }
 
@@ -1027,7 +1215,7 @@ void poisson_free(wec_poisson *P)
         cudaFree(P->L64[l].xp); cudaFree(P->L32[l].xp);
     }
     cudaFree(P->lu64); cudaFree(P->lu32);
-    cudaFree(P->V); cudaFree(P->Z); cudaFree(P->w); cudaFree(P->part); cudaFree(P->dots); cudaFree(P->hess);
+    cudaFree(P->V); cudaFree(P->Z); cudaFree(P->w); cudaFree(P->d0); cudaFree(P->part); cudaFree(P->dots); cudaFree(P->hess);
     cudaFree(P->ks);
     if (P->ksh) cudaFreeHost(P->ksh);
     *P = wec_poisson();
@@ -1035,6 +1223,11 @@ void poisson_free(wec_poisson *P)
 
 int poisson_build(wec_poisson *P, cudaStream_t st)
 {
+    {
+        const int n = P->nx * P->ny;
+        WEC_PROF("diag", 0, 8.0 * (n + (P->nx + 1.0) * P->ny + P->nx * (P->ny + 1.0)), st);
+        k_diag0<<<nblk(n, 256), 256, 0, st>>>(P->nx, P->ny, P->L64[0].bu, P->L64[0].bv, P->d0);
+    }
     if (P->prec == WEC_PREC_MIXED) {
         // the V-cycle is FP32 throughout: level 0 converted once, coarse levels
         // and the coarsest LU formed in FP32 (the FP64 operator is level 0 only)
@@ -1090,13 +1283,13 @@ int poisson_vcycle(wec_poisson *P, const double *b, double *x)
     int n = P->nx * P->ny;
     cudaStream_t st = P->st;
     if (P->prec == WEC_PREC_FP64) {
-        vcycle_t<double>(P, P->L64, b, x, nullptr, nullptr, st);
+        vcycle_t<double, double>(P, P->L64, b, x, nullptr, nullptr, st);
     } else {
         {
             WEC_PROF("convert", -1, 12.0 * n, st);
             k_convert<float, double><<<nblk(n, 256), 256, 0, st>>>(n, b, P->L32[0].b, nullptr);
         }
-        vcycle_t<float>(P, P->L32, P->L32[0].b, P->L32[0].x, nullptr, nullptr, st);
+        vcycle_t<float, float>(P, P->L32, P->L32[0].b, P->L32[0].x, nullptr, nullptr, st);
         WEC_PROF("convert", -1, 12.0 * n, st);
         k_convert<double, float><<<nblk(n, 256), 256, 0, st>>>(n, P->L32[0].x, x, nullptr);
     }
