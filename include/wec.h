@@ -78,11 +78,20 @@ typedef struct {
     double xc, yc, width, height, mass, added_mass, kappa_p, pto_damping;
 } wec_body;
 
-enum { WEC_PREC_FP64 = 0, WEC_PREC_MIXED = 1 };
+enum { WEC_PREC_FP64 = 0, WEC_PREC_MIXED = 1, WEC_PREC_MIXED_MG = 2 };
 
-/* Pressure solver and step options.  precision: WEC_PREC_FP64 (everything FP64)
- * or WEC_PREC_MIXED (multigrid V-cycles in FP32 inside the FP64 FGMRES; the
- * residual, orthogonalisation and all step arithmetic stay FP64).
+/* Pressure solver and step options.  precision:
+ *   WEC_PREC_FP64      everything FP64;
+ *   WEC_PREC_MIXED_MG  multigrid V-cycles in FP32 inside the FP64 FGMRES; the
+ *                      residual, orthogonalisation and all step arithmetic FP64;
+ *   WEC_PREC_MIXED     as WEC_PREC_MIXED_MG, and the step's stencil arithmetic
+ *                      (level-set advection and reinitialisation, materials,
+ *                      momentum, Jacobi sweeps) in FP32 over FP32 working copies
+ *                      of FP64 state; the force integral (Eq. int_fh), the heave
+ *                      update (Eq. newton_u), the projection and the persistent
+ *                      fields stay FP64.
+ * A Poisson object (wec_poisson_create) takes WEC_PREC_FP64 or WEC_PREC_MIXED
+ * (FP32 V-cycles); WEC_PREC_MIXED_MG is a tank option.
  * rtol: relative FP64 residual ||b - A x||_2 <= rtol ||b||_2 of each solve.
  * restart: FGMRES restart length m (1..32).  n_reinit: Sussman pseudo-steps per
  * step.  n_jacobi: Jacobi sweeps of the Crank-Nicolson momentum system.

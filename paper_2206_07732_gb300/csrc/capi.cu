@@ -37,8 +37,8 @@ static int check_device()
 static int check_opts(const wec_solver_opts *o)
 {
     if (!o) return fail(WEC_ERR_INVALID, "solver options are NULL");
-    if (o->precision != WEC_PREC_FP64 && o->precision != WEC_PREC_MIXED)
-        return fail(WEC_ERR_INVALID, "precision must be WEC_PREC_FP64 or WEC_PREC_MIXED");
+    if (o->precision != WEC_PREC_FP64 && o->precision != WEC_PREC_MIXED && o->precision != WEC_PREC_MIXED_MG)
+        return fail(WEC_ERR_INVALID, "precision must be WEC_PREC_FP64, WEC_PREC_MIXED or WEC_PREC_MIXED_MG");
     if (!(o->rtol > 0.0) || o->max_iters < 1) return fail(WEC_ERR_INVALID, "rtol must be > 0 and max_iters >= 1");
     if (o->restart < 1 || o->restart > kMaxRestart) return fail(WEC_ERR_INVALID, "restart must be in 1..32");
     if (o->n_reinit < 0 || o->n_jacobi < 1 || o->mg_pre < 1 || o->mg_post < 0 || o->mg_pre > 4 || o->mg_post > 4)

@@ -994,7 +994,9 @@ int tank_alloc_and_init(wec_tank *T)
     WEC_CK(cudaMalloc(&T->S, sizeof(StepScalars)));
     WEC_CK(cudaMallocHost(&T->Sh, sizeof(StepScalars)));
     *T->Sh = StepScalars{};
-    if (int e = poisson_init(&T->solver, P.nx, P.ny, T->opts.precision, T->opts.restart, T->opts.mg_pre,
+    // the solver runs FP32 V-cycles for both mixed modes
+    const int sprec = T->opts.precision == WEC_PREC_FP64 ? WEC_PREC_FP64 : WEC_PREC_MIXED;
+    if (int e = poisson_init(&T->solver, P.nx, P.ny, sprec, T->opts.restart, T->opts.mg_pre,
                              T->opts.mg_post, T->gst))
         return e;
     long long ninit = (long long)nc + nu + nv;

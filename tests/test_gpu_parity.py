@@ -255,6 +255,24 @@ def test_mixed_precision_step_reaches_tolerance():
     assert errs["p"] < 1e-5
 
 
+def test_mixed_mg_step_matches_oracle_to_solver_tolerance():
+    # FP32 V-cycles only: every step stencil is FP64, so the fields differ from
+    # the oracle only through the pressure solve, which both sides converge to
+    # the same relative residual (rtol 1e-8, different preconditioner rounding).
+    cfg = synth.tank_small(seed=0)
+    g = wec.Tank(cfg, precision=wec.PREC_MIXED_MG)
+    o = O.OracleTank(cfg)
+    for _ in range(20):
+        rg = g.step(cfg["dt"])
+        ro = o.step(cfg["dt"])
+        assert rg["status"] == 0 and rg["residual"] <= cfg["solver"]["rtol"]
+    errs = {name: rel(g.get(name), o.get(fo)) for name, fo in FIELDS[:4]}
+    print("mixed_mg vs oracle after 20 steps:", errs, "z", rg["z"], ro["z"])
+    assert rg["z"] == pytest.approx(ro["z"], rel=1e-6, abs=1e-12)
+    for name in ("sigma", "u", "v", "p"):
+        assert errs[name] < 1e-6, name
+
+
 def test_checkpoint_resume_is_bit_identical():
     cfg = synth.tank_small(seed=7, nx=64, ny=32)
     a = wec.Tank(cfg)
