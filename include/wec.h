@@ -162,6 +162,36 @@ int wec_step(wec_tank *tank, double dt, double pto_force, wec_step_result *out);
 int wec_step_n(wec_tank *tank, int nsteps, double dt, const double *pto_forces,
                wec_step_result *out_n);
 
+/* ---------------------------------------------------------------- batches --
+ * Many independent tanks (uneven sizes, waves, bodies) stepping together: one
+ * CUDA graph launch per batch step runs every tank's whole step as independent
+ * branches, so the tanks' kernels share the GPU concurrently.  Each tank is the
+ * same as one made by wec_tank_create (its own multigrid tile autotuning, its
+ * own results; a batch step gives each tank exactly the bits a wec_step would).
+ *
+ * wec_batch_create: ntanks (1..4096) descriptions, each argument an array of
+ * ntanks host structs (copied), validated as in wec_tank_create; the batch owns
+ * the tanks.  cuda_stream: the caller's stream (ordering only).
+ * wec_batch_step: dt[ntanks] (> 0), pto_force[ntanks] or NULL (zeros),
+ * out[ntanks] records or NULL.  Host-synchronous.  Returns WEC_OK, or the first
+ * tank's non-OK status (WEC_ERR_NOT_CONVERGED etc.; every tank still stepped).
+ * wec_batch_step_n: nsteps batch steps; dt, pto_force, out are [nsteps][ntanks]
+ * row-major.  Stops at the first hard error.
+ * wec_batch_tank: borrow tank i (fields, state, checkpoints, a single wec_step;
+ * valid until wec_batch_destroy, not to be destroyed by the caller).
+ * With event profiling on (wec_profile_enable), batch steps launch each tank's
+ * kernels one by one instead of the batch graph. */
+typedef struct wec_batch wec_batch;
+
+int wec_batch_create(int ntanks, const wec_grid *grids, const wec_fluids *fluids, const wec_waves *waves,
+                     const wec_body *bodies, const wec_solver_opts *opts, void *cuda_stream, wec_batch **out);
+int wec_batch_size(const wec_batch *batch);
+int wec_batch_tank(wec_batch *batch, int i, wec_tank **out);
+int wec_batch_step(wec_batch *batch, const double *dt, const double *pto_force, wec_step_result *out);
+int wec_batch_step_n(wec_batch *batch, int nsteps, const double *dt, const double *pto_force,
+                     wec_step_result *out);
+void wec_batch_destroy(wec_batch *batch);
+
 /* Execution mode.  enable = 1 (default): the whole step -- including the
  * pressure solve's iteration, steered on the GPU by conditional WHILE / IF graph
  * nodes -- runs as one CUDA graph, captured at the first step and replayed.

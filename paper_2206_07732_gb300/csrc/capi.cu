@@ -77,15 +77,11 @@ static double *field_ptr(const wec_tank *T, int id, size_t *n, bool *writable)
 
 using namespace wec;
 
-extern "C" {
+namespace wec {
 
-const char *wec_last_error(void) { return g_err.c_str(); }
-
-int wec_tank_create(const wec_grid *grid, const wec_fluids *fl, const wec_waves *wv, const wec_body *body,
-                    const wec_solver_opts *opts, void *cuda_stream, wec_tank **out)
+int validate_tank(const wec_grid *grid, const wec_fluids *fl, const wec_waves *wv, const wec_body *body,
+                  const wec_solver_opts *opts)
 {
-    if (!out) return fail(WEC_ERR_INVALID, "out is NULL");
-    *out = nullptr;
     if (!grid || !fl || !wv || !body) return fail(WEC_ERR_INVALID, "NULL argument");
     if (int e = check_opts(opts)) return e;
     if (grid->nx < 8 || grid->ny < 8 || (grid->nx & 1) || (grid->ny & 1))
@@ -105,6 +101,22 @@ int wec_tank_create(const wec_grid *grid, const wec_fluids *fl, const wec_waves 
         if (!(body->width > 0 && body->height > 0 && body->mass > 0 && body->kappa_p > 0 && body->added_mass >= 0))
             return fail(WEC_ERR_INVALID, "body: width, height, mass, kappa_p must be > 0, added_mass >= 0");
     }
+    return WEC_OK;
+}
+
+}  // namespace wec
+
+extern "C" {
+
+const char *wec_last_error(void) { return g_err.c_str(); }
+
+int wec_tank_create(const wec_grid *grid, const wec_fluids *fl, const wec_waves *wv, const wec_body *body,
+                    const wec_solver_opts *opts, void *cuda_stream, wec_tank **out)
+{
+    if (!out) return fail(WEC_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (int e = validate_tank(grid, fl, wv, body, opts)) return e;
+    const double h = grid->lx / grid->nx;
     if (int e = check_device()) return e;
 
     wec_tank *T = new (std::nothrow) wec_tank();

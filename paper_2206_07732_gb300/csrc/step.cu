@@ -1176,36 +1176,34 @@ void enqueue_back(wec_tank *T, cudaStream_t st)
     k_finalize<<<1, TB, 0, st>>>(P, T->S, T->part, T->sig, T->inp, S->ks, T->n_fixed, T->n_body, T->n_close);
 }
 
-int build_graph(wec_tank *T)
+// Kernels per replay (front + the solve's opening + back once, then the
+// Arnoldi-step kernels per iteration and the cycle-closing kernels per cycle),
+// counted on a throwaway capture; k_finalize uses them to report launches.
+int count_kernels(wec_tank *T)
 {
     wec_poisson *S = &T->solver;
-    S->st = T->gst;
-    // kernels per replay: front + the solve's opening + back once, then the
-    // Arnoldi-step kernels per iteration and the cycle-closing kernels per cycle
-    {
-        cudaGraph_t tmp = nullptr;
-        WEC_CK(cudaStreamBeginCapture(T->h1, cudaStreamCaptureModeThreadLocal));
-        prof::begin_capture();
-        enqueue_front(T, T->h1);
-        enqueue_back(T, T->h1);
-        long long nfb = prof::captured();
-        prof::end_capture();
-        WEC_CK(cudaStreamEndCapture(T->h1, &tmp));
-        if (tmp) cudaGraphDestroy(tmp);
-        int nbeg = 0, nb = 0, ncl = 0;
-        if (int e = poisson_count_kernels(S, T->h1, &nbeg, &nb, &ncl)) return e;
-        T->n_fixed = (int)nfb + nbeg;
-        T->n_body = nb;
-        T->n_close = ncl;
-    }
-    WEC_CK(cudaStreamBeginCapture(T->gst, cudaStreamCaptureModeThreadLocal));
+    cudaGraph_t tmp = nullptr;
+    WEC_CK(cudaStreamBeginCapture(T->h1, cudaStreamCaptureModeThreadLocal));
     prof::begin_capture();
-    enqueue_front(T, T->gst);
-    int e = poisson_capture_solve(S, T->rhs, T->phi, T->opts.rtol, T->opts.max_iters, T->gst, T->h1, T->h2);
-    enqueue_back(T, T->gst);
-    cudaMemcpyAsync(T->Sh, T->S, sizeof(StepScalars), cudaMemcpyDeviceToHost, T->gst);
-    poisson_state_to_host(S, T->gst);
+    enqueue_front(T, T->h1);
+    enqueue_back(T, T->h1);
+    long long nfb = prof::captured();
     prof::end_capture();
+    WEC_CK(cudaStreamEndCapture(T->h1, &tmp));
+    if (tmp) cudaGraphDestroy(tmp);
+    int nbeg = 0, nb = 0, ncl = 0;
+    if (int e = poisson_count_kernels(S, T->h1, &nbeg, &nb, &ncl)) return e;
+    T->n_fixed = (int)nfb + nbeg;
+    T->n_body = nb;
+    T->n_close = ncl;
+    return WEC_OK;
+}
+
+int build_graph(wec_tank *T)
+{
+    if (int e = count_kernels(T)) return e;
+    WEC_CK(cudaStreamBeginCapture(T->gst, cudaStreamCaptureModeThreadLocal));
+    int e = tank_capture_step(T, T->gst);
     cudaGraph_t g = nullptr;
     cudaError_t ce = cudaStreamEndCapture(T->gst, &g);
     if (e) {
@@ -1246,6 +1244,28 @@ int finish_step(wec_tank *T, int status, wec_step_result *out)
 }
 
 }  // namespace
+
+int tank_prepare_capture(wec_tank *T) { return count_kernels(T); }
+
+int tank_capture_step(wec_tank *T, cudaStream_t st)
+{
+    wec_poisson *S = &T->solver;
+    S->st = st;
+    prof::begin_capture();
+    enqueue_front(T, st);
+    int e = poisson_capture_solve(S, T->rhs, T->phi, T->opts.rtol, T->opts.max_iters, st, T->h1, T->h2);
+    enqueue_back(T, st);
+    cudaMemcpyAsync(T->Sh, T->S, sizeof(StepScalars), cudaMemcpyDeviceToHost, st);
+    poisson_state_to_host(S, st);
+    prof::end_capture();
+    return e;
+}
+
+int tank_finish_step(wec_tank *T, wec_step_result *out)
+{
+    prof::add_launches(T->Sh->launches);
+    return finish_step(T, WEC_OK, out);
+}
 
 int tank_step(wec_tank *T, double dt, double fpto, wec_step_result *out)
 {
@@ -1289,9 +1309,10 @@ void tank_free(wec_tank *T)
     if (T->graph) cudaGraphDestroy(T->graph);
     double *all[] = {T->sig, T->sa, T->r0, T->r1, T->rt, T->p, T->phi, T->rhs, T->rho_n, T->mu_n, T->mu_1,
                      T->rf_1, T->chi_1, T->u, T->us, T->ua, T->ub, T->uc, T->Ru, T->Du, T->v, T->vs,
-                     T->va, T->vb, T->vc, T->Rv, T->Dv, T->bcbuf, T->part, T->waves, T->inp,
+                     T->va, T->vb, T->vc, T->Rv, T->Dv, T->bcbuf, T->part, T->waves,
                      T->tabs, T->sgn};
     for (double *q : all) cudaFree(q);
+    if (T->inp_owned) cudaFree(T->inp);
     cudaFree(T->w32);
     cudaFree(T->tabs32);
     cudaFree(T->S);

@@ -79,13 +79,25 @@ struct wec_tank {
     wec::StepScalars *Sh = nullptr;  // pinned host mirror
     wec_poisson solver;
     bool stepped = false;
+    bool inp_owned = true;            // false when inp points into a batch's input array
     int last_iters = 0;
     double last_relres = 0.0;
 };
 
 namespace wec {
+// Host-side checks of a tank description (no device call); WEC_ERR_INVALID + message.
+int validate_tank(const wec_grid *grid, const wec_fluids *fl, const wec_waves *wv, const wec_body *body,
+                  const wec_solver_opts *opts);
 int tank_alloc_and_init(wec_tank *T);
 int tank_init_pressure(wec_tank *T);  // after the host filled T->Sh (initial body state)
 int tank_step(wec_tank *T, double dt, double fpto, wec_step_result *out);
+// Count the kernels of one step (launch accounting); call before capturing.
+int tank_prepare_capture(wec_tank *T);
+// Enqueue one whole step (front, conditional-node solve, back, D2H of the step
+// record and solver state) on st, which must be capturing; used by the tank's
+// own graph and by a batch graph (one branch per tank).
+int tank_capture_step(wec_tank *T, cudaStream_t st);
+// After a replay that ran the captured step: launch accounting + the record.
+int tank_finish_step(wec_tank *T, wec_step_result *out);
 void tank_free(wec_tank *T);
 }  // namespace wec

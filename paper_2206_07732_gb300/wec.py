@@ -82,6 +82,14 @@ def load():
     L.wec_tank_destroy.restype = None
     L.wec_step.argtypes = [vp, C.c_double, C.c_double, C.POINTER(StepResult)]
     L.wec_step_n.argtypes = [vp, C.c_int, C.c_double, _dp, C.POINTER(StepResult)]
+    L.wec_batch_create.argtypes = [C.c_int, C.POINTER(Grid), C.POINTER(Fluids), C.POINTER(Waves), C.POINTER(Body),
+                                   C.POINTER(SolverOpts), vp, C.POINTER(vp)]
+    L.wec_batch_size.argtypes = [vp]
+    L.wec_batch_tank.argtypes = [vp, C.c_int, C.POINTER(vp)]
+    L.wec_batch_step.argtypes = [vp, _dp, _dp, C.POINTER(StepResult)]
+    L.wec_batch_step_n.argtypes = [vp, C.c_int, _dp, _dp, C.POINTER(StepResult)]
+    L.wec_batch_destroy.argtypes = [vp]
+    L.wec_batch_destroy.restype = None
     L.wec_pressure_solve.argtypes = [vp, vp, vp, C.c_double, C.POINTER(C.c_int), _dp]
     L.wec_tank_use_graph.argtypes = [vp, C.c_int]
     L.wec_set_option.argtypes = [C.c_char_p, C.c_int]
@@ -177,31 +185,42 @@ def solver_opts(s, precision=None):
     return o
 
 
-class Tank:
-    """A 2D wave tank on the GPU (wec_tank_create ... wec_tank_destroy)."""
+def tank_structs(cfg, precision=None):
+    """(grid, fluids, waves, body, opts, keep) structs of a workload dict; keep
+    holds the wave arrays the Waves struct points to."""
+    g = Grid(cfg["nx"], cfg["ny"], cfg["lx"], cfg["ly"], cfg["depth"])
+    f = Fluids(cfg["rho_w"], cfg["rho_a"], cfg["mu_w"], cfg["mu_a"], cfg["g"])
+    amp, om, ph = wave_components(cfg["wave"])
+    keep = [np.ascontiguousarray(a, dtype=np.float64) for a in (amp, om, ph)]
+    w = Waves(len(amp), _ptr(keep[0]), _ptr(keep[1]), _ptr(keep[2]), cfg["damp_x0"], cfg["damp_len"],
+              cfg["probe_x"])
+    b = cfg.get("body")
+    body = Body(1, b["xc"], b["yc"], b["width"], b["height"], b["mass"], b["added_mass"], b["kappa_p"],
+                b["pto_damping"]) if b else Body(0)
+    return g, f, w, body, solver_opts(cfg["solver"], precision), keep
 
-    def __init__(self, cfg, precision=None, stream=None):
+
+class Tank:
+    """A 2D wave tank on the GPU (wec_tank_create ... wec_tank_destroy).
+    handle: wrap a tank owned by a batch (borrowed; not destroyed here)."""
+
+    def __init__(self, cfg, precision=None, stream=None, handle=None):
         L = load()
         self.cfg = cfg
         self.nx, self.ny = cfg["nx"], cfg["ny"]
-        g = Grid(cfg["nx"], cfg["ny"], cfg["lx"], cfg["ly"], cfg["depth"])
-        f = Fluids(cfg["rho_w"], cfg["rho_a"], cfg["mu_w"], cfg["mu_a"], cfg["g"])
-        amp, om, ph = wave_components(cfg["wave"])
-        self._w = [np.ascontiguousarray(a, dtype=np.float64) for a in (amp, om, ph)]
-        w = Waves(len(amp), _ptr(self._w[0]), _ptr(self._w[1]), _ptr(self._w[2]),
-                  cfg["damp_x0"], cfg["damp_len"], cfg["probe_x"])
-        b = cfg.get("body")
-        body = Body(1, b["xc"], b["yc"], b["width"], b["height"], b["mass"], b["added_mass"], b["kappa_p"],
-                    b["pto_damping"]) if b else Body(0)
-        o = solver_opts(cfg["solver"], precision)
+        if handle is not None:
+            self.h, self.owned = handle, False
+            return
+        g, f, w, body, o, self._w = tank_structs(cfg, precision)
         h = C.c_void_p()
         _check(L.wec_tank_create(C.byref(g), C.byref(f), C.byref(w), C.byref(body), C.byref(o),
                                  _stream(stream), C.byref(h)))
-        self.h = h
+        self.h, self.owned = h, True
 
     def close(self):
         if getattr(self, "h", None):
-            load().wec_tank_destroy(self.h)
+            if self.owned:
+                load().wec_tank_destroy(self.h)
             self.h = None
 
     __del__ = close
@@ -300,6 +319,57 @@ def profile_read():
         nm = names.raw[k * stride:(k + 1) * stride].split(b"\0")[0].decode()
         out.append(dict(name=nm, level=lv[k], launches=la[k], ms=ms[k], bytes=by[k]))
     return out
+
+
+class Batch:
+    """Tanks stepping together, one graph launch per batch step
+    (wec_batch_create ... wec_batch_destroy)."""
+
+    def __init__(self, cfgs, precision=None, stream=None):
+        L = load()
+        self.cfgs = list(cfgs)
+        n = len(self.cfgs)
+        st = [tank_structs(c, precision) for c in self.cfgs]
+        self._keep = [x[5] for x in st]
+        arrs = [(T * n)(*[x[k] for x in st]) for k, T in enumerate((Grid, Fluids, Waves, Body, SolverOpts))]
+        h = C.c_void_p()
+        _check(L.wec_batch_create(n, *arrs, _stream(stream), C.byref(h)))
+        self.h = h
+        self.tanks = []
+        for i, c in enumerate(self.cfgs):
+            th = C.c_void_p()
+            _check(L.wec_batch_tank(h, i, C.byref(th)))
+            self.tanks.append(Tank(c, handle=th))
+
+    def __len__(self):
+        return len(self.cfgs)
+
+    def close(self):
+        if getattr(self, "h", None):
+            for t in self.tanks:
+                t.h = None
+            load().wec_batch_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def step(self, dt, pto=None, allow=(WEC_OK, WEC_ERR_NOT_CONVERGED)):
+        n = len(self)
+        d = np.ascontiguousarray(np.broadcast_to(np.asarray(dt, dtype=np.float64), (n,)))
+        p = None if pto is None else np.ascontiguousarray(np.broadcast_to(np.asarray(pto, np.float64), (n,)))
+        out = (StepResult * n)()
+        _check(load().wec_batch_step(self.h, _ptr(d), None if p is None else _ptr(p), out), ok=allow)
+        return [r.as_dict() for r in out]
+
+    def step_n(self, nsteps, dt, pto=None, records=True):
+        n = len(self)
+        d = np.ascontiguousarray(np.broadcast_to(np.asarray(dt, dtype=np.float64), (nsteps, n)))
+        p = None if pto is None else np.ascontiguousarray(np.broadcast_to(np.asarray(pto, np.float64),
+                                                                               (nsteps, n)))
+        out = (StepResult * (nsteps * n))() if records else None
+        _check(load().wec_batch_step_n(self.h, nsteps, _ptr(d), None if p is None else _ptr(p), out),
+               ok=(WEC_OK, WEC_ERR_NOT_CONVERGED))
+        return [r.as_dict() for r in out] if records else None
 
 
 class Poisson:

@@ -105,3 +105,24 @@ def test_wave_utilities_match_oracle(lib):
     a0, om0, _ = W.jonswap_components(0.15, 1.6, 3.3, 64, ph)
     np.testing.assert_allclose(om, om0, rtol=1e-14)
     np.testing.assert_allclose(a, a0, rtol=1e-12)
+
+
+@pytest.mark.parametrize("bad", ["count", "null", "tank"])
+def test_batch_create_rejects_invalid_arguments_on_host(lib, bad):
+    cfgs = [synth.tank_small(nx=64, ny=32), synth.tank_small(nx=96, ny=48)]
+    st = [_structs(c) for c in cfgs]
+    arrs = [(T * 2)(*[x[k] for x in st]) for k, T in enumerate((wec.Grid, wec.Fluids, wec.Waves, wec.Body,
+                                                                  wec.SolverOpts))]
+    n = 2
+    if bad == "count":
+        n = 0
+    elif bad == "null":
+        arrs[3] = None
+    elif bad == "tank":
+        arrs[0][1].nx = 95  # the second tank is invalid: nothing is left allocated
+    h = C.c_void_p(123)
+    code = lib.wec_batch_create(n, *arrs, None, C.byref(h))
+    assert code == wec.WEC_ERR_INVALID
+    assert not h.value
+    msg = lib.wec_last_error().decode()
+    assert ("tank 1" in msg) if bad == "tank" else ("batch" in msg)
