@@ -9,6 +9,10 @@ and FP32 multigrid V-cycles over FP64 storage, FP64 FGMRES, force and heave)
 and, beside it, the plain FP64 path on the same GPU.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload tank|batch]
+
+--workload batch times the 64 uneven tanks of the batched configuration (one
+graph launch per batch step; tanks sharded over ranks when N > 1).
 
 N > 1 (under torchrun): independent replicas, one tank per rank (the single
 tank is not partitioned), value = all ranks' cell-steps / max-over-ranks time.
@@ -44,6 +48,8 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU-baseline sample budget")
+    ap.add_argument("--workload", default="tank", choices=["tank", "batch"],
+                    help="tank: the 1024x256 JONSWAP tank (default); batch: 64 uneven tanks in one graph launch")
     ap.add_argument("--ncu-steps", type=int, default=0,
                     help="profiling helper: run warm-up + this many mixed-path steps only, print nothing")
     return ap.parse_args()
@@ -243,6 +249,96 @@ def e2e_path(wec, torch, cfg, precision, steps, warmup, flush):
     return t
 
 
+def time_batch(wec, torch, cfgs, precision, steps, warmup, flush):
+    """K batch steps, CUDA events on the caller's stream around each (the batch
+    orders itself after and before that stream), L2 flushed in between."""
+    B = wec.Batch(cfgs, precision=precision, stream=torch.cuda.current_stream().cuda_stream)
+    dts = [c["dt"] for c in cfgs]
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        B.step(dts)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    its, res, wall = [], [], []
+    n0 = wec.launch_count()
+    if torch.distributed.is_initialized():
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    for k in range(steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        t0 = time.perf_counter()
+        r = B.step(dts)  # host dt / PTO in, host records out, inside the call
+        wall.append(time.perf_counter() - t0)
+        ev[k][1].record(stream)
+        its += [x["iters"] for x in r]
+        res += [x["residual"] for x in r]
+    torch.cuda.synchronize()
+    launches = wec.launch_count() - n0
+    B.close()
+    return dict(ms=[a.elapsed_time(b) for a, b in ev], iters=its, residual=max(res), launches=launches, wall=wall)
+
+
+def main_batch(args):
+    import torch
+    from paper_2206_07732_gb300 import synth
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    L, wec = setup_lib()
+    allc = synth.batch_tanks(64, seed=args.seed)
+    cfgs = [c for i, c in enumerate(allc) if i % world == rank]  # tanks sharded over ranks, no collective
+    cells_all = sum(c["nx"] * c["ny"] for c in allc)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    steps, warmup = args.steps, max(args.warmup, 3)
+    clocks = Clocks(local)
+    clocks.start()
+    mixed = time_batch(wec, torch, cfgs, wec.PREC_MIXED, steps, warmup, flush)
+    ck = clocks.stop()
+    fp64 = time_batch(wec, torch, cfgs, wec.PREC_FP64, steps, warmup, flush)
+
+    def reduce_max(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    t_mixed = reduce_max(sum(mixed["ms"]) / 1e3)
+    t_fp64 = reduce_max(sum(fp64["ms"]) / 1e3)
+    t_e2e = reduce_max(sum(mixed["wall"]))
+    value = cells_all * steps / t_mixed
+    nt = len(cfgs)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": warmup,
+        "ms_per_step": t_mixed / steps * 1e3, "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+        "dtype": "f64+f32(stencils,multigrid)", "data": "synthetic (seeded grids, Airy waves, boxes)",
+        "config": {"workload": "batch of 64 uneven 2D tanks (256x128 .. 768x256, regular Airy waves, boxes), "
+                               "one CUDA graph launch per batch step",
+                   "cells": cells_all, "tanks": 64, "tanks_per_rank": nt, "rtol": 1e-8,
+                   "precision": "mixed: FP32 stencils and V-cycles, FP64 storage/FGMRES/force/heave",
+                   "l2": "flushed between timed steps (256 MiB write)", "seed": args.seed},
+        "fp64_value": cells_all * steps / t_fp64, "fp64_ms_per_step": t_fp64 / steps * 1e3,
+        "speedup_mixed_vs_fp64": t_fp64 / t_mixed,
+        "fgmres_iters_per_step": {"mixed": statistics.mean(mixed["iters"]), "fp64": statistics.mean(fp64["iters"])},
+        "max_relative_residual": {"mixed": mixed["residual"], "fp64": fp64["residual"]},
+        "e2e": {"value": cells_all * steps / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 16 * nt,
+                "d2h_bytes_per_step": 72 * nt,
+                "note": "wec_batch_step wall clock: host dt / PTO arrays in, host records out, per step"},
+        "gpu_launches": mixed["launches"],
+        "clocks": ck,
+        "roofline": None,
+        "roofline_note": "per-kernel rooflines are reported by the default (single-tank) workload",
+        "cpu_baseline": None,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main_ours(args):
     import torch
     rank = int(os.environ.get("RANK", "0"))
@@ -399,5 +495,7 @@ if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         main_reference(a)
+    elif a.workload == "batch":
+        main_batch(a)
     else:
         main_ours(a)

@@ -14,6 +14,7 @@ namespace wec {
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kMaxLevels = 24;
 constexpr int kMaxRestart = 32;
+constexpr int kInvMax = 32;         // coarsest levels up to this size also get an explicit inverse
 constexpr int kMaxCoarse = 512;      // cells on the coarsest multigrid level
 constexpr int kRedBlocks = 304;      // partial-sum blocks of the step's reductions (2 x 152 SMs)
 constexpr int kRedThreads = 256;
@@ -57,6 +58,7 @@ struct Level {
     int nx = 0, ny = 0;
     T *bu = nullptr, *bv = nullptr, *x = nullptr, *b = nullptr;
     T *xp = nullptr;  // pre-smoothed iterate of a tiled (fused) level, read by its post kernel
+    T *id = nullptr;  // 1 / diagonal per cell, formed by poisson_build (fused V-cycle)
 };
 
 // FGMRES state on the device (read by the kernels that steer the iteration).
@@ -78,6 +80,8 @@ struct wec_poisson {
     int ncoarse = 0;
     double *lu64 = nullptr;
     float *lu32 = nullptr;
+    double *inv64 = nullptr;  // explicit inverse of the coarsest operator (at most kInvMax cells)
+    float *inv32 = nullptr;
     // FGMRES workspace (FP64 outer iteration)
     double *V = nullptr;        // (m+1) x n
     double *Z = nullptr;        // m x n preconditioned vectors (FP64 in both precisions)

@@ -16,8 +16,9 @@
 //   k_mg_post   per fine level: prolongation + correction and nu2 sweeps, same
 //               tiling.
 // A cell update is x = (b + sum_f beta_f x_nb) * (1 / d) with the reciprocal of
-// the diagonal formed once per launch in shared memory (the one-pass kernels of
-// solver.cu divide by d instead: the two V-cycles agree to rounding).  Face
+// the diagonal formed once per coefficient set (poisson_build) and staged with
+// the tile (the one-pass kernels of solver.cu divide by d instead: the two
+// V-cycles agree to rounding).  Face
 // coefficients are zero on the Neumann walls and x is zero outside the domain,
 // so a tile update needs no boundary branches (the staging zeroes the wall
 // faces); 1/d is zero outside the domain, which keeps those cells at zero.
@@ -77,12 +78,11 @@ struct TileView {
     }
 };
 
-// Stage b, x (xg + prolonged xc when xg is given, else 0), bu, bv of the tile
-// (zero outside the domain and on the Neumann walls), then 1/d (zero outside
-// the domain).
+// Stage b, 1/d, x (xg + prolonged xc when xg is given, else 0), bu, bv of the
+// tile (zero outside the domain; bu, bv also zero on the Neumann walls).
 template <typename T>
 __device__ void tile_load(TileView<T> &t, const T *__restrict__ bu, const T *__restrict__ bv,
-                          const T *__restrict__ b, const T *xg, const T *__restrict__ xc)
+                          const T *__restrict__ b, const T *__restrict__ idg, const T *xg, const T *__restrict__ xc)
 {
     const int nx = t.nx, ny = t.ny, ex = t.ex, ey = t.ey;
     const unsigned mex = magic_u16(ex), mex1 = magic_u16(ex + 1);
@@ -90,6 +90,7 @@ __device__ void tile_load(TileView<T> &t, const T *__restrict__ bu, const T *__r
         const int lj = div_u16(k, mex), li = k - lj * ex, gi = t.gx0 + li, gj = t.gy0 + lj;
         const bool in = gi >= 0 && gi < nx && gj >= 0 && gj < ny;
         cp_async_el(t.b + k, in ? b + gj * nx + gi : b, in);
+        cp_async_el(t.id + k, in ? idg + gj * nx + gi : idg, in);
     }
     for (int k = threadIdx.x; k < (ex + 1) * ey; k += blockDim.x) {
         const int lj = div_u16(k, mex1), li = k - lj * (ex + 1), gi = t.gx0 + li, gj = t.gy0 + lj;
@@ -110,12 +111,6 @@ __device__ void tile_load(TileView<T> &t, const T *__restrict__ bu, const T *__r
         t.x[k] = xv;
     }
     cp_async_wait_all();
-    __syncthreads();
-    for (int k = threadIdx.x; k < ex * ey; k += blockDim.x) {
-        const int lj = div_u16(k, mex), li = k - lj * ex, gi = t.gx0 + li, gj = t.gy0 + lj;
-        const bool in = gi >= 0 && gi < nx && gj >= 0 && gj < ny;
-        t.id[k] = in ? T(1) / t.diag(li, lj) : T(0);
-    }
     __syncthreads();
 }
 
@@ -162,8 +157,9 @@ __device__ __forceinline__ void tile_setup(TileView<T> &t, unsigned char *smem_r
 // the restricted residual into bc.
 template <typename T, int kTX, int kTY>
 __global__ void __launch_bounds__(256) k_mg_pre(int nx, int ny, const T *__restrict__ bu, const T *__restrict__ bv,
-                                                const T *__restrict__ b, T *__restrict__ xp, T *__restrict__ bc,
-                                                int nu1, int H, const int *bsel)
+                                                const T *__restrict__ b, const T *__restrict__ idg,
+                                                T *__restrict__ xp, T *__restrict__ bc, int nu1, int H,
+                                                const int *bsel)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const long long n = (long long)nx * ny;
@@ -171,7 +167,7 @@ __global__ void __launch_bounds__(256) k_mg_pre(int nx, int ny, const T *__restr
     TileView<T> t;
     tile_setup(t, smem_raw, nx, ny, kTX, kTY, H);
     const unsigned mwh = magic_u16(t.ex >> 1);
-    tile_load(t, bu, bv, b, (const T *)nullptr, (const T *)nullptr);
+    tile_load(t, bu, bv, b, idg, (const T *)nullptr, (const T *)nullptr);
     for (int q = 0; q < nu1; ++q) {
         tile_pass(t, 0, q == 0, mwh);
         tile_pass(t, 1, false, mwh);
@@ -202,9 +198,9 @@ __global__ void __launch_bounds__(256) k_mg_pre(int nx, int ny, const T *__restr
 // writes x (different arrays): tiles read their halos while others write.
 template <typename T, int kTX, int kTY, typename TO>
 __global__ void __launch_bounds__(256) k_mg_post(int nx, int ny, const T *__restrict__ bu, const T *__restrict__ bv,
-                                                 const T *__restrict__ b, const T *__restrict__ xp, TO *x,
-                                                 const T *__restrict__ xc, int nu2, int H, const int *bsel,
-                                                 const int *xsel)
+                                                 const T *__restrict__ b, const T *__restrict__ idg,
+                                                 const T *__restrict__ xp, TO *x, const T *__restrict__ xc,
+                                                 int nu2, int H, const int *bsel, const int *xsel)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const long long n = (long long)nx * ny;
@@ -213,7 +209,7 @@ __global__ void __launch_bounds__(256) k_mg_post(int nx, int ny, const T *__rest
     TileView<T> t;
     tile_setup(t, smem_raw, nx, ny, kTX, kTY, H);
     const unsigned mwh = magic_u16(t.ex >> 1);
-    tile_load(t, bu, bv, b, xp, xc);
+    tile_load(t, bu, bv, b, idg, xp, xc);
     for (int q = 0; q < nu2; ++q) {
         tile_pass(t, 0, false, mwh);
         tile_pass(t, 1, false, mwh);
@@ -230,17 +226,20 @@ struct BottomLevels {
     int nx[kMaxLevels], ny[kMaxLevels];
     const T *bu[kMaxLevels], *bv[kMaxLevels];
     T *x[kMaxLevels], *b[kMaxLevels];
+    const T *id[kMaxLevels];
     const T *lu;
+    const T *inv;  // explicit inverse of the coarsest operator, or nullptr (use lu)
     double *x0d;  // when set (lb = 0, FP32 levels): level-0 result stored widened here instead of x[0]
 };
 
-// The LU of the coarsest level is staged in shared memory when it takes at most
-// 16 KB (n <= 64 cells in FP32, 45 in FP64); larger ones are read from global.
+// The coarsest level's explicit inverse (n <= kInvMax), or else its LU, is
+// staged in shared memory when it takes at most 16 KB (n <= 64 cells in FP32, 45
+// in FP64); a larger LU is read from global.
 template <typename T>
 __host__ __device__ inline bool lu_staged(const BottomLevels<T> &L)
 {
     const long long n = (long long)L.nx[L.nlev - 1] * L.ny[L.nlev - 1];
-    return n * n * (long long)sizeof(T) <= 16 * 1024;
+    return L.inv || n * n * (long long)sizeof(T) <= 16 * 1024;
 }
 
 template <typename T>
@@ -323,23 +322,18 @@ __global__ void __launch_bounds__(kBottomThreads) k_mg_bottom(BottomLevels<T> L,
         const T *gu = L.bu[l], *gv = L.bv[l];
         for (int k = threadIdx.x; k < (nx + 1) * ny; k += blockDim.x) cp_async_el(su + k, gu + k);
         for (int k = threadIdx.x; k < nx * (ny + 1); k += blockDim.x) cp_async_el(sv + k, gv + k);
+        T *sid = ID(l);
+        const T *gid = L.id[l];
+        for (int k = threadIdx.x; k < nx * ny; k += blockDim.x) cp_async_el(sid + k, gid + k);
     }
+    // the coarsest level's explicit inverse, or its LU when that is staged
     const int nlu = L.nx[last] * L.ny[last];
-    const bool lu_sm = lu_staged(L);
-    const T *lu = lu_sm ? sm + off[kMaxLevels] : L.lu;
-    if (lu_sm)
-        for (int k = threadIdx.x; k < nlu * nlu; k += blockDim.x) cp_async_el(sm + off[kMaxLevels] + k, L.lu + k);
+    const T *csrc = L.inv ? L.inv : L.lu;
+    const bool c_sm = lu_staged(L);
+    const T *lu = c_sm ? sm + off[kMaxLevels] : L.lu;
+    if (c_sm)
+        for (int k = threadIdx.x; k < nlu * nlu; k += blockDim.x) cp_async_el(sm + off[kMaxLevels] + k, csrc + k);
     cp_async_wait_all();
-    __syncthreads();
-    for (int l = lb; l < L.nlev; ++l) {
-        const int nx = L.nx[l], ny = L.ny[l];
-        const T *su = BU(l), *sv = BV(l);
-        T *id = ID(l);
-        for (int k = threadIdx.x; k < nx * ny; k += blockDim.x) {
-            const int j = k / nx, i = k - j * nx;
-            id[k] = T(1) / diag_at(su, sv, nx, ny, i, j);
-        }
-    }
     __syncthreads();
     for (int l = lb; l < last; ++l) {
         const int nx = L.nx[l], ny = L.ny[l];
@@ -366,7 +360,19 @@ __global__ void __launch_bounds__(kBottomThreads) k_mg_bottom(BottomLevels<T> L,
         }
         __syncthreads();
     }
-    {
+    if (L.inv) {
+        // x = A^{-1} b: one warp per row, lanes over columns, fixed shuffle tree
+        const int n = nlu;
+        T *x = X(last);
+        const T *b = B(last);
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        for (int r = w; r < n; r += kBottomThreads / 32) {
+            T s = lane < n ? lu[r * n + lane] * b[lane] : T(0);
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) x[r] = s;
+        }
+        __syncthreads();
+    } else {
         const int n = nlu;
         T *x = X(last);
         const T *b = B(last);

@@ -178,9 +178,10 @@ __global__ void k_convert(long long n, const TI *__restrict__ in, TO *__restrict
 }
 
 // Dense LU of the coarsest operator (no pivoting: A is a symmetric M-matrix).
-// One block; the matrix lives in global memory (n <= 512).
+// One block; the matrix lives in global memory (n <= 512).  inv (n <= kInvMax,
+// else nullptr): also A^{-1}, column t by thread t from the two triangular solves.
 template <typename T>
-__global__ void k_lu_factor(int nx, int ny, const T *__restrict__ bu, const T *__restrict__ bv, T *A)
+__global__ void k_lu_factor(int nx, int ny, const T *__restrict__ bu, const T *__restrict__ bv, T *A, T *inv)
 {
     int n = nx * ny;
     for (long long q = threadIdx.x; q < (long long)n * n; q += blockDim.x) A[q] = T(0);
@@ -203,6 +204,42 @@ __global__ void k_lu_factor(int nx, int ny, const T *__restrict__ bu, const T *_
         }
         __syncthreads();
     }
+    if (!inv) return;
+    const int t = threadIdx.x;
+    if (t < n) {
+        for (int r = 0; r < n; ++r) {  // L y = e_t (unit lower), y in column t of inv
+            T s = r == t ? T(1) : T(0);
+            for (int c = 0; c < r; ++c) s -= A[(long long)r * n + c] * inv[(long long)c * n + t];
+            inv[(long long)r * n + t] = s;
+        }
+        for (int r = n - 1; r >= 0; --r) {  // U x = y
+            T s = inv[(long long)r * n + t];
+            for (int c = r + 1; c < n; ++c) s -= A[(long long)r * n + c] * inv[(long long)c * n + t];
+            inv[(long long)r * n + t] = s / A[(long long)r * n + r];
+        }
+    }
+}
+
+// 1/d of every cell of levels 0..nlev-1 (one launch; thread per cell of the
+// concatenated levels, level found from the prefix offsets).
+template <typename T>
+struct LevelDiag {
+    int nlev;
+    int nx[kMaxLevels], ny[kMaxLevels];
+    long long off[kMaxLevels + 1];
+    const T *bu[kMaxLevels], *bv[kMaxLevels];
+    T *id[kMaxLevels];
+};
+
+template <typename T>
+__global__ void k_invdiag(LevelDiag<T> D)
+{
+    const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k >= D.off[D.nlev]) return;
+    int l = 0;
+    while (k >= D.off[l + 1]) ++l;
+    const int c = (int)(k - D.off[l]), nx = D.nx[l], j = c / nx, i = c - j * nx;
+    D.id[l][c] = T(1) / diag_at(D.bu[l], D.bv[l], nx, D.ny[l], i, j);
 }
 
 // x = U^{-1} L^{-1} b, one warp.
@@ -790,7 +827,8 @@ template <typename T, int TX, int TY>
 void launch_pre_t(const Level<T> &A, const T *b, T *bc, int nu1, int H, const int *bsel, cudaStream_t st)
 {
     dim3 grid((A.nx + TX - 1) / TX, (A.ny + TY - 1) / TY);
-    k_mg_pre<T, TX, TY><<<grid, 256, tile_smem<T>(H, TX, TY), st>>>(A.nx, A.ny, A.bu, A.bv, b, A.xp, bc, nu1, H, bsel);
+    k_mg_pre<T, TX, TY><<<grid, 256, tile_smem<T>(H, TX, TY), st>>>(A.nx, A.ny, A.bu, A.bv, b, A.id, A.xp, bc, nu1,
+                                                                     H, bsel);
 }
 
 template <typename T, int TX, int TY, typename TO>
@@ -798,8 +836,8 @@ void launch_post_t(const Level<T> &A, const T *b, TO *x, const T *xc, int nu2, i
                    const int *xsel, cudaStream_t st)
 {
     dim3 grid((A.nx + TX - 1) / TX, (A.ny + TY - 1) / TY);
-    k_mg_post<T, TX, TY, TO><<<grid, 256, tile_smem<T>(H, TX, TY), st>>>(A.nx, A.ny, A.bu, A.bv, b, A.xp, x, xc, nu2,
-                                                                         H, bsel, xsel);
+    k_mg_post<T, TX, TY, TO><<<grid, 256, tile_smem<T>(H, TX, TY), st>>>(A.nx, A.ny, A.bu, A.bv, b, A.id, A.xp, x,
+                                                                         xc, nu2, H, bsel, xsel);
 }
 
 template <typename T>
@@ -838,11 +876,19 @@ void vcycle_fused(wec_poisson *P, Level<T> *L, const T *b0, TO *x0, const int *b
     B.nlev = P->nlev;
     B.nu1 = P->nu1;
     B.nu2 = P->nu2;
+    if constexpr (sizeof(T) == 8) {
+        B.lu = (const T *)P->lu64;
+        B.inv = (const T *)P->inv64;
+    } else {
+        B.lu = (const T *)P->lu32;
+        B.inv = (const T *)P->inv32;
+    }
     for (int l = 0; l < P->nlev; ++l) {
         B.nx[l] = L[l].nx;
         B.ny[l] = L[l].ny;
         B.bu[l] = L[l].bu;
         B.bv[l] = L[l].bv;
+        B.id[l] = L[l].id;
         B.x[l] = l == 0 ? nullptr : L[l].x;
         B.b[l] = l == 0 ? (T *)b0 : L[l].b;
     }
@@ -869,7 +915,6 @@ void vcycle_fused(wec_poisson *P, Level<T> *L, const T *b0, TO *x0, const int *b
         const double nb = (double)L[lb].nx * L[lb].ny, nc = (double)L[P->nlev - 1].nx * L[P->nlev - 1].ny;
         double bytes = (2.0 * nb + nc * nc) * ts;
         for (int l = lb; l < P->nlev; ++l) bytes += ((L[l].nx + 1.0) * L[l].ny + L[l].nx * (L[l].ny + 1.0)) * ts;
-        if constexpr (sizeof(T) == 8) B.lu = (const T *)P->lu64; else B.lu = (const T *)P->lu32;
         const size_t smem_b = (size_t)bottom_elems(B, lb) * sizeof(T);
         WEC_PROF("mg_bottom", lb, bytes, st);
         k_mg_bottom<T><<<1, kBottomThreads, smem_b, st>>>(B, bsel, xsel);
@@ -1174,7 +1219,13 @@ int poisson_init(wec_poisson *P, int nx, int ny, int prec, int restart, int nu1,
             WEC_CK(cudaMalloc(&P->L64[l].xp, nc * 8));
             if (prec == WEC_PREC_MIXED) WEC_CK(cudaMalloc(&P->L32[l].xp, nc * 4));
         }
+        if (prec == WEC_PREC_FP64) {
+            WEC_CK(cudaMalloc(&P->L64[l].id, nc * 8));
+            WEC_CK(cudaMemset(P->L64[l].id, 0, nc * 8));
+        }
         if (prec == WEC_PREC_MIXED) {
+            WEC_CK(cudaMalloc(&P->L32[l].id, nc * 4));
+            WEC_CK(cudaMemset(P->L32[l].id, 0, nc * 4));
             WEC_CK(cudaMalloc(&P->L32[l].bu, nu * 4));
             WEC_CK(cudaMalloc(&P->L32[l].bv, nv * 4));
             WEC_CK(cudaMalloc(&P->L32[l].x, nc * 4));
@@ -1184,6 +1235,12 @@ int poisson_init(wec_poisson *P, int nx, int ny, int prec, int restart, int nu1,
     }
     WEC_CK(cudaMalloc(&P->lu64, (size_t)P->ncoarse * P->ncoarse * 8));
     if (prec == WEC_PREC_MIXED) WEC_CK(cudaMalloc(&P->lu32, (size_t)P->ncoarse * P->ncoarse * 4));
+    if (P->ncoarse <= kInvMax) {
+        if (prec == WEC_PREC_FP64)
+            WEC_CK(cudaMalloc(&P->inv64, (size_t)P->ncoarse * P->ncoarse * 8));
+        else
+            WEC_CK(cudaMalloc(&P->inv32, (size_t)P->ncoarse * P->ncoarse * 4));
+    }
     size_t n = (size_t)nx * ny;
     int m = restart;
     WEC_CK(cudaMalloc(&P->V, (m + 1) * n * 8));
@@ -1213,12 +1270,35 @@ void poisson_free(wec_poisson *P)
         cudaFree(P->L64[l].bu); cudaFree(P->L64[l].bv); cudaFree(P->L64[l].x); cudaFree(P->L64[l].b);
         cudaFree(P->L32[l].bu); cudaFree(P->L32[l].bv); cudaFree(P->L32[l].x); cudaFree(P->L32[l].b);
         cudaFree(P->L64[l].xp); cudaFree(P->L32[l].xp);
+        cudaFree(P->L64[l].id); cudaFree(P->L32[l].id);
     }
     cudaFree(P->lu64); cudaFree(P->lu32);
+    cudaFree(P->inv64); cudaFree(P->inv32);
     cudaFree(P->V); cudaFree(P->Z); cudaFree(P->w); cudaFree(P->d0); cudaFree(P->part); cudaFree(P->dots); cudaFree(P->hess);
     cudaFree(P->ks);
     if (P->ksh) cudaFreeHost(P->ksh);
     *P = wec_poisson();
+}
+
+template <typename T>
+int build_invdiag(wec_poisson *P, Level<T> *L, cudaStream_t st)
+{
+    LevelDiag<T> D;
+    D.nlev = P->nlev;
+    D.off[0] = 0;
+    for (int l = 0; l < P->nlev; ++l) {
+        D.nx[l] = L[l].nx;
+        D.ny[l] = L[l].ny;
+        D.bu[l] = L[l].bu;
+        D.bv[l] = L[l].bv;
+        D.id[l] = L[l].id;
+        D.off[l + 1] = D.off[l] + (long long)L[l].nx * L[l].ny;
+    }
+    const long long tot = D.off[P->nlev];
+    WEC_PROF("mg_invdiag", -1, (double)sizeof(T) * 4.0 * tot, st);
+    k_invdiag<T><<<nblk(tot, 256), 256, 0, st>>>(D);
+    WEC_CK(cudaGetLastError());
+    return WEC_OK;
 }
 
 int poisson_build(wec_poisson *P, cudaStream_t st)
@@ -1251,7 +1331,8 @@ int poisson_build(wec_poisson *P, cudaStream_t st)
         Level<float> &Lf = P->L32[P->nlev - 1];
         const double nn = (double)Lf.nx * Lf.ny;
         WEC_PROF("mg_lu_factor", P->nlev - 1, 4.0 * nn * nn, st);
-        k_lu_factor<float><<<1, 256, 0, st>>>(Lf.nx, Lf.ny, Lf.bu, Lf.bv, P->lu32);
+        k_lu_factor<float><<<1, 256, 0, st>>>(Lf.nx, Lf.ny, Lf.bu, Lf.bv, P->lu32, P->inv32);
+        if (int e = build_invdiag<float>(P, P->L32, st)) return e;
     } else {
         for (int l = 0; l + 1 < P->nlev; ++l) {
             Level<double> &F = P->L64[l], &C = P->L64[l + 1];
@@ -1262,7 +1343,8 @@ int poisson_build(wec_poisson *P, cudaStream_t st)
         Level<double> &Lc = P->L64[P->nlev - 1];
         const double nn = (double)Lc.nx * Lc.ny;
         WEC_PROF("mg_lu_factor", P->nlev - 1, 8.0 * nn * nn, st);
-        k_lu_factor<double><<<1, 256, 0, st>>>(Lc.nx, Lc.ny, Lc.bu, Lc.bv, P->lu64);
+        k_lu_factor<double><<<1, 256, 0, st>>>(Lc.nx, Lc.ny, Lc.bu, Lc.bv, P->lu64, P->inv64);
+        if (int e = build_invdiag<double>(P, P->L64, st)) return e;
     }
     WEC_CK(cudaGetLastError());
     P->have_coef = true;
