@@ -32,6 +32,36 @@ int cuda_fail(cudaError_t e, const char *what);
 
 inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
 
+// Programmatic dependent launch.  Every kernel of the library starts with
+// pdl_entry(), which waits until the previous kernel on the stream has
+// completed and its writes are visible -- the same ordering as plain stream
+// order -- while the launch itself (launch_k) may be processed before that
+// kernel ends.  No kernel triggers its dependents early: measured, an early
+// trigger let waiting grids take SM slots and slowed the step by 6 %.
+__device__ __forceinline__ void pdl_entry()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+// kern<<<grid, block, smem, st>>>(args...) with programmatic dependent launch
+// allowed (captured into graphs as programmatic edges).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                            Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<Args &&>(args)...);
+}
+
 // Launch accounting (profile.cu): open one Scope around every kernel launch.
 namespace prof {
 class Scope {

@@ -161,6 +161,7 @@ __global__ void __launch_bounds__(256) k_mg_pre(int nx, int ny, const T *__restr
                                                 T *__restrict__ xp, T *__restrict__ bc, int nu1, int H,
                                                 const int *bsel)
 {
+    pdl_entry();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const long long n = (long long)nx * ny;
     b = at_sel(b, bsel, n);
@@ -202,6 +203,7 @@ __global__ void __launch_bounds__(256) k_mg_post(int nx, int ny, const T *__rest
                                                  const T *__restrict__ xp, TO *x, const T *__restrict__ xc,
                                                  int nu2, int H, const int *bsel, const int *xsel)
 {
+    pdl_entry();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const long long n = (long long)nx * ny;
     b = at_sel(b, bsel, n);
@@ -291,6 +293,7 @@ template <typename T>
 __global__ void __launch_bounds__(kBottomThreads) k_mg_bottom(BottomLevels<T> L, const int *bsel,
                                                                const int *xsel)
 {
+    pdl_entry();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ long long off[kMaxLevels + 1];
     const int lb = L.lb, last = L.nlev - 1;

@@ -63,6 +63,7 @@ template <typename TX>
 __global__ void k_apply(int nx, int ny, const double *__restrict__ bu, const double *__restrict__ bv,
                         const TX *__restrict__ x, double *__restrict__ y)
 {
+    pdl_entry();
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= nx * ny) return;
     int i = c % nx, j = c / nx;
@@ -74,6 +75,7 @@ __global__ void k_apply(int nx, int ny, const double *__restrict__ bu, const dou
 __global__ void k_residual(int nx, int ny, const double *__restrict__ bu, const double *__restrict__ bv,
                            const double *__restrict__ x, const double *__restrict__ b, double *__restrict__ w)
 {
+    pdl_entry();
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= nx * ny) return;
     int i = c % nx, j = c / nx;
@@ -89,6 +91,7 @@ template <typename T>
 __global__ void k_rbgs(int nx, int ny, const T *__restrict__ bu, const T *__restrict__ bv, T *x,
                        const T *__restrict__ b, int color, int first, const int *bsel, const int *xsel)
 {
+    pdl_entry();
     int half = nx >> 1;
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= half * ny) return;
@@ -113,6 +116,7 @@ __global__ void k_resid_restrict(int nx, int ny, const T *__restrict__ bu, const
                                  const T *__restrict__ x, const T *__restrict__ b, T *__restrict__ bc,
                                  const int *bsel, const int *xsel)
 {
+    pdl_entry();
     int ncx = nx >> 1, ncy = ny >> 1;
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= ncx * ncy) return;
@@ -135,6 +139,7 @@ __global__ void k_resid_restrict(int nx, int ny, const T *__restrict__ bu, const
 template <typename T>
 __global__ void k_prolong(int nx, int ny, T *__restrict__ x, const T *__restrict__ xc, const int *sel)
 {
+    pdl_entry();
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= nx * ny) return;
     x = at_sel(x, sel, (long long)nx * ny);
@@ -146,6 +151,7 @@ template <typename T>
 __global__ void k_coarsen(int nx, int ny, const T *__restrict__ fu, const T *__restrict__ fv,
                           T *__restrict__ cu, T *__restrict__ cv)
 {
+    pdl_entry();
     int ncx = nx >> 1, ncy = ny >> 1;
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     int nu = (ncx + 1) * ncy, nv = ncx * (ncy + 1);
@@ -162,6 +168,7 @@ __global__ void k_coarsen(int nx, int ny, const T *__restrict__ fu, const T *__r
 // out (column outsel, if given) = in widened to FP64
 __global__ void k_widen(long long n, const float *__restrict__ in, double *out, const int *outsel)
 {
+    pdl_entry();
     long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (c >= n) return;
     out = at_sel(out, outsel, n);
@@ -171,6 +178,7 @@ __global__ void k_widen(long long n, const float *__restrict__ in, double *out, 
 template <typename TO, typename TI>
 __global__ void k_convert(long long n, const TI *__restrict__ in, TO *__restrict__ out, const int *insel)
 {
+    pdl_entry();
     long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (c >= n) return;
     in = at_sel(in, insel, n);
@@ -183,6 +191,7 @@ __global__ void k_convert(long long n, const TI *__restrict__ in, TO *__restrict
 template <typename T>
 __global__ void k_lu_factor(int nx, int ny, const T *__restrict__ bu, const T *__restrict__ bv, T *A, T *inv)
 {
+    pdl_entry();
     int n = nx * ny;
     for (long long q = threadIdx.x; q < (long long)n * n; q += blockDim.x) A[q] = T(0);
     __syncthreads();
@@ -234,6 +243,7 @@ struct LevelDiag {
 template <typename T>
 __global__ void k_invdiag(LevelDiag<T> D)
 {
+    pdl_entry();
     const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (k >= D.off[D.nlev]) return;
     int l = 0;
@@ -247,6 +257,7 @@ template <typename T>
 __global__ void k_lu_solve(int n, const T *__restrict__ A, const T *__restrict__ b, T *__restrict__ x,
                            const int *bsel, const int *xsel)
 {
+    pdl_entry();
     int lane = threadIdx.x;
     b = at_sel(b, bsel, n);
     x = at_sel(x, xsel, n);
@@ -472,6 +483,7 @@ __device__ __forceinline__ void set_cond(unsigned long long h, int use, unsigned
 
 __global__ void k_ks_init(KState *ks, double rtol, int maxit, int m)
 {
+    pdl_entry();
     ks->rtol = rtol;
     ks->maxit = maxit;
     ks->m = m;
@@ -488,6 +500,7 @@ __global__ void k_ks_init(KState *ks, double rtol, int maxit, int m)
 __global__ void k_diag0(int nx, int ny, const double *__restrict__ bu, const double *__restrict__ bv,
                         double *__restrict__ d)
 {
+    pdl_entry();
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= nx * ny) return;
     const int j = c / nx, i = c - j * nx;
@@ -498,6 +511,7 @@ __global__ void k_diag0(int nx, int ny, const double *__restrict__ bu, const dou
 __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 2)
     k_bnorm(long long n, const double *__restrict__ b, double *part, KState *ks)
 {
+    pdl_entry();
     __shared__ double sh[KT / 32];
     __shared__ double bsm[1];
     double a = 0.0;
@@ -525,6 +539,7 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 2)
                     const double *__restrict__ d0, const double *__restrict__ b, double *x, double *__restrict__ w,
                     double *part, KState *ks, double *g, int mode, unsigned long long hwhile, int use)
 {
+    pdl_entry();
     __shared__ double sh[KT / 32];
     __shared__ double bsm[1];
     const long long n = (long long)nx * ny;
@@ -581,6 +596,7 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 2)
 __global__ void k_scale0(long long n, const double *__restrict__ w, double *__restrict__ V, float *__restrict__ b32,
                          const KState *ks)
 {
+    pdl_entry();
     if (ks->done) return;
     const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (c >= n) return;
@@ -595,6 +611,7 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 2)
                   const double *__restrict__ d0, const double *__restrict__ Z, const double *__restrict__ V, double *w,
                   double *part, double *h1, KState *ks)
 {
+    pdl_entry();
     __shared__ double sh[KT / 32][KMAXV];
     __shared__ double bsm[KMAXV];
     const long long n = (long long)nx * ny;
@@ -616,6 +633,7 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 2)
     k_orth_dots(long long n, const double *__restrict__ V, double *w, const double *__restrict__ h1, double *part,
                 double *h2, KState *ks)
 {
+    pdl_entry();
     __shared__ double sh[KT / 32][KMAXV];
     __shared__ double bsm[KMAXV];
     __shared__ double hs[KMAXV];
@@ -644,6 +662,7 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 2)
                 const double *__restrict__ h2, double *part, KState *ks, double *H, double *cs, double *sn,
                 double *g, unsigned long long hif, int use)
 {
+    pdl_entry();
     __shared__ double sh[KT / 32];
     __shared__ double bsm[1];
     __shared__ double hs[KMAXV];
@@ -698,6 +717,7 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 2)
 __global__ void __launch_bounds__(KT) k_next_basis(long long n, const double *__restrict__ w, double *V,
                                                      float *__restrict__ b32, KState *ks)
 {
+    pdl_entry();
     const int j = ks->j;
     if (!ks->cycle_end) {
         double *vn = V + (long long)(j + 1) * n;
@@ -718,6 +738,7 @@ __global__ void __launch_bounds__(KT) k_next_basis(long long n, const double *__
 __global__ void k_backsolve(int m, const double *__restrict__ H, const double *__restrict__ g, double *__restrict__ y,
                             const KState *ks)
 {
+    pdl_entry();
     const int jd = ks->jd;
     for (int k = jd - 1; k >= 0; --k) {
         double s = g[k];
@@ -729,6 +750,7 @@ __global__ void k_backsolve(int m, const double *__restrict__ H, const double *_
 __global__ void k_update_x(long long n, const double *__restrict__ y, const double *__restrict__ Z, double *__restrict__ x,
                            const KState *ks)
 {
+    pdl_entry();
     long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (c >= n) return;
     const int jd = ks->jd;
@@ -757,23 +779,23 @@ void vcycle_unfused(wec_poisson *P, Level<T> *L, const T *b0, T *x0, const int *
             T *lu = nullptr;
             if constexpr (sizeof(T) == 8) lu = (T *)P->lu64; else lu = (T *)P->lu32;
             WEC_PROF("mg_lu_solve", l, (n * n + 2 * n) * ts, st);
-            k_lu_solve<T><<<1, 32, 0, st>>>(A.nx * A.ny, lu, b, x, bs, xs);
+            launch_k(k_lu_solve<T>, 1, 32, 0, st, A.nx * A.ny, lu, b, x, bs, xs);
             break;
         }
         int nh = (A.nx >> 1) * A.ny;
         for (int q = 0; q < P->nu1; ++q) {
             {
                 WEC_PROF("mg_rbgs", l, (1.5 * n + nf) * ts, st);
-                k_rbgs<T><<<nblk(nh, TB), TB, 0, st>>>(A.nx, A.ny, A.bu, A.bv, x, b, 0, q == 0, bs, xs);
+                launch_k(k_rbgs<T>, nblk(nh, TB), TB, 0, st, A.nx, A.ny, A.bu, A.bv, x, b, 0, q == 0, bs, xs);
             }
             {
                 WEC_PROF("mg_rbgs", l, (1.5 * n + nf) * ts, st);
-                k_rbgs<T><<<nblk(nh, TB), TB, 0, st>>>(A.nx, A.ny, A.bu, A.bv, x, b, 1, 0, bs, xs);
+                launch_k(k_rbgs<T>, nblk(nh, TB), TB, 0, st, A.nx, A.ny, A.bu, A.bv, x, b, 1, 0, bs, xs);
             }
         }
         Level<T> &C = L[l + 1];
         WEC_PROF("mg_resid_restrict", l, (2.25 * n + nf) * ts, st);
-        k_resid_restrict<T><<<nblk(C.nx * C.ny, TB), TB, 0, st>>>(A.nx, A.ny, A.bu, A.bv, x, b, C.b, bs, xs);
+        launch_k(k_resid_restrict<T>, nblk(C.nx * C.ny, TB), TB, 0, st, A.nx, A.ny, A.bu, A.bv, x, b, C.b, bs, xs);
     }
     for (int l = P->nlev - 2; l >= 0; --l) {
         Level<T> &A = L[l];
@@ -784,16 +806,16 @@ void vcycle_unfused(wec_poisson *P, Level<T> *L, const T *b0, T *x0, const int *
         int nh = (A.nx >> 1) * A.ny;
         {
             WEC_PROF("mg_prolong", l, 2.25 * n * ts, st);
-            k_prolong<T><<<nblk(A.nx * A.ny, TB), TB, 0, st>>>(A.nx, A.ny, x, L[l + 1].x, xs);
+            launch_k(k_prolong<T>, nblk(A.nx * A.ny, TB), TB, 0, st, A.nx, A.ny, x, L[l + 1].x, xs);
         }
         for (int q = 0; q < P->nu2; ++q) {
             {
                 WEC_PROF("mg_rbgs", l, (1.5 * n + nf) * ts, st);
-                k_rbgs<T><<<nblk(nh, TB), TB, 0, st>>>(A.nx, A.ny, A.bu, A.bv, x, b, 0, 0, bs, xs);
+                launch_k(k_rbgs<T>, nblk(nh, TB), TB, 0, st, A.nx, A.ny, A.bu, A.bv, x, b, 0, 0, bs, xs);
             }
             {
                 WEC_PROF("mg_rbgs", l, (1.5 * n + nf) * ts, st);
-                k_rbgs<T><<<nblk(nh, TB), TB, 0, st>>>(A.nx, A.ny, A.bu, A.bv, x, b, 1, 0, bs, xs);
+                launch_k(k_rbgs<T>, nblk(nh, TB), TB, 0, st, A.nx, A.ny, A.bu, A.bv, x, b, 1, 0, bs, xs);
             }
         }
     }
@@ -827,7 +849,7 @@ template <typename T, int TX, int TY>
 void launch_pre_t(const Level<T> &A, const T *b, T *bc, int nu1, int H, const int *bsel, cudaStream_t st)
 {
     dim3 grid((A.nx + TX - 1) / TX, (A.ny + TY - 1) / TY);
-    k_mg_pre<T, TX, TY><<<grid, 256, tile_smem<T>(H, TX, TY), st>>>(A.nx, A.ny, A.bu, A.bv, b, A.id, A.xp, bc, nu1,
+    launch_k(k_mg_pre<T, TX, TY>, grid, 256, tile_smem<T>(H, TX, TY), st, A.nx, A.ny, A.bu, A.bv, b, A.id, A.xp, bc, nu1,
                                                                      H, bsel);
 }
 
@@ -836,7 +858,7 @@ void launch_post_t(const Level<T> &A, const T *b, TO *x, const T *xc, int nu2, i
                    const int *xsel, cudaStream_t st)
 {
     dim3 grid((A.nx + TX - 1) / TX, (A.ny + TY - 1) / TY);
-    k_mg_post<T, TX, TY, TO><<<grid, 256, tile_smem<T>(H, TX, TY), st>>>(A.nx, A.ny, A.bu, A.bv, b, A.id, A.xp, x,
+    launch_k(k_mg_post<T, TX, TY, TO>, grid, 256, tile_smem<T>(H, TX, TY), st, A.nx, A.ny, A.bu, A.bv, b, A.id, A.xp, x,
                                                                          xc, nu2, H, bsel, xsel);
 }
 
@@ -917,7 +939,7 @@ void vcycle_fused(wec_poisson *P, Level<T> *L, const T *b0, TO *x0, const int *b
         for (int l = lb; l < P->nlev; ++l) bytes += ((L[l].nx + 1.0) * L[l].ny + L[l].nx * (L[l].ny + 1.0)) * ts;
         const size_t smem_b = (size_t)bottom_elems(B, lb) * sizeof(T);
         WEC_PROF("mg_bottom", lb, bytes, st);
-        k_mg_bottom<T><<<1, kBottomThreads, smem_b, st>>>(B, bsel, xsel);
+        launch_k(k_mg_bottom<T>, 1, kBottomThreads, smem_b, st, B, bsel, xsel);
     }
     for (int l = lb - 1; l >= 0; --l) {
         Level<T> &A = L[l];
@@ -983,6 +1005,7 @@ int autotune_levels(wec_poisson *P, Level<T> *L, int *tiles, cudaStream_t st)
 template <typename T>
 __global__ void k_fill(long long n, T *a, T v)
 {
+    pdl_entry();
     long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (c < n) a[c] = v;
 }
@@ -994,11 +1017,11 @@ int poisson_autotune(wec_poisson *P, cudaStream_t st)
     // placeholder coefficients (the real ones are set before every solve)
     for (int l = 0; l < P->nlev; ++l) {
         long long nu = (long long)(P->L64[l].nx + 1) * P->L64[l].ny, nv = (long long)P->L64[l].nx * (P->L64[l].ny + 1);
-        k_fill<double><<<nblk(nu, 256), 256, 0, st>>>(nu, P->L64[l].bu, 1.0);
-        k_fill<double><<<nblk(nv, 256), 256, 0, st>>>(nv, P->L64[l].bv, 1.0);
+        launch_k(k_fill<double>, nblk(nu, 256), 256, 0, st, nu, P->L64[l].bu, 1.0);
+        launch_k(k_fill<double>, nblk(nv, 256), 256, 0, st, nv, P->L64[l].bv, 1.0);
         if (P->prec == WEC_PREC_MIXED) {
-            k_fill<float><<<nblk(nu, 256), 256, 0, st>>>(nu, P->L32[l].bu, 1.0f);
-            k_fill<float><<<nblk(nv, 256), 256, 0, st>>>(nv, P->L32[l].bv, 1.0f);
+            launch_k(k_fill<float>, nblk(nu, 256), 256, 0, st, nu, P->L32[l].bu, 1.0f);
+            launch_k(k_fill<float>, nblk(nv, 256), 256, 0, st, nv, P->L32[l].bv, 1.0f);
         }
     }
     int e = P->prec == WEC_PREC_FP64 ? autotune_levels<double>(P, P->L64, P->tile64, st)
@@ -1023,7 +1046,7 @@ void vcycle_t(wec_poisson *P, Level<T> *L, const T *b0, TO *x0, const int *bsel,
         const long long n = (long long)L[0].nx * L[0].ny;
         vcycle_unfused<T>(P, L, b0, L[0].x, bsel, nullptr, st);
         WEC_PROF("convert", 0, 12.0 * n, st);
-        k_widen<<<nblk(n, 256), 256, 0, st>>>(n, L[0].x, x0, xsel);
+        launch_k(k_widen, nblk(n, 256), 256, 0, st, n, L[0].x, x0, xsel);
     }
 }
 
@@ -1081,19 +1104,19 @@ void enqueue_begin(wec_poisson *P, const double *b, double *x, double rtol, int 
     float *b32 = P->prec == WEC_PREC_MIXED ? P->L32[0].b : nullptr;
     {
         WEC_PROF("scalar", -1, 64.0, st);
-        k_ks_init<<<1, 1, 0, st>>>(P->ks, rtol, maxit, P->restart);
+        launch_k(k_ks_init, 1, 1, 0, st, P->ks, rtol, maxit, P->restart);
     }
     {
         WEC_PROF("krylov_norm", -1, 8.0 * n, st);
-        k_bnorm<<<G, KT, 0, st>>>(n, b, P->part, P->ks);
+        launch_k(k_bnorm, G, KT, 0, st, n, b, P->part, P->ks);
     }
     {
         WEC_PROF("krylov_residual", -1, 8.0 * (4.0 * n + nf), st);
-        k_residual_norm<<<G, KT, 0, st>>>(P->nx, P->ny, P->L64[0].bu, P->L64[0].bv, P->d0, b, x, P->w, P->part,
+        launch_k(k_residual_norm, G, KT, 0, st, P->nx, P->ny, P->L64[0].bu, P->L64[0].bv, P->d0, b, x, P->w, P->part,
                                           P->ks, P->g, 0, hw, use);
     }
     WEC_PROF("krylov_scale", -1, (16.0 + (b32 ? 4.0 : 0.0)) * n, st);
-    k_scale0<<<nblk(n, 256), 256, 0, st>>>(n, P->w, P->V, b32, P->ks);
+    launch_k(k_scale0, nblk(n, 256), 256, 0, st, n, P->w, P->V, b32, P->ks);
 }
 
 // One Arnoldi step j (preconditioner, matvec, CGS2, Givens, next basis vector).
@@ -1112,19 +1135,19 @@ void enqueue_body(wec_poisson *P, unsigned long long hif, int use, cudaStream_t 
         vcycle_t<float, double>(P, P->L32, P->L32[0].b, P->Z, nullptr, &P->ks->j, st);
     {
         WEC_PROF("krylov_matvec_dots", -1, 8.0 * (3.0 * n + nf) + 8.0 * n * m, st);
-        k_matvec_dots<<<G, KT, 0, st>>>(P->nx, P->ny, P->L64[0].bu, P->L64[0].bv, P->d0, P->Z, P->V, P->w, P->part,
+        launch_k(k_matvec_dots, G, KT, 0, st, P->nx, P->ny, P->L64[0].bu, P->L64[0].bv, P->d0, P->Z, P->V, P->w, P->part,
                                         h1, P->ks);
     }
     {
         WEC_PROF("krylov_orth_dots", -1, 8.0 * n * (m + 2), st);
-        k_orth_dots<<<G, KT, 0, st>>>(n, P->V, P->w, h1, P->part, h2, P->ks);
+        launch_k(k_orth_dots, G, KT, 0, st, n, P->V, P->w, h1, P->part, h2, P->ks);
     }
     {
         WEC_PROF("krylov_orth_norm", -1, 8.0 * n * (m + 2), st);
-        k_orth_norm<<<G, KT, 0, st>>>(n, P->V, P->w, h1, h2, P->part, P->ks, P->hess, P->cs, P->sn, P->g, hif, use);
+        launch_k(k_orth_norm, G, KT, 0, st, n, P->V, P->w, h1, h2, P->part, P->ks, P->hess, P->cs, P->sn, P->g, hif, use);
     }
     WEC_PROF("krylov_next_basis", -1, (16.0 + (mixed ? 4.0 : 0.0)) * n, st);
-    k_next_basis<<<nblk(n, KT), KT, 0, st>>>(n, P->w, P->V, mixed ? P->L32[0].b : nullptr, P->ks);
+    launch_k(k_next_basis, nblk(n, KT), KT, 0, st, n, P->w, P->V, mixed ? P->L32[0].b : nullptr, P->ks);
 }
 
 // End of a cycle: y from the triangular system, x += Z y, true residual, then
@@ -1137,19 +1160,19 @@ void enqueue_close(wec_poisson *P, const double *b, double *x, unsigned long lon
     const bool mixed = P->prec == WEC_PREC_MIXED;
     {
         WEC_PROF("scalar", -1, 8.0 * m * m, st);
-        k_backsolve<<<1, 1, 0, st>>>(m, P->hess, P->g, P->y, P->ks);
+        launch_k(k_backsolve, 1, 1, 0, st, m, P->hess, P->g, P->y, P->ks);
     }
     {
         WEC_PROF("krylov_update_x", -1, 16.0 * n + 8.0 * n * m, st);
-        k_update_x<<<nblk(n, 256), 256, 0, st>>>(n, P->y, P->Z, x, P->ks);
+        launch_k(k_update_x, nblk(n, 256), 256, 0, st, n, P->y, P->Z, x, P->ks);
     }
     {
         WEC_PROF("krylov_residual", -1, 8.0 * (4.0 * n + nf), st);
-        k_residual_norm<<<G, KT, 0, st>>>(P->nx, P->ny, P->L64[0].bu, P->L64[0].bv, P->d0, b, x, P->w, P->part,
+        launch_k(k_residual_norm, G, KT, 0, st, P->nx, P->ny, P->L64[0].bu, P->L64[0].bv, P->d0, b, x, P->w, P->part,
                                           P->ks, P->g, 1, hw, use);
     }
     WEC_PROF("krylov_scale", -1, (16.0 + (mixed ? 4.0 : 0.0)) * n, st);
-    k_scale0<<<nblk(n, 256), 256, 0, st>>>(n, P->w, P->V, mixed ? P->L32[0].b : nullptr, P->ks);
+    launch_k(k_scale0, nblk(n, 256), 256, 0, st, n, P->w, P->V, mixed ? P->L32[0].b : nullptr, P->ks);
 }
 
 int read_state(wec_poisson *P, cudaStream_t st)
@@ -1296,7 +1319,7 @@ int build_invdiag(wec_poisson *P, Level<T> *L, cudaStream_t st)
     }
     const long long tot = D.off[P->nlev];
     WEC_PROF("mg_invdiag", -1, (double)sizeof(T) * 4.0 * tot, st);
-    k_invdiag<T><<<nblk(tot, 256), 256, 0, st>>>(D);
+    launch_k(k_invdiag<T>, nblk(tot, 256), 256, 0, st, D);
     WEC_CK(cudaGetLastError());
     return WEC_OK;
 }
@@ -1306,7 +1329,7 @@ int poisson_build(wec_poisson *P, cudaStream_t st)
     {
         const int n = P->nx * P->ny;
         WEC_PROF("diag", 0, 8.0 * (n + (P->nx + 1.0) * P->ny + P->nx * (P->ny + 1.0)), st);
-        k_diag0<<<nblk(n, 256), 256, 0, st>>>(P->nx, P->ny, P->L64[0].bu, P->L64[0].bv, P->d0);
+        launch_k(k_diag0, nblk(n, 256), 256, 0, st, P->nx, P->ny, P->L64[0].bu, P->L64[0].bv, P->d0);
     }
     if (P->prec == WEC_PREC_MIXED) {
         // the V-cycle is FP32 throughout: level 0 converted once, coarse levels
@@ -1316,34 +1339,34 @@ int poisson_build(wec_poisson *P, cudaStream_t st)
         const long long nu = (long long)(A.nx + 1) * A.ny, nv = (long long)A.nx * (A.ny + 1);
         {
             WEC_PROF("convert", 0, 12.0 * nu, st);
-            k_convert<float, double><<<nblk(nu, 256), 256, 0, st>>>(nu, A.bu, F.bu, nullptr);
+            launch_k(k_convert<float, double>, nblk(nu, 256), 256, 0, st, nu, A.bu, F.bu, nullptr);
         }
         {
             WEC_PROF("convert", 0, 12.0 * nv, st);
-            k_convert<float, double><<<nblk(nv, 256), 256, 0, st>>>(nv, A.bv, F.bv, nullptr);
+            launch_k(k_convert<float, double>, nblk(nv, 256), 256, 0, st, nv, A.bv, F.bv, nullptr);
         }
         for (int l = 0; l + 1 < P->nlev; ++l) {
             Level<float> &Fl = P->L32[l], &C = P->L32[l + 1];
             int cnt = (C.nx + 1) * C.ny + C.nx * (C.ny + 1);
             WEC_PROF("mg_coarsen", l, 12.0 * cnt, st);
-            k_coarsen<float><<<nblk(cnt, 256), 256, 0, st>>>(Fl.nx, Fl.ny, Fl.bu, Fl.bv, C.bu, C.bv);
+            launch_k(k_coarsen<float>, nblk(cnt, 256), 256, 0, st, Fl.nx, Fl.ny, Fl.bu, Fl.bv, C.bu, C.bv);
         }
         Level<float> &Lf = P->L32[P->nlev - 1];
         const double nn = (double)Lf.nx * Lf.ny;
         WEC_PROF("mg_lu_factor", P->nlev - 1, 4.0 * nn * nn, st);
-        k_lu_factor<float><<<1, 256, 0, st>>>(Lf.nx, Lf.ny, Lf.bu, Lf.bv, P->lu32, P->inv32);
+        launch_k(k_lu_factor<float>, 1, 256, 0, st, Lf.nx, Lf.ny, Lf.bu, Lf.bv, P->lu32, P->inv32);
         if (int e = build_invdiag<float>(P, P->L32, st)) return e;
     } else {
         for (int l = 0; l + 1 < P->nlev; ++l) {
             Level<double> &F = P->L64[l], &C = P->L64[l + 1];
             int cnt = (C.nx + 1) * C.ny + C.nx * (C.ny + 1);
             WEC_PROF("mg_coarsen", l, 24.0 * cnt, st);
-            k_coarsen<double><<<nblk(cnt, 256), 256, 0, st>>>(F.nx, F.ny, F.bu, F.bv, C.bu, C.bv);
+            launch_k(k_coarsen<double>, nblk(cnt, 256), 256, 0, st, F.nx, F.ny, F.bu, F.bv, C.bu, C.bv);
         }
         Level<double> &Lc = P->L64[P->nlev - 1];
         const double nn = (double)Lc.nx * Lc.ny;
         WEC_PROF("mg_lu_factor", P->nlev - 1, 8.0 * nn * nn, st);
-        k_lu_factor<double><<<1, 256, 0, st>>>(Lc.nx, Lc.ny, Lc.bu, Lc.bv, P->lu64, P->inv64);
+        launch_k(k_lu_factor<double>, 1, 256, 0, st, Lc.nx, Lc.ny, Lc.bu, Lc.bv, P->lu64, P->inv64);
         if (int e = build_invdiag<double>(P, P->L64, st)) return e;
     }
     WEC_CK(cudaGetLastError());
@@ -1355,7 +1378,7 @@ int poisson_apply(wec_poisson *P, const double *x, double *y)
 {
     int n = P->nx * P->ny;
     WEC_PROF("krylov_matvec", -1, 8.0 * (2.0 * n + (P->nx + 1.0) * P->ny + P->nx * (P->ny + 1.0)), P->st);
-    k_apply<double><<<nblk(n, 256), 256, 0, P->st>>>(P->nx, P->ny, P->L64[0].bu, P->L64[0].bv, x, y);
+    launch_k(k_apply<double>, nblk(n, 256), 256, 0, P->st, P->nx, P->ny, P->L64[0].bu, P->L64[0].bv, x, y);
     WEC_CK(cudaGetLastError());
     return WEC_OK;
 }
@@ -1369,11 +1392,11 @@ int poisson_vcycle(wec_poisson *P, const double *b, double *x)
     } else {
         {
             WEC_PROF("convert", -1, 12.0 * n, st);
-            k_convert<float, double><<<nblk(n, 256), 256, 0, st>>>(n, b, P->L32[0].b, nullptr);
+            launch_k(k_convert<float, double>, nblk(n, 256), 256, 0, st, n, b, P->L32[0].b, nullptr);
         }
         vcycle_t<float, float>(P, P->L32, P->L32[0].b, P->L32[0].x, nullptr, nullptr, st);
         WEC_PROF("convert", -1, 12.0 * n, st);
-        k_convert<double, float><<<nblk(n, 256), 256, 0, st>>>(n, P->L32[0].x, x, nullptr);
+        launch_k(k_convert<double, float>, nblk(n, 256), 256, 0, st, n, P->L32[0].x, x, nullptr);
     }
     WEC_CK(cudaGetLastError());
     return WEC_OK;

@@ -236,6 +236,7 @@ __device__ __forceinline__ R warp_sum_d(R v)
 // and t^{n+1}: one warp per value, lanes over the wave components.
 __global__ void k_bc_eta(TankP P, const StepScalars *S, const double *__restrict__ inp, Bc bc)
 {
+    pdl_entry();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;  // 8 warps: (time, position)
     const double t = (w & 1) ? S->t + inp[0] : S->t;
     const int pos = w >> 1;                                    // 0: x = 0; 1..3: ghost columns
@@ -256,6 +257,7 @@ __global__ void k_bc_eta(TankP P, const StepScalars *S, const double *__restrict
 template <typename R>
 __global__ void k_bc_rows(TankP P, const StepScalars *S, const double *__restrict__ inp, Bc bc)
 {
+    pdl_entry();
     const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (j > P.ny) return;
     const R t0 = R(S->t), t1 = R(S->t) + R(inp[0]), d = cst<R>(P).depth;
@@ -300,6 +302,7 @@ template <typename R>
 __global__ void k_materials(TankP P, const StepScalars *S, int which, const double *__restrict__ sig,
                             R *rho, R *mu, R *rhof, R *chi)
 {
+    pdl_entry();
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= P.nx * P.ny) return;
     int i = c % P.nx, j = c / P.nx;
@@ -337,6 +340,7 @@ __global__ void k_force_partial(TankP P, const StepScalars *S, const double *__r
                                 const M *__restrict__ mu, const double *__restrict__ vin0,
                                 double *__restrict__ part)
 {
+    pdl_entry();
     __shared__ double sh[TB];
     const int nx = P.nx, ny = P.ny;
     const double h = P.h, yc = S->yc;
@@ -389,6 +393,7 @@ __global__ void k_force_partial(TankP P, const StepScalars *S, const double *__r
 // (m + m_a)(zdot^{n+1} - zdot^n) = dt (F - m g + F_PTO) + m_a (zdot^n - zdot^{n-1}).
 __global__ void k_heave(TankP P, StepScalars *S, const double *__restrict__ part, const double *__restrict__ inp)
 {
+    pdl_entry();
     const double dt = inp[0], fpto_in = inp[1];
     __shared__ double sh[TB];
     double s = 0.0;
@@ -415,6 +420,7 @@ __global__ void k_advect(TankP P, const R *__restrict__ s, const R *__restrict__
                          const double *__restrict__ inp, const R *__restrict__ alpha_c,
                          double *__restrict__ out, R *__restrict__ out_w)
 {
+    pdl_entry();
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= P.nx * P.ny) return;
     const R dt = R(inp[0]);
@@ -473,6 +479,7 @@ __device__ R reinit_rhs(const TankP &P, const R *__restrict__ f, const R *__rest
 template <typename R>
 __global__ void k_reinit_sign(TankP P, const R *__restrict__ s0, R *__restrict__ sgn)
 {
+    pdl_entry();
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= P.nx * P.ny) return;
     R g0 = s0[c];
@@ -485,6 +492,7 @@ __global__ void k_reinit(TankP P, const R *__restrict__ f, const R *__restrict__
                          const R *__restrict__ fprev, const double *__restrict__ eta1, R dtau,
                          TO *__restrict__ out)
 {
+    pdl_entry();
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= P.nx * P.ny) return;
     int i = c % P.nx, j = c / P.nx;
@@ -504,6 +512,7 @@ struct Tabs {
 // t32 (optional) receives the same tables in FP32.
 __global__ void k_tables(TankP P, double *t, float *t32)
 {
+    pdl_entry();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int nx = P.nx, ny = P.ny, o1 = nx, o2 = 2 * nx + 1, o3 = 2 * nx + 1 + ny;
     auto put = [&](int o, double val) {
@@ -664,6 +673,7 @@ __global__ void k_mom_u(TankP P, const StepScalars *S, const double *__restrict_
                         const R *__restrict__ u, const R *__restrict__ v, const double *__restrict__ p,
                         Bc bc, R *Ru, R *Du, R *ua)
 {
+    pdl_entry();
     int f = blockIdx.x * blockDim.x + threadIdx.x;
     const int nx = P.nx;
     if (f >= (nx + 1) * P.ny) return;
@@ -695,6 +705,7 @@ __global__ void k_mom_v(TankP P, const StepScalars *S, const double *__restrict_
                         const R *__restrict__ rf_1, const R *__restrict__ u, const R *__restrict__ v,
                         const double *__restrict__ p, Bc bc, R *Rv, R *Dv, R *va)
 {
+    pdl_entry();
     int f = blockIdx.x * blockDim.x + threadIdx.x;
     const int nx = P.nx, ny = P.ny;
     if (f >= nx * (ny + 1)) return;
@@ -736,6 +747,7 @@ __global__ void k_mirror(long long nc, long long nu, long long nv, const double 
                          const double *__restrict__ u, const double *__restrict__ v, float *__restrict__ sig32,
                          float *__restrict__ u32, float *__restrict__ v32)
 {
+    pdl_entry();
     long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (k < nc) sig32[k] = float(sig[k]);
     if (k < nu) u32[k] = float(u[k]);
@@ -751,6 +763,7 @@ __global__ void k_jacobi(TankP P, const R *__restrict__ mu_1, const double *__re
                          const R *__restrict__ ua, const R *__restrict__ va, TO *__restrict__ ub,
                          TO *__restrict__ vb)
 {
+    pdl_entry();
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int nx = P.nx, ny = P.ny;
     const int nu = (nx + 1) * ny, nv = nx * (ny + 1);
@@ -781,6 +794,7 @@ __global__ void k_proj_rhs(TankP P, const double *__restrict__ us, const double 
                            const TD *__restrict__ Du, const TD *__restrict__ Dv, double *rhs,
                            double *bu, double *bv)
 {
+    pdl_entry();
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int nx = P.nx, ny = P.ny;
     const int nc = nx * ny, nu = (nx + 1) * ny, nv = nx * (ny + 1);
@@ -801,6 +815,7 @@ __global__ void k_project(TankP P, const double *__restrict__ us, const double *
                           const double *__restrict__ bu, const double *__restrict__ bv,
                           const double *__restrict__ phi, double *u, double *v, double *p)
 {
+    pdl_entry();
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int nx = P.nx, ny = P.ny;
     const int nc = nx * ny, nu = (nx + 1) * ny, nv = nx * (ny + 1);
@@ -825,6 +840,7 @@ __global__ void k_project(TankP P, const double *__restrict__ us, const double *
 __global__ void k_div_partial(TankP P, const double *__restrict__ u, const double *__restrict__ v,
                               double *__restrict__ part)
 {
+    pdl_entry();
     __shared__ double sh[TB];
     const int nx = P.nx;
     double acc = 0.0;
@@ -843,6 +859,7 @@ __global__ void k_finalize(TankP P, StepScalars *S, const double *__restrict__ p
                            const double *__restrict__ sig, const double *__restrict__ inp, const KState *ks,
                            int n_fixed, int n_body, int n_close)
 {
+    pdl_entry();
     __shared__ double sh[TB];
     double s = 0.0;
     for (int b = threadIdx.x; b < kRedBlocks; b += blockDim.x) s += part[b];
@@ -877,6 +894,7 @@ __global__ void k_finalize(TankP P, StepScalars *S, const double *__restrict__ p
 // right wall, v = 0 on the bed).
 __global__ void k_init_fields(TankP P, double *sig, double *u, double *v)
 {
+    pdl_entry();
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int nx = P.nx, ny = P.ny;
     const int nc = nx * ny, nu = (nx + 1) * ny, nv = nx * (ny + 1);
@@ -900,6 +918,7 @@ __global__ void k_init_fields(TankP P, double *sig, double *u, double *v)
 // face): p_{ny-1} = rho_f g h / 2, p_{j-1} = p_j + (face mean rho_f) g h.
 __global__ void k_init_pressure(TankP P, const double *__restrict__ rf, double *p)
 {
+    pdl_entry();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int nx = P.nx, ny = P.ny;
     if (i >= nx) return;
@@ -987,7 +1006,7 @@ int tank_alloc_and_init(wec_tank *T)
     WEC_CK(cudaMalloc(&T->sgn, nc * 8));
     {
         WEC_PROF("init", -1, 8.0 * (2 * P.nx + 2 * P.ny + 2), T->gst);
-        k_tables<<<nblk(std::max(P.nx, P.ny) + 1, 128), 128, 0, T->gst>>>(P, T->tabs, T->tabs32);
+        launch_k(k_tables, nblk(std::max(P.nx, P.ny) + 1, 128), 128, 0, T->gst, P, T->tabs, T->tabs32);
     }
     WEC_CK(cudaMalloc(&T->inp, 2 * 8));
     WEC_CK(cudaMemset(T->inp, 0, 2 * 8));
@@ -1001,7 +1020,7 @@ int tank_alloc_and_init(wec_tank *T)
         return e;
     long long ninit = (long long)nc + nu + nv;
     WEC_PROF("init", -1, 8.0 * ninit, T->gst);
-    k_init_fields<<<nblk(ninit, TB), TB, 0, T->gst>>>(P, T->sig, T->u, T->v);
+    launch_k(k_init_fields, nblk(ninit, TB), TB, 0, T->gst, P, T->sig, T->u, T->v);
     WEC_CK(cudaGetLastError());
     return WEC_OK;
 }
@@ -1013,11 +1032,12 @@ int tank_init_pressure(wec_tank *T)
     const TankP &P = T->P;
     {
         WEC_PROF("materials", -1, 16.0 * T->nc, T->gst);
-        k_materials<double><<<nblk(T->nc, TB), TB, 0, T->gst>>>(P, T->S, 0, T->sig, nullptr, nullptr, T->rf_1, nullptr);
+        launch_k(k_materials<double>, nblk(T->nc, TB), TB, 0, T->gst, P, T->S, 0, T->sig, (double *)nullptr,
+                 (double *)nullptr, T->rf_1, (double *)nullptr);
     }
     {
         WEC_PROF("init", -1, 16.0 * T->nc, T->gst);
-        k_init_pressure<<<nblk(P.nx, 128), 128, 0, T->gst>>>(P, T->rf_1, T->p);
+        launch_k(k_init_pressure, nblk(P.nx, 128), 128, 0, T->gst, P, T->rf_1, T->p);
     }
     WEC_CK(cudaGetLastError());
     WEC_CK(cudaStreamSynchronize(T->gst));
@@ -1049,36 +1069,36 @@ void enqueue_front_t(wec_tank *T, const Work<R> &W, cudaStream_t st)
     constexpr bool f32 = sizeof(R) == 4;
     if constexpr (f32) {
         WEC_PROF("mirror", -1, (fb + rb) * (nc + nu + nv), st);
-        k_mirror<<<nblk(std::max(nc, std::max(nu, nv)), TB), TB, 0, st>>>(nc, nu, nv, T->sig, T->u, T->v, W.sig,
+        launch_k(k_mirror, nblk(std::max(nc, std::max(nu, nv)), TB), TB, 0, st, nc, nu, nv, T->sig, T->u, T->v, W.sig,
                                                                             W.u, W.v);
     }
     // (1) inflow / ghost data at t^n and t^{n+1}
     {
         WEC_PROF("bc", -1, fb * 8.0, st);
-        k_bc_eta<<<1, 256, 0, st>>>(P, T->S, T->inp, T->bc);
+        launch_k(k_bc_eta, 1, 256, 0, st, P, T->S, T->inp, T->bc);
     }
     {
         WEC_PROF("bc", -1, fb * (3.0 * P.ny + 2), st);
-        k_bc_rows<R><<<nblk(P.ny + 1, 2), 64, 0, st>>>(P, T->S, T->inp, T->bc);
+        launch_k(k_bc_rows<R>, nblk(P.ny + 1, 2), 64, 0, st, P, T->S, T->inp, T->bc);
     }
     // (2) materials at n, force from p^{n-1/2}, u^n (Eq. int_fh), heave (Eq. newton_u)
     {
         WEC_PROF("materials", -1, (fb + 2.0 * rb) * nc, st);
-        k_materials<R><<<nblk(nc, TB), TB, 0, st>>>(P, T->S, 0, T->sig, W.rho_n, W.mu_n, nullptr, nullptr);
+        launch_k(k_materials<R>, nblk(nc, TB), TB, 0, st, P, T->S, 0, T->sig, W.rho_n, W.mu_n, nullptr, nullptr);
     }
     {
         WEC_PROF("force", -1, fb * kRedBlocks, st);
-        k_force_partial<R><<<kRedBlocks, TB, 0, st>>>(P, T->S, T->p, T->u, T->v, W.mu_n, T->bc.vin0, T->part);
+        launch_k(k_force_partial<R>, kRedBlocks, TB, 0, st, P, T->S, T->p, T->u, T->v, W.mu_n, T->bc.vin0, T->part);
     }
     {
         WEC_PROF("scalar", -1, fb * kRedBlocks, st);
-        k_heave<<<1, TB, 0, st>>>(P, T->S, T->part, T->inp);
+        launch_k(k_heave, 1, TB, 0, st, P, T->S, T->part, T->inp);
     }
     // (3) sigma advection + damping-zone relaxation, then reinitialisation; the
     // last pseudo-step writes sigma^{n+1} over sigma^n (no longer needed).
     {
         WEC_PROF("advect", -1, rb * (nc + nu + nv) + (fb + (f32 ? rb : 0.0)) * nc, st);
-        k_advect<R><<<nblk(nc, TB), TB, 0, st>>>(P, W.sig, W.u, W.v, T->bc.eta0, T->inp, tabs<R>(T).alpha_c, T->sa,
+        launch_k(k_advect<R>, nblk(nc, TB), TB, 0, st, P, W.sig, W.u, W.v, T->bc.eta0, T->inp, tabs<R>(T).alpha_c, T->sa,
                                                  f32 ? W.sa : nullptr);
     }
     const R dtau = R(0.3 * P.h);
@@ -1087,19 +1107,19 @@ void enqueue_front_t(wec_tank *T, const Work<R> &W, cudaStream_t st)
     const int nr = T->opts.n_reinit;
     if (nr > 0) {
         WEC_PROF("reinit", -1, rb * 2.0 * nc, st);
-        k_reinit_sign<R><<<nblk(nc, TB), TB, 0, st>>>(P, W.sa, W.sgn);
+        launch_k(k_reinit_sign<R>, nblk(nc, TB), TB, 0, st, P, W.sa, W.sgn);
     }
     for (int it = 0; it < nr; ++it) {
         {
             WEC_PROF("reinit", -1, rb * 3.0 * nc, st);
-            k_reinit<R, R><<<nblk(nc, TB), TB, 0, st>>>(P, f, W.sgn, nullptr, T->bc.eta1, dtau, W.rt);
+            launch_k(k_reinit<R, R>, nblk(nc, TB), TB, 0, st, P, f, W.sgn, nullptr, T->bc.eta1, dtau, W.rt);
         }
         WEC_PROF("reinit", -1, rb * 3.0 * nc + (it == nr - 1 ? fb : rb) * nc, st);
         if (it == nr - 1) {
-            k_reinit<R, double><<<nblk(nc, TB), TB, 0, st>>>(P, W.rt, W.sgn, f, T->bc.eta1, dtau, T->sig);
+            launch_k(k_reinit<R, double>, nblk(nc, TB), TB, 0, st, P, W.rt, W.sgn, f, T->bc.eta1, dtau, T->sig);
         } else {
             R *dst = bufs[it & 1];
-            k_reinit<R, R><<<nblk(nc, TB), TB, 0, st>>>(P, W.rt, W.sgn, f, T->bc.eta1, dtau, dst);
+            launch_k(k_reinit<R, R>, nblk(nc, TB), TB, 0, st, P, W.rt, W.sgn, f, T->bc.eta1, dtau, dst);
             f = dst;
         }
     }
@@ -1107,17 +1127,17 @@ void enqueue_front_t(wec_tank *T, const Work<R> &W, cudaStream_t st)
     // (4) materials at n+1 (psi at the new body position)
     {
         WEC_PROF("materials", -1, (fb + 3.0 * rb) * nc, st);
-        k_materials<R><<<nblk(nc, TB), TB, 0, st>>>(P, T->S, 1, T->sig, nullptr, W.mu_1, W.rf_1, W.chi_1);
+        launch_k(k_materials<R>, nblk(nc, TB), TB, 0, st, P, T->S, 1, T->sig, nullptr, W.mu_1, W.rf_1, W.chi_1);
     }
     // (5) momentum right-hand side and diagonal, (6) Crank-Nicolson Jacobi sweeps
     {
         WEC_PROF("mom_u", -1, rb * (3.0 * nc + nu + nv + 2.0 * nu) + fb * (nc + nu), st);
-        k_mom_u<R><<<nblk(nu, TB), TB, 0, st>>>(P, T->S, T->inp, tabs<R>(T), W.rho_n, W.mu_n, W.chi_1, W.u, W.v, T->p,
+        launch_k(k_mom_u<R>, nblk(nu, TB), TB, 0, st, P, T->S, T->inp, tabs<R>(T), W.rho_n, W.mu_n, W.chi_1, W.u, W.v, T->p,
                                                 T->bc, W.Ru, W.Du, W.ua);
     }
     {
         WEC_PROF("mom_v", -1, rb * (4.0 * nc + nu + nv + 2.0 * nv) + fb * (nc + nv), st);
-        k_mom_v<R><<<nblk(nv, TB), TB, 0, st>>>(P, T->S, T->inp, tabs<R>(T), W.rho_n, W.mu_n, W.chi_1, W.rf_1, W.u,
+        launch_k(k_mom_v<R>, nblk(nv, TB), TB, 0, st, P, T->S, T->inp, tabs<R>(T), W.rho_n, W.mu_n, W.chi_1, W.rf_1, W.u,
                                                 W.v, T->p, T->bc, W.Rv, W.Dv, W.va);
     }
     const R *ju = W.ua, *jv = W.va;
@@ -1128,10 +1148,10 @@ void enqueue_front_t(wec_tank *T, const Work<R> &W, cudaStream_t st)
         WEC_PROF("jacobi", -1, rb * (nc + 4.0 * (nu + nv)) + fb * (nu + nv) + (last ? fb - rb : 0.0) * (nu + nv),
                  st);
         if (last) {
-            k_jacobi<R, double><<<nblk(nu + nv, TB), TB, 0, st>>>(P, W.mu_1, T->bc.vin1, W.Ru, W.Du, W.Rv, W.Dv,
+            launch_k(k_jacobi<R, double>, nblk(nu + nv, TB), TB, 0, st, P, W.mu_1, T->bc.vin1, W.Ru, W.Du, W.Rv, W.Dv,
                                                                   ju, jv, T->us, T->vs);
         } else {
-            k_jacobi<R, R><<<nblk(nu + nv, TB), TB, 0, st>>>(P, W.mu_1, T->bc.vin1, W.Ru, W.Du, W.Rv, W.Dv, ju,
+            launch_k(k_jacobi<R, R>, nblk(nu + nv, TB), TB, 0, st, P, W.mu_1, T->bc.vin1, W.Ru, W.Du, W.Rv, W.Dv, ju,
                                                              jv, tu[it & 1], tv[it & 1]);
             ju = tu[it & 1];
             jv = tv[it & 1];
@@ -1141,7 +1161,7 @@ void enqueue_front_t(wec_tank *T, const Work<R> &W, cudaStream_t st)
     wec_poisson *S = &T->solver;
     {
         WEC_PROF("proj_rhs", -1, fb * (nc + 3.0 * (nu + nv)), st);
-        k_proj_rhs<R><<<nblk(nc + nu + nv, TB), TB, 0, st>>>(P, T->us, T->vs, W.Du, W.Dv, T->rhs, S->L64[0].bu,
+        launch_k(k_proj_rhs<R>, nblk(nc + nu + nv, TB), TB, 0, st, P, T->us, T->vs, W.Du, W.Dv, T->rhs, S->L64[0].bu,
                                                           S->L64[0].bv);
     }
     poisson_build(S, st);
@@ -1165,15 +1185,15 @@ void enqueue_back(wec_tank *T, cudaStream_t st)
     wec_poisson *S = &T->solver;
     {
         WEC_PROF("project", -1, fb * (3.0 * nc + 3.0 * (nu + nv)), st);
-        k_project<<<nblk(nu + nv + nc, TB), TB, 0, st>>>(P, T->us, T->vs, S->L64[0].bu, S->L64[0].bv, T->phi,
+        launch_k(k_project, nblk(nu + nv + nc, TB), TB, 0, st, P, T->us, T->vs, S->L64[0].bu, S->L64[0].bv, T->phi,
                                                          T->u, T->v, T->p);
     }
     {
         WEC_PROF("divergence", -1, fb * (nu + nv), st);
-        k_div_partial<<<kRedBlocks, TB, 0, st>>>(P, T->u, T->v, T->part);
+        launch_k(k_div_partial, kRedBlocks, TB, 0, st, P, T->u, T->v, T->part);
     }
     WEC_PROF("scalar", -1, fb * (kRedBlocks + P.ny), st);
-    k_finalize<<<1, TB, 0, st>>>(P, T->S, T->part, T->sig, T->inp, S->ks, T->n_fixed, T->n_body, T->n_close);
+    launch_k(k_finalize, 1, TB, 0, st, P, T->S, T->part, T->sig, T->inp, S->ks, T->n_fixed, T->n_body, T->n_close);
 }
 
 // Kernels per replay (front + the solve's opening + back once, then the
