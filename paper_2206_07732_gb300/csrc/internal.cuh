@@ -121,6 +121,7 @@ struct wec_poisson {
     double *dots = nullptr;     // h1, h2 of the two Gram-Schmidt passes
     double *hess = nullptr;     // (m+1) x m Hessenberg, then cs, sn, g, y
     double *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr;
+    double *sc = nullptr;       // m+1: 1 / ||u_k|| of the unnormalised basis vectors u_k (V's columns)
     int tile64[wec::kMaxLevels] = {}, tile32[wec::kMaxLevels] = {};  // fused tile shape per level (autotuned)
     bool tuned = false;
     wec::KState *ks = nullptr;  // device

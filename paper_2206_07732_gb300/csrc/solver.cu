@@ -530,14 +530,16 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 2)
     }
 }
 
-// w = b - A x and beta = ||w||.  mode 0 (start): converged if beta <= tol.
+// u_0 = b - A x into V's column 0 (and its FP32 copy b32 for a mixed V-cycle),
+// beta = ||u_0||, scale s_0 = 1 / beta.  mode 0 (start): converged if beta <= tol.
 // mode 1 (end of a cycle): converged, out of iterations, or restart.
 // A zero right-hand side gives x = 0.  Opens a new Arnoldi cycle unless done and
 // sets the WHILE condition to !done.
 __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 2)
     k_residual_norm(int nx, int ny, const double *__restrict__ bu, const double *__restrict__ bv,
                     const double *__restrict__ d0, const double *__restrict__ b, double *x, double *__restrict__ w,
-                    double *part, KState *ks, double *g, int mode, unsigned long long hwhile, int use)
+                    float *__restrict__ b32, double *sc, double *part, KState *ks, double *g, int mode,
+                    unsigned long long hwhile, int use)
 {
     pdl_entry();
     __shared__ double sh[KT / 32];
@@ -554,6 +556,7 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 2)
         const int j = (int)(c / nx), i = (int)(c - (long long)j * nx);
         double r = b[c] - (d0[c] * x[c] - offsum_at(bu, bv, x, nx, ny, i, j));
         w[c] = r;
+        if (b32) b32[c] = (float)r;
         a += r * r;
     }
     a = block_sum(a, sh);
@@ -565,6 +568,7 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 2)
         double beta = sqrt(t);
         ks->beta = beta;
         ks->ibeta = beta != 0.0 ? 1.0 / beta : 0.0;
+        sc[0] = ks->ibeta;
         if (mode == 1) ks->ncycles += 1;
         int done;
         if (zero) {
@@ -592,23 +596,13 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 2)
     }
 }
 
-// V_0 = w / beta for a new cycle (and its FP32 copy b32 for a mixed V-cycle).
-__global__ void k_scale0(long long n, const double *__restrict__ w, double *__restrict__ V, float *__restrict__ b32,
-                         const KState *ks)
-{
-    pdl_entry();
-    if (ks->done) return;
-    const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (c >= n) return;
-    const double v = w[c] * ks->ibeta;
-    V[c] = v;
-    if (b32) b32[c] = (float)v;
-}
-
-// w = A z_j and the first Gram-Schmidt dot products h1_k = V_k . w (k <= j).
+// Arnoldi step j on the unnormalised basis u_k = ||u_k|| v_k (V's columns, scales
+// s_k = 1 / ||u_k|| in sc): the new vector w is built in place in column j+1.
+// w = A z_j = s_j A z'_j (z'_j = M u_j, the V-cycle being linear), and the
+// first Gram-Schmidt dot products h1_k = v_k . w = s_k (u_k . w), k <= j.
 __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 2)
     k_matvec_dots(int nx, int ny, const double *__restrict__ bu, const double *__restrict__ bv,
-                  const double *__restrict__ d0, const double *__restrict__ Z, const double *__restrict__ V, double *w,
+                  const double *__restrict__ d0, const double *__restrict__ Z, double *V, const double *__restrict__ sc,
                   double *part, double *h1, KState *ks)
 {
     pdl_entry();
@@ -617,20 +611,25 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 2)
     const long long n = (long long)nx * ny;
     const int j = ks->j, nk = j + 1;
     const double *z = Z + (long long)j * n;
+    double *w = V + (long long)(j + 1) * n;
+    const double sj = sc[j];
     for (long long c = blockIdx.x * (long long)KT + threadIdx.x; c < n; c += (long long)gridDim.x * KT) {
         const int jj = (int)(c / nx), i = (int)(c - (long long)jj * nx);
-        w[c] = d0[c] * z[c] - offsum_at(bu, bv, z, nx, ny, i, jj);
+        w[c] = sj * (d0[c] * z[c] - offsum_at(bu, bv, z, nx, ny, i, jj));
     }
     block_dots(V, w, n, nk, sh, bsm);
     cluster_partials(bsm, nk, part);
     if (!last_cluster(&ks->cnt[2])) return;
     final_partials(part, nk, gridDim.x / kCl, h1);
+    __syncthreads();
+    if (threadIdx.x < nk) h1[threadIdx.x] *= sc[threadIdx.x];
     if (threadIdx.x == 0) ks->cnt[2] = 0;
 }
 
-// First Gram-Schmidt update w -= sum_k h1_k V_k, then h2_k = V_k . w.
+// First Gram-Schmidt update w -= sum_k h1_k v_k = w - sum_k (h1_k s_k) u_k, then
+// h2_k = v_k . w.
 __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 2)
-    k_orth_dots(long long n, const double *__restrict__ V, double *w, const double *__restrict__ h1, double *part,
+    k_orth_dots(long long n, double *V, const double *__restrict__ sc, const double *__restrict__ h1, double *part,
                 double *h2, KState *ks)
 {
     pdl_entry();
@@ -638,7 +637,8 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 2)
     __shared__ double bsm[KMAXV];
     __shared__ double hs[KMAXV];
     const int j = ks->j, nk = j + 1;
-    if (threadIdx.x < nk) hs[threadIdx.x] = h1[threadIdx.x];
+    double *w = V + (long long)(j + 1) * n;
+    if (threadIdx.x < nk) hs[threadIdx.x] = h1[threadIdx.x] * sc[threadIdx.x];
     __syncthreads();
     for (long long c = blockIdx.x * (long long)KT + threadIdx.x; c < n; c += (long long)gridDim.x * KT) {
         double a = w[c];
@@ -650,15 +650,19 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 2)
     cluster_partials(bsm, nk, part);
     if (!last_cluster(&ks->cnt[2])) return;
     final_partials(part, nk, gridDim.x / kCl, h2);
+    __syncthreads();
+    if (threadIdx.x < nk) h2[threadIdx.x] *= sc[threadIdx.x];
     if (threadIdx.x == 0) ks->cnt[2] = 0;
 }
 
-// Second update w -= sum_k h2_k V_k and h_{j+1,j} = ||w||; the last cluster
-// applies the Givens rotations to column j, counts the iteration, decides whether
-// the cycle ends (converged estimate, iteration cap, breakdown, or full basis)
-// and sets the IF condition.
+// Second update w -= sum_k (h2_k s_k) u_k, which leaves u_{j+1} = w in column j+1
+// (and its FP32 copy b32 for the next mixed V-cycle), h_{j+1,j} = ||w||, s_{j+1} =
+// 1 / h_{j+1,j}; the last cluster applies the Givens rotations to column j,
+// counts the iteration, decides whether the cycle ends (converged estimate,
+// iteration cap, breakdown, or full basis), advances j otherwise, and sets the
+// IF condition.
 __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 2)
-    k_orth_norm(long long n, const double *__restrict__ V, double *__restrict__ w, const double *__restrict__ h1,
+    k_orth_norm(long long n, double *V, double *sc, float *__restrict__ b32, const double *__restrict__ h1,
                 const double *__restrict__ h2, double *part, KState *ks, double *H, double *cs, double *sn,
                 double *g, unsigned long long hif, int use)
 {
@@ -667,7 +671,8 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 2)
     __shared__ double bsm[1];
     __shared__ double hs[KMAXV];
     const int j = ks->j;
-    if (threadIdx.x <= j) hs[threadIdx.x] = h2[threadIdx.x];
+    double *w = V + (long long)(j + 1) * n;
+    if (threadIdx.x <= j) hs[threadIdx.x] = h2[threadIdx.x] * sc[threadIdx.x];
     __syncthreads();
     double a2 = 0.0;
     for (long long c = blockIdx.x * (long long)KT + threadIdx.x; c < n; c += (long long)gridDim.x * KT) {
@@ -675,6 +680,7 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 2)
 #pragma unroll 4
         for (int k = 0; k <= j; ++k) a -= hs[k] * V[(long long)k * n + c];
         w[c] = a;
+        if (b32) b32[c] = (float)a;
         a2 += a * a;
     }
     a2 = block_sum(a2, sh);
@@ -704,39 +710,20 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 2)
     ks->jd = j + 1;
     ks->hn = hn;
     ks->ihn = hn != 0.0 ? 1.0 / hn : 0.0;
+    sc[j + 1] = ks->ihn;
     double est = fabs(g[j + 1]);
     int ce = est <= ks->tol || ks->its >= ks->maxit || hn == 0.0 || j + 1 == m || !isfinite(est);
     if (!isfinite(est)) ks->status = WEC_ERR_NONFINITE;
     ks->cycle_end = ce;
+    if (!ce) ks->j = j + 1;  // every CTA read j at its start
     ks->cnt[2] = 0;
     set_cond(hif, use, (unsigned)ce);
 }
 
-// V_{j+1} = w / h_{j+1,j} (and its FP32 copy b32 for a mixed V-cycle), then
-// j += 1 (unless the cycle ends).
-__global__ void __launch_bounds__(KT) k_next_basis(long long n, const double *__restrict__ w, double *V,
-                                                     float *__restrict__ b32, KState *ks)
-{
-    pdl_entry();
-    const int j = ks->j;
-    if (!ks->cycle_end) {
-        double *vn = V + (long long)(j + 1) * n;
-        const double ih = ks->ihn;
-        for (long long c = blockIdx.x * (long long)KT + threadIdx.x; c < n; c += (long long)gridDim.x * KT) {
-            const double v = w[c] * ih;
-            vn[c] = v;
-            if (b32) b32[c] = (float)v;
-        }
-    }
-    if (!last_block(&ks->cnt[3])) return;
-    if (threadIdx.x == 0) {
-        if (!ks->cycle_end) ks->j = j + 1;
-        ks->cnt[3] = 0;
-    }
-}
-
+// y from the triangular system, then y_k s_k: the preconditioned vectors are
+// stored for the unnormalised basis (z'_k = z_k / s_k), so x += sum_k (y_k s_k) z'_k.
 __global__ void k_backsolve(int m, const double *__restrict__ H, const double *__restrict__ g, double *__restrict__ y,
-                            const KState *ks)
+                            const double *__restrict__ sc, const KState *ks)
 {
     pdl_entry();
     const int jd = ks->jd;
@@ -745,6 +732,7 @@ __global__ void k_backsolve(int m, const double *__restrict__ H, const double *_
         for (int l = k + 1; l < jd; ++l) s -= H[k * m + l] * y[l];
         y[k] = s / H[k * m + k];
     }
+    for (int k = 0; k < jd; ++k) y[k] *= sc[k];
 }
 
 __global__ void k_update_x(long long n, const double *__restrict__ y, const double *__restrict__ Z, double *__restrict__ x,
@@ -1110,17 +1098,14 @@ void enqueue_begin(wec_poisson *P, const double *b, double *x, double rtol, int 
         WEC_PROF("krylov_norm", -1, 8.0 * n, st);
         launch_k(k_bnorm, G, KT, 0, st, n, b, P->part, P->ks);
     }
-    {
-        WEC_PROF("krylov_residual", -1, 8.0 * (4.0 * n + nf), st);
-        launch_k(k_residual_norm, G, KT, 0, st, P->nx, P->ny, P->L64[0].bu, P->L64[0].bv, P->d0, b, x, P->w, P->part,
-                                          P->ks, P->g, 0, hw, use);
-    }
-    WEC_PROF("krylov_scale", -1, (16.0 + (b32 ? 4.0 : 0.0)) * n, st);
-    launch_k(k_scale0, nblk(n, 256), 256, 0, st, n, P->w, P->V, b32, P->ks);
+    WEC_PROF("krylov_residual", -1, 8.0 * (4.0 * n + nf) + (b32 ? 4.0 * n : 0.0), st);
+    launch_k(k_residual_norm, G, KT, 0, st, P->nx, P->ny, P->L64[0].bu, P->L64[0].bv, P->d0, b, x, P->V, b32, P->sc,
+             P->part, P->ks, P->g, 0, hw, use);
 }
 
-// One Arnoldi step j (preconditioner, matvec, CGS2, Givens, next basis vector).
-// Algorithmic bytes of the Krylov kernels are counted at the largest j (m - 1).
+// One Arnoldi step j (preconditioner, matvec, CGS2 in place in V's column j+1,
+// Givens).  Algorithmic bytes of the Krylov kernels are counted at the largest
+// j (m - 1).
 void enqueue_body(wec_poisson *P, unsigned long long hif, int use, cudaStream_t st)
 {
     const long long n = (long long)P->nx * P->ny;
@@ -1128,26 +1113,23 @@ void enqueue_body(wec_poisson *P, unsigned long long hif, int use, cudaStream_t 
     const int G = kgrid(n), m = P->restart;
     const bool mixed = P->prec == WEC_PREC_MIXED;
     double *h1 = P->dots, *h2 = P->dots + (kMaxRestart + 2);
-    // the mixed V-cycle reads b = V_j in FP32, written beside V_j by k_scale0 / k_next_basis
+    // the mixed V-cycle reads u_j in FP32, written beside it by k_residual_norm / k_orth_norm
     if (!mixed)
         vcycle_t<double, double>(P, P->L64, P->V, P->Z, &P->ks->j, &P->ks->j, st);
     else
         vcycle_t<float, double>(P, P->L32, P->L32[0].b, P->Z, nullptr, &P->ks->j, st);
     {
         WEC_PROF("krylov_matvec_dots", -1, 8.0 * (3.0 * n + nf) + 8.0 * n * m, st);
-        launch_k(k_matvec_dots, G, KT, 0, st, P->nx, P->ny, P->L64[0].bu, P->L64[0].bv, P->d0, P->Z, P->V, P->w, P->part,
-                                        h1, P->ks);
+        launch_k(k_matvec_dots, G, KT, 0, st, P->nx, P->ny, P->L64[0].bu, P->L64[0].bv, P->d0, P->Z, P->V, P->sc,
+                 P->part, h1, P->ks);
     }
     {
         WEC_PROF("krylov_orth_dots", -1, 8.0 * n * (m + 2), st);
-        launch_k(k_orth_dots, G, KT, 0, st, n, P->V, P->w, h1, P->part, h2, P->ks);
+        launch_k(k_orth_dots, G, KT, 0, st, n, P->V, P->sc, h1, P->part, h2, P->ks);
     }
-    {
-        WEC_PROF("krylov_orth_norm", -1, 8.0 * n * (m + 2), st);
-        launch_k(k_orth_norm, G, KT, 0, st, n, P->V, P->w, h1, h2, P->part, P->ks, P->hess, P->cs, P->sn, P->g, hif, use);
-    }
-    WEC_PROF("krylov_next_basis", -1, (16.0 + (mixed ? 4.0 : 0.0)) * n, st);
-    launch_k(k_next_basis, nblk(n, KT), KT, 0, st, n, P->w, P->V, mixed ? P->L32[0].b : nullptr, P->ks);
+    WEC_PROF("krylov_orth_norm", -1, 8.0 * n * (m + 2) + (mixed ? 4.0 * n : 0.0), st);
+    launch_k(k_orth_norm, G, KT, 0, st, n, P->V, P->sc, mixed ? P->L32[0].b : nullptr, h1, h2, P->part, P->ks,
+             P->hess, P->cs, P->sn, P->g, hif, use);
 }
 
 // End of a cycle: y from the triangular system, x += Z y, true residual, then
@@ -1160,19 +1142,15 @@ void enqueue_close(wec_poisson *P, const double *b, double *x, unsigned long lon
     const bool mixed = P->prec == WEC_PREC_MIXED;
     {
         WEC_PROF("scalar", -1, 8.0 * m * m, st);
-        launch_k(k_backsolve, 1, 1, 0, st, m, P->hess, P->g, P->y, P->ks);
+        launch_k(k_backsolve, 1, 1, 0, st, m, P->hess, P->g, P->y, P->sc, P->ks);
     }
     {
         WEC_PROF("krylov_update_x", -1, 16.0 * n + 8.0 * n * m, st);
         launch_k(k_update_x, nblk(n, 256), 256, 0, st, n, P->y, P->Z, x, P->ks);
     }
-    {
-        WEC_PROF("krylov_residual", -1, 8.0 * (4.0 * n + nf), st);
-        launch_k(k_residual_norm, G, KT, 0, st, P->nx, P->ny, P->L64[0].bu, P->L64[0].bv, P->d0, b, x, P->w, P->part,
-                                          P->ks, P->g, 1, hw, use);
-    }
-    WEC_PROF("krylov_scale", -1, (16.0 + (mixed ? 4.0 : 0.0)) * n, st);
-    launch_k(k_scale0, nblk(n, 256), 256, 0, st, n, P->w, P->V, mixed ? P->L32[0].b : nullptr, P->ks);
+    WEC_PROF("krylov_residual", -1, 8.0 * (4.0 * n + nf) + (mixed ? 4.0 * n : 0.0), st);
+    launch_k(k_residual_norm, G, KT, 0, st, P->nx, P->ny, P->L64[0].bu, P->L64[0].bv, P->d0, b, x, P->V,
+             mixed ? P->L32[0].b : nullptr, P->sc, P->part, P->ks, P->g, 1, hw, use);
 }
 
 int read_state(wec_poisson *P, cudaStream_t st)
@@ -1270,16 +1248,17 @@ int poisson_init(wec_poisson *P, int nx, int ny, int prec, int restart, int nu1,
     WEC_CK(cudaMalloc(&P->Z, m * n * 8));
     WEC_CK(cudaMalloc(&P->w, n * 8));
     WEC_CK(cudaMalloc(&P->d0, n * 8));
-    // reduction partials: one per cluster and quantity (k_next_basis counts blocks only)
+    // reduction partials: one per cluster and quantity
     WEC_CK(cudaMalloc(&P->part, (size_t)(kMaxRestart + 2) * (kKrylovBlocks / kCl) * 8));
     WEC_CK(cudaMalloc(&P->dots, 2 * (kMaxRestart + 2) * 8));
-    size_t nh = (size_t)(m + 1) * m + 3 * (m + 1) + m + 8;
+    size_t nh = (size_t)(m + 1) * m + 3 * (m + 1) + m + 8 + (m + 1);
     WEC_CK(cudaMalloc(&P->hess, nh * 8));
     WEC_CK(cudaMemset(P->hess, 0, nh * 8));
     P->cs = P->hess + (m + 1) * m;
     P->sn = P->cs + (m + 1);
     P->g = P->sn + (m + 1);
     P->y = P->g + (m + 1);
+    P->sc = P->y + m + 8;
     WEC_CK(cudaMalloc(&P->ks, sizeof(KState)));
     WEC_CK(cudaMemset(P->ks, 0, sizeof(KState)));
     WEC_CK(cudaMallocHost(&P->ksh, sizeof(KState)));
