@@ -286,14 +286,22 @@ int wec_jonswap(double Hs, double Tp, double gamma, int ncomp, double *amp, doub
  * pass, restriction and prolongation.  Both compute the same values up to
  * rounding.  "mg_autotune" (default 1): when a solver is created, time the fused
  * kernels' tile shapes (64x16, 32x16, 32x8, 16x8) on each level and keep the
- * fastest; 0 uses 64x16 everywhere.  Options apply to solvers created, graphs
- * captured and solves started after the call.  Unknown name: WEC_ERR_INVALID. */
+ * fastest, then time whole V-cycles with the single-CTA kernel starting at the
+ * smallest admissible level or one or two levels coarser and keep the fastest;
+ * 0 uses 64x16 everywhere and the smallest admissible level.  Tuning results
+ * are kept per (grid, precision, mg_pre, mg_post) for the life of the process:
+ * later solvers of the same shape reuse them and compute the same bits.
+ * "mg_bottom_shift" (default -1 = autotuned): start the single-CTA kernel this
+ * many levels below the smallest admissible one (0..8, capped at the coarsest).
+ * Options apply to solvers created, graphs captured and solves started after the
+ * call.  Unknown name or value out of range: WEC_ERR_INVALID. */
 int wec_set_option(const char *name, int value);
 
 /* Fused multigrid tile shape (interior cells) per level of the tank's solver, as
  * chosen by the autotuner when the tank was created ("mg_autotune" option; the
- * coarsest level's entry is meaningless).  *nlev receives the number of levels;
- * at most max entries are written. */
+ * coarsest level's entry is meaningless; 0 x 0 marks a level run inside the
+ * single-CTA kernel).  *nlev receives the number of levels; at most max entries
+ * are written. */
 int wec_tank_mg_tiles(const wec_tank *tank, int *tile_x, int *tile_y, int max, int *nlev);
 
 /* ---- launch accounting and profiling ------------------------------------ */

@@ -124,6 +124,8 @@ struct wec_poisson {
     double *sc = nullptr;       // m+1: 1 / ||u_k|| of the unnormalised basis vectors u_k (V's columns)
     int tile64[wec::kMaxLevels] = {}, tile32[wec::kMaxLevels] = {};  // fused tile shape per level (autotuned)
     bool tuned = false;
+    int bottom_shift = 0;       // bottom kernel starts this many levels below the smallest admissible one (autotuned)
+    int bottom_level = -1;      // the level the bottom kernel starts at (set by the last fused V-cycle)
     wec::KState *ks = nullptr;  // device
     wec::KState *ksh = nullptr; // pinned host mirror
     size_t bytes = 0;
@@ -151,6 +153,7 @@ int solve_result(wec_poisson *P, int *iters, double *relres);
 int poisson_apply(wec_poisson *P, const double *x, double *y);
 void set_mg_fused(bool on);
 void set_mg_autotune(bool on);
+void set_mg_bottom_shift(int shift);  // -1: autotune
 void poisson_tiles(const wec_poisson *P, int *tx, int *ty, int max);
 int poisson_vcycle(wec_poisson *P, const double *b, double *x);
 

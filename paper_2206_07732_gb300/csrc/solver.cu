@@ -15,6 +15,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include <cooperative_groups.h>
 
@@ -913,7 +916,9 @@ void vcycle_fused(wec_poisson *P, Level<T> *L, const T *b0, TO *x0, const int *b
     while (lb < P->nlev - 1 &&
            ((long long)L[lb].nx * L[lb].ny > kBottomCells || bottom_elems(B, lb) * (long long)sizeof(T) > kBottomSmemMax))
         ++lb;
+    lb = std::min(lb + P->bottom_shift, P->nlev - 1);  // autotuned: coarser levels may run faster in one CTA
     B.lb = lb;
+    P->bottom_level = lb;
     for (int l = 0; l < lb; ++l) {
         Level<T> &A = L[l];
         const double n = (double)A.nx * A.ny, nf = (double)(A.nx + 1) * A.ny + (double)A.nx * (A.ny + 1);
@@ -940,7 +945,8 @@ void vcycle_fused(wec_poisson *P, Level<T> *L, const T *b0, TO *x0, const int *b
     }
 }
 
-bool g_mg_autotune = true;  // wec_set_option "mg_autotune"
+bool g_mg_autotune = true;     // wec_set_option "mg_autotune"
+int g_mg_bottom_shift = -1;    // wec_set_option "mg_bottom_shift" (-1: autotune)
 
 // Autotuner of the fused level kernels: on each non-coarsest level, time the
 // pre + post pair of every tile shape (3 runs each, CUDA events on the solver's
@@ -990,6 +996,47 @@ int autotune_levels(wec_poisson *P, Level<T> *L, int *tiles, cudaStream_t st)
     return rc;
 }
 
+// Where the single-CTA bottom starts: time whole fused V-cycles with the bottom
+// at the smallest admissible level and up to two levels coarser (tiled kernels
+// above it), keep the fastest.  Runs after the tile shapes are tuned.
+template <typename T>
+int autotune_bottom(wec_poisson *P, Level<T> *L, cudaStream_t st)
+{
+    cudaEvent_t e0, e1;
+    WEC_CK(cudaEventCreate(&e0));
+    WEC_CK(cudaEventCreate(&e1));
+    // level-0 stand-ins in V (at least 2 n doubles; overwritten at the start of every solve)
+    const long long n0 = (long long)L[0].nx * L[0].ny;
+    T *b = (T *)P->V, *x = (T *)P->V + n0;
+    float best = 1e30f;
+    int best_shift = 0;
+    for (int shift = 0; shift <= 2; ++shift) {
+        P->bottom_shift = shift;
+        vcycle_fused<T, T>(P, L, b, x, nullptr, nullptr, st);  // sets bottom_level
+        if (shift > 0 && P->bottom_level >= P->nlev - 1) break;
+        float tmin = 1e30f;
+        for (int r = 0; r < 4; ++r) {
+            cudaEventRecord(e0, st);
+            vcycle_fused<T, T>(P, L, b, x, nullptr, nullptr, st);
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) break;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            tmin = std::min(tmin, ms);
+        }
+        if (tmin < best) {
+            best = tmin;
+            best_shift = shift;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    P->bottom_shift = best_shift;
+    vcycle_fused<T, T>(P, L, b, x, nullptr, nullptr, st);  // records the chosen bottom level
+    const cudaError_t ce = cudaGetLastError();
+    return ce == cudaSuccess ? WEC_OK : cuda_fail(ce, "autotune_bottom");
+}
+
 template <typename T>
 __global__ void k_fill(long long n, T *a, T v)
 {
@@ -998,10 +1045,33 @@ __global__ void k_fill(long long n, T *a, T v)
     if (c < n) a[c] = v;
 }
 
+// Tuning results per (nx, ny, precision, nu1, nu2), shared by every solver of
+// the process: the first solver of a shape times the candidates, later ones
+// reuse its choices, so equal tanks run the same kernels and give the same bits
+// (the bottom split changes rounding; timings alone would not repeat).
+struct TuneResult {
+    int tile[kMaxLevels];
+    int bottom_shift, bottom_level;
+};
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int, int>, TuneResult> g_tune_cache;
+
 int poisson_autotune(wec_poisson *P, cudaStream_t st)
 {
     for (int l = 0; l < kMaxLevels; ++l) P->tile64[l] = P->tile32[l] = 0;
+    P->bottom_shift = g_mg_bottom_shift > 0 ? g_mg_bottom_shift : 0;
     if (!g_mg_autotune || P->nlev < 2) return WEC_OK;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    const auto key = std::make_tuple(P->nx, P->ny, P->prec, P->nu1, P->nu2);
+    int *tiles = P->prec == WEC_PREC_FP64 ? P->tile64 : P->tile32;
+    auto hit = g_tune_cache.find(key);
+    if (hit != g_tune_cache.end()) {
+        for (int l = 0; l < kMaxLevels; ++l) tiles[l] = hit->second.tile[l];
+        P->bottom_shift = g_mg_bottom_shift >= 0 ? g_mg_bottom_shift : hit->second.bottom_shift;
+        P->bottom_level = g_mg_bottom_shift >= 0 ? -1 : hit->second.bottom_level;
+        P->tuned = true;
+        return WEC_OK;
+    }
     // placeholder coefficients (the real ones are set before every solve)
     for (int l = 0; l < P->nlev; ++l) {
         long long nu = (long long)(P->L64[l].nx + 1) * P->L64[l].ny, nv = (long long)P->L64[l].nx * (P->L64[l].ny + 1);
@@ -1012,9 +1082,24 @@ int poisson_autotune(wec_poisson *P, cudaStream_t st)
             launch_k(k_fill<float>, nblk(nv, 256), 256, 0, st, nv, P->L32[l].bv, 1.0f);
         }
     }
+    // the placeholder operator's hierarchy, diagonals and coarsest factors, so the
+    // trial V-cycles run on finite values
+    if (int e = poisson_build(P, st)) return e;
     int e = P->prec == WEC_PREC_FP64 ? autotune_levels<double>(P, P->L64, P->tile64, st)
                                      : autotune_levels<float>(P, P->L32, P->tile32, st);
+    if (!e && g_mg_bottom_shift < 0)
+        e = P->prec == WEC_PREC_FP64 ? autotune_bottom<double>(P, P->L64, st) : autotune_bottom<float>(P, P->L32, st);
     if (e) return e;
+    if (g_mg_bottom_shift < 0) {  // a forced split is not a tuning result
+        TuneResult r;
+        for (int l = 0; l < kMaxLevels; ++l) r.tile[l] = tiles[l];
+        r.bottom_shift = P->bottom_shift;
+        r.bottom_level = P->bottom_level;
+        g_tune_cache[key] = r;
+    } else {
+        P->bottom_shift = g_mg_bottom_shift;
+    }
+    P->have_coef = false;  // the real operator must still be set
     P->tuned = true;
     WEC_CK(cudaStreamSynchronize(st));
     return WEC_OK;
@@ -1164,13 +1249,15 @@ int read_state(wec_poisson *P, cudaStream_t st)
 
 void set_mg_fused(bool on) { g_mg_fused = on; }
 void set_mg_autotune(bool on) { g_mg_autotune = on; }
+void set_mg_bottom_shift(int shift) { g_mg_bottom_shift = shift; }
 
 void poisson_tiles(const wec_poisson *P, int *tx, int *ty, int max)
 {
     const int *t = P->prec == WEC_PREC_FP64 ? P->tile64 : P->tile32;
     for (int l = 0; l < max && l < P->nlev; ++l) {
-        tx[l] = kTileX[t[l]];
-        ty[l] = kTileY[t[l]];
+        const bool tiled = P->bottom_level < 0 || l < P->bottom_level;  // 0 x 0: run by the bottom kernel
+        tx[l] = tiled ? kTileX[t[l]] : 0;
+        ty[l] = tiled ? kTileY[t[l]] : 0;
     }
 }
 

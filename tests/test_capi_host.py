@@ -126,3 +126,11 @@ def test_batch_create_rejects_invalid_arguments_on_host(lib, bad):
     assert not h.value
     msg = lib.wec_last_error().decode()
     assert ("tank 1" in msg) if bad == "tank" else ("batch" in msg)
+
+
+def test_options_are_validated_on_host(lib):
+    assert lib.wec_set_option(b"mg_bottom_shift", 9) == wec.WEC_ERR_INVALID
+    assert lib.wec_set_option(b"mg_bottom_shift", -2) == wec.WEC_ERR_INVALID
+    assert lib.wec_set_option(b"no_such_option", 1) == wec.WEC_ERR_INVALID
+    assert lib.wec_set_option(b"mg_bottom_shift", 1) == wec.WEC_OK
+    assert lib.wec_set_option(b"mg_bottom_shift", -1) == wec.WEC_OK

@@ -80,6 +80,31 @@ def test_fgmres_solution_matches_oracle(nx, ny, contrast, rtol):
     assert rel(x.cpu().numpy(), xo) < 1e3 * rtol
 
 
+@pytest.mark.parametrize("shift", [0, 1, 2])
+@pytest.mark.parametrize("prec", [wec.PREC_FP64, wec.PREC_MIXED])
+def test_bottom_split_levels_agree(shift, prec):
+    # the single-CTA kernel may start at the smallest admissible level or
+    # coarser (autotuned); every split computes the same V-cycle up to rounding
+    nx, ny = 512, 128
+    bu, bv = synth.random_coefficients(nx, ny, seed=5, contrast=1e3)
+    b = np.random.default_rng(8).standard_normal((ny, nx))
+    out = []
+    try:
+        for fused, sh in ((0, -1), (1, shift)):
+            wec.set_option("mg_fused", fused)
+            wec.set_option("mg_bottom_shift", sh)
+            P = wec.Poisson(nx, ny, precision=prec)
+            P.set_coefficients(cuda(bu), cuda(bv))
+            z = torch.zeros(ny, nx, dtype=torch.float64, device="cuda")
+            P.vcycle(cuda(b), z)
+            out.append(z.cpu().numpy())
+    finally:
+        wec.set_option("mg_fused", 1)
+        wec.set_option("mg_bottom_shift", -1)
+    tol = 1e-12 if prec == wec.PREC_FP64 else 1e-5
+    assert rel(out[1], out[0]) < tol
+
+
 @pytest.mark.parametrize("nx,ny", [(96, 40), (256, 128), (288, 80), (1024, 256)])
 @pytest.mark.parametrize("prec", [wec.PREC_FP64, wec.PREC_MIXED])
 def test_fused_vcycle_matches_unfused(nx, ny, prec):
