@@ -195,41 +195,51 @@ template <typename T>
 __global__ void k_lu_factor(int nx, int ny, const T *__restrict__ bu, const T *__restrict__ bv, T *A, T *inv)
 {
     pdl_entry();
-    int n = nx * ny;
-    for (long long q = threadIdx.x; q < (long long)n * n; q += blockDim.x) A[q] = T(0);
+    // small systems (n <= 64) are built, factored and inverted in shared memory
+    constexpr int kSmallN = 64;
+    __shared__ T Ms[kSmallN * kSmallN];
+    __shared__ T Is[kInvMax * kInvMax];
+    const int n = nx * ny;
+    const bool small = n <= kSmallN;
+    T *M = small ? Ms : A;
+    for (long long q = threadIdx.x; q < (long long)n * n; q += blockDim.x) M[q] = T(0);
     __syncthreads();
     for (int r = threadIdx.x; r < n; r += blockDim.x) {
         int i = r % nx, j = r / nx;
-        A[(long long)r * n + r] = diag_at(bu, bv, nx, ny, i, j);
-        if (i > 0) A[(long long)r * n + r - 1] = -bu[j * (nx + 1) + i];
-        if (i < nx - 1) A[(long long)r * n + r + 1] = -bu[j * (nx + 1) + i + 1];
-        if (j > 0) A[(long long)r * n + r - nx] = -bv[j * nx + i];
-        if (j < ny - 1) A[(long long)r * n + r + nx] = -bv[(j + 1) * nx + i];
+        M[(long long)r * n + r] = diag_at(bu, bv, nx, ny, i, j);
+        if (i > 0) M[(long long)r * n + r - 1] = -bu[j * (nx + 1) + i];
+        if (i < nx - 1) M[(long long)r * n + r + 1] = -bu[j * (nx + 1) + i + 1];
+        if (j > 0) M[(long long)r * n + r - nx] = -bv[j * nx + i];
+        if (j < ny - 1) M[(long long)r * n + r + nx] = -bv[(j + 1) * nx + i];
     }
     __syncthreads();
     for (int k = 0; k < n; ++k) {
-        T piv = A[(long long)k * n + k];
+        T piv = M[(long long)k * n + k];
         for (int r = k + 1 + threadIdx.x; r < n; r += blockDim.x) {
-            T f = A[(long long)r * n + k] / piv;
-            A[(long long)r * n + k] = f;
-            for (int c = k + 1; c < n; ++c) A[(long long)r * n + c] -= f * A[(long long)k * n + c];
+            T f = M[(long long)r * n + k] / piv;
+            M[(long long)r * n + k] = f;
+            for (int c = k + 1; c < n; ++c) M[(long long)r * n + c] -= f * M[(long long)k * n + c];
         }
         __syncthreads();
     }
-    if (!inv) return;
+    if (small)
+        for (int q = threadIdx.x; q < n * n; q += blockDim.x) A[q] = M[q];
+    if (!inv) return;  // inv is given only for n <= kInvMax
     const int t = threadIdx.x;
     if (t < n) {
-        for (int r = 0; r < n; ++r) {  // L y = e_t (unit lower), y in column t of inv
+        for (int r = 0; r < n; ++r) {  // L y = e_t (unit lower), y in column t of Is
             T s = r == t ? T(1) : T(0);
-            for (int c = 0; c < r; ++c) s -= A[(long long)r * n + c] * inv[(long long)c * n + t];
-            inv[(long long)r * n + t] = s;
+            for (int c = 0; c < r; ++c) s -= M[(long long)r * n + c] * Is[c * n + t];
+            Is[r * n + t] = s;
         }
         for (int r = n - 1; r >= 0; --r) {  // U x = y
-            T s = inv[(long long)r * n + t];
-            for (int c = r + 1; c < n; ++c) s -= A[(long long)r * n + c] * inv[(long long)c * n + t];
-            inv[(long long)r * n + t] = s / A[(long long)r * n + r];
+            T s = Is[r * n + t];
+            for (int c = r + 1; c < n; ++c) s -= M[(long long)r * n + c] * Is[c * n + t];
+            Is[r * n + t] = s / M[(long long)r * n + r];
         }
     }
+    __syncthreads();
+    for (int q = threadIdx.x; q < n * n; q += blockDim.x) inv[q] = Is[q];
 }
 
 // 1/d of every cell of levels 0..nlev-1 (one launch; thread per cell of the
