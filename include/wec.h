@@ -192,6 +192,35 @@ int wec_batch_step_n(wec_batch *batch, int nsteps, const double *dt, const doubl
                      wec_step_result *out);
 void wec_batch_destroy(wec_batch *batch);
 
+/* ------------------------------------------------- static-grid NLFK force --
+ * Non-linear Froude-Krylov force (paper: section "Non-linear Froude-Krylov
+ * (NLFK) forces: A novel static grid approach based on implicit surfaces", Eqs.
+ * p_dynamic and NLFK_p), independent of any tank.  A static region R of nx x ny
+ * square cells of size h, lower-left corner (x0, y0), covers the body and the
+ * wave surface's excursion.  Per cell the incident surface sigma = y - (depth +
+ * eta(x, t)) marks water (sigma <= 0); the box body (wec_body: xc, width, height;
+ * centre height yc given per call) marks the body by its SDF psi.  mode 0: the
+ * incident-wave pressure of Eq. p_dynamic, summed over the wave components
+ * (wave numbers from the dispersion relation at this depth); mode 1: the
+ * hydrostatic pressure -rho_w g (y - depth) (the nonlinear-buoyancy variant).
+ * Both are zero where sigma > 0.  The force sums -p_f n_f h over the faces whose
+ * two cells have opposite psi sign (p_f interpolated to psi = 0 with |psi|
+ * weights, n_f out of the body): *fy heave, *fx surge, per unit span.
+ * wec_nlfk_create copies the waves (amp, omega, phase; host) and validates all
+ * arguments (WEC_ERR_INVALID); wec_nlfk_force is host-synchronous on the
+ * object's stream; results are reproducible bit for bit. */
+typedef struct {
+    double x0, y0, h;
+    int nx, ny;
+} wec_region;
+
+typedef struct wec_nlfk wec_nlfk;
+
+int wec_nlfk_create(const wec_region *region, const wec_fluids *fluids, double depth, const wec_waves *waves,
+                    const wec_body *body, void *cuda_stream, wec_nlfk **out);
+int wec_nlfk_force(wec_nlfk *nlfk, double t, double yc, int mode, double *fx, double *fy);
+void wec_nlfk_destroy(wec_nlfk *nlfk);
+
 /* Execution mode.  enable = 1 (default): the whole step -- including the
  * pressure solve's iteration, steered on the GPU by conditional WHILE / IF graph
  * nodes -- runs as one CUDA graph, captured at the first step and replayed.

@@ -42,6 +42,13 @@ class Result(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class NlfkParams(C.Structure):
+    _fields_ = [("x0", C.c_double), ("y0", C.c_double), ("h", C.c_double), ("nx", C.c_int), ("ny", C.c_int),
+                ("depth", C.c_double), ("rho_w", C.c_double), ("g", C.c_double), ("ncomp", C.c_int),
+                ("amp", _dp), ("omega", _dp), ("kwave", _dp), ("phase", _dp),
+                ("body_xc", C.c_double), ("body_w", C.c_double), ("body_h", C.c_double)]
+
+
 def lib():
     global _lib
     if _lib is None:
@@ -69,6 +76,7 @@ def lib():
                                            C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int),
                                            C.POINTER(C.c_double)]
         L.oracle_vcycle.argtypes = [C.c_int, C.c_int, _dp, _dp, C.c_int, C.c_int, _dp, _dp]
+        L.oracle_nlfk.argtypes = [C.POINTER(NlfkParams), C.c_double, C.c_double, C.c_int, _dp, _dp]
         _lib = L
     return _lib
 
@@ -213,3 +221,15 @@ def vcycle(bu, bv, b, nu1=2, nu2=2):
     x = np.zeros_like(b)
     nl = lib().oracle_vcycle(nx, ny, _ptr(bu), _ptr(bv), nu1, nu2, _ptr(b), _ptr(x))
     return x, nl
+
+
+def nlfk(region, depth, rho_w, g, amp, omega, kwave, phase, body, t, yc, mode):
+    """Static-grid NLFK force (fx, fy) per unit span (oracle_nlfk).
+    region = (x0, y0, h, nx, ny); body = (xc, width, height); mode 0: incident
+    wave pressure, 1: hydrostatic (nonlinear buoyancy)."""
+    arrs = [_f64(np.atleast_1d(np.asarray(a, dtype=np.float64))) for a in (amp, omega, kwave, phase)]
+    x0, y0, h, nx, ny = region
+    P = NlfkParams(x0, y0, h, nx, ny, depth, rho_w, g, len(arrs[0]), *[_ptr(a) for a in arrs], *body)
+    fx, fy = C.c_double(0), C.c_double(0)
+    lib().oracle_nlfk(C.byref(P), t, yc, mode, C.byref(fx), C.byref(fy))
+    return fx.value, fy.value

@@ -35,4 +35,20 @@ enum {
     OF_RHOB_U = 10, OF_RHOB_V = 11
 };
 
+/* Static-grid NLFK force: region R of nx x ny cells of size h with lower-left
+ * corner (x0, y0); waves (ncomp components, wave numbers given); box body of
+ * width body_w, height body_h centred at x = body_xc (y centre per call).
+ * oracle_nlfk: mode 0 incident-wave pressure, 1 hydrostatic; heave force *fy,
+ * surge force *fx (per unit span). */
+typedef struct {
+    double x0, y0, h;
+    int nx, ny;
+    double depth, rho_w, g;
+    int ncomp;
+    const double *amp, *omega, *kwave, *phase;
+    double body_xc, body_w, body_h;
+} oracle_nlfk_params;
+
+int oracle_nlfk(const oracle_nlfk_params *P, double t, double yc, int mode, double *fx, double *fy);
+
 #endif

@@ -36,6 +36,10 @@ class Waves(C.Structure):
                 ("damp_x0", C.c_double), ("damp_len", C.c_double), ("probe_x", C.c_double)]
 
 
+class Region(C.Structure):
+    _fields_ = [("x0", C.c_double), ("y0", C.c_double), ("h", C.c_double), ("nx", C.c_int), ("ny", C.c_int)]
+
+
 class Body(C.Structure):
     _fields_ = [("present", C.c_int)] + [(k, C.c_double) for k in
                                          ("xc", "yc", "width", "height", "mass", "added_mass", "kappa_p",
@@ -90,6 +94,11 @@ def load():
     L.wec_batch_step_n.argtypes = [vp, C.c_int, _dp, _dp, C.POINTER(StepResult)]
     L.wec_batch_destroy.argtypes = [vp]
     L.wec_batch_destroy.restype = None
+    L.wec_nlfk_create.argtypes = [C.POINTER(Region), C.POINTER(Fluids), C.c_double, C.POINTER(Waves), C.POINTER(Body),
+                                  vp, C.POINTER(vp)]
+    L.wec_nlfk_force.argtypes = [vp, C.c_double, C.c_double, C.c_int, _dp, _dp]
+    L.wec_nlfk_destroy.argtypes = [vp]
+    L.wec_nlfk_destroy.restype = None
     L.wec_pressure_solve.argtypes = [vp, vp, vp, C.c_double, C.POINTER(C.c_int), _dp]
     L.wec_tank_use_graph.argtypes = [vp, C.c_int]
     L.wec_set_option.argtypes = [C.c_char_p, C.c_int]
@@ -319,6 +328,36 @@ def profile_read():
         nm = names.raw[k * stride:(k + 1) * stride].split(b"\0")[0].decode()
         out.append(dict(name=nm, level=lv[k], launches=la[k], ms=ms[k], bytes=by[k]))
     return out
+
+
+class Nlfk:
+    """Static-grid non-linear Froude-Krylov force (wec_nlfk_create ... destroy).
+    region = (x0, y0, h, nx, ny); body = dict(xc, width, height); waves: arrays
+    (amp, omega, phase).  force(t, yc, mode) -> (fx, fy) per unit span; mode 0
+    incident-wave pressure, 1 hydrostatic (nonlinear buoyancy)."""
+
+    def __init__(self, region, depth, amp, omega, phase, body, rho_w=1025.0, g=9.81, stream=None):
+        self._w = [np.ascontiguousarray(np.atleast_1d(a), dtype=np.float64) for a in (amp, omega, phase)]
+        w = Waves(len(self._w[0]), _ptr(self._w[0]), _ptr(self._w[1]), _ptr(self._w[2]), 0.0, 0.0, 0.0)
+        f = Fluids(rho_w, 1.225, 1e-3, 1.8e-5, g)
+        bd = Body(1, body["xc"], 0.0, body["width"], body["height"], 1.0, 0.0, 1e-8, 0.0)
+        R = Region(*region)
+        h = C.c_void_p()
+        _check(load().wec_nlfk_create(C.byref(R), C.byref(f), depth, C.byref(w), C.byref(bd), _stream(stream),
+                                      C.byref(h)))
+        self.h = h
+
+    def force(self, t, yc, mode=0):
+        fx, fy = C.c_double(0), C.c_double(0)
+        _check(load().wec_nlfk_force(self.h, t, yc, mode, C.byref(fx), C.byref(fy)))
+        return fx.value, fy.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().wec_nlfk_destroy(self.h)
+            self.h = None
+
+    __del__ = close
 
 
 class Batch:

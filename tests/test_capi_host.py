@@ -134,3 +134,26 @@ def test_options_are_validated_on_host(lib):
     assert lib.wec_set_option(b"no_such_option", 1) == wec.WEC_ERR_INVALID
     assert lib.wec_set_option(b"mg_bottom_shift", 1) == wec.WEC_OK
     assert lib.wec_set_option(b"mg_bottom_shift", -1) == wec.WEC_OK
+
+
+@pytest.mark.parametrize("bad", ["region", "depth", "body", "omega"])
+def test_nlfk_create_validates_on_host(lib, bad):
+    R = wec.Region(0.0, 0.0, 0.01, 100, 50)
+    f = wec.Fluids(1025.0, 1.225, 1e-3, 1.8e-5, 9.81)
+    amp, om, ph = np.array([0.01]), np.array([5.0]), np.array([0.0])
+    w = wec.Waves(1, wec._ptr(amp), wec._ptr(om), wec._ptr(ph), 0.0, 0.0, 0.0)
+    b = wec.Body(1, 0.5, 0.25, 0.2, 0.1, 1.0, 0.0, 1e-8, 0.0)
+    depth = 0.3
+    if bad == "region":
+        R.h = 0.0
+    elif bad == "depth":
+        depth = -1.0
+    elif bad == "body":
+        b.present = 0
+    elif bad == "omega":
+        om[0] = 0.0
+    h = C.c_void_p(123)
+    assert lib.wec_nlfk_create(C.byref(R), C.byref(f), depth, C.byref(w), C.byref(b), None, C.byref(h)) == \
+        wec.WEC_ERR_INVALID
+    assert not h.value
+    assert b"nlfk" in lib.wec_last_error()
