@@ -162,3 +162,18 @@ def random_coefficients(nx, ny, seed, contrast=1.0):
     bu[:, nx] = 0.0
     bv[0, :] = 0.0
     return bu, bv
+
+
+def unet_weights(shapes, seed):
+    """Seeded He-normal weights for a list of parameter shapes (weights, then
+    biases, layer by layer); biases start at zero.  Returns one flat FP32
+    vector.  A weight tensor's fan-in is the product of all but its last axis."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for s in shapes:
+        if len(s) == 1:
+            parts.append(np.zeros(s, dtype=np.float32))
+        else:
+            fan_in = int(np.prod(s[:-1]))
+            parts.append((rng.standard_normal(s) * math.sqrt(2.0 / fan_in)).astype(np.float32))
+    return np.concatenate([p.ravel() for p in parts])
