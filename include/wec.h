@@ -221,6 +221,73 @@ int wec_nlfk_create(const wec_region *region, const wec_fluids *fluids, double d
 int wec_nlfk_force(wec_nlfk *nlfk, double t, double yc, int mode, double *fx, double *fy);
 void wec_nlfk_destroy(wec_nlfk *nlfk);
 
+/* ------------------------------------------------- learned warm start -----
+ * A convolutional U-Net, trained on the pressure problems the tank itself
+ * solves, predicts a step's pressure increment phi (the solution of the
+ * incremental projection's A phi = b) from b and the face coefficients beta; the
+ * prediction is the solver's initial guess, checked by its FP64 residual.
+ *
+ * Network (BF16 tensors and weights on the tensor cores, FP32 accumulation,
+ * FP32 master weights): two 3x3 convolutions per level with 32, 64, 128 and 256
+ * channels; a 2x2 stride-2 convolution down; nearest upsampling by 2 followed by
+ * a 3x3 convolution up; the level's skip tensor concatenated after the
+ * upsampled one; ReLU after every convolution; no normalisation layers; a 1x1
+ * FP32 head.  Tensors are NHWC: N images of H rows (y) by W columns (x).
+ * Parameters (FP32, wec_net_param_count() of them), layer by layer: enc0a
+ * (2->32), enc0b, down0 (32->64), enc1a, enc1b, down1, enc2a, enc2b, down2,
+ * enc3a, enc3b (256), up2 (256->128), cat2 (256->128), dec2, up1, cat1, dec1,
+ * up0, cat0, dec0 (32), head (32->1); each layer's weights [kh][kw][cin][cout]
+ * (head: [32][1]) followed by its bias [cout].
+ *
+ * Features of a pressure problem, per cell c (FP32): beta_c is the mean of the
+ * cell's four face coefficients (wall faces count as 0) and rms(b) the root
+ * mean square of b over the cells;
+ *   x[c][0] = b_c / rms(b),   x[c][1] = log(rho_w beta_c / dt) / 4,
+ *   target t_c = phi_c beta_c / rms(b), prediction phi_c = out_c rms(b) / beta_c.
+ * (All zero when b = 0.)
+ *
+ * Each call runs on the net's stream (or, for a tank's guess, the tank's) and
+ * is host-synchronous where it returns a host value.  A net serves one tank at a
+ * time.  Invalid sizes, batch < 1 or > max_batch, n != wec_net_param_count():
+ * WEC_ERR_INVALID. */
+typedef struct wec_net wec_net;
+
+size_t wec_net_param_count(void);
+/* H, W: multiples of 8, >= 8; max_batch >= 1.  Weights start at zero. */
+int wec_net_create(int H, int W, int max_batch, void *cuda_stream, wec_net **out);
+void wec_net_destroy(wec_net *net);
+/* Host FP32 parameter vectors (layout above); set also resets the Adam state. */
+int wec_net_set_params(wec_net *net, const float *host, size_t n);
+int wec_net_get_params(const wec_net *net, float *host, size_t n);
+/* BF16 output (raw 16-bit words, NHWC) of layer (0 = enc0a .. 19 = dec0, the
+ * order above) from the last forward pass over `batch` images; n must equal
+ * batch x (H >> level) x (W >> level) x cout of that layer. */
+int wec_net_get_activation(const wec_net *net, int layer, int batch, unsigned short *host, size_t n);
+/* Gradient of the last wec_net_loss_grad / wec_net_train_step. */
+int wec_net_get_grads(const wec_net *net, float *host, size_t n);
+/* out = net(x).  x: device FP32 [batch][H][W][2]; out: device FP32 [batch][H][W]. */
+int wec_net_forward(wec_net *net, int batch, const float *x, float *out);
+/* Mean squared error of net(x) against target (device FP32 [batch][H][W]) into
+ * *loss (host), and its gradient (kept in the net). */
+int wec_net_loss_grad(wec_net *net, int batch, const float *x, const float *target, double *loss);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) with
+ * learning rate lr > 0 on the kept gradient. */
+int wec_net_adam(wec_net *net, float lr);
+/* wec_net_loss_grad on samples idx[0..batch) (host indices) of a dataset in
+ * device memory -- xs [S][H][W][2], ts [S][H][W], FP32 -- then wec_net_adam. */
+int wec_net_train_step(wec_net *net, const float *xs, const float *ts, const int *idx, int batch, float lr,
+                       double *loss);
+/* Features x (device FP32 [ny][nx][2]) and target t (device FP32 [ny][nx]) of
+ * the pressure problem of the tank's last step. */
+int wec_net_sample(wec_tank *tank, float *x, float *t);
+/* From the next step on, the tank's solve starts from the net's prediction
+ * (net H = ny, W = nx; NULL: from zero again).  The prediction is kept only if
+ * its FP64 residual ||b - A phi0|| is below ||b||; otherwise phi0 = 0 (the plain
+ * method).  The tank does not own the net: keep it alive while it is set. */
+int wec_tank_set_net(wec_tank *tank, wec_net *net);
+/* Steps that ran with a net (*tried) and kept its prediction (*kept). */
+int wec_tank_net_stats(const wec_tank *tank, long long *tried, long long *kept);
+
 /* Execution mode.  enable = 1 (default): the whole step -- including the
  * pressure solve's iteration, steered on the GPU by conditional WHILE / IF graph
  * nodes -- runs as one CUDA graph, captured at the first step and replayed.

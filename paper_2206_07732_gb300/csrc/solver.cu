@@ -22,6 +22,7 @@
 #include <cooperative_groups.h>
 
 #include "internal.cuh"
+#include "poisson_op.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -37,30 +38,6 @@ __device__ __forceinline__ T *at_sel(T *p, const int *sel, long long stride)
 }
 
 // ------------------------------------------------------------ stencil ----
-template <typename T>
-__device__ __forceinline__ T diag_at(const T *bu, const T *bv, int nx, int ny, int i, int j)
-{
-    T d = T(0);
-    if (i > 0) d += bu[j * (nx + 1) + i];
-    if (i < nx - 1) d += bu[j * (nx + 1) + i + 1];
-    if (j > 0) d += bv[j * nx + i];
-    d += (j < ny - 1 ? T(1) : T(2)) * bv[(j + 1) * nx + i];
-    return d;
-}
-
-template <typename T, typename TX>
-__device__ __forceinline__ T offsum_at(const T *bu, const T *bv, const TX *x, int nx, int ny, int i,
-                                       int j)
-{
-    int c = j * nx + i;
-    T s = T(0);
-    if (i > 0) s += bu[j * (nx + 1) + i] * T(x[c - 1]);
-    if (i < nx - 1) s += bu[j * (nx + 1) + i + 1] * T(x[c + 1]);
-    if (j > 0) s += bv[j * nx + i] * T(x[c - nx]);
-    if (j < ny - 1) s += bv[(j + 1) * nx + i] * T(x[c + nx]);
-    return s;
-}
-
 // y = A x (FP64 operator; x may be FP32 storage of a preconditioned vector)
 template <typename TX>
 __global__ void k_apply(int nx, int ny, const double *__restrict__ bu, const double *__restrict__ bv,

@@ -1165,7 +1165,10 @@ void enqueue_front_t(wec_tank *T, const Work<R> &W, cudaStream_t st)
                                                           S->L64[0].bv);
     }
     poisson_build(S, st);
-    cudaMemsetAsync(T->phi, 0, nc * 8, st);
+    if (T->net)
+        net_enqueue_guess(T, st);  // launch errors surface at the capture / the step's error check
+    else
+        cudaMemsetAsync(T->phi, 0, nc * 8, st);
 }
 
 void enqueue_front(wec_tank *T, cudaStream_t st)
@@ -1297,6 +1300,8 @@ int tank_step(wec_tank *T, double dt, double fpto, wec_step_result *out)
     WEC_CK(cudaMemcpyAsync(T->inp, in, sizeof(in), cudaMemcpyHostToDevice, st));  // pageable: staged before return
     const bool graph = T->use_graph && !prof::enabled();
     int status = WEC_OK;
+    if (T->net)
+        if (int e = net_sync_weights(T->net)) return e;
     if (graph) {
         if (!T->exec)
             if (int e = build_graph(T)) return e;
@@ -1335,6 +1340,7 @@ void tank_free(wec_tank *T)
     if (T->inp_owned) cudaFree(T->inp);
     cudaFree(T->w32);
     cudaFree(T->tabs32);
+    cudaFree(T->net_stats);
     cudaFree(T->S);
     if (T->Sh) cudaFreeHost(T->Sh);
     poisson_free(&T->solver);

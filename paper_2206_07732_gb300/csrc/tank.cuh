@@ -82,6 +82,8 @@ struct wec_tank {
     bool inp_owned = true;            // false when inp points into a batch's input array
     int last_iters = 0;
     double last_relres = 0.0;
+    wec_net *net = nullptr;           // learned initial guess of the solve (not owned)
+    long long *net_stats = nullptr;   // device: steps with a net, steps that kept its guess
 };
 
 namespace wec {
@@ -100,4 +102,8 @@ int tank_capture_step(wec_tank *T, cudaStream_t st);
 // After a replay that ran the captured step: launch accounting + the record.
 int tank_finish_step(wec_tank *T, wec_step_result *out);
 void tank_free(wec_tank *T);
+// unet.cu: the learned initial guess of the tank's increment (enqueued in the
+// step front in place of phi = 0), and the BF16 weight refresh it relies on.
+int net_enqueue_guess(wec_tank *T, cudaStream_t st);
+int net_sync_weights(wec_net *N);
 }  // namespace wec

@@ -1,0 +1,1333 @@
+// Learned warm start of the pressure solve: a 4-level convolutional U-Net in
+// BF16 on the tensor cores with FP32 accumulation, its training (forward,
+// backward, Adam) and its use as the initial guess of a tank's solve.
+//
+// Every convolution is an implicit GEMM: rows are output pixels (NHWC, batch
+// folded in), columns output channels, and the reduction runs over
+// (tap, input channel).  The A operand is gathered straight from the
+// activation tensors into shared memory (16-byte cp.async, zero fill at the
+// image border), so no im2col buffer exists; nearest upsampling, skip
+// concatenation and the stride-2 down convolution are gather modes of the same
+// kernel.  The backward pass uses the same kernel for the input gradients (a
+// 3x3 convolution of the output gradient with the flipped, transposed weights;
+// one 1x1 GEMM per sub-pixel for the stride-2 layer) and a second kernel for
+// the weight gradients (reduction over pixels, split across CTAs, partial tiles
+// summed in a fixed order: results are reproducible bit for bit).  ReLU masks,
+// biases, the skip gradient and the BF16 rounding are fused into the GEMM
+// epilogues.  Tiles: 128 pixels x 32/64 channels x 32 reduction elements,
+// 3-stage cp.async pipeline, 8 warps of m16n8k16 BF16 MMAs.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.cuh"
+#include "poisson_op.cuh"
+#include "tank.cuh"
+
+typedef __nv_bfloat16 bf16;
+typedef __nv_bfloat162 bf162;
+
+namespace wec {
+namespace {
+
+// ------------------------------------------------------------ architecture --
+enum LayerKind { L_CONV3 = 0, L_UP3 = 1, L_DOWN2 = 2, L_HEAD = 3 };
+
+struct LayerDef {
+    int kind, ci, co, level;  // level of the output tensor (0 = full resolution)
+};
+
+constexpr int kNumLayers = 21;
+constexpr int kInCh = 2;   // features per cell
+constexpr int kInPad = 8;  // channels of the stored BF16 input (16-byte rows)
+const LayerDef kLayers[kNumLayers] = {
+    {L_CONV3, 2, 32, 0},    {L_CONV3, 32, 32, 0},                           // enc0a, enc0b
+    {L_DOWN2, 32, 64, 1},   {L_CONV3, 64, 64, 1},   {L_CONV3, 64, 64, 1},   // down0, enc1a, enc1b
+    {L_DOWN2, 64, 128, 2},  {L_CONV3, 128, 128, 2}, {L_CONV3, 128, 128, 2}, // down1, enc2a, enc2b
+    {L_DOWN2, 128, 256, 3}, {L_CONV3, 256, 256, 3}, {L_CONV3, 256, 256, 3}, // down2, enc3a, enc3b
+    {L_UP3, 256, 128, 2},   {L_CONV3, 256, 128, 2}, {L_CONV3, 128, 128, 2}, // up2, cat2, dec2
+    {L_UP3, 128, 64, 1},    {L_CONV3, 128, 64, 1},  {L_CONV3, 64, 64, 1},   // up1, cat1, dec1
+    {L_UP3, 64, 32, 0},     {L_CONV3, 64, 32, 0},   {L_CONV3, 32, 32, 0},   // up0, cat0, dec0
+    {L_HEAD, 32, 1, 0}};                                                    // head
+constexpr int kHead = 20;
+inline int enc_a(int l) { return 3 * l; }
+inline int enc_b(int l) { return 3 * l + 1; }
+inline int down(int l) { return 3 * l + 2; }      // l = 0..2: level l -> l + 1
+inline int up(int l) { return 11 + 3 * (2 - l); }  // l = 2..0: level l + 1 -> l
+inline int cat(int l) { return up(l) + 1; }
+inline int dec(int l) { return up(l) + 2; }
+
+inline int taps(int kind) { return kind == L_DOWN2 ? 4 : (kind == L_HEAD ? 1 : 9); }
+inline int cin_pad(int ci) { return ci == kInCh ? kInPad : ci; }
+inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
+inline size_t round_up_z(size_t a, size_t b) { return (a + b - 1) / b * b; }
+
+// ----------------------------------------------------------- tile constants --
+constexpr int kBM = 128;     // GEMM rows (pixels, or weight rows in k_wgrad) per CTA
+constexpr int kBK = 32;      // reduction elements per pipeline stage
+constexpr int kGT = 256;     // threads (8 warps: 4 along M x 2 along N)
+constexpr int kStages = 3;
+constexpr int kAS = kBK + 8; // shared row stride of the A tile (conflict-free ldmatrix)
+
+enum GatherKind { G_CONV3 = 0, G_UP3 = 1, G_DOWN2 = 2, G_DIRECT = 3 };
+enum EpiKind { E_FWD = 0, E_DX = 1, E_F32 = 2, E_DOWNDX = 3 };
+
+// A operand of a convolution as an implicit GEMM.  Row (n, i, j) of the N x H x
+// W output grid, reduction index k = tap * cin + c with cin = c0 + c1 a power of
+// two; channel c < c0 comes from in0, the rest from in1 (concatenation).
+struct Gat {
+    const bf16 *in0, *in1;
+    int c0, c1, lcin;  // log2(cin)
+    int kind;
+    int N, H, W;       // output grid
+    int Hi, Wi;        // grid of the input tensors
+    int K;             // taps * cin; k >= K reads zeros (padding of the reduction)
+};
+
+// Fused epilogue.  E_FWD: out0 = bf16(relu(acc + bias)).  E_DX: input gradient;
+// columns < nsplit: out0 = bf16(acc * (mask0 > 0)), the rest: out1 = bf16(acc).
+// E_F32: outf = acc.  E_DOWNDX: the stride-2 layer's input gradient at the
+// sub-pixel blockIdx.z of each row's 2x2 block: out0 = bf16((acc + add) * (mask0 > 0)).
+struct Epi {
+    int kind;
+    const float *bias;
+    bf16 *out0;
+    const bf16 *mask0;
+    int ld0;
+    bf16 *out1;
+    int ld1, nsplit;
+    float *outf;
+    const bf16 *add;
+};
+
+// ------------------------------------------------------------- PTX helpers --
+__device__ __forceinline__ unsigned smem_u32(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+// 16-byte global -> shared copy; src_bytes = 0 fills the destination with zeros.
+__device__ __forceinline__ void cp16(void *dst, const void *src, int src_bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ void ldm_x4(unsigned r[4], const void *p)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(smem_u32(p)));
+}
+__device__ __forceinline__ void ldm_x4_t(unsigned r[4], const void *p)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(smem_u32(p)));
+}
+
+// d += a (16x16, row) * b (16x8, col), BF16 inputs, FP32 accumulators.
+__device__ __forceinline__ void mma16816(float d[4], const unsigned a[4], const unsigned b[2])
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// ------------------------------------------------------------------ gather --
+// Address of the 8 channels [c, c + 8) of reduction index k for output pixel
+// (n, i, j), or nullptr where the operand is zero (outside the image, k >= K).
+__device__ __forceinline__ const bf16 *gat_src(const Gat &g, int n, int i, int j, int k)
+{
+    if (k >= g.K) return nullptr;
+    const int t = k >> g.lcin, c = k & ((1 << g.lcin) - 1);
+    int ii = i, jj = j;
+    if (g.kind == G_CONV3 || g.kind == G_UP3) {
+        const int ta = t / 3, tb = t - 3 * ta;
+        ii = i + ta - 1;
+        jj = j + tb - 1;
+        if (ii < 0 || jj < 0 || ii >= g.H || jj >= g.W) return nullptr;
+        if (g.kind == G_UP3) {  // nearest upsampling: the input is the half grid
+            ii >>= 1;
+            jj >>= 1;
+        }
+    } else if (g.kind == G_DOWN2) {
+        ii = 2 * i + (t >> 1);
+        jj = 2 * j + (t & 1);
+    }
+    const size_t pix = ((size_t)n * g.Hi + ii) * g.Wi + jj;
+    return c < g.c0 ? g.in0 + pix * g.c0 + c : g.in1 + pix * g.c1 + (c - g.c0);
+}
+
+__device__ __forceinline__ void epi_store(const Epi &e, const Gat &g, int p, int col, float v0, float v1)
+{
+    if (e.kind == E_FWD) {
+        v0 = fmaxf(v0 + e.bias[col], 0.0f);
+        v1 = fmaxf(v1 + e.bias[col + 1], 0.0f);
+        *reinterpret_cast<bf162 *>(e.out0 + (size_t)p * e.ld0 + col) = __floats2bfloat162_rn(v0, v1);
+    } else if (e.kind == E_DX) {
+        if (col < e.nsplit) {
+            const size_t o = (size_t)p * e.ld0 + col;
+            const bf162 m = *reinterpret_cast<const bf162 *>(e.mask0 + o);
+            v0 = __bfloat162float(m.x) > 0.0f ? v0 : 0.0f;
+            v1 = __bfloat162float(m.y) > 0.0f ? v1 : 0.0f;
+            *reinterpret_cast<bf162 *>(e.out0 + o) = __floats2bfloat162_rn(v0, v1);
+        } else {
+            *reinterpret_cast<bf162 *>(e.out1 + (size_t)p * e.ld1 + col - e.nsplit) = __floats2bfloat162_rn(v0, v1);
+        }
+    } else if (e.kind == E_F32) {
+        *reinterpret_cast<float2 *>(e.outf + (size_t)p * e.ld0 + col) = make_float2(v0, v1);
+    } else {  // E_DOWNDX: row p = (n, i, j) of the half grid -> (n, 2i + a, 2j + b)
+        const int hw = g.H * g.W, n = p / hw, r = p - n * hw, i = r / g.W, j = r - i * g.W;
+        const int a = blockIdx.z >> 1, b = blockIdx.z & 1;
+        const size_t q = ((size_t)n * (2 * g.H) + 2 * i + a) * (2 * g.W) + 2 * j + b;
+        const size_t o = q * e.ld0 + col;
+        const bf162 s = *reinterpret_cast<const bf162 *>(e.add + o);
+        const bf162 m = *reinterpret_cast<const bf162 *>(e.mask0 + o);
+        v0 = __bfloat162float(m.x) > 0.0f ? v0 + __bfloat162float(s.x) : 0.0f;
+        v1 = __bfloat162float(m.y) > 0.0f ? v1 + __bfloat162float(s.y) : 0.0f;
+        *reinterpret_cast<bf162 *>(e.out0 + o) = __floats2bfloat162_rn(v0, v1);
+    }
+}
+
+// ---------------------------------------------------------- implicit GEMM --
+// C[p][n] = sum_k A(p, k) B[k][n] over Kpad (a multiple of kBK) for the rows p
+// of the grid and the columns [blockIdx.y BN, +BN) of B (row-major, ldb
+// columns; blockIdx.z selects a matrix bz elements further on), with the fused
+// epilogue.  Grid: (ceil(rows / kBM), columns / BN, sub-pixels).
+template <int BN>
+__global__ void __launch_bounds__(kGT) k_conv_gemm(Gat g, const bf16 *__restrict__ B, int ldb, size_t bz, int Kpad,
+                                                   Epi e)
+{
+    pdl_entry();
+    constexpr int BS = BN + 8;   // shared row stride of the B tile
+    constexpr int WN = BN / 2;   // columns per warp
+    constexpr int NT = WN / 8;   // n8 tiles per warp
+    __shared__ __align__(128) bf16 As[kStages][kBM][kAS];
+    __shared__ __align__(128) bf16 Bs[kStages][kBK][BS];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp & 3, wn = warp >> 2;
+    const int M = g.N * g.H * g.W;
+    const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
+    B += blockIdx.z * bz;
+
+    // this thread stages rows (tid >> 2) and (tid >> 2) + 64 of A, 8 channels at kc * 8
+    const int kc = tid & 3;
+    int rn[2], ri[2], rj[2];
+    bool rv[2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const int p = m0 + (tid >> 2) + 64 * s;
+        rv[s] = p < M;
+        const int hw = g.H * g.W, n = rv[s] ? p / hw : 0, r = p - n * hw;
+        rn[s] = n;
+        ri[s] = rv[s] ? r / g.W : 0;
+        rj[s] = rv[s] ? r - ri[s] * g.W : 0;
+    }
+    const int br = tid / (BN / 8), bc = tid % (BN / 8);
+    auto load = [&](int stage, int kt) {
+        const int k0 = kt * kBK;
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const bf16 *src = rv[s] ? gat_src(g, rn[s], ri[s], rj[s], k0 + kc * 8) : nullptr;
+            cp16(&As[stage][(tid >> 2) + 64 * s][kc * 8], src ? src : g.in0, src ? 16 : 0);
+        }
+        if (br < kBK) cp16(&Bs[stage][br][bc * 8], B + (size_t)(k0 + br) * ldb + n0 + bc * 8, 16);
+    };
+
+    float acc[2][NT][4];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < NT; ++b)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.0f;
+
+    const int KT = Kpad / kBK;
+#pragma unroll
+    for (int s = 0; s < kStages - 1; ++s) {
+        if (s < KT) load(s, s);
+        cp_commit();
+    }
+    for (int kt = 0; kt < KT; ++kt) {
+        cp_wait<kStages - 2>();
+        __syncthreads();
+        {
+            const int nk = kt + kStages - 1;
+            if (nk < KT) load(nk % kStages, nk);
+            cp_commit();
+        }
+        const int st = kt % kStages;
+#pragma unroll
+        for (int kk = 0; kk < kBK; kk += 16) {
+            unsigned a[2][4], b[NT][2];
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+                ldm_x4(a[mt], &As[st][wm * 32 + mt * 16 + (lane & 15)][kk + (lane >> 4) * 8]);
+#pragma unroll
+            for (int np = 0; np < NT / 2; ++np) {
+                unsigned r[4];
+                ldm_x4_t(r, &Bs[st][kk + (lane & 15)][wn * WN + np * 16 + (lane >> 4) * 8]);
+                b[2 * np][0] = r[0];
+                b[2 * np][1] = r[1];
+                b[2 * np + 1][0] = r[2];
+                b[2 * np + 1][1] = r[3];
+            }
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < NT; ++nt) mma16816(acc[mt][nt], a[mt], b[nt]);
+        }
+    }
+    cp_wait<0>();
+
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int p = m0 + wm * 32 + mt * 16 + (lane >> 2) + 8 * h;
+                if (p >= M) continue;
+                const int col = n0 + wn * WN + nt * 8 + 2 * (lane & 3);
+                epi_store(e, g, p, col, acc[mt][nt][2 * h], acc[mt][nt][2 * h + 1]);
+            }
+}
+
+// Weight gradient: part[z][k][n] = sum over the rows p of split z of A(p, k)
+// G[p][n] for the weight rows [blockIdx.x kBM, +kBM) and columns [blockIdx.y BN,
+// +BN).  A(p, k) is the layer's forward gather; rows are taken kBK at a time.
+template <int BN>
+__global__ void __launch_bounds__(kGT) k_wgrad(Gat g, const bf16 *__restrict__ G, int ldg, int chunks_per_split,
+                                               int Kpad, float *__restrict__ part)
+{
+    pdl_entry();
+    constexpr int AS = kBM + 8;
+    constexpr int BS = BN + 8;
+    constexpr int WN = BN / 2;
+    constexpr int NT = WN / 8;
+    __shared__ __align__(128) bf16 As[kStages][kBK][AS];  // [pixel][weight row]
+    __shared__ __align__(128) bf16 Bs[kStages][kBK][BS];  // [pixel][channel]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp & 3, wn = warp >> 2;
+    const int M = g.N * g.H * g.W, hw = g.H * g.W;
+    const int k0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
+    const int nchunks = (M + kBK - 1) / kBK;
+    const int c_begin = blockIdx.z * chunks_per_split;
+    const int c_end = min(c_begin + chunks_per_split, nchunks);
+    const int br = tid / (BN / 8), bc = tid % (BN / 8);
+
+    auto load = [&](int stage, int chunk) {
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const int q = tid + kGT * s, row = q >> 4, kcol = q & 15;
+            const int p = chunk * kBK + row;
+            const bf16 *src = nullptr;
+            if (p < M) {
+                const int n = p / hw, r = p - n * hw, i = r / g.W, j = r - i * g.W;
+                src = gat_src(g, n, i, j, k0 + kcol * 8);
+            }
+            cp16(&As[stage][row][kcol * 8], src ? src : g.in0, src ? 16 : 0);
+        }
+        if (br < kBK) {
+            const int p = chunk * kBK + br;
+            const bf16 *src = p < M ? G + (size_t)p * ldg + n0 + bc * 8 : G;
+            cp16(&Bs[stage][br][bc * 8], src, p < M ? 16 : 0);
+        }
+    };
+
+    float acc[2][NT][4];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < NT; ++b)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.0f;
+
+    const int KT = max(c_end - c_begin, 0);
+#pragma unroll
+    for (int s = 0; s < kStages - 1; ++s) {
+        if (s < KT) load(s, c_begin + s);
+        cp_commit();
+    }
+    for (int kt = 0; kt < KT; ++kt) {
+        cp_wait<kStages - 2>();
+        __syncthreads();
+        {
+            const int nk = kt + kStages - 1;
+            if (nk < KT) load(nk % kStages, c_begin + nk);
+            cp_commit();
+        }
+        const int st = kt % kStages;
+#pragma unroll
+        for (int kk = 0; kk < kBK; kk += 16) {
+            unsigned a[2][4], b[NT][2];
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+                ldm_x4_t(a[mt], &As[st][kk + (lane & 7) + ((lane >> 4) << 3)][wm * 32 + mt * 16 + ((lane >> 3) & 1) * 8]);
+#pragma unroll
+            for (int np = 0; np < NT / 2; ++np) {
+                unsigned r[4];
+                ldm_x4_t(r, &Bs[st][kk + (lane & 15)][wn * WN + np * 16 + (lane >> 4) * 8]);
+                b[2 * np][0] = r[0];
+                b[2 * np][1] = r[1];
+                b[2 * np + 1][0] = r[2];
+                b[2 * np + 1][1] = r[3];
+            }
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < NT; ++nt) mma16816(acc[mt][nt], a[mt], b[nt]);
+        }
+    }
+    cp_wait<0>();
+
+    const int ldp = gridDim.y * BN;
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int k = k0 + wm * 32 + mt * 16 + (lane >> 2) + 8 * h;
+                const int col = n0 + wn * WN + nt * 8 + 2 * (lane & 3);
+                *reinterpret_cast<float2 *>(part + ((size_t)blockIdx.z * Kpad + k) * ldp + col) =
+                    make_float2(acc[mt][nt][2 * h], acc[mt][nt][2 * h + 1]);
+            }
+}
+
+// ------------------------------------------------------------ small kernels --
+constexpr int kT = 256;
+constexpr int kHeadVals = 34;  // per-block partials of the head: dw[32], db, loss
+
+// x FP32 [M][2] -> BF16 [M][8], channels 2..7 zero.
+__global__ void k_input(const float *__restrict__ x, long long M, bf16 *__restrict__ xin)
+{
+    pdl_entry();
+    const long long p = blockIdx.x * (long long)kT + threadIdx.x;
+    if (p >= M) return;
+    const float2 v = *reinterpret_cast<const float2 *>(x + 2 * p);
+    __align__(16) bf16 row[kInPad];
+    row[0] = __float2bfloat16_rn(v.x);
+    row[1] = __float2bfloat16_rn(v.y);
+#pragma unroll
+    for (int c = 2; c < kInPad; ++c) row[c] = __float2bfloat16_rn(0.0f);
+    *reinterpret_cast<uint4 *>(xin + p * kInPad) = *reinterpret_cast<const uint4 *>(row);
+}
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// 1x1 FP32 head over the 32-channel tensor a: out = a . w + b.  With a target
+// (training): dout = 2 (out - t) / M, the gradient of the head input's
+// pre-activation G = bf16(dout w * (a > 0)), and per-block partials of dw, db and
+// the squared error (kHeadVals per block).
+__global__ void __launch_bounds__(kT) k_head(const bf16 *__restrict__ a, const float *__restrict__ w, long long M,
+                                             float *__restrict__ out, const float *__restrict__ target, float inv_m,
+                                             bf16 *__restrict__ G, float *__restrict__ part)
+{
+    pdl_entry();
+    __shared__ float sh[kT / 32][kHeadVals];
+    const long long p = blockIdx.x * (long long)kT + threadIdx.x;
+    float av[32];
+    float o = 0.0f;
+    if (p < M) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(a + p * 32);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            uint4 u = src[q];
+            const bf16 *h = reinterpret_cast<const bf16 *>(&u);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) av[8 * q + c] = __bfloat162float(h[c]);
+        }
+        o = w[32];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) o = fmaf(av[c], w[c], o);
+        out[p] = o;
+    }
+    if (!target) return;
+    float d = 0.0f, se = 0.0f;
+    if (p < M) {
+        const float r = o - target[p];
+        d = 2.0f * r * inv_m;
+        se = r * r;
+        __align__(16) bf16 g[32];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) g[c] = __float2bfloat16_rn(av[c] > 0.0f ? d * w[c] : 0.0f);
+        uint4 *dst = reinterpret_cast<uint4 *>(G + p * 32);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) dst[q] = reinterpret_cast<const uint4 *>(g)[q];
+    } else {
+#pragma unroll
+        for (int c = 0; c < 32; ++c) av[c] = 0.0f;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+        const float s = warp_sum(d * av[c]);
+        if (lane == 0) sh[warp][c] = s;
+    }
+    {
+        const float s = warp_sum(d);
+        if (lane == 0) sh[warp][32] = s;
+        const float q = warp_sum(se);
+        if (lane == 0) sh[warp][33] = q;
+    }
+    __syncthreads();
+    if (threadIdx.x < kHeadVals) {
+        float s = 0.0f;
+        for (int wv = 0; wv < kT / 32; ++wv) s += sh[wv][threadIdx.x];
+        part[(size_t)blockIdx.x * kHeadVals + threadIdx.x] = s;
+    }
+}
+
+// Head gradient and loss from the per-block partials (fixed order).
+__global__ void k_head_final(const float *__restrict__ part, int nblocks, float *__restrict__ gw, double *loss,
+                             double inv_m)
+{
+    pdl_entry();
+    const int v = threadIdx.x;
+    if (v >= kHeadVals) return;
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += part[(size_t)b * kHeadVals + v];
+    if (v < 33)
+        gw[v] = (float)s;
+    else
+        *loss = s * inv_m;
+}
+
+// Input gradient of an upsampling layer: G[n][i][j][c] = bf16(sum of the 2x2
+// block of tmp (full grid) * (low > 0)), low the half-grid input tensor.
+__global__ void k_up_pool(const float *__restrict__ tmp, const bf16 *__restrict__ low, int N, int h, int w, int C,
+                          bf16 *__restrict__ G)
+{
+    pdl_entry();
+    const long long k = blockIdx.x * (long long)kT + threadIdx.x;
+    const long long total = (long long)N * h * w * C;
+    if (k >= total) return;
+    const int c = (int)(k % C);
+    const long long pix = k / C;
+    const int j = (int)(pix % w);
+    const long long r = pix / w;
+    const int i = (int)(r % h), n = (int)(r / h);
+    const size_t W2 = 2 * (size_t)w;
+    const size_t q = (((size_t)n * 2 * h + 2 * i) * W2 + 2 * j) * C + c;
+    const float s = (tmp[q] + tmp[q + C]) + (tmp[q + W2 * C] + tmp[q + W2 * C + C]);
+    G[k] = __float2bfloat16_rn(__bfloat162float(low[k]) > 0.0f ? s : 0.0f);
+}
+
+// Column sums of G [M][C] (bias gradient): per-block partials part[b][C].
+__global__ void __launch_bounds__(kT) k_colsum(const bf16 *__restrict__ G, long long M, int C, int rows_per_block,
+                                               float *__restrict__ part)
+{
+    pdl_entry();
+    __shared__ float sh[kT];
+    const int c = threadIdx.x % C, lanes = kT / C, r0 = threadIdx.x / C;
+    const long long b = (long long)blockIdx.x * rows_per_block;
+    const long long e = min(b + rows_per_block, M);
+    float s = 0.0f;
+    for (long long p = b + r0; p < e; p += lanes) s += __bfloat162float(G[p * C + c]);
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x < C) {
+        float t = 0.0f;
+        for (int q = 0; q < lanes; ++q) t += sh[q * C + threadIdx.x];
+        part[(size_t)blockIdx.x * C + threadIdx.x] = t;
+    }
+}
+
+__global__ void k_colsum_final(const float *__restrict__ part, int nblocks, int C, float *__restrict__ gb)
+{
+    pdl_entry();
+    const int c = blockIdx.x * kT + threadIdx.x;
+    if (c >= C) return;
+    float s = 0.0f;
+    for (int b = 0; b < nblocks; ++b) s += part[(size_t)b * C + c];
+    gb[c] = s;
+}
+
+// Weight gradient of a layer from the split partials: gw[(t ci + c) co + o] =
+// sum_z part[z][t cinp + c][o], in split order.
+__global__ void k_wgrad_reduce(const float *__restrict__ part, int splits, int Kpad, int co, int cinp, int ci,
+                               int ntaps, float *__restrict__ gw)
+{
+    pdl_entry();
+    const long long idx = blockIdx.x * (long long)kT + threadIdx.x;
+    const long long total = (long long)ntaps * ci * co;
+    if (idx >= total) return;
+    const int o = (int)(idx % co);
+    const long long r = idx / co;
+    const int c = (int)(r % ci), t = (int)(r / ci);
+    const int k = t * cinp + c;
+    float s = 0.0f;
+    for (int z = 0; z < splits; ++z) s += part[((size_t)z * Kpad + k) * co + o];
+    gw[idx] = s;
+}
+
+// Adam with bias correction (b1t = 1 - beta1^t, b2t = 1 - beta2^t).
+__global__ void k_adam(float *__restrict__ th, const float *__restrict__ g, float *__restrict__ m,
+                       float *__restrict__ v, long long n, float lr, float b1t, float b2t)
+{
+    pdl_entry();
+    const long long k = blockIdx.x * (long long)kT + threadIdx.x;
+    if (k >= n) return;
+    const float gk = g[k];
+    const float mk = 0.9f * m[k] + 0.1f * gk;
+    const float vk = 0.999f * v[k] + 0.001f * gk * gk;
+    m[k] = mk;
+    v[k] = vk;
+    th[k] -= lr * (mk / b1t) / (sqrtf(vk / b2t) + 1e-8f);
+}
+
+// BF16 matrices of a layer from its FP32 weights W [ntaps][ci][co]:
+//   forward   F[k][o], k = t cinp + c (rows up to Kpad; padding zero)
+//   backward  conv/up: Bk[t' co + o][c] = W[8 - t'][c][o];  down: Bd[t][o][c] = W[t][c][o]
+__global__ void k_pack(const float *__restrict__ W, int kind, int ntaps, int ci, int co, int cinp, int Kpad,
+                       bf16 *__restrict__ F, bf16 *__restrict__ Bk)
+{
+    pdl_entry();
+    const long long idx = blockIdx.x * (long long)kT + threadIdx.x;
+    const long long nf = (long long)Kpad * co;
+    if (idx < nf) {
+        const int o = (int)(idx % co), k = (int)(idx / co);
+        const int t = k / cinp, c = k - t * cinp;
+        const float w = (t < ntaps && c < ci) ? W[((size_t)t * ci + c) * co + o] : 0.0f;
+        F[idx] = __float2bfloat16_rn(w);
+        return;
+    }
+    if (!Bk) return;
+    const long long q = idx - nf;
+    if (q >= (long long)ntaps * co * ci) return;
+    const int c = (int)(q % ci);
+    const long long r = q / ci;
+    const int o = (int)(r % co), t = (int)(r / co);
+    const int ts = kind == L_DOWN2 ? t : 8 - t;
+    Bk[q] = __float2bfloat16_rn(W[((size_t)ts * ci + c) * co + o]);
+}
+
+// ------------------------------------------------- features of a pressure problem --
+// part[b] = sum of b^2 over block b's cells (FP64).
+__global__ void __launch_bounds__(kT) k_feat_bsum(const double *__restrict__ b, int n, double *__restrict__ part)
+{
+    pdl_entry();
+    __shared__ double sh[kT / 32];
+    double s = 0.0;
+    for (int c = blockIdx.x * kT + threadIdx.x; c < n; c += gridDim.x * kT) s += b[c] * b[c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kT / 32; ++w) t += sh[w];
+        part[blockIdx.x] = t;
+    }
+}
+
+__device__ __forceinline__ double sum_parts(const double *part, int n)
+{
+    double s = 0.0;
+    for (int k = 0; k < n; ++k) s += part[k];
+    return s;
+}
+
+__device__ __forceinline__ double cell_beta(const double *bu, const double *bv, int nx, int i, int j)
+{
+    return 0.25 * (bu[j * (nx + 1) + i] + bu[j * (nx + 1) + i + 1] + bv[j * nx + i] + bv[(j + 1) * nx + i]);
+}
+
+// Features x [n][2] (and, if phi is given, the target t [n]) of A phi = b.
+__global__ void k_features(int nx, int ny, const double *__restrict__ b, const double *__restrict__ bu,
+                           const double *__restrict__ bv, const double *__restrict__ inp, double rho_w,
+                           const double *__restrict__ part, int nparts, const double *__restrict__ phi,
+                           float *__restrict__ x, float *__restrict__ t)
+{
+    pdl_entry();
+    const int c = blockIdx.x * kT + threadIdx.x;
+    if (c >= nx * ny) return;
+    const double s2 = sum_parts(part, nparts);
+    const int i = c % nx, j = c / nx;
+    const double beta = cell_beta(bu, bv, nx, i, j);
+    float x0 = 0.0f, x1 = 0.0f, tt = 0.0f;
+    if (s2 > 0.0 && beta > 0.0) {
+        const double rms = sqrt(s2 / (double(nx) * ny));
+        x0 = (float)(b[c] / rms);
+        x1 = (float)(0.25 * log(rho_w * beta / inp[0]));
+        if (phi) tt = (float)(phi[c] * beta / rms);
+    }
+    *reinterpret_cast<float2 *>(x + 2 * (size_t)c) = make_float2(x0, x1);
+    if (phi) t[c] = tt;
+}
+
+// phi0 = out rms(b) / beta_c; then part2[b] = sum of (b - A phi0)^2 over block b.
+__global__ void k_guess(int nx, int ny, const double *__restrict__ b, const double *__restrict__ bu,
+                        const double *__restrict__ bv, const double *__restrict__ part, int nparts,
+                        const float *__restrict__ out, double *__restrict__ phi)
+{
+    pdl_entry();
+    const int c = blockIdx.x * kT + threadIdx.x;
+    if (c >= nx * ny) return;
+    const double s2 = sum_parts(part, nparts);
+    const int i = c % nx, j = c / nx;
+    const double beta = cell_beta(bu, bv, nx, i, j);
+    phi[c] = (s2 > 0.0 && beta > 0.0) ? double(out[c]) * sqrt(s2 / (double(nx) * ny)) / beta : 0.0;
+}
+
+__global__ void __launch_bounds__(kT) k_guess_resid(int nx, int ny, const double *__restrict__ b,
+                                                    const double *__restrict__ bu, const double *__restrict__ bv,
+                                                    const double *__restrict__ phi, double *__restrict__ part)
+{
+    pdl_entry();
+    __shared__ double sh[kT / 32];
+    double s = 0.0;
+    for (int c = blockIdx.x * kT + threadIdx.x; c < nx * ny; c += gridDim.x * kT) {
+        const int i = c % nx, j = c / nx;
+        const double r = b[c] - (diag_at(bu, bv, nx, ny, i, j) * phi[c] - offsum_at(bu, bv, phi, nx, ny, i, j));
+        s += r * r;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kT / 32; ++w) t += sh[w];
+        part[blockIdx.x] = t;
+    }
+}
+
+// Keep phi0 only if ||b - A phi0|| < ||b|| (else phi0 = 0); count tried / kept.
+__global__ void k_guess_select(int n, const double *__restrict__ pb, const double *__restrict__ pr, int nparts,
+                               double *__restrict__ phi, long long *stats)
+{
+    pdl_entry();
+    const double b2 = sum_parts(pb, nparts), r2 = sum_parts(pr, nparts);
+    const bool keep = r2 < b2;
+    const int c = blockIdx.x * kT + threadIdx.x;
+    if (!keep && c < n) phi[c] = 0.0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        stats[0] += 1;
+        stats[1] += keep ? 1 : 0;
+    }
+}
+
+}  // namespace
+}  // namespace wec
+
+struct wec_net {
+    int H = 0, W = 0, maxb = 0;
+    cudaStream_t st = nullptr;
+    size_t nparam = 0;
+    float *theta = nullptr, *grad = nullptr, *am = nullptr, *av = nullptr;  // FP32 [nparam] each
+    long long adam_t = 0;
+    bool wdirty = true;                       // BF16 matrices older than theta
+    bf16 *wmat = nullptr;                     // every layer's BF16 matrices
+    size_t flat[wec::kNumLayers] = {};        // layer weights in theta (bias follows)
+    size_t wf[wec::kNumLayers] = {}, wb[wec::kNumLayers] = {};  // forward / backward matrices in wmat
+    bf16 *xin = nullptr;                      // [maxb][H][W][8]
+    bf16 *act[wec::kNumLayers] = {};          // layer outputs
+    float *out = nullptr;                     // [maxb][H][W]
+    bf16 *gA[4] = {}, *gB[4] = {}, *skip[3] = {};  // gradients per level
+    float *tmpf = nullptr;                    // input gradient of an upsampling layer (full grid)
+    float *part = nullptr;                    // split-K partials of the weight gradients
+    size_t part_n = 0;
+    float *cpart = nullptr;                   // column-sum / head partials
+    float *xb = nullptr, *tb = nullptr;       // gathered batch (or a tank's features)
+    double *loss = nullptr, *lossh = nullptr; // device / pinned host
+    double *dpart = nullptr;                  // FP64 partials of the tank guess (2 x kRedBlocks)
+    std::vector<void *> allocs;
+};
+
+namespace wec {
+namespace {
+
+constexpr int kCsumBlocks = 304;
+constexpr int kWgradTarget = 608;  // CTAs a weight-gradient launch aims for (4 per SM)
+
+int ilog2(int v)
+{
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+}
+
+size_t weight_count(int L) { return (size_t)taps(kLayers[L].kind) * kLayers[L].ci * kLayers[L].co; }
+int fwd_K(int L) { return taps(kLayers[L].kind) * cin_pad(kLayers[L].ci); }
+int level_h(const wec_net *N, int l) { return N->H >> l; }
+int level_w(const wec_net *N, int l) { return N->W >> l; }
+int chans(int l) { return 32 << l; }
+
+void layer_inputs(const wec_net *N, int L, const bf16 **in0, const bf16 **in1)
+{
+    *in1 = nullptr;
+    for (int l = 0; l < 4; ++l) {
+        if (L == enc_a(l)) *in0 = l == 0 ? N->xin : N->act[down(l - 1)];
+        if (L == enc_b(l)) *in0 = N->act[enc_a(l)];
+        if (l < 3 && L == down(l)) *in0 = N->act[enc_b(l)];
+        if (l < 3 && L == up(l)) *in0 = l == 2 ? N->act[enc_b(3)] : N->act[dec(l + 1)];
+        if (l < 3 && L == cat(l)) {
+            *in0 = N->act[up(l)];
+            *in1 = N->act[enc_b(l)];
+        }
+        if (l < 3 && L == dec(l)) *in0 = N->act[cat(l)];
+    }
+}
+
+// The forward gather of layer L (its input tensors, output grid of its level).
+Gat fwd_gather(const wec_net *N, int L, int batch)
+{
+    const LayerDef &d = kLayers[L];
+    const int cinp = cin_pad(d.ci), H = level_h(N, d.level), W = level_w(N, d.level);
+    Gat g{};
+    layer_inputs(N, L, &g.in0, &g.in1);
+    g.c0 = g.in1 ? cinp / 2 : cinp;
+    g.c1 = g.in1 ? cinp / 2 : 0;
+    g.lcin = ilog2(cinp);
+    g.kind = d.kind == L_CONV3 ? G_CONV3 : (d.kind == L_UP3 ? G_UP3 : G_DOWN2);
+    g.N = batch;
+    g.H = H;
+    g.W = W;
+    g.Hi = d.kind == L_UP3 ? H / 2 : (d.kind == L_DOWN2 ? 2 * H : H);
+    g.Wi = d.kind == L_UP3 ? W / 2 : (d.kind == L_DOWN2 ? 2 * W : W);
+    g.K = fwd_K(L);
+    return g;
+}
+
+int gemm(cudaStream_t st, const Gat &g, const bf16 *B, int ldb, size_t bz, int Kpad, int ncols, int nz, const Epi &e)
+{
+    const long long M = (long long)g.N * g.H * g.W;
+    dim3 grid((unsigned)((M + kBM - 1) / kBM), (unsigned)(ncols / (ncols % 64 == 0 ? 64 : 32)), (unsigned)nz);
+    WEC_PROF("net_conv", -1, 2.0 * M * nz * ((double)(g.c0 + g.c1) + ncols) + 2.0 * Kpad * ldb * nz, st);
+    if (ncols % 64 == 0)
+        WEC_CK(launch_k(k_conv_gemm<64>, grid, kGT, 0, st, g, B, ldb, bz, Kpad, e));
+    else
+        WEC_CK(launch_k(k_conv_gemm<32>, grid, kGT, 0, st, g, B, ldb, bz, Kpad, e));
+    return WEC_OK;
+}
+
+int wgrad_splits(long long M, int L, int *cps)
+{
+    const int co = kLayers[L].co, BN = co % 64 == 0 ? 64 : 32;
+    const int tiles = round_up(fwd_K(L), kBM) / kBM * (co / BN);
+    const int nchunks = (int)((M + kBK - 1) / kBK);
+    int splits = std::max(1, std::min((kWgradTarget + tiles - 1) / tiles, nchunks));
+    *cps = (nchunks + splits - 1) / splits;
+    return (nchunks + *cps - 1) / *cps;
+}
+
+// grad of layer L's weights and bias from its output gradient G.
+int wgrad(wec_net *N, int L, int batch, const bf16 *G)
+{
+    const LayerDef &d = kLayers[L];
+    const Gat g = fwd_gather(N, L, batch);
+    const long long M = (long long)g.N * g.H * g.W;
+    const int Kw = round_up(g.K, kBM), BN = d.co % 64 == 0 ? 64 : 32;
+    int cps = 0;
+    const int splits = wgrad_splits(M, L, &cps);
+    cudaStream_t st = N->st;
+    {
+        WEC_PROF("net_wgrad", -1, 2.0 * M * ((double)(g.c0 + g.c1) * taps(d.kind) + d.co), st);
+        dim3 grid((unsigned)(Kw / kBM), (unsigned)(d.co / BN), (unsigned)splits);
+        if (BN == 64)
+            WEC_CK(launch_k(k_wgrad<64>, grid, kGT, 0, st, g, G, d.co, cps, Kw, N->part));
+        else
+            WEC_CK(launch_k(k_wgrad<32>, grid, kGT, 0, st, g, G, d.co, cps, Kw, N->part));
+    }
+    float *gw = N->grad + N->flat[L];
+    const long long nw = (long long)weight_count(L);
+    {
+        WEC_PROF("net_wgrad_reduce", -1, 4.0 * nw * (splits + 1), st);
+        WEC_CK(launch_k(k_wgrad_reduce, nblk(nw, kT), kT, 0, st, (const float *)N->part, splits, Kw, d.co,
+                        cin_pad(d.ci), d.ci, taps(d.kind), gw));
+    }
+    const int nb = (int)std::min<long long>(kCsumBlocks, (M + 63) / 64);
+    const int rows = (int)((M + nb - 1) / nb);
+    {
+        WEC_PROF("net_bias_grad", -1, 2.0 * M * d.co, st);
+        WEC_CK(launch_k(k_colsum, nb, kT, 0, st, G, M, d.co, rows, N->cpart));
+    }
+    {
+        WEC_PROF("net_bias_grad", -1, 4.0 * nb * d.co, st);
+        WEC_CK(launch_k(k_colsum_final, nblk(d.co, kT), kT, 0, st, (const float *)N->cpart, nb, d.co, gw + nw));
+    }
+    return WEC_OK;
+}
+
+// Input gradient of a 3x3 layer (conv or up): the 3x3 convolution of G (its
+// output gradient, level grid) with the flipped, transposed weights.
+int dx_conv(wec_net *N, int L, int batch, const bf16 *G, const Epi &e)
+{
+    const LayerDef &d = kLayers[L];
+    Gat g{};
+    g.in0 = G;
+    g.c0 = d.co;
+    g.lcin = ilog2(d.co);
+    g.kind = G_CONV3;
+    g.N = batch;
+    g.H = g.Hi = level_h(N, d.level);
+    g.W = g.Wi = level_w(N, d.level);
+    g.K = 9 * d.co;
+    return gemm(N->st, g, N->wmat + N->wb[L], d.ci, 0, 9 * d.co, d.ci, 1, e);
+}
+
+int pack_weights(wec_net *N)
+{
+    for (int L = 0; L < kHead; ++L) {
+        const LayerDef &d = kLayers[L];
+        const int Kp = round_up(fwd_K(L), kBK);
+        const bool back = L != enc_a(0);
+        const long long n = (long long)Kp * d.co + (back ? (long long)weight_count(L) : 0);
+        WEC_PROF("net_pack", -1, 4.0 * weight_count(L) + 2.0 * n, N->st);
+        WEC_CK(launch_k(k_pack, nblk(n, kT), kT, 0, N->st, (const float *)(N->theta + N->flat[L]), d.kind,
+                        taps(d.kind), d.ci, d.co, cin_pad(d.ci), Kp, N->wmat + N->wf[L],
+                        back ? N->wmat + N->wb[L] : (bf16 *)nullptr));
+    }
+    N->wdirty = false;
+    return WEC_OK;
+}
+
+// Forward pass of batch images x (FP32 [batch][H][W][2]) into out; with a
+// target, also the head's gradient, loss partials and G of dec0 (in gA[0]).
+int forward(wec_net *N, int batch, const float *x, float *out, const float *target)
+{
+    cudaStream_t st = N->st;
+    if (N->wdirty)
+        if (int e = pack_weights(N)) return e;
+    const long long M = (long long)batch * N->H * N->W;
+    {
+        WEC_PROF("net_input", -1, 8.0 * M + 16.0 * M, st);
+        WEC_CK(launch_k(k_input, nblk(M, kT), kT, 0, st, x, M, N->xin));
+    }
+    for (int L = 0; L < kHead; ++L) {
+        const LayerDef &d = kLayers[L];
+        Epi e{};
+        e.kind = E_FWD;
+        e.bias = N->theta + N->flat[L] + weight_count(L);
+        e.out0 = N->act[L];
+        e.ld0 = d.co;
+        const Gat g = fwd_gather(N, L, batch);
+        if (int r = gemm(st, g, N->wmat + N->wf[L], d.co, 0, round_up(g.K, kBK), d.co, 1, e)) return r;
+    }
+    const int nb = nblk(M, kT);
+    {
+        WEC_PROF("net_head", -1, 64.0 * M + 8.0 * M, st);
+        WEC_CK(launch_k(k_head, nb, kT, 0, st, (const bf16 *)N->act[dec(0)], (const float *)(N->theta + N->flat[kHead]),
+                        M, out, target, (float)(1.0 / (double)M), N->gA[0], N->cpart));
+    }
+    if (target) {
+        WEC_PROF("net_head", -1, 4.0 * kHeadVals * nb, st);
+        WEC_CK(launch_k(k_head_final, 1, 64, 0, st, (const float *)N->cpart, nb, N->grad + N->flat[kHead], N->loss,
+                        1.0 / (double)M));
+    }
+    return WEC_OK;
+}
+
+int backward(wec_net *N, int batch)
+{
+    cudaStream_t st = N->st;
+    for (int l = 0; l < 3; ++l) {  // decoder, last level first; G of dec(l) is in gA[l]
+        const int C = chans(l);
+        if (int r = wgrad(N, dec(l), batch, N->gA[l])) return r;
+        Epi e{};
+        e.kind = E_DX;
+        e.out0 = N->gB[l];
+        e.mask0 = N->act[cat(l)];
+        e.ld0 = C;
+        e.nsplit = C;
+        if (int r = dx_conv(N, dec(l), batch, N->gA[l], e)) return r;
+        if (int r = wgrad(N, cat(l), batch, N->gB[l])) return r;
+        e.out0 = N->gA[l];
+        e.mask0 = N->act[up(l)];
+        e.out1 = N->skip[l];
+        e.ld1 = C;
+        if (int r = dx_conv(N, cat(l), batch, N->gB[l], e)) return r;
+        if (int r = wgrad(N, up(l), batch, N->gA[l])) return r;
+        Epi f{};
+        f.kind = E_F32;
+        f.outf = N->tmpf;
+        f.ld0 = 2 * C;
+        if (int r = dx_conv(N, up(l), batch, N->gA[l], f)) return r;
+        const int h = level_h(N, l + 1), w = level_w(N, l + 1);
+        const long long n = (long long)batch * h * w * 2 * C;
+        WEC_PROF("net_up_pool", -1, 16.0 * n + 4.0 * n, st);
+        WEC_CK(launch_k(k_up_pool, nblk(n, kT), kT, 0, st, (const float *)N->tmpf,
+                        (const bf16 *)(l == 2 ? N->act[enc_b(3)] : N->act[dec(l + 1)]), batch, h, w, 2 * C,
+                        N->gA[l + 1]));
+    }
+    for (int l = 3; l >= 0; --l) {  // encoder; G of down(l)'s output is in gA[l + 1]
+        const int C = chans(l);
+        if (l < 3) {
+            if (int r = wgrad(N, down(l), batch, N->gA[l + 1])) return r;
+            Gat g{};
+            g.in0 = N->gA[l + 1];
+            g.c0 = 2 * C;
+            g.lcin = ilog2(2 * C);
+            g.kind = G_DIRECT;
+            g.N = batch;
+            g.H = g.Hi = level_h(N, l + 1);
+            g.W = g.Wi = level_w(N, l + 1);
+            g.K = 2 * C;
+            Epi e{};
+            e.kind = E_DOWNDX;
+            e.out0 = N->gA[l];
+            e.mask0 = N->act[enc_b(l)];
+            e.ld0 = C;
+            e.add = N->skip[l];
+            if (int r = gemm(st, g, N->wmat + N->wb[down(l)], C, (size_t)2 * C * C, 2 * C, C, 4, e)) return r;
+        }
+        if (int r = wgrad(N, enc_b(l), batch, N->gA[l])) return r;
+        Epi e{};
+        e.kind = E_DX;
+        e.out0 = N->gB[l];
+        e.mask0 = N->act[enc_a(l)];
+        e.ld0 = C;
+        e.nsplit = C;
+        if (int r = dx_conv(N, enc_b(l), batch, N->gA[l], e)) return r;
+        if (int r = wgrad(N, enc_a(l), batch, N->gB[l])) return r;
+        if (l > 0) {
+            e.out0 = N->gA[l];
+            e.mask0 = N->act[down(l - 1)];
+            if (int r = dx_conv(N, enc_a(l), batch, N->gB[l], e)) return r;
+        }
+    }
+    return WEC_OK;
+}
+
+int net_alloc(wec_net *N, void **p, size_t bytes)
+{
+    cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 256));
+    if (e != cudaSuccess) return cuda_fail(e, "net: device allocation");
+    N->allocs.push_back(*p);
+    return WEC_OK;
+}
+
+void net_free(wec_net *N)
+{
+    if (!N) return;
+    if (N->st) cudaStreamSynchronize(N->st);
+    for (void *p : N->allocs) cudaFree(p);
+    if (N->lossh) cudaFreeHost(N->lossh);
+    delete N;
+}
+
+}  // namespace
+
+size_t net_param_count()
+{
+    size_t n = 0;
+    for (int L = 0; L < kNumLayers; ++L) n += weight_count(L) + kLayers[L].co;
+    return n;
+}
+
+int net_sync_weights(wec_net *N)
+{
+    if (!N->wdirty) return WEC_OK;
+    if (int r = pack_weights(N)) return r;
+    WEC_CK(cudaStreamSynchronize(N->st));
+    return WEC_OK;
+}
+
+// Enqueue the net's guess for the tank's increment phi (step front, after the
+// pressure problem is built).
+int net_enqueue_guess(wec_tank *T, cudaStream_t st)
+{
+    wec_net *N = T->net;
+    if (N->wdirty) return fail(WEC_ERR_INVALID, "net guess: BF16 weights not packed");
+    const int nx = T->P.nx, ny = T->P.ny, nc = nx * ny;
+    const double *bu = T->solver.L64[0].bu, *bv = T->solver.L64[0].bv;
+    cudaStream_t keep = N->st;
+    N->st = st;
+    {
+        WEC_PROF("net_features", -1, 8.0 * nc, st);
+        WEC_CK(launch_k(k_feat_bsum, kRedBlocks, kT, 0, st, (const double *)T->rhs, nc, N->dpart));
+    }
+    {
+        WEC_PROF("net_features", -1, 8.0 * nc * 4 + 8.0 * nc, st);
+        WEC_CK(launch_k(k_features, nblk(nc, kT), kT, 0, st, nx, ny, (const double *)T->rhs, bu, bv,
+                        (const double *)T->inp, T->P.rho_w, (const double *)N->dpart, kRedBlocks,
+                        (const double *)nullptr, N->xb, (float *)nullptr));
+    }
+    int r = forward(N, 1, N->xb, N->out, nullptr);
+    N->st = keep;
+    if (r) return r;
+    {
+        WEC_PROF("net_guess", -1, 8.0 * nc * 4 + 4.0 * nc, st);
+        WEC_CK(launch_k(k_guess, nblk(nc, kT), kT, 0, st, nx, ny, (const double *)T->rhs, bu, bv,
+                        (const double *)N->dpart, kRedBlocks, (const float *)N->out, T->phi));
+    }
+    {
+        WEC_PROF("net_guess", -1, 8.0 * nc * 5, st);
+        WEC_CK(launch_k(k_guess_resid, kRedBlocks, kT, 0, st, nx, ny, (const double *)T->rhs, bu, bv,
+                        (const double *)T->phi, N->dpart + kRedBlocks));
+    }
+    {
+        WEC_PROF("net_guess", -1, 8.0 * nc, st);
+        WEC_CK(launch_k(k_guess_select, nblk(nc, kT), kT, 0, st, nc, (const double *)N->dpart,
+                        (const double *)(N->dpart + kRedBlocks), kRedBlocks, T->phi, T->net_stats));
+    }
+    return WEC_OK;
+}
+
+}  // namespace wec
+
+using namespace wec;
+
+extern "C" {
+
+size_t wec_net_param_count(void) { return net_param_count(); }
+
+int wec_net_create(int H, int W, int max_batch, void *cuda_stream, wec_net **out)
+{
+    if (!out) return fail(WEC_ERR_INVALID, "net_create: out is NULL");
+    *out = nullptr;
+    if (H < 8 || W < 8 || H % 8 || W % 8 || max_batch < 1)
+        return fail(WEC_ERR_INVALID, "net_create: H, W must be multiples of 8 (>= 8) and max_batch >= 1");
+    if ((long long)H * W * max_batch > (1LL << 26))
+        return fail(WEC_ERR_INVALID, "net_create: max_batch * H * W above 2^26 pixels");
+    wec_net *N = new (std::nothrow) wec_net();
+    if (!N) return fail(WEC_ERR_NOMEM, "net_create: host allocation failed");
+    N->H = H;
+    N->W = W;
+    N->maxb = max_batch;
+    N->st = (cudaStream_t)cuda_stream;
+    N->nparam = net_param_count();
+    size_t nw = 0, off = 0;
+    for (int L = 0; L < kNumLayers; ++L) {
+        N->flat[L] = off;
+        off += weight_count(L) + kLayers[L].co;
+        if (L == kHead) break;
+        N->wf[L] = nw;
+        nw += (size_t)round_up(fwd_K(L), kBK) * kLayers[L].co;
+        nw = round_up_z(nw, 64);
+        N->wb[L] = nw;
+        nw += weight_count(L);
+        nw = round_up_z(nw, 64);
+    }
+    const size_t P0 = (size_t)max_batch * H * W;
+    auto pix = [&](int l) { return P0 >> (2 * l); };
+    size_t part_n = 0;
+    for (int L = 0; L < kHead; ++L) {
+        int cps = 0;
+        const int s = wgrad_splits((long long)pix(kLayers[L].level), L, &cps);
+        part_n = std::max(part_n, (size_t)s * round_up(fwd_K(L), kBM) * kLayers[L].co);
+    }
+    int r = WEC_OK;
+    auto A = [&](void **p, size_t bytes) {
+        if (!r) r = net_alloc(N, p, bytes);
+    };
+    A((void **)&N->theta, 4 * N->nparam);
+    A((void **)&N->grad, 4 * N->nparam);
+    A((void **)&N->am, 4 * N->nparam);
+    A((void **)&N->av, 4 * N->nparam);
+    A((void **)&N->wmat, 2 * nw);
+    A((void **)&N->xin, 2 * P0 * kInPad);
+    for (int L = 0; L < kHead; ++L) A((void **)&N->act[L], 2 * pix(kLayers[L].level) * kLayers[L].co);
+    A((void **)&N->out, 4 * P0);
+    for (int l = 0; l < 4; ++l) {
+        A((void **)&N->gA[l], 2 * pix(l) * chans(l));
+        A((void **)&N->gB[l], 2 * pix(l) * chans(l));
+        if (l < 3) A((void **)&N->skip[l], 2 * pix(l) * chans(l));
+    }
+    A((void **)&N->tmpf, 4 * P0 * 64);
+    A((void **)&N->part, 4 * part_n);
+    A((void **)&N->cpart, 4 * (size_t)std::max(kCsumBlocks * 256, nblk((long long)P0, kT) * kHeadVals));
+    A((void **)&N->xb, 4 * P0 * kInCh);
+    A((void **)&N->tb, 4 * P0);
+    A((void **)&N->loss, 8);
+    A((void **)&N->dpart, 8 * 2 * kRedBlocks);
+    N->part_n = part_n;
+    if (!r) {
+        cudaError_t ce = cudaMallocHost((void **)&N->lossh, 8);
+        if (ce != cudaSuccess) r = cuda_fail(ce, "net_create: pinned allocation");
+    }
+    if (!r) {
+        cudaError_t ce = cudaMemsetAsync(N->theta, 0, 4 * N->nparam, N->st);
+        if (ce == cudaSuccess) ce = cudaMemsetAsync(N->grad, 0, 4 * N->nparam, N->st);
+        if (ce == cudaSuccess) ce = cudaMemsetAsync(N->am, 0, 4 * N->nparam, N->st);
+        if (ce == cudaSuccess) ce = cudaMemsetAsync(N->av, 0, 4 * N->nparam, N->st);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(N->st);
+        if (ce != cudaSuccess) r = cuda_fail(ce, "net_create: initialisation");
+    }
+    if (r) {
+        net_free(N);
+        return r;
+    }
+    *out = N;
+    return WEC_OK;
+}
+
+void wec_net_destroy(wec_net *N) { net_free(N); }
+
+int wec_net_set_params(wec_net *N, const float *host, size_t n)
+{
+    if (!N || !host) return fail(WEC_ERR_INVALID, "net_set_params: NULL argument");
+    if (n != N->nparam) return fail(WEC_ERR_INVALID, "net_set_params: n must equal wec_net_param_count()");
+    for (size_t k = 0; k < n; ++k)
+        if (!std::isfinite(host[k])) return fail(WEC_ERR_INVALID, "net_set_params: non-finite parameter");
+    WEC_CK(cudaMemcpyAsync(N->theta, host, 4 * n, cudaMemcpyHostToDevice, N->st));
+    WEC_CK(cudaMemsetAsync(N->am, 0, 4 * n, N->st));
+    WEC_CK(cudaMemsetAsync(N->av, 0, 4 * n, N->st));
+    WEC_CK(cudaStreamSynchronize(N->st));
+    N->adam_t = 0;
+    N->wdirty = true;
+    return WEC_OK;
+}
+
+static int copy_out(const wec_net *N, const float *src, float *host, size_t n, const char *what)
+{
+    if (!N || !host) return fail(WEC_ERR_INVALID, std::string(what) + ": NULL argument");
+    if (n != N->nparam) return fail(WEC_ERR_INVALID, std::string(what) + ": n must equal wec_net_param_count()");
+    WEC_CK(cudaMemcpyAsync(host, src, 4 * n, cudaMemcpyDeviceToHost, N->st));
+    WEC_CK(cudaStreamSynchronize(N->st));
+    return WEC_OK;
+}
+
+int wec_net_get_params(const wec_net *N, float *host, size_t n)
+{
+    return copy_out(N, N ? N->theta : nullptr, host, n, "net_get_params");
+}
+
+int wec_net_get_grads(const wec_net *N, float *host, size_t n)
+{
+    return copy_out(N, N ? N->grad : nullptr, host, n, "net_get_grads");
+}
+
+int wec_net_get_activation(const wec_net *N, int layer, int batch, unsigned short *host, size_t n)
+{
+    if (!N || !host) return fail(WEC_ERR_INVALID, "net_get_activation: NULL argument");
+    if (layer < 0 || layer >= kHead || batch < 1 || batch > N->maxb)
+        return fail(WEC_ERR_INVALID, "net_get_activation: layer outside [0, 19] or batch outside [1, max_batch]");
+    const LayerDef &d = kLayers[layer];
+    const size_t want = (size_t)batch * level_h(N, d.level) * level_w(N, d.level) * d.co;
+    if (n != want) return fail(WEC_ERR_INVALID, "net_get_activation: n does not match the layer's tensor");
+    WEC_CK(cudaMemcpyAsync(host, N->act[layer], 2 * n, cudaMemcpyDeviceToHost, N->st));
+    WEC_CK(cudaStreamSynchronize(N->st));
+    return WEC_OK;
+}
+
+int wec_net_forward(wec_net *N, int batch, const float *x, float *out)
+{
+    if (!N || !x || !out) return fail(WEC_ERR_INVALID, "net_forward: NULL argument");
+    if (batch < 1 || batch > N->maxb) return fail(WEC_ERR_INVALID, "net_forward: batch outside [1, max_batch]");
+    if (int r = forward(N, batch, x, out, nullptr)) return r;
+    WEC_CK(cudaStreamSynchronize(N->st));
+    return WEC_OK;
+}
+
+int wec_net_loss_grad(wec_net *N, int batch, const float *x, const float *target, double *loss)
+{
+    if (!N || !x || !target || !loss) return fail(WEC_ERR_INVALID, "net_loss_grad: NULL argument");
+    if (batch < 1 || batch > N->maxb) return fail(WEC_ERR_INVALID, "net_loss_grad: batch outside [1, max_batch]");
+    if (int r = forward(N, batch, x, N->out, target)) return r;
+    if (int r = backward(N, batch)) return r;
+    WEC_CK(cudaMemcpyAsync(N->lossh, N->loss, 8, cudaMemcpyDeviceToHost, N->st));
+    WEC_CK(cudaStreamSynchronize(N->st));
+    *loss = *N->lossh;
+    return std::isfinite(*loss) ? WEC_OK : fail(WEC_ERR_NONFINITE, "net_loss_grad: non-finite loss");
+}
+
+int wec_net_adam(wec_net *N, float lr)
+{
+    if (!N) return fail(WEC_ERR_INVALID, "net_adam: NULL net");
+    if (!(lr > 0.0f) || !std::isfinite(lr)) return fail(WEC_ERR_INVALID, "net_adam: lr must be finite and > 0");
+    N->adam_t += 1;
+    const float b1t = (float)(1.0 - std::pow(0.9, (double)N->adam_t));
+    const float b2t = (float)(1.0 - std::pow(0.999, (double)N->adam_t));
+    {
+        WEC_PROF("net_adam", -1, 4.0 * 7 * N->nparam, N->st);
+        WEC_CK(launch_k(k_adam, nblk((long long)N->nparam, kT), kT, 0, N->st, N->theta, (const float *)N->grad, N->am,
+                        N->av, (long long)N->nparam, lr, b1t, b2t));
+    }
+    N->wdirty = true;
+    return WEC_OK;
+}
+
+int wec_net_train_step(wec_net *N, const float *xs, const float *ts, const int *idx, int batch, float lr,
+                       double *loss)
+{
+    if (!N || !xs || !ts || !idx || !loss) return fail(WEC_ERR_INVALID, "net_train_step: NULL argument");
+    if (batch < 1 || batch > N->maxb) return fail(WEC_ERR_INVALID, "net_train_step: batch outside [1, max_batch]");
+    const size_t px = (size_t)N->H * N->W;
+    for (int b = 0; b < batch; ++b) {
+        if (idx[b] < 0) return fail(WEC_ERR_INVALID, "net_train_step: negative sample index");
+        WEC_CK(cudaMemcpyAsync(N->xb + b * px * kInCh, xs + (size_t)idx[b] * px * kInCh, 4 * px * kInCh,
+                               cudaMemcpyDeviceToDevice, N->st));
+        WEC_CK(cudaMemcpyAsync(N->tb + b * px, ts + (size_t)idx[b] * px, 4 * px, cudaMemcpyDeviceToDevice, N->st));
+    }
+    if (int r = wec_net_loss_grad(N, batch, N->xb, N->tb, loss)) return r;
+    return wec_net_adam(N, lr);
+}
+
+int wec_net_sample(wec_tank *T, float *x, float *t)
+{
+    if (!T || !x || !t) return fail(WEC_ERR_INVALID, "net_sample: NULL argument");
+    if (!T->stepped) return fail(WEC_ERR_INVALID, "net_sample: the tank has not stepped yet");
+    const int nx = T->P.nx, ny = T->P.ny, nc = nx * ny;
+    cudaStream_t st = T->gst;
+    {
+        WEC_PROF("net_features", -1, 8.0 * nc, st);
+        WEC_CK(launch_k(k_feat_bsum, kRedBlocks, kT, 0, st, (const double *)T->rhs, nc, T->part));
+    }
+    {
+        WEC_PROF("net_features", -1, 8.0 * nc * 6 + 12.0 * nc, st);
+        WEC_CK(launch_k(k_features, nblk(nc, kT), kT, 0, st, nx, ny, (const double *)T->rhs,
+                        (const double *)T->solver.L64[0].bu, (const double *)T->solver.L64[0].bv,
+                        (const double *)T->inp, T->P.rho_w, (const double *)T->part, kRedBlocks,
+                        (const double *)T->phi, x, t));
+    }
+    WEC_CK(cudaStreamSynchronize(st));
+    return WEC_OK;
+}
+
+int wec_tank_set_net(wec_tank *T, wec_net *N)
+{
+    if (!T) return fail(WEC_ERR_INVALID, "tank_set_net: NULL tank");
+    if (N && (N->H != T->P.ny || N->W != T->P.nx))
+        return fail(WEC_ERR_INVALID, "tank_set_net: the net's H x W must be the tank's ny x nx");
+    if (!T->inp_owned) return fail(WEC_ERR_INVALID, "tank_set_net: tanks of a batch take no net");
+    if (N)
+        if (int r = net_sync_weights(N)) return r;
+    if (!T->net_stats) {
+        WEC_CK(cudaMalloc(&T->net_stats, 2 * sizeof(long long)));
+        WEC_CK(cudaMemsetAsync(T->net_stats, 0, 2 * sizeof(long long), T->gst));
+        WEC_CK(cudaStreamSynchronize(T->gst));
+    }
+    WEC_CK(cudaStreamSynchronize(T->gst));
+    if (T->exec) cudaGraphExecDestroy(T->exec);
+    if (T->graph) cudaGraphDestroy(T->graph);
+    T->exec = nullptr;
+    T->graph = nullptr;
+    T->net = N;
+    return WEC_OK;
+}
+
+int wec_tank_net_stats(const wec_tank *T, long long *tried, long long *kept)
+{
+    if (!T || !tried || !kept) return fail(WEC_ERR_INVALID, "tank_net_stats: NULL argument");
+    long long h[2] = {0, 0};
+    if (T->net_stats) {
+        WEC_CK(cudaMemcpyAsync(h, T->net_stats, sizeof(h), cudaMemcpyDeviceToHost, T->gst));
+        WEC_CK(cudaStreamSynchronize(T->gst));
+    }
+    *tried = h[0];
+    *kept = h[1];
+    return WEC_OK;
+}
+
+}  // extern "C"

@@ -93,6 +93,26 @@ def tank_large(seed=0, nx=1024, ny=256, **solver_kw):
     return c
 
 
+def tank_learned(seed=0, nx=512, ny=256, **solver_kw):
+    """Training tanks of the learned warm start: the 1024x256 JONSWAP physics
+    (h = 1/64 m, depth 2.5 m, box 1 m x 0.8 m at half draft) on an 8 m x 4 m
+    tank, 512x256, with the sea state drawn from the seed (Hs in 0.1..0.2 m, Tp
+    in 1.2..1.8 s, 64 components).  Damping zone over the last 2 m; box at x = 3 m."""
+    rng = np.random.default_rng(seed)
+    c = _base(nx, ny, 8.0, 4.0, 2.5)
+    Hs = float(rng.uniform(0.1, 0.2))
+    Tp = float(rng.uniform(1.2, 1.8))
+    c["wave"] = irregular_wave(Hs, Tp, 3.3, 64, rng)
+    c["damp_len"] = 2.0
+    c["damp_x0"] = 6.0
+    c["probe_x"] = 1.0
+    c["body"] = box_body(3.0, 1.0, 0.8, 0.4, 2.5, c["rho_w"], pto_damping=0.0)
+    c["solver"] = _solver(**solver_kw)
+    c["dt"], c["steps"] = 5e-4, 2000
+    c["name"] = f"tank {nx}x{ny} 8mx4m JONSWAP Hs={Hs:.3f} Tp={Tp:.3f} box"
+    return c
+
+
 def still_water(nx=64, ny=32, body=False, seed=0, **solver_kw):
     """Still water (H=0) in a 4 m x 2 m tank; optional box at its floating draft."""
     rng = np.random.default_rng(seed)

@@ -125,6 +125,22 @@ def load():
     L.wec_wave_number_fenton_kd.restype = C.c_double
     L.wec_wave_number_fenton_kd.argtypes = [C.c_double, C.c_double, C.c_double]
     L.wec_jonswap.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int, _dp, _dp]
+    _fp = C.POINTER(C.c_float)
+    L.wec_net_param_count.restype = C.c_size_t
+    L.wec_net_create.argtypes = [C.c_int, C.c_int, C.c_int, vp, C.POINTER(vp)]
+    L.wec_net_destroy.argtypes = [vp]
+    L.wec_net_destroy.restype = None
+    L.wec_net_set_params.argtypes = [vp, _fp, C.c_size_t]
+    L.wec_net_get_params.argtypes = [vp, _fp, C.c_size_t]
+    L.wec_net_get_grads.argtypes = [vp, _fp, C.c_size_t]
+    L.wec_net_get_activation.argtypes = [vp, C.c_int, C.c_int, C.POINTER(C.c_uint16), C.c_size_t]
+    L.wec_net_forward.argtypes = [vp, C.c_int, vp, vp]
+    L.wec_net_loss_grad.argtypes = [vp, C.c_int, vp, vp, _dp]
+    L.wec_net_adam.argtypes = [vp, C.c_float]
+    L.wec_net_train_step.argtypes = [vp, vp, vp, C.POINTER(C.c_int), C.c_int, C.c_float, _dp]
+    L.wec_net_sample.argtypes = [vp, vp, vp]
+    L.wec_tank_set_net.argtypes = [vp, vp]
+    L.wec_tank_net_stats.argtypes = [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
     _lib = L
     return L
 
@@ -144,6 +160,14 @@ def _dev(t):
     import torch
     if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
         raise TypeError("expected a contiguous float64 CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _dev32(t):
+    """Device pointer of a contiguous float32 CUDA tensor."""
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise TypeError("expected a contiguous float32 CUDA tensor")
     return C.c_void_p(t.data_ptr())
 
 
@@ -282,6 +306,15 @@ class Tank:
         _check(load().wec_step_n(self.h, n, dt, p, out))
         return [r.as_dict() for r in out] if records else None
 
+    def set_net(self, net):
+        self._net = net  # keep it alive while set
+        _check(load().wec_tank_set_net(self.h, None if net is None else net.h))
+
+    def net_stats(self):
+        a, b = C.c_longlong(0), C.c_longlong(0)
+        _check(load().wec_tank_net_stats(self.h, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
     def pressure_solve(self, rhs, p, rtol):
         it = C.c_int(0)
         rr = C.c_double(0)
@@ -358,6 +391,70 @@ class Nlfk:
             self.h = None
 
     __del__ = close
+
+
+class Net:
+    """The learned warm start's U-Net (wec_net_create ... wec_net_destroy).
+    Inputs and targets are float32 CUDA tensors: x [batch, H, W, 2], target and
+    output [batch, H, W]; parameters are host float32 vectors."""
+
+    def __init__(self, H, W, max_batch=1, stream=None):
+        h = C.c_void_p()
+        _check(load().wec_net_create(H, W, max_batch, _stream(stream), C.byref(h)))
+        self.h, self.H, self.W, self.max_batch = h, H, W, max_batch
+        self.n = int(load().wec_net_param_count())
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().wec_net_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def set_params(self, flat):
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        _check(load().wec_net_set_params(self.h, a.ctypes.data_as(C.POINTER(C.c_float)), a.size))
+
+    def _get(self, fn):
+        a = np.empty(self.n, dtype=np.float32)
+        _check(fn(self.h, a.ctypes.data_as(C.POINTER(C.c_float)), a.size))
+        return a
+
+    def params(self):
+        return self._get(load().wec_net_get_params)
+
+    def grads(self):
+        return self._get(load().wec_net_get_grads)
+
+    def activation(self, layer, batch, shape):
+        """Layer output of the last forward pass as float32 [batch, h, w, c]."""
+        a = np.empty(int(np.prod(shape)), dtype=np.uint16)
+        _check(load().wec_net_get_activation(self.h, layer, batch, a.ctypes.data_as(C.POINTER(C.c_uint16)), a.size))
+        return (a.astype(np.uint32) << 16).view(np.float32).reshape(shape)
+
+    def forward(self, x, out):
+        _check(load().wec_net_forward(self.h, x.shape[0], _dev32(x), _dev32(out)))
+
+    def loss_grad(self, x, target):
+        loss = C.c_double(0)
+        _check(load().wec_net_loss_grad(self.h, x.shape[0], _dev32(x), _dev32(target), C.byref(loss)))
+        return loss.value
+
+    def adam(self, lr):
+        _check(load().wec_net_adam(self.h, lr))
+
+    def train_step(self, xs, ts, idx, lr):
+        i = np.ascontiguousarray(idx, dtype=np.int32)
+        loss = C.c_double(0)
+        _check(load().wec_net_train_step(self.h, _dev32(xs), _dev32(ts), i.ctypes.data_as(C.POINTER(C.c_int)),
+                                         i.size, lr, C.byref(loss)))
+        return loss.value
+
+
+def net_sample(tank, x, t):
+    """Features x [ny, nx, 2] and target t [ny, nx] (float32 CUDA tensors) of the
+    tank's last pressure problem."""
+    _check(load().wec_net_sample(tank.h, _dev32(x), _dev32(t)))
 
 
 class Batch:

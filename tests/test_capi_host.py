@@ -157,3 +157,20 @@ def test_nlfk_create_validates_on_host(lib, bad):
         wec.WEC_ERR_INVALID
     assert not h.value
     assert b"nlfk" in lib.wec_last_error()
+
+
+def test_net_matches_the_oracle_layout_and_validates_on_host(lib):
+    # the parameter vector has the oracle's layout size; bad sizes and NULLs
+    # are rejected before any device work
+    from oracle import unet as U
+    assert lib.wec_net_param_count() == sum(int(np.prod(s)) for s in U.param_shapes(32))
+    h = C.c_void_p()
+    for H, W, b in ((12, 16, 1), (16, 4, 1), (16, 16, 0), (0, 8, 1), (8192, 8192, 2)):
+        assert lib.wec_net_create(H, W, b, None, C.byref(h)) == wec.WEC_ERR_INVALID
+        assert not h.value
+    assert lib.wec_net_create(16, 16, 1, None, None) == wec.WEC_ERR_INVALID
+    assert lib.wec_net_forward(None, 1, None, None) == wec.WEC_ERR_INVALID
+    assert lib.wec_net_adam(None, C.c_float(1e-3)) == wec.WEC_ERR_INVALID
+    assert lib.wec_tank_set_net(None, None) == wec.WEC_ERR_INVALID
+    assert lib.wec_net_sample(None, None, None) == wec.WEC_ERR_INVALID
+    lib.wec_net_destroy(None)

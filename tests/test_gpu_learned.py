@@ -1,0 +1,87 @@
+"""The learned warm start end to end: pressure problems generated by the tank
+itself (the 8 m x 4 m JONSWAP tanks, 512x256), the U-Net trained on them on the
+GPU by the library's own kernels, and the trained network used as the initial
+guess of held-out runs.  The FP64 residual judges the guess: the solve still
+reaches rtol, and the guess is dropped (phi0 = 0) when it is worse than zero.
+What the network gains is printed and bounded."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import unet as U  # noqa: E402
+from paper_2206_07732_gb300 import build as B  # noqa: E402
+from paper_2206_07732_gb300 import synth  # noqa: E402
+from paper_2206_07732_gb300 import wec  # noqa: E402
+
+NX, NY = 512, 256
+
+
+@pytest.fixture(scope="module")
+def trained():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    B.build()
+    wec.load()
+    per, skip = 240, 40
+    seeds = (11, 12, 13)
+    xs = torch.zeros((per * len(seeds), NY, NX, 2), dtype=torch.float32, device="cuda")
+    ts = torch.zeros((per * len(seeds), NY, NX), dtype=torch.float32, device="cuda")
+    k = 0
+    for s in seeds:
+        cfg = synth.tank_learned(seed=s)
+        t = wec.Tank(cfg, precision=wec.PREC_FP64)
+        t.step_n(skip, cfg["dt"], records=False)
+        for _ in range(per):
+            t.step(cfg["dt"])
+            wec.net_sample(t, xs[k], ts[k])
+            k += 1
+        t.close()
+    net = wec.Net(NY, NX, max_batch=4)
+    net.set_params(synth.unet_weights(U.param_shapes(32), 0))
+    rng = np.random.default_rng(0)
+    losses = []
+    for it in range(1500):
+        lr = 1e-3 if it < 1000 else 3e-4
+        losses.append(net.train_step(xs, ts, rng.integers(0, k, 4), lr))
+    return net, losses
+
+
+def _run(cfg, net, n):
+    t = wec.Tank(cfg, precision=wec.PREC_FP64)
+    if net is not None:
+        t.set_net(net)
+    recs = t.step_n(n, cfg["dt"])
+    stats = t.net_stats() if net is not None else (0, 0)
+    t.close()
+    return recs, stats
+
+
+def test_training_converges(trained):
+    _, losses = trained
+    first, last = np.mean(losses[:50]), np.mean(losses[-100:])
+    print(f"training loss: first 50 steps {first:.4f}, last 100 steps {last:.4f}")
+    assert last < 0.5 * first
+
+
+def test_trained_guess_on_held_out_runs(trained):
+    net, _ = trained
+    cfg = synth.tank_learned(seed=99)
+    cfg["solver"]["rtol"] = 1e-8
+    n = 200
+    plain, _ = _run(cfg, None, n)
+    learned, (tried, kept) = _run(cfg, net, n)
+    ip = np.array([r["iters"] for r in plain])
+    il = np.array([r["iters"] for r in learned])
+    print(f"held-out 512x256 run, {n} steps: FGMRES iterations per step plain {ip.mean():.2f}, "
+          f"with the learned guess {il.mean():.2f}; guess kept in {kept} of {tried} steps")
+    assert tried == n
+    assert all(r["residual"] <= 1e-8 for r in learned)  # the FP64 residual still decides
+    # the fallback bounds the loss; the trained guess is better than zero most of the time
+    assert il.mean() <= ip.mean() + 0.25
+    assert kept >= 0.5 * n
+    # the two runs stay within the solver tolerance of each other
+    zp = np.array([r["z"] for r in plain])
+    zl = np.array([r["z"] for r in learned])
+    assert np.max(np.abs(zp - zl)) <= 1e-6 * max(np.max(np.abs(zp)), 1e-3)
