@@ -4,9 +4,12 @@
 Workload: the 16 m x 4 m tank on a 1024 x 256 grid (depth 2.5 m, JONSWAP Hs 0.15 m,
 Tp 1.6 s, gamma 3.3, 64 seeded components, heaving 1 m x 0.8 m box, dt 5e-4 s).
 A step is one wec_step: force, heave, level set, momentum, pressure solve,
-projection.  Our arm runs the mixed-precision path (FP32 stencil arithmetic
-and FP32 multigrid V-cycles over FP64 storage, FP64 FGMRES, force and heave)
-and, beside it, the plain FP64 path on the same GPU.
+projection.  Our arm's headline is the mixed-precision path (FP32 stencil
+arithmetic and FP32 multigrid V-cycles over FP64 storage, FP64 FGMRES, force
+and heave) with the learned warm start: a BF16 U-Net, trained at the start of
+the run (untimed) on pressure problems of the same tank with other wave
+phases, gives each solve its initial guess.  Beside it: mixed without the
+network, mixed_mg (FP32 V-cycles only) and the plain FP64 path, same GPU.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload tank|batch]
@@ -142,6 +145,19 @@ def peaks():
     return 6800.0, "fallback"
 
 
+def tensor_peak():
+    """Dense BF16 tensor peak: the sustained measurement (kernels timed inside a
+    long step), else the burst one, else the fallback figure."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        if d.get("bf16_tflops_sustained"):
+            return float(d["bf16_tflops_sustained"]), "measured bf16_tflops_sustained"
+        return float(d["bf16_tflops"]), "measured bf16_tflops (burst)"
+    except (OSError, ValueError, KeyError):
+        return 1700.0, "fallback 1.7 PFLOP/s sustained"
+
+
 def source_sha():
     h = hashlib.sha256()
     for f in sorted(glob.glob(os.path.join(ROOT, "paper_2206_07732_gb300", "csrc", "*"))):
@@ -173,12 +189,15 @@ def setup_lib():
 
 
 # ---------------------------------------------------------------- our arm --
-def time_path(L, wec, torch, cfg, precision, steps, warmup, flush, graph=True, profile_kernel=None):
+def time_path(L, wec, torch, cfg, precision, steps, warmup, flush, graph=True, profile_kernel=None, net=None):
     """Time K steps (CUDA events per step on the caller's stream, L2 flushed in
     between).  graph=False with profile_kernel: the eager pass that times one
-    kernel's launches with event pairs (graph bodies cannot hold events)."""
+    kernel's launches with event pairs (graph bodies cannot hold events).
+    net: the trained U-Net giving each solve its initial guess."""
     tank = wec.Tank(cfg, precision=precision)
     tank.use_graph(graph)
+    if net is not None:
+        tank.set_net(net)
     stream = torch.cuda.current_stream()
     for _ in range(warmup):
         tank.step(cfg["dt"])
@@ -210,14 +229,17 @@ def time_path(L, wec, torch, cfg, precision, steps, warmup, flush, graph=True, p
         wec.profile_enable(0)
         prof = wec.profile_read()
     ms = [a.elapsed_time(b) for a, b in ev]
+    stats = tank.net_stats() if net is not None else None
     tank.close()
-    return dict(ms=ms, iters=its, residual=max(res), launches=launches, wall=wall, prof=prof)
+    return dict(ms=ms, iters=its, residual=max(res), launches=launches, wall=wall, prof=prof, net_stats=stats)
 
 
-def profile_all(wec, torch, cfg, precision, steps=2):
+def profile_all(wec, torch, cfg, precision, steps=2, net=None):
     """Untimed eager pass with every launch timed: which kernel dominates."""
     tank = wec.Tank(cfg, precision=precision)
     tank.use_graph(False)
+    if net is not None:
+        tank.set_net(net)
     for _ in range(3):
         tank.step(cfg["dt"])
     torch.cuda.synchronize()
@@ -231,10 +253,12 @@ def profile_all(wec, torch, cfg, precision, steps=2):
     return p
 
 
-def e2e_path(wec, torch, cfg, precision, steps, warmup, flush):
+def e2e_path(wec, torch, cfg, precision, steps, warmup, flush, net=None):
     """Through the public call with host buffers: wec_step takes the host PTO
     force and returns the host step record (synchronous D2H) every step."""
     tank = wec.Tank(cfg, precision=precision)
+    if net is not None:
+        tank.set_net(net)
     for _ in range(warmup):
         tank.step(cfg["dt"])
     torch.cuda.synchronize()
@@ -339,6 +363,43 @@ def main_batch(args):
         torch.distributed.destroy_process_group()
 
 
+def train_learned(wec, torch, cfg, seed, per_seed=120, skip=40, iters=800, batch=4):
+    """The learned warm start's network, trained (untimed) on the pressure
+    problems of mixed-precision runs of the same tank with other wave phases
+    (seeds seed+1, seed+2): features and targets from wec_net_sample, Adam
+    on batches of 4 drawn from them."""
+    from paper_2206_07732_gb300 import synth
+    t0 = time.perf_counter()
+    ny, nx = cfg["ny"], cfg["nx"]
+    seeds = (seed + 1, seed + 2)
+    xs = torch.zeros((per_seed * len(seeds), ny, nx, 2), dtype=torch.float32, device="cuda")
+    ts = torch.zeros((per_seed * len(seeds), ny, nx), dtype=torch.float32, device="cuda")
+    k = 0
+    for s in seeds:
+        c = workload(s)
+        tank = wec.Tank(c, precision=wec.PREC_MIXED)
+        tank.step_n(skip, c["dt"], records=False)
+        for _ in range(per_seed):
+            tank.step(c["dt"])
+            wec.net_sample(tank, xs[k], ts[k])
+            k += 1
+        tank.close()
+    t1 = time.perf_counter()
+    net = wec.Net(ny, nx, max_batch=batch)
+    net.set_params(synth.unet_weights(wec.net_param_shapes(), seed))
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    losses = [net.train_step(xs, ts, rng.integers(0, k, batch), 1e-3 if it < 0.7 * iters else 3e-4)
+              for it in range(iters)]
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    del xs, ts
+    info = {"samples": k, "sample_seeds": list(seeds), "iterations": iters, "batch": batch,
+            "loss_first_50": float(np.mean(losses[:50])), "loss_last_50": float(np.mean(losses[-50:])),
+            "sampling_s": t1 - t0, "training_s": t2 - t1, "ms_per_training_step": (t2 - t1) / iters * 1e3}
+    return net, info
+
+
 def main_ours(args):
     import torch
     rank = int(os.environ.get("RANK", "0"))
@@ -353,8 +414,13 @@ def main_ours(args):
     if args.ncu_steps:
         # one-by-one launches: ncu cannot profile kernel nodes of graphs with
         # conditional nodes (same kernels, same order as the graph)
+        # the headline path's kernels: an untrained network runs the same work
+        from paper_2206_07732_gb300 import synth
+        net = wec.Net(cfg["ny"], cfg["nx"], max_batch=1)
+        net.set_params(synth.unet_weights(wec.net_param_shapes(), args.seed))
         tank = wec.Tank(cfg, precision=wec.PREC_MIXED)
         tank.use_graph(False)
+        tank.set_net(net)
         for _ in range(max(args.warmup, 1) + args.ncu_steps):
             tank.step(cfg["dt"])
         torch.cuda.synchronize()
@@ -362,8 +428,11 @@ def main_ours(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 256 MiB > L2
     steps, warmup = args.steps, max(args.warmup, 3)
 
-    # which kernel dominates the mixed path (untimed, eager, every launch timed)
-    prof_all = profile_all(wec, torch, cfg, wec.PREC_MIXED)
+    # the learned warm start's network, trained on runs of the same tank (untimed)
+    net, train_info = train_learned(wec, torch, cfg, args.seed)
+
+    # which kernel dominates the headline path (untimed, eager, every launch timed)
+    prof_all = profile_all(wec, torch, cfg, wec.PREC_MIXED, net=net)
     by_name = {}
     for p in prof_all:
         d = by_name.setdefault(p["name"], dict(ms=0.0, bytes=0.0, launches=0))
@@ -380,13 +449,14 @@ def main_ours(args):
 
     clocks = Clocks(local)
     clocks.start()
-    mixed = time_path(L, wec, torch, cfg, wec.PREC_MIXED, steps, warmup, flush)
+    learned = time_path(L, wec, torch, cfg, wec.PREC_MIXED, steps, warmup, flush, net=net)
     ck = clocks.stop()
+    mixed = time_path(L, wec, torch, cfg, wec.PREC_MIXED, steps, warmup, flush)
     fp64 = time_path(L, wec, torch, cfg, wec.PREC_FP64, steps, warmup, flush)
     mixed_mg = time_path(L, wec, torch, cfg, wec.PREC_MIXED_MG, steps, warmup, flush)
     kpass = time_path(L, wec, torch, cfg, wec.PREC_MIXED, max(steps // 4, 5), warmup, flush, graph=False,
-                      profile_kernel=top)
-    e2e = e2e_path(wec, torch, cfg, wec.PREC_MIXED, max(steps // 2, 5), warmup, flush)
+                      profile_kernel=top, net=net)
+    e2e = e2e_path(wec, torch, cfg, wec.PREC_MIXED, max(steps // 2, 5), warmup, flush, net=net)
 
     def reduce_max(x):
         if world == 1:
@@ -395,11 +465,13 @@ def main_ours(args):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         return float(t.item())
 
+    t_learned = reduce_max(sum(learned["ms"]) / 1e3)
     t_mixed = reduce_max(sum(mixed["ms"]) / 1e3)
     t_fp64 = reduce_max(sum(fp64["ms"]) / 1e3)
     t_mg = reduce_max(sum(mixed_mg["ms"]) / 1e3)
     t_e2e = reduce_max(sum(e2e))
-    value = world * n * steps / t_mixed
+    value = world * n * steps / t_learned
+    mixed_value = world * n * steps / t_mixed
     fp64_value = world * n * steps / t_fp64
     e2e_value = world * n * len(e2e) / t_e2e
 
@@ -407,21 +479,41 @@ def main_ours(args):
     peak, peak_kind = peaks()
     pk = [p for p in (kpass["prof"] or []) if p["name"] == top]
     tot_ms = sum(p["ms"] for p in pk)
-    tot_b = sum(p["bytes"] for p in pk)
     nl = sum(p["launches"] for p in pk)
-    achieved = (tot_b / nl) / (tot_ms / nl / 1e3) / 1e9 if nl and tot_ms > 0 else None
-    share = by_name[top]["ms"] / sum(d["ms"] for d in by_name.values())
+    share = by_name[top]["ms"] / tot_prof
     lvl = {}
-    for p in pk:
-        lvl[str(p["level"])] = {"launches": p["launches"], "avg_us": p["ms"] / p["launches"] * 1e3,
-                                "GBps": p["bytes"] / (p["ms"] / 1e3) / 1e9 if p["ms"] > 0 else None}
-    roofline = {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": (achieved / peak) if achieved else None,
-                "traffic": ncu_traffic(top), "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
-                "algorithmic_bytes_per_launch": (tot_b / nl) if nl else None,
-                "launches_timed": nl, "avg_launch_us": (tot_ms / nl * 1e3) if nl else None,
-                "share_of_step_gpu_time": share, "per_level": lvl,
-                "timing": "event pair per launch of this kernel over an eager pass of the same steps"}
+    if top == "net_conv":
+        # tensor-bound: algorithmic FLOPs of each layer's forward GEMM (profile level = layer)
+        fl = wec.net_layer_flops(cfg["ny"], cfg["nx"])
+        tot_f = sum(fl[p["level"]] * p["launches"] for p in pk if p["level"] < 100)
+        tot_fm = sum(p["ms"] for p in pk if p["level"] < 100)
+        nf = sum(p["launches"] for p in pk if p["level"] < 100)
+        achieved = tot_f / (tot_fm / 1e3) / 1e12 if tot_fm > 0 else None
+        tpeak, tkind = tensor_peak()
+        for p in pk:
+            lvl[str(p["level"])] = {"launches": p["launches"], "avg_us": p["ms"] / p["launches"] * 1e3,
+                                    "TFLOPs": (fl[p["level"]] / (p["ms"] / p["launches"] / 1e3) / 1e12)
+                                    if p["level"] < 100 and p["ms"] > 0 else None}
+        roofline = {"bound": "tensor", "kernel": top, "achieved": achieved, "peak": tpeak, "unit": "TFLOP/s",
+                    "frac": (achieved / tpeak) if achieved else None, "traffic": ncu_traffic(top),
+                    "peak_source": f"{tkind} (MEASURED_PEAKS.json)",
+                    "algorithmic_flops_per_launch": (tot_f / nf) if nf else None,
+                    "launches_timed": nf, "avg_launch_us": (tot_fm / nf * 1e3) if nf else None,
+                    "share_of_step_gpu_time": share, "per_layer": lvl,
+                    "timing": "event pair per launch of this kernel over an eager pass of the same steps"}
+    else:
+        tot_b = sum(p["bytes"] for p in pk)
+        achieved = (tot_b / nl) / (tot_ms / nl / 1e3) / 1e9 if nl and tot_ms > 0 else None
+        for p in pk:
+            lvl[str(p["level"])] = {"launches": p["launches"], "avg_us": p["ms"] / p["launches"] * 1e3,
+                                    "GBps": p["bytes"] / (p["ms"] / 1e3) / 1e9 if p["ms"] > 0 else None}
+        roofline = {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": (achieved / peak) if achieved else None,
+                    "traffic": ncu_traffic(top), "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
+                    "algorithmic_bytes_per_launch": (tot_b / nl) if nl else None,
+                    "launches_timed": nl, "avg_launch_us": (tot_ms / nl * 1e3) if nl else None,
+                    "share_of_step_gpu_time": share, "per_level": lvl,
+                    "timing": "event pair per launch of this kernel over an eager pass of the same steps"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -429,29 +521,37 @@ def main_ours(args):
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{k} oracle steps of the 1024x256 tank from its initial state ({el:.1f} s, 1 thread)"}
 
+    tried, kept = learned["net_stats"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": warmup,
-        "ms_per_step": t_mixed / steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64+f32(stencils,multigrid)", "data": "synthetic (seeded JONSWAP phases)",
-        "config": config_dict(cfg, "mixed: FP32 stencils and V-cycles, FP64 storage/FGMRES/force/heave", "flushed between timed steps (256 MiB write)"),
+        "ms_per_step": t_learned / steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64+f32(stencils,multigrid)+bf16(U-Net)", "data": "synthetic (seeded JONSWAP phases)",
+        "config": config_dict(cfg, "mixed + learned: FP32 stencils and V-cycles, FP64 storage/FGMRES/force/heave, "
+                                   "BF16 U-Net initial guess of each solve", "flushed between timed steps (256 MiB write)"),
         "fp64_value": fp64_value, "fp64_ms_per_step": t_fp64 / steps * 1e3,
-        "speedup_mixed_vs_fp64": value / fp64_value,
+        "speedup_vs_fp64": value / fp64_value,
+        "mixed_value": mixed_value, "mixed_ms_per_step": t_mixed / steps * 1e3,
+        "speedup_mixed_vs_fp64": mixed_value / fp64_value,
         "mixed_mg_value": world * n * steps / t_mg, "mixed_mg_ms_per_step": t_mg / steps * 1e3,
         "speedup_mixed_mg_vs_fp64": t_fp64 / t_mg,
-        "precision_modes": {"value (mixed)": "FP32 stencil arithmetic and V-cycles over FP64 state; FP64 FGMRES, "
-                                             "residual, force, heave",
+        "precision_modes": {"value (mixed + learned)": "mixed, with the trained U-Net's prediction as each "
+                                                       "solve's initial guess (kept only if its FP64 residual "
+                                                       "is below ||b||)",
+                            "mixed": "FP32 stencil arithmetic and V-cycles over FP64 state; FP64 FGMRES, "
+                                     "residual, force, heave",
                             "mixed_mg": "FP32 V-cycles only; every step stencil FP64",
                             "fp64": "everything FP64"},
-        "learned_warm_start": "not built",
+        "learned_warm_start": {"training": train_info, "guess_kept_steps": kept, "steps_with_net": tried},
         "execution": "one CUDA graph per step (conditional WHILE/IF nodes steer FGMRES on the GPU)",
         "mg_tiles_autotuned": mg_tiles,
-        "fgmres_iters_per_step": {"mixed": statistics.mean(mixed["iters"]), "fp64": statistics.mean(fp64["iters"]),
+        "fgmres_iters_per_step": {"mixed+learned": statistics.mean(learned["iters"]),
+                                  "mixed": statistics.mean(mixed["iters"]), "fp64": statistics.mean(fp64["iters"]),
                                   "mixed_mg": statistics.mean(mixed_mg["iters"])},
-        "max_relative_residual": {"mixed": mixed["residual"], "fp64": fp64["residual"],
-                                  "mixed_mg": mixed_mg["residual"]},
+        "max_relative_residual": {"mixed+learned": learned["residual"], "mixed": mixed["residual"],
+                                  "fp64": fp64["residual"], "mixed_mg": mixed_mg["residual"]},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 16, "d2h_bytes_per_step": 72,
-                "note": "wec_step wall clock: host dt and PTO force in, host step record out, per step"},
-        "gpu_launches": mixed["launches"],
+                "note": "wec_step wall clock (mixed + learned): host dt and PTO force in, host step record out"},
+        "gpu_launches": learned["launches"],
         "clocks": ck,
         "roofline": roofline,
         "kernel_breakdown_eager": breakdown,
@@ -459,6 +559,7 @@ def main_ours(args):
     }
     if rank == 0:
         print(json.dumps(line))
+    net.close()
     if world > 1:
         torch.distributed.destroy_process_group()
 

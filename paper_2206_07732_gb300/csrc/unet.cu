@@ -8,14 +8,13 @@
 // activation tensors into shared memory (16-byte cp.async, zero fill at the
 // image border), so no im2col buffer exists; nearest upsampling, skip
 // concatenation and the stride-2 down convolution are gather modes of the same
-// kernel.  The backward pass uses the same kernel for the input gradients (a
-// 3x3 convolution of the output gradient with the flipped, transposed weights;
-// one 1x1 GEMM per sub-pixel for the stride-2 layer) and a second kernel for
-// the weight gradients (reduction over pixels, split across CTAs, partial tiles
-// summed in a fixed order: results are reproducible bit for bit).  ReLU masks,
-// biases, the skip gradient and the BF16 rounding are fused into the GEMM
-// epilogues.  Tiles: 128 pixels x 32/64 channels x 32 reduction elements,
-// 3-stage cp.async pipeline, 8 warps of m16n8k16 BF16 MMAs.
+// kernel.  Forward and input-gradient GEMMs (a 3x3 convolution of the output
+// gradient with the flipped, transposed weights; one 1x1 GEMM per sub-pixel
+// for the stride-2 layer) run on tcgen05 with the accumulator in tensor memory
+// (k_conv_tc).  Weight gradients reduce over pixels, split across CTAs, with
+// m16n8k16 MMAs (k_wgrad); their partial tiles are summed in a fixed order, so
+// results are reproducible bit for bit.  ReLU masks, biases, the skip gradient
+// and the BF16 rounding are fused into the GEMM epilogues.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -71,7 +70,6 @@ constexpr int kBM = 128;     // GEMM rows (pixels, or weight rows in k_wgrad) pe
 constexpr int kBK = 32;      // reduction elements per pipeline stage
 constexpr int kGT = 256;     // threads (8 warps: 4 along M x 2 along N)
 constexpr int kStages = 3;
-constexpr int kAS = kBK + 8; // shared row stride of the A tile (conflict-free ldmatrix)
 
 enum GatherKind { G_CONV3 = 0, G_UP3 = 1, G_DOWN2 = 2, G_DIRECT = 3 };
 enum EpiKind { E_FWD = 0, E_DX = 1, E_F32 = 2, E_DOWNDX = 3 };
@@ -123,12 +121,6 @@ __device__ __forceinline__ void cp_wait()
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-__device__ __forceinline__ void ldm_x4(unsigned r[4], const void *p)
-{
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(smem_u32(p)));
-}
 __device__ __forceinline__ void ldm_x4_t(unsigned r[4], const void *p)
 {
     asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
@@ -202,108 +194,268 @@ __device__ __forceinline__ void epi_store(const Epi &e, const Gat &g, int p, int
     }
 }
 
-// ---------------------------------------------------------- implicit GEMM --
-// C[p][n] = sum_k A(p, k) B[k][n] over Kpad (a multiple of kBK) for the rows p
-// of the grid and the columns [blockIdx.y BN, +BN) of B (row-major, ldb
-// columns; blockIdx.z selects a matrix bz elements further on), with the fused
-// epilogue.  Grid: (ceil(rows / kBM), columns / BN, sub-pixels).
+// ------------------------------------------------- tcgen05 implicit GEMM --
+// The same convolution GEMM on the 5th-generation tensor cores: one CTA owns a
+// 128-pixel x BN-channel tile whose FP32 accumulator lives in tensor memory.
+// Warps 0-3 gather A (one pixel row each) and B (K-major weights) into shared
+// memory in the no-swizzle K-major core-matrix layout (8 rows x 16 bytes per
+// core matrix; K-adjacent core matrices 128 B apart, 8-row groups 1024 B
+// apart), kTcStages stages of 64 reduction elements; one thread of warp 4
+// issues tcgen05.mma (M = 128, N = BN, K = 16, BF16 x BF16 -> FP32) and
+// signals each consumed stage through tcgen05.commit.  Warps 0-3 then read
+// their 32 TMEM lanes (tcgen05.ld) and run the fused epilogue.  Every wait is
+// bounded: on expiry the kernel raises *err, drains its copies, frees its
+// tensor memory and returns.
+constexpr int kTcStages = 4;
+constexpr int kTcK = 64;               // reduction elements per stage
+constexpr int kTcThreads = 160;        // warps 0-3: producers / epilogue; warp 4: MMA
+constexpr int kTcLag = 2;              // stages a producer keeps in flight before signalling
+constexpr long long kWaitLimit = 1LL << 22;  // polls; far above any legitimate wait here
+
 template <int BN>
-__global__ void __launch_bounds__(kGT) k_conv_gemm(Gat g, const bf16 *__restrict__ B, int ldb, size_t bz, int Kpad,
-                                                   Epi e)
+struct TcSmem {
+    static constexpr int kA = kBM * kTcK * 2;   // 16 KB
+    static constexpr int kB = BN * kTcK * 2;
+    static constexpr int kStage = kA + kB;
+    static constexpr int kBytes = kTcStages * kStage + 256;  // + barriers and the TMEM address
+};
+
+__device__ __forceinline__ void mbar_init(unsigned a, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(a), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned a)
+{
+    asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(a) : "memory");
+}
+// Wait for the phase with the given parity to complete; false after kWaitLimit polls.
+__device__ __forceinline__ bool mbar_wait(unsigned a, unsigned parity)
+{
+    for (long long it = 0; it < kWaitLimit; ++it) {
+        unsigned ok;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ uint64_t umma_desc(unsigned saddr)
+{
+    // start address, K-direction core-matrix stride 128 B, 8-row-group stride
+    // 1024 B (both >> 4), descriptor version 1 (bit 46), no swizzle
+    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           (1ull << 46);
+}
+
+template <int BN>
+__host__ __device__ constexpr unsigned umma_idesc()
+{
+    // kind::f16: D F32 (bits 4-5 = 1), A BF16 (bits 7-9 = 1), B BF16 (bits 10-12 = 1),
+    // both K-major, N >> 3 at bit 17, M >> 4 at bit 24
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(BN >> 3) << 17) | ((unsigned)(kBM >> 4) << 24);
+}
+
+template <int BN>
+__global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(Gat g, const bf16 *__restrict__ B, int Kpad, size_t bz,
+                                                          Epi e, int *err)
 {
     pdl_entry();
-    constexpr int BS = BN + 8;   // shared row stride of the B tile
-    constexpr int WN = BN / 2;   // columns per warp
-    constexpr int NT = WN / 8;   // n8 tiles per warp
-    __shared__ __align__(128) bf16 As[kStages][kBM][kAS];
-    __shared__ __align__(128) bf16 Bs[kStages][kBK][BS];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm = warp & 3, wn = warp >> 2;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    using S = TcSmem<BN>;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    unsigned char *bar_base = smem + kTcStages * S::kStage;
+    const unsigned full0 = smem_u32(bar_base), empty0 = full0 + 8 * kTcStages, done = empty0 + 8 * kTcStages;
+    unsigned *tmem_slot = reinterpret_cast<unsigned *>(bar_base + 8 * (2 * kTcStages + 1));
     const int M = g.N * g.H * g.W;
     const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
     B += blockIdx.z * bz;
+    const int KT = Kpad / kTcK;
+    constexpr int kCols = BN < 32 ? 32 : BN;
 
-    // this thread stages rows (tid >> 2) and (tid >> 2) + 64 of A, 8 channels at kc * 8
-    const int kc = tid & 3;
-    int rn[2], ri[2], rj[2];
-    bool rv[2];
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-        const int p = m0 + (tid >> 2) + 64 * s;
-        rv[s] = p < M;
-        const int hw = g.H * g.W, n = rv[s] ? p / hw : 0, r = p - n * hw;
-        rn[s] = n;
-        ri[s] = rv[s] ? r / g.W : 0;
-        rj[s] = rv[s] ? r - ri[s] * g.W : 0;
-    }
-    const int br = tid / (BN / 8), bc = tid % (BN / 8);
-    auto load = [&](int stage, int kt) {
-        const int k0 = kt * kBK;
-#pragma unroll
-        for (int s = 0; s < 2; ++s) {
-            const bf16 *src = rv[s] ? gat_src(g, rn[s], ri[s], rj[s], k0 + kc * 8) : nullptr;
-            cp16(&As[stage][(tid >> 2) + 64 * s][kc * 8], src ? src : g.in0, src ? 16 : 0);
+    if (tid == 0) {
+        for (int s = 0; s < kTcStages; ++s) {
+            mbar_init(full0 + 8 * s, 128);
+            mbar_init(empty0 + 8 * s, 1);
         }
-        if (br < kBK) cp16(&Bs[stage][br][bc * 8], B + (size_t)(k0 + br) * ldb + n0 + bc * 8, 16);
-    };
-
-    float acc[2][NT][4];
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int b = 0; b < NT; ++b)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.0f;
-
-    const int KT = Kpad / kBK;
-#pragma unroll
-    for (int s = 0; s < kStages - 1; ++s) {
-        if (s < KT) load(s, s);
-        cp_commit();
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
-    for (int kt = 0; kt < KT; ++kt) {
-        cp_wait<kStages - 2>();
-        __syncthreads();
-        {
-            const int nk = kt + kStages - 1;
-            if (nk < KT) load(nk % kStages, nk);
+    if (warp == 4) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const unsigned tmem = *tmem_slot;
+    bool ok = true;
+
+    if (warp < 4) {
+        // ---- producers.  A: lane l of warp w stages rows 32 w + 8 s + (l & 7),
+        // s = 0..3, chunks (l >> 3) and (l >> 3) + 4: one warp instruction reads
+        // 8 pixels x 64 contiguous bytes.  B: BN / 16 chunks per thread, 4 rows
+        // x 128 contiguous bytes per warp instruction ----
+        const int hw = g.H * g.W, qh = lane >> 3;
+        int rn[4], ri[4], rj[4];
+        bool rv[4];
+#pragma unroll
+        for (int s4 = 0; s4 < 4; ++s4) {
+            const int p = m0 + warp * 32 + 8 * s4 + (lane & 7);
+            rv[s4] = p < M;
+            const int n = rv[s4] ? p / hw : 0, r = p - n * hw;
+            rn[s4] = n;
+            ri[s4] = rv[s4] ? r / g.W : 0;
+            rj[s4] = rv[s4] ? r - ri[s4] * g.W : 0;
+        }
+        int signalled = 0;
+        for (int kt = 0; kt < KT && ok; ++kt) {
+            const int s = kt % kTcStages;
+            if (kt >= kTcStages) ok = mbar_wait(empty0 + 8 * s, ((kt / kTcStages) - 1) & 1);
+            if (!ok) break;
+            unsigned char *As = smem + s * S::kStage, *Bs = As + S::kA;
+            const int k0 = kt * kTcK;
+#pragma unroll
+            for (int s4 = 0; s4 < 4; ++s4) {
+                const int row = warp * 32 + 8 * s4 + (lane & 7);
+                unsigned char *dst = As + ((row >> 3) * 8) * 128 + (row & 7) * 16;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int q = qh + 4 * h;
+                    const bf16 *src = rv[s4] ? gat_src(g, rn[s4], ri[s4], rj[s4], k0 + q * 8) : nullptr;
+                    cp16(dst + q * 128, src ? src : g.in0, src ? 16 : 0);
+                }
+            }
+#pragma unroll
+            for (int rr = 0; rr < BN / 16; ++rr) {
+                const int c = tid + 128 * rr, nn = c >> 3, q = c & 7;
+                cp16(Bs + ((nn >> 3) * 8 + q) * 128 + (nn & 7) * 16, B + (size_t)(n0 + nn) * Kpad + k0 + q * 8, 16);
+            }
             cp_commit();
-        }
-        const int st = kt % kStages;
-#pragma unroll
-        for (int kk = 0; kk < kBK; kk += 16) {
-            unsigned a[2][4], b[NT][2];
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt)
-                ldm_x4(a[mt], &As[st][wm * 32 + mt * 16 + (lane & 15)][kk + (lane >> 4) * 8]);
-#pragma unroll
-            for (int np = 0; np < NT / 2; ++np) {
-                unsigned r[4];
-                ldm_x4_t(r, &Bs[st][kk + (lane & 15)][wn * WN + np * 16 + (lane >> 4) * 8]);
-                b[2 * np][0] = r[0];
-                b[2 * np][1] = r[1];
-                b[2 * np + 1][0] = r[2];
-                b[2 * np + 1][1] = r[3];
+            if (kt >= kTcLag) {
+                cp_wait<kTcLag>();
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                mbar_arrive(full0 + 8 * ((kt - kTcLag) % kTcStages));
+                signalled = kt - kTcLag + 1;
             }
+        }
+        cp_wait<0>();
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        if (ok)
+            for (int kt = signalled; kt < KT; ++kt) mbar_arrive(full0 + 8 * (kt % kTcStages));
+    } else if (lane == 0) {
+        // ---- MMA issuer ----
+        constexpr unsigned idesc = umma_idesc<BN>();
+        for (int kt = 0; kt < KT && ok; ++kt) {
+            const int s = kt % kTcStages;
+            ok = mbar_wait(full0 + 8 * s, (kt / kTcStages) & 1);
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const unsigned a0 = smem_u32(smem + s * S::kStage), b0 = a0 + S::kA;
 #pragma unroll
-            for (int mt = 0; mt < 2; ++mt)
+            for (int kk = 0; kk < kTcK / 16; ++kk) {
+                const uint64_t ad = umma_desc(a0 + kk * 256), bd = umma_desc(b0 + kk * 256);
+                const unsigned acc = (kt > 0 || kk > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                             empty0 + 8 * s)
+                         : "memory");
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(done)
+                     : "memory");
+        if (!mbar_wait(done, 0)) ok = false;  // no MMA in flight past this point
+    }
+
+    if (warp < 4) {
+        // ---- epilogue: TMEM lanes 32 warp .. +31 are this warp's rows.  The
+        // forward and the input-gradient epilogues stage the BF16 tile in the
+        // (now idle) pipeline memory and store it with coalesced 16-byte writes ----
+        if (ok) ok = mbar_wait(done, 0);
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const bool go = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-collective
+        const bool staged = e.kind == E_FWD || e.kind == E_DX;
+        constexpr int TS = BN * 2 + 16;  // staged row stride (bytes): rows 16 B apart in banks
+        const int row = warp * 32 + lane, p = m0 + row;
+        if (go) {
+#pragma unroll 1
+            for (int c0 = 0; c0 < BN; c0 += 16) {
+                unsigned v[16];
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                    "[%16];\n"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                      "=r"(v[15])
+                    : "r"(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c0));
+                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+                const int col = n0 + c0;
+                if (staged) {
+                    float f[16];
 #pragma unroll
-                for (int nt = 0; nt < NT; ++nt) mma16816(acc[mt][nt], a[mt], b[nt]);
+                    for (int q = 0; q < 16; ++q) f[q] = __uint_as_float(v[q]);
+                    if (e.kind == E_FWD) {
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) f[q] = fmaxf(f[q] + e.bias[col + q], 0.0f);
+                    } else if (col < e.nsplit) {  // E_DX: ReLU mask of the layer input (nsplit is a multiple of 16)
+                        __align__(16) bf16 m[16];
+                        if (p < M) {
+                            const uint4 *mp = reinterpret_cast<const uint4 *>(e.mask0 + (size_t)p * e.ld0 + col);
+                            reinterpret_cast<uint4 *>(m)[0] = mp[0];
+                            reinterpret_cast<uint4 *>(m)[1] = mp[1];
+                        } else {
+#pragma unroll
+                            for (int q = 0; q < 16; ++q) m[q] = __float2bfloat16_rn(0.0f);
+                        }
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) f[q] = __bfloat162float(m[q]) > 0.0f ? f[q] : 0.0f;
+                    }
+                    __align__(16) bf162 h[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) h[q] = __floats2bfloat162_rn(f[2 * q], f[2 * q + 1]);
+                    uint4 *t = reinterpret_cast<uint4 *>(smem + row * TS + c0 * 2);
+                    t[0] = reinterpret_cast<const uint4 *>(h)[0];
+                    t[1] = reinterpret_cast<const uint4 *>(h)[1];
+                } else if (p < M) {
+#pragma unroll
+                    for (int q = 0; q < 16; q += 2)
+                        epi_store(e, g, p, col + q, __uint_as_float(v[q]), __uint_as_float(v[q + 1]));
+                }
+            }
+        }
+        if (staged) {
+            asm volatile("bar.sync 1, 128;\n" ::: "memory");  // the 4 epilogue warps only
+            if (go) {
+                constexpr int CPR = BN / 8;  // 16-byte chunks per tile row
+#pragma unroll 4
+                for (int c = tid; c < kBM * CPR; c += 128) {
+                    const int r = c / CPR, q = c - r * CPR, pp = m0 + r;
+                    if (pp >= M) continue;
+                    const int col = n0 + q * 8;
+                    const uint4 val = *reinterpret_cast<const uint4 *>(smem + r * TS + q * 16);
+                    bf16 *dst = (e.kind == E_DX && col >= e.nsplit) ? e.out1 + (size_t)pp * e.ld1 + (col - e.nsplit)
+                                                                    : e.out0 + (size_t)pp * e.ld0 + col;
+                    *reinterpret_cast<uint4 *>(dst) = val;
+                }
+            }
         }
     }
-    cp_wait<0>();
-
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int p = m0 + wm * 32 + mt * 16 + (lane >> 2) + 8 * h;
-                if (p >= M) continue;
-                const int col = n0 + wn * WN + nt * 8 + 2 * (lane & 3);
-                epi_store(e, g, p, col, acc[mt][nt][2 * h], acc[mt][nt][2 * h + 1]);
-            }
+    if (!ok) atomicExch(err, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 4) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kCols) : "memory");
+    }
 }
 
 // Weight gradient: part[z][k][n] = sum over the rows p of split z of A(p, k)
@@ -595,17 +747,18 @@ __global__ void k_adam(float *__restrict__ th, const float *__restrict__ g, floa
     th[k] -= lr * (mk / b1t) / (sqrtf(vk / b2t) + 1e-8f);
 }
 
-// BF16 matrices of a layer from its FP32 weights W [ntaps][ci][co]:
-//   forward   F[k][o], k = t cinp + c (rows up to Kpad; padding zero)
-//   backward  conv/up: Bk[t' co + o][c] = W[8 - t'][c][o];  down: Bd[t][o][c] = W[t][c][o]
-__global__ void k_pack(const float *__restrict__ W, int kind, int ntaps, int ci, int co, int cinp, int Kpad,
+// BF16 K-major matrices of a layer from its FP32 weights W [ntaps][ci][co]:
+//   forward   F[o][k], k = t cinp + c < Kf (zero where t, c are padding)
+//   backward  conv/up: Bk[c][k'], k' = t' co + o < Kb: W[8 - t'][c][o] (zero beyond 9 co);
+//             down: Bk[t][c][o] = W[t][c][o]
+__global__ void k_pack(const float *__restrict__ W, int kind, int ntaps, int ci, int co, int cinp, int Kf, int Kb,
                        bf16 *__restrict__ F, bf16 *__restrict__ Bk)
 {
     pdl_entry();
     const long long idx = blockIdx.x * (long long)kT + threadIdx.x;
-    const long long nf = (long long)Kpad * co;
+    const long long nf = (long long)co * Kf;
     if (idx < nf) {
-        const int o = (int)(idx % co), k = (int)(idx / co);
+        const int o = (int)(idx / Kf), k = (int)(idx % Kf);
         const int t = k / cinp, c = k - t * cinp;
         const float w = (t < ntaps && c < ci) ? W[((size_t)t * ci + c) * co + o] : 0.0f;
         F[idx] = __float2bfloat16_rn(w);
@@ -613,12 +766,13 @@ __global__ void k_pack(const float *__restrict__ W, int kind, int ntaps, int ci,
     }
     if (!Bk) return;
     const long long q = idx - nf;
-    if (q >= (long long)ntaps * co * ci) return;
-    const int c = (int)(q % ci);
-    const long long r = q / ci;
-    const int o = (int)(r % co), t = (int)(r / co);
-    const int ts = kind == L_DOWN2 ? t : 8 - t;
-    Bk[q] = __float2bfloat16_rn(W[((size_t)ts * ci + c) * co + o]);
+    if (kind == L_DOWN2) {
+        if (q < (long long)ntaps * ci * co) Bk[q] = __float2bfloat16_rn(W[q]);
+        return;
+    }
+    if (q >= (long long)ci * Kb) return;
+    const int c = (int)(q / Kb), k = (int)(q % Kb), t = k / co, o = k - t * co;
+    Bk[q] = __float2bfloat16_rn(t < ntaps ? W[((size_t)(8 - t) * ci + c) * co + o] : 0.0f);
 }
 
 // ------------------------------------------------- features of a pressure problem --
@@ -640,11 +794,22 @@ __global__ void __launch_bounds__(kT) k_feat_bsum(const double *__restrict__ b, 
     }
 }
 
-__device__ __forceinline__ double sum_parts(const double *part, int n)
+// Sum of n partials, computed once per block (warp 0, fixed order) and shared:
+// the same value in every block.  Call from all threads of the block.
+__device__ double block_sum_parts(const double *part, int n)
 {
-    double s = 0.0;
-    for (int k = 0; k < n; ++k) s += part[k];
-    return s;
+    __shared__ double r;
+    if (threadIdx.x < 32) {
+        double s = 0.0;
+        for (int k = threadIdx.x; k < n; k += 32) s += part[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) r = s;
+    }
+    __syncthreads();
+    const double v = r;
+    __syncthreads();  // r may be written again by the next call
+    return v;
 }
 
 __device__ __forceinline__ double cell_beta(const double *bu, const double *bv, int nx, int i, int j)
@@ -659,9 +824,9 @@ __global__ void k_features(int nx, int ny, const double *__restrict__ b, const d
                            float *__restrict__ x, float *__restrict__ t)
 {
     pdl_entry();
+    const double s2 = block_sum_parts(part, nparts);
     const int c = blockIdx.x * kT + threadIdx.x;
     if (c >= nx * ny) return;
-    const double s2 = sum_parts(part, nparts);
     const int i = c % nx, j = c / nx;
     const double beta = cell_beta(bu, bv, nx, i, j);
     float x0 = 0.0f, x1 = 0.0f, tt = 0.0f;
@@ -681,9 +846,9 @@ __global__ void k_guess(int nx, int ny, const double *__restrict__ b, const doub
                         const float *__restrict__ out, double *__restrict__ phi)
 {
     pdl_entry();
+    const double s2 = block_sum_parts(part, nparts);
     const int c = blockIdx.x * kT + threadIdx.x;
     if (c >= nx * ny) return;
-    const double s2 = sum_parts(part, nparts);
     const int i = c % nx, j = c / nx;
     const double beta = cell_beta(bu, bv, nx, i, j);
     phi[c] = (s2 > 0.0 && beta > 0.0) ? double(out[c]) * sqrt(s2 / (double(nx) * ny)) / beta : 0.0;
@@ -717,7 +882,8 @@ __global__ void k_guess_select(int n, const double *__restrict__ pb, const doubl
                                double *__restrict__ phi, long long *stats)
 {
     pdl_entry();
-    const double b2 = sum_parts(pb, nparts), r2 = sum_parts(pr, nparts);
+    const double b2 = block_sum_parts(pb, nparts);
+    const double r2 = block_sum_parts(pr, nparts);
     const bool keep = r2 < b2;
     const int c = blockIdx.x * kT + threadIdx.x;
     if (!keep && c < n) phi[c] = 0.0;
@@ -751,6 +917,7 @@ struct wec_net {
     float *xb = nullptr, *tb = nullptr;       // gathered batch (or a tank's features)
     double *loss = nullptr, *lossh = nullptr; // device / pinned host
     double *dpart = nullptr;                  // FP64 partials of the tank guess (2 x kRedBlocks)
+    int *err = nullptr;                       // device: set when a tensor-core pipeline wait expired
     std::vector<void *> allocs;
 };
 
@@ -809,16 +976,50 @@ Gat fwd_gather(const wec_net *N, int L, int batch)
     return g;
 }
 
-int gemm(cudaStream_t st, const Gat &g, const bf16 *B, int ldb, size_t bz, int Kpad, int ncols, int nz, const Epi &e)
+inline int fwd_Kt(int L) { return round_up(fwd_K(L), kTcK); }      // forward K-major row length
+inline int bwd_Kt(int L) { return kLayers[L].kind == L_DOWN2 ? kLayers[L].co : round_up(9 * kLayers[L].co, kTcK); }
+inline size_t bwd_elems(int L)
+{
+    const LayerDef &d = kLayers[L];
+    return d.kind == L_DOWN2 ? weight_count(L) : (size_t)d.ci * bwd_Kt(L);
+}
+
+template <int BN>
+int launch_tc(cudaStream_t st, dim3 grid, const Gat &g, const bf16 *B, int Kpad, size_t bz, const Epi &e, int *err)
+{
+    static bool attr = false;  // dynamic shared memory above 48 KB, set once per instantiation
+    if (!attr) {
+        WEC_CK(cudaFuncSetAttribute(k_conv_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcSmem<BN>::kBytes));
+        attr = true;
+    }
+    WEC_CK(launch_k(k_conv_tc<BN>, grid, kTcThreads, TcSmem<BN>::kBytes, st, g, B, Kpad, bz, e, err));
+    return WEC_OK;
+}
+
+// One convolution GEMM on the tensor cores: B is the K-major weight matrix
+// (ncols rows of Kpad elements; blockIdx.z selects one bz elements further on).
+// Tile width: the widest of 256/128/64/32 dividing ncols that still gives >= 256
+// CTAs (about two per SM), else 32.  tag: the layer index (forward) or 100 +
+// layer (input gradient), reported as the profile level of the launch.
+int gemm(wec_net *N, cudaStream_t st, int tag, const Gat &g, const bf16 *B, int Kpad, size_t bz, int ncols, int nz,
+         const Epi &e)
 {
     const long long M = (long long)g.N * g.H * g.W;
-    dim3 grid((unsigned)((M + kBM - 1) / kBM), (unsigned)(ncols / (ncols % 64 == 0 ? 64 : 32)), (unsigned)nz);
-    WEC_PROF("net_conv", -1, 2.0 * M * nz * ((double)(g.c0 + g.c1) + ncols) + 2.0 * Kpad * ldb * nz, st);
-    if (ncols % 64 == 0)
-        WEC_CK(launch_k(k_conv_gemm<64>, grid, kGT, 0, st, g, B, ldb, bz, Kpad, e));
-    else
-        WEC_CK(launch_k(k_conv_gemm<32>, grid, kGT, 0, st, g, B, ldb, bz, Kpad, e));
-    return WEC_OK;
+    const long long mt = (M + kBM - 1) / kBM;
+    int bn = 32;
+    for (int c : {256, 128, 64})
+        if (ncols % c == 0 && mt * (ncols / c) * nz >= 256) {
+            bn = c;
+            break;
+        }
+    dim3 grid((unsigned)mt, (unsigned)(ncols / bn), (unsigned)nz);
+    WEC_PROF("net_conv", tag, 2.0 * M * nz * ((double)(g.c0 + g.c1) + ncols) + 2.0 * Kpad * ncols * nz, st);
+    switch (bn) {
+    case 256: return launch_tc<256>(st, grid, g, B, Kpad, bz, e, N->err);
+    case 128: return launch_tc<128>(st, grid, g, B, Kpad, bz, e, N->err);
+    case 64: return launch_tc<64>(st, grid, g, B, Kpad, bz, e, N->err);
+    default: return launch_tc<32>(st, grid, g, B, Kpad, bz, e, N->err);
+    }
 }
 
 int wgrad_splits(long long M, int L, int *cps)
@@ -883,19 +1084,18 @@ int dx_conv(wec_net *N, int L, int batch, const bf16 *G, const Epi &e)
     g.H = g.Hi = level_h(N, d.level);
     g.W = g.Wi = level_w(N, d.level);
     g.K = 9 * d.co;
-    return gemm(N->st, g, N->wmat + N->wb[L], d.ci, 0, 9 * d.co, d.ci, 1, e);
+    return gemm(N, N->st, 100 + L, g, N->wmat + N->wb[L], bwd_Kt(L), 0, d.ci, 1, e);
 }
 
 int pack_weights(wec_net *N)
 {
     for (int L = 0; L < kHead; ++L) {
         const LayerDef &d = kLayers[L];
-        const int Kp = round_up(fwd_K(L), kBK);
         const bool back = L != enc_a(0);
-        const long long n = (long long)Kp * d.co + (back ? (long long)weight_count(L) : 0);
+        const long long n = (long long)d.co * fwd_Kt(L) + (back ? (long long)bwd_elems(L) : 0);
         WEC_PROF("net_pack", -1, 4.0 * weight_count(L) + 2.0 * n, N->st);
         WEC_CK(launch_k(k_pack, nblk(n, kT), kT, 0, N->st, (const float *)(N->theta + N->flat[L]), d.kind,
-                        taps(d.kind), d.ci, d.co, cin_pad(d.ci), Kp, N->wmat + N->wf[L],
+                        taps(d.kind), d.ci, d.co, cin_pad(d.ci), fwd_Kt(L), bwd_Kt(L), N->wmat + N->wf[L],
                         back ? N->wmat + N->wb[L] : (bf16 *)nullptr));
     }
     N->wdirty = false;
@@ -922,7 +1122,7 @@ int forward(wec_net *N, int batch, const float *x, float *out, const float *targ
         e.out0 = N->act[L];
         e.ld0 = d.co;
         const Gat g = fwd_gather(N, L, batch);
-        if (int r = gemm(st, g, N->wmat + N->wf[L], d.co, 0, round_up(g.K, kBK), d.co, 1, e)) return r;
+        if (int r = gemm(N, st, L, g, N->wmat + N->wf[L], fwd_Kt(L), 0, d.co, 1, e)) return r;
     }
     const int nb = nblk(M, kT);
     {
@@ -989,7 +1189,8 @@ int backward(wec_net *N, int batch)
             e.mask0 = N->act[enc_b(l)];
             e.ld0 = C;
             e.add = N->skip[l];
-            if (int r = gemm(st, g, N->wmat + N->wb[down(l)], C, (size_t)2 * C * C, 2 * C, C, 4, e)) return r;
+            if (int r = gemm(N, st, 100 + down(l), g, N->wmat + N->wb[down(l)], 2 * C, (size_t)2 * C * C, C, 4, e))
+                return r;
         }
         if (int r = wgrad(N, enc_b(l), batch, N->gA[l])) return r;
         Epi e{};
@@ -1113,10 +1314,10 @@ int wec_net_create(int H, int W, int max_batch, void *cuda_stream, wec_net **out
         off += weight_count(L) + kLayers[L].co;
         if (L == kHead) break;
         N->wf[L] = nw;
-        nw += (size_t)round_up(fwd_K(L), kBK) * kLayers[L].co;
+        nw += (size_t)fwd_Kt(L) * kLayers[L].co;
         nw = round_up_z(nw, 64);
         N->wb[L] = nw;
-        nw += weight_count(L);
+        nw += bwd_elems(L);
         nw = round_up_z(nw, 64);
     }
     const size_t P0 = (size_t)max_batch * H * W;
@@ -1151,6 +1352,7 @@ int wec_net_create(int H, int W, int max_batch, void *cuda_stream, wec_net **out
     A((void **)&N->tb, 4 * P0);
     A((void **)&N->loss, 8);
     A((void **)&N->dpart, 8 * 2 * kRedBlocks);
+    A((void **)&N->err, sizeof(int));
     N->part_n = part_n;
     if (!r) {
         cudaError_t ce = cudaMallocHost((void **)&N->lossh, 8);
@@ -1161,6 +1363,7 @@ int wec_net_create(int H, int W, int max_batch, void *cuda_stream, wec_net **out
         if (ce == cudaSuccess) ce = cudaMemsetAsync(N->grad, 0, 4 * N->nparam, N->st);
         if (ce == cudaSuccess) ce = cudaMemsetAsync(N->am, 0, 4 * N->nparam, N->st);
         if (ce == cudaSuccess) ce = cudaMemsetAsync(N->av, 0, 4 * N->nparam, N->st);
+        if (ce == cudaSuccess) ce = cudaMemsetAsync(N->err, 0, sizeof(int), N->st);
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(N->st);
         if (ce != cudaSuccess) r = cuda_fail(ce, "net_create: initialisation");
     }
@@ -1187,6 +1390,16 @@ int wec_net_set_params(wec_net *N, const float *host, size_t n)
     N->adam_t = 0;
     N->wdirty = true;
     return WEC_OK;
+}
+
+// After a synchronising call: a tensor-core pipeline wait that expired is an error.
+static int check_pipeline(wec_net *N, const char *what)
+{
+    int h = 0;
+    WEC_CK(cudaMemcpy(&h, N->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (!h) return WEC_OK;
+    WEC_CK(cudaMemset(N->err, 0, sizeof(int)));
+    return fail(WEC_ERR_CUDA, std::string(what) + ": a tensor-core pipeline wait expired");
 }
 
 static int copy_out(const wec_net *N, const float *src, float *host, size_t n, const char *what)
@@ -1227,7 +1440,7 @@ int wec_net_forward(wec_net *N, int batch, const float *x, float *out)
     if (batch < 1 || batch > N->maxb) return fail(WEC_ERR_INVALID, "net_forward: batch outside [1, max_batch]");
     if (int r = forward(N, batch, x, out, nullptr)) return r;
     WEC_CK(cudaStreamSynchronize(N->st));
-    return WEC_OK;
+    return check_pipeline(N, "net_forward");
 }
 
 int wec_net_loss_grad(wec_net *N, int batch, const float *x, const float *target, double *loss)
@@ -1238,6 +1451,7 @@ int wec_net_loss_grad(wec_net *N, int batch, const float *x, const float *target
     if (int r = backward(N, batch)) return r;
     WEC_CK(cudaMemcpyAsync(N->lossh, N->loss, 8, cudaMemcpyDeviceToHost, N->st));
     WEC_CK(cudaStreamSynchronize(N->st));
+    if (int r = check_pipeline(N, "net_loss_grad")) return r;
     *loss = *N->lossh;
     return std::isfinite(*loss) ? WEC_OK : fail(WEC_ERR_NONFINITE, "net_loss_grad: non-finite loss");
 }

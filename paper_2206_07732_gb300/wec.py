@@ -393,6 +393,37 @@ class Nlfk:
     __del__ = close
 
 
+# The U-Net's layers (kind, input channels, output channels, level of the
+# output), in the parameter order of wec.h; "head" is the 1x1 FP32 output layer.
+NET_LAYERS = [("conv3", 2, 32, 0), ("conv3", 32, 32, 0),
+              ("down2", 32, 64, 1), ("conv3", 64, 64, 1), ("conv3", 64, 64, 1),
+              ("down2", 64, 128, 2), ("conv3", 128, 128, 2), ("conv3", 128, 128, 2),
+              ("down2", 128, 256, 3), ("conv3", 256, 256, 3), ("conv3", 256, 256, 3),
+              ("up3", 256, 128, 2), ("conv3", 256, 128, 2), ("conv3", 128, 128, 2),
+              ("up3", 128, 64, 1), ("conv3", 128, 64, 1), ("conv3", 64, 64, 1),
+              ("up3", 64, 32, 0), ("conv3", 64, 32, 0), ("conv3", 32, 32, 0),
+              ("head", 32, 1, 0)]
+
+
+def net_param_shapes():
+    """Shapes of the parameter tensors (weights, then bias, per layer)."""
+    out = []
+    for kind, ci, co, _ in NET_LAYERS:
+        w = (ci, co) if kind == "head" else ((2, 2, ci, co) if kind == "down2" else (3, 3, ci, co))
+        out += [w, (co,)]
+    return out
+
+
+def net_layer_flops(H, W, batch=1):
+    """Multiply-add FLOPs (2 per MAC) of each layer's forward convolution."""
+    out = []
+    for kind, ci, co, lev in NET_LAYERS:
+        px = batch * (H >> lev) * (W >> lev)
+        taps = 1 if kind == "head" else (4 if kind == "down2" else 9)
+        out.append(2.0 * px * taps * ci * co)
+    return out
+
+
 class Net:
     """The learned warm start's U-Net (wec_net_create ... wec_net_destroy).
     Inputs and targets are float32 CUDA tensors: x [batch, H, W, 2], target and

@@ -174,3 +174,10 @@ def test_net_matches_the_oracle_layout_and_validates_on_host(lib):
     assert lib.wec_tank_set_net(None, None) == wec.WEC_ERR_INVALID
     assert lib.wec_net_sample(None, None, None) == wec.WEC_ERR_INVALID
     lib.wec_net_destroy(None)
+
+
+def test_binding_layer_table_matches_the_oracle():
+    from oracle import unet as U
+    assert wec.net_param_shapes() == [tuple(s) for s in U.param_shapes(32)]
+    assert [(k if k != "head" else "head", ci, co) for k, ci, co, _ in wec.NET_LAYERS] == \
+        [(k, ci, co) for _, k, ci, co in U.layers(32)]
