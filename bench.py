@@ -363,7 +363,7 @@ def main_batch(args):
         torch.distributed.destroy_process_group()
 
 
-def train_learned(wec, torch, cfg, seed, per_seed=120, skip=40, iters=800, batch=4):
+def train_learned(wec, torch, cfg, seed, per_seed=120, skip=40, iters=2000, batch=4):
     """The learned warm start's network, trained (untimed) on the pressure
     problems of mixed-precision runs of the same tank with other wave phases
     (seeds seed+1, seed+2): features and targets from wec_net_sample, Adam

@@ -42,7 +42,7 @@ struct LayerDef {
 
 constexpr int kNumLayers = 21;
 constexpr int kInCh = 2;   // features per cell
-constexpr int kInPad = 8;  // channels of the stored BF16 input (16-byte rows)
+constexpr int kInPad = 16; // channels of the stored BF16 input (two 16-byte chunks per pixel)
 const LayerDef kLayers[kNumLayers] = {
     {L_CONV3, 2, 32, 0},    {L_CONV3, 32, 32, 0},                           // enc0a, enc0b
     {L_DOWN2, 32, 64, 1},   {L_CONV3, 64, 64, 1},   {L_CONV3, 64, 64, 1},   // down0, enc1a, enc1b
@@ -259,6 +259,82 @@ __host__ __device__ constexpr unsigned umma_idesc()
     return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(BN >> 3) << 17) | ((unsigned)(kBM >> 4) << 24);
 }
 
+// Epilogue of a tensor-core tile (warps 0-3; TMEM lane r = tile row r, pixel
+// m0 + r, valid below M).  The forward and the input-gradient epilogues stage
+// the BF16 tile in the (then idle) pipeline memory and store it with coalesced
+// 16-byte writes; the others store pairs.  go is warp-uniform (tcgen05.ld is
+// warp-collective); the named barrier runs regardless so that no warp waits alone.
+template <int BN>
+__device__ __forceinline__ void tc_epilogue(const Epi &e, const Gat &g, unsigned tmem, int m0, int n0, int M,
+                                            unsigned char *smem, int warp, int lane, int tid, bool go)
+{
+    const bool staged = e.kind == E_FWD || e.kind == E_DX;
+    constexpr int TS = BN * 2 + 16;  // staged row stride (bytes): rows 16 B apart in banks
+    const int row = warp * 32 + lane, p = m0 + row;
+    if (go) {
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+            unsigned v[16];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                "[%16];\n"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                  "=r"(v[15])
+                : "r"(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c0));
+            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+            const int col = n0 + c0;
+            if (staged) {
+                float f[16];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) f[q] = __uint_as_float(v[q]);
+                if (e.kind == E_FWD) {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) f[q] = fmaxf(f[q] + e.bias[col + q], 0.0f);
+                } else if (col < e.nsplit) {  // E_DX: ReLU mask of the layer input (nsplit is a multiple of 16)
+                    __align__(16) bf16 m[16];
+                    if (p < M) {
+                        const uint4 *mp = reinterpret_cast<const uint4 *>(e.mask0 + (size_t)p * e.ld0 + col);
+                        reinterpret_cast<uint4 *>(m)[0] = mp[0];
+                        reinterpret_cast<uint4 *>(m)[1] = mp[1];
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) m[q] = __float2bfloat16_rn(0.0f);
+                    }
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) f[q] = __bfloat162float(m[q]) > 0.0f ? f[q] : 0.0f;
+                }
+                __align__(16) bf162 h[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) h[q] = __floats2bfloat162_rn(f[2 * q], f[2 * q + 1]);
+                uint4 *t = reinterpret_cast<uint4 *>(smem + row * TS + c0 * 2);
+                t[0] = reinterpret_cast<const uint4 *>(h)[0];
+                t[1] = reinterpret_cast<const uint4 *>(h)[1];
+            } else if (p < M) {
+#pragma unroll
+                for (int q = 0; q < 16; q += 2)
+                    epi_store(e, g, p, col + q, __uint_as_float(v[q]), __uint_as_float(v[q + 1]));
+            }
+        }
+    }
+    if (staged) {
+        asm volatile("bar.sync 1, 128;\n" ::: "memory");  // the 4 epilogue warps only
+        if (go) {
+            constexpr int CPR = BN / 8;  // 16-byte chunks per tile row
+#pragma unroll 4
+            for (int c = tid; c < kBM * CPR; c += 128) {
+                const int r = c / CPR, q = c - r * CPR, pp = m0 + r;
+                if (pp >= M) continue;
+                const int col = n0 + q * 8;
+                const uint4 val = *reinterpret_cast<const uint4 *>(smem + r * TS + q * 16);
+                bf16 *dst = (e.kind == E_DX && col >= e.nsplit) ? e.out1 + (size_t)pp * e.ld1 + (col - e.nsplit)
+                                                                : e.out0 + (size_t)pp * e.ld0 + col;
+                *reinterpret_cast<uint4 *>(dst) = val;
+            }
+        }
+    }
+}
+
 template <int BN>
 __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(Gat g, const bf16 *__restrict__ B, int Kpad, size_t bz,
                                                           Epi e, int *err)
@@ -377,77 +453,212 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(Gat g, const bf16 *__
     }
 
     if (warp < 4) {
-        // ---- epilogue: TMEM lanes 32 warp .. +31 are this warp's rows.  The
-        // forward and the input-gradient epilogues stage the BF16 tile in the
-        // (now idle) pipeline memory and store it with coalesced 16-byte writes ----
+        // ---- epilogue: TMEM lanes 32 warp .. +31 are this warp's rows ----
         if (ok) ok = mbar_wait(done, 0);
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        const bool go = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-collective
-        const bool staged = e.kind == E_FWD || e.kind == E_DX;
-        constexpr int TS = BN * 2 + 16;  // staged row stride (bytes): rows 16 B apart in banks
-        const int row = warp * 32 + lane, p = m0 + row;
-        if (go) {
-#pragma unroll 1
-            for (int c0 = 0; c0 < BN; c0 += 16) {
-                unsigned v[16];
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-                    "[%16];\n"
-                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-                      "=r"(v[15])
-                    : "r"(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c0));
-                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-                const int col = n0 + c0;
-                if (staged) {
-                    float f[16];
-#pragma unroll
-                    for (int q = 0; q < 16; ++q) f[q] = __uint_as_float(v[q]);
-                    if (e.kind == E_FWD) {
-#pragma unroll
-                        for (int q = 0; q < 16; ++q) f[q] = fmaxf(f[q] + e.bias[col + q], 0.0f);
-                    } else if (col < e.nsplit) {  // E_DX: ReLU mask of the layer input (nsplit is a multiple of 16)
-                        __align__(16) bf16 m[16];
-                        if (p < M) {
-                            const uint4 *mp = reinterpret_cast<const uint4 *>(e.mask0 + (size_t)p * e.ld0 + col);
-                            reinterpret_cast<uint4 *>(m)[0] = mp[0];
-                            reinterpret_cast<uint4 *>(m)[1] = mp[1];
-                        } else {
-#pragma unroll
-                            for (int q = 0; q < 16; ++q) m[q] = __float2bfloat16_rn(0.0f);
-                        }
-#pragma unroll
-                        for (int q = 0; q < 16; ++q) f[q] = __bfloat162float(m[q]) > 0.0f ? f[q] : 0.0f;
-                    }
-                    __align__(16) bf162 h[8];
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) h[q] = __floats2bfloat162_rn(f[2 * q], f[2 * q + 1]);
-                    uint4 *t = reinterpret_cast<uint4 *>(smem + row * TS + c0 * 2);
-                    t[0] = reinterpret_cast<const uint4 *>(h)[0];
-                    t[1] = reinterpret_cast<const uint4 *>(h)[1];
-                } else if (p < M) {
-#pragma unroll
-                    for (int q = 0; q < 16; q += 2)
-                        epi_store(e, g, p, col + q, __uint_as_float(v[q]), __uint_as_float(v[q + 1]));
+        tc_epilogue<BN>(e, g, tmem, m0, n0, M, smem, warp, lane, tid, __all_sync(0xffffffffu, ok));
+    }
+    if (!ok) atomicExch(err, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 4) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kCols) : "memory");
+    }
+}
+
+// ------------------------------------------------ tcgen05 halo convolution --
+// A convolution whose CTA tile is 128 consecutive pixels of one output image
+// row (n, i, x0 .. x0 + 127) by BN output channels, the accumulator in tensor
+// memory.  The reduction runs in stages of CS input channels x one vertical
+// tap: a stage holds the input row of that tap once, K-chunk by K-chunk (16
+// bytes per pixel slot, the next chunk LBO bytes on), and the horizontal taps
+// read it through descriptors whose start addresses differ by one slot (8-row
+// groups 128 B apart).  Modes:
+//   3x3 (stride 1, zero border): slots x0 - 1 .. x0 + 134 of input row i + ta - 1;
+//   up: the same over the nearest-upsampled input (slot x reads pixel x / 2 of
+//       row (i + ta - 1) / 2 of the half-resolution tensor);
+//   down (2x2, stride 2): input row 2 i + ta, even pixels 2 (x0 + r) in slots
+//       0 .. 127 and odd pixels in slots 128 .. 255, one array per horizontal tap.
+// The stage's weights for all its horizontal taps arrive in one bulk copy,
+// pre-packed in core-matrix order (k_pack_halo).
+enum HaloMode { H_CONV3 = 0, H_UP3 = 1, H_DOWN2 = 2 };
+
+struct Halo {
+    const bf16 *in0, *in1;  // channels [0, c0) from in0, [c0, c0 + c1) from in1 (concatenation)
+    int c0, c1;
+    int N, H, W, xtiles;    // output image grid; 128-pixel tiles per image row
+    int Hi, Wi;             // input tensor grid
+    int mode, nst;          // HaloMode; stages: (c0 + c1) / CS x vertical taps
+};
+
+template <int BN, int CS, bool DOWN>
+struct HaloSmem {
+    static constexpr int kSlots = DOWN ? 256 : 136;       // pixel slots per K-chunk (a multiple of 8)
+    static constexpr int kLBO = (kSlots + 1) * 16;         // one padding slot: chunks fall in different banks
+    static constexpr int kTH = DOWN ? 2 : 3;               // horizontal taps per stage
+    static constexpr int kA = (CS / 8) * kLBO;
+    static constexpr int kB = kTH * BN * CS * 2;
+    static constexpr int kStage = kA + kB;
+    static constexpr int kStages = kStage <= 40 * 1024 ? 4 : 3;
+    static constexpr int kBytes = kStages * kStage + 256;
+};
+
+__device__ __forceinline__ uint64_t umma_desc_s(unsigned saddr, unsigned lbo, unsigned sbo)
+{
+    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned a, unsigned bytes)
+{
+    asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(a), "r"(bytes)
+                 : "memory");
+}
+
+// Contiguous global -> shared bulk copy completing on an mbarrier (tx bytes).
+__device__ __forceinline__ void bulk_g2s(unsigned dst, const void *src, unsigned bytes, unsigned mbar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(mbar)
+        : "memory");
+}
+
+template <int BN, int CS, bool DOWN>
+__global__ void __launch_bounds__(kTcThreads, 1) k_conv_halo(Halo h, const bf16 *__restrict__ Bp, Epi e, int *err)
+{
+    pdl_entry();
+    extern __shared__ __align__(1024) unsigned char smem[];
+    using S = HaloSmem<BN, CS, DOWN>;
+    constexpr int TH = S::kTH, TV = DOWN ? 2 : 3;
+    constexpr int NS = S::kStages;
+    constexpr int CH = CS / 8;  // 16-byte chunks per halo pixel
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    unsigned char *bar_base = smem + NS * S::kStage;
+    const unsigned full0 = smem_u32(bar_base), empty0 = full0 + 8 * NS, done = empty0 + 8 * NS;
+    unsigned *tmem_slot = reinterpret_cast<unsigned *>(bar_base + 8 * (2 * NS + 1));
+    const int xt = blockIdx.x % h.xtiles, rowid = blockIdx.x / h.xtiles;
+    const int i = rowid % h.H, n = rowid / h.H, x0 = xt * kBM;
+    const int m0 = rowid * h.W + x0, M = m0 + min(kBM, h.W - x0);  // pixel rows of the tile
+    const int n0 = blockIdx.y * BN;
+    const bf16 *Bt = Bp + (size_t)blockIdx.y * h.nst * TH * BN * CS;
+    constexpr int kCols = BN < 32 ? 32 : BN;
+
+    if (tid == 0) {
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(full0 + 8 * s, 129);  // 128 producers + the bulk copy's expect_tx arrival
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 4) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const unsigned tmem = *tmem_slot;
+    bool ok = true;
+    const int KT = h.nst;
+
+    if (warp < 4) {
+        // ---- producers: the halo row of the stage (8 consecutive threads read one
+        // pixel's CS channels, 16 bytes each); thread 0 also issues the B bulk copy ----
+        int signalled = 0;
+        for (int kt = 0; kt < KT && ok; ++kt) {
+            const int s = kt % NS;
+            if (kt >= NS) ok = mbar_wait(empty0 + 8 * s, ((kt / NS) - 1) & 1);
+            if (!ok) break;
+            unsigned char *As = smem + s * S::kStage, *Bs = As + S::kA;
+            if (tid == 0) {
+                mbar_expect_tx(full0 + 8 * s, S::kB);
+                bulk_g2s(smem_u32(Bs), Bt + (size_t)kt * TH * BN * CS, S::kB, full0 + 8 * s);
+            }
+            const int cc = kt / TV, ta = kt - TV * cc, cb = cc * CS;
+            int y = DOWN ? 2 * i + ta : i + ta - 1;  // input row (output grid for the up mode)
+            const bool row_ok = y >= 0 && y < (DOWN ? h.Hi : h.H);
+            if (h.mode == H_UP3) y >>= 1;
+            const bf16 *src_row;
+            int cstride, coff;
+            if (cb < h.c0) {
+                src_row = h.in0;
+                cstride = h.c0;
+                coff = cb;
+            } else {
+                src_row = h.in1;
+                cstride = h.c1;
+                coff = cb - h.c0;
+            }
+            src_row += ((size_t)(n * h.Hi + (row_ok ? y : 0)) * h.Wi) * cstride + coff;
+            for (int idx = tid; idx < S::kSlots * CH; idx += 128) {
+                const int q = idx % CH, sl = idx / CH;
+                int x;      // input pixel of the slot
+                bool v;
+                if (DOWN) {
+                    const int r = sl & (kBM - 1);
+                    x = 2 * (x0 + r) + (sl >> 7);
+                    v = row_ok && x0 + r < h.W;
+                } else {
+                    x = x0 - 1 + sl;  // output-grid column
+                    v = row_ok && x >= 0 && x < h.W;
+                    if (h.mode == H_UP3) x >>= 1;
                 }
+                cp16(As + q * S::kLBO + sl * 16, v ? src_row + (size_t)x * cstride + q * 8 : h.in0, v ? 16 : 0);
+            }
+            cp_commit();
+            if (kt >= kTcLag) {
+                cp_wait<kTcLag>();
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                mbar_arrive(full0 + 8 * ((kt - kTcLag) % NS));
+                signalled = kt - kTcLag + 1;
             }
         }
-        if (staged) {
-            asm volatile("bar.sync 1, 128;\n" ::: "memory");  // the 4 epilogue warps only
-            if (go) {
-                constexpr int CPR = BN / 8;  // 16-byte chunks per tile row
-#pragma unroll 4
-                for (int c = tid; c < kBM * CPR; c += 128) {
-                    const int r = c / CPR, q = c - r * CPR, pp = m0 + r;
-                    if (pp >= M) continue;
-                    const int col = n0 + q * 8;
-                    const uint4 val = *reinterpret_cast<const uint4 *>(smem + r * TS + q * 16);
-                    bf16 *dst = (e.kind == E_DX && col >= e.nsplit) ? e.out1 + (size_t)pp * e.ld1 + (col - e.nsplit)
-                                                                    : e.out0 + (size_t)pp * e.ld0 + col;
-                    *reinterpret_cast<uint4 *>(dst) = val;
+        cp_wait<0>();
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        if (ok)
+            for (int kt = signalled; kt < KT; ++kt) mbar_arrive(full0 + 8 * (kt % NS));
+    } else if (lane == 0) {
+        // ---- MMA issuer: per stage TH taps x CS / 16 K-steps ----
+        constexpr unsigned idesc = umma_idesc<BN>();
+        for (int kt = 0; kt < KT && ok; ++kt) {
+            const int s = kt % NS;
+            ok = mbar_wait(full0 + 8 * s, (kt / NS) & 1);
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const unsigned a0 = smem_u32(smem + s * S::kStage), b0 = a0 + S::kA;
+#pragma unroll
+            for (int tb = 0; tb < TH; ++tb)
+#pragma unroll
+                for (int kk = 0; kk < CS / 16; ++kk) {
+                    const uint64_t ad =
+                        umma_desc_s(a0 + 2 * kk * S::kLBO + tb * (DOWN ? kBM * 16 : 16), S::kLBO, 128);
+                    const uint64_t bd = umma_desc_s(b0 + tb * (BN * CS * 2) + 2 * kk * 128, 128, CH * 128);
+                    const unsigned acc = (kt > 0 || tb > 0 || kk > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                        : "memory");
                 }
-            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                             empty0 + 8 * s)
+                         : "memory");
         }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(done)
+                     : "memory");
+        if (!mbar_wait(done, 0)) ok = false;  // no MMA in flight past this point
+    }
+
+    if (warp < 4) {
+        if (ok) ok = mbar_wait(done, 0);
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        Gat g{};  // (the staged and E_F32 epilogues need no gather)
+        tc_epilogue<BN>(e, g, tmem, m0, n0, M, smem, warp, lane, tid, __all_sync(0xffffffffu, ok));
     }
     if (!ok) atomicExch(err, 1);
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -564,7 +775,7 @@ __global__ void __launch_bounds__(kGT) k_wgrad(Gat g, const bf16 *__restrict__ G
 constexpr int kT = 256;
 constexpr int kHeadVals = 34;  // per-block partials of the head: dw[32], db, loss
 
-// x FP32 [M][2] -> BF16 [M][8], channels 2..7 zero.
+// x FP32 [M][2] -> BF16 [M][kInPad], channels 2.. zero.
 __global__ void k_input(const float *__restrict__ x, long long M, bf16 *__restrict__ xin)
 {
     pdl_entry();
@@ -576,7 +787,9 @@ __global__ void k_input(const float *__restrict__ x, long long M, bf16 *__restri
     row[1] = __float2bfloat16_rn(v.y);
 #pragma unroll
     for (int c = 2; c < kInPad; ++c) row[c] = __float2bfloat16_rn(0.0f);
-    *reinterpret_cast<uint4 *>(xin + p * kInPad) = *reinterpret_cast<const uint4 *>(row);
+#pragma unroll
+    for (int q = 0; q < kInPad / 8; ++q)
+        reinterpret_cast<uint4 *>(xin + p * kInPad)[q] = reinterpret_cast<const uint4 *>(row)[q];
 }
 
 __device__ __forceinline__ float warp_sum(float v)
@@ -747,6 +960,36 @@ __global__ void k_adam(float *__restrict__ th, const float *__restrict__ g, floa
     th[k] -= lr * (mk / b1t) / (sqrtf(vk / b2t) + 1e-8f);
 }
 
+// Halo-ordered BF16 weights of a halo GEMM: for each column tile nt (BN wide),
+// stage (cc, ta) and horizontal tap tb (tv x th taps, tap t = th ta + tb), a
+// BN x CS block in core-matrix order: element (n, ch) at
+// ((n / 8) (CS / 8) + ch / 8) 64 + (n % 8) 8 + ch % 8.  Forward (flip = 0):
+// value W[t][cc CS + ch][nt BN + n] (zero for channels >= ci, the input
+// layer's padding); 3x3 input gradient (flip = 1): W[8 - t][nt BN + n][cc CS + ch].
+// W is [tv th][ci][co] FP32.
+__global__ void k_pack_halo(const float *__restrict__ W, int ci, int co, int kin, int ncols, int BN, int CS, int tv,
+                            int th, int flip, bf16 *__restrict__ out)
+{
+    pdl_entry();
+    const long long idx = blockIdx.x * (long long)kT + threadIdx.x;
+    const long long nst = (long long)(kin / CS) * tv;
+    const long long blk = (long long)BN * CS;
+    if (idx >= (long long)(ncols / BN) * nst * th * blk) return;
+    const long long b = idx / blk;
+    const int w = (int)(idx - b * blk);
+    const int tb = (int)(b % th), st = (int)((b / th) % nst), nt = (int)(b / (th * nst));
+    const int cc = st / tv, ta = st - tv * cc;
+    const int rb = w / 64, r = w - rb * 64, nb = rb / (CS / 8), qb = rb - nb * (CS / 8);
+    const int nn = nb * 8 + r / 8, ch = qb * 8 + r % 8;
+    const int col = nt * BN + nn, kc = cc * CS + ch, t = th * ta + tb;
+    float v;
+    if (!flip)
+        v = kc < ci ? W[((size_t)t * ci + kc) * co + col] : 0.0f;
+    else
+        v = W[((size_t)(8 - t) * ci + col) * co + kc];
+    out[idx] = __float2bfloat16_rn(v);
+}
+
 // BF16 K-major matrices of a layer from its FP32 weights W [ntaps][ci][co]:
 //   forward   F[o][k], k = t cinp + c < Kf (zero where t, c are padding)
 //   backward  conv/up: Bk[c][k'], k' = t' co + o < Kb: W[8 - t'][c][o] (zero beyond 9 co);
@@ -906,6 +1149,8 @@ struct wec_net {
     bf16 *wmat = nullptr;                     // every layer's BF16 matrices
     size_t flat[wec::kNumLayers] = {};        // layer weights in theta (bias follows)
     size_t wf[wec::kNumLayers] = {}, wb[wec::kNumLayers] = {};  // forward / backward matrices in wmat
+    size_t hf[wec::kNumLayers] = {}, hb[wec::kNumLayers] = {};  // halo-ordered 3x3 matrices (forward / input gradient)
+    int bnf[wec::kNumLayers] = {}, bnb[wec::kNumLayers] = {};   // their column-tile widths
     bf16 *xin = nullptr;                      // [maxb][H][W][8]
     bf16 *act[wec::kNumLayers] = {};          // layer outputs
     float *out = nullptr;                     // [maxb][H][W]
@@ -1022,6 +1267,81 @@ int gemm(wec_net *N, cudaStream_t st, int tag, const Gat &g, const bf16 *B, int 
     }
 }
 
+// ---- convolutions with the halo kernel ----
+inline int halo_cs(int c) { return c >= 64 ? 64 : c; }  // channels per stage (c: channels of one input tensor)
+inline bool halo_fwd(int L) { return kLayers[L].kind != L_HEAD; }
+inline bool halo_bwd(int L) { return L != enc_a(0) && (kLayers[L].kind == L_CONV3 || kLayers[L].kind == L_UP3); }
+inline int halo_kin(int L, bool bwd) { return bwd ? kLayers[L].co : cin_pad(kLayers[L].ci); }
+inline int halo_mode(int kind) { return kind == L_UP3 ? H_UP3 : (kind == L_DOWN2 ? H_DOWN2 : H_CONV3); }
+
+// Column-tile width: the widest of 128 / 64 dividing ncols that still gives >= 256
+// CTAs for one image, else 32.
+int halo_bn(const wec_net *N, int level, int ncols)
+{
+    const long long tiles = (long long)level_h(N, level) * ((level_w(N, level) + kBM - 1) / kBM);
+    for (int c : {128, 64})
+        if (ncols % c == 0 && tiles * (ncols / c) >= 256) return c;
+    return 32;
+}
+
+template <int BN, int CS, bool DOWN>
+int launch_halo_t(cudaStream_t st, dim3 grid, const Halo &h, const bf16 *B, const Epi &e, int *err)
+{
+    static bool attr = false;  // dynamic shared memory above 48 KB, set once per instantiation
+    if (!attr) {
+        WEC_CK(cudaFuncSetAttribute(k_conv_halo<BN, CS, DOWN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    HaloSmem<BN, CS, DOWN>::kBytes));
+        attr = true;
+    }
+    WEC_CK(launch_k(k_conv_halo<BN, CS, DOWN>, grid, kTcThreads, HaloSmem<BN, CS, DOWN>::kBytes, st, h, B, e, err));
+    return WEC_OK;
+}
+
+template <int BN>
+int launch_halo_cs(int CS, bool down, cudaStream_t st, dim3 grid, const Halo &h, const bf16 *B, const Epi &e,
+                   int *err)
+{
+    if (down) {
+        if (CS == 64) return launch_halo_t<BN, 64, true>(st, grid, h, B, e, err);
+        if (CS == 32) return launch_halo_t<BN, 32, true>(st, grid, h, B, e, err);
+    } else {
+        if (CS == 64) return launch_halo_t<BN, 64, false>(st, grid, h, B, e, err);
+        if (CS == 32) return launch_halo_t<BN, 32, false>(st, grid, h, B, e, err);
+        if (CS == 16) return launch_halo_t<BN, 16, false>(st, grid, h, B, e, err);
+    }
+    return fail(WEC_ERR_INVALID, "net: unsupported channels per stage");
+}
+
+// A convolution of the given HaloMode whose output grid is the level's: input
+// channels [0, c0) from in0 and [c0, c0 + c1) from in1 (concatenation; c1 = 0:
+// one tensor), ncols output channels, halo-ordered weights B of tile width BN.
+int conv_halo(wec_net *N, cudaStream_t st, int tag, int mode, int batch, int level, const bf16 *in0, int c0,
+              const bf16 *in1, int c1, const bf16 *B, int BN, int ncols, const Epi &e)
+{
+    Halo h{};
+    h.in0 = in0;
+    h.in1 = in1 ? in1 : in0;
+    h.c0 = c0;
+    h.c1 = in1 ? c1 : 0;
+    h.N = batch;
+    h.H = level_h(N, level);
+    h.W = level_w(N, level);
+    h.xtiles = (h.W + kBM - 1) / kBM;
+    h.Hi = mode == H_UP3 ? h.H / 2 : (mode == H_DOWN2 ? 2 * h.H : h.H);
+    h.Wi = mode == H_UP3 ? h.W / 2 : (mode == H_DOWN2 ? 2 * h.W : h.W);
+    h.mode = mode;
+    const int CS = halo_cs(c0), tv = mode == H_DOWN2 ? 2 : 3;
+    h.nst = (h.c0 + h.c1) / CS * tv;
+    dim3 grid((unsigned)(batch * h.H * h.xtiles), (unsigned)(ncols / BN));
+    const double M = (double)batch * h.H * h.W;
+    WEC_PROF("net_conv", tag, 2.0 * M * ((double)(h.c0 + h.c1) + ncols) + 2.0 * tv * tv * (h.c0 + h.c1) * ncols, st);
+    switch (BN) {
+    case 128: return launch_halo_cs<128>(CS, mode == H_DOWN2, st, grid, h, B, e, N->err);
+    case 64: return launch_halo_cs<64>(CS, mode == H_DOWN2, st, grid, h, B, e, N->err);
+    default: return launch_halo_cs<32>(CS, mode == H_DOWN2, st, grid, h, B, e, N->err);
+    }
+}
+
 int wgrad_splits(long long M, int L, int *cps)
 {
     const int co = kLayers[L].co, BN = co % 64 == 0 ? 64 : 32;
@@ -1075,16 +1395,8 @@ int wgrad(wec_net *N, int L, int batch, const bf16 *G)
 int dx_conv(wec_net *N, int L, int batch, const bf16 *G, const Epi &e)
 {
     const LayerDef &d = kLayers[L];
-    Gat g{};
-    g.in0 = G;
-    g.c0 = d.co;
-    g.lcin = ilog2(d.co);
-    g.kind = G_CONV3;
-    g.N = batch;
-    g.H = g.Hi = level_h(N, d.level);
-    g.W = g.Wi = level_w(N, d.level);
-    g.K = 9 * d.co;
-    return gemm(N, N->st, 100 + L, g, N->wmat + N->wb[L], bwd_Kt(L), 0, d.ci, 1, e);
+    return conv_halo(N, N->st, 100 + L, H_CONV3, batch, d.level, G, d.co, nullptr, 0, N->wmat + N->hb[L], N->bnb[L],
+                     d.ci, e);
 }
 
 int pack_weights(wec_net *N)
@@ -1097,6 +1409,17 @@ int pack_weights(wec_net *N)
         WEC_CK(launch_k(k_pack, nblk(n, kT), kT, 0, N->st, (const float *)(N->theta + N->flat[L]), d.kind,
                         taps(d.kind), d.ci, d.co, cin_pad(d.ci), fwd_Kt(L), bwd_Kt(L), N->wmat + N->wf[L],
                         back ? N->wmat + N->wb[L] : (bf16 *)nullptr));
+        for (int bwd = 0; bwd < 2; ++bwd) {
+            if (!(bwd ? halo_bwd(L) : halo_fwd(L))) continue;
+            const int kin = halo_kin(L, bwd), ncols = bwd ? d.ci : d.co, BN = bwd ? N->bnb[L] : N->bnf[L];
+            const bool concat = L == cat(0) || L == cat(1) || L == cat(2);
+            const int cs = halo_cs(bwd ? d.co : (concat ? d.ci / 2 : kin));
+            const int tv = (!bwd && d.kind == L_DOWN2) ? 2 : 3;
+            const long long nh = (long long)tv * tv * kin * ncols;
+            WEC_PROF("net_pack", -1, 4.0 * weight_count(L) + 2.0 * nh, N->st);
+            WEC_CK(launch_k(k_pack_halo, nblk(nh, kT), kT, 0, N->st, (const float *)(N->theta + N->flat[L]), d.ci,
+                            d.co, kin, ncols, BN, cs, tv, tv, bwd, N->wmat + (bwd ? N->hb[L] : N->hf[L])));
+        }
     }
     N->wdirty = false;
     return WEC_OK;
@@ -1122,7 +1445,9 @@ int forward(wec_net *N, int batch, const float *x, float *out, const float *targ
         e.out0 = N->act[L];
         e.ld0 = d.co;
         const Gat g = fwd_gather(N, L, batch);
-        if (int r = gemm(N, st, L, g, N->wmat + N->wf[L], fwd_Kt(L), 0, d.co, 1, e)) return r;
+        if (int r = conv_halo(N, st, L, halo_mode(d.kind), batch, d.level, g.in0, g.c0, g.in1, g.c1,
+                              N->wmat + N->hf[L], N->bnf[L], d.co, e))
+            return r;
     }
     const int nb = nblk(M, kT);
     {
@@ -1319,6 +1644,17 @@ int wec_net_create(int H, int W, int max_batch, void *cuda_stream, wec_net **out
         N->wb[L] = nw;
         nw += bwd_elems(L);
         nw = round_up_z(nw, 64);
+        const LayerDef &d = kLayers[L];
+        if (halo_fwd(L)) {
+            N->bnf[L] = halo_bn(N, d.level, d.co);
+            N->hf[L] = nw;
+            nw = round_up_z(nw + (size_t)taps(d.kind) * halo_kin(L, false) * d.co, 64);
+        }
+        if (halo_bwd(L)) {
+            N->bnb[L] = halo_bn(N, d.level, d.ci);
+            N->hb[L] = nw;
+            nw = round_up_z(nw + 9 * (size_t)halo_kin(L, true) * d.ci, 64);
+        }
     }
     const size_t P0 = (size_t)max_batch * H * W;
     auto pix = [&](int l) { return P0 >> (2 * l); };
