@@ -363,15 +363,15 @@ def main_batch(args):
         torch.distributed.destroy_process_group()
 
 
-def train_learned(wec, torch, cfg, seed, per_seed=120, skip=40, iters=2000, batch=4):
+def train_learned(wec, torch, cfg, seed, per_seed=60, skip=40, nseeds=6, iters=2000, batch=4):
     """The learned warm start's network, trained (untimed) on the pressure
     problems of mixed-precision runs of the same tank with other wave phases
-    (seeds seed+1, seed+2): features and targets from wec_net_sample, Adam
-    on batches of 4 drawn from them."""
+    (seeds seed+1 .. seed+nseeds): features and targets from wec_net_sample,
+    Adam on batches of 4 drawn from them."""
     from paper_2206_07732_gb300 import synth
     t0 = time.perf_counter()
     ny, nx = cfg["ny"], cfg["nx"]
-    seeds = (seed + 1, seed + 2)
+    seeds = tuple(seed + 1 + k for k in range(nseeds))
     xs = torch.zeros((per_seed * len(seeds), ny, nx, 2), dtype=torch.float32, device="cuda")
     ts = torch.zeros((per_seed * len(seeds), ny, nx), dtype=torch.float32, device="cuda")
     k = 0

@@ -1073,11 +1073,11 @@ __global__ void k_features(int nx, int ny, const double *__restrict__ b, const d
     const int i = c % nx, j = c / nx;
     const double beta = cell_beta(bu, bv, nx, i, j);
     float x0 = 0.0f, x1 = 0.0f, tt = 0.0f;
-    if (s2 > 0.0 && beta > 0.0) {
-        const double rms = sqrt(s2 / (double(nx) * ny));
-        x0 = (float)(b[c] / rms);
-        x1 = (float)(0.25 * log(rho_w * beta / inp[0]));
-        if (phi) tt = (float)(phi[c] * beta / rms);
+    if (s2 > 0.0 && beta > 0.0) {  // FP32 arithmetic: the features are FP32 network inputs
+        const float irms = (float)(1.0 / sqrt(s2 / (double(nx) * ny)));
+        x0 = (float)b[c] * irms;
+        x1 = 0.25f * logf((float)(rho_w * beta) / (float)inp[0]);
+        if (phi) tt = (float)phi[c] * (float)beta * irms;
     }
     *reinterpret_cast<float2 *>(x + 2 * (size_t)c) = make_float2(x0, x1);
     if (phi) t[c] = tt;
@@ -1094,7 +1094,8 @@ __global__ void k_guess(int nx, int ny, const double *__restrict__ b, const doub
     if (c >= nx * ny) return;
     const int i = c % nx, j = c / nx;
     const double beta = cell_beta(bu, bv, nx, i, j);
-    phi[c] = (s2 > 0.0 && beta > 0.0) ? double(out[c]) * sqrt(s2 / (double(nx) * ny)) / beta : 0.0;
+    const float rms = (float)sqrt(s2 / (double(nx) * ny));  // FP32: an initial guess, judged by its FP64 residual
+    phi[c] = (s2 > 0.0 && beta > 0.0) ? double(out[c] * rms / (float)beta) : 0.0;
 }
 
 __global__ void __launch_bounds__(kT) k_guess_resid(int nx, int ny, const double *__restrict__ b,

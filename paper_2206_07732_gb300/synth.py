@@ -197,3 +197,27 @@ def unet_weights(shapes, seed):
             fan_in = int(np.prod(s[:-1]))
             parts.append((rng.standard_normal(s) * math.sqrt(2.0 / fan_in)).astype(np.float32))
     return np.concatenate([p.ravel() for p in parts])
+
+
+def unet_dyadic_case(shapes, seed, n, h, w):
+    """Seeded U-Net parameters and data on which BF16 / FP32 / FP64 arithmetic
+    are all exact: one nonzero weight (+-1) per output channel of each
+    convolution, head weights in {-1, 0, 1}, biases, inputs (2 channels) and
+    targets in half-integer steps.  Returns (flat FP32 parameters, x, t)."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for s in shapes:
+        if len(s) == 1:
+            parts.append(rng.integers(-2, 3, size=s) * 0.5)
+        elif len(s) == 2:
+            parts.append(rng.choice([-1.0, 0.0, 1.0], size=s))
+        else:
+            W = np.zeros(s)
+            kh, kw, ci, co = s
+            for o in range(co):
+                W[rng.integers(kh), rng.integers(kw), rng.integers(ci), o] = rng.choice([-1.0, 1.0])
+            parts.append(W)
+    flat = np.concatenate([p.ravel() for p in parts]).astype(np.float32)
+    x = (rng.integers(-8, 9, size=(n, h, w, 2)) * 0.5).astype(np.float32)
+    t = (rng.integers(-8, 9, size=(n, h, w)) * 0.5).astype(np.float32)
+    return flat, x, t

@@ -10,6 +10,7 @@ import pytest
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
+from oracle import tank as O  # noqa: E402
 from oracle import unet as U  # noqa: E402
 from paper_2206_07732_gb300 import build as B  # noqa: E402
 from paper_2206_07732_gb300 import synth  # noqa: E402
@@ -85,3 +86,34 @@ def test_trained_guess_on_held_out_runs(trained):
     zp = np.array([r["z"] for r in plain])
     zl = np.array([r["z"] for r in learned])
     assert np.max(np.abs(zp - zl)) <= 1e-6 * max(np.max(np.abs(zp)), 1e-3)
+
+
+def test_features_follow_their_definition():
+    # the features and target of a step's pressure problem, computed in numpy
+    # from the oracle tank's own fields (b, face coefficients, the increment
+    # p^{n+1/2} - p^{n-1/2}) after the same step, against wec_net_sample
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    B.build()
+    wec.load()
+    cfg = synth.tank_small(seed=4, nx=64, ny=32, rtol=1e-13)
+    t = wec.Tank(cfg, precision=wec.PREC_FP64)
+    t.step(cfg["dt"])
+    x = torch.zeros((32, 64, 2), dtype=torch.float32, device="cuda")
+    y = torch.zeros((32, 64), dtype=torch.float32, device="cuda")
+    wec.net_sample(t, x, y)
+    t.close()
+    o = O.OracleTank(cfg)
+    p0 = o.get(O.F_P).copy()
+    o.step(cfg["dt"])
+    b, bu, bv = o.get(O.F_RHS), o.get(O.F_BETA_U), o.get(O.F_BETA_V)
+    phi = o.get(O.F_P) - p0
+    beta = 0.25 * (bu[:, :-1] + bu[:, 1:] + bv[:-1, :] + bv[1:, :])
+    rms = np.sqrt(np.mean(b * b))
+    x0 = b / rms
+    x1 = 0.25 * np.log(cfg["rho_w"] * beta / cfg["dt"])
+    tt = phi * beta / rms
+    g = x.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(g[..., 0] - x0)) <= 1e-5 * np.max(np.abs(x0))
+    assert np.max(np.abs(g[..., 1] - x1)) <= 1e-5 * np.max(np.abs(x1))
+    assert np.max(np.abs(y.cpu().numpy() - tt)) <= 1e-4 * np.max(np.abs(tt))

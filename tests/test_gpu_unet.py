@@ -42,27 +42,11 @@ def _cuda(a):
 
 
 def _dyadic_case(seed, n, h, w):
-    """Weights with one nonzero (+-1) per output channel and half-integer biases,
-    inputs and targets: every activation, gradient and weight-gradient sum is a
-    short sum of dyadic numbers, exact in BF16 and FP32, so both sides compute
-    the same numbers exactly (no rounding happens anywhere)."""
-    rng = np.random.default_rng(seed)
-    parts = []
-    for s in U.param_shapes(32):
-        if len(s) == 1:
-            parts.append(rng.integers(-2, 3, size=s) * 0.5)
-        elif len(s) == 2:  # head [32][1]
-            parts.append(rng.choice([-1.0, 0.0, 1.0], size=s))
-        else:
-            W = np.zeros(s)
-            kh, kw, ci, co = s
-            for o in range(co):
-                W[rng.integers(kh), rng.integers(kw), rng.integers(ci), o] = rng.choice([-1.0, 1.0])
-            parts.append(W)
-    flat = np.concatenate([p.ravel() for p in parts]).astype(np.float32)
-    x = (rng.integers(-8, 9, size=(n, h, w, 2)) * 0.5).astype(np.float32)
-    t = (rng.integers(-8, 9, size=(n, h, w)) * 0.5).astype(np.float32)
-    return flat, x, t
+    # weights with one nonzero (+-1) per output channel and half-integer biases,
+    # inputs and targets: every activation, gradient and weight-gradient sum is a
+    # short sum of dyadic numbers, exact in BF16 and FP32, so both sides compute
+    # the same numbers exactly (no rounding happens anywhere)
+    return synth.unet_dyadic_case(U.param_shapes(32), seed, n, h, w)
 
 
 @pytest.mark.parametrize("n,h,w", [(2, 32, 32), (1, 16, 64), (4, 8, 32)])
