@@ -35,6 +35,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -189,18 +191,83 @@ def setup_lib():
 
 
 # ---------------------------------------------------------------- our arm --
-def time_path(L, wec, torch, cfg, precision, steps, warmup, flush, graph=True, profile_kernel=None, net=None):
+def make_controller(wec, torch, cfg, steps=8000):
+    """The host MPC of the PTO force (untimed set-up): the box's effective mass
+    and radiation damping from a free-decay run of the same tank in still water
+    (released 2 cm below its draft), then the controller with the paper's
+    parameters: dt_p 0.05 s, horizon one peak period, lam1 2 s, lam2 0.2 s,
+    |F_PTO| <= the configuration's force limit."""
+    import copy
+    from paper_2206_07732_gb300 import mpc
+    c = copy.deepcopy(cfg)
+    c["wave"] = {"kind": "regular", "H": 0.0, "T": 1.6, "phase": 0.0}
+    c["body"]["yc"] -= 0.02
+    tank = wec.Tank(c, precision=wec.PREC_MIXED)
+    recs = tank.step_n(steps, c["dt"])
+    tank.close()
+    kh = mpc.hydrostatic_stiffness(cfg["rho_w"], cfg["g"], cfg["body"]["width"])
+    m_eff, c_r, wn, zeta = mpc.identify_free_decay([r["t"] for r in recs], [r["z"] - 0.02 for r in recs], kh)
+    dt_p = 0.05
+    Np = math.ceil(cfg["wave"]["Tp"] / dt_p)
+    ctl = mpc.MPC(m_eff, kh, c_r, dt_p, Np, lam1=2.0, lam2=0.2, f_max=cfg["pto_limit"])
+    info = {"model": "FOH heave model, J_3 objective, box QP (projected Newton) on the force sequence",
+            "dt_p_s": dt_p, "Np": Np, "lam1_s": 2.0, "lam2_s": 0.2, "f_max_N_per_m": cfg["pto_limit"],
+            "identified": {"m_eff_kg_per_m": m_eff, "c_r_Ns_per_m2": c_r, "omega_n": wn, "zeta": zeta,
+                           "free_decay_steps": steps},
+            "excitation": "k_h eta(x_B, t) of the tank's incident components (analytic forecast)"}
+    return ctl, info
+
+
+class PtoSchedule:
+    """Per-step PTO force of the MPC: a QP every dt_p of simulated time, the
+    first force reached by first-order hold over the solver steps in between."""
+
+    def __init__(self, ctl, cfg, wec):
+        self.ctl, self.dt = ctl, cfg["dt"]
+        self.nsub = int(round(ctl.dt_p / cfg["dt"]))
+        amp, om, ph = wec.wave_components(cfg["wave"])
+        kw = np.array([wec.wave_number(w, cfg["depth"], cfg["g"]) for w in om])
+        xb = cfg["body"]["xc"]
+        self.fexc = lambda t: ctl.kh * float(np.sum(amp * np.cos(kw * xb - om * t + ph)))
+        self.F_now, self.ramp, self.k = 0.0, None, 0
+        self.solves, self.fmax = 0, 0.0
+
+    def force(self, z, zd):
+        """Force for the next step, given the body state after the last one."""
+        if self.k % self.nsub == 0:
+            t0 = self.k * self.dt
+            fut = [self.fexc(t0 + (i + 1) * self.ctl.dt_p) for i in range(self.ctl.Np)]
+            F_next = float(self.ctl.solve(z, zd, self.F_now, self.fexc(t0), fut)[0])
+            self.ramp = self.ctl.ramp(self.F_now, F_next, self.nsub)
+            self.F_now = F_next
+            self.solves += 1
+        f = float(self.ramp[self.k % self.nsub])
+        self.fmax = max(self.fmax, abs(f))
+        self.k += 1
+        return f
+
+
+def time_path(L, wec, torch, cfg, precision, steps, warmup, flush, graph=True, profile_kernel=None, net=None,
+              ctl=None):
     """Time K steps (CUDA events per step on the caller's stream, L2 flushed in
     between).  graph=False with profile_kernel: the eager pass that times one
     kernel's launches with event pairs (graph bodies cannot hold events).
-    net: the trained U-Net giving each solve its initial guess."""
+    net: the trained U-Net giving each solve its initial guess; ctl: the MPC
+    setting each step's PTO force (its QP runs on the host between steps)."""
+    sched = PtoSchedule(ctl, cfg, wec) if ctl is not None else None
+    state = [0.0, 0.0]
+
+    def pto():
+        return sched.force(*state) if sched else 0.0
+
     tank = wec.Tank(cfg, precision=precision)
     tank.use_graph(graph)
     if net is not None:
         tank.set_net(net)
     stream = torch.cuda.current_stream()
     for _ in range(warmup):
-        tank.step(cfg["dt"])
+        r = tank.step(cfg["dt"], pto())
+        state[:] = [r["z"], r["zdot"]]
     torch.cuda.synchronize()
     if profile_kernel:
         wec.profile_read()
@@ -213,10 +280,12 @@ def time_path(L, wec, torch, cfg, precision, steps, warmup, flush, graph=True, p
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
     for k in range(steps):
+        f = pto()  # host QP (every dt_p) outside the timed events
         flush.zero_()  # evict the working set from L2 (outside the timed events)
         ev[k][0].record(stream)
-        r = tank.step(cfg["dt"])
+        r = tank.step(cfg["dt"], f)
         ev[k][1].record(stream)
+        state[:] = [r["z"], r["zdot"]]
         its.append(r["iters"])
         res.append(r["residual"])
     torch.cuda.synchronize()
@@ -231,7 +300,8 @@ def time_path(L, wec, torch, cfg, precision, steps, warmup, flush, graph=True, p
     ms = [a.elapsed_time(b) for a, b in ev]
     stats = tank.net_stats() if net is not None else None
     tank.close()
-    return dict(ms=ms, iters=its, residual=max(res), launches=launches, wall=wall, prof=prof, net_stats=stats)
+    return dict(ms=ms, iters=its, residual=max(res), launches=launches, wall=wall, prof=prof, net_stats=stats,
+                qp_solves=sched.solves if sched else 0, max_pto=sched.fmax if sched else 0.0)
 
 
 def profile_all(wec, torch, cfg, precision, steps=2, net=None):
@@ -253,21 +323,26 @@ def profile_all(wec, torch, cfg, precision, steps=2, net=None):
     return p
 
 
-def e2e_path(wec, torch, cfg, precision, steps, warmup, flush, net=None):
+def e2e_path(wec, torch, cfg, precision, steps, warmup, flush, net=None, ctl=None):
     """Through the public call with host buffers: wec_step takes the host PTO
-    force and returns the host step record (synchronous D2H) every step."""
+    force and returns the host step record (synchronous D2H) every step; the
+    MPC's host QP (every dt_p) is inside the timed region."""
+    sched = PtoSchedule(ctl, cfg, wec) if ctl is not None else None
     tank = wec.Tank(cfg, precision=precision)
     if net is not None:
         tank.set_net(net)
+    z = zd = 0.0
     for _ in range(warmup):
-        tank.step(cfg["dt"])
+        r = tank.step(cfg["dt"], sched.force(z, zd) if sched else 0.0)
+        z, zd = r["z"], r["zdot"]
     torch.cuda.synchronize()
     t = []
     for _ in range(steps):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        tank.step(cfg["dt"], 0.0)  # result record read back to the host inside the call
+        r = tank.step(cfg["dt"], sched.force(z, zd) if sched else 0.0)  # record read back inside the call
+        z, zd = r["z"], r["zdot"]
         t.append(time.perf_counter() - t0)
     tank.close()
     return t
@@ -428,7 +503,9 @@ def main_ours(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 256 MiB > L2
     steps, warmup = args.steps, max(args.warmup, 3)
 
-    # the learned warm start's network, trained on runs of the same tank (untimed)
+    # the PTO controller (host MPC; free-decay identification untimed) and the
+    # learned warm start's network, trained on runs of the same tank (untimed)
+    ctl, ctl_info = make_controller(wec, torch, cfg)
     net, train_info = train_learned(wec, torch, cfg, args.seed)
 
     # which kernel dominates the headline path (untimed, eager, every launch timed)
@@ -449,14 +526,14 @@ def main_ours(args):
 
     clocks = Clocks(local)
     clocks.start()
-    learned = time_path(L, wec, torch, cfg, wec.PREC_MIXED, steps, warmup, flush, net=net)
+    learned = time_path(L, wec, torch, cfg, wec.PREC_MIXED, steps, warmup, flush, net=net, ctl=ctl)
     ck = clocks.stop()
-    mixed = time_path(L, wec, torch, cfg, wec.PREC_MIXED, steps, warmup, flush)
-    fp64 = time_path(L, wec, torch, cfg, wec.PREC_FP64, steps, warmup, flush)
-    mixed_mg = time_path(L, wec, torch, cfg, wec.PREC_MIXED_MG, steps, warmup, flush)
+    mixed = time_path(L, wec, torch, cfg, wec.PREC_MIXED, steps, warmup, flush, ctl=ctl)
+    fp64 = time_path(L, wec, torch, cfg, wec.PREC_FP64, steps, warmup, flush, ctl=ctl)
+    mixed_mg = time_path(L, wec, torch, cfg, wec.PREC_MIXED_MG, steps, warmup, flush, ctl=ctl)
     kpass = time_path(L, wec, torch, cfg, wec.PREC_MIXED, max(steps // 4, 5), warmup, flush, graph=False,
-                      profile_kernel=top, net=net)
-    e2e = e2e_path(wec, torch, cfg, wec.PREC_MIXED, max(steps // 2, 5), warmup, flush, net=net)
+                      profile_kernel=top, net=net, ctl=ctl)
+    e2e = e2e_path(wec, torch, cfg, wec.PREC_MIXED, max(steps // 2, 5), warmup, flush, net=net, ctl=ctl)
 
     def reduce_max(x):
         if world == 1:
@@ -542,6 +619,8 @@ def main_ours(args):
                             "mixed_mg": "FP32 V-cycles only; every step stencil FP64",
                             "fp64": "everything FP64"},
         "learned_warm_start": {"training": train_info, "guess_kept_steps": kept, "steps_with_net": tried},
+        "pto_control": dict(ctl_info, qp_solves_timed_run=learned["qp_solves"],
+                            max_abs_pto_force_timed_run=learned["max_pto"]),
         "execution": "one CUDA graph per step (conditional WHILE/IF nodes steer FGMRES on the GPU)",
         "mg_tiles_autotuned": mg_tiles,
         "fgmres_iters_per_step": {"mixed+learned": statistics.mean(learned["iters"]),

@@ -1,0 +1,74 @@
+"""The host MPC on the GPU tank: the box's effective mass and damping from a
+free-decay run of the 128x64 tank, then the controller setting the PTO force
+of the regular-wave run every 0.05 s (first-order hold in between): the force
+limit holds and the PTO absorbs energy from the waves."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2206_07732_gb300 import build as B  # noqa: E402
+from paper_2206_07732_gb300 import mpc  # noqa: E402
+from paper_2206_07732_gb300 import synth  # noqa: E402
+from paper_2206_07732_gb300 import wec  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def identified():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    B.build()
+    wec.load()
+    cfg = synth.still_water(nx=128, ny=64, body=True)
+    cfg["body"]["yc"] -= 0.02
+    t = wec.Tank(cfg, precision=wec.PREC_MIXED)
+    recs = t.step_n(4000, cfg["dt"])
+    t.close()
+    kh = mpc.hydrostatic_stiffness(cfg["rho_w"], cfg["g"], cfg["body"]["width"])
+    return cfg, kh, mpc.identify_free_decay([r["t"] for r in recs], [r["z"] - 0.02 for r in recs], kh)
+
+
+def test_free_decay_is_physical(identified):
+    cfg, kh, (m_eff, c_r, wn, zeta) = identified
+    m = cfg["body"]["mass"]
+    print(f"free decay: m_eff {m_eff:.1f} kg/m (body {m:.1f}), c_r {c_r:.1f} N s/m^2, w_n {wn:.3f}, zeta {zeta:.3f}")
+    assert m < m_eff < 4.0 * m  # the added mass of a floating box is positive
+    assert 0.0 < zeta < 0.5
+
+
+def test_mpc_closed_loop_on_the_tank(identified):
+    _, kh, (m_eff, c_r, _, _) = identified
+    cfg = synth.tank_small(seed=2)
+    cfg["body"]["pto_damping"] = 0.0
+    f_max = 50.0
+    T = cfg["wave"]["T"]
+    ctl = mpc.MPC(m_eff, kh, c_r, 0.05, math.ceil(T / 0.05), lam1=2.0, lam2=0.2, f_max=f_max)
+    amp, om, ph = wec.wave_components(cfg["wave"])
+    kw = np.array([wec.wave_number(w, cfg["depth"], cfg["g"]) for w in om])
+    xb = cfg["body"]["xc"]
+    fexc = lambda t: kh * float(np.sum(amp * np.cos(kw * xb - om * t + ph)))
+    t = wec.Tank(cfg, precision=wec.PREC_MIXED)
+    nsub = int(round(0.05 / cfg["dt"]))
+    z = zd = 0.0
+    F_now, E, Fmax = 0.0, [], 0.0
+    for k in range(int(3 * T / 0.05)):
+        t0 = k * 0.05
+        F_next = float(ctl.solve(z, zd, F_now, fexc(t0), [fexc(t0 + (i + 1) * 0.05) for i in range(ctl.Np)])[0])
+        ramp = ctl.ramp(F_now, F_next, nsub)
+        recs = t.step_n(nsub, cfg["dt"], pto=ramp)
+        zd_prev = zd
+        for f, r in zip(ramp, recs):
+            E.append(-f * 0.5 * (zd_prev + r["zdot"]) * cfg["dt"])
+            zd_prev = r["zdot"]
+            Fmax = max(Fmax, abs(r["f_pto"]))
+        z, zd = recs[-1]["z"], recs[-1]["zdot"]
+        F_now = F_next
+    t.close()
+    n1 = int(T / cfg["dt"])
+    absorbed = float(np.sum(E[n1:]))
+    print(f"closed loop: absorbed {absorbed:.4f} J/m over the last two periods, max |F_PTO| {Fmax:.2f} N/m")
+    assert Fmax <= f_max * (1 + 1e-9)
+    assert absorbed > 0.0
