@@ -259,9 +259,11 @@ void wec_net_destroy(wec_net *net);
 /* Host FP32 parameter vectors (layout above); set also resets the Adam state. */
 int wec_net_set_params(wec_net *net, const float *host, size_t n);
 int wec_net_get_params(const wec_net *net, float *host, size_t n);
-/* BF16 output (raw 16-bit words, NHWC) of layer (0 = enc0a .. 19 = dec0, the
- * order above) from the last forward pass over `batch` images; n must equal
- * batch x (H >> level) x (W >> level) x cout of that layer. */
+/* BF16 output (raw 16-bit words) of layer (0 = enc0a .. 19 = dec0, the order
+ * above) from the last forward pass over `batch` images, in the library's
+ * chunk-planar layout [batch][h][cout / 8][w][8] (h = H >> level, w = W >> level:
+ * the 8 channels [8q, 8q + 8) of a whole image row are contiguous); n must equal
+ * batch x h x w x cout. */
 int wec_net_get_activation(const wec_net *net, int layer, int batch, unsigned short *host, size_t n);
 /* Gradient of the last wec_net_loss_grad / wec_net_train_step. */
 int wec_net_get_grads(const wec_net *net, float *host, size_t n);

@@ -138,6 +138,16 @@ __device__ __forceinline__ void mma16816(float d[4], const unsigned a[4], const 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
+// ---------------------------------------------------------- tensor layout --
+// Activations and their gradients are chunk-planar BF16 tensors
+// [rows][C / 8][W][8] (row = n H + y): the 8 channels [8q, 8q + 8) of a whole
+// image row are contiguous, so a row segment of one channel chunk is one
+// contiguous block (what the convolutions stage with bulk copies).
+__device__ __forceinline__ size_t cofs(size_t row, int x, int c, int C, int W)
+{
+    return ((row * (size_t)(C >> 3) + (size_t)(c >> 3)) * (size_t)W + (size_t)x) * 8 + (size_t)(c & 7);
+}
+
 // ------------------------------------------------------------------ gather --
 // Address of the 8 channels [c, c + 8) of reduction index k for output pixel
 // (n, i, j), or nullptr where the operand is zero (outside the image, k >= K).
@@ -159,33 +169,35 @@ __device__ __forceinline__ const bf16 *gat_src(const Gat &g, int n, int i, int j
         ii = 2 * i + (t >> 1);
         jj = 2 * j + (t & 1);
     }
-    const size_t pix = ((size_t)n * g.Hi + ii) * g.Wi + jj;
-    return c < g.c0 ? g.in0 + pix * g.c0 + c : g.in1 + pix * g.c1 + (c - g.c0);
+    const size_t row = (size_t)n * g.Hi + ii;
+    return c < g.c0 ? g.in0 + cofs(row, jj, c, g.c0, g.Wi) : g.in1 + cofs(row, jj, c - g.c0, g.c1, g.Wi);
 }
 
 __device__ __forceinline__ void epi_store(const Epi &e, const Gat &g, int p, int col, float v0, float v1)
 {
+    const size_t prow = (size_t)(p / g.W);
+    const int px = p - (int)prow * g.W;
     if (e.kind == E_FWD) {
         v0 = fmaxf(v0 + e.bias[col], 0.0f);
         v1 = fmaxf(v1 + e.bias[col + 1], 0.0f);
-        *reinterpret_cast<bf162 *>(e.out0 + (size_t)p * e.ld0 + col) = __floats2bfloat162_rn(v0, v1);
+        *reinterpret_cast<bf162 *>(e.out0 + cofs(prow, px, col, e.ld0, g.W)) = __floats2bfloat162_rn(v0, v1);
     } else if (e.kind == E_DX) {
         if (col < e.nsplit) {
-            const size_t o = (size_t)p * e.ld0 + col;
+            const size_t o = cofs(prow, px, col, e.ld0, g.W);
             const bf162 m = *reinterpret_cast<const bf162 *>(e.mask0 + o);
             v0 = __bfloat162float(m.x) > 0.0f ? v0 : 0.0f;
             v1 = __bfloat162float(m.y) > 0.0f ? v1 : 0.0f;
             *reinterpret_cast<bf162 *>(e.out0 + o) = __floats2bfloat162_rn(v0, v1);
         } else {
-            *reinterpret_cast<bf162 *>(e.out1 + (size_t)p * e.ld1 + col - e.nsplit) = __floats2bfloat162_rn(v0, v1);
+            *reinterpret_cast<bf162 *>(e.out1 + cofs(prow, px, col - e.nsplit, e.ld1, g.W)) =
+                __floats2bfloat162_rn(v0, v1);
         }
     } else if (e.kind == E_F32) {
         *reinterpret_cast<float2 *>(e.outf + (size_t)p * e.ld0 + col) = make_float2(v0, v1);
     } else {  // E_DOWNDX: row p = (n, i, j) of the half grid -> (n, 2i + a, 2j + b)
         const int hw = g.H * g.W, n = p / hw, r = p - n * hw, i = r / g.W, j = r - i * g.W;
         const int a = blockIdx.z >> 1, b = blockIdx.z & 1;
-        const size_t q = ((size_t)n * (2 * g.H) + 2 * i + a) * (2 * g.W) + 2 * j + b;
-        const size_t o = q * e.ld0 + col;
+        const size_t o = cofs((size_t)n * (2 * g.H) + 2 * i + a, 2 * j + b, col, e.ld0, 2 * g.W);
         const bf162 s = *reinterpret_cast<const bf162 *>(e.add + o);
         const bf162 m = *reinterpret_cast<const bf162 *>(e.mask0 + o);
         v0 = __bfloat162float(m.x) > 0.0f ? v0 + __bfloat162float(s.x) : 0.0f;
@@ -294,9 +306,12 @@ __device__ __forceinline__ void tc_epilogue(const Epi &e, const Gat &g, unsigned
                 } else if (col < e.nsplit) {  // E_DX: ReLU mask of the layer input (nsplit is a multiple of 16)
                     __align__(16) bf16 m[16];
                     if (p < M) {
-                        const uint4 *mp = reinterpret_cast<const uint4 *>(e.mask0 + (size_t)p * e.ld0 + col);
-                        reinterpret_cast<uint4 *>(m)[0] = mp[0];
-                        reinterpret_cast<uint4 *>(m)[1] = mp[1];
+                        const size_t prow = (size_t)(p / g.W);
+                        const int px = p - (int)prow * g.W;
+                        reinterpret_cast<uint4 *>(m)[0] =
+                            *reinterpret_cast<const uint4 *>(e.mask0 + cofs(prow, px, col, e.ld0, g.W));
+                        reinterpret_cast<uint4 *>(m)[1] =
+                            *reinterpret_cast<const uint4 *>(e.mask0 + cofs(prow, px, col + 8, e.ld0, g.W));
                     } else {
 #pragma unroll
                         for (int q = 0; q < 16; ++q) m[q] = __float2bfloat16_rn(0.0f);
@@ -320,15 +335,18 @@ __device__ __forceinline__ void tc_epilogue(const Epi &e, const Gat &g, unsigned
     if (staged) {
         asm volatile("bar.sync 1, 128;\n" ::: "memory");  // the 4 epilogue warps only
         if (go) {
-            constexpr int CPR = BN / 8;  // 16-byte chunks per tile row
+            // consecutive threads: consecutive pixels of one channel chunk
+            // (contiguous in the chunk-planar layout)
 #pragma unroll 4
-            for (int c = tid; c < kBM * CPR; c += 128) {
-                const int r = c / CPR, q = c - r * CPR, pp = m0 + r;
+            for (int c = tid; c < kBM * (BN / 8); c += 128) {
+                const int q = c / kBM, r = c - q * kBM, pp = m0 + r;
                 if (pp >= M) continue;
                 const int col = n0 + q * 8;
+                const size_t prow = (size_t)(pp / g.W);
+                const int px = pp - (int)prow * g.W;
                 const uint4 val = *reinterpret_cast<const uint4 *>(smem + r * TS + q * 16);
-                bf16 *dst = (e.kind == E_DX && col >= e.nsplit) ? e.out1 + (size_t)pp * e.ld1 + (col - e.nsplit)
-                                                                : e.out0 + (size_t)pp * e.ld0 + col;
+                bf16 *dst = (e.kind == E_DX && col >= e.nsplit) ? e.out1 + cofs(prow, px, col - e.nsplit, e.ld1, g.W)
+                                                                : e.out0 + cofs(prow, px, col, e.ld0, g.W);
                 *reinterpret_cast<uint4 *>(dst) = val;
             }
         }
@@ -532,6 +550,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_halo(Halo h, const bf16 
     extern __shared__ __align__(1024) unsigned char smem[];
     using S = HaloSmem<BN, CS, DOWN>;
     constexpr int TH = S::kTH, TV = DOWN ? 2 : 3;
+    // cp.async stages a producer keeps in flight before signalling: one stage of
+    // slack between the MMA being waited for and the one being fed
+    constexpr int LAG = S::kStages - 2;
     constexpr int NS = S::kStages;
     constexpr int CH = CS / 8;  // 16-byte chunks per halo pixel
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -575,47 +596,77 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_halo(Halo h, const bf16 
             if (kt >= NS) ok = mbar_wait(empty0 + 8 * s, ((kt / NS) - 1) & 1);
             if (!ok) break;
             unsigned char *As = smem + s * S::kStage, *Bs = As + S::kA;
-            if (tid == 0) {
-                mbar_expect_tx(full0 + 8 * s, S::kB);
-                bulk_g2s(smem_u32(Bs), Bt + (size_t)kt * TH * BN * CS, S::kB, full0 + 8 * s);
-            }
             const int cc = kt / TV, ta = kt - TV * cc, cb = cc * CS;
             int y = DOWN ? 2 * i + ta : i + ta - 1;  // input row (output grid for the up mode)
             const bool row_ok = y >= 0 && y < (DOWN ? h.Hi : h.H);
             if (h.mode == H_UP3) y >>= 1;
-            const bf16 *src_row;
-            int cstride, coff;
+            const bf16 *tbase;
+            int tC, coff;
             if (cb < h.c0) {
-                src_row = h.in0;
-                cstride = h.c0;
+                tbase = h.in0;
+                tC = h.c0;
                 coff = cb;
             } else {
-                src_row = h.in1;
-                cstride = h.c1;
+                tbase = h.in1;
+                tC = h.c1;
                 coff = cb - h.c0;
             }
-            src_row += ((size_t)(n * h.Hi + (row_ok ? y : 0)) * h.Wi) * cstride + coff;
-            for (int idx = tid; idx < S::kSlots * CH; idx += 128) {
-                const int q = idx % CH, sl = idx / CH;
-                int x;      // input pixel of the slot
-                bool v;
-                if (DOWN) {
-                    const int r = sl & (kBM - 1);
-                    x = 2 * (x0 + r) + (sl >> 7);
-                    v = row_ok && x0 + r < h.W;
-                } else {
-                    x = x0 - 1 + sl;  // output-grid column
-                    v = row_ok && x >= 0 && x < h.W;
-                    if (h.mode == H_UP3) x >>= 1;
+            const size_t trow = (size_t)n * h.Hi + (row_ok ? y : 0);
+            if (!DOWN && h.mode == H_CONV3) {
+                // slots x0 - 1 + sl: the columns inside [0, W) arrive by one bulk copy
+                // per channel chunk (a contiguous row segment of its plane), the
+                // others are zero
+                const int xs = max(x0 - 1, 0), xe = min(x0 - 1 + S::kSlots, h.W), s0 = xs - (x0 - 1);
+                if (tid == 0) {
+                    const unsigned abytes = row_ok ? (unsigned)(xe - xs) * 16u * CH : 0u;
+                    mbar_expect_tx(full0 + 8 * s, S::kB + abytes);
+                    bulk_g2s(smem_u32(Bs), Bt + (size_t)kt * TH * BN * CS, S::kB, full0 + 8 * s);
+                    if (row_ok)
+                        for (int q = 0; q < CH; ++q)
+                            bulk_g2s(smem_u32(As + q * S::kLBO + s0 * 16), tbase + cofs(trow, xs, coff + 8 * q, tC, h.Wi),
+                                     (unsigned)(xe - xs) * 16u, full0 + 8 * s);
                 }
-                cp16(As + q * S::kLBO + sl * 16, v ? src_row + (size_t)x * cstride + q * 8 : h.in0, v ? 16 : 0);
+                for (int idx = tid; idx < S::kSlots * CH; idx += 128) {
+                    const int q = idx % CH, sl = idx / CH;
+                    if (!(row_ok && sl >= s0 && sl < s0 + (xe - xs)))
+                        *reinterpret_cast<uint4 *>(As + q * S::kLBO + sl * 16) = make_uint4(0u, 0u, 0u, 0u);
+                }
+            } else {
+                if (tid == 0) {
+                    mbar_expect_tx(full0 + 8 * s, S::kB);
+                    bulk_g2s(smem_u32(Bs), Bt + (size_t)kt * TH * BN * CS, S::kB, full0 + 8 * s);
+                }
+                for (int idx = tid; idx < S::kSlots * CH; idx += 128) {
+                    const int q = idx % CH, sl = idx / CH;
+                    int x;  // input pixel of the slot
+                    bool v;
+                    if (DOWN) {
+                        const int r = sl & (kBM - 1);
+                        x = 2 * (x0 + r) + (sl >> 7);
+                        v = row_ok && x0 + r < h.W;
+                    } else {
+                        x = x0 - 1 + sl;  // output-grid column
+                        v = row_ok && x >= 0 && x < h.W;
+                        x >>= 1;
+                    }
+                    cp16(As + q * S::kLBO + sl * 16, v ? tbase + cofs(trow, x, coff + 8 * q, tC, h.Wi) : h.in0,
+                         v ? 16 : 0);
+                }
             }
-            cp_commit();
-            if (kt >= kTcLag) {
-                cp_wait<kTcLag>();
+            if (!DOWN && h.mode == H_CONV3) {
+                // only bulk copies (tracked by the barrier's byte count) and zero
+                // stores of this thread: signal at once
                 asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-                mbar_arrive(full0 + 8 * ((kt - kTcLag) % NS));
-                signalled = kt - kTcLag + 1;
+                mbar_arrive(full0 + 8 * s);
+                signalled = kt + 1;
+            } else {
+                cp_commit();
+                if (kt >= LAG) {
+                    cp_wait<LAG>();
+                    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                    mbar_arrive(full0 + 8 * ((kt - LAG) % NS));
+                    signalled = kt - LAG + 1;
+                }
             }
         }
         cp_wait<0>();
@@ -657,7 +708,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_halo(Halo h, const bf16 
     if (warp < 4) {
         if (ok) ok = mbar_wait(done, 0);
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        Gat g{};  // (the staged and E_F32 epilogues need no gather)
+        Gat g{};  // the epilogue needs only the output grid
+        g.N = h.N;
+        g.H = h.H;
+        g.W = h.W;
         tc_epilogue<BN>(e, g, tmem, m0, n0, M, smem, warp, lane, tid, __all_sync(0xffffffffu, ok));
     }
     if (!ok) atomicExch(err, 1);
@@ -706,7 +760,11 @@ __global__ void __launch_bounds__(kGT) k_wgrad(Gat g, const bf16 *__restrict__ G
         }
         if (br < kBK) {
             const int p = chunk * kBK + br;
-            const bf16 *src = p < M ? G + (size_t)p * ldg + n0 + bc * 8 : G;
+            const bf16 *src = G;
+            if (p < M) {
+                const size_t prow = (size_t)(p / g.W);
+                src = G + cofs(prow, p - (int)prow * g.W, n0 + bc * 8, ldg, g.W);
+            }
             cp16(&Bs[stage][br][bc * 8], src, p < M ? 16 : 0);
         }
     };
@@ -775,12 +833,14 @@ __global__ void __launch_bounds__(kGT) k_wgrad(Gat g, const bf16 *__restrict__ G
 constexpr int kT = 256;
 constexpr int kHeadVals = 34;  // per-block partials of the head: dw[32], db, loss
 
-// x FP32 [M][2] -> BF16 [M][kInPad], channels 2.. zero.
-__global__ void k_input(const float *__restrict__ x, long long M, bf16 *__restrict__ xin)
+// x FP32 [M][2] (pixel p = row W + x) -> chunk-planar BF16 with kInPad channels, channels 2.. zero.
+__global__ void k_input(const float *__restrict__ x, long long M, int W, bf16 *__restrict__ xin)
 {
     pdl_entry();
     const long long p = blockIdx.x * (long long)kT + threadIdx.x;
     if (p >= M) return;
+    const size_t prow = (size_t)(p / W);
+    const int px = (int)(p - (long long)prow * W);
     const float2 v = *reinterpret_cast<const float2 *>(x + 2 * p);
     __align__(16) bf16 row[kInPad];
     row[0] = __float2bfloat16_rn(v.x);
@@ -789,7 +849,7 @@ __global__ void k_input(const float *__restrict__ x, long long M, bf16 *__restri
     for (int c = 2; c < kInPad; ++c) row[c] = __float2bfloat16_rn(0.0f);
 #pragma unroll
     for (int q = 0; q < kInPad / 8; ++q)
-        reinterpret_cast<uint4 *>(xin + p * kInPad)[q] = reinterpret_cast<const uint4 *>(row)[q];
+        *reinterpret_cast<uint4 *>(xin + cofs(prow, px, 8 * q, kInPad, W)) = reinterpret_cast<const uint4 *>(row)[q];
 }
 
 __device__ __forceinline__ float warp_sum(float v)
@@ -804,19 +864,20 @@ __device__ __forceinline__ float warp_sum(float v)
 // pre-activation G = bf16(dout w * (a > 0)), and per-block partials of dw, db and
 // the squared error (kHeadVals per block).
 __global__ void __launch_bounds__(kT) k_head(const bf16 *__restrict__ a, const float *__restrict__ w, long long M,
-                                             float *__restrict__ out, const float *__restrict__ target, float inv_m,
-                                             bf16 *__restrict__ G, float *__restrict__ part)
+                                             int W, float *__restrict__ out, const float *__restrict__ target,
+                                             float inv_m, bf16 *__restrict__ G, float *__restrict__ part)
 {
     pdl_entry();
     __shared__ float sh[kT / 32][kHeadVals];
     const long long p = blockIdx.x * (long long)kT + threadIdx.x;
     float av[32];
     float o = 0.0f;
+    const size_t prow = (size_t)(p / W);
+    const int px = (int)(p - (long long)prow * W);
     if (p < M) {
-        const uint4 *src = reinterpret_cast<const uint4 *>(a + p * 32);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            uint4 u = src[q];
+            uint4 u = *reinterpret_cast<const uint4 *>(a + cofs(prow, px, 8 * q, 32, W));
             const bf16 *h = reinterpret_cast<const bf16 *>(&u);
 #pragma unroll
             for (int c = 0; c < 8; ++c) av[8 * q + c] = __bfloat162float(h[c]);
@@ -835,9 +896,9 @@ __global__ void __launch_bounds__(kT) k_head(const bf16 *__restrict__ a, const f
         __align__(16) bf16 g[32];
 #pragma unroll
         for (int c = 0; c < 32; ++c) g[c] = __float2bfloat16_rn(av[c] > 0.0f ? d * w[c] : 0.0f);
-        uint4 *dst = reinterpret_cast<uint4 *>(G + p * 32);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) dst[q] = reinterpret_cast<const uint4 *>(g)[q];
+        for (int q = 0; q < 4; ++q)
+            *reinterpret_cast<uint4 *>(G + cofs(prow, px, 8 * q, 32, W)) = reinterpret_cast<const uint4 *>(g)[q];
     } else {
 #pragma unroll
         for (int c = 0; c < 32; ++c) av[c] = 0.0f;
@@ -877,8 +938,9 @@ __global__ void k_head_final(const float *__restrict__ part, int nblocks, float 
         *loss = s * inv_m;
 }
 
-// Input gradient of an upsampling layer: G[n][i][j][c] = bf16(sum of the 2x2
-// block of tmp (full grid) * (low > 0)), low the half-grid input tensor.
+// Input gradient of an upsampling layer: G(n, i, j, c) = bf16(sum of the 2x2
+// block of tmp (full grid, NHWC FP32) * (low > 0)), low the half-grid input
+// tensor; G and low chunk-planar, the thread index running in their order.
 __global__ void k_up_pool(const float *__restrict__ tmp, const bf16 *__restrict__ low, int N, int h, int w, int C,
                           bf16 *__restrict__ G)
 {
@@ -886,34 +948,48 @@ __global__ void k_up_pool(const float *__restrict__ tmp, const bf16 *__restrict_
     const long long k = blockIdx.x * (long long)kT + threadIdx.x;
     const long long total = (long long)N * h * w * C;
     if (k >= total) return;
-    const int c = (int)(k % C);
-    const long long pix = k / C;
-    const int j = (int)(pix % w);
-    const long long r = pix / w;
-    const int i = (int)(r % h), n = (int)(r / h);
+    const int c8 = (int)(k & 7);
+    const long long t = k >> 3;
+    const int j = (int)(t % w);
+    const long long t2 = t / w;
+    const int q = (int)(t2 % (C / 8));
+    const long long row = t2 / (C / 8);
+    const int i = (int)(row % h), n = (int)(row / h), c = 8 * q + c8;
     const size_t W2 = 2 * (size_t)w;
-    const size_t q = (((size_t)n * 2 * h + 2 * i) * W2 + 2 * j) * C + c;
-    const float s = (tmp[q] + tmp[q + C]) + (tmp[q + W2 * C] + tmp[q + W2 * C + C]);
+    const size_t o = (((size_t)n * 2 * h + 2 * i) * W2 + 2 * j) * C + c;
+    const float s = (tmp[o] + tmp[o + C]) + (tmp[o + W2 * C] + tmp[o + W2 * C + C]);
     G[k] = __float2bfloat16_rn(__bfloat162float(low[k]) > 0.0f ? s : 0.0f);
 }
 
-// Column sums of G [M][C] (bias gradient): per-block partials part[b][C].
-__global__ void __launch_bounds__(kT) k_colsum(const bf16 *__restrict__ G, long long M, int C, int rows_per_block,
+// Column sums of a chunk-planar G [rows][C / 8][W][8] (bias gradient): block b
+// sums rows [b rpb, (b + 1) rpb) into part[b][C].  Thread t always meets
+// channel 8 q + t % 8 of chunk q (kT is a multiple of 8).
+__global__ void __launch_bounds__(kT) k_colsum(const bf16 *__restrict__ G, int rows, int W, int C, int rpb,
                                                float *__restrict__ part)
 {
     pdl_entry();
-    __shared__ float sh[kT];
-    const int c = threadIdx.x % C, lanes = kT / C, r0 = threadIdx.x / C;
-    const long long b = (long long)blockIdx.x * rows_per_block;
-    const long long e = min(b + rows_per_block, M);
-    float s = 0.0f;
-    for (long long p = b + r0; p < e; p += lanes) s += __bfloat162float(G[p * C + c]);
-    sh[threadIdx.x] = s;
+    __shared__ float sh[32][kT];  // C / 8 <= 32 chunks
+    const int nq = C / 8;
+    float acc[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) acc[q] = 0.0f;
+    const int r0 = blockIdx.x * rpb, r1 = min(r0 + rpb, rows);
+    for (int r = r0; r < r1; ++r)
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+            if (q >= nq) break;
+            const bf16 *seg = G + ((size_t)r * nq + q) * (size_t)W * 8;
+            for (int idx = threadIdx.x; idx < W * 8; idx += kT) acc[q] += __bfloat162float(seg[idx]);
+        }
+#pragma unroll
+    for (int q = 0; q < 32; ++q)
+        if (q < nq) sh[q][threadIdx.x] = acc[q];
     __syncthreads();
     if (threadIdx.x < C) {
-        float t = 0.0f;
-        for (int q = 0; q < lanes; ++q) t += sh[q * C + threadIdx.x];
-        part[(size_t)blockIdx.x * C + threadIdx.x] = t;
+        const int q = threadIdx.x >> 3, c8 = threadIdx.x & 7;
+        float s = 0.0f;
+        for (int t = c8; t < kT; t += 8) s += sh[q][t];
+        part[(size_t)blockIdx.x * C + threadIdx.x] = s;
     }
 }
 
@@ -1378,11 +1454,12 @@ int wgrad(wec_net *N, int L, int batch, const bf16 *G)
         WEC_CK(launch_k(k_wgrad_reduce, nblk(nw, kT), kT, 0, st, (const float *)N->part, splits, Kw, d.co,
                         cin_pad(d.ci), d.ci, taps(d.kind), gw));
     }
-    const int nb = (int)std::min<long long>(kCsumBlocks, (M + 63) / 64);
-    const int rows = (int)((M + nb - 1) / nb);
+    const int rows = g.N * g.H;
+    const int nb = std::min(kCsumBlocks, rows);
+    const int rpb = (rows + nb - 1) / nb;
     {
         WEC_PROF("net_bias_grad", -1, 2.0 * M * d.co, st);
-        WEC_CK(launch_k(k_colsum, nb, kT, 0, st, G, M, d.co, rows, N->cpart));
+        WEC_CK(launch_k(k_colsum, nb, kT, 0, st, G, rows, g.W, d.co, rpb, N->cpart));
     }
     {
         WEC_PROF("net_bias_grad", -1, 4.0 * nb * d.co, st);
@@ -1436,7 +1513,7 @@ int forward(wec_net *N, int batch, const float *x, float *out, const float *targ
     const long long M = (long long)batch * N->H * N->W;
     {
         WEC_PROF("net_input", -1, 8.0 * M + 16.0 * M, st);
-        WEC_CK(launch_k(k_input, nblk(M, kT), kT, 0, st, x, M, N->xin));
+        WEC_CK(launch_k(k_input, nblk(M, kT), kT, 0, st, x, M, N->W, N->xin));
     }
     for (int L = 0; L < kHead; ++L) {
         const LayerDef &d = kLayers[L];
@@ -1454,7 +1531,7 @@ int forward(wec_net *N, int batch, const float *x, float *out, const float *targ
     {
         WEC_PROF("net_head", -1, 64.0 * M + 8.0 * M, st);
         WEC_CK(launch_k(k_head, nb, kT, 0, st, (const bf16 *)N->act[dec(0)], (const float *)(N->theta + N->flat[kHead]),
-                        M, out, target, (float)(1.0 / (double)M), N->gA[0], N->cpart));
+                        M, N->W, out, target, (float)(1.0 / (double)M), N->gA[0], N->cpart));
     }
     if (target) {
         WEC_PROF("net_head", -1, 4.0 * kHeadVals * nb, st);

@@ -458,10 +458,13 @@ class Net:
         return self._get(load().wec_net_get_grads)
 
     def activation(self, layer, batch, shape):
-        """Layer output of the last forward pass as float32 [batch, h, w, c]."""
+        """Layer output of the last forward pass as float32 [batch, h, w, c]
+        (the library's chunk-planar [batch, h, c / 8, w, 8] reordered)."""
+        n, h, w, c = shape
         a = np.empty(int(np.prod(shape)), dtype=np.uint16)
         _check(load().wec_net_get_activation(self.h, layer, batch, a.ctypes.data_as(C.POINTER(C.c_uint16)), a.size))
-        return (a.astype(np.uint32) << 16).view(np.float32).reshape(shape)
+        f = (a.astype(np.uint32) << 16).view(np.float32).reshape(n, h, c // 8, w, 8)
+        return np.ascontiguousarray(f.transpose(0, 1, 3, 2, 4).reshape(n, h, w, c))
 
     def forward(self, x, out):
         _check(load().wec_net_forward(self.h, x.shape[0], _dev32(x), _dev32(out)))
