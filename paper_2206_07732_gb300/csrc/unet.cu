@@ -278,11 +278,11 @@ __host__ __device__ constexpr unsigned umma_idesc()
 // warp-collective); the named barrier runs regardless so that no warp waits alone.
 template <int BN>
 __device__ __forceinline__ void tc_epilogue(const Epi &e, const Gat &g, unsigned tmem, int m0, int n0, int M,
-                                            unsigned char *smem, int warp, int lane, int tid, bool go)
+                                            unsigned char *smem, int warp, int lane, int tid, bool go, int ps = 1)
 {
     const bool staged = e.kind == E_FWD || e.kind == E_DX;
     constexpr int TS = BN * 2 + 16;  // staged row stride (bytes): rows 16 B apart in banks
-    const int row = warp * 32 + lane, p = m0 + row;
+    const int row = warp * 32 + lane, p = m0 + row * ps;  // tile row r is pixel m0 + r ps
     if (go) {
 #pragma unroll 1
         for (int c0 = 0; c0 < BN; c0 += 16) {
@@ -339,7 +339,7 @@ __device__ __forceinline__ void tc_epilogue(const Epi &e, const Gat &g, unsigned
             // (contiguous in the chunk-planar layout)
 #pragma unroll 4
             for (int c = tid; c < kBM * (BN / 8); c += 128) {
-                const int q = c / kBM, r = c - q * kBM, pp = m0 + r;
+                const int q = c / kBM, r = c - q * kBM, pp = m0 + r * ps;
                 if (pp >= M) continue;
                 const int col = n0 + q * 8;
                 const size_t prow = (size_t)(pp / g.W);
@@ -350,6 +350,7 @@ __device__ __forceinline__ void tc_epilogue(const Epi &e, const Gat &g, unsigned
                 *reinterpret_cast<uint4 *>(dst) = val;
             }
         }
+        asm volatile("bar.sync 1, 128;\n" ::: "memory");  // the staging tile is free again
     }
 }
 
@@ -559,12 +560,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_halo(Halo h, const bf16 
     unsigned char *bar_base = smem + NS * S::kStage;
     const unsigned full0 = smem_u32(bar_base), empty0 = full0 + 8 * NS, done = empty0 + 8 * NS;
     unsigned *tmem_slot = reinterpret_cast<unsigned *>(bar_base + 8 * (2 * NS + 1));
+    // The tile: 128 columns from x0 of output row i -- of the input row for the up
+    // mode, whose two accumulators hold the output columns 2 (x0 + r) + b, b = 0, 1
+    // (each tap of either parity reads the half-resolution row one slot apart).
+    const bool up = !DOWN && h.mode == H_UP3;
     const int xt = blockIdx.x % h.xtiles, rowid = blockIdx.x / h.xtiles;
     const int i = rowid % h.H, n = rowid / h.H, x0 = xt * kBM;
-    const int m0 = rowid * h.W + x0, M = m0 + min(kBM, h.W - x0);  // pixel rows of the tile
+    const int nvalid = min(kBM, (up ? h.Wi : h.W) - x0);  // valid tile rows
     const int n0 = blockIdx.y * BN;
     const bf16 *Bt = Bp + (size_t)blockIdx.y * h.nst * TH * BN * CS;
-    constexpr int kCols = BN < 32 ? 32 : BN;
+    constexpr int kCols = DOWN ? (BN < 32 ? 32 : BN) : 2 * BN;  // the up mode's two accumulators
 
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) {
@@ -612,11 +617,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_halo(Halo h, const bf16 
                 coff = cb - h.c0;
             }
             const size_t trow = (size_t)n * h.Hi + (row_ok ? y : 0);
-            if (!DOWN && h.mode == H_CONV3) {
-                // slots x0 - 1 + sl: the columns inside [0, W) arrive by one bulk copy
-                // per channel chunk (a contiguous row segment of its plane), the
-                // others are zero
-                const int xs = max(x0 - 1, 0), xe = min(x0 - 1 + S::kSlots, h.W), s0 = xs - (x0 - 1);
+            if (!DOWN) {
+                // slots x0 - 1 + sl of the input row: the columns inside [0, Wi) arrive
+                // by one bulk copy per channel chunk (a contiguous row segment of its
+                // plane), the others are zero
+                const int xs = max(x0 - 1, 0), xe = min(x0 - 1 + S::kSlots, h.Wi), s0 = xs - (x0 - 1);
                 if (tid == 0) {
                     const unsigned abytes = row_ok ? (unsigned)(xe - xs) * 16u * CH : 0u;
                     mbar_expect_tx(full0 + 8 * s, S::kB + abytes);
@@ -638,22 +643,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_halo(Halo h, const bf16 
                 }
                 for (int idx = tid; idx < S::kSlots * CH; idx += 128) {
                     const int q = idx % CH, sl = idx / CH;
-                    int x;  // input pixel of the slot
-                    bool v;
-                    if (DOWN) {
-                        const int r = sl & (kBM - 1);
-                        x = 2 * (x0 + r) + (sl >> 7);
-                        v = row_ok && x0 + r < h.W;
-                    } else {
-                        x = x0 - 1 + sl;  // output-grid column
-                        v = row_ok && x >= 0 && x < h.W;
-                        x >>= 1;
-                    }
+                    const int r = sl & (kBM - 1), x = 2 * (x0 + r) + (sl >> 7);  // even / odd input pixels
+                    const bool v = row_ok && x0 + r < h.W;
                     cp16(As + q * S::kLBO + sl * 16, v ? tbase + cofs(trow, x, coff + 8 * q, tC, h.Wi) : h.in0,
                          v ? 16 : 0);
                 }
             }
-            if (!DOWN && h.mode == H_CONV3) {
+            if (!DOWN) {
                 // only bulk copies (tracked by the barrier's byte count) and zero
                 // stores of this thread: signal at once
                 asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
@@ -682,19 +678,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_halo(Halo h, const bf16 
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
             const unsigned a0 = smem_u32(smem + s * S::kStage), b0 = a0 + S::kA;
+            for (int b = 0; b < (up ? 2 : 1); ++b)
 #pragma unroll
-            for (int tb = 0; tb < TH; ++tb)
+                for (int tb = 0; tb < TH; ++tb) {
+                    // slot offset of the tap: tb (3x3), the even / odd input array (down),
+                    // (b + tb + 1) / 2 (up: output column 2 (x0 + r) + b reads input x0 + r + that - 1)
+                    const int so = DOWN ? tb * kBM : (up ? (b + tb + 1) >> 1 : tb);
 #pragma unroll
-                for (int kk = 0; kk < CS / 16; ++kk) {
-                    const uint64_t ad =
-                        umma_desc_s(a0 + 2 * kk * S::kLBO + tb * (DOWN ? kBM * 16 : 16), S::kLBO, 128);
-                    const uint64_t bd = umma_desc_s(b0 + tb * (BN * CS * 2) + 2 * kk * 128, 128, CH * 128);
-                    const unsigned acc = (kt > 0 || tb > 0 || kk > 0) ? 1u : 0u;
-                    asm volatile(
-                        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-                        : "memory");
+                    for (int kk = 0; kk < CS / 16; ++kk) {
+                        const uint64_t ad = umma_desc_s(a0 + 2 * kk * S::kLBO + so * 16, S::kLBO, 128);
+                        const uint64_t bd = umma_desc_s(b0 + tb * (BN * CS * 2) + 2 * kk * 128, 128, CH * 128);
+                        const unsigned acc = (kt > 0 || tb > 0 || kk > 0) ? 1u : 0u;
+                        asm volatile(
+                            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + b * BN),
+                            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                            : "memory");
+                    }
                 }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
                              empty0 + 8 * s)
@@ -712,7 +712,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_halo(Halo h, const bf16 
         g.N = h.N;
         g.H = h.H;
         g.W = h.W;
-        tc_epilogue<BN>(e, g, tmem, m0, n0, M, smem, warp, lane, tid, __all_sync(0xffffffffu, ok));
+        const bool go = __all_sync(0xffffffffu, ok);
+        for (int b = 0; b < (up ? 2 : 1); ++b) {
+            const int ps = up ? 2 : 1, m0 = rowid * h.W + ps * x0 + b;
+            tc_epilogue<BN>(e, g, tmem + b * BN, m0, n0, m0 + ps * nvalid, smem, warp, lane, tid, go, ps);
+        }
     }
     if (!ok) atomicExch(err, 1);
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -1403,9 +1407,9 @@ int conv_halo(wec_net *N, cudaStream_t st, int tag, int mode, int batch, int lev
     h.N = batch;
     h.H = level_h(N, level);
     h.W = level_w(N, level);
-    h.xtiles = (h.W + kBM - 1) / kBM;
     h.Hi = mode == H_UP3 ? h.H / 2 : (mode == H_DOWN2 ? 2 * h.H : h.H);
     h.Wi = mode == H_UP3 ? h.W / 2 : (mode == H_DOWN2 ? 2 * h.W : h.W);
+    h.xtiles = ((mode == H_UP3 ? h.Wi : h.W) + kBM - 1) / kBM;  // the up mode tiles its input row
     h.mode = mode;
     const int CS = halo_cs(c0), tv = mode == H_DOWN2 ? 2 : 3;
     h.nst = (h.c0 + h.c1) / CS * tv;
