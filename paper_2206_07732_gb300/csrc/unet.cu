@@ -271,86 +271,64 @@ __host__ __device__ constexpr unsigned umma_idesc()
     return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(BN >> 3) << 17) | ((unsigned)(kBM >> 4) << 24);
 }
 
-// Epilogue of a tensor-core tile (warps 0-3; TMEM lane r = tile row r, pixel
-// m0 + r, valid below M).  The forward and the input-gradient epilogues stage
-// the BF16 tile in the (then idle) pipeline memory and store it with coalesced
-// 16-byte writes; the others store pairs.  go is warp-uniform (tcgen05.ld is
-// warp-collective); the named barrier runs regardless so that no warp waits alone.
+// Epilogue of a tensor-core tile: the calling warp (warp = TMEM lane quarter)
+// reads its 32 tile rows; tile row r is pixel m0 + r ps, valid below M.  The
+// forward (bias + ReLU) and input-gradient (ReLU mask of the layer input, split
+// into two outputs at nsplit) epilogues store each 8-channel chunk of a row as
+// one 16-byte vector: the warp's 32 rows are consecutive pixels of one image
+// row, so in the chunk-planar layout a warp's store of one chunk is contiguous.
+// The others store pairs.  go is warp-uniform (tcgen05.ld is warp-collective).
 template <int BN>
 __device__ __forceinline__ void tc_epilogue(const Epi &e, const Gat &g, unsigned tmem, int m0, int n0, int M,
-                                            unsigned char *smem, int warp, int lane, int tid, bool go, int ps = 1)
+                                            int warp, int lane, bool go, int ps = 1)
 {
-    const bool staged = e.kind == E_FWD || e.kind == E_DX;
-    constexpr int TS = BN * 2 + 16;  // staged row stride (bytes): rows 16 B apart in banks
-    const int row = warp * 32 + lane, p = m0 + row * ps;  // tile row r is pixel m0 + r ps
-    if (go) {
+    if (!go) return;
+    const bool vec = e.kind == E_FWD || e.kind == E_DX;
+    const int row = warp * 32 + lane, p = m0 + row * ps;
+    const size_t prow = (size_t)(p / g.W);
+    const int px = p - (int)prow * g.W;
 #pragma unroll 1
-        for (int c0 = 0; c0 < BN; c0 += 16) {
-            unsigned v[16];
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-                "[%16];\n"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-                  "=r"(v[15])
-                : "r"(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c0));
-            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-            const int col = n0 + c0;
-            if (staged) {
-                float f[16];
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+        unsigned v[16];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+            "[%16];\n"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c0));
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+        if (p >= M) continue;
+        const int col = n0 + c0;
+        if (!vec) {
 #pragma unroll
-                for (int q = 0; q < 16; ++q) f[q] = __uint_as_float(v[q]);
-                if (e.kind == E_FWD) {
-#pragma unroll
-                    for (int q = 0; q < 16; ++q) f[q] = fmaxf(f[q] + e.bias[col + q], 0.0f);
-                } else if (col < e.nsplit) {  // E_DX: ReLU mask of the layer input (nsplit is a multiple of 16)
-                    __align__(16) bf16 m[16];
-                    if (p < M) {
-                        const size_t prow = (size_t)(p / g.W);
-                        const int px = p - (int)prow * g.W;
-                        reinterpret_cast<uint4 *>(m)[0] =
-                            *reinterpret_cast<const uint4 *>(e.mask0 + cofs(prow, px, col, e.ld0, g.W));
-                        reinterpret_cast<uint4 *>(m)[1] =
-                            *reinterpret_cast<const uint4 *>(e.mask0 + cofs(prow, px, col + 8, e.ld0, g.W));
-                    } else {
-#pragma unroll
-                        for (int q = 0; q < 16; ++q) m[q] = __float2bfloat16_rn(0.0f);
-                    }
-#pragma unroll
-                    for (int q = 0; q < 16; ++q) f[q] = __bfloat162float(m[q]) > 0.0f ? f[q] : 0.0f;
-                }
-                __align__(16) bf162 h[8];
-#pragma unroll
-                for (int q = 0; q < 8; ++q) h[q] = __floats2bfloat162_rn(f[2 * q], f[2 * q + 1]);
-                uint4 *t = reinterpret_cast<uint4 *>(smem + row * TS + c0 * 2);
-                t[0] = reinterpret_cast<const uint4 *>(h)[0];
-                t[1] = reinterpret_cast<const uint4 *>(h)[1];
-            } else if (p < M) {
-#pragma unroll
-                for (int q = 0; q < 16; q += 2)
-                    epi_store(e, g, p, col + q, __uint_as_float(v[q]), __uint_as_float(v[q + 1]));
-            }
+            for (int q = 0; q < 16; q += 2) epi_store(e, g, p, col + q, __uint_as_float(v[q]), __uint_as_float(v[q + 1]));
+            continue;
         }
-    }
-    if (staged) {
-        asm volatile("bar.sync 1, 128;\n" ::: "memory");  // the 4 epilogue warps only
-        if (go) {
-            // consecutive threads: consecutive pixels of one channel chunk
-            // (contiguous in the chunk-planar layout)
-#pragma unroll 4
-            for (int c = tid; c < kBM * (BN / 8); c += 128) {
-                const int q = c / kBM, r = c - q * kBM, pp = m0 + r * ps;
-                if (pp >= M) continue;
-                const int col = n0 + q * 8;
-                const size_t prow = (size_t)(pp / g.W);
-                const int px = pp - (int)prow * g.W;
-                const uint4 val = *reinterpret_cast<const uint4 *>(smem + r * TS + q * 16);
-                bf16 *dst = (e.kind == E_DX && col >= e.nsplit) ? e.out1 + cofs(prow, px, col - e.nsplit, e.ld1, g.W)
-                                                                : e.out0 + cofs(prow, px, col, e.ld0, g.W);
-                *reinterpret_cast<uint4 *>(dst) = val;
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {  // two 8-channel chunks
+            const int cc = col + 8 * hh;
+            float f[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) f[q] = __uint_as_float(v[8 * hh + q]);
+            bf16 *dst;
+            if (e.kind == E_FWD) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) f[q] = fmaxf(f[q] + e.bias[cc + q], 0.0f);
+                dst = e.out0 + cofs(prow, px, cc, e.ld0, g.W);
+            } else if (cc < e.nsplit) {
+                const uint4 mv = *reinterpret_cast<const uint4 *>(e.mask0 + cofs(prow, px, cc, e.ld0, g.W));
+                const bf16 *m = reinterpret_cast<const bf16 *>(&mv);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) f[q] = __bfloat162float(m[q]) > 0.0f ? f[q] : 0.0f;
+                dst = e.out0 + cofs(prow, px, cc, e.ld0, g.W);
+            } else {
+                dst = e.out1 + cofs(prow, px, cc - e.nsplit, e.ld1, g.W);
             }
+            __align__(16) bf162 hv[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) hv[q] = __floats2bfloat162_rn(f[2 * q], f[2 * q + 1]);
+            *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(hv);
         }
-        asm volatile("bar.sync 1, 128;\n" ::: "memory");  // the staging tile is free again
     }
 }
 
@@ -475,7 +453,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(Gat g, const bf16 *__
         // ---- epilogue: TMEM lanes 32 warp .. +31 are this warp's rows ----
         if (ok) ok = mbar_wait(done, 0);
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        tc_epilogue<BN>(e, g, tmem, m0, n0, M, smem, warp, lane, tid, __all_sync(0xffffffffu, ok));
+        tc_epilogue<BN>(e, g, tmem, m0, n0, M, warp, lane, __all_sync(0xffffffffu, ok));
     }
     if (!ok) atomicExch(err, 1);
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -509,6 +487,7 @@ struct Halo {
     int N, H, W, xtiles;    // output image grid; 128-pixel tiles per image row
     int Hi, Wi;             // input tensor grid
     int mode, nst;          // HaloMode; stages: (c0 + c1) / CS x vertical taps
+    int ncols;              // output channels (column tiles of BN)
 };
 
 template <int BN, int CS, bool DOWN>
@@ -519,8 +498,9 @@ struct HaloSmem {
     static constexpr int kA = (CS / 8) * kLBO;
     static constexpr int kB = kTH * BN * CS * 2;
     static constexpr int kStage = kA + kB;
-    static constexpr int kStages = kStage <= 40 * 1024 ? 4 : 3;
-    static constexpr int kBytes = kStages * kStage + 256;
+    static constexpr int kFit = (227 * 1024 - 512) / kStage;
+    static constexpr int kStages = kFit >= 4 ? 4 : (kFit >= 2 ? kFit : 2);
+    static constexpr int kBytes = kStages * kStage + 512;  // + barriers and the TMEM address
 };
 
 __device__ __forceinline__ uint64_t umma_desc_s(unsigned saddr, unsigned lbo, unsigned sbo)
@@ -544,12 +524,250 @@ __device__ __forceinline__ void bulk_g2s(unsigned dst, const void *src, unsigned
         : "memory");
 }
 
+// Persistent and warp-specialised: a CTA walks the tiles blockIdx.x,
+// blockIdx.x + gridDim.x, ...; warps 0-3 stage operands through the stage ring
+// (continuing across tiles), one thread of warp 8 issues the MMAs into one of
+// two tensor-memory accumulator buffers, and warps 4-7 drain the other buffer
+// (epilogue of tile t overlapping the loads and MMAs of tile t + 1).
+constexpr int kPThreads = 288;  // warps 0-3 producers, 4-7 epilogue, 8 MMA issue
+
 template <int BN, int CS, bool DOWN>
-__global__ void __launch_bounds__(kTcThreads, 1) k_conv_halo(Halo h, const bf16 *__restrict__ Bp, Epi e, int *err)
+__global__ void __launch_bounds__(kPThreads, 1) k_conv_halo(Halo h, const bf16 *__restrict__ Bp, Epi e, int *err)
 {
     pdl_entry();
     extern __shared__ __align__(1024) unsigned char smem[];
     using S = HaloSmem<BN, CS, DOWN>;
+    constexpr int TH = S::kTH, TV = DOWN ? 2 : 3, NS = S::kStages, CH = CS / 8;
+    // cp.async stages a producer keeps in flight before signalling: one stage of
+    // slack between the MMA being waited for and the one being fed
+    constexpr int LAG = NS >= 3 ? NS - 2 : 0;
+    constexpr int kCols = DOWN ? 2 * BN : 4 * BN;  // two tile buffers (x two parities for the up mode)
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    unsigned char *bar_base = smem + NS * S::kStage;
+    const unsigned full0 = smem_u32(bar_base), empty0 = full0 + 8 * NS;
+    const unsigned accf0 = empty0 + 8 * NS, acce0 = accf0 + 16;  // accumulator full[2] / empty[2]
+    unsigned *tmem_slot = reinterpret_cast<unsigned *>(bar_base + 8 * (2 * NS + 4));
+    const bool up = !DOWN && h.mode == H_UP3;
+    const int nacc = up ? 2 : 1;
+    const int ntn = h.ncols / BN, ntiles = h.N * h.H * h.xtiles * ntn, KT = h.nst;
+
+    if (tid == 0) {
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(full0 + 8 * s, 129);  // 128 producers + the bulk copies' expect_tx arrival
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(accf0 + 8 * b, 1);
+            mbar_init(acce0 + 8 * b, 128);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 8) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const unsigned tmem = *tmem_slot;
+    bool ok = true;
+
+    // tile t: column tile nt (fastest), then 128-column tile xt of image row rowid
+    auto decode = [&](int t, int &nt, int &rowid, int &x0) {
+        nt = t % ntn;
+        const int r = t / ntn;
+        x0 = (r % h.xtiles) * kBM;
+        rowid = r / h.xtiles;
+    };
+
+    if (warp < 4) {
+        // ---- producers ----
+        long long g = 0, sig = 0;  // stages staged / signalled by this thread
+        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            int nt, rowid, x0;
+            decode(t, nt, rowid, x0);
+            const int i = rowid % h.H, n = rowid / h.H;
+            const bf16 *Bt = Bp + (size_t)nt * h.nst * TH * BN * CS;
+            for (int kt = 0; kt < KT && ok; ++kt, ++g) {
+                const int s = (int)(g % NS);
+                if (g >= NS) ok = mbar_wait(empty0 + 8 * s, (unsigned)(((g / NS) - 1) & 1));
+                if (!ok) break;
+                unsigned char *As = smem + s * S::kStage, *Bs = As + S::kA;
+                const int cc = kt / TV, ta = kt - TV * cc, cb = cc * CS;
+                int y = DOWN ? 2 * i + ta : i + ta - 1;  // input row (output grid for the up mode)
+                const bool row_ok = y >= 0 && y < (DOWN ? h.Hi : h.H);
+                if (up) y >>= 1;
+                const bf16 *tbase;
+                int tC, coff;
+                if (cb < h.c0) {
+                    tbase = h.in0;
+                    tC = h.c0;
+                    coff = cb;
+                } else {
+                    tbase = h.in1;
+                    tC = h.c1;
+                    coff = cb - h.c0;
+                }
+                const size_t trow = (size_t)n * h.Hi + (row_ok ? y : 0);
+                if (!DOWN) {
+                    // slots x0 - 1 + sl of the input row: the columns inside [0, Wi)
+                    // arrive by one bulk copy per channel chunk (a contiguous row
+                    // segment of its plane), the others are zero
+                    const int xs = max(x0 - 1, 0), xe = min(x0 - 1 + S::kSlots, h.Wi), s0 = xs - (x0 - 1);
+                    if (tid == 0) {
+                        const unsigned abytes = row_ok ? (unsigned)(xe - xs) * 16u * CH : 0u;
+                        mbar_expect_tx(full0 + 8 * s, S::kB + abytes);
+                        bulk_g2s(smem_u32(Bs), Bt + (size_t)kt * TH * BN * CS, S::kB, full0 + 8 * s);
+                        if (row_ok)
+                            for (int q = 0; q < CH; ++q)
+                                bulk_g2s(smem_u32(As + q * S::kLBO + s0 * 16),
+                                         tbase + cofs(trow, xs, coff + 8 * q, tC, h.Wi), (unsigned)(xe - xs) * 16u,
+                                         full0 + 8 * s);
+                    }
+                    for (int idx = tid; idx < S::kSlots * CH; idx += 128) {
+                        const int q = idx % CH, sl = idx / CH;
+                        if (!(row_ok && sl >= s0 && sl < s0 + (xe - xs)))
+                            *reinterpret_cast<uint4 *>(As + q * S::kLBO + sl * 16) = make_uint4(0u, 0u, 0u, 0u);
+                    }
+                    // only bulk copies (tracked by the byte count) and this thread's
+                    // zero stores: signal at once
+                    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                    mbar_arrive(full0 + 8 * s);
+                    sig = g + 1;
+                } else {
+                    if (tid == 0) {
+                        mbar_expect_tx(full0 + 8 * s, S::kB);
+                        bulk_g2s(smem_u32(Bs), Bt + (size_t)kt * TH * BN * CS, S::kB, full0 + 8 * s);
+                    }
+                    for (int idx = tid; idx < S::kSlots * CH; idx += 128) {
+                        const int q = idx % CH, sl = idx / CH;
+                        const int r = sl & (kBM - 1), x = 2 * (x0 + r) + (sl >> 7);  // even / odd input pixels
+                        const bool v = row_ok && x0 + r < h.W;
+                        cp16(As + q * S::kLBO + sl * 16, v ? tbase + cofs(trow, x, coff + 8 * q, tC, h.Wi) : h.in0,
+                             v ? 16 : 0);
+                    }
+                    cp_commit();
+                    if (g >= LAG) {
+                        cp_wait<LAG>();
+                        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                        mbar_arrive(full0 + 8 * (int)((g - LAG) % NS));
+                        sig = g - LAG + 1;
+                    }
+                }
+            }
+        }
+        cp_wait<0>();
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        if (ok)
+            for (; sig < g; ++sig) mbar_arrive(full0 + 8 * (int)(sig % NS));
+    } else if (warp == 8) {
+        if (lane == 0) {
+            // ---- MMA issue: per stage TH taps x CS / 16 K-steps (x 2 parities for up) ----
+            constexpr unsigned idesc = umma_idesc<BN>();
+            long long g = 0;
+            int lt = 0;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++lt) {
+                const int buf = lt & 1;
+                if (lt >= 2) ok = mbar_wait(acce0 + 8 * buf, (unsigned)(((lt >> 1) - 1) & 1));
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                const unsigned acc0 = tmem + (unsigned)(buf * nacc * BN);
+                for (int kt = 0; kt < KT && ok; ++kt, ++g) {
+                    const int s = (int)(g % NS);
+                    ok = mbar_wait(full0 + 8 * s, (unsigned)((g / NS) & 1));
+                    if (!ok) break;
+                    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                    const unsigned a0 = smem_u32(smem + s * S::kStage), b0 = a0 + S::kA;
+                    for (int b = 0; b < nacc; ++b)
+#pragma unroll
+                        for (int tb = 0; tb < TH; ++tb) {
+                            // slot offset of the tap: tb (3x3), the even / odd input array
+                            // (down), (b + tb + 1) / 2 (up: output column 2 (x0 + r) + b
+                            // reads input column x0 + r + that - 1)
+                            const int so = DOWN ? tb * kBM : (up ? (b + tb + 1) >> 1 : tb);
+#pragma unroll
+                            for (int kk = 0; kk < CS / 16; ++kk) {
+                                const uint64_t ad = umma_desc_s(a0 + 2 * kk * S::kLBO + so * 16, S::kLBO, 128);
+                                const uint64_t bd =
+                                    umma_desc_s(b0 + tb * (BN * CS * 2) + 2 * kk * 128, 128, CH * 128);
+                                const unsigned acc = (kt > 0 || tb > 0 || kk > 0) ? 1u : 0u;
+                                asm volatile(
+                                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                                        acc0 + (unsigned)(b * BN)),
+                                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                                    : "memory");
+                            }
+                        }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                                     empty0 + 8 * s)
+                                 : "memory");
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                                 accf0 + 8 * buf)
+                             : "memory");
+            }
+            // no MMA in flight past this point (the last tile's commit completed)
+            if (lt > 0 && !mbar_wait(accf0 + 8 * ((lt - 1) & 1), (unsigned)(((lt - 1) >> 1) & 1))) ok = false;
+        }
+    } else {
+        // ---- epilogue (warps 4-7: TMEM lanes 32 (warp - 4) .. +31) ----
+        const int ew = warp - 4;
+        Gat g{};  // the epilogue needs only the output grid
+        g.N = h.N;
+        g.H = h.H;
+        g.W = h.W;
+        int lt = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
+            const int buf = lt & 1;
+            const bool ok2 = ok && mbar_wait(accf0 + 8 * buf, (unsigned)((lt >> 1) & 1));
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const bool go = __all_sync(0xffffffffu, ok2);
+            int nt, rowid, x0;
+            decode(t, nt, rowid, x0);
+            const int ps = up ? 2 : 1, nvalid = min(kBM, (up ? h.Wi : h.W) - x0);
+            for (int b = 0; b < nacc; ++b) {
+                const int m0 = rowid * h.W + ps * x0 + b;
+                tc_epilogue<BN>(e, g, tmem + (unsigned)((buf * nacc + b) * BN), m0, nt * BN, m0 + ps * nvalid, ew,
+                                lane, go, ps);
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+            mbar_arrive(acce0 + 8 * buf);
+            if (!go) {
+                ok = false;
+                break;
+            }
+        }
+    }
+    if (!ok) atomicExch(err, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 8) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kCols) : "memory");
+    }
+}
+
+// One tile per CTA (the schedule for the full-resolution layers with at most 32
+// input channels per tensor, where many short tiles favour more resident CTAs
+// over the persistent kernel's overlap): warps 0-3 stage and then run the
+// epilogue, one thread of warp 4 issues the MMAs.
+template <int BN, int CS, bool DOWN>
+struct HaloSmem1 {
+    using P = HaloSmem<BN, CS, DOWN>;
+    static constexpr int kSlots = P::kSlots, kLBO = P::kLBO, kTH = P::kTH, kA = P::kA, kB = P::kB, kStage = P::kStage;
+    static constexpr int kStages = kStage <= 40 * 1024 ? 4 : 3;
+    static constexpr int kBytes = kStages * kStage + 256;
+};
+
+template <int BN, int CS, bool DOWN>
+__global__ void __launch_bounds__(kTcThreads, 1) k_conv_halo1(Halo h, const bf16 *__restrict__ Bp, Epi e, int *err)
+{
+    pdl_entry();
+    extern __shared__ __align__(1024) unsigned char smem[];
+    using S = HaloSmem1<BN, CS, DOWN>;
     constexpr int TH = S::kTH, TV = DOWN ? 2 : 3;
     // cp.async stages a producer keeps in flight before signalling: one stage of
     // slack between the MMA being waited for and the one being fed
@@ -715,7 +933,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_halo(Halo h, const bf16 
         const bool go = __all_sync(0xffffffffu, ok);
         for (int b = 0; b < (up ? 2 : 1); ++b) {
             const int ps = up ? 2 : 1, m0 = rowid * h.W + ps * x0 + b;
-            tc_epilogue<BN>(e, g, tmem + b * BN, m0, n0, m0 + ps * nvalid, smem, warp, lane, tid, go, ps);
+            tc_epilogue<BN>(e, g, tmem + b * BN, m0, n0, m0 + ps * nvalid, warp, lane, go, ps);
         }
     }
     if (!ok) atomicExch(err, 1);
@@ -726,6 +944,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_halo(Halo h, const bf16 
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kCols) : "memory");
     }
 }
+
 
 // Weight gradient: part[z][k][n] = sum over the rows p of split z of A(p, k)
 // G[p][n] for the weight rows [blockIdx.x kBM, +kBM) and columns [blockIdx.y BN,
@@ -1365,30 +1584,59 @@ int halo_bn(const wec_net *N, int level, int ncols)
     return 32;
 }
 
+// Persistent grid: as many CTAs as fit on the GPU at once (shared memory and
+// tensor-memory columns), at most one per tile.
 template <int BN, int CS, bool DOWN>
-int launch_halo_t(cudaStream_t st, dim3 grid, const Halo &h, const bf16 *B, const Epi &e, int *err)
+int launch_halo_t(cudaStream_t st, long long ntiles, const Halo &h, const bf16 *B, const Epi &e, int *err)
 {
+    using S = HaloSmem<BN, CS, DOWN>;
+    static int ctas = 0;  // resident CTAs on the device, computed once per instantiation
+    if (!ctas) {
+        WEC_CK(cudaFuncSetAttribute(k_conv_halo<BN, CS, DOWN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    S::kBytes));
+        int dev = 0, sms = 0, occ = 0;
+        WEC_CK(cudaGetDevice(&dev));
+        WEC_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        WEC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_conv_halo<BN, CS, DOWN>, kPThreads, S::kBytes));
+        const int cols = DOWN ? 2 * BN : 4 * BN;
+        ctas = sms * std::max(1, std::min(occ, 512 / cols));
+    }
+    const unsigned grid = (unsigned)std::min<long long>(ntiles, ctas);
+    WEC_CK(launch_k(k_conv_halo<BN, CS, DOWN>, grid, kPThreads, S::kBytes, st, h, B, e, err));
+    return WEC_OK;
+}
+
+// One tile per CTA (k_conv_halo1): grid (image rows x column tiles of 128, column tiles of BN).
+template <int BN, int CS>
+int launch_halo1_t(cudaStream_t st, const Halo &h, const bf16 *B, const Epi &e, int *err)
+{
+    using S = HaloSmem1<BN, CS, false>;
     static bool attr = false;  // dynamic shared memory above 48 KB, set once per instantiation
     if (!attr) {
-        WEC_CK(cudaFuncSetAttribute(k_conv_halo<BN, CS, DOWN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    HaloSmem<BN, CS, DOWN>::kBytes));
+        WEC_CK(cudaFuncSetAttribute(k_conv_halo1<BN, CS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    S::kBytes));
         attr = true;
     }
-    WEC_CK(launch_k(k_conv_halo<BN, CS, DOWN>, grid, kTcThreads, HaloSmem<BN, CS, DOWN>::kBytes, st, h, B, e, err));
+    dim3 grid((unsigned)(h.N * h.H * h.xtiles), (unsigned)(h.ncols / BN));
+    WEC_CK(launch_k(k_conv_halo1<BN, CS, false>, grid, kTcThreads, S::kBytes, st, h, B, e, err));
     return WEC_OK;
 }
 
 template <int BN>
-int launch_halo_cs(int CS, bool down, cudaStream_t st, dim3 grid, const Halo &h, const bf16 *B, const Epi &e,
+int launch_halo_cs(int CS, bool down, cudaStream_t st, long long ntiles, const Halo &h, const bf16 *B, const Epi &e,
                    int *err)
 {
+    // schedule: layers with at most 32 input channels per tensor (full resolution:
+    // many short tiles) one tile per CTA; the others persistent
+    if (!down && CS == 32) return launch_halo1_t<BN, 32>(st, h, B, e, err);
+    if (!down && CS == 16) return launch_halo1_t<BN, 16>(st, h, B, e, err);
     if (down) {
-        if (CS == 64) return launch_halo_t<BN, 64, true>(st, grid, h, B, e, err);
-        if (CS == 32) return launch_halo_t<BN, 32, true>(st, grid, h, B, e, err);
+        if (CS == 64) return launch_halo_t<BN, 64, true>(st, ntiles, h, B, e, err);
+        if (CS == 32) return launch_halo_t<BN, 32, true>(st, ntiles, h, B, e, err);
     } else {
-        if (CS == 64) return launch_halo_t<BN, 64, false>(st, grid, h, B, e, err);
-        if (CS == 32) return launch_halo_t<BN, 32, false>(st, grid, h, B, e, err);
-        if (CS == 16) return launch_halo_t<BN, 16, false>(st, grid, h, B, e, err);
+        if (CS == 64) return launch_halo_t<BN, 64, false>(st, ntiles, h, B, e, err);
+        if (CS == 32) return launch_halo_t<BN, 32, false>(st, ntiles, h, B, e, err);
+        if (CS == 16) return launch_halo_t<BN, 16, false>(st, ntiles, h, B, e, err);
     }
     return fail(WEC_ERR_INVALID, "net: unsupported channels per stage");
 }
@@ -1413,13 +1661,14 @@ int conv_halo(wec_net *N, cudaStream_t st, int tag, int mode, int batch, int lev
     h.mode = mode;
     const int CS = halo_cs(c0), tv = mode == H_DOWN2 ? 2 : 3;
     h.nst = (h.c0 + h.c1) / CS * tv;
-    dim3 grid((unsigned)(batch * h.H * h.xtiles), (unsigned)(ncols / BN));
+    h.ncols = ncols;
+    const long long ntiles = (long long)batch * h.H * h.xtiles * (ncols / BN);
     const double M = (double)batch * h.H * h.W;
     WEC_PROF("net_conv", tag, 2.0 * M * ((double)(h.c0 + h.c1) + ncols) + 2.0 * tv * tv * (h.c0 + h.c1) * ncols, st);
     switch (BN) {
-    case 128: return launch_halo_cs<128>(CS, mode == H_DOWN2, st, grid, h, B, e, N->err);
-    case 64: return launch_halo_cs<64>(CS, mode == H_DOWN2, st, grid, h, B, e, N->err);
-    default: return launch_halo_cs<32>(CS, mode == H_DOWN2, st, grid, h, B, e, N->err);
+    case 128: return launch_halo_cs<128>(CS, mode == H_DOWN2, st, ntiles, h, B, e, N->err);
+    case 64: return launch_halo_cs<64>(CS, mode == H_DOWN2, st, ntiles, h, B, e, N->err);
+    default: return launch_halo_cs<32>(CS, mode == H_DOWN2, st, ntiles, h, B, e, N->err);
     }
 }
 
