@@ -117,3 +117,62 @@ def test_features_follow_their_definition():
     assert np.max(np.abs(g[..., 0] - x0)) <= 1e-5 * np.max(np.abs(x0))
     assert np.max(np.abs(g[..., 1] - x1)) <= 1e-5 * np.max(np.abs(x1))
     assert np.max(np.abs(y.cpu().numpy() - tt)) <= 1e-4 * np.max(np.abs(tt))
+
+
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    B.build()
+    wec.load()
+
+
+def test_batched_forward_equals_single_images():
+    _built()
+    rng = np.random.default_rng(8)
+    x = torch.from_numpy(rng.standard_normal((3, 64, 128, 2)).astype(np.float32)).cuda()
+    net = wec.Net(64, 128, max_batch=3)
+    net.set_params(synth.unet_weights(wec.net_param_shapes(), 8))
+    out3 = torch.zeros((3, 64, 128), dtype=torch.float32, device="cuda")
+    net.forward(x, out3)
+    for k in range(3):
+        o = torch.zeros((1, 64, 128), dtype=torch.float32, device="cuda")
+        net.forward(x[k:k + 1].contiguous(), o)
+        assert torch.equal(o[0], out3[k])
+    net.close()
+
+
+def test_rejected_guess_is_the_plain_method_bit_for_bit():
+    # an untrained network's guess is worse than zero: every step falls back to
+    # phi0 = 0 and the run is identical to the plain tank's; set_net(None)
+    # restores the plain graph
+    _built()
+    cfg = synth.tank_small(seed=9, nx=128, ny=64)
+    net = wec.Net(64, 128, max_batch=1)
+    net.set_params(synth.unet_weights(wec.net_param_shapes(), 9))
+    a = wec.Tank(cfg, precision=wec.PREC_MIXED)
+    b = wec.Tank(cfg, precision=wec.PREC_MIXED)
+    b.set_net(net)
+    ra = a.step_n(20, cfg["dt"])
+    rb = b.step_n(20, cfg["dt"])
+    tried, kept = b.net_stats()
+    assert tried == 20 and kept == 0
+    assert ra == rb
+    assert np.array_equal(a.get("p"), b.get("p"))
+    b.set_net(None)
+    assert a.step_n(5, cfg["dt"]) == b.step_n(5, cfg["dt"])
+    assert b.net_stats() == (20, 0)
+    a.close()
+    b.close()
+    net.close()
+
+
+def test_net_size_must_match_the_tank():
+    _built()
+    cfg = synth.tank_small(seed=1, nx=128, ny=64)
+    t = wec.Tank(cfg)
+    net = wec.Net(64, 64, max_batch=1)
+    with pytest.raises(wec.WecError) as e:
+        t.set_net(net)
+    assert e.value.code == wec.WEC_ERR_INVALID
+    t.close()
+    net.close()
