@@ -438,7 +438,7 @@ def main_batch(args):
         torch.distributed.destroy_process_group()
 
 
-def train_learned(wec, torch, cfg, seed, per_seed=60, skip=40, nseeds=6, iters=2000, batch=4):
+def train_learned(wec, torch, cfg, seed, per_seed=60, skip=40, nseeds=10, iters=3000, batch=4):
     """The learned warm start's network, trained (untimed) on the pressure
     problems of mixed-precision runs of the same tank with other wave phases
     (seeds seed+1 .. seed+nseeds): features and targets from wec_net_sample,

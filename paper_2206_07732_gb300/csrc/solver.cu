@@ -51,19 +51,6 @@ __global__ void k_apply(int nx, int ny, const double *__restrict__ bu, const dou
     y[c] = d * double(x[c]) - offsum_at(bu, bv, x, nx, ny, i, j);
 }
 
-// w = b - A x
-__global__ void k_residual(int nx, int ny, const double *__restrict__ bu, const double *__restrict__ bv,
-                           const double *__restrict__ x, const double *__restrict__ b, double *__restrict__ w)
-{
-    pdl_entry();
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= nx * ny) return;
-    int i = c % nx, j = c / nx;
-    double d = diag_at(bu, bv, nx, ny, i, j);
-    double ax = d * x[c] - offsum_at(bu, bv, x, nx, ny, i, j);
-    w[c] = b[c] - ax;
-}
-
 // One colour of a red-black Gauss-Seidel sweep; thread k -> k-th cell of the
 // colour (nx even on every smoothed level).  first != 0: the sweep starts from
 // x = 0, so the red pass writes b / d and zeroes the black cells.
@@ -338,19 +325,6 @@ __device__ bool last_cluster(unsigned int *cnt)
     if (threadIdx.x == 0) {
         __threadfence();
         s_last = atomicAdd(cnt, 1u) == gridDim.x / kCl - 1;
-    }
-    __syncthreads();
-    return s_last != 0;
-}
-
-// True in the block that finishes last (all other blocks' writes are visible).
-__device__ bool last_block(unsigned int *cnt)
-{
-    __shared__ int s_last;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        s_last = atomicAdd(cnt, 1u) == gridDim.x - 1;
     }
     __syncthreads();
     return s_last != 0;

@@ -819,7 +819,6 @@ __global__ void k_project(TankP P, const double *__restrict__ us, const double *
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int nx = P.nx, ny = P.ny;
     const int nc = nx * ny, nu = (nx + 1) * ny, nv = nx * (ny + 1);
-    const double h = P.h;
     if (k < nu) {
         int i = k % (nx + 1), j = k / (nx + 1);
         double uu = us[k];
