@@ -2,19 +2,21 @@
 // BF16 on the tensor cores with FP32 accumulation, its training (forward,
 // backward, Adam) and its use as the initial guess of a tank's solve.
 //
-// Every convolution is an implicit GEMM: rows are output pixels (NHWC, batch
-// folded in), columns output channels, and the reduction runs over
-// (tap, input channel).  The A operand is gathered straight from the
-// activation tensors into shared memory (16-byte cp.async, zero fill at the
-// image border), so no im2col buffer exists; nearest upsampling, skip
-// concatenation and the stride-2 down convolution are gather modes of the same
-// kernel.  Forward and input-gradient GEMMs (a 3x3 convolution of the output
-// gradient with the flipped, transposed weights; one 1x1 GEMM per sub-pixel
-// for the stride-2 layer) run on tcgen05 with the accumulator in tensor memory
-// (k_conv_tc).  Weight gradients reduce over pixels, split across CTAs, with
-// m16n8k16 MMAs (k_wgrad); their partial tiles are summed in a fixed order, so
-// results are reproducible bit for bit.  ReLU masks, biases, the skip gradient
-// and the BF16 rounding are fused into the GEMM epilogues.
+// Every convolution is an implicit GEMM on tcgen05 with the accumulator in
+// tensor memory: rows are output pixels, columns output channels, the reduction
+// runs over (tap, input channel).  Activations and gradients are chunk-planar
+// BF16 tensors ([rows][C / 8][W][8]).  The forward convolutions (3x3, nearest
+// upsampling + 3x3, 2x2 stride 2) and the 3x3 input gradients (the 3x3
+// convolution of the output gradient with the flipped, transposed weights) run
+// in the halo kernels (k_conv_halo persistent and warp-specialised,
+// k_conv_halo1 one tile per CTA): a stage holds one input row of one channel
+// chunk, staged by bulk copy, and every horizontal tap reads it through a
+// shifted descriptor; the weights of a stage arrive pre-packed in one bulk copy.
+// The stride-2 layer's input gradient (one 1x1 GEMM per sub-pixel) gathers its
+// operand with cp.async (k_conv_tc).  Weight gradients reduce over pixels, split
+// across CTAs, with m16n8k16 MMAs (k_wgrad); their partial tiles are summed in a
+// fixed order, so results are reproducible bit for bit.  ReLU masks, biases,
+// the skip gradient and the BF16 rounding are fused into the GEMM epilogues.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -1289,32 +1291,13 @@ __global__ void k_pack_halo(const float *__restrict__ W, int ci, int co, int kin
     out[idx] = __float2bfloat16_rn(v);
 }
 
-// BF16 K-major matrices of a layer from its FP32 weights W [ntaps][ci][co]:
-//   forward   F[o][k], k = t cinp + c < Kf (zero where t, c are padding)
-//   backward  conv/up: Bk[c][k'], k' = t' co + o < Kb: W[8 - t'][c][o] (zero beyond 9 co);
-//             down: Bk[t][c][o] = W[t][c][o]
-__global__ void k_pack(const float *__restrict__ W, int kind, int ntaps, int ci, int co, int cinp, int Kf, int Kb,
-                       bf16 *__restrict__ F, bf16 *__restrict__ Bk)
+// BF16 copy of a stride-2 layer's weights W [4][ci][co]: the K-major matrices
+// [t][c][o] of its input-gradient GEMMs (one per sub-pixel t).
+__global__ void k_pack_down(const float *__restrict__ W, long long n, bf16 *__restrict__ Bk)
 {
     pdl_entry();
-    const long long idx = blockIdx.x * (long long)kT + threadIdx.x;
-    const long long nf = (long long)co * Kf;
-    if (idx < nf) {
-        const int o = (int)(idx / Kf), k = (int)(idx % Kf);
-        const int t = k / cinp, c = k - t * cinp;
-        const float w = (t < ntaps && c < ci) ? W[((size_t)t * ci + c) * co + o] : 0.0f;
-        F[idx] = __float2bfloat16_rn(w);
-        return;
-    }
-    if (!Bk) return;
-    const long long q = idx - nf;
-    if (kind == L_DOWN2) {
-        if (q < (long long)ntaps * ci * co) Bk[q] = __float2bfloat16_rn(W[q]);
-        return;
-    }
-    if (q >= (long long)ci * Kb) return;
-    const int c = (int)(q / Kb), k = (int)(q % Kb), t = k / co, o = k - t * co;
-    Bk[q] = __float2bfloat16_rn(t < ntaps ? W[((size_t)(8 - t) * ci + c) * co + o] : 0.0f);
+    const long long q = blockIdx.x * (long long)kT + threadIdx.x;
+    if (q < n) Bk[q] = __float2bfloat16_rn(W[q]);
 }
 
 // ------------------------------------------------- features of a pressure problem --
@@ -1448,7 +1431,7 @@ struct wec_net {
     bool wdirty = true;                       // BF16 matrices older than theta
     bf16 *wmat = nullptr;                     // every layer's BF16 matrices
     size_t flat[wec::kNumLayers] = {};        // layer weights in theta (bias follows)
-    size_t wf[wec::kNumLayers] = {}, wb[wec::kNumLayers] = {};  // forward / backward matrices in wmat
+    size_t wb[wec::kNumLayers] = {};          // stride-2 layers: input-gradient matrices in wmat
     size_t hf[wec::kNumLayers] = {}, hb[wec::kNumLayers] = {};  // halo-ordered 3x3 matrices (forward / input gradient)
     int bnf[wec::kNumLayers] = {}, bnb[wec::kNumLayers] = {};   // their column-tile widths
     bf16 *xin = nullptr;                      // [maxb][H][W][8]
@@ -1521,13 +1504,6 @@ Gat fwd_gather(const wec_net *N, int L, int batch)
     return g;
 }
 
-inline int fwd_Kt(int L) { return round_up(fwd_K(L), kTcK); }      // forward K-major row length
-inline int bwd_Kt(int L) { return kLayers[L].kind == L_DOWN2 ? kLayers[L].co : round_up(9 * kLayers[L].co, kTcK); }
-inline size_t bwd_elems(int L)
-{
-    const LayerDef &d = kLayers[L];
-    return d.kind == L_DOWN2 ? weight_count(L) : (size_t)d.ci * bwd_Kt(L);
-}
 
 template <int BN>
 int launch_tc(cudaStream_t st, dim3 grid, const Gat &g, const bf16 *B, int Kpad, size_t bz, const Epi &e, int *err)
@@ -1734,12 +1710,12 @@ int pack_weights(wec_net *N)
 {
     for (int L = 0; L < kHead; ++L) {
         const LayerDef &d = kLayers[L];
-        const bool back = L != enc_a(0);
-        const long long n = (long long)d.co * fwd_Kt(L) + (back ? (long long)bwd_elems(L) : 0);
-        WEC_PROF("net_pack", -1, 4.0 * weight_count(L) + 2.0 * n, N->st);
-        WEC_CK(launch_k(k_pack, nblk(n, kT), kT, 0, N->st, (const float *)(N->theta + N->flat[L]), d.kind,
-                        taps(d.kind), d.ci, d.co, cin_pad(d.ci), fwd_Kt(L), bwd_Kt(L), N->wmat + N->wf[L],
-                        back ? N->wmat + N->wb[L] : (bf16 *)nullptr));
+        if (d.kind == L_DOWN2) {
+            const long long n = (long long)weight_count(L);
+            WEC_PROF("net_pack", -1, 6.0 * n, N->st);
+            WEC_CK(launch_k(k_pack_down, nblk(n, kT), kT, 0, N->st, (const float *)(N->theta + N->flat[L]), n,
+                            N->wmat + N->wb[L]));
+        }
         for (int bwd = 0; bwd < 2; ++bwd) {
             if (!(bwd ? halo_bwd(L) : halo_fwd(L))) continue;
             const int kin = halo_kin(L, bwd), ncols = bwd ? d.ci : d.co, BN = bwd ? N->bnb[L] : N->bnf[L];
@@ -1969,13 +1945,11 @@ int wec_net_create(int H, int W, int max_batch, void *cuda_stream, wec_net **out
         N->flat[L] = off;
         off += weight_count(L) + kLayers[L].co;
         if (L == kHead) break;
-        N->wf[L] = nw;
-        nw += (size_t)fwd_Kt(L) * kLayers[L].co;
-        nw = round_up_z(nw, 64);
-        N->wb[L] = nw;
-        nw += bwd_elems(L);
-        nw = round_up_z(nw, 64);
         const LayerDef &d = kLayers[L];
+        if (d.kind == L_DOWN2) {
+            N->wb[L] = nw;
+            nw = round_up_z(nw + weight_count(L), 64);
+        }
         if (halo_fwd(L)) {
             N->bnf[L] = halo_bn(N, d.level, d.co);
             N->hf[L] = nw;
