@@ -1550,13 +1550,15 @@ inline bool halo_bwd(int L) { return L != enc_a(0) && (kLayers[L].kind == L_CONV
 inline int halo_kin(int L, bool bwd) { return bwd ? kLayers[L].co : cin_pad(kLayers[L].ci); }
 inline int halo_mode(int kind) { return kind == L_UP3 ? H_UP3 : (kind == L_DOWN2 ? H_DOWN2 : H_CONV3); }
 
-// Column-tile width: the widest of 128 / 64 dividing ncols that still gives >= 256
-// CTAs for one image, else 32.
-int halo_bn(const wec_net *N, int level, int ncols)
+// Column-tile width: the widest of 128 / 64 dividing ncols that still gives >= 128
+// tiles for one image (measured: wider tiles beat more, narrower ones down to
+// about one tile per SM), else 32.  The up mode tiles the half-resolution row.
+int halo_bn(const wec_net *N, int level, int ncols, bool up = false)
 {
-    const long long tiles = (long long)level_h(N, level) * ((level_w(N, level) + kBM - 1) / kBM);
+    const int w = up ? level_w(N, level) / 2 : level_w(N, level);
+    const long long tiles = (long long)level_h(N, level) * ((w + kBM - 1) / kBM);
     for (int c : {128, 64})
-        if (ncols % c == 0 && tiles * (ncols / c) >= 256) return c;
+        if (ncols % c == 0 && tiles * (ncols / c) >= 128) return c;
     return 32;
 }
 
@@ -1951,7 +1953,7 @@ int wec_net_create(int H, int W, int max_batch, void *cuda_stream, wec_net **out
             nw = round_up_z(nw + weight_count(L), 64);
         }
         if (halo_fwd(L)) {
-            N->bnf[L] = halo_bn(N, d.level, d.co);
+            N->bnf[L] = halo_bn(N, d.level, d.co, d.kind == L_UP3);
             N->hf[L] = nw;
             nw = round_up_z(nw + (size_t)taps(d.kind) * halo_kin(L, false) * d.co, 64);
         }
