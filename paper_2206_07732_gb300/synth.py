@@ -221,3 +221,75 @@ def unet_dyadic_case(shapes, seed, n, h, w):
     x = (rng.integers(-8, 9, size=(n, h, w, 2)) * 0.5).astype(np.float32)
     t = (rng.integers(-8, 9, size=(n, h, w)) * 0.5).astype(np.float32)
     return flat, x, t
+
+
+def random_coefficients3(nx, ny, nz, seed, contrast=1.0):
+    """Seeded positive face coefficients of the 3D pressure operator.
+
+    Arrays (x fastest): beta_x (nz, ny, nx+1), beta_y (nz, ny+1, nx), beta_z
+    (nz+1, ny, nx).  Wall and bed faces are zero (Neumann); the top faces are
+    kept (Dirichlet p = 0 above the top layer).  ``contrast`` > 1 draws a
+    log-uniform spread over that ratio."""
+    rng = np.random.default_rng(seed)
+    hi = math.log(max(contrast, 1.0))
+
+    def draw(shape):
+        return np.exp(rng.uniform(0.0, hi, size=shape)) if contrast > 1 else 0.5 + rng.uniform(size=shape)
+
+    bx, by, bz = draw((nz, ny, nx + 1)), draw((nz, ny + 1, nx)), draw((nz + 1, ny, nx))
+    bx[:, :, 0] = bx[:, :, nx] = 0.0
+    by[:, 0, :] = by[:, ny, :] = 0.0
+    bz[0] = 0.0
+    return bx, by, bz
+
+
+# Face-coefficient magnitudes of the 3D tank's pressure equation at dt = 1e-3 s
+# (water, air, and the Brinkman-penalised body with kappa_p = 1e-8): the values
+# the coefficient field takes in each region.
+BETA3_WATER, BETA3_AIR, BETA3_BODY = 1e-3 / 1025.0, 1e-3 / 1.225, 1e-8
+
+
+def poisson3d_case(nx=512, ny=256, nz=256, seed=0, lx=8.0, depth=2.0, Hs=0.2, ncomp=128, body=True):
+    """Seeded coefficient field and right-hand side with the structure of the 3D
+    tank's pressure equation: an 8 m x 4 m x 4 m tank (h = lx / nx), water below
+    a unidirectional irregular surface (ncomp components along x with seeded
+    phases and amplitudes giving a significant height ~Hs), air above, the
+    coefficient blended linearly over one cell at the surface, and a vertical
+    cylinder (radius 0.5 m, length 0.8 m, centred on the still-water level at
+    the tank's centre) holding the body value.  Wall and bed faces are zero.
+    The right-hand side is standard normal (every wavelength present).
+    Returns (bx, by, bz, b) as FP64 arrays (layouts of random_coefficients3)."""
+    rng = np.random.default_rng(seed)
+    h = lx / nx
+    ly, lz = ny * h, nz * h
+    k = 2.0 * math.pi * rng.uniform(0.2, 2.0, ncomp)
+    a = rng.rayleigh(1.0, ncomp)
+    a *= Hs / (4.0 * math.sqrt(0.5 * np.sum(a * a)))
+    ph = rng.uniform(0.0, 2.0 * math.pi, ncomp)
+
+    def surface(x):
+        return depth + np.sum(a[None, :] * np.cos(k[None, :] * x[:, None] + ph[None, :]), axis=1)
+
+    xc, yc, zc = (np.arange(nx) + 0.5) * h, (np.arange(ny) + 0.5) * h, (np.arange(nz) + 0.5) * h
+    xf, yf, zf = np.arange(nx + 1) * h, np.arange(ny + 1) * h, np.arange(nz + 1) * h
+    R, L, x0, y0 = 0.5, 0.8, 0.5 * lx, 0.5 * ly
+
+    def field(X, Y, Z, eta):
+        s = np.clip(0.5 + (Z - eta) / h, 0.0, 1.0)
+        beta = (1.0 - s) * BETA3_WATER + s * BETA3_AIR
+        if body:
+            inside = (np.hypot(X - x0, Y - y0) < R) & (np.abs(Z - depth) < 0.5 * L)
+            beta = np.where(inside, BETA3_BODY, beta)
+        return beta
+
+    Zx, Yx, Xx = np.meshgrid(zc, yc, xf, indexing="ij")
+    bx = field(Xx, Yx, Zx, surface(xf)[None, None, :])
+    Zy, Yy, Xy = np.meshgrid(zc, yf, xc, indexing="ij")
+    by = field(Xy, Yy, Zy, surface(xc)[None, None, :])
+    Zz, Yz, Xz = np.meshgrid(zf, yc, xc, indexing="ij")
+    bz = field(Xz, Yz, Zz, surface(xc)[None, None, :])
+    bx[:, :, 0] = bx[:, :, nx] = 0.0
+    by[:, 0, :] = by[:, ny, :] = 0.0
+    bz[0] = 0.0
+    b = rng.standard_normal((nz, ny, nx))
+    return bx, by, bz, b
