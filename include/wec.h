@@ -344,6 +344,30 @@ int wec_poisson_vcycle(wec_poisson *P, const double *b, double *x);
 int wec_poisson_solve(wec_poisson *P, const double *b, double *x, double rtol, int max_iters,
                       int *iters, double *final_rel_residual);
 
+/* ---- three dimensions ---------------------------------------------------- */
+/* The pressure operator of the projection with d = 3 (section "Continuous
+ * equations of motion"; z vertical) on an nx x ny x nz cell grid:
+ * (A p)_c = sum over the cell's six faces of beta_f (p_c - p_nb), the walls
+ * x = 0, x = lx, y = 0, y = ly and the bed Neumann whatever beta holds there,
+ * the top face Dirichlet p = 0 (ghost -p_c).  Layouts, x fastest: cells
+ * [nz][ny][nx]; beta_x [nz][ny][nx+1]; beta_y [nz][ny+1][nx]; beta_z
+ * [nz+1][ny][nx] (face k below cell layer k).  The same object type and the
+ * same apply / vcycle / solve calls as in 2D (vectors of nx*ny*nz doubles).
+ * Preconditioner: one V(mg_pre, mg_post) cycle with red-black Gauss-Seidel
+ * (colour (i+j+k) mod 2), 2x2x2 sum restriction, piecewise-constant
+ * prolongation, coarse face = half the sum of the four fine faces it covers,
+ * dense LU on the coarsest level; coarsening halves all three sizes while all
+ * are even and >= 4, and must end at <= 512 cells.  WEC_PREC_MIXED runs the
+ * V-cycle in FP32 (FP32 copies of the hierarchy) inside the FP64 FGMRES.
+ * nx, ny >= 2, nz >= 2; every face array below 2^31 entries; otherwise
+ * WEC_ERR_INVALID. */
+int wec_poisson_create3(int nx, int ny, int nz, const wec_solver_opts *opts, void *cuda_stream,
+                        wec_poisson **out);
+/* beta_x, beta_y, beta_z: device, sizes as above.  Copied; builds the
+ * hierarchy.  WEC_ERR_INVALID on a 2D object (and set_coefficients on a 3D one). */
+int wec_poisson_set_coefficients3(wec_poisson *P, const double *beta_x, const double *beta_y,
+                                  const double *beta_z);
+
 /* ---- without device allocation ------------------------------------------ */
 /* ||b - A x||_2 for the pressure operator above (same coefficient layout and
  * boundary rules as wec_poisson_*), written to *norm_out (device, 1 double).

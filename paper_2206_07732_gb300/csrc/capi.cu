@@ -354,7 +354,8 @@ int wec_load(wec_tank *T, const void *buf, size_t n)
     return wec_set_state(T, sc[0], sc[1], sc[2], sc[3]);
 }
 
-int wec_poisson_create(int nx, int ny, const wec_solver_opts *opts, void *cuda_stream, wec_poisson **out)
+static int poisson_create_any(int nx, int ny, int nz, const wec_solver_opts *opts, void *cuda_stream,
+                              wec_poisson **out)
 {
     if (!out) return fail(WEC_ERR_INVALID, "out is NULL");
     *out = nullptr;
@@ -363,7 +364,7 @@ int wec_poisson_create(int nx, int ny, const wec_solver_opts *opts, void *cuda_s
     wec_poisson *P = new (std::nothrow) wec_poisson();
     if (!P) return fail(WEC_ERR_NOMEM, "host allocation failed");
     int rc = poisson_init(P, nx, ny, opts->precision, opts->restart, opts->mg_pre, opts->mg_post,
-                          (cudaStream_t)cuda_stream);
+                          (cudaStream_t)cuda_stream, nz);
     if (rc != WEC_OK) {
         std::string msg = g_err;
         poisson_free(P);
@@ -373,6 +374,18 @@ int wec_poisson_create(int nx, int ny, const wec_solver_opts *opts, void *cuda_s
     }
     *out = P;
     return WEC_OK;
+}
+
+int wec_poisson_create(int nx, int ny, const wec_solver_opts *opts, void *cuda_stream, wec_poisson **out)
+{
+    return poisson_create_any(nx, ny, 1, opts, cuda_stream, out);
+}
+
+int wec_poisson_create3(int nx, int ny, int nz, const wec_solver_opts *opts, void *cuda_stream, wec_poisson **out)
+{
+    if (out) *out = nullptr;
+    if (nz < 2) return fail(WEC_ERR_INVALID, "poisson3: nz must be >= 2");
+    return poisson_create_any(nx, ny, nz, opts, cuda_stream, out);
 }
 
 void wec_poisson_destroy(wec_poisson *P)
@@ -386,9 +399,24 @@ void wec_poisson_destroy(wec_poisson *P)
 int wec_poisson_set_coefficients(wec_poisson *P, const double *bu, const double *bv)
 {
     if (!P || !bu || !bv) return fail(WEC_ERR_INVALID, "NULL argument");
+    if (P->nz > 1) return fail(WEC_ERR_INVALID, "a 3D operator takes wec_poisson_set_coefficients3");
     size_t nu = (size_t)(P->nx + 1) * P->ny, nv = (size_t)P->nx * (P->ny + 1);
     WEC_CK(cudaMemcpyAsync(P->L64[0].bu, bu, nu * 8, cudaMemcpyDeviceToDevice, P->st));
     WEC_CK(cudaMemcpyAsync(P->L64[0].bv, bv, nv * 8, cudaMemcpyDeviceToDevice, P->st));
+    int e = poisson_build(P, P->st);
+    if (e) return e;
+    WEC_CK(cudaStreamSynchronize(P->st));
+    return WEC_OK;
+}
+
+int wec_poisson_set_coefficients3(wec_poisson *P, const double *bx, const double *by, const double *bz)
+{
+    if (!P || !bx || !by || !bz) return fail(WEC_ERR_INVALID, "NULL argument");
+    if (P->nz == 1) return fail(WEC_ERR_INVALID, "a 2D operator takes wec_poisson_set_coefficients");
+    const size_t nx = P->nx, ny = P->ny, nz = P->nz;
+    WEC_CK(cudaMemcpyAsync(P->L64[0].bu, bx, (nx + 1) * ny * nz * 8, cudaMemcpyDeviceToDevice, P->st));
+    WEC_CK(cudaMemcpyAsync(P->L64[0].bv, by, nx * (ny + 1) * nz * 8, cudaMemcpyDeviceToDevice, P->st));
+    WEC_CK(cudaMemcpyAsync(P->L64[0].bw, bz, nx * ny * (nz + 1) * 8, cudaMemcpyDeviceToDevice, P->st));
     int e = poisson_build(P, P->st);
     if (e) return e;
     WEC_CK(cudaStreamSynchronize(P->st));

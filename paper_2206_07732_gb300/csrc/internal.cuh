@@ -85,8 +85,9 @@ bool enabled();                // event profiling on (graphs are then not used)
 // ------------------------------------------------------------------ solver --
 template <typename T>
 struct Level {
-    int nx = 0, ny = 0;
+    int nx = 0, ny = 0, nz = 1;  // nz > 1: a level of the 3D operator (bu, bv, bw = beta_x, beta_y, beta_z)
     T *bu = nullptr, *bv = nullptr, *x = nullptr, *b = nullptr;
+    T *bw = nullptr;
     T *xp = nullptr;  // pre-smoothed iterate of a tiled (fused) level, read by its post kernel
     T *id = nullptr;  // 1 / diagonal per cell, formed by poisson_build (fused V-cycle)
 };
@@ -103,6 +104,7 @@ struct KState {
 
 struct wec_poisson {
     int nx = 0, ny = 0, nlev = 0, prec = 0, restart = 20, nu1 = 2, nu2 = 2;
+    int nz = 1;                 // > 1: the 3D operator (wec_poisson_create3)
     cudaStream_t st = nullptr;
     bool have_coef = false;
     wec::Level<double> L64[wec::kMaxLevels];
@@ -135,9 +137,9 @@ namespace wec {
 
 // solver.cu
 int poisson_init(wec_poisson *P, int nx, int ny, int prec, int restart, int nu1, int nu2,
-                 cudaStream_t st);
+                 cudaStream_t st, int nz = 1);
 void poisson_free(wec_poisson *P);
-// Level-0 coefficients already in P->L64[0].bu / bv (device): build coarse levels,
+// Level-0 coefficients already in P->L64[0].bu / bv (/ bw in 3D) (device): build coarse levels,
 // FP32 copies and the coarse LU (enqueued on st).
 int poisson_build(wec_poisson *P, cudaStream_t st);
 // Host-polled FGMRES solve on P->st.

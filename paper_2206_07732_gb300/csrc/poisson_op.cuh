@@ -30,4 +30,39 @@ __device__ __forceinline__ T offsum_at(const T *bu, const T *bv, const TX *x, in
     return s;
 }
 
+// Three dimensions (z vertical): cells [nz][ny][nx], beta_x [nz][ny][nx+1],
+// beta_y [nz][ny+1][nx], beta_z [nz+1][ny][nx] (face k of beta_z is the bottom
+// face of cell layer k); the walls and the bed are Neumann, the top face
+// Dirichlet (counted twice in the diagonal).  c = (k ny + j) nx + i; index
+// arithmetic in 32 bits (the library caps every array below 2^31 entries).
+template <typename T>
+__device__ __forceinline__ T diag3_at(const T *bx, const T *by, const T *bz, int nx, int ny, int nz, int i, int j,
+                                      int k)
+{
+    const int r = k * ny + j, fx = r * (nx + 1) + i, fy = (r + k) * nx + i, c = r * nx + i;
+    T d = T(0);
+    if (i > 0) d += bx[fx];
+    if (i < nx - 1) d += bx[fx + 1];
+    if (j > 0) d += by[fy];
+    if (j < ny - 1) d += by[fy + nx];
+    if (k > 0) d += bz[c];
+    d += (k < nz - 1 ? T(1) : T(2)) * bz[c + nx * ny];
+    return d;
+}
+
+template <typename T, typename TX>
+__device__ __forceinline__ T offsum3_at(const T *bx, const T *by, const T *bz, const TX *x, int nx, int ny, int nz,
+                                        int i, int j, int k)
+{
+    const int r = k * ny + j, fx = r * (nx + 1) + i, fy = (r + k) * nx + i, c = r * nx + i, pl = nx * ny;
+    T s = T(0);
+    if (i > 0) s += bx[fx] * T(x[c - 1]);
+    if (i < nx - 1) s += bx[fx + 1] * T(x[c + 1]);
+    if (j > 0) s += by[fy] * T(x[c - nx]);
+    if (j < ny - 1) s += by[fy + nx] * T(x[c + nx]);
+    if (k > 0) s += bz[c] * T(x[c - pl]);
+    if (k < nz - 1) s += bz[c + pl] * T(x[c + pl]);
+    return s;
+}
+
 }  // namespace wec

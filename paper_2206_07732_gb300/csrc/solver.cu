@@ -264,6 +264,8 @@ namespace {
 
 bool g_mg_fused = true;  // fused V-cycle kernels (wec_set_option "mg_fused")
 
+#include "mg3d.cuh"
+
 // --------------------------------------------------- Krylov (FP64 outer) ----
 // Device-resident FGMRES state: the iteration is steered by the GPU, so the
 // same kernels run host-polled (one status read per iteration) or inside one
@@ -460,6 +462,25 @@ __global__ void k_ks_init(KState *ks, double rtol, int maxit, int m)
     ks->ncycles = 0;
 }
 
+// The FP64 level-0 operator seen by the Krylov kernels: D = 2 (bx, by = beta_u,
+// beta_v; nz = 1) or D = 3 (beta_x, beta_y, beta_z).
+struct Op0 {
+    int nx, ny, nz;
+    const double *bx, *by, *bz;
+};
+
+template <int D>
+__device__ __forceinline__ double op_offsum(const Op0 &o, const double *__restrict__ x, long long c)
+{
+    if constexpr (D == 2) {
+        const int j = (int)(c / o.nx), i = (int)(c - (long long)j * o.nx);
+        return offsum_at(o.bx, o.by, x, o.nx, o.ny, i, j);
+    } else {
+        const int cc = (int)c, r = cc / o.nx, i = cc - r * o.nx, k = r / o.ny, j = r - k * o.ny;
+        return offsum3_at(o.bx, o.by, o.bz, x, o.nx, o.ny, o.nz, i, j, k);
+    }
+}
+
 // d = diag(A) of level 0 (FP64), once per set of coefficients.
 __global__ void k_diag0(int nx, int ny, const double *__restrict__ bu, const double *__restrict__ bv,
                         double *__restrict__ d)
@@ -499,16 +520,16 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 2)
 // mode 1 (end of a cycle): converged, out of iterations, or restart.
 // A zero right-hand side gives x = 0.  Opens a new Arnoldi cycle unless done and
 // sets the WHILE condition to !done.
+template <int D>
 __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 2)
-    k_residual_norm(int nx, int ny, const double *__restrict__ bu, const double *__restrict__ bv,
-                    const double *__restrict__ d0, const double *__restrict__ b, double *x, double *__restrict__ w,
-                    float *__restrict__ b32, double *sc, double *part, KState *ks, double *g, int mode,
-                    unsigned long long hwhile, int use)
+    k_residual_norm(Op0 op, const double *__restrict__ d0, const double *__restrict__ b, double *x,
+                    double *__restrict__ w, float *__restrict__ b32, double *sc, double *part, KState *ks, double *g,
+                    int mode, unsigned long long hwhile, int use)
 {
     pdl_entry();
     __shared__ double sh[KT / 32];
     __shared__ double bsm[1];
-    const long long n = (long long)nx * ny;
+    const long long n = (long long)op.nx * op.ny * op.nz;
     const bool zero = ks->bn == 0.0;
     double a = 0.0;
     for (long long c = blockIdx.x * (long long)KT + threadIdx.x; c < n; c += (long long)gridDim.x * KT) {
@@ -517,8 +538,7 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 2)
             w[c] = 0.0;
             continue;
         }
-        const int j = (int)(c / nx), i = (int)(c - (long long)j * nx);
-        double r = b[c] - (d0[c] * x[c] - offsum_at(bu, bv, x, nx, ny, i, j));
+        double r = b[c] - (d0[c] * x[c] - op_offsum<D>(op, x, c));
         w[c] = r;
         if (b32) b32[c] = (float)r;
         a += r * r;
@@ -564,23 +584,21 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 2)
 // s_k = 1 / ||u_k|| in sc): the new vector w is built in place in column j+1.
 // w = A z_j = s_j A z'_j (z'_j = M u_j, the V-cycle being linear), and the
 // first Gram-Schmidt dot products h1_k = v_k . w = s_k (u_k . w), k <= j.
+template <int D>
 __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 2)
-    k_matvec_dots(int nx, int ny, const double *__restrict__ bu, const double *__restrict__ bv,
-                  const double *__restrict__ d0, const double *__restrict__ Z, double *V, const double *__restrict__ sc,
-                  double *part, double *h1, KState *ks)
+    k_matvec_dots(Op0 op, const double *__restrict__ d0, const double *__restrict__ Z, double *V,
+                  const double *__restrict__ sc, double *part, double *h1, KState *ks)
 {
     pdl_entry();
     __shared__ double sh[KT / 32][KMAXV];
     __shared__ double bsm[KMAXV];
-    const long long n = (long long)nx * ny;
+    const long long n = (long long)op.nx * op.ny * op.nz;
     const int j = ks->j, nk = j + 1;
     const double *z = Z + (long long)j * n;
     double *w = V + (long long)(j + 1) * n;
     const double sj = sc[j];
-    for (long long c = blockIdx.x * (long long)KT + threadIdx.x; c < n; c += (long long)gridDim.x * KT) {
-        const int jj = (int)(c / nx), i = (int)(c - (long long)jj * nx);
-        w[c] = sj * (d0[c] * z[c] - offsum_at(bu, bv, z, nx, ny, i, jj));
-    }
+    for (long long c = blockIdx.x * (long long)KT + threadIdx.x; c < n; c += (long long)gridDim.x * KT)
+        w[c] = sj * (d0[c] * z[c] - op_offsum<D>(op, z, c));
     block_dots(V, w, n, nk, sh, bsm);
     cluster_partials(bsm, nk, part);
     if (!last_cluster(&ks->cnt[2])) return;
@@ -1071,7 +1089,9 @@ int poisson_autotune(wec_poisson *P, cudaStream_t st)
 template <typename T, typename TO>
 void vcycle_t(wec_poisson *P, Level<T> *L, const T *b0, TO *x0, const int *bsel, const int *xsel, cudaStream_t st)
 {
-    if (g_mg_fused) {
+    if (P->nz > 1) {
+        vcycle3_t<T, TO>(P, L, b0, x0, bsel, xsel, st);
+    } else if (g_mg_fused) {
         vcycle_fused<T, TO>(P, L, b0, x0, bsel, xsel, st);
     } else if constexpr (std::is_same<T, TO>::value) {
         vcycle_unfused<T>(P, L, b0, x0, bsel, xsel, st);
@@ -1087,7 +1107,7 @@ void vcycle_t(wec_poisson *P, Level<T> *L, const T *b0, TO *x0, const int *bsel,
 // CTAs of the cluster reduction kernels that run as one wave on this GPU: the
 // scheduler places whole clusters inside a GPC, so the count comes from the
 // occupancy query, not from SMs x CTAs per SM.  Set once by poisson_init.
-int g_kgrid_max = kKrylovBlocks;
+int g_kgrid_max[2] = {kKrylovBlocks, kKrylovBlocks};  // 2D, 3D operator
 
 template <typename K>
 int clusters_resident(K kern, int *out)
@@ -1108,33 +1128,62 @@ int clusters_resident(K kern, int *out)
 
 int set_kgrid_max()
 {
-    int c[6];
+    int c[7];
     int e = clusters_resident(k_bnorm, &c[0]);
-    if (!e) e = clusters_resident(k_residual_norm, &c[1]);
-    if (!e) e = clusters_resident(k_matvec_dots, &c[2]);
-    if (!e) e = clusters_resident(k_matvec_dots, &c[3]);
-    if (!e) e = clusters_resident(k_orth_dots, &c[4]);
-    if (!e) e = clusters_resident(k_orth_norm, &c[5]);
+    if (!e) e = clusters_resident(k_orth_dots, &c[1]);
+    if (!e) e = clusters_resident(k_orth_norm, &c[2]);
+    if (!e) e = clusters_resident(k_residual_norm<2>, &c[3]);
+    if (!e) e = clusters_resident(k_matvec_dots<2>, &c[4]);
+    if (!e) e = clusters_resident(k_residual_norm<3>, &c[5]);
+    if (!e) e = clusters_resident(k_matvec_dots<3>, &c[6]);
     if (e) return e;
-    int m = *std::min_element(c, c + 6);
-    g_kgrid_max = std::max(1, std::min(m, kKrylovBlocks / kCl)) * kCl;
+    const int common = *std::min_element(c, c + 3);
+    const int m2 = std::min({common, c[3], c[4]}), m3 = std::min({common, c[5], c[6]});
+    g_kgrid_max[0] = std::max(1, std::min(m2, kKrylovBlocks / kCl)) * kCl;
+    g_kgrid_max[1] = std::max(1, std::min(m3, kKrylovBlocks / kCl)) * kCl;
     return WEC_OK;
 }
 
 // Reduction kernels: a multiple of the cluster size, at most one wave.
-int kgrid(long long n)
+int kgrid(long long n, bool d3)
 {
-    const long long g = std::min<long long>(nblk(n, KT), g_kgrid_max);
+    const long long g = std::min<long long>(nblk(n, KT), g_kgrid_max[d3 ? 1 : 0]);
     return (int)((g + kCl - 1) / kCl * kCl);
 }
 
 // ---------------------------------------------------------- FGMRES parts ----
+Op0 op0(const wec_poisson *P)
+{
+    return Op0{P->nx, P->ny, P->nz, P->L64[0].bu, P->L64[0].bv, P->L64[0].bw};
+}
+
+long long ncells(const wec_poisson *P) { return (long long)P->nx * P->ny * P->nz; }
+
+// faces of the level-0 operator (bytes accounting)
+double nfaces(const wec_poisson *P)
+{
+    const double nx = P->nx, ny = P->ny, nz = P->nz;
+    if (P->nz == 1) return (nx + 1.0) * ny + nx * (ny + 1.0);
+    return (nx + 1.0) * ny * nz + nx * (ny + 1.0) * nz + nx * ny * (nz + 1.0);
+}
+
+void launch_residual_norm(wec_poisson *P, int G, const double *b, double *x, float *b32, int mode,
+                          unsigned long long hw, int use, cudaStream_t st)
+{
+    if (P->nz > 1)
+        launch_k(k_residual_norm<3>, G, KT, 0, st, op0(P), P->d0, b, x, P->V, b32, P->sc, P->part, P->ks, P->g, mode,
+                 hw, use);
+    else
+        launch_k(k_residual_norm<2>, G, KT, 0, st, op0(P), P->d0, b, x, P->V, b32, P->sc, P->part, P->ks, P->g, mode,
+                 hw, use);
+}
+
 void enqueue_begin(wec_poisson *P, const double *b, double *x, double rtol, int maxit, unsigned long long hw,
                    int use, cudaStream_t st)
 {
-    const long long n = (long long)P->nx * P->ny;
-    const double nf = (P->nx + 1.0) * P->ny + P->nx * (P->ny + 1.0);
-    const int G = kgrid(n);
+    const long long n = ncells(P);
+    const double nf = nfaces(P);
+    const int G = kgrid(n, P->nz > 1);
     float *b32 = P->prec == WEC_PREC_MIXED ? P->L32[0].b : nullptr;
     {
         WEC_PROF("scalar", -1, 64.0, st);
@@ -1145,8 +1194,7 @@ void enqueue_begin(wec_poisson *P, const double *b, double *x, double rtol, int 
         launch_k(k_bnorm, G, KT, 0, st, n, b, P->part, P->ks);
     }
     WEC_PROF("krylov_residual", -1, 8.0 * (4.0 * n + nf) + (b32 ? 4.0 * n : 0.0), st);
-    launch_k(k_residual_norm, G, KT, 0, st, P->nx, P->ny, P->L64[0].bu, P->L64[0].bv, P->d0, b, x, P->V, b32, P->sc,
-             P->part, P->ks, P->g, 0, hw, use);
+    launch_residual_norm(P, G, b, x, b32, 0, hw, use, st);
 }
 
 // One Arnoldi step j (preconditioner, matvec, CGS2 in place in V's column j+1,
@@ -1154,9 +1202,9 @@ void enqueue_begin(wec_poisson *P, const double *b, double *x, double rtol, int 
 // j (m - 1).
 void enqueue_body(wec_poisson *P, unsigned long long hif, int use, cudaStream_t st)
 {
-    const long long n = (long long)P->nx * P->ny;
-    const double nf = (P->nx + 1.0) * P->ny + P->nx * (P->ny + 1.0);
-    const int G = kgrid(n), m = P->restart;
+    const long long n = ncells(P);
+    const double nf = nfaces(P);
+    const int G = kgrid(n, P->nz > 1), m = P->restart;
     const bool mixed = P->prec == WEC_PREC_MIXED;
     double *h1 = P->dots, *h2 = P->dots + (kMaxRestart + 2);
     // the mixed V-cycle reads u_j in FP32, written beside it by k_residual_norm / k_orth_norm
@@ -1166,8 +1214,10 @@ void enqueue_body(wec_poisson *P, unsigned long long hif, int use, cudaStream_t 
         vcycle_t<float, double>(P, P->L32, P->L32[0].b, P->Z, nullptr, &P->ks->j, st);
     {
         WEC_PROF("krylov_matvec_dots", -1, 8.0 * (3.0 * n + nf) + 8.0 * n * m, st);
-        launch_k(k_matvec_dots, G, KT, 0, st, P->nx, P->ny, P->L64[0].bu, P->L64[0].bv, P->d0, P->Z, P->V, P->sc,
-                 P->part, h1, P->ks);
+        if (P->nz > 1)
+            launch_k(k_matvec_dots<3>, G, KT, 0, st, op0(P), P->d0, P->Z, P->V, P->sc, P->part, h1, P->ks);
+        else
+            launch_k(k_matvec_dots<2>, G, KT, 0, st, op0(P), P->d0, P->Z, P->V, P->sc, P->part, h1, P->ks);
     }
     {
         WEC_PROF("krylov_orth_dots", -1, 8.0 * n * (m + 2), st);
@@ -1182,9 +1232,9 @@ void enqueue_body(wec_poisson *P, unsigned long long hif, int use, cudaStream_t 
 // converge / stop / restart.
 void enqueue_close(wec_poisson *P, const double *b, double *x, unsigned long long hw, int use, cudaStream_t st)
 {
-    const long long n = (long long)P->nx * P->ny;
-    const double nf = (P->nx + 1.0) * P->ny + P->nx * (P->ny + 1.0);
-    const int G = kgrid(n), m = P->restart;
+    const long long n = ncells(P);
+    const double nf = nfaces(P);
+    const int G = kgrid(n, P->nz > 1), m = P->restart;
     const bool mixed = P->prec == WEC_PREC_MIXED;
     {
         WEC_PROF("scalar", -1, 8.0 * m * m, st);
@@ -1195,8 +1245,7 @@ void enqueue_close(wec_poisson *P, const double *b, double *x, unsigned long lon
         launch_k(k_update_x, nblk(n, 256), 256, 0, st, n, P->y, P->Z, x, P->ks);
     }
     WEC_PROF("krylov_residual", -1, 8.0 * (4.0 * n + nf) + (mixed ? 4.0 * n : 0.0), st);
-    launch_k(k_residual_norm, G, KT, 0, st, P->nx, P->ny, P->L64[0].bu, P->L64[0].bv, P->d0, b, x, P->V,
-             mixed ? P->L32[0].b : nullptr, P->sc, P->part, P->ks, P->g, 1, hw, use);
+    launch_residual_norm(P, G, b, x, mixed ? P->L32[0].b : nullptr, 1, hw, use, st);
 }
 
 int read_state(wec_poisson *P, cudaStream_t st)
@@ -1216,13 +1265,13 @@ void poisson_tiles(const wec_poisson *P, int *tx, int *ty, int max)
 {
     const int *t = P->prec == WEC_PREC_FP64 ? P->tile64 : P->tile32;
     for (int l = 0; l < max && l < P->nlev; ++l) {
-        const bool tiled = P->bottom_level < 0 || l < P->bottom_level;  // 0 x 0: run by the bottom kernel
+        const bool tiled = P->nz == 1 && (P->bottom_level < 0 || l < P->bottom_level);  // 0 x 0: not a fused tile
         tx[l] = tiled ? kTileX[t[l]] : 0;
         ty[l] = tiled ? kTileY[t[l]] : 0;
     }
 }
 
-int poisson_init(wec_poisson *P, int nx, int ny, int prec, int restart, int nu1, int nu2, cudaStream_t st)
+int poisson_init(wec_poisson *P, int nx, int ny, int prec, int restart, int nu1, int nu2, cudaStream_t st, int nz)
 {
     static bool attrs_done = false;
     if (!attrs_done) {
@@ -1233,38 +1282,52 @@ int poisson_init(wec_poisson *P, int nx, int ny, int prec, int restart, int nu1,
         if (int e = set_kgrid_max()) return e;
         attrs_done = true;
     }
-    if (nx < 2 || ny < 2) return fail(WEC_ERR_INVALID, "poisson: nx, ny must be >= 2");
+    if (nx < 2 || ny < 2 || nz < 1) return fail(WEC_ERR_INVALID, "poisson: nx, ny must be >= 2");
+    if (nz > 1) {  // 3D: every face array below 2^31 entries (32-bit index arithmetic in the kernels)
+        const long long big = std::max({(long long)(nx + 1) * ny * nz, (long long)nx * (ny + 1) * nz,
+                                        (long long)nx * ny * (nz + 1)});
+        if (big >= (1ll << 31)) return fail(WEC_ERR_INVALID, "poisson: 3D grid too large (a face array >= 2^31)");
+    }
     if (restart < 1 || restart > kMaxRestart) return fail(WEC_ERR_INVALID, "poisson: restart must be in 1..32");
     if (nu1 < 1 || nu2 < 0 || nu1 > 4 || nu2 > 4)
         return fail(WEC_ERR_INVALID, "poisson: need 1 <= mg_pre <= 4 and 0 <= mg_post <= 4");
     if (prec != WEC_PREC_FP64 && prec != WEC_PREC_MIXED) return fail(WEC_ERR_INVALID, "poisson: unknown precision");
-    P->nx = nx; P->ny = ny; P->prec = prec; P->restart = restart; P->nu1 = nu1; P->nu2 = nu2; P->st = st;
-    int lx = nx, ly = ny, nl = 0;
+    P->nx = nx; P->ny = ny; P->nz = nz; P->prec = prec; P->restart = restart; P->nu1 = nu1; P->nu2 = nu2; P->st = st;
+    const bool d3 = nz > 1;
+    int lx = nx, ly = ny, lz = nz, nl = 0;
     for (;;) {
-        P->L64[nl].nx = lx; P->L64[nl].ny = ly;
-        P->L32[nl].nx = lx; P->L32[nl].ny = ly;
+        P->L64[nl].nx = lx; P->L64[nl].ny = ly; P->L64[nl].nz = lz;
+        P->L32[nl].nx = lx; P->L32[nl].ny = ly; P->L32[nl].nz = lz;
         nl++;
         if ((lx & 1) || (ly & 1) || lx < 4 || ly < 4 || nl == kMaxLevels) break;
+        if (d3 && ((lz & 1) || lz < 4)) break;
         lx >>= 1; ly >>= 1;
+        if (d3) lz >>= 1;
     }
     P->nlev = nl;
-    P->ncoarse = lx * ly;
+    P->ncoarse = lx * ly * lz;
     if (P->ncoarse > kMaxCoarse)
         return fail(WEC_ERR_INVALID, "poisson: the grid must coarsen (by halving even sizes) to at most 512 cells; got " +
-                                         std::to_string(lx) + "x" + std::to_string(ly));
+                                         std::to_string(lx) + "x" + std::to_string(ly) +
+                                         (d3 ? "x" + std::to_string(lz) : std::string()));
     for (int l = 0; l < nl; ++l) {
-        size_t nc = (size_t)P->L64[l].nx * P->L64[l].ny;
-        size_t nu = (size_t)(P->L64[l].nx + 1) * P->L64[l].ny, nv = (size_t)P->L64[l].nx * (P->L64[l].ny + 1);
+        const size_t Nx = P->L64[l].nx, Ny = P->L64[l].ny, Nz = P->L64[l].nz;
+        size_t nc = Nx * Ny * Nz;
+        size_t nu = (Nx + 1) * Ny * Nz, nv = Nx * (Ny + 1) * Nz, nw = d3 ? Nx * Ny * (Nz + 1) : 0;
         WEC_CK(cudaMalloc(&P->L64[l].bu, nu * 8));
         WEC_CK(cudaMalloc(&P->L64[l].bv, nv * 8));
         WEC_CK(cudaMemset(P->L64[l].bu, 0, nu * 8));
         WEC_CK(cudaMemset(P->L64[l].bv, 0, nv * 8));
+        if (d3) {
+            WEC_CK(cudaMalloc(&P->L64[l].bw, nw * 8));
+            WEC_CK(cudaMemset(P->L64[l].bw, 0, nw * 8));
+        }
         if (l > 0) {
             WEC_CK(cudaMalloc(&P->L64[l].x, nc * 8));
             WEC_CK(cudaMalloc(&P->L64[l].b, nc * 8));
         }
-        P->bytes += (nu + nv) * 8 + (l > 0 ? 2 * nc * 8 : 0);
-        if (l < nl - 1) {  // may be a tiled level of the fused V-cycle
+        P->bytes += (nu + nv + nw) * 8 + (l > 0 ? 2 * nc * 8 : 0);
+        if (l < nl - 1 && !d3) {  // may be a tiled level of the fused V-cycle
             WEC_CK(cudaMalloc(&P->L64[l].xp, nc * 8));
             if (prec == WEC_PREC_MIXED) WEC_CK(cudaMalloc(&P->L32[l].xp, nc * 4));
         }
@@ -1277,9 +1340,10 @@ int poisson_init(wec_poisson *P, int nx, int ny, int prec, int restart, int nu1,
             WEC_CK(cudaMemset(P->L32[l].id, 0, nc * 4));
             WEC_CK(cudaMalloc(&P->L32[l].bu, nu * 4));
             WEC_CK(cudaMalloc(&P->L32[l].bv, nv * 4));
+            if (d3) WEC_CK(cudaMalloc(&P->L32[l].bw, nw * 4));
             WEC_CK(cudaMalloc(&P->L32[l].x, nc * 4));
             WEC_CK(cudaMalloc(&P->L32[l].b, nc * 4));
-            P->bytes += (nu + nv + 2 * nc) * 4;
+            P->bytes += (nu + nv + nw + 2 * nc) * 4;
         }
     }
     WEC_CK(cudaMalloc(&P->lu64, (size_t)P->ncoarse * P->ncoarse * 8));
@@ -1290,7 +1354,7 @@ int poisson_init(wec_poisson *P, int nx, int ny, int prec, int restart, int nu1,
         else
             WEC_CK(cudaMalloc(&P->inv32, (size_t)P->ncoarse * P->ncoarse * 4));
     }
-    size_t n = (size_t)nx * ny;
+    size_t n = (size_t)nx * ny * nz;
     int m = restart;
     WEC_CK(cudaMalloc(&P->V, (m + 1) * n * 8));
     WEC_CK(cudaMalloc(&P->Z, m * n * 8));
@@ -1311,6 +1375,7 @@ int poisson_init(wec_poisson *P, int nx, int ny, int prec, int restart, int nu1,
     WEC_CK(cudaMemset(P->ks, 0, sizeof(KState)));
     WEC_CK(cudaMallocHost(&P->ksh, sizeof(KState)));
     P->bytes += ((m + 1) * n + n) * 8 + m * n * 8;
+    if (d3) return WEC_OK;  // the 3D V-cycle has no tile shapes to tune
     return poisson_autotune(P, st);
 }
 
@@ -1319,6 +1384,7 @@ void poisson_free(wec_poisson *P)
     for (int l = 0; l < P->nlev; ++l) {
         cudaFree(P->L64[l].bu); cudaFree(P->L64[l].bv); cudaFree(P->L64[l].x); cudaFree(P->L64[l].b);
         cudaFree(P->L32[l].bu); cudaFree(P->L32[l].bv); cudaFree(P->L32[l].x); cudaFree(P->L32[l].b);
+        cudaFree(P->L64[l].bw); cudaFree(P->L32[l].bw);
         cudaFree(P->L64[l].xp); cudaFree(P->L32[l].xp);
         cudaFree(P->L64[l].id); cudaFree(P->L32[l].id);
     }
@@ -1351,8 +1417,79 @@ int build_invdiag(wec_poisson *P, Level<T> *L, cudaStream_t st)
     return WEC_OK;
 }
 
+template <typename T>
+int build_invdiag3(wec_poisson *P, Level<T> *L, cudaStream_t st)
+{
+    Level3Diag<T> D;
+    D.nlev = P->nlev;
+    D.off[0] = 0;
+    for (int l = 0; l < P->nlev; ++l) {
+        D.nx[l] = L[l].nx;
+        D.ny[l] = L[l].ny;
+        D.nz[l] = L[l].nz;
+        D.bx[l] = L[l].bu;
+        D.by[l] = L[l].bv;
+        D.bz[l] = L[l].bw;
+        D.id[l] = L[l].id;
+        D.off[l + 1] = D.off[l] + (long long)L[l].nx * L[l].ny * L[l].nz;
+    }
+    const long long tot = D.off[P->nlev];
+    WEC_PROF("mg_invdiag", -1, (double)sizeof(T) * 5.0 * tot, st);
+    launch_k(k3_invdiag<T>, nblk(tot, 256), 256, 0, st, D);
+    WEC_CK(cudaGetLastError());
+    return WEC_OK;
+}
+
+template <typename T>
+int build_hierarchy3(wec_poisson *P, Level<T> *L, T *lu, cudaStream_t st)
+{
+    for (int l = 0; l + 1 < P->nlev; ++l) {
+        Level<T> &F = L[l], &C = L[l + 1];
+        const long long cnt = (C.nx + 1ll) * C.ny * C.nz + C.nx * (C.ny + 1ll) * C.nz + (long long)C.nx * C.ny * (C.nz + 1);
+        WEC_PROF("mg_coarsen", l, 5.0 * sizeof(T) * cnt, st);
+        launch_k(k3_coarsen<T>, nblk(cnt, 256), 256, 0, st, F.nx, F.ny, F.nz, F.bu, F.bv, F.bw, C.bu, C.bv, C.bw);
+    }
+    Level<T> &Lc = L[P->nlev - 1];
+    const double nn = (double)Lc.nx * Lc.ny * Lc.nz;
+    WEC_PROF("mg_lu_factor", P->nlev - 1, sizeof(T) * nn * nn, st);
+    launch_k(k3_lu_factor<T>, 1, 256, 0, st, Lc.nx, Lc.ny, Lc.nz, Lc.bu, Lc.bv, Lc.bw, lu);
+    return build_invdiag3<T>(P, L, st);
+}
+
+int poisson_build3(wec_poisson *P, cudaStream_t st)
+{
+    const long long n = ncells(P);
+    {
+        WEC_PROF("diag", 0, 8.0 * (n + nfaces(P)), st);
+        launch_k(k3_diag0, nblk(n, 256), 256, 0, st, P->nx, P->ny, P->nz, P->L64[0].bu, P->L64[0].bv, P->L64[0].bw,
+                 P->d0);
+    }
+    int e;
+    if (P->prec == WEC_PREC_MIXED) {
+        // the V-cycle is FP32 throughout: level-0 faces converted once
+        Level<double> &A = P->L64[0];
+        Level<float> &F = P->L32[0];
+        const long long nf[3] = {(A.nx + 1ll) * A.ny * A.nz, A.nx * (A.ny + 1ll) * A.nz,
+                                 (long long)A.nx * A.ny * (A.nz + 1)};
+        const double *src[3] = {A.bu, A.bv, A.bw};
+        float *dst[3] = {F.bu, F.bv, F.bw};
+        for (int q = 0; q < 3; ++q) {
+            WEC_PROF("convert", 0, 12.0 * nf[q], st);
+            launch_k(k_convert<float, double>, nblk(nf[q], 256), 256, 0, st, nf[q], src[q], dst[q], nullptr);
+        }
+        e = build_hierarchy3<float>(P, P->L32, P->lu32, st);
+    } else {
+        e = build_hierarchy3<double>(P, P->L64, P->lu64, st);
+    }
+    if (e) return e;
+    WEC_CK(cudaGetLastError());
+    P->have_coef = true;
+    return WEC_OK;
+}
+
 int poisson_build(wec_poisson *P, cudaStream_t st)
 {
+    if (P->nz > 1) return poisson_build3(P, st);
     {
         const int n = P->nx * P->ny;
         WEC_PROF("diag", 0, 8.0 * (n + (P->nx + 1.0) * P->ny + P->nx * (P->ny + 1.0)), st);
@@ -1403,6 +1540,14 @@ int poisson_build(wec_poisson *P, cudaStream_t st)
 
 int poisson_apply(wec_poisson *P, const double *x, double *y)
 {
+    if (P->nz > 1) {
+        const long long n = ncells(P);
+        WEC_PROF("krylov_matvec", -1, 8.0 * (2.0 * n + nfaces(P)), P->st);
+        launch_k(k3_apply<double>, nblk(n, 256), 256, 0, P->st, P->nx, P->ny, P->nz, P->L64[0].bu, P->L64[0].bv,
+                 P->L64[0].bw, x, y);
+        WEC_CK(cudaGetLastError());
+        return WEC_OK;
+    }
     int n = P->nx * P->ny;
     WEC_PROF("krylov_matvec", -1, 8.0 * (2.0 * n + (P->nx + 1.0) * P->ny + P->nx * (P->ny + 1.0)), P->st);
     launch_k(k_apply<double>, nblk(n, 256), 256, 0, P->st, P->nx, P->ny, P->L64[0].bu, P->L64[0].bv, x, y);
@@ -1412,7 +1557,7 @@ int poisson_apply(wec_poisson *P, const double *x, double *y)
 
 int poisson_vcycle(wec_poisson *P, const double *b, double *x)
 {
-    int n = P->nx * P->ny;
+    const long long n = ncells(P);
     cudaStream_t st = P->st;
     if (P->prec == WEC_PREC_FP64) {
         vcycle_t<double, double>(P, P->L64, b, x, nullptr, nullptr, st);

@@ -120,6 +120,8 @@ def load():
     L.wec_poisson_apply.argtypes = [vp, vp, vp]
     L.wec_poisson_vcycle.argtypes = [vp, vp, vp]
     L.wec_poisson_solve.argtypes = [vp, vp, vp, C.c_double, C.c_int, C.POINTER(C.c_int), _dp]
+    L.wec_poisson_create3.argtypes = [C.c_int, C.c_int, C.c_int, C.POINTER(SolverOpts), vp, C.POINTER(vp)]
+    L.wec_poisson_set_coefficients3.argtypes = [vp, vp, vp, vp]
     L.wec_wave_number.restype = C.c_double
     L.wec_wave_number.argtypes = [C.c_double, C.c_double, C.c_double]
     L.wec_wave_number_fenton_kd.restype = C.c_double
@@ -573,3 +575,40 @@ class Poisson:
         code = _check(load().wec_poisson_solve(self.h, _dev(b), _dev(x), rtol, max_iters, C.byref(it),
                                                C.byref(rr)), ok=(WEC_OK, WEC_ERR_NOT_CONVERGED))
         return dict(iters=it.value, relres=rr.value, status=code)
+
+
+class Poisson3(Poisson):
+    """The 3D pressure operator and solver (wec_poisson_create3) on caller
+    coefficients beta_x (nz, ny, nx+1), beta_y (nz, ny+1, nx), beta_z (nz+1,
+    ny, nx); vectors (nz, ny, nx); torch CUDA FP64 tensors."""
+
+    def __init__(self, nx, ny, nz, precision=PREC_FP64, restart=20, mg_pre=2, mg_post=2, stream=None):
+        o = SolverOpts(precision, 1e-8, 1000, restart, 0, 1, mg_pre, mg_post)
+        h = C.c_void_p()
+        _check(load().wec_poisson_create3(nx, ny, nz, C.byref(o), _stream(stream), C.byref(h)))
+        self.h, self.nx, self.ny, self.nz = h, nx, ny, nz
+
+    def _n(self, *ts):
+        n = self.nx * self.ny * self.nz
+        for t in ts:
+            if t.numel() != n:
+                raise ValueError(f"expected {n} cells, got {t.numel()}")
+
+    def set_coefficients(self, bx, by, bz):
+        nx, ny, nz = self.nx, self.ny, self.nz
+        for t, m in ((bx, (nx + 1) * ny * nz), (by, nx * (ny + 1) * nz), (bz, nx * ny * (nz + 1))):
+            if t.numel() != m:
+                raise ValueError(f"expected {m} face coefficients, got {t.numel()}")
+        _check(load().wec_poisson_set_coefficients3(self.h, _dev(bx), _dev(by), _dev(bz)))
+
+    def apply(self, x, y):
+        self._n(x, y)
+        super().apply(x, y)
+
+    def vcycle(self, b, x):
+        self._n(b, x)
+        super().vcycle(b, x)
+
+    def solve(self, b, x, rtol=1e-10, max_iters=500):
+        self._n(b, x)
+        return super().solve(b, x, rtol, max_iters)

@@ -1,0 +1,169 @@
+"""The 3D pressure solve on the GPU (wec_poisson_create3) against the 3D oracle:
+the operator, one V-cycle and the FGMRES solution element by element on grids
+whose levels span several thread blocks and end on ragged coarsest levels; the
+mixed-precision path against the FP64 tolerance; the 512 x 256 x 256 tank-
+structured case at full size through the residual the oracle's operator
+computes; and the edge cases (no coarsening, a zero right-hand side, a grid
+that does not coarsen far enough, the wrong coefficient call)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import poisson3d as O3  # noqa: E402
+from paper_2206_07732_gb300 import build as B  # noqa: E402
+from paper_2206_07732_gb300 import synth  # noqa: E402
+from paper_2206_07732_gb300 import wec  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    B.build()
+    wec.load()
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def _coef(shape, seed, contrast):
+    nx, ny, nz = shape
+    if contrast == "tank":
+        bx, by, bz, _ = synth.poisson3d_case(nx, ny, nz, seed=seed)
+        return bx, by, bz
+    return synth.random_coefficients3(nx, ny, nz, seed=seed, contrast=contrast)
+
+
+def _solver(shape, coef, prec=wec.PREC_FP64):
+    P = wec.Poisson3(*shape, precision=prec)
+    P.set_coefficients(*(cuda(a) for a in coef))
+    return P
+
+
+CASES = [((16, 8, 8), 1.0), ((48, 24, 32), 1e2), ((40, 24, 16), 1e3), ((64, 32, 32), "tank"), ((96, 40, 24), 1.0)]
+
+
+@pytest.mark.parametrize("shape,contrast", CASES)
+def test_operator_and_vcycle_match_oracle(shape, contrast):
+    nx, ny, nz = shape
+    coef = _coef(shape, sum(shape), contrast)
+    x = np.random.default_rng(1).standard_normal((nz, ny, nx))
+    P = _solver(shape, coef)
+    y = torch.zeros(nz, ny, nx, dtype=torch.float64, device="cuda")
+    P.apply(cuda(x), y)
+    assert rel(y.cpu().numpy(), O3.apply(*coef, x)) < 1e-14
+    z = torch.zeros_like(y)
+    P.vcycle(cuda(x), z)
+    zo, _ = O3.vcycle(*coef, x)
+    assert rel(z.cpu().numpy(), zo) < 1e-11
+    P.close()
+
+
+@pytest.mark.parametrize("shape,contrast,rtol", [((16, 8, 8), 1.0, 1e-13), ((48, 24, 32), 1e2, 1e-12),
+                                                 ((40, 24, 16), 1e3, 1e-11), ((64, 32, 32), "tank", 1e-10)])
+def test_fgmres_solution_matches_oracle(shape, contrast, rtol):
+    nx, ny, nz = shape
+    coef = _coef(shape, 3 * nx + ny + nz, contrast)
+    b = np.random.default_rng(2).standard_normal((nz, ny, nx))
+    P = _solver(shape, coef)
+    x = torch.zeros(nz, ny, nx, dtype=torch.float64, device="cuda")
+    info = P.solve(cuda(b), x, rtol=rtol)
+    xo, io = O3.solve(*coef, b, rtol=rtol)
+    print(f"{shape} contrast {contrast}: GPU {info['iters']} iterations, oracle {io['iters']}")
+    assert info["status"] == 0 and info["relres"] <= rtol
+    assert io["status"] == 0
+    assert abs(info["iters"] - io["iters"]) <= 1
+    assert rel(x.cpu().numpy(), xo) < 1e3 * rtol
+    P.close()
+
+
+@pytest.mark.parametrize("shape,contrast", [((48, 24, 32), 1e2), ((64, 32, 32), "tank")])
+def test_mixed_precision_solve_reaches_fp64_tolerance(shape, contrast):
+    # FP32 V-cycle inside the FP64 FGMRES: the FP64 residual (recomputed here with
+    # the oracle's operator) decides convergence; the solution's error against a
+    # tight oracle solve is of the size the FP64 path's own error has at 1e-8
+    nx, ny, nz = shape
+    coef = _coef(shape, 5, contrast)
+    b = np.random.default_rng(3).standard_normal((nz, ny, nx))
+    xs = {}
+    for prec in (wec.PREC_FP64, wec.PREC_MIXED):
+        P = _solver(shape, coef, prec)
+        x = torch.zeros(nz, ny, nx, dtype=torch.float64, device="cuda")
+        info = P.solve(cuda(b), x, rtol=1e-8)
+        assert info["status"] == 0
+        xs[prec] = (x.cpu().numpy(), info["iters"])
+        P.close()
+    xm = xs[wec.PREC_MIXED][0]
+    r = b - O3.apply(*coef, xm)
+    assert np.linalg.norm(r) <= 1e-8 * np.linalg.norm(b) * 1.0001
+    xo, _ = O3.solve(*coef, b, rtol=1e-12)
+    em, ed = rel(xm, xo), rel(xs[wec.PREC_FP64][0], xo)
+    print(f"{shape}: error vs oracle, mixed {em:.2e} ({xs[wec.PREC_MIXED][1]} its), "
+          f"FP64 {ed:.2e} ({xs[wec.PREC_FP64][1]} its)")
+    assert em < 10.0 * ed + 1e-9
+
+
+def test_mixed_vcycle_is_fp32_close():
+    shape = (48, 24, 32)
+    coef = _coef(shape, 9, 1.0)
+    b = np.random.default_rng(4).standard_normal(shape[::-1])
+    P = _solver(shape, coef, wec.PREC_MIXED)
+    z = torch.zeros(shape[::-1], dtype=torch.float64, device="cuda")
+    P.vcycle(cuda(b), z)
+    zo, _ = O3.vcycle(*coef, b)
+    assert 1e-9 < rel(z.cpu().numpy(), zo) < 1e-4
+    P.close()
+
+
+@pytest.mark.parametrize("prec", [wec.PREC_FP64, wec.PREC_MIXED])
+def test_full_size_tank_solve(prec):
+    # 512 x 256 x 256 (33.5 M cells), the coefficient structure of the 3D tank:
+    # the relative residual the oracle's operator computes from the GPU solution
+    nx, ny, nz = 512, 256, 256
+    bx, by, bz, b = synth.poisson3d_case(nx, ny, nz, seed=0)
+    P = _solver((nx, ny, nz), (bx, by, bz), prec)
+    x = torch.zeros(nz, ny, nx, dtype=torch.float64, device="cuda")
+    info = P.solve(cuda(b), x, rtol=1e-8)
+    assert info["status"] == 0
+    r = b - O3.apply(bx, by, bz, x.cpu().numpy())
+    rr = np.linalg.norm(r) / np.linalg.norm(b)
+    print(f"512x256x256 prec {prec}: {info['iters']} iterations, relative residual {rr:.3e}")
+    assert rr <= 1e-8 * 1.0001
+    P.close()
+
+
+def test_uncoarsened_grid_is_the_dense_solve():
+    # 2 x 2 x 2 does not coarsen: the V-cycle is the coarsest level's LU, exact
+    shape = (2, 2, 2)
+    coef = _coef(shape, 1, 10.0)
+    b = np.random.default_rng(5).standard_normal((2, 2, 2))
+    P = _solver(shape, coef)
+    z = torch.zeros(2, 2, 2, dtype=torch.float64, device="cuda")
+    P.vcycle(cuda(b), z)
+    assert rel(z.cpu().numpy(), O3.vcycle(*coef, b)[0]) < 1e-13
+    x = torch.zeros_like(z)
+    info = P.solve(cuda(b), x, rtol=1e-12)
+    assert info["status"] == 0 and info["iters"] == 1
+    P.close()
+
+
+def test_zero_rhs_and_invalid_uses():
+    shape = (16, 8, 8)
+    P = _solver(shape, _coef(shape, 2, 1.0))
+    x = cuda(np.ones((8, 8, 16)))
+    info = P.solve(cuda(np.zeros((8, 8, 16))), x, rtol=1e-8)
+    assert info["status"] == 0 and info["iters"] == 0 and not torch.any(x != 0)
+    with pytest.raises(wec.WecError):  # the 2D call on a 3D object
+        wec._check(wec.load().wec_poisson_set_coefficients(P.h, wec._dev(x), wec._dev(x)))
+    P.close()
+    with pytest.raises(wec.WecError):  # 18^3 coarsens to 9^3 = 729 > 512 cells
+        wec.Poisson3(18, 18, 18)
+    with pytest.raises(wec.WecError):
+        wec.Poisson3(16, 8, 1)
