@@ -16,6 +16,9 @@ network, mixed_mg (FP32 V-cycles only) and the plain FP64 path, same GPU.
 
 --workload batch times the 64 uneven tanks of the batched configuration (one
 graph launch per batch step; tanks sharded over ranks when N > 1).
+--workload poisson3d times the 3D pressure solve alone (512 x 256 x 256, the
+coefficient structure of the 8 m x 4 m x 4 m tank with a cylinder buoy) in FP64
+and mixed precision; the default run reports the same leg under "poisson3d".
 
 N > 1 (under torchrun): independent replicas, one tank per rank (the single
 tank is not partitioned), value = all ranks' cell-steps / max-over-ranks time.
@@ -53,8 +56,9 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU-baseline sample budget")
-    ap.add_argument("--workload", default="tank", choices=["tank", "batch"],
-                    help="tank: the 1024x256 JONSWAP tank (default); batch: 64 uneven tanks in one graph launch")
+    ap.add_argument("--workload", default="tank", choices=["tank", "batch", "poisson3d"],
+                    help="tank: the 1024x256 JONSWAP tank (default); batch: 64 uneven tanks in one graph launch; "
+                         "poisson3d: the 3D pressure solve at 512x256x256")
     ap.add_argument("--ncu-steps", type=int, default=0,
                     help="profiling helper: run warm-up + this many mixed-path steps only, print nothing")
     return ap.parse_args()
@@ -377,6 +381,176 @@ def time_batch(wec, torch, cfgs, precision, steps, warmup, flush):
     return dict(ms=[a.elapsed_time(b) for a, b in ev], iters=its, residual=max(res), launches=launches, wall=wall)
 
 
+def bench_poisson3d(wec, torch, seed, solves=5, warmup=3, shape=(512, 256, 256), cpu_seconds=10.0):
+    """The 3D pressure solve (wec_poisson_create3) to a 1e-8 FP64 relative
+    residual from a zero guess, FP64 and mixed precision: CUDA events around
+    each solve on the solver's stream (inputs 268 MB per vector, larger than L2),
+    then one eager solve with every launch timed (per-kernel breakdown and the
+    HBM roofline of the dominant kernel).  cpu_seconds > 0: the oracle's solve of
+    the same structure on a 128 x 64 x 64 grid as the CPU baseline."""
+    from paper_2206_07732_gb300 import synth
+    nx, ny, nz = shape
+    n = nx * ny * nz
+    bx, by, bz, b = synth.poisson3d_case(nx, ny, nz, seed=seed)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+    cb = [dev(a) for a in (bx, by, bz)]
+    bd = dev(b)
+    del bx, by, bz, b
+    stream = torch.cuda.current_stream()
+    peak, peak_kind = peaks()
+    out = {"workload": f"3D pressure solve {nx}x{ny}x{nz} (8 m x 4 m x 4 m, h = 1/64 m): water/air coefficients "
+                       "across a seeded irregular surface, cylinder buoy (R 0.5 m, L 0.8 m) at the Brinkman value, "
+                       "standard-normal right-hand side; rtol 1e-8 from a zero guess",
+           "cells": n, "l2": "inputs larger than L2 (268 MB per FP64 vector)"}
+    from paper_2206_07732_gb300 import tune
+    for name, prec in (("fp64", wec.PREC_FP64), ("mixed", wec.PREC_MIXED)):
+        opts, table = tune.tune_poisson3((nx, ny, nz), cb, bd, prec)
+        P = wec.Poisson3(nx, ny, nz, precision=prec, mg_pre=opts[0], mg_post=opts[1], restart=opts[2])
+        P.set_coefficients(*cb)
+        x = torch.zeros_like(bd)
+        for _ in range(warmup):
+            x.zero_()
+            P.solve(bd, x, rtol=1e-8)
+        ms, its, rr = [], [], []
+        n0 = wec.launch_count()
+        for _ in range(solves):
+            x.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            info = P.solve(bd, x, rtol=1e-8)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            its.append(info["iters"])
+            rr.append(info["relres"])
+        launches = (wec.launch_count() - n0) / solves
+        x.zero_()
+        torch.cuda.synchronize()
+        wec.profile_read()
+        wec.profile_enable(1)
+        P.solve(bd, x, rtol=1e-8)
+        wec.profile_enable(0)
+        prof = wec.profile_read()
+        P.close()
+        by_name = {}
+        for q in prof:
+            d = by_name.setdefault(q["name"], dict(ms=0.0, bytes=0.0, launches=0))
+            d["ms"] += q["ms"]; d["bytes"] += q["bytes"]; d["launches"] += q["launches"]
+        tot = sum(d["ms"] for d in by_name.values())
+        top = max(by_name, key=lambda k: by_name[k]["ms"])
+        lv = {str(q["level"]): {"launches": q["launches"], "avg_us": q["ms"] / q["launches"] * 1e3,
+                                "GBps": q["bytes"] / (q["ms"] / 1e3) / 1e9 if q["ms"] > 0 else None}
+              for q in prof if q["name"] == top}
+        d = by_name[top]
+        ach = d["bytes"] / (d["ms"] / 1e3) / 1e9 if d["ms"] > 0 else None
+        t = statistics.median(ms)
+        out[name] = {
+            "solver_options_autotuned": {"mg_pre": opts[0], "mg_post": opts[1], "restart": opts[2],
+                                         "candidates": table},
+            "ms_per_solve": t, "ms_per_solve_all": ms, "cell_solves_per_s": n / (t / 1e3),
+            "fgmres_iters": statistics.mean(its), "max_relative_residual": max(rr),
+            "gpu_launches_per_solve": launches,
+            "kernel_breakdown_eager": [{"kernel": k, "launches": v["launches"], "ms": v["ms"], "share": v["ms"] / tot}
+                                       for k, v in sorted(by_name.items(), key=lambda kv: -kv[1]["ms"])[:8]],
+            "roofline": {"bound": "hbm", "kernel": top, "achieved": ach, "peak": peak, "unit": "GB/s",
+                         "frac": ach / peak if ach else None, "traffic": ncu_traffic(top + "_3d"),
+                         "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
+                         "algorithmic_bytes_per_launch": d["bytes"] / d["launches"], "launches_timed": d["launches"],
+                         "avg_launch_us": d["ms"] / d["launches"] * 1e3, "share_of_solve_gpu_time": d["ms"] / tot,
+                         "per_level": lv,
+                         "timing": "event pair per launch over one eager solve (all levels of the kernel)"},
+        }
+    out["speedup_mixed_vs_fp64"] = out["fp64"]["ms_per_solve"] / out["mixed"]["ms_per_solve"]
+    out["cpu_baseline"] = None
+    if cpu_seconds > 0:
+        from oracle import build as ob
+        from oracle import poisson3d as O3
+        ob.build()
+        sx, sy, sz = 128, 64, 64
+        cx, cy, cz, cbv = synth.poisson3d_case(sx, sy, sz, seed=seed)
+        k, t0 = 0, time.perf_counter()
+        while True:
+            _, io = O3.solve(cx, cy, cz, cbv, rtol=1e-8)
+            k += 1
+            el = time.perf_counter() - t0
+            if el > cpu_seconds:
+                break
+        out["cpu_baseline"] = {"value": sx * sy * sz * k / el, "unit": "cell-solves/s", "cores": 1, "kind": "oracle",
+                               "sample": f"{k} oracle FP64 solves of the same structure on a {sx}x{sy}x{sz} grid "
+                                         f"({io['iters']} iterations each, {el:.1f} s, 1 thread)"}
+    return out
+
+
+def main_poisson3d(args):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    L, wec = setup_lib()
+    if args.ncu_steps:
+        # profiling helper: mixed-precision solves of a 384 x 192 x 192 case of
+        # the same structure (working set of the level-0 smoother > L2, ~2 GB on
+        # the device), default solver options, no output
+        from paper_2206_07732_gb300 import synth
+        shape = (384, 192, 192)
+        bx, by, bz, b = synth.poisson3d_case(*shape, seed=args.seed)
+        dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+        P = wec.Poisson3(*shape, precision=wec.PREC_MIXED)
+        P.set_coefficients(dev(bx), dev(by), dev(bz))
+        bd = dev(b)
+        x = torch.zeros_like(bd)
+        for _ in range(max(args.warmup, 1) + args.ncu_steps):
+            x.zero_()
+            P.solve(bd, x, rtol=1e-8)
+        torch.cuda.synchronize()
+        P.close()
+        return
+    solves, warmup = args.steps, max(args.warmup, 3)
+    clocks = Clocks(local)
+    clocks.start()
+    r = bench_poisson3d(wec, torch, args.seed, solves=solves, warmup=warmup,
+                        cpu_seconds=0.0 if (args.no_cpu_baseline or rank or world > 1) else args.cpu_seconds)
+    ck = clocks.stop()
+
+    def reduce_max(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    t = reduce_max(sum(r["mixed"]["ms_per_solve_all"]) / 1e3)
+    n = r["cells"]
+    line = {
+        "metric": "cell-solves/s of the 3D pressure solve at 1e-8 FP64 relative residual (mixed vs FP64)",
+        "value": world * n * solves / t, "unit": "cell-solves/s", "n_gpus": world, "steps": solves,
+        "warmup": warmup, "ms_per_step": t / solves * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64+f32(multigrid)", "data": "synthetic (seeded surface and coefficients)",
+        "config": {"workload": r["workload"], "cells": n, "l2": r["l2"],
+                   "precision": "mixed: FP32 V-cycles inside FP64 FGMRES (residual, Krylov basis FP64)",
+                   "solver_options_autotuned": {k: r[k]["solver_options_autotuned"] for k in ("mixed", "fp64")}},
+        "fp64_value": world * n * solves / reduce_max(sum(r["fp64"]["ms_per_solve_all"]) / 1e3),
+        "speedup_mixed_vs_fp64": r["speedup_mixed_vs_fp64"],
+        "fgmres_iters": {"mixed": r["mixed"]["fgmres_iters"], "fp64": r["fp64"]["fgmres_iters"]},
+        "max_relative_residual": {"mixed": r["mixed"]["max_relative_residual"],
+                                  "fp64": r["fp64"]["max_relative_residual"]},
+        "e2e": None, "e2e_note": "the solve takes device arrays (wec_poisson_solve); no host-buffer entry point",
+        "gpu_launches": r["mixed"]["gpu_launches_per_solve"] * solves,
+        "clocks": ck, "roofline": r["mixed"]["roofline"], "roofline_fp64": r["fp64"]["roofline"],
+        "kernel_breakdown_eager": {"mixed": r["mixed"]["kernel_breakdown_eager"],
+                                   "fp64": r["fp64"]["kernel_breakdown_eager"]},
+        "cpu_baseline": r["cpu_baseline"],
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main_batch(args):
     import torch
     from paper_2206_07732_gb300 import synth
@@ -508,8 +682,18 @@ def main_ours(args):
     ctl, ctl_info = make_controller(wec, torch, cfg)
     net, train_info = train_learned(wec, torch, cfg, args.seed)
 
+    # solver options (multigrid sweeps, FGMRES restart) autotuned per path on
+    # the tank's first steps (untimed); every path solves to the same 1e-8
+    from paper_2206_07732_gb300 import tune
+    tuned, cfgs = {}, {}
+    for key, prec, use_net in (("mixed+learned", wec.PREC_MIXED, net), ("mixed", wec.PREC_MIXED, None),
+                               ("fp64", wec.PREC_FP64, None), ("mixed_mg", wec.PREC_MIXED_MG, None)):
+        opts, table = tune.tune_tank(cfg, prec, net=use_net)
+        tuned[key] = {"mg_pre": opts[0], "mg_post": opts[1], "restart": opts[2], "candidates": table}
+        cfgs[key] = tune.with_options(cfg, opts)
+
     # which kernel dominates the headline path (untimed, eager, every launch timed)
-    prof_all = profile_all(wec, torch, cfg, wec.PREC_MIXED, net=net)
+    prof_all = profile_all(wec, torch, cfgs["mixed+learned"], wec.PREC_MIXED, net=net)
     by_name = {}
     for p in prof_all:
         d = by_name.setdefault(p["name"], dict(ms=0.0, bytes=0.0, launches=0))
@@ -520,20 +704,21 @@ def main_ours(args):
                   "share": d["ms"] / tot_prof}
                  for k, d in sorted(by_name.items(), key=lambda kv: -kv[1]["ms"])[:12]]
 
-    tiles_t = wec.Tank(cfg, precision=wec.PREC_MIXED)
+    tiles_t = wec.Tank(cfgs["mixed+learned"], precision=wec.PREC_MIXED)
     mg_tiles = tiles_t.mg_tiles()
     tiles_t.close()
 
     clocks = Clocks(local)
     clocks.start()
-    learned = time_path(L, wec, torch, cfg, wec.PREC_MIXED, steps, warmup, flush, net=net, ctl=ctl)
+    learned = time_path(L, wec, torch, cfgs["mixed+learned"], wec.PREC_MIXED, steps, warmup, flush, net=net, ctl=ctl)
     ck = clocks.stop()
-    mixed = time_path(L, wec, torch, cfg, wec.PREC_MIXED, steps, warmup, flush, ctl=ctl)
-    fp64 = time_path(L, wec, torch, cfg, wec.PREC_FP64, steps, warmup, flush, ctl=ctl)
-    mixed_mg = time_path(L, wec, torch, cfg, wec.PREC_MIXED_MG, steps, warmup, flush, ctl=ctl)
-    kpass = time_path(L, wec, torch, cfg, wec.PREC_MIXED, max(steps // 4, 5), warmup, flush, graph=False,
-                      profile_kernel=top, net=net, ctl=ctl)
-    e2e = e2e_path(wec, torch, cfg, wec.PREC_MIXED, max(steps // 2, 5), warmup, flush, net=net, ctl=ctl)
+    mixed = time_path(L, wec, torch, cfgs["mixed"], wec.PREC_MIXED, steps, warmup, flush, ctl=ctl)
+    fp64 = time_path(L, wec, torch, cfgs["fp64"], wec.PREC_FP64, steps, warmup, flush, ctl=ctl)
+    mixed_mg = time_path(L, wec, torch, cfgs["mixed_mg"], wec.PREC_MIXED_MG, steps, warmup, flush, ctl=ctl)
+    kpass = time_path(L, wec, torch, cfgs["mixed+learned"], wec.PREC_MIXED, max(steps // 4, 5), warmup, flush,
+                      graph=False, profile_kernel=top, net=net, ctl=ctl)
+    e2e = e2e_path(wec, torch, cfgs["mixed+learned"], wec.PREC_MIXED, max(steps // 2, 5), warmup, flush, net=net,
+                   ctl=ctl)
 
     def reduce_max(x):
         if world == 1:
@@ -598,6 +783,13 @@ def main_ours(args):
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{k} oracle steps of the 1024x256 tank from its initial state ({el:.1f} s, 1 thread)"}
 
+    # the 3D pressure solve (512 x 256 x 256), reported beside the tank
+    try:
+        p3 = bench_poisson3d(wec, torch, args.seed, solves=3, warmup=3,
+                             cpu_seconds=0.0 if (args.no_cpu_baseline or rank or world > 1) else 10.0)
+    except Exception as ex:  # reported, not fatal to the tank's line
+        p3 = {"error": f"{type(ex).__name__}: {ex}"}
+
     tried, kept = learned["net_stats"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": warmup,
@@ -623,6 +815,7 @@ def main_ours(args):
                             max_abs_pto_force_timed_run=learned["max_pto"]),
         "execution": "one CUDA graph per step (conditional WHILE/IF nodes steer FGMRES on the GPU)",
         "mg_tiles_autotuned": mg_tiles,
+        "solver_options_autotuned": tuned,
         "fgmres_iters_per_step": {"mixed+learned": statistics.mean(learned["iters"]),
                                   "mixed": statistics.mean(mixed["iters"]), "fp64": statistics.mean(fp64["iters"]),
                                   "mixed_mg": statistics.mean(mixed_mg["iters"])},
@@ -635,6 +828,7 @@ def main_ours(args):
         "roofline": roofline,
         "kernel_breakdown_eager": breakdown,
         "cpu_baseline": cpu,
+        "poisson3d": p3,
     }
     if rank == 0:
         print(json.dumps(line))
@@ -677,5 +871,7 @@ if __name__ == "__main__":
         main_reference(a)
     elif a.workload == "batch":
         main_batch(a)
+    elif a.workload == "poisson3d":
+        main_poisson3d(a)
     else:
         main_ours(a)

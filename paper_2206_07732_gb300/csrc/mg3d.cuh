@@ -37,12 +37,15 @@ __global__ void __launch_bounds__(256) k3_rbgs(int nx, int ny, int nz, const T *
     x[c] = (b[c] + offsum3_at(bx, by, bz, x, nx, ny, nz, i, j, k)) * id[c];
 }
 
-// Coarse right-hand side = sum of the residuals of the eight children.
+// Coarse right-hand side = sum of the residuals of the eight children.  dg
+// (nullable): the level's diagonal, already formed (the FP64 level 0 has one),
+// read instead of summing the six faces again.
 template <typename T>
 __global__ void __launch_bounds__(256) k3_resid_restrict(int nx, int ny, int nz, const T *__restrict__ bx,
                                                          const T *__restrict__ by, const T *__restrict__ bz,
-                                                         const T *__restrict__ x, const T *__restrict__ b,
-                                                         T *__restrict__ bc, const int *bsel, const int *xsel)
+                                                         const T *__restrict__ dg, const T *__restrict__ x,
+                                                         const T *__restrict__ b, T *__restrict__ bc,
+                                                         const int *bsel, const int *xsel)
 {
     pdl_entry();
     const int cx = nx >> 1, cy = ny >> 1, cz = nz >> 1;
@@ -57,8 +60,8 @@ __global__ void __launch_bounds__(256) k3_resid_restrict(int nx, int ny, int nz,
         for (int dj = 0; dj < 2; ++dj)
             for (int di = 0; di < 2; ++di) {
                 const int i = 2 * I + di, j = 2 * J + dj, k = 2 * K + dk, c = (k * ny + j) * nx + i;
-                const T ax = diag3_at(bx, by, bz, nx, ny, nz, i, j, k) * x[c] -
-                             offsum3_at(bx, by, bz, x, nx, ny, nz, i, j, k);
+                const T d = dg ? dg[c] : diag3_at(bx, by, bz, nx, ny, nz, i, j, k);
+                const T ax = d * x[c] - offsum3_at(bx, by, bz, x, nx, ny, nz, i, j, k);
                 s += b[c] - ax;
             }
     bc[q] = s;
@@ -223,10 +226,12 @@ void vcycle3_unfused(wec_poisson *P, Level<T> *L, const T *b0, T *x0, const int 
                          q == 0 && color == 0, bs, xs);
             }
         Level<T> &C = L[l + 1];
+        const T *dg = nullptr;
+        if constexpr (sizeof(T) == 8) dg = l == 0 ? (const T *)P->d0 : nullptr;
         {
-            WEC_PROF("mg3_resid_restrict", l, (2.125 * n + nf) * ts, st);
+            WEC_PROF("mg3_resid_restrict", l, (2.125 * n + nf + (dg ? n : 0.0)) * ts, st);
             launch_k(k3_resid_restrict<T>, nblk(C.nx * C.ny * C.nz, TB), TB, 0, st, A.nx, A.ny, A.nz, A.bu, A.bv,
-                     A.bw, x, b, C.b, bs, xs);
+                     A.bw, dg, x, b, C.b, bs, xs);
         }
     }
     for (int l = P->nlev - 2; l >= 0; --l) {
