@@ -167,9 +167,13 @@ def tensor_peak():
         return 1700.0, "fallback 1.7 PFLOP/s sustained"
 
 
-def source_sha():
+def source_sha(files=None):
+    """Hash of the library's kernel sources: the listed files of csrc/ (the
+    translation unit of a profiled kernel), or all of them."""
+    csrc = os.path.join(ROOT, "paper_2206_07732_gb300", "csrc")
+    paths = sorted(glob.glob(os.path.join(csrc, "*"))) if files is None else [os.path.join(csrc, f) for f in files]
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2206_07732_gb300", "csrc", "*"))):
+    for f in paths:
         with open(f, "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -177,15 +181,17 @@ def source_sha():
 
 def ncu_traffic(kernel_key):
     """dram bytes per launch of `kernel_key` from a committed ncu summary, if it
-    was captured on the current kernel sources (else None)."""
-    sha = source_sha()
+    was captured on the current sources of that kernel (the summary's
+    source_files, hashed; else None)."""
     for f in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
         with open(f) as fh:
             text = fh.read()
         m_k = re.search(r"^roofline_kernel:\s*(\S+)", text, re.M)
         m_s = re.search(r"^source_sha:\s*(\S+)", text, re.M)
         m_t = re.search(r"^traffic_bytes_per_launch:\s*([0-9.eE+]+)", text, re.M)
-        if m_k and m_s and m_t and m_k.group(1) == kernel_key and m_s.group(1) == sha:
+        m_f = re.search(r"^source_files:\s*(.+)$", text, re.M)
+        files = m_f.group(1).split() if m_f else None
+        if m_k and m_s and m_t and m_k.group(1) == kernel_key and m_s.group(1) == source_sha(files):
             return float(m_t.group(1))
     return None
 
