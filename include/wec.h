@@ -368,6 +368,58 @@ int wec_poisson_create3(int nx, int ny, int nz, const wec_solver_opts *opts, voi
 int wec_poisson_set_coefficients3(wec_poisson *P, const double *beta_x, const double *beta_y,
                                   const double *beta_z);
 
+/* ---- the three-dimensional tank (level-set part) ------------------------ */
+/* Uniform 3D grid, z vertical: h = lx / nx = ly / ny = lz / nz; nx, nz >= 4,
+ * ny >= 1, ny, nz <= 65535; depth = still-water depth above the bed. */
+typedef struct {
+    int nx, ny, nz;
+    double lx, ly, lz, depth;
+} wec_grid3;
+
+/* Heaving vertical cylinder (the configuration's buoy): axis at (xc, yc),
+ * centre height zc (per call of wec_tank3_materials), radius, length, mass;
+ * SDF psi = max(r - radius, |z - zc| - length / 2) (section "Interface
+ * tracking", CSG intersection of a cylinder and a slab); solid density
+ * mass / (pi radius^2 length).  present = 0: no body. */
+typedef struct {
+    int present;
+    double xc, yc, radius, length, mass;
+} wec_cylinder;
+
+typedef struct wec_tank3 wec_tank3;
+
+/* Fields (FP64, x fastest): cells [nz][ny][nx]; u [nz][ny][nx+1], v
+ * [nz][ny+1][nx], w [nz+1][ny][nx] (face k of w below cell layer k). */
+enum {
+    WEC_F3_SIGMA = 0, WEC_F3_U = 1, WEC_F3_V = 2, WEC_F3_W = 3, /* state: get and set */
+    WEC_F3_RHO = 4, WEC_F3_MU = 5, WEC_F3_RHO_FLOW = 6, WEC_F3_CHI = 7 /* materials: get */
+};
+
+/* The level-set part of the 3D step on the GPU (FP64): sigma, the face
+ * velocities and the materials.  Waves travel along x (uniform along y): the
+ * components of wec_waves give the inflow ghost z - depth - eta(x, t) of sigma
+ * (k from the dispersion relation) and the damping zone [damp_x0,
+ * damp_x0 + damp_len] at the outlet.  All fields start at zero.  Host arrays
+ * are copied; the calls synchronise the object's stream before returning. */
+int wec_tank3_create(const wec_grid3 *grid, const wec_fluids *fluids, const wec_waves *waves,
+                     const wec_cylinder *body, void *cuda_stream, wec_tank3 **out);
+void wec_tank3_destroy(wec_tank3 *tank);
+/* host_dst / host_src: n doubles, n = the field's size (WEC_ERR_INVALID otherwise;
+ * only the state fields can be set). */
+int wec_tank3_get_field(const wec_tank3 *tank, int field_id, double *host_dst, size_t n);
+int wec_tank3_set_field(wec_tank3 *tank, int field_id, const double *host_src, size_t n);
+/* Two-stage materials (Eqs. ls_flow then ls_solid, half-width h) from sigma and
+ * the cylinder centred at height zc: rho, mu, rho^flow and chi = 1 - H_body. */
+int wec_tank3_materials(wec_tank3 *tank, double zc);
+/* sigma <- sigma - dt Q(u, sigma) (single-stage PPM per direction; section
+ * "Level set advection"), then the damping-zone blend toward z - depth; ghosts
+ * of sigma at time t (inflow: the incident wave; outlet and side walls: zero
+ * gradient; bed and top: linear extrapolation). */
+int wec_tank3_advect(wec_tank3 *tank, double dt, double t);
+/* nit Sussman pseudo-steps (TVD-RK2, d tau = 0.3 h) toward |grad sigma| = 1 with
+ * the sign of sigma at the call (section "Interface tracking"); ghosts at t. */
+int wec_tank3_reinit(wec_tank3 *tank, int nit, double t);
+
 /* ---- without device allocation ------------------------------------------ */
 /* ||b - A x||_2 for the pressure operator above (same coefficient layout and
  * boundary rules as wec_poisson_*), written to *norm_out (device, 1 double).

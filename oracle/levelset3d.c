@@ -154,33 +154,50 @@ static double damp3(const oracle3_tank *P, double x)
     return (exp(pow(xi, 3.5)) - 1.0) / (exp(1.0) - 1.0);
 }
 
+/* sigma* at cell (i, j, k) */
+static double advect_cell3(const oracle3_tank *P, const double *s, const double *u, const double *v, const double *w,
+                           double dt, double t, int i, int j, int k)
+{
+    int nx = P->nx, ny = P->ny;
+    double h = P->h, a[6];
+    size_t r = (size_t)k * ny + j, c = r * nx + i;
+    size_t fu = r * (nx + 1) + i, fv = ((size_t)k * (ny + 1) + j) * nx + i;
+    double fx[2], fy[2], fz[2];
+    for (int f = 0; f < 2; ++f) {
+        for (int q = 0; q < 6; ++q) a[q] = sig3(P, s, i + f - 3 + q, j, k, t);
+        fx[f] = ppmface3(a, u[fu + f], dt, h);
+        for (int q = 0; q < 6; ++q) a[q] = sig3(P, s, i, j + f - 3 + q, k, t);
+        fy[f] = ppmface3(a, v[fv + (size_t)f * nx], dt, h);
+        for (int q = 0; q < 6; ++q) a[q] = sig3(P, s, i, j, k + f - 3 + q, t);
+        fz[f] = ppmface3(a, w[c + (size_t)f * nx * ny], dt, h);
+    }
+    double ub = 0.5 * (u[fu] + u[fu + 1]);
+    double vb = 0.5 * (v[fv] + v[fv + nx]);
+    double wb = 0.5 * (w[c] + w[c + (size_t)nx * ny]);
+    double Q = ub * (fx[1] - fx[0]) / h + vb * (fy[1] - fy[0]) / h + wb * (fz[1] - fz[0]) / h;
+    double sa = s[c] - dt * Q;
+    double al = damp3(P, (i + 0.5) * h);
+    return (1.0 - al) * sa + al * ((k + 0.5) * h - P->depth);
+}
+
 void oracle3_advect(const oracle3_tank *P, const double *s, const double *u, const double *v, const double *w,
                     double dt, double t, double *out)
 {
-    int nx = P->nx, ny = P->ny, nz = P->nz;
-    double h = P->h, a[6];
-    for (int k = 0; k < nz; ++k)
-        for (int j = 0; j < ny; ++j)
-            for (int i = 0; i < nx; ++i) {
-                size_t r = (size_t)k * ny + j, c = r * nx + i;
-                size_t fu = r * (nx + 1) + i, fv = ((size_t)k * (ny + 1) + j) * nx + i;
-                double fx[2], fy[2], fz[2];
-                for (int f = 0; f < 2; ++f) {
-                    for (int q = 0; q < 6; ++q) a[q] = sig3(P, s, i + f - 3 + q, j, k, t);
-                    fx[f] = ppmface3(a, u[fu + f], dt, h);
-                    for (int q = 0; q < 6; ++q) a[q] = sig3(P, s, i, j + f - 3 + q, k, t);
-                    fy[f] = ppmface3(a, v[fv + (size_t)f * nx], dt, h);
-                    for (int q = 0; q < 6; ++q) a[q] = sig3(P, s, i, j, k + f - 3 + q, t);
-                    fz[f] = ppmface3(a, w[c + (size_t)f * nx * ny], dt, h);
-                }
-                double ub = 0.5 * (u[fu] + u[fu + 1]);
-                double vb = 0.5 * (v[fv] + v[fv + nx]);
-                double wb = 0.5 * (w[c] + w[c + (size_t)nx * ny]);
-                double Q = ub * (fx[1] - fx[0]) / h + vb * (fy[1] - fy[0]) / h + wb * (fz[1] - fz[0]) / h;
-                double sa = s[c] - dt * Q;
-                double al = damp3(P, (i + 0.5) * h);
-                out[c] = (1.0 - al) * sa + al * ((k + 0.5) * h - P->depth);
-            }
+    for (int k = 0; k < P->nz; ++k)
+        for (int j = 0; j < P->ny; ++j)
+            for (int i = 0; i < P->nx; ++i)
+                out[((size_t)k * P->ny + j) * P->nx + i] = advect_cell3(P, s, u, v, w, dt, t, i, j, k);
+}
+
+/* The same at ncell listed cells (cell index c = (k ny + j) nx + i). */
+void oracle3_advect_cells(const oracle3_tank *P, const double *s, const double *u, const double *v, const double *w,
+                          double dt, double t, const long long *cells, int ncell, double *out)
+{
+    for (int q = 0; q < ncell; ++q) {
+        long long c = cells[q];
+        int i = (int)(c % P->nx), j = (int)((c / P->nx) % P->ny), k = (int)(c / ((long long)P->nx * P->ny));
+        out[q] = advect_cell3(P, s, u, v, w, dt, t, i, j, k);
+    }
 }
 
 static double mm3(double a, double b)

@@ -35,6 +35,9 @@ def _lib():
         L.oracle3_advect.restype = None
         L.oracle3_reinit.argtypes = [C.POINTER(Tank3), _dp, C.c_int, C.c_double]
         L.oracle3_reinit.restype = None
+        L.oracle3_advect_cells.argtypes = [C.POINTER(Tank3), _dp, _dp, _dp, _dp, C.c_double, C.c_double,
+                                           C.POINTER(C.c_longlong), C.c_int, _dp]
+        L.oracle3_advect_cells.restype = None
         _done = True
     return L
 
@@ -82,6 +85,15 @@ class Oracle3:
         assert u.shape == (nz, ny, nx + 1) and v.shape == (nz, ny + 1, nx) and w.shape == (nz + 1, ny, nx)
         out = np.zeros(self.shape)
         _lib().oracle3_advect(C.byref(self.P), _ptr(s), _ptr(u), _ptr(v), _ptr(w), dt, t, _ptr(out))
+        return out
+
+    def advect_cells(self, sigma, u, v, w, dt, t, cells):
+        """The advected sigma at the listed flat cell indices only."""
+        s, u, v, w = _f64(sigma), _f64(u), _f64(v), _f64(w)
+        cl = np.ascontiguousarray(cells, dtype=np.int64)
+        out = np.zeros(len(cl))
+        _lib().oracle3_advect_cells(C.byref(self.P), _ptr(s), _ptr(u), _ptr(v), _ptr(w), dt, t,
+                                    cl.ctypes.data_as(C.POINTER(C.c_longlong)), len(cl), _ptr(out))
         return out
 
     def reinit(self, sigma, nit, t):

@@ -36,6 +36,18 @@ class Waves(C.Structure):
                 ("damp_x0", C.c_double), ("damp_len", C.c_double), ("probe_x", C.c_double)]
 
 
+class Grid3(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("lx", C.c_double), ("ly", C.c_double),
+                ("lz", C.c_double), ("depth", C.c_double)]
+
+
+class Cylinder(C.Structure):
+    _fields_ = [("present", C.c_int)] + [(k, C.c_double) for k in ("xc", "yc", "radius", "length", "mass")]
+
+
+F3_SIGMA, F3_U, F3_V, F3_W, F3_RHO, F3_MU, F3_RHO_FLOW, F3_CHI = range(8)
+
+
 class Region(C.Structure):
     _fields_ = [("x0", C.c_double), ("y0", C.c_double), ("h", C.c_double), ("nx", C.c_int), ("ny", C.c_int)]
 
@@ -121,6 +133,15 @@ def load():
     L.wec_poisson_vcycle.argtypes = [vp, vp, vp]
     L.wec_poisson_solve.argtypes = [vp, vp, vp, C.c_double, C.c_int, C.POINTER(C.c_int), _dp]
     L.wec_poisson_create3.argtypes = [C.c_int, C.c_int, C.c_int, C.POINTER(SolverOpts), vp, C.POINTER(vp)]
+    L.wec_tank3_create.argtypes = [C.POINTER(Grid3), C.POINTER(Fluids), C.POINTER(Waves), C.POINTER(Cylinder), vp,
+                                   C.POINTER(vp)]
+    L.wec_tank3_destroy.argtypes = [vp]
+    L.wec_tank3_destroy.restype = None
+    L.wec_tank3_get_field.argtypes = [vp, C.c_int, _dp, C.c_size_t]
+    L.wec_tank3_set_field.argtypes = [vp, C.c_int, _dp, C.c_size_t]
+    L.wec_tank3_materials.argtypes = [vp, C.c_double]
+    L.wec_tank3_advect.argtypes = [vp, C.c_double, C.c_double]
+    L.wec_tank3_reinit.argtypes = [vp, C.c_int, C.c_double]
     L.wec_poisson_set_coefficients3.argtypes = [vp, vp, vp, vp]
     L.wec_wave_number.restype = C.c_double
     L.wec_wave_number.argtypes = [C.c_double, C.c_double, C.c_double]
@@ -612,3 +633,58 @@ class Poisson3(Poisson):
     def solve(self, b, x, rtol=1e-10, max_iters=500):
         self._n(b, x)
         return super().solve(b, x, rtol, max_iters)
+
+
+class Tank3:
+    """The level-set part of the 3D tank on the GPU (wec_tank3_*): ``cfg`` is a
+    3D workload dict (synth.tank3d); fields are numpy FP64 arrays, cells (nz, ny,
+    nx), u (nz, ny, nx+1), v (nz, ny+1, nx), w (nz+1, ny, nx)."""
+
+    def __init__(self, cfg, stream=None):
+        L = load()
+        self.cfg = cfg
+        nx, ny, nz = cfg["nx"], cfg["ny"], cfg["nz"]
+        g = Grid3(nx, ny, nz, cfg["lx"], cfg["ly"], cfg["lz"], cfg["depth"])
+        f = Fluids(cfg["rho_w"], cfg["rho_a"], cfg["mu_w"], cfg["mu_a"], cfg["g"])
+        amp, om, ph = wave_components(cfg["wave"])
+        self._w = [np.ascontiguousarray(a, dtype=np.float64) for a in (amp, om, ph)]
+        w = Waves(len(amp), _ptr(self._w[0]), _ptr(self._w[1]), _ptr(self._w[2]), cfg["damp_x0"], cfg["damp_len"],
+                  cfg["probe_x"])
+        b = cfg.get("body")
+        body = Cylinder(1, b["xc"], b["yc"], b["radius"], b["length"], b["mass"]) if b else Cylinder(0)
+        h = C.c_void_p()
+        _check(L.wec_tank3_create(C.byref(g), C.byref(f), C.byref(w), C.byref(body), _stream(stream), C.byref(h)))
+        self.h = h
+        self.shapes = {F3_SIGMA: (nz, ny, nx), F3_U: (nz, ny, nx + 1), F3_V: (nz, ny + 1, nx),
+                       F3_W: (nz + 1, ny, nx)}
+        for fid in (F3_RHO, F3_MU, F3_RHO_FLOW, F3_CHI):
+            self.shapes[fid] = (nz, ny, nx)
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().wec_tank3_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def get(self, fid):
+        a = np.zeros(self.shapes[fid])
+        _check(load().wec_tank3_get_field(self.h, fid, _ptr(a), a.size))
+        return a
+
+    def set(self, fid, a):
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        if a.shape != self.shapes[fid]:
+            raise ValueError(f"expected shape {self.shapes[fid]}, got {a.shape}")
+        _check(load().wec_tank3_set_field(self.h, fid, _ptr(a), a.size))
+
+    def materials(self, zc):
+        _check(load().wec_tank3_materials(self.h, zc))
+        return {k: self.get(f) for k, f in (("rho", F3_RHO), ("mu", F3_MU), ("rho_flow", F3_RHO_FLOW),
+                                            ("chi", F3_CHI))}
+
+    def advect(self, dt, t):
+        _check(load().wec_tank3_advect(self.h, dt, t))
+
+    def reinit(self, nit, t):
+        _check(load().wec_tank3_reinit(self.h, nit, t))
