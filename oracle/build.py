@@ -8,7 +8,7 @@ import os
 import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SRCS = [os.path.join(HERE, f) for f in ("wec_oracle.c", "poisson3d.c", "levelset3d.c")]
+SRCS = [os.path.join(HERE, f) for f in ("wec_oracle.c", "poisson3d.c", "levelset3d.c", "tank3d.c")]
 LIB = os.path.join(HERE, "liboracle.so")
 
 
