@@ -384,6 +384,10 @@ typedef struct {
 typedef struct {
     int present;
     double xc, yc, radius, length, mass;
+    double zc, kappa_p, added_mass, pto_damping; /* initial centre height; Brinkman
+                                                     permeability; artificial added mass of
+                                                     the stabilised heave update; linear PTO
+                                                     damper c (F_PTO = f_pto - c zdot) */
 } wec_cylinder;
 
 typedef struct wec_tank3 wec_tank3;
@@ -392,7 +396,8 @@ typedef struct wec_tank3 wec_tank3;
  * [nz][ny+1][nx], w [nz+1][ny][nx] (face k of w below cell layer k). */
 enum {
     WEC_F3_SIGMA = 0, WEC_F3_U = 1, WEC_F3_V = 2, WEC_F3_W = 3, /* state: get and set */
-    WEC_F3_RHO = 4, WEC_F3_MU = 5, WEC_F3_RHO_FLOW = 6, WEC_F3_CHI = 7 /* materials: get */
+    WEC_F3_RHO = 4, WEC_F3_MU = 5, WEC_F3_RHO_FLOW = 6, WEC_F3_CHI = 7, /* materials: get */
+    WEC_F3_P = 8 /* p^{n-1/2} (cells; state of a stepping tank): get and set */
 };
 
 /* The level-set part of the 3D step on the GPU (FP64): sigma, the face
@@ -402,7 +407,8 @@ enum {
  * damp_x0 + damp_len] at the outlet.  All fields start at zero.  Host arrays
  * are copied; the calls synchronise the object's stream before returning. */
 int wec_tank3_create(const wec_grid3 *grid, const wec_fluids *fluids, const wec_waves *waves,
-                     const wec_cylinder *body, void *cuda_stream, wec_tank3 **out);
+                     const wec_cylinder *body, const wec_solver_opts *opts, void *cuda_stream,
+                     wec_tank3 **out);
 void wec_tank3_destroy(wec_tank3 *tank);
 /* host_dst / host_src: n doubles, n = the field's size (WEC_ERR_INVALID otherwise;
  * only the state fields can be set). */
@@ -419,6 +425,23 @@ int wec_tank3_advect(wec_tank3 *tank, double dt, double t);
 /* nit Sussman pseudo-steps (TVD-RK2, d tau = 0.3 h) toward |grad sigma| = 1 with
  * the sign of sigma at the call (section "Interface tracking"); ghosts at t. */
 int wec_tank3_reinit(wec_tank3 *tank, int nit, double t);
+/* One time step of the 3D tank (needs opts at creation; precision WEC_PREC_FP64 or
+ * WEC_PREC_MIXED_MG, the stencils FP64): heave force from p^{n-1/2}, u^n (Eq.
+ * int_fh: pressure interpolated to psi = 0 and the normal viscous stress on
+ * z-faces, the shear stresses on x- and y-faces, face area h^2); heave update
+ * (Eq. newton_u, stabilised by added_mass); sigma advection + damping zone and
+ * n_reinit reinitialisation pseudo-steps; materials at n+1; consistent transport
+ * and the Crank-Nicolson momentum system (n_jacobi Jacobi sweeps; Dirichlet:
+ * Airy inflow u at x = 0, u = 0 at the outlet, v = 0 on the side walls, w = 0 on
+ * the bed; vorticity damping over the top four cells, momentum damping in the
+ * zone); the pressure increment with beta = 1 / D (rtol, FGMRES + V-cycle) and
+ * the projection.  At creation with opts: sigma = z - depth - eta(x, 0), the
+ * incident Airy velocities, p = the discrete hydrostatic pressure of rho^flow.
+ * out: the step record (z relative to the initial zc; eta at (probe_x, ly / 2)).
+ * Returns the solver's status (WEC_ERR_NOT_CONVERGED still advances the state). */
+int wec_tank3_step(wec_tank3 *tank, double dt, double pto_force, wec_step_result *out);
+/* t, zc, zdot, zc at creation, zdot of the previous step. */
+int wec_tank3_get_state(const wec_tank3 *tank, double *out5);
 
 /* ---- without device allocation ------------------------------------------ */
 /* ||b - A x||_2 for the pressure operator above (same coefficient layout and

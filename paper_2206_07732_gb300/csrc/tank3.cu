@@ -1,9 +1,13 @@
-// The three-dimensional tank (wec_tank3): its level-set part -- materials,
-// advection and reinitialisation of sigma on an nx x ny x nz grid with z
-// vertical and a heaving vertical cylinder (sections "Interface tracking",
-// "Level set advection", "Density and viscosity specification", d = 3) -- as
-// FP64 kernels, one thread per cell, x fastest.  The 3D pressure equation is
-// the wec_poisson object made by wec_poisson_create3.
+// The three-dimensional tank (wec_tank3): one time step of the two-phase flow
+// with a heaving vertical cylinder on an nx x ny x nz grid with z vertical
+// (sections "Continuous equations of motion" through "Fluid-structure
+// coupling", d = 3) as FP64 kernels, one thread per cell or face, x fastest;
+// the pressure increment is solved by a 3D wec_poisson object the tank owns
+// (FP64, or FP32 V-cycles for WEC_PREC_MIXED_MG).  The step is the
+// two-dimensional one with three velocity components: heave force (Eq. int_fh)
+// and update, sigma advection + damping zone and reinitialisation, materials,
+// consistent transport and the Crank-Nicolson momentum system by Jacobi
+// sweeps, the pressure increment, the projection.
 //
 // Readings (the two-dimensional ones carried to three directions):
 //   materials: H_flow(sigma) then H_body(psi) with half-width h; psi of the
@@ -21,6 +25,7 @@
 //     differences with minmod corrections, TVD-RK2, d tau = 0.3 h, sign of the
 //     input field S = sigma0 / sqrt(sigma0^2 + h^2).
 #include <cmath>
+#include <algorithm>
 #include <new>
 #include <string>
 #include <utility>
@@ -46,6 +51,18 @@ struct wec_tank3 {
     double *u = nullptr, *v = nullptr, *w = nullptr;
     double *rho = nullptr, *mu = nullptr, *rhof = nullptr, *chi = nullptr;
     double *consts = nullptr;  // wave components and damping table
+    // the step
+    wec_solver_opts opts{};
+    double g = 9.81, lz = 0, kappa_p = 1e-8, mass = 0, added_mass = 0, pto_c = 0, probe_x = 0;
+    double t = 0, zc = 0, zc0 = 0, zdot = 0, zdot_prev = 0;
+    double *p = nullptr, *phi = nullptr, *rhs = nullptr;
+    double *mu1 = nullptr, *rf1 = nullptr, *chi1 = nullptr;
+    double *D[3] = {}, *R[3] = {}, *A[3] = {}, *B[3] = {};  // per component u, v, w
+    double *bc = nullptr;    // [nz] u_in(t1) at the cell layers; [nz+1] w_in(t0), w_in(t1) at the faces
+    double *tabs = nullptr;  // damping weight of the u-faces [nx+1]; vorticity damping at cell / face heights
+    double *part = nullptr;  // reduction partials
+    wec_poisson *solver = nullptr;
+    bool stepping = false;   // created with solver options (wec_tank3_create_step)
 };
 
 namespace wec {
@@ -53,14 +70,18 @@ namespace {
 
 constexpr double kPi3 = 3.14159265358979323846;
 
-__device__ __forceinline__ double heav3(double phi, double eps)
+// FP64 division and square root expand into long FMA sequences on this GPU:
+// the kernels multiply by reciprocals formed once (1/h, 1/6, ...), which
+// differs from dividing by at most an ulp.
+__device__ __forceinline__ double heav3(double phi, double eps, double ieps)
 {
     if (phi < -eps) return 0.0;
     if (phi > eps) return 1.0;
-    return 0.5 * (1.0 + phi / eps + sin(kPi3 * phi / eps) / kPi3);
+    const double r = phi * ieps;
+    return 0.5 * (1.0 + r + sin(kPi3 * r) * (1.0 / kPi3));
 }
 
-__device__ double eta3(const Tank3P &P, double x, double t)
+__device__ __noinline__ double eta3(const Tank3P &P, double x, double t)
 {
     double e = 0.0;
     for (int c = 0; c < P.ncomp; ++c) e += P.amp[c] * cos(P.kw[c] * x - P.omega[c] * t + P.phase[c]);
@@ -95,14 +116,15 @@ __device__ __forceinline__ double vl3(double am, double a0, double ap)
 __device__ __forceinline__ void ppm_edges3(const double *a, double &eL, double &eR)
 {
     const double dm = vl3(a[0], a[1], a[2]), d0 = vl3(a[1], a[2], a[3]), dp = vl3(a[2], a[3], a[4]);
-    double L = a[1] + 0.5 * (a[2] - a[1]) - (d0 - dm) / 6.0;
-    double R = a[2] + 0.5 * (a[3] - a[2]) - (dp - d0) / 6.0;
+    constexpr double i6 = 1.0 / 6.0;
+    double L = a[1] + 0.5 * (a[2] - a[1]) - (d0 - dm) * i6;
+    double R = a[2] + 0.5 * (a[3] - a[2]) - (dp - d0) * i6;
     const double c = a[2];
     if ((R - c) * (c - L) <= 0.0) {
         L = c;
         R = c;
     } else {
-        const double dA = R - L, m6 = dA * (c - 0.5 * (L + R)), q = dA * dA / 6.0;
+        const double dA = R - L, m6 = dA * (c - 0.5 * (L + R)), q = dA * dA * i6;
         if (m6 > q)
             L = 3.0 * c - 2.0 * R;
         else if (-q > m6)
@@ -112,18 +134,20 @@ __device__ __forceinline__ void ppm_edges3(const double *a, double &eL, double &
     eR = R;
 }
 
-// time-centred upwind state at the face between a[2] and a[3] (a: cells f-3 .. f+2)
-__device__ __forceinline__ double ppm_face3(const double *a, double vel, double dt, double h)
+// time-centred upwind state at the face between a[2] and a[3] (a: cells f-3 .. f+2);
+// dtih = dt / h
+__device__ __forceinline__ double ppm_face3(const double *a, double vel, double dtih)
 {
+    constexpr double t3 = 2.0 / 3.0;
     double L, R;
     if (vel >= 0.0) {
         ppm_edges3(a, L, R);
-        const double C = vel * dt / h, dA = R - L, a6 = 6.0 * (a[2] - 0.5 * (L + R));
-        return R - 0.5 * C * (dA - (1.0 - 2.0 * C / 3.0) * a6);
+        const double C = vel * dtih, dA = R - L, a6 = 6.0 * (a[2] - 0.5 * (L + R));
+        return R - 0.5 * C * (dA - (1.0 - C * t3) * a6);
     }
     ppm_edges3(a + 1, L, R);
-    const double C = -vel * dt / h, dA = R - L, a6 = 6.0 * (a[3] - 0.5 * (L + R));
-    return L + 0.5 * C * (dA + (1.0 - 2.0 * C / 3.0) * a6);
+    const double C = -vel * dtih, dA = R - L, a6 = 6.0 * (a[3] - 0.5 * (L + R));
+    return L + 0.5 * C * (dA + (1.0 - C * t3) * a6);
 }
 
 struct Cell3 {
@@ -154,7 +178,7 @@ __global__ void __launch_bounds__(128) k3t_materials(Tank3P P, const double *__r
         const double x = (q.i + 0.5) * h - P.bxc, y = (q.j + 0.5) * h - P.byc, z = (q.k + 0.5) * h - zc;
         psi = fmax(sqrt(x * x + y * y) - P.br, fabs(z) - 0.5 * P.blen);
     }
-    const double hf = heav3(sig[q.c], h), hb = heav3(psi, h);
+    const double hf = heav3(sig[q.c], h, P.ih), hb = heav3(psi, h, P.ih);
     const double rf = P.rho_w + (P.rho_a - P.rho_w) * hf;
     const double mf = P.mu_w + (P.mu_a - P.mu_w) * hf;
     rho[q.c] = P.rho_s + (rf - P.rho_s) * hb;
@@ -173,23 +197,24 @@ __global__ void __launch_bounds__(128) k3t_advect(Tank3P P, const double *__rest
     const int nx = P.nx, ny = P.ny, i = q.i, j = q.j, k = q.k;
     const long long r = (long long)k * ny + j, fu = r * (nx + 1) + i, fv = ((long long)k * (ny + 1) + j) * nx + i;
     const long long pl = (long long)nx * ny;
-    const double h = P.h;
+    const double h = P.h, ih = P.ih, dtih = dt * ih;
     double a[6], fx[2], fy[2], fz[2];
+#pragma unroll
     for (int f = 0; f < 2; ++f) {
 #pragma unroll
         for (int m = 0; m < 6; ++m) a[m] = sig3(P, s, i + f - 3 + m, j, k, t);
-        fx[f] = ppm_face3(a, u[fu + f], dt, h);
+        fx[f] = ppm_face3(a, u[fu + f], dtih);
 #pragma unroll
         for (int m = 0; m < 6; ++m) a[m] = sig3(P, s, i, j + f - 3 + m, k, t);
-        fy[f] = ppm_face3(a, v[fv + f * nx], dt, h);
+        fy[f] = ppm_face3(a, v[fv + f * nx], dtih);
 #pragma unroll
         for (int m = 0; m < 6; ++m) a[m] = sig3(P, s, i, j, k + f - 3 + m, t);
-        fz[f] = ppm_face3(a, w[q.c + f * pl], dt, h);
+        fz[f] = ppm_face3(a, w[q.c + f * pl], dtih);
     }
     const double ub = 0.5 * (u[fu] + u[fu + 1]);
     const double vb = 0.5 * (v[fv] + v[fv + nx]);
     const double wb = 0.5 * (w[q.c] + w[q.c + pl]);
-    const double Q = ub * (fx[1] - fx[0]) / h + vb * (fy[1] - fy[0]) / h + wb * (fz[1] - fz[0]) / h;
+    const double Q = ub * (fx[1] - fx[0]) * ih + vb * (fy[1] - fy[0]) * ih + wb * (fz[1] - fz[0]) * ih;
     const double sa = s[q.c] - dt * Q;
     const double al = P.damp[i];
     out[q.c] = (1.0 - al) * sa + al * ((k + 0.5) * h - P.depth);
@@ -205,7 +230,7 @@ __device__ __forceinline__ double mm3(double a, double b)
 __device__ double reinit_rhs3(const Tank3P &P, const double *__restrict__ f, const double *__restrict__ s0,
                               const Cell3 &q, double t)
 {
-    const double h = P.h, c = f[q.c];
+    const double h = P.h, ih = P.ih, hih = 0.5 * P.ih, c = f[q.c];
     const double sg0 = s0[q.c];
     const bool pos = sg0 > 0.0;
     double g2 = 0.0;
@@ -217,8 +242,8 @@ __device__ double reinit_rhs3(const Tank3P &P, const double *__restrict__ f, con
         const double p1 = sig3(P, f, q.i + di, q.j + dj, q.k + dk, t);
         const double p2 = sig3(P, f, q.i + 2 * di, q.j + 2 * dj, q.k + 2 * dk, t);
         const double dm = m2 - 2.0 * m1 + c, d0 = m1 - 2.0 * c + p1, dp = c - 2.0 * p1 + p2;
-        const double a = (c - m1) / h + mm3(dm, d0) / (2.0 * h);
-        const double b = (p1 - c) / h - mm3(d0, dp) / (2.0 * h);
+        const double a = (c - m1) * ih + mm3(dm, d0) * hih;
+        const double b = (p1 - c) * ih - mm3(d0, dp) * hih;
         double g;
         if (pos) {
             const double x = fmax(a, 0.0), y = fmin(b, 0.0);
@@ -229,7 +254,7 @@ __device__ double reinit_rhs3(const Tank3P &P, const double *__restrict__ f, con
         }
         g2 = d == 0 ? g : g2 + g;
     }
-    const double S = sg0 / sqrt(sg0 * sg0 + h * h);
+    const double S = sg0 * rsqrt(sg0 * sg0 + h * h);
     return S * (sqrt(g2) - 1.0);
 }
 
@@ -246,11 +271,566 @@ __global__ void __launch_bounds__(128) k3t_reinit_stage(Tank3P P, const double *
     out[q.c] = stage == 1 ? y : 0.5 * (out[q.c] + y);
 }
 
+// ------------------------------------------------------------ the step ----
+// Velocity ghosts: nearest face (free slip); at the inflow v is reflected oddly
+// about 0 and w about the incident wave's w_in (win: [nz+1] at the time used).
+__device__ __forceinline__ double cellq(const Tank3P &P, const double *__restrict__ a, int i, int j, int k)
+{
+    i = min(max(i, 0), P.nx - 1);
+    j = min(max(j, 0), P.ny - 1);
+    k = min(max(k, 0), P.nz - 1);
+    return a[((long long)k * P.ny + j) * P.nx + i];
+}
+__device__ __forceinline__ double uq(const Tank3P &P, const double *__restrict__ u, int i, int j, int k)
+{
+    i = min(max(i, 0), P.nx);
+    j = min(max(j, 0), P.ny - 1);
+    k = min(max(k, 0), P.nz - 1);
+    return u[((long long)k * P.ny + j) * (P.nx + 1) + i];
+}
+__device__ __forceinline__ double vq(const Tank3P &P, const double *__restrict__ v, int i, int j, int k)
+{
+    j = min(max(j, 0), P.ny);
+    k = min(max(k, 0), P.nz - 1);
+    if (i > P.nx - 1) i = P.nx - 1;
+    if (i < 0) return -v[((long long)k * (P.ny + 1) + j) * P.nx + (-1 - i)];
+    return v[((long long)k * (P.ny + 1) + j) * P.nx + i];
+}
+__device__ __forceinline__ double wq(const Tank3P &P, const double *__restrict__ w, const double *__restrict__ win,
+                                     int i, int j, int k)
+{
+    k = min(max(k, 0), P.nz);
+    j = min(max(j, 0), P.ny - 1);
+    if (i > P.nx - 1) i = P.nx - 1;
+    if (i < 0) return 2.0 * win[k] - w[((long long)k * P.ny + j) * P.nx + (-1 - i)];
+    return w[((long long)k * P.ny + j) * P.nx + i];
+}
+
+__device__ __forceinline__ double koren3(double quu, double qu, double qd)
+{
+    const double d1 = qu - quu, d2 = qd - qu;
+    if (d1 * d2 <= 0.0) return qu;
+    const double m = fmin(2.0 * fabs(d2), fmin((fabs(d1) + 2.0 * fabs(d2)) / 3.0, 2.0 * fabs(d1)));
+    return d1 > 0.0 ? qu + 0.5 * m : qu - 0.5 * m;
+}
+__device__ __forceinline__ double upw3(double q0, double q1, double q2, double q3, double vel)
+{
+    return vel >= 0.0 ? koren3(q0, q1, q2) : koren3(q3, q2, q1);
+}
+// face densities: the mean of the face's two cells (face index clamped first)
+__device__ __forceinline__ double ruq(const Tank3P &P, const double *rc, int i, int j, int k)
+{
+    i = min(max(i, 0), P.nx);
+    j = min(max(j, 0), P.ny - 1);
+    k = min(max(k, 0), P.nz - 1);
+    return 0.5 * (cellq(P, rc, i - 1, j, k) + cellq(P, rc, i, j, k));
+}
+__device__ __forceinline__ double rvq(const Tank3P &P, const double *rc, int i, int j, int k)
+{
+    i = min(max(i, 0), P.nx - 1);
+    j = min(max(j, 0), P.ny);
+    k = min(max(k, 0), P.nz - 1);
+    return 0.5 * (cellq(P, rc, i, j - 1, k) + cellq(P, rc, i, j, k));
+}
+__device__ __forceinline__ double rwq(const Tank3P &P, const double *rc, int i, int j, int k)
+{
+    i = min(max(i, 0), P.nx - 1);
+    j = min(max(j, 0), P.ny - 1);
+    k = min(max(k, 0), P.nz);
+    return 0.5 * (cellq(P, rc, i, j, k - 1) + cellq(P, rc, i, j, k));
+}
+
+struct Vel3 {
+    const double *u, *v, *w, *win;
+};
+
+// rho-breve and C of a momentum control volume: comp 0 u-face, 1 v-face, 2 w-face;
+// the three pairs of CV faces summed x, then y, then z
+__device__ void transport3(const Tank3P &P, const double *rc, const Vel3 &V, int comp, int i, int j, int k, double dt,
+                           double &rb, double &C)
+{
+    const double h = P.h;
+    double m[6], f[6];
+#define QV(a, b, c) (comp == 0 ? uq(P, V.u, a, b, c) : comp == 1 ? vq(P, V.v, a, b, c) : wq(P, V.w, V.win, a, b, c))
+#define RV(a, b, c) (comp == 0 ? ruq(P, rc, a, b, c) : comp == 1 ? rvq(P, rc, a, b, c) : rwq(P, rc, a, b, c))
+    for (int d = 0; d < 3; ++d)
+        for (int s = 0; s < 2; ++s) {
+            // the advecting velocity of the CV face and the stencil direction
+            double U;
+            if (d == comp) {  // CV faces at the cell centres on either side
+                const int o = s - 1;
+                U = comp == 0   ? 0.5 * (uq(P, V.u, i + o, j, k) + uq(P, V.u, i + o + 1, j, k))
+                    : comp == 1 ? 0.5 * (vq(P, V.v, i, j + o, k) + vq(P, V.v, i, j + o + 1, k))
+                                : 0.5 * (wq(P, V.w, V.win, i, j, k + o) + wq(P, V.w, V.win, i, j, k + o + 1));
+            } else {  // CV faces on the edges: the d-velocity averaged over the comp direction
+                const int e = s;  // edge index offset in d
+                if (d == 0)
+                    U = comp == 1 ? 0.5 * (uq(P, V.u, i + e, j - 1, k) + uq(P, V.u, i + e, j, k))
+                                  : 0.5 * (uq(P, V.u, i + e, j, k - 1) + uq(P, V.u, i + e, j, k));
+                else if (d == 1)
+                    U = comp == 0 ? 0.5 * (vq(P, V.v, i - 1, j + e, k) + vq(P, V.v, i, j + e, k))
+                                  : 0.5 * (vq(P, V.v, i, j + e, k - 1) + vq(P, V.v, i, j + e, k));
+                else
+                    U = comp == 0 ? 0.5 * (wq(P, V.w, V.win, i - 1, j, k + e) + wq(P, V.w, V.win, i, j, k + e))
+                                  : 0.5 * (wq(P, V.w, V.win, i, j - 1, k + e) + wq(P, V.w, V.win, i, j, k + e));
+            }
+            const int a0 = s - 1;  // the stencil runs over (base + a0 - 1 .. base + a0 + 2) along d
+            const int di = d == 0, dj = d == 1, dk = d == 2;
+            double rr[4], qq[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int o = a0 - 1 + q;
+                rr[q] = RV(i + o * di, j + o * dj, k + o * dk);
+                qq[q] = QV(i + o * di, j + o * dj, k + o * dk);
+            }
+            const double r = upw3(rr[0], rr[1], rr[2], rr[3], U);
+            const double qv = upw3(qq[0], qq[1], qq[2], qq[3], U);
+            m[2 * d + s] = U * r;
+            f[2 * d + s] = m[2 * d + s] * qv;
+        }
+    rb = RV(i, j, k) - dt / h * (((m[1] - m[0]) + (m[3] - m[2])) + (m[5] - m[4]));
+    C = (((f[1] - f[0]) + (f[3] - f[2])) + (f[5] - f[4])) / h;
+#undef QV
+#undef RV
+}
+
+// viscous stresses and div[mu (grad u + grad u^T)] with edge viscosities (the
+// mean of the four cells around the edge)
+struct Visc3 {
+    const double *mu;
+    Vel3 V;
+};
+__device__ __forceinline__ double mxy3(const Tank3P &P, const double *mu, int i, int j, int k)
+{
+    return 0.25 * (cellq(P, mu, i - 1, j - 1, k) + cellq(P, mu, i, j - 1, k) + cellq(P, mu, i - 1, j, k) +
+                   cellq(P, mu, i, j, k));
+}
+__device__ __forceinline__ double mxz3(const Tank3P &P, const double *mu, int i, int j, int k)
+{
+    return 0.25 * (cellq(P, mu, i - 1, j, k - 1) + cellq(P, mu, i, j, k - 1) + cellq(P, mu, i - 1, j, k) +
+                   cellq(P, mu, i, j, k));
+}
+__device__ __forceinline__ double myz3(const Tank3P &P, const double *mu, int i, int j, int k)
+{
+    return 0.25 * (cellq(P, mu, i, j - 1, k - 1) + cellq(P, mu, i, j, k - 1) + cellq(P, mu, i, j - 1, k) +
+                   cellq(P, mu, i, j, k));
+}
+#define U3(a, b, c) uq(P, X.V.u, a, b, c)
+#define V3(a, b, c) vq(P, X.V.v, a, b, c)
+#define W3(a, b, c) wq(P, X.V.w, X.V.win, a, b, c)
+__device__ __forceinline__ double txx(const Tank3P &P, const Visc3 &X, int i, int j, int k)
+{
+    return 2.0 * cellq(P, X.mu, i, j, k) * (U3(i + 1, j, k) - U3(i, j, k)) / P.h;
+}
+__device__ __forceinline__ double tyy(const Tank3P &P, const Visc3 &X, int i, int j, int k)
+{
+    return 2.0 * cellq(P, X.mu, i, j, k) * (V3(i, j + 1, k) - V3(i, j, k)) / P.h;
+}
+__device__ __forceinline__ double tzz(const Tank3P &P, const Visc3 &X, int i, int j, int k)
+{
+    return 2.0 * cellq(P, X.mu, i, j, k) * (W3(i, j, k + 1) - W3(i, j, k)) / P.h;
+}
+__device__ __forceinline__ double txy(const Tank3P &P, const Visc3 &X, int i, int j, int k)
+{
+    return mxy3(P, X.mu, i, j, k) * ((U3(i, j, k) - U3(i, j - 1, k)) / P.h + (V3(i, j, k) - V3(i - 1, j, k)) / P.h);
+}
+__device__ __forceinline__ double txz(const Tank3P &P, const Visc3 &X, int i, int j, int k)
+{
+    return mxz3(P, X.mu, i, j, k) * ((U3(i, j, k) - U3(i, j, k - 1)) / P.h + (W3(i, j, k) - W3(i - 1, j, k)) / P.h);
+}
+__device__ __forceinline__ double tyz(const Tank3P &P, const Visc3 &X, int i, int j, int k)
+{
+    return myz3(P, X.mu, i, j, k) * ((V3(i, j, k) - V3(i, j, k - 1)) / P.h + (W3(i, j, k) - W3(i, j - 1, k)) / P.h);
+}
+#undef U3
+#undef V3
+#undef W3
+__device__ double visc3(const Tank3P &P, const Visc3 &X, int comp, int i, int j, int k)
+{
+    const double h = P.h;
+    if (comp == 0)
+        return ((txx(P, X, i, j, k) - txx(P, X, i - 1, j, k)) / h + (txy(P, X, i, j + 1, k) - txy(P, X, i, j, k)) / h) +
+               (txz(P, X, i, j, k + 1) - txz(P, X, i, j, k)) / h;
+    if (comp == 1)
+        return ((tyy(P, X, i, j, k) - tyy(P, X, i, j - 1, k)) / h + (txy(P, X, i + 1, j, k) - txy(P, X, i, j, k)) / h) +
+               (tyz(P, X, i, j, k + 1) - tyz(P, X, i, j, k)) / h;
+    return ((tzz(P, X, i, j, k) - tzz(P, X, i, j, k - 1)) / h + (txz(P, X, i + 1, j, k) - txz(P, X, i, j, k)) / h) +
+           (tyz(P, X, i, j + 1, k) - tyz(P, X, i, j, k)) / h;
+}
+// interior-formula diagonal (the Jacobi splitting only)
+__device__ double vdiag3(const Tank3P &P, const double *mu, int comp, int i, int j, int k)
+{
+    const double h2 = P.h * P.h;
+    if (comp == 0)
+        return -(2.0 * cellq(P, mu, i, j, k) + 2.0 * cellq(P, mu, i - 1, j, k) + mxy3(P, mu, i, j + 1, k) +
+                 mxy3(P, mu, i, j, k) + mxz3(P, mu, i, j, k + 1) + mxz3(P, mu, i, j, k)) / h2;
+    if (comp == 1)
+        return -(2.0 * cellq(P, mu, i, j, k) + 2.0 * cellq(P, mu, i, j - 1, k) + mxy3(P, mu, i + 1, j, k) +
+                 mxy3(P, mu, i, j, k) + myz3(P, mu, i, j, k + 1) + myz3(P, mu, i, j, k)) / h2;
+    return -(2.0 * cellq(P, mu, i, j, k) + 2.0 * cellq(P, mu, i, j, k - 1) + mxz3(P, mu, i + 1, j, k) +
+             mxz3(P, mu, i, j, k) + myz3(P, mu, i, j + 1, k) + myz3(P, mu, i, j, k)) / h2;
+}
+
+// solved faces of component comp: u i = 1..nx-1; v j = 1..ny-1; w k = 1..nz
+__device__ __forceinline__ bool face_of(const Tank3P &P, int comp, int &i, int &j, int &k, long long &f)
+{
+    i = blockIdx.x * blockDim.x + threadIdx.x;
+    j = blockIdx.y;
+    k = blockIdx.z;
+    if (comp == 0) {
+        i += 1;
+        if (i > P.nx - 1) return false;
+        f = ((long long)k * P.ny + j) * (P.nx + 1) + i;
+    } else if (comp == 1) {
+        j += 1;
+        if (i > P.nx - 1 || j > P.ny - 1) return false;
+        f = ((long long)k * (P.ny + 1) + j) * P.nx + i;
+    } else {
+        k += 1;
+        if (i > P.nx - 1) return false;
+        f = ((long long)k * P.ny + j) * P.nx + i;
+    }
+    return true;
+}
+
+struct MomIn {
+    const double *rho_n, *mu_n, *chi1, *rf1, *p;
+    Vel3 V;                      // u^n, v^n, w^n with w_in(t^n)
+    const double *dampu, *vortc, *vortf;  // damping weight at u-faces; vorticity damping at cell / face heights
+    double dt, zd1, g, ikp;
+};
+
+__global__ void __launch_bounds__(128) k3t_momentum(Tank3P P, MomIn M, int comp, double *__restrict__ D,
+                                                    double *__restrict__ R)
+{
+    pdl_entry();
+    int i, j, k;
+    long long f;
+    if (!face_of(P, comp, i, j, k, f)) return;
+    double rb, C;
+    transport3(P, M.rho_n, M.V, comp, i, j, k, M.dt, rb, C);
+    const Visc3 X{M.mu_n, M.V};
+    const double h = P.h;
+    const int ci = comp == 0 ? i - 1 : i, cj = comp == 1 ? j - 1 : j, ck = comp == 2 ? k - 1 : k;
+    const double chi = 0.5 * (cellq(P, M.chi1, ci, cj, ck) + cellq(P, M.chi1, i, j, k));
+    const double al = comp == 0 ? M.dampu[i] : P.damp[i];
+    const double vd = comp == 2 ? M.vortf[k] : M.vortc[k];
+    D[f] = rb / M.dt + chi * M.ikp + al * rb / M.dt + vd;
+    const double pc = k < P.nz ? M.p[((long long)k * P.ny + j) * P.nx + i] : 0.0;
+    if (comp == 0) {
+        R[f] = ruq(P, M.rho_n, i, j, k) * M.V.u[f] / M.dt - C + 0.5 * visc3(P, X, 0, i, j, k) -
+               (pc - M.p[((long long)k * P.ny + j) * P.nx + i - 1]) / h;
+    } else if (comp == 1) {
+        R[f] = rvq(P, M.rho_n, i, j, k) * M.V.v[f] / M.dt - C + 0.5 * visc3(P, X, 1, i, j, k) -
+               (pc - M.p[((long long)k * P.ny + j - 1) * P.nx + i]) / h;
+    } else {
+        const double rf = 0.5 * (cellq(P, M.rf1, i, j, k - 1) + cellq(P, M.rf1, i, j, k));
+        const double pb = M.p[((long long)(k - 1) * P.ny + j) * P.nx + i];
+        const double gp = k < P.nz ? (pc - pb) / h : -2.0 * pb / h;
+        R[f] = rwq(P, M.rho_n, i, j, k) * M.V.w[f] / M.dt - C + 0.5 * visc3(P, X, 2, i, j, k) - rf * M.g +
+               chi * M.zd1 * M.ikp - gp;
+    }
+}
+
+// one Crank-Nicolson Jacobi sweep of component comp: B = (R + (L(A) - ld A) / 2) / (D - ld / 2)
+__global__ void __launch_bounds__(128) k3t_jacobi(Tank3P P, const double *__restrict__ mu1, Vel3 A, int comp,
+                                                  const double *__restrict__ D, const double *__restrict__ R,
+                                                  double *__restrict__ B)
+{
+    pdl_entry();
+    int i, j, k;
+    long long f;
+    if (!face_of(P, comp, i, j, k, f)) return;
+    const Visc3 X{mu1, A};
+    const double ld = vdiag3(P, mu1, comp, i, j, k);
+    const double a = comp == 0 ? A.u[f] : comp == 1 ? A.v[f] : A.w[f];
+    B[f] = (R[f] + 0.5 * (visc3(P, X, comp, i, j, k) - ld * a)) / (D[f] - 0.5 * ld);
+}
+
+// Dirichlet faces of the predictor: u_in(t1) at x = 0, u = 0 at the outlet, v = 0
+// on the side walls, w = 0 on the bed
+__global__ void k3t_dirichlet(Tank3P P, const double *__restrict__ uin1, double *u, double *v, double *w)
+{
+    pdl_entry();
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nx = P.nx, ny = P.ny, nz = P.nz;
+    if (a < ny * nz) {
+        const int k = a / ny, j = a - k * ny;
+        const long long r = ((long long)k * ny + j) * (nx + 1);
+        u[r] = uin1[k];
+        u[r + nx] = 0.0;
+    }
+    if (a < nx * nz) {
+        const int k = a / nx, i = a - k * nx;
+        v[((long long)k * (ny + 1)) * nx + i] = 0.0;
+        v[((long long)k * (ny + 1) + ny) * nx + i] = 0.0;
+    }
+    if (a < nx * ny) w[a] = 0.0;
+}
+
+// beta = 1 / D on the solved faces, 0 on the walls and the bed; rhs = -h div u*
+__global__ void k3t_beta(Tank3P P, int comp, const double *__restrict__ D, double *__restrict__ beta, long long n)
+{
+    pdl_entry();
+    const long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (f >= n) return;
+    bool wall;
+    if (comp == 0) {
+        const int i = (int)(f % (P.nx + 1));
+        wall = i == 0 || i == P.nx;
+    } else if (comp == 1) {
+        const int j = (int)((f / P.nx) % (P.ny + 1));
+        wall = j == 0 || j == P.ny;
+    } else {
+        wall = f < (long long)P.nx * P.ny;
+    }
+    beta[f] = wall ? 0.0 : 1.0 / D[f];
+}
+
+__global__ void __launch_bounds__(128) k3t_rhs(Tank3P P, Vel3 S, double *__restrict__ rhs)
+{
+    pdl_entry();
+    Cell3 q;
+    if (!cell_of(P, q)) return;
+    const int nx = P.nx, ny = P.ny;
+    const long long fu = ((long long)q.k * ny + q.j) * (nx + 1) + q.i, fv = ((long long)q.k * (ny + 1) + q.j) * nx + q.i;
+    const long long pl = (long long)nx * ny;
+    rhs[q.c] = -P.h * (((S.u[fu + 1] - S.u[fu]) + (S.v[fv + nx] - S.v[fv])) + (S.w[q.c + pl] - S.w[q.c]));
+}
+
+// u^{n+1} = u* - beta grad phi (top w face: the ghost -phi); p += phi
+__global__ void k3t_project(Tank3P P, int comp, const double *__restrict__ S, const double *__restrict__ beta,
+                            const double *__restrict__ phi, double *__restrict__ out, long long n)
+{
+    pdl_entry();
+    const long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (f >= n) return;
+    const int nx = P.nx, ny = P.ny, nz = P.nz;
+    const double ih = 1.0 / P.h;
+    double a = S[f];
+    if (comp == 0) {
+        const int i = (int)(f % (nx + 1));
+        const long long r = f / (nx + 1);
+        if (i > 0 && i < nx) a -= beta[f] * (phi[r * nx + i] - phi[r * nx + i - 1]) * ih;
+    } else if (comp == 1) {
+        const int i = (int)(f % nx);
+        const long long q = f / nx;
+        const int j = (int)(q % (ny + 1)), k = (int)(q / (ny + 1));
+        if (j > 0 && j < ny) {
+            const long long c = ((long long)k * ny + j) * nx + i;
+            a -= beta[f] * (phi[c] - phi[c - nx]) * ih;
+        }
+    } else {
+        const long long pl = (long long)nx * ny;
+        const int k = (int)(f / pl);
+        if (k > 0 && k < nz) a -= beta[f] * (phi[f] - phi[f - pl]) * ih;
+        if (k == nz) a += 2.0 * beta[f] * phi[f - pl] * ih;
+    }
+    out[f] = a;
+}
+
+__global__ void k3t_add(long long n, const double *__restrict__ a, double *__restrict__ b)
+{
+    pdl_entry();
+    const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c < n) b[c] += a[c];
+}
+
+constexpr int kRT = 256;  // threads of the reduction kernels
+
+__device__ double block_sum3(double v, double *sh)
+{
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = kRT / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    return sh[0];
+}
+
+// heave force, Eq. int_fh, over the faces of a box around the cylinder
+// [i0, i1) x [j0, j1) x [k0, k1) of cells (a block per (face kind, layer k))
+__global__ void __launch_bounds__(kRT) k3t_force(Tank3P P, const double *__restrict__ p, const double *__restrict__ mu,
+                                                 Vel3 V, double zc, int i0, int i1, int j0, int j1, int k0, int k1,
+                                                 double *__restrict__ part)
+{
+    pdl_entry();
+    __shared__ double sh[kRT];
+    const int kind = blockIdx.y, k = k0 + blockIdx.x;  // kind 0: z-faces below cell k; 1: x-faces; 2: y-faces
+    const double h = P.h, A = h * h;
+    const int nx = P.nx, ny = P.ny, nz = P.nz;
+    auto psi = [&](double x, double y, double z) {
+        const double r = sqrt((x - P.bxc) * (x - P.bxc) + (y - P.byc) * (y - P.byc));
+        return fmax(r - P.br, fabs(z - zc) - 0.5 * P.blen);
+    };
+    double acc = 0.0;
+    const int ni = i1 - i0, nj = j1 - j0;
+    for (int q = threadIdx.x; q < ni * nj; q += kRT) {
+        const int i = i0 + q % ni, j = j0 + q / ni;
+        if (kind == 0) {
+            if (k < 1 || k > nz - 1) continue;
+            const double x = (i + 0.5) * h, y = (j + 0.5) * h;
+            const double pl = psi(x, y, (k - 0.5) * h), pr = psi(x, y, (k + 0.5) * h);
+            if (!(pl * pr < 0.0)) continue;
+            const double nz_ = pl < 0.0 ? 1.0 : -1.0, wl = fabs(pl), wr = fabs(pr);
+            const long long c = ((long long)k * ny + j) * nx + i, cb = c - (long long)nx * ny;
+            const double pf = (p[cb] * wr + p[c] * wl) / (wl + wr);
+            const double muf = 0.5 * (mu[cb] + mu[c]);
+            const double dwdz = (wq(P, V.w, V.win, i, j, k + 1) - wq(P, V.w, V.win, i, j, k - 1)) / (2.0 * h);
+            acc += (-pf * nz_ + muf * 2.0 * dwdz * nz_) * A;
+        } else if (kind == 1) {
+            if (i < 1 || k > nz - 1) continue;
+            const double y = (j + 0.5) * h, z = (k + 0.5) * h;
+            const double pl = psi((i - 0.5) * h, y, z), pr = psi((i + 0.5) * h, y, z);
+            if (!(pl * pr < 0.0)) continue;
+            const double nx_ = pl < 0.0 ? 1.0 : -1.0;
+            const long long c = ((long long)k * ny + j) * nx + i;
+            const double muf = 0.5 * (mu[c - 1] + mu[c]);
+            const double dwdx = 0.5 * ((wq(P, V.w, V.win, i, j, k) - wq(P, V.w, V.win, i - 1, j, k)) +
+                                       (wq(P, V.w, V.win, i, j, k + 1) - wq(P, V.w, V.win, i - 1, j, k + 1))) / h;
+            const double dudz = (uq(P, V.u, i, j, k + 1) - uq(P, V.u, i, j, k - 1)) / (2.0 * h);
+            acc += muf * (dwdx + dudz) * nx_ * A;
+        } else {
+            if (j < 1 || k > nz - 1) continue;
+            const double x = (i + 0.5) * h, z = (k + 0.5) * h;
+            const double pl = psi(x, (j - 0.5) * h, z), pr = psi(x, (j + 0.5) * h, z);
+            if (!(pl * pr < 0.0)) continue;
+            const double ny_ = pl < 0.0 ? 1.0 : -1.0;
+            const long long c = ((long long)k * ny + j) * nx + i;
+            const double muf = 0.5 * (mu[c - nx] + mu[c]);
+            const double dwdy = 0.5 * ((wq(P, V.w, V.win, i, j, k) - wq(P, V.w, V.win, i, j - 1, k)) +
+                                       (wq(P, V.w, V.win, i, j, k + 1) - wq(P, V.w, V.win, i, j - 1, k + 1))) / h;
+            const double dvdz = (vq(P, V.v, i, j, k + 1) - vq(P, V.v, i, j, k - 1)) / (2.0 * h);
+            acc += muf * (dwdy + dvdz) * ny_ * A;
+        }
+    }
+    const double s = block_sum3(acc, sh);
+    if (threadIdx.x == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = s;
+}
+
+// sum of n partials in order (one block)
+__global__ void __launch_bounds__(kRT) k3t_sum(const double *__restrict__ part, int n, double *__restrict__ out)
+{
+    pdl_entry();
+    __shared__ double sh[kRT];
+    double a = 0.0;
+    for (int q = threadIdx.x; q < n; q += kRT) a += part[q];
+    const double s = block_sum3(a, sh);
+    if (threadIdx.x == 0) *out = s;
+}
+
+// ||h div u||^2 partials, one per block of cells
+__global__ void __launch_bounds__(kRT) k3t_div2(Tank3P P, Vel3 S, double *__restrict__ part)
+{
+    pdl_entry();
+    __shared__ double sh[kRT];
+    const long long n = (long long)P.nx * P.ny * P.nz;
+    double a = 0.0;
+    for (long long c = blockIdx.x * (long long)kRT + threadIdx.x; c < n; c += (long long)gridDim.x * kRT) {
+        const int i = (int)(c % P.nx);
+        const long long r = c / P.nx;
+        const int j = (int)(r % P.ny), k = (int)(r / P.ny);
+        const long long fu = r * (P.nx + 1) + i, fv = ((long long)k * (P.ny + 1) + j) * P.nx + i;
+        const double d = P.h * (((S.u[fu + 1] - S.u[fu]) + (S.v[fv + P.nx] - S.v[fv])) + (S.w[c + (long long)P.nx * P.ny] - S.w[c]));
+        a += d * d;
+    }
+    const double s = block_sum3(a, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// initial state: sigma = z - depth - eta(x) (eta per column given), u and w from
+// (x, z) tables broadcast along y, v = 0
+__global__ void __launch_bounds__(128) k3t_init(Tank3P P, const double *__restrict__ eta, const double *__restrict__ uxz,
+                                                const double *__restrict__ wxz, double *sig, double *u, double *w)
+{
+    pdl_entry();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    const int nx = P.nx, ny = P.ny;
+    if (i <= nx) u[((long long)k * ny + j) * (nx + 1) + i] = uxz[(long long)k * (nx + 1) + i];
+    if (i < nx) {
+        sig[((long long)k * ny + j) * nx + i] = (k + 0.5) * P.h - P.depth - eta[i];
+        w[((long long)(k + 1) * ny + j) * nx + i] = wxz[(long long)(k + 1) * nx + i];
+        if (k == 0) w[(long long)j * nx + i] = 0.0;
+    }
+}
+
+// p^{-1/2}: the discrete hydrostatic pressure of rho^flow from the top face down
+__global__ void k3t_hydrostatic(Tank3P P, const double *__restrict__ rf, double g, double *__restrict__ p)
+{
+    pdl_entry();
+    const long long col = blockIdx.x * (long long)blockDim.x + threadIdx.x, pl = (long long)P.nx * P.ny;
+    if (col >= pl) return;
+    double pp = 0.5 * rf[(P.nz - 1) * pl + col] * g * P.h;
+    p[(P.nz - 1) * pl + col] = pp;
+    for (int k = P.nz - 2; k >= 0; --k) {
+        pp += 0.5 * (rf[k * pl + col] + rf[(k + 1) * pl + col]) * g * P.h;
+        p[k * pl + col] = pp;
+    }
+}
+
 dim3 grid3(const Tank3P &P) { return dim3((P.nx + 127) / 128, P.ny, P.nz); }
 
 int tank3_check(const wec_tank3 *T)
 {
     if (!T) return fail(WEC_ERR_INVALID, "tank3 is NULL");
+    return WEC_OK;
+}
+
+// host copies of the wave components: amp, omega, k, phase (4 x ncomp)
+struct Waves3 {
+    int n;
+    const double *amp, *om, *k, *ph;
+};
+
+double eta_host(const Waves3 &W, double x, double t)
+{
+    double e = 0.0;
+    for (int c = 0; c < W.n; ++c) e += W.amp[c] * std::cos(W.k[c] * x - W.om[c] * t + W.ph[c]);
+    return e;
+}
+
+double heav_host(double phi, double eps)
+{
+    if (phi < -eps) return 0.0;
+    if (phi > eps) return 1.0;
+    return 0.5 * (1.0 + phi / eps + std::sin(kPi3 * phi / eps) / kPi3);
+}
+
+// Airy (u, w) at (x, z, t): linear potential with Wheeler stretching up to the
+// surface, blended to zero in the air over a half-width h
+void airy_host(const Waves3 &W, double depth, double h, double x, double z, double t, double *uo, double *wo)
+{
+    const double e = eta_host(W, x, t);
+    const double zs = z < depth + e ? z : depth + e;
+    const double zp = depth * zs / (depth + e);
+    const double blend = 1.0 - heav_host(z - depth - e, h);
+    double su = 0.0, sw = 0.0;
+    for (int c = 0; c < W.n; ++c) {
+        const double k = W.k[c], om = W.om[c], ph = k * x - om * t + W.ph[c], sk = std::sinh(k * depth);
+        su += W.amp[c] * om * std::cosh(k * zp) / sk * std::cos(ph);
+        sw += W.amp[c] * om * std::sinh(k * zp) / sk * std::sin(ph);
+    }
+    *uo = blend * su;
+    *wo = blend * sw;
+}
+
+// nit Sussman pseudo-steps on the field s (scratch T->s0, T->s1)
+int reinit_buf(wec_tank3 *T, double *s, int nit, double t)
+{
+    const double dtau = 0.3 * T->P.h;
+    WEC_CK(cudaMemcpyAsync(T->s0, s, T->nc * 8, cudaMemcpyDeviceToDevice, T->st));
+    for (int it = 0; it < nit; ++it) {
+        {
+            WEC_PROF("tank3_reinit", 0, 24.0 * T->nc, T->st);
+            launch_k(k3t_reinit_stage, grid3(T->P), 128, 0, T->st, T->P, (const double *)s, (const double *)T->s0,
+                     T->s1, t, dtau, 1);
+        }
+        WEC_PROF("tank3_reinit", 0, 32.0 * T->nc, T->st);
+        launch_k(k3t_reinit_stage, grid3(T->P), 128, 0, T->st, T->P, (const double *)T->s1, (const double *)T->s0,
+                 s, t, dtau, 2);
+    }
+    WEC_CK(cudaGetLastError());
     return WEC_OK;
 }
 
@@ -262,7 +842,7 @@ using namespace wec;
 extern "C" {
 
 int wec_tank3_create(const wec_grid3 *grid, const wec_fluids *fl, const wec_waves *wv, const wec_cylinder *body,
-                     void *cuda_stream, wec_tank3 **out)
+                     const wec_solver_opts *opts, void *cuda_stream, wec_tank3 **out)
 {
     if (!out) return fail(WEC_ERR_INVALID, "out is NULL");
     *out = nullptr;
@@ -277,8 +857,18 @@ int wec_tank3_create(const wec_grid3 *grid, const wec_fluids *fl, const wec_wave
         return fail(WEC_ERR_INVALID, "tank3: densities must be positive, viscosities non-negative");
     if (wv->ncomp < 0 || (wv->ncomp > 0 && (!wv->amp || !wv->omega || !wv->phase)))
         return fail(WEC_ERR_INVALID, "tank3: wave arrays are NULL");
-    if (body->present && (!(body->radius > 0.0) || !(body->length > 0.0) || !(body->mass > 0.0)))
-        return fail(WEC_ERR_INVALID, "tank3: the cylinder needs radius, length and mass > 0");
+    if (body->present && (!(body->radius > 0.0) || !(body->length > 0.0) || !(body->mass > 0.0) ||
+                          !(body->kappa_p > 0.0) || !(body->added_mass >= 0.0)))
+        return fail(WEC_ERR_INVALID, "tank3: the cylinder needs radius, length, mass, kappa_p > 0, added_mass >= 0");
+    if (opts) {
+        if (opts->precision != WEC_PREC_FP64 && opts->precision != WEC_PREC_MIXED_MG)
+            return fail(WEC_ERR_INVALID, "tank3: precision must be WEC_PREC_FP64 or WEC_PREC_MIXED_MG (the 3D stencils "
+                                         "are FP64)");
+        if (!(opts->rtol > 0.0) || opts->max_iters < 1 || opts->restart < 1 || opts->restart > kMaxRestart ||
+            opts->n_reinit < 0 || opts->n_jacobi < 1 || opts->mg_pre < 1 || opts->mg_pre > 4 || opts->mg_post < 0 ||
+            opts->mg_post > 4)
+            return fail(WEC_ERR_INVALID, "tank3: invalid solver options");
+    }
     if (int e = [] {
             int n = 0;
             return (cudaGetDeviceCount(&n) != cudaSuccess || n == 0)
@@ -297,6 +887,16 @@ int wec_tank3_create(const wec_grid3 *grid, const wec_fluids *fl, const wec_wave
     if (P.has_body) {
         P.bxc = body->xc; P.byc = body->yc; P.br = body->radius; P.blen = body->length;
         P.rho_s = body->mass / (kPi3 * body->radius * body->radius * body->length);
+    }
+    T->g = fl->g;
+    T->lz = grid->lz;
+    T->probe_x = wv->probe_x;
+    if (P.has_body) {
+        T->kappa_p = body->kappa_p;
+        T->mass = body->mass;
+        T->added_mass = body->added_mass;
+        T->pto_c = body->pto_damping;
+        T->zc = T->zc0 = body->zc;
     }
     P.ncomp = wv->ncomp;
     // host tables: wave components (k from the dispersion relation) and the
@@ -345,6 +945,89 @@ int wec_tank3_create(const wec_grid3 *grid, const wec_fluids *fl, const wec_wave
     P.kw = T->consts + 2 * P.ncomp;
     P.phase = T->consts + 3 * P.ncomp;
     P.damp = T->consts + 4 * P.ncomp;
+    if (opts) {  // the step: its buffers, its solver, the initial state
+        T->opts = *opts;
+        T->stepping = true;
+        size_t nf[3] = {T->nu, T->nv, T->nw};
+        for (double **q : {&T->p, &T->phi, &T->rhs, &T->mu1, &T->rf1, &T->chi1})
+            if (e == cudaSuccess) e = cudaMalloc(q, T->nc * 8);
+        for (int c = 0; c < 3; ++c)
+            for (double **q : {&T->D[c], &T->R[c], &T->A[c], &T->B[c]})
+                if (e == cudaSuccess) e = cudaMalloc(q, nf[c] * 8);
+        if (e == cudaSuccess) e = cudaMalloc(&T->bc, (size_t)(3 * nz + 2 + nz + nz + 1) * 8);
+        if (e == cudaSuccess) e = cudaMalloc(&T->tabs, (size_t)(nx + 1) * 8);
+        if (e == cudaSuccess) e = cudaMalloc(&T->part, (size_t)(3 * nz + 1024 + 8) * 8);
+        if (e != cudaSuccess) {
+            wec_tank3_destroy(T);
+            return cuda_fail(e, "tank3 step allocation");
+        }
+        T->solver = new (std::nothrow) wec_poisson();
+        if (!T->solver) {
+            wec_tank3_destroy(T);
+            return fail(WEC_ERR_NOMEM, "host allocation failed");
+        }
+        const int sprec = opts->precision == WEC_PREC_FP64 ? WEC_PREC_FP64 : WEC_PREC_MIXED;
+        if (int rc = poisson_init(T->solver, nx, ny, sprec, opts->restart, opts->mg_pre, opts->mg_post, T->st, nz)) {
+            std::string msg = wec_last_error();
+            wec_tank3_destroy(T);
+            return fail(rc, msg);
+        }
+        // damping weight at the u-faces (x = i h)
+        std::vector<double> du(nx + 1);
+        for (int i = 0; i <= nx; ++i) {
+            const double x = i * h;
+            double a = 0.0;
+            if (wv->damp_len > 0.0 && x > wv->damp_x0) {
+                double xi = (x - wv->damp_x0) / wv->damp_len;
+                if (xi > 1.0) xi = 1.0;
+                a = (std::exp(std::pow(xi, 3.5)) - 1.0) / (std::exp(1.0) - 1.0);
+            }
+            du[i] = a;
+        }
+        // initial state: sigma = z - depth - eta(x, 0), Airy u and w (v = 0), p the
+        // discrete hydrostatic pressure of rho^flow from the top face (p = 0 there)
+        const Waves3 W{P.ncomp, hc.data(), hc.data() + P.ncomp, hc.data() + 2 * P.ncomp, hc.data() + 3 * P.ncomp};
+        std::vector<double> eta(nx), uxz((size_t)nz * (nx + 1)), wxz((size_t)(nz + 1) * nx, 0.0);
+        for (int i = 0; i < nx; ++i) eta[i] = eta_host(W, (i + 0.5) * h, 0.0);
+        for (int k = 0; k < nz; ++k)
+            for (int i = 0; i <= nx; ++i) {
+                double uu, ww;
+                airy_host(W, grid->depth, h, i * h, (k + 0.5) * h, 0.0, &uu, &ww);
+                uxz[(size_t)k * (nx + 1) + i] = i == nx ? 0.0 : uu;
+            }
+        for (int k = 1; k <= nz; ++k)
+            for (int i = 0; i < nx; ++i) {
+                double uu, ww;
+                airy_host(W, grid->depth, h, (i + 0.5) * h, k * h, 0.0, &uu, &ww);
+                wxz[(size_t)k * nx + i] = ww;
+            }
+        double *dtab = nullptr;
+        e = cudaMalloc(&dtab, (eta.size() + uxz.size() + wxz.size()) * 8);
+        if (e == cudaSuccess) e = cudaMemcpy(dtab, eta.data(), eta.size() * 8, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(dtab + eta.size(), uxz.data(), uxz.size() * 8, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(dtab + eta.size() + uxz.size(), wxz.data(), wxz.size() * 8, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(T->tabs, du.data(), du.size() * 8, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(dtab);
+            wec_tank3_destroy(T);
+            return cuda_fail(e, "tank3 initial state");
+        }
+        launch_k(k3t_init, dim3((nx + 128) / 128, ny, nz), 128, 0, T->st, T->P, (const double *)dtab,
+                 (const double *)(dtab + eta.size()), (const double *)(dtab + eta.size() + uxz.size()), T->sig, T->u,
+                 T->w);
+        launch_k(k3t_materials, grid3(T->P), 128, 0, T->st, T->P, (const double *)T->sig, T->zc, T->rho, T->mu,
+                 T->rhof, T->chi);
+        launch_k(k3t_hydrostatic, nblk((long long)nx * ny, 128), 128, 0, T->st, T->P, (const double *)T->rhof, T->g,
+                 T->p);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(T->st);
+        cudaFree(dtab);
+        if (e != cudaSuccess) {
+            wec_tank3_destroy(T);
+            return cuda_fail(e, "tank3 initial state");
+        }
+    }
     *out = T;
     return WEC_OK;
 }
@@ -353,8 +1036,15 @@ void wec_tank3_destroy(wec_tank3 *T)
 {
     if (!T) return;
     cudaStreamSynchronize(T->st);
-    for (double *p : {T->sig, T->tmp, T->s0, T->s1, T->rho, T->mu, T->rhof, T->chi, T->u, T->v, T->w, T->consts})
+    for (double *p : {T->sig, T->tmp, T->s0, T->s1, T->rho, T->mu, T->rhof, T->chi, T->u, T->v, T->w, T->consts,
+                      T->p, T->phi, T->rhs, T->mu1, T->rf1, T->chi1, T->bc, T->tabs, T->part})
         cudaFree(p);
+    for (int c = 0; c < 3; ++c)
+        for (double *p : {T->D[c], T->R[c], T->A[c], T->B[c]}) cudaFree(p);
+    if (T->solver) {
+        poisson_free(T->solver);
+        delete T->solver;
+    }
     delete T;
 }
 
@@ -369,6 +1059,7 @@ static double *field3(const wec_tank3 *T, int f, size_t *n)
     case WEC_F3_MU: *n = T->nc; return T->mu;
     case WEC_F3_RHO_FLOW: *n = T->nc; return T->rhof;
     case WEC_F3_CHI: *n = T->nc; return T->chi;
+    case WEC_F3_P: *n = T->p ? T->nc : 0; return T->p;
     default: *n = 0; return nullptr;
     }
 }
@@ -389,7 +1080,8 @@ int wec_tank3_set_field(wec_tank3 *T, int f, const double *host, size_t n)
     if (int e = tank3_check(T)) return e;
     size_t m = 0;
     double *p = field3(T, f, &m);
-    if (!p || !host || n != m || f > WEC_F3_W) return fail(WEC_ERR_INVALID, "tank3_set_field: not a state field or wrong size");
+    if (!p || !host || n != m || (f > WEC_F3_W && f != WEC_F3_P))
+        return fail(WEC_ERR_INVALID, "tank3_set_field: not a state field or wrong size");
     WEC_CK(cudaStreamSynchronize(T->st));
     WEC_CK(cudaMemcpy(p, host, m * 8, cudaMemcpyHostToDevice));
     return WEC_OK;
@@ -427,21 +1119,183 @@ int wec_tank3_reinit(wec_tank3 *T, int nit, double t)
 {
     if (int e = tank3_check(T)) return e;
     if (nit < 0) return fail(WEC_ERR_INVALID, "tank3_reinit: nit must be >= 0");
-    const double dtau = 0.3 * T->P.h;
-    WEC_CK(cudaMemcpyAsync(T->s0, T->sig, T->nc * 8, cudaMemcpyDeviceToDevice, T->st));
-    for (int it = 0; it < nit; ++it) {
-        {
-            WEC_PROF("tank3_reinit", 0, 24.0 * T->nc, T->st);
-            launch_k(k3t_reinit_stage, grid3(T->P), 128, 0, T->st, T->P, (const double *)T->sig,
-                     (const double *)T->s0, T->s1, t, dtau, 1);
-        }
-        WEC_PROF("tank3_reinit", 0, 32.0 * T->nc, T->st);
-        launch_k(k3t_reinit_stage, grid3(T->P), 128, 0, T->st, T->P, (const double *)T->s1, (const double *)T->s0,
-                 T->sig, t, dtau, 2);
-    }
-    WEC_CK(cudaGetLastError());
+    if (int e = reinit_buf(T, T->sig, nit, t)) return e;
     WEC_CK(cudaStreamSynchronize(T->st));
     return WEC_OK;
+}
+
+int wec_tank3_get_state(const wec_tank3 *T, double *out5)
+{
+    if (int e = tank3_check(T)) return e;
+    if (!out5) return fail(WEC_ERR_INVALID, "NULL argument");
+    out5[0] = T->t;
+    out5[1] = T->zc;
+    out5[2] = T->zdot;
+    out5[3] = T->zc0;
+    out5[4] = T->zdot_prev;
+    return WEC_OK;
+}
+
+int wec_tank3_step(wec_tank3 *T, double dt, double pto_force, wec_step_result *out)
+{
+    if (int e = tank3_check(T)) return e;
+    if (!T->stepping) return fail(WEC_ERR_INVALID, "tank3_step: the tank was created without solver options");
+    if (!(dt > 0.0)) return fail(WEC_ERR_INVALID, "tank3_step: dt must be > 0");
+    const Tank3P &P = T->P;
+    cudaStream_t st = T->st;
+    const int nx = P.nx, ny = P.ny, nz = P.nz;
+    const double h = P.h, t0 = T->t, t1 = T->t + dt;
+    // boundary data of this step (host): u_in(t1) at the cell layers, w_in(t0)
+    // and w_in(t1) at the face heights, vorticity damping at cell / face heights
+    std::vector<double> hb((size_t)3 * nz + 2 + nz + nz + 1);
+    std::vector<double> hw(4 * (size_t)P.ncomp);
+    WEC_CK(cudaMemcpyAsync(hw.data(), T->consts, hw.size() * 8, cudaMemcpyDeviceToHost, st));
+    WEC_CK(cudaStreamSynchronize(st));
+    const Waves3 W{P.ncomp, hw.data(), hw.data() + P.ncomp, hw.data() + 2 * P.ncomp, hw.data() + 3 * P.ncomp};
+    double *uin1 = hb.data(), *win0 = uin1 + nz, *win1 = win0 + nz + 1, *vc = win1 + nz + 1, *vf = vc + nz;
+    for (int k = 0; k < nz; ++k) {
+        double uu, ww;
+        airy_host(W, P.depth, h, 0.0, (k + 0.5) * h, t1, &uu, &ww);
+        uin1[k] = uu;
+    }
+    for (int k = 0; k <= nz; ++k) {
+        double uu, ww;
+        airy_host(W, P.depth, h, 0.0, k * h, t0, &uu, &ww);
+        win0[k] = ww;
+        airy_host(W, P.depth, h, 0.0, k * h, t1, &uu, &ww);
+        win1[k] = ww;
+    }
+    auto vort = [&](double z) {
+        const double wd = 4.0 * h;
+        if (z < T->lz - wd) return 0.0;
+        const double zt = (z - T->lz) / wd;
+        return P.rho_a * (std::cos(kPi3 * zt) + 1.0) / (4.0 * dt);
+    };
+    for (int k = 0; k < nz; ++k) vc[k] = vort((k + 0.5) * h);
+    for (int k = 0; k <= nz; ++k) vf[k] = vort(k * h);
+    WEC_CK(cudaMemcpyAsync(T->bc, hb.data(), hb.size() * 8, cudaMemcpyHostToDevice, st));
+    const double *d_uin1 = T->bc, *d_win0 = d_uin1 + nz, *d_win1 = d_win0 + nz + 1, *d_vc = d_win1 + nz + 1,
+                 *d_vf = d_vc + nz;
+
+    // (1) materials at n and the heave force from p^{n-1/2}, u^n (Eq. int_fh)
+    launch_k(k3t_materials, grid3(P), 128, 0, st, P, (const double *)T->sig, T->zc, T->rho, T->mu, T->rhof, T->chi);
+    double F = 0.0;
+    const int kcb = (int)(T->zc / h), mkb = (int)std::ceil(0.5 * P.blen / h) + 3;
+    if (P.has_body && std::min(nz, kcb + mkb + 1) > std::max(0, kcb - mkb)) {
+        const int mi = (int)std::ceil((P.br) / h) + 3, mk = (int)std::ceil(0.5 * P.blen / h) + 3;
+        const int ic = (int)(P.bxc / h), jc = (int)(P.byc / h), kc = (int)(T->zc / h);
+        const int i0 = std::max(0, ic - mi), i1 = std::min(nx, ic + mi + 1), j0 = std::max(0, jc - mi),
+                  j1 = std::min(ny, jc + mi + 1), k0 = std::max(0, kc - mk), k1 = std::min(nz, kc + mk + 1);
+        const Vel3 Vn{T->u, T->v, T->w, d_win0};
+        WEC_PROF("tank3_force", 0, 0.0, st);
+        launch_k(k3t_force, dim3(k1 - k0, 3), kRT, 0, st, P, (const double *)T->p, (const double *)T->mu, Vn, T->zc,
+                 i0, i1, j0, j1, k0, k1, T->part);
+        launch_k(k3t_sum, 1, kRT, 0, st, (const double *)T->part, 3 * (k1 - k0), T->part + 3 * nz + 1024);
+        WEC_CK(cudaMemcpyAsync(&F, T->part + 3 * nz + 1024, 8, cudaMemcpyDeviceToHost, st));
+        WEC_CK(cudaStreamSynchronize(st));
+    }
+    // (2) heave (the stabilised update of the 2D reading)
+    const double fpto = pto_force - T->pto_c * T->zdot;
+    double zd1 = T->zdot, zc1 = T->zc;
+    if (P.has_body) {
+        const double m = T->mass, ma = T->added_mass;
+        zd1 = T->zdot + (dt * (F - m * T->g + fpto) + ma * (T->zdot - T->zdot_prev)) / (m + ma);
+        zc1 = T->zc + 0.5 * dt * (T->zdot + zd1);
+    }
+    // (3) sigma: advection + damping zone, reinitialisation (ghosts at t0, t1)
+    {
+        WEC_PROF("tank3_advect", 0, 8.0 * (2.0 * T->nc + T->nu + T->nv + T->nw), st);
+        launch_k(k3t_advect, grid3(P), 128, 0, st, P, (const double *)T->sig, (const double *)T->u,
+                 (const double *)T->v, (const double *)T->w, dt, t0, T->tmp);
+    }
+    if (int e = reinit_buf(T, T->tmp, T->opts.n_reinit, t1)) return e;
+    // (4) materials at n+1 (rho^{n+1} itself is not used: s1 is scratch)
+    launch_k(k3t_materials, grid3(P), 128, 0, st, P, (const double *)T->tmp, zc1, T->s1, T->mu1, T->rf1, T->chi1);
+    // (5) transport and the momentum system
+    MomIn M{T->rho, T->mu, T->chi1, T->rf1, T->p, Vel3{T->u, T->v, T->w, d_win0}, T->tabs, d_vc, d_vf, dt, zd1, T->g,
+            1.0 / T->kappa_p};
+    const dim3 gu((nx - 1 + 127) / 128, ny, nz), gv((nx + 127) / 128, ny - 1 > 0 ? ny - 1 : 1, nz),
+        gw((nx + 127) / 128, ny, nz);
+    const dim3 gc[3] = {gu, gv, gw};
+    for (int c = 0; c < 3; ++c) {
+        if (c == 1 && ny < 2) continue;
+        WEC_PROF("tank3_momentum", c, 0.0, st);
+        launch_k(k3t_momentum, gc[c], 128, 0, st, P, M, c, T->D[c], T->R[c]);
+    }
+    // (6) Crank-Nicolson Jacobi sweeps from u^n with the Dirichlet faces at n+1
+    const size_t nf[3] = {T->nu, T->nv, T->nw};
+    double *src[3] = {T->u, T->v, T->w};
+    for (int c = 0; c < 3; ++c) WEC_CK(cudaMemcpyAsync(T->A[c], src[c], nf[c] * 8, cudaMemcpyDeviceToDevice, st));
+    {
+        const long long nd = std::max({(long long)ny * nz, (long long)nx * nz, (long long)nx * ny});
+        launch_k(k3t_dirichlet, nblk(nd, 256), 256, 0, st, P, d_uin1, T->A[0], T->A[1], T->A[2]);
+    }
+    for (int c = 0; c < 3; ++c) WEC_CK(cudaMemcpyAsync(T->B[c], T->A[c], nf[c] * 8, cudaMemcpyDeviceToDevice, st));
+    for (int it = 0; it < T->opts.n_jacobi; ++it) {
+        const Vel3 Va{T->A[0], T->A[1], T->A[2], d_win1};
+        for (int c = 0; c < 3; ++c) {
+            if (c == 1 && ny < 2) continue;
+            WEC_PROF("tank3_jacobi", c, 0.0, st);
+            launch_k(k3t_jacobi, gc[c], 128, 0, st, P, (const double *)T->mu1, Va, c, (const double *)T->D[c],
+                     (const double *)T->R[c], T->B[c]);
+        }
+        for (int c = 0; c < 3; ++c) std::swap(T->A[c], T->B[c]);
+    }
+    // (7) pressure increment: beta = 1 / D, b = -h div u*, phi from zero
+    wec_poisson *S = T->solver;
+    double *beta[3] = {S->L64[0].bu, S->L64[0].bv, S->L64[0].bw};
+    for (int c = 0; c < 3; ++c)
+        launch_k(k3t_beta, nblk((long long)nf[c], 256), 256, 0, st, P, c, (const double *)T->D[c], beta[c],
+                 (long long)nf[c]);
+    if (int e = poisson_build(S, st)) return e;
+    launch_k(k3t_rhs, grid3(P), 128, 0, st, P, Vel3{T->A[0], T->A[1], T->A[2], d_win1}, T->rhs);
+    WEC_CK(cudaMemsetAsync(T->phi, 0, T->nc * 8, st));
+    WEC_CK(cudaGetLastError());
+    int iters = 0;
+    double relres = 0.0;
+    const int rc = poisson_solve(S, T->rhs, T->phi, T->opts.rtol, T->opts.max_iters, &iters, &relres);
+    if (rc != WEC_OK && rc != WEC_ERR_NOT_CONVERGED) return rc;
+    // (8) projection and p += phi; sigma^{n+1}
+    for (int c = 0; c < 3; ++c)
+        launch_k(k3t_project, nblk((long long)nf[c], 256), 256, 0, st, P, c, (const double *)T->A[c],
+                 (const double *)beta[c], (const double *)T->phi, src[c], (long long)nf[c]);
+    launch_k(k3t_add, nblk((long long)T->nc, 256), 256, 0, st, (long long)T->nc, (const double *)T->phi, T->p);
+    std::swap(T->sig, T->tmp);
+    // diagnostics: ||h div u||, eta at the probe column (x = probe_x, middle y)
+    const int G = 1024;
+    launch_k(k3t_div2, G, kRT, 0, st, P, Vel3{T->u, T->v, T->w, d_win1}, T->part);
+    launch_k(k3t_sum, 1, kRT, 0, st, (const double *)T->part, G, T->part + 3 * nz + 1024 + 1);
+    double d2 = 0.0;
+    WEC_CK(cudaMemcpyAsync(&d2, T->part + 3 * nz + 1024 + 1, 8, cudaMemcpyDeviceToHost, st));
+    const int ip = std::min(std::max((int)std::floor(T->probe_x / h), 0), nx - 1), jp = ny / 2;
+    std::vector<double> col(nz);
+    WEC_CK(cudaMemcpy2DAsync(col.data(), 8, T->sig + (size_t)jp * nx + ip, (size_t)nx * ny * 8, 8, nz,
+                             cudaMemcpyDeviceToHost, st));
+    WEC_CK(cudaGetLastError());
+    WEC_CK(cudaStreamSynchronize(st));
+    double eta = std::nan("");
+    for (int k = 0; k + 1 < nz; ++k)
+        if (col[k] < 0.0 && col[k + 1] >= 0.0) {
+            eta = (k + 0.5) * h + h * col[k] / (col[k] - col[k + 1]) - P.depth;
+            break;
+        }
+    T->t = t1;
+    T->zc = zc1;
+    T->zdot_prev = T->zdot;
+    T->zdot = zd1;
+    if (out) {
+        out->t = T->t;
+        out->z = T->zc - T->zc0;
+        out->zdot = T->zdot;
+        out->f_hydro = F;
+        out->f_pto = fpto;
+        out->eta_probe = eta;
+        out->residual = relres;
+        out->div_norm = std::sqrt(d2);
+        out->iters = iters;
+        out->status = rc;
+    }
+    return rc;
 }
 
 }  // extern "C"

@@ -42,10 +42,11 @@ class Grid3(C.Structure):
 
 
 class Cylinder(C.Structure):
-    _fields_ = [("present", C.c_int)] + [(k, C.c_double) for k in ("xc", "yc", "radius", "length", "mass")]
+    _fields_ = [("present", C.c_int)] + [(k, C.c_double) for k in ("xc", "yc", "radius", "length", "mass", "zc",
+                                                                   "kappa_p", "added_mass", "pto_damping")]
 
 
-F3_SIGMA, F3_U, F3_V, F3_W, F3_RHO, F3_MU, F3_RHO_FLOW, F3_CHI = range(8)
+F3_SIGMA, F3_U, F3_V, F3_W, F3_RHO, F3_MU, F3_RHO_FLOW, F3_CHI, F3_P = range(9)
 
 
 class Region(C.Structure):
@@ -133,8 +134,10 @@ def load():
     L.wec_poisson_vcycle.argtypes = [vp, vp, vp]
     L.wec_poisson_solve.argtypes = [vp, vp, vp, C.c_double, C.c_int, C.POINTER(C.c_int), _dp]
     L.wec_poisson_create3.argtypes = [C.c_int, C.c_int, C.c_int, C.POINTER(SolverOpts), vp, C.POINTER(vp)]
-    L.wec_tank3_create.argtypes = [C.POINTER(Grid3), C.POINTER(Fluids), C.POINTER(Waves), C.POINTER(Cylinder), vp,
-                                   C.POINTER(vp)]
+    L.wec_tank3_create.argtypes = [C.POINTER(Grid3), C.POINTER(Fluids), C.POINTER(Waves), C.POINTER(Cylinder),
+                                   C.POINTER(SolverOpts), vp, C.POINTER(vp)]
+    L.wec_tank3_step.argtypes = [vp, C.c_double, C.c_double, C.POINTER(StepResult)]
+    L.wec_tank3_get_state.argtypes = [vp, _dp]
     L.wec_tank3_destroy.argtypes = [vp]
     L.wec_tank3_destroy.restype = None
     L.wec_tank3_get_field.argtypes = [vp, C.c_int, _dp, C.c_size_t]
@@ -640,7 +643,7 @@ class Tank3:
     3D workload dict (synth.tank3d); fields are numpy FP64 arrays, cells (nz, ny,
     nx), u (nz, ny, nx+1), v (nz, ny+1, nx), w (nz+1, ny, nx)."""
 
-    def __init__(self, cfg, stream=None):
+    def __init__(self, cfg, precision=None, stream=None, step=True):
         L = load()
         self.cfg = cfg
         nx, ny, nz = cfg["nx"], cfg["ny"], cfg["nz"]
@@ -651,13 +654,16 @@ class Tank3:
         w = Waves(len(amp), _ptr(self._w[0]), _ptr(self._w[1]), _ptr(self._w[2]), cfg["damp_x0"], cfg["damp_len"],
                   cfg["probe_x"])
         b = cfg.get("body")
-        body = Cylinder(1, b["xc"], b["yc"], b["radius"], b["length"], b["mass"]) if b else Cylinder(0)
+        body = Cylinder(1, b["xc"], b["yc"], b["radius"], b["length"], b["mass"], b["zc"], b["kappa_p"],
+                        b["added_mass"], b.get("pto_damping", 0.0)) if b else Cylinder(0)
+        o = solver_opts(cfg["solver"], precision) if step else None
         h = C.c_void_p()
-        _check(L.wec_tank3_create(C.byref(g), C.byref(f), C.byref(w), C.byref(body), _stream(stream), C.byref(h)))
+        _check(L.wec_tank3_create(C.byref(g), C.byref(f), C.byref(w), C.byref(body), C.byref(o) if o else None,
+                                  _stream(stream), C.byref(h)))
         self.h = h
         self.shapes = {F3_SIGMA: (nz, ny, nx), F3_U: (nz, ny, nx + 1), F3_V: (nz, ny + 1, nx),
                        F3_W: (nz + 1, ny, nx)}
-        for fid in (F3_RHO, F3_MU, F3_RHO_FLOW, F3_CHI):
+        for fid in (F3_RHO, F3_MU, F3_RHO_FLOW, F3_CHI, F3_P):
             self.shapes[fid] = (nz, ny, nx)
 
     def close(self):
@@ -688,3 +694,15 @@ class Tank3:
 
     def reinit(self, nit, t):
         _check(load().wec_tank3_reinit(self.h, nit, t))
+
+    def step(self, dt, pto=0.0):
+        r = StepResult()
+        code = _check(load().wec_tank3_step(self.h, dt, pto, C.byref(r)), ok=(WEC_OK, WEC_ERR_NOT_CONVERGED))
+        d = r.as_dict()
+        d["status"] = code
+        return d
+
+    def state(self):
+        a = np.zeros(5)
+        _check(load().wec_tank3_get_state(self.h, _ptr(a)))
+        return dict(t=a[0], zc=a[1], zdot=a[2], zc0=a[3], zdot_prev=a[4])

@@ -1,0 +1,129 @@
+"""The 3D tank step on the GPU (wec_tank3_step) against the 3D step oracle:
+the initial state, every field after each step (FP64, 1e-10 relative per step),
+the heave after 200 steps (1e-6 relative), the FP32-V-cycle path's error, and
+the 512 x 256 x 256 tank by its properties (solve residual, divergence, finite
+heave)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import tank3d as T3  # noqa: E402
+from paper_2206_07732_gb300 import build as B  # noqa: E402
+from paper_2206_07732_gb300 import synth  # noqa: E402
+from paper_2206_07732_gb300 import wec  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    B.build()
+    wec.load()
+
+
+FIELDS = ((wec.F3_SIGMA, T3.F_SIGMA, "sigma"), (wec.F3_U, T3.F_U, "u"), (wec.F3_V, T3.F_V, "v"),
+          (wec.F3_W, T3.F_W, "w"), (wec.F3_P, T3.F_P, "p"))
+
+
+def rel(a, b, floor=1e-300):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), floor))
+
+
+def _cfg(nx, ny, nz, seed=1, rtol=1e-12, **kw):
+    c = synth.tank3d(seed=seed, nx=nx, ny=ny, nz=nz, rtol=rtol, **kw)
+    return c
+
+
+@pytest.mark.parametrize("shape", [(32, 8, 16), (40, 12, 20)])
+def test_initial_state_matches_oracle(shape):
+    c = _cfg(*shape)
+    t, o = wec.Tank3(c), T3.OracleTank3(c)
+    for fg, fo, name in FIELDS:
+        assert rel(t.get(fg), o.get(fo), 1e-12) < 1e-12, name
+    t.close()
+
+
+@pytest.mark.parametrize("shape,body", [((32, 8, 16), True), ((40, 12, 20), True), ((24, 8, 16), False)])
+def test_steps_match_oracle(shape, body):
+    c = _cfg(*shape)
+    if not body:
+        c["body"] = None
+    t, o = wec.Tank3(c), T3.OracleTank3(c)
+    for s in range(4):
+        r, ro = t.step(c["dt"]), o.step(c["dt"])
+        assert r["status"] == 0 and ro["status"] == 0
+        # v is identically zero in the oracle when nothing breaks the y-symmetry:
+        # its error is measured against the velocity scale max|u|
+        vs = np.max(np.abs(o.get(T3.F_U)))
+        errs = {name: rel(t.get(fg), o.get(fo), vs if name == "v" else 1e-12) for fg, fo, name in FIELDS}
+        print(f"{shape} step {s}: {errs} F {r['f_hydro']:.6f} / {ro['f_hydro']:.6f} its {r['iters']}/{ro['iters']}")
+        for name, e in errs.items():
+            assert e < 1e-10, (s, name, e)
+        if body:
+            assert r["f_hydro"] == pytest.approx(ro["f_hydro"], rel=1e-10)
+            assert r["zdot"] == pytest.approx(ro["zdot"], rel=1e-10, abs=1e-14)
+        assert abs(r["iters"] - ro["iters"]) <= 1
+    t.close()
+
+
+def test_heave_after_200_steps():
+    c = _cfg(32, 8, 16, seed=3, rtol=1e-10)
+    t, o = wec.Tank3(c), T3.OracleTank3(c)
+    for _ in range(200):
+        r, ro = t.step(c["dt"]), o.step(c["dt"])
+    print(f"200 steps: z {r['z']:.9e} / {ro['z']:.9e}, zdot {r['zdot']:.9e} / {ro['zdot']:.9e}")
+    assert r["z"] == pytest.approx(ro["z"], rel=1e-6)
+    assert r["zdot"] == pytest.approx(ro["zdot"], rel=1e-6)
+    t.close()
+
+
+def test_fp32_vcycle_path_error_against_the_oracle():
+    # FP32 V-cycles inside the FP64 FGMRES: every solve reaches the same FP64
+    # residual; the fields differ from the oracle by what rtol allows
+    c = _cfg(32, 8, 16, seed=4, rtol=1e-8)
+    t, o = wec.Tank3(c, precision=wec.PREC_MIXED_MG), T3.OracleTank3(c)
+    for _ in range(10):
+        r, ro = t.step(c["dt"]), o.step(c["dt"])
+        assert r["status"] == 0 and r["residual"] <= 1e-8
+    errs = {name: rel(t.get(fg), o.get(fo), 1e-12) for fg, fo, name in FIELDS}
+    print(f"FP32 V-cycles, 10 steps: {errs}, heave {abs(r['z'] - ro['z']) / abs(ro['z']):.2e}")
+    assert max(errs.values()) < 1e-5
+    t.close()
+
+
+def test_full_size_tank_step():
+    c = synth.tank3d(seed=0)
+    t = wec.Tank3(c)
+    rs = []
+    for _ in range(2):
+        r = t.step(c["dt"])
+        assert r["status"] == 0
+        assert r["residual"] <= c["solver"]["rtol"]
+        assert np.isfinite(r["f_hydro"]) and np.isfinite(r["zdot"])
+        rs.append(r)
+    # the first step's force is the initial hydrostatic pressure's: the weight of
+    # the floating cylinder times (1 + eta / draft) with the incident wave at the
+    # body (|eta| well below the 0.4 m draft); the second carries the impulsive
+    # pressure that brings the Airy flow through the body to rest
+    b = c["body"]
+    ratio = rs[0]["f_hydro"] / (b["mass"] * c["g"])
+    print(f"512x256x256: {[q['iters'] for q in rs]} iterations, first-step F / mg {ratio:.4f}, "
+          f"div {rs[-1]['div_norm']:.3e}")
+    assert 0.5 < ratio < 1.5
+    t.close()
+
+
+def test_invalid_step_uses():
+    c = _cfg(16, 8, 8)
+    t = wec.Tank3(c, step=False)
+    with pytest.raises(wec.WecError):  # created without solver options
+        t.step(c["dt"])
+    t.close()
+    with pytest.raises(wec.WecError):  # FP32 stencils are not built in 3D
+        wec.Tank3(c, precision=wec.PREC_MIXED)
+    t = wec.Tank3(c)
+    with pytest.raises(wec.WecError):
+        t.step(0.0)
+    t.close()
