@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU-baseline sample budget")
-    ap.add_argument("--workload", default="tank", choices=["tank", "batch", "poisson3d"],
+    ap.add_argument("--workload", default="tank", choices=["tank", "batch", "poisson3d", "tank3d"],
                     help="tank: the 1024x256 JONSWAP tank (default); batch: 64 uneven tanks in one graph launch; "
                          "poisson3d: the 3D pressure solve at 512x256x256")
     ap.add_argument("--ncu-steps", type=int, default=0,
@@ -480,6 +480,9 @@ def bench_poisson3d(wec, torch, seed, solves=5, warmup=3, shape=(512, 256, 256),
                                    "launches"},
         }
     out["speedup_mixed_vs_fp64"] = out["fp64"]["ms_per_solve"] / out["mixed"]["ms_per_solve"]
+    del cb, bd
+    torch.cuda.empty_cache()
+    out["levelset3d"] = bench_levelset3d(wec, torch, seed, shape, peak, peak_kind)
     out["cpu_baseline"] = None
     if cpu_seconds > 0:
         from oracle import build as ob
@@ -497,6 +500,137 @@ def bench_poisson3d(wec, torch, seed, solves=5, warmup=3, shape=(512, 256, 256),
         out["cpu_baseline"] = {"value": sx * sy * sz * k / el, "unit": "cell-solves/s", "cores": 1, "kind": "oracle",
                                "sample": f"{k} oracle FP64 solves of the same structure on a {sx}x{sy}x{sz} grid "
                                          f"({io['iters']} iterations each, {el:.1f} s, 1 thread)"}
+    return out
+
+
+def bench_levelset3d(wec, torch, seed, shape, peak, peak_kind, reps=3):
+    """The 3D tank's level-set kernels (wec_tank3, FP64) on the same grid: the
+    incident JONSWAP surface with a cylinder, 0.3 m/s random face velocities;
+    CUDA events around each call (advection, 4 reinitialisation pseudo-steps,
+    materials), best of `reps`; algorithmic bytes over the measured HBM peak."""
+    from paper_2206_07732_gb300 import synth
+    nx, ny, nz = shape
+    c = synth.tank3d(seed=seed, nx=nx, ny=ny, nz=nz)
+    h = c["lx"] / nx
+    amp, om, ph = wec.wave_components(c["wave"])
+    k = np.array([wec.wave_number(w, c["depth"], c["g"]) for w in om])
+    x = (np.arange(nx) + 0.5) * h
+    eta = np.sum(amp[:, None] * np.cos(k[:, None] * x[None, :] + ph[:, None]), axis=0)
+    z = (np.arange(nz) + 0.5) * h
+    sig = np.broadcast_to(z[:, None, None] - c["depth"] - eta[None, None, :], (nz, ny, nx))
+    f = synth.random_fields3(nx, ny, nz, seed=seed + 1, scale=0.3)
+    T = wec.Tank3(c)
+    for fid, a in ((wec.F3_SIGMA, sig), (wec.F3_U, f["u"]), (wec.F3_V, f["v"]), (wec.F3_W, f["w"])):
+        T.set(fid, a)
+    del f
+    n = nx * ny * nz
+    nfs = (nx + 1) * ny * nz + nx * (ny + 1) * nz + nx * ny * (nz + 1)
+    calls = {"advect": (lambda: T.advect(c["dt"], 0.0), 8.0 * (2 * n + nfs)),
+             "reinit_4": (lambda: T.reinit(4, 0.0), 4 * 56.0 * n),
+             "materials": (lambda: wec._check(wec.load().wec_tank3_materials(T.h, c["body"]["zc"])), 40.0 * n)}
+    stream = torch.cuda.current_stream()
+    out = {"precision": "fp64", "cells": n}
+    for name, (fn, nbytes) in calls.items():
+        fn()
+        best = None
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        gbs = nbytes / (best / 1e3) / 1e9
+        out[name] = {"ms": best, "algorithmic_bytes": nbytes, "achieved_GBps": gbs, "frac_of_hbm": gbs / peak}
+    out["peak_source"] = f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)"
+    out["note"] = ("the calls synchronise the stream (timed with it); FP64 PPM / ENO stencils do hundreds of FP64 "
+                   "operations per cell, so on this GPU they are bound by the FP64 pipe, not by HBM")
+    T.close()
+    return out
+
+
+def bench_tank3d(wec, torch, seed, steps=3, warmup=1, shape=(512, 256, 256), cpu_seconds=10.0):
+    """The 3D tank step (wec_tank3_step) on the 8 m x 4 m x 4 m JONSWAP tank with
+    the cylinder buoy: FP64; FP32 V-cycles in the FP64 solve (mixed_mg); and
+    FP32 stencils over FP32 working copies with FP32 V-cycles (mixed; force,
+    heave, solve, projection FP64); CUDA events around each step after `warmup`
+    steps (inputs far larger than L2), then one eager step with every launch
+    timed (breakdown, the dominant kernel's HBM roofline).  The oracle's 3D step
+    on a 64 x 32 x 32 tank of the same physics is the CPU baseline."""
+    from paper_2206_07732_gb300 import synth
+    nx, ny, nz = shape
+    c = synth.tank3d(seed=seed, nx=nx, ny=ny, nz=nz)
+    n = nx * ny * nz
+    stream = torch.cuda.current_stream()
+    peak, peak_kind = peaks()
+    out = {"workload": c["name"] + f", dt {c['dt']} s, rtol {c['solver']['rtol']}", "cells": n,
+           "solver_options": {k: c["solver"][k] for k in ("mg_pre", "mg_post", "restart", "n_reinit", "n_jacobi")},
+           "l2": "inputs larger than L2 (268 MB per FP64 cell array)"}
+    for name, prec in (("fp64", wec.PREC_FP64), ("mixed_mg", wec.PREC_MIXED_MG), ("mixed", wec.PREC_MIXED)):
+        T = wec.Tank3(c, precision=prec)
+        for _ in range(warmup):
+            T.step(c["dt"])
+        ms, its, rr = [], [], []
+        n0 = wec.launch_count()
+        for _ in range(steps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = T.step(c["dt"])
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            its.append(r["iters"])
+            rr.append(r["residual"])
+        launches = (wec.launch_count() - n0) / steps
+        wec.profile_read()
+        wec.profile_enable(1)
+        T.step(c["dt"])
+        wec.profile_enable(0)
+        prof = wec.profile_read()
+        T.close()
+        by = {}
+        for q in prof:
+            d = by.setdefault(q["name"], dict(ms=0.0, bytes=0.0, launches=0))
+            d["ms"] += q["ms"]; d["bytes"] += q["bytes"]; d["launches"] += q["launches"]
+        tot = sum(d["ms"] for d in by.values())
+        top = max(by, key=lambda k: by[k]["ms"])
+        d = by[top]
+        ach = d["bytes"] / (d["ms"] / 1e3) / 1e9 if d["ms"] > 0 and d["bytes"] > 0 else None
+        t = statistics.median(ms)
+        out[name] = {"ms_per_step": t, "ms_per_step_all": ms, "cell_steps_per_s": n / (t / 1e3),
+                     "fgmres_iters": statistics.mean(its), "max_relative_residual": max(rr),
+                     "gpu_launches_per_step": launches,
+                     "kernel_breakdown_eager": [{"kernel": k, "launches": v["launches"], "ms": v["ms"],
+                                                 "share": v["ms"] / tot}
+                                                for k, v in sorted(by.items(), key=lambda kv: -kv[1]["ms"])[:10]],
+                     "roofline": {"bound": "hbm", "kernel": top, "achieved": ach, "peak": peak, "unit": "GB/s",
+                                  "frac": ach / peak if ach else None, "traffic": None,
+                                  "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
+                                  "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
+                                  "avg_launch_us": d["ms"] / d["launches"] * 1e3, "share_of_step_gpu_time": d["ms"] / tot,
+                                  "note": "FP64 stencils of hundreds of FP64 operations per face: bound by the FP64 "
+                                          "pipe on this GPU, not by HBM"}}
+    out["speedup_mixed_mg_vs_fp64"] = out["fp64"]["ms_per_step"] / out["mixed_mg"]["ms_per_step"]
+    out["speedup_mixed_vs_fp64"] = out["fp64"]["ms_per_step"] / out["mixed"]["ms_per_step"]
+    out["cpu_baseline"] = None
+    if cpu_seconds > 0:
+        from oracle import build as ob
+        from oracle import tank3d as OT3
+        ob.build()
+        sc = synth.tank3d(seed=seed, nx=64, ny=32, nz=32)
+        o = OT3.OracleTank3(sc)
+        k, t0 = 0, time.perf_counter()
+        while True:
+            o.step(sc["dt"])
+            k += 1
+            el = time.perf_counter() - t0
+            if el > cpu_seconds:
+                break
+        out["cpu_baseline"] = {"value": 64 * 32 * 32 * k / el, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
+                               "sample": f"{k} oracle steps of the same tank on a 64x32x32 grid ({el:.1f} s, 1 thread)"}
     return out
 
 
@@ -562,6 +696,59 @@ def main_poisson3d(args):
         "clocks": ck, "roofline": r["mixed"]["roofline"], "roofline_fp64": r["fp64"]["roofline"],
         "kernel_breakdown_eager": {"mixed": r["mixed"]["kernel_breakdown_eager"],
                                    "fp64": r["fp64"]["kernel_breakdown_eager"]},
+        "levelset3d": r["levelset3d"],
+        "cpu_baseline": r["cpu_baseline"],
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main_tank3d(args):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    L, wec = setup_lib()
+    steps, warmup = args.steps, max(args.warmup, 3)
+    clocks = Clocks(local)
+    clocks.start()
+    r = bench_tank3d(wec, torch, args.seed, steps=steps, warmup=warmup,
+                     cpu_seconds=0.0 if (args.no_cpu_baseline or rank or world > 1) else args.cpu_seconds)
+    ck = clocks.stop()
+
+    def reduce_max(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    n = r["cells"]
+    t_m = reduce_max(sum(r["mixed"]["ms_per_step_all"]) / 1e3)
+    t_g = reduce_max(sum(r["mixed_mg"]["ms_per_step_all"]) / 1e3)
+    t_d = reduce_max(sum(r["fp64"]["ms_per_step_all"]) / 1e3)
+    line = {
+        "metric": METRIC + " (3D tank)", "value": world * n * steps / t_m, "unit": UNIT, "n_gpus": world,
+        "steps": steps, "warmup": warmup, "ms_per_step": t_m / steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32(stencils,multigrid)",
+        "data": "synthetic (seeded JONSWAP phases)",
+        "config": {"workload": r["workload"], "cells": n, "l2": r["l2"], "solver_options": r["solver_options"],
+                   "precision": "mixed: FP32 stencils over FP32 working copies and FP32 V-cycles; FP64 FGMRES, "
+                                "residual, force, heave, projection and fields"},
+        "fp64_value": world * n * steps / t_d, "speedup_mixed_vs_fp64": t_d / t_m,
+        "mixed_mg_value": world * n * steps / t_g, "speedup_mixed_mg_vs_fp64": t_d / t_g,
+        "fgmres_iters": {k: r[k]["fgmres_iters"] for k in ("mixed", "mixed_mg", "fp64")},
+        "max_relative_residual": {k: r[k]["max_relative_residual"] for k in ("mixed", "mixed_mg", "fp64")},
+        "e2e": None, "e2e_note": "wec_tank3_step is the public call and returns a host record each step: value is "
+                                 "measured around it",
+        "gpu_launches": r["mixed"]["gpu_launches_per_step"] * steps,
+        "clocks": ck, "roofline": r["mixed"]["roofline"], "roofline_fp64": r["fp64"]["roofline"],
+        "kernel_breakdown_eager": {k: r[k]["kernel_breakdown_eager"] for k in ("mixed", "mixed_mg", "fp64")},
         "cpu_baseline": r["cpu_baseline"],
     }
     if rank == 0:
@@ -812,6 +999,12 @@ def main_ours(args):
     except Exception as ex:  # reported, not fatal to the tank's line
         p3 = {"error": f"{type(ex).__name__}: {ex}"}
 
+    try:
+        t3 = bench_tank3d(wec, torch, args.seed,
+                          cpu_seconds=0.0 if (args.no_cpu_baseline or rank or world > 1) else 10.0)
+    except Exception as ex:  # reported, not fatal to the tank's line
+        t3 = {"error": f"{type(ex).__name__}: {ex}"}
+
     tried, kept = learned["net_stats"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": warmup,
@@ -851,6 +1044,7 @@ def main_ours(args):
         "kernel_breakdown_eager": breakdown,
         "cpu_baseline": cpu,
         "poisson3d": p3,
+        "tank3d": t3,
     }
     if rank == 0:
         print(json.dumps(line))
@@ -895,5 +1089,7 @@ if __name__ == "__main__":
         main_batch(a)
     elif a.workload == "poisson3d":
         main_poisson3d(a)
+    elif a.workload == "tank3d":
+        main_tank3d(a)
     else:
         main_ours(a)

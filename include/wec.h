@@ -425,8 +425,12 @@ int wec_tank3_advect(wec_tank3 *tank, double dt, double t);
 /* nit Sussman pseudo-steps (TVD-RK2, d tau = 0.3 h) toward |grad sigma| = 1 with
  * the sign of sigma at the call (section "Interface tracking"); ghosts at t. */
 int wec_tank3_reinit(wec_tank3 *tank, int nit, double t);
-/* One time step of the 3D tank (needs opts at creation; precision WEC_PREC_FP64 or
- * WEC_PREC_MIXED_MG, the stencils FP64): heave force from p^{n-1/2}, u^n (Eq.
+/* One time step of the 3D tank (needs opts at creation).  Precision: WEC_PREC_FP64;
+ * WEC_PREC_MIXED_MG (FP32 V-cycles in the FP64 solve, FP64 stencils); WEC_PREC_MIXED
+ * (also the stencils -- materials, advection, reinitialisation, transport, viscous
+ * terms, Jacobi sweeps -- in FP32 over FP32 working copies of the FP64 state; the
+ * force, heave, beta, right-hand side, solve, projection and fields stay FP64).
+ * The step: heave force from p^{n-1/2}, u^n (Eq.
  * int_fh: pressure interpolated to psi = 0 and the normal viscous stress on
  * z-faces, the shear stresses on x- and y-faces, face area h^2); heave update
  * (Eq. newton_u, stabilised by added_mass); sigma advection + damping zone and

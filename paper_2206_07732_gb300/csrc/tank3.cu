@@ -1,9 +1,12 @@
 // The three-dimensional tank (wec_tank3): one time step of the two-phase flow
 // with a heaving vertical cylinder on an nx x ny x nz grid with z vertical
 // (sections "Continuous equations of motion" through "Fluid-structure
-// coupling", d = 3) as FP64 kernels, one thread per cell or face, x fastest;
-// the pressure increment is solved by a 3D wec_poisson object the tank owns
-// (FP64, or FP32 V-cycles for WEC_PREC_MIXED_MG).  The step is the
+// coupling", d = 3), one thread per cell or face, x fastest; the pressure
+// increment is solved by a 3D wec_poisson object the tank owns (FP64, or FP32
+// V-cycles for WEC_PREC_MIXED_MG and WEC_PREC_MIXED).  The stencils are FP64,
+// or, for WEC_PREC_MIXED, FP32 over FP32 working copies of the FP64 state (the
+// force integral, the heave update, the projection and the persistent fields
+// stay FP64).  The step is the
 // two-dimensional one with three velocity components: heave force (Eq. int_fh)
 // and update, sigma advection + damping zone and reinitialisation, materials,
 // consistent transport and the Crank-Nicolson momentum system by Jacobi
@@ -33,6 +36,12 @@
 
 #include "internal.cuh"
 
+// the tank's constants in the working type of a kernel
+template <typename R>
+struct Tank3C {
+    R h, ih, depth, rho_w, rho_a, mu_w, mu_a, rho_s, bxc, byc, br, blen;
+};
+
 struct Tank3P {
     int nx, ny, nz;
     double h, ih, depth, rho_w, rho_a, mu_w, mu_a, rho_s;
@@ -41,6 +50,19 @@ struct Tank3P {
     int ncomp;
     const double *amp, *omega, *kw, *phase;  // device
     const double *damp;                       // device, [nx]: damping-zone weight of each column
+    const float *dampf;                       // the same in FP32
+    Tank3C<float> cf;
+    Tank3C<double> cd;
+};
+
+// the working arrays of one precision of the step's stencils
+template <typename R>
+struct Work3 {
+    R *sig = nullptr, *tmp = nullptr, *s0 = nullptr, *s1 = nullptr, *u = nullptr, *v = nullptr, *w = nullptr;
+    R *rho = nullptr, *mu = nullptr, *rf = nullptr, *chi = nullptr, *mu1 = nullptr, *rf1 = nullptr, *chi1 = nullptr;
+    R *D[3] = {}, *R3[3] = {}, *A[3] = {}, *B[3] = {};
+    R *bc = nullptr;     // u_in(t1) [nz], w_in(t0) [nz+1], w_in(t1) [nz+1], vorticity damping [nz], [nz+1]
+    R *dampu = nullptr;  // damping weight of the u-faces [nx+1]
 };
 
 struct wec_tank3 {
@@ -62,7 +84,10 @@ struct wec_tank3 {
     double *tabs = nullptr;  // damping weight of the u-faces [nx+1]; vorticity damping at cell / face heights
     double *part = nullptr;  // reduction partials
     wec_poisson *solver = nullptr;
-    bool stepping = false;   // created with solver options (wec_tank3_create_step)
+    bool stepping = false;   // created with solver options
+    Work3<float> wf;         // FP32 working copies (WEC_PREC_MIXED)
+    float *fconsts = nullptr;
+    std::vector<double> hwave;  // host copy of the wave components: amp, omega, k, phase
 };
 
 namespace wec {
@@ -70,84 +95,108 @@ namespace {
 
 constexpr double kPi3 = 3.14159265358979323846;
 
-// FP64 division and square root expand into long FMA sequences on this GPU:
-// the kernels multiply by reciprocals formed once (1/h, 1/6, ...), which
-// differs from dividing by at most an ulp.
-__device__ __forceinline__ double heav3(double phi, double eps, double ieps)
+// The stencils are templates on their working type R: double (WEC_PREC_FP64,
+// WEC_PREC_MIXED_MG) or float over FP32 working copies of the FP64 state
+// (WEC_PREC_MIXED).  The FP64 pipe of this GPU runs at 1/64 of the FP32 rate,
+// so an FP32 kernel reads its constants in FP32 (cst3) and converts nothing in
+// its inner loops; the force integral, the heave, the solve and the projection
+// stay FP64.  FP64 division and square root expand into long FMA sequences:
+// the kernels multiply by reciprocals formed once (1/h, 1/6, ...), which differs
+// from dividing by at most an ulp.
+template <typename R>
+__device__ __forceinline__ const Tank3C<R> &cst3(const Tank3P &P)
 {
-    if (phi < -eps) return 0.0;
-    if (phi > eps) return 1.0;
-    const double r = phi * ieps;
-    return 0.5 * (1.0 + r + sin(kPi3 * r) * (1.0 / kPi3));
+    if constexpr (sizeof(R) == 4) return P.cf; else return P.cd;
 }
 
-__device__ __noinline__ double eta3(const Tank3P &P, double x, double t)
+template <typename R>
+__device__ __forceinline__ R dampc(const Tank3P &P, int i)
 {
-    double e = 0.0;
-    for (int c = 0; c < P.ncomp; ++c) e += P.amp[c] * cos(P.kw[c] * x - P.omega[c] * t + P.phase[c]);
-    return e;
+    if constexpr (sizeof(R) == 4) return P.dampf[i]; else return P.damp[i];
 }
 
-// sigma at (i, j, k), with the ghosts of the header
-__device__ __forceinline__ double sig3(const Tank3P &P, const double *__restrict__ s, int i, int j, int k, double t)
+template <typename R>
+__device__ __forceinline__ R heav3(R phi, R eps, R ieps)
 {
-    if (i < 0) return (k + 0.5) * P.h - P.depth - eta3(P, (i + 0.5) * P.h, t);
+    if (phi < -eps) return R(0);
+    if (phi > eps) return R(1);
+    const R r = phi * ieps;
+    return R(0.5) * (R(1) + r + sin(R(kPi3) * r) * R(1.0 / kPi3));
+}
+
+// The incident surface at the three ghost columns x = -(m + 1/2) h, m = 0, 1, 2,
+// at the time of a call (eta of the wave components, summed on the host): the
+// inflow ghost of sigma.  Summing the components per ghost read on the GPU ran
+// 128 FP64 cosines in the first warp of every row, which serialised those
+// warps on the FP64 pipe and dominated the level-set kernels.
+struct Ghost3 {
+    double e[3];
+};
+
+// sigma at (i, j, k), with the ghosts of the header (the inflow ghost in FP64)
+template <typename R>
+__device__ __forceinline__ R sig3(const Tank3P &P, const R *__restrict__ s, int i, int j, int k, const Ghost3 &G)
+{
+    if (i < 0) return R((k + 0.5) * P.h - P.depth - G.e[-1 - i]);
     i = min(i, P.nx - 1);
     j = min(max(j, 0), P.ny - 1);
     const long long col = (long long)j * P.nx + i, pl = (long long)P.nx * P.ny;
-    if (k < 0) return s[col] + k * (s[pl + col] - s[col]);
+    if (k < 0) return s[col] + R(k) * (s[pl + col] - s[col]);
     if (k > P.nz - 1) {
-        const double a = s[(P.nz - 1) * pl + col], b = s[(P.nz - 2) * pl + col];
-        return a + (k - (P.nz - 1)) * (a - b);
+        const R a = s[(P.nz - 1) * pl + col], b = s[(P.nz - 2) * pl + col];
+        return a + R(k - (P.nz - 1)) * (a - b);
     }
     return s[k * pl + col];
 }
 
-__device__ __forceinline__ double vl3(double am, double a0, double ap)
+template <typename R>
+__device__ __forceinline__ R vl3(R am, R a0, R ap)
 {
-    const double dl = a0 - am, dr = ap - a0;
-    if (dl * dr <= 0.0) return 0.0;
-    const double dc = 0.5 * (ap - am);
-    const double m = fmin(fabs(dc), fmin(2.0 * fabs(dl), 2.0 * fabs(dr)));
-    return dc > 0.0 ? m : -m;
+    const R dl = a0 - am, dr = ap - a0;
+    if (dl * dr <= R(0)) return R(0);
+    const R dc = R(0.5) * (ap - am);
+    const R m = fmin(fabs(dc), fmin(R(2) * fabs(dl), R(2) * fabs(dr)));
+    return dc > R(0) ? m : -m;
 }
 
 // limited PPM edge values (eL, eR) of the middle cell of a[0..4]
-__device__ __forceinline__ void ppm_edges3(const double *a, double &eL, double &eR)
+template <typename R>
+__device__ __forceinline__ void ppm_edges3(const R *a, R &eL, R &eR)
 {
-    const double dm = vl3(a[0], a[1], a[2]), d0 = vl3(a[1], a[2], a[3]), dp = vl3(a[2], a[3], a[4]);
-    constexpr double i6 = 1.0 / 6.0;
-    double L = a[1] + 0.5 * (a[2] - a[1]) - (d0 - dm) * i6;
-    double R = a[2] + 0.5 * (a[3] - a[2]) - (dp - d0) * i6;
-    const double c = a[2];
-    if ((R - c) * (c - L) <= 0.0) {
+    const R i6 = R(1.0 / 6.0);
+    const R dm = vl3(a[0], a[1], a[2]), d0 = vl3(a[1], a[2], a[3]), dp = vl3(a[2], a[3], a[4]);
+    R L = a[1] + R(0.5) * (a[2] - a[1]) - (d0 - dm) * i6;
+    R Rr = a[2] + R(0.5) * (a[3] - a[2]) - (dp - d0) * i6;
+    const R c = a[2];
+    if ((Rr - c) * (c - L) <= R(0)) {
         L = c;
-        R = c;
+        Rr = c;
     } else {
-        const double dA = R - L, m6 = dA * (c - 0.5 * (L + R)), q = dA * dA * i6;
+        const R dA = Rr - L, m6 = dA * (c - R(0.5) * (L + Rr)), q = dA * dA * i6;
         if (m6 > q)
-            L = 3.0 * c - 2.0 * R;
+            L = R(3) * c - R(2) * Rr;
         else if (-q > m6)
-            R = 3.0 * c - 2.0 * L;
+            Rr = R(3) * c - R(2) * L;
     }
     eL = L;
-    eR = R;
+    eR = Rr;
 }
 
 // time-centred upwind state at the face between a[2] and a[3] (a: cells f-3 .. f+2);
 // dtih = dt / h
-__device__ __forceinline__ double ppm_face3(const double *a, double vel, double dtih)
+template <typename R>
+__device__ __forceinline__ R ppm_face3(const R *a, R vel, R dtih)
 {
-    constexpr double t3 = 2.0 / 3.0;
-    double L, R;
-    if (vel >= 0.0) {
-        ppm_edges3(a, L, R);
-        const double C = vel * dtih, dA = R - L, a6 = 6.0 * (a[2] - 0.5 * (L + R));
-        return R - 0.5 * C * (dA - (1.0 - C * t3) * a6);
+    const R t3 = R(2.0 / 3.0);
+    R L, Rr;
+    if (vel >= R(0)) {
+        ppm_edges3(a, L, Rr);
+        const R C = vel * dtih, dA = Rr - L, a6 = R(6) * (a[2] - R(0.5) * (L + Rr));
+        return Rr - R(0.5) * C * (dA - (R(1) - C * t3) * a6);
     }
-    ppm_edges3(a + 1, L, R);
-    const double C = -vel * dtih, dA = R - L, a6 = 6.0 * (a[3] - 0.5 * (L + R));
-    return L + 0.5 * C * (dA + (1.0 - C * t3) * a6);
+    ppm_edges3(a + 1, L, Rr);
+    const R C = -vel * dtih, dA = Rr - L, a6 = R(6) * (a[3] - R(0.5) * (L + Rr));
+    return L + R(0.5) * C * (dA + (R(1) - C * t3) * a6);
 }
 
 struct Cell3 {
@@ -165,130 +214,158 @@ __device__ __forceinline__ bool cell_of(const Tank3P &P, Cell3 &q)
     return true;
 }
 
-__global__ void __launch_bounds__(128) k3t_materials(Tank3P P, const double *__restrict__ sig, double zc,
-                                                     double *__restrict__ rho, double *__restrict__ mu,
-                                                     double *__restrict__ rhof, double *__restrict__ chi)
+template <typename R>
+__global__ void __launch_bounds__(128) k3t_materials(Tank3P P, const R *__restrict__ sig, double zc,
+                                                     R *__restrict__ rho, R *__restrict__ mu, R *__restrict__ rhof,
+                                                     R *__restrict__ chi)
 {
     pdl_entry();
     Cell3 q;
     if (!cell_of(P, q)) return;
-    const double h = P.h;
-    double psi = 1.0e3;
+    const Tank3C<R> &K = cst3<R>(P);
+    const R h = K.h;
+    R psi = R(1.0e3);
     if (P.has_body) {
-        const double x = (q.i + 0.5) * h - P.bxc, y = (q.j + 0.5) * h - P.byc, z = (q.k + 0.5) * h - zc;
-        psi = fmax(sqrt(x * x + y * y) - P.br, fabs(z) - 0.5 * P.blen);
+        const R x = (R(q.i) + R(0.5)) * h - K.bxc, y = (R(q.j) + R(0.5)) * h - K.byc,
+                z = (R(q.k) + R(0.5)) * h - R(zc);
+        psi = fmax(sqrt(x * x + y * y) - K.br, fabs(z) - R(0.5) * K.blen);
     }
-    const double hf = heav3(sig[q.c], h, P.ih), hb = heav3(psi, h, P.ih);
-    const double rf = P.rho_w + (P.rho_a - P.rho_w) * hf;
-    const double mf = P.mu_w + (P.mu_a - P.mu_w) * hf;
-    rho[q.c] = P.rho_s + (rf - P.rho_s) * hb;
-    mu[q.c] = P.mu_w + (mf - P.mu_w) * hb;
+    const R hf = heav3<R>(sig[q.c], h, K.ih), hb = heav3<R>(psi, h, K.ih);
+    const R rf = K.rho_w + (K.rho_a - K.rho_w) * hf;
+    const R mf = K.mu_w + (K.mu_a - K.mu_w) * hf;
+    rho[q.c] = K.rho_s + (rf - K.rho_s) * hb;
+    mu[q.c] = K.mu_w + (mf - K.mu_w) * hb;
     rhof[q.c] = rf;
-    chi[q.c] = 1.0 - hb;
+    chi[q.c] = R(1) - hb;
 }
 
-__global__ void __launch_bounds__(128) k3t_advect(Tank3P P, const double *__restrict__ s, const double *__restrict__ u,
-                                                  const double *__restrict__ v, const double *__restrict__ w, double dt,
-                                                  double t, double *__restrict__ out)
+template <typename R>
+__global__ void __launch_bounds__(128) k3t_advect(Tank3P P, const R *__restrict__ s, const R *__restrict__ u,
+                                                  const R *__restrict__ v, const R *__restrict__ w, double dt,
+                                                  Ghost3 G, R *__restrict__ out)
 {
     pdl_entry();
     Cell3 q;
     if (!cell_of(P, q)) return;
+    const Tank3C<R> &K = cst3<R>(P);
     const int nx = P.nx, ny = P.ny, i = q.i, j = q.j, k = q.k;
     const long long r = (long long)k * ny + j, fu = r * (nx + 1) + i, fv = ((long long)k * (ny + 1) + j) * nx + i;
     const long long pl = (long long)nx * ny;
-    const double h = P.h, ih = P.ih, dtih = dt * ih;
-    double a[6], fx[2], fy[2], fz[2];
+    const R h = K.h, ih = K.ih, dtih = R(dt) * ih;
+    R a[6], fx[2], fy[2], fz[2];
+    // cells three or more from every boundary read their stencils at fixed
+    // offsets (no ghosts, 32-bit indices); the others through sig3
+    const bool inner = i >= 3 && i < nx - 3 && j >= 3 && j < ny - 3 && k >= 3 && k < P.nz - 3;
+    const int c32 = (int)q.c, sy = nx, sz = nx * ny;
 #pragma unroll
     for (int f = 0; f < 2; ++f) {
 #pragma unroll
-        for (int m = 0; m < 6; ++m) a[m] = sig3(P, s, i + f - 3 + m, j, k, t);
-        fx[f] = ppm_face3(a, u[fu + f], dtih);
+        for (int m = 0; m < 6; ++m) a[m] = inner ? s[c32 + (f - 3 + m)] : sig3<R>(P, s, i + f - 3 + m, j, k, G);
+        fx[f] = ppm_face3<R>(a, u[fu + f], dtih);
 #pragma unroll
-        for (int m = 0; m < 6; ++m) a[m] = sig3(P, s, i, j + f - 3 + m, k, t);
-        fy[f] = ppm_face3(a, v[fv + f * nx], dtih);
+        for (int m = 0; m < 6; ++m) a[m] = inner ? s[c32 + (f - 3 + m) * sy] : sig3<R>(P, s, i, j + f - 3 + m, k, G);
+        fy[f] = ppm_face3<R>(a, v[fv + f * nx], dtih);
 #pragma unroll
-        for (int m = 0; m < 6; ++m) a[m] = sig3(P, s, i, j, k + f - 3 + m, t);
-        fz[f] = ppm_face3(a, w[q.c + f * pl], dtih);
+        for (int m = 0; m < 6; ++m) a[m] = inner ? s[c32 + (f - 3 + m) * sz] : sig3<R>(P, s, i, j, k + f - 3 + m, G);
+        fz[f] = ppm_face3<R>(a, w[q.c + f * pl], dtih);
     }
-    const double ub = 0.5 * (u[fu] + u[fu + 1]);
-    const double vb = 0.5 * (v[fv] + v[fv + nx]);
-    const double wb = 0.5 * (w[q.c] + w[q.c + pl]);
-    const double Q = ub * (fx[1] - fx[0]) * ih + vb * (fy[1] - fy[0]) * ih + wb * (fz[1] - fz[0]) * ih;
-    const double sa = s[q.c] - dt * Q;
-    const double al = P.damp[i];
-    out[q.c] = (1.0 - al) * sa + al * ((k + 0.5) * h - P.depth);
+    const R ub = R(0.5) * (u[fu] + u[fu + 1]);
+    const R vb = R(0.5) * (v[fv] + v[fv + nx]);
+    const R wb = R(0.5) * (w[q.c] + w[q.c + pl]);
+    const R Q = ub * (fx[1] - fx[0]) * ih + vb * (fy[1] - fy[0]) * ih + wb * (fz[1] - fz[0]) * ih;
+    const R sa = s[q.c] - R(dt) * Q;
+    const R al = dampc<R>(P, i);
+    out[q.c] = (R(1) - al) * sa + al * ((R(k) + R(0.5)) * h - K.depth);
 }
 
-__device__ __forceinline__ double mm3(double a, double b)
+template <typename R>
+__device__ __forceinline__ R mm3(R a, R b)
 {
-    if (a * b <= 0.0) return 0.0;
+    if (a * b <= R(0)) return R(0);
     return fabs(a) < fabs(b) ? a : b;
 }
 
 // S(sigma0) (|grad f| - 1) at a cell
-__device__ double reinit_rhs3(const Tank3P &P, const double *__restrict__ f, const double *__restrict__ s0,
-                              const Cell3 &q, double t)
+template <typename R>
+__device__ __forceinline__ R reinit_rhs3(const Tank3P &P, const R *__restrict__ f, const R *__restrict__ s0,
+                                         const Cell3 &q, const Ghost3 &G)
 {
-    const double h = P.h, ih = P.ih, hih = 0.5 * P.ih, c = f[q.c];
-    const double sg0 = s0[q.c];
-    const bool pos = sg0 > 0.0;
-    double g2 = 0.0;
+    const Tank3C<R> &K = cst3<R>(P);
+    const R h = K.h, ih = K.ih, hih = R(0.5) * K.ih, c = f[q.c];
+    const R sg0 = s0[q.c];
+    const bool pos = sg0 > R(0);
+    // cells two or more from every boundary read their neighbours at fixed
+    // offsets (no ghosts, 32-bit indices); the others through sig3
+    const bool inner = q.i >= 2 && q.i < P.nx - 2 && q.j >= 2 && q.j < P.ny - 2 && q.k >= 2 && q.k < P.nz - 2;
+    const int c32 = (int)q.c, st3[3] = {1, P.nx, P.nx * P.ny};
+    R g2 = R(0);
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         const int di = d == 0, dj = d == 1, dk = d == 2;
-        const double m2 = sig3(P, f, q.i - 2 * di, q.j - 2 * dj, q.k - 2 * dk, t);
-        const double m1 = sig3(P, f, q.i - di, q.j - dj, q.k - dk, t);
-        const double p1 = sig3(P, f, q.i + di, q.j + dj, q.k + dk, t);
-        const double p2 = sig3(P, f, q.i + 2 * di, q.j + 2 * dj, q.k + 2 * dk, t);
-        const double dm = m2 - 2.0 * m1 + c, d0 = m1 - 2.0 * c + p1, dp = c - 2.0 * p1 + p2;
-        const double a = (c - m1) * ih + mm3(dm, d0) * hih;
-        const double b = (p1 - c) * ih - mm3(d0, dp) * hih;
-        double g;
+        R m2, m1, p1, p2;
+        if (inner) {
+            const int o = st3[d];
+            m2 = f[c32 - 2 * o];
+            m1 = f[c32 - o];
+            p1 = f[c32 + o];
+            p2 = f[c32 + 2 * o];
+        } else {
+            m2 = sig3<R>(P, f, q.i - 2 * di, q.j - 2 * dj, q.k - 2 * dk, G);
+            m1 = sig3<R>(P, f, q.i - di, q.j - dj, q.k - dk, G);
+            p1 = sig3<R>(P, f, q.i + di, q.j + dj, q.k + dk, G);
+            p2 = sig3<R>(P, f, q.i + 2 * di, q.j + 2 * dj, q.k + 2 * dk, G);
+        }
+        const R dm = m2 - R(2) * m1 + c, d0 = m1 - R(2) * c + p1, dp = c - R(2) * p1 + p2;
+        const R a = (c - m1) * ih + mm3(dm, d0) * hih;
+        const R b = (p1 - c) * ih - mm3(d0, dp) * hih;
+        R g;
         if (pos) {
-            const double x = fmax(a, 0.0), y = fmin(b, 0.0);
+            const R x = fmax(a, R(0)), y = fmin(b, R(0));
             g = fmax(x * x, y * y);
         } else {
-            const double x = fmin(a, 0.0), y = fmax(b, 0.0);
+            const R x = fmin(a, R(0)), y = fmax(b, R(0));
             g = fmax(x * x, y * y);
         }
         g2 = d == 0 ? g : g2 + g;
     }
-    const double S = sg0 * rsqrt(sg0 * sg0 + h * h);
-    return S * (sqrt(g2) - 1.0);
+    const R S = sg0 * rsqrt(sg0 * sg0 + h * h);
+    return S * (sqrt(g2) - R(1));
 }
 
 // stage 1: out = f - dtau L(f); stage 2: out = (out + (f - dtau L(f))) / 2 with
 // out holding sigma at the start of the pseudo-step
-__global__ void __launch_bounds__(128) k3t_reinit_stage(Tank3P P, const double *__restrict__ f,
-                                                        const double *__restrict__ s0, double *out, double t,
-                                                        double dtau, int stage)
+template <typename R>
+__global__ void __launch_bounds__(128) k3t_reinit_stage(Tank3P P, const R *__restrict__ f, const R *__restrict__ s0,
+                                                        R *out, Ghost3 G, double dtau, int stage)
 {
     pdl_entry();
     Cell3 q;
     if (!cell_of(P, q)) return;
-    const double y = f[q.c] - dtau * reinit_rhs3(P, f, s0, q, t);
-    out[q.c] = stage == 1 ? y : 0.5 * (out[q.c] + y);
+    const R y = f[q.c] - R(dtau) * reinit_rhs3<R>(P, f, s0, q, G);
+    out[q.c] = stage == 1 ? y : R(0.5) * (out[q.c] + y);
 }
 
 // ------------------------------------------------------------ the step ----
 // Velocity ghosts: nearest face (free slip); at the inflow v is reflected oddly
 // about 0 and w about the incident wave's w_in (win: [nz+1] at the time used).
-__device__ __forceinline__ double cellq(const Tank3P &P, const double *__restrict__ a, int i, int j, int k)
+template <typename R>
+__device__ __forceinline__ R cellq(const Tank3P &P, const R *__restrict__ a, int i, int j, int k)
 {
     i = min(max(i, 0), P.nx - 1);
     j = min(max(j, 0), P.ny - 1);
     k = min(max(k, 0), P.nz - 1);
     return a[((long long)k * P.ny + j) * P.nx + i];
 }
-__device__ __forceinline__ double uq(const Tank3P &P, const double *__restrict__ u, int i, int j, int k)
+template <typename R>
+__device__ __forceinline__ R uq(const Tank3P &P, const R *__restrict__ u, int i, int j, int k)
 {
     i = min(max(i, 0), P.nx);
     j = min(max(j, 0), P.ny - 1);
     k = min(max(k, 0), P.nz - 1);
     return u[((long long)k * P.ny + j) * (P.nx + 1) + i];
 }
-__device__ __forceinline__ double vq(const Tank3P &P, const double *__restrict__ v, int i, int j, int k)
+template <typename R>
+__device__ __forceinline__ R vq(const Tank3P &P, const R *__restrict__ v, int i, int j, int k)
 {
     j = min(max(j, 0), P.ny);
     k = min(max(k, 0), P.nz - 1);
@@ -296,95 +373,102 @@ __device__ __forceinline__ double vq(const Tank3P &P, const double *__restrict__
     if (i < 0) return -v[((long long)k * (P.ny + 1) + j) * P.nx + (-1 - i)];
     return v[((long long)k * (P.ny + 1) + j) * P.nx + i];
 }
-__device__ __forceinline__ double wq(const Tank3P &P, const double *__restrict__ w, const double *__restrict__ win,
-                                     int i, int j, int k)
+template <typename R>
+__device__ __forceinline__ R wq(const Tank3P &P, const R *__restrict__ w, const R *__restrict__ win, int i, int j,
+                                int k)
 {
     k = min(max(k, 0), P.nz);
     j = min(max(j, 0), P.ny - 1);
     if (i > P.nx - 1) i = P.nx - 1;
-    if (i < 0) return 2.0 * win[k] - w[((long long)k * P.ny + j) * P.nx + (-1 - i)];
+    if (i < 0) return R(2) * win[k] - w[((long long)k * P.ny + j) * P.nx + (-1 - i)];
     return w[((long long)k * P.ny + j) * P.nx + i];
 }
 
-__device__ __forceinline__ double koren3(double quu, double qu, double qd)
+template <typename R>
+__device__ __forceinline__ R koren3(R quu, R qu, R qd)
 {
-    const double d1 = qu - quu, d2 = qd - qu;
-    if (d1 * d2 <= 0.0) return qu;
-    const double m = fmin(2.0 * fabs(d2), fmin((fabs(d1) + 2.0 * fabs(d2)) / 3.0, 2.0 * fabs(d1)));
-    return d1 > 0.0 ? qu + 0.5 * m : qu - 0.5 * m;
+    const R d1 = qu - quu, d2 = qd - qu;
+    if (d1 * d2 <= R(0)) return qu;
+    const R m = fmin(R(2) * fabs(d2), fmin((fabs(d1) + R(2) * fabs(d2)) / R(3), R(2) * fabs(d1)));
+    return d1 > R(0) ? qu + R(0.5) * m : qu - R(0.5) * m;
 }
-__device__ __forceinline__ double upw3(double q0, double q1, double q2, double q3, double vel)
+template <typename R>
+__device__ __forceinline__ R upw3(R q0, R q1, R q2, R q3, R vel)
 {
-    return vel >= 0.0 ? koren3(q0, q1, q2) : koren3(q3, q2, q1);
+    return vel >= R(0) ? koren3(q0, q1, q2) : koren3(q3, q2, q1);
 }
 // face densities: the mean of the face's two cells (face index clamped first)
-__device__ __forceinline__ double ruq(const Tank3P &P, const double *rc, int i, int j, int k)
+template <typename R>
+__device__ __forceinline__ R ruq(const Tank3P &P, const R *rc, int i, int j, int k)
 {
     i = min(max(i, 0), P.nx);
     j = min(max(j, 0), P.ny - 1);
     k = min(max(k, 0), P.nz - 1);
-    return 0.5 * (cellq(P, rc, i - 1, j, k) + cellq(P, rc, i, j, k));
+    return R(0.5) * (cellq(P, rc, i - 1, j, k) + cellq(P, rc, i, j, k));
 }
-__device__ __forceinline__ double rvq(const Tank3P &P, const double *rc, int i, int j, int k)
+template <typename R>
+__device__ __forceinline__ R rvq(const Tank3P &P, const R *rc, int i, int j, int k)
 {
     i = min(max(i, 0), P.nx - 1);
     j = min(max(j, 0), P.ny);
     k = min(max(k, 0), P.nz - 1);
-    return 0.5 * (cellq(P, rc, i, j - 1, k) + cellq(P, rc, i, j, k));
+    return R(0.5) * (cellq(P, rc, i, j - 1, k) + cellq(P, rc, i, j, k));
 }
-__device__ __forceinline__ double rwq(const Tank3P &P, const double *rc, int i, int j, int k)
+template <typename R>
+__device__ __forceinline__ R rwq(const Tank3P &P, const R *rc, int i, int j, int k)
 {
     i = min(max(i, 0), P.nx - 1);
     j = min(max(j, 0), P.ny - 1);
     k = min(max(k, 0), P.nz);
-    return 0.5 * (cellq(P, rc, i, j, k - 1) + cellq(P, rc, i, j, k));
+    return R(0.5) * (cellq(P, rc, i, j, k - 1) + cellq(P, rc, i, j, k));
 }
 
+template <typename R>
 struct Vel3 {
-    const double *u, *v, *w, *win;
+    const R *u, *v, *w, *win;
 };
 
 // rho-breve and C of a momentum control volume: comp 0 u-face, 1 v-face, 2 w-face;
 // the three pairs of CV faces summed x, then y, then z
-__device__ void transport3(const Tank3P &P, const double *rc, const Vel3 &V, int comp, int i, int j, int k, double dt,
-                           double &rb, double &C)
+template <typename R>
+__device__ void transport3(const Tank3P &P, const R *rc, const Vel3<R> &V, int comp, int i, int j, int k, R dt, R &rb,
+                           R &C)
 {
-    const double h = P.h;
-    double m[6], f[6];
+    const R h = cst3<R>(P).h;
+    R m[6], f[6];
 #define QV(a, b, c) (comp == 0 ? uq(P, V.u, a, b, c) : comp == 1 ? vq(P, V.v, a, b, c) : wq(P, V.w, V.win, a, b, c))
 #define RV(a, b, c) (comp == 0 ? ruq(P, rc, a, b, c) : comp == 1 ? rvq(P, rc, a, b, c) : rwq(P, rc, a, b, c))
     for (int d = 0; d < 3; ++d)
         for (int s = 0; s < 2; ++s) {
-            // the advecting velocity of the CV face and the stencil direction
-            double U;
+            R U;
             if (d == comp) {  // CV faces at the cell centres on either side
                 const int o = s - 1;
-                U = comp == 0   ? 0.5 * (uq(P, V.u, i + o, j, k) + uq(P, V.u, i + o + 1, j, k))
-                    : comp == 1 ? 0.5 * (vq(P, V.v, i, j + o, k) + vq(P, V.v, i, j + o + 1, k))
-                                : 0.5 * (wq(P, V.w, V.win, i, j, k + o) + wq(P, V.w, V.win, i, j, k + o + 1));
+                U = comp == 0   ? R(0.5) * (uq(P, V.u, i + o, j, k) + uq(P, V.u, i + o + 1, j, k))
+                    : comp == 1 ? R(0.5) * (vq(P, V.v, i, j + o, k) + vq(P, V.v, i, j + o + 1, k))
+                                : R(0.5) * (wq(P, V.w, V.win, i, j, k + o) + wq(P, V.w, V.win, i, j, k + o + 1));
             } else {  // CV faces on the edges: the d-velocity averaged over the comp direction
-                const int e = s;  // edge index offset in d
+                const int e = s;
                 if (d == 0)
-                    U = comp == 1 ? 0.5 * (uq(P, V.u, i + e, j - 1, k) + uq(P, V.u, i + e, j, k))
-                                  : 0.5 * (uq(P, V.u, i + e, j, k - 1) + uq(P, V.u, i + e, j, k));
+                    U = comp == 1 ? R(0.5) * (uq(P, V.u, i + e, j - 1, k) + uq(P, V.u, i + e, j, k))
+                                  : R(0.5) * (uq(P, V.u, i + e, j, k - 1) + uq(P, V.u, i + e, j, k));
                 else if (d == 1)
-                    U = comp == 0 ? 0.5 * (vq(P, V.v, i - 1, j + e, k) + vq(P, V.v, i, j + e, k))
-                                  : 0.5 * (vq(P, V.v, i, j + e, k - 1) + vq(P, V.v, i, j + e, k));
+                    U = comp == 0 ? R(0.5) * (vq(P, V.v, i - 1, j + e, k) + vq(P, V.v, i, j + e, k))
+                                  : R(0.5) * (vq(P, V.v, i, j + e, k - 1) + vq(P, V.v, i, j + e, k));
                 else
-                    U = comp == 0 ? 0.5 * (wq(P, V.w, V.win, i - 1, j, k + e) + wq(P, V.w, V.win, i, j, k + e))
-                                  : 0.5 * (wq(P, V.w, V.win, i, j - 1, k + e) + wq(P, V.w, V.win, i, j, k + e));
+                    U = comp == 0 ? R(0.5) * (wq(P, V.w, V.win, i - 1, j, k + e) + wq(P, V.w, V.win, i, j, k + e))
+                                  : R(0.5) * (wq(P, V.w, V.win, i, j - 1, k + e) + wq(P, V.w, V.win, i, j, k + e));
             }
             const int a0 = s - 1;  // the stencil runs over (base + a0 - 1 .. base + a0 + 2) along d
             const int di = d == 0, dj = d == 1, dk = d == 2;
-            double rr[4], qq[4];
+            R rr[4], qq[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int o = a0 - 1 + q;
                 rr[q] = RV(i + o * di, j + o * dj, k + o * dk);
                 qq[q] = QV(i + o * di, j + o * dj, k + o * dk);
             }
-            const double r = upw3(rr[0], rr[1], rr[2], rr[3], U);
-            const double qv = upw3(qq[0], qq[1], qq[2], qq[3], U);
+            const R r = upw3(rr[0], rr[1], rr[2], rr[3], U);
+            const R qv = upw3(qq[0], qq[1], qq[2], qq[3], U);
             m[2 * d + s] = U * r;
             f[2 * d + s] = m[2 * d + s] * qv;
         }
@@ -396,58 +480,72 @@ __device__ void transport3(const Tank3P &P, const double *rc, const Vel3 &V, int
 
 // viscous stresses and div[mu (grad u + grad u^T)] with edge viscosities (the
 // mean of the four cells around the edge)
+template <typename R>
 struct Visc3 {
-    const double *mu;
-    Vel3 V;
+    const R *mu;
+    Vel3<R> V;
 };
-__device__ __forceinline__ double mxy3(const Tank3P &P, const double *mu, int i, int j, int k)
+template <typename R>
+__device__ __forceinline__ R mxy3(const Tank3P &P, const R *mu, int i, int j, int k)
 {
-    return 0.25 * (cellq(P, mu, i - 1, j - 1, k) + cellq(P, mu, i, j - 1, k) + cellq(P, mu, i - 1, j, k) +
-                   cellq(P, mu, i, j, k));
+    return R(0.25) * (cellq(P, mu, i - 1, j - 1, k) + cellq(P, mu, i, j - 1, k) + cellq(P, mu, i - 1, j, k) +
+                      cellq(P, mu, i, j, k));
 }
-__device__ __forceinline__ double mxz3(const Tank3P &P, const double *mu, int i, int j, int k)
+template <typename R>
+__device__ __forceinline__ R mxz3(const Tank3P &P, const R *mu, int i, int j, int k)
 {
-    return 0.25 * (cellq(P, mu, i - 1, j, k - 1) + cellq(P, mu, i, j, k - 1) + cellq(P, mu, i - 1, j, k) +
-                   cellq(P, mu, i, j, k));
+    return R(0.25) * (cellq(P, mu, i - 1, j, k - 1) + cellq(P, mu, i, j, k - 1) + cellq(P, mu, i - 1, j, k) +
+                      cellq(P, mu, i, j, k));
 }
-__device__ __forceinline__ double myz3(const Tank3P &P, const double *mu, int i, int j, int k)
+template <typename R>
+__device__ __forceinline__ R myz3(const Tank3P &P, const R *mu, int i, int j, int k)
 {
-    return 0.25 * (cellq(P, mu, i, j - 1, k - 1) + cellq(P, mu, i, j, k - 1) + cellq(P, mu, i, j - 1, k) +
-                   cellq(P, mu, i, j, k));
+    return R(0.25) * (cellq(P, mu, i, j - 1, k - 1) + cellq(P, mu, i, j, k - 1) + cellq(P, mu, i, j - 1, k) +
+                      cellq(P, mu, i, j, k));
 }
 #define U3(a, b, c) uq(P, X.V.u, a, b, c)
 #define V3(a, b, c) vq(P, X.V.v, a, b, c)
 #define W3(a, b, c) wq(P, X.V.w, X.V.win, a, b, c)
-__device__ __forceinline__ double txx(const Tank3P &P, const Visc3 &X, int i, int j, int k)
+template <typename R>
+__device__ __forceinline__ R txx(const Tank3P &P, const Visc3<R> &X, int i, int j, int k)
 {
-    return 2.0 * cellq(P, X.mu, i, j, k) * (U3(i + 1, j, k) - U3(i, j, k)) / P.h;
+    return R(2) * cellq(P, X.mu, i, j, k) * (U3(i + 1, j, k) - U3(i, j, k)) / cst3<R>(P).h;
 }
-__device__ __forceinline__ double tyy(const Tank3P &P, const Visc3 &X, int i, int j, int k)
+template <typename R>
+__device__ __forceinline__ R tyy(const Tank3P &P, const Visc3<R> &X, int i, int j, int k)
 {
-    return 2.0 * cellq(P, X.mu, i, j, k) * (V3(i, j + 1, k) - V3(i, j, k)) / P.h;
+    return R(2) * cellq(P, X.mu, i, j, k) * (V3(i, j + 1, k) - V3(i, j, k)) / cst3<R>(P).h;
 }
-__device__ __forceinline__ double tzz(const Tank3P &P, const Visc3 &X, int i, int j, int k)
+template <typename R>
+__device__ __forceinline__ R tzz(const Tank3P &P, const Visc3<R> &X, int i, int j, int k)
 {
-    return 2.0 * cellq(P, X.mu, i, j, k) * (W3(i, j, k + 1) - W3(i, j, k)) / P.h;
+    return R(2) * cellq(P, X.mu, i, j, k) * (W3(i, j, k + 1) - W3(i, j, k)) / cst3<R>(P).h;
 }
-__device__ __forceinline__ double txy(const Tank3P &P, const Visc3 &X, int i, int j, int k)
+template <typename R>
+__device__ __forceinline__ R txy(const Tank3P &P, const Visc3<R> &X, int i, int j, int k)
 {
-    return mxy3(P, X.mu, i, j, k) * ((U3(i, j, k) - U3(i, j - 1, k)) / P.h + (V3(i, j, k) - V3(i - 1, j, k)) / P.h);
+    const R h = cst3<R>(P).h;
+    return mxy3(P, X.mu, i, j, k) * ((U3(i, j, k) - U3(i, j - 1, k)) / h + (V3(i, j, k) - V3(i - 1, j, k)) / h);
 }
-__device__ __forceinline__ double txz(const Tank3P &P, const Visc3 &X, int i, int j, int k)
+template <typename R>
+__device__ __forceinline__ R txz(const Tank3P &P, const Visc3<R> &X, int i, int j, int k)
 {
-    return mxz3(P, X.mu, i, j, k) * ((U3(i, j, k) - U3(i, j, k - 1)) / P.h + (W3(i, j, k) - W3(i - 1, j, k)) / P.h);
+    const R h = cst3<R>(P).h;
+    return mxz3(P, X.mu, i, j, k) * ((U3(i, j, k) - U3(i, j, k - 1)) / h + (W3(i, j, k) - W3(i - 1, j, k)) / h);
 }
-__device__ __forceinline__ double tyz(const Tank3P &P, const Visc3 &X, int i, int j, int k)
+template <typename R>
+__device__ __forceinline__ R tyz(const Tank3P &P, const Visc3<R> &X, int i, int j, int k)
 {
-    return myz3(P, X.mu, i, j, k) * ((V3(i, j, k) - V3(i, j, k - 1)) / P.h + (W3(i, j, k) - W3(i, j - 1, k)) / P.h);
+    const R h = cst3<R>(P).h;
+    return myz3(P, X.mu, i, j, k) * ((V3(i, j, k) - V3(i, j, k - 1)) / h + (W3(i, j, k) - W3(i, j - 1, k)) / h);
 }
 #undef U3
 #undef V3
 #undef W3
-__device__ double visc3(const Tank3P &P, const Visc3 &X, int comp, int i, int j, int k)
+template <typename R>
+__device__ R visc3(const Tank3P &P, const Visc3<R> &X, int comp, int i, int j, int k)
 {
-    const double h = P.h;
+    const R h = cst3<R>(P).h;
     if (comp == 0)
         return ((txx(P, X, i, j, k) - txx(P, X, i - 1, j, k)) / h + (txy(P, X, i, j + 1, k) - txy(P, X, i, j, k)) / h) +
                (txz(P, X, i, j, k + 1) - txz(P, X, i, j, k)) / h;
@@ -458,16 +556,17 @@ __device__ double visc3(const Tank3P &P, const Visc3 &X, int comp, int i, int j,
            (tyz(P, X, i, j + 1, k) - tyz(P, X, i, j, k)) / h;
 }
 // interior-formula diagonal (the Jacobi splitting only)
-__device__ double vdiag3(const Tank3P &P, const double *mu, int comp, int i, int j, int k)
+template <typename R>
+__device__ R vdiag3(const Tank3P &P, const R *mu, int comp, int i, int j, int k)
 {
-    const double h2 = P.h * P.h;
+    const R h2 = cst3<R>(P).h * cst3<R>(P).h;
     if (comp == 0)
-        return -(2.0 * cellq(P, mu, i, j, k) + 2.0 * cellq(P, mu, i - 1, j, k) + mxy3(P, mu, i, j + 1, k) +
+        return -(R(2) * cellq(P, mu, i, j, k) + R(2) * cellq(P, mu, i - 1, j, k) + mxy3(P, mu, i, j + 1, k) +
                  mxy3(P, mu, i, j, k) + mxz3(P, mu, i, j, k + 1) + mxz3(P, mu, i, j, k)) / h2;
     if (comp == 1)
-        return -(2.0 * cellq(P, mu, i, j, k) + 2.0 * cellq(P, mu, i, j - 1, k) + mxy3(P, mu, i + 1, j, k) +
+        return -(R(2) * cellq(P, mu, i, j, k) + R(2) * cellq(P, mu, i, j - 1, k) + mxy3(P, mu, i + 1, j, k) +
                  mxy3(P, mu, i, j, k) + myz3(P, mu, i, j, k + 1) + myz3(P, mu, i, j, k)) / h2;
-    return -(2.0 * cellq(P, mu, i, j, k) + 2.0 * cellq(P, mu, i, j, k - 1) + mxz3(P, mu, i + 1, j, k) +
+    return -(R(2) * cellq(P, mu, i, j, k) + R(2) * cellq(P, mu, i, j, k - 1) + mxz3(P, mu, i + 1, j, k) +
              mxz3(P, mu, i, j, k) + myz3(P, mu, i, j + 1, k) + myz3(P, mu, i, j, k)) / h2;
 }
 
@@ -493,63 +592,68 @@ __device__ __forceinline__ bool face_of(const Tank3P &P, int comp, int &i, int &
     return true;
 }
 
+template <typename R>
 struct MomIn {
-    const double *rho_n, *mu_n, *chi1, *rf1, *p;
-    Vel3 V;                      // u^n, v^n, w^n with w_in(t^n)
-    const double *dampu, *vortc, *vortf;  // damping weight at u-faces; vorticity damping at cell / face heights
-    double dt, zd1, g, ikp;
+    const R *rho_n, *mu_n, *chi1, *rf1;
+    const double *p;                       // p^{n-1/2} (FP64: its differences are taken before rounding)
+    Vel3<R> V;                             // u^n, v^n, w^n with w_in(t^n)
+    const R *dampu, *vortc, *vortf;        // damping weight at u-faces; vorticity damping at cell / face heights
+    R dt, zd1, g, ikp;
 };
 
-__global__ void __launch_bounds__(128) k3t_momentum(Tank3P P, MomIn M, int comp, double *__restrict__ D,
-                                                    double *__restrict__ R)
+template <typename R>
+__global__ void __launch_bounds__(128) k3t_momentum(Tank3P P, MomIn<R> M, int comp, R *__restrict__ Dout,
+                                                    R *__restrict__ Rout)
 {
     pdl_entry();
     int i, j, k;
     long long f;
     if (!face_of(P, comp, i, j, k, f)) return;
-    double rb, C;
-    transport3(P, M.rho_n, M.V, comp, i, j, k, M.dt, rb, C);
-    const Visc3 X{M.mu_n, M.V};
+    R rb, C;
+    transport3<R>(P, M.rho_n, M.V, comp, i, j, k, M.dt, rb, C);
+    const Visc3<R> X{M.mu_n, M.V};
     const double h = P.h;
     const int ci = comp == 0 ? i - 1 : i, cj = comp == 1 ? j - 1 : j, ck = comp == 2 ? k - 1 : k;
-    const double chi = 0.5 * (cellq(P, M.chi1, ci, cj, ck) + cellq(P, M.chi1, i, j, k));
-    const double al = comp == 0 ? M.dampu[i] : P.damp[i];
-    const double vd = comp == 2 ? M.vortf[k] : M.vortc[k];
-    D[f] = rb / M.dt + chi * M.ikp + al * rb / M.dt + vd;
+    const R chi = R(0.5) * (cellq(P, M.chi1, ci, cj, ck) + cellq(P, M.chi1, i, j, k));
+    const R al = comp == 0 ? M.dampu[i] : dampc<R>(P, i);
+    const R vd = comp == 2 ? M.vortf[k] : M.vortc[k];
+    Dout[f] = rb / M.dt + chi * M.ikp + al * rb / M.dt + vd;
     const double pc = k < P.nz ? M.p[((long long)k * P.ny + j) * P.nx + i] : 0.0;
     if (comp == 0) {
-        R[f] = ruq(P, M.rho_n, i, j, k) * M.V.u[f] / M.dt - C + 0.5 * visc3(P, X, 0, i, j, k) -
-               (pc - M.p[((long long)k * P.ny + j) * P.nx + i - 1]) / h;
+        Rout[f] = ruq(P, M.rho_n, i, j, k) * M.V.u[f] / M.dt - C + R(0.5) * visc3<R>(P, X, 0, i, j, k) -
+                  R((pc - M.p[((long long)k * P.ny + j) * P.nx + i - 1]) / h);
     } else if (comp == 1) {
-        R[f] = rvq(P, M.rho_n, i, j, k) * M.V.v[f] / M.dt - C + 0.5 * visc3(P, X, 1, i, j, k) -
-               (pc - M.p[((long long)k * P.ny + j - 1) * P.nx + i]) / h;
+        Rout[f] = rvq(P, M.rho_n, i, j, k) * M.V.v[f] / M.dt - C + R(0.5) * visc3<R>(P, X, 1, i, j, k) -
+                  R((pc - M.p[((long long)k * P.ny + j - 1) * P.nx + i]) / h);
     } else {
-        const double rf = 0.5 * (cellq(P, M.rf1, i, j, k - 1) + cellq(P, M.rf1, i, j, k));
+        const R rf = R(0.5) * (cellq(P, M.rf1, i, j, k - 1) + cellq(P, M.rf1, i, j, k));
         const double pb = M.p[((long long)(k - 1) * P.ny + j) * P.nx + i];
         const double gp = k < P.nz ? (pc - pb) / h : -2.0 * pb / h;
-        R[f] = rwq(P, M.rho_n, i, j, k) * M.V.w[f] / M.dt - C + 0.5 * visc3(P, X, 2, i, j, k) - rf * M.g +
-               chi * M.zd1 * M.ikp - gp;
+        Rout[f] = rwq(P, M.rho_n, i, j, k) * M.V.w[f] / M.dt - C + R(0.5) * visc3<R>(P, X, 2, i, j, k) - rf * M.g +
+                  chi * M.zd1 * M.ikp - R(gp);
     }
 }
 
 // one Crank-Nicolson Jacobi sweep of component comp: B = (R + (L(A) - ld A) / 2) / (D - ld / 2)
-__global__ void __launch_bounds__(128) k3t_jacobi(Tank3P P, const double *__restrict__ mu1, Vel3 A, int comp,
-                                                  const double *__restrict__ D, const double *__restrict__ R,
-                                                  double *__restrict__ B)
+template <typename R>
+__global__ void __launch_bounds__(128) k3t_jacobi(Tank3P P, const R *__restrict__ mu1, Vel3<R> A, int comp,
+                                                  const R *__restrict__ D, const R *__restrict__ Rr,
+                                                  R *__restrict__ B)
 {
     pdl_entry();
     int i, j, k;
     long long f;
     if (!face_of(P, comp, i, j, k, f)) return;
-    const Visc3 X{mu1, A};
-    const double ld = vdiag3(P, mu1, comp, i, j, k);
-    const double a = comp == 0 ? A.u[f] : comp == 1 ? A.v[f] : A.w[f];
-    B[f] = (R[f] + 0.5 * (visc3(P, X, comp, i, j, k) - ld * a)) / (D[f] - 0.5 * ld);
+    const Visc3<R> X{mu1, A};
+    const R ld = vdiag3<R>(P, mu1, comp, i, j, k);
+    const R a = comp == 0 ? A.u[f] : comp == 1 ? A.v[f] : A.w[f];
+    B[f] = (Rr[f] + R(0.5) * (visc3<R>(P, X, comp, i, j, k) - ld * a)) / (D[f] - R(0.5) * ld);
 }
 
 // Dirichlet faces of the predictor: u_in(t1) at x = 0, u = 0 at the outlet, v = 0
 // on the side walls, w = 0 on the bed
-__global__ void k3t_dirichlet(Tank3P P, const double *__restrict__ uin1, double *u, double *v, double *w)
+template <typename R>
+__global__ void k3t_dirichlet(Tank3P P, const R *__restrict__ uin1, R *u, R *v, R *w)
 {
     pdl_entry();
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
@@ -558,18 +662,19 @@ __global__ void k3t_dirichlet(Tank3P P, const double *__restrict__ uin1, double 
         const int k = a / ny, j = a - k * ny;
         const long long r = ((long long)k * ny + j) * (nx + 1);
         u[r] = uin1[k];
-        u[r + nx] = 0.0;
+        u[r + nx] = R(0);
     }
     if (a < nx * nz) {
         const int k = a / nx, i = a - k * nx;
-        v[((long long)k * (ny + 1)) * nx + i] = 0.0;
-        v[((long long)k * (ny + 1) + ny) * nx + i] = 0.0;
+        v[((long long)k * (ny + 1)) * nx + i] = R(0);
+        v[((long long)k * (ny + 1) + ny) * nx + i] = R(0);
     }
-    if (a < nx * ny) w[a] = 0.0;
+    if (a < nx * ny) w[a] = R(0);
 }
 
-// beta = 1 / D on the solved faces, 0 on the walls and the bed; rhs = -h div u*
-__global__ void k3t_beta(Tank3P P, int comp, const double *__restrict__ D, double *__restrict__ beta, long long n)
+// beta = 1 / D on the solved faces, 0 on the walls and the bed (FP64 coefficients)
+template <typename R>
+__global__ void k3t_beta(Tank3P P, int comp, const R *__restrict__ D, double *__restrict__ beta, long long n)
 {
     pdl_entry();
     const long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -584,10 +689,12 @@ __global__ void k3t_beta(Tank3P P, int comp, const double *__restrict__ D, doubl
     } else {
         wall = f < (long long)P.nx * P.ny;
     }
-    beta[f] = wall ? 0.0 : 1.0 / D[f];
+    beta[f] = wall ? 0.0 : double(R(1) / D[f]);
 }
 
-__global__ void __launch_bounds__(128) k3t_rhs(Tank3P P, Vel3 S, double *__restrict__ rhs)
+// rhs = -h div u* (FP64 from the predictor's values)
+template <typename R>
+__global__ void __launch_bounds__(128) k3t_rhs(Tank3P P, Vel3<R> S, double *__restrict__ rhs)
 {
     pdl_entry();
     Cell3 q;
@@ -595,11 +702,13 @@ __global__ void __launch_bounds__(128) k3t_rhs(Tank3P P, Vel3 S, double *__restr
     const int nx = P.nx, ny = P.ny;
     const long long fu = ((long long)q.k * ny + q.j) * (nx + 1) + q.i, fv = ((long long)q.k * (ny + 1) + q.j) * nx + q.i;
     const long long pl = (long long)nx * ny;
-    rhs[q.c] = -P.h * (((S.u[fu + 1] - S.u[fu]) + (S.v[fv + nx] - S.v[fv])) + (S.w[q.c + pl] - S.w[q.c]));
+    rhs[q.c] = -P.h * (((double(S.u[fu + 1]) - double(S.u[fu])) + (double(S.v[fv + nx]) - double(S.v[fv]))) +
+                       (double(S.w[q.c + pl]) - double(S.w[q.c])));
 }
 
-// u^{n+1} = u* - beta grad phi (top w face: the ghost -phi); p += phi
-__global__ void k3t_project(Tank3P P, int comp, const double *__restrict__ S, const double *__restrict__ beta,
+// u^{n+1} = u* - beta grad phi in FP64 (top w face: the ghost -phi); p += phi
+template <typename R>
+__global__ void k3t_project(Tank3P P, int comp, const R *__restrict__ S, const double *__restrict__ beta,
                             const double *__restrict__ phi, double *__restrict__ out, long long n)
 {
     pdl_entry();
@@ -607,7 +716,7 @@ __global__ void k3t_project(Tank3P P, int comp, const double *__restrict__ S, co
     if (f >= n) return;
     const int nx = P.nx, ny = P.ny, nz = P.nz;
     const double ih = 1.0 / P.h;
-    double a = S[f];
+    double a = double(S[f]);
     if (comp == 0) {
         const int i = (int)(f % (nx + 1));
         const long long r = f / (nx + 1);
@@ -636,6 +745,20 @@ __global__ void k3t_add(long long n, const double *__restrict__ a, double *__res
     if (c < n) b[c] += a[c];
 }
 
+// FP32 working copies: out = float(in) / double(in)
+__global__ void k3t_narrow(long long n, const double *__restrict__ in, float *__restrict__ out)
+{
+    pdl_entry();
+    const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c < n) out[c] = float(in[c]);
+}
+__global__ void k3t_widen(long long n, const float *__restrict__ in, double *__restrict__ out)
+{
+    pdl_entry();
+    const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c < n) out[c] = double(in[c]);
+}
+
 constexpr int kRT = 256;  // threads of the reduction kernels
 
 __device__ double block_sum3(double v, double *sh)
@@ -649,11 +772,11 @@ __device__ double block_sum3(double v, double *sh)
     return sh[0];
 }
 
-// heave force, Eq. int_fh, over the faces of a box around the cylinder
-// [i0, i1) x [j0, j1) x [k0, k1) of cells (a block per (face kind, layer k))
+// heave force, Eq. int_fh (FP64), over the faces of a box around the cylinder
+// [i0, i1) x [j0, j1) x [k0, k1) of cells (a block per (layer k, face kind))
 __global__ void __launch_bounds__(kRT) k3t_force(Tank3P P, const double *__restrict__ p, const double *__restrict__ mu,
-                                                 Vel3 V, double zc, int i0, int i1, int j0, int j1, int k0, int k1,
-                                                 double *__restrict__ part)
+                                                 Vel3<double> V, double zc, int i0, int i1, int j0, int j1, int k0,
+                                                 int k1, double *__restrict__ part)
 {
     pdl_entry();
     __shared__ double sh[kRT];
@@ -721,7 +844,7 @@ __global__ void __launch_bounds__(kRT) k3t_sum(const double *__restrict__ part, 
 }
 
 // ||h div u||^2 partials, one per block of cells
-__global__ void __launch_bounds__(kRT) k3t_div2(Tank3P P, Vel3 S, double *__restrict__ part)
+__global__ void __launch_bounds__(kRT) k3t_div2(Tank3P P, Vel3<double> S, double *__restrict__ part)
 {
     pdl_entry();
     __shared__ double sh[kRT];
@@ -732,7 +855,8 @@ __global__ void __launch_bounds__(kRT) k3t_div2(Tank3P P, Vel3 S, double *__rest
         const long long r = c / P.nx;
         const int j = (int)(r % P.ny), k = (int)(r / P.ny);
         const long long fu = r * (P.nx + 1) + i, fv = ((long long)k * (P.ny + 1) + j) * P.nx + i;
-        const double d = P.h * (((S.u[fu + 1] - S.u[fu]) + (S.v[fv + P.nx] - S.v[fv])) + (S.w[c + (long long)P.nx * P.ny] - S.w[c]));
+        const double d = P.h * (((S.u[fu + 1] - S.u[fu]) + (S.v[fv + P.nx] - S.v[fv])) +
+                                (S.w[c + (long long)P.nx * P.ny] - S.w[c]));
         a += d * d;
     }
     const double s = block_sum3(a, sh);
@@ -815,20 +939,31 @@ void airy_host(const Waves3 &W, double depth, double h, double x, double z, doub
     *wo = blend * sw;
 }
 
-// nit Sussman pseudo-steps on the field s (scratch T->s0, T->s1)
-int reinit_buf(wec_tank3 *T, double *s, int nit, double t)
+// eta at the three ghost columns at time t (host, FP64)
+Ghost3 ghost_at(const wec_tank3 *T, double t)
 {
-    const double dtau = 0.3 * T->P.h;
-    WEC_CK(cudaMemcpyAsync(T->s0, s, T->nc * 8, cudaMemcpyDeviceToDevice, T->st));
+    const int n = T->P.ncomp;
+    const Waves3 W{n, T->hwave.data(), T->hwave.data() + n, T->hwave.data() + 2 * n, T->hwave.data() + 3 * n};
+    Ghost3 G;
+    for (int m = 0; m < 3; ++m) G.e[m] = eta_host(W, -(m + 0.5) * T->P.h, t);
+    return G;
+}
+
+// nit Sussman pseudo-steps on the field s (scratch s0, s1 of the same type)
+template <typename R>
+int reinit_buf(wec_tank3 *T, R *s, R *s0, R *s1, int nit, double t)
+{
+    const double dtau = 0.3 * T->P.h, b = sizeof(R);
+    WEC_CK(cudaMemcpyAsync(s0, s, T->nc * sizeof(R), cudaMemcpyDeviceToDevice, T->st));
     for (int it = 0; it < nit; ++it) {
         {
-            WEC_PROF("tank3_reinit", 0, 24.0 * T->nc, T->st);
-            launch_k(k3t_reinit_stage, grid3(T->P), 128, 0, T->st, T->P, (const double *)s, (const double *)T->s0,
-                     T->s1, t, dtau, 1);
+            WEC_PROF("tank3_reinit", 0, 3.0 * b * T->nc, T->st);
+            launch_k(k3t_reinit_stage<R>, grid3(T->P), 128, 0, T->st, T->P, (const R *)s, (const R *)s0, s1,
+                     ghost_at(T, t), dtau, 1);
         }
-        WEC_PROF("tank3_reinit", 0, 32.0 * T->nc, T->st);
-        launch_k(k3t_reinit_stage, grid3(T->P), 128, 0, T->st, T->P, (const double *)T->s1, (const double *)T->s0,
-                 s, t, dtau, 2);
+        WEC_PROF("tank3_reinit", 0, 4.0 * b * T->nc, T->st);
+        launch_k(k3t_reinit_stage<R>, grid3(T->P), 128, 0, T->st, T->P, (const R *)s1, (const R *)s0, s,
+                 ghost_at(T, t), dtau, 2);
     }
     WEC_CK(cudaGetLastError());
     return WEC_OK;
@@ -838,6 +973,204 @@ int reinit_buf(wec_tank3 *T, double *s, int nit, double t)
 }  // namespace wec
 
 using namespace wec;
+
+// One step in working type R (double: the FP64 stencils; float: FP32 working
+// copies of sigma and the velocities, refreshed from the FP64 state at the
+// start of the step, with FP32 materials, advection, reinitialisation,
+// transport, viscous terms and Jacobi sweeps).  The force (from the FP64
+// materials at n), the heave, beta and the right-hand side, the solve, the
+// projection and the persistent fields are FP64 in both.
+template <typename R>
+static int tank3_step_impl(wec_tank3 *T, Work3<R> &W, double dt, double pto_force, wec_step_result *out)
+{
+    constexpr bool f32 = sizeof(R) == 4;
+    const Tank3P &P = T->P;
+    cudaStream_t st = T->st;
+    const int nx = P.nx, ny = P.ny, nz = P.nz;
+    const double h = P.h, t0 = T->t, t1 = T->t + dt;
+    // boundary data of this step (host): u_in(t1) at the cell layers, w_in(t0)
+    // and w_in(t1) at the face heights, vorticity damping at cell / face heights
+    std::vector<double> hb((size_t)5 * nz + 3);
+    const std::vector<double> &hw = T->hwave;
+    const Waves3 Wv{P.ncomp, hw.data(), hw.data() + P.ncomp, hw.data() + 2 * P.ncomp, hw.data() + 3 * P.ncomp};
+    double *uin1 = hb.data(), *win0 = uin1 + nz, *win1 = win0 + nz + 1, *vc = win1 + nz + 1, *vf = vc + nz;
+    for (int k = 0; k < nz; ++k) {
+        double uu, ww;
+        airy_host(Wv, P.depth, h, 0.0, (k + 0.5) * h, t1, &uu, &ww);
+        uin1[k] = uu;
+    }
+    for (int k = 0; k <= nz; ++k) {
+        double uu, ww;
+        airy_host(Wv, P.depth, h, 0.0, k * h, t0, &uu, &ww);
+        win0[k] = ww;
+        airy_host(Wv, P.depth, h, 0.0, k * h, t1, &uu, &ww);
+        win1[k] = ww;
+    }
+    auto vort = [&](double z) {
+        const double wd = 4.0 * h;
+        if (z < T->lz - wd) return 0.0;
+        const double zt = (z - T->lz) / wd;
+        return P.rho_a * (std::cos(kPi3 * zt) + 1.0) / (4.0 * dt);
+    };
+    for (int k = 0; k < nz; ++k) vc[k] = vort((k + 0.5) * h);
+    for (int k = 0; k <= nz; ++k) vf[k] = vort(k * h);
+    WEC_CK(cudaMemcpyAsync(T->bc, hb.data(), hb.size() * 8, cudaMemcpyHostToDevice, st));
+    std::vector<float> hbf;
+    if constexpr (f32) {
+        hbf.assign(hb.begin(), hb.end());
+        WEC_CK(cudaMemcpyAsync(W.bc, hbf.data(), hbf.size() * 4, cudaMemcpyHostToDevice, st));
+    }
+    const double *d_win0 = T->bc + nz, *d_win1 = d_win0 + nz + 1;
+    const R *r_uin1 = W.bc, *r_win0 = r_uin1 + nz, *r_win1 = r_win0 + nz + 1, *r_vc = r_win1 + nz + 1,
+            *r_vf = r_vc + nz;
+    if constexpr (f32) {  // FP32 working copies of the state
+        launch_k(k3t_narrow, nblk((long long)T->nc, 256), 256, 0, st, (long long)T->nc, (const double *)T->sig, W.sig);
+        launch_k(k3t_narrow, nblk((long long)T->nu, 256), 256, 0, st, (long long)T->nu, (const double *)T->u, W.u);
+        launch_k(k3t_narrow, nblk((long long)T->nv, 256), 256, 0, st, (long long)T->nv, (const double *)T->v, W.v);
+        launch_k(k3t_narrow, nblk((long long)T->nw, 256), 256, 0, st, (long long)T->nw, (const double *)T->w, W.w);
+    }
+
+    // (1) materials at n (FP64, for the force) and the heave force from
+    // p^{n-1/2}, u^n (Eq. int_fh)
+    {
+        WEC_PROF("tank3_materials", 0, 40.0 * T->nc, st);
+        launch_k(k3t_materials<double>, grid3(P), 128, 0, st, P, (const double *)T->sig, T->zc, T->rho, T->mu,
+                 T->rhof, T->chi);
+    }
+    if constexpr (f32) {
+        WEC_PROF("tank3_materials", 0, 20.0 * T->nc, st);
+        launch_k(k3t_materials<R>, grid3(P), 128, 0, st, P, (const R *)W.sig, T->zc, W.rho, W.mu, W.rf, W.chi);
+    }
+    double F = 0.0;
+    const int kcb = (int)(T->zc / h), mkb = (int)std::ceil(0.5 * P.blen / h) + 3;
+    if (P.has_body && std::min(nz, kcb + mkb + 1) > std::max(0, kcb - mkb)) {
+        const int mi = (int)std::ceil((P.br) / h) + 3, mk = mkb;
+        const int ic = (int)(P.bxc / h), jc = (int)(P.byc / h), kc = kcb;
+        const int i0 = std::max(0, ic - mi), i1 = std::min(nx, ic + mi + 1), j0 = std::max(0, jc - mi),
+                  j1 = std::min(ny, jc + mi + 1), k0 = std::max(0, kc - mk), k1 = std::min(nz, kc + mk + 1);
+        const Vel3<double> Vn{T->u, T->v, T->w, d_win0};
+        {
+            WEC_PROF("tank3_force", 0, 0.0, st);
+            launch_k(k3t_force, dim3(k1 - k0, 3), kRT, 0, st, P, (const double *)T->p, (const double *)T->mu, Vn,
+                     T->zc, i0, i1, j0, j1, k0, k1, T->part);
+        }
+        launch_k(k3t_sum, 1, kRT, 0, st, (const double *)T->part, 3 * (k1 - k0), T->part + 3 * nz + 1024);
+        WEC_CK(cudaMemcpyAsync(&F, T->part + 3 * nz + 1024, 8, cudaMemcpyDeviceToHost, st));
+        WEC_CK(cudaStreamSynchronize(st));
+    }
+    // (2) heave (the stabilised update of the 2D reading)
+    const double fpto = pto_force - T->pto_c * T->zdot;
+    double zd1 = T->zdot, zc1 = T->zc;
+    if (P.has_body) {
+        const double m = T->mass, ma = T->added_mass;
+        zd1 = T->zdot + (dt * (F - m * T->g + fpto) + ma * (T->zdot - T->zdot_prev)) / (m + ma);
+        zc1 = T->zc + 0.5 * dt * (T->zdot + zd1);
+    }
+    // (3) sigma: advection + damping zone, reinitialisation (ghosts at t0, t1)
+    {
+        WEC_PROF("tank3_advect", 0, sizeof(R) * (2.0 * T->nc + T->nu + T->nv + T->nw), st);
+        launch_k(k3t_advect<R>, grid3(P), 128, 0, st, P, (const R *)W.sig, (const R *)W.u, (const R *)W.v,
+                 (const R *)W.w, dt, ghost_at(T, t0), W.tmp);
+    }
+    if (int e = reinit_buf<R>(T, W.tmp, W.s0, W.s1, T->opts.n_reinit, t1)) return e;
+    // (4) materials at n+1 (rho^{n+1} itself is not used: s1 is scratch)
+    {
+        WEC_PROF("tank3_materials", 0, 5.0 * sizeof(R) * T->nc, st);
+        launch_k(k3t_materials<R>, grid3(P), 128, 0, st, P, (const R *)W.tmp, zc1, W.s1, W.mu1, W.rf1, W.chi1);
+    }
+    // (5) transport and the momentum system
+    MomIn<R> M{W.rho, W.mu, W.chi1, W.rf1, T->p, Vel3<R>{W.u, W.v, W.w, r_win0}, W.dampu, r_vc, r_vf, R(dt), R(zd1),
+               R(T->g), R(1.0 / T->kappa_p)};
+    const dim3 gu((nx - 1 + 127) / 128, ny, nz), gv((nx + 127) / 128, ny - 1 > 0 ? ny - 1 : 1, nz),
+        gw((nx + 127) / 128, ny, nz);
+    const dim3 gc[3] = {gu, gv, gw};
+    const double b = sizeof(R);
+    for (int c = 0; c < 3; ++c) {
+        if (c == 1 && ny < 2) continue;
+        const double nfc = c == 0 ? (nx - 1.0) * ny * nz : c == 1 ? nx * (ny - 1.0) * nz : (double)nx * ny * nz;
+        WEC_PROF("tank3_momentum", c, b * (4.0 * T->nc + T->nu + T->nv + T->nw + 2.0 * nfc) + 8.0 * T->nc, st);
+        launch_k(k3t_momentum<R>, gc[c], 128, 0, st, P, M, c, W.D[c], W.R3[c]);
+    }
+    // (6) Crank-Nicolson Jacobi sweeps from u^n with the Dirichlet faces at n+1
+    const size_t nf[3] = {T->nu, T->nv, T->nw};
+    R *src[3] = {W.u, W.v, W.w};
+    for (int c = 0; c < 3; ++c) WEC_CK(cudaMemcpyAsync(W.A[c], src[c], nf[c] * sizeof(R), cudaMemcpyDeviceToDevice, st));
+    {
+        const long long nd = std::max({(long long)ny * nz, (long long)nx * nz, (long long)nx * ny});
+        launch_k(k3t_dirichlet<R>, nblk(nd, 256), 256, 0, st, P, r_uin1, W.A[0], W.A[1], W.A[2]);
+    }
+    for (int c = 0; c < 3; ++c) WEC_CK(cudaMemcpyAsync(W.B[c], W.A[c], nf[c] * sizeof(R), cudaMemcpyDeviceToDevice, st));
+    for (int it = 0; it < T->opts.n_jacobi; ++it) {
+        const Vel3<R> Va{W.A[0], W.A[1], W.A[2], r_win1};
+        for (int c = 0; c < 3; ++c) {
+            if (c == 1 && ny < 2) continue;
+            const double nfc = c == 0 ? (nx - 1.0) * ny * nz : c == 1 ? nx * (ny - 1.0) * nz : (double)nx * ny * nz;
+            WEC_PROF("tank3_jacobi", c, b * (T->nc + T->nu + T->nv + T->nw + 3.0 * nfc), st);
+            launch_k(k3t_jacobi<R>, gc[c], 128, 0, st, P, (const R *)W.mu1, Va, c, (const R *)W.D[c],
+                     (const R *)W.R3[c], W.B[c]);
+        }
+        for (int c = 0; c < 3; ++c) std::swap(W.A[c], W.B[c]);
+    }
+    // (7) pressure increment: beta = 1 / D, b = -h div u* (FP64), phi from zero
+    wec_poisson *S = T->solver;
+    double *beta[3] = {S->L64[0].bu, S->L64[0].bv, S->L64[0].bw};
+    for (int c = 0; c < 3; ++c)
+        launch_k(k3t_beta<R>, nblk((long long)nf[c], 256), 256, 0, st, P, c, (const R *)W.D[c], beta[c],
+                 (long long)nf[c]);
+    if (int e = poisson_build(S, st)) return e;
+    launch_k(k3t_rhs<R>, grid3(P), 128, 0, st, P, Vel3<R>{W.A[0], W.A[1], W.A[2], r_win1}, T->rhs);
+    WEC_CK(cudaMemsetAsync(T->phi, 0, T->nc * 8, st));
+    WEC_CK(cudaGetLastError());
+    int iters = 0;
+    double relres = 0.0;
+    const int rc = poisson_solve(S, T->rhs, T->phi, T->opts.rtol, T->opts.max_iters, &iters, &relres);
+    if (rc != WEC_OK && rc != WEC_ERR_NOT_CONVERGED) return rc;
+    // (8) projection (FP64) and p += phi; sigma^{n+1}
+    double *dst[3] = {T->u, T->v, T->w};
+    for (int c = 0; c < 3; ++c)
+        launch_k(k3t_project<R>, nblk((long long)nf[c], 256), 256, 0, st, P, c, (const R *)W.A[c],
+                 (const double *)beta[c], (const double *)T->phi, dst[c], (long long)nf[c]);
+    launch_k(k3t_add, nblk((long long)T->nc, 256), 256, 0, st, (long long)T->nc, (const double *)T->phi, T->p);
+    if constexpr (f32)
+        launch_k(k3t_widen, nblk((long long)T->nc, 256), 256, 0, st, (long long)T->nc, (const float *)W.tmp, T->sig);
+    else
+        std::swap(T->sig, T->tmp);
+    // diagnostics: ||h div u||, eta at the probe column (x = probe_x, middle y)
+    const int G = 1024;
+    launch_k(k3t_div2, G, kRT, 0, st, P, Vel3<double>{T->u, T->v, T->w, d_win1}, T->part);
+    launch_k(k3t_sum, 1, kRT, 0, st, (const double *)T->part, G, T->part + 3 * nz + 1024 + 1);
+    double d2 = 0.0;
+    WEC_CK(cudaMemcpyAsync(&d2, T->part + 3 * nz + 1024 + 1, 8, cudaMemcpyDeviceToHost, st));
+    const int ip = std::min(std::max((int)std::floor(T->probe_x / h), 0), nx - 1), jp = ny / 2;
+    std::vector<double> col(nz);
+    WEC_CK(cudaMemcpy2DAsync(col.data(), 8, T->sig + (size_t)jp * nx + ip, (size_t)nx * ny * 8, 8, nz,
+                             cudaMemcpyDeviceToHost, st));
+    WEC_CK(cudaGetLastError());
+    WEC_CK(cudaStreamSynchronize(st));
+    double eta = std::nan("");
+    for (int k = 0; k + 1 < nz; ++k)
+        if (col[k] < 0.0 && col[k + 1] >= 0.0) {
+            eta = (k + 0.5) * h + h * col[k] / (col[k] - col[k + 1]) - P.depth;
+            break;
+        }
+    T->t = t1;
+    T->zc = zc1;
+    T->zdot_prev = T->zdot;
+    T->zdot = zd1;
+    if (out) {
+        out->t = T->t;
+        out->z = T->zc - T->zc0;
+        out->zdot = T->zdot;
+        out->f_hydro = F;
+        out->f_pto = fpto;
+        out->eta_probe = eta;
+        out->residual = relres;
+        out->div_norm = std::sqrt(d2);
+        out->iters = iters;
+        out->status = rc;
+    }
+    return rc;
+}
 
 extern "C" {
 
@@ -861,9 +1194,9 @@ int wec_tank3_create(const wec_grid3 *grid, const wec_fluids *fl, const wec_wave
                           !(body->kappa_p > 0.0) || !(body->added_mass >= 0.0)))
         return fail(WEC_ERR_INVALID, "tank3: the cylinder needs radius, length, mass, kappa_p > 0, added_mass >= 0");
     if (opts) {
-        if (opts->precision != WEC_PREC_FP64 && opts->precision != WEC_PREC_MIXED_MG)
-            return fail(WEC_ERR_INVALID, "tank3: precision must be WEC_PREC_FP64 or WEC_PREC_MIXED_MG (the 3D stencils "
-                                         "are FP64)");
+        if (opts->precision != WEC_PREC_FP64 && opts->precision != WEC_PREC_MIXED_MG &&
+            opts->precision != WEC_PREC_MIXED)
+            return fail(WEC_ERR_INVALID, "tank3: unknown precision");
         if (!(opts->rtol > 0.0) || opts->max_iters < 1 || opts->restart < 1 || opts->restart > kMaxRestart ||
             opts->n_reinit < 0 || opts->n_jacobi < 1 || opts->mg_pre < 1 || opts->mg_pre > 4 || opts->mg_post < 0 ||
             opts->mg_post > 4)
@@ -918,6 +1251,7 @@ int wec_tank3_create(const wec_grid3 *grid, const wec_fluids *fl, const wec_wave
         }
         hc[4 * (size_t)P.ncomp + i] = a;
     }
+    T->hwave.assign(hc.begin(), hc.begin() + 4 * (size_t)P.ncomp);
     T->nc = (size_t)nx * ny * nz;
     T->nu = (size_t)(nx + 1) * ny * nz;
     T->nv = (size_t)nx * (ny + 1) * nz;
@@ -945,6 +1279,20 @@ int wec_tank3_create(const wec_grid3 *grid, const wec_fluids *fl, const wec_wave
     P.kw = T->consts + 2 * P.ncomp;
     P.phase = T->consts + 3 * P.ncomp;
     P.damp = T->consts + 4 * P.ncomp;
+    {  // the constants in both working types, and the damping table in FP32
+        P.cd = Tank3C<double>{P.h, P.ih, P.depth, P.rho_w, P.rho_a, P.mu_w, P.mu_a, P.rho_s, P.bxc, P.byc, P.br, P.blen};
+        P.cf = Tank3C<float>{(float)P.h, (float)P.ih, (float)P.depth, (float)P.rho_w, (float)P.rho_a, (float)P.mu_w,
+                             (float)P.mu_a, (float)P.rho_s, (float)P.bxc, (float)P.byc, (float)P.br, (float)P.blen};
+        std::vector<float> df(nx);
+        for (int i = 0; i < nx; ++i) df[i] = (float)hc[4 * (size_t)P.ncomp + i];
+        e = cudaMalloc(&T->fconsts, (size_t)nx * 4);
+        if (e == cudaSuccess) e = cudaMemcpy(T->fconsts, df.data(), (size_t)nx * 4, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            wec_tank3_destroy(T);
+            return cuda_fail(e, "tank3 allocation");
+        }
+        P.dampf = T->fconsts;
+    }
     if (opts) {  // the step: its buffers, its solver, the initial state
         T->opts = *opts;
         T->stepping = true;
@@ -966,7 +1314,7 @@ int wec_tank3_create(const wec_grid3 *grid, const wec_fluids *fl, const wec_wave
             wec_tank3_destroy(T);
             return fail(WEC_ERR_NOMEM, "host allocation failed");
         }
-        const int sprec = opts->precision == WEC_PREC_FP64 ? WEC_PREC_FP64 : WEC_PREC_MIXED;
+        const int sprec = opts->precision == WEC_PREC_FP64 ? WEC_PREC_FP64 : WEC_PREC_MIXED;  // FP32 V-cycles
         if (int rc = poisson_init(T->solver, nx, ny, sprec, opts->restart, opts->mg_pre, opts->mg_post, T->st, nz)) {
             std::string msg = wec_last_error();
             wec_tank3_destroy(T);
@@ -1008,6 +1356,23 @@ int wec_tank3_create(const wec_grid3 *grid, const wec_fluids *fl, const wec_wave
         if (e == cudaSuccess)
             e = cudaMemcpy(dtab + eta.size() + uxz.size(), wxz.data(), wxz.size() * 8, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(T->tabs, du.data(), du.size() * 8, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && opts->precision == WEC_PREC_MIXED) {
+            // FP32 working copies of the stencils (WEC_PREC_MIXED)
+            Work3<float> &F = T->wf;
+            for (float **q : {&F.sig, &F.tmp, &F.s0, &F.s1, &F.rho, &F.mu, &F.rf, &F.chi, &F.mu1, &F.rf1, &F.chi1})
+                if (e == cudaSuccess) e = cudaMalloc(q, T->nc * 4);
+            const size_t nf3[3] = {T->nu, T->nv, T->nw};
+            if (e == cudaSuccess) e = cudaMalloc(&F.u, T->nu * 4);
+            if (e == cudaSuccess) e = cudaMalloc(&F.v, T->nv * 4);
+            if (e == cudaSuccess) e = cudaMalloc(&F.w, T->nw * 4);
+            for (int c = 0; c < 3; ++c)
+                for (float **q : {&F.D[c], &F.R3[c], &F.A[c], &F.B[c]})
+                    if (e == cudaSuccess) e = cudaMalloc(q, nf3[c] * 4);
+            if (e == cudaSuccess) e = cudaMalloc(&F.bc, (size_t)(5 * nz + 3) * 4);
+            if (e == cudaSuccess) e = cudaMalloc(&F.dampu, (size_t)(nx + 1) * 4);
+            std::vector<float> duf(du.begin(), du.end());
+            if (e == cudaSuccess) e = cudaMemcpy(F.dampu, duf.data(), duf.size() * 4, cudaMemcpyHostToDevice);
+        }
         if (e != cudaSuccess) {
             cudaFree(dtab);
             wec_tank3_destroy(T);
@@ -1016,8 +1381,8 @@ int wec_tank3_create(const wec_grid3 *grid, const wec_fluids *fl, const wec_wave
         launch_k(k3t_init, dim3((nx + 128) / 128, ny, nz), 128, 0, T->st, T->P, (const double *)dtab,
                  (const double *)(dtab + eta.size()), (const double *)(dtab + eta.size() + uxz.size()), T->sig, T->u,
                  T->w);
-        launch_k(k3t_materials, grid3(T->P), 128, 0, T->st, T->P, (const double *)T->sig, T->zc, T->rho, T->mu,
-                 T->rhof, T->chi);
+        launch_k(k3t_materials<double>, grid3(T->P), 128, 0, T->st, T->P, (const double *)T->sig, T->zc, T->rho,
+                 T->mu, T->rhof, T->chi);
         launch_k(k3t_hydrostatic, nblk((long long)nx * ny, 128), 128, 0, T->st, T->P, (const double *)T->rhof, T->g,
                  T->p);
         e = cudaGetLastError();
@@ -1041,6 +1406,12 @@ void wec_tank3_destroy(wec_tank3 *T)
         cudaFree(p);
     for (int c = 0; c < 3; ++c)
         for (double *p : {T->D[c], T->R[c], T->A[c], T->B[c]}) cudaFree(p);
+    Work3<float> &F = T->wf;
+    for (float *p : {F.sig, F.tmp, F.s0, F.s1, F.u, F.v, F.w, F.rho, F.mu, F.rf, F.chi, F.mu1, F.rf1, F.chi1, F.bc,
+                     F.dampu, T->fconsts})
+        cudaFree(p);
+    for (int c = 0; c < 3; ++c)
+        for (float *p : {F.D[c], F.R3[c], F.A[c], F.B[c]}) cudaFree(p);
     if (T->solver) {
         poisson_free(T->solver);
         delete T->solver;
@@ -1092,7 +1463,7 @@ int wec_tank3_materials(wec_tank3 *T, double zc)
     if (int e = tank3_check(T)) return e;
     {
         WEC_PROF("tank3_materials", 0, 40.0 * T->nc, T->st);
-        launch_k(k3t_materials, grid3(T->P), 128, 0, T->st, T->P, (const double *)T->sig, zc, T->rho, T->mu, T->rhof,
+        launch_k(k3t_materials<double>, grid3(T->P), 128, 0, T->st, T->P, (const double *)T->sig, zc, T->rho, T->mu, T->rhof,
                  T->chi);
     }
     WEC_CK(cudaGetLastError());
@@ -1106,8 +1477,8 @@ int wec_tank3_advect(wec_tank3 *T, double dt, double t)
     if (!(dt >= 0.0)) return fail(WEC_ERR_INVALID, "tank3_advect: dt must be >= 0");
     {
         WEC_PROF("tank3_advect", 0, 8.0 * (2.0 * T->nc + T->nu + T->nv + T->nw), T->st);
-        launch_k(k3t_advect, grid3(T->P), 128, 0, T->st, T->P, (const double *)T->sig, (const double *)T->u,
-                 (const double *)T->v, (const double *)T->w, dt, t, T->tmp);
+        launch_k(k3t_advect<double>, grid3(T->P), 128, 0, T->st, T->P, (const double *)T->sig, (const double *)T->u,
+                 (const double *)T->v, (const double *)T->w, dt, ghost_at(T, t), T->tmp);
     }
     WEC_CK(cudaGetLastError());
     std::swap(T->sig, T->tmp);
@@ -1119,7 +1490,7 @@ int wec_tank3_reinit(wec_tank3 *T, int nit, double t)
 {
     if (int e = tank3_check(T)) return e;
     if (nit < 0) return fail(WEC_ERR_INVALID, "tank3_reinit: nit must be >= 0");
-    if (int e = reinit_buf(T, T->sig, nit, t)) return e;
+    if (int e = reinit_buf<double>(T, T->sig, T->s0, T->s1, nit, t)) return e;
     WEC_CK(cudaStreamSynchronize(T->st));
     return WEC_OK;
 }
@@ -1141,159 +1512,18 @@ int wec_tank3_step(wec_tank3 *T, double dt, double pto_force, wec_step_result *o
     if (int e = tank3_check(T)) return e;
     if (!T->stepping) return fail(WEC_ERR_INVALID, "tank3_step: the tank was created without solver options");
     if (!(dt > 0.0)) return fail(WEC_ERR_INVALID, "tank3_step: dt must be > 0");
-    const Tank3P &P = T->P;
-    cudaStream_t st = T->st;
-    const int nx = P.nx, ny = P.ny, nz = P.nz;
-    const double h = P.h, t0 = T->t, t1 = T->t + dt;
-    // boundary data of this step (host): u_in(t1) at the cell layers, w_in(t0)
-    // and w_in(t1) at the face heights, vorticity damping at cell / face heights
-    std::vector<double> hb((size_t)3 * nz + 2 + nz + nz + 1);
-    std::vector<double> hw(4 * (size_t)P.ncomp);
-    WEC_CK(cudaMemcpyAsync(hw.data(), T->consts, hw.size() * 8, cudaMemcpyDeviceToHost, st));
-    WEC_CK(cudaStreamSynchronize(st));
-    const Waves3 W{P.ncomp, hw.data(), hw.data() + P.ncomp, hw.data() + 2 * P.ncomp, hw.data() + 3 * P.ncomp};
-    double *uin1 = hb.data(), *win0 = uin1 + nz, *win1 = win0 + nz + 1, *vc = win1 + nz + 1, *vf = vc + nz;
-    for (int k = 0; k < nz; ++k) {
-        double uu, ww;
-        airy_host(W, P.depth, h, 0.0, (k + 0.5) * h, t1, &uu, &ww);
-        uin1[k] = uu;
-    }
-    for (int k = 0; k <= nz; ++k) {
-        double uu, ww;
-        airy_host(W, P.depth, h, 0.0, k * h, t0, &uu, &ww);
-        win0[k] = ww;
-        airy_host(W, P.depth, h, 0.0, k * h, t1, &uu, &ww);
-        win1[k] = ww;
-    }
-    auto vort = [&](double z) {
-        const double wd = 4.0 * h;
-        if (z < T->lz - wd) return 0.0;
-        const double zt = (z - T->lz) / wd;
-        return P.rho_a * (std::cos(kPi3 * zt) + 1.0) / (4.0 * dt);
-    };
-    for (int k = 0; k < nz; ++k) vc[k] = vort((k + 0.5) * h);
-    for (int k = 0; k <= nz; ++k) vf[k] = vort(k * h);
-    WEC_CK(cudaMemcpyAsync(T->bc, hb.data(), hb.size() * 8, cudaMemcpyHostToDevice, st));
-    const double *d_uin1 = T->bc, *d_win0 = d_uin1 + nz, *d_win1 = d_win0 + nz + 1, *d_vc = d_win1 + nz + 1,
-                 *d_vf = d_vc + nz;
-
-    // (1) materials at n and the heave force from p^{n-1/2}, u^n (Eq. int_fh)
-    launch_k(k3t_materials, grid3(P), 128, 0, st, P, (const double *)T->sig, T->zc, T->rho, T->mu, T->rhof, T->chi);
-    double F = 0.0;
-    const int kcb = (int)(T->zc / h), mkb = (int)std::ceil(0.5 * P.blen / h) + 3;
-    if (P.has_body && std::min(nz, kcb + mkb + 1) > std::max(0, kcb - mkb)) {
-        const int mi = (int)std::ceil((P.br) / h) + 3, mk = (int)std::ceil(0.5 * P.blen / h) + 3;
-        const int ic = (int)(P.bxc / h), jc = (int)(P.byc / h), kc = (int)(T->zc / h);
-        const int i0 = std::max(0, ic - mi), i1 = std::min(nx, ic + mi + 1), j0 = std::max(0, jc - mi),
-                  j1 = std::min(ny, jc + mi + 1), k0 = std::max(0, kc - mk), k1 = std::min(nz, kc + mk + 1);
-        const Vel3 Vn{T->u, T->v, T->w, d_win0};
-        WEC_PROF("tank3_force", 0, 0.0, st);
-        launch_k(k3t_force, dim3(k1 - k0, 3), kRT, 0, st, P, (const double *)T->p, (const double *)T->mu, Vn, T->zc,
-                 i0, i1, j0, j1, k0, k1, T->part);
-        launch_k(k3t_sum, 1, kRT, 0, st, (const double *)T->part, 3 * (k1 - k0), T->part + 3 * nz + 1024);
-        WEC_CK(cudaMemcpyAsync(&F, T->part + 3 * nz + 1024, 8, cudaMemcpyDeviceToHost, st));
-        WEC_CK(cudaStreamSynchronize(st));
-    }
-    // (2) heave (the stabilised update of the 2D reading)
-    const double fpto = pto_force - T->pto_c * T->zdot;
-    double zd1 = T->zdot, zc1 = T->zc;
-    if (P.has_body) {
-        const double m = T->mass, ma = T->added_mass;
-        zd1 = T->zdot + (dt * (F - m * T->g + fpto) + ma * (T->zdot - T->zdot_prev)) / (m + ma);
-        zc1 = T->zc + 0.5 * dt * (T->zdot + zd1);
-    }
-    // (3) sigma: advection + damping zone, reinitialisation (ghosts at t0, t1)
-    {
-        WEC_PROF("tank3_advect", 0, 8.0 * (2.0 * T->nc + T->nu + T->nv + T->nw), st);
-        launch_k(k3t_advect, grid3(P), 128, 0, st, P, (const double *)T->sig, (const double *)T->u,
-                 (const double *)T->v, (const double *)T->w, dt, t0, T->tmp);
-    }
-    if (int e = reinit_buf(T, T->tmp, T->opts.n_reinit, t1)) return e;
-    // (4) materials at n+1 (rho^{n+1} itself is not used: s1 is scratch)
-    launch_k(k3t_materials, grid3(P), 128, 0, st, P, (const double *)T->tmp, zc1, T->s1, T->mu1, T->rf1, T->chi1);
-    // (5) transport and the momentum system
-    MomIn M{T->rho, T->mu, T->chi1, T->rf1, T->p, Vel3{T->u, T->v, T->w, d_win0}, T->tabs, d_vc, d_vf, dt, zd1, T->g,
-            1.0 / T->kappa_p};
-    const dim3 gu((nx - 1 + 127) / 128, ny, nz), gv((nx + 127) / 128, ny - 1 > 0 ? ny - 1 : 1, nz),
-        gw((nx + 127) / 128, ny, nz);
-    const dim3 gc[3] = {gu, gv, gw};
+    if (T->opts.precision == WEC_PREC_MIXED) return tank3_step_impl<float>(T, T->wf, dt, pto_force, out);
+    Work3<double> W;
+    W.sig = T->sig; W.tmp = T->tmp; W.s0 = T->s0; W.s1 = T->s1; W.u = T->u; W.v = T->v; W.w = T->w;
+    W.rho = T->rho; W.mu = T->mu; W.rf = T->rhof; W.chi = T->chi; W.mu1 = T->mu1; W.rf1 = T->rf1; W.chi1 = T->chi1;
     for (int c = 0; c < 3; ++c) {
-        if (c == 1 && ny < 2) continue;
-        WEC_PROF("tank3_momentum", c, 0.0, st);
-        launch_k(k3t_momentum, gc[c], 128, 0, st, P, M, c, T->D[c], T->R[c]);
+        W.D[c] = T->D[c]; W.R3[c] = T->R[c]; W.A[c] = T->A[c]; W.B[c] = T->B[c];
     }
-    // (6) Crank-Nicolson Jacobi sweeps from u^n with the Dirichlet faces at n+1
-    const size_t nf[3] = {T->nu, T->nv, T->nw};
-    double *src[3] = {T->u, T->v, T->w};
-    for (int c = 0; c < 3; ++c) WEC_CK(cudaMemcpyAsync(T->A[c], src[c], nf[c] * 8, cudaMemcpyDeviceToDevice, st));
-    {
-        const long long nd = std::max({(long long)ny * nz, (long long)nx * nz, (long long)nx * ny});
-        launch_k(k3t_dirichlet, nblk(nd, 256), 256, 0, st, P, d_uin1, T->A[0], T->A[1], T->A[2]);
-    }
-    for (int c = 0; c < 3; ++c) WEC_CK(cudaMemcpyAsync(T->B[c], T->A[c], nf[c] * 8, cudaMemcpyDeviceToDevice, st));
-    for (int it = 0; it < T->opts.n_jacobi; ++it) {
-        const Vel3 Va{T->A[0], T->A[1], T->A[2], d_win1};
-        for (int c = 0; c < 3; ++c) {
-            if (c == 1 && ny < 2) continue;
-            WEC_PROF("tank3_jacobi", c, 0.0, st);
-            launch_k(k3t_jacobi, gc[c], 128, 0, st, P, (const double *)T->mu1, Va, c, (const double *)T->D[c],
-                     (const double *)T->R[c], T->B[c]);
-        }
-        for (int c = 0; c < 3; ++c) std::swap(T->A[c], T->B[c]);
-    }
-    // (7) pressure increment: beta = 1 / D, b = -h div u*, phi from zero
-    wec_poisson *S = T->solver;
-    double *beta[3] = {S->L64[0].bu, S->L64[0].bv, S->L64[0].bw};
-    for (int c = 0; c < 3; ++c)
-        launch_k(k3t_beta, nblk((long long)nf[c], 256), 256, 0, st, P, c, (const double *)T->D[c], beta[c],
-                 (long long)nf[c]);
-    if (int e = poisson_build(S, st)) return e;
-    launch_k(k3t_rhs, grid3(P), 128, 0, st, P, Vel3{T->A[0], T->A[1], T->A[2], d_win1}, T->rhs);
-    WEC_CK(cudaMemsetAsync(T->phi, 0, T->nc * 8, st));
-    WEC_CK(cudaGetLastError());
-    int iters = 0;
-    double relres = 0.0;
-    const int rc = poisson_solve(S, T->rhs, T->phi, T->opts.rtol, T->opts.max_iters, &iters, &relres);
-    if (rc != WEC_OK && rc != WEC_ERR_NOT_CONVERGED) return rc;
-    // (8) projection and p += phi; sigma^{n+1}
-    for (int c = 0; c < 3; ++c)
-        launch_k(k3t_project, nblk((long long)nf[c], 256), 256, 0, st, P, c, (const double *)T->A[c],
-                 (const double *)beta[c], (const double *)T->phi, src[c], (long long)nf[c]);
-    launch_k(k3t_add, nblk((long long)T->nc, 256), 256, 0, st, (long long)T->nc, (const double *)T->phi, T->p);
-    std::swap(T->sig, T->tmp);
-    // diagnostics: ||h div u||, eta at the probe column (x = probe_x, middle y)
-    const int G = 1024;
-    launch_k(k3t_div2, G, kRT, 0, st, P, Vel3{T->u, T->v, T->w, d_win1}, T->part);
-    launch_k(k3t_sum, 1, kRT, 0, st, (const double *)T->part, G, T->part + 3 * nz + 1024 + 1);
-    double d2 = 0.0;
-    WEC_CK(cudaMemcpyAsync(&d2, T->part + 3 * nz + 1024 + 1, 8, cudaMemcpyDeviceToHost, st));
-    const int ip = std::min(std::max((int)std::floor(T->probe_x / h), 0), nx - 1), jp = ny / 2;
-    std::vector<double> col(nz);
-    WEC_CK(cudaMemcpy2DAsync(col.data(), 8, T->sig + (size_t)jp * nx + ip, (size_t)nx * ny * 8, 8, nz,
-                             cudaMemcpyDeviceToHost, st));
-    WEC_CK(cudaGetLastError());
-    WEC_CK(cudaStreamSynchronize(st));
-    double eta = std::nan("");
-    for (int k = 0; k + 1 < nz; ++k)
-        if (col[k] < 0.0 && col[k + 1] >= 0.0) {
-            eta = (k + 0.5) * h + h * col[k] / (col[k] - col[k + 1]) - P.depth;
-            break;
-        }
-    T->t = t1;
-    T->zc = zc1;
-    T->zdot_prev = T->zdot;
-    T->zdot = zd1;
-    if (out) {
-        out->t = T->t;
-        out->z = T->zc - T->zc0;
-        out->zdot = T->zdot;
-        out->f_hydro = F;
-        out->f_pto = fpto;
-        out->eta_probe = eta;
-        out->residual = relres;
-        out->div_norm = std::sqrt(d2);
-        out->iters = iters;
-        out->status = rc;
+    W.bc = T->bc;
+    W.dampu = T->tabs;
+    const int rc = tank3_step_impl<double>(T, W, dt, pto_force, out);
+    for (int c = 0; c < 3; ++c) {  // the Jacobi ping-pong swapped the buffers
+        T->A[c] = W.A[c]; T->B[c] = W.B[c];
     }
     return rc;
 }

@@ -93,6 +93,23 @@ def test_fp32_vcycle_path_error_against_the_oracle():
     t.close()
 
 
+def test_fp32_stencil_path_error_against_the_oracle():
+    # WEC_PREC_MIXED: the step's stencils in FP32 over FP32 working copies, the
+    # force, heave, solve and projection FP64; the error against the FP64 oracle
+    # after 20 steps is of FP32 size (stated, bounded by 1e-4)
+    c = _cfg(32, 8, 16, seed=6, rtol=1e-8)
+    t, o = wec.Tank3(c, precision=wec.PREC_MIXED), T3.OracleTank3(c)
+    for _ in range(20):
+        r, ro = t.step(c["dt"]), o.step(c["dt"])
+        assert r["status"] == 0 and r["residual"] <= 1e-8
+    vs = np.max(np.abs(o.get(T3.F_U)))
+    errs = {name: rel(t.get(fg), o.get(fo), vs if name == "v" else 1e-12) for fg, fo, name in FIELDS}
+    hz = abs(r["z"] - ro["z"]) / abs(ro["z"])
+    print(f"FP32 stencils, 20 steps: {errs}, heave {hz:.2e}")
+    assert max(errs.values()) < 1e-4
+    assert hz < 1e-4
+
+
 def test_full_size_tank_step():
     c = synth.tank3d(seed=0)
     t = wec.Tank3(c)
@@ -121,8 +138,6 @@ def test_invalid_step_uses():
     with pytest.raises(wec.WecError):  # created without solver options
         t.step(c["dt"])
     t.close()
-    with pytest.raises(wec.WecError):  # FP32 stencils are not built in 3D
-        wec.Tank3(c, precision=wec.PREC_MIXED)
     t = wec.Tank3(c)
     with pytest.raises(wec.WecError):
         t.step(0.0)

@@ -52,7 +52,7 @@ def test_materials_match_oracle(shape):
     nx, ny, nz = shape
     c = synth.tank3d(seed=1, nx=nx, ny=ny, nz=nz)
     s, *_ = _state(c, 3)
-    T = wec.Tank3(c)
+    T = wec.Tank3(c, step=False)
     T.set(wec.F3_SIGMA, s)
     zc = c["body"]["zc"] - 0.013
     m = T.materials(zc)
@@ -67,7 +67,7 @@ def test_advection_matches_oracle(shape):
     nx, ny, nz = shape
     c = synth.tank3d(seed=2, nx=nx, ny=ny, nz=nz)
     s, u, v, w = _state(c, 5)
-    T = wec.Tank3(c)
+    T = wec.Tank3(c, step=False)
     for fid, a in ((wec.F3_SIGMA, s), (wec.F3_U, u), (wec.F3_V, v), (wec.F3_W, w)):
         T.set(fid, a)
     T.advect(0.02, 0.37)
@@ -83,7 +83,7 @@ def test_reinitialisation_matches_oracle(shape):
     c = synth.tank3d(seed=3, nx=nx, ny=ny, nz=nz)
     s, *_ = _state(c, 7)
     s = 1.6 * s
-    T = wec.Tank3(c)
+    T = wec.Tank3(c, step=False)
     T.set(wec.F3_SIGMA, s)
     T.reinit(4, 0.11)
     ref = L3.Oracle3(c).reinit(s, 4, 0.11)
@@ -95,7 +95,7 @@ def test_chain_advect_reinit_materials():
     nx, ny, nz = 48, 16, 24
     c = synth.tank3d(seed=4, nx=nx, ny=ny, nz=nz)
     s, u, v, w = _state(c, 9)
-    T = wec.Tank3(c)
+    T = wec.Tank3(c, step=False)
     for fid, a in ((wec.F3_SIGMA, s), (wec.F3_U, u), (wec.F3_V, v), (wec.F3_W, w)):
         T.set(fid, a)
     O = L3.Oracle3(c)
@@ -118,7 +118,7 @@ def test_full_size_tank_sampled_cells():
     c = synth.tank3d(seed=0)
     nx, ny, nz = c["nx"], c["ny"], c["nz"]
     s, u, v, w = _state(c, 11)
-    T = wec.Tank3(c)
+    T = wec.Tank3(c, step=False)
     for fid, a in ((wec.F3_SIGMA, s), (wec.F3_U, u), (wec.F3_V, v), (wec.F3_W, w)):
         T.set(fid, a)
     zc = c["body"]["zc"]
@@ -147,7 +147,7 @@ def test_full_size_tank_sampled_cells():
 
 def test_invalid_uses_are_errors():
     c = synth.tank3d(seed=0, nx=16, ny=8, nz=8)
-    T = wec.Tank3(c)
+    T = wec.Tank3(c, step=False)
     with pytest.raises(ValueError):
         T.set(wec.F3_SIGMA, np.zeros((8, 8, 15)))
     with pytest.raises(wec.WecError):  # materials are not settable
