@@ -86,3 +86,32 @@ def tune_poisson3(shape, coef, b, precision, candidates=CANDIDATES_3D, rtol=1e-8
                       "iters": its})
     best = min(table, key=lambda r: r["ms_per_solve"])
     return (best["mg_pre"], best["mg_post"], best["restart"]), table
+
+
+CANDIDATES_TANK3 = ((2, 2, 20), (3, 3, 5))
+
+
+def tune_tank3(cfg, precision, candidates=CANDIDATES_TANK3, steps=2, warmup=1):
+    """Fastest (mg_pre, mg_post, restart) for a 3D tank (wec_tank3): each
+    candidate steps a fresh tank from the workload's initial state.  Returns
+    (best, table)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    table = []
+    for opts in candidates:
+        t = wec.Tank3(with_options(cfg, opts), precision=precision)
+        for _ in range(warmup):
+            t.step(cfg["dt"])
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        its = []
+        e0.record(stream)
+        for _ in range(steps):
+            its.append(t.step(cfg["dt"])["iters"])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t.close()
+        table.append({"mg_pre": opts[0], "mg_post": opts[1], "restart": opts[2],
+                      "ms_per_step": e0.elapsed_time(e1) / steps, "iters": statistics.mean(its)})
+    best = min(table, key=lambda r: r["ms_per_step"])
+    return (best["mg_pre"], best["mg_post"], best["restart"]), table
