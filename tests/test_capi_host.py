@@ -181,3 +181,38 @@ def test_binding_layer_table_matches_the_oracle():
     assert wec.net_param_shapes() == [tuple(s) for s in U.param_shapes(32)]
     assert [(k if k != "head" else "head", ci, co) for k, ci, co, _ in wec.NET_LAYERS] == \
         [(k, ci, co) for _, k, ci, co in U.layers(32)]
+
+
+@pytest.mark.parametrize("bad", ["nonuniform", "small", "rho", "precision", "restart", "radius", "kappa"])
+def test_tank3_create_rejects_invalid_arguments_on_host(lib, bad):
+    cfg = synth.tank3d(nx=16, ny=8, nz=8)
+    g = wec.Grid3(cfg["nx"], cfg["ny"], cfg["nz"], cfg["lx"], cfg["ly"], cfg["lz"], cfg["depth"])
+    f = wec.Fluids(cfg["rho_w"], cfg["rho_a"], cfg["mu_w"], cfg["mu_a"], cfg["g"])
+    amp, om, ph = np.array([0.01]), np.array([3.0]), np.array([0.0])
+    w = wec.Waves(1, wec._ptr(amp), wec._ptr(om), wec._ptr(ph), 6.0, 2.0, 1.0)
+    b = cfg["body"]
+    body = wec.Cylinder(1, b["xc"], b["yc"], b["radius"], b["length"], b["mass"], b["zc"], b["kappa_p"],
+                        b["added_mass"], 0.0)
+    o = wec.solver_opts(cfg["solver"])
+    if bad == "nonuniform":
+        g.lz = 2.0 * g.lz
+    elif bad == "small":
+        g.nz = 2
+    elif bad == "rho":
+        f.rho_w = 0.0
+    elif bad == "precision":
+        o.precision = 7
+    elif bad == "restart":
+        o.restart = 0
+    elif bad == "radius":
+        body.radius = -0.5
+    elif bad == "kappa":
+        body.kappa_p = 0.0
+    h = C.c_void_p(123)
+    code = lib.wec_tank3_create(C.byref(g), C.byref(f), C.byref(w), C.byref(body), C.byref(o), None, C.byref(h))
+    assert code == wec.WEC_ERR_INVALID
+    assert h.value is None
+    assert lib.wec_last_error().decode()
+    r = wec.StepResult()
+    assert lib.wec_tank3_step(None, 1e-3, 0.0, C.byref(r)) == wec.WEC_ERR_INVALID
+    lib.wec_tank3_destroy(None)
