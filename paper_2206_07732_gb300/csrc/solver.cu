@@ -396,20 +396,32 @@ __device__ __forceinline__ void warp_reduce_scatter(double (&a)[K], int lane)
     wrs_stage<K, 16, K>(a, lane);
 }
 
-template <int K>
-__device__ void block_dots_k(const double *__restrict__ V, const double *__restrict__ w, long long n, int nk,
-                             double (*sh)[KMAXV], double *bsm)
+// The CTA's partials of V_k . w (k < nk <= 32) into bsm[k], in fixed order, over
+// one grid-stride pass that also produces w: wof(c, v) returns w[c] (storing it
+// if it makes it) given v[q] = V_q[c] for q < nk when HOLD (the columns read once
+// per element, kept in registers for the update and the dots); without HOLD
+// (K = 32, where 2 K held values would not fit the register budget) v is unset
+// and the dots read V_q[c] again, from L1 right after the update read it.
+template <int K, typename F>
+__device__ __forceinline__ void block_dots_k(const double *V, long long n, int nk, F &&wof, double (*sh)[KMAXV],
+                                             double *bsm)
 {
+    constexpr bool HOLD = K <= 16;
     constexpr int P2 = K >= 32 ? 5 : K >= 16 ? 4 : K >= 8 ? 3 : K >= 4 ? 2 : K >= 2 ? 1 : 0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double a[K];
 #pragma unroll
     for (int q = 0; q < K; ++q) a[q] = 0.0;
     for (long long c = blockIdx.x * (long long)KT + threadIdx.x; c < n; c += (long long)gridDim.x * KT) {
-        const double wc = w[c];
+        double v[HOLD ? K : 1];
+        if constexpr (HOLD) {
+#pragma unroll
+            for (int q = 0; q < K; ++q) v[q] = q < nk ? V[(long long)q * n + c] : 0.0;
+        }
+        const double wc = wof(c, v);
 #pragma unroll
         for (int q = 0; q < K; ++q)
-            if (q < nk) a[q] += V[(long long)q * n + c] * wc;
+            if (q < nk) a[q] += (HOLD ? v[HOLD ? q : 0] : V[(long long)q * n + c]) * wc;
     }
     warp_reduce_scatter<K>(a, lane);
     if ((lane & ((32 >> P2) - 1)) == 0) {
@@ -424,23 +436,34 @@ __device__ void block_dots_k(const double *__restrict__ V, const double *__restr
     }
 }
 
-// The CTA's partials of V_k . w (k < nk <= 32) into bsm[k], in fixed order.
-__device__ void block_dots(const double *__restrict__ V, const double *__restrict__ w, long long n, int nk,
-                           double (*sh)[KMAXV], double *bsm)
+// nk <= KB (KB = 8: restarts up to 8, whose kernels hold few values per thread
+// and run more CTAs per SM; KB = 32: any restart)
+template <int KB, typename F>
+__device__ __forceinline__ void block_dots(const double *V, long long n, int nk, F &&wof, double (*sh)[KMAXV],
+                                          double *bsm)
 {
-    if (nk <= 1)
-        block_dots_k<1>(V, w, n, nk, sh, bsm);
-    else if (nk <= 2)
-        block_dots_k<2>(V, w, n, nk, sh, bsm);
-    else if (nk <= 4)
-        block_dots_k<4>(V, w, n, nk, sh, bsm);
-    else if (nk <= 8)
-        block_dots_k<8>(V, w, n, nk, sh, bsm);
-    else if (nk <= 16)
-        block_dots_k<16>(V, w, n, nk, sh, bsm);
-    else
-        block_dots_k<32>(V, w, n, nk, sh, bsm);
+    if (nk <= 1) {
+        block_dots_k<1>(V, n, nk, wof, sh, bsm);
+    } else if (nk <= 2) {
+        block_dots_k<2>(V, n, nk, wof, sh, bsm);
+    } else if (nk <= 4) {
+        block_dots_k<4>(V, n, nk, wof, sh, bsm);
+    } else if constexpr (KB <= 8) {
+        block_dots_k<8>(V, n, nk, wof, sh, bsm);
+    } else {
+        if (nk <= 8)
+            block_dots_k<8>(V, n, nk, wof, sh, bsm);
+        else if (nk <= 16)
+            block_dots_k<16>(V, n, nk, wof, sh, bsm);
+        else
+            block_dots_k<32>(V, n, nk, wof, sh, bsm);
+    }
 }
+
+// CTAs per SM the matrix-vector kernel is compiled for: 4 (64 registers) where
+// the dot products hold at most 8 sums per thread, else 2 (the Gram-Schmidt
+// kernel, holding the basis values as well: 3 and 2)
+constexpr int kb_blocks(int KB) { return KB <= 8 ? 4 : 2; }
 
 __device__ __forceinline__ void set_cond(unsigned long long h, int use, unsigned int v)
 {
@@ -493,7 +516,7 @@ __global__ void k_diag0(int nx, int ny, const double *__restrict__ bu, const dou
 }
 
 // bn = ||b||_2, tol = rtol bn.
-__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 2)
+__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 4)
     k_bnorm(long long n, const double *__restrict__ b, double *part, KState *ks)
 {
     pdl_entry();
@@ -521,7 +544,7 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 2)
 // A zero right-hand side gives x = 0.  Opens a new Arnoldi cycle unless done and
 // sets the WHILE condition to !done.
 template <int D>
-__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 2)
+__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 4)
     k_residual_norm(Op0 op, const double *__restrict__ d0, const double *__restrict__ b, double *x,
                     double *__restrict__ w, float *__restrict__ b32, double *sc, double *part, KState *ks, double *g,
                     int mode, unsigned long long hwhile, int use)
@@ -584,8 +607,8 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 2)
 // s_k = 1 / ||u_k|| in sc): the new vector w is built in place in column j+1.
 // w = A z_j = s_j A z'_j (z'_j = M u_j, the V-cycle being linear), and the
 // first Gram-Schmidt dot products h1_k = v_k . w = s_k (u_k . w), k <= j.
-template <int D>
-__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 2)
+template <int D, int KB>
+__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, kb_blocks(KB))
     k_matvec_dots(Op0 op, const double *__restrict__ d0, const double *__restrict__ Z, double *V,
                   const double *__restrict__ sc, double *part, double *h1, KState *ks)
 {
@@ -597,9 +620,15 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 2)
     const double *z = Z + (long long)j * n;
     double *w = V + (long long)(j + 1) * n;
     const double sj = sc[j];
-    for (long long c = blockIdx.x * (long long)KT + threadIdx.x; c < n; c += (long long)gridDim.x * KT)
-        w[c] = sj * (d0[c] * z[c] - op_offsum<D>(op, z, c));
-    block_dots(V, w, n, nk, sh, bsm);
+    // w and its dots in one pass (w is not read back)
+    block_dots<KB>(
+        V, n, nk,
+        [&](long long c, const auto &) {
+            const double r = sj * (d0[c] * z[c] - op_offsum<D>(op, z, c));
+            w[c] = r;
+            return r;
+        },
+        sh, bsm);
     cluster_partials(bsm, nk, part);
     if (!last_cluster(&ks->cnt[2])) return;
     final_partials(part, nk, gridDim.x / kCl, h1);
@@ -610,7 +639,8 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 2)
 
 // First Gram-Schmidt update w -= sum_k h1_k v_k = w - sum_k (h1_k s_k) u_k, then
 // h2_k = v_k . w.
-__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 2)
+template <int KB>
+__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, KB <= 8 ? 3 : 2)
     k_orth_dots(long long n, double *V, const double *__restrict__ sc, const double *__restrict__ h1, double *part,
                 double *h2, KState *ks)
 {
@@ -622,13 +652,23 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 2)
     double *w = V + (long long)(j + 1) * n;
     if (threadIdx.x < nk) hs[threadIdx.x] = h1[threadIdx.x] * sc[threadIdx.x];
     __syncthreads();
-    for (long long c = blockIdx.x * (long long)KT + threadIdx.x; c < n; c += (long long)gridDim.x * KT) {
-        double a = w[c];
-#pragma unroll 4
-        for (int k = 0; k < nk; ++k) a -= hs[k] * V[(long long)k * n + c];
-        w[c] = a;
-    }
-    block_dots(V, w, n, nk, sh, bsm);
+    // the update and the second dots in one pass over the basis (V_k[c] read once)
+    block_dots<KB>(
+        V, n, nk,
+        [&](long long c, const auto &v) {
+            constexpr int KH = std::extent<std::remove_reference_t<decltype(v)>>::value;
+            double a = w[c];
+            if (nk <= KH) {
+#pragma unroll
+                for (int k = 0; k < KH; ++k)
+                    if (k < nk) a -= hs[k] * v[k];
+            } else {
+                for (int k = 0; k < nk; ++k) a -= hs[k] * V[(long long)k * n + c];
+            }
+            w[c] = a;
+            return a;
+        },
+        sh, bsm);
     cluster_partials(bsm, nk, part);
     if (!last_cluster(&ks->cnt[2])) return;
     final_partials(part, nk, gridDim.x / kCl, h2);
@@ -643,7 +683,7 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 2)
 // counts the iteration, decides whether the cycle ends (converged estimate,
 // iteration cap, breakdown, or full basis), advances j otherwise, and sets the
 // IF condition.
-__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 2)
+__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 4)
     k_orth_norm(long long n, double *V, double *sc, float *__restrict__ b32, const double *__restrict__ h1,
                 const double *__restrict__ h2, double *part, KState *ks, double *H, double *cs, double *sn,
                 double *g, unsigned long long hif, int use)
@@ -1107,7 +1147,12 @@ void vcycle_t(wec_poisson *P, Level<T> *L, const T *b0, TO *x0, const int *bsel,
 // CTAs of the cluster reduction kernels that run as one wave on this GPU: the
 // scheduler places whole clusters inside a GPC, so the count comes from the
 // occupancy query, not from SMs x CTAs per SM.  Set once by poisson_init.
-int g_kgrid_max[2] = {kKrylovBlocks, kKrylovBlocks};  // 2D, 3D operator
+// the largest grid (CTAs) of each Krylov reduction kernel: its resident
+// clusters, at most kKrylovBlocks; res[d3], mv[d3][restart <= 8], od[restart <= 8]
+struct KGrids {
+    int bnorm = kCl, on = kCl, res[2] = {kCl, kCl}, mv[2][2] = {{kCl, kCl}, {kCl, kCl}}, od[2] = {kCl, kCl};
+};
+KGrids g_kg;
 
 template <typename K>
 int clusters_resident(K kern, int *out)
@@ -1128,26 +1173,34 @@ int clusters_resident(K kern, int *out)
 
 int set_kgrid_max()
 {
-    int c[7];
-    int e = clusters_resident(k_bnorm, &c[0]);
-    if (!e) e = clusters_resident(k_orth_dots, &c[1]);
-    if (!e) e = clusters_resident(k_orth_norm, &c[2]);
-    if (!e) e = clusters_resident(k_residual_norm<2>, &c[3]);
-    if (!e) e = clusters_resident(k_matvec_dots<2>, &c[4]);
-    if (!e) e = clusters_resident(k_residual_norm<3>, &c[5]);
-    if (!e) e = clusters_resident(k_matvec_dots<3>, &c[6]);
-    if (e) return e;
-    const int common = *std::min_element(c, c + 3);
-    const int m2 = std::min({common, c[3], c[4]}), m3 = std::min({common, c[5], c[6]});
-    g_kgrid_max[0] = std::max(1, std::min(m2, kKrylovBlocks / kCl)) * kCl;
-    g_kgrid_max[1] = std::max(1, std::min(m3, kKrylovBlocks / kCl)) * kCl;
-    return WEC_OK;
+    auto r = [](auto kern, int &g) {
+        int c = 0;
+        if (int e = clusters_resident(kern, &c)) return e;
+        g = std::max(1, std::min(c, kKrylovBlocks / kCl)) * kCl;
+        return (int)WEC_OK;
+    };
+    KGrids &k = g_kg;
+    int e = r(k_bnorm, k.bnorm);
+    if (!e) e = r(k_orth_norm, k.on);
+    if (!e) e = r(k_residual_norm<2>, k.res[0]);
+    if (!e) e = r(k_residual_norm<3>, k.res[1]);
+    if (!e) e = r(k_matvec_dots<2, 32>, k.mv[0][0]);
+    if (!e) e = r(k_matvec_dots<2, 8>, k.mv[0][1]);
+    if (!e) e = r(k_matvec_dots<3, 32>, k.mv[1][0]);
+    if (!e) e = r(k_matvec_dots<3, 8>, k.mv[1][1]);
+    if (!e) e = r(k_orth_dots<32>, k.od[0]);
+    if (!e) e = r(k_orth_dots<8>, k.od[1]);
+    return e;
 }
 
-// Reduction kernels: a multiple of the cluster size, at most one wave.
-int kgrid(long long n, bool d3)
+// Reduction kernels: a multiple of the cluster size, at most one wave of the
+// kernel's resident clusters (gmax).  Vectors that stay in L2 (up to 2^22
+// cells) take at most 2 CTAs per SM: those passes are latency-bound and half
+// the partials shorten the final reduction.
+int kgrid(long long n, int gmax)
 {
-    const long long g = std::min<long long>(nblk(n, KT), g_kgrid_max[d3 ? 1 : 0]);
+    if (n <= (1ll << 22)) gmax = std::min(gmax, kKrylovBlocks / 2);
+    const long long g = std::min<long long>(nblk(n, KT), gmax);
     return (int)((g + kCl - 1) / kCl * kCl);
 }
 
@@ -1167,9 +1220,10 @@ double nfaces(const wec_poisson *P)
     return (nx + 1.0) * ny * nz + nx * (ny + 1.0) * nz + nx * ny * (nz + 1.0);
 }
 
-void launch_residual_norm(wec_poisson *P, int G, const double *b, double *x, float *b32, int mode,
-                          unsigned long long hw, int use, cudaStream_t st)
+void launch_residual_norm(wec_poisson *P, const double *b, double *x, float *b32, int mode, unsigned long long hw,
+                          int use, cudaStream_t st)
 {
+    const int G = kgrid(ncells(P), g_kg.res[P->nz > 1 ? 1 : 0]);
     if (P->nz > 1)
         launch_k(k_residual_norm<3>, G, KT, 0, st, op0(P), P->d0, b, x, P->V, b32, P->sc, P->part, P->ks, P->g, mode,
                  hw, use);
@@ -1183,7 +1237,6 @@ void enqueue_begin(wec_poisson *P, const double *b, double *x, double rtol, int 
 {
     const long long n = ncells(P);
     const double nf = nfaces(P);
-    const int G = kgrid(n, P->nz > 1);
     float *b32 = P->prec == WEC_PREC_MIXED ? P->L32[0].b : nullptr;
     {
         WEC_PROF("scalar", -1, 64.0, st);
@@ -1191,10 +1244,10 @@ void enqueue_begin(wec_poisson *P, const double *b, double *x, double rtol, int 
     }
     {
         WEC_PROF("krylov_norm", -1, 8.0 * n, st);
-        launch_k(k_bnorm, G, KT, 0, st, n, b, P->part, P->ks);
+        launch_k(k_bnorm, kgrid(n, g_kg.bnorm), KT, 0, st, n, b, P->part, P->ks);
     }
     WEC_PROF("krylov_residual", -1, 8.0 * (4.0 * n + nf) + (b32 ? 4.0 * n : 0.0), st);
-    launch_residual_norm(P, G, b, x, b32, 0, hw, use, st);
+    launch_residual_norm(P, b, x, b32, 0, hw, use, st);
 }
 
 // One Arnoldi step j (preconditioner, matvec, CGS2 in place in V's column j+1,
@@ -1204,7 +1257,7 @@ void enqueue_body(wec_poisson *P, unsigned long long hif, int use, cudaStream_t 
 {
     const long long n = ncells(P);
     const double nf = nfaces(P);
-    const int G = kgrid(n, P->nz > 1), m = P->restart;
+    const int m = P->restart, d3 = P->nz > 1 ? 1 : 0, kb8 = m <= 8 ? 1 : 0;
     const bool mixed = P->prec == WEC_PREC_MIXED;
     double *h1 = P->dots, *h2 = P->dots + (kMaxRestart + 2);
     // the mixed V-cycle reads u_j in FP32, written beside it by k_residual_norm / k_orth_norm
@@ -1214,17 +1267,17 @@ void enqueue_body(wec_poisson *P, unsigned long long hif, int use, cudaStream_t 
         vcycle_t<float, double>(P, P->L32, P->L32[0].b, P->Z, nullptr, &P->ks->j, st);
     {
         WEC_PROF("krylov_matvec_dots", -1, 8.0 * (3.0 * n + nf) + 8.0 * n * m, st);
-        if (P->nz > 1)
-            launch_k(k_matvec_dots<3>, G, KT, 0, st, op0(P), P->d0, P->Z, P->V, P->sc, P->part, h1, P->ks);
-        else
-            launch_k(k_matvec_dots<2>, G, KT, 0, st, op0(P), P->d0, P->Z, P->V, P->sc, P->part, h1, P->ks);
+        auto kern = d3 ? (kb8 ? k_matvec_dots<3, 8> : k_matvec_dots<3, 32>)
+                       : (kb8 ? k_matvec_dots<2, 8> : k_matvec_dots<2, 32>);
+        launch_k(kern, kgrid(n, g_kg.mv[d3][kb8]), KT, 0, st, op0(P), P->d0, P->Z, P->V, P->sc, P->part, h1, P->ks);
     }
     {
         WEC_PROF("krylov_orth_dots", -1, 8.0 * n * (m + 2), st);
-        launch_k(k_orth_dots, G, KT, 0, st, n, P->V, P->sc, h1, P->part, h2, P->ks);
+        launch_k(kb8 ? k_orth_dots<8> : k_orth_dots<32>, kgrid(n, g_kg.od[kb8]), KT, 0, st, n, P->V, P->sc, h1,
+                 P->part, h2, P->ks);
     }
     WEC_PROF("krylov_orth_norm", -1, 8.0 * n * (m + 2) + (mixed ? 4.0 * n : 0.0), st);
-    launch_k(k_orth_norm, G, KT, 0, st, n, P->V, P->sc, mixed ? P->L32[0].b : nullptr, h1, h2, P->part, P->ks,
+    launch_k(k_orth_norm, kgrid(n, g_kg.on), KT, 0, st, n, P->V, P->sc, mixed ? P->L32[0].b : nullptr, h1, h2, P->part, P->ks,
              P->hess, P->cs, P->sn, P->g, hif, use);
 }
 
@@ -1234,7 +1287,7 @@ void enqueue_close(wec_poisson *P, const double *b, double *x, unsigned long lon
 {
     const long long n = ncells(P);
     const double nf = nfaces(P);
-    const int G = kgrid(n, P->nz > 1), m = P->restart;
+    const int m = P->restart;
     const bool mixed = P->prec == WEC_PREC_MIXED;
     {
         WEC_PROF("scalar", -1, 8.0 * m * m, st);
@@ -1245,7 +1298,7 @@ void enqueue_close(wec_poisson *P, const double *b, double *x, unsigned long lon
         launch_k(k_update_x, nblk(n, 256), 256, 0, st, n, P->y, P->Z, x, P->ks);
     }
     WEC_PROF("krylov_residual", -1, 8.0 * (4.0 * n + nf) + (mixed ? 4.0 * n : 0.0), st);
-    launch_residual_norm(P, G, b, x, mixed ? P->L32[0].b : nullptr, 1, hw, use, st);
+    launch_residual_norm(P, b, x, mixed ? P->L32[0].b : nullptr, 1, hw, use, st);
 }
 
 int read_state(wec_poisson *P, cudaStream_t st)

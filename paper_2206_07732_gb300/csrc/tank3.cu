@@ -48,6 +48,7 @@ struct Tank3P {
     int has_body;
     double bxc, byc, br, blen;
     int ncomp;
+    int idx32;  // every face array's index fits in 32 bits (the interior stencils' indexing)
     const double *amp, *omega, *kw, *phase;  // device
     const double *damp;                       // device, [nx]: damping-zone weight of each column
     const float *dampf;                       // the same in FP32
@@ -348,35 +349,39 @@ __global__ void __launch_bounds__(128) k3t_reinit_stage(Tank3P P, const R *__res
 // ------------------------------------------------------------ the step ----
 // Velocity ghosts: nearest face (free slip); at the inflow v is reflected oddly
 // about 0 and w about the incident wave's w_in (win: [nz+1] at the time used).
-template <typename R>
+template <bool IN, typename R>
 __device__ __forceinline__ R cellq(const Tank3P &P, const R *__restrict__ a, int i, int j, int k)
 {
+    if constexpr (IN) return a[(k * P.ny + j) * P.nx + i];
     i = min(max(i, 0), P.nx - 1);
     j = min(max(j, 0), P.ny - 1);
     k = min(max(k, 0), P.nz - 1);
     return a[((long long)k * P.ny + j) * P.nx + i];
 }
-template <typename R>
+template <bool IN, typename R>
 __device__ __forceinline__ R uq(const Tank3P &P, const R *__restrict__ u, int i, int j, int k)
 {
+    if constexpr (IN) return u[(k * P.ny + j) * (P.nx + 1) + i];
     i = min(max(i, 0), P.nx);
     j = min(max(j, 0), P.ny - 1);
     k = min(max(k, 0), P.nz - 1);
     return u[((long long)k * P.ny + j) * (P.nx + 1) + i];
 }
-template <typename R>
+template <bool IN, typename R>
 __device__ __forceinline__ R vq(const Tank3P &P, const R *__restrict__ v, int i, int j, int k)
 {
+    if constexpr (IN) return v[(k * (P.ny + 1) + j) * P.nx + i];
     j = min(max(j, 0), P.ny);
     k = min(max(k, 0), P.nz - 1);
     if (i > P.nx - 1) i = P.nx - 1;
     if (i < 0) return -v[((long long)k * (P.ny + 1) + j) * P.nx + (-1 - i)];
     return v[((long long)k * (P.ny + 1) + j) * P.nx + i];
 }
-template <typename R>
+template <bool IN, typename R>
 __device__ __forceinline__ R wq(const Tank3P &P, const R *__restrict__ w, const R *__restrict__ win, int i, int j,
                                 int k)
 {
+    if constexpr (IN) return w[(k * P.ny + j) * P.nx + i];
     k = min(max(k, 0), P.nz);
     j = min(max(j, 0), P.ny - 1);
     if (i > P.nx - 1) i = P.nx - 1;
@@ -398,29 +403,35 @@ __device__ __forceinline__ R upw3(R q0, R q1, R q2, R q3, R vel)
     return vel >= R(0) ? koren3(q0, q1, q2) : koren3(q3, q2, q1);
 }
 // face densities: the mean of the face's two cells (face index clamped first)
-template <typename R>
+template <bool IN, typename R>
 __device__ __forceinline__ R ruq(const Tank3P &P, const R *rc, int i, int j, int k)
 {
-    i = min(max(i, 0), P.nx);
-    j = min(max(j, 0), P.ny - 1);
-    k = min(max(k, 0), P.nz - 1);
-    return R(0.5) * (cellq(P, rc, i - 1, j, k) + cellq(P, rc, i, j, k));
+    if constexpr (!IN) {
+        i = min(max(i, 0), P.nx);
+        j = min(max(j, 0), P.ny - 1);
+        k = min(max(k, 0), P.nz - 1);
+    }
+    return R(0.5) * (cellq<IN>(P, rc, i - 1, j, k) + cellq<IN>(P, rc, i, j, k));
 }
-template <typename R>
+template <bool IN, typename R>
 __device__ __forceinline__ R rvq(const Tank3P &P, const R *rc, int i, int j, int k)
 {
-    i = min(max(i, 0), P.nx - 1);
-    j = min(max(j, 0), P.ny);
-    k = min(max(k, 0), P.nz - 1);
-    return R(0.5) * (cellq(P, rc, i, j - 1, k) + cellq(P, rc, i, j, k));
+    if constexpr (!IN) {
+        i = min(max(i, 0), P.nx - 1);
+        j = min(max(j, 0), P.ny);
+        k = min(max(k, 0), P.nz - 1);
+    }
+    return R(0.5) * (cellq<IN>(P, rc, i, j - 1, k) + cellq<IN>(P, rc, i, j, k));
 }
-template <typename R>
+template <bool IN, typename R>
 __device__ __forceinline__ R rwq(const Tank3P &P, const R *rc, int i, int j, int k)
 {
-    i = min(max(i, 0), P.nx - 1);
-    j = min(max(j, 0), P.ny - 1);
-    k = min(max(k, 0), P.nz);
-    return R(0.5) * (cellq(P, rc, i, j, k - 1) + cellq(P, rc, i, j, k));
+    if constexpr (!IN) {
+        i = min(max(i, 0), P.nx - 1);
+        j = min(max(j, 0), P.ny - 1);
+        k = min(max(k, 0), P.nz);
+    }
+    return R(0.5) * (cellq<IN>(P, rc, i, j, k - 1) + cellq<IN>(P, rc, i, j, k));
 }
 
 template <typename R>
@@ -430,33 +441,35 @@ struct Vel3 {
 
 // rho-breve and C of a momentum control volume: comp 0 u-face, 1 v-face, 2 w-face;
 // the three pairs of CV faces summed x, then y, then z
-template <typename R>
-__device__ void transport3(const Tank3P &P, const R *rc, const Vel3<R> &V, int comp, int i, int j, int k, R dt, R &rb,
+template <bool IN, typename R>
+__device__ __forceinline__ void transport3(const Tank3P &P, const R *rc, const Vel3<R> &V, int comp, int i, int j, int k, R dt, R &rb,
                            R &C)
 {
     const R h = cst3<R>(P).h;
     R m[6], f[6];
-#define QV(a, b, c) (comp == 0 ? uq(P, V.u, a, b, c) : comp == 1 ? vq(P, V.v, a, b, c) : wq(P, V.w, V.win, a, b, c))
-#define RV(a, b, c) (comp == 0 ? ruq(P, rc, a, b, c) : comp == 1 ? rvq(P, rc, a, b, c) : rwq(P, rc, a, b, c))
+#define QV(a, b, c) (comp == 0 ? uq<IN>(P, V.u, a, b, c) : comp == 1 ? vq<IN>(P, V.v, a, b, c) : wq<IN>(P, V.w, V.win, a, b, c))
+#define RV(a, b, c) (comp == 0 ? ruq<IN>(P, rc, a, b, c) : comp == 1 ? rvq<IN>(P, rc, a, b, c) : rwq<IN>(P, rc, a, b, c))
+#pragma unroll
     for (int d = 0; d < 3; ++d)
+#pragma unroll
         for (int s = 0; s < 2; ++s) {
             R U;
             if (d == comp) {  // CV faces at the cell centres on either side
                 const int o = s - 1;
-                U = comp == 0   ? R(0.5) * (uq(P, V.u, i + o, j, k) + uq(P, V.u, i + o + 1, j, k))
-                    : comp == 1 ? R(0.5) * (vq(P, V.v, i, j + o, k) + vq(P, V.v, i, j + o + 1, k))
-                                : R(0.5) * (wq(P, V.w, V.win, i, j, k + o) + wq(P, V.w, V.win, i, j, k + o + 1));
+                U = comp == 0   ? R(0.5) * (uq<IN>(P, V.u, i + o, j, k) + uq<IN>(P, V.u, i + o + 1, j, k))
+                    : comp == 1 ? R(0.5) * (vq<IN>(P, V.v, i, j + o, k) + vq<IN>(P, V.v, i, j + o + 1, k))
+                                : R(0.5) * (wq<IN>(P, V.w, V.win, i, j, k + o) + wq<IN>(P, V.w, V.win, i, j, k + o + 1));
             } else {  // CV faces on the edges: the d-velocity averaged over the comp direction
                 const int e = s;
                 if (d == 0)
-                    U = comp == 1 ? R(0.5) * (uq(P, V.u, i + e, j - 1, k) + uq(P, V.u, i + e, j, k))
-                                  : R(0.5) * (uq(P, V.u, i + e, j, k - 1) + uq(P, V.u, i + e, j, k));
+                    U = comp == 1 ? R(0.5) * (uq<IN>(P, V.u, i + e, j - 1, k) + uq<IN>(P, V.u, i + e, j, k))
+                                  : R(0.5) * (uq<IN>(P, V.u, i + e, j, k - 1) + uq<IN>(P, V.u, i + e, j, k));
                 else if (d == 1)
-                    U = comp == 0 ? R(0.5) * (vq(P, V.v, i - 1, j + e, k) + vq(P, V.v, i, j + e, k))
-                                  : R(0.5) * (vq(P, V.v, i, j + e, k - 1) + vq(P, V.v, i, j + e, k));
+                    U = comp == 0 ? R(0.5) * (vq<IN>(P, V.v, i - 1, j + e, k) + vq<IN>(P, V.v, i, j + e, k))
+                                  : R(0.5) * (vq<IN>(P, V.v, i, j + e, k - 1) + vq<IN>(P, V.v, i, j + e, k));
                 else
-                    U = comp == 0 ? R(0.5) * (wq(P, V.w, V.win, i - 1, j, k + e) + wq(P, V.w, V.win, i, j, k + e))
-                                  : R(0.5) * (wq(P, V.w, V.win, i, j - 1, k + e) + wq(P, V.w, V.win, i, j, k + e));
+                    U = comp == 0 ? R(0.5) * (wq<IN>(P, V.w, V.win, i - 1, j, k + e) + wq<IN>(P, V.w, V.win, i, j, k + e))
+                                  : R(0.5) * (wq<IN>(P, V.w, V.win, i, j - 1, k + e) + wq<IN>(P, V.w, V.win, i, j, k + e));
             }
             const int a0 = s - 1;  // the stencil runs over (base + a0 - 1 .. base + a0 + 2) along d
             const int di = d == 0, dj = d == 1, dk = d == 2;
@@ -485,89 +498,89 @@ struct Visc3 {
     const R *mu;
     Vel3<R> V;
 };
-template <typename R>
+template <bool IN, typename R>
 __device__ __forceinline__ R mxy3(const Tank3P &P, const R *mu, int i, int j, int k)
 {
-    return R(0.25) * (cellq(P, mu, i - 1, j - 1, k) + cellq(P, mu, i, j - 1, k) + cellq(P, mu, i - 1, j, k) +
-                      cellq(P, mu, i, j, k));
+    return R(0.25) * (cellq<IN>(P, mu, i - 1, j - 1, k) + cellq<IN>(P, mu, i, j - 1, k) + cellq<IN>(P, mu, i - 1, j, k) +
+                      cellq<IN>(P, mu, i, j, k));
 }
-template <typename R>
+template <bool IN, typename R>
 __device__ __forceinline__ R mxz3(const Tank3P &P, const R *mu, int i, int j, int k)
 {
-    return R(0.25) * (cellq(P, mu, i - 1, j, k - 1) + cellq(P, mu, i, j, k - 1) + cellq(P, mu, i - 1, j, k) +
-                      cellq(P, mu, i, j, k));
+    return R(0.25) * (cellq<IN>(P, mu, i - 1, j, k - 1) + cellq<IN>(P, mu, i, j, k - 1) + cellq<IN>(P, mu, i - 1, j, k) +
+                      cellq<IN>(P, mu, i, j, k));
 }
-template <typename R>
+template <bool IN, typename R>
 __device__ __forceinline__ R myz3(const Tank3P &P, const R *mu, int i, int j, int k)
 {
-    return R(0.25) * (cellq(P, mu, i, j - 1, k - 1) + cellq(P, mu, i, j, k - 1) + cellq(P, mu, i, j - 1, k) +
-                      cellq(P, mu, i, j, k));
+    return R(0.25) * (cellq<IN>(P, mu, i, j - 1, k - 1) + cellq<IN>(P, mu, i, j, k - 1) + cellq<IN>(P, mu, i, j - 1, k) +
+                      cellq<IN>(P, mu, i, j, k));
 }
-#define U3(a, b, c) uq(P, X.V.u, a, b, c)
-#define V3(a, b, c) vq(P, X.V.v, a, b, c)
-#define W3(a, b, c) wq(P, X.V.w, X.V.win, a, b, c)
-template <typename R>
+#define U3(a, b, c) uq<IN>(P, X.V.u, a, b, c)
+#define V3(a, b, c) vq<IN>(P, X.V.v, a, b, c)
+#define W3(a, b, c) wq<IN>(P, X.V.w, X.V.win, a, b, c)
+template <bool IN, typename R>
 __device__ __forceinline__ R txx(const Tank3P &P, const Visc3<R> &X, int i, int j, int k)
 {
-    return R(2) * cellq(P, X.mu, i, j, k) * (U3(i + 1, j, k) - U3(i, j, k)) / cst3<R>(P).h;
+    return R(2) * cellq<IN>(P, X.mu, i, j, k) * (U3(i + 1, j, k) - U3(i, j, k)) / cst3<R>(P).h;
 }
-template <typename R>
+template <bool IN, typename R>
 __device__ __forceinline__ R tyy(const Tank3P &P, const Visc3<R> &X, int i, int j, int k)
 {
-    return R(2) * cellq(P, X.mu, i, j, k) * (V3(i, j + 1, k) - V3(i, j, k)) / cst3<R>(P).h;
+    return R(2) * cellq<IN>(P, X.mu, i, j, k) * (V3(i, j + 1, k) - V3(i, j, k)) / cst3<R>(P).h;
 }
-template <typename R>
+template <bool IN, typename R>
 __device__ __forceinline__ R tzz(const Tank3P &P, const Visc3<R> &X, int i, int j, int k)
 {
-    return R(2) * cellq(P, X.mu, i, j, k) * (W3(i, j, k + 1) - W3(i, j, k)) / cst3<R>(P).h;
+    return R(2) * cellq<IN>(P, X.mu, i, j, k) * (W3(i, j, k + 1) - W3(i, j, k)) / cst3<R>(P).h;
 }
-template <typename R>
+template <bool IN, typename R>
 __device__ __forceinline__ R txy(const Tank3P &P, const Visc3<R> &X, int i, int j, int k)
 {
     const R h = cst3<R>(P).h;
-    return mxy3(P, X.mu, i, j, k) * ((U3(i, j, k) - U3(i, j - 1, k)) / h + (V3(i, j, k) - V3(i - 1, j, k)) / h);
+    return mxy3<IN>(P, X.mu, i, j, k) * ((U3(i, j, k) - U3(i, j - 1, k)) / h + (V3(i, j, k) - V3(i - 1, j, k)) / h);
 }
-template <typename R>
+template <bool IN, typename R>
 __device__ __forceinline__ R txz(const Tank3P &P, const Visc3<R> &X, int i, int j, int k)
 {
     const R h = cst3<R>(P).h;
-    return mxz3(P, X.mu, i, j, k) * ((U3(i, j, k) - U3(i, j, k - 1)) / h + (W3(i, j, k) - W3(i - 1, j, k)) / h);
+    return mxz3<IN>(P, X.mu, i, j, k) * ((U3(i, j, k) - U3(i, j, k - 1)) / h + (W3(i, j, k) - W3(i - 1, j, k)) / h);
 }
-template <typename R>
+template <bool IN, typename R>
 __device__ __forceinline__ R tyz(const Tank3P &P, const Visc3<R> &X, int i, int j, int k)
 {
     const R h = cst3<R>(P).h;
-    return myz3(P, X.mu, i, j, k) * ((V3(i, j, k) - V3(i, j, k - 1)) / h + (W3(i, j, k) - W3(i, j - 1, k)) / h);
+    return myz3<IN>(P, X.mu, i, j, k) * ((V3(i, j, k) - V3(i, j, k - 1)) / h + (W3(i, j, k) - W3(i, j - 1, k)) / h);
 }
 #undef U3
 #undef V3
 #undef W3
-template <typename R>
-__device__ R visc3(const Tank3P &P, const Visc3<R> &X, int comp, int i, int j, int k)
+template <bool IN, typename R>
+__device__ __forceinline__ R visc3(const Tank3P &P, const Visc3<R> &X, int comp, int i, int j, int k)
 {
     const R h = cst3<R>(P).h;
     if (comp == 0)
-        return ((txx(P, X, i, j, k) - txx(P, X, i - 1, j, k)) / h + (txy(P, X, i, j + 1, k) - txy(P, X, i, j, k)) / h) +
-               (txz(P, X, i, j, k + 1) - txz(P, X, i, j, k)) / h;
+        return ((txx<IN>(P, X, i, j, k) - txx<IN>(P, X, i - 1, j, k)) / h + (txy<IN>(P, X, i, j + 1, k) - txy<IN>(P, X, i, j, k)) / h) +
+               (txz<IN>(P, X, i, j, k + 1) - txz<IN>(P, X, i, j, k)) / h;
     if (comp == 1)
-        return ((tyy(P, X, i, j, k) - tyy(P, X, i, j - 1, k)) / h + (txy(P, X, i + 1, j, k) - txy(P, X, i, j, k)) / h) +
-               (tyz(P, X, i, j, k + 1) - tyz(P, X, i, j, k)) / h;
-    return ((tzz(P, X, i, j, k) - tzz(P, X, i, j, k - 1)) / h + (txz(P, X, i + 1, j, k) - txz(P, X, i, j, k)) / h) +
-           (tyz(P, X, i, j + 1, k) - tyz(P, X, i, j, k)) / h;
+        return ((tyy<IN>(P, X, i, j, k) - tyy<IN>(P, X, i, j - 1, k)) / h + (txy<IN>(P, X, i + 1, j, k) - txy<IN>(P, X, i, j, k)) / h) +
+               (tyz<IN>(P, X, i, j, k + 1) - tyz<IN>(P, X, i, j, k)) / h;
+    return ((tzz<IN>(P, X, i, j, k) - tzz<IN>(P, X, i, j, k - 1)) / h + (txz<IN>(P, X, i + 1, j, k) - txz<IN>(P, X, i, j, k)) / h) +
+           (tyz<IN>(P, X, i, j + 1, k) - tyz<IN>(P, X, i, j, k)) / h;
 }
 // interior-formula diagonal (the Jacobi splitting only)
-template <typename R>
-__device__ R vdiag3(const Tank3P &P, const R *mu, int comp, int i, int j, int k)
+template <bool IN, typename R>
+__device__ __forceinline__ R vdiag3(const Tank3P &P, const R *mu, int comp, int i, int j, int k)
 {
     const R h2 = cst3<R>(P).h * cst3<R>(P).h;
     if (comp == 0)
-        return -(R(2) * cellq(P, mu, i, j, k) + R(2) * cellq(P, mu, i - 1, j, k) + mxy3(P, mu, i, j + 1, k) +
-                 mxy3(P, mu, i, j, k) + mxz3(P, mu, i, j, k + 1) + mxz3(P, mu, i, j, k)) / h2;
+        return -(R(2) * cellq<IN>(P, mu, i, j, k) + R(2) * cellq<IN>(P, mu, i - 1, j, k) + mxy3<IN>(P, mu, i, j + 1, k) +
+                 mxy3<IN>(P, mu, i, j, k) + mxz3<IN>(P, mu, i, j, k + 1) + mxz3<IN>(P, mu, i, j, k)) / h2;
     if (comp == 1)
-        return -(R(2) * cellq(P, mu, i, j, k) + R(2) * cellq(P, mu, i, j - 1, k) + mxy3(P, mu, i + 1, j, k) +
-                 mxy3(P, mu, i, j, k) + myz3(P, mu, i, j, k + 1) + myz3(P, mu, i, j, k)) / h2;
-    return -(R(2) * cellq(P, mu, i, j, k) + R(2) * cellq(P, mu, i, j, k - 1) + mxz3(P, mu, i + 1, j, k) +
-             mxz3(P, mu, i, j, k) + myz3(P, mu, i, j + 1, k) + myz3(P, mu, i, j, k)) / h2;
+        return -(R(2) * cellq<IN>(P, mu, i, j, k) + R(2) * cellq<IN>(P, mu, i, j - 1, k) + mxy3<IN>(P, mu, i + 1, j, k) +
+                 mxy3<IN>(P, mu, i, j, k) + myz3<IN>(P, mu, i, j, k + 1) + myz3<IN>(P, mu, i, j, k)) / h2;
+    return -(R(2) * cellq<IN>(P, mu, i, j, k) + R(2) * cellq<IN>(P, mu, i, j, k - 1) + mxz3<IN>(P, mu, i + 1, j, k) +
+             mxz3<IN>(P, mu, i, j, k) + myz3<IN>(P, mu, i, j + 1, k) + myz3<IN>(P, mu, i, j, k)) / h2;
 }
 
 // solved faces of component comp: u i = 1..nx-1; v j = 1..ny-1; w k = 1..nz
@@ -601,53 +614,77 @@ struct MomIn {
     R dt, zd1, g, ikp;
 };
 
-template <typename R>
-__global__ void __launch_bounds__(128) k3t_momentum(Tank3P P, MomIn<R> M, int comp, R *__restrict__ Dout,
-                                                    R *__restrict__ Rout)
+// faces whose whole stencil (three cells each way) lies inside the grid: there
+// every ghost rule of the accessors is inactive, so the unclamped form computes
+// the same values
+__device__ __forceinline__ bool interior3(const Tank3P &P, int i, int j, int k)
 {
-    pdl_entry();
-    int i, j, k;
-    long long f;
-    if (!face_of(P, comp, i, j, k, f)) return;
+    return P.idx32 && i >= 3 && i <= P.nx - 4 && j >= 3 && j <= P.ny - 4 && k >= 3 && k <= P.nz - 4;
+}
+
+template <bool IN, typename R>
+__device__ __forceinline__ void momentum_at(const Tank3P &P, const MomIn<R> &M, int comp, int i, int j, int k,
+                                            long long f, R *__restrict__ Dout, R *__restrict__ Rout)
+{
     R rb, C;
-    transport3<R>(P, M.rho_n, M.V, comp, i, j, k, M.dt, rb, C);
+    transport3<IN, R>(P, M.rho_n, M.V, comp, i, j, k, M.dt, rb, C);
     const Visc3<R> X{M.mu_n, M.V};
     const double h = P.h;
     const int ci = comp == 0 ? i - 1 : i, cj = comp == 1 ? j - 1 : j, ck = comp == 2 ? k - 1 : k;
-    const R chi = R(0.5) * (cellq(P, M.chi1, ci, cj, ck) + cellq(P, M.chi1, i, j, k));
+    const R chi = R(0.5) * (cellq<IN>(P, M.chi1, ci, cj, ck) + cellq<IN>(P, M.chi1, i, j, k));
     const R al = comp == 0 ? M.dampu[i] : dampc<R>(P, i);
     const R vd = comp == 2 ? M.vortf[k] : M.vortc[k];
     Dout[f] = rb / M.dt + chi * M.ikp + al * rb / M.dt + vd;
     const double pc = k < P.nz ? M.p[((long long)k * P.ny + j) * P.nx + i] : 0.0;
     if (comp == 0) {
-        Rout[f] = ruq(P, M.rho_n, i, j, k) * M.V.u[f] / M.dt - C + R(0.5) * visc3<R>(P, X, 0, i, j, k) -
+        Rout[f] = ruq<IN>(P, M.rho_n, i, j, k) * M.V.u[f] / M.dt - C + R(0.5) * visc3<IN, R>(P, X, 0, i, j, k) -
                   R((pc - M.p[((long long)k * P.ny + j) * P.nx + i - 1]) / h);
     } else if (comp == 1) {
-        Rout[f] = rvq(P, M.rho_n, i, j, k) * M.V.v[f] / M.dt - C + R(0.5) * visc3<R>(P, X, 1, i, j, k) -
+        Rout[f] = rvq<IN>(P, M.rho_n, i, j, k) * M.V.v[f] / M.dt - C + R(0.5) * visc3<IN, R>(P, X, 1, i, j, k) -
                   R((pc - M.p[((long long)k * P.ny + j - 1) * P.nx + i]) / h);
     } else {
-        const R rf = R(0.5) * (cellq(P, M.rf1, i, j, k - 1) + cellq(P, M.rf1, i, j, k));
+        const R rf = R(0.5) * (cellq<IN>(P, M.rf1, i, j, k - 1) + cellq<IN>(P, M.rf1, i, j, k));
         const double pb = M.p[((long long)(k - 1) * P.ny + j) * P.nx + i];
         const double gp = k < P.nz ? (pc - pb) / h : -2.0 * pb / h;
-        Rout[f] = rwq(P, M.rho_n, i, j, k) * M.V.w[f] / M.dt - C + R(0.5) * visc3<R>(P, X, 2, i, j, k) - rf * M.g +
+        Rout[f] = rwq<IN>(P, M.rho_n, i, j, k) * M.V.w[f] / M.dt - C + R(0.5) * visc3<IN, R>(P, X, 2, i, j, k) - rf * M.g +
                   chi * M.zd1 * M.ikp - R(gp);
     }
 }
 
+template <int COMP, typename R>
+__global__ void __launch_bounds__(128) k3t_momentum(Tank3P P, MomIn<R> M, R *__restrict__ Dout, R *__restrict__ Rout)
+{
+    pdl_entry();
+    int i, j, k;
+    long long f;
+    if (!face_of(P, COMP, i, j, k, f)) return;
+    if (interior3(P, i, j, k))
+        momentum_at<true, R>(P, M, COMP, i, j, k, f, Dout, Rout);
+    else
+        momentum_at<false, R>(P, M, COMP, i, j, k, f, Dout, Rout);
+}
+
 // one Crank-Nicolson Jacobi sweep of component comp: B = (R + (L(A) - ld A) / 2) / (D - ld / 2)
-template <typename R>
-__global__ void __launch_bounds__(128) k3t_jacobi(Tank3P P, const R *__restrict__ mu1, Vel3<R> A, int comp,
+template <bool IN, typename R>
+__device__ __forceinline__ R jacobi_at(const Tank3P &P, const R *__restrict__ mu1, const Vel3<R> &A, int comp,
+                                       int i, int j, int k, R a, R d, R r)
+{
+    const Visc3<R> X{mu1, A};
+    const R ld = vdiag3<IN, R>(P, mu1, comp, i, j, k);
+    return (r + R(0.5) * (visc3<IN, R>(P, X, comp, i, j, k) - ld * a)) / (d - R(0.5) * ld);
+}
+template <int COMP, typename R>
+__global__ void __launch_bounds__(128) k3t_jacobi(Tank3P P, const R *__restrict__ mu1, Vel3<R> A,
                                                   const R *__restrict__ D, const R *__restrict__ Rr,
                                                   R *__restrict__ B)
 {
     pdl_entry();
     int i, j, k;
     long long f;
-    if (!face_of(P, comp, i, j, k, f)) return;
-    const Visc3<R> X{mu1, A};
-    const R ld = vdiag3<R>(P, mu1, comp, i, j, k);
-    const R a = comp == 0 ? A.u[f] : comp == 1 ? A.v[f] : A.w[f];
-    B[f] = (Rr[f] + R(0.5) * (visc3<R>(P, X, comp, i, j, k) - ld * a)) / (D[f] - R(0.5) * ld);
+    if (!face_of(P, COMP, i, j, k, f)) return;
+    const R a = COMP == 0 ? A.u[f] : COMP == 1 ? A.v[f] : A.w[f];
+    B[f] = interior3(P, i, j, k) ? jacobi_at<true, R>(P, mu1, A, COMP, i, j, k, a, D[f], Rr[f])
+                                 : jacobi_at<false, R>(P, mu1, A, COMP, i, j, k, a, D[f], Rr[f]);
 }
 
 // Dirichlet faces of the predictor: u_in(t1) at x = 0, u = 0 at the outlet, v = 0
@@ -800,7 +837,7 @@ __global__ void __launch_bounds__(kRT) k3t_force(Tank3P P, const double *__restr
             const long long c = ((long long)k * ny + j) * nx + i, cb = c - (long long)nx * ny;
             const double pf = (p[cb] * wr + p[c] * wl) / (wl + wr);
             const double muf = 0.5 * (mu[cb] + mu[c]);
-            const double dwdz = (wq(P, V.w, V.win, i, j, k + 1) - wq(P, V.w, V.win, i, j, k - 1)) / (2.0 * h);
+            const double dwdz = (wq<false>(P, V.w, V.win, i, j, k + 1) - wq<false>(P, V.w, V.win, i, j, k - 1)) / (2.0 * h);
             acc += (-pf * nz_ + muf * 2.0 * dwdz * nz_) * A;
         } else if (kind == 1) {
             if (i < 1 || k > nz - 1) continue;
@@ -810,9 +847,9 @@ __global__ void __launch_bounds__(kRT) k3t_force(Tank3P P, const double *__restr
             const double nx_ = pl < 0.0 ? 1.0 : -1.0;
             const long long c = ((long long)k * ny + j) * nx + i;
             const double muf = 0.5 * (mu[c - 1] + mu[c]);
-            const double dwdx = 0.5 * ((wq(P, V.w, V.win, i, j, k) - wq(P, V.w, V.win, i - 1, j, k)) +
-                                       (wq(P, V.w, V.win, i, j, k + 1) - wq(P, V.w, V.win, i - 1, j, k + 1))) / h;
-            const double dudz = (uq(P, V.u, i, j, k + 1) - uq(P, V.u, i, j, k - 1)) / (2.0 * h);
+            const double dwdx = 0.5 * ((wq<false>(P, V.w, V.win, i, j, k) - wq<false>(P, V.w, V.win, i - 1, j, k)) +
+                                       (wq<false>(P, V.w, V.win, i, j, k + 1) - wq<false>(P, V.w, V.win, i - 1, j, k + 1))) / h;
+            const double dudz = (uq<false>(P, V.u, i, j, k + 1) - uq<false>(P, V.u, i, j, k - 1)) / (2.0 * h);
             acc += muf * (dwdx + dudz) * nx_ * A;
         } else {
             if (j < 1 || k > nz - 1) continue;
@@ -822,9 +859,9 @@ __global__ void __launch_bounds__(kRT) k3t_force(Tank3P P, const double *__restr
             const double ny_ = pl < 0.0 ? 1.0 : -1.0;
             const long long c = ((long long)k * ny + j) * nx + i;
             const double muf = 0.5 * (mu[c - nx] + mu[c]);
-            const double dwdy = 0.5 * ((wq(P, V.w, V.win, i, j, k) - wq(P, V.w, V.win, i, j - 1, k)) +
-                                       (wq(P, V.w, V.win, i, j, k + 1) - wq(P, V.w, V.win, i, j - 1, k + 1))) / h;
-            const double dvdz = (vq(P, V.v, i, j, k + 1) - vq(P, V.v, i, j, k - 1)) / (2.0 * h);
+            const double dwdy = 0.5 * ((wq<false>(P, V.w, V.win, i, j, k) - wq<false>(P, V.w, V.win, i, j - 1, k)) +
+                                       (wq<false>(P, V.w, V.win, i, j, k + 1) - wq<false>(P, V.w, V.win, i, j - 1, k + 1))) / h;
+            const double dvdz = (vq<false>(P, V.v, i, j, k + 1) - vq<false>(P, V.v, i, j, k - 1)) / (2.0 * h);
             acc += muf * (dwdy + dvdz) * ny_ * A;
         }
     }
@@ -1089,7 +1126,8 @@ static int tank3_step_impl(wec_tank3 *T, Work3<R> &W, double dt, double pto_forc
         if (c == 1 && ny < 2) continue;
         const double nfc = c == 0 ? (nx - 1.0) * ny * nz : c == 1 ? nx * (ny - 1.0) * nz : (double)nx * ny * nz;
         WEC_PROF("tank3_momentum", c, b * (4.0 * T->nc + T->nu + T->nv + T->nw + 2.0 * nfc) + 8.0 * T->nc, st);
-        launch_k(k3t_momentum<R>, gc[c], 128, 0, st, P, M, c, W.D[c], W.R3[c]);
+        auto kern = c == 0 ? k3t_momentum<0, R> : c == 1 ? k3t_momentum<1, R> : k3t_momentum<2, R>;
+        launch_k(kern, gc[c], 128, 0, st, P, M, W.D[c], W.R3[c]);
     }
     // (6) Crank-Nicolson Jacobi sweeps from u^n with the Dirichlet faces at n+1
     const size_t nf[3] = {T->nu, T->nv, T->nw};
@@ -1106,8 +1144,9 @@ static int tank3_step_impl(wec_tank3 *T, Work3<R> &W, double dt, double pto_forc
             if (c == 1 && ny < 2) continue;
             const double nfc = c == 0 ? (nx - 1.0) * ny * nz : c == 1 ? nx * (ny - 1.0) * nz : (double)nx * ny * nz;
             WEC_PROF("tank3_jacobi", c, b * (T->nc + T->nu + T->nv + T->nw + 3.0 * nfc), st);
-            launch_k(k3t_jacobi<R>, gc[c], 128, 0, st, P, (const R *)W.mu1, Va, c, (const R *)W.D[c],
-                     (const R *)W.R3[c], W.B[c]);
+            auto kern = c == 0 ? k3t_jacobi<0, R> : c == 1 ? k3t_jacobi<1, R> : k3t_jacobi<2, R>;
+            launch_k(kern, gc[c], 128, 0, st, P, (const R *)W.mu1, Va, (const R *)W.D[c], (const R *)W.R3[c],
+                     W.B[c]);
         }
         for (int c = 0; c < 3; ++c) std::swap(W.A[c], W.B[c]);
     }
@@ -1216,6 +1255,7 @@ int wec_tank3_create(const wec_grid3 *grid, const wec_fluids *fl, const wec_wave
     P.nx = nx; P.ny = ny; P.nz = nz; P.h = h; P.ih = 1.0 / h; P.depth = grid->depth;
     P.rho_w = fl->rho_w; P.rho_a = fl->rho_a; P.mu_w = fl->mu_w; P.mu_a = fl->mu_a;
     P.has_body = body->present ? 1 : 0;
+    P.idx32 = (double)(nx + 1) * (ny + 1) * (nz + 1) < 2147483647.0 ? 1 : 0;
     P.rho_s = fl->rho_w;
     if (P.has_body) {
         P.bxc = body->xc; P.byc = body->yc; P.br = body->radius; P.blen = body->length;
