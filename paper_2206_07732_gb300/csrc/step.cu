@@ -970,6 +970,9 @@ int tank_alloc_and_init(wec_tank *T)
     WEC_CK(cudaStreamCreateWithFlags(&T->h2, cudaStreamNonBlocking));
     WEC_CK(cudaEventCreateWithFlags(&T->ev_in, cudaEventDisableTiming));
     WEC_CK(cudaEventCreateWithFlags(&T->ev_out, cudaEventDisableTiming));
+    WEC_CK(cudaStreamCreateWithFlags(&T->nst, cudaStreamNonBlocking));
+    WEC_CK(cudaEventCreateWithFlags(&T->ev_nf, cudaEventDisableTiming));
+    WEC_CK(cudaEventCreateWithFlags(&T->ev_nj, cudaEventDisableTiming));
     double **cells[] = {&T->sig, &T->sa, &T->r0, &T->r1, &T->rt, &T->p, &T->phi, &T->rhs,
                         &T->rho_n, &T->mu_n, &T->mu_1, &T->rf_1, &T->chi_1};
     for (double **q : cells) {
@@ -1163,11 +1166,20 @@ void enqueue_front_t(wec_tank *T, const Work<R> &W, cudaStream_t st)
         launch_k(k_proj_rhs<R>, nblk(nc + nu + nv, TB), TB, 0, st, P, T->us, T->vs, W.Du, W.Dv, T->rhs, S->L64[0].bu,
                                                           S->L64[0].bv);
     }
-    poisson_build(S, st);
-    if (T->net)
-        net_enqueue_guess(T, st);  // launch errors surface at the capture / the step's error check
-    else
+    if (T->net) {
+        // the guess reads the right-hand side and the level-0 coefficients only:
+        // it runs on the net's stream while this one builds the hierarchy
+        // (launch errors surface at the capture / the step's error check)
+        cudaEventRecord(T->ev_nf, st);
+        cudaStreamWaitEvent(T->nst, T->ev_nf, 0);
+        net_enqueue_guess(T, T->nst);
+        cudaEventRecord(T->ev_nj, T->nst);
+        poisson_build(S, st);
+        cudaStreamWaitEvent(st, T->ev_nj, 0);
+    } else {
+        poisson_build(S, st);
         cudaMemsetAsync(T->phi, 0, nc * 8, st);
+    }
 }
 
 void enqueue_front(wec_tank *T, cudaStream_t st)
@@ -1345,6 +1357,9 @@ void tank_free(wec_tank *T)
     poisson_free(&T->solver);
     if (T->ev_in) cudaEventDestroy(T->ev_in);
     if (T->ev_out) cudaEventDestroy(T->ev_out);
+    if (T->ev_nf) cudaEventDestroy(T->ev_nf);
+    if (T->ev_nj) cudaEventDestroy(T->ev_nj);
+    if (T->nst) cudaStreamDestroy(T->nst);
     if (T->h1) cudaStreamDestroy(T->h1);
     if (T->h2) cudaStreamDestroy(T->h2);
     if (T->gst) cudaStreamDestroy(T->gst);

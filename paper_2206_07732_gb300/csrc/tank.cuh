@@ -54,6 +54,9 @@ struct wec_tank {
     cudaStream_t gst = nullptr;       // the tank's own stream: every kernel runs here
     cudaStream_t h1 = nullptr, h2 = nullptr;  // capture helpers for the solver's conditional bodies
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    // the net's guess runs on its own stream beside the multigrid hierarchy build
+    cudaStream_t nst = nullptr;
+    cudaEvent_t ev_nf = nullptr, ev_nj = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     bool use_graph = true;
