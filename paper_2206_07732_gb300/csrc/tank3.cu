@@ -215,14 +215,17 @@ __device__ __forceinline__ bool cell_of(const Tank3P &P, Cell3 &q)
     return true;
 }
 
+// (cell layers k0 + blockIdx.z)
 template <typename R>
 __global__ void __launch_bounds__(128) k3t_materials(Tank3P P, const R *__restrict__ sig, double zc,
                                                      R *__restrict__ rho, R *__restrict__ mu, R *__restrict__ rhof,
-                                                     R *__restrict__ chi)
+                                                     R *__restrict__ chi, int k0)
 {
     pdl_entry();
     Cell3 q;
     if (!cell_of(P, q)) return;
+    q.k += k0;
+    q.c += (long long)k0 * P.ny * P.nx;
     const Tank3C<R> &K = cst3<R>(P);
     const R h = K.h;
     R psi = R(1.0e3);
@@ -1068,23 +1071,32 @@ static int tank3_step_impl(wec_tank3 *T, Work3<R> &W, double dt, double pto_forc
     }
 
     // (1) materials at n (FP64, for the force) and the heave force from
-    // p^{n-1/2}, u^n (Eq. int_fh)
-    {
-        WEC_PROF("tank3_materials", 0, 40.0 * T->nc, st);
-        launch_k(k3t_materials<double>, grid3(P), 128, 0, st, P, (const double *)T->sig, T->zc, T->rho, T->mu,
-                 T->rhof, T->chi);
-    }
-    if constexpr (f32) {
-        WEC_PROF("tank3_materials", 0, 20.0 * T->nc, st);
-        launch_k(k3t_materials<R>, grid3(P), 128, 0, st, P, (const R *)W.sig, T->zc, W.rho, W.mu, W.rf, W.chi);
-    }
+    // p^{n-1/2}, u^n (Eq. int_fh) over a box of cells around the cylinder
     double F = 0.0;
     const int kcb = (int)(T->zc / h), mkb = (int)std::ceil(0.5 * P.blen / h) + 3;
-    if (P.has_body && std::min(nz, kcb + mkb + 1) > std::max(0, kcb - mkb)) {
-        const int mi = (int)std::ceil((P.br) / h) + 3, mk = mkb;
-        const int ic = (int)(P.bxc / h), jc = (int)(P.byc / h), kc = kcb;
+    const bool force_box = P.has_body && std::min(nz, kcb + mkb + 1) > std::max(0, kcb - mkb);
+    const int fk0 = std::max(0, kcb - mkb), fk1 = std::min(nz, kcb + mkb + 1);
+    if constexpr (f32) {
+        // the stencils read FP32 materials; the FP64 ones are needed by the
+        // force only: the box's cell layers and the layer below it
+        if (force_box) {
+            const int s0 = std::max(0, fk0 - 1);
+            WEC_PROF("tank3_materials", 0, 40.0 * T->nc * (fk1 - s0) / nz, st);
+            launch_k(k3t_materials<double>, dim3((nx + 127) / 128, ny, fk1 - s0), 128, 0, st, P,
+                     (const double *)T->sig, T->zc, T->rho, T->mu, T->rhof, T->chi, s0);
+        }
+        WEC_PROF("tank3_materials", 0, 20.0 * T->nc, st);
+        launch_k(k3t_materials<R>, grid3(P), 128, 0, st, P, (const R *)W.sig, T->zc, W.rho, W.mu, W.rf, W.chi, 0);
+    } else {
+        WEC_PROF("tank3_materials", 0, 40.0 * T->nc, st);
+        launch_k(k3t_materials<double>, grid3(P), 128, 0, st, P, (const double *)T->sig, T->zc, T->rho, T->mu,
+                 T->rhof, T->chi, 0);
+    }
+    if (force_box) {
+        const int mi = (int)std::ceil((P.br) / h) + 3;
+        const int ic = (int)(P.bxc / h), jc = (int)(P.byc / h);
         const int i0 = std::max(0, ic - mi), i1 = std::min(nx, ic + mi + 1), j0 = std::max(0, jc - mi),
-                  j1 = std::min(ny, jc + mi + 1), k0 = std::max(0, kc - mk), k1 = std::min(nz, kc + mk + 1);
+                  j1 = std::min(ny, jc + mi + 1), k0 = fk0, k1 = fk1;
         const Vel3<double> Vn{T->u, T->v, T->w, d_win0};
         {
             WEC_PROF("tank3_force", 0, 0.0, st);
@@ -1113,7 +1125,7 @@ static int tank3_step_impl(wec_tank3 *T, Work3<R> &W, double dt, double pto_forc
     // (4) materials at n+1 (rho^{n+1} itself is not used: s1 is scratch)
     {
         WEC_PROF("tank3_materials", 0, 5.0 * sizeof(R) * T->nc, st);
-        launch_k(k3t_materials<R>, grid3(P), 128, 0, st, P, (const R *)W.tmp, zc1, W.s1, W.mu1, W.rf1, W.chi1);
+        launch_k(k3t_materials<R>, grid3(P), 128, 0, st, P, (const R *)W.tmp, zc1, W.s1, W.mu1, W.rf1, W.chi1, 0);
     }
     // (5) transport and the momentum system
     MomIn<R> M{W.rho, W.mu, W.chi1, W.rf1, T->p, Vel3<R>{W.u, W.v, W.w, r_win0}, W.dampu, r_vc, r_vf, R(dt), R(zd1),
@@ -1422,7 +1434,7 @@ int wec_tank3_create(const wec_grid3 *grid, const wec_fluids *fl, const wec_wave
                  (const double *)(dtab + eta.size()), (const double *)(dtab + eta.size() + uxz.size()), T->sig, T->u,
                  T->w);
         launch_k(k3t_materials<double>, grid3(T->P), 128, 0, T->st, T->P, (const double *)T->sig, T->zc, T->rho,
-                 T->mu, T->rhof, T->chi);
+                 T->mu, T->rhof, T->chi, 0);
         launch_k(k3t_hydrostatic, nblk((long long)nx * ny, 128), 128, 0, T->st, T->P, (const double *)T->rhof, T->g,
                  T->p);
         e = cudaGetLastError();
@@ -1504,7 +1516,7 @@ int wec_tank3_materials(wec_tank3 *T, double zc)
     {
         WEC_PROF("tank3_materials", 0, 40.0 * T->nc, T->st);
         launch_k(k3t_materials<double>, grid3(T->P), 128, 0, T->st, T->P, (const double *)T->sig, zc, T->rho, T->mu, T->rhof,
-                 T->chi);
+                 T->chi, 0);
     }
     WEC_CK(cudaGetLastError());
     WEC_CK(cudaStreamSynchronize(T->st));
