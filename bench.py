@@ -763,7 +763,9 @@ def main_tank3d(args):
         "data": "synthetic (seeded JONSWAP phases)",
         "config": {"workload": r["workload"], "cells": n, "l2": r["l2"], "solver_options": r["solver_options"],
                    "precision": "mixed: FP32 stencils over FP32 working copies and FP32 V-cycles; FP64 FGMRES, "
-                                "residual, force, heave, projection and fields"},
+                                "residual, force, heave, projection and fields",
+                   "solver_options_autotuned": {k: r[k]["solver_options_autotuned"]
+                                                for k in ("mixed", "mixed_mg", "fp64")}},
         "fp64_value": world * n * steps / t_d, "speedup_mixed_vs_fp64": t_d / t_m,
         "mixed_mg_value": world * n * steps / t_g, "speedup_mixed_mg_vs_fp64": t_d / t_g,
         "fgmres_iters": {k: r[k]["fgmres_iters"] for k in ("mixed", "mixed_mg", "fp64")},
