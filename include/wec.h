@@ -456,16 +456,19 @@ int wec_tank3_get_state(const wec_tank3 *tank, double *out5);
  * The paper has no counterpart: this exists for callers that cannot allocate
  * device memory when they need the number -- e.g. a control loop under a fixed
  * memory budget, or a process whose device memory all belongs to another
- * allocator.  The call allocates nothing: its scratch (residual vector, partial
- * sums, a counter) is one file-scope device array sized for nx * ny <= 1048576
- * cells (about 8 MiB, held by every GPU that loads the library until exit);
- * larger sizes return WEC_ERR_INVALID.  beta_u, beta_v, x, b: device, caller
+ * allocator.  The call allocates nothing: its scratch (608 per-block partial
+ * sums and a completion counter, about 4.9 KB) is one file-scope device array,
+ * held by every GPU that loads the library until exit.  Grids of up to
+ * nx * ny <= 2^28 cells are accepted (32-bit face indexing); larger sizes
+ * return WEC_ERR_INVALID.  beta_u, beta_v, x, b: device, caller
  * owned, layouts as in wec_poisson_set_coefficients.  Enqueued on cuda_stream
  * (NULL = legacy default stream); *norm_out is valid once that stream reaches
  * it.  The first call on each device looks up the array's device address (with
- * that device current); make that first call before any stream capture.  All
- * calls share the one array: calls that overlap on the GPU (different streams,
- * no ordering between them) race and may return wrong norms. */
+ * that device current); make that first call before any stream capture.  The
+ * address is kept for the life of the process: calls after a cudaDeviceReset
+ * are not supported.  All calls share the one array: calls that overlap on the
+ * GPU (different streams, no ordering between them) race and may return wrong
+ * norms. */
 int wec_residual_norm_noalloc(int nx, int ny, const double *beta_u, const double *beta_v, const double *x,
                               const double *b, double *norm_out, void *cuda_stream);
 

@@ -29,6 +29,16 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* Loops whose iterations are independent (each writes only its own output
+ * element; no reduction) may run on several host threads; every reduction and
+ * every order-dependent loop stays serial, so results do not depend on the
+ * thread count. */
+#ifdef _OPENMP
+#define ORACLE_PAR_FOR _Pragma("omp parallel for schedule(static)")
+#else
+#define ORACLE_PAR_FOR
+#endif
+
 #define PI3 3.14159265358979323846
 
 typedef struct {
@@ -72,6 +82,7 @@ void oracle3_materials(const oracle3_tank *P, const double *sg, double zc, doubl
 {
     double h = P->h;
     double rho_s = P->has_body ? P->body_mass / (PI3 * P->body_r * P->body_r * P->body_len) : P->rho_w;
+    ORACLE_PAR_FOR
     for (int k = 0; k < P->nz; ++k)
         for (int j = 0; j < P->ny; ++j)
             for (int i = 0; i < P->nx; ++i) {
@@ -183,6 +194,7 @@ static double advect_cell3(const oracle3_tank *P, const double *s, const double 
 void oracle3_advect(const oracle3_tank *P, const double *s, const double *u, const double *v, const double *w,
                     double dt, double t, double *out)
 {
+    ORACLE_PAR_FOR
     for (int k = 0; k < P->nz; ++k)
         for (int j = 0; j < P->ny; ++j)
             for (int i = 0; i < P->nx; ++i)
@@ -238,12 +250,14 @@ void oracle3_reinit(const oracle3_tank *P, double *s, int nit, double t)
     if (!s0 || !s1 || !s2) abort();
     memcpy(s0, s, n * sizeof(double));
     for (int it = 0; it < nit; ++it) {
+        ORACLE_PAR_FOR
         for (int k = 0; k < P->nz; ++k)
             for (int j = 0; j < P->ny; ++j)
                 for (int i = 0; i < P->nx; ++i) {
                     size_t c = ((size_t)k * P->ny + j) * P->nx + i;
                     s1[c] = s[c] - dtau * rrhs3(P, s, s0, i, j, k, t);
                 }
+        ORACLE_PAR_FOR
         for (int k = 0; k < P->nz; ++k)
             for (int j = 0; j < P->ny; ++j)
                 for (int i = 0; i < P->nx; ++i) {

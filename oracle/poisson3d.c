@@ -34,6 +34,16 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* Loops whose iterations are independent (each writes only its own output
+ * element; no reduction) may run on several host threads; every reduction and
+ * every order-dependent loop stays serial, so results do not depend on the
+ * thread count. */
+#ifdef _OPENMP
+#define ORACLE_PAR_FOR _Pragma("omp parallel for schedule(static)")
+#else
+#define ORACLE_PAR_FOR
+#endif
+
 typedef struct {
     int nx, ny, nz;
     double *bx, *by, *bz, *x, *b, *r;
@@ -79,6 +89,7 @@ static double offsum3(const lev3 *L, const double *x, int i, int j, int k)
 
 static void apply3(const lev3 *L, const double *x, double *y)
 {
+    ORACLE_PAR_FOR
     for (int k = 0; k < L->nz; ++k)
         for (int j = 0; j < L->ny; ++j)
             for (int i = 0; i < L->nx; ++i)
@@ -87,7 +98,8 @@ static void apply3(const lev3 *L, const double *x, double *y)
 
 static void rbgs3(lev3 *L)
 {
-    for (int color = 0; color < 2; ++color)
+    for (int color = 0; color < 2; ++color) {
+        ORACLE_PAR_FOR
         for (int k = 0; k < L->nz; ++k)
             for (int j = 0; j < L->ny; ++j)
                 for (int i = 0; i < L->nx; ++i)
@@ -95,6 +107,7 @@ static void rbgs3(lev3 *L)
                         size_t c = CELL(L, i, j, k);
                         L->x[c] = (L->b[c] + offsum3(L, L->x, i, j, k)) / diag3(L, i, j, k);
                     }
+    }
 }
 
 /* Dense LU without pivoting (A is a symmetric M-matrix), columns A e_q. */
@@ -159,6 +172,7 @@ static void hier3_build(hier3 *H, int nx, int ny, int nz, const double *bx, cons
             memcpy(L->bz, bz, sizeof(double) * nfz);
         } else {
             lev3 *F = &H->lev[H->nlev - 1];
+            ORACLE_PAR_FOR
             for (int K = 0; K < nz; ++K)
                 for (int J = 0; J < ny; ++J)
                     for (int I = 0; I <= nx; ++I) {
@@ -167,6 +181,7 @@ static void hier3_build(hier3 *H, int nx, int ny, int nz, const double *bx, cons
                             for (int a = 0; a < 2; ++a) s += BX(F, 2 * I, 2 * J + a, 2 * K + b);
                         BX(L, I, J, K) = 0.5 * s;
                     }
+            ORACLE_PAR_FOR
             for (int K = 0; K < nz; ++K)
                 for (int J = 0; J <= ny; ++J)
                     for (int I = 0; I < nx; ++I) {
@@ -175,6 +190,7 @@ static void hier3_build(hier3 *H, int nx, int ny, int nz, const double *bx, cons
                             for (int a = 0; a < 2; ++a) s += BY(F, 2 * I + a, 2 * J, 2 * K + b);
                         BY(L, I, J, K) = 0.5 * s;
                     }
+            ORACLE_PAR_FOR
             for (int K = 0; K <= nz; ++K)
                 for (int J = 0; J < ny; ++J)
                     for (int I = 0; I < nx; ++I) {
@@ -216,8 +232,10 @@ static void vcycle3(hier3 *H, int l)
     memset(L->x, 0, sizeof(double) * n);
     for (int s = 0; s < H->nu1; ++s) rbgs3(L);
     apply3(L, L->x, L->r);
+    ORACLE_PAR_FOR
     for (size_t c = 0; c < n; ++c) L->r[c] = L->b[c] - L->r[c];
     lev3 *C = &H->lev[l + 1];
+    ORACLE_PAR_FOR
     for (int K = 0; K < C->nz; ++K)
         for (int J = 0; J < C->ny; ++J)
             for (int I = 0; I < C->nx; ++I) {
@@ -228,6 +246,7 @@ static void vcycle3(hier3 *H, int l)
                 C->b[CELL(C, I, J, K)] = s;
             }
     vcycle3(H, l + 1);
+    ORACLE_PAR_FOR
     for (int k = 0; k < L->nz; ++k)
         for (int j = 0; j < L->ny; ++j)
             for (int i = 0; i < L->nx; ++i) L->x[CELL(L, i, j, k)] += C->x[CELL(C, i / 2, j / 2, k / 2)];
@@ -259,10 +278,12 @@ static int fgmres3(hier3 *H, const double *b, double *x, double rtol, int maxit,
     double *h = zalloc(m + 1), *y = zalloc(m);
     int its = 0, conv = 0;
     apply3(L0, x, w);
+    ORACLE_PAR_FOR
     for (size_t c = 0; c < n; ++c) w[c] = b[c] - w[c];
     double beta = sqrt(dot3(w, w, n));
     if (beta <= tol) conv = 1;
     while (!conv && its < maxit) {
+        ORACLE_PAR_FOR
         for (size_t c = 0; c < n; ++c) V[c] = w[c] / beta;
         for (int q = 0; q <= m; ++q) g[q] = 0.0;
         g[0] = beta;
@@ -280,6 +301,7 @@ static int fgmres3(hier3 *H, const double *b, double *x, double rtol, int maxit,
                 for (int q = 0; q <= j; ++q) h[q] = dot3(V + (size_t)q * n, w, n);
                 for (int q = 0; q <= j; ++q) {
                     const double *vq = V + (size_t)q * n;
+                    ORACLE_PAR_FOR
                     for (size_t c = 0; c < n; ++c) w[c] -= h[q] * vq[c];
                     Hm[q * m + j] += h[q];
                 }
@@ -302,6 +324,7 @@ static int fgmres3(hier3 *H, const double *b, double *x, double rtol, int maxit,
             g[j] = cs[j] * g[j];
             used = j + 1;
             if (fabs(g[j + 1]) <= tol || its >= maxit || hn == 0.0) break;
+            ORACLE_PAR_FOR
             for (size_t c = 0; c < n; ++c) V[(size_t)(j + 1) * n + c] = w[c] / hn;
         }
         /* x += Z y with R y = g */
@@ -312,9 +335,11 @@ static int fgmres3(hier3 *H, const double *b, double *x, double rtol, int maxit,
         }
         for (int q = 0; q < used; ++q) {
             const double *zq = Z + (size_t)q * n;
+            ORACLE_PAR_FOR
             for (size_t c = 0; c < n; ++c) x[c] += y[q] * zq[c];
         }
         apply3(L0, x, w);
+        ORACLE_PAR_FOR
         for (size_t c = 0; c < n; ++c) w[c] = b[c] - w[c];
         beta = sqrt(dot3(w, w, n));
         if (beta <= tol) conv = 1;

@@ -53,6 +53,8 @@ def lib():
     global _lib
     if _lib is None:
         L = C.CDLL(_build.build())
+        L.oracle_threads.restype = C.c_int
+        L.oracle_threads.argtypes = [C.c_int]
         L.oracle_create.restype = C.c_void_p
         L.oracle_create.argtypes = [C.POINTER(Params)]
         L.oracle_destroy.argtypes = [C.c_void_p]

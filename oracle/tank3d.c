@@ -31,6 +31,30 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* Loops whose iterations are independent (each writes only its own output
+ * element; no reduction) may run on several host threads; every reduction and
+ * every order-dependent loop stays serial, so results do not depend on the
+ * thread count. */
+#ifdef _OPENMP
+#include <omp.h>
+#define ORACLE_PAR_FOR _Pragma("omp parallel for schedule(static)")
+#else
+#define ORACLE_PAR_FOR
+#endif
+
+/* Host threads of the marked loops of every oracle file: n > 0 sets the count;
+ * returns the count in use (1 when built without OpenMP). */
+int oracle_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
 #define PIT 3.14159265358979323846
 
 /* the level-set oracle's parameter block (levelset3d.c) */
@@ -510,6 +534,7 @@ int oracle3_step(void *handle, double dt, double f_pto_in, oracle3_result *out)
     /* (5) transport and the momentum system */
     tctx3 X = {T, rho_n, T->u, T->v, T->w, t0};
     vctx3 Vn = {T, mu_n, T->u, T->v, T->w, t0};
+    ORACLE_PAR_FOR
     for (int k = 0; k < nz; ++k)
         for (int j = 0; j < ny; ++j)
             for (int i = 1; i < nx; ++i) {
@@ -521,6 +546,7 @@ int oracle3_step(void *handle, double dt, double f_pto_in, oracle3_result *out)
                 Ru[f] = rut(T, rho_n, i, j, k) * T->u[f] / dt - C + 0.5 * viscx3(&Vn, i, j, k) -
                         (T->p[CI(i, j, k)] - T->p[CI(i - 1, j, k)]) / h;
             }
+    ORACLE_PAR_FOR
     for (int k = 0; k < nz; ++k)
         for (int j = 1; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
@@ -532,6 +558,7 @@ int oracle3_step(void *handle, double dt, double f_pto_in, oracle3_result *out)
                 Rv[f] = rvt(T, rho_n, i, j, k) * T->v[f] / dt - C + 0.5 * viscy3(&Vn, i, j, k) -
                         (T->p[CI(i, j, k)] - T->p[CI(i, j - 1, k)]) / h;
             }
+    ORACLE_PAR_FOR
     for (int k = 1; k <= nz; ++k)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
@@ -571,6 +598,7 @@ int oracle3_step(void *handle, double dt, double f_pto_in, oracle3_result *out)
     memcpy(wb, wa, nw * sizeof(double));
     for (int it = 0; it < T->P.n_jacobi; ++it) {
         vctx3 Vk = {T, mu_1, ua, va, wa, t1};
+        ORACLE_PAR_FOR
         for (int k = 0; k < nz; ++k)
             for (int j = 0; j < ny; ++j)
                 for (int i = 1; i < nx; ++i) {
@@ -578,6 +606,7 @@ int oracle3_step(void *handle, double dt, double f_pto_in, oracle3_result *out)
                     double ld = vdiagx3(&Vk, i, j, k);
                     ub[f] = (Ru[f] + 0.5 * (viscx3(&Vk, i, j, k) - ld * ua[f])) / (Du[f] - 0.5 * ld);
                 }
+        ORACLE_PAR_FOR
         for (int k = 0; k < nz; ++k)
             for (int j = 1; j < ny; ++j)
                 for (int i = 0; i < nx; ++i) {
@@ -585,6 +614,7 @@ int oracle3_step(void *handle, double dt, double f_pto_in, oracle3_result *out)
                     double ld = vdiagy3(&Vk, i, j, k);
                     vb[f] = (Rv[f] + 0.5 * (viscy3(&Vk, i, j, k) - ld * va[f])) / (Dv[f] - 0.5 * ld);
                 }
+        ORACLE_PAR_FOR
         for (int k = 1; k <= nz; ++k)
             for (int j = 0; j < ny; ++j)
                 for (int i = 0; i < nx; ++i) {
@@ -599,15 +629,19 @@ int oracle3_step(void *handle, double dt, double f_pto_in, oracle3_result *out)
 
     /* (7) pressure increment */
     double *bx = zal(nu), *by = zal(nv), *bz = zal(nw), *rhs = zal(n), *phi = zal(n);
+    ORACLE_PAR_FOR
     for (int k = 0; k < nz; ++k)
         for (int j = 0; j < ny; ++j)
             for (int i = 1; i < nx; ++i) bx[UI(i, j, k)] = 1.0 / Du[UI(i, j, k)];
+    ORACLE_PAR_FOR
     for (int k = 0; k < nz; ++k)
         for (int j = 1; j < ny; ++j)
             for (int i = 0; i < nx; ++i) by[VI(i, j, k)] = 1.0 / Dv[VI(i, j, k)];
+    ORACLE_PAR_FOR
     for (int k = 1; k <= nz; ++k)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) bz[WI(i, j, k)] = 1.0 / Dw[WI(i, j, k)];
+    ORACLE_PAR_FOR
     for (int k = 0; k < nz; ++k)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i)
@@ -621,6 +655,7 @@ int oracle3_step(void *handle, double dt, double f_pto_in, oracle3_result *out)
     for (size_t c = 0; c < n; ++c) bn += rhs[c] * rhs[c];
 
     /* (8) projection */
+    ORACLE_PAR_FOR
     for (int k = 0; k < nz; ++k)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i <= nx; ++i) {
@@ -629,6 +664,7 @@ int oracle3_step(void *handle, double dt, double f_pto_in, oracle3_result *out)
                 if (i > 0 && i < nx) uu -= bx[f] * (phi[CI(i, j, k)] - phi[CI(i - 1, j, k)]) / h;
                 T->u[f] = uu;
             }
+    ORACLE_PAR_FOR
     for (int k = 0; k < nz; ++k)
         for (int j = 0; j <= ny; ++j)
             for (int i = 0; i < nx; ++i) {
@@ -637,6 +673,7 @@ int oracle3_step(void *handle, double dt, double f_pto_in, oracle3_result *out)
                 if (j > 0 && j < ny) vv -= by[f] * (phi[CI(i, j, k)] - phi[CI(i, j - 1, k)]) / h;
                 T->v[f] = vv;
             }
+    ORACLE_PAR_FOR
     for (int k = 0; k <= nz; ++k)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
@@ -646,6 +683,7 @@ int oracle3_step(void *handle, double dt, double f_pto_in, oracle3_result *out)
                 if (k == nz) ww += 2.0 * bz[f] * phi[CI(i, j, nz - 1)] / h;
                 T->w[f] = ww;
             }
+    ORACLE_PAR_FOR
     for (size_t c = 0; c < n; ++c) T->p[c] += phi[c];
     memcpy(T->sig, sig1, n * sizeof(double));
     T->t = t1;
@@ -706,24 +744,28 @@ void *oracle3_create(const oracle3_params *P, double zc)
     T->p = zal(n);
     T->zc = T->zc0 = zc;
     double h = T->h;
+    /* the incident wave does not depend on y: each value is evaluated once per
+     * (x, z) and copied along y */
+    ORACLE_PAR_FOR
     for (int k = 0; k < nz; ++k)
-        for (int j = 0; j < ny; ++j)
-            for (int i = 0; i < nx; ++i)
-                T->sig[CI(i, j, k)] = (k + 0.5) * h - P->L.depth - etat(T, (i + 0.5) * h, 0.0);
+        for (int i = 0; i < nx; ++i) {
+            double s = (k + 0.5) * h - P->L.depth - etat(T, (i + 0.5) * h, 0.0);
+            for (int j = 0; j < ny; ++j) T->sig[CI(i, j, k)] = s;
+        }
+    ORACLE_PAR_FOR
     for (int k = 0; k < nz; ++k)
-        for (int j = 0; j < ny; ++j)
-            for (int i = 0; i <= nx; ++i) {
-                double uu, ww;
-                airyt(T, i * h, (k + 0.5) * h, 0.0, &uu, &ww);
-                T->u[UI(i, j, k)] = i == nx ? 0.0 : uu;
-            }
+        for (int i = 0; i <= nx; ++i) {
+            double uu, ww;
+            airyt(T, i * h, (k + 0.5) * h, 0.0, &uu, &ww);
+            for (int j = 0; j < ny; ++j) T->u[UI(i, j, k)] = i == nx ? 0.0 : uu;
+        }
+    ORACLE_PAR_FOR
     for (int k = 1; k <= nz; ++k)
-        for (int j = 0; j < ny; ++j)
-            for (int i = 0; i < nx; ++i) {
-                double uu, ww;
-                airyt(T, (i + 0.5) * h, k * h, 0.0, &uu, &ww);
-                T->w[WI(i, j, k)] = ww;
-            }
+        for (int i = 0; i < nx; ++i) {
+            double uu, ww;
+            airyt(T, (i + 0.5) * h, k * h, 0.0, &uu, &ww);
+            for (int j = 0; j < ny; ++j) T->w[WI(i, j, k)] = ww;
+        }
     double *rho = zal(n), *mu = zal(n), *rf = zal(n), *chi = zal(n);
     oracle3_materials(&T->P.L, T->sig, zc, rho, mu, rf, chi);
     for (int j = 0; j < ny; ++j)

@@ -43,12 +43,17 @@ __device__ __forceinline__ void pdl_entry()
     asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
+namespace prof {
+void count_launch();  // one kernel launch (or one kernel node recorded into a graph being captured)
+}
+
 // kern<<<grid, block, smem, st>>>(args...) with programmatic dependent launch
-// allowed (captured into graphs as programmatic edges).
+// allowed (captured into graphs as programmatic edges); every launch is counted.
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
                             Args &&...args)
 {
+    prof::count_launch();
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
     cfg.blockDim = block;
@@ -62,7 +67,8 @@ inline cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_
     return cudaLaunchKernelEx(&cfg, kern, static_cast<Args &&>(args)...);
 }
 
-// Launch accounting (profile.cu): open one Scope around every kernel launch.
+// Per-kernel event profiling (profile.cu): a Scope around a launch names the
+// kernel, its level and its algorithmic bytes.
 namespace prof {
 class Scope {
   public:

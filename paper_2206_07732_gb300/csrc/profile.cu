@@ -1,9 +1,11 @@
 // Launch counter and per-kernel CUDA-event profiler of libwec.
 //
-// Every kernel launch site opens a prof::Scope naming the kernel, its multigrid
+// Every kernel launch goes through launch_k, which counts it (a launch recorded
+// into a graph is counted each time the graph runs).  Launch sites of the
+// kernels worth timing open a prof::Scope naming the kernel, its multigrid
 // level (or -1) and its algorithmic bytes (the bytes the operation must move
-// at least once: inputs read, outputs written).  The counter always runs; when
-// profiling is on, the scope records a CUDA event pair on the launching stream.
+// at least once: inputs read, outputs written); when profiling is on, the
+// scope records a CUDA event pair on the launching stream.
 #include <mutex>
 #include <string>
 #include <vector>
@@ -44,7 +46,7 @@ cudaEvent_t take_event()
 
 }  // namespace
 
-Scope::Scope(const char *name, int level, double bytes, cudaStream_t st) : slot_(-1), st_(st)
+void count_launch()
 {
     if (t_capturing) {  // recorded into a graph: counted when the graph runs
         ++t_captured;
@@ -52,6 +54,12 @@ Scope::Scope(const char *name, int level, double bytes, cudaStream_t st) : slot_
     }
     std::lock_guard<std::mutex> lk(g_mu);
     ++g_launches;
+}
+
+Scope::Scope(const char *name, int level, double bytes, cudaStream_t st) : slot_(-1), st_(st)
+{
+    if (t_capturing) return;  // graph bodies hold no events
+    std::lock_guard<std::mutex> lk(g_mu);
     if (g_mode == 0 || (g_mode == 2 && g_only != name)) return;
     Rec r{name, level, bytes, take_event(), take_event()};
     cudaEventRecord(r.a, st);

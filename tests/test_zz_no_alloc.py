@@ -65,8 +65,9 @@ def test_noalloc_norm_matches_solver_residual(lib, nx, ny):
 
 
 def test_noalloc_rejects_oversize(lib):
+    # 2^29 cells, above the 2^28 maximum: rejected on the host before any launch
     t = torch.zeros(8, dtype=torch.float64, device="cuda")
     p = C.c_void_p(t.data_ptr())
-    code = lib.wec_residual_norm_noalloc(2048, 1024, p, p, p, p, p, None)
+    code = lib.wec_residual_norm_noalloc(32768, 16384, p, p, p, p, p, None)
     assert code == wec.WEC_ERR_INVALID
     assert b"exceeds" in lib.wec_last_error()
