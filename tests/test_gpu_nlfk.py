@@ -21,10 +21,13 @@ def wec():
 @pytest.mark.parametrize("mode", [0, 1])
 def test_nlfk_matches_oracle(wec, mode):
     from oracle import tank as O
+    from oracle import waves as OW
     depth = 2.5
-    amp, om = wec.jonswap(0.15, 1.6, 3.3, 64)  # the large tank's sea state
+    # the large tank's sea state and the oracle's own wave numbers (the library
+    # solves the dispersion relation itself from omega)
     ph = np.random.default_rng(4).uniform(0.0, 2.0 * math.pi, 64)
-    kw = np.array([wec.wave_number(o, depth, 9.81) for o in om])
+    amp, om, _ = OW.jonswap_components(0.15, 1.6, 3.3, 64, ph)
+    kw = np.array([OW.dispersion_k(o, depth, 9.81) for o in om])
     region = (4.0, 1.5, 1.0 / 64.0, 192, 128)  # 3 m x 2 m around the body, large-tank spacing
     body = dict(xc=5.5, width=1.0, height=0.8)
     N = wec.Nlfk(region, depth, amp, om, ph, body)
