@@ -67,6 +67,8 @@ def parse():
                     help="profiling helper: run warm-up + this many steps only, print nothing")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "mixed_fp32_stencils"],
                     help="profiling helper (tank3d): the path of the --ncu-steps run")
+    ap.add_argument("--shape3", default=None,
+                    help="profiling helper (tank3d): grid 'nx,ny,nz' of the --ncu-steps run (default 512,256,256)")
     ap.add_argument("--mg-opts", default=None,
                     help="profiling helper: solver options 'mg_pre,mg_post,restart' of the --ncu-steps run "
                          "(default: the workload's own)")
@@ -234,6 +236,32 @@ def make_controller(wec, torch, cfg, steps=8000):
             "identified": {"m_eff_kg_per_m": m_eff, "c_r_Ns_per_m2": c_r, "omega_n": wn, "zeta": zeta,
                            "free_decay_steps": steps},
             "excitation": "k_h eta(x_B, t) of the tank's incident components (analytic forecast)"}
+    return ctl, info
+
+
+def make_controller3(wec, cfg, f_max=2000.0, shape=(128, 64, 64), dt=2e-3, steps=2000):
+    """The host MPC of the 3D buoy's PTO force (untimed set-up): effective mass
+    and radiation damping from a free-decay run of the same tank physics in
+    still water on a coarser grid (128 x 64 x 64, h = 1/16 m), the cylinder
+    released 2 cm below its draft; k_h = rho_w g pi R^2; then the controller
+    with the paper's parameters (dt_p 0.05 s, horizon one peak period, lam1 2 s,
+    lam2 0.2 s) and |F_PTO| <= f_max."""
+    from paper_2206_07732_gb300 import mpc, synth
+    c = synth.tank3d(seed=0, nx=shape[0], ny=shape[1], nz=shape[2])
+    c["wave"] = {"kind": "regular", "H": 0.0, "T": 2.0, "phase": 0.0}
+    c["body"]["zc"] -= 0.02
+    T = wec.Tank3(c, precision=wec.PREC_MIXED)
+    recs = [T.step(dt) for _ in range(steps)]
+    T.close()
+    b = cfg["body"]
+    kh = cfg["rho_w"] * cfg["g"] * math.pi * b["radius"] ** 2
+    m_eff, c_r, wn, zeta = mpc.identify_free_decay([r["t"] for r in recs], [r["z"] - 0.02 for r in recs], kh)
+    dt_p = 0.05
+    Np = math.ceil(cfg["wave"]["Tp"] / dt_p)
+    ctl = mpc.MPC(m_eff, kh, c_r, dt_p, Np, lam1=2.0, lam2=0.2, f_max=f_max)
+    info = {"identified": {"m_eff_kg": m_eff, "body_mass_kg": b["mass"], "c_r_Ns_per_m": c_r, "omega_n": wn,
+                           "zeta": zeta, "free_decay": f"{steps} steps of dt {dt} s on {shape}"},
+            "dt_p_s": dt_p, "Np": Np, "f_max_N": f_max}
     return ctl, info
 
 
@@ -972,7 +1000,8 @@ def make_line3(c, seed, world, steps, warmup, tuned, res, t, tw, ck, roof, cpu, 
                    "cells": n, "precision": PATH3_NOTE["mixed"],
                    "learned_warm_start": "not used: the U-Net is two-dimensional, so configuration 5 runs without "
                                          "the network (the 2D tank's learned path is under tank2d)",
-                   "pto": "none applied (the cylinder's heave is free)",
+                   "pto": "host MPC (FOH heave model identified by a free decay, J_3, |F_PTO| <= 2 kN, QP every "
+                          "0.05 s of simulated time, between steps)",
                    "solver_options_autotuned": tuned,
                    "l2": "inputs larger than L2 (268 MB per FP64 cell array), no flush", "seed": seed},
         "fp64_value": val["fp64"], "speedup_vs_fp64": val["mixed"] / val["fp64"],
@@ -997,7 +1026,11 @@ def main_tank3d(args):
     c = synth.tank3d(seed=args.seed)
     if args.ncu_steps:
         # profiling helper: warm-up + ncu_steps steps of the tank at the given
-        # precision (--precision) and solver options (--mg-opts), no output
+        # precision (--precision), grid (--shape3) and solver options (--mg-opts),
+        # no output
+        if args.shape3:
+            nx, ny, nz = (int(v) for v in args.shape3.split(","))
+            c = synth.tank3d(seed=args.seed, nx=nx, ny=ny, nz=nz)
         if args.mg_opts:
             c = tune.with_options(c, [int(v) for v in args.mg_opts.split(",")])
         prec = getattr(wec, dict(PATHS3)[args.precision])
@@ -1018,12 +1051,16 @@ def main_tank3d(args):
         detail.setdefault("tuning", {})[key] = table
         cfgs[key] = tune.with_options(c, opts)
     # the timed runs: the credited path with the clocks sampled, then the others
+    # the PTO force of every path: the host MPC (its QP runs between steps)
+    ctl, ctl_info = make_controller3(wec, c)
+    detail["pto_control"] = ctl_info
     res = {}
     clocks = Clocks(local)
     for key, pname in PATHS3:
         if key == "mixed":
             clocks.start()
-        res[key] = time_tank3(wec, torch, cfgs[key], getattr(wec, pname), steps, warmup, world)
+        res[key] = time_tank3(wec, torch, cfgs[key], getattr(wec, pname), steps, warmup, world,
+                              pto=lambda cfg: PtoSchedule(ctl, cfg, wec))
         if key == "mixed":
             ck = clocks.stop()
     t = {k: reduce_max(torch, world, sum(v["ms"]) / 1e3) for k, v in res.items()}
@@ -1058,7 +1095,9 @@ def main_tank3d(args):
         except Exception as ex:  # reported, not fatal to the 3D line
             tank2d = {"error": f"{type(ex).__name__}: {ex}"}
     detail.update({"paths": {k: {"ms_per_step_all": res[k]["ms"], "wall_s_all": res[k]["wall"],
-                                 "fgmres_iters": res[k]["iters"], "max_relative_residual": res[k]["residual"]}
+                                 "fgmres_iters": res[k]["iters"], "max_relative_residual": res[k]["residual"],
+                                 "qp_solves": res[k]["qp_solves"], "max_abs_pto_force_N": res[k]["max_pto"],
+                                 "heave_z_m": res[k]["z"]}
                              for k in res}, "solver_options_autotuned": tuned, "clocks": ck})
     line = make_line3(c, args.seed, world, steps, warmup, tuned, res, t, tw, ck, roof, cpu, tank2d)
     line["detail_file"] = write_detail(args.detail, dict(detail, line=line)) if rank == 0 else None

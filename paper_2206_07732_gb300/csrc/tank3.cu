@@ -62,6 +62,9 @@ struct Work3 {
     R *sig = nullptr, *tmp = nullptr, *s0 = nullptr, *s1 = nullptr, *u = nullptr, *v = nullptr, *w = nullptr;
     R *rho = nullptr, *mu = nullptr, *rf = nullptr, *chi = nullptr, *mu1 = nullptr, *rf1 = nullptr, *chi1 = nullptr;
     R *D[3] = {}, *R3[3] = {}, *A[3] = {}, *B[3] = {};
+    R *E[3] = {};        // edge viscosities (xy, xz, yz) of the viscosity the current kernels read
+    R *RF[3] = {};       // face densities of rho^n at the u-, v-, w-faces
+    R *Q[3] = {};        // Jacobi factor (1/2 h^-2) / (D + L / (2 h^2)) per solved face
     R *bc = nullptr;     // u_in(t1) [nz], w_in(t0) [nz+1], w_in(t1) [nz+1], vorticity damping [nz], [nz+1]
     R *dampu = nullptr;  // damping weight of the u-faces [nx+1]
 };
@@ -81,6 +84,7 @@ struct wec_tank3 {
     double *p = nullptr, *phi = nullptr, *rhs = nullptr;
     double *mu1 = nullptr, *rf1 = nullptr, *chi1 = nullptr;
     double *D[3] = {}, *R[3] = {}, *A[3] = {}, *B[3] = {};  // per component u, v, w
+    double *E[3] = {}, *RF[3] = {}, *Q[3] = {};             // as Work3: edge viscosities, face densities, Jacobi factors
     double *bc = nullptr;    // [nz] u_in(t1) at the cell layers; [nz+1] w_in(t0), w_in(t1) at the faces
     double *tabs = nullptr;  // damping weight of the u-faces [nx+1]; vorticity damping at cell / face heights
     double *part = nullptr;  // reduction partials
@@ -150,14 +154,67 @@ __device__ __forceinline__ R sig3(const Tank3P &P, const R *__restrict__ s, int 
     return s[k * pl + col];
 }
 
+// Sign and magnitude decisions of the FP64 stencils on the integer pipe: for
+// finite doubles the bit pattern orders magnitudes (sign bit shifted out) and
+// carries the sign, and this GPU issues FP64 compares, min / max and products
+// at 1/64 of its FP32 rate.  The FP32 stencils keep plain float compares.
+__device__ __forceinline__ unsigned long long mag_bits(double a)
+{
+    return (unsigned long long)__double_as_longlong(a) << 1;
+}
+// a * b <= 0 (opposite signs, or a zero factor)
+template <typename R>
+__device__ __forceinline__ bool nonpos_prod(R a, R b)
+{
+    if constexpr (sizeof(R) == 8) {
+        const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+        return (ia ^ ib) < 0 || (ia << 1) == 0 || (ib << 1) == 0;
+    } else {
+        return a * b <= R(0);
+    }
+}
+// |a| < |b|
+template <typename R>
+__device__ __forceinline__ bool abs_lt(R a, R b)
+{
+    if constexpr (sizeof(R) == 8) return mag_bits(a) < mag_bits(b); else return fabs(a) < fabs(b);
+}
+// a > 0
+template <typename R>
+__device__ __forceinline__ bool positive(R a)
+{
+    if constexpr (sizeof(R) == 8) return __double_as_longlong(a) > 0; else return a > R(0);
+}
+
+// van Leer slope of the middle cell: 0 at an extremum, else the smallest of
+// |dc|, 2|dl|, 2|dr| with the sign of dc (the magnitude choice and the sign on
+// the integer pipe in FP64)
 template <typename R>
 __device__ __forceinline__ R vl3(R am, R a0, R ap)
 {
     const R dl = a0 - am, dr = ap - a0;
-    if (dl * dr <= R(0)) return R(0);
-    const R dc = R(0.5) * (ap - am);
-    const R m = fmin(fabs(dc), fmin(R(2) * fabs(dl), R(2) * fabs(dr)));
-    return dc > R(0) ? m : -m;
+    if (nonpos_prod(dl, dr)) return R(0);
+    const R dc = R(0.5) * (ap - am), tl = R(2) * dl, tr = R(2) * dr;
+    if constexpr (sizeof(R) == 8) {
+        unsigned long long m = mag_bits(dc);
+        const unsigned long long ml = mag_bits(tl), mr = mag_bits(tr);
+        m = ml < m ? ml : m;
+        m = mr < m ? mr : m;
+        // |result| = the smallest magnitude, sign of dc
+        const unsigned long long sgn = (unsigned long long)__double_as_longlong(dc) & 0x8000000000000000ull;
+        return __longlong_as_double((long long)((m >> 1) | sgn));
+    } else {
+        const R m = fmin(fabs(dc), fmin(fabs(tl), fabs(tr)));
+        return dc > R(0) ? m : -m;
+    }
+}
+
+// a > b for b >= 0 (FP64 on the integer pipe: the signed bit patterns order
+// a against a non-negative b)
+template <typename R>
+__device__ __forceinline__ bool gt_nonneg(R a, R b)
+{
+    if constexpr (sizeof(R) == 8) return __double_as_longlong(a) > __double_as_longlong(b); else return a > b;
 }
 
 // limited PPM edge values (eL, eR) of the middle cell of a[0..4]
@@ -169,14 +226,14 @@ __device__ __forceinline__ void ppm_edges3(const R *a, R &eL, R &eR)
     R L = a[1] + R(0.5) * (a[2] - a[1]) - (d0 - dm) * i6;
     R Rr = a[2] + R(0.5) * (a[3] - a[2]) - (dp - d0) * i6;
     const R c = a[2];
-    if ((Rr - c) * (c - L) <= R(0)) {
+    if (nonpos_prod(Rr - c, c - L)) {
         L = c;
         Rr = c;
     } else {
         const R dA = Rr - L, m6 = dA * (c - R(0.5) * (L + Rr)), q = dA * dA * i6;
-        if (m6 > q)
+        if (gt_nonneg(m6, q))
             L = R(3) * c - R(2) * Rr;
-        else if (-q > m6)
+        else if (gt_nonneg(-m6, q))
             Rr = R(3) * c - R(2) * L;
     }
     eL = L;
@@ -190,7 +247,12 @@ __device__ __forceinline__ R ppm_face3(const R *a, R vel, R dtih)
 {
     const R t3 = R(2.0 / 3.0);
     R L, Rr;
-    if (vel >= R(0)) {
+    bool up;
+    if constexpr (sizeof(R) == 8)  // vel >= 0, -0 included
+        up = __double_as_longlong(vel) >= 0 || (__double_as_longlong(vel) << 1) == 0;
+    else
+        up = vel >= R(0);
+    if (up) {
         ppm_edges3(a, L, Rr);
         const R C = vel * dtih, dA = Rr - L, a6 = R(6) * (a[2] - R(0.5) * (L + Rr));
         return Rr - R(0.5) * C * (dA - (R(1) - C * t3) * a6);
@@ -285,19 +347,23 @@ __global__ void __launch_bounds__(128) k3t_advect(Tank3P P, const R *__restrict_
 template <typename R>
 __device__ __forceinline__ R mm3(R a, R b)
 {
-    if (a * b <= R(0)) return R(0);
-    return fabs(a) < fabs(b) ? a : b;
+    if (nonpos_prod(a, b)) return R(0);
+    return abs_lt(a, b) ? a : b;
 }
 
-// S(sigma0) (|grad f| - 1) at a cell
+// S(sigma0) (|grad f| - 1) at a cell; S = sigma0 / sqrt(sigma0^2 + h^2), formed
+// once per reinitialisation (k3t_reinit_sign).  The one-sided ENO-2 slopes are
+// taken in units of 1/h (a_h = h a) and the Godunov Hamiltonian's squares
+// summed before the single scaling by 1/h^2; max(max(a, 0)^2, min(b, 0)^2) for
+// S > 0 (mirrored for S <= 0) is the square of the largest of a, -b and 0.
 template <typename R>
-__device__ __forceinline__ R reinit_rhs3(const Tank3P &P, const R *__restrict__ f, const R *__restrict__ s0,
+__device__ __forceinline__ R reinit_rhs3(const Tank3P &P, const R *__restrict__ f, const R *__restrict__ sg,
                                          const Cell3 &q, const Ghost3 &G)
 {
     const Tank3C<R> &K = cst3<R>(P);
-    const R h = K.h, ih = K.ih, hih = R(0.5) * K.ih, c = f[q.c];
-    const R sg0 = s0[q.c];
-    const bool pos = sg0 > R(0);
+    const R c = f[q.c];
+    const R S = sg[q.c];
+    const bool pos = positive(S);
     // cells two or more from every boundary read their neighbours at fixed
     // offsets (no ghosts, 32-bit indices); the others through sig3
     const bool inner = q.i >= 2 && q.i < P.nx - 2 && q.j >= 2 && q.j < P.ny - 2 && q.k >= 2 && q.k < P.nz - 2;
@@ -320,32 +386,43 @@ __device__ __forceinline__ R reinit_rhs3(const Tank3P &P, const R *__restrict__ 
             p2 = sig3<R>(P, f, q.i + 2 * di, q.j + 2 * dj, q.k + 2 * dk, G);
         }
         const R dm = m2 - R(2) * m1 + c, d0 = m1 - R(2) * c + p1, dp = c - R(2) * p1 + p2;
-        const R a = (c - m1) * ih + mm3(dm, d0) * hih;
-        const R b = (p1 - c) * ih - mm3(d0, dp) * hih;
-        R g;
-        if (pos) {
-            const R x = fmax(a, R(0)), y = fmin(b, R(0));
-            g = fmax(x * x, y * y);
-        } else {
-            const R x = fmin(a, R(0)), y = fmax(b, R(0));
-            g = fmax(x * x, y * y);
-        }
-        g2 = d == 0 ? g : g2 + g;
+        const R a = (c - m1) + R(0.5) * mm3(dm, d0);
+        const R nb = (c - p1) + R(0.5) * mm3(d0, dp);  // -b
+        // pos: the largest of a, -b and 0; else of -a, b and 0
+        const R x = pos ? a : -a, y = pos ? nb : -nb;
+        R m = positive(x) ? x : R(0);
+        bool ybig;
+        if constexpr (sizeof(R) == 8)
+            ybig = positive(y) && mag_bits(y) > mag_bits(m);
+        else
+            ybig = y > m;
+        if (ybig) m = y;
+        g2 += m * m;
     }
-    const R S = sg0 * rsqrt(sg0 * sg0 + h * h);
-    return S * (sqrt(g2) - R(1));
+    return S * (sqrt(g2 * K.ih * K.ih) - R(1));
+}
+
+// S(sigma0) = sigma0 / sqrt(sigma0^2 + h^2) in place
+template <typename R>
+__global__ void __launch_bounds__(128) k3t_reinit_sign(Tank3P P, R *__restrict__ s0)
+{
+    pdl_entry();
+    Cell3 q;
+    if (!cell_of(P, q)) return;
+    const R h = cst3<R>(P).h, g = s0[q.c];
+    s0[q.c] = g * rsqrt(g * g + h * h);
 }
 
 // stage 1: out = f - dtau L(f); stage 2: out = (out + (f - dtau L(f))) / 2 with
 // out holding sigma at the start of the pseudo-step
 template <typename R>
-__global__ void __launch_bounds__(128) k3t_reinit_stage(Tank3P P, const R *__restrict__ f, const R *__restrict__ s0,
+__global__ void __launch_bounds__(128) k3t_reinit_stage(Tank3P P, const R *__restrict__ f, const R *__restrict__ sg,
                                                         R *out, Ghost3 G, double dtau, int stage)
 {
     pdl_entry();
     Cell3 q;
     if (!cell_of(P, q)) return;
-    const R y = f[q.c] - R(dtau) * reinit_rhs3<R>(P, f, s0, q, G);
+    const R y = f[q.c] - R(dtau) * reinit_rhs3<R>(P, f, sg, q, G);
     out[q.c] = stage == 1 ? y : R(0.5) * (out[q.c] + y);
 }
 
@@ -392,18 +469,36 @@ __device__ __forceinline__ R wq(const Tank3P &P, const R *__restrict__ w, const 
     return w[((long long)k * P.ny + j) * P.nx + i];
 }
 
+// Koren-limited upwind face value: qu at an extremum, else qu + m/2 with m the
+// smallest of 2|d2|, (|d1| + 2|d2|)/3, 2|d1| carrying the sign of d1 (FP64: the
+// choice and the sign on the integer pipe)
 template <typename R>
 __device__ __forceinline__ R koren3(R quu, R qu, R qd)
 {
     const R d1 = qu - quu, d2 = qd - qu;
-    if (d1 * d2 <= R(0)) return qu;
-    const R m = fmin(R(2) * fabs(d2), fmin((fabs(d1) + R(2) * fabs(d2)) / R(3), R(2) * fabs(d1)));
-    return d1 > R(0) ? qu + R(0.5) * m : qu - R(0.5) * m;
+    if (nonpos_prod(d1, d2)) return qu;
+    if constexpr (sizeof(R) == 8) {
+        const R t2 = R(2) * d2, t1 = R(2) * d1, tm = (fabs(d1) + fabs(t2)) * R(1.0 / 3.0);
+        unsigned long long m = mag_bits(t2);
+        const unsigned long long mm = mag_bits(tm), m1 = mag_bits(t1);
+        m = mm < m ? mm : m;
+        m = m1 < m ? m1 : m;
+        const unsigned long long sgn = (unsigned long long)__double_as_longlong(d1) & 0x8000000000000000ull;
+        return qu + R(0.5) * __longlong_as_double((long long)((m >> 1) | sgn));
+    } else {
+        const R m = fmin(R(2) * fabs(d2), fmin((fabs(d1) + R(2) * fabs(d2)) * R(1.0 / 3.0), R(2) * fabs(d1)));
+        return d1 > R(0) ? qu + R(0.5) * m : qu - R(0.5) * m;
+    }
 }
 template <typename R>
 __device__ __forceinline__ R upw3(R q0, R q1, R q2, R q3, R vel)
 {
-    return vel >= R(0) ? koren3(q0, q1, q2) : koren3(q3, q2, q1);
+    bool up;
+    if constexpr (sizeof(R) == 8)  // vel >= 0, -0 included
+        up = __double_as_longlong(vel) >= 0 || (__double_as_longlong(vel) << 1) == 0;
+    else
+        up = vel >= R(0);
+    return up ? koren3(q0, q1, q2) : koren3(q3, q2, q1);
 }
 // face densities: the mean of the face's two cells (face index clamped first)
 template <bool IN, typename R>
@@ -442,16 +537,46 @@ struct Vel3 {
     const R *u, *v, *w, *win;
 };
 
-// rho-breve and C of a momentum control volume: comp 0 u-face, 1 v-face, 2 w-face;
-// the three pairs of CV faces summed x, then y, then z
+// Face density arrays of rho^n (the mean of the face's two cells, ruq / rvq /
+// rwq), read at the face index clamped as those accessors clamp it: the same
+// values, formed once per step instead of at every read.
 template <bool IN, typename R>
-__device__ __forceinline__ void transport3(const Tank3P &P, const R *rc, const Vel3<R> &V, int comp, int i, int j, int k, R dt, R &rb,
-                           R &C)
+__device__ __forceinline__ R frq(const Tank3P &P, const R *__restrict__ a, int comp, int i, int j, int k)
 {
-    const R h = cst3<R>(P).h;
+    const int nx = P.nx, ny = P.ny;
+    if constexpr (IN) {
+        if (comp == 0) return a[(k * ny + j) * (nx + 1) + i];
+        if (comp == 1) return a[(k * (ny + 1) + j) * nx + i];
+        return a[(k * ny + j) * nx + i];
+    }
+    if (comp == 0) {
+        i = min(max(i, 0), nx);
+        j = min(max(j, 0), ny - 1);
+        k = min(max(k, 0), P.nz - 1);
+        return a[((long long)k * ny + j) * (nx + 1) + i];
+    }
+    if (comp == 1) {
+        i = min(max(i, 0), nx - 1);
+        j = min(max(j, 0), ny);
+        k = min(max(k, 0), P.nz - 1);
+        return a[((long long)k * (ny + 1) + j) * nx + i];
+    }
+    i = min(max(i, 0), nx - 1);
+    j = min(max(j, 0), ny - 1);
+    k = min(max(k, 0), P.nz);
+    return a[((long long)k * ny + j) * nx + i];
+}
+
+// rho-breve and C of a momentum control volume: comp 0 u-face, 1 v-face, 2 w-face;
+// the three pairs of CV faces summed x, then y, then z.  rfc: the face
+// densities of component comp; dtih = dt / h.
+template <bool IN, typename R>
+__device__ __forceinline__ void transport3(const Tank3P &P, const R *__restrict__ rfc, const Vel3<R> &V, int comp,
+                                           int i, int j, int k, R dtih, R &rb, R &C)
+{
+    const R ih = cst3<R>(P).ih;
     R m[6], f[6];
 #define QV(a, b, c) (comp == 0 ? uq<IN>(P, V.u, a, b, c) : comp == 1 ? vq<IN>(P, V.v, a, b, c) : wq<IN>(P, V.w, V.win, a, b, c))
-#define RV(a, b, c) (comp == 0 ? ruq<IN>(P, rc, a, b, c) : comp == 1 ? rvq<IN>(P, rc, a, b, c) : rwq<IN>(P, rc, a, b, c))
 #pragma unroll
     for (int d = 0; d < 3; ++d)
 #pragma unroll
@@ -480,7 +605,7 @@ __device__ __forceinline__ void transport3(const Tank3P &P, const R *rc, const V
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int o = a0 - 1 + q;
-                rr[q] = RV(i + o * di, j + o * dj, k + o * dk);
+                rr[q] = frq<IN>(P, rfc, comp, i + o * di, j + o * dj, k + o * dk);
                 qq[q] = QV(i + o * di, j + o * dj, k + o * dk);
             }
             const R r = upw3(rr[0], rr[1], rr[2], rr[3], U);
@@ -488,102 +613,81 @@ __device__ __forceinline__ void transport3(const Tank3P &P, const R *rc, const V
             m[2 * d + s] = U * r;
             f[2 * d + s] = m[2 * d + s] * qv;
         }
-    rb = RV(i, j, k) - dt / h * (((m[1] - m[0]) + (m[3] - m[2])) + (m[5] - m[4]));
-    C = (((f[1] - f[0]) + (f[3] - f[2])) + (f[5] - f[4])) / h;
+    rb = frq<IN>(P, rfc, comp, i, j, k) - dtih * (((m[1] - m[0]) + (m[3] - m[2])) + (m[5] - m[4]));
+    C = (((f[1] - f[0]) + (f[3] - f[2])) + (f[5] - f[4])) * ih;
 #undef QV
-#undef RV
 }
 
-// viscous stresses and div[mu (grad u + grad u^T)] with edge viscosities (the
-// mean of the four cells around the edge)
+// The viscous operator div[mu (grad u + grad u^T)] of component comp at a face,
+// with cell viscosities and the edge viscosities ex[0] (xy), ex[1] (xz), ex[2]
+// (yz) -- each the mean of the four cells around its edge, formed once per
+// viscosity field.  Returned as h^2 L_mu(u) = S - Lc u_f: S the sum over the
+// face's neighbours (its own component and the cross terms), Lc the sum of the
+// six coefficients (the diagonal, which the Jacobi splitting moves to the left).
+// Edge arrays: xy [nz][ny+1][nx+1], xz [nz+1][ny][nx+1], yz [nz+1][ny+1][nx].
 template <typename R>
-struct Visc3 {
-    const R *mu;
-    Vel3<R> V;
+struct Edges3 {
+    const R *xy, *xz, *yz;
 };
 template <bool IN, typename R>
-__device__ __forceinline__ R mxy3(const Tank3P &P, const R *mu, int i, int j, int k)
+__device__ __forceinline__ R exy_at(const Tank3P &P, const R *__restrict__ a, int i, int j, int k)
 {
-    return R(0.25) * (cellq<IN>(P, mu, i - 1, j - 1, k) + cellq<IN>(P, mu, i, j - 1, k) + cellq<IN>(P, mu, i - 1, j, k) +
-                      cellq<IN>(P, mu, i, j, k));
+    if constexpr (IN) return a[(k * (P.ny + 1) + j) * (P.nx + 1) + i];
+    return a[((long long)k * (P.ny + 1) + j) * (P.nx + 1) + i];
 }
 template <bool IN, typename R>
-__device__ __forceinline__ R mxz3(const Tank3P &P, const R *mu, int i, int j, int k)
+__device__ __forceinline__ R exz_at(const Tank3P &P, const R *__restrict__ a, int i, int j, int k)
 {
-    return R(0.25) * (cellq<IN>(P, mu, i - 1, j, k - 1) + cellq<IN>(P, mu, i, j, k - 1) + cellq<IN>(P, mu, i - 1, j, k) +
-                      cellq<IN>(P, mu, i, j, k));
+    if constexpr (IN) return a[(k * P.ny + j) * (P.nx + 1) + i];
+    return a[((long long)k * P.ny + j) * (P.nx + 1) + i];
 }
 template <bool IN, typename R>
-__device__ __forceinline__ R myz3(const Tank3P &P, const R *mu, int i, int j, int k)
+__device__ __forceinline__ R eyz_at(const Tank3P &P, const R *__restrict__ a, int i, int j, int k)
 {
-    return R(0.25) * (cellq<IN>(P, mu, i, j - 1, k - 1) + cellq<IN>(P, mu, i, j, k - 1) + cellq<IN>(P, mu, i, j - 1, k) +
-                      cellq<IN>(P, mu, i, j, k));
-}
-#define U3(a, b, c) uq<IN>(P, X.V.u, a, b, c)
-#define V3(a, b, c) vq<IN>(P, X.V.v, a, b, c)
-#define W3(a, b, c) wq<IN>(P, X.V.w, X.V.win, a, b, c)
-template <bool IN, typename R>
-__device__ __forceinline__ R txx(const Tank3P &P, const Visc3<R> &X, int i, int j, int k)
-{
-    return R(2) * cellq<IN>(P, X.mu, i, j, k) * (U3(i + 1, j, k) - U3(i, j, k)) / cst3<R>(P).h;
+    if constexpr (IN) return a[(k * (P.ny + 1) + j) * P.nx + i];
+    return a[((long long)k * (P.ny + 1) + j) * P.nx + i];
 }
 template <bool IN, typename R>
-__device__ __forceinline__ R tyy(const Tank3P &P, const Visc3<R> &X, int i, int j, int k)
+__device__ __forceinline__ void offdiag3(const Tank3P &P, const R *__restrict__ mu, const Edges3<R> &E,
+                                         const Vel3<R> &V, int comp, int i, int j, int k, R &S, R &Lc)
 {
-    return R(2) * cellq<IN>(P, X.mu, i, j, k) * (V3(i, j + 1, k) - V3(i, j, k)) / cst3<R>(P).h;
-}
-template <bool IN, typename R>
-__device__ __forceinline__ R tzz(const Tank3P &P, const Visc3<R> &X, int i, int j, int k)
-{
-    return R(2) * cellq<IN>(P, X.mu, i, j, k) * (W3(i, j, k + 1) - W3(i, j, k)) / cst3<R>(P).h;
-}
-template <bool IN, typename R>
-__device__ __forceinline__ R txy(const Tank3P &P, const Visc3<R> &X, int i, int j, int k)
-{
-    const R h = cst3<R>(P).h;
-    return mxy3<IN>(P, X.mu, i, j, k) * ((U3(i, j, k) - U3(i, j - 1, k)) / h + (V3(i, j, k) - V3(i - 1, j, k)) / h);
-}
-template <bool IN, typename R>
-__device__ __forceinline__ R txz(const Tank3P &P, const Visc3<R> &X, int i, int j, int k)
-{
-    const R h = cst3<R>(P).h;
-    return mxz3<IN>(P, X.mu, i, j, k) * ((U3(i, j, k) - U3(i, j, k - 1)) / h + (W3(i, j, k) - W3(i - 1, j, k)) / h);
-}
-template <bool IN, typename R>
-__device__ __forceinline__ R tyz(const Tank3P &P, const Visc3<R> &X, int i, int j, int k)
-{
-    const R h = cst3<R>(P).h;
-    return myz3<IN>(P, X.mu, i, j, k) * ((V3(i, j, k) - V3(i, j, k - 1)) / h + (W3(i, j, k) - W3(i, j - 1, k)) / h);
-}
+#define U3(a, b, c) uq<IN>(P, V.u, a, b, c)
+#define V3(a, b, c) vq<IN>(P, V.v, a, b, c)
+#define W3(a, b, c) wq<IN>(P, V.w, V.win, a, b, c)
+    if (comp == 0) {
+        const R m1 = cellq<IN>(P, mu, i, j, k), m0 = cellq<IN>(P, mu, i - 1, j, k);
+        const R e1 = exy_at<IN>(P, E.xy, i, j + 1, k), e0 = exy_at<IN>(P, E.xy, i, j, k);
+        const R f1 = exz_at<IN>(P, E.xz, i, j, k + 1), f0 = exz_at<IN>(P, E.xz, i, j, k);
+        S = R(2) * (m1 * U3(i + 1, j, k) + m0 * U3(i - 1, j, k)) +
+            ((e1 * ((U3(i, j + 1, k) + V3(i, j + 1, k)) - V3(i - 1, j + 1, k)) +
+              e0 * ((U3(i, j - 1, k) - V3(i, j, k)) + V3(i - 1, j, k))) +
+             (f1 * ((U3(i, j, k + 1) + W3(i, j, k + 1)) - W3(i - 1, j, k + 1)) +
+              f0 * ((U3(i, j, k - 1) - W3(i, j, k)) + W3(i - 1, j, k))));
+        Lc = R(2) * (m1 + m0) + ((e1 + e0) + (f1 + f0));
+    } else if (comp == 1) {
+        const R m1 = cellq<IN>(P, mu, i, j, k), m0 = cellq<IN>(P, mu, i, j - 1, k);
+        const R e1 = exy_at<IN>(P, E.xy, i + 1, j, k), e0 = exy_at<IN>(P, E.xy, i, j, k);
+        const R f1 = eyz_at<IN>(P, E.yz, i, j, k + 1), f0 = eyz_at<IN>(P, E.yz, i, j, k);
+        S = R(2) * (m1 * V3(i, j + 1, k) + m0 * V3(i, j - 1, k)) +
+            ((e1 * ((V3(i + 1, j, k) + U3(i + 1, j, k)) - U3(i + 1, j - 1, k)) +
+              e0 * ((V3(i - 1, j, k) - U3(i, j, k)) + U3(i, j - 1, k))) +
+             (f1 * ((V3(i, j, k + 1) + W3(i, j, k + 1)) - W3(i, j - 1, k + 1)) +
+              f0 * ((V3(i, j, k - 1) - W3(i, j, k)) + W3(i, j - 1, k))));
+        Lc = R(2) * (m1 + m0) + ((e1 + e0) + (f1 + f0));
+    } else {
+        const R m1 = cellq<IN>(P, mu, i, j, k), m0 = cellq<IN>(P, mu, i, j, k - 1);
+        const R e1 = exz_at<IN>(P, E.xz, i + 1, j, k), e0 = exz_at<IN>(P, E.xz, i, j, k);
+        const R f1 = eyz_at<IN>(P, E.yz, i, j + 1, k), f0 = eyz_at<IN>(P, E.yz, i, j, k);
+        S = R(2) * (m1 * W3(i, j, k + 1) + m0 * W3(i, j, k - 1)) +
+            ((e1 * ((W3(i + 1, j, k) + U3(i + 1, j, k)) - U3(i + 1, j, k - 1)) +
+              e0 * ((W3(i - 1, j, k) - U3(i, j, k)) + U3(i, j, k - 1))) +
+             (f1 * ((W3(i, j + 1, k) + V3(i, j + 1, k)) - V3(i, j + 1, k - 1)) +
+              f0 * ((W3(i, j - 1, k) - V3(i, j, k)) + V3(i, j, k - 1))));
+        Lc = R(2) * (m1 + m0) + ((e1 + e0) + (f1 + f0));
+    }
 #undef U3
 #undef V3
 #undef W3
-template <bool IN, typename R>
-__device__ __forceinline__ R visc3(const Tank3P &P, const Visc3<R> &X, int comp, int i, int j, int k)
-{
-    const R h = cst3<R>(P).h;
-    if (comp == 0)
-        return ((txx<IN>(P, X, i, j, k) - txx<IN>(P, X, i - 1, j, k)) / h + (txy<IN>(P, X, i, j + 1, k) - txy<IN>(P, X, i, j, k)) / h) +
-               (txz<IN>(P, X, i, j, k + 1) - txz<IN>(P, X, i, j, k)) / h;
-    if (comp == 1)
-        return ((tyy<IN>(P, X, i, j, k) - tyy<IN>(P, X, i, j - 1, k)) / h + (txy<IN>(P, X, i + 1, j, k) - txy<IN>(P, X, i, j, k)) / h) +
-               (tyz<IN>(P, X, i, j, k + 1) - tyz<IN>(P, X, i, j, k)) / h;
-    return ((tzz<IN>(P, X, i, j, k) - tzz<IN>(P, X, i, j, k - 1)) / h + (txz<IN>(P, X, i + 1, j, k) - txz<IN>(P, X, i, j, k)) / h) +
-           (tyz<IN>(P, X, i, j + 1, k) - tyz<IN>(P, X, i, j, k)) / h;
-}
-// interior-formula diagonal (the Jacobi splitting only)
-template <bool IN, typename R>
-__device__ __forceinline__ R vdiag3(const Tank3P &P, const R *mu, int comp, int i, int j, int k)
-{
-    const R h2 = cst3<R>(P).h * cst3<R>(P).h;
-    if (comp == 0)
-        return -(R(2) * cellq<IN>(P, mu, i, j, k) + R(2) * cellq<IN>(P, mu, i - 1, j, k) + mxy3<IN>(P, mu, i, j + 1, k) +
-                 mxy3<IN>(P, mu, i, j, k) + mxz3<IN>(P, mu, i, j, k + 1) + mxz3<IN>(P, mu, i, j, k)) / h2;
-    if (comp == 1)
-        return -(R(2) * cellq<IN>(P, mu, i, j, k) + R(2) * cellq<IN>(P, mu, i, j - 1, k) + mxy3<IN>(P, mu, i + 1, j, k) +
-                 mxy3<IN>(P, mu, i, j, k) + myz3<IN>(P, mu, i, j, k + 1) + myz3<IN>(P, mu, i, j, k)) / h2;
-    return -(R(2) * cellq<IN>(P, mu, i, j, k) + R(2) * cellq<IN>(P, mu, i, j, k - 1) + mxz3<IN>(P, mu, i + 1, j, k) +
-             mxz3<IN>(P, mu, i, j, k) + myz3<IN>(P, mu, i, j + 1, k) + myz3<IN>(P, mu, i, j, k)) / h2;
 }
 
 // solved faces of component comp: u i = 1..nx-1; v j = 1..ny-1; w k = 1..nz
@@ -608,13 +712,53 @@ __device__ __forceinline__ bool face_of(const Tank3P &P, int comp, int &i, int &
     return true;
 }
 
+// edge viscosities of the cell field mu (cells clamped into the grid, as the
+// stencils' accessors clamp them): one thread per (i, j, k) of the corner lattice
+template <typename R>
+__global__ void __launch_bounds__(128) k3t_edges(Tank3P P, const R *__restrict__ mu, R *__restrict__ xy,
+                                                 R *__restrict__ xz, R *__restrict__ yz)
+{
+    pdl_entry();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    const int nx = P.nx, ny = P.ny, nz = P.nz;
+    if (i > nx) return;
+    if (k < nz)
+        xy[((long long)k * (ny + 1) + j) * (nx + 1) + i] =
+            R(0.25) * (cellq<false>(P, mu, i - 1, j - 1, k) + cellq<false>(P, mu, i, j - 1, k) +
+                       cellq<false>(P, mu, i - 1, j, k) + cellq<false>(P, mu, i, j, k));
+    if (j < ny)
+        xz[((long long)k * ny + j) * (nx + 1) + i] =
+            R(0.25) * (cellq<false>(P, mu, i - 1, j, k - 1) + cellq<false>(P, mu, i, j, k - 1) +
+                       cellq<false>(P, mu, i - 1, j, k) + cellq<false>(P, mu, i, j, k));
+    if (i < nx)
+        yz[((long long)k * (ny + 1) + j) * nx + i] =
+            R(0.25) * (cellq<false>(P, mu, i, j - 1, k - 1) + cellq<false>(P, mu, i, j, k - 1) +
+                       cellq<false>(P, mu, i, j - 1, k) + cellq<false>(P, mu, i, j, k));
+}
+
+// face densities of the cell field rho: the u-, v- and w-face arrays
+template <typename R>
+__global__ void __launch_bounds__(128) k3t_face_rho(Tank3P P, const R *__restrict__ rho, R *__restrict__ ru,
+                                                    R *__restrict__ rv, R *__restrict__ rw)
+{
+    pdl_entry();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    const int nx = P.nx, ny = P.ny, nz = P.nz;
+    if (i > nx) return;
+    if (j < ny && k < nz) ru[((long long)k * ny + j) * (nx + 1) + i] = ruq<false>(P, rho, i, j, k);
+    if (i < nx && k < nz) rv[((long long)k * (ny + 1) + j) * nx + i] = rvq<false>(P, rho, i, j, k);
+    if (i < nx && j < ny) rw[((long long)k * ny + j) * nx + i] = rwq<false>(P, rho, i, j, k);
+}
+
 template <typename R>
 struct MomIn {
-    const R *rho_n, *mu_n, *chi1, *rf1;
+    const R *rfc[3];                       // face densities of rho^n (u-, v-, w-faces)
+    const R *mu_n, *chi1, *rf1;
+    Edges3<R> E;                           // edge viscosities of mu^n
     const double *p;                       // p^{n-1/2} (FP64: its differences are taken before rounding)
     Vel3<R> V;                             // u^n, v^n, w^n with w_in(t^n)
     const R *dampu, *vortc, *vortf;        // damping weight at u-faces; vorticity damping at cell / face heights
-    R dt, zd1, g, ikp;
+    R dt, idt, dtih, ih2, zd1, g, ikp;
 };
 
 // faces whose whole stencil (three cells each way) lies inside the grid: there
@@ -630,27 +774,29 @@ __device__ __forceinline__ void momentum_at(const Tank3P &P, const MomIn<R> &M, 
                                             long long f, R *__restrict__ Dout, R *__restrict__ Rout)
 {
     R rb, C;
-    transport3<IN, R>(P, M.rho_n, M.V, comp, i, j, k, M.dt, rb, C);
-    const Visc3<R> X{M.mu_n, M.V};
-    const double h = P.h;
+    transport3<IN, R>(P, M.rfc[comp], M.V, comp, i, j, k, M.dtih, rb, C);
+    R S, Lc;
+    offdiag3<IN, R>(P, M.mu_n, M.E, M.V, comp, i, j, k, S, Lc);
+    const R uc = comp == 0 ? M.V.u[f] : comp == 1 ? M.V.v[f] : M.V.w[f];
+    const R visc = (S - Lc * uc) * M.ih2;
+    const double ih = P.ih;
     const int ci = comp == 0 ? i - 1 : i, cj = comp == 1 ? j - 1 : j, ck = comp == 2 ? k - 1 : k;
     const R chi = R(0.5) * (cellq<IN>(P, M.chi1, ci, cj, ck) + cellq<IN>(P, M.chi1, i, j, k));
     const R al = comp == 0 ? M.dampu[i] : dampc<R>(P, i);
     const R vd = comp == 2 ? M.vortf[k] : M.vortc[k];
-    Dout[f] = rb / M.dt + chi * M.ikp + al * rb / M.dt + vd;
+    const R rbdt = rb * M.idt;
+    Dout[f] = rbdt + chi * M.ikp + al * rbdt + vd;
     const double pc = k < P.nz ? M.p[((long long)k * P.ny + j) * P.nx + i] : 0.0;
+    const R adv = frq<IN>(P, M.rfc[comp], comp, i, j, k) * uc * M.idt - C + R(0.5) * visc;
     if (comp == 0) {
-        Rout[f] = ruq<IN>(P, M.rho_n, i, j, k) * M.V.u[f] / M.dt - C + R(0.5) * visc3<IN, R>(P, X, 0, i, j, k) -
-                  R((pc - M.p[((long long)k * P.ny + j) * P.nx + i - 1]) / h);
+        Rout[f] = adv - R((pc - M.p[((long long)k * P.ny + j) * P.nx + i - 1]) * ih);
     } else if (comp == 1) {
-        Rout[f] = rvq<IN>(P, M.rho_n, i, j, k) * M.V.v[f] / M.dt - C + R(0.5) * visc3<IN, R>(P, X, 1, i, j, k) -
-                  R((pc - M.p[((long long)k * P.ny + j - 1) * P.nx + i]) / h);
+        Rout[f] = adv - R((pc - M.p[((long long)k * P.ny + j - 1) * P.nx + i]) * ih);
     } else {
         const R rf = R(0.5) * (cellq<IN>(P, M.rf1, i, j, k - 1) + cellq<IN>(P, M.rf1, i, j, k));
         const double pb = M.p[((long long)(k - 1) * P.ny + j) * P.nx + i];
-        const double gp = k < P.nz ? (pc - pb) / h : -2.0 * pb / h;
-        Rout[f] = rwq<IN>(P, M.rho_n, i, j, k) * M.V.w[f] / M.dt - C + R(0.5) * visc3<IN, R>(P, X, 2, i, j, k) - rf * M.g +
-                  chi * M.zd1 * M.ikp - R(gp);
+        const double gp = k < P.nz ? (pc - pb) * ih : -2.0 * pb * ih;
+        Rout[f] = adv - rf * M.g + chi * M.zd1 * M.ikp - R(gp);
     }
 }
 
@@ -667,27 +813,55 @@ __global__ void __launch_bounds__(128) k3t_momentum(Tank3P P, MomIn<R> M, R *__r
         momentum_at<false, R>(P, M, COMP, i, j, k, f, Dout, Rout);
 }
 
-// one Crank-Nicolson Jacobi sweep of component comp: B = (R + (L(A) - ld A) / 2) / (D - ld / 2)
-template <bool IN, typename R>
-__device__ __forceinline__ R jacobi_at(const Tank3P &P, const R *__restrict__ mu1, const Vel3<R> &A, int comp,
-                                       int i, int j, int k, R a, R d, R r)
-{
-    const Visc3<R> X{mu1, A};
-    const R ld = vdiag3<IN, R>(P, mu1, comp, i, j, k);
-    return (r + R(0.5) * (visc3<IN, R>(P, X, comp, i, j, k) - ld * a)) / (d - R(0.5) * ld);
-}
+// The Crank-Nicolson system of component comp, split on its diagonal:
+// B = (R + (L(A) - ld A) / 2) / (D - ld / 2) with h^2 (L(A) - ld A) = S(A) and
+// -h^2 ld = Lc.  Formed once per step (mu^{n+1} is fixed during the sweeps):
+// Rr <- R / (D + Lc / (2 h^2)) and Q = (1 / (2 h^2)) / (D + Lc / (2 h^2)), so that a
+// sweep is B = Rr + Q S(A).
 template <int COMP, typename R>
-__global__ void __launch_bounds__(128) k3t_jacobi(Tank3P P, const R *__restrict__ mu1, Vel3<R> A,
-                                                  const R *__restrict__ D, const R *__restrict__ Rr,
+__global__ void __launch_bounds__(128) k3t_jprep(Tank3P P, const R *__restrict__ mu1, Edges3<R> E,
+                                                 const R *__restrict__ D, R *__restrict__ Rr, R *__restrict__ Qo,
+                                                 R ih2)
+{
+    pdl_entry();
+    int i, j, k;
+    long long f;
+    if (!face_of(P, COMP, i, j, k, f)) return;
+    R Lc;
+    if (COMP == 0)
+        Lc = R(2) * (cellq<false>(P, mu1, i, j, k) + cellq<false>(P, mu1, i - 1, j, k)) +
+             ((exy_at<false>(P, E.xy, i, j + 1, k) + exy_at<false>(P, E.xy, i, j, k)) +
+              (exz_at<false>(P, E.xz, i, j, k + 1) + exz_at<false>(P, E.xz, i, j, k)));
+    else if (COMP == 1)
+        Lc = R(2) * (cellq<false>(P, mu1, i, j, k) + cellq<false>(P, mu1, i, j - 1, k)) +
+             ((exy_at<false>(P, E.xy, i + 1, j, k) + exy_at<false>(P, E.xy, i, j, k)) +
+              (eyz_at<false>(P, E.yz, i, j, k + 1) + eyz_at<false>(P, E.yz, i, j, k)));
+    else
+        Lc = R(2) * (cellq<false>(P, mu1, i, j, k) + cellq<false>(P, mu1, i, j, k - 1)) +
+             ((exz_at<false>(P, E.xz, i + 1, j, k) + exz_at<false>(P, E.xz, i, j, k)) +
+              (eyz_at<false>(P, E.yz, i, j + 1, k) + eyz_at<false>(P, E.yz, i, j, k)));
+    const R hi2 = R(0.5) * ih2;
+    const R inv = R(1) / (D[f] + hi2 * Lc);
+    Rr[f] = Rr[f] * inv;
+    Qo[f] = hi2 * inv;
+}
+
+// one Crank-Nicolson Jacobi sweep of component comp: B = Rr + Q S(A)
+template <int COMP, typename R>
+__global__ void __launch_bounds__(128) k3t_jacobi(Tank3P P, const R *__restrict__ mu1, Edges3<R> E, Vel3<R> A,
+                                                  const R *__restrict__ Rr, const R *__restrict__ Qf,
                                                   R *__restrict__ B)
 {
     pdl_entry();
     int i, j, k;
     long long f;
     if (!face_of(P, COMP, i, j, k, f)) return;
-    const R a = COMP == 0 ? A.u[f] : COMP == 1 ? A.v[f] : A.w[f];
-    B[f] = interior3(P, i, j, k) ? jacobi_at<true, R>(P, mu1, A, COMP, i, j, k, a, D[f], Rr[f])
-                                 : jacobi_at<false, R>(P, mu1, A, COMP, i, j, k, a, D[f], Rr[f]);
+    R S, Lc;
+    if (interior3(P, i, j, k))
+        offdiag3<true, R>(P, mu1, E, A, COMP, i, j, k, S, Lc);
+    else
+        offdiag3<false, R>(P, mu1, E, A, COMP, i, j, k, S, Lc);
+    B[f] = Rr[f] + Qf[f] * S;
 }
 
 // Dirichlet faces of the predictor: u_in(t1) at x = 0, u = 0 at the outlet, v = 0
@@ -995,6 +1169,10 @@ int reinit_buf(wec_tank3 *T, R *s, R *s0, R *s1, int nit, double t)
 {
     const double dtau = 0.3 * T->P.h, b = sizeof(R);
     WEC_CK(cudaMemcpyAsync(s0, s, T->nc * sizeof(R), cudaMemcpyDeviceToDevice, T->st));
+    {
+        WEC_PROF("tank3_reinit", 1, 2.0 * b * T->nc, T->st);
+        launch_k(k3t_reinit_sign<R>, grid3(T->P), 128, 0, T->st, T->P, s0);
+    }
     for (int it = 0; it < nit; ++it) {
         {
             WEC_PROF("tank3_reinit", 0, 3.0 * b * T->nc, T->st);
@@ -1127,22 +1305,46 @@ static int tank3_step_impl(wec_tank3 *T, Work3<R> &W, double dt, double pto_forc
         WEC_PROF("tank3_materials", 0, 5.0 * sizeof(R) * T->nc, st);
         launch_k(k3t_materials<R>, grid3(P), 128, 0, st, P, (const R *)W.tmp, zc1, W.s1, W.mu1, W.rf1, W.chi1, 0);
     }
-    // (5) transport and the momentum system
-    MomIn<R> M{W.rho, W.mu, W.chi1, W.rf1, T->p, Vel3<R>{W.u, W.v, W.w, r_win0}, W.dampu, r_vc, r_vf, R(dt), R(zd1),
-               R(T->g), R(1.0 / T->kappa_p)};
+    // (5) transport and the momentum system: face densities of rho^n and edge
+    // viscosities of mu^n, then one kernel per component
+    const dim3 gcorner((nx + 1 + 127) / 128, ny + 1, nz + 1);
+    const double b = sizeof(R);
+    {
+        WEC_PROF("tank3_faces_edges", 0, b * (T->nc + T->nu + T->nv + T->nw), st);
+        launch_k(k3t_face_rho<R>, gcorner, 128, 0, st, P, (const R *)W.rho, W.RF[0], W.RF[1], W.RF[2]);
+    }
+    {
+        WEC_PROF("tank3_faces_edges", 0, b * 4.0 * T->nc, st);
+        launch_k(k3t_edges<R>, gcorner, 128, 0, st, P, (const R *)W.mu, W.E[0], W.E[1], W.E[2]);
+    }
+    const Edges3<R> E{W.E[0], W.E[1], W.E[2]};
+    MomIn<R> M{{W.RF[0], W.RF[1], W.RF[2]}, W.mu, W.chi1, W.rf1, E, T->p, Vel3<R>{W.u, W.v, W.w, r_win0}, W.dampu,
+               r_vc, r_vf, R(dt), R(1.0 / dt), R(dt / h), R(1.0 / (h * h)), R(zd1), R(T->g), R(1.0 / T->kappa_p)};
     const dim3 gu((nx - 1 + 127) / 128, ny, nz), gv((nx + 127) / 128, ny - 1 > 0 ? ny - 1 : 1, nz),
         gw((nx + 127) / 128, ny, nz);
     const dim3 gc[3] = {gu, gv, gw};
-    const double b = sizeof(R);
+    const size_t nf[3] = {T->nu, T->nv, T->nw};
     for (int c = 0; c < 3; ++c) {
         if (c == 1 && ny < 2) continue;
-        const double nfc = c == 0 ? (nx - 1.0) * ny * nz : c == 1 ? nx * (ny - 1.0) * nz : (double)nx * ny * nz;
-        WEC_PROF("tank3_momentum", c, b * (4.0 * T->nc + T->nu + T->nv + T->nw + 2.0 * nfc) + 8.0 * T->nc, st);
+        // face density, mu, two edge arrays, chi (+ rho^flow for w), p, u, v, w in; D, R out
+        WEC_PROF("tank3_momentum", c,
+                 b * (nf[c] + (c == 2 ? 5.0 : 4.0) * T->nc + T->nu + T->nv + T->nw + 2.0 * nf[c]) + 8.0 * T->nc, st);
         auto kern = c == 0 ? k3t_momentum<0, R> : c == 1 ? k3t_momentum<1, R> : k3t_momentum<2, R>;
         launch_k(kern, gc[c], 128, 0, st, P, M, W.D[c], W.R3[c]);
     }
-    // (6) Crank-Nicolson Jacobi sweeps from u^n with the Dirichlet faces at n+1
-    const size_t nf[3] = {T->nu, T->nv, T->nw};
+    // (6) Crank-Nicolson Jacobi sweeps from u^n with the Dirichlet faces at n+1:
+    // edge viscosities of mu^{n+1}, the per-face factors, then the sweeps
+    {
+        WEC_PROF("tank3_faces_edges", 0, b * 4.0 * T->nc, st);
+        launch_k(k3t_edges<R>, gcorner, 128, 0, st, P, (const R *)W.mu1, W.E[0], W.E[1], W.E[2]);
+    }
+    for (int c = 0; c < 3; ++c) {
+        if (c == 1 && ny < 2) continue;
+        WEC_PROF("tank3_jprep", c, b * (3.0 * T->nc + 4.0 * nf[c]), st);
+        auto kern = c == 0 ? k3t_jprep<0, R> : c == 1 ? k3t_jprep<1, R> : k3t_jprep<2, R>;
+        launch_k(kern, gc[c], 128, 0, st, P, (const R *)W.mu1, E, (const R *)W.D[c], W.R3[c], W.Q[c],
+                 R(1.0 / (h * h)));
+    }
     R *src[3] = {W.u, W.v, W.w};
     for (int c = 0; c < 3; ++c) WEC_CK(cudaMemcpyAsync(W.A[c], src[c], nf[c] * sizeof(R), cudaMemcpyDeviceToDevice, st));
     {
@@ -1154,10 +1356,10 @@ static int tank3_step_impl(wec_tank3 *T, Work3<R> &W, double dt, double pto_forc
         const Vel3<R> Va{W.A[0], W.A[1], W.A[2], r_win1};
         for (int c = 0; c < 3; ++c) {
             if (c == 1 && ny < 2) continue;
-            const double nfc = c == 0 ? (nx - 1.0) * ny * nz : c == 1 ? nx * (ny - 1.0) * nz : (double)nx * ny * nz;
-            WEC_PROF("tank3_jacobi", c, b * (T->nc + T->nu + T->nv + T->nw + 3.0 * nfc), st);
+            // mu, two edge arrays, u, v, w, Rr, Q in; B out
+            WEC_PROF("tank3_jacobi", c, b * (3.0 * T->nc + T->nu + T->nv + T->nw + 3.0 * nf[c]), st);
             auto kern = c == 0 ? k3t_jacobi<0, R> : c == 1 ? k3t_jacobi<1, R> : k3t_jacobi<2, R>;
-            launch_k(kern, gc[c], 128, 0, st, P, (const R *)W.mu1, Va, (const R *)W.D[c], (const R *)W.R3[c],
+            launch_k(kern, gc[c], 128, 0, st, P, (const R *)W.mu1, E, Va, (const R *)W.R3[c], (const R *)W.Q[c],
                      W.B[c]);
         }
         for (int c = 0; c < 3; ++c) std::swap(W.A[c], W.B[c]);
@@ -1233,7 +1435,7 @@ int wec_tank3_create(const wec_grid3 *grid, const wec_fluids *fl, const wec_wave
     if (!grid || !fl || !wv || !body) return fail(WEC_ERR_INVALID, "NULL argument");
     const int nx = grid->nx, ny = grid->ny, nz = grid->nz;
     if (nx < 4 || ny < 1 || nz < 4) return fail(WEC_ERR_INVALID, "tank3: need nx >= 4, ny >= 1, nz >= 4");
-    if (ny > 65535 || nz > 65535) return fail(WEC_ERR_INVALID, "tank3: ny, nz must be <= 65535");
+    if (ny > 65534 || nz > 65534) return fail(WEC_ERR_INVALID, "tank3: ny, nz must be <= 65534");
     const double h = grid->lx / nx;
     if (!(h > 0.0) || std::fabs(grid->ly / ny - h) > 1e-9 * h || std::fabs(grid->lz / nz - h) > 1e-9 * h)
         return fail(WEC_ERR_INVALID, "tank3: the grid must be uniform (lx/nx = ly/ny = lz/nz)");
@@ -1352,8 +1554,13 @@ int wec_tank3_create(const wec_grid3 *grid, const wec_fluids *fl, const wec_wave
         for (double **q : {&T->p, &T->phi, &T->rhs, &T->mu1, &T->rf1, &T->chi1})
             if (e == cudaSuccess) e = cudaMalloc(q, T->nc * 8);
         for (int c = 0; c < 3; ++c)
-            for (double **q : {&T->D[c], &T->R[c], &T->A[c], &T->B[c]})
+            for (double **q : {&T->D[c], &T->R[c], &T->A[c], &T->B[c], &T->RF[c], &T->Q[c]})
                 if (e == cudaSuccess) e = cudaMalloc(q, nf[c] * 8);
+        const size_t ne[3] = {(size_t)nz * (ny + 1) * (nx + 1), (size_t)(nz + 1) * ny * (nx + 1),
+                              (size_t)(nz + 1) * (ny + 1) * nx};
+        if (opts->precision != WEC_PREC_MIXED)
+            for (int c = 0; c < 3; ++c)
+                if (e == cudaSuccess) e = cudaMalloc(&T->E[c], ne[c] * 8);
         if (e == cudaSuccess) e = cudaMalloc(&T->bc, (size_t)(3 * nz + 2 + nz + nz + 1) * 8);
         if (e == cudaSuccess) e = cudaMalloc(&T->tabs, (size_t)(nx + 1) * 8);
         if (e == cudaSuccess) e = cudaMalloc(&T->part, (size_t)(3 * nz + 1024 + 8) * 8);
@@ -1418,8 +1625,10 @@ int wec_tank3_create(const wec_grid3 *grid, const wec_fluids *fl, const wec_wave
             if (e == cudaSuccess) e = cudaMalloc(&F.v, T->nv * 4);
             if (e == cudaSuccess) e = cudaMalloc(&F.w, T->nw * 4);
             for (int c = 0; c < 3; ++c)
-                for (float **q : {&F.D[c], &F.R3[c], &F.A[c], &F.B[c]})
+                for (float **q : {&F.D[c], &F.R3[c], &F.A[c], &F.B[c], &F.RF[c], &F.Q[c]})
                     if (e == cudaSuccess) e = cudaMalloc(q, nf3[c] * 4);
+            for (int c = 0; c < 3; ++c)
+                if (e == cudaSuccess) e = cudaMalloc(&F.E[c], ne[c] * 4);
             if (e == cudaSuccess) e = cudaMalloc(&F.bc, (size_t)(5 * nz + 3) * 4);
             if (e == cudaSuccess) e = cudaMalloc(&F.dampu, (size_t)(nx + 1) * 4);
             std::vector<float> duf(du.begin(), du.end());
@@ -1457,13 +1666,13 @@ void wec_tank3_destroy(wec_tank3 *T)
                       T->p, T->phi, T->rhs, T->mu1, T->rf1, T->chi1, T->bc, T->tabs, T->part})
         cudaFree(p);
     for (int c = 0; c < 3; ++c)
-        for (double *p : {T->D[c], T->R[c], T->A[c], T->B[c]}) cudaFree(p);
+        for (double *p : {T->D[c], T->R[c], T->A[c], T->B[c], T->E[c], T->RF[c], T->Q[c]}) cudaFree(p);
     Work3<float> &F = T->wf;
     for (float *p : {F.sig, F.tmp, F.s0, F.s1, F.u, F.v, F.w, F.rho, F.mu, F.rf, F.chi, F.mu1, F.rf1, F.chi1, F.bc,
                      F.dampu, T->fconsts})
         cudaFree(p);
     for (int c = 0; c < 3; ++c)
-        for (float *p : {F.D[c], F.R3[c], F.A[c], F.B[c]}) cudaFree(p);
+        for (float *p : {F.D[c], F.R3[c], F.A[c], F.B[c], F.E[c], F.RF[c], F.Q[c]}) cudaFree(p);
     if (T->solver) {
         poisson_free(T->solver);
         delete T->solver;
@@ -1570,6 +1779,7 @@ int wec_tank3_step(wec_tank3 *T, double dt, double pto_force, wec_step_result *o
     W.rho = T->rho; W.mu = T->mu; W.rf = T->rhof; W.chi = T->chi; W.mu1 = T->mu1; W.rf1 = T->rf1; W.chi1 = T->chi1;
     for (int c = 0; c < 3; ++c) {
         W.D[c] = T->D[c]; W.R3[c] = T->R[c]; W.A[c] = T->A[c]; W.B[c] = T->B[c];
+        W.E[c] = T->E[c]; W.RF[c] = T->RF[c]; W.Q[c] = T->Q[c];
     }
     W.bc = T->bc;
     W.dampu = T->tabs;

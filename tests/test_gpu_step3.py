@@ -1,8 +1,8 @@
 """The 3D tank step on the GPU (wec_tank3_step) against the 3D step oracle:
 the initial state, every field after each step (FP64, 1e-10 relative per step),
 the heave after 200 steps (1e-6 relative), the FP32-V-cycle path's error, and
-the 512 x 256 x 256 tank by its properties (solve residual, divergence, finite
-heave)."""
+the 512 x 256 x 256 tank: by its properties (solve residual, divergence, finite
+heave) and, for one step, every field against the oracle's step."""
 import numpy as np
 import pytest
 
@@ -130,6 +130,34 @@ def test_full_size_tank_step():
           f"div {rs[-1]['div_norm']:.3e}")
     assert 0.5 < ratio < 1.5
     t.close()
+
+
+def test_full_size_step_matches_the_oracle_everywhere():
+    # One step of the 512 x 256 x 256 tank of configuration 5 from its initial
+    # state: every cell and face of sigma, u, v, w and p against the oracle's step
+    # (run on all host cores), for the FP64 path and the FP32-V-cycle path, both
+    # sides solving to 1e-12.  The comparison covers the interior fast path of
+    # the momentum and Jacobi stencils (32-bit offsets, no ghost rules), every
+    # boundary face, and the cell layers of the force integral around the cylinder.
+    c = synth.tank3d(seed=0, rtol=1e-12, mg_pre=3, mg_post=3, restart=5)
+    o = T3.OracleTank3(c)
+    ro = o.step(c["dt"])
+    assert ro["status"] == 0
+    ref = {name: o.get(fo) for _, fo, name in FIELDS}
+    del o
+    vs = np.max(np.abs(ref["u"]))
+    for prec, bound in ((wec.PREC_FP64, 1e-10), (wec.PREC_MIXED_MG, 1e-9)):
+        t = wec.Tank3(c, precision=prec)
+        r = t.step(c["dt"])
+        assert r["status"] == 0 and r["residual"] <= 1e-12
+        errs = {name: rel(t.get(fg), ref[name], vs if name == "v" else 1e-12) for fg, _, name in FIELDS}
+        t.close()
+        print(f"512x256x256 step, precision {prec}: {errs}, F {r['f_hydro']:.9f} / {ro['f_hydro']:.9f}, "
+              f"its {r['iters']} / {ro['iters']}")
+        for name, e in errs.items():
+            assert e < bound, (prec, name, e)
+        assert r["f_hydro"] == pytest.approx(ro["f_hydro"], rel=1e-10)
+        assert r["zdot"] == pytest.approx(ro["zdot"], rel=1e-10, abs=1e-14)
 
 
 def test_invalid_step_uses():
