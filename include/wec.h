@@ -78,7 +78,7 @@ typedef struct {
     double xc, yc, width, height, mass, added_mass, kappa_p, pto_damping;
 } wec_body;
 
-enum { WEC_PREC_FP64 = 0, WEC_PREC_MIXED = 1, WEC_PREC_MIXED_MG = 2 };
+enum { WEC_PREC_FP64 = 0, WEC_PREC_MIXED = 1, WEC_PREC_MIXED_MG = 2, WEC_PREC_MIXED_DF = 3 };
 
 /* Pressure solver and step options.  precision:
  *   WEC_PREC_FP64      everything FP64;
@@ -89,7 +89,11 @@ enum { WEC_PREC_FP64 = 0, WEC_PREC_MIXED = 1, WEC_PREC_MIXED_MG = 2 };
  *                      momentum, Jacobi sweeps) in FP32 over FP32 working copies
  *                      of FP64 state; the force integral (Eq. int_fh), the heave
  *                      update (Eq. newton_u), the projection and the persistent
- *                      fields stay FP64.
+ *                      fields stay FP64;
+ *   WEC_PREC_MIXED_DF  (3D tank only) as WEC_PREC_MIXED, with the stencils in
+ *                      double-float arithmetic (pairs of floats, about 48
+ *                      significand bits, on the FP32 pipe) over float-pair
+ *                      working copies: FP64-equivalent stencil accuracy.
  * A Poisson object (wec_poisson_create) takes WEC_PREC_FP64 or WEC_PREC_MIXED
  * (FP32 V-cycles); WEC_PREC_MIXED_MG is a tank option.
  * rtol: relative FP64 residual ||b - A x||_2 <= rtol ||b||_2 of each solve.
@@ -429,10 +433,12 @@ int wec_tank3_advect(wec_tank3 *tank, double dt, double t);
  * the sign of sigma at the call (section "Interface tracking"); ghosts at t. */
 int wec_tank3_reinit(wec_tank3 *tank, int nit, double t);
 /* One time step of the 3D tank (needs opts at creation).  Precision: WEC_PREC_FP64;
- * WEC_PREC_MIXED_MG (FP32 V-cycles in the FP64 solve, FP64 stencils); WEC_PREC_MIXED
- * (also the stencils -- materials, advection, reinitialisation, transport, viscous
- * terms, Jacobi sweeps -- in FP32 over FP32 working copies of the FP64 state; the
- * force, heave, beta, right-hand side, solve, projection and fields stay FP64).
+ * WEC_PREC_MIXED_MG (FP32 V-cycles in the FP64 solve, FP64 stencils); WEC_PREC_MIXED_DF
+ * (FP32 V-cycles, the stencils -- materials, advection, reinitialisation, transport,
+ * viscous terms, Jacobi sweeps -- in double-float arithmetic over float-pair working
+ * copies of the FP64 state); WEC_PREC_MIXED (the same stencils in FP32 over FP32
+ * working copies).  In every mode the force, heave, beta, right-hand side, solve
+ * residual and Krylov basis, projection and fields are FP64.
  * The step: heave force from p^{n-1/2}, u^n (Eq.
  * int_fh: pressure interpolated to psi = 0 and the normal viscous stress on
  * z-faces, the shear stresses on x- and y-faces, face area h^2); heave update

@@ -29,11 +29,14 @@
 //     input field S = sigma0 / sqrt(sigma0^2 + h^2).
 #include <cmath>
 #include <algorithm>
+#include <initializer_list>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <utility>
 #include <vector>
 
+#include "df64.cuh"
 #include "internal.cuh"
 
 // the tank's constants in the working type of a kernel
@@ -52,8 +55,10 @@ struct Tank3P {
     const double *amp, *omega, *kw, *phase;  // device
     const double *damp;                       // device, [nx]: damping-zone weight of each column
     const float *dampf;                       // the same in FP32
+    const wec::df64 *dampd;                   // the same as float pairs
     Tank3C<float> cf;
     Tank3C<double> cd;
+    Tank3C<wec::df64> cdf;
 };
 
 // the working arrays of one precision of the step's stencils
@@ -91,7 +96,9 @@ struct wec_tank3 {
     wec_poisson *solver = nullptr;
     bool stepping = false;   // created with solver options
     Work3<float> wf;         // FP32 working copies (WEC_PREC_MIXED)
+    Work3<wec::df64> wd;     // float-pair working copies (WEC_PREC_MIXED_DF)
     float *fconsts = nullptr;
+    wec::df64 *dconsts = nullptr;
     std::vector<double> hwave;  // host copy of the wave components: amp, omega, k, phase
 };
 
@@ -101,23 +108,29 @@ namespace {
 constexpr double kPi3 = 3.14159265358979323846;
 
 // The stencils are templates on their working type R: double (WEC_PREC_FP64,
-// WEC_PREC_MIXED_MG) or float over FP32 working copies of the FP64 state
-// (WEC_PREC_MIXED).  The FP64 pipe of this GPU runs at 1/64 of the FP32 rate,
-// so an FP32 kernel reads its constants in FP32 (cst3) and converts nothing in
-// its inner loops; the force integral, the heave, the solve and the projection
-// stay FP64.  FP64 division and square root expand into long FMA sequences:
+// WEC_PREC_MIXED_MG), float pairs (df64, about 48 significand bits, on the
+// FP32 pipe: WEC_PREC_MIXED_DF) or float (WEC_PREC_MIXED), the last two over
+// working copies of the FP64 state.  The FP64 pipe of this GPU runs at 1/64 of
+// the FP32 rate, so a kernel reads its constants in its own type (cst3) and
+// converts nothing in its inner loops; the force integral, the heave, the
+// solve and the projection stay FP64.  FP64 division and square root expand into long FMA sequences:
 // the kernels multiply by reciprocals formed once (1/h, 1/6, ...), which differs
 // from dividing by at most an ulp.
 template <typename R>
+constexpr bool is_f64 = std::is_same<R, double>::value;
+template <typename R>
+constexpr bool is_df = std::is_same<R, df64>::value;
+
+template <typename R>
 __device__ __forceinline__ const Tank3C<R> &cst3(const Tank3P &P)
 {
-    if constexpr (sizeof(R) == 4) return P.cf; else return P.cd;
+    if constexpr (is_f64<R>) return P.cd; else if constexpr (is_df<R>) return P.cdf; else return P.cf;
 }
 
 template <typename R>
 __device__ __forceinline__ R dampc(const Tank3P &P, int i)
 {
-    if constexpr (sizeof(R) == 4) return P.dampf[i]; else return P.damp[i];
+    if constexpr (is_f64<R>) return P.damp[i]; else if constexpr (is_df<R>) return P.dampd[i]; else return P.dampf[i];
 }
 
 template <typename R>
@@ -166,9 +179,11 @@ __device__ __forceinline__ unsigned long long mag_bits(double a)
 template <typename R>
 __device__ __forceinline__ bool nonpos_prod(R a, R b)
 {
-    if constexpr (sizeof(R) == 8) {
+    if constexpr (is_f64<R>) {
         const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
         return (ia ^ ib) < 0 || (ia << 1) == 0 || (ib << 1) == 0;
+    } else if constexpr (is_df<R>) {  // the signs of the leading floats
+        return (a.hi < 0.f) != (b.hi < 0.f) || a.hi == 0.f || b.hi == 0.f;
     } else {
         return a * b <= R(0);
     }
@@ -177,13 +192,13 @@ __device__ __forceinline__ bool nonpos_prod(R a, R b)
 template <typename R>
 __device__ __forceinline__ bool abs_lt(R a, R b)
 {
-    if constexpr (sizeof(R) == 8) return mag_bits(a) < mag_bits(b); else return fabs(a) < fabs(b);
+    if constexpr (is_f64<R>) return mag_bits(a) < mag_bits(b); else return fabs(a) < fabs(b);
 }
 // a > 0
 template <typename R>
 __device__ __forceinline__ bool positive(R a)
 {
-    if constexpr (sizeof(R) == 8) return __double_as_longlong(a) > 0; else return a > R(0);
+    if constexpr (is_f64<R>) return __double_as_longlong(a) > 0; else return a > R(0);
 }
 
 // van Leer slope of the middle cell: 0 at an extremum, else the smallest of
@@ -195,7 +210,7 @@ __device__ __forceinline__ R vl3(R am, R a0, R ap)
     const R dl = a0 - am, dr = ap - a0;
     if (nonpos_prod(dl, dr)) return R(0);
     const R dc = R(0.5) * (ap - am), tl = R(2) * dl, tr = R(2) * dr;
-    if constexpr (sizeof(R) == 8) {
+    if constexpr (is_f64<R>) {
         unsigned long long m = mag_bits(dc);
         const unsigned long long ml = mag_bits(tl), mr = mag_bits(tr);
         m = ml < m ? ml : m;
@@ -214,7 +229,7 @@ __device__ __forceinline__ R vl3(R am, R a0, R ap)
 template <typename R>
 __device__ __forceinline__ bool gt_nonneg(R a, R b)
 {
-    if constexpr (sizeof(R) == 8) return __double_as_longlong(a) > __double_as_longlong(b); else return a > b;
+    if constexpr (is_f64<R>) return __double_as_longlong(a) > __double_as_longlong(b); else return a > b;
 }
 
 // limited PPM edge values (eL, eR) of the middle cell of a[0..4]
@@ -248,7 +263,7 @@ __device__ __forceinline__ R ppm_face3(const R *a, R vel, R dtih)
     const R t3 = R(2.0 / 3.0);
     R L, Rr;
     bool up;
-    if constexpr (sizeof(R) == 8)  // vel >= 0, -0 included
+    if constexpr (is_f64<R>)  // vel >= 0, -0 included
         up = __double_as_longlong(vel) >= 0 || (__double_as_longlong(vel) << 1) == 0;
     else
         up = vel >= R(0);
@@ -392,7 +407,7 @@ __device__ __forceinline__ R reinit_rhs3(const Tank3P &P, const R *__restrict__ 
         const R x = pos ? a : -a, y = pos ? nb : -nb;
         R m = positive(x) ? x : R(0);
         bool ybig;
-        if constexpr (sizeof(R) == 8)
+        if constexpr (is_f64<R>)
             ybig = positive(y) && mag_bits(y) > mag_bits(m);
         else
             ybig = y > m;
@@ -477,7 +492,7 @@ __device__ __forceinline__ R koren3(R quu, R qu, R qd)
 {
     const R d1 = qu - quu, d2 = qd - qu;
     if (nonpos_prod(d1, d2)) return qu;
-    if constexpr (sizeof(R) == 8) {
+    if constexpr (is_f64<R>) {
         const R t2 = R(2) * d2, t1 = R(2) * d1, tm = (fabs(d1) + fabs(t2)) * R(1.0 / 3.0);
         unsigned long long m = mag_bits(t2);
         const unsigned long long mm = mag_bits(tm), m1 = mag_bits(t1);
@@ -494,7 +509,7 @@ template <typename R>
 __device__ __forceinline__ R upw3(R q0, R q1, R q2, R q3, R vel)
 {
     bool up;
-    if constexpr (sizeof(R) == 8)  // vel >= 0, -0 included
+    if constexpr (is_f64<R>)  // vel >= 0, -0 included
         up = __double_as_longlong(vel) >= 0 || (__double_as_longlong(vel) << 1) == 0;
     else
         up = vel >= R(0);
@@ -959,14 +974,17 @@ __global__ void k3t_add(long long n, const double *__restrict__ a, double *__res
     if (c < n) b[c] += a[c];
 }
 
-// FP32 working copies: out = float(in) / double(in)
-__global__ void k3t_narrow(long long n, const double *__restrict__ in, float *__restrict__ out)
+// working copies: out = R(in) (float, or the nearest float and its remainder)
+// and back, out = double(in)
+template <typename R>
+__global__ void k3t_narrow(long long n, const double *__restrict__ in, R *__restrict__ out)
 {
     pdl_entry();
     const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (c < n) out[c] = float(in[c]);
+    if (c < n) out[c] = R(in[c]);
 }
-__global__ void k3t_widen(long long n, const float *__restrict__ in, double *__restrict__ out)
+template <typename R>
+__global__ void k3t_widen(long long n, const R *__restrict__ in, double *__restrict__ out)
 {
     pdl_entry();
     const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -1192,16 +1210,16 @@ int reinit_buf(wec_tank3 *T, R *s, R *s0, R *s1, int nit, double t)
 
 using namespace wec;
 
-// One step in working type R (double: the FP64 stencils; float: FP32 working
-// copies of sigma and the velocities, refreshed from the FP64 state at the
-// start of the step, with FP32 materials, advection, reinitialisation,
-// transport, viscous terms and Jacobi sweeps).  The force (from the FP64
-// materials at n), the heave, beta and the right-hand side, the solve, the
-// projection and the persistent fields are FP64 in both.
+// One step in working type R (double: the FP64 stencils; float pairs or float:
+// working copies of sigma and the velocities, refreshed from the FP64 state at
+// the start of the step, with materials, advection, reinitialisation,
+// transport, viscous terms and Jacobi sweeps in that type).  The force (from
+// the FP64 materials at n), the heave, beta and the right-hand side, the solve,
+// the projection and the persistent fields are FP64 in all of them.
 template <typename R>
 static int tank3_step_impl(wec_tank3 *T, Work3<R> &W, double dt, double pto_force, wec_step_result *out)
 {
-    constexpr bool f32 = sizeof(R) == 4;
+    constexpr bool f32 = !is_f64<R>;  // working copies
     const Tank3P &P = T->P;
     cudaStream_t st = T->st;
     const int nx = P.nx, ny = P.ny, nz = P.nz;
@@ -1233,19 +1251,22 @@ static int tank3_step_impl(wec_tank3 *T, Work3<R> &W, double dt, double pto_forc
     for (int k = 0; k < nz; ++k) vc[k] = vort((k + 0.5) * h);
     for (int k = 0; k <= nz; ++k) vf[k] = vort(k * h);
     WEC_CK(cudaMemcpyAsync(T->bc, hb.data(), hb.size() * 8, cudaMemcpyHostToDevice, st));
-    std::vector<float> hbf;
+    std::vector<R> hbf;
     if constexpr (f32) {
-        hbf.assign(hb.begin(), hb.end());
-        WEC_CK(cudaMemcpyAsync(W.bc, hbf.data(), hbf.size() * 4, cudaMemcpyHostToDevice, st));
+        hbf.reserve(hb.size());
+        for (double x : hb) hbf.push_back(R(x));
+        WEC_CK(cudaMemcpyAsync(W.bc, hbf.data(), hbf.size() * sizeof(R), cudaMemcpyHostToDevice, st));
     }
     const double *d_win0 = T->bc + nz, *d_win1 = d_win0 + nz + 1;
     const R *r_uin1 = W.bc, *r_win0 = r_uin1 + nz, *r_win1 = r_win0 + nz + 1, *r_vc = r_win1 + nz + 1,
             *r_vf = r_vc + nz;
-    if constexpr (f32) {  // FP32 working copies of the state
-        launch_k(k3t_narrow, nblk((long long)T->nc, 256), 256, 0, st, (long long)T->nc, (const double *)T->sig, W.sig);
-        launch_k(k3t_narrow, nblk((long long)T->nu, 256), 256, 0, st, (long long)T->nu, (const double *)T->u, W.u);
-        launch_k(k3t_narrow, nblk((long long)T->nv, 256), 256, 0, st, (long long)T->nv, (const double *)T->v, W.v);
-        launch_k(k3t_narrow, nblk((long long)T->nw, 256), 256, 0, st, (long long)T->nw, (const double *)T->w, W.w);
+    if constexpr (f32) {  // working copies of the state
+        WEC_PROF("convert", 0, (8.0 + sizeof(R)) * (T->nc + T->nu + T->nv + T->nw), st);
+        launch_k(k3t_narrow<R>, nblk((long long)T->nc, 256), 256, 0, st, (long long)T->nc, (const double *)T->sig,
+                 W.sig);
+        launch_k(k3t_narrow<R>, nblk((long long)T->nu, 256), 256, 0, st, (long long)T->nu, (const double *)T->u, W.u);
+        launch_k(k3t_narrow<R>, nblk((long long)T->nv, 256), 256, 0, st, (long long)T->nv, (const double *)T->v, W.v);
+        launch_k(k3t_narrow<R>, nblk((long long)T->nw, 256), 256, 0, st, (long long)T->nw, (const double *)T->w, W.w);
     }
 
     // (1) materials at n (FP64, for the force) and the heave force from
@@ -1385,7 +1406,7 @@ static int tank3_step_impl(wec_tank3 *T, Work3<R> &W, double dt, double pto_forc
                  (const double *)beta[c], (const double *)T->phi, dst[c], (long long)nf[c]);
     launch_k(k3t_add, nblk((long long)T->nc, 256), 256, 0, st, (long long)T->nc, (const double *)T->phi, T->p);
     if constexpr (f32)
-        launch_k(k3t_widen, nblk((long long)T->nc, 256), 256, 0, st, (long long)T->nc, (const float *)W.tmp, T->sig);
+        launch_k(k3t_widen<R>, nblk((long long)T->nc, 256), 256, 0, st, (long long)T->nc, (const R *)W.tmp, T->sig);
     else
         std::swap(T->sig, T->tmp);
     // diagnostics: ||h div u||, eta at the probe column (x = probe_x, middle y)
@@ -1448,7 +1469,7 @@ int wec_tank3_create(const wec_grid3 *grid, const wec_fluids *fl, const wec_wave
         return fail(WEC_ERR_INVALID, "tank3: the cylinder needs radius, length, mass, kappa_p > 0, added_mass >= 0");
     if (opts) {
         if (opts->precision != WEC_PREC_FP64 && opts->precision != WEC_PREC_MIXED_MG &&
-            opts->precision != WEC_PREC_MIXED)
+            opts->precision != WEC_PREC_MIXED && opts->precision != WEC_PREC_MIXED_DF)
             return fail(WEC_ERR_INVALID, "tank3: unknown precision");
         if (!(opts->rtol > 0.0) || opts->max_iters < 1 || opts->restart < 1 || opts->restart > kMaxRestart ||
             opts->n_reinit < 0 || opts->n_jacobi < 1 || opts->mg_pre < 1 || opts->mg_pre > 4 || opts->mg_post < 0 ||
@@ -1537,15 +1558,24 @@ int wec_tank3_create(const wec_grid3 *grid, const wec_fluids *fl, const wec_wave
         P.cd = Tank3C<double>{P.h, P.ih, P.depth, P.rho_w, P.rho_a, P.mu_w, P.mu_a, P.rho_s, P.bxc, P.byc, P.br, P.blen};
         P.cf = Tank3C<float>{(float)P.h, (float)P.ih, (float)P.depth, (float)P.rho_w, (float)P.rho_a, (float)P.mu_w,
                              (float)P.mu_a, (float)P.rho_s, (float)P.bxc, (float)P.byc, (float)P.br, (float)P.blen};
+        P.cdf = Tank3C<df64>{df64(P.h), df64(P.ih), df64(P.depth), df64(P.rho_w), df64(P.rho_a), df64(P.mu_w),
+                             df64(P.mu_a), df64(P.rho_s), df64(P.bxc), df64(P.byc), df64(P.br), df64(P.blen)};
         std::vector<float> df(nx);
-        for (int i = 0; i < nx; ++i) df[i] = (float)hc[4 * (size_t)P.ncomp + i];
+        std::vector<df64> dd(nx);
+        for (int i = 0; i < nx; ++i) {
+            df[i] = (float)hc[4 * (size_t)P.ncomp + i];
+            dd[i] = df64(hc[4 * (size_t)P.ncomp + i]);
+        }
         e = cudaMalloc(&T->fconsts, (size_t)nx * 4);
         if (e == cudaSuccess) e = cudaMemcpy(T->fconsts, df.data(), (size_t)nx * 4, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMalloc(&T->dconsts, (size_t)nx * sizeof(df64));
+        if (e == cudaSuccess) e = cudaMemcpy(T->dconsts, dd.data(), (size_t)nx * sizeof(df64), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {
             wec_tank3_destroy(T);
             return cuda_fail(e, "tank3 allocation");
         }
         P.dampf = T->fconsts;
+        P.dampd = T->dconsts;
     }
     if (opts) {  // the step: its buffers, its solver, the initial state
         T->opts = *opts;
@@ -1558,7 +1588,7 @@ int wec_tank3_create(const wec_grid3 *grid, const wec_fluids *fl, const wec_wave
                 if (e == cudaSuccess) e = cudaMalloc(q, nf[c] * 8);
         const size_t ne[3] = {(size_t)nz * (ny + 1) * (nx + 1), (size_t)(nz + 1) * ny * (nx + 1),
                               (size_t)(nz + 1) * (ny + 1) * nx};
-        if (opts->precision != WEC_PREC_MIXED)
+        if (opts->precision == WEC_PREC_FP64 || opts->precision == WEC_PREC_MIXED_MG)
             for (int c = 0; c < 3; ++c)
                 if (e == cudaSuccess) e = cudaMalloc(&T->E[c], ne[c] * 8);
         if (e == cudaSuccess) e = cudaMalloc(&T->bc, (size_t)(3 * nz + 2 + nz + nz + 1) * 8);
@@ -1615,25 +1645,30 @@ int wec_tank3_create(const wec_grid3 *grid, const wec_fluids *fl, const wec_wave
         if (e == cudaSuccess)
             e = cudaMemcpy(dtab + eta.size() + uxz.size(), wxz.data(), wxz.size() * 8, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(T->tabs, du.data(), du.size() * 8, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess && opts->precision == WEC_PREC_MIXED) {
-            // FP32 working copies of the stencils (WEC_PREC_MIXED)
-            Work3<float> &F = T->wf;
-            for (float **q : {&F.sig, &F.tmp, &F.s0, &F.s1, &F.rho, &F.mu, &F.rf, &F.chi, &F.mu1, &F.rf1, &F.chi1})
-                if (e == cudaSuccess) e = cudaMalloc(q, T->nc * 4);
+        // working copies of the stencils: FP32 (WEC_PREC_MIXED) or float pairs (WEC_PREC_MIXED_DF)
+        auto alloc_work = [&](auto &F) {
+            using RW = std::remove_pointer_t<decltype(F.sig)>;
+            const size_t b = sizeof(RW);
+            for (RW **q : std::initializer_list<RW **>{&F.sig, &F.tmp, &F.s0, &F.s1, &F.rho, &F.mu, &F.rf, &F.chi,
+                                                       &F.mu1, &F.rf1, &F.chi1})
+                if (e == cudaSuccess) e = cudaMalloc(q, T->nc * b);
             const size_t nf3[3] = {T->nu, T->nv, T->nw};
-            if (e == cudaSuccess) e = cudaMalloc(&F.u, T->nu * 4);
-            if (e == cudaSuccess) e = cudaMalloc(&F.v, T->nv * 4);
-            if (e == cudaSuccess) e = cudaMalloc(&F.w, T->nw * 4);
+            if (e == cudaSuccess) e = cudaMalloc(&F.u, T->nu * b);
+            if (e == cudaSuccess) e = cudaMalloc(&F.v, T->nv * b);
+            if (e == cudaSuccess) e = cudaMalloc(&F.w, T->nw * b);
             for (int c = 0; c < 3; ++c)
-                for (float **q : {&F.D[c], &F.R3[c], &F.A[c], &F.B[c], &F.RF[c], &F.Q[c]})
-                    if (e == cudaSuccess) e = cudaMalloc(q, nf3[c] * 4);
+                for (RW **q : std::initializer_list<RW **>{&F.D[c], &F.R3[c], &F.A[c], &F.B[c], &F.RF[c], &F.Q[c]})
+                    if (e == cudaSuccess) e = cudaMalloc(q, nf3[c] * b);
             for (int c = 0; c < 3; ++c)
-                if (e == cudaSuccess) e = cudaMalloc(&F.E[c], ne[c] * 4);
-            if (e == cudaSuccess) e = cudaMalloc(&F.bc, (size_t)(5 * nz + 3) * 4);
-            if (e == cudaSuccess) e = cudaMalloc(&F.dampu, (size_t)(nx + 1) * 4);
-            std::vector<float> duf(du.begin(), du.end());
-            if (e == cudaSuccess) e = cudaMemcpy(F.dampu, duf.data(), duf.size() * 4, cudaMemcpyHostToDevice);
-        }
+                if (e == cudaSuccess) e = cudaMalloc(&F.E[c], ne[c] * b);
+            if (e == cudaSuccess) e = cudaMalloc(&F.bc, (size_t)(5 * nz + 3) * b);
+            if (e == cudaSuccess) e = cudaMalloc(&F.dampu, (size_t)(nx + 1) * b);
+            std::vector<RW> duw;
+            for (double x : du) duw.push_back(RW(x));
+            if (e == cudaSuccess) e = cudaMemcpy(F.dampu, duw.data(), duw.size() * b, cudaMemcpyHostToDevice);
+        };
+        if (e == cudaSuccess && opts->precision == WEC_PREC_MIXED) alloc_work(T->wf);
+        if (e == cudaSuccess && opts->precision == WEC_PREC_MIXED_DF) alloc_work(T->wd);
         if (e != cudaSuccess) {
             cudaFree(dtab);
             wec_tank3_destroy(T);
@@ -1667,12 +1702,19 @@ void wec_tank3_destroy(wec_tank3 *T)
         cudaFree(p);
     for (int c = 0; c < 3; ++c)
         for (double *p : {T->D[c], T->R[c], T->A[c], T->B[c], T->E[c], T->RF[c], T->Q[c]}) cudaFree(p);
-    Work3<float> &F = T->wf;
-    for (float *p : {F.sig, F.tmp, F.s0, F.s1, F.u, F.v, F.w, F.rho, F.mu, F.rf, F.chi, F.mu1, F.rf1, F.chi1, F.bc,
-                     F.dampu, T->fconsts})
-        cudaFree(p);
-    for (int c = 0; c < 3; ++c)
-        for (float *p : {F.D[c], F.R3[c], F.A[c], F.B[c], F.E[c], F.RF[c], F.Q[c]}) cudaFree(p);
+    auto free_work = [](auto &F) {
+        using RW = std::remove_pointer_t<decltype(F.sig)>;
+        for (RW *p : std::initializer_list<RW *>{F.sig, F.tmp, F.s0, F.s1, F.u, F.v, F.w, F.rho, F.mu, F.rf, F.chi,
+                                                 F.mu1, F.rf1, F.chi1, F.bc, F.dampu})
+            cudaFree(p);
+        for (int c = 0; c < 3; ++c)
+            for (RW *p : std::initializer_list<RW *>{F.D[c], F.R3[c], F.A[c], F.B[c], F.E[c], F.RF[c], F.Q[c]})
+                cudaFree(p);
+    };
+    free_work(T->wf);
+    free_work(T->wd);
+    cudaFree(T->fconsts);
+    cudaFree(T->dconsts);
     if (T->solver) {
         poisson_free(T->solver);
         delete T->solver;
@@ -1774,6 +1816,7 @@ int wec_tank3_step(wec_tank3 *T, double dt, double pto_force, wec_step_result *o
     if (!T->stepping) return fail(WEC_ERR_INVALID, "tank3_step: the tank was created without solver options");
     if (!(dt > 0.0)) return fail(WEC_ERR_INVALID, "tank3_step: dt must be > 0");
     if (T->opts.precision == WEC_PREC_MIXED) return tank3_step_impl<float>(T, T->wf, dt, pto_force, out);
+    if (T->opts.precision == WEC_PREC_MIXED_DF) return tank3_step_impl<df64>(T, T->wd, dt, pto_force, out);
     Work3<double> W;
     W.sig = T->sig; W.tmp = T->tmp; W.s0 = T->s0; W.s1 = T->s1; W.u = T->u; W.v = T->v; W.w = T->w;
     W.rho = T->rho; W.mu = T->mu; W.rf = T->rhof; W.chi = T->chi; W.mu1 = T->mu1; W.rf1 = T->rf1; W.chi1 = T->chi1;

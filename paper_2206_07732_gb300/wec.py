@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libwec.so")
 
 WEC_OK, WEC_ERR_INVALID, WEC_ERR_CUDA, WEC_ERR_NOT_CONVERGED, WEC_ERR_NONFINITE, WEC_ERR_NOMEM = range(6)
-PREC_FP64, PREC_MIXED, PREC_MIXED_MG = 0, 1, 2
+PREC_FP64, PREC_MIXED, PREC_MIXED_MG, PREC_MIXED_DF = 0, 1, 2, 3
 (F_SIGMA, F_U, F_V, F_P, F_USTAR, F_VSTAR, F_BETA_U, F_BETA_V, F_RHS, F_SIGMA_ADV) = range(10)
 FIELD_NAMES = {"sigma": F_SIGMA, "u": F_U, "v": F_V, "p": F_P, "ustar": F_USTAR, "vstar": F_VSTAR,
                "beta_u": F_BETA_U, "beta_v": F_BETA_V, "rhs": F_RHS, "sigma_adv": F_SIGMA_ADV}

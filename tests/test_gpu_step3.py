@@ -45,12 +45,15 @@ def test_initial_state_matches_oracle(shape):
     t.close()
 
 
+@pytest.mark.parametrize("prec", [wec.PREC_FP64, wec.PREC_MIXED_DF])
 @pytest.mark.parametrize("shape,body", [((32, 8, 16), True), ((40, 12, 20), True), ((24, 8, 16), False)])
-def test_steps_match_oracle(shape, body):
+def test_steps_match_oracle(shape, body, prec):
+    # FP64 stencils, and double-float stencils (FP32 pairs) with FP32 V-cycles:
+    # both hold every field within 1e-10 of the FP64 oracle step after step
     c = _cfg(*shape)
     if not body:
         c["body"] = None
-    t, o = wec.Tank3(c), T3.OracleTank3(c)
+    t, o = wec.Tank3(c, precision=prec), T3.OracleTank3(c)
     for s in range(4):
         r, ro = t.step(c["dt"]), o.step(c["dt"])
         assert r["status"] == 0 and ro["status"] == 0
@@ -64,13 +67,15 @@ def test_steps_match_oracle(shape, body):
         if body:
             assert r["f_hydro"] == pytest.approx(ro["f_hydro"], rel=1e-10)
             assert r["zdot"] == pytest.approx(ro["zdot"], rel=1e-10, abs=1e-14)
-        assert abs(r["iters"] - ro["iters"]) <= 1
+        if prec == wec.PREC_FP64:  # the same preconditioner as the oracle's
+            assert abs(r["iters"] - ro["iters"]) <= 1
     t.close()
 
 
-def test_heave_after_200_steps():
+@pytest.mark.parametrize("prec", [wec.PREC_FP64, wec.PREC_MIXED_DF])
+def test_heave_after_200_steps(prec):
     c = _cfg(32, 8, 16, seed=3, rtol=1e-10)
-    t, o = wec.Tank3(c), T3.OracleTank3(c)
+    t, o = wec.Tank3(c, precision=prec), T3.OracleTank3(c)
     for _ in range(200):
         r, ro = t.step(c["dt"]), o.step(c["dt"])
     print(f"200 steps: z {r['z']:.9e} / {ro['z']:.9e}, zdot {r['zdot']:.9e} / {ro['zdot']:.9e}")
@@ -139,14 +144,15 @@ def test_full_size_step_matches_the_oracle_everywhere():
     # sides solving to 1e-12.  The comparison covers the interior fast path of
     # the momentum and Jacobi stencils (32-bit offsets, no ghost rules), every
     # boundary face, and the cell layers of the force integral around the cylinder.
-    c = synth.tank3d(seed=0, rtol=1e-12, mg_pre=3, mg_post=3, restart=5)
+    from paper_2206_07732_gb300 import tune
+    c = tune.with_options(synth.tank3d(seed=0, rtol=1e-12), (3, 3, 5))
     o = T3.OracleTank3(c)
     ro = o.step(c["dt"])
     assert ro["status"] == 0
     ref = {name: o.get(fo) for _, fo, name in FIELDS}
     del o
     vs = np.max(np.abs(ref["u"]))
-    for prec, bound in ((wec.PREC_FP64, 1e-10), (wec.PREC_MIXED_MG, 1e-9)):
+    for prec, bound in ((wec.PREC_FP64, 1e-10), (wec.PREC_MIXED_MG, 1e-9), (wec.PREC_MIXED_DF, 1e-9)):
         t = wec.Tank3(c, precision=prec)
         r = t.step(c["dt"])
         assert r["status"] == 0 and r["residual"] <= 1e-12
