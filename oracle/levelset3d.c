@@ -98,10 +98,17 @@ void oracle3_materials(const oracle3_tank *P, const double *sg, double zc, doubl
             }
 }
 
-static double sig3(const oracle3_tank *P, const double *s, int i, int j, int k, double t)
+/* sigma at (i, j, k) with its ghosts; the inflow ghost is the incident wave's
+ * z - depth - eta at time ta, or, for a field that is the mean of two time
+ * levels (ta != tb), with the mean of eta at ta and tb. */
+static double sig3(const oracle3_tank *P, const double *s, int i, int j, int k, double ta, double tb)
 {
     int nx = P->nx, ny = P->ny, nz = P->nz;
-    if (i < 0) return (k + 0.5) * P->h - P->depth - eta3(P, (i + 0.5) * P->h, t);
+    if (i < 0) {
+        double x = (i + 0.5) * P->h, e = eta3(P, x, ta);
+        if (tb != ta) e = 0.5 * (e + eta3(P, x, tb));
+        return (k + 0.5) * P->h - P->depth - e;
+    }
     i = i > nx - 1 ? nx - 1 : i;
     j = clamp3(j, 0, ny - 1);
     size_t col = (size_t)j * nx + i, pl = (size_t)nx * ny;
@@ -165,9 +172,10 @@ static double damp3(const oracle3_tank *P, double x)
     return (exp(pow(xi, 3.5)) - 1.0) / (exp(1.0) - 1.0);
 }
 
-/* sigma* at cell (i, j, k) */
-static double advect_cell3(const oracle3_tank *P, const double *s, const double *u, const double *v, const double *w,
-                           double dt, double t, int i, int j, int k)
+/* sigma* at cell (i, j, k): base - dt Q(u, s), then the damping-zone blend
+ * (base = s for the plain update; the ghosts of s at ta, tb as in sig3) */
+static double advect_cell3(const oracle3_tank *P, const double *base, const double *s, const double *u,
+                           const double *v, const double *w, double dt, double ta, double tb, int i, int j, int k)
 {
     int nx = P->nx, ny = P->ny;
     double h = P->h, a[6];
@@ -175,18 +183,18 @@ static double advect_cell3(const oracle3_tank *P, const double *s, const double 
     size_t fu = r * (nx + 1) + i, fv = ((size_t)k * (ny + 1) + j) * nx + i;
     double fx[2], fy[2], fz[2];
     for (int f = 0; f < 2; ++f) {
-        for (int q = 0; q < 6; ++q) a[q] = sig3(P, s, i + f - 3 + q, j, k, t);
+        for (int q = 0; q < 6; ++q) a[q] = sig3(P, s, i + f - 3 + q, j, k, ta, tb);
         fx[f] = ppmface3(a, u[fu + f], dt, h);
-        for (int q = 0; q < 6; ++q) a[q] = sig3(P, s, i, j + f - 3 + q, k, t);
+        for (int q = 0; q < 6; ++q) a[q] = sig3(P, s, i, j + f - 3 + q, k, ta, tb);
         fy[f] = ppmface3(a, v[fv + (size_t)f * nx], dt, h);
-        for (int q = 0; q < 6; ++q) a[q] = sig3(P, s, i, j, k + f - 3 + q, t);
+        for (int q = 0; q < 6; ++q) a[q] = sig3(P, s, i, j, k + f - 3 + q, ta, tb);
         fz[f] = ppmface3(a, w[c + (size_t)f * nx * ny], dt, h);
     }
     double ub = 0.5 * (u[fu] + u[fu + 1]);
     double vb = 0.5 * (v[fv] + v[fv + nx]);
     double wb = 0.5 * (w[c] + w[c + (size_t)nx * ny]);
     double Q = ub * (fx[1] - fx[0]) / h + vb * (fy[1] - fy[0]) / h + wb * (fz[1] - fz[0]) / h;
-    double sa = s[c] - dt * Q;
+    double sa = base[c] - dt * Q;
     double al = damp3(P, (i + 0.5) * h);
     return (1.0 - al) * sa + al * ((k + 0.5) * h - P->depth);
 }
@@ -198,7 +206,21 @@ void oracle3_advect(const oracle3_tank *P, const double *s, const double *u, con
     for (int k = 0; k < P->nz; ++k)
         for (int j = 0; j < P->ny; ++j)
             for (int i = 0; i < P->nx; ++i)
-                out[((size_t)k * P->ny + j) * P->nx + i] = advect_cell3(P, s, u, v, w, dt, t, i, j, k);
+                out[((size_t)k * P->ny + j) * P->nx + i] = advect_cell3(P, s, s, u, v, w, dt, t, t, i, j, k);
+}
+
+/* The update of a fixed-point cycle k >= 1 (section "Time stepping scheme"):
+ * out = base - dt Q(u, s) then the damping-zone blend, with base = sigma^n and
+ * s, u the means of time levels n and n+1,k (inflow ghosts: the mean of the
+ * incident wave at ta = t^n and tb = t^{n+1}). */
+void oracle3_advect_half(const oracle3_tank *P, const double *base, const double *s, const double *u, const double *v,
+                         const double *w, double dt, double ta, double tb, double *out)
+{
+    ORACLE_PAR_FOR
+    for (int k = 0; k < P->nz; ++k)
+        for (int j = 0; j < P->ny; ++j)
+            for (int i = 0; i < P->nx; ++i)
+                out[((size_t)k * P->ny + j) * P->nx + i] = advect_cell3(P, base, s, u, v, w, dt, ta, tb, i, j, k);
 }
 
 /* The same at ncell listed cells (cell index c = (k ny + j) nx + i). */
@@ -208,7 +230,7 @@ void oracle3_advect_cells(const oracle3_tank *P, const double *s, const double *
     for (int q = 0; q < ncell; ++q) {
         long long c = cells[q];
         int i = (int)(c % P->nx), j = (int)((c / P->nx) % P->ny), k = (int)(c / ((long long)P->nx * P->ny));
-        out[q] = advect_cell3(P, s, u, v, w, dt, t, i, j, k);
+        out[q] = advect_cell3(P, s, s, u, v, w, dt, t, t, i, j, k);
     }
 }
 
@@ -221,13 +243,13 @@ static double mm3(double a, double b)
 /* S(sigma0) (|grad sigma| - 1) at cell (i, j, k), Godunov on ENO-2 differences */
 static double rrhs3(const oracle3_tank *P, const double *f, const double *s0, int i, int j, int k, double t)
 {
-    double h = P->h, c = sig3(P, f, i, j, k, t);
+    double h = P->h, c = sig3(P, f, i, j, k, t, t);
     double g[3];
     int sgn_pos = s0[((size_t)k * P->ny + j) * P->nx + i] > 0.0;
     for (int d = 0; d < 3; ++d) {
         int di = d == 0, dj = d == 1, dk = d == 2;
-        double m2 = sig3(P, f, i - 2 * di, j - 2 * dj, k - 2 * dk, t), m1 = sig3(P, f, i - di, j - dj, k - dk, t);
-        double p1 = sig3(P, f, i + di, j + dj, k + dk, t), p2 = sig3(P, f, i + 2 * di, j + 2 * dj, k + 2 * dk, t);
+        double m2 = sig3(P, f, i - 2 * di, j - 2 * dj, k - 2 * dk, t, t), m1 = sig3(P, f, i - di, j - dj, k - dk, t, t);
+        double p1 = sig3(P, f, i + di, j + dj, k + dk, t, t), p2 = sig3(P, f, i + 2 * di, j + 2 * dj, k + 2 * dk, t, t);
         double dm = m2 - 2.0 * m1 + c, d0 = m1 - 2.0 * c + p1, dp = c - 2.0 * p1 + p2;
         double a = (c - m1) / h + mm3(dm, d0) / (2.0 * h);
         double b = (p1 - c) / h - mm3(d0, dp) / (2.0 * h);

@@ -38,6 +38,9 @@ def _lib():
         L.oracle3_advect_cells.argtypes = [C.POINTER(Tank3), _dp, _dp, _dp, _dp, C.c_double, C.c_double,
                                            C.POINTER(C.c_longlong), C.c_int, _dp]
         L.oracle3_advect_cells.restype = None
+        L.oracle3_advect_half.argtypes = [C.POINTER(Tank3), _dp, _dp, _dp, _dp, _dp, C.c_double, C.c_double,
+                                          C.c_double, _dp]
+        L.oracle3_advect_half.restype = None
         _done = True
     return L
 
@@ -85,6 +88,18 @@ class Oracle3:
         assert u.shape == (nz, ny, nx + 1) and v.shape == (nz, ny + 1, nx) and w.shape == (nz + 1, ny, nx)
         out = np.zeros(self.shape)
         _lib().oracle3_advect(C.byref(self.P), _ptr(s), _ptr(u), _ptr(v), _ptr(w), dt, t, _ptr(out))
+        return out
+
+    def advect_half(self, base, sigma, u, v, w, dt, ta, tb):
+        """A fixed-point cycle's update: base - dt Q(u, sigma), then the damping
+        blend; the inflow ghosts of sigma and w use the mean of times ta, tb."""
+        b, s, u, v, w = _f64(base), _f64(sigma), _f64(u), _f64(v), _f64(w)
+        nz, ny, nx = self.shape
+        assert b.shape == s.shape == self.shape
+        assert u.shape == (nz, ny, nx + 1) and v.shape == (nz, ny + 1, nx) and w.shape == (nz + 1, ny, nx)
+        out = np.zeros(self.shape)
+        _lib().oracle3_advect_half(C.byref(self.P), _ptr(b), _ptr(s), _ptr(u), _ptr(v), _ptr(w), dt, ta, tb,
+                                   _ptr(out))
         return out
 
     def advect_cells(self, sigma, u, v, w, dt, t, cells):

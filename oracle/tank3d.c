@@ -73,6 +73,8 @@ void oracle3_materials(const oracle3_tank *P, const double *sg, double zc, doubl
                        double *chi);
 void oracle3_advect(const oracle3_tank *P, const double *s, const double *u, const double *v, const double *w,
                     double dt, double t, double *out);
+void oracle3_advect_half(const oracle3_tank *P, const double *base, const double *s, const double *u, const double *v,
+                         const double *w, double dt, double ta, double tb, double *out);
 void oracle3_reinit(const oracle3_tank *P, double *s, int nit, double t);
 int oracle3_poisson_solve(int nx, int ny, int nz, const double *bx, const double *by, const double *bz,
                           const double *b, double *x, double rtol, int maxit, int restart, int nu1, int nu2,
@@ -83,6 +85,7 @@ typedef struct {
     double g, kappa_p, added_mass, pto_damping, probe_x, lz;
     double rtol;
     int max_iters, restart, n_reinit, n_jacobi, mg_pre, mg_post;
+    int n_cycles; /* fixed-point cycles per step (section "Time stepping scheme"); 0 or 1: one */
 } oracle3_params;
 
 typedef struct {
@@ -169,14 +172,22 @@ static double vt(const o3tank *T, const double *v, int i, int j, int k)
     return v[VI(i, j, k)];
 }
 
-static double wt(const o3tank *T, const double *w, int i, int j, int k, double t)
+/* w with its ghosts; at the inflow the odd reflection about the incident wave's
+ * w_in at time ta, or, for the mean of two time levels (ta != tb), about the
+ * mean of w_in at ta and tb */
+static double wt(const o3tank *T, const double *w, int i, int j, int k, double ta, double tb)
 {
     k = cl3(k, 0, NZ);
     j = cl3(j, 0, NY - 1);
     if (i > NX - 1) i = NX - 1;
     if (i < 0) {
         double ui, wi;
-        airyt(T, 0.0, k * T->h, t, &ui, &wi);
+        airyt(T, 0.0, k * T->h, ta, &ui, &wi);
+        if (tb != ta) {
+            double u2, w2;
+            airyt(T, 0.0, k * T->h, tb, &u2, &w2);
+            wi = 0.5 * (wi + w2);
+        }
         return 2.0 * wi - w[WI(-1 - i, j, k)];
     }
     return w[WI(i, j, k)];
@@ -223,7 +234,7 @@ static double rwt(const o3tank *T, const double *rc, int i, int j, int k)
 typedef struct {
     const o3tank *T;
     const double *rc, *u, *v, *w;
-    double t;
+    double t, t2; /* the velocity's time level(s): ghosts as in wt */
 } tctx3;
 
 /* rho-breve and C of the u-face (i, j, k) */
@@ -253,7 +264,7 @@ static void trans_u(const tctx3 *X, int i, int j, int k, double dt, double *rb, 
     }
     for (int s = 0; s < 2; ++s) { /* z: CV faces on the xz-edges (i, k+s) */
         int c = k - 1 + s;
-        double W = 0.5 * (wt(T, X->w, i - 1, j, c + 1, X->t) + wt(T, X->w, i, j, c + 1, X->t));
+        double W = 0.5 * (wt(T, X->w, i - 1, j, c + 1, X->t, X->t2) + wt(T, X->w, i, j, c + 1, X->t, X->t2));
         double r = upw(rut(T, X->rc, i, j, c - 1), rut(T, X->rc, i, j, c), rut(T, X->rc, i, j, c + 1),
                        rut(T, X->rc, i, j, c + 2), W);
         double q = upw(ut(T, X->u, i, j, c - 1), ut(T, X->u, i, j, c), ut(T, X->u, i, j, c + 1),
@@ -291,7 +302,7 @@ static void trans_v(const tctx3 *X, int i, int j, int k, double dt, double *rb, 
     }
     for (int s = 0; s < 2; ++s) { /* z: CV faces on the yz-edges (j, k+s) */
         int c = k - 1 + s;
-        double W = 0.5 * (wt(T, X->w, i, j - 1, c + 1, X->t) + wt(T, X->w, i, j, c + 1, X->t));
+        double W = 0.5 * (wt(T, X->w, i, j - 1, c + 1, X->t, X->t2) + wt(T, X->w, i, j, c + 1, X->t, X->t2));
         double r = upw(rvt(T, X->rc, i, j, c - 1), rvt(T, X->rc, i, j, c), rvt(T, X->rc, i, j, c + 1),
                        rvt(T, X->rc, i, j, c + 2), W);
         double q = upw(vt(T, X->v, i, j, c - 1), vt(T, X->v, i, j, c), vt(T, X->v, i, j, c + 1),
@@ -307,14 +318,14 @@ static void trans_w(const tctx3 *X, int i, int j, int k, double dt, double *rb, 
 {
     const o3tank *T = X->T;
     double h = T->h, m[6], f[6];
-    double t = X->t;
+    double t = X->t, t2 = X->t2;
     for (int s = 0; s < 2; ++s) { /* x: CV faces on the xz-edges (i+s, k) */
         int a = i - 1 + s;
         double U = 0.5 * (ut(T, X->u, a + 1, j, k - 1) + ut(T, X->u, a + 1, j, k));
         double r = upw(rwt(T, X->rc, a - 1, j, k), rwt(T, X->rc, a, j, k), rwt(T, X->rc, a + 1, j, k),
                        rwt(T, X->rc, a + 2, j, k), U);
-        double q = upw(wt(T, X->w, a - 1, j, k, t), wt(T, X->w, a, j, k, t), wt(T, X->w, a + 1, j, k, t),
-                       wt(T, X->w, a + 2, j, k, t), U);
+        double q = upw(wt(T, X->w, a - 1, j, k, t, t2), wt(T, X->w, a, j, k, t, t2), wt(T, X->w, a + 1, j, k, t, t2),
+                       wt(T, X->w, a + 2, j, k, t, t2), U);
         m[s] = U * r;
         f[s] = m[s] * q;
     }
@@ -323,18 +334,18 @@ static void trans_w(const tctx3 *X, int i, int j, int k, double dt, double *rb, 
         double V = 0.5 * (vt(T, X->v, i, b + 1, k - 1) + vt(T, X->v, i, b + 1, k));
         double r = upw(rwt(T, X->rc, i, b - 1, k), rwt(T, X->rc, i, b, k), rwt(T, X->rc, i, b + 1, k),
                        rwt(T, X->rc, i, b + 2, k), V);
-        double q = upw(wt(T, X->w, i, b - 1, k, t), wt(T, X->w, i, b, k, t), wt(T, X->w, i, b + 1, k, t),
-                       wt(T, X->w, i, b + 2, k, t), V);
+        double q = upw(wt(T, X->w, i, b - 1, k, t, t2), wt(T, X->w, i, b, k, t, t2), wt(T, X->w, i, b + 1, k, t, t2),
+                       wt(T, X->w, i, b + 2, k, t, t2), V);
         m[2 + s] = V * r;
         f[2 + s] = m[2 + s] * q;
     }
     for (int s = 0; s < 2; ++s) { /* z: CV faces at cell centres k-1+s */
         int c = k - 1 + s;
-        double W = 0.5 * (wt(T, X->w, i, j, c, t) + wt(T, X->w, i, j, c + 1, t));
+        double W = 0.5 * (wt(T, X->w, i, j, c, t, t2) + wt(T, X->w, i, j, c + 1, t, t2));
         double r = upw(rwt(T, X->rc, i, j, c - 1), rwt(T, X->rc, i, j, c), rwt(T, X->rc, i, j, c + 1),
                        rwt(T, X->rc, i, j, c + 2), W);
-        double q = upw(wt(T, X->w, i, j, c - 1, t), wt(T, X->w, i, j, c, t), wt(T, X->w, i, j, c + 1, t),
-                       wt(T, X->w, i, j, c + 2, t), W);
+        double q = upw(wt(T, X->w, i, j, c - 1, t, t2), wt(T, X->w, i, j, c, t, t2), wt(T, X->w, i, j, c + 1, t, t2),
+                       wt(T, X->w, i, j, c + 2, t, t2), W);
         m[4 + s] = W * r;
         f[4 + s] = m[4 + s] * q;
     }
@@ -346,13 +357,13 @@ static void trans_w(const tctx3 *X, int i, int j, int k, double dt, double *rb, 
 typedef struct {
     const o3tank *T;
     const double *mu, *u, *v, *w;
-    double t;
+    double t, t2; /* the velocity's time level(s): ghosts as in wt */
 } vctx3;
 
 #define MU(i, j, k) cellt(X->T, X->mu, i, j, k)
 #define UT(i, j, k) ut(X->T, X->u, i, j, k)
 #define VT(i, j, k) vt(X->T, X->v, i, j, k)
-#define WT(i, j, k) wt(X->T, X->w, i, j, k, X->t)
+#define WT(i, j, k) wt(X->T, X->w, i, j, k, X->t, X->t2)
 
 /* edge viscosities: the mean of the four cells around the edge */
 static double mxy(const vctx3 *X, int i, int j, int k)
@@ -445,7 +456,7 @@ static double vortt(const o3tank *T, double z, double dt)
 }
 
 /* heave force, Eq. int_fh */
-static double force3(const o3tank *T, const double *mu)
+static double force3(const o3tank *T, const double *mu, double tv)
 {
     double h = T->h, F = 0.0, A = h * h;
     if (!T->P.L.has_body) return 0.0;
@@ -458,7 +469,7 @@ static double force3(const o3tank *T, const double *mu)
                 double nz_ = pl < 0.0 ? 1.0 : -1.0, wl = fabs(pl), wr = fabs(pr);
                 double pf = (T->p[CI(i, j, k - 1)] * wr + T->p[CI(i, j, k)] * wl) / (wl + wr);
                 double muf = 0.5 * (mu[CI(i, j, k - 1)] + mu[CI(i, j, k)]);
-                double dwdz = (wt(T, T->w, i, j, k + 1, T->t) - wt(T, T->w, i, j, k - 1, T->t)) / (2.0 * h);
+                double dwdz = (wt(T, T->w, i, j, k + 1, tv, tv) - wt(T, T->w, i, j, k - 1, tv, tv)) / (2.0 * h);
                 F += (-pf * nz_ + muf * 2.0 * dwdz * nz_) * A;
             }
     for (int k = 0; k < NZ; ++k) /* x-faces: mu (dw/dx + du/dz) */
@@ -469,8 +480,8 @@ static double force3(const o3tank *T, const double *mu)
                 if (!(pl * pr < 0.0)) continue;
                 double nx_ = pl < 0.0 ? 1.0 : -1.0;
                 double muf = 0.5 * (mu[CI(i - 1, j, k)] + mu[CI(i, j, k)]);
-                double dwdx = 0.5 * ((wt(T, T->w, i, j, k, T->t) - wt(T, T->w, i - 1, j, k, T->t)) +
-                                     (wt(T, T->w, i, j, k + 1, T->t) - wt(T, T->w, i - 1, j, k + 1, T->t))) / h;
+                double dwdx = 0.5 * ((wt(T, T->w, i, j, k, tv, tv) - wt(T, T->w, i - 1, j, k, tv, tv)) +
+                                     (wt(T, T->w, i, j, k + 1, tv, tv) - wt(T, T->w, i - 1, j, k + 1, tv, tv))) / h;
                 double dudz = (ut(T, T->u, i, j, k + 1) - ut(T, T->u, i, j, k - 1)) / (2.0 * h);
                 F += muf * (dwdx + dudz) * nx_ * A;
             }
@@ -482,8 +493,8 @@ static double force3(const o3tank *T, const double *mu)
                 if (!(pl * pr < 0.0)) continue;
                 double ny_ = pl < 0.0 ? 1.0 : -1.0;
                 double muf = 0.5 * (mu[CI(i, j - 1, k)] + mu[CI(i, j, k)]);
-                double dwdy = 0.5 * ((wt(T, T->w, i, j, k, T->t) - wt(T, T->w, i, j - 1, k, T->t)) +
-                                     (wt(T, T->w, i, j, k + 1, T->t) - wt(T, T->w, i, j - 1, k + 1, T->t))) / h;
+                double dwdy = 0.5 * ((wt(T, T->w, i, j, k, tv, tv) - wt(T, T->w, i, j - 1, k, tv, tv)) +
+                                     (wt(T, T->w, i, j, k + 1, tv, tv) - wt(T, T->w, i, j - 1, k + 1, tv, tv))) / h;
                 double dvdz = (vt(T, T->v, i, j, k + 1) - vt(T, T->v, i, j, k - 1)) / (2.0 * h);
                 F += muf * (dwdy + dvdz) * ny_ * A;
             }
@@ -509,31 +520,88 @@ int oracle3_step(void *handle, double dt, double f_pto_in, oracle3_result *out)
     double *mu_1 = zal(n), *rf_1 = zal(n), *chi_1 = zal(n), *rho_1 = zal(n);
     double *Ru = zal(nu), *Rv = zal(nv), *Rw = zal(nw), *Du = zal(nu), *Dv = zal(nv), *Dw = zal(nw);
     double *ua = zal(nu), *va = zal(nv), *wa = zal(nw), *ub = zal(nu), *vb = zal(nv), *wb = zal(nw);
+    double *bx = zal(nu), *by = zal(nv), *bz = zal(nw), *rhs = zal(n), *phi = zal(n), *sig1 = zal(n);
 
-    /* (1) force from p^{n-1/2}, u^n */
-    oracle3_materials(&T->P.L, T->sig, T->zc, rho_n, mu_n, rf_n, chi_n);
-    double F = force3(T, mu_n);
+    /* Fixed-point cycles k = 0 .. n_cycles - 1 (section "Time stepping scheme"):
+     * the iterate (sigma, u, p, z)^{n+1,k} lives in the tank's fields and starts
+     * from time level n (k = 0: u^n, p^{n-1/2}, sigma^n, the body at z^n); cycle
+     * k takes the force from it, advects sigma^n with the means of levels n and
+     * n+1,k, and solves the momentum system of level n with the pressure and
+     * the body velocity of the iterate.  One cycle is the plain step. */
+    const int ncyc = T->P.n_cycles > 1 ? T->P.n_cycles : 1;
+    const double *sig_n = T->sig, *u_n = T->u, *v_n = T->v, *w_n = T->w;
+    double *keep[4] = {0, 0, 0, 0}, *sh = 0, *uh = 0, *vh = 0, *wh = 0, *mk[4] = {0, 0, 0, 0};
+    if (ncyc > 1) { /* level n, kept while the tank's fields hold the iterate */
+        keep[0] = zal(n);
+        keep[1] = zal(nu);
+        keep[2] = zal(nv);
+        keep[3] = zal(nw);
+        memcpy(keep[0], T->sig, n * sizeof(double));
+        memcpy(keep[1], T->u, nu * sizeof(double));
+        memcpy(keep[2], T->v, nv * sizeof(double));
+        memcpy(keep[3], T->w, nw * sizeof(double));
+        sig_n = keep[0];
+        u_n = keep[1];
+        v_n = keep[2];
+        w_n = keep[3];
+        sh = zal(n);
+        uh = zal(nu);
+        vh = zal(nv);
+        wh = zal(nw);
+        for (int q = 0; q < 4; ++q) mk[q] = zal(n);
+    }
+    const double zc_n = T->zc, zd_n = T->zdot, zd_prev = T->zdot_prev;
+    /* materials at level n: the explicit half of the momentum system, and the
+     * force of the first cycle */
+    oracle3_materials(&T->P.L, sig_n, zc_n, rho_n, mu_n, rf_n, chi_n);
+    const double fpto = f_pto_in - T->P.pto_damping * zd_n;
+    double F = 0.0, zd1 = zd_n, zc1 = zc_n, relres = 0.0, bn = 0.0;
+    int iters = 0, st = 0;
+    for (int cyc = 0; cyc < ncyc; ++cyc) {
 
-    /* (2) heave */
-    double fpto = f_pto_in - T->P.pto_damping * T->zdot;
-    double zd1 = T->zdot, zc1 = T->zc;
-    if (T->P.L.has_body) {
-        double m = T->P.L.body_mass, ma = T->P.added_mass;
-        zd1 = T->zdot + (dt * (F - m * g + fpto) + ma * (T->zdot - T->zdot_prev)) / (m + ma);
-        zc1 = T->zc + 0.5 * dt * (T->zdot + zd1);
+    /* (1) force from p^{n+1/2,k}, u^{n+1,k} and the body at z^{n+1,k} (k = 0:
+     * p^{n-1/2}, u^n, z^n) */
+    if (cyc == 0) {
+        F = force3(T, mu_n, t0);
+    } else {
+        oracle3_materials(&T->P.L, T->sig, T->zc, mk[0], mk[1], mk[2], mk[3]);
+        F = force3(T, mk[1], t1);
     }
 
-    /* (3) sigma */
-    double *sig1 = zal(n);
-    oracle3_advect(&T->P.L, T->sig, T->u, T->v, T->w, dt, t0, sig1);
+    /* (2) heave */
+    zd1 = zd_n;
+    zc1 = zc_n;
+    if (T->P.L.has_body) {
+        double m = T->P.L.body_mass, ma = T->P.added_mass;
+        zd1 = zd_n + (dt * (F - m * g + fpto) + ma * (zd_n - zd_prev)) / (m + ma);
+        zc1 = zc_n + 0.5 * dt * (zd_n + zd1);
+    }
+
+    /* (3) sigma: sigma^n advected with u^{n+1/2,k}, sigma^{n+1/2,k} */
+    if (cyc == 0) {
+        oracle3_advect(&T->P.L, sig_n, u_n, v_n, w_n, dt, t0, sig1);
+    } else {
+        ORACLE_PAR_FOR
+        for (size_t c = 0; c < n; ++c) sh[c] = 0.5 * (sig_n[c] + T->sig[c]);
+        for (size_t f = 0; f < nu; ++f) uh[f] = 0.5 * (u_n[f] + T->u[f]);
+        for (size_t f = 0; f < nv; ++f) vh[f] = 0.5 * (v_n[f] + T->v[f]);
+        for (size_t f = 0; f < nw; ++f) wh[f] = 0.5 * (w_n[f] + T->w[f]);
+        oracle3_advect_half(&T->P.L, sig_n, sh, uh, vh, wh, dt, t0, t1, sig1);
+    }
     oracle3_reinit(&T->P.L, sig1, T->P.n_reinit, t1);
 
     /* (4) materials at n+1 */
     oracle3_materials(&T->P.L, sig1, zc1, rho_1, mu_1, rf_1, chi_1);
 
-    /* (5) transport and the momentum system */
-    tctx3 X = {T, rho_n, T->u, T->v, T->w, t0};
-    vctx3 Vn = {T, mu_n, T->u, T->v, T->w, t0};
+    /* (5) transport (advecting velocity u^{n+1/2,k}) and the momentum system */
+    tctx3 X = {T, rho_n, u_n, v_n, w_n, t0, t0};
+    if (cyc > 0) {
+        X.u = uh;
+        X.v = vh;
+        X.w = wh;
+        X.t2 = t1;
+    }
+    vctx3 Vn = {T, mu_n, u_n, v_n, w_n, t0, t0};
     ORACLE_PAR_FOR
     for (int k = 0; k < nz; ++k)
         for (int j = 0; j < ny; ++j)
@@ -543,7 +611,7 @@ int oracle3_step(void *handle, double dt, double f_pto_in, oracle3_result *out)
                 trans_u(&X, i, j, k, dt, &rb, &C);
                 double chi = 0.5 * (cellt(T, chi_1, i - 1, j, k) + cellt(T, chi_1, i, j, k));
                 Du[f] = rb / dt + chi / kp + dampt(T, i * h) * rb / dt + vortt(T, (k + 0.5) * h, dt);
-                Ru[f] = rut(T, rho_n, i, j, k) * T->u[f] / dt - C + 0.5 * viscx3(&Vn, i, j, k) -
+                Ru[f] = rut(T, rho_n, i, j, k) * u_n[f] / dt - C + 0.5 * viscx3(&Vn, i, j, k) -
                         (T->p[CI(i, j, k)] - T->p[CI(i - 1, j, k)]) / h;
             }
     ORACLE_PAR_FOR
@@ -555,7 +623,7 @@ int oracle3_step(void *handle, double dt, double f_pto_in, oracle3_result *out)
                 trans_v(&X, i, j, k, dt, &rb, &C);
                 double chi = 0.5 * (cellt(T, chi_1, i, j - 1, k) + cellt(T, chi_1, i, j, k));
                 Dv[f] = rb / dt + chi / kp + dampt(T, (i + 0.5) * h) * rb / dt + vortt(T, (k + 0.5) * h, dt);
-                Rv[f] = rvt(T, rho_n, i, j, k) * T->v[f] / dt - C + 0.5 * viscy3(&Vn, i, j, k) -
+                Rv[f] = rvt(T, rho_n, i, j, k) * v_n[f] / dt - C + 0.5 * viscy3(&Vn, i, j, k) -
                         (T->p[CI(i, j, k)] - T->p[CI(i, j - 1, k)]) / h;
             }
     ORACLE_PAR_FOR
@@ -570,14 +638,14 @@ int oracle3_step(void *handle, double dt, double f_pto_in, oracle3_result *out)
                 Dw[f] = rb / dt + chi / kp + dampt(T, (i + 0.5) * h) * rb / dt + vortt(T, k * h, dt);
                 double gp = k < nz ? (T->p[CI(i, j, k)] - T->p[CI(i, j, k - 1)]) / h
                                    : -2.0 * T->p[CI(i, j, nz - 1)] / h;
-                Rw[f] = rwt(T, rho_n, i, j, k) * T->w[f] / dt - C + 0.5 * viscz3(&Vn, i, j, k) - rf * g +
+                Rw[f] = rwt(T, rho_n, i, j, k) * w_n[f] / dt - C + 0.5 * viscz3(&Vn, i, j, k) - rf * g +
                         chi * zd1 / kp - gp;
             }
 
     /* (6) Crank-Nicolson Jacobi sweeps; Dirichlet faces at n+1 */
-    memcpy(ua, T->u, nu * sizeof(double));
-    memcpy(va, T->v, nv * sizeof(double));
-    memcpy(wa, T->w, nw * sizeof(double));
+    memcpy(ua, u_n, nu * sizeof(double));
+    memcpy(va, v_n, nv * sizeof(double));
+    memcpy(wa, w_n, nw * sizeof(double));
     for (int k = 0; k < nz; ++k) {
         double uin, win;
         airyt(T, 0.0, (k + 0.5) * h, t1, &uin, &win);
@@ -597,7 +665,7 @@ int oracle3_step(void *handle, double dt, double f_pto_in, oracle3_result *out)
     memcpy(vb, va, nv * sizeof(double));
     memcpy(wb, wa, nw * sizeof(double));
     for (int it = 0; it < T->P.n_jacobi; ++it) {
-        vctx3 Vk = {T, mu_1, ua, va, wa, t1};
+        vctx3 Vk = {T, mu_1, ua, va, wa, t1, t1};
         ORACLE_PAR_FOR
         for (int k = 0; k < nz; ++k)
             for (int j = 0; j < ny; ++j)
@@ -628,7 +696,6 @@ int oracle3_step(void *handle, double dt, double f_pto_in, oracle3_result *out)
     }
 
     /* (7) pressure increment */
-    double *bx = zal(nu), *by = zal(nv), *bz = zal(nw), *rhs = zal(n), *phi = zal(n);
     ORACLE_PAR_FOR
     for (int k = 0; k < nz; ++k)
         for (int j = 0; j < ny; ++j)
@@ -647,11 +714,10 @@ int oracle3_step(void *handle, double dt, double f_pto_in, oracle3_result *out)
             for (int i = 0; i < nx; ++i)
                 rhs[CI(i, j, k)] = -h * (((ua[UI(i + 1, j, k)] - ua[UI(i, j, k)]) + (va[VI(i, j + 1, k)] - va[VI(i, j, k)])) +
                                          (wa[WI(i, j, k + 1)] - wa[WI(i, j, k)]));
-    int iters = 0;
-    double relres = 0.0;
-    int st = oracle3_poisson_solve(nx, ny, nz, bx, by, bz, rhs, phi, T->P.rtol, T->P.max_iters, T->P.restart,
-                                   T->P.mg_pre, T->P.mg_post, &iters, &relres);
-    double bn = 0.0;
+    memset(phi, 0, n * sizeof(double));
+    st = oracle3_poisson_solve(nx, ny, nz, bx, by, bz, rhs, phi, T->P.rtol, T->P.max_iters, T->P.restart,
+                               T->P.mg_pre, T->P.mg_post, &iters, &relres);
+    bn = 0.0;
     for (size_t c = 0; c < n; ++c) bn += rhs[c] * rhs[c];
 
     /* (8) projection */
@@ -686,9 +752,10 @@ int oracle3_step(void *handle, double dt, double f_pto_in, oracle3_result *out)
     ORACLE_PAR_FOR
     for (size_t c = 0; c < n; ++c) T->p[c] += phi[c];
     memcpy(T->sig, sig1, n * sizeof(double));
-    T->t = t1;
     T->zc = zc1;
-    T->zdot_prev = T->zdot;
+    } /* cycles */
+    T->t = t1;
+    T->zdot_prev = zd_n;
     T->zdot = zd1;
 
     /* diagnostics: ||h div u||_2; eta at the probe column (x = probe_x, middle y) */
@@ -720,7 +787,8 @@ int oracle3_step(void *handle, double dt, double f_pto_in, oracle3_result *out)
         out->iters = iters;
     }
     double *fr[] = {rho_n, mu_n, rf_n, chi_n, mu_1, rf_1, chi_1, rho_1, Ru, Rv, Rw, Du, Dv, Dw,
-                    ua, va, wa, ub, vb, wb, bx, by, bz, rhs, phi, sig1};
+                    ua, va, wa, ub, vb, wb, bx, by, bz, rhs, phi, sig1,
+                    keep[0], keep[1], keep[2], keep[3], sh, uh, vh, wh, mk[0], mk[1], mk[2], mk[3]};
     for (size_t q = 0; q < sizeof(fr) / sizeof(fr[0]); ++q) free(fr[q]);
     return st;
 }
@@ -845,7 +913,7 @@ double oracle3_force(void *handle)
     size_t n = (size_t)NX * NY * NZ;
     double *rho = zal(n), *mu = zal(n), *rf = zal(n), *chi = zal(n);
     oracle3_materials(&T->P.L, T->sig, T->zc, rho, mu, rf, chi);
-    double F = force3(T, mu);
+    double F = force3(T, mu, T->t);
     free(rho);
     free(mu);
     free(rf);

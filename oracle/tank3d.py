@@ -18,7 +18,7 @@ class Params3(C.Structure):
     _fields_ = [("L", _ls.Tank3), ("g", C.c_double), ("kappa_p", C.c_double), ("added_mass", C.c_double),
                 ("pto_damping", C.c_double), ("probe_x", C.c_double), ("lz", C.c_double), ("rtol", C.c_double),
                 ("max_iters", C.c_int), ("restart", C.c_int), ("n_reinit", C.c_int), ("n_jacobi", C.c_int),
-                ("mg_pre", C.c_int), ("mg_post", C.c_int)]
+                ("mg_pre", C.c_int), ("mg_post", C.c_int), ("n_cycles", C.c_int)]
 
 
 class Result3(C.Structure):
@@ -67,6 +67,7 @@ class OracleTank3:
         P.probe_x, P.lz, P.rtol = cfg["probe_x"], cfg["lz"], s["rtol"]
         P.max_iters, P.restart, P.n_reinit, P.n_jacobi = s["max_iters"], s["restart"], s["n_reinit"], s["n_jacobi"]
         P.mg_pre, P.mg_post = s["mg_pre"], s["mg_post"]
+        P.n_cycles = s.get("n_cycles", 1)
         self._P = P
         nx, ny, nz = cfg["nx"], cfg["ny"], cfg["nz"]
         self.shapes = {F_SIGMA: (nz, ny, nx), F_U: (nz, ny, nx + 1), F_V: (nz, ny + 1, nx), F_W: (nz + 1, ny, nx),
