@@ -99,11 +99,17 @@ enum { WEC_PREC_FP64 = 0, WEC_PREC_MIXED = 1, WEC_PREC_MIXED_MG = 2, WEC_PREC_MI
  * rtol: relative FP64 residual ||b - A x||_2 <= rtol ||b||_2 of each solve.
  * restart: FGMRES restart length m (1..32).  n_reinit: Sussman pseudo-steps per
  * step.  n_jacobi: Jacobi sweeps of the Crank-Nicolson momentum system.
- * mg_pre / mg_post: red-black Gauss-Seidel sweeps before / after coarse correction. */
+ * mg_pre / mg_post: red-black Gauss-Seidel sweeps before / after coarse correction.
+ * n_cycles (section "Time stepping scheme"): cycles k = 0 .. n_cycles - 1 per step,
+ * each taking the heave force from the iterate (p, u, z)^{n+1,k}, the heave update
+ * from level n, sigma^n advected with the means of levels n and n+1,k, and level
+ * n's momentum system with the iterate's pressure and body velocity; built for the
+ * 3D tank (at most 8); the 2D tank and the Poisson objects take only one. */
 typedef struct {
     int precision;
     double rtol;
     int max_iters, restart, n_reinit, n_jacobi, mg_pre, mg_post;
+    int n_cycles;  /* fixed-point cycles per step (3D tank; 0 or 1: one cycle, the plain step) */
 } wec_solver_opts;
 
 /* Record of one step.  z: heave displacement from the initial position;

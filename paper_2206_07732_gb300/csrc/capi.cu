@@ -43,6 +43,7 @@ static int check_opts(const wec_solver_opts *o)
     if (o->restart < 1 || o->restart > kMaxRestart) return fail(WEC_ERR_INVALID, "restart must be in 1..32");
     if (o->n_reinit < 0 || o->n_jacobi < 1 || o->mg_pre < 1 || o->mg_post < 0 || o->mg_pre > 4 || o->mg_post > 4)
         return fail(WEC_ERR_INVALID, "need n_reinit >= 0, n_jacobi >= 1, 1 <= mg_pre <= 4, 0 <= mg_post <= 4");
+    if (o->n_cycles > 1) return fail(WEC_ERR_INVALID, "n_cycles > 1 is built for the 3D tank (wec_tank3) only");
     return WEC_OK;
 }
 

@@ -37,7 +37,8 @@ struct df64 {
     // constants folded at compile time; at run time two conversions and a
     // subtraction on the FP64 pipe)
     __host__ __device__ constexpr df64(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
-    __host__ __device__ constexpr explicit df64(int i) : df64((double)i) {}
+    // from an int: exact for |i| < 2^24 (grid indices), on the FP32 pipe
+    __host__ __device__ constexpr explicit df64(int i) : hi((float)i), lo(0.f) {}
     __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
 };
 

@@ -70,7 +70,9 @@ struct Work3 {
     R *E[3] = {};        // edge viscosities (xy, xz, yz) of the viscosity the current kernels read
     R *RF[3] = {};       // face densities of rho^n at the u-, v-, w-faces
     R *Q[3] = {};        // Jacobi factor (1/2 h^-2) / (D + L / (2 h^2)) per solved face
-    R *bc = nullptr;     // u_in(t1) [nz], w_in(t0) [nz+1], w_in(t1) [nz+1], vorticity damping [nz], [nz+1]
+    R *sh = nullptr, *uh[3] = {};  // n_cycles > 1: the means of levels n and n+1,k (sigma; u, v, w)
+    R *bc = nullptr;     // u_in(t1) [nz], w_in(t0) [nz+1], w_in(t1) [nz+1], vorticity damping [nz], [nz+1],
+                         // mean of w_in(t0) and w_in(t1) [nz+1]
     R *dampu = nullptr;  // damping weight of the u-faces [nx+1]
 };
 
@@ -90,6 +92,8 @@ struct wec_tank3 {
     double *mu1 = nullptr, *rf1 = nullptr, *chi1 = nullptr;
     double *D[3] = {}, *R[3] = {}, *A[3] = {}, *B[3] = {};  // per component u, v, w
     double *E[3] = {}, *RF[3] = {}, *Q[3] = {};             // as Work3: edge viscosities, face densities, Jacobi factors
+    double *sh = nullptr, *uh[3] = {};                      // as Work3 (FP64 stencils, n_cycles > 1)
+    double *uk[3] = {}, *muk = nullptr;                     // n_cycles > 1: the iterate u^{n+1,k}; its force's mu
     double *bc = nullptr;    // [nz] u_in(t1) at the cell layers; [nz+1] w_in(t0), w_in(t1) at the faces
     double *tabs = nullptr;  // damping weight of the u-faces [nx+1]; vorticity damping at cell / face heights
     double *part = nullptr;  // reduction partials
@@ -320,10 +324,13 @@ __global__ void __launch_bounds__(128) k3t_materials(Tank3P P, const R *__restri
     chi[q.c] = R(1) - hb;
 }
 
+// out = base - dt Q(u, s), then the damping-zone blend (base = s for the plain
+// update; a fixed-point cycle k >= 1 passes sigma^n as base and the means of
+// levels n and n+1,k as s and u)
 template <typename R>
-__global__ void __launch_bounds__(128) k3t_advect(Tank3P P, const R *__restrict__ s, const R *__restrict__ u,
-                                                  const R *__restrict__ v, const R *__restrict__ w, double dt,
-                                                  Ghost3 G, R *__restrict__ out)
+__global__ void __launch_bounds__(128) k3t_advect(Tank3P P, const R *__restrict__ base, const R *__restrict__ s,
+                                                  const R *__restrict__ u, const R *__restrict__ v,
+                                                  const R *__restrict__ w, double dt, Ghost3 G, R *__restrict__ out)
 {
     pdl_entry();
     Cell3 q;
@@ -332,31 +339,39 @@ __global__ void __launch_bounds__(128) k3t_advect(Tank3P P, const R *__restrict_
     const int nx = P.nx, ny = P.ny, i = q.i, j = q.j, k = q.k;
     const long long r = (long long)k * ny + j, fu = r * (nx + 1) + i, fv = ((long long)k * (ny + 1) + j) * nx + i;
     const long long pl = (long long)nx * ny;
-    const R h = K.h, ih = K.ih, dtih = R(dt) * ih;
-    R a[6], fx[2], fy[2], fz[2];
+    const R ih = K.ih, dtih = R(dt) * ih;
     // cells three or more from every boundary read their stencils at fixed
-    // offsets (no ghosts, 32-bit indices); the others through sig3
+    // offsets (no ghosts, 32-bit indices); the others through sig3.  The
+    // directions and the two faces are loops, not unrolled: one copy of the
+    // PPM face code (the float-pair instantiation unrolled six times overflowed
+    // the instruction cache)
     const bool inner = i >= 3 && i < nx - 3 && j >= 3 && j < ny - 3 && k >= 3 && k < P.nz - 3;
-    const int c32 = (int)q.c, sy = nx, sz = nx * ny;
+    const int c32 = (int)q.c;
+    R Q = R(0);
+#pragma unroll 1
+    for (int d = 0; d < 3; ++d) {
+        const int di = d == 0, dj = d == 1, dk = d == 2;
+        const int sd = d == 0 ? 1 : d == 1 ? nx : nx * ny;  // cell stride along d
+        const R *vel = d == 0 ? u + fu : d == 1 ? v + fv : w + q.c;
+        const long long vs = d == 0 ? 1 : d == 1 ? nx : pl;  // face stride along d
+        R F0 = R(0), F1 = R(0);
+#pragma unroll 1
+        for (int f = 0; f < 2; ++f) {
+            R a[6];
 #pragma unroll
-    for (int f = 0; f < 2; ++f) {
-#pragma unroll
-        for (int m = 0; m < 6; ++m) a[m] = inner ? s[c32 + (f - 3 + m)] : sig3<R>(P, s, i + f - 3 + m, j, k, G);
-        fx[f] = ppm_face3<R>(a, u[fu + f], dtih);
-#pragma unroll
-        for (int m = 0; m < 6; ++m) a[m] = inner ? s[c32 + (f - 3 + m) * sy] : sig3<R>(P, s, i, j + f - 3 + m, k, G);
-        fy[f] = ppm_face3<R>(a, v[fv + f * nx], dtih);
-#pragma unroll
-        for (int m = 0; m < 6; ++m) a[m] = inner ? s[c32 + (f - 3 + m) * sz] : sig3<R>(P, s, i, j, k + f - 3 + m, G);
-        fz[f] = ppm_face3<R>(a, w[q.c + f * pl], dtih);
+            for (int m = 0; m < 6; ++m) {
+                const int o = f - 3 + m;
+                a[m] = inner ? s[c32 + o * sd] : sig3<R>(P, s, i + o * di, j + o * dj, k + o * dk, G);
+            }
+            const R fv2 = ppm_face3<R>(a, vel[f * vs], dtih);
+            if (f == 0) F0 = fv2; else F1 = fv2;
+        }
+        const R vb = R(0.5) * (vel[0] + vel[vs]);
+        Q = Q + vb * (F1 - F0) * ih;
     }
-    const R ub = R(0.5) * (u[fu] + u[fu + 1]);
-    const R vb = R(0.5) * (v[fv] + v[fv + nx]);
-    const R wb = R(0.5) * (w[q.c] + w[q.c + pl]);
-    const R Q = ub * (fx[1] - fx[0]) * ih + vb * (fy[1] - fy[0]) * ih + wb * (fz[1] - fz[0]) * ih;
-    const R sa = s[q.c] - R(dt) * Q;
+    const R sa = base[q.c] - R(dt) * Q;
     const R al = dampc<R>(P, i);
-    out[q.c] = (R(1) - al) * sa + al * ((R(k) + R(0.5)) * h - K.depth);
+    out[q.c] = (R(1) - al) * sa + al * ((R(k) + R(0.5)) * K.h - K.depth);
 }
 
 template <typename R>
@@ -770,8 +785,9 @@ struct MomIn {
     const R *rfc[3];                       // face densities of rho^n (u-, v-, w-faces)
     const R *mu_n, *chi1, *rf1;
     Edges3<R> E;                           // edge viscosities of mu^n
-    const double *p;                       // p^{n-1/2} (FP64: its differences are taken before rounding)
-    Vel3<R> V;                             // u^n, v^n, w^n with w_in(t^n)
+    const double *p;                       // p^{n+1/2,k} (FP64: its differences are taken before rounding)
+    Vel3<R> V;                             // the advecting velocity: u^n (cycle 0) or the mean of n and n+1,k
+    Vel3<R> Vn;                            // u^n, v^n, w^n with w_in(t^n): the explicit half of the system
     const R *dampu, *vortc, *vortf;        // damping weight at u-faces; vorticity damping at cell / face heights
     R dt, idt, dtih, ih2, zd1, g, ikp;
 };
@@ -791,8 +807,8 @@ __device__ __forceinline__ void momentum_at(const Tank3P &P, const MomIn<R> &M, 
     R rb, C;
     transport3<IN, R>(P, M.rfc[comp], M.V, comp, i, j, k, M.dtih, rb, C);
     R S, Lc;
-    offdiag3<IN, R>(P, M.mu_n, M.E, M.V, comp, i, j, k, S, Lc);
-    const R uc = comp == 0 ? M.V.u[f] : comp == 1 ? M.V.v[f] : M.V.w[f];
+    offdiag3<IN, R>(P, M.mu_n, M.E, M.Vn, comp, i, j, k, S, Lc);
+    const R uc = comp == 0 ? M.Vn.u[f] : comp == 1 ? M.Vn.v[f] : M.Vn.w[f];
     const R visc = (S - Lc * uc) * M.ih2;
     const double ih = P.ih;
     const int ci = comp == 0 ? i - 1 : i, cj = comp == 1 ? j - 1 : j, ck = comp == 2 ? k - 1 : k;
@@ -989,6 +1005,14 @@ __global__ void k3t_widen(long long n, const R *__restrict__ in, double *__restr
     pdl_entry();
     const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (c < n) out[c] = double(in[c]);
+}
+// the mean of two time levels: out = (a + b) / 2 (b in the working type or FP64)
+template <typename R, typename RB>
+__global__ void k3t_mean(long long n, const R *__restrict__ a, const RB *__restrict__ b, R *__restrict__ out)
+{
+    pdl_entry();
+    const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c < n) out[c] = R(0.5) * (a[c] + R(b[c]));
 }
 
 constexpr int kRT = 256;  // threads of the reduction kernels
@@ -1226,7 +1250,7 @@ static int tank3_step_impl(wec_tank3 *T, Work3<R> &W, double dt, double pto_forc
     const double h = P.h, t0 = T->t, t1 = T->t + dt;
     // boundary data of this step (host): u_in(t1) at the cell layers, w_in(t0)
     // and w_in(t1) at the face heights, vorticity damping at cell / face heights
-    std::vector<double> hb((size_t)5 * nz + 3);
+    std::vector<double> hb((size_t)6 * nz + 4);
     const std::vector<double> &hw = T->hwave;
     const Waves3 Wv{P.ncomp, hw.data(), hw.data() + P.ncomp, hw.data() + 2 * P.ncomp, hw.data() + 3 * P.ncomp};
     double *uin1 = hb.data(), *win0 = uin1 + nz, *win1 = win0 + nz + 1, *vc = win1 + nz + 1, *vf = vc + nz;
@@ -1250,6 +1274,8 @@ static int tank3_step_impl(wec_tank3 *T, Work3<R> &W, double dt, double pto_forc
     };
     for (int k = 0; k < nz; ++k) vc[k] = vort((k + 0.5) * h);
     for (int k = 0; k <= nz; ++k) vf[k] = vort(k * h);
+    double *wmean = vf + nz + 1;  // the ghost of w at the mean of the two time levels
+    for (int k = 0; k <= nz; ++k) wmean[k] = 0.5 * (win0[k] + win1[k]);
     WEC_CK(cudaMemcpyAsync(T->bc, hb.data(), hb.size() * 8, cudaMemcpyHostToDevice, st));
     std::vector<R> hbf;
     if constexpr (f32) {
@@ -1269,21 +1295,34 @@ static int tank3_step_impl(wec_tank3 *T, Work3<R> &W, double dt, double pto_forc
         launch_k(k3t_narrow<R>, nblk((long long)T->nw, 256), 256, 0, st, (long long)T->nw, (const double *)T->w, W.w);
     }
 
-    // (1) materials at n (FP64, for the force) and the heave force from
-    // p^{n-1/2}, u^n (Eq. int_fh) over a box of cells around the cylinder
-    double F = 0.0;
-    const int kcb = (int)(T->zc / h), mkb = (int)std::ceil(0.5 * P.blen / h) + 3;
-    const bool force_box = P.has_body && std::min(nz, kcb + mkb + 1) > std::max(0, kcb - mkb);
-    const int fk0 = std::max(0, kcb - mkb), fk1 = std::min(nz, kcb + mkb + 1);
+    // Fixed-point cycles k = 0 .. n_cycles - 1 (section "Time stepping scheme"):
+    // the iterate (sigma, u, p, z)^{n+1,k} starts from time level n (k = 0:
+    // sigma^n, u^n, p^{n-1/2}, the body at z^n); cycle k takes the force from
+    // it, the heave from level n, advects sigma^n with the means of levels n
+    // and n+1,k, and solves level n's momentum system with the iterate's
+    // pressure and body velocity.  One cycle is the plain step.  Between
+    // cycles the iterate's sigma is in W.tmp, its velocity in T->uk (FP64), its
+    // pressure in T->p; the last cycle's projection writes T->u.
+    const int ncyc = T->opts.n_cycles > 1 ? T->opts.n_cycles : 1;
+    const double fpto = pto_force - T->pto_c * T->zdot;
+    const double zc_n = T->zc, zd_n = T->zdot, zd_prev = T->zdot_prev;
+    double F = 0.0, zd1 = zd_n, zc1 = zc_n, relres = 0.0;
+    int iters = 0, rc = WEC_OK;
+    const dim3 gcorner((nx + 1 + 127) / 128, ny + 1, nz + 1);
+    const double b = sizeof(R);
+    const dim3 gu((nx - 1 + 127) / 128, ny, nz), gv((nx + 127) / 128, ny - 1 > 0 ? ny - 1 : 1, nz),
+        gw((nx + 127) / 128, ny, nz);
+    const dim3 gc[3] = {gu, gv, gw};
+    const size_t nf[3] = {T->nu, T->nv, T->nw};
+    const R *r_whalf = r_vf + nz + 1;
+    const Ghost3 G0 = ghost_at(T, t0), G1 = ghost_at(T, t1);
+    Ghost3 Gh;  // the ghost of the mean of sigma^n and sigma^{n+1,k}
+    for (int m = 0; m < 3; ++m) Gh.e[m] = 0.5 * (G0.e[m] + G1.e[m]);
+    wec_poisson *S = T->solver;
+    double *beta[3] = {S->L64[0].bu, S->L64[0].bv, S->L64[0].bw};
+
+    // materials at level n: the stencils' (W.rho, W.mu) and, FP64, the force's
     if constexpr (f32) {
-        // the stencils read FP32 materials; the FP64 ones are needed by the
-        // force only: the box's cell layers and the layer below it
-        if (force_box) {
-            const int s0 = std::max(0, fk0 - 1);
-            WEC_PROF("tank3_materials", 0, 40.0 * T->nc * (fk1 - s0) / nz, st);
-            launch_k(k3t_materials<double>, dim3((nx + 127) / 128, ny, fk1 - s0), 128, 0, st, P,
-                     (const double *)T->sig, T->zc, T->rho, T->mu, T->rhof, T->chi, s0);
-        }
         WEC_PROF("tank3_materials", 0, 20.0 * T->nc, st);
         launch_k(k3t_materials<R>, grid3(P), 128, 0, st, P, (const R *)W.sig, T->zc, W.rho, W.mu, W.rf, W.chi, 0);
     } else {
@@ -1291,120 +1330,161 @@ static int tank3_step_impl(wec_tank3 *T, Work3<R> &W, double dt, double pto_forc
         launch_k(k3t_materials<double>, grid3(P), 128, 0, st, P, (const double *)T->sig, T->zc, T->rho, T->mu,
                  T->rhof, T->chi, 0);
     }
-    if (force_box) {
-        const int mi = (int)std::ceil((P.br) / h) + 3;
-        const int ic = (int)(P.bxc / h), jc = (int)(P.byc / h);
-        const int i0 = std::max(0, ic - mi), i1 = std::min(nx, ic + mi + 1), j0 = std::max(0, jc - mi),
-                  j1 = std::min(ny, jc + mi + 1), k0 = fk0, k1 = fk1;
-        const Vel3<double> Vn{T->u, T->v, T->w, d_win0};
-        {
-            WEC_PROF("tank3_force", 0, 0.0, st);
-            launch_k(k3t_force, dim3(k1 - k0, 3), kRT, 0, st, P, (const double *)T->p, (const double *)T->mu, Vn,
-                     T->zc, i0, i1, j0, j1, k0, k1, T->part);
+    for (int cyc = 0; cyc < ncyc; ++cyc) {
+        // (1) the heave force (Eq. int_fh) from p^{n+1/2,k}, u^{n+1,k} over a box
+        // of cells around the cylinder at z^{n+1,k}
+        const double zck = T->zc;
+        const int kcb = (int)(zck / h), mkb = (int)std::ceil(0.5 * P.blen / h) + 3;
+        const bool force_box = P.has_body && std::min(nz, kcb + mkb + 1) > std::max(0, kcb - mkb);
+        const int fk0 = std::max(0, kcb - mkb), fk1 = std::min(nz, kcb + mkb + 1), sk0 = std::max(0, fk0 - 1);
+        const double *fmu = T->mu;  // FP64 viscosity of the force integral
+        if (force_box && cyc == 0 && f32) {
+            // the stencils read materials in their own type; the FP64 ones are
+            // needed by the force only: the box's cell layers and the layer below
+            WEC_PROF("tank3_materials", 0, 40.0 * T->nc * (fk1 - sk0) / nz, st);
+            launch_k(k3t_materials<double>, dim3((nx + 127) / 128, ny, fk1 - sk0), 128, 0, st, P,
+                     (const double *)T->sig, zck, T->rho, T->mu, T->rhof, T->chi, sk0);
         }
-        launch_k(k3t_sum, 1, kRT, 0, st, (const double *)T->part, 3 * (k1 - k0), T->part + 3 * nz + 1024);
-        WEC_CK(cudaMemcpyAsync(&F, T->part + 3 * nz + 1024, 8, cudaMemcpyDeviceToHost, st));
-        WEC_CK(cudaStreamSynchronize(st));
-    }
-    // (2) heave (the stabilised update of the 2D reading)
-    const double fpto = pto_force - T->pto_c * T->zdot;
-    double zd1 = T->zdot, zc1 = T->zc;
-    if (P.has_body) {
-        const double m = T->mass, ma = T->added_mass;
-        zd1 = T->zdot + (dt * (F - m * T->g + fpto) + ma * (T->zdot - T->zdot_prev)) / (m + ma);
-        zc1 = T->zc + 0.5 * dt * (T->zdot + zd1);
-    }
-    // (3) sigma: advection + damping zone, reinitialisation (ghosts at t0, t1)
-    {
-        WEC_PROF("tank3_advect", 0, sizeof(R) * (2.0 * T->nc + T->nu + T->nv + T->nw), st);
-        launch_k(k3t_advect<R>, grid3(P), 128, 0, st, P, (const R *)W.sig, (const R *)W.u, (const R *)W.v,
-                 (const R *)W.w, dt, ghost_at(T, t0), W.tmp);
-    }
-    if (int e = reinit_buf<R>(T, W.tmp, W.s0, W.s1, T->opts.n_reinit, t1)) return e;
-    // (4) materials at n+1 (rho^{n+1} itself is not used: s1 is scratch)
-    {
-        WEC_PROF("tank3_materials", 0, 5.0 * sizeof(R) * T->nc, st);
-        launch_k(k3t_materials<R>, grid3(P), 128, 0, st, P, (const R *)W.tmp, zc1, W.s1, W.mu1, W.rf1, W.chi1, 0);
-    }
-    // (5) transport and the momentum system: face densities of rho^n and edge
-    // viscosities of mu^n, then one kernel per component
-    const dim3 gcorner((nx + 1 + 127) / 128, ny + 1, nz + 1);
-    const double b = sizeof(R);
-    {
-        WEC_PROF("tank3_faces_edges", 0, b * (T->nc + T->nu + T->nv + T->nw), st);
-        launch_k(k3t_face_rho<R>, gcorner, 128, 0, st, P, (const R *)W.rho, W.RF[0], W.RF[1], W.RF[2]);
-    }
-    {
-        WEC_PROF("tank3_faces_edges", 0, b * 4.0 * T->nc, st);
-        launch_k(k3t_edges<R>, gcorner, 128, 0, st, P, (const R *)W.mu, W.E[0], W.E[1], W.E[2]);
-    }
-    const Edges3<R> E{W.E[0], W.E[1], W.E[2]};
-    MomIn<R> M{{W.RF[0], W.RF[1], W.RF[2]}, W.mu, W.chi1, W.rf1, E, T->p, Vel3<R>{W.u, W.v, W.w, r_win0}, W.dampu,
-               r_vc, r_vf, R(dt), R(1.0 / dt), R(dt / h), R(1.0 / (h * h)), R(zd1), R(T->g), R(1.0 / T->kappa_p)};
-    const dim3 gu((nx - 1 + 127) / 128, ny, nz), gv((nx + 127) / 128, ny - 1 > 0 ? ny - 1 : 1, nz),
-        gw((nx + 127) / 128, ny, nz);
-    const dim3 gc[3] = {gu, gv, gw};
-    const size_t nf[3] = {T->nu, T->nv, T->nw};
-    for (int c = 0; c < 3; ++c) {
-        if (c == 1 && ny < 2) continue;
-        // face density, mu, two edge arrays, chi (+ rho^flow for w), p, u, v, w in; D, R out
-        WEC_PROF("tank3_momentum", c,
-                 b * (nf[c] + (c == 2 ? 5.0 : 4.0) * T->nc + T->nu + T->nv + T->nw + 2.0 * nf[c]) + 8.0 * T->nc, st);
-        auto kern = c == 0 ? k3t_momentum<0, R> : c == 1 ? k3t_momentum<1, R> : k3t_momentum<2, R>;
-        launch_k(kern, gc[c], 128, 0, st, P, M, W.D[c], W.R3[c]);
-    }
-    // (6) Crank-Nicolson Jacobi sweeps from u^n with the Dirichlet faces at n+1:
-    // edge viscosities of mu^{n+1}, the per-face factors, then the sweeps
-    {
-        WEC_PROF("tank3_faces_edges", 0, b * 4.0 * T->nc, st);
-        launch_k(k3t_edges<R>, gcorner, 128, 0, st, P, (const R *)W.mu1, W.E[0], W.E[1], W.E[2]);
-    }
-    for (int c = 0; c < 3; ++c) {
-        if (c == 1 && ny < 2) continue;
-        WEC_PROF("tank3_jprep", c, b * (3.0 * T->nc + 4.0 * nf[c]), st);
-        auto kern = c == 0 ? k3t_jprep<0, R> : c == 1 ? k3t_jprep<1, R> : k3t_jprep<2, R>;
-        launch_k(kern, gc[c], 128, 0, st, P, (const R *)W.mu1, E, (const R *)W.D[c], W.R3[c], W.Q[c],
-                 R(1.0 / (h * h)));
-    }
-    R *src[3] = {W.u, W.v, W.w};
-    for (int c = 0; c < 3; ++c) WEC_CK(cudaMemcpyAsync(W.A[c], src[c], nf[c] * sizeof(R), cudaMemcpyDeviceToDevice, st));
-    {
-        const long long nd = std::max({(long long)ny * nz, (long long)nx * nz, (long long)nx * ny});
-        launch_k(k3t_dirichlet<R>, nblk(nd, 256), 256, 0, st, P, r_uin1, W.A[0], W.A[1], W.A[2]);
-    }
-    for (int c = 0; c < 3; ++c) WEC_CK(cudaMemcpyAsync(W.B[c], W.A[c], nf[c] * sizeof(R), cudaMemcpyDeviceToDevice, st));
-    for (int it = 0; it < T->opts.n_jacobi; ++it) {
-        const Vel3<R> Va{W.A[0], W.A[1], W.A[2], r_win1};
+        if (force_box && cyc > 0) {
+            // materials of the iterate (sigma^{n+1,k} in FP64 in T->tmp) on the force layers
+            if constexpr (f32)
+                launch_k(k3t_widen<R>, nblk((long long)T->nc, 256), 256, 0, st, (long long)T->nc, (const R *)W.tmp,
+                         T->tmp);
+            WEC_PROF("tank3_materials", 0, 40.0 * T->nc * (fk1 - sk0) / nz, st);
+            launch_k(k3t_materials<double>, dim3((nx + 127) / 128, ny, fk1 - sk0), 128, 0, st, P,
+                     (const double *)T->tmp, zck, T->s0, T->muk, T->s1, T->phi, sk0);
+            fmu = T->muk;
+        }
+        if (force_box) {
+            const int mi = (int)std::ceil((P.br) / h) + 3;
+            const int ic = (int)(P.bxc / h), jc = (int)(P.byc / h);
+            const int i0 = std::max(0, ic - mi), i1 = std::min(nx, ic + mi + 1), j0 = std::max(0, jc - mi),
+                      j1 = std::min(ny, jc + mi + 1), k0 = fk0, k1 = fk1;
+            const Vel3<double> Vk = cyc == 0 ? Vel3<double>{T->u, T->v, T->w, d_win0}
+                                             : Vel3<double>{T->uk[0], T->uk[1], T->uk[2], d_win1};
+            {
+                WEC_PROF("tank3_force", 0, 0.0, st);
+                launch_k(k3t_force, dim3(k1 - k0, 3), kRT, 0, st, P, (const double *)T->p, fmu, Vk, zck, i0, i1, j0,
+                         j1, k0, k1, T->part);
+            }
+            launch_k(k3t_sum, 1, kRT, 0, st, (const double *)T->part, 3 * (k1 - k0), T->part + 3 * nz + 1024);
+            WEC_CK(cudaMemcpyAsync(&F, T->part + 3 * nz + 1024, 8, cudaMemcpyDeviceToHost, st));
+            WEC_CK(cudaStreamSynchronize(st));
+        }
+        // (2) heave from level n (the stabilised update of the 2D reading)
+        zd1 = zd_n;
+        zc1 = zc_n;
+        if (P.has_body) {
+            const double m = T->mass, ma = T->added_mass;
+            zd1 = zd_n + (dt * (F - m * T->g + fpto) + ma * (zd_n - zd_prev)) / (m + ma);
+            zc1 = zc_n + 0.5 * dt * (zd_n + zd1);
+        }
+        // (3) sigma: sigma^n advected with u^{n+1/2,k}, sigma^{n+1/2,k} (cycle 0:
+        // u^n, sigma^n; ghosts at t0), damping zone, reinitialisation (ghosts at t1)
+        Vel3<R> Vt{W.u, W.v, W.w, r_win0};
+        const R *sadv = W.sig;
+        Ghost3 Ga = G0;
+        if (cyc > 0) {
+            launch_k(k3t_mean<R, R>, nblk((long long)T->nc, 256), 256, 0, st, (long long)T->nc, (const R *)W.sig,
+                     (const R *)W.tmp, W.sh);
+            const R *un[3] = {W.u, W.v, W.w};
+            for (int c = 0; c < 3; ++c)
+                launch_k(k3t_mean<R, double>, nblk((long long)nf[c], 256), 256, 0, st, (long long)nf[c], un[c],
+                         (const double *)T->uk[c], W.uh[c]);
+            Vt = Vel3<R>{W.uh[0], W.uh[1], W.uh[2], r_whalf};
+            sadv = W.sh;
+            Ga = Gh;
+        }
+        {
+            WEC_PROF("tank3_advect", 0, sizeof(R) * (2.0 * T->nc + T->nu + T->nv + T->nw), st);
+            launch_k(k3t_advect<R>, grid3(P), 128, 0, st, P, (const R *)W.sig, sadv, Vt.u, Vt.v, Vt.w, dt, Ga, W.tmp);
+        }
+        if (int e = reinit_buf<R>(T, W.tmp, W.s0, W.s1, T->opts.n_reinit, t1)) return e;
+        // (4) materials at n+1,k+1 (rho itself is not used: s1 is scratch)
+        {
+            WEC_PROF("tank3_materials", 0, 5.0 * sizeof(R) * T->nc, st);
+            launch_k(k3t_materials<R>, grid3(P), 128, 0, st, P, (const R *)W.tmp, zc1, W.s1, W.mu1, W.rf1, W.chi1,
+                     0);
+        }
+        // (5) transport and the momentum system: face densities of rho^n and
+        // edge viscosities of mu^n, then one kernel per component
+        {
+            WEC_PROF("tank3_faces_edges", 0, b * (T->nc + T->nu + T->nv + T->nw), st);
+            launch_k(k3t_face_rho<R>, gcorner, 128, 0, st, P, (const R *)W.rho, W.RF[0], W.RF[1], W.RF[2]);
+        }
+        {
+            WEC_PROF("tank3_faces_edges", 0, b * 4.0 * T->nc, st);
+            launch_k(k3t_edges<R>, gcorner, 128, 0, st, P, (const R *)W.mu, W.E[0], W.E[1], W.E[2]);
+        }
+        const Edges3<R> E{W.E[0], W.E[1], W.E[2]};
+        MomIn<R> M{{W.RF[0], W.RF[1], W.RF[2]}, W.mu, W.chi1, W.rf1, E, T->p, Vt, Vel3<R>{W.u, W.v, W.w, r_win0},
+                   W.dampu, r_vc, r_vf, R(dt), R(1.0 / dt), R(dt / h), R(1.0 / (h * h)), R(zd1), R(T->g),
+                   R(1.0 / T->kappa_p)};
         for (int c = 0; c < 3; ++c) {
             if (c == 1 && ny < 2) continue;
-            // mu, two edge arrays, u, v, w, Rr, Q in; B out
-            WEC_PROF("tank3_jacobi", c, b * (3.0 * T->nc + T->nu + T->nv + T->nw + 3.0 * nf[c]), st);
-            auto kern = c == 0 ? k3t_jacobi<0, R> : c == 1 ? k3t_jacobi<1, R> : k3t_jacobi<2, R>;
-            launch_k(kern, gc[c], 128, 0, st, P, (const R *)W.mu1, E, Va, (const R *)W.R3[c], (const R *)W.Q[c],
-                     W.B[c]);
+            // face density, mu, two edge arrays, chi (+ rho^flow for w), p, u, v, w in; D, R out
+            WEC_PROF("tank3_momentum", c,
+                     b * (nf[c] + (c == 2 ? 5.0 : 4.0) * T->nc + T->nu + T->nv + T->nw + 2.0 * nf[c]) + 8.0 * T->nc,
+                     st);
+            auto kern = c == 0 ? k3t_momentum<0, R> : c == 1 ? k3t_momentum<1, R> : k3t_momentum<2, R>;
+            launch_k(kern, gc[c], 128, 0, st, P, M, W.D[c], W.R3[c]);
         }
-        for (int c = 0; c < 3; ++c) std::swap(W.A[c], W.B[c]);
+        // (6) Crank-Nicolson Jacobi sweeps from u^n with the Dirichlet faces at
+        // n+1: edge viscosities of mu^{n+1}, the per-face factors, then the sweeps
+        {
+            WEC_PROF("tank3_faces_edges", 0, b * 4.0 * T->nc, st);
+            launch_k(k3t_edges<R>, gcorner, 128, 0, st, P, (const R *)W.mu1, W.E[0], W.E[1], W.E[2]);
+        }
+        for (int c = 0; c < 3; ++c) {
+            if (c == 1 && ny < 2) continue;
+            WEC_PROF("tank3_jprep", c, b * (3.0 * T->nc + 4.0 * nf[c]), st);
+            auto kern = c == 0 ? k3t_jprep<0, R> : c == 1 ? k3t_jprep<1, R> : k3t_jprep<2, R>;
+            launch_k(kern, gc[c], 128, 0, st, P, (const R *)W.mu1, E, (const R *)W.D[c], W.R3[c], W.Q[c],
+                     R(1.0 / (h * h)));
+        }
+        R *src[3] = {W.u, W.v, W.w};
+        for (int c = 0; c < 3; ++c)
+            WEC_CK(cudaMemcpyAsync(W.A[c], src[c], nf[c] * sizeof(R), cudaMemcpyDeviceToDevice, st));
+        {
+            const long long nd = std::max({(long long)ny * nz, (long long)nx * nz, (long long)nx * ny});
+            launch_k(k3t_dirichlet<R>, nblk(nd, 256), 256, 0, st, P, r_uin1, W.A[0], W.A[1], W.A[2]);
+        }
+        for (int c = 0; c < 3; ++c)
+            WEC_CK(cudaMemcpyAsync(W.B[c], W.A[c], nf[c] * sizeof(R), cudaMemcpyDeviceToDevice, st));
+        for (int it = 0; it < T->opts.n_jacobi; ++it) {
+            const Vel3<R> Va{W.A[0], W.A[1], W.A[2], r_win1};
+            for (int c = 0; c < 3; ++c) {
+                if (c == 1 && ny < 2) continue;
+                // mu, two edge arrays, u, v, w, Rr, Q in; B out
+                WEC_PROF("tank3_jacobi", c, b * (3.0 * T->nc + T->nu + T->nv + T->nw + 3.0 * nf[c]), st);
+                auto kern = c == 0 ? k3t_jacobi<0, R> : c == 1 ? k3t_jacobi<1, R> : k3t_jacobi<2, R>;
+                launch_k(kern, gc[c], 128, 0, st, P, (const R *)W.mu1, E, Va, (const R *)W.R3[c], (const R *)W.Q[c],
+                         W.B[c]);
+            }
+            for (int c = 0; c < 3; ++c) std::swap(W.A[c], W.B[c]);
+        }
+        // (7) pressure increment: beta = 1 / D, b = -h div u* (FP64), phi from zero
+        for (int c = 0; c < 3; ++c)
+            launch_k(k3t_beta<R>, nblk((long long)nf[c], 256), 256, 0, st, P, c, (const R *)W.D[c], beta[c],
+                     (long long)nf[c]);
+        if (int e = poisson_build(S, st)) return e;
+        launch_k(k3t_rhs<R>, grid3(P), 128, 0, st, P, Vel3<R>{W.A[0], W.A[1], W.A[2], r_win1}, T->rhs);
+        WEC_CK(cudaMemsetAsync(T->phi, 0, T->nc * 8, st));
+        WEC_CK(cudaGetLastError());
+        rc = poisson_solve(S, T->rhs, T->phi, T->opts.rtol, T->opts.max_iters, &iters, &relres);
+        if (rc != WEC_OK && rc != WEC_ERR_NOT_CONVERGED) return rc;
+        // (8) projection (FP64) and p^{n+1/2,k+1} = p^{n+1/2,k} + phi: into the
+        // iterate's velocity, the last cycle into the tank's
+        double *dst[3] = {T->u, T->v, T->w};
+        if (cyc + 1 < ncyc)
+            for (int c = 0; c < 3; ++c) dst[c] = T->uk[c];
+        for (int c = 0; c < 3; ++c)
+            launch_k(k3t_project<R>, nblk((long long)nf[c], 256), 256, 0, st, P, c, (const R *)W.A[c],
+                     (const double *)beta[c], (const double *)T->phi, dst[c], (long long)nf[c]);
+        launch_k(k3t_add, nblk((long long)T->nc, 256), 256, 0, st, (long long)T->nc, (const double *)T->phi, T->p);
+        T->zc = zc1;
     }
-    // (7) pressure increment: beta = 1 / D, b = -h div u* (FP64), phi from zero
-    wec_poisson *S = T->solver;
-    double *beta[3] = {S->L64[0].bu, S->L64[0].bv, S->L64[0].bw};
-    for (int c = 0; c < 3; ++c)
-        launch_k(k3t_beta<R>, nblk((long long)nf[c], 256), 256, 0, st, P, c, (const R *)W.D[c], beta[c],
-                 (long long)nf[c]);
-    if (int e = poisson_build(S, st)) return e;
-    launch_k(k3t_rhs<R>, grid3(P), 128, 0, st, P, Vel3<R>{W.A[0], W.A[1], W.A[2], r_win1}, T->rhs);
-    WEC_CK(cudaMemsetAsync(T->phi, 0, T->nc * 8, st));
-    WEC_CK(cudaGetLastError());
-    int iters = 0;
-    double relres = 0.0;
-    const int rc = poisson_solve(S, T->rhs, T->phi, T->opts.rtol, T->opts.max_iters, &iters, &relres);
-    if (rc != WEC_OK && rc != WEC_ERR_NOT_CONVERGED) return rc;
-    // (8) projection (FP64) and p += phi; sigma^{n+1}
-    double *dst[3] = {T->u, T->v, T->w};
-    for (int c = 0; c < 3; ++c)
-        launch_k(k3t_project<R>, nblk((long long)nf[c], 256), 256, 0, st, P, c, (const R *)W.A[c],
-                 (const double *)beta[c], (const double *)T->phi, dst[c], (long long)nf[c]);
-    launch_k(k3t_add, nblk((long long)T->nc, 256), 256, 0, st, (long long)T->nc, (const double *)T->phi, T->p);
+    // sigma^{n+1}
     if constexpr (f32)
         launch_k(k3t_widen<R>, nblk((long long)T->nc, 256), 256, 0, st, (long long)T->nc, (const R *)W.tmp, T->sig);
     else
@@ -1429,7 +1509,7 @@ static int tank3_step_impl(wec_tank3 *T, Work3<R> &W, double dt, double pto_forc
         }
     T->t = t1;
     T->zc = zc1;
-    T->zdot_prev = T->zdot;
+    T->zdot_prev = zd_n;
     T->zdot = zd1;
     if (out) {
         out->t = T->t;
@@ -1475,6 +1555,8 @@ int wec_tank3_create(const wec_grid3 *grid, const wec_fluids *fl, const wec_wave
             opts->n_reinit < 0 || opts->n_jacobi < 1 || opts->mg_pre < 1 || opts->mg_pre > 4 || opts->mg_post < 0 ||
             opts->mg_post > 4)
             return fail(WEC_ERR_INVALID, "tank3: invalid solver options");
+        if (opts->n_cycles < 0 || opts->n_cycles > 8)
+            return fail(WEC_ERR_INVALID, "tank3: n_cycles must be 0..8 (0 and 1: one cycle)");
     }
     if (int e = [] {
             int n = 0;
@@ -1588,10 +1670,21 @@ int wec_tank3_create(const wec_grid3 *grid, const wec_fluids *fl, const wec_wave
                 if (e == cudaSuccess) e = cudaMalloc(q, nf[c] * 8);
         const size_t ne[3] = {(size_t)nz * (ny + 1) * (nx + 1), (size_t)(nz + 1) * ny * (nx + 1),
                               (size_t)(nz + 1) * (ny + 1) * nx};
-        if (opts->precision == WEC_PREC_FP64 || opts->precision == WEC_PREC_MIXED_MG)
+        const bool f64_stencils = opts->precision == WEC_PREC_FP64 || opts->precision == WEC_PREC_MIXED_MG;
+        if (f64_stencils)
             for (int c = 0; c < 3; ++c)
                 if (e == cudaSuccess) e = cudaMalloc(&T->E[c], ne[c] * 8);
-        if (e == cudaSuccess) e = cudaMalloc(&T->bc, (size_t)(3 * nz + 2 + nz + nz + 1) * 8);
+        if (opts->n_cycles > 1) {  // the iterate's velocity and its force's viscosity (+ FP64 means)
+            for (int c = 0; c < 3; ++c)
+                if (e == cudaSuccess) e = cudaMalloc(&T->uk[c], nf[c] * 8);
+            if (e == cudaSuccess) e = cudaMalloc(&T->muk, T->nc * 8);
+            if (f64_stencils) {
+                if (e == cudaSuccess) e = cudaMalloc(&T->sh, T->nc * 8);
+                for (int c = 0; c < 3; ++c)
+                    if (e == cudaSuccess) e = cudaMalloc(&T->uh[c], nf[c] * 8);
+            }
+        }
+        if (e == cudaSuccess) e = cudaMalloc(&T->bc, (size_t)(6 * nz + 4) * 8);
         if (e == cudaSuccess) e = cudaMalloc(&T->tabs, (size_t)(nx + 1) * 8);
         if (e == cudaSuccess) e = cudaMalloc(&T->part, (size_t)(3 * nz + 1024 + 8) * 8);
         if (e != cudaSuccess) {
@@ -1661,7 +1754,12 @@ int wec_tank3_create(const wec_grid3 *grid, const wec_fluids *fl, const wec_wave
                     if (e == cudaSuccess) e = cudaMalloc(q, nf3[c] * b);
             for (int c = 0; c < 3; ++c)
                 if (e == cudaSuccess) e = cudaMalloc(&F.E[c], ne[c] * b);
-            if (e == cudaSuccess) e = cudaMalloc(&F.bc, (size_t)(5 * nz + 3) * b);
+            if (opts->n_cycles > 1) {  // the means of levels n and n+1,k
+                if (e == cudaSuccess) e = cudaMalloc(&F.sh, T->nc * b);
+                for (int c = 0; c < 3; ++c)
+                    if (e == cudaSuccess) e = cudaMalloc(&F.uh[c], nf3[c] * b);
+            }
+            if (e == cudaSuccess) e = cudaMalloc(&F.bc, (size_t)(6 * nz + 4) * b);
             if (e == cudaSuccess) e = cudaMalloc(&F.dampu, (size_t)(nx + 1) * b);
             std::vector<RW> duw;
             for (double x : du) duw.push_back(RW(x));
@@ -1701,11 +1799,14 @@ void wec_tank3_destroy(wec_tank3 *T)
                       T->p, T->phi, T->rhs, T->mu1, T->rf1, T->chi1, T->bc, T->tabs, T->part})
         cudaFree(p);
     for (int c = 0; c < 3; ++c)
-        for (double *p : {T->D[c], T->R[c], T->A[c], T->B[c], T->E[c], T->RF[c], T->Q[c]}) cudaFree(p);
+        for (double *p : {T->D[c], T->R[c], T->A[c], T->B[c], T->E[c], T->RF[c], T->Q[c], T->uk[c], T->uh[c]})
+            cudaFree(p);
+    cudaFree(T->muk);
+    cudaFree(T->sh);
     auto free_work = [](auto &F) {
         using RW = std::remove_pointer_t<decltype(F.sig)>;
         for (RW *p : std::initializer_list<RW *>{F.sig, F.tmp, F.s0, F.s1, F.u, F.v, F.w, F.rho, F.mu, F.rf, F.chi,
-                                                 F.mu1, F.rf1, F.chi1, F.bc, F.dampu})
+                                                 F.mu1, F.rf1, F.chi1, F.bc, F.dampu, F.sh, F.uh[0], F.uh[1], F.uh[2]})
             cudaFree(p);
         for (int c = 0; c < 3; ++c)
             for (RW *p : std::initializer_list<RW *>{F.D[c], F.R3[c], F.A[c], F.B[c], F.E[c], F.RF[c], F.Q[c]})
@@ -1780,8 +1881,9 @@ int wec_tank3_advect(wec_tank3 *T, double dt, double t)
     if (!(dt >= 0.0)) return fail(WEC_ERR_INVALID, "tank3_advect: dt must be >= 0");
     {
         WEC_PROF("tank3_advect", 0, 8.0 * (2.0 * T->nc + T->nu + T->nv + T->nw), T->st);
-        launch_k(k3t_advect<double>, grid3(T->P), 128, 0, T->st, T->P, (const double *)T->sig, (const double *)T->u,
-                 (const double *)T->v, (const double *)T->w, dt, ghost_at(T, t), T->tmp);
+        launch_k(k3t_advect<double>, grid3(T->P), 128, 0, T->st, T->P, (const double *)T->sig,
+                 (const double *)T->sig, (const double *)T->u, (const double *)T->v, (const double *)T->w, dt,
+                 ghost_at(T, t), T->tmp);
     }
     WEC_CK(cudaGetLastError());
     std::swap(T->sig, T->tmp);
@@ -1822,8 +1924,9 @@ int wec_tank3_step(wec_tank3 *T, double dt, double pto_force, wec_step_result *o
     W.rho = T->rho; W.mu = T->mu; W.rf = T->rhof; W.chi = T->chi; W.mu1 = T->mu1; W.rf1 = T->rf1; W.chi1 = T->chi1;
     for (int c = 0; c < 3; ++c) {
         W.D[c] = T->D[c]; W.R3[c] = T->R[c]; W.A[c] = T->A[c]; W.B[c] = T->B[c];
-        W.E[c] = T->E[c]; W.RF[c] = T->RF[c]; W.Q[c] = T->Q[c];
+        W.E[c] = T->E[c]; W.RF[c] = T->RF[c]; W.Q[c] = T->Q[c]; W.uh[c] = T->uh[c];
     }
+    W.sh = T->sh;
     W.bc = T->bc;
     W.dampu = T->tabs;
     const int rc = tank3_step_impl<double>(T, W, dt, pto_force, out);

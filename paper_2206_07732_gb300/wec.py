@@ -61,7 +61,8 @@ class Body(C.Structure):
 
 class SolverOpts(C.Structure):
     _fields_ = [("precision", C.c_int), ("rtol", C.c_double), ("max_iters", C.c_int), ("restart", C.c_int),
-                ("n_reinit", C.c_int), ("n_jacobi", C.c_int), ("mg_pre", C.c_int), ("mg_post", C.c_int)]
+                ("n_reinit", C.c_int), ("n_jacobi", C.c_int), ("mg_pre", C.c_int), ("mg_post", C.c_int),
+                ("n_cycles", C.c_int)]
 
 
 class StepResult(C.Structure):
@@ -241,6 +242,7 @@ def solver_opts(s, precision=None):
     o.rtol = s["rtol"]
     o.max_iters, o.restart = s["max_iters"], s["restart"]
     o.n_reinit, o.n_jacobi, o.mg_pre, o.mg_post = s["n_reinit"], s["n_jacobi"], s["mg_pre"], s["mg_post"]
+    o.n_cycles = s.get("n_cycles", 1)
     return o
 
 

@@ -73,6 +73,35 @@ def test_steps_match_oracle(shape, body, prec):
 
 
 @pytest.mark.parametrize("prec", [wec.PREC_FP64, wec.PREC_MIXED_DF])
+@pytest.mark.parametrize("ncyc", [2, 3])
+def test_fixed_point_cycles_match_oracle(prec, ncyc):
+    # n_cycles > 1 (section "Time stepping scheme"): force on the iterate, heave
+    # from level n, sigma^n advected with the means of levels n and n+1,k, level
+    # n's momentum system; every field within 1e-10 of the oracle's cycles
+    c = _cfg(40, 12, 20, seed=7)
+    c["solver"]["n_cycles"] = ncyc
+    t, o = wec.Tank3(c, precision=prec), T3.OracleTank3(c)
+    for s in range(3):
+        r, ro = t.step(c["dt"]), o.step(c["dt"])
+        assert r["status"] == 0 and ro["status"] == 0
+        vs = np.max(np.abs(o.get(T3.F_U)))
+        errs = {name: rel(t.get(fg), o.get(fo), vs if name == "v" else 1e-12) for fg, fo, name in FIELDS}
+        print(f"{ncyc} cycles, step {s}: {errs}, F {r['f_hydro']:.6f} / {ro['f_hydro']:.6f}")
+        for name, e in errs.items():
+            assert e < 1e-10, (s, name, e)
+        assert r["f_hydro"] == pytest.approx(ro["f_hydro"], rel=1e-10)
+        assert r["zdot"] == pytest.approx(ro["zdot"], rel=1e-10, abs=1e-14)
+    t.close()
+
+
+def test_cycle_options_are_checked():
+    c = _cfg(16, 8, 8)
+    c["solver"]["n_cycles"] = 9
+    with pytest.raises(wec.WecError):
+        wec.Tank3(c)
+
+
+@pytest.mark.parametrize("prec", [wec.PREC_FP64, wec.PREC_MIXED_DF])
 def test_heave_after_200_steps(prec):
     c = _cfg(32, 8, 16, seed=3, rtol=1e-10)
     t, o = wec.Tank3(c, precision=prec), T3.OracleTank3(c)
