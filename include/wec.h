@@ -512,6 +512,9 @@ int wec_jonswap(double Hs, double Tp, double gamma, int ncomp, double *amp, doub
  * later solvers of the same shape reuse them and compute the same bits.
  * "mg_bottom_shift" (default -1 = autotuned): start the single-CTA kernel this
  * many levels below the smallest admissible one (0..8, capped at the coarsest).
+ * "tank3_split_momentum" (default 1): the 3D momentum system per component as
+ * two kernels (transport terms, then viscous terms and assembly); 0: one
+ * kernel.  Both compute the same values.
  * Options apply to solvers created, graphs captured and solves started after the
  * call.  Unknown name or value out of range: WEC_ERR_INVALID. */
 int wec_set_option(const char *name, int value);

@@ -220,6 +220,10 @@ int wec_set_option(const char *name, int value)
         set_mg_autotune(value != 0);
         return WEC_OK;
     }
+    if (std::string(name) == "tank3_split_momentum") {
+        set_tank3_split_momentum(value != 0);
+        return WEC_OK;
+    }
     if (std::string(name) == "mg_bottom_shift") {
         if (value < -1 || value > 8) return fail(WEC_ERR_INVALID, "mg_bottom_shift must be in -1..8");
         set_mg_bottom_shift(value);
