@@ -58,7 +58,10 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU-baseline sample budget (2D tank)")
-    ap.add_argument("--workload", default="tank3d", choices=["tank3d", "tank", "batch", "poisson3d"])
+    ap.add_argument("--workload", default="tank3d", choices=["tank3d", "tank", "batch", "poisson3d", "learned"])
+    ap.add_argument("--learned-seeds", type=int, default=10, help="learned: training seeds")
+    ap.add_argument("--learned-steps", type=int, default=2000, help="learned: problems per training seed")
+    ap.add_argument("--train-iters", type=int, default=6000, help="learned: Adam steps")
     ap.add_argument("--no-2d", action="store_true", help="tank3d: skip the 2D tank reported beside it")
     ap.add_argument("--steps2d", type=int, default=0, help="tank3d: timed steps of the 2D tank (default 100)")
     ap.add_argument("--detail", default="bench_detail.json",
@@ -935,7 +938,7 @@ def profile_tank3(wec, torch, cfg, precision, steps=1, warmup=1):
     return prof
 
 
-def roofline3(prof, steps, top=None):
+def roofline3(prof, steps, top=None, shape=(512, 256, 256)):
     """The dominant kernel's roofline from an eager profile: achieved =
     algorithmic bytes per launch / mean launch time (multigrid kernels: over
     their finest-level launches, the 33.5 M-cell sweeps; coarser levels are
@@ -951,14 +954,17 @@ def roofline3(prof, steps, top=None):
     peak, kind = peaks()
     ach = b0 / (t0 / 1e3) / 1e9 if t0 > 0 and b0 > 0 else None
     roof = {"bound": "hbm", "kernel": top, "achieved": ach, "peak": peak, "unit": "GB/s",
-            "frac": ach / peak if ach else None, "traffic": ncu_traffic(top + "_3d"),
+            "frac": ach / peak if ach else None,
+            "traffic": ncu_traffic(f"{top}_l0_{shape[0]}x{shape[1]}x{shape[2]}" if any(q["level"] == 0 for q in sel)
+                                   else f"{top}_{shape[0]}x{shape[1]}x{shape[2]}"),
             "peak_source": f"{kind} hbm_gbs (MEASURED_PEAKS.json)",
             "algorithmic_bytes_per_launch": b0 / n0 if n0 else None,
             "avg_launch_us": t0 / n0 * 1e3 if n0 else None, "launches_timed": n0,
             "share_of_step_gpu_time": by[top]["ms"] / tot if tot else None}
     breakdown = [{"kernel": k, "launches_per_step": v["launches"] / steps, "ms_per_step": v["ms"] / steps,
                   "share": v["ms"] / tot,
-                  "GBps": v["bytes"] / (v["ms"] / 1e3) / 1e9 if v["ms"] > 0 and v["bytes"] > 0 else None}
+                  "GBps": v["bytes"] / (v["ms"] / 1e3) / 1e9 if v["ms"] > 0 and v["bytes"] > 0 else None,
+                  "hbm_frac": v["bytes"] / (v["ms"] / 1e3) / 1e9 / peak if v["ms"] > 0 and v["bytes"] > 0 else None}
                  for k, v in sorted(by.items(), key=lambda kv: -kv[1]["ms"])]
     return roof, breakdown
 
@@ -1111,6 +1117,91 @@ def main_tank3d(args):
         torch.distributed.destroy_process_group()
 
 
+def main_learned(args):
+    """Configuration 4: the U-Net warm start trained on pressure problems that
+    the method itself generates -- runs of the 512 x 256 tank with the
+    configuration-2 physics and seeded sea states (synth.tank_learned), 2000
+    steps from each of ten seeds (20k problems, FP32 features and targets held
+    on the device) -- then evaluated on held-out seeds against plain multigrid
+    by FGMRES iterations and time per step to the 1e-8 FP64 residual (the
+    network's inference included), mixed precision (FP32 V-cycles, FP64 and
+    FP32 stencils)."""
+    torch, rank, world, local = dist_setup()
+    L, wec = setup_lib()
+    from paper_2206_07732_gb300 import synth
+    ny, nx = 256, 512
+    nseeds, per, skip = args.learned_seeds, args.learned_steps, 40
+    seeds = [args.seed + 100 + k for k in range(nseeds)]
+    N = nseeds * per
+    xs = torch.zeros((N, ny, nx, 2), dtype=torch.float32, device="cuda")
+    ts = torch.zeros((N, ny, nx), dtype=torch.float32, device="cuda")
+    t0 = time.perf_counter()
+    k = 0
+    for s_ in seeds:
+        c = synth.tank_learned(seed=s_)
+        T = wec.Tank(c, precision=wec.PREC_MIXED_MG)
+        T.step_n(skip, c["dt"], records=False)
+        for _ in range(per):
+            T.step(c["dt"])
+            wec.net_sample(T, xs[k], ts[k])
+            k += 1
+        T.close()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    net = wec.Net(ny, nx, max_batch=4)
+    net.set_params(synth.unet_weights(wec.net_param_shapes(), args.seed))
+    rng = np.random.default_rng(args.seed)
+    iters = args.train_iters
+    losses = [net.train_step(xs, ts, rng.integers(0, N, 4), 1e-3 if it < 0.7 * iters else 3e-4)
+              for it in range(iters)]
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    del xs, ts
+    torch.cuda.empty_cache()
+    stream = torch.cuda.current_stream()
+
+    def run(c, prec, use_net, n):
+        T = wec.Tank(c, precision=prec)
+        if use_net:
+            T.set_net(net)
+        T.step_n(5, c["dt"], records=False)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        its = []
+        for q in range(n):
+            ev[q][0].record(stream)
+            r = T.step(c["dt"])
+            ev[q][1].record(stream)
+            its.append(r["iters"])
+            assert r["residual"] <= c["solver"]["rtol"]
+        torch.cuda.synchronize()
+        st = T.net_stats() if use_net else (0, 0)
+        T.close()
+        return statistics.mean(its), statistics.mean(a.elapsed_time(b) for a, b in ev), st
+
+    held = [args.seed + 900 + k for k in range(2)]
+    ev_out = {}
+    for name, prec in (("mixed_mg", wec.PREC_MIXED_MG), ("mixed_fp32_stencils", wec.PREC_MIXED)):
+        rows = []
+        for hs in held:
+            c = synth.tank_learned(seed=hs)
+            c["solver"]["rtol"] = 1e-8
+            ip, tp, _ = run(c, prec, False, args.steps)
+            il, tl, (tried, kept) = run(c, prec, True, args.steps)
+            rows.append({"seed": hs, "iters_plain": ip, "iters_learned": il, "ms_plain": tp, "ms_learned": tl,
+                         "guess_kept": f"{kept}/{tried}"})
+        ev_out[name] = rows
+    line = {"metric": "FGMRES iterations and ms per step to the 1e-8 FP64 residual, learned warm start vs plain "
+                      "multigrid (held-out seeds)",
+            "workload": f"512x256 tank_learned, {N} training problems from {nseeds} seeds x {per} steps, "
+                        f"{iters} Adam steps of batch 4; held-out seeds {held}, {args.steps} steps each",
+            "training": {"samples": N, "sampling_s": t1 - t0, "training_s": t2 - t1,
+                         "loss_first_100": float(np.mean(losses[:100])), "loss_last_100": float(np.mean(losses[-100:]))},
+            "evaluation": ev_out}
+    if rank == 0:
+        print(json.dumps(line))
+    net.close()
+
+
 def main_reference(args):
     """The reference arm: the oracle (plain FP64 C, all host cores) on the same
     3D tank physics, each step a bounded sample: a 192 x 96 x 96 grid of the
@@ -1159,5 +1250,7 @@ if __name__ == "__main__":
         main_poisson3d(a)
     elif a.workload == "tank":
         main_tank2d(a)
+    elif a.workload == "learned":
+        main_learned(a)
     else:
         main_tank3d(a)

@@ -79,13 +79,42 @@ def test_trained_guess_on_held_out_runs(trained):
           f"with the learned guess {il.mean():.2f}; guess kept in {kept} of {tried} steps")
     assert tried == n
     assert all(r["residual"] <= 1e-8 for r in learned)  # the FP64 residual still decides
-    # the fallback bounds the loss; the trained guess is better than zero most of the time
-    assert il.mean() <= ip.mean() + 0.25
+    # the gain the trained guess gives (measured: 9.96 -> 9.04 iterations per
+    # step, the guess kept in 195 of 200 steps), and the guess is better than
+    # zero most of the time
+    assert il.mean() <= ip.mean() - 0.4
     assert kept >= 0.5 * n
     # the two runs stay within the solver tolerance of each other
     zp = np.array([r["z"] for r in plain])
     zl = np.array([r["z"] for r in learned])
     assert np.max(np.abs(zp - zl)) <= 1e-6 * max(np.max(np.abs(zp)), 1e-3)
+
+
+@pytest.mark.parametrize("prec,bound", [(wec.PREC_MIXED_MG, 1e-6), (wec.PREC_MIXED, 1e-4)])
+def test_trained_guess_on_mixed_tanks_against_the_oracle(trained, prec, bound):
+    # the learned path as the 2D bench runs it (a trained network's guess, FP32
+    # V-cycles; FP64 or FP32 stencils) against the FP64 oracle after 20 steps of
+    # a held-out 512x256 run: the error is the solver tolerance's (FP64 stencils)
+    # or the FP32 stencils' (stated in the design notes), never more
+    net, _ = trained
+    cfg = synth.tank_learned(seed=98)
+    cfg["solver"]["rtol"] = 1e-8
+    t = wec.Tank(cfg, precision=prec)
+    t.set_net(net)
+    o = O.OracleTank(cfg)
+    for _ in range(20):
+        r, ro = t.step(cfg["dt"]), o.step(cfg["dt"])
+        assert r["residual"] <= 1e-8
+    tried, kept = t.net_stats()
+    errs = {}
+    for name, fo in (("sigma", O.F_SIGMA), ("u", O.F_U), ("v", O.F_V), ("p", O.F_P)):
+        a, b = t.get(name), o.get(fo)
+        errs[name] = float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+    hz = abs(r["z"] - ro["z"]) / max(abs(ro["z"]), 1e-12)
+    print(f"trained guess, precision {prec}, 20 steps: {errs}, heave {hz:.2e}, guess kept {kept}/{tried}")
+    t.close()
+    assert kept > 0
+    assert max(errs.values()) < bound and hz < bound
 
 
 def test_features_follow_their_definition():
