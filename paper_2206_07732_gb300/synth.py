@@ -295,14 +295,14 @@ def poisson3d_case(nx=512, ny=256, nz=256, seed=0, lx=8.0, depth=2.0, Hs=0.2, nc
     return bx, by, bz, b
 
 
-def cylinder_body(xc, yc, radius, length, draft, depth, rho_w, kappa_p=1e-8, pto_damping=0.0):
+def cylinder_body(xc, yc, radius, length, draft, depth, rho_w, kappa_p=1e-8, pto_damping=0.0, added_mass=0.0):
     """Vertical heaving cylinder whose mass floats it at ``draft`` (the displaced
-    water mass); centred so that its bottom sits ``draft`` below still water."""
+    water mass); centred so that its bottom sits ``draft`` below still water.
+    added_mass: the stabilising mass of the heave update (0: Eq. newton_u as the
+    paper writes it; the cylinder's own heave added mass, ~0.9 of its mass, is
+    below its mass, so the explicit force coupling is stable without it)."""
     mass = rho_w * math.pi * radius ** 2 * draft
     zc = depth - draft + 0.5 * length
-    # artificial added mass of the stabilised heave update: the water mass that
-    # would fill the cylinder (the 2D box's rule, in three dimensions)
-    added_mass = rho_w * math.pi * radius ** 2 * length
     return dict(xc=xc, yc=yc, zc=zc, radius=radius, length=length, mass=mass, kappa_p=kappa_p,
                 added_mass=added_mass, pto_damping=pto_damping)
 
