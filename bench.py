@@ -943,6 +943,7 @@ def roofline3(prof, steps, top=None, shape=(512, 256, 256)):
     algorithmic bytes per launch / mean launch time (multigrid kernels: over
     their finest-level launches, the 33.5 M-cell sweeps; coarser levels are
     latency-bound), against the measured HBM copy bandwidth."""
+    prof = [q for q in prof if q["name"] != "tank3_section"]  # phase spans, not kernels
     by = {}
     for q in prof:
         d = by.setdefault(q["name"], dict(ms=0.0, bytes=0.0, launches=0))

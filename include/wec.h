@@ -512,6 +512,10 @@ int wec_jonswap(double Hs, double Tp, double gamma, int ncomp, double *amp, doub
  * later solvers of the same shape reuse them and compute the same bits.
  * "mg_bottom_shift" (default -1 = autotuned): start the single-CTA kernel this
  * many levels below the smallest admissible one (0..8, capped at the coarsest).
+ * "mg3_bottom" (default 1): the 3D V-cycle runs its levels of at most 8192
+ * cells, down to the coarsest, in one 1024-thread CTA (iterates and right-hand
+ * sides in shared memory); 0 launches them level by level.  Both compute the same
+ * bits.
  * "tank3_split_momentum" (default 1): the 3D momentum system per component as
  * two kernels (transport terms, then viscous terms and assembly); 0: one
  * kernel.  Both compute the same values.

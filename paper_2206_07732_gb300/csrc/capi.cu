@@ -220,6 +220,10 @@ int wec_set_option(const char *name, int value)
         set_mg_autotune(value != 0);
         return WEC_OK;
     }
+    if (std::string(name) == "mg3_bottom") {
+        set_mg3_bottom(value != 0);
+        return WEC_OK;
+    }
     if (std::string(name) == "tank3_split_momentum") {
         set_tank3_split_momentum(value != 0);
         return WEC_OK;

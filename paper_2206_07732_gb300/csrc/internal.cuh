@@ -163,6 +163,7 @@ void set_mg_fused(bool on);
 void set_mg_autotune(bool on);
 void set_mg_bottom_shift(int shift);  // -1: autotune
 void set_tank3_split_momentum(bool on);
+void set_mg3_bottom(bool on);
 void poisson_tiles(const wec_poisson *P, int *tx, int *ty, int max);
 int poisson_vcycle(wec_poisson *P, const double *b, double *x);
 

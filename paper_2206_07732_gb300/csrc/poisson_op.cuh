@@ -30,6 +30,15 @@ __device__ __forceinline__ T offsum_at(const T *bu, const T *bv, const TX *x, in
     return s;
 }
 
+// a * b + c rounded once, written out: the 3D multigrid forms the same terms in
+// its per-level kernels and in its one-CTA coarse levels, and left to the
+// compiler the contraction of a product into a sum differs between them
+template <typename T>
+__device__ __forceinline__ T fma3(T a, T b, T c)
+{
+    if constexpr (sizeof(T) == 4) return __fmaf_rn(a, b, c); else return __fma_rn(a, b, c);
+}
+
 // Three dimensions (z vertical): cells [nz][ny][nx], beta_x [nz][ny][nx+1],
 // beta_y [nz][ny+1][nx], beta_z [nz+1][ny][nx] (face k of beta_z is the bottom
 // face of cell layer k); the walls and the bed are Neumann, the top face
@@ -56,12 +65,12 @@ __device__ __forceinline__ T offsum3_at(const T *bx, const T *by, const T *bz, c
 {
     const int r = k * ny + j, fx = r * (nx + 1) + i, fy = (r + k) * nx + i, c = r * nx + i, pl = nx * ny;
     T s = T(0);
-    if (i > 0) s += bx[fx] * T(x[c - 1]);
-    if (i < nx - 1) s += bx[fx + 1] * T(x[c + 1]);
-    if (j > 0) s += by[fy] * T(x[c - nx]);
-    if (j < ny - 1) s += by[fy + nx] * T(x[c + nx]);
-    if (k > 0) s += bz[c] * T(x[c - pl]);
-    if (k < nz - 1) s += bz[c + pl] * T(x[c + pl]);
+    if (i > 0) s = fma3(bx[fx], T(x[c - 1]), s);
+    if (i < nx - 1) s = fma3(bx[fx + 1], T(x[c + 1]), s);
+    if (j > 0) s = fma3(by[fy], T(x[c - nx]), s);
+    if (j < ny - 1) s = fma3(by[fy + nx], T(x[c + nx]), s);
+    if (k > 0) s = fma3(bz[c], T(x[c - pl]), s);
+    if (k < nz - 1) s = fma3(bz[c + pl], T(x[c + pl]), s);
     return s;
 }
 

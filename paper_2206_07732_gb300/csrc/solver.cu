@@ -263,6 +263,7 @@ namespace wec {
 namespace {
 
 bool g_mg_fused = true;  // fused V-cycle kernels (wec_set_option "mg_fused")
+bool g_mg3_bottom = true;  // the 3D coarse levels in one CTA (wec_set_option "mg3_bottom")
 
 #include "mg3d.cuh"
 
@@ -1312,6 +1313,7 @@ int read_state(wec_poisson *P, cudaStream_t st)
 
 void set_mg_fused(bool on) { g_mg_fused = on; }
 void set_mg_autotune(bool on) { g_mg_autotune = on; }
+void set_mg3_bottom(bool on) { g_mg3_bottom = on; }
 void set_mg_bottom_shift(int shift) { g_mg_bottom_shift = shift; }
 
 void poisson_tiles(const wec_poisson *P, int *tx, int *ty, int max)
@@ -1332,6 +1334,8 @@ int poisson_init(wec_poisson *P, int nx, int ny, int prec, int restart, int nu1,
         if (int e = set_tile_attrs()) return e;
         WEC_CK(cudaFuncSetAttribute(k_mg_bottom<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBottomSmemMax));
         WEC_CK(cudaFuncSetAttribute(k_mg_bottom<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBottomSmemMax));
+        WEC_CK(cudaFuncSetAttribute(k3_bottom<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBottom3Smem));
+        WEC_CK(cudaFuncSetAttribute(k3_bottom<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBottom3Smem));
         if (int e = set_kgrid_max()) return e;
         attrs_done = true;
     }
@@ -1476,6 +1480,8 @@ int build_invdiag3(wec_poisson *P, Level<T> *L, cudaStream_t st)
     Level3Diag<T> D;
     D.nlev = P->nlev;
     D.off[0] = 0;
+    // FP32 levels above the coarsest are colour-packed (mg3d.cuh)
+    D.pk = std::is_same<T, float>::value ? (1u << (P->nlev - 1)) - 1u : 0u;
     for (int l = 0; l < P->nlev; ++l) {
         D.nx[l] = L[l].nx;
         D.ny[l] = L[l].ny;
@@ -1619,9 +1625,13 @@ int poisson_vcycle(wec_poisson *P, const double *b, double *x)
             WEC_PROF("convert", -1, 12.0 * n, st);
             launch_k(k_convert<float, double>, nblk(n, 256), 256, 0, st, n, b, P->L32[0].b, nullptr);
         }
-        vcycle_t<float, float>(P, P->L32, P->L32[0].b, P->L32[0].x, nullptr, nullptr, st);
-        WEC_PROF("convert", -1, 12.0 * n, st);
-        launch_k(k_convert<double, float>, nblk(n, 256), 256, 0, st, n, P->L32[0].x, x, nullptr);
+        if (P->nz > 1) {  // unpacked from the colour-packed level-0 iterate into x
+            vcycle_t<float, double>(P, P->L32, P->L32[0].b, x, nullptr, nullptr, st);
+        } else {
+            vcycle_t<float, float>(P, P->L32, P->L32[0].b, P->L32[0].x, nullptr, nullptr, st);
+            WEC_PROF("convert", -1, 12.0 * n, st);
+            launch_k(k_convert<double, float>, nblk(n, 256), 256, 0, st, n, P->L32[0].x, x, nullptr);
+        }
     }
     WEC_CK(cudaGetLastError());
     return WEC_OK;

@@ -31,6 +31,7 @@
 #include <algorithm>
 #include <initializer_list>
 #include <new>
+#include <optional>
 #include <string>
 #include <type_traits>
 #include <utility>
@@ -261,25 +262,28 @@ __device__ __forceinline__ void ppm_edges3(const R *a, R &eL, R &eR)
 }
 
 // time-centred upwind state at the face between a[2] and a[3] (a: cells f-3 .. f+2);
-// dtih = dt / h
+// dtih = dt / h.  The upwind cell's five-cell window is selected first and its
+// parabola built once: vel >= 0 takes the right edge of a[2]'s parabola,
+// Rr - C/2 (dA - (1 - 2C/3) a6), vel < 0 the left edge of a[3]'s, L + C/2 (dA +
+// (1 - 2C/3) a6), with C = |vel| dt / h -- one copy of the edge code and no
+// divergence between the two cases.
 template <typename R>
 __device__ __forceinline__ R ppm_face3(const R *a, R vel, R dtih)
 {
     const R t3 = R(2.0 / 3.0);
-    R L, Rr;
     bool up;
     if constexpr (is_f64<R>)  // vel >= 0, -0 included
         up = __double_as_longlong(vel) >= 0 || (__double_as_longlong(vel) << 1) == 0;
     else
         up = vel >= R(0);
-    if (up) {
-        ppm_edges3(a, L, Rr);
-        const R C = vel * dtih, dA = Rr - L, a6 = R(6) * (a[2] - R(0.5) * (L + Rr));
-        return Rr - R(0.5) * C * (dA - (R(1) - C * t3) * a6);
-    }
-    ppm_edges3(a + 1, L, Rr);
-    const R C = -vel * dtih, dA = Rr - L, a6 = R(6) * (a[3] - R(0.5) * (L + Rr));
-    return L + R(0.5) * C * (dA + (R(1) - C * t3) * a6);
+    R b[5];
+#pragma unroll
+    for (int m = 0; m < 5; ++m) b[m] = up ? a[m] : a[m + 1];
+    R L, Rr;
+    ppm_edges3(b, L, Rr);
+    const R C = (up ? vel : -vel) * dtih, dA = Rr - L, a6 = R(6) * (b[2] - R(0.5) * (L + Rr));
+    const R e = (R(1) - C * t3) * a6, hc = R(0.5) * C;
+    return (up ? Rr : L) + (up ? -hc : hc) * (dA + (up ? -e : e));
 }
 
 struct Cell3 {
@@ -299,7 +303,7 @@ __device__ __forceinline__ bool cell_of(const Tank3P &P, Cell3 &q)
 
 // (cell layers k0 + blockIdx.z)
 template <typename R>
-__global__ void __launch_bounds__(128) k3t_materials(Tank3P P, const R *__restrict__ sig, double zc,
+__global__ void __launch_bounds__(128) k3t_materials(Tank3P P, const R *__restrict__ sig, R zc,
                                                      R *__restrict__ rho, R *__restrict__ mu, R *__restrict__ rhof,
                                                      R *__restrict__ chi, int k0)
 {
@@ -313,7 +317,7 @@ __global__ void __launch_bounds__(128) k3t_materials(Tank3P P, const R *__restri
     R psi = R(1.0e3);
     if (P.has_body) {
         const R x = (R(q.i) + R(0.5)) * h - K.bxc, y = (R(q.j) + R(0.5)) * h - K.byc,
-                z = (R(q.k) + R(0.5)) * h - R(zc);
+                z = (R(q.k) + R(0.5)) * h - zc;
         psi = fmax(sqrt(x * x + y * y) - K.br, fabs(z) - R(0.5) * K.blen);
     }
     const R hf = heav3<R>(sig[q.c], h, K.ih), hb = heav3<R>(psi, h, K.ih);
@@ -331,7 +335,7 @@ __global__ void __launch_bounds__(128) k3t_materials(Tank3P P, const R *__restri
 template <typename R>
 __global__ void __launch_bounds__(128) k3t_advect(Tank3P P, const R *__restrict__ base, const R *__restrict__ s,
                                                   const R *__restrict__ u, const R *__restrict__ v,
-                                                  const R *__restrict__ w, double dt, Ghost3 G, R *__restrict__ out)
+                                                  const R *__restrict__ w, R dt, Ghost3 G, R *__restrict__ out)
 {
     pdl_entry();
     Cell3 q;
@@ -340,7 +344,7 @@ __global__ void __launch_bounds__(128) k3t_advect(Tank3P P, const R *__restrict_
     const int nx = P.nx, ny = P.ny, i = q.i, j = q.j, k = q.k;
     const long long r = (long long)k * ny + j, fu = r * (nx + 1) + i, fv = ((long long)k * (ny + 1) + j) * nx + i;
     const long long pl = (long long)nx * ny;
-    const R ih = K.ih, dtih = R(dt) * ih;
+    const R ih = K.ih, dtih = dt * ih;
     // cells three or more from every boundary read their stencils at fixed
     // offsets (no ghosts, 32-bit indices); the others through sig3.  The
     // directions and the two faces are loops, not unrolled: one copy of the
@@ -370,7 +374,7 @@ __global__ void __launch_bounds__(128) k3t_advect(Tank3P P, const R *__restrict_
         const R vb = R(0.5) * (vel[0] + vel[vs]);
         Q = Q + vb * (F1 - F0) * ih;
     }
-    const R sa = base[q.c] - R(dt) * Q;
+    const R sa = base[q.c] - dt * Q;
     const R al = dampc<R>(P, i);
     out[q.c] = (R(1) - al) * sa + al * ((R(k) + R(0.5)) * K.h - K.depth);
 }
@@ -433,14 +437,14 @@ __device__ __forceinline__ R reinit_rhs3(const Tank3P &P, const R *__restrict__ 
     return S * (sqrt(g2 * K.ih * K.ih) - R(1));
 }
 
-// S(sigma0) = sigma0 / sqrt(sigma0^2 + h^2) in place
+// S(sigma0) = sigma0 / sqrt(sigma0^2 + h^2) of the field s into s0
 template <typename R>
-__global__ void __launch_bounds__(128) k3t_reinit_sign(Tank3P P, R *__restrict__ s0)
+__global__ void __launch_bounds__(128) k3t_reinit_sign(Tank3P P, const R *__restrict__ s, R *__restrict__ s0)
 {
     pdl_entry();
     Cell3 q;
     if (!cell_of(P, q)) return;
-    const R h = cst3<R>(P).h, g = s0[q.c];
+    const R h = cst3<R>(P).h, g = s[q.c];
     s0[q.c] = g * rsqrt(g * g + h * h);
 }
 
@@ -448,12 +452,12 @@ __global__ void __launch_bounds__(128) k3t_reinit_sign(Tank3P P, R *__restrict__
 // out holding sigma at the start of the pseudo-step
 template <typename R>
 __global__ void __launch_bounds__(128) k3t_reinit_stage(Tank3P P, const R *__restrict__ f, const R *__restrict__ sg,
-                                                        R *out, Ghost3 G, double dtau, int stage)
+                                                        R *out, Ghost3 G, R dtau, int stage)
 {
     pdl_entry();
     Cell3 q;
     if (!cell_of(P, q)) return;
-    const R y = f[q.c] - R(dtau) * reinit_rhs3<R>(P, f, sg, q, G);
+    const R y = f[q.c] - dtau * reinit_rhs3<R>(P, f, sg, q, G);
     out[q.c] = stage == 1 ? y : R(0.5) * (out[q.c] + y);
 }
 
@@ -529,7 +533,8 @@ __device__ __forceinline__ R upw3(R q0, R q1, R q2, R q3, R vel)
         up = __double_as_longlong(vel) >= 0 || (__double_as_longlong(vel) << 1) == 0;
     else
         up = vel >= R(0);
-    return up ? koren3(q0, q1, q2) : koren3(q3, q2, q1);
+    // the upwind triple selected first: one copy of the limiter, no divergence
+    return koren3(up ? q0 : q3, up ? q1 : q2, up ? q2 : q1);
 }
 // face densities: the mean of the face's two cells (face index clamped first)
 template <bool IN, typename R>
@@ -962,6 +967,19 @@ __global__ void k3t_dirichlet(Tank3P P, const R *__restrict__ uin1, R *u, R *v, 
     if (a < nx * ny) w[a] = R(0);
 }
 
+// a = b = src (n values)
+template <typename R>
+__global__ void __launch_bounds__(256) k3t_dup(long long n, const R *__restrict__ src, R *__restrict__ a,
+                                               R *__restrict__ b)
+{
+    pdl_entry();
+    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const R v = src[q];
+    a[q] = v;
+    b[q] = v;
+}
+
 // beta = 1 / D on the solved faces, 0 on the walls and the bed (FP64 coefficients)
 template <typename R>
 __global__ void k3t_beta(Tank3P P, int comp, const R *__restrict__ D, double *__restrict__ beta, long long n)
@@ -1194,6 +1212,66 @@ __global__ void k3t_hydrostatic(Tank3P P, const double *__restrict__ rf, double 
     }
 }
 
+// Inflow data of a step at x = 0: the Airy velocity of the incident components,
+// Wheeler-stretched up to the surface and blended to zero in the air over a
+// half-width h (the arithmetic of airy_host) -- u_in(t1) at the cell layers,
+// w_in(t0), w_in(t1) and their mean at the face heights -- into bc (FP64; the
+// host has written the vorticity-damping entries), and all entries narrowed
+// into bcr (nullable).  One warp per layer: rows 0..nz-1 the cells, nz..2nz the
+// faces (both times); the components are split over the lanes.  Evaluated on
+// the host, these ~6 x 10^5 transcendentals per step kept the GPU idle for
+// several milliseconds at the start of every step.
+__device__ __forceinline__ double warp_sum_d(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+template <typename R>
+__global__ void __launch_bounds__(128) k3t_inflow(Tank3P P, double t0, double t1, double *__restrict__ bc, R *bcr)
+{
+    pdl_entry();
+    const int nz = P.nz, lane = threadIdx.x & 31, row = blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (row > 2 * nz) return;
+    double *uin1 = bc, *win0 = uin1 + nz, *win1 = win0 + nz + 1, *vc = win1 + nz + 1, *vf = vc + nz,
+           *wmean = vf + nz + 1;
+    const bool cell = row < nz;
+    const int k = cell ? row : row - nz;
+    const double z = cell ? (k + 0.5) * P.h : k * P.h, d = P.depth;
+    double out[2] = {0.0, 0.0};
+    for (int tt = 0; tt < (cell ? 1 : 2); ++tt) {
+        const double t = cell || tt == 1 ? t1 : t0;
+        double e = 0.0;  // eta at x = 0
+        for (int c = lane; c < P.ncomp; c += 32) e += P.amp[c] * cos(P.kw[c] * 0.0 - P.omega[c] * t + P.phase[c]);
+        e = warp_sum_d(e);
+        const double zs = z < d + e ? z : d + e, zp = d * zs / (d + e), phi = z - d - e;
+        const double blend = 1.0 - (phi < -P.h ? 0.0 : phi > P.h ? 1.0
+                                    : 0.5 * (1.0 + phi / P.h + sin(kPi3 * phi / P.h) / kPi3));
+        double s = 0.0;
+        for (int c = lane; c < P.ncomp; c += 32) {
+            const double kk = P.kw[c], om = P.omega[c], ph = kk * 0.0 - om * t + P.phase[c], sk = sinh(kk * d);
+            s += cell ? P.amp[c] * om * cosh(kk * zp) / sk * cos(ph) : P.amp[c] * om * sinh(kk * zp) / sk * sin(ph);
+        }
+        out[tt] = blend * warp_sum_d(s);
+    }
+    if (lane != 0) return;
+    if (cell) {
+        uin1[k] = out[0];
+        if (bcr) bcr[k] = R(out[0]);
+    } else {
+        const double m = 0.5 * (out[0] + out[1]);
+        win0[k] = out[0];
+        win1[k] = out[1];
+        wmean[k] = m;
+        if (bcr) {
+            bcr[nz + k] = R(out[0]);
+            bcr[2 * nz + 1 + k] = R(out[1]);
+            bcr[5 * nz + 3 + k] = R(m);
+        }
+    }
+    if (bcr && row < nz) bcr[3 * nz + 2 + row] = R(vc[row]);
+    if (bcr && row < nz + 1) bcr[4 * nz + 2 + row] = R(vf[row]);
+}
+
 dim3 grid3(const Tank3P &P) { return dim3((P.nx + 127) / 128, P.ny, P.nz); }
 
 int tank3_check(const wec_tank3 *T)
@@ -1255,10 +1333,9 @@ template <typename R>
 int reinit_buf(wec_tank3 *T, R *s, R *s0, R *s1, int nit, double t)
 {
     const double dtau = 0.3 * T->P.h, b = sizeof(R);
-    WEC_CK(cudaMemcpyAsync(s0, s, T->nc * sizeof(R), cudaMemcpyDeviceToDevice, T->st));
     {
         WEC_PROF("tank3_reinit", 1, 2.0 * b * T->nc, T->st);
-        launch_k(k3t_reinit_sign<R>, grid3(T->P), 128, 0, T->st, T->P, s0);
+        launch_k(k3t_reinit_sign<R>, grid3(T->P), 128, 0, T->st, T->P, (const R *)s, s0);
     }
     for (int it = 0; it < nit; ++it) {
         {
@@ -1293,24 +1370,21 @@ static int tank3_step_impl(wec_tank3 *T, Work3<R> &W, double dt, double pto_forc
     cudaStream_t st = T->st;
     const int nx = P.nx, ny = P.ny, nz = P.nz;
     const double h = P.h, t0 = T->t, t1 = T->t + dt;
-    // boundary data of this step (host): u_in(t1) at the cell layers, w_in(t0)
-    // and w_in(t1) at the face heights, vorticity damping at cell / face heights
-    std::vector<double> hb((size_t)6 * nz + 4);
-    const std::vector<double> &hw = T->hwave;
-    const Waves3 Wv{P.ncomp, hw.data(), hw.data() + P.ncomp, hw.data() + 2 * P.ncomp, hw.data() + 3 * P.ncomp};
-    double *uin1 = hb.data(), *win0 = uin1 + nz, *win1 = win0 + nz + 1, *vc = win1 + nz + 1, *vf = vc + nz;
-    for (int k = 0; k < nz; ++k) {
-        double uu, ww;
-        airy_host(Wv, P.depth, h, 0.0, (k + 0.5) * h, t1, &uu, &ww);
-        uin1[k] = uu;
-    }
-    for (int k = 0; k <= nz; ++k) {
-        double uu, ww;
-        airy_host(Wv, P.depth, h, 0.0, k * h, t0, &uu, &ww);
-        win0[k] = ww;
-        airy_host(Wv, P.depth, h, 0.0, k * h, t1, &uu, &ww);
-        win1[k] = ww;
-    }
+    // the step's phases on the GPU timeline: profile name "tank3_section",
+    // level = phase (0 set-up, 1 force and heave, 2 advection, 3 reinitialisation,
+    // 4 materials and face data, 5 transport and momentum, 6 Jacobi sweeps, 7 beta,
+    // hierarchy and right-hand side, 8 pressure solve, 9 projection, 10 close)
+    std::optional<prof::Scope> sec;
+    auto section = [&](int id) {
+        sec.reset();
+        sec.emplace("tank3_section", id, 0.0, st);
+    };
+    section(0);
+    // boundary data of this step: u_in(t1) at the cell layers, w_in(t0) and
+    // w_in(t1) at the face heights and their mean (k3t_inflow, on the device),
+    // vorticity damping at cell / face heights (here)
+    std::vector<double> hb((size_t)6 * nz + 4, 0.0);
+    double *vc = hb.data() + 3 * nz + 2, *vf = vc + nz;
     auto vort = [&](double z) {
         const double wd = 4.0 * h;
         if (z < T->lz - wd) return 0.0;
@@ -1319,15 +1393,8 @@ static int tank3_step_impl(wec_tank3 *T, Work3<R> &W, double dt, double pto_forc
     };
     for (int k = 0; k < nz; ++k) vc[k] = vort((k + 0.5) * h);
     for (int k = 0; k <= nz; ++k) vf[k] = vort(k * h);
-    double *wmean = vf + nz + 1;  // the ghost of w at the mean of the two time levels
-    for (int k = 0; k <= nz; ++k) wmean[k] = 0.5 * (win0[k] + win1[k]);
     WEC_CK(cudaMemcpyAsync(T->bc, hb.data(), hb.size() * 8, cudaMemcpyHostToDevice, st));
-    std::vector<R> hbf;
-    if constexpr (f32) {
-        hbf.reserve(hb.size());
-        for (double x : hb) hbf.push_back(R(x));
-        WEC_CK(cudaMemcpyAsync(W.bc, hbf.data(), hbf.size() * sizeof(R), cudaMemcpyHostToDevice, st));
-    }
+    launch_k(k3t_inflow<R>, nblk(2 * nz + 1, 4), 128, 0, st, P, t0, t1, T->bc, f32 ? W.bc : (R *)nullptr);
     const double *d_win0 = T->bc + nz, *d_win1 = d_win0 + nz + 1;
     const R *r_uin1 = W.bc, *r_win0 = r_uin1 + nz, *r_win1 = r_win0 + nz + 1, *r_vc = r_win1 + nz + 1,
             *r_vf = r_vc + nz;
@@ -1376,6 +1443,7 @@ static int tank3_step_impl(wec_tank3 *T, Work3<R> &W, double dt, double pto_forc
                  T->rhof, T->chi, 0);
     }
     for (int cyc = 0; cyc < ncyc; ++cyc) {
+        section(1);
         // (1) the heave force (Eq. int_fh) from p^{n+1/2,k}, u^{n+1,k} over a box
         // of cells around the cylinder at z^{n+1,k}
         const double zck = T->zc;
@@ -1424,6 +1492,7 @@ static int tank3_step_impl(wec_tank3 *T, Work3<R> &W, double dt, double pto_forc
             zd1 = zd_n + (dt * (F - m * T->g + fpto) + ma * (zd_n - zd_prev)) / (m + ma);
             zc1 = zc_n + 0.5 * dt * (zd_n + zd1);
         }
+        section(2);
         // (3) sigma: sigma^n advected with u^{n+1/2,k}, sigma^{n+1/2,k} (cycle 0:
         // u^n, sigma^n; ghosts at t0), damping zone, reinitialisation (ghosts at t1)
         Vel3<R> Vt{W.u, W.v, W.w, r_win0};
@@ -1444,7 +1513,9 @@ static int tank3_step_impl(wec_tank3 *T, Work3<R> &W, double dt, double pto_forc
             WEC_PROF("tank3_advect", 0, sizeof(R) * (2.0 * T->nc + T->nu + T->nv + T->nw), st);
             launch_k(k3t_advect<R>, grid3(P), 128, 0, st, P, (const R *)W.sig, sadv, Vt.u, Vt.v, Vt.w, dt, Ga, W.tmp);
         }
+        section(3);
         if (int e = reinit_buf<R>(T, W.tmp, W.s0, W.s1, T->opts.n_reinit, t1)) return e;
+        section(4);
         // (4) materials at n+1,k+1 (rho itself is not used: s1 is scratch)
         {
             WEC_PROF("tank3_materials", 0, 5.0 * sizeof(R) * T->nc, st);
@@ -1465,6 +1536,7 @@ static int tank3_step_impl(wec_tank3 *T, Work3<R> &W, double dt, double pto_forc
         MomIn<R> M{{W.RF[0], W.RF[1], W.RF[2]}, W.mu, W.chi1, W.rf1, E, T->p, Vt, Vel3<R>{W.u, W.v, W.w, r_win0},
                    W.dampu, r_vc, r_vf, R(dt), R(1.0 / dt), R(dt / h), R(1.0 / (h * h)), R(zd1), R(T->g),
                    R(1.0 / T->kappa_p)};
+        section(5);
         for (int c = 0; c < 3; ++c) {
             if (c == 1 && ny < 2) continue;
             // face density, mu, two edge arrays, chi (+ rho^flow for w), p, u, v, w in; D, R out
@@ -1483,6 +1555,7 @@ static int tank3_step_impl(wec_tank3 *T, Work3<R> &W, double dt, double pto_forc
                 launch_k(kern, gc[c], 128, 0, st, P, M, W.D[c], W.R3[c]);
             }
         }
+        section(6);
         // (6) Crank-Nicolson Jacobi sweeps from u^n with the Dirichlet faces at
         // n+1: edge viscosities of mu^{n+1}, the per-face factors, then the sweeps
         {
@@ -1496,15 +1569,18 @@ static int tank3_step_impl(wec_tank3 *T, Work3<R> &W, double dt, double pto_forc
             launch_k(kern, gc[c], 128, 0, st, P, (const R *)W.mu1, E, (const R *)W.D[c], W.R3[c], W.Q[c],
                      R(1.0 / (h * h)));
         }
-        R *src[3] = {W.u, W.v, W.w};
-        for (int c = 0; c < 3; ++c)
-            WEC_CK(cudaMemcpyAsync(W.A[c], src[c], nf[c] * sizeof(R), cudaMemcpyDeviceToDevice, st));
+        // both sweep buffers start as u^n with the Dirichlet faces at n+1 (the
+        // sweeps write the solved faces only)
+        const R *src[3] = {W.u, W.v, W.w};
+        for (int c = 0; c < 3; ++c) {
+            WEC_PROF("tank3_jacobi", c, 3.0 * b * nf[c], st);
+            launch_k(k3t_dup<R>, nblk((long long)nf[c], 256), 256, 0, st, (long long)nf[c], src[c], W.A[c], W.B[c]);
+        }
         {
             const long long nd = std::max({(long long)ny * nz, (long long)nx * nz, (long long)nx * ny});
             launch_k(k3t_dirichlet<R>, nblk(nd, 256), 256, 0, st, P, r_uin1, W.A[0], W.A[1], W.A[2]);
+            launch_k(k3t_dirichlet<R>, nblk(nd, 256), 256, 0, st, P, r_uin1, W.B[0], W.B[1], W.B[2]);
         }
-        for (int c = 0; c < 3; ++c)
-            WEC_CK(cudaMemcpyAsync(W.B[c], W.A[c], nf[c] * sizeof(R), cudaMemcpyDeviceToDevice, st));
         for (int it = 0; it < T->opts.n_jacobi; ++it) {
             const Vel3<R> Va{W.A[0], W.A[1], W.A[2], r_win1};
             for (int c = 0; c < 3; ++c) {
@@ -1517,6 +1593,7 @@ static int tank3_step_impl(wec_tank3 *T, Work3<R> &W, double dt, double pto_forc
             }
             for (int c = 0; c < 3; ++c) std::swap(W.A[c], W.B[c]);
         }
+        section(7);
         // (7) pressure increment: beta = 1 / D, b = -h div u* (FP64), phi from zero
         for (int c = 0; c < 3; ++c)
             launch_k(k3t_beta<R>, nblk((long long)nf[c], 256), 256, 0, st, P, c, (const R *)W.D[c], beta[c],
@@ -1525,8 +1602,10 @@ static int tank3_step_impl(wec_tank3 *T, Work3<R> &W, double dt, double pto_forc
         launch_k(k3t_rhs<R>, grid3(P), 128, 0, st, P, Vel3<R>{W.A[0], W.A[1], W.A[2], r_win1}, T->rhs);
         WEC_CK(cudaMemsetAsync(T->phi, 0, T->nc * 8, st));
         WEC_CK(cudaGetLastError());
+        section(8);
         rc = poisson_solve(S, T->rhs, T->phi, T->opts.rtol, T->opts.max_iters, &iters, &relres);
         if (rc != WEC_OK && rc != WEC_ERR_NOT_CONVERGED) return rc;
+        section(9);
         // (8) projection (FP64) and p^{n+1/2,k+1} = p^{n+1/2,k} + phi: into the
         // iterate's velocity, the last cycle into the tank's
         double *dst[3] = {T->u, T->v, T->w};
@@ -1538,6 +1617,7 @@ static int tank3_step_impl(wec_tank3 *T, Work3<R> &W, double dt, double pto_forc
         launch_k(k3t_add, nblk((long long)T->nc, 256), 256, 0, st, (long long)T->nc, (const double *)T->phi, T->p);
         T->zc = zc1;
     }
+    section(10);
     // sigma^{n+1}
     if constexpr (f32)
         launch_k(k3t_widen<R>, nblk((long long)T->nc, 256), 256, 0, st, (long long)T->nc, (const R *)W.tmp, T->sig);
@@ -1554,6 +1634,7 @@ static int tank3_step_impl(wec_tank3 *T, Work3<R> &W, double dt, double pto_forc
     WEC_CK(cudaMemcpy2DAsync(col.data(), 8, T->sig + (size_t)jp * nx + ip, (size_t)nx * ny * 8, 8, nz,
                              cudaMemcpyDeviceToHost, st));
     WEC_CK(cudaGetLastError());
+    sec.reset();
     WEC_CK(cudaStreamSynchronize(st));
     double eta = std::nan("");
     for (int k = 0; k + 1 < nz; ++k)

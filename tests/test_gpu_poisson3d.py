@@ -66,6 +66,27 @@ def test_operator_and_vcycle_match_oracle(shape, contrast):
     P.close()
 
 
+@pytest.mark.parametrize("prec", [wec.PREC_FP64, wec.PREC_MIXED])
+@pytest.mark.parametrize("shape", [(64, 32, 32), (128, 64, 64), (96, 40, 24)])
+def test_one_cta_coarse_levels_give_the_same_bits(shape, prec):
+    # the levels of at most 8192 cells down to the coarsest in one CTA
+    # ("mg3_bottom") against the per-level kernels: the same passes and
+    # arithmetic, so the same bits, in FP64 and FP32 V-cycles
+    nx, ny, nz = shape
+    coef = _coef(shape, 7, "tank" if shape[0] % 64 == 0 else 1e2)
+    x = cuda(np.random.default_rng(2).standard_normal((nz, ny, nx)))
+    zs = []
+    for on in (0, 1):
+        wec.set_option("mg3_bottom", on)
+        P = _solver(shape, coef, prec)
+        z = torch.zeros(nz, ny, nx, dtype=torch.float64, device="cuda")
+        P.vcycle(x, z)
+        zs.append(z.cpu().numpy())
+        P.close()
+    wec.set_option("mg3_bottom", 1)
+    assert np.array_equal(zs[0], zs[1])
+
+
 @pytest.mark.parametrize("shape,contrast,rtol", [((16, 8, 8), 1.0, 1e-13), ((48, 24, 32), 1e2, 1e-12),
                                                  ((40, 24, 16), 1e3, 1e-11), ((64, 32, 32), "tank", 1e-10)])
 def test_fgmres_solution_matches_oracle(shape, contrast, rtol):
