@@ -484,6 +484,19 @@ int wec_tank3_get_state(const wec_tank3 *tank, double *out5);
 int wec_residual_norm_noalloc(int nx, int ny, const double *beta_u, const double *beta_v, const double *x,
                               const double *b, double *norm_out, void *cuda_stream);
 
+/* ---- conversion check of the double-float stencils ------------------------ */
+/* The double-float stencils (WEC_PREC_MIXED_DF) and the FP32 ones convert
+ * between their working types and the FP64 state with integer operations
+ * instead of this GPU's conversion instructions, which issue on its narrow FP64
+ * pipe.  This call checks those conversions against the instructions on n
+ * values (device, caller owned): for each value d, float(d) rounded to nearest
+ * and the float pair of d (nearest float, then the nearest float of the
+ * remainder), each widened back to double.  *mismatches (device, one unsigned
+ * long long, caller owned) receives the number of values for which any result
+ * differs in any bit.  Enqueued on cuda_stream (NULL = legacy default);
+ * WEC_ERR_INVALID for n < 0 or NULL pointers. */
+int wec_check_conversions(long long n, const double *values, unsigned long long *mismatches, void *cuda_stream);
+
 /* ---- host wave utilities (no device work) ------------------------------- */
 /* k solving omega^2 = g k tanh(k d) (Eq. dispersion_relation), |residual| <= 1e-14 omega^2. */
 double wec_wave_number(double omega, double depth, double g);

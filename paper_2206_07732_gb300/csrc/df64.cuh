@@ -42,6 +42,44 @@ struct df64 {
     __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
 };
 
+// --- conversions on the integer pipe ---------------------------------------------
+// This GPU issues float <-> double conversions on its narrow FP64 pipe; the
+// working copies convert every value of a field each step.  For normal
+// numbers both directions are plain IEEE 754 bit manipulations: float ->
+// double is exact (the exponent rebiased by 1023 - 127 = 896, the 23-bit
+// significand shifted into the top of the 52-bit one); double -> float keeps
+// the top 23 significand bits and rounds to nearest, ties to even, on the
+// discarded 29 (a carry out of the significand increments the exponent, and
+// out of the largest finite exponent gives infinity, as rounding does).
+// Zeros are handled here; subnormal, infinite and NaN operands (and results
+// that would be subnormal) take the conversion instruction, in a function of
+// its own: inlined, the compiler evaluated it on every path (ncu: the FP64 pipe
+// as busy as before).
+static __device__ __noinline__ double f2d_rare(float f) { return (double)f; }
+static __device__ __noinline__ float d2f_rare(double d) { return __double2float_rn(d); }
+__device__ __forceinline__ double f2d_exact(float f)
+{
+    const unsigned u = __float_as_uint(f), e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+    if (e - 1u >= 0xfeu) {  // e == 0 or e == 255
+        if (e == 0u && m == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
+        return f2d_rare(f);
+    }
+    return __hiloint2double((int)((u & 0x80000000u) | ((e + 896u) << 20) | (m >> 3)), (int)(m << 29));
+}
+__device__ __forceinline__ float d2f_rn(double d)
+{
+    const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+    const unsigned e = (hi >> 20) & 0x7ffu;
+    if (e - 897u > 253u) {  // zero, or a result outside the normal float range
+        if (e == 0u && (hi & 0xfffffu) == 0u && lo == 0u) return __uint_as_float(hi & 0x80000000u);
+        return d2f_rare(d);
+    }
+    unsigned f = (hi & 0x80000000u) | ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const unsigned rem = lo & 0x1fffffffu;
+    if (rem > 0x10000000u || (rem == 0x10000000u && (f & 1u))) ++f;
+    return __uint_as_float(f);
+}
+
 // --- error-free transformations ---------------------------------------------
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
 {
@@ -91,6 +129,16 @@ __device__ __forceinline__ df64 &operator+=(df64 &a, df64 b) { return a = a + b;
 __device__ __forceinline__ df64 &operator-=(df64 &a, df64 b) { return a = a - b; }
 __device__ __forceinline__ df64 &operator*=(df64 &a, df64 b) { return a = a * b; }
 
+// a double as the nearest float and the float nearest its remainder (the value
+// of df64(double), on the integer pipe but for the one exact subtraction)
+__device__ __forceinline__ df64 from_double(double d)
+{
+    const float h = d2f_rn(d);
+    return df64(h, d2f_rn(d - f2d_exact(h)));
+}
+// hi + lo rounded to double (the value of double(df64))
+__device__ __forceinline__ double to_double(df64 a) { return f2d_exact(a.hi) + f2d_exact(a.lo); }
+
 // --- comparisons (lexicographic on hi, lo) -----------------------------------------
 __device__ __forceinline__ bool operator<(df64 a, df64 b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
 __device__ __forceinline__ bool operator>(df64 a, df64 b) { return b < a; }
@@ -123,4 +171,8 @@ __device__ __forceinline__ df64 sin(df64 a) { return df64(::sin((double)a)); }
 
 }  // namespace dfl
 using dfl::df64;
+using dfl::d2f_rn;
+using dfl::f2d_exact;
+using dfl::from_double;
+using dfl::to_double;
 }  // namespace wec

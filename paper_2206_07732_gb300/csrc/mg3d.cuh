@@ -113,8 +113,13 @@ __global__ void __launch_bounds__(128) k3_rbgs_pk(int nx, int ny, int nz, const 
         if (first) {
             x[(1 - color) * nh + q] = T(0);  // (i ^ 1, j, k)
         } else if (out) {
-            out[c] = double(v[u]);
-            out[c ^ 1] = double(w[u]);
+            if constexpr (std::is_same<T, float>::value) {  // (double) on the integer pipe
+                out[c] = f2d_exact(v[u]);
+                out[c ^ 1] = f2d_exact(w[u]);
+            } else {
+                out[c] = double(v[u]);
+                out[c ^ 1] = double(w[u]);
+            }
         }
     }
 }
@@ -467,7 +472,8 @@ __global__ void __launch_bounds__(256) k3_unpack(int nx, int ny, int nz, const f
     if (c >= nx * ny * nz) return;
     out = at_sel(out, outsel, (long long)nx * ny * nz);
     const int r = c / nx, i = c - r * nx, k = r / ny, j = r - k * ny;
-    out[c] = TO(x[ix3(pk, nx, ny, nz, i, j, k)]);
+    const float v = x[ix3(pk, nx, ny, nz, i, j, k)];
+    if constexpr (std::is_same<TO, double>::value) out[c] = f2d_exact(v); else out[c] = v;
 }
 
 // x0 = M^{-1} b0, one V-cycle over the 3D levels L (precision T).  FP32: x0

@@ -21,6 +21,7 @@
 
 #include <cooperative_groups.h>
 
+#include "df64.cuh"
 #include "internal.cuh"
 #include "poisson_op.cuh"
 
@@ -139,7 +140,7 @@ __global__ void k_widen(long long n, const float *__restrict__ in, double *out, 
     long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (c >= n) return;
     out = at_sel(out, outsel, n);
-    out[c] = double(in[c]);
+    out[c] = f2d_exact(in[c]);
 }
 
 template <typename TO, typename TI>
@@ -149,7 +150,12 @@ __global__ void k_convert(long long n, const TI *__restrict__ in, TO *__restrict
     long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (c >= n) return;
     in = at_sel(in, insel, n);
-    out[c] = TO(in[c]);
+    if constexpr (std::is_same<TO, float>::value && std::is_same<TI, double>::value)
+        out[c] = d2f_rn(in[c]);
+    else if constexpr (std::is_same<TO, double>::value && std::is_same<TI, float>::value)
+        out[c] = f2d_exact(in[c]);
+    else
+        out[c] = TO(in[c]);
 }
 
 // Dense LU of the coarsest operator (no pivoting: A is a symmetric M-matrix).
@@ -564,7 +570,7 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 4)
         }
         double r = b[c] - (d0[c] * x[c] - op_offsum<D>(op, x, c));
         w[c] = r;
-        if (b32) b32[c] = (float)r;
+        if (b32) b32[c] = d2f_rn(r);  // (float)r on the integer pipe
         a += r * r;
     }
     a = block_sum(a, sh);
@@ -703,7 +709,7 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 4)
 #pragma unroll 4
         for (int k = 0; k <= j; ++k) a -= hs[k] * V[(long long)k * n + c];
         w[c] = a;
-        if (b32) b32[c] = (float)a;
+        if (b32) b32[c] = d2f_rn(a);
         a2 += a * a;
     }
     a2 = block_sum(a2, sh);

@@ -126,6 +126,24 @@ template <typename R>
 constexpr bool is_f64 = std::is_same<R, double>::value;
 template <typename R>
 constexpr bool is_df = std::is_same<R, df64>::value;
+// FP64 state <-> working type, the conversions on the integer pipe (df64.cuh)
+template <typename R>
+__device__ __forceinline__ R narrow_r(double d)
+{
+    if constexpr (is_f64<R>) return d; else if constexpr (is_df<R>) return from_double(d); else return d2f_rn(d);
+}
+template <typename R>
+__device__ __forceinline__ double widen_r(R a)
+{
+    if constexpr (is_f64<R>) return a; else if constexpr (is_df<R>) return to_double(a); else return f2d_exact(a);
+}
+// k x for k a power of two (2 or 1/2 here): exact; for a float pair, both
+// floats scaled (the value of the full pair product, in two multiplications)
+template <typename R>
+__device__ __forceinline__ R scl2(float k, R x)
+{
+    if constexpr (is_df<R>) return R(k * x.hi, k * x.lo); else return R(k) * x;
+}
 
 template <typename R>
 __device__ __forceinline__ const Tank3C<R> &cst3(const Tank3P &P)
@@ -145,7 +163,7 @@ __device__ __forceinline__ R heav3(R phi, R eps, R ieps)
     if (phi < -eps) return R(0);
     if (phi > eps) return R(1);
     const R r = phi * ieps;
-    return R(0.5) * (R(1) + r + sin(R(kPi3) * r) * R(1.0 / kPi3));
+    return scl2<R>(0.5f, R(1) + r + sin(R(kPi3) * r) * R(1.0 / kPi3));
 }
 
 // The incident surface at the three ghost columns x = -(m + 1/2) h, m = 0, 1, 2,
@@ -215,7 +233,7 @@ __device__ __forceinline__ R vl3(R am, R a0, R ap)
 {
     const R dl = a0 - am, dr = ap - a0;
     if (nonpos_prod(dl, dr)) return R(0);
-    const R dc = R(0.5) * (ap - am), tl = R(2) * dl, tr = R(2) * dr;
+    const R dc = scl2<R>(0.5f, ap - am), tl = scl2<R>(2.f, dl), tr = scl2<R>(2.f, dr);
     if constexpr (is_f64<R>) {
         unsigned long long m = mag_bits(dc);
         const unsigned long long ml = mag_bits(tl), mr = mag_bits(tr);
@@ -244,18 +262,18 @@ __device__ __forceinline__ void ppm_edges3(const R *a, R &eL, R &eR)
 {
     const R i6 = R(1.0 / 6.0);
     const R dm = vl3(a[0], a[1], a[2]), d0 = vl3(a[1], a[2], a[3]), dp = vl3(a[2], a[3], a[4]);
-    R L = a[1] + R(0.5) * (a[2] - a[1]) - (d0 - dm) * i6;
-    R Rr = a[2] + R(0.5) * (a[3] - a[2]) - (dp - d0) * i6;
+    R L = a[1] + scl2<R>(0.5f, a[2] - a[1]) - (d0 - dm) * i6;
+    R Rr = a[2] + scl2<R>(0.5f, a[3] - a[2]) - (dp - d0) * i6;
     const R c = a[2];
     if (nonpos_prod(Rr - c, c - L)) {
         L = c;
         Rr = c;
     } else {
-        const R dA = Rr - L, m6 = dA * (c - R(0.5) * (L + Rr)), q = dA * dA * i6;
+        const R dA = Rr - L, m6 = dA * (c - scl2<R>(0.5f, L + Rr)), q = dA * dA * i6;
         if (gt_nonneg(m6, q))
-            L = R(3) * c - R(2) * Rr;
+            L = R(3) * c - scl2<R>(2.f, Rr);
         else if (gt_nonneg(-m6, q))
-            Rr = R(3) * c - R(2) * L;
+            Rr = R(3) * c - scl2<R>(2.f, L);
     }
     eL = L;
     eR = Rr;
@@ -281,8 +299,8 @@ __device__ __forceinline__ R ppm_face3(const R *a, R vel, R dtih)
     for (int m = 0; m < 5; ++m) b[m] = up ? a[m] : a[m + 1];
     R L, Rr;
     ppm_edges3(b, L, Rr);
-    const R C = (up ? vel : -vel) * dtih, dA = Rr - L, a6 = R(6) * (b[2] - R(0.5) * (L + Rr));
-    const R e = (R(1) - C * t3) * a6, hc = R(0.5) * C;
+    const R C = (up ? vel : -vel) * dtih, dA = Rr - L, a6 = R(6) * (b[2] - scl2<R>(0.5f, L + Rr));
+    const R e = (R(1) - C * t3) * a6, hc = scl2<R>(0.5f, C);
     return (up ? Rr : L) + (up ? -hc : hc) * (dA + (up ? -e : e));
 }
 
@@ -318,7 +336,7 @@ __global__ void __launch_bounds__(128) k3t_materials(Tank3P P, const R *__restri
     if (P.has_body) {
         const R x = (R(q.i) + R(0.5)) * h - K.bxc, y = (R(q.j) + R(0.5)) * h - K.byc,
                 z = (R(q.k) + R(0.5)) * h - zc;
-        psi = fmax(sqrt(x * x + y * y) - K.br, fabs(z) - R(0.5) * K.blen);
+        psi = fmax(sqrt(x * x + y * y) - K.br, fabs(z) - scl2<R>(0.5f, K.blen));
     }
     const R hf = heav3<R>(sig[q.c], h, K.ih), hb = heav3<R>(psi, h, K.ih);
     const R rf = K.rho_w + (K.rho_a - K.rho_w) * hf;
@@ -371,7 +389,7 @@ __global__ void __launch_bounds__(128) k3t_advect(Tank3P P, const R *__restrict_
             const R fv2 = ppm_face3<R>(a, vel[f * vs], dtih);
             if (f == 0) F0 = fv2; else F1 = fv2;
         }
-        const R vb = R(0.5) * (vel[0] + vel[vs]);
+        const R vb = scl2<R>(0.5f, vel[0] + vel[vs]);
         Q = Q + vb * (F1 - F0) * ih;
     }
     const R sa = base[q.c] - dt * Q;
@@ -420,9 +438,9 @@ __device__ __forceinline__ R reinit_rhs3(const Tank3P &P, const R *__restrict__ 
             p1 = sig3<R>(P, f, q.i + di, q.j + dj, q.k + dk, G);
             p2 = sig3<R>(P, f, q.i + 2 * di, q.j + 2 * dj, q.k + 2 * dk, G);
         }
-        const R dm = m2 - R(2) * m1 + c, d0 = m1 - R(2) * c + p1, dp = c - R(2) * p1 + p2;
-        const R a = (c - m1) + R(0.5) * mm3(dm, d0);
-        const R nb = (c - p1) + R(0.5) * mm3(d0, dp);  // -b
+        const R dm = m2 - scl2<R>(2.f, m1) + c, d0 = m1 - scl2<R>(2.f, c) + p1, dp = c - scl2<R>(2.f, p1) + p2;
+        const R a = (c - m1) + scl2<R>(0.5f, mm3(dm, d0));
+        const R nb = (c - p1) + scl2<R>(0.5f, mm3(d0, dp));  // -b
         // pos: the largest of a, -b and 0; else of -a, b and 0
         const R x = pos ? a : -a, y = pos ? nb : -nb;
         R m = positive(x) ? x : R(0);
@@ -458,7 +476,7 @@ __global__ void __launch_bounds__(128) k3t_reinit_stage(Tank3P P, const R *__res
     Cell3 q;
     if (!cell_of(P, q)) return;
     const R y = f[q.c] - dtau * reinit_rhs3<R>(P, f, sg, q, G);
-    out[q.c] = stage == 1 ? y : R(0.5) * (out[q.c] + y);
+    out[q.c] = stage == 1 ? y : scl2<R>(0.5f, out[q.c] + y);
 }
 
 // ------------------------------------------------------------ the step ----
@@ -500,7 +518,7 @@ __device__ __forceinline__ R wq(const Tank3P &P, const R *__restrict__ w, const 
     k = min(max(k, 0), P.nz);
     j = min(max(j, 0), P.ny - 1);
     if (i > P.nx - 1) i = P.nx - 1;
-    if (i < 0) return R(2) * win[k] - w[((long long)k * P.ny + j) * P.nx + (-1 - i)];
+    if (i < 0) return scl2<R>(2.f, win[k]) - w[((long long)k * P.ny + j) * P.nx + (-1 - i)];
     return w[((long long)k * P.ny + j) * P.nx + i];
 }
 
@@ -513,16 +531,16 @@ __device__ __forceinline__ R koren3(R quu, R qu, R qd)
     const R d1 = qu - quu, d2 = qd - qu;
     if (nonpos_prod(d1, d2)) return qu;
     if constexpr (is_f64<R>) {
-        const R t2 = R(2) * d2, t1 = R(2) * d1, tm = (fabs(d1) + fabs(t2)) * R(1.0 / 3.0);
+        const R t2 = scl2<R>(2.f, d2), t1 = scl2<R>(2.f, d1), tm = (fabs(d1) + fabs(t2)) * R(1.0 / 3.0);
         unsigned long long m = mag_bits(t2);
         const unsigned long long mm = mag_bits(tm), m1 = mag_bits(t1);
         m = mm < m ? mm : m;
         m = m1 < m ? m1 : m;
         const unsigned long long sgn = (unsigned long long)__double_as_longlong(d1) & 0x8000000000000000ull;
-        return qu + R(0.5) * __longlong_as_double((long long)((m >> 1) | sgn));
+        return qu + scl2<R>(0.5f, __longlong_as_double((long long)((m >> 1) | sgn)));
     } else {
-        const R m = fmin(R(2) * fabs(d2), fmin((fabs(d1) + R(2) * fabs(d2)) * R(1.0 / 3.0), R(2) * fabs(d1)));
-        return d1 > R(0) ? qu + R(0.5) * m : qu - R(0.5) * m;
+        const R m = fmin(scl2<R>(2.f, fabs(d2)), fmin((fabs(d1) + scl2<R>(2.f, fabs(d2))) * R(1.0 / 3.0), scl2<R>(2.f, fabs(d1))));
+        return d1 > R(0) ? qu + scl2<R>(0.5f, m) : qu - scl2<R>(0.5f, m);
     }
 }
 template <typename R>
@@ -545,7 +563,7 @@ __device__ __forceinline__ R ruq(const Tank3P &P, const R *rc, int i, int j, int
         j = min(max(j, 0), P.ny - 1);
         k = min(max(k, 0), P.nz - 1);
     }
-    return R(0.5) * (cellq<IN>(P, rc, i - 1, j, k) + cellq<IN>(P, rc, i, j, k));
+    return scl2<R>(0.5f, cellq<IN>(P, rc, i - 1, j, k) + cellq<IN>(P, rc, i, j, k));
 }
 template <bool IN, typename R>
 __device__ __forceinline__ R rvq(const Tank3P &P, const R *rc, int i, int j, int k)
@@ -555,7 +573,7 @@ __device__ __forceinline__ R rvq(const Tank3P &P, const R *rc, int i, int j, int
         j = min(max(j, 0), P.ny);
         k = min(max(k, 0), P.nz - 1);
     }
-    return R(0.5) * (cellq<IN>(P, rc, i, j - 1, k) + cellq<IN>(P, rc, i, j, k));
+    return scl2<R>(0.5f, cellq<IN>(P, rc, i, j - 1, k) + cellq<IN>(P, rc, i, j, k));
 }
 template <bool IN, typename R>
 __device__ __forceinline__ R rwq(const Tank3P &P, const R *rc, int i, int j, int k)
@@ -565,7 +583,7 @@ __device__ __forceinline__ R rwq(const Tank3P &P, const R *rc, int i, int j, int
         j = min(max(j, 0), P.ny - 1);
         k = min(max(k, 0), P.nz);
     }
-    return R(0.5) * (cellq<IN>(P, rc, i, j, k - 1) + cellq<IN>(P, rc, i, j, k));
+    return scl2<R>(0.5f, cellq<IN>(P, rc, i, j, k - 1) + cellq<IN>(P, rc, i, j, k));
 }
 
 template <typename R>
@@ -620,20 +638,20 @@ __device__ __forceinline__ void transport3(const Tank3P &P, const R *__restrict_
             R U;
             if (d == comp) {  // CV faces at the cell centres on either side
                 const int o = s - 1;
-                U = comp == 0   ? R(0.5) * (uq<IN>(P, V.u, i + o, j, k) + uq<IN>(P, V.u, i + o + 1, j, k))
-                    : comp == 1 ? R(0.5) * (vq<IN>(P, V.v, i, j + o, k) + vq<IN>(P, V.v, i, j + o + 1, k))
-                                : R(0.5) * (wq<IN>(P, V.w, V.win, i, j, k + o) + wq<IN>(P, V.w, V.win, i, j, k + o + 1));
+                U = comp == 0   ? scl2<R>(0.5f, uq<IN>(P, V.u, i + o, j, k) + uq<IN>(P, V.u, i + o + 1, j, k))
+                    : comp == 1 ? scl2<R>(0.5f, vq<IN>(P, V.v, i, j + o, k) + vq<IN>(P, V.v, i, j + o + 1, k))
+                                : scl2<R>(0.5f, wq<IN>(P, V.w, V.win, i, j, k + o) + wq<IN>(P, V.w, V.win, i, j, k + o + 1));
             } else {  // CV faces on the edges: the d-velocity averaged over the comp direction
                 const int e = s;
                 if (d == 0)
-                    U = comp == 1 ? R(0.5) * (uq<IN>(P, V.u, i + e, j - 1, k) + uq<IN>(P, V.u, i + e, j, k))
-                                  : R(0.5) * (uq<IN>(P, V.u, i + e, j, k - 1) + uq<IN>(P, V.u, i + e, j, k));
+                    U = comp == 1 ? scl2<R>(0.5f, uq<IN>(P, V.u, i + e, j - 1, k) + uq<IN>(P, V.u, i + e, j, k))
+                                  : scl2<R>(0.5f, uq<IN>(P, V.u, i + e, j, k - 1) + uq<IN>(P, V.u, i + e, j, k));
                 else if (d == 1)
-                    U = comp == 0 ? R(0.5) * (vq<IN>(P, V.v, i - 1, j + e, k) + vq<IN>(P, V.v, i, j + e, k))
-                                  : R(0.5) * (vq<IN>(P, V.v, i, j + e, k - 1) + vq<IN>(P, V.v, i, j + e, k));
+                    U = comp == 0 ? scl2<R>(0.5f, vq<IN>(P, V.v, i - 1, j + e, k) + vq<IN>(P, V.v, i, j + e, k))
+                                  : scl2<R>(0.5f, vq<IN>(P, V.v, i, j + e, k - 1) + vq<IN>(P, V.v, i, j + e, k));
                 else
-                    U = comp == 0 ? R(0.5) * (wq<IN>(P, V.w, V.win, i - 1, j, k + e) + wq<IN>(P, V.w, V.win, i, j, k + e))
-                                  : R(0.5) * (wq<IN>(P, V.w, V.win, i, j - 1, k + e) + wq<IN>(P, V.w, V.win, i, j, k + e));
+                    U = comp == 0 ? scl2<R>(0.5f, wq<IN>(P, V.w, V.win, i - 1, j, k + e) + wq<IN>(P, V.w, V.win, i, j, k + e))
+                                  : scl2<R>(0.5f, wq<IN>(P, V.w, V.win, i, j - 1, k + e) + wq<IN>(P, V.w, V.win, i, j, k + e));
             }
             const int a0 = s - 1;  // the stencil runs over (base + a0 - 1 .. base + a0 + 2) along d
             const int di = d == 0, dj = d == 1, dk = d == 2;
@@ -694,32 +712,32 @@ __device__ __forceinline__ void offdiag3(const Tank3P &P, const R *__restrict__ 
         const R m1 = cellq<IN>(P, mu, i, j, k), m0 = cellq<IN>(P, mu, i - 1, j, k);
         const R e1 = exy_at<IN>(P, E.xy, i, j + 1, k), e0 = exy_at<IN>(P, E.xy, i, j, k);
         const R f1 = exz_at<IN>(P, E.xz, i, j, k + 1), f0 = exz_at<IN>(P, E.xz, i, j, k);
-        S = R(2) * (m1 * U3(i + 1, j, k) + m0 * U3(i - 1, j, k)) +
+        S = scl2<R>(2.f, m1 * U3(i + 1, j, k) + m0 * U3(i - 1, j, k)) +
             ((e1 * ((U3(i, j + 1, k) + V3(i, j + 1, k)) - V3(i - 1, j + 1, k)) +
               e0 * ((U3(i, j - 1, k) - V3(i, j, k)) + V3(i - 1, j, k))) +
              (f1 * ((U3(i, j, k + 1) + W3(i, j, k + 1)) - W3(i - 1, j, k + 1)) +
               f0 * ((U3(i, j, k - 1) - W3(i, j, k)) + W3(i - 1, j, k))));
-        Lc = R(2) * (m1 + m0) + ((e1 + e0) + (f1 + f0));
+        Lc = scl2<R>(2.f, m1 + m0) + ((e1 + e0) + (f1 + f0));
     } else if (comp == 1) {
         const R m1 = cellq<IN>(P, mu, i, j, k), m0 = cellq<IN>(P, mu, i, j - 1, k);
         const R e1 = exy_at<IN>(P, E.xy, i + 1, j, k), e0 = exy_at<IN>(P, E.xy, i, j, k);
         const R f1 = eyz_at<IN>(P, E.yz, i, j, k + 1), f0 = eyz_at<IN>(P, E.yz, i, j, k);
-        S = R(2) * (m1 * V3(i, j + 1, k) + m0 * V3(i, j - 1, k)) +
+        S = scl2<R>(2.f, m1 * V3(i, j + 1, k) + m0 * V3(i, j - 1, k)) +
             ((e1 * ((V3(i + 1, j, k) + U3(i + 1, j, k)) - U3(i + 1, j - 1, k)) +
               e0 * ((V3(i - 1, j, k) - U3(i, j, k)) + U3(i, j - 1, k))) +
              (f1 * ((V3(i, j, k + 1) + W3(i, j, k + 1)) - W3(i, j - 1, k + 1)) +
               f0 * ((V3(i, j, k - 1) - W3(i, j, k)) + W3(i, j - 1, k))));
-        Lc = R(2) * (m1 + m0) + ((e1 + e0) + (f1 + f0));
+        Lc = scl2<R>(2.f, m1 + m0) + ((e1 + e0) + (f1 + f0));
     } else {
         const R m1 = cellq<IN>(P, mu, i, j, k), m0 = cellq<IN>(P, mu, i, j, k - 1);
         const R e1 = exz_at<IN>(P, E.xz, i + 1, j, k), e0 = exz_at<IN>(P, E.xz, i, j, k);
         const R f1 = eyz_at<IN>(P, E.yz, i, j + 1, k), f0 = eyz_at<IN>(P, E.yz, i, j, k);
-        S = R(2) * (m1 * W3(i, j, k + 1) + m0 * W3(i, j, k - 1)) +
+        S = scl2<R>(2.f, m1 * W3(i, j, k + 1) + m0 * W3(i, j, k - 1)) +
             ((e1 * ((W3(i + 1, j, k) + U3(i + 1, j, k)) - U3(i + 1, j, k - 1)) +
               e0 * ((W3(i - 1, j, k) - U3(i, j, k)) + U3(i, j, k - 1))) +
              (f1 * ((W3(i, j + 1, k) + V3(i, j + 1, k)) - V3(i, j + 1, k - 1)) +
               f0 * ((W3(i, j - 1, k) - V3(i, j, k)) + V3(i, j, k - 1))));
-        Lc = R(2) * (m1 + m0) + ((e1 + e0) + (f1 + f0));
+        Lc = scl2<R>(2.f, m1 + m0) + ((e1 + e0) + (f1 + f0));
     }
 #undef U3
 #undef V3
@@ -817,19 +835,19 @@ __device__ __forceinline__ void momentum_finish(const Tank3P &P, const MomIn<R> 
     const R visc = (S - Lc * uc) * M.ih2;
     const double ih = P.ih;
     const int ci = comp == 0 ? i - 1 : i, cj = comp == 1 ? j - 1 : j, ck = comp == 2 ? k - 1 : k;
-    const R chi = R(0.5) * (cellq<IN>(P, M.chi1, ci, cj, ck) + cellq<IN>(P, M.chi1, i, j, k));
+    const R chi = scl2<R>(0.5f, cellq<IN>(P, M.chi1, ci, cj, ck) + cellq<IN>(P, M.chi1, i, j, k));
     const R al = comp == 0 ? M.dampu[i] : dampc<R>(P, i);
     const R vd = comp == 2 ? M.vortf[k] : M.vortc[k];
     const R rbdt = rb * M.idt;
     Dout[f] = rbdt + chi * M.ikp + al * rbdt + vd;
     const double pc = k < P.nz ? M.p[((long long)k * P.ny + j) * P.nx + i] : 0.0;
-    const R adv = frq<IN>(P, M.rfc[comp], comp, i, j, k) * uc * M.idt - C + R(0.5) * visc;
+    const R adv = frq<IN>(P, M.rfc[comp], comp, i, j, k) * uc * M.idt - C + scl2<R>(0.5f, visc);
     if (comp == 0) {
         Rout[f] = adv - R((pc - M.p[((long long)k * P.ny + j) * P.nx + i - 1]) * ih);
     } else if (comp == 1) {
         Rout[f] = adv - R((pc - M.p[((long long)k * P.ny + j - 1) * P.nx + i]) * ih);
     } else {
-        const R rf = R(0.5) * (cellq<IN>(P, M.rf1, i, j, k - 1) + cellq<IN>(P, M.rf1, i, j, k));
+        const R rf = scl2<R>(0.5f, cellq<IN>(P, M.rf1, i, j, k - 1) + cellq<IN>(P, M.rf1, i, j, k));
         const double pb = M.p[((long long)(k - 1) * P.ny + j) * P.nx + i];
         const double gp = k < P.nz ? (pc - pb) * ih : -2.0 * pb * ih;
         Rout[f] = adv - rf * M.g + chi * M.zd1 * M.ikp - R(gp);
@@ -910,18 +928,18 @@ __global__ void __launch_bounds__(128) k3t_jprep(Tank3P P, const R *__restrict__
     if (!face_of(P, COMP, i, j, k, f)) return;
     R Lc;
     if (COMP == 0)
-        Lc = R(2) * (cellq<false>(P, mu1, i, j, k) + cellq<false>(P, mu1, i - 1, j, k)) +
+        Lc = scl2<R>(2.f, cellq<false>(P, mu1, i, j, k) + cellq<false>(P, mu1, i - 1, j, k)) +
              ((exy_at<false>(P, E.xy, i, j + 1, k) + exy_at<false>(P, E.xy, i, j, k)) +
               (exz_at<false>(P, E.xz, i, j, k + 1) + exz_at<false>(P, E.xz, i, j, k)));
     else if (COMP == 1)
-        Lc = R(2) * (cellq<false>(P, mu1, i, j, k) + cellq<false>(P, mu1, i, j - 1, k)) +
+        Lc = scl2<R>(2.f, cellq<false>(P, mu1, i, j, k) + cellq<false>(P, mu1, i, j - 1, k)) +
              ((exy_at<false>(P, E.xy, i + 1, j, k) + exy_at<false>(P, E.xy, i, j, k)) +
               (eyz_at<false>(P, E.yz, i, j, k + 1) + eyz_at<false>(P, E.yz, i, j, k)));
     else
-        Lc = R(2) * (cellq<false>(P, mu1, i, j, k) + cellq<false>(P, mu1, i, j, k - 1)) +
+        Lc = scl2<R>(2.f, cellq<false>(P, mu1, i, j, k) + cellq<false>(P, mu1, i, j, k - 1)) +
              ((exz_at<false>(P, E.xz, i + 1, j, k) + exz_at<false>(P, E.xz, i, j, k)) +
               (eyz_at<false>(P, E.yz, i, j + 1, k) + eyz_at<false>(P, E.yz, i, j, k)));
-    const R hi2 = R(0.5) * ih2;
+    const R hi2 = scl2<R>(0.5f, ih2);
     const R inv = R(1) / (D[f] + hi2 * Lc);
     Rr[f] = Rr[f] * inv;
     Qo[f] = hi2 * inv;
@@ -980,24 +998,19 @@ __global__ void __launch_bounds__(256) k3t_dup(long long n, const R *__restrict_
     b[q] = v;
 }
 
-// beta = 1 / D on the solved faces, 0 on the walls and the bed (FP64 coefficients)
+// beta = 1 / D on the solved faces, 0 on the walls and the bed (FP64 coefficients);
+// one block row per face row (gridf)
 template <typename R>
-__global__ void k3t_beta(Tank3P P, int comp, const R *__restrict__ D, double *__restrict__ beta, long long n)
+__global__ void __launch_bounds__(128) k3t_beta(Tank3P P, int comp, const R *__restrict__ D,
+                                                double *__restrict__ beta)
 {
     pdl_entry();
-    const long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (f >= n) return;
-    bool wall;
-    if (comp == 0) {
-        const int i = (int)(f % (P.nx + 1));
-        wall = i == 0 || i == P.nx;
-    } else if (comp == 1) {
-        const int j = (int)((f / P.nx) % (P.ny + 1));
-        wall = j == 0 || j == P.ny;
-    } else {
-        wall = f < (long long)P.nx * P.ny;
-    }
-    beta[f] = wall ? 0.0 : double(R(1) / D[f]);
+    const int nxf = P.nx + (comp == 0), nyf = P.ny + (comp == 1);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    if (i >= nxf) return;
+    const long long f = ((long long)k * nyf + j) * nxf + i;
+    const bool wall = comp == 0 ? (i == 0 || i == P.nx) : comp == 1 ? (j == 0 || j == P.ny) : k == 0;
+    beta[f] = wall ? 0.0 : widen_r<R>(R(1) / D[f]);
 }
 
 // rhs = -h div u* (FP64 from the predictor's values)
@@ -1010,36 +1023,34 @@ __global__ void __launch_bounds__(128) k3t_rhs(Tank3P P, Vel3<R> S, double *__re
     const int nx = P.nx, ny = P.ny;
     const long long fu = ((long long)q.k * ny + q.j) * (nx + 1) + q.i, fv = ((long long)q.k * (ny + 1) + q.j) * nx + q.i;
     const long long pl = (long long)nx * ny;
-    rhs[q.c] = -P.h * (((double(S.u[fu + 1]) - double(S.u[fu])) + (double(S.v[fv + nx]) - double(S.v[fv]))) +
-                       (double(S.w[q.c + pl]) - double(S.w[q.c])));
+    rhs[q.c] = -P.h * (((widen_r<R>(S.u[fu + 1]) - widen_r<R>(S.u[fu])) +
+                        (widen_r<R>(S.v[fv + nx]) - widen_r<R>(S.v[fv]))) +
+                       (widen_r<R>(S.w[q.c + pl]) - widen_r<R>(S.w[q.c])));
 }
 
 // u^{n+1} = u* - beta grad phi in FP64 (top w face: the ghost -phi); p += phi
 template <typename R>
-__global__ void k3t_project(Tank3P P, int comp, const R *__restrict__ S, const double *__restrict__ beta,
-                            const double *__restrict__ phi, double *__restrict__ out, long long n)
+__global__ void __launch_bounds__(128) k3t_project(Tank3P P, int comp, const R *__restrict__ S,
+                                                   const double *__restrict__ beta, const double *__restrict__ phi,
+                                                   double *__restrict__ out)
 {
     pdl_entry();
-    const long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (f >= n) return;
-    const int nx = P.nx, ny = P.ny, nz = P.nz;
-    const double ih = 1.0 / P.h;
-    double a = double(S[f]);
+    const int nx = P.nx, ny = P.ny, nz = P.nz, nxf = nx + (comp == 0), nyf = ny + (comp == 1);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    if (i >= nxf) return;
+    const long long f = ((long long)k * nyf + j) * nxf + i;
+    const double ih = P.ih;
+    double a = widen_r<R>(S[f]);
     if (comp == 0) {
-        const int i = (int)(f % (nx + 1));
-        const long long r = f / (nx + 1);
-        if (i > 0 && i < nx) a -= beta[f] * (phi[r * nx + i] - phi[r * nx + i - 1]) * ih;
+        const long long c = ((long long)k * ny + j) * nx + i;
+        if (i > 0 && i < nx) a -= beta[f] * (phi[c] - phi[c - 1]) * ih;
     } else if (comp == 1) {
-        const int i = (int)(f % nx);
-        const long long q = f / nx;
-        const int j = (int)(q % (ny + 1)), k = (int)(q / (ny + 1));
         if (j > 0 && j < ny) {
             const long long c = ((long long)k * ny + j) * nx + i;
             a -= beta[f] * (phi[c] - phi[c - nx]) * ih;
         }
     } else {
         const long long pl = (long long)nx * ny;
-        const int k = (int)(f / pl);
         if (k > 0 && k < nz) a -= beta[f] * (phi[f] - phi[f - pl]) * ih;
         if (k == nz) a += 2.0 * beta[f] * phi[f - pl] * ih;
     }
@@ -1060,14 +1071,14 @@ __global__ void k3t_narrow(long long n, const double *__restrict__ in, R *__rest
 {
     pdl_entry();
     const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (c < n) out[c] = R(in[c]);
+    if (c < n) out[c] = narrow_r<R>(in[c]);
 }
 template <typename R>
 __global__ void k3t_widen(long long n, const R *__restrict__ in, double *__restrict__ out)
 {
     pdl_entry();
     const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (c < n) out[c] = double(in[c]);
+    if (c < n) out[c] = widen_r<R>(in[c]);
 }
 // the mean of two time levels: out = (a + b) / 2 (b in the working type or FP64)
 template <typename R, typename RB>
@@ -1075,7 +1086,11 @@ __global__ void k3t_mean(long long n, const R *__restrict__ a, const RB *__restr
 {
     pdl_entry();
     const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (c < n) out[c] = R(0.5) * (a[c] + R(b[c]));
+    if (c >= n) return;
+    if constexpr (std::is_same<RB, double>::value)
+        out[c] = scl2<R>(0.5f, a[c] + narrow_r<R>(b[c]));
+    else
+        out[c] = scl2<R>(0.5f, a[c] + b[c]);
 }
 
 constexpr int kRT = 256;  // threads of the reduction kernels
@@ -1167,16 +1182,18 @@ __global__ void __launch_bounds__(kRT) k3t_div2(Tank3P P, Vel3<double> S, double
 {
     pdl_entry();
     __shared__ double sh[kRT];
-    const long long n = (long long)P.nx * P.ny * P.nz;
     double a = 0.0;
-    for (long long c = blockIdx.x * (long long)kRT + threadIdx.x; c < n; c += (long long)gridDim.x * kRT) {
-        const int i = (int)(c % P.nx);
-        const long long r = c / P.nx;
-        const int j = (int)(r % P.ny), k = (int)(r / P.ny);
-        const long long fu = r * (P.nx + 1) + i, fv = ((long long)k * (P.ny + 1) + j) * P.nx + i;
-        const double d = P.h * (((S.u[fu + 1] - S.u[fu]) + (S.v[fv + P.nx] - S.v[fv])) +
-                                (S.w[c + (long long)P.nx * P.ny] - S.w[c]));
-        a += d * d;
+    // row by row (one 32-bit division per row, none per cell)
+    const int nx = P.nx, ny = P.ny;
+    const long long rows = (long long)ny * P.nz, pl = (long long)nx * ny;
+    for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
+        const int k = (int)(r / ny), j = (int)(r - (long long)k * ny);
+        const long long c0 = r * nx, fu0 = r * (nx + 1), fv0 = ((long long)k * (ny + 1) + j) * nx;
+        for (int i = threadIdx.x; i < nx; i += kRT) {
+            const double d = P.h * (((S.u[fu0 + i + 1] - S.u[fu0 + i]) + (S.v[fv0 + i + nx] - S.v[fv0 + i])) +
+                                    (S.w[c0 + i + pl] - S.w[c0 + i]));
+            a += d * d;
+        }
     }
     const double s = block_sum3(a, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = s;
@@ -1273,6 +1290,11 @@ __global__ void __launch_bounds__(128) k3t_inflow(Tank3P P, double t0, double t1
 }
 
 dim3 grid3(const Tank3P &P) { return dim3((P.nx + 127) / 128, P.ny, P.nz); }
+// the faces of component comp, one 128-thread row per face row
+dim3 gridf(const Tank3P &P, int comp)
+{
+    return dim3((P.nx + (comp == 0) + 127) / 128, P.ny + (comp == 1), P.nz + (comp == 2));
+}
 
 int tank3_check(const wec_tank3 *T)
 {
@@ -1596,8 +1618,7 @@ static int tank3_step_impl(wec_tank3 *T, Work3<R> &W, double dt, double pto_forc
         section(7);
         // (7) pressure increment: beta = 1 / D, b = -h div u* (FP64), phi from zero
         for (int c = 0; c < 3; ++c)
-            launch_k(k3t_beta<R>, nblk((long long)nf[c], 256), 256, 0, st, P, c, (const R *)W.D[c], beta[c],
-                     (long long)nf[c]);
+            launch_k(k3t_beta<R>, gridf(P, c), 128, 0, st, P, c, (const R *)W.D[c], beta[c]);
         if (int e = poisson_build(S, st)) return e;
         launch_k(k3t_rhs<R>, grid3(P), 128, 0, st, P, Vel3<R>{W.A[0], W.A[1], W.A[2], r_win1}, T->rhs);
         WEC_CK(cudaMemsetAsync(T->phi, 0, T->nc * 8, st));
@@ -1612,8 +1633,8 @@ static int tank3_step_impl(wec_tank3 *T, Work3<R> &W, double dt, double pto_forc
         if (cyc + 1 < ncyc)
             for (int c = 0; c < 3; ++c) dst[c] = T->uk[c];
         for (int c = 0; c < 3; ++c)
-            launch_k(k3t_project<R>, nblk((long long)nf[c], 256), 256, 0, st, P, c, (const R *)W.A[c],
-                     (const double *)beta[c], (const double *)T->phi, dst[c], (long long)nf[c]);
+            launch_k(k3t_project<R>, gridf(P, c), 128, 0, st, P, c, (const R *)W.A[c], (const double *)beta[c],
+                     (const double *)T->phi, dst[c]);
         launch_k(k3t_add, nblk((long long)T->nc, 256), 256, 0, st, (long long)T->nc, (const double *)T->phi, T->p);
         T->zc = zc1;
     }

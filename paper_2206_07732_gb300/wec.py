@@ -166,6 +166,7 @@ def load():
     L.wec_net_adam.argtypes = [vp, C.c_float]
     L.wec_net_train_step.argtypes = [vp, vp, vp, C.POINTER(C.c_int), C.c_int, C.c_float, _dp]
     L.wec_net_sample.argtypes = [vp, vp, vp]
+    L.wec_check_conversions.argtypes = [C.c_longlong, vp, vp, vp]
     L.wec_tank_set_net.argtypes = [vp, vp]
     L.wec_tank_net_stats.argtypes = [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
     _lib = L
@@ -368,6 +369,18 @@ def set_option(name, value):
 
 def launch_count():
     return load().wec_launch_count()
+
+
+def check_conversions(values):
+    """Values (a contiguous FP64 CUDA tensor) for which the library's
+    integer-pipe float <-> double conversions differ in any bit from the
+    conversion instructions (wec_check_conversions)."""
+    import torch
+    bad = torch.zeros(1, dtype=torch.int64, device=values.device)
+    stream = C.c_void_p(torch.cuda.current_stream(values.device).cuda_stream)
+    _check(load().wec_check_conversions(values.numel(), C.c_void_p(values.data_ptr()), C.c_void_p(bad.data_ptr()),
+                                        stream))
+    return int(bad.item())
 
 
 def profile_enable(mode, only=None):
