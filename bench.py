@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--learned-steps", type=int, default=2000, help="learned: problems per training seed")
     ap.add_argument("--train-iters", type=int, default=6000, help="learned: Adam steps")
     ap.add_argument("--no-2d", action="store_true", help="tank3d: skip the 2D tank reported beside it")
+    ap.add_argument("--no-batch", action="store_true", help="tank3d: skip the batched 2D tanks reported beside it")
     ap.add_argument("--steps2d", type=int, default=0, help="tank3d: timed steps of the 2D tank (default 100)")
     ap.add_argument("--detail", default="bench_detail.json",
                     help="file for the breakdowns, tuning tables and per-step records ('' = none)")
@@ -425,6 +426,35 @@ def time_batch(wec, torch, cfgs, precision, steps, warmup, flush):
     launches = wec.launch_count() - n0
     B.close()
     return dict(ms=[a.elapsed_time(b) for a, b in ev], iters=its, residual=max(res), launches=launches, wall=wall)
+
+
+def run_batch_leg(wec, torch, seed, rank, world, steps=20, warmup=3):
+    """The 64 uneven 2D tanks of the batched configuration, mixed and FP64,
+    `steps` timed batch steps each (the tanks sharded over ranks, the slowest
+    rank's time): a compact summary and the detail."""
+    from paper_2206_07732_gb300 import synth
+    allc = synth.batch_tanks(64, seed=seed)
+    cfgs = [c for i, c in enumerate(allc) if i % world == rank]
+    cells = sum(c["nx"] * c["ny"] for c in allc)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    mixed = time_batch(wec, torch, cfgs, wec.PREC_MIXED, steps, warmup, flush)
+    fp64 = time_batch(wec, torch, cfgs, wec.PREC_FP64, steps, warmup, flush)
+    del flush
+
+    def slowest(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    tm, tf = slowest(sum(mixed["ms"]) / 1e3), slowest(sum(fp64["ms"]) / 1e3)
+    summary = {"workload": "64 uneven 2D tanks, one graph launch per batch step", "value": cells * steps / tm,
+               "ms_per_step": tm / steps * 1e3, "fp64_value": cells * steps / tf, "speedup_vs_fp64": tf / tm}
+    detail = dict(summary, cells=cells, tanks=64, steps=steps, warmup=warmup, ms_all=mixed["ms"],
+                  fp64_ms_all=fp64["ms"], fgmres_iters_mean=sum(mixed["iters"]) / max(1, len(mixed["iters"])),
+                  launches=mixed["launches"])
+    return summary, detail
 
 
 def bench_poisson3d(wec, torch, seed, solves=5, warmup=3, shape=(512, 256, 256), cpu_seconds=10.0):
@@ -1116,12 +1146,22 @@ def main_tank3d(args):
                       "conv_roofline_frac": s2["roofline"]["frac"]}
         except Exception as ex:  # reported, not fatal to the 3D line
             tank2d = {"error": f"{type(ex).__name__}: {ex}"[:200]}
+    # the batched configuration (64 uneven 2D tanks, one graph launch per batch
+    # step; tanks sharded over ranks, no collective), beside it
+    batch = None
+    if not args.no_2d and not args.no_batch:
+        try:
+            batch, detail["batch"] = run_batch_leg(wec, torch, args.seed, rank, world)
+        except Exception as ex:  # reported, not fatal to the 3D line
+            batch = {"error": f"{type(ex).__name__}: {ex}"[:200]}
     detail.update({"paths": {k: {"ms_per_step_all": res[k]["ms"], "wall_s_all": res[k]["wall"],
                                  "fgmres_iters": res[k]["iters"], "max_relative_residual": res[k]["residual"],
                                  "qp_solves": res[k]["qp_solves"], "max_abs_pto_force_N": res[k]["max_pto"],
                                  "heave_z_m": res[k]["z"]}
                              for k in res}, "solver_options_autotuned": tuned, "clocks": ck})
     line = make_line3(c, args.seed, world, steps, warmup, tuned, res, t, tw, ck, roof, cpu, tank2d)
+    if batch is not None:
+        line["batch"] = rnd(batch)
     line["detail_file"] = write_detail(args.detail, dict(detail, line=line)) if rank == 0 else None
     if rank == 0:
         print(json.dumps(line))

@@ -179,7 +179,7 @@ struct Ghost3 {
 template <typename R>
 __device__ __forceinline__ R sig3(const Tank3P &P, const R *__restrict__ s, int i, int j, int k, const Ghost3 &G)
 {
-    if (i < 0) return R((k + 0.5) * P.h - P.depth - G.e[-1 - i]);
+    if (i < 0) return narrow_r<R>((k + 0.5) * P.h - P.depth - G.e[-1 - i]);
     i = min(i, P.nx - 1);
     j = min(max(j, 0), P.ny - 1);
     const long long col = (long long)j * P.nx + i, pl = (long long)P.nx * P.ny;
@@ -843,14 +843,14 @@ __device__ __forceinline__ void momentum_finish(const Tank3P &P, const MomIn<R> 
     const double pc = k < P.nz ? M.p[((long long)k * P.ny + j) * P.nx + i] : 0.0;
     const R adv = frq<IN>(P, M.rfc[comp], comp, i, j, k) * uc * M.idt - C + scl2<R>(0.5f, visc);
     if (comp == 0) {
-        Rout[f] = adv - R((pc - M.p[((long long)k * P.ny + j) * P.nx + i - 1]) * ih);
+        Rout[f] = adv - narrow_r<R>((pc - M.p[((long long)k * P.ny + j) * P.nx + i - 1]) * ih);
     } else if (comp == 1) {
-        Rout[f] = adv - R((pc - M.p[((long long)k * P.ny + j - 1) * P.nx + i]) * ih);
+        Rout[f] = adv - narrow_r<R>((pc - M.p[((long long)k * P.ny + j - 1) * P.nx + i]) * ih);
     } else {
         const R rf = scl2<R>(0.5f, cellq<IN>(P, M.rf1, i, j, k - 1) + cellq<IN>(P, M.rf1, i, j, k));
         const double pb = M.p[((long long)(k - 1) * P.ny + j) * P.nx + i];
         const double gp = k < P.nz ? (pc - pb) * ih : -2.0 * pb * ih;
-        Rout[f] = adv - rf * M.g + chi * M.zd1 * M.ikp - R(gp);
+        Rout[f] = adv - rf * M.g + chi * M.zd1 * M.ikp - narrow_r<R>(gp);
     }
 }
 
@@ -883,7 +883,7 @@ __global__ void __launch_bounds__(128) k3t_momentum(Tank3P P, MomIn<R> M, R *__r
 // registers, fewer instruction-fetch stalls), FP64 unchanged (its FP64 pipe
 // bounds both forms)
 template <int COMP, typename R>
-__global__ void __launch_bounds__(128) k3t_transport(Tank3P P, MomIn<R> M, R *__restrict__ Dout, R *__restrict__ Rout)
+__global__ void __launch_bounds__(128, 8) k3t_transport(Tank3P P, MomIn<R> M, R *__restrict__ Dout, R *__restrict__ Rout)
 {
     pdl_entry();
     int i, j, k;

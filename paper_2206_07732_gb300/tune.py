@@ -88,7 +88,7 @@ def tune_poisson3(shape, coef, b, precision, candidates=CANDIDATES_3D, rtol=1e-8
     return (best["mg_pre"], best["mg_post"], best["restart"]), table
 
 
-CANDIDATES_TANK3 = ((2, 2, 20), (3, 3, 5), (4, 4, 5))
+CANDIDATES_TANK3 = ((2, 2, 20), (2, 2, 5), (3, 3, 5), (4, 4, 5))
 
 
 def tune_tank3(cfg, precision, candidates=CANDIDATES_TANK3, steps=2, warmup=1):

@@ -34,6 +34,9 @@ def test_tank3d_line_is_compact_and_complete():
               "value": {k: 1.23456789123e8 for k in ("mixed+learned", "mixed", "mixed_mg", "fp64")},
               "e2e": 1.765432123e8, "conv_roofline_frac": 0.149428196309143}
     line = bench.make_line3(c, 0, 1, steps, 5, tuned, res, t, tw, ck, roof, cpu, tank2d)
+    line["batch"] = bench.rnd({"workload": "64 uneven 2D tanks, one graph launch per batch step",
+                               "value": 3.1412345678e8, "ms_per_step": 21.912345678, "fp64_value": 1.2123456789e8,
+                               "speedup_vs_fp64": 2.5987654321})
     line["detail_file"] = "gpurun_out/bench_detail.json"
     text = json.dumps(line)
     assert len(text) < 2500, len(text)
