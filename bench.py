@@ -1047,12 +1047,12 @@ def make_line3(c, seed, world, steps, warmup, tuned, res, t, tw, ck, roof, cpu, 
     line = {
         "metric": METRIC, "value": val["mixed"], "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": warmup,
         "ms_per_step": t["mixed"] / steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64+f32x2(stencils)+f32(multigrid)", "data": "synthetic (seeded JONSWAP phases)",
+        "dtype": "f64+f32x2(stencils,krylov)+f32(multigrid)", "data": "synthetic (seeded JONSWAP phases)",
         "config": {"workload": "configuration 5: 3D tank 512x256x256 (8x4x4 m, depth 2 m, JONSWAP Hs 0.2 m Tp 2 s "
                                "128 comps, heaving cylinder R 0.5 m, dt 1e-3 s, rtol 1e-8)",
                    "cells": n,
-                   "precision": "FP32 V-cycles in FP64 FGMRES; double-float stencils (<=1e-10 of the FP64 oracle); "
-                                "FP64 residual, Krylov, force, heave, fields",
+                   "precision": "FP32 V-cycles; double-float stencils and Arnoldi step (<=1e-10 of the FP64 "
+                                "oracle); FP64 true residual, solution, force, heave, fields",
                    "learned": "not used in 3D (2D U-Net: see tank2d)", "pto": "host MPC, |F| <= 2 kN",
                    "mg_pre,mg_post,restart": f"{o['mg_pre']},{o['mg_post']},{o['restart']}",
                    "l2": "inputs > L2, no flush", "seed": seed},

@@ -90,12 +90,19 @@ enum { WEC_PREC_FP64 = 0, WEC_PREC_MIXED = 1, WEC_PREC_MIXED_MG = 2, WEC_PREC_MI
  *                      of FP64 state; the force integral (Eq. int_fh), the heave
  *                      update (Eq. newton_u), the projection and the persistent
  *                      fields stay FP64;
- *   WEC_PREC_MIXED_DF  (3D tank only) as WEC_PREC_MIXED, with the stencils in
+ *   WEC_PREC_MIXED_DF  (3D only) as WEC_PREC_MIXED, with the stencils in
  *                      double-float arithmetic (pairs of floats, about 48
  *                      significand bits, on the FP32 pipe) over float-pair
- *                      working copies: FP64-equivalent stencil accuracy.
- * A Poisson object (wec_poisson_create) takes WEC_PREC_FP64 or WEC_PREC_MIXED
- * (FP32 V-cycles); WEC_PREC_MIXED_MG is a tank option.
+ *                      working copies: FP64-equivalent stencil accuracy; and
+ *                      the solver's Arnoldi step (the operator products, the
+ *                      Gram-Schmidt dot products and updates, the correction
+ *                      of the solution) in float pairs over a float-pair
+ *                      basis, the right-hand side, the solution and the true
+ *                      residual at every restart staying FP64 (so rtol is met
+ *                      in FP64 terms).
+ * A Poisson object takes WEC_PREC_FP64 or WEC_PREC_MIXED (FP32 V-cycles), and
+ * a 3D one (wec_poisson_create3) also WEC_PREC_MIXED_DF (its solver part);
+ * WEC_PREC_MIXED_MG is a tank option.
  * rtol: relative FP64 residual ||b - A x||_2 <= rtol ||b||_2 of each solve.
  * restart: FGMRES restart length m (1..32).  n_reinit: Sussman pseudo-steps per
  * step.  n_jacobi: Jacobi sweeps of the Crank-Nicolson momentum system.

@@ -37,8 +37,10 @@ static int check_device()
 static int check_opts(const wec_solver_opts *o)
 {
     if (!o) return fail(WEC_ERR_INVALID, "solver options are NULL");
-    if (o->precision != WEC_PREC_FP64 && o->precision != WEC_PREC_MIXED && o->precision != WEC_PREC_MIXED_MG)
-        return fail(WEC_ERR_INVALID, "precision must be WEC_PREC_FP64, WEC_PREC_MIXED or WEC_PREC_MIXED_MG");
+    if (o->precision != WEC_PREC_FP64 && o->precision != WEC_PREC_MIXED && o->precision != WEC_PREC_MIXED_MG &&
+        o->precision != WEC_PREC_MIXED_DF)
+        return fail(WEC_ERR_INVALID,
+                    "precision must be WEC_PREC_FP64, WEC_PREC_MIXED, WEC_PREC_MIXED_MG or WEC_PREC_MIXED_DF");
     if (!(o->rtol > 0.0) || o->max_iters < 1) return fail(WEC_ERR_INVALID, "rtol must be > 0 and max_iters >= 1");
     if (o->restart < 1 || o->restart > kMaxRestart) return fail(WEC_ERR_INVALID, "restart must be in 1..32");
     if (o->n_reinit < 0 || o->n_jacobi < 1 || o->mg_pre < 1 || o->mg_post < 0 || o->mg_pre > 4 || o->mg_post > 4)
@@ -85,6 +87,8 @@ int validate_tank(const wec_grid *grid, const wec_fluids *fl, const wec_waves *w
 {
     if (!grid || !fl || !wv || !body) return fail(WEC_ERR_INVALID, "NULL argument");
     if (int e = check_opts(opts)) return e;
+    if (opts->precision == WEC_PREC_MIXED_DF)
+        return fail(WEC_ERR_INVALID, "WEC_PREC_MIXED_DF is built for the 3D tank and 3D solver only");
     if (grid->nx < 8 || grid->ny < 8 || (grid->nx & 1) || (grid->ny & 1))
         return fail(WEC_ERR_INVALID, "nx, ny must be even and >= 8");
     double h = grid->lx / grid->nx;

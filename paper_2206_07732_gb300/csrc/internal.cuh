@@ -130,6 +130,11 @@ struct wec_poisson {
     double *hess = nullptr;     // (m+1) x m Hessenberg, then cs, sn, g, y
     double *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr;
     double *sc = nullptr;       // m+1: 1 / ||u_k|| of the unnormalised basis vectors u_k (V's columns)
+    // Arnoldi arithmetic in float pairs (3D, WEC_PREC_MIXED_DF): V and Z then hold
+    // pairs (8 bytes, as FP64), and the level-0 faces and diagonal have pair copies
+    bool kdf = false;
+    double *kdf_face[3] = {};   // beta_x, beta_y, beta_z as float pairs
+    double *kdf_d0 = nullptr;   // the diagonal as float pairs
     int tile64[wec::kMaxLevels] = {}, tile32[wec::kMaxLevels] = {};  // fused tile shape per level (autotuned)
     bool tuned = false;
     int bottom_shift = 0;       // bottom kernel starts this many levels below the smallest admissible one (autotuned)

@@ -80,11 +80,17 @@ __global__ void __launch_bounds__(256) k3_rbgs(int nx, int ny, int nz, const T *
 // the V-cycle also writes the finished iterate in the natural order and in
 // FP64 -- its own cell and the other-colour cell beside it in the row (i ^ 1),
 // whose pass came before -- so no separate pass reads it again.
-template <typename T, int CPT>
+// (OT: the result's type, FP64 or float pairs)
+template <typename OT>
+__device__ __forceinline__ OT widen_out(float v)
+{
+    if constexpr (std::is_same<OT, double>::value) return f2d_exact(v); else return OT(v, 0.f);
+}
+template <typename T, int CPT, typename OT = double>
 __global__ void __launch_bounds__(128) k3_rbgs_pk(int nx, int ny, int nz, const T *__restrict__ bx,
                                                   const T *__restrict__ by, const T *__restrict__ bz,
                                                   const T *__restrict__ id, T *x, const T *__restrict__ b, int color,
-                                                  int first, int bpk, double *out, const int *osel)
+                                                  int first, int bpk, OT *out, const int *osel)
 {
     pdl_entry();
     const int half = nx >> 1, nh = half * ny * nz, j = blockIdx.y, k = blockIdx.z, r = k * ny + j;
@@ -113,13 +119,8 @@ __global__ void __launch_bounds__(128) k3_rbgs_pk(int nx, int ny, int nz, const 
         if (first) {
             x[(1 - color) * nh + q] = T(0);  // (i ^ 1, j, k)
         } else if (out) {
-            if constexpr (std::is_same<T, float>::value) {  // (double) on the integer pipe
-                out[c] = f2d_exact(v[u]);
-                out[c ^ 1] = f2d_exact(w[u]);
-            } else {
-                out[c] = double(v[u]);
-                out[c ^ 1] = double(w[u]);
-            }
+            out[c] = widen_out<OT>(v[u]);
+            out[c ^ 1] = widen_out<OT>(w[u]);
         }
     }
 }
@@ -462,7 +463,7 @@ __global__ void __launch_bounds__(1024) k3_bottom(Bot3<T> B, const T *__restrict
     for (int t = tid; t < n0; t += nt) xg[t] = X(0)[nat0(t)];
 }
 
-// out (natural order, FP64 or FP32) = x of an FP32 level (colour-packed if pk)
+// out (natural order: FP64, FP32 or float pairs) = x of an FP32 level (colour-packed if pk)
 template <typename TO>
 __global__ void __launch_bounds__(256) k3_unpack(int nx, int ny, int nz, const float *__restrict__ x, int pk, TO *out,
                                                  const int *outsel)
@@ -473,16 +474,16 @@ __global__ void __launch_bounds__(256) k3_unpack(int nx, int ny, int nz, const f
     out = at_sel(out, outsel, (long long)nx * ny * nz);
     const int r = c / nx, i = c - r * nx, k = r / ny, j = r - k * ny;
     const float v = x[ix3(pk, nx, ny, nz, i, j, k)];
-    if constexpr (std::is_same<TO, double>::value) out[c] = f2d_exact(v); else out[c] = v;
+    if constexpr (std::is_same<TO, float>::value) out[c] = v; else out[c] = widen_out<TO>(v);
 }
 
 // x0 = M^{-1} b0, one V-cycle over the 3D levels L (precision T).  FP32: x0
 // is the level-0 iterate (colour-packed unless level 0 is the coarsest), b0 in
 // the natural order; xout (nullable): where the last level-0 pass also writes
 // the result in FP64 (osel: its column).  Returns whether it did.
-template <typename T>
+template <typename T, typename OT = double>
 bool vcycle3_unfused(wec_poisson *P, Level<T> *L, const T *b0, T *x0, const int *bsel, const int *xsel,
-                     cudaStream_t st, double *xout = nullptr, const int *osel = nullptr)
+                     cudaStream_t st, OT *xout = nullptr, const int *osel = nullptr)
 {
     bool wrote = false;
     const int TB = 256;
@@ -501,17 +502,17 @@ bool vcycle3_unfused(wec_poisson *P, Level<T> *L, const T *b0, T *x0, const int 
         return Split{((w + nb * cpt - 1) / (nb * cpt) + 31) / 32 * 32, nb};
     };
     auto rbgs = [&](int l, Level<T> &A, T *x, const T *b, const int *bs, const int *xs, int color, int first,
-                    double *o, const int *os) {
+                    OT *o, const int *os) {
         if constexpr (PK) {
             const int half = A.nx >> 1, cpt = half >= 64 ? 2 : 1;
             const Split sp = rows(half, cpt);
             const int tx = sp.tx;
             const dim3 g(sp.nb, A.ny, A.nz);
             if (cpt == 2)
-                launch_k(k3_rbgs_pk<T, 2>, g, tx, 0, st, A.nx, A.ny, A.nz, A.bu, A.bv, A.bw, A.id, x, b, color, first,
+                launch_k(k3_rbgs_pk<T, 2, OT>, g, tx, 0, st, A.nx, A.ny, A.nz, A.bu, A.bv, A.bw, A.id, x, b, color, first,
                          l > 0 ? 1 : 0, o, os);
             else
-                launch_k(k3_rbgs_pk<T, 1>, g, tx, 0, st, A.nx, A.ny, A.nz, A.bu, A.bv, A.bw, A.id, x, b, color, first,
+                launch_k(k3_rbgs_pk<T, 1, OT>, g, tx, 0, st, A.nx, A.ny, A.nz, A.bu, A.bv, A.bw, A.id, x, b, color, first,
                          l > 0 ? 1 : 0, o, os);
         } else {
             const int nh = (A.nx >> 1) * A.ny * A.nz;
@@ -573,7 +574,7 @@ bool vcycle3_unfused(wec_poisson *P, Level<T> *L, const T *b0, T *x0, const int 
         for (int q = 0; q < P->nu1; ++q)
             for (int color = 0; color < 2; ++color) {
                 WEC_PROF("mg3_rbgs", l, (2.0 * n + nf) * ts, st);
-                rbgs(l, A, x, b, bs, xs, color, q == 0 && color == 0, nullptr, nullptr);
+                rbgs(l, A, x, b, bs, xs, color, q == 0 && color == 0, (OT *)nullptr, nullptr);
             }
         Level<T> &C = L[l + 1];
         const T *dg = nullptr;
@@ -615,7 +616,7 @@ bool vcycle3_unfused(wec_poisson *P, Level<T> *L, const T *b0, T *x0, const int 
                 const bool last = PK && l == 0 && xout && q == P->nu2 - 1 && color == 1;
                 // (+ the FP64 result and the other colour's values it reads)
                 WEC_PROF("mg3_rbgs", l, (2.0 * n + nf) * ts + (last ? 10.0 * n : 0.0), st);
-                rbgs(l, A, x, b, bs, xs, color, 0, last ? xout : nullptr, last ? osel : nullptr);
+                rbgs(l, A, x, b, bs, xs, color, 0, last ? xout : (OT *)nullptr, last ? osel : nullptr);
                 wrote = wrote || last;
             }
     }
@@ -633,10 +634,12 @@ void vcycle3_t(wec_poisson *P, Level<T> *L, const T *b0, TO *x0, const int *bsel
         static_assert(std::is_same<TO, double>::value, "an FP64 V-cycle delivers FP64");
         vcycle3_unfused<T>(P, L, b0, x0, bsel, xsel, st);
     } else {
-        // an FP64 result is written by the last level-0 pass where there is one
-        double *xd = nullptr;
-        if constexpr (std::is_same<TO, double>::value) xd = x0;
-        if (vcycle3_unfused<T>(P, L, b0, L[0].x, bsel, nullptr, st, xd, xsel)) return;
+        // an FP64 (or float-pair) result is written by the last level-0 pass where there is one
+        if constexpr (std::is_same<TO, float>::value) {
+            vcycle3_unfused<T>(P, L, b0, L[0].x, bsel, nullptr, st);
+        } else {
+            if (vcycle3_unfused<T, TO>(P, L, b0, L[0].x, bsel, nullptr, st, x0, xsel)) return;
+        }
         const long long n = (long long)L[0].nx * L[0].ny * L[0].nz;
         WEC_PROF("convert", 0, (4.0 + sizeof(TO)) * n, st);
         launch_k(k3_unpack<TO>, nblk(n, 256), 256, 0, st, L[0].nx, L[0].ny, L[0].nz, (const float *)L[0].x,

@@ -4,6 +4,8 @@
 // top boundary) doubles its weight in the diagonal.
 #pragma once
 
+#include <type_traits>
+
 namespace wec {
 
 template <typename T>
@@ -36,7 +38,12 @@ __device__ __forceinline__ T offsum_at(const T *bu, const T *bv, const TX *x, in
 template <typename T>
 __device__ __forceinline__ T fma3(T a, T b, T c)
 {
-    if constexpr (sizeof(T) == 4) return __fmaf_rn(a, b, c); else return __fma_rn(a, b, c);
+    if constexpr (std::is_same<T, float>::value)
+        return __fmaf_rn(a, b, c);
+    else if constexpr (std::is_same<T, double>::value)
+        return __fma_rn(a, b, c);
+    else
+        return a * b + c;  // float pairs: the pair product and sum
 }
 
 // Three dimensions (z vertical): cells [nz][ny][nx], beta_x [nz][ny][nx+1],

@@ -143,6 +143,14 @@ __global__ void k_widen(long long n, const float *__restrict__ in, double *out, 
     out[c] = f2d_exact(in[c]);
 }
 
+// out = the float pairs of in (n values)
+__global__ void k_to_pairs(long long n, const double *__restrict__ in, df64 *__restrict__ out)
+{
+    pdl_entry();
+    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c < n) out[c] = from_double(in[c]);
+}
+
 template <typename TO, typename TI>
 __global__ void k_convert(long long n, const TI *__restrict__ in, TO *__restrict__ out, const int *insel)
 {
@@ -403,33 +411,48 @@ __device__ __forceinline__ void warp_reduce_scatter(double (&a)[K], int lane)
     wrs_stage<K, 16, K>(a, lane);
 }
 
+// Krylov values: FP64, or float pairs over the same 8 bytes
+__device__ __forceinline__ double vt_double(double a) { return a; }
+__device__ __forceinline__ double vt_double(df64 a) { return to_double(a); }
+template <typename VT>
+__device__ __forceinline__ VT vt_from(double a)
+{
+    if constexpr (std::is_same<VT, double>::value) return a; else return from_double(a);
+}
+__device__ __forceinline__ float vt_float(double a) { return d2f_rn(a); }
+__device__ __forceinline__ float vt_float(df64 a) { return a.hi; }  // the nearest float but in exact ties
+
 // The CTA's partials of V_k . w (k < nk <= 32) into bsm[k], in fixed order, over
 // one grid-stride pass that also produces w: wof(c, v) returns w[c] (storing it
 // if it makes it) given v[q] = V_q[c] for q < nk when HOLD (the columns read once
 // per element, kept in registers for the update and the dots); without HOLD
 // (K = 32, where 2 K held values would not fit the register budget) v is unset
 // and the dots read V_q[c] again, from L1 right after the update read it.
-template <int K, typename F>
-__device__ __forceinline__ void block_dots_k(const double *V, long long n, int nk, F &&wof, double (*sh)[KMAXV],
+template <int K, typename VT, typename F>
+__device__ __forceinline__ void block_dots_k(const VT *V, long long n, int nk, F &&wof, double (*sh)[KMAXV],
                                              double *bsm)
 {
     constexpr bool HOLD = K <= 16;
     constexpr int P2 = K >= 32 ? 5 : K >= 16 ? 4 : K >= 8 ? 3 : K >= 4 ? 2 : K >= 2 ? 1 : 0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double a[K];
+    VT av[K];
 #pragma unroll
-    for (int q = 0; q < K; ++q) a[q] = 0.0;
+    for (int q = 0; q < K; ++q) av[q] = VT(0.0);
     for (long long c = blockIdx.x * (long long)KT + threadIdx.x; c < n; c += (long long)gridDim.x * KT) {
-        double v[HOLD ? K : 1];
+        VT v[HOLD ? K : 1];
         if constexpr (HOLD) {
 #pragma unroll
-            for (int q = 0; q < K; ++q) v[q] = q < nk ? V[(long long)q * n + c] : 0.0;
+            for (int q = 0; q < K; ++q) v[q] = q < nk ? V[(long long)q * n + c] : VT(0.0);
         }
-        const double wc = wof(c, v);
+        const VT wc = wof(c, v);
 #pragma unroll
         for (int q = 0; q < K; ++q)
-            if (q < nk) a[q] += (HOLD ? v[HOLD ? q : 0] : V[(long long)q * n + c]) * wc;
+            if (q < nk) av[q] += (HOLD ? v[HOLD ? q : 0] : V[(long long)q * n + c]) * wc;
     }
+    // the thread's sums, FP64 from here on
+    double a[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q) a[q] = vt_double(av[q]);
     warp_reduce_scatter<K>(a, lane);
     if ((lane & ((32 >> P2) - 1)) == 0) {
         const int k = lane >> (5 - P2);
@@ -445,8 +468,8 @@ __device__ __forceinline__ void block_dots_k(const double *V, long long n, int n
 
 // nk <= KB (KB = 8: restarts up to 8, whose kernels hold few values per thread
 // and run more CTAs per SM; KB = 32: any restart)
-template <int KB, typename F>
-__device__ __forceinline__ void block_dots(const double *V, long long n, int nk, F &&wof, double (*sh)[KMAXV],
+template <int KB, typename VT, typename F>
+__device__ __forceinline__ void block_dots(const VT *V, long long n, int nk, F &&wof, double (*sh)[KMAXV],
                                           double *bsm)
 {
     if (nk <= 1) {
@@ -492,15 +515,18 @@ __global__ void k_ks_init(KState *ks, double rtol, int maxit, int m)
     ks->ncycles = 0;
 }
 
-// The FP64 level-0 operator seen by the Krylov kernels: D = 2 (bx, by = beta_u,
-// beta_v; nz = 1) or D = 3 (beta_x, beta_y, beta_z).
-struct Op0 {
+// The level-0 operator seen by the Krylov kernels: D = 2 (bx, by = beta_u,
+// beta_v; nz = 1) or D = 3 (beta_x, beta_y, beta_z); FP64, or float pairs (VT =
+// df64) for the pair-arithmetic Arnoldi step.
+template <typename VT>
+struct OpT {
     int nx, ny, nz;
-    const double *bx, *by, *bz;
+    const VT *bx, *by, *bz;
 };
+using Op0 = OpT<double>;
 
-template <int D>
-__device__ __forceinline__ double op_offsum(const Op0 &o, const double *__restrict__ x, long long c)
+template <int D, typename VT>
+__device__ __forceinline__ VT op_offsum(const OpT<VT> &o, const VT *__restrict__ x, long long c)
 {
     if constexpr (D == 2) {
         const int j = (int)(c / o.nx), i = (int)(c - (long long)j * o.nx);
@@ -550,10 +576,10 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 4)
 // mode 1 (end of a cycle): converged, out of iterations, or restart.
 // A zero right-hand side gives x = 0.  Opens a new Arnoldi cycle unless done and
 // sets the WHILE condition to !done.
-template <int D>
+template <int D, typename VT = double>
 __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 4)
     k_residual_norm(Op0 op, const double *__restrict__ d0, const double *__restrict__ b, double *x,
-                    double *__restrict__ w, float *__restrict__ b32, double *sc, double *part, KState *ks, double *g,
+                    VT *__restrict__ w, float *__restrict__ b32, double *sc, double *part, KState *ks, double *g,
                     int mode, unsigned long long hwhile, int use)
 {
     pdl_entry();
@@ -565,11 +591,11 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 4)
     for (long long c = blockIdx.x * (long long)KT + threadIdx.x; c < n; c += (long long)gridDim.x * KT) {
         if (zero) {
             x[c] = 0.0;
-            w[c] = 0.0;
+            w[c] = VT(0.0);
             continue;
         }
-        double r = b[c] - (d0[c] * x[c] - op_offsum<D>(op, x, c));
-        w[c] = r;
+        double r = b[c] - (d0[c] * x[c] - op_offsum<D, double>(op, x, c));
+        w[c] = vt_from<VT>(r);
         if (b32) b32[c] = d2f_rn(r);  // (float)r on the integer pipe
         a += r * r;
     }
@@ -614,9 +640,9 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 4)
 // s_k = 1 / ||u_k|| in sc): the new vector w is built in place in column j+1.
 // w = A z_j = s_j A z'_j (z'_j = M u_j, the V-cycle being linear), and the
 // first Gram-Schmidt dot products h1_k = v_k . w = s_k (u_k . w), k <= j.
-template <int D, int KB>
+template <int D, int KB, typename VT = double>
 __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, kb_blocks(KB))
-    k_matvec_dots(Op0 op, const double *__restrict__ d0, const double *__restrict__ Z, double *V,
+    k_matvec_dots(OpT<VT> op, const VT *__restrict__ d0, const VT *__restrict__ Z, VT *V,
                   const double *__restrict__ sc, double *part, double *h1, KState *ks)
 {
     pdl_entry();
@@ -624,14 +650,14 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, kb_blocks(KB))
     __shared__ double bsm[KMAXV];
     const long long n = (long long)op.nx * op.ny * op.nz;
     const int j = ks->j, nk = j + 1;
-    const double *z = Z + (long long)j * n;
-    double *w = V + (long long)(j + 1) * n;
-    const double sj = sc[j];
+    const VT *z = Z + (long long)j * n;
+    VT *w = V + (long long)(j + 1) * n;
+    const VT sj = VT(sc[j]);  // (once per thread of the grid-stride loop)
     // w and its dots in one pass (w is not read back)
     block_dots<KB>(
         V, n, nk,
         [&](long long c, const auto &) {
-            const double r = sj * (d0[c] * z[c] - op_offsum<D>(op, z, c));
+            const VT r = sj * (d0[c] * z[c] - op_offsum<D, VT>(op, z, c));
             w[c] = r;
             return r;
         },
@@ -646,25 +672,25 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, kb_blocks(KB))
 
 // First Gram-Schmidt update w -= sum_k h1_k v_k = w - sum_k (h1_k s_k) u_k, then
 // h2_k = v_k . w.
-template <int KB>
+template <int KB, typename VT = double>
 __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, KB <= 8 ? 3 : 2)
-    k_orth_dots(long long n, double *V, const double *__restrict__ sc, const double *__restrict__ h1, double *part,
+    k_orth_dots(long long n, VT *V, const double *__restrict__ sc, const double *__restrict__ h1, double *part,
                 double *h2, KState *ks)
 {
     pdl_entry();
     __shared__ double sh[KT / 32][KMAXV];
     __shared__ double bsm[KMAXV];
-    __shared__ double hs[KMAXV];
+    __shared__ VT hs[KMAXV];
     const int j = ks->j, nk = j + 1;
-    double *w = V + (long long)(j + 1) * n;
-    if (threadIdx.x < nk) hs[threadIdx.x] = h1[threadIdx.x] * sc[threadIdx.x];
+    VT *w = V + (long long)(j + 1) * n;
+    if (threadIdx.x < nk) hs[threadIdx.x] = VT(h1[threadIdx.x] * sc[threadIdx.x]);
     __syncthreads();
     // the update and the second dots in one pass over the basis (V_k[c] read once)
     block_dots<KB>(
         V, n, nk,
         [&](long long c, const auto &v) {
             constexpr int KH = std::extent<std::remove_reference_t<decltype(v)>>::value;
-            double a = w[c];
+            VT a = w[c];
             if (nk <= KH) {
 #pragma unroll
                 for (int k = 0; k < KH; ++k)
@@ -690,29 +716,30 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, KB <= 8 ? 3 : 
 // counts the iteration, decides whether the cycle ends (converged estimate,
 // iteration cap, breakdown, or full basis), advances j otherwise, and sets the
 // IF condition.
+template <typename VT = double>
 __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 4)
-    k_orth_norm(long long n, double *V, double *sc, float *__restrict__ b32, const double *__restrict__ h1,
+    k_orth_norm(long long n, VT *V, double *sc, float *__restrict__ b32, const double *__restrict__ h1,
                 const double *__restrict__ h2, double *part, KState *ks, double *H, double *cs, double *sn,
                 double *g, unsigned long long hif, int use)
 {
     pdl_entry();
     __shared__ double sh[KT / 32];
     __shared__ double bsm[1];
-    __shared__ double hs[KMAXV];
+    __shared__ VT hs[KMAXV];
     const int j = ks->j;
-    double *w = V + (long long)(j + 1) * n;
-    if (threadIdx.x <= j) hs[threadIdx.x] = h2[threadIdx.x] * sc[threadIdx.x];
+    VT *w = V + (long long)(j + 1) * n;
+    if (threadIdx.x <= j) hs[threadIdx.x] = VT(h2[threadIdx.x] * sc[threadIdx.x]);
     __syncthreads();
-    double a2 = 0.0;
+    VT av2 = VT(0.0);
     for (long long c = blockIdx.x * (long long)KT + threadIdx.x; c < n; c += (long long)gridDim.x * KT) {
-        double a = w[c];
+        VT a = w[c];
 #pragma unroll 4
         for (int k = 0; k <= j; ++k) a -= hs[k] * V[(long long)k * n + c];
         w[c] = a;
-        if (b32) b32[c] = d2f_rn(a);
-        a2 += a * a;
+        if (b32) b32[c] = vt_float(a);
+        av2 += a * a;
     }
-    a2 = block_sum(a2, sh);
+    double a2 = block_sum(vt_double(av2), sh);
     if (threadIdx.x == 0) bsm[0] = a2;
     cluster_partials(bsm, 1, part);
     if (!last_cluster(&ks->cnt[2])) return;
@@ -764,17 +791,27 @@ __global__ void k_backsolve(int m, const double *__restrict__ H, const double *_
     for (int k = 0; k < jd; ++k) y[k] *= sc[k];
 }
 
-__global__ void k_update_x(long long n, const double *__restrict__ y, const double *__restrict__ Z, double *__restrict__ x,
+template <typename VT = double>
+__global__ void k_update_x(long long n, const double *__restrict__ y, const VT *__restrict__ Z, double *__restrict__ x,
                            const KState *ks)
 {
     pdl_entry();
-    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (c >= n) return;
     const int jd = ks->jd;
-    double a = x[c];
+    if constexpr (std::is_same<VT, double>::value) {
+        long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+        if (c >= n) return;
+        double a = x[c];
 #pragma unroll 4
-    for (int k = 0; k < jd; ++k) a += y[k] * Z[(long long)k * n + c];
-    x[c] = a;
+        for (int k = 0; k < jd; ++k) a += y[k] * Z[(long long)k * n + c];
+        x[c] = a;
+    } else {  // pair columns holding the FP32 V-cycle's values (lo = 0): the same FP64 update
+        long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+        if (c >= n) return;
+        double a = x[c];
+#pragma unroll 4
+        for (int k = 0; k < jd; ++k) a += y[k] * f2d_exact(Z[(long long)k * n + c].hi);
+        x[c] = a;
+    }
 }
 
 // ------------------------------------------------------------ V-cycle ----
@@ -1158,6 +1195,8 @@ void vcycle_t(wec_poisson *P, Level<T> *L, const T *b0, TO *x0, const int *bsel,
 // clusters, at most kKrylovBlocks; res[d3], mv[d3][restart <= 8], od[restart <= 8]
 struct KGrids {
     int bnorm = kCl, on = kCl, res[2] = {kCl, kCl}, mv[2][2] = {{kCl, kCl}, {kCl, kCl}}, od[2] = {kCl, kCl};
+    // the float-pair Arnoldi kernels (3D): residual, matvec[restart <= 8], orth dots[restart <= 8], orth norm
+    int res_df = kCl, mv_df[2] = {kCl, kCl}, od_df[2] = {kCl, kCl}, on_df = kCl;
 };
 KGrids g_kg;
 
@@ -1188,7 +1227,7 @@ int set_kgrid_max()
     };
     KGrids &k = g_kg;
     int e = r(k_bnorm, k.bnorm);
-    if (!e) e = r(k_orth_norm, k.on);
+    if (!e) e = r(k_orth_norm<double>, k.on);
     if (!e) e = r(k_residual_norm<2>, k.res[0]);
     if (!e) e = r(k_residual_norm<3>, k.res[1]);
     if (!e) e = r(k_matvec_dots<2, 32>, k.mv[0][0]);
@@ -1197,6 +1236,12 @@ int set_kgrid_max()
     if (!e) e = r(k_matvec_dots<3, 8>, k.mv[1][1]);
     if (!e) e = r(k_orth_dots<32>, k.od[0]);
     if (!e) e = r(k_orth_dots<8>, k.od[1]);
+    if (!e) e = r(k_residual_norm<3, df64>, k.res_df);
+    if (!e) e = r(k_matvec_dots<3, 32, df64>, k.mv_df[0]);
+    if (!e) e = r(k_matvec_dots<3, 8, df64>, k.mv_df[1]);
+    if (!e) e = r(k_orth_dots<32, df64>, k.od_df[0]);
+    if (!e) e = r(k_orth_dots<8, df64>, k.od_df[1]);
+    if (!e) e = r(k_orth_norm<df64>, k.on_df);
     return e;
 }
 
@@ -1216,6 +1261,12 @@ Op0 op0(const wec_poisson *P)
 {
     return Op0{P->nx, P->ny, P->nz, P->L64[0].bu, P->L64[0].bv, P->L64[0].bw};
 }
+// the pair copies of the level-0 operator (P->kdf)
+OpT<df64> op0df(const wec_poisson *P)
+{
+    return OpT<df64>{P->nx, P->ny, P->nz, (const df64 *)P->kdf_face[0], (const df64 *)P->kdf_face[1],
+                     (const df64 *)P->kdf_face[2]};
+}
 
 long long ncells(const wec_poisson *P) { return (long long)P->nx * P->ny * P->nz; }
 
@@ -1230,6 +1281,11 @@ double nfaces(const wec_poisson *P)
 void launch_residual_norm(wec_poisson *P, const double *b, double *x, float *b32, int mode, unsigned long long hw,
                           int use, cudaStream_t st)
 {
+    if (P->kdf) {  // (3D) the FP64 residual into the pair basis
+        launch_k(k_residual_norm<3, df64>, kgrid(ncells(P), g_kg.res_df), KT, 0, st, op0(P), P->d0, b, x,
+                 (df64 *)P->V, b32, P->sc, P->part, P->ks, P->g, mode, hw, use);
+        return;
+    }
     const int G = kgrid(ncells(P), g_kg.res[P->nz > 1 ? 1 : 0]);
     if (P->nz > 1)
         launch_k(k_residual_norm<3>, G, KT, 0, st, op0(P), P->d0, b, x, P->V, b32, P->sc, P->part, P->ks, P->g, mode,
@@ -1268,6 +1324,24 @@ void enqueue_body(wec_poisson *P, unsigned long long hif, int use, cudaStream_t 
     const bool mixed = P->prec == WEC_PREC_MIXED;
     double *h1 = P->dots, *h2 = P->dots + (kMaxRestart + 2);
     // the mixed V-cycle reads u_j in FP32, written beside it by k_residual_norm / k_orth_norm
+    if (P->kdf) {  // (3D, FP32 V-cycles) the float-pair Arnoldi step
+        vcycle3_t<float, df64>(P, P->L32, P->L32[0].b, (df64 *)P->Z, nullptr, &P->ks->j, st);
+        {
+            WEC_PROF("krylov_matvec_dots", -1, 8.0 * (3.0 * n + nf) + 8.0 * n * m, st);
+            launch_k(kb8 ? k_matvec_dots<3, 8, df64> : k_matvec_dots<3, 32, df64>, kgrid(n, g_kg.mv_df[kb8]), KT, 0,
+                     st, op0df(P), (const df64 *)P->kdf_d0, (const df64 *)P->Z, (df64 *)P->V, P->sc, P->part, h1,
+                     P->ks);
+        }
+        {
+            WEC_PROF("krylov_orth_dots", -1, 8.0 * n * (m + 2), st);
+            launch_k(kb8 ? k_orth_dots<8, df64> : k_orth_dots<32, df64>, kgrid(n, g_kg.od_df[kb8]), KT, 0, st, n,
+                     (df64 *)P->V, P->sc, h1, P->part, h2, P->ks);
+        }
+        WEC_PROF("krylov_orth_norm", -1, 8.0 * n * (m + 2) + 4.0 * n, st);
+        launch_k(k_orth_norm<df64>, kgrid(n, g_kg.on_df), KT, 0, st, n, (df64 *)P->V, P->sc, P->L32[0].b, h1, h2,
+                 P->part, P->ks, P->hess, P->cs, P->sn, P->g, hif, use);
+        return;
+    }
     if (!mixed)
         vcycle_t<double, double>(P, P->L64, P->V, P->Z, &P->ks->j, &P->ks->j, st);
     else
@@ -1284,7 +1358,7 @@ void enqueue_body(wec_poisson *P, unsigned long long hif, int use, cudaStream_t 
                  P->part, h2, P->ks);
     }
     WEC_PROF("krylov_orth_norm", -1, 8.0 * n * (m + 2) + (mixed ? 4.0 * n : 0.0), st);
-    launch_k(k_orth_norm, kgrid(n, g_kg.on), KT, 0, st, n, P->V, P->sc, mixed ? P->L32[0].b : nullptr, h1, h2, P->part, P->ks,
+    launch_k(k_orth_norm<double>, kgrid(n, g_kg.on), KT, 0, st, n, P->V, P->sc, mixed ? P->L32[0].b : nullptr, h1, h2, P->part, P->ks,
              P->hess, P->cs, P->sn, P->g, hif, use);
 }
 
@@ -1302,7 +1376,10 @@ void enqueue_close(wec_poisson *P, const double *b, double *x, unsigned long lon
     }
     {
         WEC_PROF("krylov_update_x", -1, 16.0 * n + 8.0 * n * m, st);
-        launch_k(k_update_x, nblk(n, 256), 256, 0, st, n, P->y, P->Z, x, P->ks);
+        if (P->kdf)
+            launch_k(k_update_x<df64>, nblk(n, 256), 256, 0, st, n, P->y, (const df64 *)P->Z, x, P->ks);
+        else
+            launch_k(k_update_x<double>, nblk(n, 256), 256, 0, st, n, P->y, P->Z, x, P->ks);
     }
     WEC_PROF("krylov_residual", -1, 8.0 * (4.0 * n + nf) + (mixed ? 4.0 * n : 0.0), st);
     launch_residual_norm(P, b, x, mixed ? P->L32[0].b : nullptr, 1, hw, use, st);
@@ -1354,8 +1431,16 @@ int poisson_init(wec_poisson *P, int nx, int ny, int prec, int restart, int nu1,
     if (restart < 1 || restart > kMaxRestart) return fail(WEC_ERR_INVALID, "poisson: restart must be in 1..32");
     if (nu1 < 1 || nu2 < 0 || nu1 > 4 || nu2 > 4)
         return fail(WEC_ERR_INVALID, "poisson: need 1 <= mg_pre <= 4 and 0 <= mg_post <= 4");
+    // WEC_PREC_MIXED_DF (3D): FP32 V-cycles and the Arnoldi step in float pairs
+    bool kdf = false;
+    if (prec == WEC_PREC_MIXED_DF) {
+        if (nz <= 1) return fail(WEC_ERR_INVALID, "poisson: WEC_PREC_MIXED_DF is for the 3D operator");
+        prec = WEC_PREC_MIXED;
+        kdf = true;
+    }
     if (prec != WEC_PREC_FP64 && prec != WEC_PREC_MIXED) return fail(WEC_ERR_INVALID, "poisson: unknown precision");
     P->nx = nx; P->ny = ny; P->nz = nz; P->prec = prec; P->restart = restart; P->nu1 = nu1; P->nu2 = nu2; P->st = st;
+    P->kdf = kdf;
     const bool d3 = nz > 1;
     int lx = nx, ly = ny, lz = nz, nl = 0;
     for (;;) {
@@ -1423,6 +1508,12 @@ int poisson_init(wec_poisson *P, int nx, int ny, int prec, int restart, int nu1,
     WEC_CK(cudaMalloc(&P->Z, m * n * 8));
     WEC_CK(cudaMalloc(&P->w, n * 8));
     WEC_CK(cudaMalloc(&P->d0, n * 8));
+    if (P->kdf) {  // pair copies of the level-0 operator: faces and diagonal
+        const size_t nf3[3] = {(size_t)(nx + 1) * ny * nz, (size_t)nx * (ny + 1) * nz, (size_t)nx * ny * (nz + 1)};
+        for (int q = 0; q < 3; ++q) WEC_CK(cudaMalloc(&P->kdf_face[q], nf3[q] * 8));
+        WEC_CK(cudaMalloc(&P->kdf_d0, n * 8));
+        P->bytes += (nf3[0] + nf3[1] + nf3[2] + n) * 8;
+    }
     // reduction partials: one per cluster and quantity
     WEC_CK(cudaMalloc(&P->part, (size_t)(kMaxRestart + 2) * (kKrylovBlocks / kCl) * 8));
     WEC_CK(cudaMalloc(&P->dots, 2 * (kMaxRestart + 2) * 8));
@@ -1454,6 +1545,12 @@ void poisson_free(wec_poisson *P)
     cudaFree(P->lu64); cudaFree(P->lu32);
     cudaFree(P->inv64); cudaFree(P->inv32);
     cudaFree(P->V); cudaFree(P->Z); cudaFree(P->w); cudaFree(P->d0); cudaFree(P->part); cudaFree(P->dots); cudaFree(P->hess);
+    for (double *&q : P->kdf_face) {
+        cudaFree(q);
+        q = nullptr;
+    }
+    cudaFree(P->kdf_d0);
+    P->kdf_d0 = nullptr;
     cudaFree(P->ks);
     if (P->ksh) cudaFreeHost(P->ksh);
     *P = wec_poisson();
@@ -1528,6 +1625,18 @@ int poisson_build3(wec_poisson *P, cudaStream_t st)
         WEC_PROF("diag", 0, 8.0 * (n + nfaces(P)), st);
         launch_k(k3_diag0, nblk(n, 256), 256, 0, st, P->nx, P->ny, P->nz, P->L64[0].bu, P->L64[0].bv, P->L64[0].bw,
                  P->d0);
+    }
+    if (P->kdf) {  // the pair copies of the level-0 faces and diagonal
+        Level<double> &A = P->L64[0];
+        const long long nf[3] = {(A.nx + 1ll) * A.ny * A.nz, A.nx * (A.ny + 1ll) * A.nz,
+                                 (long long)A.nx * A.ny * (A.nz + 1)};
+        const double *src[3] = {A.bu, A.bv, A.bw};
+        for (int q = 0; q < 3; ++q) {
+            WEC_PROF("convert", 0, 16.0 * nf[q], st);
+            launch_k(k_to_pairs, nblk(nf[q], 256), 256, 0, st, nf[q], src[q], (df64 *)P->kdf_face[q]);
+        }
+        WEC_PROF("convert", 0, 16.0 * n, st);
+        launch_k(k_to_pairs, nblk(n, 256), 256, 0, st, n, (const double *)P->d0, (df64 *)P->kdf_d0);
     }
     int e;
     if (P->prec == WEC_PREC_MIXED) {

@@ -1856,7 +1856,10 @@ int wec_tank3_create(const wec_grid3 *grid, const wec_fluids *fl, const wec_wave
             wec_tank3_destroy(T);
             return fail(WEC_ERR_NOMEM, "host allocation failed");
         }
-        const int sprec = opts->precision == WEC_PREC_FP64 ? WEC_PREC_FP64 : WEC_PREC_MIXED;  // FP32 V-cycles
+        // FP32 V-cycles; the double-float path also runs the Arnoldi step in float pairs
+        const int sprec = opts->precision == WEC_PREC_FP64      ? WEC_PREC_FP64
+                          : opts->precision == WEC_PREC_MIXED_DF ? WEC_PREC_MIXED_DF
+                                                                 : WEC_PREC_MIXED;
         if (int rc = poisson_init(T->solver, nx, ny, sprec, opts->restart, opts->mg_pre, opts->mg_post, T->st, nz)) {
             std::string msg = wec_last_error();
             wec_tank3_destroy(T);
