@@ -430,8 +430,9 @@ void wec_tank3_destroy(wec_tank3 *tank);
 /* host_dst / host_src: n doubles, n = the field's size (WEC_ERR_INVALID otherwise;
  * only the state fields can be set).  The material fields hold the last
  * wec_tank3_materials call, or a step's time level n: everywhere after an FP64 or
- * WEC_PREC_MIXED_MG step, after a WEC_PREC_MIXED step (whose stencils use FP32
- * copies) only in the cell layers of the force integral around the cylinder. */
+ * WEC_PREC_MIXED_MG step; after a WEC_PREC_MIXED or WEC_PREC_MIXED_DF step (whose
+ * stencils use working copies) only in the box of cells of the force integral
+ * around the cylinder and the cells just before it in x, y and z. */
 int wec_tank3_get_field(const wec_tank3 *tank, int field_id, double *host_dst, size_t n);
 int wec_tank3_set_field(wec_tank3 *tank, int field_id, const double *host_src, size_t n);
 /* Two-stage materials (Eqs. ls_flow then ls_solid, half-width h) from sigma and

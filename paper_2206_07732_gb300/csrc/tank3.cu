@@ -323,13 +323,16 @@ __device__ __forceinline__ bool cell_of(const Tank3P &P, Cell3 &q)
 template <typename R>
 __global__ void __launch_bounds__(128) k3t_materials(Tank3P P, const R *__restrict__ sig, R zc,
                                                      R *__restrict__ rho, R *__restrict__ mu, R *__restrict__ rhof,
-                                                     R *__restrict__ chi, int k0)
+                                                     R *__restrict__ chi, int k0, int i0, int j0)
 {
     pdl_entry();
+    // (the grid covers cells from (i0, j0, k0) on: a box, or the whole grid)
     Cell3 q;
-    if (!cell_of(P, q)) return;
-    q.k += k0;
-    q.c += (long long)k0 * P.ny * P.nx;
+    q.i = i0 + blockIdx.x * blockDim.x + threadIdx.x;
+    q.j = j0 + blockIdx.y;
+    q.k = k0 + blockIdx.z;
+    if (q.i >= P.nx || q.j >= P.ny) return;
+    q.c = ((long long)q.k * P.ny + q.j) * P.nx + q.i;
     const Tank3C<R> &K = cst3<R>(P);
     const R h = K.h;
     R psi = R(1.0e3);
@@ -1458,11 +1461,11 @@ static int tank3_step_impl(wec_tank3 *T, Work3<R> &W, double dt, double pto_forc
     // materials at level n: the stencils' (W.rho, W.mu) and, FP64, the force's
     if constexpr (f32) {
         WEC_PROF("tank3_materials", 0, 20.0 * T->nc, st);
-        launch_k(k3t_materials<R>, grid3(P), 128, 0, st, P, (const R *)W.sig, T->zc, W.rho, W.mu, W.rf, W.chi, 0);
+        launch_k(k3t_materials<R>, grid3(P), 128, 0, st, P, (const R *)W.sig, T->zc, W.rho, W.mu, W.rf, W.chi, 0, 0, 0);
     } else {
         WEC_PROF("tank3_materials", 0, 40.0 * T->nc, st);
         launch_k(k3t_materials<double>, grid3(P), 128, 0, st, P, (const double *)T->sig, T->zc, T->rho, T->mu,
-                 T->rhof, T->chi, 0);
+                 T->rhof, T->chi, 0, 0, 0);
     }
     for (int cyc = 0; cyc < ncyc; ++cyc) {
         section(1);
@@ -1472,29 +1475,34 @@ static int tank3_step_impl(wec_tank3 *T, Work3<R> &W, double dt, double pto_forc
         const int kcb = (int)(zck / h), mkb = (int)std::ceil(0.5 * P.blen / h) + 3;
         const bool force_box = P.has_body && std::min(nz, kcb + mkb + 1) > std::max(0, kcb - mkb);
         const int fk0 = std::max(0, kcb - mkb), fk1 = std::min(nz, kcb + mkb + 1), sk0 = std::max(0, fk0 - 1);
+        // the box's columns; its FP64 materials on them and the column before each side
+        const int mi = (int)std::ceil((P.br) / h) + 3;
+        const int ic = (int)(P.bxc / h), jc = (int)(P.byc / h);
+        const int i0 = std::max(0, ic - mi), i1 = std::min(nx, ic + mi + 1), j0 = std::max(0, jc - mi),
+                  j1 = std::min(ny, jc + mi + 1);
+        const int si0 = std::max(0, i0 - 1), sj0 = std::max(0, j0 - 1);
+        const dim3 gbox((i1 - si0 + 127) / 128, std::max(1, j1 - sj0), std::max(1, fk1 - sk0));
+        const double fbox = (double)(i1 - si0) * (j1 - sj0) * (fk1 - sk0);  // cells
         const double *fmu = T->mu;  // FP64 viscosity of the force integral
         if (force_box && cyc == 0 && f32) {
             // the stencils read materials in their own type; the FP64 ones are
-            // needed by the force only: the box's cell layers and the layer below
-            WEC_PROF("tank3_materials", 0, 40.0 * T->nc * (fk1 - sk0) / nz, st);
-            launch_k(k3t_materials<double>, dim3((nx + 127) / 128, ny, fk1 - sk0), 128, 0, st, P,
-                     (const double *)T->sig, zck, T->rho, T->mu, T->rhof, T->chi, sk0);
+            // needed by the force only: the box and the cells before it in x, y, z
+            WEC_PROF("tank3_materials", 0, 40.0 * fbox, st);
+            launch_k(k3t_materials<double>, gbox, 128, 0, st, P, (const double *)T->sig, zck, T->rho, T->mu, T->rhof,
+                     T->chi, sk0, si0, sj0);
         }
         if (force_box && cyc > 0) {
             // materials of the iterate (sigma^{n+1,k} in FP64 in T->tmp) on the force layers
             if constexpr (f32)
                 launch_k(k3t_widen<R>, nblk((long long)T->nc, 256), 256, 0, st, (long long)T->nc, (const R *)W.tmp,
                          T->tmp);
-            WEC_PROF("tank3_materials", 0, 40.0 * T->nc * (fk1 - sk0) / nz, st);
-            launch_k(k3t_materials<double>, dim3((nx + 127) / 128, ny, fk1 - sk0), 128, 0, st, P,
-                     (const double *)T->tmp, zck, T->s0, T->muk, T->s1, T->phi, sk0);
+            WEC_PROF("tank3_materials", 0, 40.0 * fbox, st);
+            launch_k(k3t_materials<double>, gbox, 128, 0, st, P, (const double *)T->tmp, zck, T->s0, T->muk, T->s1,
+                     T->phi, sk0, si0, sj0);
             fmu = T->muk;
         }
         if (force_box) {
-            const int mi = (int)std::ceil((P.br) / h) + 3;
-            const int ic = (int)(P.bxc / h), jc = (int)(P.byc / h);
-            const int i0 = std::max(0, ic - mi), i1 = std::min(nx, ic + mi + 1), j0 = std::max(0, jc - mi),
-                      j1 = std::min(ny, jc + mi + 1), k0 = fk0, k1 = fk1;
+            const int k0 = fk0, k1 = fk1;
             const Vel3<double> Vk = cyc == 0 ? Vel3<double>{T->u, T->v, T->w, d_win0}
                                              : Vel3<double>{T->uk[0], T->uk[1], T->uk[2], d_win1};
             {
@@ -1542,7 +1550,7 @@ static int tank3_step_impl(wec_tank3 *T, Work3<R> &W, double dt, double pto_forc
         {
             WEC_PROF("tank3_materials", 0, 5.0 * sizeof(R) * T->nc, st);
             launch_k(k3t_materials<R>, grid3(P), 128, 0, st, P, (const R *)W.tmp, zc1, W.s1, W.mu1, W.rf1, W.chi1,
-                     0);
+                     0, 0, 0);
         }
         // (5) transport and the momentum system: face densities of rho^n and
         // edge viscosities of mu^n, then one kernel per component
@@ -1939,7 +1947,7 @@ int wec_tank3_create(const wec_grid3 *grid, const wec_fluids *fl, const wec_wave
                  (const double *)(dtab + eta.size()), (const double *)(dtab + eta.size() + uxz.size()), T->sig, T->u,
                  T->w);
         launch_k(k3t_materials<double>, grid3(T->P), 128, 0, T->st, T->P, (const double *)T->sig, T->zc, T->rho,
-                 T->mu, T->rhof, T->chi, 0);
+                 T->mu, T->rhof, T->chi, 0, 0, 0);
         launch_k(k3t_hydrostatic, nblk((long long)nx * ny, 128), 128, 0, T->st, T->P, (const double *)T->rhof, T->g,
                  T->p);
         e = cudaGetLastError();
@@ -2031,7 +2039,7 @@ int wec_tank3_materials(wec_tank3 *T, double zc)
     {
         WEC_PROF("tank3_materials", 0, 40.0 * T->nc, T->st);
         launch_k(k3t_materials<double>, grid3(T->P), 128, 0, T->st, T->P, (const double *)T->sig, zc, T->rho, T->mu, T->rhof,
-                 T->chi, 0);
+                 T->chi, 0, 0, 0);
     }
     WEC_CK(cudaGetLastError());
     WEC_CK(cudaStreamSynchronize(T->st));
