@@ -47,7 +47,8 @@ __device__ __forceinline__ T offsum3_pk(const T *bx, const T *by, const T *bz, c
 
 // One colour of a red-black sweep on a natural-order level (FP64); thread q ->
 // the q-th cell of the colour.  first != 0: the sweep starts from x = 0, so the
-// red pass writes b / d and zeroes the black cell beside it in the row.
+// red pass writes b / d (the black cells' starting values are never read: a
+// cell's new value depends on the other colour only).
 template <typename T>
 __global__ void __launch_bounds__(256) k3_rbgs(int nx, int ny, int nz, const T *__restrict__ bx,
                                                const T *__restrict__ by, const T *__restrict__ bz,
@@ -67,7 +68,6 @@ __global__ void __launch_bounds__(256) k3_rbgs(int nx, int ny, int nz, const T *
     const int c = r * nx + i;
     if (first) {
         x[c] = (b[c] + T(0)) * id[c];
-        x[c ^ 1] = T(0);  // nx even: c and i have the same parity
         return;
     }
     x[c] = (b[c] + offsum3_at(bx, by, bz, x, nx, ny, nz, i, j, k)) * id[c];
@@ -76,10 +76,11 @@ __global__ void __launch_bounds__(256) k3_rbgs(int nx, int ny, int nz, const T *
 // The same pass on a colour-packed level.  One block row per (j, k) = (blockIdx.y,
 // blockIdx.z), CPT cells of the row per thread, blockDim.x apart: no index
 // division, and every load of the CPT cells is issued before the first store.
-// bpk: b colour-packed too (levels below 0).  out (nullable): the last pass of
-// the V-cycle also writes the finished iterate in the natural order and in
-// FP64 -- its own cell and the other-colour cell beside it in the row (i ^ 1),
-// whose pass came before -- so no separate pass reads it again.
+// bpk: b colour-packed too (levels below 0).  first: as in k3_rbgs.
+// out (nullable): the last pass of the V-cycle also writes the finished
+// iterate in the natural order and in FP64 -- its own cell and the other-colour
+// cell beside it in the row (i ^ 1), whose pass came before -- so no separate
+// pass reads it again.
 // (OT: the result's type, FP64 or float pairs)
 template <typename OT>
 __device__ __forceinline__ OT widen_out(float v)
@@ -116,9 +117,7 @@ __global__ void __launch_bounds__(128) k3_rbgs_pk(int nx, int ny, int nz, const 
         if (ih >= half) continue;
         const int c = r * nx + 2 * ih + p, q = r * half + ih;
         x[color * nh + q] = v[u];
-        if (first) {
-            x[(1 - color) * nh + q] = T(0);  // (i ^ 1, j, k)
-        } else if (out) {
+        if (!first && out) {
             out[c] = widen_out<OT>(v[u]);
             out[c ^ 1] = widen_out<OT>(w[u]);
         }
@@ -195,14 +194,16 @@ __global__ void __launch_bounds__(256) k3_prolong(int nx, int ny, int nz, T *__r
 
 // The same into a colour-packed level from a coarse x that is colour-packed
 // when cpk: threads along the packed rows, (j, k) = (blockIdx.y, blockIdx.z),
-// the colour in the upper half of blockIdx.x (nbx blocks per row and colour).
+// nbx blocks per row and colour, colours c0.. in turn along blockIdx.x.  c0 = 1
+// (post-smoothing follows): the black cells only -- the red pass that comes next
+// reads the black values and never the red cells' own.
 template <typename T>
 __global__ void __launch_bounds__(128) k3_prolong_pk(int nx, int ny, int nz, T *__restrict__ x,
-                                                     const T *__restrict__ xc, int cpk, int nbx)
+                                                     const T *__restrict__ xc, int cpk, int nbx, int c0)
 {
     pdl_entry();
-    const int col = blockIdx.x >= nbx ? 1 : 0, half = nx >> 1, j = blockIdx.y, k = blockIdx.z;
-    const int ih = (blockIdx.x - col * nbx) * blockDim.x + threadIdx.x;
+    const int col = c0 + (blockIdx.x >= nbx ? 1 : 0), half = nx >> 1, j = blockIdx.y, k = blockIdx.z;
+    const int ih = (blockIdx.x - (col - c0) * nbx) * blockDim.x + threadIdx.x;
     if (ih >= half) return;
     const int i = 2 * ih + ((j + k + col) & 1);
     x[(col * nz * ny + k * ny + j) * half + ih] += xc[ix3(cpk, nx >> 1, ny >> 1, nz >> 1, i >> 1, j >> 1, k >> 1)];
@@ -573,7 +574,9 @@ bool vcycle3_unfused(wec_poisson *P, Level<T> *L, const T *b0, T *x0, const int 
         }
         for (int q = 0; q < P->nu1; ++q)
             for (int color = 0; color < 2; ++color) {
-                WEC_PROF("mg3_rbgs", l, (2.0 * n + nf) * ts, st);
+                // (the red pass from zero reads no neighbours: b, 1/d in, x out)
+                WEC_PROF(q == 0 && color == 0 ? "mg3_rbgs_from0" : "mg3_rbgs", l,
+                         (q == 0 && color == 0 ? 1.5 * n : 2.0 * n + nf) * ts, st);
                 rbgs(l, A, x, b, bs, xs, color, q == 0 && color == 0, (OT *)nullptr, nullptr);
             }
         Level<T> &C = L[l + 1];
@@ -601,12 +604,15 @@ bool vcycle3_unfused(wec_poisson *P, Level<T> *L, const T *b0, T *x0, const int 
         const double n = (double)A.nx * A.ny * A.nz;
         const double nf = (A.nx + 1.0) * A.ny * A.nz + A.nx * (A.ny + 1.0) * A.nz + A.nx * A.ny * (A.nz + 1.0);
         {
-            WEC_PROF("mg3_prolong", l, 2.125 * n * ts, st);
+            // colour-packed, post-smoothing next: the black cells only (their
+            // values are all the next red pass reads; the red cells' are replaced)
+            const int c0 = PK && P->nu2 > 0 ? 1 : 0;
+            WEC_PROF("mg3_prolong", l, (c0 ? 1.125 : 2.125) * n * ts, st);
             if constexpr (PK) {
                 const Split sp = rows(A.nx >> 1, 1);
                 const int tx = sp.tx, nbx = sp.nb;
-                launch_k(k3_prolong_pk<T>, dim3(2 * nbx, A.ny, A.nz), tx, 0, st, A.nx, A.ny, A.nz, x,
-                         (const T *)L[l + 1].x, packed(l + 1), nbx);
+                launch_k(k3_prolong_pk<T>, dim3((2 - c0) * nbx, A.ny, A.nz), tx, 0, st, A.nx, A.ny, A.nz, x,
+                         (const T *)L[l + 1].x, packed(l + 1), nbx, c0);
             } else {
                 launch_k(k3_prolong<T>, nblk((long long)n, TB), TB, 0, st, A.nx, A.ny, A.nz, x, L[l + 1].x, xs);
             }

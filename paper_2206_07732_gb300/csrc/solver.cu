@@ -423,14 +423,17 @@ __device__ __forceinline__ float vt_float(double a) { return d2f_rn(a); }
 __device__ __forceinline__ float vt_float(df64 a) { return a.hi; }  // the nearest float but in exact ties
 
 // The CTA's partials of V_k . w (k < nk <= 32) into bsm[k], in fixed order, over
-// one grid-stride pass that also produces w: wof(c, v) returns w[c] (storing it
-// if it makes it) given v[q] = V_q[c] for q < nk when HOLD (the columns read once
-// per element, kept in registers for the update and the dots); without HOLD
-// (K = 32, where 2 K held values would not fit the register budget) v is unset
-// and the dots read V_q[c] again, from L1 right after the update read it.
-template <int K, typename VT, typename F>
-__device__ __forceinline__ void block_dots_k(const VT *V, long long n, int nk, F &&wof, double (*sh)[KMAXV],
-                                             double *bsm)
+// one pass that also produces w: wof(c, v, i, r) returns w[c] (storing it if it
+// makes it) given v[q] = V_q[c] for q < nk when HOLD (the columns read once per
+// element, kept in registers for the update and the dots); without HOLD (K = 32,
+// where 2 K held values would not fit the register budget) v is unset and the
+// dots read V_q[c] again, from L1 right after the update read it.  The pass is
+// grid-stride over the elements, or (ROWS, nx > 0) over rows of nx elements --
+// row r = blockIdx.x + t gridDim.x, element i along it, c = r nx + i -- so a
+// stencil needs no index division per element.
+template <int K, bool ROWS, typename VT, typename F>
+__device__ __forceinline__ void block_dots_k(const VT *V, long long n, int nx, int nk, F &&wof,
+                                             double (*sh)[KMAXV], double *bsm)
 {
     constexpr bool HOLD = K <= 16;
     constexpr int P2 = K >= 32 ? 5 : K >= 16 ? 4 : K >= 8 ? 3 : K >= 4 ? 2 : K >= 2 ? 1 : 0;
@@ -438,16 +441,24 @@ __device__ __forceinline__ void block_dots_k(const VT *V, long long n, int nk, F
     VT av[K];
 #pragma unroll
     for (int q = 0; q < K; ++q) av[q] = VT(0.0);
-    for (long long c = blockIdx.x * (long long)KT + threadIdx.x; c < n; c += (long long)gridDim.x * KT) {
+    auto elem = [&](long long c, int i, int r) {
         VT v[HOLD ? K : 1];
         if constexpr (HOLD) {
 #pragma unroll
             for (int q = 0; q < K; ++q) v[q] = q < nk ? V[(long long)q * n + c] : VT(0.0);
         }
-        const VT wc = wof(c, v);
+        const VT wc = wof(c, v, i, r);
 #pragma unroll
         for (int q = 0; q < K; ++q)
             if (q < nk) av[q] += (HOLD ? v[HOLD ? q : 0] : V[(long long)q * n + c]) * wc;
+    };
+    if constexpr (ROWS) {
+        const int nrows = (int)(n / nx);
+        for (int r = blockIdx.x; r < nrows; r += gridDim.x)
+            for (int i = threadIdx.x; i < nx; i += KT) elem((long long)r * nx + i, i, r);
+    } else {
+        for (long long c = blockIdx.x * (long long)KT + threadIdx.x; c < n; c += (long long)gridDim.x * KT)
+            elem(c, 0, 0);
     }
     // the thread's sums, FP64 from here on
     double a[K];
@@ -468,25 +479,25 @@ __device__ __forceinline__ void block_dots_k(const VT *V, long long n, int nk, F
 
 // nk <= KB (KB = 8: restarts up to 8, whose kernels hold few values per thread
 // and run more CTAs per SM; KB = 32: any restart)
-template <int KB, typename VT, typename F>
-__device__ __forceinline__ void block_dots(const VT *V, long long n, int nk, F &&wof, double (*sh)[KMAXV],
+template <int KB, bool ROWS = false, typename VT, typename F>
+__device__ __forceinline__ void block_dots(const VT *V, long long n, int nx, int nk, F &&wof, double (*sh)[KMAXV],
                                           double *bsm)
 {
     if (nk <= 1) {
-        block_dots_k<1>(V, n, nk, wof, sh, bsm);
+        block_dots_k<1, ROWS>(V, n, nx, nk, wof, sh, bsm);
     } else if (nk <= 2) {
-        block_dots_k<2>(V, n, nk, wof, sh, bsm);
+        block_dots_k<2, ROWS>(V, n, nx, nk, wof, sh, bsm);
     } else if (nk <= 4) {
-        block_dots_k<4>(V, n, nk, wof, sh, bsm);
+        block_dots_k<4, ROWS>(V, n, nx, nk, wof, sh, bsm);
     } else if constexpr (KB <= 8) {
-        block_dots_k<8>(V, n, nk, wof, sh, bsm);
+        block_dots_k<8, ROWS>(V, n, nx, nk, wof, sh, bsm);
     } else {
         if (nk <= 8)
-            block_dots_k<8>(V, n, nk, wof, sh, bsm);
+            block_dots_k<8, ROWS>(V, n, nx, nk, wof, sh, bsm);
         else if (nk <= 16)
-            block_dots_k<16>(V, n, nk, wof, sh, bsm);
+            block_dots_k<16, ROWS>(V, n, nx, nk, wof, sh, bsm);
         else
-            block_dots_k<32>(V, n, nk, wof, sh, bsm);
+            block_dots_k<32, ROWS>(V, n, nx, nk, wof, sh, bsm);
     }
 }
 
@@ -653,11 +664,18 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, kb_blocks(KB))
     const VT *z = Z + (long long)j * n;
     VT *w = V + (long long)(j + 1) * n;
     const VT sj = VT(sc[j]);  // (once per thread of the grid-stride loop)
-    // w and its dots in one pass (w is not read back)
-    block_dots<KB>(
-        V, n, nk,
-        [&](long long c, const auto &) {
-            const VT r = sj * (d0[c] * z[c] - op_offsum<D, VT>(op, z, c));
+    // w and its dots in one pass (w is not read back); 3D: along the grid's rows
+    block_dots<KB, D == 3>(
+        V, n, op.nx, nk,
+        [&](long long c, const auto &, int i, int row) {
+            VT s;
+            if constexpr (D == 3) {
+                const int k = row / op.ny, j = row - k * op.ny;
+                s = offsum3_at(op.bx, op.by, op.bz, z, op.nx, op.ny, op.nz, i, j, k);
+            } else {
+                s = op_offsum<D, VT>(op, z, c);
+            }
+            const VT r = sj * (d0[c] * z[c] - s);
             w[c] = r;
             return r;
         },
@@ -687,8 +705,8 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, KB <= 8 ? 3 : 
     __syncthreads();
     // the update and the second dots in one pass over the basis (V_k[c] read once)
     block_dots<KB>(
-        V, n, nk,
-        [&](long long c, const auto &v) {
+        V, n, 0, nk,
+        [&](long long c, const auto &v, int, int) {
             constexpr int KH = std::extent<std::remove_reference_t<decltype(v)>>::value;
             VT a = w[c];
             if (nk <= KH) {
