@@ -126,6 +126,15 @@ template <typename R>
 constexpr bool is_f64 = std::is_same<R, double>::value;
 template <typename R>
 constexpr bool is_df = std::is_same<R, df64>::value;
+// v of lane + 1 of the warp (every lane taking part)
+template <typename R>
+__device__ __forceinline__ R shfl_down1(R v)
+{
+    if constexpr (is_df<R>)
+        return R(__shfl_down_sync(0xffffffffu, v.hi, 1), __shfl_down_sync(0xffffffffu, v.lo, 1));
+    else
+        return __shfl_down_sync(0xffffffffu, v, 1);
+}
 // FP64 state <-> working type, the conversions on the integer pipe (df64.cuh)
 template <typename R>
 __device__ __forceinline__ R narrow_r(double d)
@@ -350,13 +359,50 @@ __global__ void __launch_bounds__(128) k3t_materials(Tank3P P, const R *__restri
     chi[q.c] = R(1) - hb;
 }
 
+// The PPM value of s on every face of direction D (x, y, z = 0, 1, 2), upwind by
+// the face velocity: a face value depends on the face alone -- the six cells
+// along D around it and its velocity -- so it is formed once and read by the two
+// cells beside it (k3t_advect) instead of once by each.  One 128-thread row per
+// face row (gridf); F and vel in the face layout of component D.
+template <int D, typename R>
+__global__ void __launch_bounds__(128) k3t_ppm_faces(Tank3P P, const R *__restrict__ s, const R *__restrict__ vel,
+                                                     R dt, Ghost3 G, R *__restrict__ F)
+{
+    pdl_entry();
+    const int nx = P.nx, ny = P.ny, nz = P.nz, nxf = nx + (D == 0), nyf = ny + (D == 1);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    if (i >= nxf) return;
+    const long long f = ((long long)k * nyf + j) * nxf + i;
+    const Tank3C<R> &K = cst3<R>(P);
+    const R dtih = dt * K.ih;
+    // the face lies below cell (i, j, k) along D; its stencil is the cells -3 .. 2
+    // from that cell along D, at fixed offsets (32-bit indices) when all six are
+    // inside, else through sig3 (ghost cells)
+    constexpr int di = D == 0, dj = D == 1, dk = D == 2;
+    const int cd = D == 0 ? i : D == 1 ? j : k, nd = D == 0 ? nx : D == 1 ? ny : nz;
+    const int sd = D == 0 ? 1 : D == 1 ? nx : nx * ny;
+    R a[6];
+    if (cd >= 3 && cd + 2 < nd) {
+        const int c32 = (k * ny + j) * nx + i;
+#pragma unroll
+        for (int m = 0; m < 6; ++m) a[m] = s[c32 + (m - 3) * sd];
+    } else {
+#pragma unroll
+        for (int m = 0; m < 6; ++m) a[m] = sig3<R>(P, s, i + (m - 3) * di, j + (m - 3) * dj, k + (m - 3) * dk, G);
+    }
+    F[f] = ppm_face3<R>(a, vel[f], dtih);
+}
+
 // out = base - dt Q(u, s), then the damping-zone blend (base = s for the plain
 // update; a fixed-point cycle k >= 1 passes sigma^n as base and the means of
-// levels n and n+1,k as s and u)
+// levels n and n+1,k as s and u).  Q = sum over the directions of the cell
+// velocity (the mean of its two faces') times the difference of the upper and
+// lower face values of s (k3t_ppm_faces: Fx, Fy, Fz) over h.
 template <typename R>
-__global__ void __launch_bounds__(128) k3t_advect(Tank3P P, const R *__restrict__ base, const R *__restrict__ s,
+__global__ void __launch_bounds__(128) k3t_advect(Tank3P P, const R *__restrict__ base, const R *__restrict__ Fx,
+                                                  const R *__restrict__ Fy, const R *__restrict__ Fz,
                                                   const R *__restrict__ u, const R *__restrict__ v,
-                                                  const R *__restrict__ w, R dt, Ghost3 G, R *__restrict__ out)
+                                                  const R *__restrict__ w, R dt, R *__restrict__ out)
 {
     pdl_entry();
     Cell3 q;
@@ -365,35 +411,16 @@ __global__ void __launch_bounds__(128) k3t_advect(Tank3P P, const R *__restrict_
     const int nx = P.nx, ny = P.ny, i = q.i, j = q.j, k = q.k;
     const long long r = (long long)k * ny + j, fu = r * (nx + 1) + i, fv = ((long long)k * (ny + 1) + j) * nx + i;
     const long long pl = (long long)nx * ny;
-    const R ih = K.ih, dtih = dt * ih;
-    // cells three or more from every boundary read their stencils at fixed
-    // offsets (no ghosts, 32-bit indices); the others through sig3.  The
-    // directions and the two faces are loops, not unrolled: one copy of the
-    // PPM face code (the float-pair instantiation unrolled six times overflowed
-    // the instruction cache)
-    const bool inner = i >= 3 && i < nx - 3 && j >= 3 && j < ny - 3 && k >= 3 && k < P.nz - 3;
-    const int c32 = (int)q.c;
+    const R ih = K.ih;
     R Q = R(0);
-#pragma unroll 1
-    for (int d = 0; d < 3; ++d) {
-        const int di = d == 0, dj = d == 1, dk = d == 2;
-        const int sd = d == 0 ? 1 : d == 1 ? nx : nx * ny;  // cell stride along d
-        const R *vel = d == 0 ? u + fu : d == 1 ? v + fv : w + q.c;
-        const long long vs = d == 0 ? 1 : d == 1 ? nx : pl;  // face stride along d
-        R F0 = R(0), F1 = R(0);
-#pragma unroll 1
-        for (int f = 0; f < 2; ++f) {
-            R a[6];
 #pragma unroll
-            for (int m = 0; m < 6; ++m) {
-                const int o = f - 3 + m;
-                a[m] = inner ? s[c32 + o * sd] : sig3<R>(P, s, i + o * di, j + o * dj, k + o * dk, G);
-            }
-            const R fv2 = ppm_face3<R>(a, vel[f * vs], dtih);
-            if (f == 0) F0 = fv2; else F1 = fv2;
-        }
+    for (int d = 0; d < 3; ++d) {
+        const long long o = d == 0 ? fu : d == 1 ? fv : q.c;  // the cell's lower face along d
+        const R *vel = (d == 0 ? u : d == 1 ? v : w) + o;
+        const R *Fd = (d == 0 ? Fx : d == 1 ? Fy : Fz) + o;
+        const long long vs = d == 0 ? 1 : d == 1 ? nx : pl;  // face stride along d
         const R vb = scl2<R>(0.5f, vel[0] + vel[vs]);
-        Q = Q + vb * (F1 - F0) * ih;
+        Q = Q + vb * (Fd[vs] - Fd[0]) * ih;
     }
     const R sa = base[q.c] - dt * Q;
     const R al = dampc<R>(P, i);
@@ -624,6 +651,51 @@ __device__ __forceinline__ R frq(const Tank3P &P, const R *__restrict__ a, int c
     return a[((long long)k * ny + j) * nx + i];
 }
 
+// One face of a momentum control volume -- direction d, side s (0 lower, 1
+// upper) -- of comp's CV at face (i, j, k): its mass flux m = U r and momentum
+// flux f = m q, with U the d-velocity at the CV face and r, q the upwind values of
+// the face density and the velocity.  A CV face is shared by the two CVs beside
+// it along d and depends on it alone: side 1 of (i, j, k) is side 0 of the next
+// CV along d, the same values.
+template <bool IN, typename R>
+__device__ __forceinline__ void tface(const Tank3P &P, const R *__restrict__ rfc, const Vel3<R> &V, int comp, int i,
+                                      int j, int k, int d, int s, R &m, R &f)
+{
+#define QV(a, b, c) (comp == 0 ? uq<IN>(P, V.u, a, b, c) : comp == 1 ? vq<IN>(P, V.v, a, b, c) : wq<IN>(P, V.w, V.win, a, b, c))
+    R U;
+    if (d == comp) {  // CV faces at the cell centres on either side
+        const int o = s - 1;
+        U = comp == 0   ? scl2<R>(0.5f, uq<IN>(P, V.u, i + o, j, k) + uq<IN>(P, V.u, i + o + 1, j, k))
+            : comp == 1 ? scl2<R>(0.5f, vq<IN>(P, V.v, i, j + o, k) + vq<IN>(P, V.v, i, j + o + 1, k))
+                        : scl2<R>(0.5f, wq<IN>(P, V.w, V.win, i, j, k + o) + wq<IN>(P, V.w, V.win, i, j, k + o + 1));
+    } else {  // CV faces on the edges: the d-velocity averaged over the comp direction
+        const int e = s;
+        if (d == 0)
+            U = comp == 1 ? scl2<R>(0.5f, uq<IN>(P, V.u, i + e, j - 1, k) + uq<IN>(P, V.u, i + e, j, k))
+                          : scl2<R>(0.5f, uq<IN>(P, V.u, i + e, j, k - 1) + uq<IN>(P, V.u, i + e, j, k));
+        else if (d == 1)
+            U = comp == 0 ? scl2<R>(0.5f, vq<IN>(P, V.v, i - 1, j + e, k) + vq<IN>(P, V.v, i, j + e, k))
+                          : scl2<R>(0.5f, vq<IN>(P, V.v, i, j + e, k - 1) + vq<IN>(P, V.v, i, j + e, k));
+        else
+            U = comp == 0 ? scl2<R>(0.5f, wq<IN>(P, V.w, V.win, i - 1, j, k + e) + wq<IN>(P, V.w, V.win, i, j, k + e))
+                          : scl2<R>(0.5f, wq<IN>(P, V.w, V.win, i, j - 1, k + e) + wq<IN>(P, V.w, V.win, i, j, k + e));
+    }
+    const int a0 = s - 1;  // the stencil runs over (base + a0 - 1 .. base + a0 + 2) along d
+    const int di = d == 0, dj = d == 1, dk = d == 2;
+    R rr[4], qq[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int o = a0 - 1 + q;
+        rr[q] = frq<IN>(P, rfc, comp, i + o * di, j + o * dj, k + o * dk);
+        qq[q] = QV(i + o * di, j + o * dj, k + o * dk);
+    }
+    const R r = upw3(rr[0], rr[1], rr[2], rr[3], U);
+    const R qv = upw3(qq[0], qq[1], qq[2], qq[3], U);
+    m = U * r;
+    f = m * qv;
+#undef QV
+}
+
 // rho-breve and C of a momentum control volume: comp 0 u-face, 1 v-face, 2 w-face;
 // the three pairs of CV faces summed x, then y, then z.  rfc: the face
 // densities of component comp; dtih = dt / h.
@@ -633,46 +705,12 @@ __device__ __forceinline__ void transport3(const Tank3P &P, const R *__restrict_
 {
     const R ih = cst3<R>(P).ih;
     R m[6], f[6];
-#define QV(a, b, c) (comp == 0 ? uq<IN>(P, V.u, a, b, c) : comp == 1 ? vq<IN>(P, V.v, a, b, c) : wq<IN>(P, V.w, V.win, a, b, c))
 #pragma unroll
     for (int d = 0; d < 3; ++d)
 #pragma unroll
-        for (int s = 0; s < 2; ++s) {
-            R U;
-            if (d == comp) {  // CV faces at the cell centres on either side
-                const int o = s - 1;
-                U = comp == 0   ? scl2<R>(0.5f, uq<IN>(P, V.u, i + o, j, k) + uq<IN>(P, V.u, i + o + 1, j, k))
-                    : comp == 1 ? scl2<R>(0.5f, vq<IN>(P, V.v, i, j + o, k) + vq<IN>(P, V.v, i, j + o + 1, k))
-                                : scl2<R>(0.5f, wq<IN>(P, V.w, V.win, i, j, k + o) + wq<IN>(P, V.w, V.win, i, j, k + o + 1));
-            } else {  // CV faces on the edges: the d-velocity averaged over the comp direction
-                const int e = s;
-                if (d == 0)
-                    U = comp == 1 ? scl2<R>(0.5f, uq<IN>(P, V.u, i + e, j - 1, k) + uq<IN>(P, V.u, i + e, j, k))
-                                  : scl2<R>(0.5f, uq<IN>(P, V.u, i + e, j, k - 1) + uq<IN>(P, V.u, i + e, j, k));
-                else if (d == 1)
-                    U = comp == 0 ? scl2<R>(0.5f, vq<IN>(P, V.v, i - 1, j + e, k) + vq<IN>(P, V.v, i, j + e, k))
-                                  : scl2<R>(0.5f, vq<IN>(P, V.v, i, j + e, k - 1) + vq<IN>(P, V.v, i, j + e, k));
-                else
-                    U = comp == 0 ? scl2<R>(0.5f, wq<IN>(P, V.w, V.win, i - 1, j, k + e) + wq<IN>(P, V.w, V.win, i, j, k + e))
-                                  : scl2<R>(0.5f, wq<IN>(P, V.w, V.win, i, j - 1, k + e) + wq<IN>(P, V.w, V.win, i, j, k + e));
-            }
-            const int a0 = s - 1;  // the stencil runs over (base + a0 - 1 .. base + a0 + 2) along d
-            const int di = d == 0, dj = d == 1, dk = d == 2;
-            R rr[4], qq[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int o = a0 - 1 + q;
-                rr[q] = frq<IN>(P, rfc, comp, i + o * di, j + o * dj, k + o * dk);
-                qq[q] = QV(i + o * di, j + o * dj, k + o * dk);
-            }
-            const R r = upw3(rr[0], rr[1], rr[2], rr[3], U);
-            const R qv = upw3(qq[0], qq[1], qq[2], qq[3], U);
-            m[2 * d + s] = U * r;
-            f[2 * d + s] = m[2 * d + s] * qv;
-        }
+        for (int s = 0; s < 2; ++s) tface<IN, R>(P, rfc, V, comp, i, j, k, d, s, m[2 * d + s], f[2 * d + s]);
     rb = frq<IN>(P, rfc, comp, i, j, k) - dtih * (((m[1] - m[0]) + (m[3] - m[2])) + (m[5] - m[4]));
     C = (((f[1] - f[0]) + (f[3] - f[2])) + (f[5] - f[4])) * ih;
-#undef QV
 }
 
 // The viscous operator div[mu (grad u + grad u^T)] of component comp at a face,
@@ -889,16 +927,39 @@ template <int COMP, typename R>
 __global__ void __launch_bounds__(128, 8) k3t_transport(Tank3P P, MomIn<R> M, R *__restrict__ Dout, R *__restrict__ Rout)
 {
     pdl_entry();
-    int i, j, k;
-    long long f;
-    if (!face_of(P, COMP, i, j, k, f)) return;
-    R rb, C;
-    if (interior3(P, i, j, k))
-        transport3<true, R>(P, M.rfc[COMP], M.V, COMP, i, j, k, M.dtih, rb, C);
-    else
-        transport3<false, R>(P, M.rfc[COMP], M.V, COMP, i, j, k, M.dtih, rb, C);
-    Dout[f] = rb;
-    Rout[f] = C;
+    // a warp covers 31 CVs along x: lane l forms the lower x face of CV cv0 + l
+    // and takes the upper one from lane l + 1 (the same face); lane 31 supplies
+    // its lower face only.  (Transport3's terms in its order: the same values.)
+    const int lane = threadIdx.x & 31;
+    const int ncv = P.nx - (COMP == 0 ? 1 : 0);  // solved faces along x in the row
+    const int cv = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 31 + lane;
+    const int i = cv + (COMP == 0 ? 1 : 0), j = blockIdx.y + (COMP == 1 ? 1 : 0), k = blockIdx.z + (COMP == 2 ? 1 : 0);
+    const bool in = interior3(P, i, j, k);
+    const R *rfc = M.rfc[COMP];
+    R m0 = R(0), f0 = R(0);
+    if (cv <= ncv) {
+        if (in)
+            tface<true, R>(P, rfc, M.V, COMP, i, j, k, 0, 0, m0, f0);
+        else
+            tface<false, R>(P, rfc, M.V, COMP, i, j, k, 0, 0, m0, f0);
+    }
+    const R m1 = shfl_down1<R>(m0), f1 = shfl_down1<R>(f0);
+    if (lane == 31 || cv >= ncv) return;
+    R m[4], f[4], r0;
+    if (in) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) tface<true, R>(P, rfc, M.V, COMP, i, j, k, 1 + q / 2, q & 1, m[q], f[q]);
+        r0 = frq<true>(P, rfc, COMP, i, j, k);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) tface<false, R>(P, rfc, M.V, COMP, i, j, k, 1 + q / 2, q & 1, m[q], f[q]);
+        r0 = frq<false>(P, rfc, COMP, i, j, k);
+    }
+    const long long fi = COMP == 0   ? ((long long)k * P.ny + j) * (P.nx + 1) + i
+                         : COMP == 1 ? ((long long)k * (P.ny + 1) + j) * P.nx + i
+                                     : ((long long)k * P.ny + j) * P.nx + i;
+    Dout[fi] = r0 - M.dtih * (((m1 - m0) + (m[1] - m[0])) + (m[3] - m[2]));
+    Rout[fi] = (((f1 - f0) + (f[1] - f[0])) + (f[3] - f[2])) * cst3<R>(P).ih;
 }
 template <int COMP, typename R>
 __global__ void __launch_bounds__(128) k3t_momentum_finish(Tank3P P, MomIn<R> M, R *__restrict__ Dout,
@@ -1299,6 +1360,30 @@ dim3 gridf(const Tank3P &P, int comp)
     return dim3((P.nx + (comp == 0) + 127) / 128, P.ny + (comp == 1), P.nz + (comp == 2));
 }
 
+// sigma advected: the face values of s in the three directions into F (face
+// layouts of u, v, w), then the cells' update from them into out
+template <typename R>
+void advect3(const Tank3P &P, const size_t nf[3], const R *base, const R *s, const Vel3<R> &V, R dt,
+             const Ghost3 &G, R *const F[3], R *out, cudaStream_t st)
+{
+    const double nc = (double)P.nx * P.ny * P.nz;
+    {
+        WEC_PROF("tank3_advect_faces", 0, sizeof(R) * (nc + 2.0 * nf[0]), st);
+        launch_k(k3t_ppm_faces<0, R>, gridf(P, 0), 128, 0, st, P, s, V.u, dt, G, F[0]);
+    }
+    {
+        WEC_PROF("tank3_advect_faces", 1, sizeof(R) * (nc + 2.0 * nf[1]), st);
+        launch_k(k3t_ppm_faces<1, R>, gridf(P, 1), 128, 0, st, P, s, V.v, dt, G, F[1]);
+    }
+    {
+        WEC_PROF("tank3_advect_faces", 2, sizeof(R) * (nc + 2.0 * nf[2]), st);
+        launch_k(k3t_ppm_faces<2, R>, gridf(P, 2), 128, 0, st, P, s, V.w, dt, G, F[2]);
+    }
+    WEC_PROF("tank3_advect", 0, sizeof(R) * (2.0 * nc + 2.0 * (nf[0] + nf[1] + nf[2])), st);
+    launch_k(k3t_advect<R>, grid3(P), 128, 0, st, P, base, (const R *)F[0], (const R *)F[1], (const R *)F[2], V.u,
+             V.v, V.w, dt, out);
+}
+
 int tank3_check(const wec_tank3 *T)
 {
     if (!T) return fail(WEC_ERR_INVALID, "tank3 is NULL");
@@ -1540,8 +1625,10 @@ static int tank3_step_impl(wec_tank3 *T, Work3<R> &W, double dt, double pto_forc
             Ga = Gh;
         }
         {
-            WEC_PROF("tank3_advect", 0, sizeof(R) * (2.0 * T->nc + T->nu + T->nv + T->nw), st);
-            launch_k(k3t_advect<R>, grid3(P), 128, 0, st, P, (const R *)W.sig, sadv, Vt.u, Vt.v, Vt.w, dt, Ga, W.tmp);
+            // (the face values in the Jacobi buffers B: free until the momentum system)
+            const size_t nfa[3] = {T->nu, T->nv, T->nw};
+            R *const Fs[3] = {W.B[0], W.B[1], W.B[2]};
+            advect3<R>(P, nfa, (const R *)W.sig, sadv, Vt, dt, Ga, Fs, W.tmp, st);
         }
         section(3);
         if (int e = reinit_buf<R>(T, W.tmp, W.s0, W.s1, T->opts.n_reinit, t1)) return e;
@@ -1578,7 +1665,8 @@ static int tank3_step_impl(wec_tank3 *T, Work3<R> &W, double dt, double pto_forc
                 auto k2 = c == 0 ? k3t_momentum_finish<0, R>
                           : c == 1 ? k3t_momentum_finish<1, R>
                                    : k3t_momentum_finish<2, R>;
-                launch_k(k1, gc[c], 128, 0, st, P, M, W.D[c], W.R3[c]);
+                const dim3 gt((nx - (c == 0 ? 1 : 0) + 123) / 124, gc[c].y, gc[c].z);  // 4 warps x 31 CVs
+                launch_k(k1, gt, 128, 0, st, P, M, W.D[c], W.R3[c]);
                 launch_k(k2, gc[c], 128, 0, st, P, M, W.D[c], W.R3[c]);
             } else {
                 auto kern = c == 0 ? k3t_momentum<0, R> : c == 1 ? k3t_momentum<1, R> : k3t_momentum<2, R>;
@@ -2051,10 +2139,14 @@ int wec_tank3_advect(wec_tank3 *T, double dt, double t)
     if (int e = tank3_check(T)) return e;
     if (!(dt >= 0.0)) return fail(WEC_ERR_INVALID, "tank3_advect: dt must be >= 0");
     {
-        WEC_PROF("tank3_advect", 0, 8.0 * (2.0 * T->nc + T->nu + T->nv + T->nw), T->st);
-        launch_k(k3t_advect<double>, grid3(T->P), 128, 0, T->st, T->P, (const double *)T->sig,
-                 (const double *)T->sig, (const double *)T->u, (const double *)T->v, (const double *)T->w, dt,
-                 ghost_at(T, t), T->tmp);
+        // the face values in stream-ordered scratch (a level-set tank has no step buffers)
+        const size_t nfa[3] = {T->nu, T->nv, T->nw};
+        double *F = nullptr;
+        WEC_CK(cudaMallocAsync(&F, (nfa[0] + nfa[1] + nfa[2]) * 8, T->st));
+        double *const Fs[3] = {F, F + nfa[0], F + nfa[0] + nfa[1]};
+        advect3<double>(T->P, nfa, (const double *)T->sig, (const double *)T->sig,
+                        Vel3<double>{T->u, T->v, T->w, nullptr}, dt, ghost_at(T, t), Fs, T->tmp, T->st);
+        WEC_CK(cudaFreeAsync(F, T->st));
     }
     WEC_CK(cudaGetLastError());
     std::swap(T->sig, T->tmp);
