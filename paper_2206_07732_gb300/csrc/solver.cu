@@ -151,6 +151,19 @@ __global__ void k_to_pairs(long long n, const double *__restrict__ in, df64 *__r
     if (c < n) out[c] = from_double(in[c]);
 }
 
+// both lower-precision copies of an FP64 array in one pass: float pairs and FP32
+// (the pair's leading float is the nearest float, the FP32 copy's value)
+__global__ void k_to_pairs_f32(long long n, const double *__restrict__ in, df64 *__restrict__ out,
+                               float *__restrict__ out32)
+{
+    pdl_entry();
+    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    const df64 p = from_double(in[c]);
+    out[c] = p;
+    out32[c] = p.hi;
+}
+
 template <typename TO, typename TI>
 __global__ void k_convert(long long n, const TI *__restrict__ in, TO *__restrict__ out, const int *insel)
 {
@@ -1644,21 +1657,14 @@ int poisson_build3(wec_poisson *P, cudaStream_t st)
         launch_k(k3_diag0, nblk(n, 256), 256, 0, st, P->nx, P->ny, P->nz, P->L64[0].bu, P->L64[0].bv, P->L64[0].bw,
                  P->d0);
     }
-    if (P->kdf) {  // the pair copies of the level-0 faces and diagonal
-        Level<double> &A = P->L64[0];
-        const long long nf[3] = {(A.nx + 1ll) * A.ny * A.nz, A.nx * (A.ny + 1ll) * A.nz,
-                                 (long long)A.nx * A.ny * (A.nz + 1)};
-        const double *src[3] = {A.bu, A.bv, A.bw};
-        for (int q = 0; q < 3; ++q) {
-            WEC_PROF("convert", 0, 16.0 * nf[q], st);
-            launch_k(k_to_pairs, nblk(nf[q], 256), 256, 0, st, nf[q], src[q], (df64 *)P->kdf_face[q]);
-        }
+    if (P->kdf) {  // the pair copy of the level-0 diagonal (the faces' with their FP32 copies below)
         WEC_PROF("convert", 0, 16.0 * n, st);
         launch_k(k_to_pairs, nblk(n, 256), 256, 0, st, n, (const double *)P->d0, (df64 *)P->kdf_d0);
     }
     int e;
     if (P->prec == WEC_PREC_MIXED) {
-        // the V-cycle is FP32 throughout: level-0 faces converted once
+        // the V-cycle is FP32 throughout: level-0 faces converted once (float
+        // pairs in the same pass for the pair Arnoldi step)
         Level<double> &A = P->L64[0];
         Level<float> &F = P->L32[0];
         const long long nf[3] = {(A.nx + 1ll) * A.ny * A.nz, A.nx * (A.ny + 1ll) * A.nz,
@@ -1666,8 +1672,14 @@ int poisson_build3(wec_poisson *P, cudaStream_t st)
         const double *src[3] = {A.bu, A.bv, A.bw};
         float *dst[3] = {F.bu, F.bv, F.bw};
         for (int q = 0; q < 3; ++q) {
-            WEC_PROF("convert", 0, 12.0 * nf[q], st);
-            launch_k(k_convert<float, double>, nblk(nf[q], 256), 256, 0, st, nf[q], src[q], dst[q], nullptr);
+            if (P->kdf) {
+                WEC_PROF("convert", 0, 20.0 * nf[q], st);
+                launch_k(k_to_pairs_f32, nblk(nf[q], 256), 256, 0, st, nf[q], src[q], (df64 *)P->kdf_face[q],
+                         dst[q]);
+            } else {
+                WEC_PROF("convert", 0, 12.0 * nf[q], st);
+                launch_k(k_convert<float, double>, nblk(nf[q], 256), 256, 0, st, nf[q], src[q], dst[q], nullptr);
+            }
         }
         e = build_hierarchy3<float>(P, P->L32, P->lu32, st);
     } else {

@@ -1087,9 +1087,13 @@ __global__ void __launch_bounds__(128) k3t_rhs(Tank3P P, Vel3<R> S, double *__re
     const int nx = P.nx, ny = P.ny;
     const long long fu = ((long long)q.k * ny + q.j) * (nx + 1) + q.i, fv = ((long long)q.k * (ny + 1) + q.j) * nx + q.i;
     const long long pl = (long long)nx * ny;
-    rhs[q.c] = -P.h * (((widen_r<R>(S.u[fu + 1]) - widen_r<R>(S.u[fu])) +
-                        (widen_r<R>(S.v[fv + nx]) - widen_r<R>(S.v[fv]))) +
-                       (widen_r<R>(S.w[q.c + pl]) - widen_r<R>(S.w[q.c])));
+    if constexpr (is_df<R>) {  // the sum in pairs, widened once (two FP64 operations, not twelve)
+        rhs[q.c] = -P.h * widen_r<R>(((S.u[fu + 1] - S.u[fu]) + (S.v[fv + nx] - S.v[fv])) + (S.w[q.c + pl] - S.w[q.c]));
+    } else {
+        rhs[q.c] = -P.h * (((widen_r<R>(S.u[fu + 1]) - widen_r<R>(S.u[fu])) +
+                            (widen_r<R>(S.v[fv + nx]) - widen_r<R>(S.v[fv]))) +
+                           (widen_r<R>(S.w[q.c + pl]) - widen_r<R>(S.w[q.c])));
+    }
 }
 
 // u^{n+1} = u* - beta grad phi in FP64 (top w face: the ghost -phi); p += phi
