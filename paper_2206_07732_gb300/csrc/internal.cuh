@@ -18,7 +18,7 @@ constexpr int kInvMax = 32;         // coarsest levels up to this size also get 
 constexpr int kMaxCoarse = 512;      // cells on the coarsest multigrid level
 constexpr int kRedBlocks = 304;      // partial-sum blocks of the step's reductions (2 x 152 SMs)
 constexpr int kRedThreads = 256;
-constexpr int kKrylovBlocks = 608;   // max CTAs of the Krylov reduction kernels (4 x 152 SMs)
+constexpr int kKrylovBlocks = 912;   // max CTAs of the Krylov reduction kernels (6 x 152 SMs)
 
 void set_error(const std::string &msg);
 int fail(int code, const std::string &msg);

@@ -24,7 +24,7 @@ namespace wec {
 namespace {
 
 constexpr long long kNoAllocMaxCells = 1LL << 28;          // largest nx * ny accepted
-constexpr int kNoAllocBlocks = kKrylovBlocks;              // partial sums
+constexpr int kNoAllocBlocks = 608;                        // partial sums (4 x 152 SMs)
 constexpr int kNoAllocDoubles = kNoAllocBlocks + 32;
 constexpr int kNoAllocMaxDevices = 64;
 

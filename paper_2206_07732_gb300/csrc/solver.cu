@@ -500,7 +500,7 @@ __device__ __forceinline__ void block_dots(const VT *V, long long n, int nx, int
         block_dots_k<1, ROWS>(V, n, nx, nk, wof, sh, bsm);
     } else if (nk <= 2) {
         block_dots_k<2, ROWS>(V, n, nx, nk, wof, sh, bsm);
-    } else if (nk <= 4) {
+    } else if (nk <= 4 || KB <= 4) {  // (KB <= 4: nk <= 4)
         block_dots_k<4, ROWS>(V, n, nx, nk, wof, sh, bsm);
     } else if constexpr (KB <= 8) {
         block_dots_k<8, ROWS>(V, n, nx, nk, wof, sh, bsm);
@@ -517,7 +517,7 @@ __device__ __forceinline__ void block_dots(const VT *V, long long n, int nx, int
 // CTAs per SM the matrix-vector kernel is compiled for: 4 (64 registers) where
 // the dot products hold at most 8 sums per thread, else 2 (the Gram-Schmidt
 // kernel, holding the basis values as well: 3 and 2)
-constexpr int kb_blocks(int KB) { return KB <= 8 ? 4 : 2; }
+constexpr int kb_blocks(int KB) { return KB <= 4 ? 6 : KB <= 8 ? 4 : 2; }
 
 __device__ __forceinline__ void set_cond(unsigned long long h, int use, unsigned int v)
 {
@@ -704,7 +704,7 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, kb_blocks(KB))
 // First Gram-Schmidt update w -= sum_k h1_k v_k = w - sum_k (h1_k s_k) u_k, then
 // h2_k = v_k . w.
 template <int KB, typename VT = double>
-__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, KB <= 8 ? 3 : 2)
+__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, KB <= 4 ? 4 : KB <= 8 ? 3 : 2)
     k_orth_dots(long long n, VT *V, const double *__restrict__ sc, const double *__restrict__ h1, double *part,
                 double *h2, KState *ks)
 {
@@ -748,7 +748,7 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, KB <= 8 ? 3 : 
 // iteration cap, breakdown, or full basis), advances j otherwise, and sets the
 // IF condition.
 template <typename VT = double>
-__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 4)
+__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, std::is_same<VT, double>::value ? 4 : 6)
     k_orth_norm(long long n, VT *V, double *sc, float *__restrict__ b32, const double *__restrict__ h1,
                 const double *__restrict__ h2, double *part, KState *ks, double *H, double *cs, double *sn,
                 double *g, unsigned long long hif, int use)
@@ -1228,6 +1228,7 @@ struct KGrids {
     int bnorm = kCl, on = kCl, res[2] = {kCl, kCl}, mv[2][2] = {{kCl, kCl}, {kCl, kCl}}, od[2] = {kCl, kCl};
     // the float-pair Arnoldi kernels (3D): residual, matvec[restart <= 8], orth dots[restart <= 8], orth norm
     int res_df = kCl, mv_df[2] = {kCl, kCl}, od_df[2] = {kCl, kCl}, on_df = kCl;
+    int mv_df4 = kCl, od_df4 = kCl;  // their variants for at most 4 basis vectors (more CTAs per SM)
 };
 KGrids g_kg;
 
@@ -1250,10 +1251,11 @@ int clusters_resident(K kern, int *out)
 
 int set_kgrid_max()
 {
-    auto r = [](auto kern, int &g) {
+    // at most 4 CTAs per SM (608), the four-vector pair kernels 6 (912)
+    auto r = [](auto kern, int &g, int cap = 4 * 152) {
         int c = 0;
         if (int e = clusters_resident(kern, &c)) return e;
-        g = std::max(1, std::min(c, kKrylovBlocks / kCl)) * kCl;
+        g = std::max(1, std::min(c, cap / kCl)) * kCl;
         return (int)WEC_OK;
     };
     KGrids &k = g_kg;
@@ -1270,9 +1272,11 @@ int set_kgrid_max()
     if (!e) e = r(k_residual_norm<3, df64>, k.res_df);
     if (!e) e = r(k_matvec_dots<3, 32, df64>, k.mv_df[0]);
     if (!e) e = r(k_matvec_dots<3, 8, df64>, k.mv_df[1]);
+    if (!e) e = r(k_matvec_dots<3, 4, df64>, k.mv_df4, kKrylovBlocks);
+    if (!e) e = r(k_orth_dots<4, df64>, k.od_df4, kKrylovBlocks);
     if (!e) e = r(k_orth_dots<32, df64>, k.od_df[0]);
     if (!e) e = r(k_orth_dots<8, df64>, k.od_df[1]);
-    if (!e) e = r(k_orth_norm<df64>, k.on_df);
+    if (!e) e = r(k_orth_norm<df64>, k.on_df, kKrylovBlocks);
     return e;
 }
 
@@ -1282,7 +1286,7 @@ int set_kgrid_max()
 // the partials shorten the final reduction.
 int kgrid(long long n, int gmax)
 {
-    if (n <= (1ll << 22)) gmax = std::min(gmax, kKrylovBlocks / 2);
+    if (n <= (1ll << 22)) gmax = std::min(gmax, 2 * 152);
     const long long g = std::min<long long>(nblk(n, KT), gmax);
     return (int)((g + kCl - 1) / kCl * kCl);
 }
@@ -1346,8 +1350,11 @@ void enqueue_begin(wec_poisson *P, const double *b, double *x, double rtol, int 
 
 // One Arnoldi step j (preconditioner, matvec, CGS2 in place in V's column j+1,
 // Givens).  Algorithmic bytes of the Krylov kernels are counted at the largest
-// j (m - 1).
-void enqueue_body(wec_poisson *P, unsigned long long hif, int use, cudaStream_t st)
+// j (m - 1).  jh: j when the host knows it (a host-polled solve reads the state
+// after every step), else -1; with j + 1 <= 4 the pair Arnoldi step takes the
+// kernels compiled for at most four basis vectors (fewer registers, more CTAs
+// per SM; the kernels still read j on the device).
+void enqueue_body(wec_poisson *P, unsigned long long hif, int use, cudaStream_t st, int jh = -1)
 {
     const long long n = ncells(P);
     const double nf = nfaces(P);
@@ -1357,16 +1364,18 @@ void enqueue_body(wec_poisson *P, unsigned long long hif, int use, cudaStream_t 
     // the mixed V-cycle reads u_j in FP32, written beside it by k_residual_norm / k_orth_norm
     if (P->kdf) {  // (3D, FP32 V-cycles) the float-pair Arnoldi step
         vcycle3_t<float, df64>(P, P->L32, P->L32[0].b, (df64 *)P->Z, nullptr, &P->ks->j, st);
+        const bool k4 = jh >= 0 && jh + 1 <= 4;
         {
             WEC_PROF("krylov_matvec_dots", -1, 8.0 * (3.0 * n + nf) + 8.0 * n * m, st);
-            launch_k(kb8 ? k_matvec_dots<3, 8, df64> : k_matvec_dots<3, 32, df64>, kgrid(n, g_kg.mv_df[kb8]), KT, 0,
-                     st, op0df(P), (const df64 *)P->kdf_d0, (const df64 *)P->Z, (df64 *)P->V, P->sc, P->part, h1,
-                     P->ks);
+            auto kern = k4 ? k_matvec_dots<3, 4, df64> : kb8 ? k_matvec_dots<3, 8, df64> : k_matvec_dots<3, 32, df64>;
+            launch_k(kern, kgrid(n, k4 ? g_kg.mv_df4 : g_kg.mv_df[kb8]), KT, 0, st, op0df(P),
+                     (const df64 *)P->kdf_d0, (const df64 *)P->Z, (df64 *)P->V, P->sc, P->part, h1, P->ks);
         }
         {
             WEC_PROF("krylov_orth_dots", -1, 8.0 * n * (m + 2), st);
-            launch_k(kb8 ? k_orth_dots<8, df64> : k_orth_dots<32, df64>, kgrid(n, g_kg.od_df[kb8]), KT, 0, st, n,
-                     (df64 *)P->V, P->sc, h1, P->part, h2, P->ks);
+            auto kern = k4 ? k_orth_dots<4, df64> : kb8 ? k_orth_dots<8, df64> : k_orth_dots<32, df64>;
+            launch_k(kern, kgrid(n, k4 ? g_kg.od_df4 : g_kg.od_df[kb8]), KT, 0, st, n, (df64 *)P->V, P->sc, h1,
+                     P->part, h2, P->ks);
         }
         WEC_PROF("krylov_orth_norm", -1, 8.0 * n * (m + 2) + 4.0 * n, st);
         launch_k(k_orth_norm<df64>, kgrid(n, g_kg.on_df), KT, 0, st, n, (df64 *)P->V, P->sc, P->L32[0].b, h1, h2,
@@ -1790,7 +1799,7 @@ int poisson_solve(wec_poisson *P, const double *b, double *x, double rtol, int m
     WEC_CK(cudaGetLastError());
     if (int e = read_state(P, st)) return e;
     while (!P->ksh->done) {
-        enqueue_body(P, 0ull, 0, st);
+        enqueue_body(P, 0ull, 0, st, P->ksh->j);
         WEC_CK(cudaGetLastError());
         if (int e = read_state(P, st)) return e;
         if (P->ksh->cycle_end) {
