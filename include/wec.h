@@ -539,7 +539,9 @@ int wec_jonswap(double Hs, double Tp, double gamma, int ncomp, double *amp, doub
  * bits.
  * "tank3_split_momentum" (default 1): the 3D momentum system per component as
  * two kernels (transport terms, then viscous terms and assembly); 0: one
- * kernel.  Both compute the same values.
+ * kernel.  Both form the same terms: the same bits with double-float stencils,
+ * the same values to rounding in FP64 and FP32 (where the compiler may fuse a
+ * product into a sum differently in each kernel).
  * Options apply to solvers created, graphs captured and solves started after the
  * call.  Unknown name or value out of range: WEC_ERR_INVALID. */
 int wec_set_option(const char *name, int value);

@@ -364,33 +364,39 @@ __global__ void __launch_bounds__(128) k3t_materials(Tank3P P, const R *__restri
 // along D around it and its velocity -- so it is formed once and read by the two
 // cells beside it (k3t_advect) instead of once by each.  One 128-thread row per
 // face row (gridf); F and vel in the face layout of component D.
+// (x: the grid covers nx faces per row, the thread of face 0 forming the last
+// one, nx, as well -- an extra block per row would hold one face)
 template <int D, typename R>
 __global__ void __launch_bounds__(128) k3t_ppm_faces(Tank3P P, const R *__restrict__ s, const R *__restrict__ vel,
                                                      R dt, Ghost3 G, R *__restrict__ F)
 {
     pdl_entry();
     const int nx = P.nx, ny = P.ny, nz = P.nz, nxf = nx + (D == 0), nyf = ny + (D == 1);
-    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
-    if (i >= nxf) return;
-    const long long f = ((long long)k * nyf + j) * nxf + i;
+    const int i0 = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    if (i0 >= nx) return;
     const Tank3C<R> &K = cst3<R>(P);
     const R dtih = dt * K.ih;
     // the face lies below cell (i, j, k) along D; its stencil is the cells -3 .. 2
     // from that cell along D, at fixed offsets (32-bit indices) when all six are
     // inside, else through sig3 (ghost cells)
     constexpr int di = D == 0, dj = D == 1, dk = D == 2;
-    const int cd = D == 0 ? i : D == 1 ? j : k, nd = D == 0 ? nx : D == 1 ? ny : nz;
     const int sd = D == 0 ? 1 : D == 1 ? nx : nx * ny;
-    R a[6];
-    if (cd >= 3 && cd + 2 < nd) {
-        const int c32 = (k * ny + j) * nx + i;
+    auto face = [&](int i) {
+        const long long f = ((long long)k * nyf + j) * nxf + i;
+        const int cd = D == 0 ? i : D == 1 ? j : k, nd = D == 0 ? nx : D == 1 ? ny : nz;
+        R a[6];
+        if (cd >= 3 && cd + 2 < nd) {
+            const int c32 = (k * ny + j) * nx + i;
 #pragma unroll
-        for (int m = 0; m < 6; ++m) a[m] = s[c32 + (m - 3) * sd];
-    } else {
+            for (int m = 0; m < 6; ++m) a[m] = s[c32 + (m - 3) * sd];
+        } else {
 #pragma unroll
-        for (int m = 0; m < 6; ++m) a[m] = sig3<R>(P, s, i + (m - 3) * di, j + (m - 3) * dj, k + (m - 3) * dk, G);
-    }
-    F[f] = ppm_face3<R>(a, vel[f], dtih);
+            for (int m = 0; m < 6; ++m) a[m] = sig3<R>(P, s, i + (m - 3) * di, j + (m - 3) * dj, k + (m - 3) * dk, G);
+        }
+        F[f] = ppm_face3<R>(a, vel[f], dtih);
+    };
+    face(i0);
+    if (D == 0 && i0 == 0) face(nx);
 }
 
 // out = base - dt Q(u, s), then the damping-zone blend (base = s for the plain
@@ -1373,7 +1379,7 @@ void advect3(const Tank3P &P, const size_t nf[3], const R *base, const R *s, con
     const double nc = (double)P.nx * P.ny * P.nz;
     {
         WEC_PROF("tank3_advect_faces", 0, sizeof(R) * (nc + 2.0 * nf[0]), st);
-        launch_k(k3t_ppm_faces<0, R>, gridf(P, 0), 128, 0, st, P, s, V.u, dt, G, F[0]);
+        launch_k(k3t_ppm_faces<0, R>, grid3(P), 128, 0, st, P, s, V.u, dt, G, F[0]);
     }
     {
         WEC_PROF("tank3_advect_faces", 1, sizeof(R) * (nc + 2.0 * nf[1]), st);

@@ -72,6 +72,34 @@ def test_steps_match_oracle(shape, body, prec):
     t.close()
 
 
+@pytest.mark.parametrize("prec", [wec.PREC_FP64, wec.PREC_MIXED_DF, wec.PREC_MIXED])
+@pytest.mark.parametrize("shape", [(40, 12, 20), (48, 16, 16)])
+def test_momentum_kernel_forms_agree(shape, prec):
+    # the momentum system as one kernel or two ("tank3_split_momentum"): the
+    # same per-face arithmetic -- the same bits in float pairs, whose products
+    # and sums are explicit; in FP64 and FP32 the compiler may contract a
+    # product into a sum differently in each kernel, so there the fields agree
+    # to rounding
+    c = _cfg(*shape)
+    out = []
+    try:
+        for split in (1, 0):
+            wec.set_option("tank3_split_momentum", split)
+            t = wec.Tank3(c, precision=prec)
+            for _ in range(3):
+                assert t.step(c["dt"])["status"] == 0
+            out.append([t.get(fg) for fg, _, _ in FIELDS])
+            t.close()
+    finally:
+        wec.set_option("tank3_split_momentum", 1)
+    tol = {wec.PREC_MIXED_DF: 0.0, wec.PREC_FP64: 1e-12, wec.PREC_MIXED: 1e-5}[prec]
+    for form, fields in enumerate(out[1:], 1):
+        for (_, _, name), a, b in zip(FIELDS, fields, out[0]):
+            e = rel(a, b, 1e-12)
+            print(f"{shape} prec {prec} form {form} {name}: {e:.2e}")
+            assert e <= tol, (form, name, e)
+
+
 @pytest.mark.parametrize("prec", [wec.PREC_FP64, wec.PREC_MIXED_DF])
 @pytest.mark.parametrize("ncyc", [2, 3])
 def test_fixed_point_cycles_match_oracle(prec, ncyc):
