@@ -39,6 +39,8 @@ struct df64 {
     __host__ __device__ constexpr df64(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
     // from an int: exact for |i| < 2^24 (grid indices), on the FP32 pipe
     __host__ __device__ constexpr explicit df64(int i) : hi((float)i), lo(0.f) {}
+    // from a float: exact (no FP64 conversion)
+    __host__ __device__ constexpr explicit df64(float f) : hi(f), lo(0.f) {}
     __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
 };
 

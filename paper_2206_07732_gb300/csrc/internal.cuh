@@ -130,8 +130,9 @@ struct wec_poisson {
     double *hess = nullptr;     // (m+1) x m Hessenberg, then cs, sn, g, y
     double *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr;
     double *sc = nullptr;       // m+1: 1 / ||u_k|| of the unnormalised basis vectors u_k (V's columns)
-    // Arnoldi arithmetic in float pairs (3D, WEC_PREC_MIXED_DF): V and Z then hold
-    // pairs (8 bytes, as FP64), and the level-0 faces and diagonal have pair copies
+    // Arnoldi arithmetic in float pairs (3D, WEC_PREC_MIXED_DF): V then holds pairs
+    // (8 bytes, as FP64), Z the FP32 V-cycle's columns as floats (n floats apart),
+    // and the level-0 faces and diagonal have pair copies
     bool kdf = false;
     double *kdf_face[3] = {};   // beta_x, beta_y, beta_z as float pairs
     double *kdf_d0 = nullptr;   // the diagonal as float pairs

@@ -85,7 +85,12 @@ __global__ void __launch_bounds__(256) k3_rbgs(int nx, int ny, int nz, const T *
 template <typename OT>
 __device__ __forceinline__ OT widen_out(float v)
 {
-    if constexpr (std::is_same<OT, double>::value) return f2d_exact(v); else return OT(v, 0.f);
+    if constexpr (std::is_same<OT, double>::value)
+        return f2d_exact(v);
+    else if constexpr (std::is_same<OT, float>::value)
+        return v;
+    else
+        return OT(v, 0.f);
 }
 template <typename T, int CPT, typename OT = double>
 __global__ void __launch_bounds__(128) k3_rbgs_pk(int nx, int ny, int nz, const T *__restrict__ bx,
@@ -621,7 +626,7 @@ bool vcycle3_unfused(wec_poisson *P, Level<T> *L, const T *b0, T *x0, const int 
             for (int color = 0; color < 2; ++color) {
                 const bool last = PK && l == 0 && xout && q == P->nu2 - 1 && color == 1;
                 // (+ the FP64 result and the other colour's values it reads)
-                WEC_PROF("mg3_rbgs", l, (2.0 * n + nf) * ts + (last ? 10.0 * n : 0.0), st);
+                WEC_PROF("mg3_rbgs", l, (2.0 * n + nf) * ts + (last ? (2.0 + sizeof(OT)) * n : 0.0), st);
                 rbgs(l, A, x, b, bs, xs, color, 0, last ? xout : (OT *)nullptr, last ? osel : nullptr);
                 wrote = wrote || last;
             }
@@ -640,12 +645,15 @@ void vcycle3_t(wec_poisson *P, Level<T> *L, const T *b0, TO *x0, const int *bsel
         static_assert(std::is_same<TO, double>::value, "an FP64 V-cycle delivers FP64");
         vcycle3_unfused<T>(P, L, b0, x0, bsel, xsel, st);
     } else {
-        // an FP64 (or float-pair) result is written by the last level-0 pass where there is one
+        // the natural-order result (FP64, FP32 or float pairs) is written by the
+        // last level-0 pass where there is one
         if constexpr (std::is_same<TO, float>::value) {
-            vcycle3_unfused<T>(P, L, b0, L[0].x, bsel, nullptr, st);
-        } else {
-            if (vcycle3_unfused<T, TO>(P, L, b0, L[0].x, bsel, nullptr, st, x0, xsel)) return;
+            if (x0 == L[0].x) {
+                vcycle3_unfused<T>(P, L, b0, L[0].x, bsel, nullptr, st);
+                return;
+            }
         }
+        if (vcycle3_unfused<T, TO>(P, L, b0, L[0].x, bsel, nullptr, st, x0, xsel)) return;
         const long long n = (long long)L[0].nx * L[0].ny * L[0].nz;
         WEC_PROF("convert", 0, (4.0 + sizeof(TO)) * n, st);
         launch_k(k3_unpack<TO>, nblk(n, 256), 256, 0, st, L[0].nx, L[0].ny, L[0].nz, (const float *)L[0].x,

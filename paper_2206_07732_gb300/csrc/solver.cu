@@ -664,9 +664,9 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 4)
 // s_k = 1 / ||u_k|| in sc): the new vector w is built in place in column j+1.
 // w = A z_j = s_j A z'_j (z'_j = M u_j, the V-cycle being linear), and the
 // first Gram-Schmidt dot products h1_k = v_k . w = s_k (u_k . w), k <= j.
-template <int D, int KB, typename VT = double>
+template <int D, int KB, typename VT = double, typename ZT = VT>
 __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, kb_blocks(KB))
-    k_matvec_dots(OpT<VT> op, const VT *__restrict__ d0, const VT *__restrict__ Z, VT *V,
+    k_matvec_dots(OpT<VT> op, const VT *__restrict__ d0, const ZT *__restrict__ Z, VT *V,
                   const double *__restrict__ sc, double *part, double *h1, KState *ks)
 {
     pdl_entry();
@@ -674,7 +674,7 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, kb_blocks(KB))
     __shared__ double bsm[KMAXV];
     const long long n = (long long)op.nx * op.ny * op.nz;
     const int j = ks->j, nk = j + 1;
-    const VT *z = Z + (long long)j * n;
+    const ZT *z = Z + (long long)j * n;  // (float pairs: the FP32 V-cycle's columns as floats)
     VT *w = V + (long long)(j + 1) * n;
     const VT sj = VT(sc[j]);  // (once per thread of the grid-stride loop)
     // w and its dots in one pass (w is not read back); 3D: along the grid's rows
@@ -688,7 +688,7 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, kb_blocks(KB))
             } else {
                 s = op_offsum<D, VT>(op, z, c);
             }
-            const VT r = sj * (d0[c] * z[c] - s);
+            const VT r = sj * (d0[c] * VT(z[c]) - s);
             w[c] = r;
             return r;
         },
@@ -835,12 +835,12 @@ __global__ void k_update_x(long long n, const double *__restrict__ y, const VT *
 #pragma unroll 4
         for (int k = 0; k < jd; ++k) a += y[k] * Z[(long long)k * n + c];
         x[c] = a;
-    } else {  // pair columns holding the FP32 V-cycle's values (lo = 0): the same FP64 update
+    } else {  // FP32 columns (the FP32 V-cycle's values, widened exactly): the same FP64 update
         long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
         if (c >= n) return;
         double a = x[c];
 #pragma unroll 4
-        for (int k = 0; k < jd; ++k) a += y[k] * f2d_exact(Z[(long long)k * n + c].hi);
+        for (int k = 0; k < jd; ++k) a += y[k] * f2d_exact(Z[(long long)k * n + c]);
         x[c] = a;
     }
 }
@@ -1270,9 +1270,9 @@ int set_kgrid_max()
     if (!e) e = r(k_orth_dots<32>, k.od[0]);
     if (!e) e = r(k_orth_dots<8>, k.od[1]);
     if (!e) e = r(k_residual_norm<3, df64>, k.res_df);
-    if (!e) e = r(k_matvec_dots<3, 32, df64>, k.mv_df[0]);
-    if (!e) e = r(k_matvec_dots<3, 8, df64>, k.mv_df[1]);
-    if (!e) e = r(k_matvec_dots<3, 4, df64>, k.mv_df4, kKrylovBlocks);
+    if (!e) e = r(k_matvec_dots<3, 32, df64, float>, k.mv_df[0]);
+    if (!e) e = r(k_matvec_dots<3, 8, df64, float>, k.mv_df[1]);
+    if (!e) e = r(k_matvec_dots<3, 4, df64, float>, k.mv_df4, kKrylovBlocks);
     if (!e) e = r(k_orth_dots<4, df64>, k.od_df4, kKrylovBlocks);
     if (!e) e = r(k_orth_dots<32, df64>, k.od_df[0]);
     if (!e) e = r(k_orth_dots<8, df64>, k.od_df[1]);
@@ -1363,13 +1363,15 @@ void enqueue_body(wec_poisson *P, unsigned long long hif, int use, cudaStream_t 
     double *h1 = P->dots, *h2 = P->dots + (kMaxRestart + 2);
     // the mixed V-cycle reads u_j in FP32, written beside it by k_residual_norm / k_orth_norm
     if (P->kdf) {  // (3D, FP32 V-cycles) the float-pair Arnoldi step
-        vcycle3_t<float, df64>(P, P->L32, P->L32[0].b, (df64 *)P->Z, nullptr, &P->ks->j, st);
+        vcycle3_t<float, float>(P, P->L32, P->L32[0].b, (float *)P->Z, nullptr, &P->ks->j, st);
         const bool k4 = jh >= 0 && jh + 1 <= 4;
         {
-            WEC_PROF("krylov_matvec_dots", -1, 8.0 * (3.0 * n + nf) + 8.0 * n * m, st);
-            auto kern = k4 ? k_matvec_dots<3, 4, df64> : kb8 ? k_matvec_dots<3, 8, df64> : k_matvec_dots<3, 32, df64>;
+            WEC_PROF("krylov_matvec_dots", -1, 8.0 * (2.0 * n + nf) + 4.0 * n + 8.0 * n * m, st);
+            auto kern = k4    ? k_matvec_dots<3, 4, df64, float>
+                        : kb8 ? k_matvec_dots<3, 8, df64, float>
+                              : k_matvec_dots<3, 32, df64, float>;
             launch_k(kern, kgrid(n, k4 ? g_kg.mv_df4 : g_kg.mv_df[kb8]), KT, 0, st, op0df(P),
-                     (const df64 *)P->kdf_d0, (const df64 *)P->Z, (df64 *)P->V, P->sc, P->part, h1, P->ks);
+                     (const df64 *)P->kdf_d0, (const float *)P->Z, (df64 *)P->V, P->sc, P->part, h1, P->ks);
         }
         {
             WEC_PROF("krylov_orth_dots", -1, 8.0 * n * (m + 2), st);
@@ -1415,9 +1417,9 @@ void enqueue_close(wec_poisson *P, const double *b, double *x, unsigned long lon
         launch_k(k_backsolve, 1, 1, 0, st, m, P->hess, P->g, P->y, P->sc, P->ks);
     }
     {
-        WEC_PROF("krylov_update_x", -1, 16.0 * n + 8.0 * n * m, st);
+        WEC_PROF("krylov_update_x", -1, 16.0 * n + (P->kdf ? 4.0 : 8.0) * n * m, st);
         if (P->kdf)
-            launch_k(k_update_x<df64>, nblk(n, 256), 256, 0, st, n, P->y, (const df64 *)P->Z, x, P->ks);
+            launch_k(k_update_x<float>, nblk(n, 256), 256, 0, st, n, P->y, (const float *)P->Z, x, P->ks);
         else
             launch_k(k_update_x<double>, nblk(n, 256), 256, 0, st, n, P->y, P->Z, x, P->ks);
     }
