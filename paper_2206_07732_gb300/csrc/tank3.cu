@@ -474,9 +474,20 @@ __device__ __forceinline__ R reinit_rhs3(const Tank3P &P, const R *__restrict__ 
             p1 = sig3<R>(P, f, q.i + di, q.j + dj, q.k + dk, G);
             p2 = sig3<R>(P, f, q.i + 2 * di, q.j + 2 * dj, q.k + 2 * dk, G);
         }
-        const R dm = m2 - scl2<R>(2.f, m1) + c, d0 = m1 - scl2<R>(2.f, c) + p1, dp = c - scl2<R>(2.f, p1) + p2;
-        const R a = (c - m1) + scl2<R>(0.5f, mm3(dm, d0));
-        const R nb = (c - p1) + scl2<R>(0.5f, mm3(d0, dp));  // -b
+        R a, nb;  // nb = -b
+        if constexpr (is_df<R>) {
+            // float pairs: the second differences from the four first differences
+            // (seven pair subtractions instead of nine operations and two
+            // scalings; the same values to the pairs' rounding)
+            const R em = m1 - m2, e0 = c - m1, e1 = p1 - c, ep = p2 - p1;
+            const R dm = e0 - em, d0 = e1 - e0, dp = ep - e1;
+            a = e0 + scl2<R>(0.5f, mm3(dm, d0));
+            nb = scl2<R>(0.5f, mm3(d0, dp)) - e1;
+        } else {
+            const R dm = m2 - scl2<R>(2.f, m1) + c, d0 = m1 - scl2<R>(2.f, c) + p1, dp = c - scl2<R>(2.f, p1) + p2;
+            a = (c - m1) + scl2<R>(0.5f, mm3(dm, d0));
+            nb = (c - p1) + scl2<R>(0.5f, mm3(d0, dp));
+        }
         // pos: the largest of a, -b and 0; else of -a, b and 0
         const R x = pos ? a : -a, y = pos ? nb : -nb;
         R m = positive(x) ? x : R(0);
