@@ -45,6 +45,27 @@ __device__ __forceinline__ T offsum3_pk(const T *bx, const T *by, const T *bz, c
     return s;
 }
 
+// offsum3_pk for the black pass of a sweep from zero: its red neighbours are
+// the values the red pass from zero gives them, (b + 0) (1/d), formed here
+// instead of read -- the same terms in the same order (the same value)
+template <typename T>
+__device__ __forceinline__ T offsum3_pk_z(const T *bx, const T *by, const T *bz, const T *b, int bpk, const T *id,
+                                          int nx, int ny, int nz, int i, int j, int k)
+{
+    const int r = k * ny + j, fx = r * (nx + 1) + i, fy = (r + k) * nx + i, c = r * nx + i, pl = nx * ny;
+    const int half = nx >> 1, ih = i >> 1;
+    const int q0 = (1 - ((i + j + k) & 1)) * nz * ny * half + r * half;  // the other colour's row of the cell
+    auto red = [&](int q, int cn) { return (b[bpk ? q : cn] + T(0)) * id[q]; };
+    T s = T(0);
+    if (i > 0) s = fma3(bx[fx], red(q0 + ((i - 1) >> 1), c - 1), s);
+    if (i < nx - 1) s = fma3(bx[fx + 1], red(q0 + ((i + 1) >> 1), c + 1), s);
+    if (j > 0) s = fma3(by[fy], red(q0 + ih - half, c - nx), s);
+    if (j < ny - 1) s = fma3(by[fy + nx], red(q0 + ih + half, c + nx), s);
+    if (k > 0) s = fma3(bz[c], red(q0 + ih - ny * half, c - pl), s);
+    if (k < nz - 1) s = fma3(bz[c + pl], red(q0 + ih + ny * half, c + pl), s);
+    return s;
+}
+
 // One colour of a red-black sweep on a natural-order level (FP64); thread q ->
 // the q-th cell of the colour.  first != 0: the sweep starts from x = 0, so the
 // red pass writes b / d (the black cells' starting values are never read: a
@@ -92,7 +113,10 @@ __device__ __forceinline__ OT widen_out(float v)
     else
         return OT(v, 0.f);
 }
-template <typename T, int CPT, typename OT = double>
+// Z1: the black pass of the first pre-smoothing sweep with its red pass folded
+// in (offsum3_pk_z; the red values are not stored: with two or more sweeps the
+// next red pass replaces them before anything reads them).
+template <typename T, int CPT, typename OT = double, bool Z1 = false>
 __global__ void __launch_bounds__(128) k3_rbgs_pk(int nx, int ny, int nz, const T *__restrict__ bx,
                                                   const T *__restrict__ by, const T *__restrict__ bz,
                                                   const T *__restrict__ id, T *x, const T *__restrict__ b, int color,
@@ -110,6 +134,8 @@ __global__ void __launch_bounds__(128) k3_rbgs_pk(int nx, int ny, int nz, const 
         const T bv = b[bpk ? xo : r * nx + i];
         if (first) {
             v[u] = (bv + T(0)) * id[xo];
+        } else if constexpr (Z1) {
+            v[u] = (bv + offsum3_pk_z(bx, by, bz, b, bpk, id, nx, ny, nz, i, j, k)) * id[xo];
         } else {
             v[u] = (bv + offsum3_pk(bx, by, bz, x, nx, ny, nz, i, j, k)) * id[xo];
             if (out) w[u] = x[(1 - color) * nh + q];
@@ -508,18 +534,16 @@ bool vcycle3_unfused(wec_poisson *P, Level<T> *L, const T *b0, T *x0, const int 
         return Split{((w + nb * cpt - 1) / (nb * cpt) + 31) / 32 * 32, nb};
     };
     auto rbgs = [&](int l, Level<T> &A, T *x, const T *b, const int *bs, const int *xs, int color, int first,
-                    OT *o, const int *os) {
+                    OT *o, const int *os, bool z1) {
         if constexpr (PK) {
             const int half = A.nx >> 1, cpt = half >= 64 ? 2 : 1;
             const Split sp = rows(half, cpt);
             const int tx = sp.tx;
             const dim3 g(sp.nb, A.ny, A.nz);
-            if (cpt == 2)
-                launch_k(k3_rbgs_pk<T, 2, OT>, g, tx, 0, st, A.nx, A.ny, A.nz, A.bu, A.bv, A.bw, A.id, x, b, color, first,
-                         l > 0 ? 1 : 0, o, os);
-            else
-                launch_k(k3_rbgs_pk<T, 1, OT>, g, tx, 0, st, A.nx, A.ny, A.nz, A.bu, A.bv, A.bw, A.id, x, b, color, first,
-                         l > 0 ? 1 : 0, o, os);
+            auto kern = cpt == 2 ? (z1 ? k3_rbgs_pk<T, 2, OT, true> : k3_rbgs_pk<T, 2, OT, false>)
+                                 : (z1 ? k3_rbgs_pk<T, 1, OT, true> : k3_rbgs_pk<T, 1, OT, false>);
+            launch_k(kern, g, tx, 0, st, A.nx, A.ny, A.nz, A.bu, A.bv, A.bw, A.id, x, b, color, first, l > 0 ? 1 : 0, o,
+                     os);
         } else {
             const int nh = (A.nx >> 1) * A.ny * A.nz;
             launch_k(k3_rbgs<T>, nblk(nh, TB), TB, 0, st, A.nx, A.ny, A.nz, A.bu, A.bv, A.bw, A.id, x, b, color,
@@ -579,10 +603,16 @@ bool vcycle3_unfused(wec_poisson *P, Level<T> *L, const T *b0, T *x0, const int 
         }
         for (int q = 0; q < P->nu1; ++q)
             for (int color = 0; color < 2; ++color) {
-                // (the red pass from zero reads no neighbours: b, 1/d in, x out)
-                WEC_PROF(q == 0 && color == 0 ? "mg3_rbgs_from0" : "mg3_rbgs", l,
-                         (q == 0 && color == 0 ? 1.5 * n : 2.0 * n + nf) * ts, st);
-                rbgs(l, A, x, b, bs, xs, color, q == 0 && color == 0, (OT *)nullptr, nullptr);
+                // packed levels with two or more sweeps: the first sweep's red pass
+                // folded into its black pass (which reads b and 1/d of the red
+                // cells instead of their x); else the red pass from zero reads
+                // no neighbours (b, 1/d in, x out)
+                const bool z1 = PK && P->nu1 >= 2 && q == 0;
+                if (z1 && color == 0) continue;
+                const bool from0 = q == 0;
+                WEC_PROF(from0 ? "mg3_rbgs_from0" : "mg3_rbgs", l,
+                         (z1 ? 2.5 * n + nf : from0 && color == 0 ? 1.5 * n : 2.0 * n + nf) * ts, st);
+                rbgs(l, A, x, b, bs, xs, color, q == 0 && color == 0, (OT *)nullptr, nullptr, z1);
             }
         Level<T> &C = L[l + 1];
         const T *dg = nullptr;
@@ -627,7 +657,7 @@ bool vcycle3_unfused(wec_poisson *P, Level<T> *L, const T *b0, T *x0, const int 
                 const bool last = PK && l == 0 && xout && q == P->nu2 - 1 && color == 1;
                 // (+ the FP64 result and the other colour's values it reads)
                 WEC_PROF("mg3_rbgs", l, (2.0 * n + nf) * ts + (last ? (2.0 + sizeof(OT)) * n : 0.0), st);
-                rbgs(l, A, x, b, bs, xs, color, 0, last ? xout : (OT *)nullptr, last ? osel : nullptr);
+                rbgs(l, A, x, b, bs, xs, color, 0, last ? xout : (OT *)nullptr, last ? osel : nullptr, false);
                 wrote = wrote || last;
             }
     }
