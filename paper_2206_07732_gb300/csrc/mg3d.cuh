@@ -98,11 +98,11 @@ __global__ void __launch_bounds__(256) k3_rbgs(int nx, int ny, int nz, const T *
 // blockIdx.z), CPT cells of the row per thread, blockDim.x apart: no index
 // division, and every load of the CPT cells is issued before the first store.
 // bpk: b colour-packed too (levels below 0).  first: as in k3_rbgs.
-// out (nullable): the last pass of the V-cycle also writes the finished
-// iterate in the natural order and in FP64 -- its own cell and the other-colour
-// cell beside it in the row (i ^ 1), whose pass came before -- so no separate
-// pass reads it again.
-// (OT: the result's type, FP64 or float pairs)
+// out (nullable): the last pass of the V-cycle writes the finished iterate in
+// the natural order and in OT -- its own cell and the other-colour cell beside
+// it in the row (i ^ 1), whose pass came before -- instead of its packed x
+// (nothing reads that after it), so no separate pass reads it again.
+// (OT: the result's type, FP64, FP32 or float pairs)
 template <typename OT>
 __device__ __forceinline__ OT widen_out(float v)
 {
@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(128) k3_rbgs_pk(int nx, int ny, int nz, const 
         const int ih = (blockIdx.x * CPT + u) * blockDim.x + threadIdx.x;
         if (ih >= half) continue;
         const int c = r * nx + 2 * ih + p, q = r * half + ih;
-        x[color * nh + q] = v[u];
+        if (!out) x[color * nh + q] = v[u];
         if (!first && out) {
             out[c] = widen_out<OT>(v[u]);
             out[c ^ 1] = widen_out<OT>(w[u]);

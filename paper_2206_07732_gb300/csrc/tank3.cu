@@ -1066,17 +1066,14 @@ __global__ void k3t_dirichlet(Tank3P P, const R *__restrict__ uin1, R *u, R *v, 
     if (a < nx * ny) w[a] = R(0);
 }
 
-// a = b = src (n values)
+// a = src (n values)
 template <typename R>
-__global__ void __launch_bounds__(256) k3t_dup(long long n, const R *__restrict__ src, R *__restrict__ a,
-                                               R *__restrict__ b)
+__global__ void __launch_bounds__(256) k3t_copy(long long n, const R *__restrict__ src, R *__restrict__ a)
 {
     pdl_entry();
     const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (q >= n) return;
-    const R v = src[q];
-    a[q] = v;
-    b[q] = v;
+    a[q] = src[q];
 }
 
 // beta = 1 / D on the solved faces, 0 on the walls and the bed (FP64 coefficients);
@@ -1708,12 +1705,12 @@ static int tank3_step_impl(wec_tank3 *T, Work3<R> &W, double dt, double pto_forc
             launch_k(kern, gc[c], 128, 0, st, P, (const R *)W.mu1, E, (const R *)W.D[c], W.R3[c], W.Q[c],
                      R(1.0 / (h * h)));
         }
-        // both sweep buffers start as u^n with the Dirichlet faces at n+1 (the
-        // sweeps write the solved faces only)
+        // the first sweep buffer starts as u^n, both with the Dirichlet faces at
+        // n+1 (the sweeps write every solved face, so the second needs no more)
         const R *src[3] = {W.u, W.v, W.w};
         for (int c = 0; c < 3; ++c) {
-            WEC_PROF("tank3_jacobi", c, 3.0 * b * nf[c], st);
-            launch_k(k3t_dup<R>, nblk((long long)nf[c], 256), 256, 0, st, (long long)nf[c], src[c], W.A[c], W.B[c]);
+            WEC_PROF("tank3_jacobi", c, 2.0 * b * nf[c], st);
+            launch_k(k3t_copy<R>, nblk((long long)nf[c], 256), 256, 0, st, (long long)nf[c], src[c], W.A[c]);
         }
         {
             const long long nd = std::max({(long long)ny * nz, (long long)nx * nz, (long long)nx * ny});
