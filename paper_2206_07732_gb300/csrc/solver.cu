@@ -612,16 +612,30 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(KT, 4)
     const long long n = (long long)op.nx * op.ny * op.nz;
     const bool zero = ks->bn == 0.0;
     double a = 0.0;
-    for (long long c = blockIdx.x * (long long)KT + threadIdx.x; c < n; c += (long long)gridDim.x * KT) {
+    // s: the cell's off-diagonal sum
+    auto cell = [&](long long c, double s) {
         if (zero) {
             x[c] = 0.0;
             w[c] = VT(0.0);
-            continue;
+            return;
         }
-        double r = b[c] - (d0[c] * x[c] - op_offsum<D, double>(op, x, c));
+        const double r = b[c] - (d0[c] * x[c] - s);
         w[c] = vt_from<VT>(r);
         if (b32) b32[c] = d2f_rn(r);  // (float)r on the integer pipe
         a += r * r;
+    };
+    if constexpr (D == 3) {  // along the grid's rows: one index division per row
+        const int nrows = op.ny * op.nz;
+        for (int row = blockIdx.x; row < nrows; row += gridDim.x) {
+            const int k = row / op.ny, j = row - k * op.ny;
+            for (int i = threadIdx.x; i < op.nx; i += KT) {
+                const long long c = (long long)row * op.nx + i;
+                cell(c, zero ? 0.0 : offsum3_at(op.bx, op.by, op.bz, (const double *)x, op.nx, op.ny, op.nz, i, j, k));
+            }
+        }
+    } else {
+        for (long long c = blockIdx.x * (long long)KT + threadIdx.x; c < n; c += (long long)gridDim.x * KT)
+            cell(c, zero ? 0.0 : op_offsum<D, double>(op, x, c));
     }
     a = block_sum(a, sh);
     if (threadIdx.x == 0) bsm[0] = a;
