@@ -37,7 +37,7 @@ def test_tank3d_line_is_compact_and_complete():
     line["batch"] = bench.rnd({"workload": "64 uneven 2D tanks, one graph launch per batch step",
                                "value": 3.1412345678e8, "ms_per_step": 21.912345678, "fp64_value": 1.2123456789e8,
                                "speedup_vs_fp64": 2.5987654321})
-    line["detail_file"] = "gpurun_out/bench_detail.json"
+    line["detail_file"] = "results/run-001/bench_detail.json"
     text = json.dumps(line)
     assert len(text) < 2500, len(text)
     for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
